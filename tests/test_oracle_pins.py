@@ -1,0 +1,494 @@
+"""Pins of the FP64 oracle against facts fixed by the paper and by mathematics.
+
+Each test reaches the expected value by a route that does not reuse the oracle's
+code: values printed in the paper (tests/golden), closed forms (Bloch rotations,
+Clifford Z-propagation, plane waves), matrix exponentials and Kronecker products,
+finite differences, and the exact general parameter-shift rule.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+from scipy.linalg import expm
+
+from paper_2506_23246_b300 import workloads as W
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+X = np.array([[0, 1], [1, 0]], dtype=complex)
+Y = np.array([[0, -1j], [1j, 0]], dtype=complex)
+Z = np.array([[1, 0], [0, -1]], dtype=complex)
+
+
+def _rot_exp(P, t):
+    # exp(-i t P / 2), the half-angle rotation convention pinned by Fig. 3 (<Z> = cos t).
+    return expm(-0.5j * t * P)
+
+
+def _set_head(circ, params, rows):
+    off = W.param_offsets(circ)
+    o, shape = off["head_W"]
+    Wh = np.zeros(shape)
+    for r, i in enumerate(rows):
+        Wh[r, i] = 1.0
+    params = params.astype(np.float64).copy()
+    params[o:o + Wh.size] = Wh.ravel()
+    ob, sb = off["head_b"]
+    params[ob:ob + 3] = 0.0
+    return params
+
+
+def _z_from_state(psi, n):
+    p = np.abs(psi) ** 2
+    k = np.arange(psi.shape[0])
+    return np.array([np.sum(p * (1 - 2 * ((k >> (n - 1 - i)) & 1))) for i in range(n)])
+
+
+# ----------------------------------------------------------------------------- Fig. 3
+
+def _read_fig3():
+    rows = []
+    with open(os.path.join(GOLDEN, "fig3_scalings.txt")) as fh:
+        for line in fh:
+            line = line.strip()
+            if line and not line.startswith("#"):
+                s, a, z = line.split()
+                rows.append((s, float(a), float(z)))
+    return rows
+
+
+@pytest.mark.parametrize("row", _read_fig3())
+def test_fig3_scaling_identities(oracle, row):
+    scale, a, z_expected = row
+    circ = W.circuit(1, 0, 1, ansatz="basic_rot", enc="rx", scale=scale, premap="direct",
+                     n_direct=1)
+    params = _set_head(circ, np.zeros(W.param_offsets(circ)["total"][0]), [0, 0, 0])
+    f, df = oracle.forward(circ, params, np.array([[a, 0.0, 0.0]]))
+    assert abs(f[0, 0] - z_expected) < 1e-13
+    if abs(a) < 0.95:  # d<Z>/da = +1 (acos) or -1 (asin) away from the endpoints
+        assert abs(df[0, 0, 0] - (1.0 if scale == "acos" else -1.0)) < 1e-12
+
+
+@pytest.mark.parametrize("scale", ["none", "pi", "bias"])
+def test_single_qubit_cos_theta(oracle, scale):
+    circ = W.circuit(1, 0, 1, ansatz="basic_rot", enc="rx", scale=scale, premap="direct",
+                     n_direct=1)
+    params = _set_head(circ, np.zeros(W.param_offsets(circ)["total"][0]), [0, 0, 0])
+    for a in np.linspace(-1, 1, 7):
+        theta = {"none": a, "pi": math.pi * a, "bias": (a + 1) * math.pi / 2}[scale]
+        f, _ = oracle.forward(circ, params, np.array([[a, 0.0, 0.0]]))
+        assert abs(f[0, 0] - math.cos(theta)) < 1e-13
+
+
+# ----------------------------------------------------------------------------- Table 1
+
+def test_table1_param_counts(oracle):
+    rows = {}
+    with open(os.path.join(GOLDEN, "table1_param_counts.txt")) as fh:
+        for line in fh:
+            line = line.strip()
+            if line and not line.startswith("#"):
+                parts = line.split()
+                rows[tuple(parts[:-1])] = int(parts[-1])
+    for ans in ("basic_rot", "strong_rot", "noent_rot"):
+        circ = W.circuit(7, 4, 7, ansatz=ans, enc="rx", scale="acos", premap="direct")
+        lay = oracle.param_layout(circ)
+        assert lay["head"] - lay["circuit"] == rows[("quantum", ans)]
+    circ = W.circuit(7, 4, 7, ansatz="strong_rot", premap="rff_mlp", rff_freqs=128,
+                     mlp_width=128, mlp_depth=3)
+    lay = oracle.param_layout(circ)
+    quantum = lay["head"] - lay["circuit"]
+    classical = lay["total"] - lay["fixed"] - quantum
+    assert classical + rows[("learned_period",)] == rows[("classical_qpinn",)]
+    assert lay["total"] == W.param_offsets(circ)["total"][0]
+
+
+# ----------------------------------------------------------------------------- closed forms
+
+def _Rz3(p):
+    return np.array([[math.cos(p), -math.sin(p), 0], [math.sin(p), math.cos(p), 0], [0, 0, 1]])
+
+
+def _Ry3(p):
+    return np.array([[math.cos(p), 0, math.sin(p)], [0, 1, 0], [-math.sin(p), 0, math.cos(p)]])
+
+
+@pytest.mark.parametrize("n,L,enc", [(3, 2, "rx"), (5, 3, "ry"), (10, 4, "rx")])
+def test_noent_bloch_closed_form(oracle, n, L, enc):
+    """No-entanglement ansatz: each qubit's Bloch vector is rotated independently."""
+    circ = W.circuit(n, L, n, ansatz="noent_rot", enc=enc, scale="pi", premap="direct")
+    rng = np.random.default_rng(n)
+    params = W.init_params(circ, n).astype(np.float64)
+    off = W.param_offsets(circ)
+    o, shape = off["circuit"]
+    cp = params[o:o + int(np.prod(shape))].reshape(shape)
+    pts = np.array([[rng.uniform(-1, 1), rng.uniform(-1, 1), rng.uniform(0, 1)]])
+    theta = [math.pi * pts[0, j] if j < 3 else 0.0 for j in range(n)]
+    expect = []
+    for q in range(n):
+        t = theta[q]
+        v = np.array([0.0, -math.sin(t), math.cos(t)]) if enc == "rx" else np.array(
+            [math.sin(t), 0.0, math.cos(t)])
+        for l in range(L):
+            a, b, g = cp[l, q]
+            v = _Rz3(g) @ _Ry3(b) @ _Rz3(a) @ v
+        expect.append(v[2])
+    for start in range(0, n, 3):
+        rows = [min(start + r, n - 1) for r in range(3)]
+        p2 = _set_head(circ, params, rows)
+        f, _ = oracle.forward(circ, p2, pts)
+        for r in range(3):
+            assert abs(f[0, r] - expect[rows[r]]) < 1e-12
+
+
+def _cnot_ring(n, L, ansatz):
+    gates = []
+    for l in range(L):
+        r = 1 + (l % (n - 1)) if ansatz == "strong_rot" else 1
+        gates.append([(i, (i + r) % n) for i in range(n)])
+    return gates
+
+
+@pytest.mark.parametrize("n,L,ansatz", [(4, 2, "basic_ryrz"), (6, 4, "basic_ryrz"),
+                                        (8, 6, "strong_rot"), (10, 8, "strong_rot")])
+def test_clifford_z_propagation(oracle, n, L, ansatz):
+    """With every RY angle zero the layers are diagonal phases times CNOT permutations,
+    so <Z_i> = prod_{j in S_i} cos(theta_j) with S_i the Z-string of Z_i pulled back
+    through the CNOTs over GF(2) (CNOT^dag Z_t CNOT = Z_c Z_t)."""
+    circ = W.circuit(n, L, n, ansatz=ansatz, enc="rx", scale="pi", premap="direct")
+    params = W.init_params(circ, 7).astype(np.float64)
+    off = W.param_offsets(circ)
+    o, shape = off["circuit"]
+    cp = params[o:o + int(np.prod(shape))].reshape(shape)
+    if ansatz == "basic_ryrz":
+        cp[:, :, 0] = 0.0          # RY angles
+    else:
+        cp[:, :, 1] = 0.0          # Rot beta (the RY inside RZ RY RZ)
+    params[o:o + cp.size] = cp.ravel()
+    rng = np.random.default_rng(3)
+    theta = rng.uniform(-math.pi, math.pi, n)
+    psi = oracle.state(circ, params, theta)
+    z = _z_from_state(psi, n)
+    rings = _cnot_ring(n, L, ansatz)
+    for i in range(n):
+        s = np.zeros(n, dtype=bool)
+        s[i] = True
+        for ring in reversed(rings):
+            for c, t in reversed(ring):
+                if s[t]:
+                    s[c] = not s[c]
+        assert abs(z[i] - np.prod(np.cos(theta[s]))) < 1e-12
+
+
+@pytest.mark.parametrize("n,ansatz", [(1, "basic_rot"), (3, "basic_ryrz"), (6, "strong_rot"),
+                                      (8, "strong_rot")])
+def test_norm_and_layer_unitarity(oracle, n, ansatz):
+    L = 3
+    circ = W.circuit(n, L, 1, ansatz=ansatz, enc="rx", scale="pi", premap="direct",
+                     n_direct=min(3, n))
+    params = W.init_params(circ, 11)
+    rng = np.random.default_rng(5)
+    psi = oracle.state(circ, params, rng.uniform(-3, 3, n))
+    assert abs(np.vdot(psi, psi).real - 1.0) < 1e-13
+    for l in range(L):
+        U = oracle.layer_unitary(circ, params, l)
+        assert np.max(np.abs(U.conj().T @ U - np.eye(1 << n))) < 1e-13
+
+
+def _kron_gate(n, q, g):
+    mats = [np.eye(2, dtype=complex)] * n
+    mats = list(mats)
+    mats[q] = g
+    out = mats[0]
+    for m in mats[1:]:
+        out = np.kron(out, m)
+    return out
+
+
+def _kron_cnot(n, c, t):
+    P0 = np.array([[1, 0], [0, 0]], dtype=complex)
+    P1 = np.array([[0, 0], [0, 1]], dtype=complex)
+    a = [np.eye(2, dtype=complex)] * n
+    a = list(a)
+    a[c] = P0
+    b = [np.eye(2, dtype=complex)] * n
+    b = list(b)
+    b[c] = P1
+    b[t] = X
+    ka, kb = a[0], b[0]
+    for i in range(1, n):
+        ka = np.kron(ka, a[i])
+        kb = np.kron(kb, b[i])
+    return ka + kb
+
+
+@pytest.mark.parametrize("n,ansatz,enc", [(2, "basic_rot", "rx"), (3, "basic_ryrz", "ry"),
+                                          (4, "strong_rot", "rx"), (4, "noent_rot", "ry")])
+def test_bruteforce_dense_kronecker(oracle, n, ansatz, enc):
+    """n <= 4: the dense product of Kronecker-expanded matrix exponentials equals the
+    oracle's pair-loop state."""
+    L = 3
+    circ = W.circuit(n, L, 1, ansatz=ansatz, enc=enc, scale="pi", premap="direct",
+                     n_direct=min(3, n))
+    params = W.init_params(circ, 2).astype(np.float64)
+    off = W.param_offsets(circ)
+    o, shape = off["circuit"]
+    cp = params[o:o + int(np.prod(shape))].reshape(shape)
+    rng = np.random.default_rng(9)
+    theta = rng.uniform(-3, 3, n)
+    psi = np.zeros(1 << n, dtype=complex)
+    psi[0] = 1.0
+    for j in range(n):
+        psi = _kron_gate(n, j, _rot_exp(X if enc == "rx" else Y, theta[j])) @ psi
+    for l in range(L):
+        for q in range(n):
+            if ansatz == "basic_ryrz":
+                g = _rot_exp(Z, cp[l, q, 1]) @ _rot_exp(Y, cp[l, q, 0])
+            else:
+                a, b, gm = cp[l, q]
+                g = _rot_exp(Z, gm) @ _rot_exp(Y, b) @ _rot_exp(Z, a)
+            psi = _kron_gate(n, q, g) @ psi
+        if ansatz != "noent_rot" and n > 1:
+            r = 1 + (l % (n - 1)) if ansatz == "strong_rot" else 1
+            for i in range(n):
+                psi = _kron_cnot(n, i, (i + r) % n) @ psi
+    got = oracle.state(circ, params, theta)
+    assert np.max(np.abs(got - psi)) < 1e-12
+
+
+# ----------------------------------------------------------------------------- derivatives
+
+SMALL_MLP = dict(rff_freqs=4, mlp_width=5, mlp_depth=1)
+
+
+def _small_circuits():
+    return [
+        W.c1_circuit(),
+        W.circuit(5, 3, 4, ansatz="strong_rot", enc="rx", scale="acos", premap="rff_mlp",
+                  **SMALL_MLP),
+        W.circuit(4, 2, 4, ansatz="basic_rot", enc="ry", scale="asin", premap="rff_mlp",
+                  rff_freqs=3, mlp_width=4, mlp_depth=2),
+    ]
+
+
+@pytest.mark.parametrize("ci", range(3))
+def test_input_derivatives_vs_central_fd(oracle, ci):
+    circ = _small_circuits()[ci]
+    params = W.init_params(circ, 4)
+    pts = W.uniform_points(5, 8).astype(np.float64) * 0.9
+    f, df = oracle.forward(circ, params, pts)
+    h = 1e-5
+    for d in range(3):
+        e = np.zeros(3)
+        e[d] = h
+        fp, _ = oracle.forward(circ, params, pts + e)
+        fm, _ = oracle.forward(circ, params, pts - e)
+        fd = (fp - fm) / (2 * h)
+        assert np.max(np.abs(fd - df[:, :, d])) < 1e-7
+
+
+def test_input_derivative_direct_shift_rule(oracle):
+    """Direct RY(pi x) embedding: f is a first-harmonic trig polynomial in theta_x = pi x,
+    so df/dx = pi (f(theta + pi/2) - f(theta - pi/2)) / 2 exactly."""
+    circ = W.c1_circuit()
+    params = W.init_params(circ, 1)
+    pts = W.uniform_points(6, 2).astype(np.float64)
+    _, df = oracle.forward(circ, params, pts)
+    for d in range(3):
+        e = np.zeros(3)
+        e[d] = 0.5  # theta shift of pi/2 for theta = pi v
+        fp, _ = oracle.forward(circ, params, pts + e)
+        fm, _ = oracle.forward(circ, params, pts - e)
+        assert np.max(np.abs(math.pi * (fp - fm) / 2 - df[:, :, d])) < 1e-12
+
+
+def _shift_rule(fn, x0, R):
+    """General parameter-shift rule, exact for trig polynomials of degree <= R:
+    f'(x) = sum_{mu=1}^{2R} f(x + x_mu) (-1)^(mu-1) / (4 R sin^2(x_mu/2)),
+    x_mu = (2 mu - 1) pi / (2R)."""
+    tot = 0.0
+    for mu in range(1, 2 * R + 1):
+        xm = (2 * mu - 1) * math.pi / (2 * R)
+        tot += fn(x0 + xm) * (-1) ** (mu - 1) / (4 * R * math.sin(xm / 2) ** 2)
+    return tot
+
+
+def test_shift_rule_self_check():
+    rng = np.random.default_rng(0)
+    c = rng.standard_normal(9)
+    f = lambda x: c[0] + sum(c[2 * k - 1] * math.cos(k * x) + c[2 * k] * math.sin(k * x)
+                             for k in range(1, 5))
+    fp = lambda x: sum(-k * c[2 * k - 1] * math.sin(k * x) + k * c[2 * k] * math.cos(k * x)
+                       for k in range(1, 5))
+    for x in (0.0, 0.7, -2.1):
+        assert abs(_shift_rule(f, x, 4) - fp(x)) < 1e-12
+
+
+def _loss_setup(ci):
+    circ = _small_circuits()[ci]
+    prob = W.problem("dielectric" if ci == 1 else "vacuum", disk_x0=0.2, disk_r=0.5,
+                     w_energy=10.0 if ci != 0 else 0.0, energy_slice=4, energy_nt=2)
+    sets = {"colloc": W.uniform_points(8, 10 + ci), "ic": W.ic_points_uniform(3, 20 + ci),
+            "bc": W.bc_points(3, 30 + ci)}
+    params = W.init_params(circ, 6).astype(np.float64)
+    return circ, prob, params, sets
+
+
+@pytest.mark.parametrize("ci", range(3))
+def test_param_gradient_vs_central_fd(oracle, ci):
+    circ, prob, params, sets = _loss_setup(ci)
+    lay = oracle.param_layout(circ)
+    idx = np.arange(lay["fixed"], lay["total"])
+    g = oracle.grad(circ, prob, params, sets, idx)
+    h = 1e-5
+    for j, i in enumerate(idx):
+        pp = params.copy()
+        pp[i] += h
+        pm = params.copy()
+        pm[i] -= h
+        fd = (oracle.loss(circ, prob, pp, sets)[0] - oracle.loss(circ, prob, pm, sets)[0]) / (2 * h)
+        assert abs(fd - g[j]) < 1e-6 * max(1.0, abs(g[j])), (i, fd, g[j])
+
+
+@pytest.mark.parametrize("ci", range(3))
+def test_param_gradient_exact_shift_rule(oracle, ci):
+    """Circuit angles enter through one half-angle rotation each, so the fields and their
+    input derivatives are first-harmonic in each angle and the loss (squares, and the
+    squared Poynting residual) is a trig polynomial of degree <= 4: the R = 4 shift rule
+    is exact."""
+    circ, prob, params, sets = _loss_setup(ci)
+    lay = oracle.param_layout(circ)
+    idx = np.arange(lay["circuit"], lay["head"])
+    g = oracle.grad(circ, prob, params, sets, idx)
+    for j, i in enumerate(idx):
+        def fn(x, i=i):
+            pp = params.copy()
+            pp[i] = x
+            return oracle.loss(circ, prob, pp, sets)[0]
+        assert abs(_shift_rule(fn, params[i], 4) - g[j]) < 1e-10 * max(1.0, abs(g[j]))
+
+
+def test_omega_gradient_is_zero(oracle):
+    circ, prob, params, sets = _loss_setup(1)
+    lay = oracle.param_layout(circ)
+    g = oracle.grad(circ, prob, params, sets, np.arange(lay["fixed"]))
+    assert np.all(g == 0.0)
+
+
+# ----------------------------------------------------------------------------- losses
+
+def _vac():
+    return W.problem("vacuum", w_ic=10.0, w_bc=10.0, w_energy=10.0)
+
+
+def test_plane_wave_satisfies_residuals_and_poynting(oracle):
+    """Ez = cos(kx - wt), Hy = -cos(kx - wt), Hx = 0 with w = k solves Eqs. 5/8-10 and the
+    local Poynting balance, so every residual and the energy residual vanish."""
+    k = 2.3
+    pts = W.uniform_points(64, 1).astype(np.float64)
+    x, t = pts[:, 0], pts[:, 2]
+    ph = k * x - k * t
+    f = np.stack([np.cos(ph), np.zeros_like(ph), -np.cos(ph)], axis=1)
+    df = np.zeros((64, 3, 3))
+    df[:, 0, 0] = -k * np.sin(ph)
+    df[:, 0, 2] = k * np.sin(ph)
+    df[:, 2, 0] = k * np.sin(ph)
+    df[:, 2, 2] = -k * np.sin(ph)
+    out = oracle.loss_from_fields(_vac(), pts, f, df)
+    assert np.max(np.abs(out[:9])) < 1e-24 + 1e-13
+
+
+def test_plane_wave_wrong_speed_closed_form(oracle):
+    """With w != k: res1 = (w - k) sin, res3 = (k - w) sin, res2 = 0."""
+    k, w = 2.0, 3.0
+    pts = W.uniform_points(100, 2).astype(np.float64)
+    ph = k * pts[:, 0] - w * pts[:, 2]
+    f = np.stack([np.cos(ph), np.zeros_like(ph), -np.cos(ph)], axis=1)
+    df = np.zeros((100, 3, 3))
+    df[:, 0, 0] = -k * np.sin(ph)
+    df[:, 0, 2] = w * np.sin(ph)
+    df[:, 2, 0] = k * np.sin(ph)
+    df[:, 2, 2] = -w * np.sin(ph)
+    out = oracle.loss_from_fields(W.problem("vacuum", w_energy=0.0), pts, f, df)
+    m = np.mean(((w - k) * np.sin(ph)) ** 2)
+    assert abs(out[5] - m) < 1e-13 and abs(out[8] - m) < 1e-13 and abs(out[7]) < 1e-15
+    assert abs(out[1] - 2 * m) < 1e-12
+
+
+def test_ic_and_bc_terms(oracle):
+    prob = W.problem("vacuum", ic_sigma=0.1, w_ic=10.0, w_bc=10.0, w_energy=0.0)
+    ic = W.ic_points_uniform(50, 3).astype(np.float64)
+    r2 = ic[:, 0] ** 2 + ic[:, 1] ** 2
+    e0 = np.exp(-r2 / (2 * 0.01))
+    fi = np.stack([e0, np.zeros(50), np.zeros(50)], axis=1)
+    empty = np.zeros((0, 3))
+    out = oracle.loss_from_fields(prob, empty, empty, np.zeros((0, 9)), ic, fi)
+    assert abs(out[2]) < 1e-25
+    fi0 = np.zeros((50, 3))
+    fi0[:, 1] = 0.5
+    out = oracle.loss_from_fields(prob, empty, empty, np.zeros((0, 9)), ic, fi0)
+    assert abs(out[2] - 10.0 * np.mean(e0 ** 2 + 0.25)) < 1e-12
+    bc = W.bc_points(40, 4).astype(np.float64)
+    fb = np.zeros((40, 3))
+    fb[:, 0] = 0.3
+    out = oracle.loss_from_fields(prob, empty, empty, np.zeros((0, 9)), bc=bc, fb=fb)
+    assert abs(out[3] - 10.0 * 0.09) < 1e-13
+
+
+def test_dielectric_split_mse(oracle):
+    """Eq. 12: separate means over the vacuum and dielectric sets."""
+    prob = W.problem("dielectric", disk_x0=0.2, disk_y0=-0.1, disk_r=0.5, w_energy=0.0)
+    pts = W.uniform_points(400, 5).astype(np.float64)
+    inside = (pts[:, 0] - 0.2) ** 2 + (pts[:, 1] + 0.1) ** 2 < 0.25
+    assert 10 < inside.sum() < 390
+    df = np.zeros((400, 3, 3))
+    df[:, 0, 2] = np.where(inside, 3.0, 1.0)  # dEz/dt only: res1 = dEz/dt
+    out = oracle.loss_from_fields(prob, pts, np.zeros((400, 3)), df)
+    assert abs(out[5] - 1.0) < 1e-14 and abs(out[6] - 9.0) < 1e-14
+
+
+def test_energy_slice_sums(oracle):
+    """U(t) of Eq. 31 on a full-period grid: sum cos^2 over 2 periods of 64 points = 32."""
+    nx, ny, nt = 64, 8, 3
+    pts = W.grid_points(nx, ny, nt, 1.0).astype(np.float64)
+    prob = W.problem("vacuum", w_energy=0.0, energy_slice=nx * ny, energy_nt=nt)
+    ph = 2 * math.pi * pts[:, 0] - 0.3 * pts[:, 2]
+    f = np.stack([np.cos(ph), np.zeros_like(ph), np.cos(ph)], axis=1)
+    out = oracle.loss_from_fields(prob, pts, f, np.zeros((pts.shape[0], 9)))
+    for k in range(nt):
+        assert abs(out[9 + k] - 0.5 * 2 * ny * nx / 2) < 1e-9
+
+
+def test_plane_wave_along_y(oracle):
+    """Ez = cos(ky - wt), Hx = cos(ky - wt), Hy = 0 with w = k: exercises the Hx terms of
+    Eqs. 8 and 10a and of the Poynting residual (Eq. 23)."""
+    k = 1.7
+    pts = W.uniform_points(64, 6).astype(np.float64)
+    ph = k * pts[:, 1] - k * pts[:, 2]
+    f = np.stack([np.cos(ph), np.cos(ph), np.zeros_like(ph)], axis=1)
+    df = np.zeros((64, 3, 3))
+    df[:, 0, 1] = -k * np.sin(ph)
+    df[:, 0, 2] = k * np.sin(ph)
+    df[:, 1, 1] = -k * np.sin(ph)
+    df[:, 1, 2] = k * np.sin(ph)
+    out = oracle.loss_from_fields(_vac(), pts, f, df)
+    assert np.max(np.abs(out[:9])) < 1e-13
+    # flipping the wave direction breaks every residual
+    df[:, 1, :] *= -1
+    f[:, 1] *= -1
+    out = oracle.loss_from_fields(_vac(), pts, f, df)
+    assert out[7] > 0.1 and out[4] > 0.1
+
+
+def test_dielectric_eps_limits(oracle):
+    """eps -> eps_r at the disk centre and -> 1 far away: energy residual eps*Ez*dEz/dt."""
+    prob = W.problem("dielectric", eps_r=4.0, disk_x0=0.5, disk_y0=0.0, disk_r=0.25,
+                     sigmoid_w=0.02, w_energy=1.0)
+    for (x, y), eps in (((0.5, 0.0), 4.0), ((-0.8, 0.7), 1.0)):
+        pts = np.array([[x, y, 0.4]])
+        f = np.array([[0.4, 0.0, 0.0]])
+        df = np.zeros((1, 3, 3))
+        df[0, 0, 2] = 1.0
+        out = oracle.loss_from_fields(prob, pts, f, df)
+        assert abs(out[4] - (eps * 0.4) ** 2) < 1e-4
