@@ -1,0 +1,336 @@
+"""Benchmark of the QPINN hot path: one step = qp_loss_grad on the full-QPINN workload
+(8 qubits, 6 strongly entangling layers, RFF(64) + tanh MLP(32), dielectric disk, energy
+term) over a 64x64x16 collocation grid (65,536 points) plus a 64x64 initial-condition plane:
+forward, exact d/dx, d/dy, d/dt by tangent states, Maxwell/IC/energy losses and the adjoint
+gradient of every parameter.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Prints one JSON line. `value` is collocation points per second over all ranks (device
+time, CUDA events around each step, L2 flushed between steps). `e2e` is the same metric
+through the public call with the inputs copied from pinned host memory and the loss and
+gradient copied back inside the timed region. The reference arm times the FP64 CPU oracle
+(deliberately slow, plain definition) on a bounded sample of the same workload.
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "collocation pts/s, fwd+d/dx,dy,dt+adjoint grad, 8q x6L"
+UNIT = "colloc pts/s"
+WORKLOAD = "full QPINN step: 8q/6L strongly entangling, RFF64+MLP32, dielectric, energy term"
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def _dist():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def _config(world):
+    return {"workload": WORKLOAD, "n_qubits": 8, "n_layers": 6, "ansatz": "strongly entangling",
+            "premap": "RFF 64 freq + tanh MLP width 32", "medium": "dielectric",
+            "colloc_per_gpu": 65536, "ic_per_gpu": 4096, "global_batch": 65536 * world,
+            "parallelism": "dp%d" % world if world > 1 else "single",
+            "l2": "flushed between timed steps (256 MiB write)"}
+
+
+# ----------------------------------------------------------------------------- oracle arm
+
+def _oracle_sample(steps_budget_s=10.0, nthreads=None):
+    """Time the FP64 oracle (loss + gradient of every parameter) on a few collocation points
+    of the same workload; returns (points per second, threads, sample description)."""
+    from oracle import api as oracle
+    from paper_2506_23246_b300 import workloads as W
+    circ, prob, params, sets = W.c3_workload(0)
+    nt = nthreads or os.cpu_count() or 1
+    pts = sets["colloc"]
+    k = 1
+    done = 0
+    t0 = time.perf_counter()
+    while True:
+        sub = {"colloc": pts[done:done + k]}
+        prob_s = dict(prob, energy_nt=0)
+        oracle.loss(circ, prob_s, params, sub)
+        oracle.grad(circ, prob_s, params, sub, nthreads=nt)
+        done += k
+        el = time.perf_counter() - t0
+        if el > steps_budget_s or done >= 64:
+            break
+    return done / el, nt, "%d collocation points of the 64x64x16 grid, loss + all %d parameter " \
+        "gradients, %d threads" % (done, params.shape[0], nt)
+
+
+def run_reference(a):
+    rank, world, _ = _dist()
+    if rank != 0:
+        return 0
+    from oracle import build as obuild
+    obuild.build()
+    per_step = max(2.0, 60.0 / max(a.steps + a.warmup, 1))
+    for _ in range(a.warmup):
+        _oracle_sample(per_step * 0.2)
+    vals = []
+    t0 = time.perf_counter()
+    desc = ""
+    nt = 1
+    for _ in range(a.steps):
+        v, nt, desc = _oracle_sample(per_step)
+        vals.append(v)
+    wall = time.perf_counter() - t0
+    value = statistics.mean(vals)
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": 1000.0 * wall / a.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": _config(1), "impl": "reference",
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": nt, "kind": "oracle",
+                             "sample": desc},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+# ----------------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.QUERY,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- native arm
+
+def circuit_flops_per_point(n, L, nv):
+    """Algorithmic FP32 flops of the statevector kernel for one point: 16 flops per amplitude
+    per single-qubit gate per vector (complex 2x2 on amplitude pairs), forward on nv vectors,
+    inverse gates on 2 nv vectors for layers 1..L-1 (layer 0 is not uncomputed), and 12 flops
+    per amplitude per gate for each of the nv Pauli contractions Im<lambda|P phi>, plus the
+    3 input-Jacobian contractions of layer 0 (tangent points only)."""
+    dim = 1 << n
+    f = 16 * dim * n * L * nv            # forward gates
+    f += 16 * dim * n * (L - 1) * 2 * nv  # reverse: states and costates
+    f += 12 * dim * n * L * nv            # Pauli contractions
+    if nv == 4:
+        f += 12 * dim * n * 3
+    return f
+
+
+def run_native(a):
+    import torch
+    rank, world, local = _dist()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    from paper_2506_23246_b300 import build, qp
+    from paper_2506_23246_b300 import workloads as W
+    if rank == 0:
+        build.build()
+    if world > 1:
+        torch.distributed.barrier()
+    circ, prob, params, sets = W.c3_workload(0)
+    # weak scaling: every rank owns its own 64x64x16 slab of the time axis (independent points)
+    if world > 1:
+        sets = dict(sets)
+        sets["colloc"] = sets["colloc"].copy()
+        sets["colloc"][:, 2] += 0.7 * rank
+    plan = qp.Plan(circ, prob)
+    dev = torch.device("cuda", local)
+    dp = torch.tensor(params, device=dev)
+    dsets = {k: torch.tensor(v, device=dev) for k, v in sets.items()}
+    ncol = dsets["colloc"].shape[0]
+    plan.reserve(sum(t.shape[0] for t in dsets.values()), dev)
+    loss = torch.empty(9 + prob["energy_nt"], dtype=torch.float64, device=dev)
+    grad = torch.empty(plan.n_params, dtype=torch.float32, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    k0, k1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    plan.set_profile_events(k0, k1)
+
+    def step():
+        plan.loss_grad(dp, dsets, out=(loss, grad))
+        if world > 1:
+            torch.distributed.all_reduce(grad)
+            grad.div_(world)
+
+    for _ in range(max(a.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    launches = plan.last_launch_count()
+
+    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(a.steps)]
+    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(a.steps)]
+    kt = []
+    clk = ClockSampler(local)
+    clk.start()
+    time.sleep(0.3)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    for i in range(a.steps):
+        flush.fill_(float(i))
+        ev0[i].record(stream)
+        step()
+        ev1[i].record(stream)
+        k1.synchronize()
+        kt.append(k0.elapsed_time(k1))
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = clk.stop()
+    step_ms = [ev0[i].elapsed_time(ev1[i]) for i in range(a.steps)]
+    ms = sum(step_ms) / a.steps
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * ncol / (ms / 1000.0)
+
+    # roofline of the statevector kernel (FP32 SIMT)
+    kms = statistics.mean(kt)
+    flops = ncol * circuit_flops_per_point(8, 6, 4) + dsets["ic"].shape[0] * circuit_flops_per_point(8, 6, 1)
+    achieved = flops / (kms / 1000.0) / 1e12
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            peaks = json.load(fh)
+    except (OSError, ValueError):
+        pass
+    sm_max = peaks.get("sm_max_mhz", 2032.0)
+    peak = sms * 128 * 2 * sm_max * 1e6 / 1e12
+
+    # end to end through the public call: pinned host inputs in, loss + gradient out
+    hp = torch.tensor(params).pin_memory()
+    hs = {k: torch.tensor(v).pin_memory() for k, v in sets.items()}
+    hl = torch.empty(loss.shape, dtype=torch.float64).pin_memory()
+    hg = torch.empty(grad.shape, dtype=torch.float32).pin_memory()
+    h2d = hp.numel() * 4 + sum(v.numel() * 4 for v in hs.values())
+    d2h = hl.numel() * 8 + hg.numel() * 4
+
+    def e2e_step():
+        dp.copy_(hp, non_blocking=True)
+        for k in hs:
+            dsets[k].copy_(hs[k], non_blocking=True)
+        step()
+        hl.copy_(loss, non_blocking=True)
+        hg.copy_(grad, non_blocking=True)
+
+    for _ in range(3):
+        e2e_step()
+    torch.cuda.synchronize()
+    e0 = [torch.cuda.Event(enable_timing=True) for _ in range(a.steps)]
+    e1 = [torch.cuda.Event(enable_timing=True) for _ in range(a.steps)]
+    for i in range(a.steps):
+        flush.fill_(float(i))
+        e0[i].record(stream)
+        e2e_step()
+        e1[i].record(stream)
+    torch.cuda.synchronize()
+    ems = sum(e0[i].elapsed_time(e1[i]) for i in range(a.steps)) / a.steps
+    if world > 1:
+        t = torch.tensor([ems], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ems = float(t.item())
+    plan.set_profile_events(None, None)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
+                "warmup": max(a.warmup, 3), "ms_per_step": ms, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": _config(world),
+                "e2e": {"value": world * ncol / (ems / 1000.0), "unit": UNIT,
+                        "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+                "gpu_launches": launches * a.steps,
+                "roofline": {"bound": "alu", "achieved": achieved, "peak": peak,
+                             "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                             "kernel": "circuit_kernel<8,true>", "kernel_ms": kms,
+                             "peak_basis": "%d SMs x 128 FP32 FMA/clk x 2 x %.0f MHz (max SM clock "
+                                           "of measured peaks)" % (sms, sm_max)},
+                "clocks": clocks}
+        if not a.no_cpu_baseline and world == 1:
+            v, nt, desc = _oracle_sample(10.0)
+            line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": nt, "kind": "oracle",
+                                    "sample": desc}
+        print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    a = _args()
+    if a.impl == "reference":
+        return run_reference(a)
+    return run_native(a)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,181 @@
+/* qpinn.h -- C-ABI of the B300 QPINN hot-path library (libqpinn.so).
+ *
+ * The library evaluates the hybrid quantum PINN of arxiv 2506.23246 at a batch of
+ * collocation points on one GPU: premap (direct angle map, or random Fourier
+ * features + tanh MLP, Sec. 2.2), angle embedding and ansatz layers of the
+ * parametrized quantum circuit (Sec. 2.3, Eqs. 27-28), Pauli-Z readout and a linear
+ * head to the fields (Ez, Hx, Hy); exact first derivatives d/dx, d/dy, d/dt by
+ * forward-mode tangent states; the 2D TM Maxwell residuals and losses (Eqs. 8-17),
+ * the Poynting energy residual (Eq. 23), the total loss (Eq. 24), the energy slice
+ * sums U(t) (Eq. 31); and gradients of the total loss with respect to every
+ * parameter by a reverse (adjoint) sweep through the tangent states.
+ *
+ * Conventions shared by every call:
+ *  - All arrays are row-major and contiguous. Points are float32 [B][3] = (x, y, t).
+ *  - Pointers named d_* are device pointers owned by the caller. The library never
+ *    allocates device memory in a compute call and never synchronises the stream
+ *    (except qp_last_device_error). Scratch comes from a caller-owned workspace set
+ *    with qp_set_workspace.
+ *  - stream is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *  - Gates use the half-angle convention RX(t) = exp(-i t X / 2) (so <Z> = cos t after
+ *    RX(t) on |0>, Fig. 3); Rot(a, b, g) = RZ(g) RY(b) RZ(a) (Eq. 28); qubit q is bit
+ *    (n-1-q) of the basis index; the CNOT ring of layer l is CNOT(i, (i+r) mod n) for
+ *    i = 0..n-1 in order, r = 1 (Basic) or 1 + (l mod (n-1)) (Strongly entangling).
+ *  - Every call returns a qp_status; argument errors are detected on the host before
+ *    any launch; no C++ exception crosses this boundary.
+ */
+#ifndef QPINN_H
+#define QPINN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  QP_OK = 0,
+  QP_ERR_INVALID_ARG = 1,      /* null pointer, bad enum value, inconsistent sizes */
+  QP_ERR_UNSUPPORTED = 2,      /* valid request outside what this build implements */
+  QP_ERR_BUFFER_TOO_SMALL = 3, /* workspace missing or smaller than qp_workspace_size */
+  QP_ERR_CUDA = 4,             /* a CUDA runtime call failed (launch error, bad device) */
+  QP_ERR_NONFINITE = 5,        /* the device saw a non-finite loss (reported via status) */
+  QP_ERR_TIMEOUT = 6,          /* a bounded device-side wait ran out */
+  QP_ERR_INTERNAL = 7
+} qp_status;
+
+/* Ansatz layers (Sec. 2.3). BASIC_RYRZ is the RY(a) then RZ(b) per-qubit variant
+ * with the nearest-neighbour CNOT ring; the others use Rot gates (Eq. 28). */
+typedef enum {
+  QP_ANSATZ_BASIC_RYRZ = 0,
+  QP_ANSATZ_BASIC_ROT = 1,
+  QP_ANSATZ_STRONG_ROT = 2,
+  QP_ANSATZ_NOENT_ROT = 3
+} qp_ansatz;
+
+typedef enum { QP_ENC_RX = 0, QP_ENC_RY = 1 } qp_enc_gate;
+
+/* Angle scalings of Eq. 27a-e: none a, pi a, (a+1) pi/2, asin(a)+pi/2, acos(a). */
+typedef enum {
+  QP_SCALE_NONE = 0,
+  QP_SCALE_PI = 1,
+  QP_SCALE_BIAS = 2,
+  QP_SCALE_ASIN = 3,
+  QP_SCALE_ACOS = 4
+} qp_scale;
+
+/* DIRECT: theta_j = scale(v_j) for j < n_direct (v = (x,y,t)), theta_j = 0 otherwise.
+ * RFF_MLP: r = [cos(Omega v), sin(Omega v)] (Sec. 2.2, RFF), mlp_depth tanh layers of
+ * width mlp_width, a linear layer to n_qubits, a = tanh(.), theta = scale(a). */
+typedef enum { QP_PREMAP_DIRECT = 0, QP_PREMAP_RFF_MLP = 1 } qp_premap;
+
+typedef enum {
+  QP_PATH_AUTO = 0,
+  QP_PATH_SIMT_FP32 = 1,  /* gate-by-gate statevector in registers/shared memory */
+  QP_PATH_GEMM_3XTF32 = 2,
+  QP_PATH_GEMM_BF16X3 = 3
+} qp_path;
+
+typedef enum { QP_MEDIUM_VACUUM = 0, QP_MEDIUM_DIELECTRIC = 1 } qp_medium;
+
+typedef struct {
+  int32_t n_qubits;  /* 1..10 */
+  int32_t n_layers;  /* 1..16 */
+  int32_t n_readout; /* readout qubits 0..m-1, 1 <= m <= n_qubits */
+  int32_t ansatz;    /* qp_ansatz */
+  int32_t enc;       /* qp_enc_gate */
+  int32_t scale;     /* qp_scale */
+  int32_t premap;    /* qp_premap */
+  int32_t n_direct;  /* DIRECT premap: inputs mapped to qubits 0..n_direct-1 (<= 3) */
+  int32_t rff_freqs; /* RFF_MLP: number of frequencies F (Omega is [F][3]) */
+  int32_t mlp_width; /* RFF_MLP: hidden width H */
+  int32_t mlp_depth; /* RFF_MLP: number of hidden tanh layers */
+} qp_circuit;
+
+typedef struct {
+  int32_t medium;    /* qp_medium */
+  float eps_r;       /* dielectric: eps = 1 + (eps_r-1) sigmoid((disk_r - r)/sigmoid_w) */
+  float disk_r, disk_x0, disk_y0, sigmoid_w;
+  float ic_sigma;    /* initial pulse exp(-((x-ic_x0)^2+(y-ic_y0)^2)/(2 sigma^2)), Eq. 14 */
+  float ic_x0, ic_y0;
+  float w_ic, w_bc, w_energy; /* loss weights (Eq. 24 uses 10) */
+  int32_t energy_slice;       /* collocation point p belongs to energy slice p/energy_slice */
+  int32_t energy_nt;          /* number of energy slices U(t_k) reported (0 = none) */
+} qp_problem;
+
+/* Point sets of one loss evaluation (device pointers, float32 [n][3]). colloc points
+ * carry the residual and energy terms; ic points the initial-condition misfit (Eq. 17);
+ * bc points the PEC boundary term Ez = 0. Any set may be empty (NULL, 0). */
+typedef struct {
+  const float* colloc;
+  int64_t n_colloc;
+  const float* ic;
+  int64_t n_ic;
+  const float* bc;
+  int64_t n_bc;
+} qp_batch;
+
+/* Layout of d_loss written by qp_loss_grad (float64):
+ *  [0] total loss (Eq. 24 without L_sym), [1] L_phys (Eq. 11 or 13), [2] w_ic * L_IC,
+ *  [3] w_bc * L_BC, [4] w_energy * mean(Eq. 23 residual^2), [5] MSE(res1) over the vacuum
+ *  set (all points in vacuum), [6] MSE(res1) over the dielectric set, [7] MSE(res2),
+ *  [8] MSE(res3), [9 .. 9+energy_nt) energy slice sums U(t_k) (Eq. 31). */
+#define QP_NLOSS 9
+
+typedef struct qp_plan qp_plan;
+
+/* Create a plan for one circuit + problem. Host-only: validates the configuration and
+ * builds the shared-memory schedule of the gate passes. *out receives the plan (owned
+ * by the caller, free with qp_plan_destroy). Fails with QP_ERR_INVALID_ARG for bad
+ * values and QP_ERR_UNSUPPORTED for valid ones this build does not implement. */
+qp_status qp_plan_create(const qp_circuit* circuit, const qp_problem* problem, int32_t path,
+                         qp_plan** out);
+void qp_plan_destroy(qp_plan* plan);
+
+/* Number of float32 entries of the flat parameter vector. Layout (Sec. 2.2-2.3):
+ *   RFF_MLP premap: Omega[F][3] (fixed, gradient 0), then per hidden layer W[H][in]
+ *   (in = 2F first, H after) and b[H], then W_out[n][H], b_out[n];
+ *   circuit: [L][n][k] with k = 2 (RY angle, RZ angle) for BASIC_RYRZ, else 3 (Rot a,b,g);
+ *   head: W[3][m], b[3]. */
+qp_status qp_param_count(const qp_plan* plan, int64_t* n_params);
+/* offsets[0] circuit block, [1] head block, [2] total, [3] number of fixed (Omega) entries. */
+qp_status qp_param_layout(const qp_plan* plan, int64_t* offsets4);
+
+/* Device scratch needed by calls on up to max_points points in total (all sets). */
+qp_status qp_workspace_size(const qp_plan* plan, int64_t max_points, size_t* bytes);
+/* Attach caller-owned device scratch (>= qp_workspace_size, 256-byte aligned). The
+ * plan keeps the pointer; the caller keeps ownership and must not free it while the
+ * plan is used. Calls on one plan must not overlap on the GPU (they share it). */
+qp_status qp_set_workspace(qp_plan* plan, void* d_workspace, size_t bytes);
+
+/* Fields and input derivatives at B points: d_fields [B][3] = (Ez, Hx, Hy),
+ * d_dfields [B][3][3] = d field_c / d (x, y, t)_d, or NULL to skip derivatives. */
+qp_status qp_forward(qp_plan* plan, const float* d_params, const float* d_pts, int64_t B,
+                     float* d_fields, float* d_dfields, void* stream);
+
+/* Loss terms (layout above, float64 [QP_NLOSS + energy_nt]) and the gradient of the
+ * total loss w.r.t. every parameter (float32 [n_params]; Omega entries get 0). */
+qp_status qp_loss_grad(qp_plan* plan, const float* d_params, const qp_batch* batch,
+                       double* d_loss, float* d_grad, void* stream);
+
+/* Synchronise the stream of the last call on this plan and return the device status word
+ * (QP_OK, QP_ERR_NONFINITE or QP_ERR_TIMEOUT) or QP_ERR_CUDA for a sticky CUDA error. */
+qp_status qp_last_device_error(qp_plan* plan);
+
+const char* qp_status_str(qp_status s);
+
+/* Kernel launches issued by the last compute call on this plan (for accounting). */
+int32_t qp_last_launch_count(const qp_plan* plan);
+
+/* Optional profiling: two cudaEvent_t (passed as void*, created by the caller) that the
+ * following compute calls record on their stream immediately before and after the
+ * statevector (circuit) kernel, so its device time can be read with cudaEventElapsedTime.
+ * Pass NULL, NULL to stop. The plan does not own the events. */
+qp_status qp_set_profile_events(qp_plan* plan, void* ev_start, void* ev_stop);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QPINN_H */

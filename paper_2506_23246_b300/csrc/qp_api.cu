@@ -1,0 +1,486 @@
+// qp_api.cu -- the C-ABI of libqpinn.so (declared in include/qpinn.h): plan creation and
+// validation, workspace carving and the launch sequence of one forward or loss+gradient call.
+#include <cuda_runtime.h>
+
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "../../include/qpinn.h"
+#include "qp_aux.cuh"
+#include "qp_circuit.cuh"
+#include "qp_common.h"
+
+extern "C" int qp_build_sched(int n, int L, int ansatz, QPSched* out);
+
+struct qp_plan {
+  qp_circuit c;
+  qp_problem p;
+  int32_t path;
+  QPSched sched;
+  int device = 0, sm_count = 0;
+  int warps_grad = 0, blocks_grad = 0, warps_fwd = 0, blocks_fwd = 0;
+  int smem_grad = 0, smem_fwd = 0, sstride_grad = 0, sstride_fwd = 0;
+  int nwblk = 0, wtile = 0, smem_wgrad = 0, smem_premap = 0;
+  int64_t n_params = 0, circ_off = 0, head_off = 0, mlp_off = 0, mlp_count = 0, nfixed = 0;
+  void* ws = nullptr;
+  size_t ws_bytes = 0;
+  int32_t last_launches = 0;
+  cudaStream_t last_stream = nullptr;
+  cudaEvent_t prof_start = nullptr, prof_stop = nullptr;
+};
+
+namespace {
+
+constexpr int kMaxWarps = 12;
+
+int64_t premap_count(const qp_circuit& c) {
+  if (c.premap != QP_PREMAP_RFF_MLP) return 0;
+  int64_t cnt = 3LL * c.rff_freqs;
+  int64_t in = 2LL * c.rff_freqs;
+  for (int l = 0; l < c.mlp_depth; ++l) { cnt += (int64_t)c.mlp_width * in + c.mlp_width; in = c.mlp_width; }
+  cnt += (int64_t)c.n_qubits * in + c.n_qubits;
+  return cnt;
+}
+
+int geo_lb(int n) { return n <= 3 ? n : (n <= 8 ? 3 : n - 5); }
+int geo_ppw(int n) { return 32 >> (n - geo_lb(n)); }
+
+struct WsLayout {
+  size_t status, gates, cmat, cenc, thetaJ, dthetaJ, d1, d2, u1, blk_loss, blk_grad, wpart, total;
+};
+
+size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+WsLayout ws_layout(const qp_plan* pl, int64_t P) {
+  WsLayout w;
+  const int n = pl->c.n_qubits, H = pl->c.premap == QP_PREMAP_RFF_MLP ? pl->c.mlp_width : 0;
+  size_t o = 0;
+  w.status = o; o = al256(o + 256);
+  w.gates = o; o = al256(o + (size_t)QP_MAXL * QP_MAXQ * 8 * 4);
+  w.cmat = o; o = al256(o + (size_t)QP_MAXL * QP_MAXQ * 3 * 4 * 4);
+  w.cenc = o; o = al256(o + (size_t)QP_MAXQ * 4 * 4);
+  w.thetaJ = o; o = al256(o + (size_t)P * n * 16);
+  w.dthetaJ = o; o = al256(o + (size_t)P * n * 16);
+  w.d1 = o; o = al256(o + (size_t)P * H * 16);
+  w.d2 = o; o = al256(o + (size_t)(H ? P : 0) * n * 16);
+  w.u1 = o; o = al256(o + (size_t)P * H * 16);
+  const int nt = pl->p.energy_nt;
+  w.blk_loss = o; o = al256(o + (size_t)pl->blocks_grad * (QP_NLP + nt) * 8);
+  w.blk_grad = o; o = al256(o + (size_t)pl->blocks_grad * (3 * n * pl->c.n_layers + 3 * pl->c.n_readout + 3) * 4);
+  const int64_t nW = H ? (int64_t)H * 2 * pl->c.rff_freqs + H + (int64_t)n * H + n : 0;
+  w.wpart = o; o = al256(o + (size_t)pl->nwblk * nW * 4);
+  w.total = o;
+  return w;
+}
+
+template <int NQ, bool GRAD>
+void* circuit_fn() { return (void*)qpk::circuit_kernel<NQ, GRAD>; }
+
+void* circuit_kernel_ptr(int n, bool grad) {
+  switch (n) {
+#define QP_CASE(N) case N: return grad ? circuit_fn<N, true>() : circuit_fn<N, false>();
+    QP_CASE(1) QP_CASE(2) QP_CASE(3) QP_CASE(4) QP_CASE(5)
+    QP_CASE(6) QP_CASE(7) QP_CASE(8) QP_CASE(9) QP_CASE(10)
+#undef QP_CASE
+  }
+  return nullptr;
+}
+
+void* premap_fwd_ptr(int H) {
+  switch (H) {
+    case 4: return (void*)qpk::premap_fwd_kernel<4>;
+    case 8: return (void*)qpk::premap_fwd_kernel<8>;
+    case 16: return (void*)qpk::premap_fwd_kernel<16>;
+    case 32: return (void*)qpk::premap_fwd_kernel<32>;
+    case 64: return (void*)qpk::premap_fwd_kernel<64>;
+  }
+  return nullptr;
+}
+void* premap_bwd_ptr(int H) {
+  switch (H) {
+    case 4: return (void*)qpk::premap_bwd_kernel<4>;
+    case 8: return (void*)qpk::premap_bwd_kernel<8>;
+    case 16: return (void*)qpk::premap_bwd_kernel<16>;
+    case 32: return (void*)qpk::premap_bwd_kernel<32>;
+    case 64: return (void*)qpk::premap_bwd_kernel<64>;
+  }
+  return nullptr;
+}
+
+qp_status validate(const qp_circuit* c, const qp_problem* p, int32_t path) {
+  if (!c || !p) return QP_ERR_INVALID_ARG;
+  if (c->n_qubits < 1 || c->n_qubits > QP_MAXQ) return QP_ERR_INVALID_ARG;
+  if (c->n_layers < 1 || c->n_layers > QP_MAXL) return QP_ERR_INVALID_ARG;
+  if (c->n_readout < 1 || c->n_readout > c->n_qubits) return QP_ERR_INVALID_ARG;
+  if (c->ansatz < 0 || c->ansatz > 3 || c->enc < 0 || c->enc > 1) return QP_ERR_INVALID_ARG;
+  if (c->scale < 0 || c->scale > 4) return QP_ERR_INVALID_ARG;
+  if (c->premap == QP_PREMAP_DIRECT) {
+    if (c->n_direct < 0 || c->n_direct > 3 || c->n_direct > c->n_qubits) return QP_ERR_INVALID_ARG;
+  } else if (c->premap == QP_PREMAP_RFF_MLP) {
+    if (c->rff_freqs < 1 || c->mlp_width < 1 || c->mlp_depth < 0) return QP_ERR_INVALID_ARG;
+    if (c->mlp_depth != 1) return QP_ERR_UNSUPPORTED;
+    const int H = c->mlp_width;
+    if (H != 4 && H != 8 && H != 16 && H != 32 && H != 64) return QP_ERR_UNSUPPORTED;
+    if (c->rff_freqs > QP_MAXF || (c->rff_freqs % 2) != 0) return QP_ERR_UNSUPPORTED;
+    if ((int64_t)H * 2 * c->rff_freqs > 16 * 4 * 256 || c->n_qubits * H > 4 * 256) return QP_ERR_UNSUPPORTED;
+  } else {
+    return QP_ERR_INVALID_ARG;
+  }
+  if (p->medium != QP_MEDIUM_VACUUM && p->medium != QP_MEDIUM_DIELECTRIC) return QP_ERR_INVALID_ARG;
+  if (p->energy_nt < 0 || p->energy_nt > QP_MAXNT || p->energy_slice < 0) return QP_ERR_INVALID_ARG;
+  if (p->medium == QP_MEDIUM_DIELECTRIC && !(p->sigmoid_w > 0.f)) return QP_ERR_INVALID_ARG;
+  if (!(p->ic_sigma > 0.f)) return QP_ERR_INVALID_ARG;
+  if (path != QP_PATH_AUTO && path != QP_PATH_SIMT_FP32) return QP_ERR_UNSUPPORTED;
+  return QP_OK;
+}
+
+qp_status cuda_status(cudaError_t e) { return e == cudaSuccess ? QP_OK : QP_ERR_CUDA; }
+
+}  // namespace
+
+extern "C" {
+
+const char* qp_status_str(qp_status s) {
+  switch (s) {
+    case QP_OK: return "ok";
+    case QP_ERR_INVALID_ARG: return "invalid argument";
+    case QP_ERR_UNSUPPORTED: return "unsupported configuration";
+    case QP_ERR_BUFFER_TOO_SMALL: return "workspace missing or too small";
+    case QP_ERR_CUDA: return "CUDA error";
+    case QP_ERR_NONFINITE: return "non-finite loss";
+    case QP_ERR_TIMEOUT: return "device wait timed out";
+    case QP_ERR_INTERNAL: return "internal error";
+  }
+  return "unknown status";
+}
+
+qp_status qp_plan_create(const qp_circuit* circuit, const qp_problem* problem, int32_t path,
+                         qp_plan** out) {
+  if (!out) return QP_ERR_INVALID_ARG;
+  *out = nullptr;
+  qp_status st = validate(circuit, problem, path);
+  if (st != QP_OK) return st;
+  qp_plan* pl = new (std::nothrow) qp_plan();
+  if (!pl) return QP_ERR_INTERNAL;
+  pl->c = *circuit;
+  pl->p = *problem;
+  pl->path = path;
+  const int n = circuit->n_qubits;
+  if (qp_build_sched(n, circuit->n_layers, circuit->ansatz, &pl->sched) != 0) {
+    delete pl;
+    return QP_ERR_UNSUPPORTED;
+  }
+  const int k = circuit->ansatz == QP_ANSATZ_BASIC_RYRZ ? 2 : 3;
+  pl->mlp_count = premap_count(*circuit);
+  pl->nfixed = circuit->premap == QP_PREMAP_RFF_MLP ? 3LL * circuit->rff_freqs : 0;
+  pl->mlp_off = pl->nfixed;
+  pl->circ_off = pl->mlp_count;
+  pl->head_off = pl->circ_off + (int64_t)circuit->n_layers * n * k;
+  pl->n_params = pl->head_off + 3LL * circuit->n_readout + 3;
+
+  if (cudaGetDevice(&pl->device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&pl->sm_count, cudaDevAttrMultiProcessorCount, pl->device) != cudaSuccess) {
+    cudaGetLastError();
+    delete pl;
+    return QP_ERR_CUDA;
+  }
+  int smem_optin = 0;
+  cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, pl->device);
+  const int dim = 1 << n, ppw = geo_ppw(n);
+  const int nt = problem->energy_nt;
+  for (int g = 0; g < 2; ++g) {
+    const bool grad = g == 0;
+    const int nvec = grad ? 8 : 4;
+    const int sstride = nvec * dim + (n <= 3 ? 1 : 0);
+    int warps = kMaxWarps;
+    qpk::SmemLayout lay;
+    for (; warps >= 1; --warps) {
+      lay = qpk::smem_layout(n, circuit->n_layers, circuit->n_readout, grad ? nt : 0, warps, sstride, ppw);
+      if (lay.total <= smem_optin) break;
+    }
+    if (warps < 1) { delete pl; return QP_ERR_UNSUPPORTED; }
+    void* fn = circuit_kernel_ptr(n, grad);
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, lay.total) != cudaSuccess) {
+      cudaGetLastError();
+      delete pl;
+      return QP_ERR_CUDA;
+    }
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, warps * 32, lay.total);
+    if (per_sm < 1) per_sm = 1;
+    if (grad) {
+      pl->warps_grad = warps; pl->smem_grad = lay.total; pl->sstride_grad = sstride;
+      pl->blocks_grad = pl->sm_count * per_sm;
+    } else {
+      pl->warps_fwd = warps; pl->smem_fwd = lay.total; pl->sstride_fwd = sstride;
+      pl->blocks_fwd = pl->sm_count * per_sm;
+    }
+  }
+  if (circuit->premap == QP_PREMAP_RFF_MLP) {
+    const int F = circuit->rff_freqs, H = circuit->mlp_width;
+    pl->smem_premap = (H * 2 * F + H + n * H + n + 3 * F) * 4;
+    pl->nwblk = pl->sm_count * 2;
+    int tile = 32;
+    while (tile > 1 && (tile * (2 * F + 2 * H + n) * 16 + 3 * F * 4) > 96 * 1024) tile >>= 1;
+    pl->wtile = tile;
+    pl->smem_wgrad = tile * (2 * F + 2 * H + n) * 16 + 3 * F * 4;
+    if (cudaFuncSetAttribute(premap_fwd_ptr(H), cudaFuncAttributeMaxDynamicSharedMemorySize, pl->smem_premap) != cudaSuccess ||
+        cudaFuncSetAttribute(premap_bwd_ptr(H), cudaFuncAttributeMaxDynamicSharedMemorySize, pl->smem_premap) != cudaSuccess ||
+        cudaFuncSetAttribute((void*)qpk::premap_wgrad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, pl->smem_wgrad) != cudaSuccess) {
+      cudaGetLastError();
+      delete pl;
+      return QP_ERR_CUDA;
+    }
+  }
+  *out = pl;
+  return QP_OK;
+}
+
+void qp_plan_destroy(qp_plan* plan) { delete plan; }
+
+qp_status qp_param_count(const qp_plan* plan, int64_t* n_params) {
+  if (!plan || !n_params) return QP_ERR_INVALID_ARG;
+  *n_params = plan->n_params;
+  return QP_OK;
+}
+
+qp_status qp_param_layout(const qp_plan* plan, int64_t* o) {
+  if (!plan || !o) return QP_ERR_INVALID_ARG;
+  o[0] = plan->circ_off; o[1] = plan->head_off; o[2] = plan->n_params; o[3] = plan->nfixed;
+  return QP_OK;
+}
+
+qp_status qp_workspace_size(const qp_plan* plan, int64_t max_points, size_t* bytes) {
+  if (!plan || !bytes || max_points < 0) return QP_ERR_INVALID_ARG;
+  *bytes = ws_layout(plan, max_points).total;
+  return QP_OK;
+}
+
+qp_status qp_set_workspace(qp_plan* plan, void* d_ws, size_t bytes) {
+  if (!plan || (bytes && !d_ws)) return QP_ERR_INVALID_ARG;
+  if (((uintptr_t)d_ws & 255) != 0) return QP_ERR_INVALID_ARG;
+  plan->ws = d_ws;
+  plan->ws_bytes = bytes;
+  return QP_OK;
+}
+
+int32_t qp_last_launch_count(const qp_plan* plan) { return plan ? plan->last_launches : -1; }
+
+qp_status qp_set_profile_events(qp_plan* plan, void* ev_start, void* ev_stop) {
+  if (!plan || ((ev_start == nullptr) != (ev_stop == nullptr))) return QP_ERR_INVALID_ARG;
+  plan->prof_start = (cudaEvent_t)ev_start;
+  plan->prof_stop = (cudaEvent_t)ev_stop;
+  return QP_OK;
+}
+
+static void fill_problem(const qp_plan* pl, QPProblemDev& d) {
+  const qp_problem& p = pl->p;
+  d.medium = p.medium; d.eps_r = p.eps_r; d.disk_r = p.disk_r; d.disk_x0 = p.disk_x0;
+  d.disk_y0 = p.disk_y0; d.sigmoid_w = p.sigmoid_w; d.ic_sigma = p.ic_sigma; d.ic_x0 = p.ic_x0;
+  d.ic_y0 = p.ic_y0; d.w_ic = p.w_ic; d.w_bc = p.w_bc; d.w_energy = p.w_energy;
+  d.energy_slice = p.energy_slice; d.energy_nt = p.energy_nt;
+}
+
+// Shared prologue: gate preparation and premap forward for all point sets.
+static qp_status launch_front(qp_plan* pl, const float* d_params, const float* const pts[3],
+                              const int64_t npts[3], const WsLayout& w, cudaStream_t s) {
+  char* ws = (char*)pl->ws;
+  const int n = pl->c.n_qubits, L = pl->c.n_layers;
+  qpk::PrepArgs pa;
+  pa.params = d_params; pa.circ_off = pl->circ_off; pa.n = n; pa.L = L;
+  pa.ansatz = pl->c.ansatz; pa.enc = pl->c.enc;
+  pa.gates = (float*)(ws + w.gates); pa.cmat = (float*)(ws + w.cmat); pa.cenc = (float*)(ws + w.cenc);
+  pa.counts = (int32_t*)(ws + w.status) + 1; pa.status = (int32_t*)(ws + w.status);
+  qpk::prep_kernel<<<(L * n + 63) / 64, 64, 0, s>>>(pa);
+  qpk::PremapArgs ma;
+  std::memset(&ma, 0, sizeof(ma));
+  for (int i = 0; i < 3; ++i) { ma.pts[i] = pts[i]; ma.npts[i] = npts[i]; }
+  ma.ptot = npts[0] + npts[1] + npts[2];
+  ma.params = d_params; ma.n = n; ma.premap = pl->c.premap; ma.scale = pl->c.scale;
+  ma.n_direct = pl->c.n_direct; ma.F = pl->c.rff_freqs; ma.H = pl->c.mlp_width;
+  ma.thetaJ = (float*)(ws + w.thetaJ);
+  ma.counts = pa.counts; ma.medium = pl->p.medium;
+  ma.disk_r = pl->p.disk_r; ma.disk_x0 = pl->p.disk_x0; ma.disk_y0 = pl->p.disk_y0;
+  const int pblocks = (int)((ma.ptot + 127) / 128 < pl->sm_count * 8 ? (ma.ptot + 127) / 128 : pl->sm_count * 8);
+  if (pl->c.premap == QP_PREMAP_RFF_MLP) {
+    void* fn = premap_fwd_ptr(pl->c.mlp_width);
+    void* args[] = {&ma};
+    if (cudaLaunchKernel(fn, dim3(pblocks > 0 ? pblocks : 1), dim3(128), args, pl->smem_premap, s) != cudaSuccess)
+      return QP_ERR_CUDA;
+  } else {
+    qpk::premap_fwd_kernel<4><<<pblocks > 0 ? pblocks : 1, 128, 0, s>>>(ma);
+  }
+  return cuda_status(cudaGetLastError());
+}
+
+static void fill_circ(qp_plan* pl, QPCircArgs& a, const WsLayout& w, const float* d_params,
+                      const float* const pts[3], const int64_t npts[3], bool grad) {
+  char* ws = (char*)pl->ws;
+  const int n = pl->c.n_qubits, ppw = geo_ppw(n);
+  std::memset(&a, 0, sizeof(a));
+  a.s = pl->sched;
+  fill_problem(pl, a.pb);
+  a.n = n; a.L = pl->c.n_layers; a.m = pl->c.n_readout; a.enc = pl->c.enc;
+  a.sstride = grad ? pl->sstride_grad : pl->sstride_fwd;
+  int64_t acc = 0, base = 0;
+  for (int i = 0; i < 3; ++i) {
+    a.pts[i] = pts[i];
+    a.npts[i] = npts[i];
+    acc += (npts[i] + ppw - 1) / ppw;
+    a.task_end[i] = acc;
+    a.pt_base[i] = base;
+    base += npts[i];
+  }
+  a.thetaJ = (const float*)(ws + w.thetaJ);
+  a.dthetaJ = (float*)(ws + w.dthetaJ);
+  a.gates = (const float*)(ws + w.gates);
+  a.cenc = (const float*)(ws + w.cenc);
+  a.head = d_params + pl->head_off;
+  a.counts = (const int32_t*)(ws + w.status) + 1;
+  a.blk_loss = (double*)(ws + w.blk_loss);
+  a.blk_grad = (float*)(ws + w.blk_grad);
+  a.loss_stride = QP_NLP + pl->p.energy_nt;
+  a.grad_stride = 3 * n * pl->c.n_layers + 3 * pl->c.n_readout + 3;
+}
+
+qp_status qp_forward(qp_plan* pl, const float* d_params, const float* d_pts, int64_t B,
+                     float* d_fields, float* d_dfields, void* stream) {
+  if (!pl || !d_params || B < 0 || (B > 0 && (!d_pts || !d_fields))) return QP_ERR_INVALID_ARG;
+  pl->last_launches = 0;
+  if (B == 0) return QP_OK;
+  const WsLayout w = ws_layout(pl, B);
+  if (!pl->ws || pl->ws_bytes < w.total) return QP_ERR_BUFFER_TOO_SMALL;
+  cudaStream_t s = (cudaStream_t)stream;
+  pl->last_stream = s;
+  const float* pts[3] = {d_pts, nullptr, nullptr};
+  const int64_t npts[3] = {B, 0, 0};
+  qp_status st = launch_front(pl, d_params, pts, npts, w, s);
+  if (st != QP_OK) return st;
+  QPCircArgs a;
+  fill_circ(pl, a, w, d_params, pts, npts, false);
+  a.want_df = d_dfields != nullptr;
+  a.out_f = d_fields;
+  a.out_df = d_dfields;
+  const int64_t tasks = a.task_end[2];
+  int64_t blocks = (tasks + pl->warps_fwd - 1) / pl->warps_fwd;
+  if (blocks > pl->blocks_fwd) blocks = pl->blocks_fwd;
+  void* args[] = {&a};
+  if (pl->prof_start) cudaEventRecord(pl->prof_start, s);
+  if (cudaLaunchKernel(circuit_kernel_ptr(pl->c.n_qubits, false), dim3((unsigned)blocks),
+                       dim3(pl->warps_fwd * 32), args, pl->smem_fwd, s) != cudaSuccess)
+    return QP_ERR_CUDA;
+  if (pl->prof_stop) cudaEventRecord(pl->prof_stop, s);
+  pl->last_launches = 3;
+  return cuda_status(cudaGetLastError());
+}
+
+qp_status qp_loss_grad(qp_plan* pl, const float* d_params, const qp_batch* batch, double* d_loss,
+                       float* d_grad, void* stream) {
+  if (!pl || !d_params || !batch || !d_loss || !d_grad) return QP_ERR_INVALID_ARG;
+  if (batch->n_colloc < 0 || batch->n_ic < 0 || batch->n_bc < 0) return QP_ERR_INVALID_ARG;
+  if ((batch->n_colloc && !batch->colloc) || (batch->n_ic && !batch->ic) || (batch->n_bc && !batch->bc))
+    return QP_ERR_INVALID_ARG;
+  pl->last_launches = 0;
+  const float* pts[3] = {batch->colloc, batch->ic, batch->bc};
+  const int64_t npts[3] = {batch->n_colloc, batch->n_ic, batch->n_bc};
+  const int64_t P = npts[0] + npts[1] + npts[2];
+  const WsLayout w = ws_layout(pl, P);
+  if (!pl->ws || pl->ws_bytes < w.total) return QP_ERR_BUFFER_TOO_SMALL;
+  cudaStream_t s = (cudaStream_t)stream;
+  pl->last_stream = s;
+  char* ws = (char*)pl->ws;
+  int launches = 0;
+  if (P > 0) {
+    qp_status st = launch_front(pl, d_params, pts, npts, w, s);
+    if (st != QP_OK) return st;
+    launches += 2;
+  } else {
+    // nothing to evaluate: still clear the status/counters through the prep kernel
+    qpk::PrepArgs pa;
+    std::memset(&pa, 0, sizeof(pa));
+    pa.params = d_params; pa.circ_off = pl->circ_off; pa.n = pl->c.n_qubits; pa.L = pl->c.n_layers;
+    pa.ansatz = pl->c.ansatz; pa.enc = pl->c.enc;
+    pa.gates = (float*)(ws + w.gates); pa.cmat = (float*)(ws + w.cmat); pa.cenc = (float*)(ws + w.cenc);
+    pa.counts = (int32_t*)(ws + w.status) + 1; pa.status = (int32_t*)(ws + w.status);
+    qpk::prep_kernel<<<(pa.L * pa.n + 63) / 64, 64, 0, s>>>(pa);
+    launches += 1;
+  }
+  QPCircArgs a;
+  fill_circ(pl, a, w, d_params, pts, npts, true);
+  const bool mlp = pl->c.premap == QP_PREMAP_RFF_MLP;
+  a.want_dtheta = mlp ? 1 : 0;
+  const int64_t tasks = a.task_end[2];
+  // every block writes its partials, so the grid is fixed to the plan's block count
+  void* args[] = {&a};
+  if (pl->prof_start) cudaEventRecord(pl->prof_start, s);
+  if (cudaLaunchKernel(circuit_kernel_ptr(pl->c.n_qubits, true), dim3(pl->blocks_grad),
+                       dim3(pl->warps_grad * 32), args, pl->smem_grad, s) != cudaSuccess)
+    return QP_ERR_CUDA;
+  if (pl->prof_stop) cudaEventRecord(pl->prof_stop, s);
+  (void)tasks;
+  launches += 1;
+  qpk::PremapArgs ma;
+  std::memset(&ma, 0, sizeof(ma));
+  if (mlp) {
+    for (int i = 0; i < 3; ++i) { ma.pts[i] = pts[i]; ma.npts[i] = npts[i]; }
+    ma.ptot = P;
+    ma.params = d_params; ma.n = pl->c.n_qubits; ma.premap = pl->c.premap; ma.scale = pl->c.scale;
+    ma.F = pl->c.rff_freqs; ma.H = pl->c.mlp_width;
+    ma.thetaJ = (float*)(ws + w.thetaJ);
+    ma.dthetaJ = (const float*)(ws + w.dthetaJ);
+    ma.d1 = (float*)(ws + w.d1); ma.d2 = (float*)(ws + w.d2); ma.u1 = (float*)(ws + w.u1);
+    if (P > 0) {
+      const int pblocks = (int)((P + 127) / 128 < pl->sm_count * 8 ? (P + 127) / 128 : pl->sm_count * 8);
+      void* bargs[] = {&ma};
+      if (cudaLaunchKernel(premap_bwd_ptr(pl->c.mlp_width), dim3(pblocks), dim3(128), bargs,
+                           pl->smem_premap, s) != cudaSuccess)
+        return QP_ERR_CUDA;
+      launches += 1;
+    }
+    qpk::WgradArgs wa;
+    wa.p = ma;
+    wa.part = (float*)(ws + w.wpart);
+    wa.nW = (int32_t)(pl->mlp_count - pl->nfixed);
+    wa.tile = pl->wtile;
+    void* wargs[] = {&wa};
+    if (cudaLaunchKernel((void*)qpk::premap_wgrad_kernel, dim3(pl->nwblk), dim3(256), wargs,
+                         pl->smem_wgrad, s) != cudaSuccess)
+      return QP_ERR_CUDA;
+    launches += 1;
+  }
+  qpk::ReduceArgs ra;
+  ra.blk_loss = (const double*)(ws + w.blk_loss);
+  ra.blk_grad = (const float*)(ws + w.blk_grad);
+  ra.nblk = pl->blocks_grad; ra.loss_stride = a.loss_stride; ra.grad_stride = a.grad_stride;
+  ra.wpart = (const float*)(ws + w.wpart);
+  ra.nwblk = mlp ? pl->nwblk : 0;
+  ra.nW = (int32_t)(pl->mlp_count - pl->nfixed);
+  ra.cmat = (const float*)(ws + w.cmat);
+  ra.counts = (const int32_t*)(ws + w.status) + 1;
+  ra.status = (int32_t*)(ws + w.status);
+  ra.loss = d_loss; ra.grad = d_grad;
+  ra.nparams = pl->n_params; ra.circ_off = pl->circ_off; ra.head_off = pl->head_off;
+  ra.mlp_off = pl->nfixed; ra.mlp_count = pl->mlp_count - pl->nfixed;
+  ra.n = pl->c.n_qubits; ra.L = pl->c.n_layers; ra.m = pl->c.n_readout;
+  ra.k = pl->c.ansatz == QP_ANSATZ_BASIC_RYRZ ? 2 : 3;
+  ra.nt = pl->p.energy_nt; ra.medium = pl->p.medium;
+  ra.nc = npts[0]; ra.ni = npts[1]; ra.nb = npts[2];
+  ra.w_ic = pl->p.w_ic; ra.w_bc = pl->p.w_bc; ra.w_energy = pl->p.w_energy;
+  const int64_t nred = pl->n_params > QP_MAXNT ? pl->n_params : QP_MAXNT;
+  qpk::reduce_kernel<<<(unsigned)((nred + 255) / 256), 256, 0, s>>>(ra);
+  launches += 1;
+  pl->last_launches = launches;
+  return cuda_status(cudaGetLastError());
+}
+
+qp_status qp_last_device_error(qp_plan* pl) {
+  if (!pl) return QP_ERR_INVALID_ARG;
+  if (cudaStreamSynchronize(pl->last_stream) != cudaSuccess) return QP_ERR_CUDA;
+  if (!pl->ws) return QP_OK;
+  int32_t st = 0;
+  if (cudaMemcpy(&st, pl->ws, sizeof(st), cudaMemcpyDeviceToHost) != cudaSuccess) return QP_ERR_CUDA;
+  return (qp_status)st;
+}
+
+}  // extern "C"

@@ -1,0 +1,494 @@
+// qp_aux.cuh -- kernels around the circuit: gate preparation, premap forward/backward,
+// weight-gradient reduction and the final FP64 reduction of loss terms and gradients.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "qp_common.h"
+
+namespace qpk {
+
+struct PrepArgs {
+  const float* params;
+  int64_t circ_off;
+  int32_t n, L, ansatz, enc;
+  float* gates;   // [L][n][8]
+  float* cmat;    // [L][n][3][4]: d loss / d angle_k = sum_Q cmat[k][Q] E_Q
+  float* cenc;    // [n][4]
+  int32_t* counts;
+  int32_t* status;
+};
+
+struct dc { double x, y; };
+__device__ inline dc dmul(dc a, dc b) { return {a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x}; }
+__device__ inline dc dadd(dc a, dc b) { return {a.x + b.x, a.y + b.y}; }
+__device__ inline dc dconj(dc a) { return {a.x, -a.y}; }
+struct M2 { dc a, b, c, d; };
+__device__ inline M2 mmul(const M2& p, const M2& q) {
+  return {dadd(dmul(p.a, q.a), dmul(p.b, q.c)), dadd(dmul(p.a, q.b), dmul(p.b, q.d)),
+          dadd(dmul(p.c, q.a), dmul(p.d, q.c)), dadd(dmul(p.c, q.b), dmul(p.d, q.d))};
+}
+__device__ inline M2 mdag(const M2& p) { return {dconj(p.a), dconj(p.c), dconj(p.b), dconj(p.d)}; }
+__device__ inline M2 m_rz(double t) {
+  double s, c;
+  sincos(0.5 * t, &s, &c);
+  return {{c, -s}, {0, 0}, {0, 0}, {c, s}};
+}
+__device__ inline M2 m_ry(double t) {
+  double s, c;
+  sincos(0.5 * t, &s, &c);
+  return {{c, 0}, {-s, 0}, {s, 0}, {c, 0}};
+}
+__device__ inline M2 m_pauli(int k) {
+  if (k == 0) return {{0, 0}, {1, 0}, {1, 0}, {0, 0}};
+  if (k == 1) return {{0, 0}, {0, -1}, {0, 1}, {0, 0}};
+  return {{1, 0}, {0, 0}, {0, 0}, {-1, 0}};
+}
+// c_Q = Tr(Q V G V^dag) / 2 for Q = X, Y, Z: coordinates of the conjugated generator.
+__device__ inline void pauli_coords(const M2& V, int G, float* out) {
+  const M2 M = mmul(mmul(V, m_pauli(G)), mdag(V));
+  out[0] = (float)(0.5 * (M.c.x + M.b.x));  // Tr(X M) = M10 + M01
+  out[1] = (float)(0.5 * (M.c.y - M.b.y));  // Tr(Y M) = -i M10 + i M01 (real part)
+  out[2] = (float)(0.5 * (M.a.x - M.d.x));  // Tr(Z M) = M00 - M11
+  out[3] = 0.f;
+}
+
+// One thread per (layer, qubit): forward gate matrix and gradient coordinates.
+__global__ void prep_kernel(PrepArgs a) {
+  const int t = threadIdx.x + blockIdx.x * blockDim.x;
+  if (t == 0) { a.counts[0] = 0; a.status[0] = 0; }
+  if (t >= a.L * a.n) return;
+  const int l = t / a.n, q = t % a.n;
+  const int k = a.ansatz == 0 ? 2 : 3;
+  const float* p = a.params + a.circ_off + (int64_t)t * k;
+  M2 U, Vk[3];
+  int Gk[3];
+  if (a.ansatz == 0) {  // RY(a) then RZ(b): U = RZ(b) RY(a)
+    const M2 rz = m_rz(p[1]), ry = m_ry(p[0]);
+    U = mmul(rz, ry);
+    Vk[0] = rz; Gk[0] = 1;
+    Vk[1] = {{1, 0}, {0, 0}, {0, 0}, {1, 0}}; Gk[1] = 2;
+  } else {              // Rot(a,b,g) = RZ(g) RY(b) RZ(a), Eq. 28
+    const M2 za = m_rz(p[0]), yb = m_ry(p[1]), zg = m_rz(p[2]);
+    U = mmul(zg, mmul(yb, za));
+    Vk[0] = mmul(zg, yb); Gk[0] = 2;
+    Vk[1] = zg; Gk[1] = 1;
+    Vk[2] = {{1, 0}, {0, 0}, {0, 0}, {1, 0}}; Gk[2] = 2;
+  }
+  float* g = a.gates + (int64_t)t * 8;
+  g[0] = (float)U.a.x; g[1] = (float)U.a.y; g[2] = (float)U.b.x; g[3] = (float)U.b.y;
+  g[4] = (float)U.c.x; g[5] = (float)U.c.y; g[6] = (float)U.d.x; g[7] = (float)U.d.y;
+  for (int kk = 0; kk < 3; ++kk) {
+    float* c = a.cmat + ((int64_t)t * 3 + kk) * 4;
+    if (kk < k) pauli_coords(Vk[kk], Gk[kk], c);
+    else c[0] = c[1] = c[2] = c[3] = 0.f;
+  }
+  if (l == 0) pauli_coords(U, a.enc == 0 ? 0 : 1, a.cenc + q * 4);
+}
+
+// --------------------------------------------------------------------------- premap
+
+struct PremapArgs {
+  const float* pts[3];
+  int64_t npts[3];
+  int64_t ptot;
+  const float* params;
+  int32_t n, premap, scale, n_direct, F, H;
+  float* thetaJ;          // [P][n][4]
+  const float* dthetaJ;   // [P][n][4] (backward)
+  float* d1;              // [P][H][4] dL/dh1, dL/dh1_d
+  float* d2;              // [P][n][4] dL/dh2, dL/dh2_d
+  float* u1;              // [P][H][4] u1, u1_d
+  int32_t* counts;
+  int32_t medium;
+  float disk_r, disk_x0, disk_y0;
+};
+
+// theta = g(h) with a = tanh(h) and one of Eq. 27's scalings; g', g'' in terms of h.
+__device__ __forceinline__ void scale_tanh(int s, float h, float& g0, float& g1, float& g2) {
+  const float t = tanhf(h);
+  const float s2 = 1.f - t * t;
+  const float sh = 1.f / coshf(h);
+  switch (s) {
+    case 0: g0 = t; g1 = s2; g2 = -2.f * t * s2; break;
+    case 1: g0 = 3.14159265358979f * t; g1 = 3.14159265358979f * s2; g2 = -2.f * 3.14159265358979f * t * s2; break;
+    case 2: g0 = (t + 1.f) * 1.57079632679490f; g1 = 1.57079632679490f * s2; g2 = -3.14159265358979f * t * s2; break;
+    case 3: g0 = asinf(t) + 1.57079632679490f; g1 = sh; g2 = -sh * t; break;
+    default: g0 = acosf(t); g1 = -sh; g2 = sh * t; break;
+  }
+}
+// Direct premap: theta = scale(v), derivative w.r.t. v.
+__device__ __forceinline__ void scale_direct(int s, float v, float& g0, float& g1) {
+  switch (s) {
+    case 0: g0 = v; g1 = 1.f; break;
+    case 1: g0 = 3.14159265358979f * v; g1 = 3.14159265358979f; break;
+    case 2: g0 = (v + 1.f) * 1.57079632679490f; g1 = 1.57079632679490f; break;
+    case 3: g0 = asinf(v) + 1.57079632679490f; g1 = rsqrtf(fmaxf(1.f - v * v, 1e-30f)); break;
+    default: g0 = acosf(v); g1 = -rsqrtf(fmaxf(1.f - v * v, 1e-30f)); break;
+  }
+}
+
+__device__ __forceinline__ const float* point_ptr(const PremapArgs& a, int64_t gp, int& set, int64_t& li) {
+  set = 0;
+  li = gp;
+  if (li >= a.npts[0]) { li -= a.npts[0]; set = 1; if (li >= a.npts[1]) { li -= a.npts[1]; set = 2; } }
+  return a.pts[set] + li * 3;
+}
+
+// Hidden layer h1 = W1 r + b1 with r = [cos(Omega v), sin(Omega v)] and its x,y,t tangents.
+template <int H>
+__device__ __forceinline__ void mlp_hidden(const float* sW1, const float* sb1, const float* om, int F,
+                                           float vx, float vy, float vt, float (&h)[H][4]) {
+#pragma unroll
+  for (int o = 0; o < H; ++o) { h[o][0] = sb1[o]; h[o][1] = h[o][2] = h[o][3] = 0.f; }
+  for (int f = 0; f < F; ++f) {
+    const float ox = om[3 * f], oy = om[3 * f + 1], ot = om[3 * f + 2];
+    float sn, cs;
+    sincosf(ox * vx + oy * vy + ot * vt, &sn, &cs);
+#pragma unroll
+    for (int o = 0; o < H; ++o) {
+      const float wc = sW1[o * 2 * F + f], ws = sW1[o * 2 * F + F + f];
+      h[o][0] += wc * cs + ws * sn;
+      const float q = cs * ws - sn * wc;  // d/du of (wc cos u + ws sin u)
+      h[o][1] += q * ox;
+      h[o][2] += q * oy;
+      h[o][3] += q * ot;
+    }
+  }
+}
+
+template <int H>
+__global__ void premap_fwd_kernel(PremapArgs a) {
+  extern __shared__ __align__(16) float psm[];
+  const int F = a.F, n = a.n;
+  float* sW1 = psm;
+  float* sb1 = sW1 + H * 2 * F;
+  float* sW2 = sb1 + H;
+  float* sb2 = sW2 + n * H;
+  float* som = sb2 + n;
+  if (a.premap == 1) {
+    const float* om = a.params;
+    const float* W1 = om + 3 * F;
+    for (int i = threadIdx.x; i < 3 * F; i += blockDim.x) som[i] = om[i];
+    for (int i = threadIdx.x; i < H * 2 * F; i += blockDim.x) sW1[i] = W1[i];
+    for (int i = threadIdx.x; i < H; i += blockDim.x) sb1[i] = W1[H * 2 * F + i];
+    for (int i = threadIdx.x; i < n * H; i += blockDim.x) sW2[i] = W1[H * 2 * F + H + i];
+    for (int i = threadIdx.x; i < n; i += blockDim.x) sb2[i] = W1[H * 2 * F + H + n * H + i];
+    __syncthreads();
+  }
+  for (int64_t gp = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; gp < a.ptot;
+       gp += (int64_t)gridDim.x * blockDim.x) {
+    int set;
+    int64_t li;
+    const float* v = point_ptr(a, gp, set, li);
+    const float vx = v[0], vy = v[1], vt = v[2];
+    float4* out = reinterpret_cast<float4*>(a.thetaJ) + gp * n;
+    if (a.medium == 1 && set == 0) {
+      const float dx = vx - a.disk_x0, dy = vy - a.disk_y0;
+      if (__fmaf_rn(dx, dx, dy * dy) < a.disk_r * a.disk_r) atomicAdd(&a.counts[0], 1);
+    }
+    if (a.premap == 0) {
+      const float vv[3] = {vx, vy, vt};
+      for (int q = 0; q < n; ++q) {
+        float4 o = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (q < a.n_direct) {
+          float g0, g1;
+          scale_direct(a.scale, vv[q], g0, g1);
+          o.x = g0;
+          if (q == 0) o.y = g1;
+          if (q == 1) o.z = g1;
+          if (q == 2) o.w = g1;
+        }
+        out[q] = o;
+      }
+      continue;
+    }
+    float h[H][4];
+    mlp_hidden<H>(sW1, sb1, som, F, vx, vy, vt, h);
+#pragma unroll
+    for (int o = 0; o < H; ++o) {
+      const float u = tanhf(h[o][0]);
+      const float du = 1.f - u * u;
+      h[o][0] = u;
+      h[o][1] *= du; h[o][2] *= du; h[o][3] *= du;
+    }
+    for (int j = 0; j < n; ++j) {
+      float z0 = sb2[j], z1 = 0.f, z2 = 0.f, z3 = 0.f;
+#pragma unroll
+      for (int o = 0; o < H; ++o) {
+        const float w = sW2[j * H + o];
+        z0 += w * h[o][0]; z1 += w * h[o][1]; z2 += w * h[o][2]; z3 += w * h[o][3];
+      }
+      float g0, g1, g2;
+      scale_tanh(a.scale, z0, g0, g1, g2);
+      out[j] = make_float4(g0, g1 * z1, g1 * z2, g1 * z3);
+    }
+  }
+}
+
+// Per-point backward through scale, output layer and tanh hidden layer, given
+// dL/dtheta_j and dL/dJ_jd from the circuit's adjoint sweep.
+template <int H>
+__global__ void premap_bwd_kernel(PremapArgs a) {
+  extern __shared__ __align__(16) float psm[];
+  const int F = a.F, n = a.n;
+  float* sW1 = psm;
+  float* sb1 = sW1 + H * 2 * F;
+  float* sW2 = sb1 + H;
+  float* sb2 = sW2 + n * H;
+  float* som = sb2 + n;
+  {
+    const float* om = a.params;
+    const float* W1 = om + 3 * F;
+    for (int i = threadIdx.x; i < 3 * F; i += blockDim.x) som[i] = om[i];
+    for (int i = threadIdx.x; i < H * 2 * F; i += blockDim.x) sW1[i] = W1[i];
+    for (int i = threadIdx.x; i < H; i += blockDim.x) sb1[i] = W1[H * 2 * F + i];
+    for (int i = threadIdx.x; i < n * H; i += blockDim.x) sW2[i] = W1[H * 2 * F + H + i];
+    for (int i = threadIdx.x; i < n; i += blockDim.x) sb2[i] = W1[H * 2 * F + H + n * H + i];
+    __syncthreads();
+  }
+  for (int64_t gp = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; gp < a.ptot;
+       gp += (int64_t)gridDim.x * blockDim.x) {
+    int set;
+    int64_t li;
+    const float* v = point_ptr(a, gp, set, li);
+    float h[H][4];
+    mlp_hidden<H>(sW1, sb1, som, F, v[0], v[1], v[2], h);
+    float hd[H][4];  // tangents of h1 kept for the second-order term
+#pragma unroll
+    for (int o = 0; o < H; ++o) {
+      const float u = tanhf(h[o][0]);
+      const float du = 1.f - u * u;
+      hd[o][0] = u;
+      hd[o][1] = h[o][1]; hd[o][2] = h[o][2]; hd[o][3] = h[o][3];
+      h[o][0] = u;
+      h[o][1] *= du; h[o][2] *= du; h[o][3] *= du;
+    }
+    float4* u1o = reinterpret_cast<float4*>(a.u1) + gp * H;
+#pragma unroll
+    for (int o = 0; o < H; ++o) u1o[o] = make_float4(h[o][0], h[o][1], h[o][2], h[o][3]);
+    // dL/du1 and dL/du1_d accumulated over outputs j
+    float gu[H][4];
+#pragma unroll
+    for (int o = 0; o < H; ++o) gu[o][0] = gu[o][1] = gu[o][2] = gu[o][3] = 0.f;
+    const float4* dtj = reinterpret_cast<const float4*>(a.dthetaJ) + gp * n;
+    float4* d2o = reinterpret_cast<float4*>(a.d2) + gp * n;
+    for (int j = 0; j < n; ++j) {
+      float z0 = sb2[j], z1 = 0.f, z2 = 0.f, z3 = 0.f;
+#pragma unroll
+      for (int o = 0; o < H; ++o) {
+        const float w = sW2[j * H + o];
+        z0 += w * h[o][0]; z1 += w * h[o][1]; z2 += w * h[o][2]; z3 += w * h[o][3];
+      }
+      float g0, g1, g2;
+      scale_tanh(a.scale, z0, g0, g1, g2);
+      const float4 dt = dtj[j];
+      // theta = g(z0), J_d = g'(z0) z_d
+      const float dz1 = dt.y * g1, dz2 = dt.z * g1, dz3 = dt.w * g1;
+      const float dz0 = dt.x * g1 + g2 * (dt.y * z1 + dt.z * z2 + dt.w * z3);
+      d2o[j] = make_float4(dz0, dz1, dz2, dz3);
+#pragma unroll
+      for (int o = 0; o < H; ++o) {
+        const float w = sW2[j * H + o];
+        gu[o][0] += w * dz0; gu[o][1] += w * dz1; gu[o][2] += w * dz2; gu[o][3] += w * dz3;
+      }
+    }
+    float4* d1o = reinterpret_cast<float4*>(a.d1) + gp * H;
+#pragma unroll
+    for (int o = 0; o < H; ++o) {
+      const float u = hd[o][0];
+      const float du = 1.f - u * u;
+      // u1_d = du * h1_d; d du / d h1 = -2 u du
+      const float g1x = gu[o][1] * du, g1y = gu[o][2] * du, g1t = gu[o][3] * du;
+      const float g10 = gu[o][0] * du -
+                        2.f * u * du * (gu[o][1] * hd[o][1] + gu[o][2] * hd[o][2] + gu[o][3] * hd[o][3]);
+      d1o[o] = make_float4(g10, g1x, g1y, g1t);
+    }
+  }
+}
+
+// Weight gradients of the premap as block partials over contiguous point chunks.
+//   dW1[o][i] = sum_p d1[o].(r_i, r_{i,x}, r_{i,y}, r_{i,t}),  db1[o] = sum_p d1[o].x
+//   dW2[j][o] = sum_p d2[j].(u1[o] with tangents),             db2[j] = sum_p d2[j].x
+struct WgradArgs {
+  PremapArgs p;
+  float* part;        // [grid][nW]
+  int32_t nW;         // H*2F + H + n*H + n
+  int32_t tile;       // points per shared-memory tile
+};
+
+__global__ void premap_wgrad_kernel(WgradArgs w) {
+  extern __shared__ __align__(16) float wsm[];
+  const PremapArgs& a = w.p;
+  const int F = a.F, n = a.n, H = a.H, TP = w.tile;
+  const int F2 = 2 * F;
+  float4* rt = reinterpret_cast<float4*>(wsm);          // [TP][2F]
+  float4* dt = rt + TP * F2;                            // [TP][H]
+  float4* ut = dt + TP * H;                             // [TP][H]
+  float4* d2t = ut + TP * H;                            // [TP][n]
+  float* om = reinterpret_cast<float*>(d2t + TP * n);   // [F][3]
+  for (int i = threadIdx.x; i < 3 * F; i += blockDim.x) om[i] = a.params[i];
+  const int nb1 = (H / 4) * (F2 / 4);   // 4x4 blocks of dW1
+  const int nth = blockDim.x;
+  // per-thread accumulators: up to WS blocks of dW1 (16 each), WS dW2 entries, WS biases
+  constexpr int WS = 4;
+  float acc1[WS][16];
+  float acc2[WS], accb[WS];
+#pragma unroll
+  for (int s = 0; s < WS; ++s) {
+    acc2[s] = 0.f; accb[s] = 0.f;
+#pragma unroll
+    for (int k = 0; k < 16; ++k) acc1[s][k] = 0.f;
+  }
+  const int64_t chunk = (a.ptot + gridDim.x - 1) / gridDim.x;
+  const int64_t p0 = blockIdx.x * chunk;
+  const int64_t p1 = p0 + chunk < a.ptot ? p0 + chunk : a.ptot;
+  __syncthreads();
+  for (int64_t tb = p0; tb < p1; tb += TP) {
+    const int cnt = (int)((p1 - tb) < TP ? (p1 - tb) : TP);
+    // stage r (with tangents), d1, u1, d2 of the tile
+    for (int e = threadIdx.x; e < cnt * F; e += nth) {
+      const int pi = e / F, f = e % F;
+      int set;
+      int64_t li;
+      const float* v = point_ptr(a, tb + pi, set, li);
+      const float ox = om[3 * f], oy = om[3 * f + 1], ot = om[3 * f + 2];
+      float sn, cs;
+      sincosf(ox * v[0] + oy * v[1] + ot * v[2], &sn, &cs);
+      rt[pi * F2 + f] = make_float4(cs, -sn * ox, -sn * oy, -sn * ot);
+      rt[pi * F2 + F + f] = make_float4(sn, cs * ox, cs * oy, cs * ot);
+    }
+    for (int e = threadIdx.x; e < cnt * H; e += nth) {
+      dt[e] = reinterpret_cast<const float4*>(a.d1)[tb * H + e];
+      ut[e] = reinterpret_cast<const float4*>(a.u1)[tb * H + e];
+    }
+    for (int e = threadIdx.x; e < cnt * n; e += nth) d2t[e] = reinterpret_cast<const float4*>(a.d2)[tb * n + e];
+    __syncthreads();
+#pragma unroll
+    for (int s = 0; s < WS; ++s) {
+      const int blk = threadIdx.x + s * nth;
+      if (blk < nb1) {
+        const int ob = blk / (F2 / 4), ib = blk % (F2 / 4);
+        for (int pi = 0; pi < cnt; ++pi) {
+          float4 d[4], r[4];
+#pragma unroll
+          for (int k = 0; k < 4; ++k) { d[k] = dt[pi * H + ob * 4 + k]; r[k] = rt[pi * F2 + ib * 4 + k]; }
+#pragma unroll
+          for (int oo = 0; oo < 4; ++oo)
+#pragma unroll
+            for (int ii = 0; ii < 4; ++ii)
+              acc1[s][oo * 4 + ii] += d[oo].x * r[ii].x + d[oo].y * r[ii].y + d[oo].z * r[ii].z + d[oo].w * r[ii].w;
+        }
+      }
+      const int e2 = threadIdx.x + s * nth;
+      if (e2 < n * H) {
+        const int j = e2 / H, o = e2 % H;
+        for (int pi = 0; pi < cnt; ++pi) {
+          const float4 d = d2t[pi * n + j], u = ut[pi * H + o];
+          acc2[s] += d.x * u.x + d.y * u.y + d.z * u.z + d.w * u.w;
+        }
+      }
+      const int eb = threadIdx.x + s * nth;
+      if (eb < H + n) {
+        for (int pi = 0; pi < cnt; ++pi) accb[s] += eb < H ? dt[pi * H + eb].x : d2t[pi * n + eb - H].x;
+      }
+    }
+    __syncthreads();
+  }
+  float* out = w.part + (int64_t)blockIdx.x * w.nW;
+  // partial layout: [dW1 (H x 2F)][db1 (H)][dW2 (n x H)][db2 (n)] == parameter layout order
+#pragma unroll
+  for (int s = 0; s < WS; ++s) {
+    const int blk = threadIdx.x + s * nth;
+    if (blk < nb1) {
+      const int ob = blk / (F2 / 4), ib = blk % (F2 / 4);
+#pragma unroll
+      for (int oo = 0; oo < 4; ++oo)
+#pragma unroll
+        for (int ii = 0; ii < 4; ++ii) out[(ob * 4 + oo) * F2 + ib * 4 + ii] = acc1[s][oo * 4 + ii];
+    }
+    const int e2 = threadIdx.x + s * nth;
+    if (e2 < n * H) out[H * F2 + H + e2] = acc2[s];
+    const int eb = threadIdx.x + s * nth;
+    if (eb < H + n) out[eb < H ? H * F2 + eb : H * F2 + H + n * H + (eb - H)] = accb[s];
+  }
+}
+
+// --------------------------------------------------------------------------- final reduce
+
+struct ReduceArgs {
+  const double* blk_loss;
+  const float* blk_grad;
+  int32_t nblk, loss_stride, grad_stride;
+  const float* wpart;
+  int32_t nwblk, nW;
+  const float* cmat;
+  const int32_t* counts;
+  int32_t* status;
+  double* loss;
+  float* grad;
+  int64_t nparams, circ_off, head_off, mlp_off, mlp_count;
+  int32_t n, L, m, k, nt, medium;
+  int64_t nc, ni, nb;
+  float w_ic, w_bc, w_energy;
+};
+
+__global__ void reduce_kernel(ReduceArgs a) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < a.nparams) {
+    float val = 0.f;
+    if (i >= a.circ_off && i < a.head_off) {
+      const int64_t r = i - a.circ_off;
+      const int64_t lq = r / a.k;
+      const int kk = (int)(r % a.k);
+      const float* c = a.cmat + (lq * 3 + kk) * 4;
+      double e0 = 0, e1 = 0, e2 = 0;
+      for (int b = 0; b < a.nblk; ++b) {
+        const float* g = a.blk_grad + (int64_t)b * a.grad_stride + lq * 3;
+        e0 += g[0]; e1 += g[1]; e2 += g[2];
+      }
+      val = (float)(c[0] * e0 + c[1] * e1 + c[2] * e2);
+    } else if (i >= a.head_off) {
+      const int64_t hi = 3LL * a.n * a.L + (i - a.head_off);
+      double s = 0;
+      for (int b = 0; b < a.nblk; ++b) s += a.blk_grad[(int64_t)b * a.grad_stride + hi];
+      val = (float)s;
+    } else if (i >= a.mlp_off && a.mlp_count > 0) {
+      const int64_t wi = i - a.mlp_off;
+      double s = 0;
+      for (int b = 0; b < a.nwblk; ++b) s += a.wpart[(int64_t)b * a.nW + wi];
+      val = (float)s;
+    }
+    a.grad[i] = val;
+  }
+  if (i == 0) {
+    double s[QP_NLP] = {0, 0, 0, 0, 0, 0, 0};
+    for (int b = 0; b < a.nblk; ++b)
+      for (int k = 0; k < QP_NLP; ++k) s[k] += a.blk_loss[(int64_t)b * a.loss_stride + k];
+    const double N = (double)a.nc;
+    const double nd = a.medium == 1 ? (double)a.counts[0] : 0.0;
+    const double nv = N - nd;
+    double m1v = 0, m1d = 0;
+    if (a.medium == 1) {
+      if (nv > 0) m1v = s[0] / nv;
+      if (nd > 0) m1d = s[1] / nd;
+    } else if (N > 0) {
+      m1v = s[0] / N;
+    }
+    const double m2 = N > 0 ? s[2] / N : 0, m3 = N > 0 ? s[3] / N : 0;
+    const double phys = m1v + m1d + m2 + m3;
+    const double en = N > 0 ? a.w_energy * s[4] / N : 0;
+    const double ic = a.ni > 0 ? a.w_ic * s[5] / (double)a.ni : 0;
+    const double bc = a.nb > 0 ? a.w_bc * s[6] / (double)a.nb : 0;
+    const double tot = phys + ic + bc + en;
+    a.loss[0] = tot; a.loss[1] = phys; a.loss[2] = ic; a.loss[3] = bc; a.loss[4] = en;
+    a.loss[5] = m1v; a.loss[6] = m1d; a.loss[7] = m2; a.loss[8] = m3;
+    if (!isfinite(tot)) atomicExch(a.status, (int)5);
+  }
+  if (i < a.nt) {
+    double u = 0;
+    for (int b = 0; b < a.nblk; ++b) u += a.blk_loss[(int64_t)b * a.loss_stride + QP_NLP + i];
+    a.loss[QP_NLP + i] = u;
+  }
+}
+
+}  // namespace qpk

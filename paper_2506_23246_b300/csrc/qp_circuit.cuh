@@ -1,0 +1,646 @@
+// qp_circuit.cuh -- SIMT statevector kernel: embedding, ansatz layers, readout, head,
+// Maxwell/energy loss, costates and the adjoint sweep for one group of lanes per point.
+//
+// Per point the kernel carries four statevectors: phi (the PQC state, Sec. 2.3) and the
+// forward-mode tangents phi_x, phi_y, phi_t, whose Pauli-Z bilinears give the exact input
+// derivatives of the readout, 2 Re<phi_d|Z_i|phi> (Sec. 2.3 last paragraph: the circuit is
+// differentiated w.r.t. its input angles). For the gradient it forms four costates
+//   lambda = O phi + sum_d O_d phi_d,   lambda_d = O_d phi,
+// with O = sum_i zbar_i Z_i, O_d = sum_i zbar_{d,i} Z_i the loss cotangents of the readout,
+// and sweeps the layers backwards: for every single-qubit gate the gradient contribution is
+// sum_s Im<lambda_s|P phi_s> for the Pauli generators P, taken after the gate. Rotations of
+// the same layer act on different qubits, so all of a layer's contributions can be taken at
+// the point after the layer's rotations and before its CNOT ring.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "qp_common.h"
+
+namespace qpk {
+
+struct SmemLayout {
+  int off_gates, off_cenc, off_head, off_eacc, off_hacc, off_loss, off_state, total;
+};
+
+__host__ __device__ inline int align16(int x) { return (x + 15) & ~15; }
+
+// Shared-memory layout of the circuit kernel (identical on host and device).
+__host__ __device__ inline SmemLayout smem_layout(int n, int L, int m, int nt, int warps,
+                                                  int sstride, int ppw) {
+  SmemLayout s;
+  int o = align16((int)sizeof(QPSched));
+  s.off_gates = o; o = align16(o + L * n * 8 * 4);
+  s.off_cenc = o; o = align16(o + n * 4 * 4);
+  s.off_head = o; o = align16(o + (3 * m + 3) * 4);
+  s.off_eacc = o; o = align16(o + 3 * n * L * 4);
+  s.off_hacc = o; o = align16(o + (3 * m + 3) * 4);
+  s.off_loss = o; o = align16(o + (QP_NLP + nt) * 8);
+  s.off_state = o; o = align16(o + warps * ppw * sstride * 8);
+  s.total = o;
+  return s;
+}
+
+__device__ __forceinline__ void gate2(float2& x, float2& y, const float* u) {
+  const float xr = u[0] * x.x - u[1] * x.y + u[2] * y.x - u[3] * y.y;
+  const float xi = u[0] * x.y + u[1] * x.x + u[2] * y.y + u[3] * y.x;
+  const float yr = u[4] * x.x - u[5] * x.y + u[6] * y.x - u[7] * y.y;
+  const float yi = u[4] * x.y + u[5] * x.x + u[6] * y.y + u[7] * y.x;
+  x = make_float2(xr, xi);
+  y = make_float2(yr, yi);
+}
+// Inverse (adjoint) of the same 2x2 gate.
+__device__ __forceinline__ void gate2_inv(float2& x, float2& y, const float* u) {
+  const float xr = u[0] * x.x + u[1] * x.y + u[4] * y.x + u[5] * y.y;
+  const float xi = u[0] * x.y - u[1] * x.x + u[4] * y.y - u[5] * y.x;
+  const float yr = u[2] * x.x + u[3] * x.y + u[6] * y.x + u[7] * y.y;
+  const float yi = u[2] * x.y - u[3] * x.x + u[6] * y.y - u[7] * y.x;
+  x = make_float2(xr, xi);
+  y = make_float2(yr, yi);
+}
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+
+// Unnormalised Walsh-Hadamard transform: out[u] = sum_j (-1)^{popc(u&j)} in[j].
+template <int N>
+__device__ __forceinline__ void wht(float* v) {
+#pragma unroll
+  for (int h = 1; h < N; h <<= 1)
+#pragma unroll
+    for (int j = 0; j < N; ++j)
+      if (!(j & h)) {
+        const float a = v[j], b = v[j | h];
+        v[j] = a + b;
+        v[j | h] = a - b;
+      }
+}
+template <int N>
+__device__ __forceinline__ float pick(const float* v, int u) {
+  float r = v[0];
+#pragma unroll
+  for (int k = 1; k < N; ++k) r = (u == k) ? v[k] : r;
+  return r;
+}
+
+// Accumulate sum over pairs of Im<lam|P phi> for P = X, Y, Z on local bit b.
+template <int AMPS>
+__device__ __forceinline__ void acc_pauli(float* e, const float2* ph, const float2* lm, int b) {
+#pragma unroll
+  for (int j0 = 0; j0 < AMPS; ++j0) {
+    if (j0 & (1 << b)) continue;
+    const int j1 = j0 | (1 << b);
+    const float2 p0 = ph[j0], p1 = ph[j1], l0 = lm[j0], l1 = lm[j1];
+    e[0] += (l0.x * p1.y - l0.y * p1.x) + (l1.x * p0.y - l1.y * p0.x);
+    e[1] += (l1.x * p0.x + l1.y * p0.y) - (l0.x * p1.x + l0.y * p1.y);
+    e[2] += (l0.x * p0.y - l0.y * p0.x) - (l1.x * p1.y - l1.y * p1.x);
+  }
+}
+
+template <int GL>
+__device__ __forceinline__ float group_sum(float v) {
+#pragma unroll
+  for (int o = 1; o < GL; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+template <int GL>
+__device__ __forceinline__ float slot_sum(float v) {
+#pragma unroll
+  for (int o = GL; o < 32; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+struct Shared {
+  const QPSched* s;
+  const float* gates;
+  const float* cenc;
+  const float* head;
+  float* eacc;
+  float* hacc;
+  double* loss;
+};
+
+// One warp-task: PPW points of one set. NV = 4 (point with tangents) or 1 (fields only).
+template <int NQ, int NV, bool GRAD>
+__device__ __forceinline__ void run_task(const QPCircArgs& a, const Shared& sh, float2* wstate,
+                                         int set, int64_t first_pt, int lane) {
+  using Gm = QPGeo<NQ>;
+  constexpr int LB = Gm::LB, AMPS = Gm::AMPS, GL = Gm::GL, DIM = Gm::DIM;
+  constexpr int PG = AMPS <= 8 ? 2 : 1;  // (state, costate) pairs held in registers at once
+  const QPSched& S = *sh.s;
+  const int n = a.n, L = a.L, m = a.m, npl = S.npl;
+  const int slot = lane / GL;
+  const int lin = lane % GL;
+  const int64_t npt = a.npts[set];
+  const int64_t pt = first_pt + slot;
+  const bool active = pt < npt;
+  const int64_t ptc = active ? pt : npt - 1;
+  const int64_t gp = a.pt_base[set] + ptc;
+  float2* st = wstate + slot * a.sstride;
+  const float4* tj = reinterpret_cast<const float4*>(a.thetaJ) + gp * n;
+
+  float2 r[NV][AMPS];
+  int ad[AMPS];
+  float zb[QP_MAXQ], zbd[3][QP_MAXQ];  // readout cotangents (GRAD)
+
+  // ------------------------------------------------------------------ forward passes
+  for (int l = 0; l < L; ++l) {
+    for (int p = 0; p < npl; ++p) {
+      const int P = l * npl + p;
+      const int la = S.lane_addr[P][lane];
+#pragma unroll
+      for (int j = 0; j < AMPS; ++j) ad[j] = la ^ S.joff[P][j];
+      if (P == 0) {
+        // Embedding G(theta_q)|0> per qubit (RX or RY), product state and its tangents
+        // psi_d = sum_q J_qd dpsi/dtheta_q, built by the product rule (no division).
+        const uint32_t K = S.enc_k[lane];
+        float2 A = make_float2(1.f, 0.f);
+        float2 Ad[3] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+        uint32_t localmask = 0;
+#pragma unroll
+        for (int b = 0; b < LB; ++b) localmask |= 1u << S.ql[0][b];
+        for (int q = 0; q < n; ++q) {
+          if ((localmask >> q) & 1u) continue;
+          const float4 t = tj[q];
+          float sn, cs;
+          __sincosf(0.5f * t.x, &sn, &cs);
+          const int bit = (K >> (n - 1 - q)) & 1;
+          float2 gv, gd;
+          if (a.enc == 0) {  // RX|0> = (c, -i s); d/dtheta = (-s/2, -i c/2)
+            gv = bit ? make_float2(0.f, -sn) : make_float2(cs, 0.f);
+            gd = bit ? make_float2(0.f, -0.5f * cs) : make_float2(-0.5f * sn, 0.f);
+          } else {           // RY|0> = (c, s); d/dtheta = (-s/2, c/2)
+            gv = bit ? make_float2(sn, 0.f) : make_float2(cs, 0.f);
+            gd = bit ? make_float2(0.5f * cs, 0.f) : make_float2(-0.5f * sn, 0.f);
+          }
+          if (NV == 4) {
+            const float Jd[3] = {t.y, t.z, t.w};
+#pragma unroll
+            for (int d = 0; d < 3; ++d) Ad[d] = cadd(cmul(Ad[d], gv), cscale(cmul(A, gd), Jd[d]));
+          }
+          A = cmul(A, gv);
+        }
+        float2 g0[LB], g1[LB], h0[LB], h1[LB];
+        float Jl[LB][3];
+#pragma unroll
+        for (int b = 0; b < LB; ++b) {
+          const float4 t = tj[S.ql[0][b]];
+          float sn, cs;
+          __sincosf(0.5f * t.x, &sn, &cs);
+          if (a.enc == 0) {
+            g0[b] = make_float2(cs, 0.f); g1[b] = make_float2(0.f, -sn);
+            h0[b] = make_float2(-0.5f * sn, 0.f); h1[b] = make_float2(0.f, -0.5f * cs);
+          } else {
+            g0[b] = make_float2(cs, 0.f); g1[b] = make_float2(sn, 0.f);
+            h0[b] = make_float2(-0.5f * sn, 0.f); h1[b] = make_float2(0.5f * cs, 0.f);
+          }
+          Jl[b][0] = t.y; Jl[b][1] = t.z; Jl[b][2] = t.w;
+        }
+#pragma unroll
+        for (int j = 0; j < AMPS; ++j) {
+          float2 B = make_float2(1.f, 0.f);
+          float2 Bd[3] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+#pragma unroll
+          for (int b = 0; b < LB; ++b) {
+            const bool bit = (j >> b) & 1;
+            const float2 gv = bit ? g1[b] : g0[b];
+            if (NV == 4) {
+              const float2 gd = bit ? h1[b] : h0[b];
+#pragma unroll
+              for (int d = 0; d < 3; ++d) Bd[d] = cadd(cmul(Bd[d], gv), cscale(cmul(B, gd), Jl[b][d]));
+            }
+            B = cmul(B, gv);
+          }
+          r[0][j] = cmul(A, B);
+          if (NV == 4) {
+#pragma unroll
+            for (int d = 0; d < 3; ++d) r[1 + d][j] = cadd(cmul(Ad[d], B), cmul(A, Bd[d]));
+          }
+        }
+      } else {
+#pragma unroll
+        for (int v = 0; v < NV; ++v)
+#pragma unroll
+          for (int j = 0; j < AMPS; ++j) r[v][j] = st[v * DIM + ad[j]];
+      }
+      // single-qubit gates of this pass
+      const int ng = S.ngate[P];
+#pragma unroll
+      for (int b = 0; b < LB; ++b) {
+        if (b < ng) {
+          float u[8];
+          const float4* gp4 = reinterpret_cast<const float4*>(sh.gates + (l * n + S.ql[P][b]) * 8);
+          const float4 u0 = gp4[0], u1 = gp4[1];
+          u[0] = u0.x; u[1] = u0.y; u[2] = u0.z; u[3] = u0.w;
+          u[4] = u1.x; u[5] = u1.y; u[6] = u1.z; u[7] = u1.w;
+#pragma unroll
+          for (int v = 0; v < NV; ++v)
+#pragma unroll
+            for (int j0 = 0; j0 < AMPS; ++j0)
+              if (!(j0 & (1 << b))) gate2(r[v][j0], r[v][j0 | (1 << b)], u);
+        }
+      }
+      if (P != L * npl - 1) {
+#pragma unroll
+        for (int v = 0; v < NV; ++v)
+#pragma unroll
+          for (int j = 0; j < AMPS; ++j) st[v * DIM + ad[j]] = r[v][j];
+        __syncwarp();
+        continue;
+      }
+
+      // -------------------------------------------------------------- readout (Sec. 2.3)
+      // z_i = sum_k |phi_k|^2 s_i(k); with the lane's sign and the Walsh index of Z_i over
+      // the local bits, s_i(k_j) = sigma_i (-1)^{popc(sel_i & j)}.
+      float wv[NV][AMPS];
+#pragma unroll
+      for (int j = 0; j < AMPS; ++j) {
+        wv[0][j] = r[0][j].x * r[0][j].x + r[0][j].y * r[0][j].y;
+        if (NV == 4) {
+#pragma unroll
+          for (int d = 0; d < 3; ++d)
+            wv[1 + d][j] = 2.f * (r[1 + d][j].x * r[0][j].x + r[1 + d][j].y * r[0][j].y);
+        }
+      }
+#pragma unroll
+      for (int v = 0; v < NV; ++v) wht<AMPS>(wv[v]);
+      const uint32_t rmask = S.ro_mask[lane];
+      float z[QP_MAXQ], dz[3][QP_MAXQ];
+#pragma unroll
+      for (int i = 0; i < QP_MAXQ; ++i) {
+        if (i < m) {
+          const int u = S.ro_sel[i];
+          const float sg = ((rmask >> i) & 1u) ? -1.f : 1.f;
+          z[i] = group_sum<GL>(sg * pick<AMPS>(wv[0], u));
+#pragma unroll
+          for (int d = 0; d < 3; ++d)
+            dz[d][i] = NV == 4 ? group_sum<GL>(sg * pick<AMPS>(wv[1 + d], u)) : 0.f;
+        } else {
+          z[i] = 0.f;
+          dz[0][i] = dz[1][i] = dz[2][i] = 0.f;
+        }
+      }
+      // -------------------------------------------------------------- linear head
+      float f[3], D[3][3];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        float acc = sh.head[3 * m + c];
+        float ad3[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+        for (int i = 0; i < QP_MAXQ; ++i)
+          if (i < m) {
+            const float w = sh.head[c * m + i];
+            acc += w * z[i];
+#pragma unroll
+            for (int d = 0; d < 3; ++d) ad3[d] += w * dz[d][i];
+          }
+        f[c] = acc;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) D[c][d] = ad3[d];
+      }
+      if (!GRAD) {
+        if (active && lin == 0) {
+#pragma unroll
+          for (int c = 0; c < 3; ++c) a.out_f[pt * 3 + c] = f[c];
+          if (NV == 4 && a.out_df) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+#pragma unroll
+              for (int d = 0; d < 3; ++d) a.out_df[pt * 9 + c * 3 + d] = D[c][d];
+          }
+        }
+        return;
+      }
+      // -------------------------------------------------------------- loss and cotangents
+      const float* xp = a.pts[set] + ptc * 3;
+      const float x = xp[0], y = xp[1];
+      float g[3] = {0.f, 0.f, 0.f};
+      float gD[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
+      const QPProblemDev& pb = a.pb;
+      if (set == 0) {
+        // Eqs. 8-10 (1/eps pointwise in the dielectric case), Eq. 23 Poynting residual.
+        float eps = 1.f;
+        bool diel = false;
+        if (pb.medium == 1) {
+          const float dx = x - pb.disk_x0, dy = y - pb.disk_y0;
+          const float r2 = __fmaf_rn(dx, dx, dy * dy);
+          diel = r2 < pb.disk_r * pb.disk_r;
+          const float rr = sqrtf(r2);
+          eps = 1.f + (pb.eps_r - 1.f) / (1.f + __expf(-(pb.disk_r - rr) / pb.sigmoid_w));
+        }
+        const float ie = 1.f / eps;
+        const float res1 = D[0][2] - ie * (D[2][0] - D[1][1]);
+        const float res2 = D[1][2] + D[0][1];
+        const float res3 = D[2][2] - D[0][0];
+        const float e = eps * f[0] * D[0][2] + f[1] * D[1][2] + f[2] * D[2][2] -
+                        (D[0][0] * f[2] + f[0] * D[2][0]) + (D[0][1] * f[1] + f[0] * D[1][1]);
+        const float N = (float)npt;
+        float N1 = N;
+        if (pb.medium == 1) {
+          const float nd = (float)a.counts[0];
+          N1 = diel ? nd : N - nd;
+        }
+        if (active) {
+          const float k1 = 2.f * res1 / N1, k2 = 2.f * res2 / N, k3 = 2.f * res3 / N;
+          const float kE = 2.f * pb.w_energy * e / N;
+          g[0] = kE * (eps * D[0][2] - D[2][0] + D[1][1]);
+          g[1] = kE * (D[1][2] + D[0][1]);
+          g[2] = kE * (D[2][2] - D[0][0]);
+          gD[0][0] = -k3 - kE * f[2];
+          gD[0][1] = k2 + kE * f[1];
+          gD[0][2] = k1 + kE * eps * f[0];
+          gD[1][1] = k1 * ie + kE * f[0];
+          gD[1][2] = k2 + kE * f[1];
+          gD[2][0] = -k1 * ie - kE * f[0];
+          gD[2][2] = k3 + kE * f[2];
+          if (lin == 0) {
+            atomicAdd(&sh.loss[diel ? 1 : 0], (double)res1 * (double)res1);
+            atomicAdd(&sh.loss[2], (double)res2 * (double)res2);
+            atomicAdd(&sh.loss[3], (double)res3 * (double)res3);
+            atomicAdd(&sh.loss[4], (double)e * (double)e);
+            if (pb.energy_nt > 0 && pb.energy_slice > 0) {
+              const int64_t k = pt / pb.energy_slice;
+              if (k < pb.energy_nt)
+                atomicAdd(&sh.loss[QP_NLP + k],
+                          0.5 * ((double)eps * f[0] * f[0] + (double)f[1] * f[1] + (double)f[2] * f[2]));
+            }
+          }
+        }
+      } else if (set == 1) {
+        // Eq. 17: initial-condition misfit against the Gaussian pulse (Eq. 14), H = 0.
+        const float dx = x - pb.ic_x0, dy = y - pb.ic_y0;
+        const float e0 = __expf(-(dx * dx + dy * dy) / (2.f * pb.ic_sigma * pb.ic_sigma));
+        if (active) {
+          const float k = 2.f * pb.w_ic / (float)npt;
+          g[0] = k * (f[0] - e0);
+          g[1] = k * f[1];
+          g[2] = k * f[2];
+          if (lin == 0)
+            atomicAdd(&sh.loss[5], (double)(f[0] - e0) * (f[0] - e0) + (double)f[1] * f[1] +
+                                       (double)f[2] * f[2]);
+        }
+      } else {
+        // PEC boundary: Ez = 0 on the edges.
+        if (active) {
+          g[0] = 2.f * pb.w_bc * f[0] / (float)npt;
+          if (lin == 0) atomicAdd(&sh.loss[6], (double)f[0] * f[0]);
+        }
+      }
+      // back through the head: zbar = W^T g, zbar_d = W^T g_d; head gradients
+#pragma unroll
+      for (int i = 0; i < QP_MAXQ; ++i) {
+        zb[i] = 0.f;
+        zbd[0][i] = zbd[1][i] = zbd[2][i] = 0.f;
+        if (i < m) {
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            const float w = sh.head[c * m + i];
+            zb[i] += w * g[c];
+#pragma unroll
+            for (int d = 0; d < 3; ++d) zbd[d][i] += w * gD[c][d];
+          }
+        }
+      }
+      if (active && lin == 0) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+#pragma unroll
+          for (int i = 0; i < QP_MAXQ; ++i)
+            if (i < m)
+              atomicAdd(&sh.hacc[c * m + i],
+                        g[c] * z[i] + gD[c][0] * dz[0][i] + gD[c][1] * dz[1][i] + gD[c][2] * dz[2][i]);
+          atomicAdd(&sh.hacc[3 * m + c], g[c]);
+        }
+      }
+      // -------------------------------------------------------------- costates
+      // O_j = sum_i zbar_i s_i(k_j) = WHT(h)[j], h[u] = sum_{i: sel_i = u} sigma_i zbar_i.
+      float Ov[NV][AMPS];
+#pragma unroll
+      for (int v = 0; v < NV; ++v)
+#pragma unroll
+        for (int u = 0; u < AMPS; ++u) Ov[v][u] = 0.f;
+#pragma unroll
+      for (int i = 0; i < QP_MAXQ; ++i) {
+        if (i < m) {
+          const int u0 = S.ro_sel[i];
+          const float sg = ((rmask >> i) & 1u) ? -1.f : 1.f;
+#pragma unroll
+          for (int u = 0; u < AMPS; ++u) {
+            const float hit = (u == u0) ? sg : 0.f;
+            Ov[0][u] += hit * zb[i];
+            if (NV == 4) {
+#pragma unroll
+              for (int d = 0; d < 3; ++d) Ov[1 + d][u] += hit * zbd[d][i];
+            }
+          }
+        }
+      }
+#pragma unroll
+      for (int v = 0; v < NV; ++v) wht<AMPS>(Ov[v]);
+#pragma unroll
+      for (int j = 0; j < AMPS; ++j) {
+        const float2 ph = r[0][j];
+        float2 lam = cscale(ph, Ov[0][j]);
+        if (NV == 4) {
+#pragma unroll
+          for (int d = 0; d < 3; ++d) {
+            lam = cadd(lam, cscale(r[1 + d][j], Ov[1 + d][j]));
+            st[(NV + 1 + d) * DIM + ad[j]] = cscale(ph, Ov[1 + d][j]);
+          }
+        }
+        st[NV * DIM + ad[j]] = lam;
+#pragma unroll
+        for (int v = 0; v < NV; ++v) st[v * DIM + ad[j]] = r[v][j];
+      }
+      __syncwarp();
+    }
+  }
+  if (!GRAD) return;
+
+  // ------------------------------------------------------------------ adjoint sweep
+  const bool wdt = a.want_dtheta && NV == 4;
+  for (int l = L - 1; l >= 0; --l) {
+    for (int p = npl - 1; p >= 0; --p) {
+      const int P = l * npl + p;
+      const int la = S.lane_addr[P][lane];
+#pragma unroll
+      for (int j = 0; j < AMPS; ++j) ad[j] = la ^ S.joff[P][j];
+      const int ng = S.ngate[P];
+      float U[LB][8];
+#pragma unroll
+      for (int b = 0; b < LB; ++b) {
+        if (b < ng) {
+          const float4* gp4 = reinterpret_cast<const float4*>(sh.gates + (l * n + S.ql[P][b]) * 8);
+          const float4 u0 = gp4[0], u1 = gp4[1];
+          U[b][0] = u0.x; U[b][1] = u0.y; U[b][2] = u0.z; U[b][3] = u0.w;
+          U[b][4] = u1.x; U[b][5] = u1.y; U[b][6] = u1.z; U[b][7] = u1.w;
+        }
+      }
+      float E[LB][3];
+      float E2[LB][3][3];  // layer 0: Im<lambda_d|P phi> for the input-Jacobian gradient
+#pragma unroll
+      for (int b = 0; b < LB; ++b)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          E[b][k] = 0.f;
+          E2[b][0][k] = E2[b][1][k] = E2[b][2][k] = 0.f;
+        }
+      // (state, costate) pairs: s = 0..NV-1 -> vectors (s, NV + s)
+#pragma unroll
+      for (int s0 = 0; s0 < NV; s0 += PG) {
+        constexpr int NP = (NV < PG) ? NV : PG;
+        float2 xs[NP][AMPS], ys[NP][AMPS];
+#pragma unroll
+        for (int q = 0; q < NP; ++q)
+#pragma unroll
+          for (int j = 0; j < AMPS; ++j) {
+            xs[q][j] = st[(s0 + q) * DIM + ad[j]];
+            ys[q][j] = st[(NV + s0 + q) * DIM + ad[j]];
+          }
+#pragma unroll
+        for (int b = 0; b < LB; ++b)
+          if (b < ng)
+#pragma unroll
+            for (int q = 0; q < NP; ++q) acc_pauli<AMPS>(E[b], xs[q], ys[q], b);
+        if (l > 0) {
+#pragma unroll
+          for (int b = 0; b < LB; ++b)
+            if (b < ng)
+#pragma unroll
+              for (int q = 0; q < NP; ++q)
+#pragma unroll
+                for (int j0 = 0; j0 < AMPS; ++j0)
+                  if (!(j0 & (1 << b))) {
+                    gate2_inv(xs[q][j0], xs[q][j0 | (1 << b)], U[b]);
+                    gate2_inv(ys[q][j0], ys[q][j0 | (1 << b)], U[b]);
+                  }
+#pragma unroll
+          for (int q = 0; q < NP; ++q)
+#pragma unroll
+            for (int j = 0; j < AMPS; ++j) {
+              st[(s0 + q) * DIM + ad[j]] = xs[q][j];
+              st[(NV + s0 + q) * DIM + ad[j]] = ys[q][j];
+            }
+        }
+      }
+      if (l == 0 && wdt) {
+        float2 ph[AMPS];
+#pragma unroll
+        for (int j = 0; j < AMPS; ++j) ph[j] = st[ad[j]];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+          float2 lm[AMPS];
+#pragma unroll
+          for (int j = 0; j < AMPS; ++j) lm[j] = st[(NV + 1 + d) * DIM + ad[j]];
+#pragma unroll
+          for (int b = 0; b < LB; ++b)
+            if (b < ng) acc_pauli<AMPS>(E2[b][d], ph, lm, b);
+        }
+      }
+      __syncwarp();
+      // reductions: per point for layer 0 (embedding gradients), then over the warp
+#pragma unroll
+      for (int b = 0; b < LB; ++b) {
+        if (b >= ng) continue;
+        const int q = S.ql[P][b];
+        if (l == 0) {
+          float e3[3];
+#pragma unroll
+          for (int k = 0; k < 3; ++k) e3[k] = group_sum<GL>(E[b][k]);
+          if (a.want_dtheta) {
+            const float c0 = sh.cenc[q * 4 + 0], c1 = sh.cenc[q * 4 + 1], c2 = sh.cenc[q * 4 + 2];
+            float outv[4];
+            outv[0] = c0 * e3[0] + c1 * e3[1] + c2 * e3[2];
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+              const float s0 = group_sum<GL>(E2[b][d][0]);
+              const float s1 = group_sum<GL>(E2[b][d][1]);
+              const float s2 = group_sum<GL>(E2[b][d][2]);
+              outv[1 + d] = c0 * s0 + c1 * s1 + c2 * s2;
+            }
+            if (active && lin == 0)
+              reinterpret_cast<float4*>(a.dthetaJ)[gp * n + q] =
+                  make_float4(outv[0], outv[1], outv[2], outv[3]);
+          }
+#pragma unroll
+          for (int k = 0; k < 3; ++k) {
+            const float t = slot_sum<GL>(e3[k]);
+            if (lane == 0) atomicAdd(&sh.eacc[(l * n + q) * 3 + k], t);
+          }
+        } else {
+#pragma unroll
+          for (int k = 0; k < 3; ++k) {
+            const float t = slot_sum<GL>(group_sum<GL>(E[b][k]));
+            if (lane == 0) atomicAdd(&sh.eacc[(l * n + q) * 3 + k], t);
+          }
+        }
+      }
+    }
+  }
+}
+
+// Persistent kernel: every warp takes warp-tasks (PPW points of one set) in turn; block
+// partials of the loss sums and gradient sums are written at the end.
+template <int NQ, bool GRAD>
+__global__ void __launch_bounds__(384) circuit_kernel(const __grid_constant__ QPCircArgs a) {
+  using Gm = QPGeo<NQ>;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int warps = blockDim.x >> 5;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nt = GRAD ? a.pb.energy_nt : 0;
+  const SmemLayout lay = smem_layout(a.n, a.L, a.m, nt, warps, a.sstride, Gm::PPW);
+  {
+    const uint32_t* src = reinterpret_cast<const uint32_t*>(&a.s);
+    uint32_t* dst = reinterpret_cast<uint32_t*>(smem);
+    for (int i = threadIdx.x; i < (int)(sizeof(QPSched) / 4); i += blockDim.x) dst[i] = src[i];
+    float* g = reinterpret_cast<float*>(smem + lay.off_gates);
+    for (int i = threadIdx.x; i < a.L * a.n * 8; i += blockDim.x) g[i] = a.gates[i];
+    float* c = reinterpret_cast<float*>(smem + lay.off_cenc);
+    for (int i = threadIdx.x; i < a.n * 4; i += blockDim.x) c[i] = a.cenc ? a.cenc[i] : 0.f;
+    float* h = reinterpret_cast<float*>(smem + lay.off_head);
+    for (int i = threadIdx.x; i < 3 * a.m + 3; i += blockDim.x) h[i] = a.head[i];
+    float* e = reinterpret_cast<float*>(smem + lay.off_eacc);
+    for (int i = threadIdx.x; i < 3 * a.n * a.L; i += blockDim.x) e[i] = 0.f;
+    float* ha = reinterpret_cast<float*>(smem + lay.off_hacc);
+    for (int i = threadIdx.x; i < 3 * a.m + 3; i += blockDim.x) ha[i] = 0.f;
+    double* lo = reinterpret_cast<double*>(smem + lay.off_loss);
+    for (int i = threadIdx.x; i < QP_NLP + nt; i += blockDim.x) lo[i] = 0.0;
+  }
+  __syncthreads();
+  Shared sh;
+  sh.s = reinterpret_cast<const QPSched*>(smem);
+  sh.gates = reinterpret_cast<const float*>(smem + lay.off_gates);
+  sh.cenc = reinterpret_cast<const float*>(smem + lay.off_cenc);
+  sh.head = reinterpret_cast<const float*>(smem + lay.off_head);
+  sh.eacc = reinterpret_cast<float*>(smem + lay.off_eacc);
+  sh.hacc = reinterpret_cast<float*>(smem + lay.off_hacc);
+  sh.loss = reinterpret_cast<double*>(smem + lay.off_loss);
+  float2* wstate = reinterpret_cast<float2*>(smem + lay.off_state) + warp * Gm::PPW * a.sstride;
+
+  const int64_t total = a.task_end[2];
+  const int64_t stride = (int64_t)gridDim.x * warps;
+  for (int64_t t = (int64_t)blockIdx.x * warps + warp; t < total; t += stride) {
+    int set = 0;
+    int64_t base = 0;
+    if (t >= a.task_end[0]) { set = 1; base = a.task_end[0]; }
+    if (t >= a.task_end[1]) { set = 2; base = a.task_end[1]; }
+    const int64_t first = (t - base) * Gm::PPW;
+    if (GRAD) {
+      if (set == 0) run_task<NQ, 4, true>(a, sh, wstate, 0, first, lane);
+      else run_task<NQ, 1, true>(a, sh, wstate, set, first, lane);
+    } else {
+      if (a.want_df) run_task<NQ, 4, false>(a, sh, wstate, 0, first, lane);
+      else run_task<NQ, 1, false>(a, sh, wstate, 0, first, lane);
+    }
+  }
+  if (!GRAD) return;
+  __syncthreads();
+  double* bl = a.blk_loss + (int64_t)blockIdx.x * a.loss_stride;
+  for (int i = threadIdx.x; i < QP_NLP + nt; i += blockDim.x) bl[i] = sh.loss[i];
+  float* bg = a.blk_grad + (int64_t)blockIdx.x * a.grad_stride;
+  for (int i = threadIdx.x; i < 3 * a.n * a.L; i += blockDim.x) bg[i] = sh.eacc[i];
+  for (int i = threadIdx.x; i < 3 * a.m + 3; i += blockDim.x) bg[3 * a.n * a.L + i] = sh.hacc[i];
+}
+
+}  // namespace qpk

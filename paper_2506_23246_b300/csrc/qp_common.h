@@ -1,0 +1,72 @@
+// qp_common.h -- definitions shared by the host planner, the C-ABI and the kernels.
+#pragma once
+#include <stdint.h>
+
+#define QP_MAXQ 10      // qubits
+#define QP_MAXL 16      // ansatz layers
+#define QP_MAXP 48      // gate passes (layers x passes per layer)
+#define QP_MAXNT 256    // energy slices
+#define QP_NLP 7        // loss partial sums: res1 vac, res1 diel, res2, res3, energy, ic, bc
+#define QP_MAXF 256     // RFF frequencies
+#define QP_MAXH 64      // MLP width on the GPU path
+
+// Geometry of one statevector per point group (compile-time per qubit count).
+//   LB   : qubits held in registers per lane ("local" qubits of a pass)
+//   GL   : lanes that share one point (2^(n-LB))
+//   PPW  : points per warp
+template <int NQ>
+struct QPGeo {
+  static constexpr int LB = NQ <= 3 ? NQ : (NQ <= 8 ? 3 : NQ - 5);
+  static constexpr int AMPS = 1 << LB;
+  static constexpr int GL = 1 << (NQ - LB);
+  static constexpr int PPW = 32 / GL;
+  static constexpr int DIM = 1 << NQ;
+};
+
+// Pass schedule produced on the host (see qp_sched.cpp). Pass P = l * npl + p applies the
+// single-qubit gates of layer l to the qubits ql[P][0 .. ngate[P]-1]; lane `lane` holds,
+// for register j, the amplitude stored at shared-memory index lane_addr[P][lane] ^ joff[P][j]
+// of each vector of its point (float2 units).
+struct QPSched {
+  int32_t npass, npl, lb;
+  uint8_t ngate[QP_MAXP];
+  uint8_t ql[QP_MAXP][8];
+  uint16_t lane_addr[QP_MAXP][32];
+  uint16_t joff[QP_MAXP][32];
+  uint16_t enc_k[32];    // logical basis index of each lane's register 0 in pass 0 (frame = I)
+  uint16_t ro_mask[32];  // readout: bit i set -> lane's sign for Z_i flips
+  uint8_t ro_sel[16];    // readout: Walsh index (over local bits) of Z_i in the last pass
+  int32_t conflict_max;  // planner's worst predicted bank-conflict factor
+};
+
+struct QPProblemDev {
+  int32_t medium;
+  float eps_r, disk_r, disk_x0, disk_y0, sigmoid_w;
+  float ic_sigma, ic_x0, ic_y0, w_ic, w_bc, w_energy;
+  int32_t energy_slice, energy_nt;
+};
+
+// Arguments of the circuit kernel (passed by value; the schedule is copied to shared memory).
+struct QPCircArgs {
+  QPSched s;
+  QPProblemDev pb;
+  int32_t n, L, m, enc;
+  int32_t sstride;            // float2 per point slot in shared memory
+  int32_t want_dtheta;        // write per-point dL/dtheta, dL/dJ
+  int32_t want_df;            // forward mode: derivatives requested
+  const float* pts[3];        // colloc, ic, bc
+  int64_t npts[3];
+  int64_t task_end[3];        // cumulative warp-task counts per set
+  int64_t pt_base[3];         // first global point index of each set (theta/J rows)
+  const float* thetaJ;        // [P][n][4] (theta, dtheta/dx, dtheta/dy, dtheta/dt)
+  float* dthetaJ;             // [P][n][4] (dL/dtheta, dL/dJ_x, dL/dJ_y, dL/dJ_t)
+  const float* gates;         // [L][n][8] forward 2x2 complex gate per qubit and layer
+  const float* cenc;          // [n][4] Pauli coefficients of the embedding generator
+  const float* head;          // W[3][m], b[3]
+  const int32_t* counts;      // [0] dielectric-set size
+  double* blk_loss;           // [grid][QP_NLP + nt]
+  float* blk_grad;            // [grid][3 n L + 3 m + 3]
+  float* out_f;               // forward mode [B][3]
+  float* out_df;              // forward mode [B][3][3]
+  int32_t loss_stride, grad_stride;
+};

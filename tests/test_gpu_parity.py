@@ -1,0 +1,264 @@
+"""GPU parity: the CUDA path (through the C-ABI) against the FP64 oracle, element by element.
+
+Tolerance (spec bar, 1e-5 relative): for every output channel c,
+    max |gpu - oracle| <= 1e-5 * max(|oracle channel|_inf, floor)
+Channels: each field, each input derivative d/dx, d/dy, d/dt of each field, each loss term,
+and the gradient vector per parameter block (circuit, head, MLP).
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2506_23246_b300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2506_23246_b300 import build
+    build.build()
+    return torch
+
+
+def _rel(gpu, ref, floor=1e-12):
+    gpu = np.asarray(gpu, dtype=np.float64)
+    ref = np.asarray(ref, dtype=np.float64)
+    scale = max(float(np.max(np.abs(ref))) if ref.size else 0.0, floor)
+    return float(np.max(np.abs(gpu - ref))) / scale if ref.size else 0.0
+
+
+def _forward_check(torch, oracle, circ, params, pts, want_df=True, tol=TOL):
+    from paper_2506_23246_b300 import qp
+    plan = qp.Plan(circ)
+    dp = torch.tensor(params, device="cuda")
+    dx = torch.tensor(pts, device="cuda")
+    f, df = plan.forward(dp, dx, want_df=want_df)
+    torch.cuda.synchronize()
+    fo, dfo = oracle.forward(circ, params, pts)
+    f = f.cpu().numpy()
+    for c in range(3):
+        assert _rel(f[:, c], fo[:, c]) < tol, ("field", c, _rel(f[:, c], fo[:, c]))
+    if want_df:
+        df = df.cpu().numpy()
+        for c in range(3):
+            for d in range(3):
+                r = _rel(df[:, c, d], dfo[:, c, d])
+                assert r < tol, ("dfield", c, d, r)
+    return plan
+
+
+def test_c1_forward_parity(torch_cuda, oracle):
+    """4 qubits, 2 layers, RY(pi v) embedding, B = 1024: fields and d/dx,dy,dt."""
+    circ, params, pts = W.c1_workload(0, 1024)
+    _forward_check(torch_cuda, oracle, circ, params, pts)
+
+
+@pytest.mark.parametrize("B", [1, 2, 15, 17, 33, 1000])
+def test_c1_forward_ragged(torch_cuda, oracle, B):
+    circ, params, pts = W.c1_workload(1, B)
+    _forward_check(torch_cuda, oracle, circ, params, pts)
+
+
+def test_forward_without_derivatives(torch_cuda, oracle):
+    circ, params, pts = W.c1_workload(2, 100)
+    _forward_check(torch_cuda, oracle, circ, params, pts, want_df=False)
+
+
+@pytest.mark.parametrize("n", list(range(1, 11)))
+@pytest.mark.parametrize("ansatz", ["basic_ryrz", "strong_rot", "noent_rot"])
+def test_forward_all_qubit_counts(torch_cuda, oracle, n, ansatz):
+    L = 3 if n <= 8 else 2
+    circ = W.circuit(n, L, min(n, 3) if ansatz == "basic_ryrz" else n, ansatz=ansatz,
+                     enc="rx" if ansatz != "basic_ryrz" else "ry", scale="pi", premap="direct",
+                     n_direct=min(3, n))
+    params = W.init_params(circ, n)
+    pts = W.uniform_points(70, 100 + n)
+    _forward_check(torch_cuda, oracle, circ, params, pts)
+
+
+def test_forward_rff_mlp_premap(torch_cuda, oracle):
+    circ = W.c3_circuit(8, 6)
+    params = W.init_params(circ, 3)
+    pts = W.grid_points(8, 8, 2, 0.7)
+    _forward_check(torch_cuda, oracle, circ, params, pts)
+
+
+# ----------------------------------------------------------------------------- loss + grad
+
+def _loss_grad_check(torch, oracle, circ, prob, params, sets, idx=None, tol=TOL):
+    from paper_2506_23246_b300 import qp
+    plan = qp.Plan(circ, prob)
+    dp = torch.tensor(params, device="cuda")
+    dsets = {k: torch.tensor(v, device="cuda") for k, v in sets.items()}
+    loss, grad = plan.loss_grad(dp, dsets)
+    torch.cuda.synchronize()
+    assert plan.last_device_error() == 0
+    loss = loss.cpu().numpy()
+    grad = grad.cpu().numpy()
+    lo = oracle.loss(circ, prob, params, sets)
+    for i in range(lo.shape[0]):
+        r = abs(loss[i] - lo[i]) / max(abs(lo[i]), 1e-12)
+        assert r < tol or abs(loss[i] - lo[i]) < 1e-10, ("loss term", i, loss[i], lo[i])
+    lay = oracle.param_layout(circ)
+    if idx is None:
+        idx = np.arange(lay["total"])
+    go = oracle.grad(circ, prob, params, sets, idx)
+    gg = grad[idx]
+    blocks = [(0, lay["fixed"]), (lay["fixed"], lay["circuit"]), (lay["circuit"], lay["head"]),
+              (lay["head"], lay["total"])]
+    for lo_, hi_ in blocks:
+        sel = (idx >= lo_) & (idx < hi_)
+        if sel.any():
+            if hi_ <= lay["fixed"]:
+                assert np.all(gg[sel] == 0.0)
+                continue
+            r = _rel(gg[sel], go[sel])
+            assert r < tol, ("grad block", lo_, hi_, r)
+    return plan, loss, grad
+
+
+def test_c2_loss_grad_parity(torch_cuda, oracle):
+    """6 qubits, 4 layers: Maxwell residuals + IC (sigma 0.1) + PEC boundary, all params."""
+    circ, prob, params, sets = W.c2_workload(0, 512, 128, 128)
+    _loss_grad_check(torch_cuda, oracle, circ, prob, params, sets)
+
+
+@pytest.mark.parametrize("medium", ["vacuum", "dielectric"])
+def test_c3_loss_grad_parity(torch_cuda, oracle, medium):
+    """8 qubits, 6 strongly entangling layers, RFF(64) + tanh MLP(32), energy term:
+    every circuit and head parameter and a sample of MLP parameters."""
+    circ = W.c3_circuit(8, 6)
+    prob = W.c3_problem(medium, 4, 4, 3)
+    prob["disk_x0"], prob["disk_r"] = 0.2, 0.6
+    sets = {"colloc": W.grid_points(4, 4, 3, W.c3_tmax(medium)), "ic": W.ic_grid(4, 2)}
+    params = W.init_params(circ, 5)
+    lay = oracle.param_layout(circ)
+    rng = np.random.default_rng(0)
+    mlp = rng.choice(np.arange(lay["fixed"], lay["circuit"]), 48, replace=False)
+    idx = np.concatenate([np.arange(3), np.sort(mlp), np.arange(lay["circuit"], lay["total"])])
+    _loss_grad_check(torch_cuda, oracle, circ, prob, params, sets, idx)
+
+
+@pytest.mark.parametrize("n,L", [(4, 2), (5, 3), (7, 2), (9, 2), (10, 2)])
+def test_loss_grad_other_sizes(torch_cuda, oracle, n, L):
+    circ = W.circuit(n, L, ansatz="strong_rot", enc="rx", scale="acos", premap="rff_mlp",
+                     rff_freqs=8, mlp_width=8, mlp_depth=1)
+    prob = W.problem("vacuum", w_energy=10.0)
+    sets = {"colloc": W.uniform_points(37, n, 1.5), "ic": W.ic_points_uniform(5, n + 1),
+            "bc": W.bc_points(3, n + 2)}
+    params = W.init_params(circ, n)
+    _loss_grad_check(torch_cuda, oracle, circ, prob, params, sets)
+
+
+def test_loss_grad_empty_sets(torch_cuda, oracle):
+    circ, prob, params, sets = W.c2_workload(1, 40, 9, 0)
+    sets = {"colloc": sets["colloc"], "ic": sets["ic"]}
+    _loss_grad_check(torch_cuda, oracle, circ, prob, params, sets)
+    _loss_grad_check(torch_cuda, oracle, circ, prob, params, {"ic": sets["ic"]})
+
+
+def test_autograd_function(torch_cuda, oracle):
+    from paper_2506_23246_b300 import qp
+    torch = torch_cuda
+    circ, prob, params, sets = W.c2_workload(2, 64, 16, 16)
+    plan = qp.Plan(circ, prob)
+    p = torch.tensor(params, device="cuda", requires_grad=True)
+    dsets = {k: torch.tensor(v, device="cuda") for k, v in sets.items()}
+    total, terms = qp.qpinn_loss(p, plan, dsets)
+    (3.0 * total).backward()
+    _, g = plan.loss_grad(p.detach(), dsets)
+    assert torch.allclose(p.grad, 3.0 * g)
+    assert abs(float(total) - float(terms[0])) < 1e-6 * abs(float(terms[0]))
+
+
+# ----------------------------------------------------------------------------- full size
+
+def test_c3_full_size_sampled_fields(torch_cuda, oracle):
+    """Full 64x64x16 grid in the bench's launch configuration: fields and derivatives at
+    256 sampled points against the oracle, point by point."""
+    from paper_2506_23246_b300 import qp
+    torch = torch_cuda
+    circ, prob, params, sets = W.c3_workload(0)
+    plan = qp.Plan(circ, prob)
+    dp = torch.tensor(params, device="cuda")
+    dx = torch.tensor(sets["colloc"], device="cuda")
+    f, df = plan.forward(dp, dx)
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(1)
+    sel = rng.choice(sets["colloc"].shape[0], 256, replace=False)
+    fo, dfo = oracle.forward(circ, params, sets["colloc"][sel])
+    assert _rel(f.cpu().numpy()[sel], fo) < TOL
+    assert _rel(df.cpu().numpy()[sel].reshape(-1, 9), dfo.reshape(-1, 9)) < TOL
+
+
+def test_c3_full_size_decomposition(torch_cuda):
+    """At full size (vacuum, where every term is a plain mean): the loss and gradient of the
+    whole batch equal the count-weighted combination over two halves of it."""
+    from paper_2506_23246_b300 import qp
+    torch = torch_cuda
+    circ, prob, params, sets = W.c3_workload(0, medium="vacuum")
+    prob = dict(prob, energy_nt=0, energy_slice=0)
+    plan = qp.Plan(circ, prob)
+    dp = torch.tensor(params, device="cuda")
+    c = torch.tensor(sets["colloc"], device="cuda")
+    ic = torch.tensor(sets["ic"], device="cuda")
+    lf, gf = plan.loss_grad(dp, {"colloc": c, "ic": ic})
+    h = c.shape[0] // 2
+    hi = ic.shape[0] // 2
+    l1, g1 = plan.loss_grad(dp, {"colloc": c[:h].contiguous(), "ic": ic[:hi].contiguous()})
+    l1, g1 = l1.clone(), g1.clone()
+    l2, g2 = plan.loss_grad(dp, {"colloc": c[h:].contiguous(), "ic": ic[hi:].contiguous()})
+    torch.cuda.synchronize()
+    comb = 0.5 * (l1 + l2)
+    assert torch.allclose(lf[:9], comb[:9], rtol=1e-5, atol=1e-12)
+    gc = 0.5 * (g1 + g2)
+    assert float((gf - gc).abs().max()) <= 1e-5 * float(gf.abs().max())
+
+
+def test_determinism_and_status(torch_cuda):
+    from paper_2506_23246_b300 import qp
+    torch = torch_cuda
+    circ, prob, params, sets = W.c2_workload(3, 2048, 256, 256)
+    plan = qp.Plan(circ, prob)
+    dp = torch.tensor(params, device="cuda")
+    dsets = {k: torch.tensor(v, device="cuda") for k, v in sets.items()}
+    l1, g1 = plan.loss_grad(dp, dsets)
+    l1, g1 = l1.clone(), g1.clone()
+    l2, g2 = plan.loss_grad(dp, dsets)
+    torch.cuda.synchronize()
+    assert plan.last_device_error() == 0
+    assert torch.allclose(l1, l2, rtol=1e-12) and torch.allclose(g1, g2, rtol=1e-5, atol=1e-7)
+
+
+def test_nonfinite_params_reported(torch_cuda):
+    from paper_2506_23246_b300 import qp
+    torch = torch_cuda
+    circ, prob, params, sets = W.c2_workload(4, 64, 16, 16)
+    plan = qp.Plan(circ, prob)
+    params = params.copy()
+    params[-1] = float("nan")
+    dp = torch.tensor(params, device="cuda")
+    dsets = {k: torch.tensor(v, device="cuda") for k, v in sets.items()}
+    plan.loss_grad(dp, dsets)
+    assert plan.last_device_error() == 5
+
+
+def test_invalid_arguments_rejected_on_host(torch_cuda):
+    from paper_2506_23246_b300 import qp
+    torch = torch_cuda
+    bad = W.circuit(11, 2, premap="direct")
+    with pytest.raises(qp.QPError):
+        qp.Plan(bad)
+    circ, prob, params, sets = W.c2_workload(0, 8, 2, 2)
+    plan = qp.Plan(circ, prob)
+    with pytest.raises(ValueError):
+        plan.loss_grad(torch.zeros(3, device="cuda"), {})
+    rc = qp.lib().qp_forward(plan._h, None, None, 4, None, None, None)
+    assert rc == 1
