@@ -487,7 +487,7 @@ __global__ void reduce_kernel(ReduceArgs a) {
   if (i < a.nt) {
     double u = 0;
     for (int b = 0; b < a.nblk; ++b) u += a.blk_loss[(int64_t)b * a.loss_stride + QP_NLP + i];
-    a.loss[QP_NLP + i] = u;
+    a.loss[QP_NLOSS_OUT + i] = u;
   }
 }
 

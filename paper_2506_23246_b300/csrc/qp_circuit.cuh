@@ -164,7 +164,7 @@ __device__ __forceinline__ void run_task(const QPCircArgs& a, const Shared& sh, 
           if ((localmask >> q) & 1u) continue;
           const float4 t = tj[q];
           float sn, cs;
-          __sincosf(0.5f * t.x, &sn, &cs);
+          sincosf(0.5f * t.x, &sn, &cs);
           const int bit = (K >> (n - 1 - q)) & 1;
           float2 gv, gd;
           if (a.enc == 0) {  // RX|0> = (c, -i s); d/dtheta = (-s/2, -i c/2)
@@ -187,7 +187,7 @@ __device__ __forceinline__ void run_task(const QPCircArgs& a, const Shared& sh, 
         for (int b = 0; b < LB; ++b) {
           const float4 t = tj[S.ql[0][b]];
           float sn, cs;
-          __sincosf(0.5f * t.x, &sn, &cs);
+          sincosf(0.5f * t.x, &sn, &cs);
           if (a.enc == 0) {
             g0[b] = make_float2(cs, 0.f); g1[b] = make_float2(0.f, -sn);
             h0[b] = make_float2(-0.5f * sn, 0.f); h1[b] = make_float2(0.f, -0.5f * cs);
@@ -327,7 +327,7 @@ __device__ __forceinline__ void run_task(const QPCircArgs& a, const Shared& sh, 
           const float r2 = __fmaf_rn(dx, dx, dy * dy);
           diel = r2 < pb.disk_r * pb.disk_r;
           const float rr = sqrtf(r2);
-          eps = 1.f + (pb.eps_r - 1.f) / (1.f + __expf(-(pb.disk_r - rr) / pb.sigmoid_w));
+          eps = 1.f + (pb.eps_r - 1.f) / (1.f + expf(-(pb.disk_r - rr) / pb.sigmoid_w));
         }
         const float ie = 1.f / eps;
         const float res1 = D[0][2] - ie * (D[2][0] - D[1][1]);
@@ -370,7 +370,7 @@ __device__ __forceinline__ void run_task(const QPCircArgs& a, const Shared& sh, 
       } else if (set == 1) {
         // Eq. 17: initial-condition misfit against the Gaussian pulse (Eq. 14), H = 0.
         const float dx = x - pb.ic_x0, dy = y - pb.ic_y0;
-        const float e0 = __expf(-(dx * dx + dy * dy) / (2.f * pb.ic_sigma * pb.ic_sigma));
+        const float e0 = expf(-(dx * dx + dy * dy) / (2.f * pb.ic_sigma * pb.ic_sigma));
         if (active) {
           const float k = 2.f * pb.w_ic / (float)npt;
           g[0] = k * (f[0] - e0);

@@ -7,6 +7,7 @@
 #define QP_MAXP 48      // gate passes (layers x passes per layer)
 #define QP_MAXNT 256    // energy slices
 #define QP_NLP 7        // loss partial sums: res1 vac, res1 diel, res2, res3, energy, ic, bc
+#define QP_NLOSS_OUT 9  // loss terms written before the energy slices (QP_NLOSS of qpinn.h)
 #define QP_MAXF 256     // RFF frequencies
 #define QP_MAXH 64      // MLP width on the GPU path
 

@@ -214,6 +214,11 @@ class Plan:
 
     def set_profile_events(self, start=None, stop=None):
         """Record two torch.cuda.Event objects around the circuit kernel of later calls."""
+        if start is not None:
+            # torch creates the CUDA event on first record; make sure both handles exist
+            start.record()
+            stop.record()
+            torch.cuda.synchronize()
         s = ctypes.c_void_p(start.cuda_event) if start is not None else ctypes.c_void_p(0)
         e = ctypes.c_void_p(stop.cuda_event) if stop is not None else ctypes.c_void_p(0)
         _check(lib().qp_set_profile_events(self._h, s, e), "qp_set_profile_events")
