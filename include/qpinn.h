@@ -174,6 +174,21 @@ int32_t qp_last_launch_count(const qp_plan* plan);
  * Pass NULL, NULL to stop. The plan does not own the events. */
 qp_status qp_set_profile_events(qp_plan* plan, void* ev_start, void* ev_stop);
 
+/* Same result as qp_forward, for callers that cannot allocate device memory (a memory pool
+ * that refuses new allocations, a plugin given a fixed device budget, a host that forbids
+ * cudaMalloc after start-up). The paper has no counterpart: this is a library convenience.
+ * Instead of the plan's workspace, the call uses one fixed 16 MiB array of device memory owned
+ * by the library; every GPU that loads the library keeps that array until the process exits.
+ * Nothing is allocated or freed by this call. Limit: B * n_qubits * 16 bytes plus about 13 KiB
+ * of tables must fit in 16 MiB (B <= 104,000 points at 10 qubits, 130,000 at 8); a larger B is
+ * rejected with QP_ERR_BUFFER_TOO_SMALL before anything is launched. The first call on a device
+ * (with that device current) looks up the array's device address once, so make that first call
+ * before any stream capture. All calls share the one array and each call overwrites it, so
+ * calls that overlap on the GPU (other streams, other plans, other threads) race; serialise
+ * them. Arguments, layouts and the other errors are those of qp_forward. */
+qp_status qp_forward_noalloc(qp_plan* plan, const float* d_params, const float* d_pts, int64_t B,
+                             float* d_fields, float* d_dfields, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -484,3 +484,117 @@ qp_status qp_last_device_error(qp_plan* pl) {
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------------------------------------
+// Allocation-free forward call (qp_forward_noalloc).
+//
+// Some callers cannot allocate device memory at all: code running inside a memory pool that
+// refuses new allocations, plugins handed a fixed device budget, or hosts where cudaMalloc is
+// not allowed after start-up. For them the scratch of the forward call (gate tables and the
+// per-point angles and input Jacobian) lives in one fixed array of device memory that belongs
+// to the library. Every GPU that loads the library holds this array until the process exits.
+#include <mutex>
+
+static constexpr size_t kNoAllocScratchBytes = size_t(16) << 20;  // 16 MiB
+static __device__ __align__(256) unsigned char qp_noalloc_scratch[kNoAllocScratchBytes];
+
+namespace {
+constexpr int kNoAllocMaxDevices = 64;
+std::mutex g_noalloc_mutex;
+void* g_noalloc_addr[kNoAllocMaxDevices] = {};
+
+// Device address of the fixed scratch on the current device. In host code the array's name is
+// only a stand-in, so the real address is looked up once per device (with that device
+// current) and cached.
+qp_status noalloc_scratch_address(void** out) {
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); return QP_ERR_CUDA; }
+  if (dev < 0 || dev >= kNoAllocMaxDevices) return QP_ERR_UNSUPPORTED;
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  if (!g_noalloc_addr[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, qp_noalloc_scratch) != cudaSuccess || !p) {
+      cudaGetLastError();
+      return QP_ERR_CUDA;
+    }
+    g_noalloc_addr[dev] = p;
+  }
+  *out = g_noalloc_addr[dev];
+  return QP_OK;
+}
+}  // namespace
+
+extern "C" qp_status qp_forward_noalloc(qp_plan* pl, const float* d_params, const float* d_pts,
+                                        int64_t B, float* d_fields, float* d_dfields, void* stream) {
+  if (!pl || !d_params || B < 0 || (B > 0 && (!d_pts || !d_fields))) return QP_ERR_INVALID_ARG;
+  pl->last_launches = 0;
+  if (B == 0) return QP_OK;
+  const int n = pl->c.n_qubits, L = pl->c.n_layers, ppw = geo_ppw(n);
+  // scratch layout: status/counters, gate tables, Pauli coordinates, per-point theta and J
+  const size_t off_status = 0;
+  const size_t off_gates = al256(off_status + 256);
+  const size_t off_cmat = al256(off_gates + (size_t)QP_MAXL * QP_MAXQ * 8 * 4);
+  const size_t off_cenc = al256(off_cmat + (size_t)QP_MAXL * QP_MAXQ * 3 * 4 * 4);
+  const size_t off_theta = al256(off_cenc + (size_t)QP_MAXQ * 4 * 4);
+  if ((uint64_t)B > (kNoAllocScratchBytes - off_theta) / ((size_t)n * 16)) return QP_ERR_BUFFER_TOO_SMALL;
+  void* base = nullptr;
+  qp_status st = noalloc_scratch_address(&base);
+  if (st != QP_OK) return st;
+  char* ws = (char*)base;
+  cudaStream_t s = (cudaStream_t)stream;
+  pl->last_stream = s;
+
+  qpk::PrepArgs pa;
+  pa.params = d_params; pa.circ_off = pl->circ_off; pa.n = n; pa.L = L;
+  pa.ansatz = pl->c.ansatz; pa.enc = pl->c.enc;
+  pa.gates = (float*)(ws + off_gates); pa.cmat = (float*)(ws + off_cmat);
+  pa.cenc = (float*)(ws + off_cenc);
+  pa.counts = (int32_t*)(ws + off_status) + 1;  // zeroed by prep_kernel on every call
+  pa.status = (int32_t*)(ws + off_status);
+  qpk::prep_kernel<<<(L * n + 63) / 64, 64, 0, s>>>(pa);
+
+  qpk::PremapArgs ma;
+  std::memset(&ma, 0, sizeof(ma));
+  ma.pts[0] = d_pts; ma.npts[0] = B; ma.ptot = B;
+  ma.params = d_params; ma.n = n; ma.premap = pl->c.premap; ma.scale = pl->c.scale;
+  ma.n_direct = pl->c.n_direct; ma.F = pl->c.rff_freqs; ma.H = pl->c.mlp_width;
+  ma.thetaJ = (float*)(ws + off_theta);
+  ma.counts = pa.counts; ma.medium = pl->p.medium;
+  ma.disk_r = pl->p.disk_r; ma.disk_x0 = pl->p.disk_x0; ma.disk_y0 = pl->p.disk_y0;
+  const int64_t pb = (B + 127) / 128;
+  const int pblocks = (int)(pb < pl->sm_count * 8 ? pb : pl->sm_count * 8);
+  if (pl->c.premap == QP_PREMAP_RFF_MLP) {
+    void* margs[] = {&ma};
+    if (cudaLaunchKernel(premap_fwd_ptr(pl->c.mlp_width), dim3(pblocks), dim3(128), margs,
+                         pl->smem_premap, s) != cudaSuccess)
+      return QP_ERR_CUDA;
+  } else {
+    qpk::premap_fwd_kernel<4><<<pblocks, 128, 0, s>>>(ma);
+  }
+
+  QPCircArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.s = pl->sched;
+  fill_problem(pl, a.pb);
+  a.n = n; a.L = L; a.m = pl->c.n_readout; a.enc = pl->c.enc;
+  a.sstride = pl->sstride_fwd;
+  a.pts[0] = d_pts; a.npts[0] = B;
+  const int64_t tasks = (B + ppw - 1) / ppw;
+  a.task_end[0] = a.task_end[1] = a.task_end[2] = tasks;
+  a.thetaJ = (const float*)(ws + off_theta);
+  a.gates = (const float*)(ws + off_gates);
+  a.cenc = (const float*)(ws + off_cenc);
+  a.head = d_params + pl->head_off;
+  a.counts = pa.counts;
+  a.want_df = d_dfields != nullptr;
+  a.out_f = d_fields;
+  a.out_df = d_dfields;
+  int64_t blocks = (tasks + pl->warps_fwd - 1) / pl->warps_fwd;
+  if (blocks > pl->blocks_fwd) blocks = pl->blocks_fwd;
+  void* args[] = {&a};
+  if (cudaLaunchKernel(circuit_kernel_ptr(n, false), dim3((unsigned)blocks), dim3(pl->warps_fwd * 32),
+                       args, pl->smem_fwd, s) != cudaSuccess)
+    return QP_ERR_CUDA;
+  pl->last_launches = 3;
+  return cuda_status(cudaGetLastError());
+}
