@@ -121,13 +121,49 @@ struct Shared {
   double* loss;
 };
 
-// One warp-task: PPW points of one set. NV = 4 (point with tangents) or 1 (fields only).
-template <int NQ, int NV, bool GRAD>
+// Gate matrices of the pass's gate qubits (uniform shared-memory reads).
+template <int LB>
+__device__ __forceinline__ void load_gates(const Shared& sh, const QPSched& S, int l, int n, int P,
+                                           int ng, float (&U)[LB][8]) {
+#pragma unroll
+  for (int b = 0; b < LB; ++b) {
+    if (b < ng) {
+      const float4* g = reinterpret_cast<const float4*>(sh.gates + (l * n + S.ql[P][b]) * 8);
+      const float4 u0 = g[0], u1 = g[1];
+      U[b][0] = u0.x; U[b][1] = u0.y; U[b][2] = u0.z; U[b][3] = u0.w;
+      U[b][4] = u1.x; U[b][5] = u1.y; U[b][6] = u1.z; U[b][7] = u1.w;
+    }
+  }
+}
+
+// Embedding factor of one local qubit: G(theta)|0> and d/dtheta of it, basis 0 and 1.
+struct EmbedLocal {
+  float2 g0, g1, h0, h1;
+  float J[3];
+};
+__device__ __forceinline__ void embed_factor(int enc, float c, float s, int bit, float2& gv,
+                                             float2& gd) {
+  if (enc == 0) {  // RX|0> = (c, -i s); d/dtheta = (-s/2, -i c/2)
+    gv = bit ? make_float2(0.f, -s) : make_float2(c, 0.f);
+    gd = bit ? make_float2(0.f, -0.5f * c) : make_float2(-0.5f * s, 0.f);
+  } else {         // RY|0> = (c, s); d/dtheta = (-s/2, c/2)
+    gv = bit ? make_float2(s, 0.f) : make_float2(c, 0.f);
+    gd = bit ? make_float2(0.5f * c, 0.f) : make_float2(-0.5f * s, 0.f);
+  }
+}
+__device__ __forceinline__ float pick3(const float4& t, int d) {
+  return d == 0 ? t.y : (d == 1 ? t.z : t.w);
+}
+
+// One warp-task: PPW points of one set. nv = 4 statevectors per point (phi and the tangents
+// phi_x, phi_y, phi_t) for collocation points, 1 where only the fields are needed. Every hot
+// loop body handles one vector (forward) or one (state, costate) pair (adjoint), so the code
+// that runs per gate pass stays small.
+template <int NQ, bool GRAD>
 __device__ __forceinline__ void run_task(const QPCircArgs& a, const Shared& sh, float2* wstate,
-                                         int set, int64_t first_pt, int lane) {
+                                         int set, int64_t first_pt, int lane, int nv) {
   using Gm = QPGeo<NQ>;
   constexpr int LB = Gm::LB, AMPS = Gm::AMPS, GL = Gm::GL, DIM = Gm::DIM;
-  constexpr int PG = AMPS <= 8 ? 2 : 1;  // (state, costate) pairs held in registers at once
   const QPSched& S = *sh.s;
   const int n = a.n, L = a.L, m = a.m, npl = S.npl;
   const int slot = lane / GL;
@@ -139,10 +175,7 @@ __device__ __forceinline__ void run_task(const QPCircArgs& a, const Shared& sh, 
   const int64_t gp = a.pt_base[set] + ptc;
   float2* st = wstate + slot * a.sstride;
   const float4* tj = reinterpret_cast<const float4*>(a.thetaJ) + gp * n;
-
-  float2 r[NV][AMPS];
   int ad[AMPS];
-  float zb[QP_MAXQ], zbd[3][QP_MAXQ];  // readout cotangents (GRAD)
 
   // ------------------------------------------------------------------ forward passes
   for (int l = 0; l < L; ++l) {
@@ -151,315 +184,288 @@ __device__ __forceinline__ void run_task(const QPCircArgs& a, const Shared& sh, 
       const int la = S.lane_addr[P][lane];
 #pragma unroll
       for (int j = 0; j < AMPS; ++j) ad[j] = la ^ S.joff[P][j];
+      const int ng = S.ngate[P];
+      float U[LB][8];
+      load_gates<LB>(sh, S, l, n, P, ng, U);
+      EmbedLocal el[LB];
+      uint32_t localmask = 0;
       if (P == 0) {
-        // Embedding G(theta_q)|0> per qubit (RX or RY), product state and its tangents
-        // psi_d = sum_q J_qd dpsi/dtheta_q, built by the product rule (no division).
-        const uint32_t K = S.enc_k[lane];
-        float2 A = make_float2(1.f, 0.f);
-        float2 Ad[3] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
-        uint32_t localmask = 0;
 #pragma unroll
-        for (int b = 0; b < LB; ++b) localmask |= 1u << S.ql[0][b];
-        for (int q = 0; q < n; ++q) {
-          if ((localmask >> q) & 1u) continue;
+        for (int b = 0; b < LB; ++b) {
+          const int q = S.ql[0][b];
+          localmask |= 1u << q;
           const float4 t = tj[q];
           float sn, cs;
           sincosf(0.5f * t.x, &sn, &cs);
-          const int bit = (K >> (n - 1 - q)) & 1;
-          float2 gv, gd;
-          if (a.enc == 0) {  // RX|0> = (c, -i s); d/dtheta = (-s/2, -i c/2)
-            gv = bit ? make_float2(0.f, -sn) : make_float2(cs, 0.f);
-            gd = bit ? make_float2(0.f, -0.5f * cs) : make_float2(-0.5f * sn, 0.f);
-          } else {           // RY|0> = (c, s); d/dtheta = (-s/2, c/2)
-            gv = bit ? make_float2(sn, 0.f) : make_float2(cs, 0.f);
-            gd = bit ? make_float2(0.5f * cs, 0.f) : make_float2(-0.5f * sn, 0.f);
-          }
-          if (NV == 4) {
-            const float Jd[3] = {t.y, t.z, t.w};
-#pragma unroll
-            for (int d = 0; d < 3; ++d) Ad[d] = cadd(cmul(Ad[d], gv), cscale(cmul(A, gd), Jd[d]));
-          }
-          A = cmul(A, gv);
+          embed_factor(a.enc, cs, sn, 0, el[b].g0, el[b].h0);
+          embed_factor(a.enc, cs, sn, 1, el[b].g1, el[b].h1);
+          el[b].J[0] = t.y; el[b].J[1] = t.z; el[b].J[2] = t.w;
         }
-        float2 g0[LB], g1[LB], h0[LB], h1[LB];
-        float Jl[LB][3];
-#pragma unroll
-        for (int b = 0; b < LB; ++b) {
-          const float4 t = tj[S.ql[0][b]];
-          float sn, cs;
-          sincosf(0.5f * t.x, &sn, &cs);
-          if (a.enc == 0) {
-            g0[b] = make_float2(cs, 0.f); g1[b] = make_float2(0.f, -sn);
-            h0[b] = make_float2(-0.5f * sn, 0.f); h1[b] = make_float2(0.f, -0.5f * cs);
-          } else {
-            g0[b] = make_float2(cs, 0.f); g1[b] = make_float2(sn, 0.f);
-            h0[b] = make_float2(-0.5f * sn, 0.f); h1[b] = make_float2(0.5f * cs, 0.f);
-          }
-          Jl[b][0] = t.y; Jl[b][1] = t.z; Jl[b][2] = t.w;
-        }
-#pragma unroll
-        for (int j = 0; j < AMPS; ++j) {
-          float2 B = make_float2(1.f, 0.f);
-          float2 Bd[3] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
-#pragma unroll
-          for (int b = 0; b < LB; ++b) {
-            const bool bit = (j >> b) & 1;
-            const float2 gv = bit ? g1[b] : g0[b];
-            if (NV == 4) {
-              const float2 gd = bit ? h1[b] : h0[b];
-#pragma unroll
-              for (int d = 0; d < 3; ++d) Bd[d] = cadd(cmul(Bd[d], gv), cscale(cmul(B, gd), Jl[b][d]));
-            }
-            B = cmul(B, gv);
-          }
-          r[0][j] = cmul(A, B);
-          if (NV == 4) {
-#pragma unroll
-            for (int d = 0; d < 3; ++d) r[1 + d][j] = cadd(cmul(Ad[d], B), cmul(A, Bd[d]));
-          }
-        }
-      } else {
-#pragma unroll
-        for (int v = 0; v < NV; ++v)
-#pragma unroll
-          for (int j = 0; j < AMPS; ++j) r[v][j] = st[v * DIM + ad[j]];
       }
-      // single-qubit gates of this pass
-      const int ng = S.ngate[P];
+#pragma unroll 1
+      for (int v = 0; v < nv; ++v) {
+        float2 r[AMPS];
+        float2* sv = st + v * DIM;
+        if (P == 0) {
+          // product state G(theta_q)|0> over all qubits, or its tangent in direction d = v-1:
+          // psi_d = sum_q J_qd dpsi/dtheta_q, by the product rule (no division)
+          const int d = v - 1;
+          const uint32_t K = S.enc_k[lane];
+          float2 A = make_float2(1.f, 0.f), Ad = make_float2(0.f, 0.f);
+          for (int q = 0; q < n; ++q) {
+            if ((localmask >> q) & 1u) continue;
+            const float4 t = tj[q];
+            float sn, cs;
+            sincosf(0.5f * t.x, &sn, &cs);
+            float2 gv, gd;
+            embed_factor(a.enc, cs, sn, (K >> (n - 1 - q)) & 1, gv, gd);
+            if (v > 0) Ad = cadd(cmul(Ad, gv), cscale(cmul(A, gd), pick3(t, d)));
+            A = cmul(A, gv);
+          }
 #pragma unroll
-      for (int b = 0; b < LB; ++b) {
-        if (b < ng) {
-          float u[8];
-          const float4* gp4 = reinterpret_cast<const float4*>(sh.gates + (l * n + S.ql[P][b]) * 8);
-          const float4 u0 = gp4[0], u1 = gp4[1];
-          u[0] = u0.x; u[1] = u0.y; u[2] = u0.z; u[3] = u0.w;
-          u[4] = u1.x; u[5] = u1.y; u[6] = u1.z; u[7] = u1.w;
+          for (int j = 0; j < AMPS; ++j) {
+            float2 B = make_float2(1.f, 0.f), Bd = make_float2(0.f, 0.f);
 #pragma unroll
-          for (int v = 0; v < NV; ++v)
+            for (int b = 0; b < LB; ++b) {
+              const bool bit = (j >> b) & 1;
+              const float2 gv = bit ? el[b].g1 : el[b].g0;
+              if (v > 0) {
+                const float2 gd = bit ? el[b].h1 : el[b].h0;
+                const float Jb = d == 0 ? el[b].J[0] : (d == 1 ? el[b].J[1] : el[b].J[2]);
+                Bd = cadd(cmul(Bd, gv), cscale(cmul(B, gd), Jb));
+              }
+              B = cmul(B, gv);
+            }
+            r[j] = v > 0 ? cadd(cmul(Ad, B), cmul(A, Bd)) : cmul(A, B);
+          }
+        } else {
+#pragma unroll
+          for (int j = 0; j < AMPS; ++j) r[j] = sv[ad[j]];
+        }
+#pragma unroll
+        for (int b = 0; b < LB; ++b)
+          if (b < ng)
 #pragma unroll
             for (int j0 = 0; j0 < AMPS; ++j0)
-              if (!(j0 & (1 << b))) gate2(r[v][j0], r[v][j0 | (1 << b)], u);
-        }
-      }
-      if (P != L * npl - 1) {
+              if (!(j0 & (1 << b))) gate2(r[j0], r[j0 | (1 << b)], U[b]);
 #pragma unroll
-        for (int v = 0; v < NV; ++v)
-#pragma unroll
-          for (int j = 0; j < AMPS; ++j) st[v * DIM + ad[j]] = r[v][j];
-        __syncwarp();
-        continue;
-      }
-
-      // -------------------------------------------------------------- readout (Sec. 2.3)
-      // z_i = sum_k |phi_k|^2 s_i(k); with the lane's sign and the Walsh index of Z_i over
-      // the local bits, s_i(k_j) = sigma_i (-1)^{popc(sel_i & j)}.
-      float wv[NV][AMPS];
-#pragma unroll
-      for (int j = 0; j < AMPS; ++j) {
-        wv[0][j] = r[0][j].x * r[0][j].x + r[0][j].y * r[0][j].y;
-        if (NV == 4) {
-#pragma unroll
-          for (int d = 0; d < 3; ++d)
-            wv[1 + d][j] = 2.f * (r[1 + d][j].x * r[0][j].x + r[1 + d][j].y * r[0][j].y);
-        }
-      }
-#pragma unroll
-      for (int v = 0; v < NV; ++v) wht<AMPS>(wv[v]);
-      const uint32_t rmask = S.ro_mask[lane];
-      float z[QP_MAXQ], dz[3][QP_MAXQ];
-#pragma unroll
-      for (int i = 0; i < QP_MAXQ; ++i) {
-        if (i < m) {
-          const int u = S.ro_sel[i];
-          const float sg = ((rmask >> i) & 1u) ? -1.f : 1.f;
-          z[i] = group_sum<GL>(sg * pick<AMPS>(wv[0], u));
-#pragma unroll
-          for (int d = 0; d < 3; ++d)
-            dz[d][i] = NV == 4 ? group_sum<GL>(sg * pick<AMPS>(wv[1 + d], u)) : 0.f;
-        } else {
-          z[i] = 0.f;
-          dz[0][i] = dz[1][i] = dz[2][i] = 0.f;
-        }
-      }
-      // -------------------------------------------------------------- linear head
-      float f[3], D[3][3];
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        float acc = sh.head[3 * m + c];
-        float ad3[3] = {0.f, 0.f, 0.f};
-#pragma unroll
-        for (int i = 0; i < QP_MAXQ; ++i)
-          if (i < m) {
-            const float w = sh.head[c * m + i];
-            acc += w * z[i];
-#pragma unroll
-            for (int d = 0; d < 3; ++d) ad3[d] += w * dz[d][i];
-          }
-        f[c] = acc;
-#pragma unroll
-        for (int d = 0; d < 3; ++d) D[c][d] = ad3[d];
-      }
-      if (!GRAD) {
-        if (active && lin == 0) {
-#pragma unroll
-          for (int c = 0; c < 3; ++c) a.out_f[pt * 3 + c] = f[c];
-          if (NV == 4 && a.out_df) {
-#pragma unroll
-            for (int c = 0; c < 3; ++c)
-#pragma unroll
-              for (int d = 0; d < 3; ++d) a.out_df[pt * 9 + c * 3 + d] = D[c][d];
-          }
-        }
-        return;
-      }
-      // -------------------------------------------------------------- loss and cotangents
-      const float* xp = a.pts[set] + ptc * 3;
-      const float x = xp[0], y = xp[1];
-      float g[3] = {0.f, 0.f, 0.f};
-      float gD[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
-      const QPProblemDev& pb = a.pb;
-      if (set == 0) {
-        // Eqs. 8-10 (1/eps pointwise in the dielectric case), Eq. 23 Poynting residual.
-        float eps = 1.f;
-        bool diel = false;
-        if (pb.medium == 1) {
-          const float dx = x - pb.disk_x0, dy = y - pb.disk_y0;
-          const float r2 = __fmaf_rn(dx, dx, dy * dy);
-          diel = r2 < pb.disk_r * pb.disk_r;
-          const float rr = sqrtf(r2);
-          eps = 1.f + (pb.eps_r - 1.f) / (1.f + expf(-(pb.disk_r - rr) / pb.sigmoid_w));
-        }
-        const float ie = 1.f / eps;
-        const float res1 = D[0][2] - ie * (D[2][0] - D[1][1]);
-        const float res2 = D[1][2] + D[0][1];
-        const float res3 = D[2][2] - D[0][0];
-        const float e = eps * f[0] * D[0][2] + f[1] * D[1][2] + f[2] * D[2][2] -
-                        (D[0][0] * f[2] + f[0] * D[2][0]) + (D[0][1] * f[1] + f[0] * D[1][1]);
-        const float N = (float)npt;
-        float N1 = N;
-        if (pb.medium == 1) {
-          const float nd = (float)a.counts[0];
-          N1 = diel ? nd : N - nd;
-        }
-        if (active) {
-          const float k1 = 2.f * res1 / N1, k2 = 2.f * res2 / N, k3 = 2.f * res3 / N;
-          const float kE = 2.f * pb.w_energy * e / N;
-          g[0] = kE * (eps * D[0][2] - D[2][0] + D[1][1]);
-          g[1] = kE * (D[1][2] + D[0][1]);
-          g[2] = kE * (D[2][2] - D[0][0]);
-          gD[0][0] = -k3 - kE * f[2];
-          gD[0][1] = k2 + kE * f[1];
-          gD[0][2] = k1 + kE * eps * f[0];
-          gD[1][1] = k1 * ie + kE * f[0];
-          gD[1][2] = k2 + kE * f[1];
-          gD[2][0] = -k1 * ie - kE * f[0];
-          gD[2][2] = k3 + kE * f[2];
-          if (lin == 0) {
-            atomicAdd(&sh.loss[diel ? 1 : 0], (double)res1 * (double)res1);
-            atomicAdd(&sh.loss[2], (double)res2 * (double)res2);
-            atomicAdd(&sh.loss[3], (double)res3 * (double)res3);
-            atomicAdd(&sh.loss[4], (double)e * (double)e);
-            if (pb.energy_nt > 0 && pb.energy_slice > 0) {
-              const int64_t k = pt / pb.energy_slice;
-              if (k < pb.energy_nt)
-                atomicAdd(&sh.loss[QP_NLP + k],
-                          0.5 * ((double)eps * f[0] * f[0] + (double)f[1] * f[1] + (double)f[2] * f[2]));
-            }
-          }
-        }
-      } else if (set == 1) {
-        // Eq. 17: initial-condition misfit against the Gaussian pulse (Eq. 14), H = 0.
-        const float dx = x - pb.ic_x0, dy = y - pb.ic_y0;
-        const float e0 = expf(-(dx * dx + dy * dy) / (2.f * pb.ic_sigma * pb.ic_sigma));
-        if (active) {
-          const float k = 2.f * pb.w_ic / (float)npt;
-          g[0] = k * (f[0] - e0);
-          g[1] = k * f[1];
-          g[2] = k * f[2];
-          if (lin == 0)
-            atomicAdd(&sh.loss[5], (double)(f[0] - e0) * (f[0] - e0) + (double)f[1] * f[1] +
-                                       (double)f[2] * f[2]);
-        }
-      } else {
-        // PEC boundary: Ez = 0 on the edges.
-        if (active) {
-          g[0] = 2.f * pb.w_bc * f[0] / (float)npt;
-          if (lin == 0) atomicAdd(&sh.loss[6], (double)f[0] * f[0]);
-        }
-      }
-      // back through the head: zbar = W^T g, zbar_d = W^T g_d; head gradients
-#pragma unroll
-      for (int i = 0; i < QP_MAXQ; ++i) {
-        zb[i] = 0.f;
-        zbd[0][i] = zbd[1][i] = zbd[2][i] = 0.f;
-        if (i < m) {
-#pragma unroll
-          for (int c = 0; c < 3; ++c) {
-            const float w = sh.head[c * m + i];
-            zb[i] += w * g[c];
-#pragma unroll
-            for (int d = 0; d < 3; ++d) zbd[d][i] += w * gD[c][d];
-          }
-        }
-      }
-      if (active && lin == 0) {
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-#pragma unroll
-          for (int i = 0; i < QP_MAXQ; ++i)
-            if (i < m)
-              atomicAdd(&sh.hacc[c * m + i],
-                        g[c] * z[i] + gD[c][0] * dz[0][i] + gD[c][1] * dz[1][i] + gD[c][2] * dz[2][i]);
-          atomicAdd(&sh.hacc[3 * m + c], g[c]);
-        }
-      }
-      // -------------------------------------------------------------- costates
-      // O_j = sum_i zbar_i s_i(k_j) = WHT(h)[j], h[u] = sum_{i: sel_i = u} sigma_i zbar_i.
-      float Ov[NV][AMPS];
-#pragma unroll
-      for (int v = 0; v < NV; ++v)
-#pragma unroll
-        for (int u = 0; u < AMPS; ++u) Ov[v][u] = 0.f;
-#pragma unroll
-      for (int i = 0; i < QP_MAXQ; ++i) {
-        if (i < m) {
-          const int u0 = S.ro_sel[i];
-          const float sg = ((rmask >> i) & 1u) ? -1.f : 1.f;
-#pragma unroll
-          for (int u = 0; u < AMPS; ++u) {
-            const float hit = (u == u0) ? sg : 0.f;
-            Ov[0][u] += hit * zb[i];
-            if (NV == 4) {
-#pragma unroll
-              for (int d = 0; d < 3; ++d) Ov[1 + d][u] += hit * zbd[d][i];
-            }
-          }
-        }
-      }
-#pragma unroll
-      for (int v = 0; v < NV; ++v) wht<AMPS>(Ov[v]);
-#pragma unroll
-      for (int j = 0; j < AMPS; ++j) {
-        const float2 ph = r[0][j];
-        float2 lam = cscale(ph, Ov[0][j]);
-        if (NV == 4) {
-#pragma unroll
-          for (int d = 0; d < 3; ++d) {
-            lam = cadd(lam, cscale(r[1 + d][j], Ov[1 + d][j]));
-            st[(NV + 1 + d) * DIM + ad[j]] = cscale(ph, Ov[1 + d][j]);
-          }
-        }
-        st[NV * DIM + ad[j]] = lam;
-#pragma unroll
-        for (int v = 0; v < NV; ++v) st[v * DIM + ad[j]] = r[v][j];
+        for (int j = 0; j < AMPS; ++j) sv[ad[j]] = r[j];
       }
       __syncwarp();
     }
   }
-  if (!GRAD) return;
+
+  // ------------------------------------------------------------------ readout (Sec. 2.3)
+  // In the last pass's view: z_i = sum_k |phi_k|^2 s_i(k) with the lane's sign and the
+  // Walsh index of Z_i over the local bits, s_i(k_j) = sigma_i (-1)^{popc(sel_i & j)};
+  // d z_i / d v_d = 2 Re <phi_d|Z_i|phi>.
+  float wv[4][AMPS];
+#pragma unroll
+  for (int j = 0; j < AMPS; ++j) {
+    const float2 ph = st[ad[j]];
+    wv[0][j] = ph.x * ph.x + ph.y * ph.y;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      float q = 0.f;
+      if (nv == 4) {
+        const float2 pd = st[(1 + d) * DIM + ad[j]];
+        q = 2.f * (pd.x * ph.x + pd.y * ph.y);
+      }
+      wv[1 + d][j] = q;
+    }
+  }
+#pragma unroll
+  for (int v = 0; v < 4; ++v) wht<AMPS>(wv[v]);
+  const uint32_t rmask = S.ro_mask[lane];
+  float z[QP_MAXQ], dz[3][QP_MAXQ];
+#pragma unroll
+  for (int i = 0; i < QP_MAXQ; ++i) {
+    if (i < m) {
+      const int u = S.ro_sel[i];
+      const float sg = ((rmask >> i) & 1u) ? -1.f : 1.f;
+      z[i] = group_sum<GL>(sg * pick<AMPS>(wv[0], u));
+#pragma unroll
+      for (int d = 0; d < 3; ++d)
+        dz[d][i] = nv == 4 ? group_sum<GL>(sg * pick<AMPS>(wv[1 + d], u)) : 0.f;
+    } else {
+      z[i] = 0.f;
+      dz[0][i] = dz[1][i] = dz[2][i] = 0.f;
+    }
+  }
+  // ------------------------------------------------------------------ linear head
+  float f[3], D[3][3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    float acc = sh.head[3 * m + c];
+    float ad3[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+    for (int i = 0; i < QP_MAXQ; ++i)
+      if (i < m) {
+        const float w = sh.head[c * m + i];
+        acc += w * z[i];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) ad3[d] += w * dz[d][i];
+      }
+    f[c] = acc;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) D[c][d] = ad3[d];
+  }
+  if (!GRAD) {
+    if (active && lin == 0) {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) a.out_f[pt * 3 + c] = f[c];
+      if (nv == 4 && a.out_df) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+          for (int d = 0; d < 3; ++d) a.out_df[pt * 9 + c * 3 + d] = D[c][d];
+      }
+    }
+    return;
+  }
+  // ------------------------------------------------------------------ loss and cotangents
+  const float* xp = a.pts[set] + ptc * 3;
+  const float x = xp[0], y = xp[1];
+  float g[3] = {0.f, 0.f, 0.f};
+  float gD[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
+  const QPProblemDev& pb = a.pb;
+  if (set == 0) {
+    // Eqs. 8-10 (1/eps pointwise in the dielectric case), Eq. 23 Poynting residual.
+    float eps = 1.f;
+    bool diel = false;
+    if (pb.medium == 1) {
+      const float dx = x - pb.disk_x0, dy = y - pb.disk_y0;
+      const float r2 = __fmaf_rn(dx, dx, dy * dy);
+      diel = r2 < pb.disk_r * pb.disk_r;
+      const float rr = sqrtf(r2);
+      eps = 1.f + (pb.eps_r - 1.f) / (1.f + expf(-(pb.disk_r - rr) / pb.sigmoid_w));
+    }
+    const float ie = 1.f / eps;
+    const float res1 = D[0][2] - ie * (D[2][0] - D[1][1]);
+    const float res2 = D[1][2] + D[0][1];
+    const float res3 = D[2][2] - D[0][0];
+    const float e = eps * f[0] * D[0][2] + f[1] * D[1][2] + f[2] * D[2][2] -
+                    (D[0][0] * f[2] + f[0] * D[2][0]) + (D[0][1] * f[1] + f[0] * D[1][1]);
+    const float N = (float)npt;
+    float N1 = N;
+    if (pb.medium == 1) {
+      const float nd = (float)a.counts[0];
+      N1 = diel ? nd : N - nd;
+    }
+    if (active) {
+      const float k1 = 2.f * res1 / N1, k2 = 2.f * res2 / N, k3 = 2.f * res3 / N;
+      const float kE = 2.f * pb.w_energy * e / N;
+      g[0] = kE * (eps * D[0][2] - D[2][0] + D[1][1]);
+      g[1] = kE * (D[1][2] + D[0][1]);
+      g[2] = kE * (D[2][2] - D[0][0]);
+      gD[0][0] = -k3 - kE * f[2];
+      gD[0][1] = k2 + kE * f[1];
+      gD[0][2] = k1 + kE * eps * f[0];
+      gD[1][1] = k1 * ie + kE * f[0];
+      gD[1][2] = k2 + kE * f[1];
+      gD[2][0] = -k1 * ie - kE * f[0];
+      gD[2][2] = k3 + kE * f[2];
+      if (lin == 0) {
+        atomicAdd(&sh.loss[diel ? 1 : 0], (double)res1 * (double)res1);
+        atomicAdd(&sh.loss[2], (double)res2 * (double)res2);
+        atomicAdd(&sh.loss[3], (double)res3 * (double)res3);
+        atomicAdd(&sh.loss[4], (double)e * (double)e);
+        if (pb.energy_nt > 0 && pb.energy_slice > 0) {
+          const int64_t k = pt / pb.energy_slice;
+          if (k < pb.energy_nt)
+            atomicAdd(&sh.loss[QP_NLP + k],
+                      0.5 * ((double)eps * f[0] * f[0] + (double)f[1] * f[1] + (double)f[2] * f[2]));
+        }
+      }
+    }
+  } else if (set == 1) {
+    // Eq. 17: initial-condition misfit against the Gaussian pulse (Eq. 14), H = 0.
+    const float dx = x - pb.ic_x0, dy = y - pb.ic_y0;
+    const float e0 = expf(-(dx * dx + dy * dy) / (2.f * pb.ic_sigma * pb.ic_sigma));
+    if (active) {
+      const float k = 2.f * pb.w_ic / (float)npt;
+      g[0] = k * (f[0] - e0);
+      g[1] = k * f[1];
+      g[2] = k * f[2];
+      if (lin == 0)
+        atomicAdd(&sh.loss[5], (double)(f[0] - e0) * (f[0] - e0) + (double)f[1] * f[1] +
+                                   (double)f[2] * f[2]);
+    }
+  } else {
+    // PEC boundary: Ez = 0 on the edges.
+    if (active) {
+      g[0] = 2.f * pb.w_bc * f[0] / (float)npt;
+      if (lin == 0) atomicAdd(&sh.loss[6], (double)f[0] * f[0]);
+    }
+  }
+  // back through the head: zbar = W^T g, zbar_d = W^T g_d; head gradients
+  float zb[QP_MAXQ], zbd[3][QP_MAXQ];
+#pragma unroll
+  for (int i = 0; i < QP_MAXQ; ++i) {
+    zb[i] = 0.f;
+    zbd[0][i] = zbd[1][i] = zbd[2][i] = 0.f;
+    if (i < m) {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const float w = sh.head[c * m + i];
+        zb[i] += w * g[c];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) zbd[d][i] += w * gD[c][d];
+      }
+    }
+  }
+  if (active && lin == 0) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+#pragma unroll
+      for (int i = 0; i < QP_MAXQ; ++i)
+        if (i < m)
+          atomicAdd(&sh.hacc[c * m + i],
+                    g[c] * z[i] + gD[c][0] * dz[0][i] + gD[c][1] * dz[1][i] + gD[c][2] * dz[2][i]);
+      atomicAdd(&sh.hacc[3 * m + c], g[c]);
+    }
+  }
+  // ------------------------------------------------------------------ costates
+  // O_j = sum_i zbar_i s_i(k_j) = WHT(h)[j], h[u] = sum_{i: sel_i = u} sigma_i zbar_i.
+  float Ov[4][AMPS];
+#pragma unroll
+  for (int v = 0; v < 4; ++v)
+#pragma unroll
+    for (int u = 0; u < AMPS; ++u) Ov[v][u] = 0.f;
+#pragma unroll
+  for (int i = 0; i < QP_MAXQ; ++i) {
+    if (i < m) {
+      const int u0 = S.ro_sel[i];
+      const float sg = ((rmask >> i) & 1u) ? -1.f : 1.f;
+#pragma unroll
+      for (int u = 0; u < AMPS; ++u) {
+        const float hit = (u == u0) ? sg : 0.f;
+        Ov[0][u] += hit * zb[i];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) Ov[1 + d][u] += hit * zbd[d][i];
+      }
+    }
+  }
+#pragma unroll
+  for (int v = 0; v < 4; ++v) wht<AMPS>(Ov[v]);
+  // lambda = O phi + sum_d O_d phi_d (slot nv), lambda_d = O_d phi (slots nv + 1 + d)
+#pragma unroll
+  for (int j = 0; j < AMPS; ++j) {
+    const float2 ph = st[ad[j]];
+    float2 lam = cscale(ph, Ov[0][j]);
+    if (nv == 4) {
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        lam = cadd(lam, cscale(st[(1 + d) * DIM + ad[j]], Ov[1 + d][j]));
+        st[(5 + d) * DIM + ad[j]] = cscale(ph, Ov[1 + d][j]);
+      }
+    }
+    st[nv * DIM + ad[j]] = lam;
+  }
+  __syncwarp();
 
   // ------------------------------------------------------------------ adjoint sweep
-  const bool wdt = a.want_dtheta && NV == 4;
+  const bool wdt = a.want_dtheta && nv == 4;
   for (int l = L - 1; l >= 0; --l) {
     for (int p = npl - 1; p >= 0; --p) {
       const int P = l * npl + p;
@@ -468,62 +474,46 @@ __device__ __forceinline__ void run_task(const QPCircArgs& a, const Shared& sh, 
       for (int j = 0; j < AMPS; ++j) ad[j] = la ^ S.joff[P][j];
       const int ng = S.ngate[P];
       float U[LB][8];
-#pragma unroll
-      for (int b = 0; b < LB; ++b) {
-        if (b < ng) {
-          const float4* gp4 = reinterpret_cast<const float4*>(sh.gates + (l * n + S.ql[P][b]) * 8);
-          const float4 u0 = gp4[0], u1 = gp4[1];
-          U[b][0] = u0.x; U[b][1] = u0.y; U[b][2] = u0.z; U[b][3] = u0.w;
-          U[b][4] = u1.x; U[b][5] = u1.y; U[b][6] = u1.z; U[b][7] = u1.w;
-        }
-      }
+      load_gates<LB>(sh, S, l, n, P, ng, U);
       float E[LB][3];
-      float E2[LB][3][3];  // layer 0: Im<lambda_d|P phi> for the input-Jacobian gradient
 #pragma unroll
-      for (int b = 0; b < LB; ++b)
+      for (int b = 0; b < LB; ++b) E[b][0] = E[b][1] = E[b][2] = 0.f;
+      // (state, costate) pairs: vector s and vector nv + s
+#pragma unroll 1
+      for (int s = 0; s < nv; ++s) {
+        float2 xs[AMPS], ys[AMPS];
+        float2* sx = st + s * DIM;
+        float2* sy = st + (nv + s) * DIM;
 #pragma unroll
-        for (int k = 0; k < 3; ++k) {
-          E[b][k] = 0.f;
-          E2[b][0][k] = E2[b][1][k] = E2[b][2][k] = 0.f;
+        for (int j = 0; j < AMPS; ++j) {
+          xs[j] = sx[ad[j]];
+          ys[j] = sy[ad[j]];
         }
-      // (state, costate) pairs: s = 0..NV-1 -> vectors (s, NV + s)
-#pragma unroll
-      for (int s0 = 0; s0 < NV; s0 += PG) {
-        constexpr int NP = (NV < PG) ? NV : PG;
-        float2 xs[NP][AMPS], ys[NP][AMPS];
-#pragma unroll
-        for (int q = 0; q < NP; ++q)
-#pragma unroll
-          for (int j = 0; j < AMPS; ++j) {
-            xs[q][j] = st[(s0 + q) * DIM + ad[j]];
-            ys[q][j] = st[(NV + s0 + q) * DIM + ad[j]];
-          }
 #pragma unroll
         for (int b = 0; b < LB; ++b)
-          if (b < ng)
-#pragma unroll
-            for (int q = 0; q < NP; ++q) acc_pauli<AMPS>(E[b], xs[q], ys[q], b);
+          if (b < ng) acc_pauli<AMPS>(E[b], xs, ys, b);
         if (l > 0) {
 #pragma unroll
           for (int b = 0; b < LB; ++b)
             if (b < ng)
 #pragma unroll
-              for (int q = 0; q < NP; ++q)
+              for (int j0 = 0; j0 < AMPS; ++j0)
+                if (!(j0 & (1 << b))) {
+                  gate2_inv(xs[j0], xs[j0 | (1 << b)], U[b]);
+                  gate2_inv(ys[j0], ys[j0 | (1 << b)], U[b]);
+                }
 #pragma unroll
-                for (int j0 = 0; j0 < AMPS; ++j0)
-                  if (!(j0 & (1 << b))) {
-                    gate2_inv(xs[q][j0], xs[q][j0 | (1 << b)], U[b]);
-                    gate2_inv(ys[q][j0], ys[q][j0 | (1 << b)], U[b]);
-                  }
-#pragma unroll
-          for (int q = 0; q < NP; ++q)
-#pragma unroll
-            for (int j = 0; j < AMPS; ++j) {
-              st[(s0 + q) * DIM + ad[j]] = xs[q][j];
-              st[(NV + s0 + q) * DIM + ad[j]] = ys[q][j];
-            }
+          for (int j = 0; j < AMPS; ++j) {
+            sx[ad[j]] = xs[j];
+            sy[ad[j]] = ys[j];
+          }
         }
       }
+      float E2[LB][3][3];  // layer 0: Im<lambda_d|P phi> for the input-Jacobian gradient
+#pragma unroll
+      for (int b = 0; b < LB; ++b)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) E2[b][0][k] = E2[b][1][k] = E2[b][2][k] = 0.f;
       if (l == 0 && wdt) {
         float2 ph[AMPS];
 #pragma unroll
@@ -532,7 +522,7 @@ __device__ __forceinline__ void run_task(const QPCircArgs& a, const Shared& sh, 
         for (int d = 0; d < 3; ++d) {
           float2 lm[AMPS];
 #pragma unroll
-          for (int j = 0; j < AMPS; ++j) lm[j] = st[(NV + 1 + d) * DIM + ad[j]];
+          for (int j = 0; j < AMPS; ++j) lm[j] = st[(5 + d) * DIM + ad[j]];
 #pragma unroll
           for (int b = 0; b < LB; ++b)
             if (b < ng) acc_pauli<AMPS>(E2[b][d], ph, lm, b);
@@ -626,13 +616,8 @@ __global__ void __launch_bounds__(384) circuit_kernel(const __grid_constant__ QP
     if (t >= a.task_end[0]) { set = 1; base = a.task_end[0]; }
     if (t >= a.task_end[1]) { set = 2; base = a.task_end[1]; }
     const int64_t first = (t - base) * Gm::PPW;
-    if (GRAD) {
-      if (set == 0) run_task<NQ, 4, true>(a, sh, wstate, 0, first, lane);
-      else run_task<NQ, 1, true>(a, sh, wstate, set, first, lane);
-    } else {
-      if (a.want_df) run_task<NQ, 4, false>(a, sh, wstate, 0, first, lane);
-      else run_task<NQ, 1, false>(a, sh, wstate, 0, first, lane);
-    }
+    const int nv = (set == 0 && (GRAD || a.want_df)) ? 4 : 1;
+    run_task<NQ, GRAD>(a, sh, wstate, set, first, lane, nv);
   }
   if (!GRAD) return;
   __syncthreads();
