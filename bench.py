@@ -167,6 +167,28 @@ class ClockSampler:
 
 # ----------------------------------------------------------------------------- native arm
 
+def profiled_traffic():
+    """DRAM bytes per circuit-kernel launch from the committed ncu summary, or None when the
+    kernel source has changed since those counters were taken."""
+    import hashlib
+    try:
+        md = open(os.path.join(ROOT, "profiles", "circuit_kernel_c3_8q6l.md")).read()
+        src = open(os.path.join(ROOT, "paper_2506_23246_b300", "csrc", "qp_circuit.cuh"), "rb").read()
+    except OSError:
+        return None
+    vals = {}
+    for line in md.splitlines():
+        if ":" in line and line.split(":")[0] in ("kernel_source_sha1_12", "traffic_bytes_per_launch"):
+            k, v = line.split(":", 1)
+            vals[k.strip()] = v.strip()
+    if vals.get("kernel_source_sha1_12") != hashlib.sha1(src).hexdigest()[:12]:
+        return None
+    try:
+        return int(vals["traffic_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
 def circuit_flops_per_point(n, L, nv):
     """Algorithmic FP32 flops of the statevector kernel for one point: 16 flops per amplitude
     per single-qubit gate per vector (complex 2x2 on amplitude pairs), forward on nv vectors,
@@ -310,7 +332,7 @@ def run_native(a):
                         "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
                 "gpu_launches": launches * a.steps,
                 "roofline": {"bound": "alu", "achieved": achieved, "peak": peak,
-                             "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                             "unit": "TFLOP/s", "frac": achieved / peak, "traffic": profiled_traffic(),
                              "kernel": "circuit_kernel<8,true>", "kernel_ms": kms,
                              "peak_basis": "%d SMs x 128 FP32 FMA/clk x 2 x %.0f MHz (max SM clock "
                                            "of measured peaks)" % (sms, sm_max)},
