@@ -10,6 +10,7 @@
 #include "qp_aux.cuh"
 #include "qp_circuit.cuh"
 #include "qp_common.h"
+#include "qp_dense.cuh"
 
 extern "C" int qp_build_sched(int n, int L, int ansatz, QPSched* out);
 
@@ -47,8 +48,11 @@ int geo_lb(int n) { return n <= 3 ? n : (n <= 8 ? 3 : n - 5); }
 int geo_ppw(int n) { return 32 >> (n - geo_lb(n)); }
 
 struct WsLayout {
-  size_t status, gates, cmat, cenc, thetaJ, dthetaJ, d1, d2, u1, blk_loss, blk_grad, wpart, total;
+  size_t status, gates, cmat, cenc, thetaJ, dthetaJ, d1, d2, u1, blk_loss, blk_grad, wpart;
+  size_t dW, dphi, total;
 };
+
+bool dense_path(const qp_plan* pl) { return pl->path == QP_PATH_GEMM_3XTF32; }
 
 size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
 
@@ -70,6 +74,10 @@ WsLayout ws_layout(const qp_plan* pl, int64_t P) {
   w.blk_grad = o; o = al256(o + (size_t)pl->blocks_grad * (3 * n * pl->c.n_layers + 3 * pl->c.n_readout + 3) * 4);
   const int64_t nW = H ? (int64_t)H * 2 * pl->c.rff_freqs + H + (int64_t)n * H + n : 0;
   w.wpart = o; o = al256(o + (size_t)pl->nwblk * nW * 4);
+  const size_t dim = (size_t)1 << n;
+  const bool dn = dense_path(pl);
+  w.dW = o; o = al256(o + (dn ? 2 * (2 * dim) * dim * 4 : 0));
+  w.dphi = o; o = al256(o + (dn ? (size_t)P * 4 * dim * 8 : 0));
   w.total = o;
   return w;
 }
@@ -131,7 +139,11 @@ qp_status validate(const qp_circuit* c, const qp_problem* p, int32_t path) {
   if (p->energy_nt < 0 || p->energy_nt > QP_MAXNT || p->energy_slice < 0) return QP_ERR_INVALID_ARG;
   if (p->medium == QP_MEDIUM_DIELECTRIC && !(p->sigmoid_w > 0.f)) return QP_ERR_INVALID_ARG;
   if (!(p->ic_sigma > 0.f)) return QP_ERR_INVALID_ARG;
-  if (path != QP_PATH_AUTO && path != QP_PATH_SIMT_FP32) return QP_ERR_UNSUPPORTED;
+  if (path == QP_PATH_GEMM_3XTF32) {
+    if (c->n_qubits < 5) return QP_ERR_UNSUPPORTED;  // K = 2^n must hold one 32-wide chunk
+  } else if (path != QP_PATH_AUTO && path != QP_PATH_SIMT_FP32) {
+    return QP_ERR_UNSUPPORTED;
+  }
   return QP_OK;
 }
 
@@ -215,6 +227,16 @@ qp_status qp_plan_create(const qp_circuit* circuit, const qp_problem* problem, i
     } else {
       pl->warps_fwd = warps; pl->smem_fwd = lay.total; pl->sstride_fwd = sstride;
       pl->blocks_fwd = pl->sm_count * per_sm;
+    }
+  }
+  if (dense_path(pl)) {
+    if (cudaFuncSetAttribute((void*)qpd::dense_build_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (1 << n) * 16) != cudaSuccess ||
+        cudaFuncSetAttribute((void*)qpd::dense_fwd_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             qpd::gemm_smem_bytes(n)) != cudaSuccess) {
+      cudaGetLastError();
+      delete pl;
+      return QP_ERR_CUDA;
     }
   }
   if (circuit->premap == QP_PREMAP_RFF_MLP) {
@@ -357,6 +379,29 @@ qp_status qp_forward(qp_plan* pl, const float* d_params, const float* d_pts, int
   const int64_t npts[3] = {B, 0, 0};
   qp_status st = launch_front(pl, d_params, pts, npts, w, s);
   if (st != QP_OK) return st;
+  if (dense_path(pl)) {
+    char* ws = (char*)pl->ws;
+    const int n = pl->c.n_qubits, dim = 1 << n;
+    qpd::BuildArgs ba;
+    ba.params = d_params; ba.circ_off = pl->circ_off; ba.n = n; ba.L = pl->c.n_layers;
+    ba.ansatz = pl->c.ansatz; ba.enc = pl->c.enc; ba.W = (float*)(ws + w.dW); ba.U = nullptr;
+    qpd::dense_build_kernel<<<dim, 256, dim * 16, s>>>(ba);
+    qpd::GemmArgs ga;
+    ga.thetaJ = (const float*)(ws + w.thetaJ); ga.W = (const float*)(ws + w.dW);
+    ga.phi = (float2*)(ws + w.dphi); ga.n = n; ga.nv = d_dfields ? 4 : 1;
+    ga.npts = B; ga.pt_base = 0; ga.status = (int32_t*)(ws + w.status);
+    const int64_t ppt = qpd::TM / ga.nv;
+    const int64_t ntiles = (B + ppt - 1) / ppt;
+    const int gblocks = (int)(ntiles < pl->sm_count ? ntiles : pl->sm_count);
+    qpd::dense_fwd_gemm_kernel<<<gblocks, 128, qpd::gemm_smem_bytes(n), s>>>(ga);
+    qpd::ReadoutArgs ra;
+    ra.phi = ga.phi; ra.head = d_params + pl->head_off; ra.n = n; ra.m = pl->c.n_readout;
+    ra.nv = ga.nv; ra.npts = B; ra.pt_base = 0; ra.out_f = d_fields; ra.out_df = d_dfields;
+    const int64_t rb = (B + 7) / 8;
+    qpd::dense_readout_kernel<<<(unsigned)(rb < 4096 ? rb : 4096), 256, 0, s>>>(ra);
+    pl->last_launches = 5;
+    return cuda_status(cudaGetLastError());
+  }
   QPCircArgs a;
   fill_circ(pl, a, w, d_params, pts, npts, false);
   a.want_df = d_dfields != nullptr;
@@ -382,6 +427,7 @@ qp_status qp_loss_grad(qp_plan* pl, const float* d_params, const qp_batch* batch
   if ((batch->n_colloc && !batch->colloc) || (batch->n_ic && !batch->ic) || (batch->n_bc && !batch->bc))
     return QP_ERR_INVALID_ARG;
   pl->last_launches = 0;
+  if (dense_path(pl)) return QP_ERR_UNSUPPORTED;  // loss + gradient run on the SIMT path
   const float* pts[3] = {batch->colloc, batch->ic, batch->bc};
   const int64_t npts[3] = {batch->n_colloc, batch->n_ic, batch->n_bc};
   const int64_t P = npts[0] + npts[1] + npts[2];
