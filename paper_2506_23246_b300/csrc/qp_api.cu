@@ -49,8 +49,12 @@ int geo_ppw(int n) { return 32 >> (n - geo_lb(n)); }
 
 struct WsLayout {
   size_t status, gates, cmat, cenc, thetaJ, dthetaJ, d1, d2, u1, blk_loss, blk_grad, wpart;
-  size_t dW, dphi, total;
+  size_t dW, dphi, dU, dG, dY, dpart, total;
 };
+
+// Rows of (point, vector) accumulated per weight-gradient chunk (bounds the FP32 tensor-core
+// accumulation length; chunks are summed in FP64).
+int64_t wg_rows_per_chunk(int n) { return n <= 8 ? 2048 : 8192; }
 
 bool dense_path(const qp_plan* pl) { return pl->path == QP_PATH_GEMM_3XTF32; }
 
@@ -78,6 +82,13 @@ WsLayout ws_layout(const qp_plan* pl, int64_t P) {
   const bool dn = dense_path(pl);
   w.dW = o; o = al256(o + (dn ? 2 * (2 * dim) * dim * 4 : 0));
   w.dphi = o; o = al256(o + (dn ? (size_t)P * 4 * dim * 8 : 0));
+  const bool dg = dn && n >= 7;
+  w.dU = o; o = al256(o + (dg ? dim * dim * 16 : 0));
+  w.dG = o; o = al256(o + (dg ? dim * dim * 8 : 0));
+  w.dY = o; o = al256(o + (dg ? dim * dim * 8 : 0));
+  const int64_t rows = 4 * P;
+  const int64_t nch = dg ? (rows + wg_rows_per_chunk(n) - 1) / wg_rows_per_chunk(n) : 0;
+  w.dpart = o; o = al256(o + (size_t)nch * dim * 2 * dim * 4);
   w.total = o;
   return w;
 }
@@ -233,7 +244,9 @@ qp_status qp_plan_create(const qp_circuit* circuit, const qp_problem* problem, i
     if (cudaFuncSetAttribute((void*)qpd::dense_build_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (1 << n) * 16) != cudaSuccess ||
         cudaFuncSetAttribute((void*)qpd::dense_fwd_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             qpd::gemm_smem_bytes(n)) != cudaSuccess) {
+                             qpd::gemm_smem_bytes(n)) != cudaSuccess ||
+        cudaFuncSetAttribute((void*)qpd::dense_wgrad_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             qpd::wg_smem_bytes()) != cudaSuccess) {
       cudaGetLastError();
       delete pl;
       return QP_ERR_CUDA;
@@ -366,6 +379,84 @@ static void fill_circ(qp_plan* pl, QPCircArgs& a, const WsLayout& w, const float
   a.grad_stride = 3 * n * pl->c.n_layers + 3 * pl->c.n_readout + 3;
 }
 
+static qp_status launch_reduce(qp_plan* pl, const WsLayout& w, const float* d_params, const int64_t npts[3],
+                               double* d_loss, float* d_grad, bool mlp, cudaStream_t s);
+
+// Fused-unitary loss and gradient: forward GEMM per point set, pointwise loss and costates,
+// weight-gradient GEMM over all (point, vector) rows, FP64 chunk sum, Y = U' G and the
+// B-independent sweep for the Pauli contractions of every gate, then the common reduction.
+static qp_status dense_loss_grad(qp_plan* pl, const float* d_params, const float* const pts[3],
+                                 const int64_t npts[3], double* d_loss, float* d_grad, cudaStream_t s) {
+  pl->last_launches = 0;
+  const int64_t P = npts[0] + npts[1] + npts[2];
+  const WsLayout w = ws_layout(pl, P);
+  if (!pl->ws || pl->ws_bytes < w.total) return QP_ERR_BUFFER_TOO_SMALL;
+  pl->last_stream = s;
+  char* ws = (char*)pl->ws;
+  const int n = pl->c.n_qubits, dim = 1 << n, L = pl->c.n_layers;
+  int launches = 0;
+  qp_status st = launch_front(pl, d_params, pts, npts, w, s);
+  if (st != QP_OK) return st;
+  launches += 2;
+  qpd::BuildArgs ba;
+  ba.params = d_params; ba.circ_off = pl->circ_off; ba.n = n; ba.L = L;
+  ba.ansatz = pl->c.ansatz; ba.enc = pl->c.enc; ba.W = (float*)(ws + w.dW); ba.U = (double2*)(ws + w.dU);
+  qpd::dense_build_kernel<<<dim, 256, dim * 16, s>>>(ba);
+  launches += 1;
+  int64_t base = 0;
+  for (int set = 0; set < 3; ++set) {
+    if (npts[set] > 0) {
+      qpd::GemmArgs ga;
+      ga.thetaJ = (const float*)(ws + w.thetaJ); ga.W = (const float*)(ws + w.dW);
+      ga.phi = (float2*)(ws + w.dphi); ga.n = n; ga.nv = set == 0 ? 4 : 1;
+      ga.npts = npts[set]; ga.pt_base = base; ga.status = (int32_t*)(ws + w.status);
+      const int64_t ppt = qpd::TM / ga.nv;
+      const int64_t ntiles = (npts[set] + ppt - 1) / ppt;
+      const int gblocks = (int)(ntiles < pl->sm_count ? ntiles : pl->sm_count);
+      qpd::dense_fwd_gemm_kernel<<<gblocks, 128, qpd::gemm_smem_bytes(n), s>>>(ga);
+      launches += 1;
+    }
+    base += npts[set];
+  }
+  qpd::PointArgs pa;
+  pa.phi = (float2*)(ws + w.dphi); pa.head = d_params + pl->head_off; pa.n = n; pa.m = pl->c.n_readout;
+  base = 0;
+  for (int i = 0; i < 3; ++i) { pa.pts[i] = pts[i]; pa.npts[i] = npts[i]; pa.pt_base[i] = base; base += npts[i]; }
+  fill_problem(pl, pa.pb);
+  pa.counts = (const int32_t*)(ws + w.status) + 1;
+  pa.blk_loss = (double*)(ws + w.blk_loss); pa.blk_grad = (float*)(ws + w.blk_grad);
+  pa.loss_stride = QP_NLP + pl->p.energy_nt;
+  pa.grad_stride = 3 * n * L + 3 * pl->c.n_readout + 3;
+  pa.nE = 3 * n * L;
+  const int psmem = ((QP_NLP + pl->p.energy_nt) * 8 + 15) / 16 * 16 + (3 * pl->c.n_readout + 3) * 4;
+  qpd::dense_point_kernel<<<pl->blocks_grad, 256, psmem, s>>>(pa);
+  launches += 1;
+  qpd::WgArgs wa;
+  wa.thetaJ = (const float*)(ws + w.thetaJ); wa.lam = (const float2*)(ws + w.dphi);
+  wa.part = (float*)(ws + w.dpart); wa.n = n;
+  base = 0;
+  for (int i = 0; i < 3; ++i) { wa.npts[i] = npts[i]; wa.pt_base[i] = base; base += npts[i]; }
+  wa.rows_total = 4 * npts[0] + npts[1] + npts[2];
+  const int64_t rpc = wg_rows_per_chunk(n);
+  wa.nchunks = (int32_t)((wa.rows_total + rpc - 1) / rpc);
+  if (wa.nchunks < 1) wa.nchunks = 1;
+  wa.status = (int32_t*)(ws + w.status);
+  const int tiles = (dim / qpd::TM) * (2 * dim / 256);
+  qpd::dense_wgrad_gemm_kernel<<<dim3(tiles, wa.nchunks), 128, qpd::wg_smem_bytes(), s>>>(wa);
+  launches += 1;
+  qpd::SweepArgs sa;
+  sa.part = wa.part; sa.nchunks = wa.nchunks; sa.n = n; sa.L = L; sa.ansatz = pl->c.ansatz;
+  sa.U = (const double2*)(ws + w.dU); sa.G = (float2*)(ws + w.dG); sa.Y = (float2*)(ws + w.dY);
+  sa.params = d_params; sa.circ_off = pl->circ_off; sa.eout = (float*)(ws + w.blk_grad);
+  qpd::dense_gsum_kernel<<<(dim * dim + 255) / 256, 256, 0, s>>>(sa);
+  qpd::dense_y_kernel<<<dim3(dim / 16, dim / 16), 256, 0, s>>>(sa);
+  qpd::dense_sweep_kernel<<<1, 1024, 0, s>>>(sa);
+  launches += 3;
+  st = launch_reduce(pl, w, d_params, npts, d_loss, d_grad, false, s);
+  pl->last_launches = launches + 1;
+  return st;
+}
+
 qp_status qp_forward(qp_plan* pl, const float* d_params, const float* d_pts, int64_t B,
                      float* d_fields, float* d_dfields, void* stream) {
   if (!pl || !d_params || B < 0 || (B > 0 && (!d_pts || !d_fields))) return QP_ERR_INVALID_ARG;
@@ -427,8 +518,12 @@ qp_status qp_loss_grad(qp_plan* pl, const float* d_params, const qp_batch* batch
   if ((batch->n_colloc && !batch->colloc) || (batch->n_ic && !batch->ic) || (batch->n_bc && !batch->bc))
     return QP_ERR_INVALID_ARG;
   pl->last_launches = 0;
-  if (dense_path(pl)) return QP_ERR_UNSUPPORTED;  // loss + gradient run on the SIMT path
   const float* pts[3] = {batch->colloc, batch->ic, batch->bc};
+  if (dense_path(pl)) {
+    if (pl->c.n_qubits < 7 || pl->c.premap == QP_PREMAP_RFF_MLP) return QP_ERR_UNSUPPORTED;
+    const int64_t np3[3] = {batch->n_colloc, batch->n_ic, batch->n_bc};
+    return dense_loss_grad(pl, d_params, pts, np3, d_loss, d_grad, (cudaStream_t)stream);
+  }
   const int64_t npts[3] = {batch->n_colloc, batch->n_ic, batch->n_bc};
   const int64_t P = npts[0] + npts[1] + npts[2];
   const WsLayout w = ws_layout(pl, P);
@@ -495,10 +590,21 @@ qp_status qp_loss_grad(qp_plan* pl, const float* d_params, const qp_batch* batch
       return QP_ERR_CUDA;
     launches += 1;
   }
+  qp_status st_red;
+  st_red = launch_reduce(pl, w, d_params, npts, d_loss, d_grad, mlp, s);
+  pl->last_launches = launches + 1;
+  return st_red;
+}
+
+static qp_status launch_reduce(qp_plan* pl, const WsLayout& w, const float* d_params, const int64_t npts[3],
+                               double* d_loss, float* d_grad, bool mlp, cudaStream_t s) {
+  char* ws = (char*)pl->ws;
   qpk::ReduceArgs ra;
   ra.blk_loss = (const double*)(ws + w.blk_loss);
   ra.blk_grad = (const float*)(ws + w.blk_grad);
-  ra.nblk = pl->blocks_grad; ra.loss_stride = a.loss_stride; ra.grad_stride = a.grad_stride;
+  ra.nblk = pl->blocks_grad;
+  ra.loss_stride = QP_NLP + pl->p.energy_nt;
+  ra.grad_stride = 3 * pl->c.n_qubits * pl->c.n_layers + 3 * pl->c.n_readout + 3;
   ra.wpart = (const float*)(ws + w.wpart);
   ra.nwblk = mlp ? pl->nwblk : 0;
   ra.nW = (int32_t)(pl->mlp_count - pl->nfixed);
@@ -515,8 +621,6 @@ qp_status qp_loss_grad(qp_plan* pl, const float* d_params, const qp_batch* batch
   ra.w_ic = pl->p.w_ic; ra.w_bc = pl->p.w_bc; ra.w_energy = pl->p.w_energy;
   const int64_t nred = pl->n_params > QP_MAXNT ? pl->n_params : QP_MAXNT;
   qpk::reduce_kernel<<<(unsigned)((nred + 255) / 256), 256, 0, s>>>(ra);
-  launches += 1;
-  pl->last_launches = launches;
   return cuda_status(cudaGetLastError());
 }
 

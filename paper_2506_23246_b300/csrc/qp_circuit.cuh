@@ -111,6 +111,88 @@ __device__ __forceinline__ float slot_sum(float v) {
   return v;
 }
 
+// Loss terms of one point and their cotangents g = dL/d(Ez,Hx,Hy), gD = dL/d(d field_c/d v_d):
+// collocation points carry the residuals of Eqs. 8-10 (1/eps pointwise in the dielectric case,
+// Eq. 13 splits res1 by set) and the squared Poynting residual of Eq. 23; IC points the misfit
+// of Eq. 17 against the Gaussian pulse of Eq. 14; BC points Ez^2 (PEC). Sums go to the FP64
+// partials `loss` (only when `acc`), the energy slices of Eq. 31 after QP_NLP.
+__device__ __forceinline__ void point_loss(const QPProblemDev& pb, int set, int64_t pt, int64_t npt,
+                                           const int32_t* counts, float x, float y,
+                                           const float (&f)[3], const float (&D)[3][3], bool active,
+                                           bool acc, double* loss, float (&g)[3], float (&gD)[3][3]) {
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    g[c] = 0.f;
+    gD[c][0] = gD[c][1] = gD[c][2] = 0.f;
+  }
+  if (set == 0) {
+    float eps = 1.f;
+    bool diel = false;
+    if (pb.medium == 1) {
+      const float dx = x - pb.disk_x0, dy = y - pb.disk_y0;
+      const float r2 = __fmaf_rn(dx, dx, dy * dy);
+      diel = r2 < pb.disk_r * pb.disk_r;
+      const float rr = sqrtf(r2);
+      eps = 1.f + (pb.eps_r - 1.f) / (1.f + expf(-(pb.disk_r - rr) / pb.sigmoid_w));
+    }
+    const float ie = 1.f / eps;
+    const float res1 = D[0][2] - ie * (D[2][0] - D[1][1]);
+    const float res2 = D[1][2] + D[0][1];
+    const float res3 = D[2][2] - D[0][0];
+    const float e = eps * f[0] * D[0][2] + f[1] * D[1][2] + f[2] * D[2][2] -
+                    (D[0][0] * f[2] + f[0] * D[2][0]) + (D[0][1] * f[1] + f[0] * D[1][1]);
+    const float N = (float)npt;
+    float N1 = N;
+    if (pb.medium == 1) {
+      const float nd = (float)counts[0];
+      N1 = diel ? nd : N - nd;
+    }
+    if (active) {
+      const float k1 = 2.f * res1 / N1, k2 = 2.f * res2 / N, k3 = 2.f * res3 / N;
+      const float kE = 2.f * pb.w_energy * e / N;
+      g[0] = kE * (eps * D[0][2] - D[2][0] + D[1][1]);
+      g[1] = kE * (D[1][2] + D[0][1]);
+      g[2] = kE * (D[2][2] - D[0][0]);
+      gD[0][0] = -k3 - kE * f[2];
+      gD[0][1] = k2 + kE * f[1];
+      gD[0][2] = k1 + kE * eps * f[0];
+      gD[1][1] = k1 * ie + kE * f[0];
+      gD[1][2] = k2 + kE * f[1];
+      gD[2][0] = -k1 * ie - kE * f[0];
+      gD[2][2] = k3 + kE * f[2];
+      if (acc) {
+        atomicAdd(&loss[diel ? 1 : 0], (double)res1 * (double)res1);
+        atomicAdd(&loss[2], (double)res2 * (double)res2);
+        atomicAdd(&loss[3], (double)res3 * (double)res3);
+        atomicAdd(&loss[4], (double)e * (double)e);
+        if (pb.energy_nt > 0 && pb.energy_slice > 0) {
+          const int64_t k = pt / pb.energy_slice;
+          if (k < pb.energy_nt)
+            atomicAdd(&loss[QP_NLP + k],
+                      0.5 * ((double)eps * f[0] * f[0] + (double)f[1] * f[1] + (double)f[2] * f[2]));
+        }
+      }
+    }
+  } else if (set == 1) {
+    const float dx = x - pb.ic_x0, dy = y - pb.ic_y0;
+    const float e0 = expf(-(dx * dx + dy * dy) / (2.f * pb.ic_sigma * pb.ic_sigma));
+    if (active) {
+      const float k = 2.f * pb.w_ic / (float)npt;
+      g[0] = k * (f[0] - e0);
+      g[1] = k * f[1];
+      g[2] = k * f[2];
+      if (acc)
+        atomicAdd(&loss[5], (double)(f[0] - e0) * (f[0] - e0) + (double)f[1] * f[1] +
+                                (double)f[2] * f[2]);
+    }
+  } else {
+    if (active) {
+      g[0] = 2.f * pb.w_bc * f[0] / (float)npt;
+      if (acc) atomicAdd(&loss[6], (double)f[0] * f[0]);
+    }
+  }
+}
+
 struct Shared {
   const QPSched* s;
   const float* gates;
@@ -325,79 +407,8 @@ __device__ __forceinline__ void run_task(const QPCircArgs& a, const Shared& sh, 
   }
   // ------------------------------------------------------------------ loss and cotangents
   const float* xp = a.pts[set] + ptc * 3;
-  const float x = xp[0], y = xp[1];
-  float g[3] = {0.f, 0.f, 0.f};
-  float gD[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
-  const QPProblemDev& pb = a.pb;
-  if (set == 0) {
-    // Eqs. 8-10 (1/eps pointwise in the dielectric case), Eq. 23 Poynting residual.
-    float eps = 1.f;
-    bool diel = false;
-    if (pb.medium == 1) {
-      const float dx = x - pb.disk_x0, dy = y - pb.disk_y0;
-      const float r2 = __fmaf_rn(dx, dx, dy * dy);
-      diel = r2 < pb.disk_r * pb.disk_r;
-      const float rr = sqrtf(r2);
-      eps = 1.f + (pb.eps_r - 1.f) / (1.f + expf(-(pb.disk_r - rr) / pb.sigmoid_w));
-    }
-    const float ie = 1.f / eps;
-    const float res1 = D[0][2] - ie * (D[2][0] - D[1][1]);
-    const float res2 = D[1][2] + D[0][1];
-    const float res3 = D[2][2] - D[0][0];
-    const float e = eps * f[0] * D[0][2] + f[1] * D[1][2] + f[2] * D[2][2] -
-                    (D[0][0] * f[2] + f[0] * D[2][0]) + (D[0][1] * f[1] + f[0] * D[1][1]);
-    const float N = (float)npt;
-    float N1 = N;
-    if (pb.medium == 1) {
-      const float nd = (float)a.counts[0];
-      N1 = diel ? nd : N - nd;
-    }
-    if (active) {
-      const float k1 = 2.f * res1 / N1, k2 = 2.f * res2 / N, k3 = 2.f * res3 / N;
-      const float kE = 2.f * pb.w_energy * e / N;
-      g[0] = kE * (eps * D[0][2] - D[2][0] + D[1][1]);
-      g[1] = kE * (D[1][2] + D[0][1]);
-      g[2] = kE * (D[2][2] - D[0][0]);
-      gD[0][0] = -k3 - kE * f[2];
-      gD[0][1] = k2 + kE * f[1];
-      gD[0][2] = k1 + kE * eps * f[0];
-      gD[1][1] = k1 * ie + kE * f[0];
-      gD[1][2] = k2 + kE * f[1];
-      gD[2][0] = -k1 * ie - kE * f[0];
-      gD[2][2] = k3 + kE * f[2];
-      if (lin == 0) {
-        atomicAdd(&sh.loss[diel ? 1 : 0], (double)res1 * (double)res1);
-        atomicAdd(&sh.loss[2], (double)res2 * (double)res2);
-        atomicAdd(&sh.loss[3], (double)res3 * (double)res3);
-        atomicAdd(&sh.loss[4], (double)e * (double)e);
-        if (pb.energy_nt > 0 && pb.energy_slice > 0) {
-          const int64_t k = pt / pb.energy_slice;
-          if (k < pb.energy_nt)
-            atomicAdd(&sh.loss[QP_NLP + k],
-                      0.5 * ((double)eps * f[0] * f[0] + (double)f[1] * f[1] + (double)f[2] * f[2]));
-        }
-      }
-    }
-  } else if (set == 1) {
-    // Eq. 17: initial-condition misfit against the Gaussian pulse (Eq. 14), H = 0.
-    const float dx = x - pb.ic_x0, dy = y - pb.ic_y0;
-    const float e0 = expf(-(dx * dx + dy * dy) / (2.f * pb.ic_sigma * pb.ic_sigma));
-    if (active) {
-      const float k = 2.f * pb.w_ic / (float)npt;
-      g[0] = k * (f[0] - e0);
-      g[1] = k * f[1];
-      g[2] = k * f[2];
-      if (lin == 0)
-        atomicAdd(&sh.loss[5], (double)(f[0] - e0) * (f[0] - e0) + (double)f[1] * f[1] +
-                                   (double)f[2] * f[2]);
-    }
-  } else {
-    // PEC boundary: Ez = 0 on the edges.
-    if (active) {
-      g[0] = 2.f * pb.w_bc * f[0] / (float)npt;
-      if (lin == 0) atomicAdd(&sh.loss[6], (double)f[0] * f[0]);
-    }
-  }
+  float g[3], gD[3][3];
+  point_loss(a.pb, set, pt, npt, a.counts, xp[0], xp[1], f, D, active, lin == 0, sh.loss, g, gD);
   // back through the head: zbar = W^T g, zbar_d = W^T g_d; head gradients
   float zb[QP_MAXQ], zbd[3][QP_MAXQ];
 #pragma unroll

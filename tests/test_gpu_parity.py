@@ -116,9 +116,9 @@ def test_dense_tensorcore_forward_parity(torch_cuda, oracle, n, L, ans, enc):
 
 # ----------------------------------------------------------------------------- loss + grad
 
-def _loss_grad_check(torch, oracle, circ, prob, params, sets, idx=None, tol=TOL):
+def _loss_grad_check(torch, oracle, circ, prob, params, sets, idx=None, tol=TOL, path="auto"):
     from paper_2506_23246_b300 import qp
-    plan = qp.Plan(circ, prob)
+    plan = qp.Plan(circ, prob, path=path)
     dp = torch.tensor(params, device="cuda")
     dsets = {k: torch.tensor(v, device="cuda") for k, v in sets.items()}
     loss, grad = plan.loss_grad(dp, dsets)
@@ -179,6 +179,22 @@ def test_loss_grad_other_sizes(torch_cuda, oracle, n, L):
             "bc": W.bc_points(3, n + 2)}
     params = W.init_params(circ, n)
     _loss_grad_check(torch_cuda, oracle, circ, prob, params, sets)
+
+
+@pytest.mark.parametrize("n,L,ans,enc,medium", [(7, 3, "strong_rot", "rx", "vacuum"),
+                                                 (8, 4, "basic_ryrz", "ry", "dielectric"),
+                                                 (8, 6, "strong_rot", "rx", "dielectric")])
+def test_dense_tensorcore_loss_grad_parity(torch_cuda, oracle, n, L, ans, enc, medium):
+    """Fused-unitary loss and gradient (tcgen05 forward and weight-gradient contractions,
+    B-independent sweep): every loss term and every parameter against the oracle."""
+    circ = W.circuit(n, L, n if ans != "basic_ryrz" else 3, ansatz=ans, enc=enc, scale="pi",
+                     premap="direct")
+    prob = W.problem(medium, disk_x0=0.2, disk_r=0.6, w_energy=10.0, energy_slice=16,
+                     energy_nt=2)
+    sets = {"colloc": W.uniform_points(45, n + 3, 1.0), "ic": W.ic_points_uniform(7, n + 4),
+            "bc": W.bc_points(5, n + 5)}
+    params = W.init_params(circ, n + 7)
+    _loss_grad_check(torch_cuda, oracle, circ, prob, params, sets, path="gemm_3xtf32")
 
 
 def test_loss_grad_empty_sets(torch_cuda, oracle):
