@@ -37,6 +37,8 @@ def _args():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--path", default="auto", choices=["auto", "simt", "gemm_3xtf32"],
+                    help="statevector path of the library (auto = the library's choice)")
     return ap.parse_args()
 
 
@@ -167,13 +169,13 @@ class ClockSampler:
 
 # ----------------------------------------------------------------------------- native arm
 
-def profiled_traffic():
-    """DRAM bytes per circuit-kernel launch from the committed ncu summary, or None when the
-    kernel source has changed since those counters were taken."""
+def profiled_traffic(summary="circuit_kernel_c3_8q6l.md", source="qp_circuit.cuh"):
+    """DRAM bytes per launch of the dominant kernel from the committed ncu summary, or None
+    when the kernel source has changed since those counters were taken."""
     import hashlib
     try:
-        md = open(os.path.join(ROOT, "profiles", "circuit_kernel_c3_8q6l.md")).read()
-        src = open(os.path.join(ROOT, "paper_2506_23246_b300", "csrc", "qp_circuit.cuh"), "rb").read()
+        md = open(os.path.join(ROOT, "profiles", summary)).read()
+        src = open(os.path.join(ROOT, "paper_2506_23246_b300", "csrc", source), "rb").read()
     except OSError:
         return None
     vals = {}
@@ -223,7 +225,7 @@ def run_native(a):
         sets = dict(sets)
         sets["colloc"] = sets["colloc"].copy()
         sets["colloc"][:, 2] += 0.7 * rank
-    plan = qp.Plan(circ, prob)
+    plan = qp.Plan(circ, prob, path=a.path)
     dev = torch.device("cuda", local)
     dp = torch.tensor(params, device=dev)
     dsets = {k: torch.tensor(v, device=dev) for k, v in sets.items()}
@@ -275,10 +277,7 @@ def run_native(a):
         ms = float(t.item())
     value = world * ncol / (ms / 1000.0)
 
-    # roofline of the statevector kernel (FP32 SIMT)
     kms = statistics.mean(kt)
-    flops = ncol * circuit_flops_per_point(8, 6, 4) + dsets["ic"].shape[0] * circuit_flops_per_point(8, 6, 1)
-    achieved = flops / (kms / 1000.0) / 1e12
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     peaks = {}
     try:
@@ -287,7 +286,28 @@ def run_native(a):
     except (OSError, ValueError):
         pass
     sm_max = peaks.get("sm_max_mhz", 2032.0)
-    peak = sms * 128 * 2 * sm_max * 1e6 / 1e12
+    nic = dsets["ic"].shape[0]
+    if plan.path == "simt":
+        # statevector kernel, FP32 SIMT
+        flops = ncol * circuit_flops_per_point(8, 6, 4) + nic * circuit_flops_per_point(8, 6, 1)
+        peak = sms * 128 * 2 * sm_max * 1e6 / 1e12
+        roof = {"bound": "alu", "kernel": "circuit_kernel<8,true>",
+                "peak_basis": "%d SMs x 128 FP32 FMA/clk x 2 x %.0f MHz (max SM clock of measured "
+                              "peaks)" % (sms, sm_max),
+                "traffic": profiled_traffic()}
+    else:
+        # weight-gradient contraction G = sum R Lambda^H on the tensor cores: algorithmic
+        # 2 M N K with M = 2^n, N = 2^(n+1), K = (point, vector) rows; 3xTF32 runs three TF32
+        # products per term, so its ceiling is the TF32 peak / 3
+        dim = 1 << 8
+        flops = 2.0 * dim * (2 * dim) * (4 * ncol + nic)
+        bf16 = peaks.get("bf16_tflops", 1800.0)
+        peak = bf16 * 0.5 / 3.0
+        roof = {"bound": "tensor", "kernel": "dense_wgrad_gemm_kernel (3xTF32)",
+                "peak_basis": "measured bf16 %.0f TFLOP/s x 0.5 (nominal TF32/BF16 dense ratio) / 3 "
+                              "(three TF32 products per 3xTF32 term)" % bf16,
+                "traffic": profiled_traffic("dense_wgrad_c3_8q6l.md", "qp_dense.cuh")}
+    achieved = flops / (kms / 1000.0) / 1e12
 
     # end to end through the public call: pinned host inputs in, loss + gradient out
     hp = torch.tensor(params).pin_memory()
@@ -331,11 +351,10 @@ def run_native(a):
                 "e2e": {"value": world * ncol / (ems / 1000.0), "unit": UNIT,
                         "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
                 "gpu_launches": launches * a.steps,
-                "roofline": {"bound": "alu", "achieved": achieved, "peak": peak,
-                             "unit": "TFLOP/s", "frac": achieved / peak, "traffic": profiled_traffic(),
-                             "kernel": "circuit_kernel<8,true>", "kernel_ms": kms,
-                             "peak_basis": "%d SMs x 128 FP32 FMA/clk x 2 x %.0f MHz (max SM clock "
-                                           "of measured peaks)" % (sms, sm_max)},
+                "roofline": {"bound": roof["bound"], "achieved": achieved, "peak": peak,
+                             "unit": "TFLOP/s", "frac": achieved / peak, "traffic": roof["traffic"],
+                             "kernel": roof["kernel"], "kernel_ms": kms, "peak_basis": roof["peak_basis"]},
+                "path": plan.path,
                 "clocks": clocks}
         if not a.no_cpu_baseline and world == 1:
             v, nt, desc = _oracle_sample(10.0)

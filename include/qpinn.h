@@ -70,9 +70,14 @@ typedef enum {
  * width mlp_width, a linear layer to n_qubits, a = tanh(.), theta = scale(a). */
 typedef enum { QP_PREMAP_DIRECT = 0, QP_PREMAP_RFF_MLP = 1 } qp_premap;
 
+/* SIMT_FP32: gate-by-gate statevectors in registers and shared memory, FP32 (any n).
+ * GEMM_3XTF32: the ansatz layers fused into one 2^n x 2^n unitary applied to all points as
+ * tensor-core contractions (tcgen05, TF32 hi/lo split, FP32 accumulation); forward for
+ * n >= 5, loss + gradient for n >= 7. AUTO picks GEMM_3XTF32 for 8-9 qubits, SIMT otherwise.
+ * GEMM_BF16X3 is reserved (QP_ERR_UNSUPPORTED). */
 typedef enum {
   QP_PATH_AUTO = 0,
-  QP_PATH_SIMT_FP32 = 1,  /* gate-by-gate statevector in registers/shared memory */
+  QP_PATH_SIMT_FP32 = 1,
   QP_PATH_GEMM_3XTF32 = 2,
   QP_PATH_GEMM_BF16X3 = 3
 } qp_path;
@@ -168,10 +173,15 @@ const char* qp_status_str(qp_status s);
 /* Kernel launches issued by the last compute call on this plan (for accounting). */
 int32_t qp_last_launch_count(const qp_plan* plan);
 
+/* The path a plan resolved to (QP_PATH_SIMT_FP32 or QP_PATH_GEMM_3XTF32). */
+int32_t qp_plan_path(const qp_plan* plan);
+
 /* Optional profiling: two cudaEvent_t (passed as void*, created by the caller) that the
- * following compute calls record on their stream immediately before and after the
- * statevector (circuit) kernel, so its device time can be read with cudaEventElapsedTime.
- * Pass NULL, NULL to stop. The plan does not own the events. */
+ * following compute calls record on their stream immediately before and after the dominant
+ * kernel -- the statevector kernel on the SIMT path, the weight-gradient tensor-core
+ * contraction on the GEMM path of qp_loss_grad, the forward contraction of qp_forward -- so
+ * its device time can be read with cudaEventElapsedTime. Pass NULL, NULL to stop. The plan
+ * does not own the events. */
 qp_status qp_set_profile_events(qp_plan* plan, void* ev_start, void* ev_stop);
 
 /* Same result as qp_forward, for callers that cannot allocate device memory (a memory pool

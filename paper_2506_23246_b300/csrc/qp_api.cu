@@ -49,12 +49,12 @@ int geo_ppw(int n) { return 32 >> (n - geo_lb(n)); }
 
 struct WsLayout {
   size_t status, gates, cmat, cenc, thetaJ, dthetaJ, d1, d2, u1, blk_loss, blk_grad, wpart;
-  size_t dW, dphi, dU, dG, dY, dpart, total;
+  size_t dW, dphi, dU, dG, dY, dpart, dWT, dmu, total;
 };
 
 // Rows of (point, vector) accumulated per weight-gradient chunk (bounds the FP32 tensor-core
 // accumulation length; chunks are summed in FP64).
-int64_t wg_rows_per_chunk(int n) { return n <= 8 ? 2048 : 8192; }
+int64_t wg_rows_per_chunk(int n) { return n <= 8 ? 512 : 4096; }
 
 bool dense_path(const qp_plan* pl) { return pl->path == QP_PATH_GEMM_3XTF32; }
 
@@ -89,6 +89,9 @@ WsLayout ws_layout(const qp_plan* pl, int64_t P) {
   const int64_t rows = 4 * P;
   const int64_t nch = dg ? (rows + wg_rows_per_chunk(n) - 1) / wg_rows_per_chunk(n) : 0;
   w.dpart = o; o = al256(o + (size_t)nch * dim * 2 * dim * 4);
+  const bool dm = dg && pl->c.premap == QP_PREMAP_RFF_MLP;
+  w.dWT = o; o = al256(o + (dm ? 2 * (2 * dim) * dim * 4 : 0));
+  w.dmu = o; o = al256(o + (dm ? (size_t)P * 4 * dim * 4 : 0));
   w.total = o;
   return w;
 }
@@ -188,7 +191,10 @@ qp_status qp_plan_create(const qp_circuit* circuit, const qp_problem* problem, i
   if (!pl) return QP_ERR_INTERNAL;
   pl->c = *circuit;
   pl->p = *problem;
-  pl->path = path;
+  // AUTO: the fused-unitary tensor-core path where it is faster and stays within 1e-5 of the
+  // FP64 reference (8-9 qubits); the FP32 gate-by-gate path otherwise.
+  pl->path = path != QP_PATH_AUTO ? path
+             : (circuit->n_qubits >= 8 && circuit->n_qubits <= 9 ? QP_PATH_GEMM_3XTF32 : QP_PATH_SIMT_FP32);
   const int n = circuit->n_qubits;
   if (qp_build_sched(n, circuit->n_layers, circuit->ansatz, &pl->sched) != 0) {
     delete pl;
@@ -243,10 +249,16 @@ qp_status qp_plan_create(const qp_circuit* circuit, const qp_problem* problem, i
   if (dense_path(pl)) {
     if (cudaFuncSetAttribute((void*)qpd::dense_build_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (1 << n) * 16) != cudaSuccess ||
-        cudaFuncSetAttribute((void*)qpd::dense_fwd_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             qpd::gemm_smem_bytes(n)) != cudaSuccess ||
+        cudaFuncSetAttribute((void*)qpd::dense_row_gemm_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             qpd::gemm_smem_bytes(n, 0)) != cudaSuccess ||
+        cudaFuncSetAttribute((void*)qpd::dense_row_gemm_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             qpd::gemm_smem_bytes(n, 1)) != cudaSuccess ||
         cudaFuncSetAttribute((void*)qpd::dense_wgrad_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             qpd::wg_smem_bytes()) != cudaSuccess) {
+                             qpd::wg_smem_bytes()) != cudaSuccess ||
+        cudaFuncSetAttribute((void*)qpd::dense_sweep_left_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (1 << n) * 16 * 8) != cudaSuccess ||
+        cudaFuncSetAttribute((void*)qpd::dense_sweep_right_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (1 << n) * 16 * 8) != cudaSuccess) {
       cudaGetLastError();
       delete pl;
       return QP_ERR_CUDA;
@@ -301,6 +313,8 @@ qp_status qp_set_workspace(qp_plan* plan, void* d_ws, size_t bytes) {
 }
 
 int32_t qp_last_launch_count(const qp_plan* plan) { return plan ? plan->last_launches : -1; }
+
+int32_t qp_plan_path(const qp_plan* plan) { return plan ? plan->path : -1; }
 
 qp_status qp_set_profile_events(qp_plan* plan, void* ev_start, void* ev_stop) {
   if (!plan || ((ev_start == nullptr) != (ev_stop == nullptr))) return QP_ERR_INVALID_ARG;
@@ -381,6 +395,8 @@ static void fill_circ(qp_plan* pl, QPCircArgs& a, const WsLayout& w, const float
 
 static qp_status launch_reduce(qp_plan* pl, const WsLayout& w, const float* d_params, const int64_t npts[3],
                                double* d_loss, float* d_grad, bool mlp, cudaStream_t s);
+static qp_status launch_premap_bwd(qp_plan* pl, const WsLayout& w, const float* d_params,
+                                   const float* const pts[3], const int64_t npts[3], cudaStream_t s);
 
 // Fused-unitary loss and gradient: forward GEMM per point set, pointwise loss and costates,
 // weight-gradient GEMM over all (point, vector) rows, FP64 chunk sum, Y = U' G and the
@@ -401,6 +417,8 @@ static qp_status dense_loss_grad(qp_plan* pl, const float* d_params, const float
   qpd::BuildArgs ba;
   ba.params = d_params; ba.circ_off = pl->circ_off; ba.n = n; ba.L = L;
   ba.ansatz = pl->c.ansatz; ba.enc = pl->c.enc; ba.W = (float*)(ws + w.dW); ba.U = (double2*)(ws + w.dU);
+  const bool mlp = pl->c.premap == QP_PREMAP_RFF_MLP;
+  ba.WT = mlp ? (float*)(ws + w.dWT) : nullptr;
   qpd::dense_build_kernel<<<dim, 256, dim * 16, s>>>(ba);
   launches += 1;
   int64_t base = 0;
@@ -413,7 +431,7 @@ static qp_status dense_loss_grad(qp_plan* pl, const float* d_params, const float
       const int64_t ppt = qpd::TM / ga.nv;
       const int64_t ntiles = (npts[set] + ppt - 1) / ppt;
       const int gblocks = (int)(ntiles < pl->sm_count ? ntiles : pl->sm_count);
-      qpd::dense_fwd_gemm_kernel<<<gblocks, 128, qpd::gemm_smem_bytes(n), s>>>(ga);
+      qpd::dense_row_gemm_kernel<0><<<gblocks, 128, qpd::gemm_smem_bytes(n, 0), s>>>(ga);
       launches += 1;
     }
     base += npts[set];
@@ -436,13 +454,17 @@ static qp_status dense_loss_grad(qp_plan* pl, const float* d_params, const float
   wa.part = (float*)(ws + w.dpart); wa.n = n;
   base = 0;
   for (int i = 0; i < 3; ++i) { wa.npts[i] = npts[i]; wa.pt_base[i] = base; base += npts[i]; }
-  wa.rows_total = 4 * npts[0] + npts[1] + npts[2];
+  wa.kc_end[0] = (4 * npts[0] + qpd::KC - 1) / qpd::KC;
+  wa.kc_end[1] = wa.kc_end[0] + (npts[1] + qpd::KC - 1) / qpd::KC;
+  wa.kc_end[2] = wa.kc_end[1] + (npts[2] + qpd::KC - 1) / qpd::KC;
   const int64_t rpc = wg_rows_per_chunk(n);
-  wa.nchunks = (int32_t)((wa.rows_total + rpc - 1) / rpc);
+  wa.nchunks = (int32_t)((wa.kc_end[2] * qpd::KC + rpc - 1) / rpc);
   if (wa.nchunks < 1) wa.nchunks = 1;
   wa.status = (int32_t*)(ws + w.status);
   const int tiles = (dim / qpd::TM) * (2 * dim / 256);
+  if (pl->prof_start) cudaEventRecord(pl->prof_start, s);
   qpd::dense_wgrad_gemm_kernel<<<dim3(tiles, wa.nchunks), 128, qpd::wg_smem_bytes(), s>>>(wa);
+  if (pl->prof_stop) cudaEventRecord(pl->prof_stop, s);
   launches += 1;
   qpd::SweepArgs sa;
   sa.part = wa.part; sa.nchunks = wa.nchunks; sa.n = n; sa.L = L; sa.ansatz = pl->c.ansatz;
@@ -450,9 +472,56 @@ static qp_status dense_loss_grad(qp_plan* pl, const float* d_params, const float
   sa.params = d_params; sa.circ_off = pl->circ_off; sa.eout = (float*)(ws + w.blk_grad);
   qpd::dense_gsum_kernel<<<(dim * dim + 255) / 256, 256, 0, s>>>(sa);
   qpd::dense_y_kernel<<<dim3(dim / 16, dim / 16), 256, 0, s>>>(sa);
-  qpd::dense_sweep_kernel<<<1, 1024, 0, s>>>(sa);
-  launches += 3;
-  st = launch_reduce(pl, w, d_params, npts, d_loss, d_grad, false, s);
+  {
+    float2* Ya = sa.Y;
+    float2* Yb = sa.G;  // the G scratch is free once Y = U' G is formed
+    const int tcol = 16, trow = 16;
+    const int64_t tot = (int64_t)dim * dim;
+    const int rblocks = (int)((tot + 255) / 256 < pl->sm_count * 8 ? (tot + 255) / 256 : pl->sm_count * 8);
+    for (int l = L - 1; l >= 0; --l) {
+      qpd::dense_sweep_ring_kernel<<<rblocks, 256, 0, s>>>(sa, l, Ya, Yb);
+      if (l > 0) {
+        qpd::dense_sweep_left_kernel<16><<<dim / tcol, 256, dim * tcol * 8, s>>>(sa, l, Yb);
+        qpd::dense_sweep_right_kernel<16><<<dim / trow, 256, dim * trow * 8, s>>>(sa, l, Yb);
+        launches += 2;
+      }
+      float2* t = Ya; Ya = Yb; Yb = t;
+      launches += 1;
+    }
+  }
+  launches += 2;
+  if (mlp) {
+    // back-projection mu = Re(U'^H lambda) per (point, vector) row, then the embedding
+    // gradients per point, then the premap backward shared with the SIMT path
+    base = 0;
+    for (int set = 0; set < 3; ++set) {
+      if (npts[set] > 0) {
+        qpd::GemmArgs ga;
+        ga.thetaJ = (const float*)(ws + w.thetaJ); ga.W = (const float*)(ws + w.dWT);
+        ga.phi = nullptr; ga.lam = (const float*)(ws + w.dphi); ga.mu = (float*)(ws + w.dmu);
+        ga.n = n; ga.nv = set == 0 ? 4 : 1;
+        ga.npts = npts[set]; ga.pt_base = base; ga.status = (int32_t*)(ws + w.status);
+        const int64_t ppt = qpd::TM / ga.nv;
+        const int64_t ntiles = (npts[set] + ppt - 1) / ppt;
+        const int gblocks = (int)(ntiles < pl->sm_count ? ntiles : pl->sm_count);
+        qpd::dense_row_gemm_kernel<1><<<gblocks, 128, qpd::gemm_smem_bytes(n, 1), s>>>(ga);
+        launches += 1;
+      }
+      base += npts[set];
+    }
+    qpd::EmbedArgs ea;
+    ea.thetaJ = (const float*)(ws + w.thetaJ); ea.mu = (const float*)(ws + w.dmu);
+    ea.dthetaJ = (float*)(ws + w.dthetaJ); ea.n = n;
+    base = 0;
+    for (int i = 0; i < 3; ++i) { ea.npts[i] = npts[i]; ea.pt_base[i] = base; base += npts[i]; }
+    const int64_t eb = (P + 7) / 8;
+    qpd::dense_embed_grad_kernel<<<(unsigned)(eb < 8192 ? eb : 8192), 256, 0, s>>>(ea);
+    launches += 1;
+    st = launch_premap_bwd(pl, w, d_params, pts, npts, s);
+    if (st != QP_OK) return st;
+    launches += 2;
+  }
+  st = launch_reduce(pl, w, d_params, npts, d_loss, d_grad, mlp, s);
   pl->last_launches = launches + 1;
   return st;
 }
@@ -484,7 +553,9 @@ qp_status qp_forward(qp_plan* pl, const float* d_params, const float* d_pts, int
     const int64_t ppt = qpd::TM / ga.nv;
     const int64_t ntiles = (B + ppt - 1) / ppt;
     const int gblocks = (int)(ntiles < pl->sm_count ? ntiles : pl->sm_count);
-    qpd::dense_fwd_gemm_kernel<<<gblocks, 128, qpd::gemm_smem_bytes(n), s>>>(ga);
+    if (pl->prof_start) cudaEventRecord(pl->prof_start, s);
+    qpd::dense_row_gemm_kernel<0><<<gblocks, 128, qpd::gemm_smem_bytes(n, 0), s>>>(ga);
+    if (pl->prof_stop) cudaEventRecord(pl->prof_stop, s);
     qpd::ReadoutArgs ra;
     ra.phi = ga.phi; ra.head = d_params + pl->head_off; ra.n = n; ra.m = pl->c.n_readout;
     ra.nv = ga.nv; ra.npts = B; ra.pt_base = 0; ra.out_f = d_fields; ra.out_df = d_dfields;
@@ -520,7 +591,7 @@ qp_status qp_loss_grad(qp_plan* pl, const float* d_params, const qp_batch* batch
   pl->last_launches = 0;
   const float* pts[3] = {batch->colloc, batch->ic, batch->bc};
   if (dense_path(pl)) {
-    if (pl->c.n_qubits < 7 || pl->c.premap == QP_PREMAP_RFF_MLP) return QP_ERR_UNSUPPORTED;
+    if (pl->c.n_qubits < 7) return QP_ERR_UNSUPPORTED;
     const int64_t np3[3] = {batch->n_colloc, batch->n_ic, batch->n_bc};
     return dense_loss_grad(pl, d_params, pts, np3, d_loss, d_grad, (cudaStream_t)stream);
   }
@@ -561,39 +632,48 @@ qp_status qp_loss_grad(qp_plan* pl, const float* d_params, const qp_batch* batch
   if (pl->prof_stop) cudaEventRecord(pl->prof_stop, s);
   (void)tasks;
   launches += 1;
-  qpk::PremapArgs ma;
-  std::memset(&ma, 0, sizeof(ma));
   if (mlp) {
-    for (int i = 0; i < 3; ++i) { ma.pts[i] = pts[i]; ma.npts[i] = npts[i]; }
-    ma.ptot = P;
-    ma.params = d_params; ma.n = pl->c.n_qubits; ma.premap = pl->c.premap; ma.scale = pl->c.scale;
-    ma.F = pl->c.rff_freqs; ma.H = pl->c.mlp_width;
-    ma.thetaJ = (float*)(ws + w.thetaJ);
-    ma.dthetaJ = (const float*)(ws + w.dthetaJ);
-    ma.d1 = (float*)(ws + w.d1); ma.d2 = (float*)(ws + w.d2); ma.u1 = (float*)(ws + w.u1);
-    if (P > 0) {
-      const int pblocks = (int)((P + 127) / 128 < pl->sm_count * 8 ? (P + 127) / 128 : pl->sm_count * 8);
-      void* bargs[] = {&ma};
-      if (cudaLaunchKernel(premap_bwd_ptr(pl->c.mlp_width), dim3(pblocks), dim3(128), bargs,
-                           pl->smem_premap, s) != cudaSuccess)
-        return QP_ERR_CUDA;
-      launches += 1;
-    }
-    qpk::WgradArgs wa;
-    wa.p = ma;
-    wa.part = (float*)(ws + w.wpart);
-    wa.nW = (int32_t)(pl->mlp_count - pl->nfixed);
-    wa.tile = pl->wtile;
-    void* wargs[] = {&wa};
-    if (cudaLaunchKernel((void*)qpk::premap_wgrad_kernel, dim3(pl->nwblk), dim3(256), wargs,
-                         pl->smem_wgrad, s) != cudaSuccess)
-      return QP_ERR_CUDA;
-    launches += 1;
+    qp_status stb = launch_premap_bwd(pl, w, d_params, pts, npts, s);
+    if (stb != QP_OK) return stb;
+    launches += 2;
   }
   qp_status st_red;
   st_red = launch_reduce(pl, w, d_params, npts, d_loss, d_grad, mlp, s);
   pl->last_launches = launches + 1;
   return st_red;
+}
+
+// Premap backward (per point) and its weight-gradient partials, from dL/dtheta and dL/dJ.
+static qp_status launch_premap_bwd(qp_plan* pl, const WsLayout& w, const float* d_params,
+                                   const float* const pts[3], const int64_t npts[3], cudaStream_t s) {
+  char* ws = (char*)pl->ws;
+  const int64_t P = npts[0] + npts[1] + npts[2];
+  qpk::PremapArgs ma;
+  std::memset(&ma, 0, sizeof(ma));
+  for (int i = 0; i < 3; ++i) { ma.pts[i] = pts[i]; ma.npts[i] = npts[i]; }
+  ma.ptot = P;
+  ma.params = d_params; ma.n = pl->c.n_qubits; ma.premap = pl->c.premap; ma.scale = pl->c.scale;
+  ma.F = pl->c.rff_freqs; ma.H = pl->c.mlp_width;
+  ma.thetaJ = (float*)(ws + w.thetaJ);
+  ma.dthetaJ = (const float*)(ws + w.dthetaJ);
+  ma.d1 = (float*)(ws + w.d1); ma.d2 = (float*)(ws + w.d2); ma.u1 = (float*)(ws + w.u1);
+  if (P > 0) {
+    const int pblocks = (int)((P + 127) / 128 < pl->sm_count * 8 ? (P + 127) / 128 : pl->sm_count * 8);
+    void* bargs[] = {&ma};
+    if (cudaLaunchKernel(premap_bwd_ptr(pl->c.mlp_width), dim3(pblocks), dim3(128), bargs,
+                         pl->smem_premap, s) != cudaSuccess)
+      return QP_ERR_CUDA;
+  }
+  qpk::WgradArgs wa;
+  wa.p = ma;
+  wa.part = (float*)(ws + w.wpart);
+  wa.nW = (int32_t)(pl->mlp_count - pl->nfixed);
+  wa.tile = pl->wtile;
+  void* wargs[] = {&wa};
+  if (cudaLaunchKernel((void*)qpk::premap_wgrad_kernel, dim3(pl->nwblk), dim3(256), wargs,
+                       pl->smem_wgrad, s) != cudaSuccess)
+    return QP_ERR_CUDA;
+  return cuda_status(cudaGetLastError());
 }
 
 static qp_status launch_reduce(qp_plan* pl, const WsLayout& w, const float* d_params, const int64_t npts[3],

@@ -38,6 +38,7 @@ struct BuildArgs {
   int32_t n, L, ansatz, enc;
   float* W;        // [ncc][nkc][2 (hi, lo)][nch x KC] tiled operand blocks
   double2* U;      // [2^n][2^n] fused unitary U' (row j, column k), FP64, or null
+  float* WT;       // transpose operand (rows a = basis index, K = o), same tiling, or null
 };
 
 __device__ inline double2 zmul(double2 a, double2 b) {
@@ -136,6 +137,14 @@ __global__ void dense_build_kernel(BuildArgs a) {
       float* blk = a.W + ((int64_t)(c * nkc + kc) * 2) * (nch * KC);
       blk[core_off(r, t) / 4] = hi;
       blk[nch * KC + core_off(r, t) / 4] = lo;
+      if (a.WT) {
+        // transpose: row a = k (N = dim, chunks of nch2), K = o (2 dim, chunks of KC)
+        const int nch2 = dim < 256 ? dim : 256, nkc2 = 2 * dim / KC;
+        const int c2b = k / nch2, r2 = k % nch2, kc2 = o / KC, t2 = o % KC;
+        float* blk2 = a.WT + ((int64_t)(c2b * nkc2 + kc2) * 2) * (nch2 * KC);
+        blk2[core_off(r2, t2) / 4] = hi;
+        blk2[nch2 * KC + core_off(r2, t2) / 4] = lo;
+      }
     }
   }
 }
@@ -148,18 +157,30 @@ struct GemmArgs {
   int32_t n, nv;            // nv = 4 (state + tangents) or 1
   int64_t npts, pt_base;    // points of this set, first global point row
   int32_t* status;
+  const float* lam;         // MODE 1: costate rows [P][4][2 dim] (A operand)
+  float* mu;                // MODE 1: output rows [P][4][dim]
 };
 
+// Output columns per chunk for the two modes: MODE 0 (forward) has 2 dim outputs over K = dim;
+// MODE 1 (back-projection mu = Re(U'^H lambda)) has dim outputs over K = 2 dim.
+__host__ __device__ inline int row_nch(int n, int mode) {
+  const int ntot = mode == 0 ? (2 << n) : (1 << n);
+  return ntot < 256 ? ntot : 256;
+}
 // Smem: 2 stages x (A hi, A lo: 128 x KC fp32; W hi, W lo: nch x KC fp32) + barriers.
-__host__ __device__ inline int gemm_smem_bytes(int n) {
-  const int nch = n_cols_chunk(n);
+__host__ __device__ inline int gemm_smem_bytes(int n, int mode = 0) {
+  const int nch = row_nch(n, mode);
   return 2 * (2 * TM * KC * 4 + 2 * nch * KC * 4) + 128;
 }
 
-__global__ void __launch_bounds__(128, 1) dense_fwd_gemm_kernel(GemmArgs a) {
+// Row GEMM over (point, vector) rows. MODE 0: Phi = R W^T with R generated from the angles.
+// MODE 1: mu = Lambda W (rows of Lambda loaded, B operand the transposed blocks).
+template <int MODE>
+__global__ void __launch_bounds__(128, 1) dense_row_gemm_kernel(GemmArgs a) {
   extern __shared__ __align__(1024) unsigned char sm[];
   const int n = a.n, dim = 1 << n;
-  const int nch = n_cols_chunk(n), ncc = (2 * dim) / nch, nkc = dim / KC;
+  const int ktot = MODE == 0 ? dim : 2 * dim, ntot = MODE == 0 ? 2 * dim : dim;
+  const int nch = row_nch(n, MODE), ncc = ntot / nch, nkc = ktot / KC;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int abytes = TM * KC * 4, wbytes = nch * KC * 4;
   const int stage_bytes = 2 * abytes + 2 * wbytes;
@@ -198,7 +219,7 @@ __global__ void __launch_bounds__(128, 1) dense_fwd_gemm_kernel(GemmArgs a) {
     // low-bit tables: Lo[t] = prod over the low qubits, Lod[t] its derivative along v_{s-1}
 #pragma unroll
     for (int t = 0; t < 32; ++t) { Lo[t] = 1.f; Lod[t] = 0.f; }
-    for (int b = 0; b < low; ++b) {
+    for (int b = 0; b < (MODE == 0 ? low : 0); ++b) {
       const int q = n - 1 - b;
       const float4 tq = tj[q];
       float sn, cs;
@@ -224,7 +245,27 @@ __global__ void __launch_bounds__(128, 1) dense_fwd_gemm_kernel(GemmArgs a) {
         if (tid == 0) {
           qptc::mbar_arrive_expect_tx(&bars[st], 2 * wbytes);
           qptc::bulk_g2s(sW, a.W + (int64_t)(c * nkc + kc) * 2 * (nch * KC), 2 * wbytes, &bars[st]);
+          // (MODE 1 passes the transposed blocks in a.W)
         }
+        float* Ahi = reinterpret_cast<float*>(sA);
+        float* Alo = reinterpret_cast<float*>(sA + abytes);
+        const int r = tid;  // tile row owned by this thread
+        if (MODE == 1) {
+          const float4* src = reinterpret_cast<const float4*>(a.lam + ((a.pt_base + pc) * 4 + s) * (int64_t)ktot +
+                                                              kc * KC);
+#pragma unroll
+          for (int g4 = 0; g4 < KC / 4; ++g4) {
+            const float4 v4 = src[g4];
+            float4 h4, l4;
+            qptc::split_tf32(v4.x, h4.x, l4.x);
+            qptc::split_tf32(v4.y, h4.y, l4.y);
+            qptc::split_tf32(v4.z, h4.z, l4.z);
+            qptc::split_tf32(v4.w, h4.w, l4.w);
+            const uint32_t off = core_off(r, g4 * 4) / 4;
+            *reinterpret_cast<float4*>(Ahi + off) = h4;
+            *reinterpret_cast<float4*>(Alo + off) = l4;
+          }
+        } else {
         // high-bit factor H and its derivative for this chunk (qubits 0 .. n-1-low)
         float H = 1.f, Hd = 0.f;
         for (int q = 0; q < n - low; ++q) {
@@ -237,9 +278,6 @@ __global__ void __launch_bounds__(128, 1) dense_fwd_gemm_kernel(GemmArgs a) {
           Hd = Hd * f + H * d * J;
           H *= f;
         }
-        float* Ahi = reinterpret_cast<float*>(sA);
-        float* Alo = reinterpret_cast<float*>(sA + abytes);
-        const int r = tid;  // tile row owned by this thread
 #pragma unroll
         for (int g4 = 0; g4 < KC / 4; ++g4) {
           float4 h4, l4;
@@ -254,6 +292,7 @@ __global__ void __launch_bounds__(128, 1) dense_fwd_gemm_kernel(GemmArgs a) {
           const uint32_t off = core_off(r, g4 * 4) / 4;
           *reinterpret_cast<float4*>(Ahi + off) = h4;
           *reinterpret_cast<float4*>(Alo + off) = l4;
+        }
         }
         qptc::fence_proxy_async();
         __syncthreads();
@@ -288,8 +327,9 @@ __global__ void __launch_bounds__(128, 1) dense_fwd_gemm_kernel(GemmArgs a) {
             for (int c0 = 0; c0 < nch; c0 += 32) {
               qptc::tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + pend_buf * (tcols / 2) + c0, v);
               if (pp < a.npts) {
-                float4* dst = reinterpret_cast<float4*>(a.phi + ((a.pt_base + pp) * 4 + s) * dim) +
-                              (pending * nch + c0) / 4;
+                float* orow = MODE == 0 ? reinterpret_cast<float*>(a.phi) : a.mu;
+                float4* dst = reinterpret_cast<float4*>(orow + ((a.pt_base + pp) * 4 + s) * (int64_t)ntot +
+                                                        pending * nch + c0);
 #pragma unroll
                 for (int e = 0; e < 8; ++e) dst[e] = make_float4(v[4 * e], v[4 * e + 1], v[4 * e + 2], v[4 * e + 3]);
               }
@@ -318,8 +358,9 @@ __global__ void __launch_bounds__(128, 1) dense_fwd_gemm_kernel(GemmArgs a) {
       for (int c0 = 0; c0 < nch; c0 += 32) {
         qptc::tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + pend_buf * (tcols / 2) + c0, v);
         if (pp < a.npts) {
-          float4* dst = reinterpret_cast<float4*>(a.phi + ((a.pt_base + pp) * 4 + s) * dim) +
-                        (pending * nch + c0) / 4;
+          float* orow = MODE == 0 ? reinterpret_cast<float*>(a.phi) : a.mu;
+          float4* dst = reinterpret_cast<float4*>(orow + ((a.pt_base + pp) * 4 + s) * (int64_t)ntot +
+                                                  pending * nch + c0);
 #pragma unroll
           for (int e = 0; e < 8; ++e) dst[e] = make_float4(v[4 * e], v[4 * e + 1], v[4 * e + 2], v[4 * e + 3]);
         }
@@ -558,29 +599,22 @@ __global__ void dense_point_kernel(PointArgs a) {
 
 // ------------------------------------------------------------------------- weight-gradient GEMM
 // G_part[chunk][k][o] = sum over the chunk's (point, vector) rows of R_s[k] * Lambda_s[o]:
-// M = 128 basis indices k, N = 256 costate components o = (amp, re|im), K = (point, vector).
-// R is regenerated from the angles; Lambda is read from the costate buffer.
+// M = 128 basis indices k, N = 256 costate components o = (amp, re|im), K = (point, vector)
+// rows, 32 per K-chunk. K-chunks never straddle point sets: a collocation chunk holds 8 points
+// x 4 vectors (rows consecutive in the costate buffer), an IC/BC chunk 32 points x 1 vector.
+// R is regenerated from the angles, one product-rule pass per point giving all four vectors.
 struct WgArgs {
   const float* thetaJ;
   const float2* lam;          // [P][4][dim]
   float* part;                // [nchunks][dim][2 dim]
   int32_t n;
   int64_t npts[3], pt_base[3];
-  int64_t rows_total;         // sum over sets of points * vectors, in K order
-  int32_t nchunks;            // point chunks (grid.y)
+  int64_t kc_end[3];          // cumulative K-chunk counts per set
+  int32_t nchunks;            // point-range chunks (grid.y)
   int32_t* status;
 };
 
-__host__ __device__ inline int wg_smem_bytes() { return 2 * (2 * TM * KC * 4 + 2 * 256 * KC * 4) + 128 + 32 * 40 * 4; }
-
-// Map K row index (concatenated sets: colloc rows are (point, vector) with vector fastest)
-__device__ __forceinline__ void wg_row(const WgArgs& a, int64_t r, int& set, int64_t& p, int& s) {
-  const int64_t r0 = a.npts[0] * 4;
-  if (r < r0) { set = 0; p = r >> 2; s = (int)(r & 3); return; }
-  r -= r0;
-  if (r < a.npts[1]) { set = 1; p = r; s = 0; return; }
-  set = 2; p = r - a.npts[1]; s = 0;
-}
+__host__ __device__ inline int wg_smem_bytes() { return 2 * (2 * TM * KC * 4 + 2 * 256 * KC * 4) + 128 + 32 * QP_MAXQ * 32; }
 
 __global__ void __launch_bounds__(128, 1) dense_wgrad_gemm_kernel(WgArgs a) {
   extern __shared__ __align__(1024) unsigned char sm[];
@@ -592,7 +626,7 @@ __global__ void __launch_bounds__(128, 1) dense_wgrad_gemm_kernel(WgArgs a) {
   const int stage_bytes = 2 * abytes + 2 * bbytes;
   uint64_t* bars = reinterpret_cast<uint64_t*>(sm + 2 * stage_bytes);  // mma_done[2]
   uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + 2 * stage_bytes + 64);
-  float* fac = reinterpret_cast<float*>(sm + 2 * stage_bytes + 128);   // [32 rows][n][4]
+  float4* fac = reinterpret_cast<float4*>(sm + 2 * stage_bytes + 128);  // [32 pts][n][2]
   if (warp == 0) qptc::tmem_alloc(tslot, 256);
   if (tid == 0) { qptc::mbar_init(&bars[0], 1); qptc::mbar_init(&bars[1], 1); }
   qptc::fence_before();
@@ -600,11 +634,12 @@ __global__ void __launch_bounds__(128, 1) dense_wgrad_gemm_kernel(WgArgs a) {
   qptc::fence_after();
   const uint32_t tmem = *tslot;
   const uint32_t id = qptc::idesc(2, TM, nch);
-  const int64_t nkc_total = (a.rows_total + KC - 1) / KC;
+  const int64_t nkc_total = a.kc_end[2];
   const int64_t per = (nkc_total + a.nchunks - 1) / a.nchunks;
   const int64_t kc0 = blockIdx.y * per;
   const int64_t kc1 = kc0 + per < nkc_total ? kc0 + per : nkc_total;
   const int krow = mt * TM + tid;  // basis index owned by this thread in the A operand
+  const int o0 = nt * nch + tid;   // costate components staged by this thread: o0, o0 + 128
   bool ok = true;
   uint32_t it = 0;
   for (int64_t kc = kc0; kc < kc1 && ok; ++kc, ++it) {
@@ -615,79 +650,92 @@ __global__ void __launch_bounds__(128, 1) dense_wgrad_gemm_kernel(WgArgs a) {
     if (it >= 2) w_ok = qptc::mbar_wait(&bars[st], ((it - 2) >> 1) & 1);
     ok = __syncthreads_and(w_ok);
     if (!ok) break;
-    // per-row factors of the chunk: cos, sin of theta_q/2 and the row's Jacobian direction
-    for (int e = tid; e < KC * n; e += blockDim.x) {
-      const int t = e / n, q = e % n;
-      const int64_t r = kc * KC + t;
-      float4 v = make_float4(1.f, 0.f, 0.f, 0.f);  // rows past the end contribute zero
-      if (r < a.rows_total) {
-        int set, s;
-        int64_t p;
-        wg_row(a, r, set, p, s);
+    const int set = kc < a.kc_end[0] ? 0 : (kc < a.kc_end[1] ? 1 : 2);
+    const int64_t ck = kc - (set == 0 ? 0 : a.kc_end[set - 1]);
+    const int ppc = set == 0 ? 8 : 32;            // points in this chunk
+    const int64_t p0 = ck * ppc;
+    const int64_t np = a.npts[set];
+    // per-point factors: (cos, sin of theta_q / 2, Jx, Jy) and (Jt, valid)
+    for (int e = tid; e < ppc * n; e += blockDim.x) {
+      const int pl = e / n, q = e % n;
+      const int64_t p = p0 + pl;
+      float4 f0 = make_float4(0.f, 0.f, 0.f, 0.f), f1 = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (p < np) {
         const float4 tq = reinterpret_cast<const float4*>(a.thetaJ)[(a.pt_base[set] + p) * n + q];
         float sn, cs;
         sincosf(0.5f * tq.x, &sn, &cs);
-        v = make_float4(cs, sn, s == 1 ? tq.y : (s == 2 ? tq.z : tq.w), (float)s);
-      } else {
-        v = make_float4(0.f, 0.f, 0.f, 0.f);
+        f0 = make_float4(cs, sn, tq.y, tq.z);
+        f1 = make_float4(tq.w, 1.f, 0.f, 0.f);
       }
-      reinterpret_cast<float4*>(fac)[t * n + q] = v;
+      fac[(pl * n + q) * 2] = f0;
+      fac[(pl * n + q) * 2 + 1] = f1;
     }
     __syncthreads();
-    // A: R_s[krow] for the 32 rows of the chunk (product rule for the tangents)
-    {
-      float* Ahi = reinterpret_cast<float*>(sA);
-      float* Alo = reinterpret_cast<float*>(sA + abytes);
+    float* Ahi = reinterpret_cast<float*>(sA);
+    float* Alo = reinterpret_cast<float*>(sA + abytes);
+    float av[KC];
+    if (set == 0) {
 #pragma unroll
-      for (int g4 = 0; g4 < KC / 4; ++g4) {
-        float4 h4, l4;
-        float* hv = &h4.x;
-        float* lv = &l4.x;
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          const int t = g4 * 4 + e;
-          const float4* ft = reinterpret_cast<const float4*>(fac) + t * n;
-          float P = 1.f, Pd = 0.f;
-          const int s = (int)ft[0].w;
-          for (int q = 0; q < n; ++q) {
-            const float4 fq = ft[q];
-            const bool bit = (krow >> (n - 1 - q)) & 1;
-            const float f = bit ? fq.y : fq.x, d = bit ? 0.5f * fq.x : -0.5f * fq.y;
-            Pd = Pd * f + P * d * fq.z;
-            P *= f;
-          }
-          qptc::split_tf32(s == 0 ? P : Pd, hv[e], lv[e]);
+      for (int pl = 0; pl < 8; ++pl) {
+        float P = 1.f, D0 = 0.f, D1 = 0.f, D2 = 0.f;
+        for (int q = 0; q < n; ++q) {
+          const float4 f0 = fac[(pl * n + q) * 2], f1 = fac[(pl * n + q) * 2 + 1];
+          const bool bit = (krow >> (n - 1 - q)) & 1;
+          const float f = bit ? f0.y : f0.x, d = bit ? 0.5f * f0.x : -0.5f * f0.y;
+          D0 = D0 * f + P * d * f0.z;
+          D1 = D1 * f + P * d * f0.w;
+          D2 = D2 * f + P * d * f1.x;
+          P *= f;
         }
-        const uint32_t off = core_off(tid, g4 * 4) / 4;
-        *reinterpret_cast<float4*>(Ahi + off) = h4;
-        *reinterpret_cast<float4*>(Alo + off) = l4;
+        av[4 * pl] = P; av[4 * pl + 1] = D0; av[4 * pl + 2] = D1; av[4 * pl + 3] = D2;
+      }
+    } else {
+#pragma unroll
+      for (int pl = 0; pl < 32; ++pl) {
+        float P = 1.f;
+        for (int q = 0; q < n; ++q) {
+          const float4 f0 = fac[(pl * n + q) * 2];
+          P *= ((krow >> (n - 1 - q)) & 1) ? f0.y : f0.x;
+        }
+        av[pl] = P;
       }
     }
-    // B: Lambda rows -> (o, row) core layout; thread handles o = tid and tid + 128
+#pragma unroll
+    for (int g4 = 0; g4 < KC / 4; ++g4) {
+      float4 h4, l4;
+      qptc::split_tf32(av[4 * g4], h4.x, l4.x);
+      qptc::split_tf32(av[4 * g4 + 1], h4.y, l4.y);
+      qptc::split_tf32(av[4 * g4 + 2], h4.z, l4.z);
+      qptc::split_tf32(av[4 * g4 + 3], h4.w, l4.w);
+      const uint32_t off = core_off(tid, g4 * 4) / 4;
+      *reinterpret_cast<float4*>(Ahi + off) = h4;
+      *reinterpret_cast<float4*>(Alo + off) = l4;
+    }
+    // B: costate rows of the chunk; rows are consecutive (collocation) or every 4th (IC/BC)
     {
       float* Bhi = reinterpret_cast<float*>(sB);
       float* Blo = reinterpret_cast<float*>(sB + bbytes);
+      const float* lamf = reinterpret_cast<const float*>(a.lam);
+      const int64_t row0 = set == 0 ? (a.pt_base[0] + p0) * 4 : (a.pt_base[set] + p0) * 4;
+      const int rstep = set == 0 ? 1 : 4;
+      const int nvalid = set == 0 ? (int)((np - p0) * 4 < KC ? (np - p0) * 4 : KC) : (int)(np - p0 < KC ? np - p0 : KC);
 #pragma unroll
       for (int half = 0; half < 2; ++half) {
         const int orow = tid + half * 128;
-        const int o = nt * nch + orow;
+        const int o = o0 + half * 128;
 #pragma unroll
         for (int g4 = 0; g4 < KC / 4; ++g4) {
-          float4 h4, l4;
-          float* hv = &h4.x;
-          float* lv = &l4.x;
+          float v[4];
 #pragma unroll
           for (int e = 0; e < 4; ++e) {
-            const int64_t r = kc * KC + g4 * 4 + e;
-            float v = 0.f;
-            if (r < a.rows_total) {
-              int set, s;
-              int64_t p;
-              wg_row(a, r, set, p, s);
-              v = reinterpret_cast<const float*>(a.lam + ((a.pt_base[set] + p) * 4 + s) * dim)[o];
-            }
-            qptc::split_tf32(v, hv[e], lv[e]);
+            const int t = g4 * 4 + e;
+            v[e] = t < nvalid ? lamf[(row0 + (int64_t)t * rstep) * (2 * dim) + o] : 0.f;
           }
+          float4 h4, l4;
+          qptc::split_tf32(v[0], h4.x, l4.x);
+          qptc::split_tf32(v[1], h4.y, l4.y);
+          qptc::split_tf32(v[2], h4.z, l4.z);
+          qptc::split_tf32(v[3], h4.w, l4.w);
           const uint32_t off = core_off(orow, g4 * 4) / 4;
           *reinterpret_cast<float4*>(Bhi + off) = h4;
           *reinterpret_cast<float4*>(Blo + off) = l4;
@@ -792,110 +840,235 @@ __global__ void dense_y_kernel(SweepArgs a) {
   if (j < dim && jj < dim) a.Y[(int64_t)j * dim + jj] = acc;
 }
 
-// One block: Y <- C^dag Y C for each ring, E_P(l,q) = Im Tr(P_q Y), Y <- R^dag Y R, l = L-1..0.
-__global__ void dense_sweep_kernel(SweepArgs a) {
+// Gate of (layer l, qubit q) in double precision (same formulas as the build).
+__device__ inline void gate_fp64(const float* params, int64_t circ_off, int ansatz, int n, int l, int q,
+                                 double2* g) {
+  const int kp = ansatz == 0 ? 2 : 3;
+  const float* p = params + circ_off + ((int64_t)l * n + q) * kp;
+  if (ansatz == 0) {
+    double ca, sa, cb, sb;
+    sincos(0.5 * (double)p[0], &sa, &ca);
+    sincos(0.5 * (double)p[1], &sb, &cb);
+    g[0] = make_double2(cb * ca, -sb * ca); g[1] = make_double2(-cb * sa, sb * sa);
+    g[2] = make_double2(cb * sa, sb * sa); g[3] = make_double2(cb * ca, sb * ca);
+  } else {
+    double cb, sb;
+    sincos(0.5 * (double)p[1], &sb, &cb);
+    const double ap = 0.5 * ((double)p[0] + (double)p[2]), am = 0.5 * ((double)p[0] - (double)p[2]);
+    double cp, sp, cm, smm;
+    sincos(ap, &sp, &cp);
+    sincos(am, &smm, &cm);
+    g[0] = make_double2(cp * cb, -sp * cb); g[1] = make_double2(-cm * sb, -smm * sb);
+    g[2] = make_double2(cm * sb, -smm * sb); g[3] = make_double2(cp * cb, sp * cb);
+  }
+}
+
+// Index map of the CNOT ring of layer l (basis state |k> -> |c(k)>).
+__device__ __forceinline__ int ring_map(int n, int ansatz, int l, int k) {
+  if (ansatz == 3 || n < 2) return k;
+  const int r = ansatz == 2 ? 1 + (l % (n - 1)) : 1;
+  for (int i = 0; i < n; ++i) {
+    const int bc = 1 << (n - 1 - i), bt = 1 << (n - 1 - (i + r) % n);
+    if (k & bc) k ^= bt;
+  }
+  return k;
+}
+
+// Undo ring l (Y2[a][b] = Y[c(a)][c(b)], i.e. C^dag Y C) and accumulate, at that point,
+// E_P(l, q) = Im Tr(P_q Y2) for all q: Tr(X_q Y) = sum_a Y[a^q][a],
+// Tr(Y_q Y) = sum_a (bit_q(a) ? i : -i) Y[a^q][a], Tr(Z_q Y) = sum_a (bit_q(a) ? -1 : 1) Y[a][a].
+__global__ void dense_sweep_ring_kernel(SweepArgs a, int l, const float2* Yin, float2* Yout) {
   const int n = a.n, dim = 1 << n;
-  float2* Y = a.Y;
-  __shared__ float red[3][32];
-  __shared__ double2 gm[4];
-  const int kp = a.ansatz == 0 ? 2 : 3;
-  for (int l = a.L - 1; l >= 0; --l) {
-    if (a.ansatz != 3 && n > 1) {
-      const int r = a.ansatz == 2 ? 1 + (l % (n - 1)) : 1;
-      // undo the ring: CNOTs in reverse order, each a swap of rows and of columns
-      for (int i = n - 1; i >= 0; --i) {
-        const int bc = 1 << (n - 1 - i), bt = 1 << (n - 1 - (i + r) % n);
-        for (int64_t e = threadIdx.x; e < (int64_t)dim * dim; e += blockDim.x) {
-          const int row = (int)(e / dim), col = (int)(e % dim);
-          if ((row & bc) && !(row & bt)) {
-            const float2 t = Y[e];
-            Y[e] = Y[(int64_t)(row | bt) * dim + col];
-            Y[(int64_t)(row | bt) * dim + col] = t;
-          }
-        }
-        __syncthreads();
-        for (int64_t e = threadIdx.x; e < (int64_t)dim * dim; e += blockDim.x) {
-          const int row = (int)(e / dim), col = (int)(e % dim);
-          if ((col & bc) && !(col & bt)) {
-            const float2 t = Y[e];
-            Y[e] = Y[(int64_t)row * dim + (col | bt)];
-            Y[(int64_t)row * dim + (col | bt)] = t;
-          }
-        }
-        __syncthreads();
+  const int64_t tot = (int64_t)dim * dim;
+  __shared__ float es[QP_MAXQ * 3];
+  for (int i = threadIdx.x; i < n * 3; i += blockDim.x) es[i] = 0.f;
+  __syncthreads();
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
+    const int ra = (int)(e / dim), cb = (int)(e % dim);
+    const float2 v = Yin[(int64_t)ring_map(n, a.ansatz, l, ra) * dim + ring_map(n, a.ansatz, l, cb)];
+    Yout[e] = v;
+    const int x = ra ^ cb;
+    if (x == 0) {
+      for (int q = 0; q < n; ++q) atomicAdd(&es[q * 3 + 2], ((cb >> (n - 1 - q)) & 1) ? -v.y : v.y);
+    } else if ((x & (x - 1)) == 0) {
+      const int q = n - 1 - (31 - __clz(x));
+      // element Y[a^q][a] with a = cb
+      atomicAdd(&es[q * 3 + 0], v.y);
+      atomicAdd(&es[q * 3 + 1], ((cb >> (n - 1 - q)) & 1) ? v.x : -v.x);
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < n * 3; i += blockDim.x) atomicAdd(&a.eout[l * n * 3 + i], es[i]);
+}
+
+// Y <- R^dag Y (rows, TCOL-column tiles per block) for the rotations of layer l.
+template <int TCOL>
+__global__ void dense_sweep_left_kernel(SweepArgs a, int l, float2* Y) {
+  extern __shared__ __align__(16) float2 tile[];  // [dim][TCOL]
+  __shared__ double2 g[QP_MAXQ][4];
+  const int n = a.n, dim = 1 << n;
+  const int c0 = blockIdx.x * TCOL;
+  if (threadIdx.x < n) gate_fp64(a.params, a.circ_off, a.ansatz, n, l, threadIdx.x, g[threadIdx.x]);
+  for (int e = threadIdx.x; e < dim * TCOL; e += blockDim.x) tile[e] = Y[(int64_t)(e / TCOL) * dim + c0 + e % TCOL];
+  __syncthreads();
+  for (int q = 0; q < n; ++q) {
+    const int bit = 1 << (n - 1 - q);
+    const float2 u00 = make_float2((float)g[q][0].x, (float)g[q][0].y), u01 = make_float2((float)g[q][1].x, (float)g[q][1].y);
+    const float2 u10 = make_float2((float)g[q][2].x, (float)g[q][2].y), u11 = make_float2((float)g[q][3].x, (float)g[q][3].y);
+    for (int e = threadIdx.x; e < dim / 2 * TCOL; e += blockDim.x) {
+      const int ri = e / TCOL, c = e % TCOL;
+      const int r0 = ((ri & ~(bit - 1)) << 1) | (ri & (bit - 1)), r1 = r0 | bit;
+      const float2 x = tile[r0 * TCOL + c], y = tile[r1 * TCOL + c];
+      tile[r0 * TCOL + c] = make_float2(u00.x * x.x + u00.y * x.y + u10.x * y.x + u10.y * y.y,
+                                        u00.x * x.y - u00.y * x.x + u10.x * y.y - u10.y * y.x);
+      tile[r1 * TCOL + c] = make_float2(u01.x * x.x + u01.y * x.y + u11.x * y.x + u11.y * y.y,
+                                        u01.x * x.y - u01.y * x.x + u11.x * y.y - u11.y * y.x);
+    }
+    __syncthreads();
+  }
+  for (int e = threadIdx.x; e < dim * TCOL; e += blockDim.x) Y[(int64_t)(e / TCOL) * dim + c0 + e % TCOL] = tile[e];
+}
+
+// Y <- Y R (columns, TROW-row tiles per block) for the rotations of layer l.
+template <int TROW>
+__global__ void dense_sweep_right_kernel(SweepArgs a, int l, float2* Y) {
+  extern __shared__ __align__(16) float2 tile[];  // [TROW][dim]
+  __shared__ double2 g[QP_MAXQ][4];
+  const int n = a.n, dim = 1 << n;
+  const int r0b = blockIdx.x * TROW;
+  if (threadIdx.x < n) gate_fp64(a.params, a.circ_off, a.ansatz, n, l, threadIdx.x, g[threadIdx.x]);
+  for (int e = threadIdx.x; e < dim * TROW; e += blockDim.x) tile[e] = Y[(int64_t)r0b * dim + e];
+  __syncthreads();
+  for (int q = 0; q < n; ++q) {
+    const int bit = 1 << (n - 1 - q);
+    const float2 u00 = make_float2((float)g[q][0].x, (float)g[q][0].y), u01 = make_float2((float)g[q][1].x, (float)g[q][1].y);
+    const float2 u10 = make_float2((float)g[q][2].x, (float)g[q][2].y), u11 = make_float2((float)g[q][3].x, (float)g[q][3].y);
+    for (int e = threadIdx.x; e < dim / 2 * TROW; e += blockDim.x) {
+      const int row = e / (dim / 2), ci = e % (dim / 2);
+      const int c0 = ((ci & ~(bit - 1)) << 1) | (ci & (bit - 1)), c1 = c0 | bit;
+      const float2 x = tile[row * dim + c0], y = tile[row * dim + c1];
+      tile[row * dim + c0] = make_float2(x.x * u00.x - x.y * u00.y + y.x * u10.x - y.y * u10.y,
+                                         x.x * u00.y + x.y * u00.x + y.x * u10.y + y.y * u10.x);
+      tile[row * dim + c1] = make_float2(x.x * u01.x - x.y * u01.y + y.x * u11.x - y.y * u11.y,
+                                         x.x * u01.y + x.y * u01.x + y.x * u11.y + y.y * u11.x);
+    }
+    __syncthreads();
+  }
+  for (int e = threadIdx.x; e < dim * TROW; e += blockDim.x) Y[(int64_t)r0b * dim + e] = tile[e];
+}
+
+}  // namespace qpd
+
+namespace qpd {
+
+// Per-point embedding gradients from mu_s = Re(U'^H lambda_s). For both embeddings the folded
+// phase D satisfies D^H G_q D = Y_q (G = X for RX with D = (-i)^{popcount}, G = Y for RY with
+// D = 1), so with the real product-state vectors R_s:
+//   dL/dtheta_q = sum_s Im<lambda_s|G_q psi_s> = sum_s sum_a sigma_q(a) R_s[a ^ q] mu_s[a],
+//   dL/dJ_qd    = Im<lambda_d|G_q psi_0>      = sum_a sigma_q(a) R_0[a ^ q] mu_d[a],
+// sigma_q(a) = +1 where qubit q of a is 1, -1 where it is 0. R_s[a ^ q] comes from prefix and
+// suffix products of the per-qubit factors carried with their x, y, t derivatives.
+struct EmbedArgs {
+  const float* thetaJ;
+  const float* mu;          // [P][4][dim]
+  float* dthetaJ;           // [P][n] float4
+  int32_t n;
+  int64_t npts[3], pt_base[3];
+};
+
+struct Dual4 {
+  float v, d0, d1, d2;
+};
+__device__ __forceinline__ Dual4 dmul4(const Dual4& a, const Dual4& b) {
+  return {a.v * b.v, a.d0 * b.v + a.v * b.d0, a.d1 * b.v + a.v * b.d1, a.d2 * b.v + a.v * b.d2};
+}
+
+__global__ void dense_embed_grad_kernel(EmbedArgs a) {
+  const int n = a.n, dim = 1 << n;
+  const int lane = threadIdx.x & 31;
+  const int64_t wg = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int64_t total = a.npts[0] + a.npts[1] + a.npts[2];
+  for (int64_t gq = wg; gq < total; gq += nw) {
+    int set = 0;
+    int64_t li = gq;
+    if (li >= a.npts[0]) { li -= a.npts[0]; set = 1; if (li >= a.npts[1]) { li -= a.npts[1]; set = 2; } }
+    const int nv = set == 0 ? 4 : 1;
+    const int64_t gp = a.pt_base[set] + li;
+    const float4* tj = reinterpret_cast<const float4*>(a.thetaJ) + gp * n;
+    float cs[QP_MAXQ], sn[QP_MAXQ], Jx[QP_MAXQ], Jy[QP_MAXQ], Jt[QP_MAXQ];
+#pragma unroll
+    for (int q = 0; q < QP_MAXQ; ++q) {
+      if (q < n) {
+        const float4 t = tj[q];
+        sincosf(0.5f * t.x, &sn[q], &cs[q]);
+        Jx[q] = t.y; Jy[q] = t.z; Jt[q] = t.w;
+      } else {
+        cs[q] = 1.f; sn[q] = 0.f; Jx[q] = Jy[q] = Jt[q] = 0.f;
       }
     }
-    for (int q = 0; q < n; ++q) {
-      const int bit = 1 << (n - 1 - q);
-      // E_X = Im sum_a Y[a^q][a]; E_Y = Im sum_a P_{a,a^q} Y[a^q][a]; E_Z = Im sum_a z_a Y[a][a]
-      float ex = 0.f, ey = 0.f, ez = 0.f;
-      for (int ai = threadIdx.x; ai < dim; ai += blockDim.x) {
-        const float2 y1 = Y[(int64_t)(ai ^ bit) * dim + ai];
-        const float2 yd = Y[(int64_t)ai * dim + ai];
-        ex += y1.y;
-        // P_{a,a^q} = -i (bit 0) or +i (bit 1): Im(-i y) = -y.x, Im(i y) = y.x
-        ey += (ai & bit) ? y1.x : -y1.x;
-        ez += (ai & bit) ? -yd.y : yd.y;
+    float gth[QP_MAXQ], gJ[3][QP_MAXQ];
+#pragma unroll
+    for (int q = 0; q < QP_MAXQ; ++q) gth[q] = gJ[0][q] = gJ[1][q] = gJ[2][q] = 0.f;
+    const float* mu = a.mu + gp * 4 * dim;
+    for (int k = lane; k < dim; k += 32) {
+      float m0 = mu[k], md[3] = {0.f, 0.f, 0.f};
+      if (nv == 4) { md[0] = mu[dim + k]; md[1] = mu[2 * dim + k]; md[2] = mu[3 * dim + k]; }
+      Dual4 pre[QP_MAXQ + 1], suf[QP_MAXQ + 1];
+      pre[0] = {1.f, 0.f, 0.f, 0.f};
+#pragma unroll
+      for (int q = 0; q < QP_MAXQ; ++q) {
+        Dual4 fq = {1.f, 0.f, 0.f, 0.f};
+        if (q < n) {
+          const bool bit = (k >> (n - 1 - q)) & 1;
+          const float f = bit ? sn[q] : cs[q], d = bit ? 0.5f * cs[q] : -0.5f * sn[q];
+          fq = {f, d * Jx[q], d * Jy[q], d * Jt[q]};
+        }
+        pre[q + 1] = dmul4(pre[q], fq);
+      }
+      suf[QP_MAXQ] = {1.f, 0.f, 0.f, 0.f};
+#pragma unroll
+      for (int q = QP_MAXQ - 1; q >= 0; --q) {
+        Dual4 fq = {1.f, 0.f, 0.f, 0.f};
+        if (q < n) {
+          const bool bit = (k >> (n - 1 - q)) & 1;
+          const float f = bit ? sn[q] : cs[q], d = bit ? 0.5f * cs[q] : -0.5f * sn[q];
+          fq = {f, d * Jx[q], d * Jy[q], d * Jt[q]};
+        }
+        suf[q] = dmul4(fq, suf[q + 1]);
       }
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        ex += __shfl_xor_sync(0xffffffffu, ex, o);
-        ey += __shfl_xor_sync(0xffffffffu, ey, o);
-        ez += __shfl_xor_sync(0xffffffffu, ez, o);
-      }
-      if ((threadIdx.x & 31) == 0) { red[0][threadIdx.x >> 5] = ex; red[1][threadIdx.x >> 5] = ey; red[2][threadIdx.x >> 5] = ez; }
-      if (threadIdx.x == 0) {
-        const float* p = a.params + a.circ_off + ((int64_t)l * n + q) * kp;
-        double2 u00, u01, u10, u11;
-        if (a.ansatz == 0) {
-          double ca, sa, cb, sb;
-          sincos(0.5 * (double)p[0], &sa, &ca);
-          sincos(0.5 * (double)p[1], &sb, &cb);
-          u00 = make_double2(cb * ca, -sb * ca); u01 = make_double2(-cb * sa, sb * sa);
-          u10 = make_double2(cb * sa, sb * sa); u11 = make_double2(cb * ca, sb * ca);
-        } else {
-          double cb, sb;
-          sincos(0.5 * (double)p[1], &sb, &cb);
-          const double ap = 0.5 * ((double)p[0] + (double)p[2]), am = 0.5 * ((double)p[0] - (double)p[2]);
-          double cp, sp, cm, smm;
-          sincos(ap, &sp, &cp);
-          sincos(am, &smm, &cm);
-          u00 = make_double2(cp * cb, -sp * cb); u01 = make_double2(-cm * sb, -smm * sb);
-          u10 = make_double2(cm * sb, -smm * sb); u11 = make_double2(cp * cb, sp * cb);
+      for (int q = 0; q < QP_MAXQ; ++q) {
+        if (q < n) {
+          const bool bit = (k >> (n - 1 - q)) & 1;
+          // factor of qubit q at the flipped bit
+          const float f = bit ? cs[q] : sn[q], d = bit ? -0.5f * sn[q] : 0.5f * cs[q];
+          const Dual4 fl = dmul4(dmul4(pre[q], {f, d * Jx[q], d * Jy[q], d * Jt[q]}), suf[q + 1]);
+          const float sg = bit ? 1.f : -1.f;
+          float acc = fl.v * m0;
+          if (nv == 4) {
+            acc += fl.d0 * md[0] + fl.d1 * md[1] + fl.d2 * md[2];
+            gJ[0][q] += sg * fl.v * md[0];
+            gJ[1][q] += sg * fl.v * md[1];
+            gJ[2][q] += sg * fl.v * md[2];
+          }
+          gth[q] += sg * acc;
         }
-        gm[0] = u00; gm[1] = u01; gm[2] = u10; gm[3] = u11;
       }
-      __syncthreads();
-      if (threadIdx.x < 3) {
-        float s = 0.f;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[threadIdx.x][w];
-        a.eout[(l * n + q) * 3 + threadIdx.x] = s;
+    }
+#pragma unroll
+    for (int q = 0; q < QP_MAXQ; ++q) {
+      if (q < n) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          gth[q] += __shfl_xor_sync(0xffffffffu, gth[q], o);
+          gJ[0][q] += __shfl_xor_sync(0xffffffffu, gJ[0][q], o);
+          gJ[1][q] += __shfl_xor_sync(0xffffffffu, gJ[1][q], o);
+          gJ[2][q] += __shfl_xor_sync(0xffffffffu, gJ[2][q], o);
+        }
+        if (lane == 0)
+          reinterpret_cast<float4*>(a.dthetaJ)[gp * n + q] = make_float4(gth[q], gJ[0][q], gJ[1][q], gJ[2][q]);
       }
-      // Y <- U^dag Y U on qubit q (rows by U^dag, columns by U)
-      const float2 u00 = make_float2((float)gm[0].x, (float)gm[0].y), u01 = make_float2((float)gm[1].x, (float)gm[1].y);
-      const float2 u10 = make_float2((float)gm[2].x, (float)gm[2].y), u11 = make_float2((float)gm[3].x, (float)gm[3].y);
-      for (int64_t e = threadIdx.x; e < (int64_t)dim * dim / 2; e += blockDim.x) {
-        const int col = (int)(e % dim), ri = (int)(e / dim);
-        const int r0 = ((ri & ~(bit - 1)) << 1) | (ri & (bit - 1)), r1 = r0 | bit;
-        const float2 x = Y[(int64_t)r0 * dim + col], y = Y[(int64_t)r1 * dim + col];
-        // rows: U^dag = [[conj u00, conj u10], [conj u01, conj u11]]
-        Y[(int64_t)r0 * dim + col] = make_float2(u00.x * x.x + u00.y * x.y + u10.x * y.x + u10.y * y.y,
-                                                 u00.x * x.y - u00.y * x.x + u10.x * y.y - u10.y * y.x);
-        Y[(int64_t)r1 * dim + col] = make_float2(u01.x * x.x + u01.y * x.y + u11.x * y.x + u11.y * y.y,
-                                                 u01.x * x.y - u01.y * x.x + u11.x * y.y - u11.y * y.x);
-      }
-      __syncthreads();
-      for (int64_t e = threadIdx.x; e < (int64_t)dim * dim / 2; e += blockDim.x) {
-        const int row = (int)(e / (dim / 2)), ci = (int)(e % (dim / 2));
-        const int c0 = ((ci & ~(bit - 1)) << 1) | (ci & (bit - 1)), c1 = c0 | bit;
-        const float2 x = Y[(int64_t)row * dim + c0], y = Y[(int64_t)row * dim + c1];
-        // columns: (Y U)[., c0] = Y[.,c0] u00 + Y[.,c1] u10 ; (Y U)[., c1] = Y[.,c0] u01 + Y[.,c1] u11
-        Y[(int64_t)row * dim + c0] = make_float2(x.x * u00.x - x.y * u00.y + y.x * u10.x - y.y * u10.y,
-                                                 x.x * u00.y + x.y * u00.x + y.x * u10.y + y.y * u10.x);
-        Y[(int64_t)row * dim + c1] = make_float2(x.x * u01.x - x.y * u01.y + y.x * u11.x - y.y * u11.y,
-                                                 x.x * u01.y + x.y * u01.x + y.x * u11.y + y.y * u11.x);
-      }
-      __syncthreads();
     }
   }
 }

@@ -75,6 +75,8 @@ def lib():
         L.qp_status_str.restype = ctypes.c_char_p
         L.qp_last_launch_count.argtypes = [P]
         L.qp_last_launch_count.restype = I32
+        L.qp_plan_path.argtypes = [P]
+        L.qp_plan_path.restype = I32
         L.qp_set_profile_events.argtypes = [P, P, P]
         L.qp_set_profile_events.restype = I32
         L.qp_sched_selftest.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_uint]
@@ -139,6 +141,7 @@ class Plan:
         lay = (ctypes.c_int64 * 4)()
         _check(lib().qp_param_layout(self._h, lay), "qp_param_layout")
         self.layout = {"circuit": lay[0], "head": lay[1], "total": lay[2], "fixed": lay[3]}
+        self.path = {1: "simt", 2: "gemm_3xtf32"}.get(lib().qp_plan_path(self._h), "?")
 
     def __del__(self):
         h = getattr(self, "_h", None)

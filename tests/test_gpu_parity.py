@@ -38,7 +38,7 @@ def _rel(gpu, ref, floor=1e-12):
     return float(np.max(np.abs(gpu - ref))) / scale if ref.size else 0.0
 
 
-def _forward_check(torch, oracle, circ, params, pts, want_df=True, tol=TOL, path="auto"):
+def _forward_check(torch, oracle, circ, params, pts, want_df=True, tol=TOL, path="simt"):
     from paper_2506_23246_b300 import qp
     plan = qp.Plan(circ, path=path)
     dp = torch.tensor(params, device="cuda")
@@ -116,7 +116,7 @@ def test_dense_tensorcore_forward_parity(torch_cuda, oracle, n, L, ans, enc):
 
 # ----------------------------------------------------------------------------- loss + grad
 
-def _loss_grad_check(torch, oracle, circ, prob, params, sets, idx=None, tol=TOL, path="auto"):
+def _loss_grad_check(torch, oracle, circ, prob, params, sets, idx=None, tol=TOL, path="simt"):
     from paper_2506_23246_b300 import qp
     plan = qp.Plan(circ, prob, path=path)
     dp = torch.tensor(params, device="cuda")
@@ -197,6 +197,68 @@ def test_dense_tensorcore_loss_grad_parity(torch_cuda, oracle, n, L, ans, enc, m
     _loss_grad_check(torch_cuda, oracle, circ, prob, params, sets, path="gemm_3xtf32")
 
 
+@pytest.mark.parametrize("medium", ["vacuum", "dielectric"])
+def test_dense_tensorcore_c3_loss_grad_parity(torch_cuda, oracle, medium):
+    """Fused-unitary path on the full QPINN configuration (8 qubits, 6 strongly entangling
+    layers, RFF(64) + tanh MLP(32), energy term): every circuit and head parameter and a
+    sample of MLP parameters (embedding gradients from mu = Re(U'^H lambda))."""
+    circ = W.c3_circuit(8, 6)
+    prob = W.c3_problem(medium, 4, 4, 3)
+    prob["disk_x0"], prob["disk_r"] = 0.2, 0.6
+    sets = {"colloc": W.grid_points(4, 4, 3, W.c3_tmax(medium)), "ic": W.ic_grid(4, 2)}
+    params = W.init_params(circ, 5)
+    lay = oracle.param_layout(circ)
+    rng = np.random.default_rng(0)
+    mlp = rng.choice(np.arange(lay["fixed"], lay["circuit"]), 48, replace=False)
+    idx = np.concatenate([np.arange(3), np.sort(mlp), np.arange(lay["circuit"], lay["total"])])
+    _loss_grad_check(torch_cuda, oracle, circ, prob, params, sets, idx, path="gemm_3xtf32")
+
+
+def test_dense_tensorcore_mlp_all_params(torch_cuda, oracle):
+    circ = W.circuit(7, 3, ansatz="strong_rot", enc="rx", scale="asin", premap="rff_mlp",
+                     rff_freqs=8, mlp_width=8, mlp_depth=1)
+    prob = W.problem("vacuum", w_energy=10.0)
+    sets = {"colloc": W.uniform_points(41, 3, 1.5), "ic": W.ic_points_uniform(6, 4),
+            "bc": W.bc_points(4, 5)}
+    params = W.init_params(circ, 9)
+    _loss_grad_check(torch_cuda, oracle, circ, prob, params, sets, path="gemm_3xtf32")
+
+
+def test_dense_matches_simt_full_size(torch_cuda):
+    """Full 64x64x16 grid + IC plane in the bench's configuration: the tensor-core path and the
+    FP32 SIMT path agree on every loss term and on the gradient."""
+    from paper_2506_23246_b300 import qp
+    torch = torch_cuda
+    circ, prob, params, sets = W.c3_workload(0)
+    dp = torch.tensor(params, device="cuda")
+    dsets = {k: torch.tensor(v, device="cuda") for k, v in sets.items()}
+    out = {}
+    for path in ("simt", "gemm_3xtf32"):
+        plan = qp.Plan(circ, prob, path=path)
+        l, g = plan.loss_grad(dp, dsets)
+        torch.cuda.synchronize()
+        assert plan.last_device_error() == 0
+        out[path] = (l.clone(), g.clone())
+    ls, gs = out["simt"]
+    ld, gd = out["gemm_3xtf32"]
+    assert float(((ls - ld).abs() / ls.abs().clamp_min(1e-12)).max()) < 2e-5
+    lay = qp.Plan(circ, prob).layout
+    for lo, hi in ((lay["fixed"], lay["circuit"]), (lay["circuit"], lay["head"]),
+                   (lay["head"], lay["total"])):
+        assert float((gs[lo:hi] - gd[lo:hi]).abs().max()) <= 2e-5 * float(gs[lo:hi].abs().max())
+
+
+def test_auto_path_c3_matches_oracle(torch_cuda, oracle):
+    """The default path choice (tensor cores at 8 qubits) on a small C3 case."""
+    circ = W.c3_circuit(8, 6)
+    prob = W.c3_problem("vacuum", 4, 4, 2)
+    sets = {"colloc": W.grid_points(4, 4, 2, 1.5), "ic": W.ic_grid(4, 2)}
+    params = W.init_params(circ, 2)
+    lay = oracle.param_layout(circ)
+    idx = np.arange(lay["circuit"], lay["total"])
+    _loss_grad_check(torch_cuda, oracle, circ, prob, params, sets, idx, path="auto")
+
+
 def test_loss_grad_empty_sets(torch_cuda, oracle):
     circ, prob, params, sets = W.c2_workload(1, 40, 9, 0)
     sets = {"colloc": sets["colloc"], "ic": sets["ic"]}
@@ -226,7 +288,7 @@ def test_c3_full_size_sampled_fields(torch_cuda, oracle):
     from paper_2506_23246_b300 import qp
     torch = torch_cuda
     circ, prob, params, sets = W.c3_workload(0)
-    plan = qp.Plan(circ, prob)
+    plan = qp.Plan(circ, prob, path="simt")
     dp = torch.tensor(params, device="cuda")
     dx = torch.tensor(sets["colloc"], device="cuda")
     f, df = plan.forward(dp, dx)
@@ -245,7 +307,7 @@ def test_c3_full_size_decomposition(torch_cuda):
     torch = torch_cuda
     circ, prob, params, sets = W.c3_workload(0, medium="vacuum")
     prob = dict(prob, energy_nt=0, energy_slice=0)
-    plan = qp.Plan(circ, prob)
+    plan = qp.Plan(circ, prob, path="simt")
     dp = torch.tensor(params, device="cuda")
     c = torch.tensor(sets["colloc"], device="cuda")
     ic = torch.tensor(sets["ic"], device="cuda")
