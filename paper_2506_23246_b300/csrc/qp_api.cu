@@ -463,7 +463,7 @@ static qp_status dense_loss_grad(qp_plan* pl, const float* d_params, const float
   wa.status = (int32_t*)(ws + w.status);
   const int tiles = (dim / qpd::TM) * (2 * dim / 256);
   if (pl->prof_start) cudaEventRecord(pl->prof_start, s);
-  qpd::dense_wgrad_gemm_kernel<<<dim3(tiles, wa.nchunks), 128, qpd::wg_smem_bytes(), s>>>(wa);
+  qpd::dense_wgrad_gemm_kernel<<<dim3(tiles, wa.nchunks), qpd::WG_THREADS, qpd::wg_smem_bytes(), s>>>(wa);
   if (pl->prof_stop) cudaEventRecord(pl->prof_stop, s);
   launches += 1;
   qpd::SweepArgs sa;

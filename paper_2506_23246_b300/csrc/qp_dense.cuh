@@ -616,7 +616,46 @@ struct WgArgs {
 
 __host__ __device__ inline int wg_smem_bytes() { return 2 * (2 * TM * KC * 4 + 2 * 256 * KC * 4) + 128 + 32 * QP_MAXQ * 32; }
 
-__global__ void __launch_bounds__(128, 1) dense_wgrad_gemm_kernel(WgArgs a) {
+// Global loads of one K-chunk, issued one iteration ahead (software pipeline): the costate
+// values this thread stages (component o = nt * 256 + tid of the chunk's 32 rows) and the raw
+// angle entries (theta, J) of up to 2 (point, qubit) pairs of the chunk.
+constexpr int WG_THREADS = 256;
+struct WgPrefetch {
+  float lam[KC];
+  float4 tj[2];
+};
+
+__device__ __forceinline__ void wg_chunk_geom(const WgArgs& a, int64_t kc, int& set, int64_t& p0, int& ppc) {
+  set = kc < a.kc_end[0] ? 0 : (kc < a.kc_end[1] ? 1 : 2);
+  const int64_t ck = kc - (set == 0 ? 0 : a.kc_end[set - 1]);
+  ppc = set == 0 ? 8 : 32;
+  p0 = ck * ppc;
+}
+
+__device__ __forceinline__ void wg_prefetch(const WgArgs& a, int64_t kc, int tid, int o, WgPrefetch& f) {
+  const int n = a.n, dim = 1 << n;
+  int set, ppc;
+  int64_t p0;
+  wg_chunk_geom(a, kc, set, p0, ppc);
+  const int64_t np = a.npts[set];
+  const float* lamf = reinterpret_cast<const float*>(a.lam);
+  const int64_t row0 = (a.pt_base[set] + p0) * 4;
+  const int rstep = set == 0 ? 1 : 4;
+  const int nvalid = set == 0 ? (int)((np - p0) * 4 < KC ? (np - p0) * 4 : KC) : (int)(np - p0 < KC ? np - p0 : KC);
+#pragma unroll
+  for (int t = 0; t < KC; ++t)
+    f.lam[t] = t < nvalid ? __ldg(lamf + (row0 + (int64_t)t * rstep) * (2 * dim) + o) : 0.f;
+#pragma unroll
+  for (int j = 0; j < 2; ++j) {
+    const int e = tid + j * WG_THREADS;
+    const int pl = e / n, q = e % n;
+    f.tj[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (e < ppc * n && p0 + pl < np)
+      f.tj[j] = __ldg(reinterpret_cast<const float4*>(a.thetaJ) + (a.pt_base[set] + p0 + pl) * n + q);
+  }
+}
+
+__global__ void __launch_bounds__(WG_THREADS, 1) dense_wgrad_gemm_kernel(WgArgs a) {
   extern __shared__ __align__(1024) unsigned char sm[];
   const int n = a.n, dim = 1 << n;
   const int tid = threadIdx.x, warp = tid >> 5;
@@ -638,45 +677,64 @@ __global__ void __launch_bounds__(128, 1) dense_wgrad_gemm_kernel(WgArgs a) {
   const int64_t per = (nkc_total + a.nchunks - 1) / a.nchunks;
   const int64_t kc0 = blockIdx.y * per;
   const int64_t kc1 = kc0 + per < nkc_total ? kc0 + per : nkc_total;
-  const int krow = mt * TM + tid;  // basis index owned by this thread in the A operand
-  const int o0 = nt * nch + tid;   // costate components staged by this thread: o0, o0 + 128
+  const int arow = tid & (TM - 1), ahalf = tid >> 7;  // A row (basis index) and half of the chunk
+  const int krow = mt * TM + arow;
+  const int o = nt * nch + tid;                      // costate component staged by this thread
   bool ok = true;
   uint32_t it = 0;
+  WgPrefetch pf;
+  if (kc0 < kc1) wg_prefetch(a, kc0, tid, o, pf);
   for (int64_t kc = kc0; kc < kc1 && ok; ++kc, ++it) {
     const uint32_t st = it & 1;
     unsigned char* sA = sm + st * stage_bytes;
     unsigned char* sB = sA + 2 * abytes;
+    int set, ppc;
+    int64_t p0;
+    wg_chunk_geom(a, kc, set, p0, ppc);
     bool w_ok = true;
     if (it >= 2) w_ok = qptc::mbar_wait(&bars[st], ((it - 2) >> 1) & 1);
-    ok = __syncthreads_and(w_ok);
+    ok = __syncthreads_and(w_ok);  // also orders the previous chunk's reads of `fac`
     if (!ok) break;
-    const int set = kc < a.kc_end[0] ? 0 : (kc < a.kc_end[1] ? 1 : 2);
-    const int64_t ck = kc - (set == 0 ? 0 : a.kc_end[set - 1]);
-    const int ppc = set == 0 ? 8 : 32;            // points in this chunk
-    const int64_t p0 = ck * ppc;
-    const int64_t np = a.npts[set];
-    // per-point factors: (cos, sin of theta_q / 2, Jx, Jy) and (Jt, valid)
-    for (int e = tid; e < ppc * n; e += blockDim.x) {
-      const int pl = e / n, q = e % n;
-      const int64_t p = p0 + pl;
-      float4 f0 = make_float4(0.f, 0.f, 0.f, 0.f), f1 = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (p < np) {
-        const float4 tq = reinterpret_cast<const float4*>(a.thetaJ)[(a.pt_base[set] + p) * n + q];
+    // per-point factors from the prefetched angles: (cos, sin of theta_q / 2, Jx, Jy), (Jt, .)
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      const int e = tid + j * WG_THREADS;
+      if (e < ppc * n) {
+        const float4 tq = pf.tj[j];
         float sn, cs;
         sincosf(0.5f * tq.x, &sn, &cs);
-        f0 = make_float4(cs, sn, tq.y, tq.z);
-        f1 = make_float4(tq.w, 1.f, 0.f, 0.f);
+        const int pl = e / n, q = e % n;
+        const bool valid = p0 + pl < a.npts[set];  // rows past the end of the set contribute zero
+        fac[(pl * n + q) * 2] = valid ? make_float4(cs, sn, tq.y, tq.z) : make_float4(0.f, 0.f, 0.f, 0.f);
+        fac[(pl * n + q) * 2 + 1] = valid ? make_float4(tq.w, 1.f, 0.f, 0.f) : make_float4(0.f, 0.f, 0.f, 0.f);
       }
-      fac[(pl * n + q) * 2] = f0;
-      fac[(pl * n + q) * 2 + 1] = f1;
     }
-    __syncthreads();
+    // B: costate rows of the chunk (prefetched) -> (o, row) core layout, TF32 hi/lo
+    {
+      float* Bhi = reinterpret_cast<float*>(sB);
+      float* Blo = reinterpret_cast<float*>(sB + bbytes);
+#pragma unroll
+      for (int g4 = 0; g4 < KC / 4; ++g4) {
+        float4 h4, l4;
+        qptc::split_tf32(pf.lam[4 * g4], h4.x, l4.x);
+        qptc::split_tf32(pf.lam[4 * g4 + 1], h4.y, l4.y);
+        qptc::split_tf32(pf.lam[4 * g4 + 2], h4.z, l4.z);
+        qptc::split_tf32(pf.lam[4 * g4 + 3], h4.w, l4.w);
+        const uint32_t off = core_off(tid, g4 * 4) / 4;
+        *reinterpret_cast<float4*>(Bhi + off) = h4;
+        *reinterpret_cast<float4*>(Blo + off) = l4;
+      }
+    }
+    __syncthreads();  // fac visible
+    // next chunk's global loads are in flight while this chunk is generated and multiplied
+    if (kc + 1 < kc1) wg_prefetch(a, kc + 1, tid, o, pf);
     float* Ahi = reinterpret_cast<float*>(sA);
     float* Alo = reinterpret_cast<float*>(sA + abytes);
-    float av[KC];
+    float av[KC / 2];  // this thread's half of the row: K indices 16 * ahalf .. + 15
     if (set == 0) {
 #pragma unroll
-      for (int pl = 0; pl < 8; ++pl) {
+      for (int pi = 0; pi < 4; ++pi) {
+        const int pl = ahalf * 4 + pi;
         float P = 1.f, D0 = 0.f, D1 = 0.f, D2 = 0.f;
         for (int q = 0; q < n; ++q) {
           const float4 f0 = fac[(pl * n + q) * 2], f1 = fac[(pl * n + q) * 2 + 1];
@@ -687,60 +745,30 @@ __global__ void __launch_bounds__(128, 1) dense_wgrad_gemm_kernel(WgArgs a) {
           D2 = D2 * f + P * d * f1.x;
           P *= f;
         }
-        av[4 * pl] = P; av[4 * pl + 1] = D0; av[4 * pl + 2] = D1; av[4 * pl + 3] = D2;
+        av[4 * pi] = P; av[4 * pi + 1] = D0; av[4 * pi + 2] = D1; av[4 * pi + 3] = D2;
       }
     } else {
 #pragma unroll
-      for (int pl = 0; pl < 32; ++pl) {
+      for (int pi = 0; pi < 16; ++pi) {
+        const int pl = ahalf * 16 + pi;
         float P = 1.f;
         for (int q = 0; q < n; ++q) {
           const float4 f0 = fac[(pl * n + q) * 2];
           P *= ((krow >> (n - 1 - q)) & 1) ? f0.y : f0.x;
         }
-        av[pl] = P;
+        av[pi] = P;
       }
     }
 #pragma unroll
-    for (int g4 = 0; g4 < KC / 4; ++g4) {
+    for (int g4 = 0; g4 < KC / 8; ++g4) {
       float4 h4, l4;
       qptc::split_tf32(av[4 * g4], h4.x, l4.x);
       qptc::split_tf32(av[4 * g4 + 1], h4.y, l4.y);
       qptc::split_tf32(av[4 * g4 + 2], h4.z, l4.z);
       qptc::split_tf32(av[4 * g4 + 3], h4.w, l4.w);
-      const uint32_t off = core_off(tid, g4 * 4) / 4;
+      const uint32_t off = core_off(arow, ahalf * (KC / 2) + g4 * 4) / 4;
       *reinterpret_cast<float4*>(Ahi + off) = h4;
       *reinterpret_cast<float4*>(Alo + off) = l4;
-    }
-    // B: costate rows of the chunk; rows are consecutive (collocation) or every 4th (IC/BC)
-    {
-      float* Bhi = reinterpret_cast<float*>(sB);
-      float* Blo = reinterpret_cast<float*>(sB + bbytes);
-      const float* lamf = reinterpret_cast<const float*>(a.lam);
-      const int64_t row0 = set == 0 ? (a.pt_base[0] + p0) * 4 : (a.pt_base[set] + p0) * 4;
-      const int rstep = set == 0 ? 1 : 4;
-      const int nvalid = set == 0 ? (int)((np - p0) * 4 < KC ? (np - p0) * 4 : KC) : (int)(np - p0 < KC ? np - p0 : KC);
-#pragma unroll
-      for (int half = 0; half < 2; ++half) {
-        const int orow = tid + half * 128;
-        const int o = o0 + half * 128;
-#pragma unroll
-        for (int g4 = 0; g4 < KC / 4; ++g4) {
-          float v[4];
-#pragma unroll
-          for (int e = 0; e < 4; ++e) {
-            const int t = g4 * 4 + e;
-            v[e] = t < nvalid ? lamf[(row0 + (int64_t)t * rstep) * (2 * dim) + o] : 0.f;
-          }
-          float4 h4, l4;
-          qptc::split_tf32(v[0], h4.x, l4.x);
-          qptc::split_tf32(v[1], h4.y, l4.y);
-          qptc::split_tf32(v[2], h4.z, l4.z);
-          qptc::split_tf32(v[3], h4.w, l4.w);
-          const uint32_t off = core_off(orow, g4 * 4) / 4;
-          *reinterpret_cast<float4*>(Bhi + off) = h4;
-          *reinterpret_cast<float4*>(Blo + off) = l4;
-        }
-      }
     }
     qptc::fence_proxy_async();
     __syncthreads();
@@ -759,24 +787,24 @@ __global__ void __launch_bounds__(128, 1) dense_wgrad_gemm_kernel(WgArgs a) {
       }
       qptc::commit(&bars[st]);
     }
-    __syncthreads();
   }
-  // epilogue: 128 x 256 partial tile
-  float* outp = a.part + ((int64_t)blockIdx.y * dim + mt * TM + tid) * (2 * dim) + nt * nch;
+  // epilogue: 128 x 256 partial tile; warps w and w + 4 read the same lanes, column halves
+  const int lrow = (warp & 3) * 32 + (tid & 31), chalf = warp >> 2;
+  float* outp = a.part + ((int64_t)blockIdx.y * dim + mt * TM + lrow) * (2 * dim) + nt * nch + chalf * 128;
   if (ok && it > 0) {
     ok = __syncthreads_and(qptc::mbar_wait(&bars[(it - 1) & 1], ((it - 1) >> 1) & 1));
     if (ok) {
       qptc::fence_after();
       float v[32];
-      for (int c0 = 0; c0 < nch; c0 += 32) {
-        qptc::tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + c0, v);
+      for (int c0 = 0; c0 < 128; c0 += 32) {
+        qptc::tmem_ld32(tmem + ((uint32_t)((warp & 3) * 32) << 16) + chalf * 128 + c0, v);
 #pragma unroll
         for (int e = 0; e < 8; ++e)
           reinterpret_cast<float4*>(outp + c0)[e] = make_float4(v[4 * e], v[4 * e + 1], v[4 * e + 2], v[4 * e + 3]);
       }
     }
   } else if (ok) {
-    for (int c0 = 0; c0 < nch; c0 += 4) *reinterpret_cast<float4*>(outp + c0) = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int c0 = 0; c0 < 128; c0 += 4) *reinterpret_cast<float4*>(outp + c0) = make_float4(0.f, 0.f, 0.f, 0.f);
   }
   if (!ok) {
     if (tid == 0) atomicExch(a.status, 6);
