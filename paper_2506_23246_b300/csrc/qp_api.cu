@@ -49,7 +49,7 @@ int geo_ppw(int n) { return 32 >> (n - geo_lb(n)); }
 
 struct WsLayout {
   size_t status, gates, cmat, cenc, thetaJ, dthetaJ, d1, d2, u1, blk_loss, blk_grad, wpart;
-  size_t dW, dphi, dU, dG, dY, dpart, dWT, dmu, total;
+  size_t dW, dphi, dU, dG, dY, dpart, dWT, dmu, dW16, total;
 };
 
 // Rows of (point, vector) accumulated per weight-gradient chunk (bounds the FP32 tensor-core
@@ -57,6 +57,12 @@ struct WsLayout {
 int64_t wg_rows_per_chunk(int n) { return n <= 8 ? 512 : 4096; }
 
 bool dense_path(const qp_plan* pl) { return pl->path == QP_PATH_GEMM_3XTF32; }
+
+// The fused forward kernel keeps a tile's whole output row (2^(n+1) FP32 columns) in tensor
+// memory, which holds 512 columns: n = 7 and 8.
+bool fused_path(const qp_plan* pl) {
+  return dense_path(pl) && pl->c.n_qubits >= 7 && pl->c.n_qubits <= 8;
+}
 
 size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
 
@@ -92,6 +98,7 @@ WsLayout ws_layout(const qp_plan* pl, int64_t P) {
   const bool dm = dg && pl->c.premap == QP_PREMAP_RFF_MLP;
   w.dWT = o; o = al256(o + (dm ? 2 * (2 * dim) * dim * 4 : 0));
   w.dmu = o; o = al256(o + (dm ? (size_t)P * 4 * dim * 4 : 0));
+  w.dW16 = o; o = al256(o + (dg && fused_path(pl) ? 2 * (2 * dim) * dim * 4 : 0));
   w.total = o;
   return w;
 }
@@ -258,7 +265,10 @@ qp_status qp_plan_create(const qp_circuit* circuit, const qp_problem* problem, i
         cudaFuncSetAttribute((void*)qpd::dense_sweep_left_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (1 << n) * 16 * 8) != cudaSuccess ||
         cudaFuncSetAttribute((void*)qpd::dense_sweep_right_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (1 << n) * 16 * 8) != cudaSuccess) {
+                             (1 << n) * 16 * 8) != cudaSuccess ||
+        (fused_path(pl) &&
+         cudaFuncSetAttribute((void*)qpd::dense_fused_fwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              qpd::fused_smem(n, pl->p.energy_nt).total) != cudaSuccess)) {
       cudaGetLastError();
       delete pl;
       return QP_ERR_CUDA;
@@ -419,36 +429,63 @@ static qp_status dense_loss_grad(qp_plan* pl, const float* d_params, const float
   ba.ansatz = pl->c.ansatz; ba.enc = pl->c.enc; ba.W = (float*)(ws + w.dW); ba.U = (double2*)(ws + w.dU);
   const bool mlp = pl->c.premap == QP_PREMAP_RFF_MLP;
   ba.WT = mlp ? (float*)(ws + w.dWT) : nullptr;
+  const bool fused = fused_path(pl);
+  ba.W16 = fused ? (float*)(ws + w.dW16) : nullptr;
+  if (fused) ba.W = nullptr;
   qpd::dense_build_kernel<<<dim, 256, dim * 16, s>>>(ba);
   launches += 1;
   int64_t base = 0;
-  for (int set = 0; set < 3; ++set) {
-    if (npts[set] > 0) {
-      qpd::GemmArgs ga;
-      ga.thetaJ = (const float*)(ws + w.thetaJ); ga.W = (const float*)(ws + w.dW);
-      ga.phi = (float2*)(ws + w.dphi); ga.n = n; ga.nv = set == 0 ? 4 : 1;
-      ga.npts = npts[set]; ga.pt_base = base; ga.status = (int32_t*)(ws + w.status);
-      const int64_t ppt = qpd::TM / ga.nv;
-      const int64_t ntiles = (npts[set] + ppt - 1) / ppt;
-      const int gblocks = (int)(ntiles < pl->sm_count ? ntiles : pl->sm_count);
-      qpd::dense_row_gemm_kernel<0><<<gblocks, 128, qpd::gemm_smem_bytes(n, 0), s>>>(ga);
-      launches += 1;
+  if (fused) {
+    // forward contraction with the pointwise stage as its epilogue (states stay on chip)
+    qpd::FusedArgs fa;
+    fa.thetaJ = (const float*)(ws + w.thetaJ); fa.W16 = (const float*)(ws + w.dW16);
+    fa.lam = (float2*)(ws + w.dphi); fa.head = d_params + pl->head_off;
+    fa.n = n; fa.m = pl->c.n_readout;
+    for (int i = 0; i < 3; ++i) { fa.pts[i] = pts[i]; fa.npts[i] = npts[i]; fa.pt_base[i] = base; base += npts[i]; }
+    fa.tile_end[0] = (npts[0] + 31) / 32;
+    fa.tile_end[1] = fa.tile_end[0] + (npts[1] + qpd::TM - 1) / qpd::TM;
+    fa.tile_end[2] = fa.tile_end[1] + (npts[2] + qpd::TM - 1) / qpd::TM;
+    fill_problem(pl, fa.pb);
+    fa.counts = (const int32_t*)(ws + w.status) + 1;
+    fa.blk_loss = (double*)(ws + w.blk_loss); fa.blk_grad = (float*)(ws + w.blk_grad);
+    fa.loss_stride = QP_NLP + pl->p.energy_nt;
+    fa.grad_stride = 3 * n * L + 3 * pl->c.n_readout + 3;
+    fa.nE = 3 * n * L;
+    fa.nblk = pl->blocks_grad;
+    fa.status = (int32_t*)(ws + w.status);
+    const int64_t ftiles = fa.tile_end[2];
+    const int fblocks = (int)(ftiles < pl->sm_count ? (ftiles > 0 ? ftiles : 1) : pl->sm_count);
+    qpd::dense_fused_fwd_kernel<<<fblocks, qpd::F_THREADS, qpd::fused_smem(n, pl->p.energy_nt).total, s>>>(fa);
+    launches += 1;
+  } else {
+    for (int set = 0; set < 3; ++set) {
+      if (npts[set] > 0) {
+        qpd::GemmArgs ga;
+        ga.thetaJ = (const float*)(ws + w.thetaJ); ga.W = (const float*)(ws + w.dW);
+        ga.phi = (float2*)(ws + w.dphi); ga.n = n; ga.nv = set == 0 ? 4 : 1;
+        ga.npts = npts[set]; ga.pt_base = base; ga.status = (int32_t*)(ws + w.status);
+        const int64_t ppt = qpd::TM / ga.nv;
+        const int64_t ntiles = (npts[set] + ppt - 1) / ppt;
+        const int gblocks = (int)(ntiles < pl->sm_count ? ntiles : pl->sm_count);
+        qpd::dense_row_gemm_kernel<0><<<gblocks, 128, qpd::gemm_smem_bytes(n, 0), s>>>(ga);
+        launches += 1;
+      }
+      base += npts[set];
     }
-    base += npts[set];
+    qpd::PointArgs pa;
+    pa.phi = (float2*)(ws + w.dphi); pa.head = d_params + pl->head_off; pa.n = n; pa.m = pl->c.n_readout;
+    base = 0;
+    for (int i = 0; i < 3; ++i) { pa.pts[i] = pts[i]; pa.npts[i] = npts[i]; pa.pt_base[i] = base; base += npts[i]; }
+    fill_problem(pl, pa.pb);
+    pa.counts = (const int32_t*)(ws + w.status) + 1;
+    pa.blk_loss = (double*)(ws + w.blk_loss); pa.blk_grad = (float*)(ws + w.blk_grad);
+    pa.loss_stride = QP_NLP + pl->p.energy_nt;
+    pa.grad_stride = 3 * n * L + 3 * pl->c.n_readout + 3;
+    pa.nE = 3 * n * L;
+    const int psmem = ((QP_NLP + pl->p.energy_nt) * 8 + 15) / 16 * 16 + (3 * pl->c.n_readout + 3) * 4;
+    qpd::dense_point_kernel<<<pl->blocks_grad, 256, psmem, s>>>(pa);
+    launches += 1;
   }
-  qpd::PointArgs pa;
-  pa.phi = (float2*)(ws + w.dphi); pa.head = d_params + pl->head_off; pa.n = n; pa.m = pl->c.n_readout;
-  base = 0;
-  for (int i = 0; i < 3; ++i) { pa.pts[i] = pts[i]; pa.npts[i] = npts[i]; pa.pt_base[i] = base; base += npts[i]; }
-  fill_problem(pl, pa.pb);
-  pa.counts = (const int32_t*)(ws + w.status) + 1;
-  pa.blk_loss = (double*)(ws + w.blk_loss); pa.blk_grad = (float*)(ws + w.blk_grad);
-  pa.loss_stride = QP_NLP + pl->p.energy_nt;
-  pa.grad_stride = 3 * n * L + 3 * pl->c.n_readout + 3;
-  pa.nE = 3 * n * L;
-  const int psmem = ((QP_NLP + pl->p.energy_nt) * 8 + 15) / 16 * 16 + (3 * pl->c.n_readout + 3) * 4;
-  qpd::dense_point_kernel<<<pl->blocks_grad, 256, psmem, s>>>(pa);
-  launches += 1;
   qpd::WgArgs wa;
   wa.thetaJ = (const float*)(ws + w.thetaJ); wa.lam = (const float2*)(ws + w.dphi);
   wa.part = (float*)(ws + w.dpart); wa.n = n;
@@ -545,6 +582,7 @@ qp_status qp_forward(qp_plan* pl, const float* d_params, const float* d_pts, int
     qpd::BuildArgs ba;
     ba.params = d_params; ba.circ_off = pl->circ_off; ba.n = n; ba.L = pl->c.n_layers;
     ba.ansatz = pl->c.ansatz; ba.enc = pl->c.enc; ba.W = (float*)(ws + w.dW); ba.U = nullptr;
+    ba.W16 = nullptr;
     qpd::dense_build_kernel<<<dim, 256, dim * 16, s>>>(ba);
     qpd::GemmArgs ga;
     ga.thetaJ = (const float*)(ws + w.thetaJ); ga.W = (const float*)(ws + w.dW);

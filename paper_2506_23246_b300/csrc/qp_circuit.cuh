@@ -114,17 +114,24 @@ __device__ __forceinline__ float slot_sum(float v) {
 // Loss terms of one point and their cotangents g = dL/d(Ez,Hx,Hy), gD = dL/d(d field_c/d v_d):
 // collocation points carry the residuals of Eqs. 8-10 (1/eps pointwise in the dielectric case,
 // Eq. 13 splits res1 by set) and the squared Poynting residual of Eq. 23; IC points the misfit
-// of Eq. 17 against the Gaussian pulse of Eq. 14; BC points Ez^2 (PEC). Sums go to the FP64
-// partials `loss` (only when `acc`), the energy slices of Eq. 31 after QP_NLP.
-__device__ __forceinline__ void point_loss(const QPProblemDev& pb, int set, int64_t pt, int64_t npt,
-                                           const int32_t* counts, float x, float y,
-                                           const float (&f)[3], const float (&D)[3][3], bool active,
-                                           bool acc, double* loss, float (&g)[3], float (&gD)[3][3]) {
+// of Eq. 17 against the Gaussian pulse of Eq. 14; BC points Ez^2 (PEC). The point's
+// contributions to the QP_NLP FP64 partial sums go to `lt` (zero where the point adds
+// nothing), its energy-slice term of Eq. 31 to `ev` with slice index `slice` (-1: none).
+__device__ __forceinline__ void point_loss_terms(const QPProblemDev& pb, int set, int64_t pt, int64_t npt,
+                                                 const int32_t* counts, float x, float y,
+                                                 const float (&f)[3], const float (&D)[3][3], bool active,
+                                                 double (&lt)[QP_NLP], int& slice, double& ev,
+                                                 float (&g)[3], float (&gD)[3][3]) {
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
     g[c] = 0.f;
     gD[c][0] = gD[c][1] = gD[c][2] = 0.f;
   }
+#pragma unroll
+  for (int i = 0; i < QP_NLP; ++i) lt[i] = 0.0;
+  slice = -1;
+  ev = 0.0;
+  if (!active) return;
   if (set == 0) {
     float eps = 1.f;
     bool diel = false;
@@ -147,48 +154,64 @@ __device__ __forceinline__ void point_loss(const QPProblemDev& pb, int set, int6
       const float nd = (float)counts[0];
       N1 = diel ? nd : N - nd;
     }
-    if (active) {
-      const float k1 = 2.f * res1 / N1, k2 = 2.f * res2 / N, k3 = 2.f * res3 / N;
-      const float kE = 2.f * pb.w_energy * e / N;
-      g[0] = kE * (eps * D[0][2] - D[2][0] + D[1][1]);
-      g[1] = kE * (D[1][2] + D[0][1]);
-      g[2] = kE * (D[2][2] - D[0][0]);
-      gD[0][0] = -k3 - kE * f[2];
-      gD[0][1] = k2 + kE * f[1];
-      gD[0][2] = k1 + kE * eps * f[0];
-      gD[1][1] = k1 * ie + kE * f[0];
-      gD[1][2] = k2 + kE * f[1];
-      gD[2][0] = -k1 * ie - kE * f[0];
-      gD[2][2] = k3 + kE * f[2];
-      if (acc) {
-        atomicAdd(&loss[diel ? 1 : 0], (double)res1 * (double)res1);
-        atomicAdd(&loss[2], (double)res2 * (double)res2);
-        atomicAdd(&loss[3], (double)res3 * (double)res3);
-        atomicAdd(&loss[4], (double)e * (double)e);
-        if (pb.energy_nt > 0 && pb.energy_slice > 0) {
-          const int64_t k = pt / pb.energy_slice;
-          if (k < pb.energy_nt)
-            atomicAdd(&loss[QP_NLP + k],
-                      0.5 * ((double)eps * f[0] * f[0] + (double)f[1] * f[1] + (double)f[2] * f[2]));
-        }
+    const float k1 = 2.f * res1 / N1, k2 = 2.f * res2 / N, k3 = 2.f * res3 / N;
+    const float kE = 2.f * pb.w_energy * e / N;
+    g[0] = kE * (eps * D[0][2] - D[2][0] + D[1][1]);
+    g[1] = kE * (D[1][2] + D[0][1]);
+    g[2] = kE * (D[2][2] - D[0][0]);
+    gD[0][0] = -k3 - kE * f[2];
+    gD[0][1] = k2 + kE * f[1];
+    gD[0][2] = k1 + kE * eps * f[0];
+    gD[1][1] = k1 * ie + kE * f[0];
+    gD[1][2] = k2 + kE * f[1];
+    gD[2][0] = -k1 * ie - kE * f[0];
+    gD[2][2] = k3 + kE * f[2];
+    const double r1sq = (double)res1 * (double)res1;
+    lt[0] = diel ? 0.0 : r1sq;
+    lt[1] = diel ? r1sq : 0.0;
+    lt[2] = (double)res2 * (double)res2;
+    lt[3] = (double)res3 * (double)res3;
+    lt[4] = (double)e * (double)e;
+    if (pb.energy_nt > 0 && pb.energy_slice > 0) {
+      const int64_t k = pt / pb.energy_slice;
+      if (k < pb.energy_nt) {
+        slice = (int)k;
+        ev = 0.5 * ((double)eps * f[0] * f[0] + (double)f[1] * f[1] + (double)f[2] * f[2]);
       }
     }
   } else if (set == 1) {
     const float dx = x - pb.ic_x0, dy = y - pb.ic_y0;
     const float e0 = expf(-(dx * dx + dy * dy) / (2.f * pb.ic_sigma * pb.ic_sigma));
-    if (active) {
-      const float k = 2.f * pb.w_ic / (float)npt;
-      g[0] = k * (f[0] - e0);
-      g[1] = k * f[1];
-      g[2] = k * f[2];
-      if (acc)
-        atomicAdd(&loss[5], (double)(f[0] - e0) * (f[0] - e0) + (double)f[1] * f[1] +
-                                (double)f[2] * f[2]);
-    }
+    const float k = 2.f * pb.w_ic / (float)npt;
+    g[0] = k * (f[0] - e0);
+    g[1] = k * f[1];
+    g[2] = k * f[2];
+    lt[5] = (double)(f[0] - e0) * (f[0] - e0) + (double)f[1] * f[1] + (double)f[2] * f[2];
   } else {
-    if (active) {
-      g[0] = 2.f * pb.w_bc * f[0] / (float)npt;
-      if (acc) atomicAdd(&loss[6], (double)f[0] * f[0]);
+    g[0] = 2.f * pb.w_bc * f[0] / (float)npt;
+    lt[6] = (double)f[0] * f[0];
+  }
+}
+
+// point_loss_terms with the partial sums added to `loss` (shared FP64 partials, only when `acc`).
+__device__ __forceinline__ void point_loss(const QPProblemDev& pb, int set, int64_t pt, int64_t npt,
+                                           const int32_t* counts, float x, float y,
+                                           const float (&f)[3], const float (&D)[3][3], bool active,
+                                           bool acc, double* loss, float (&g)[3], float (&gD)[3][3]) {
+  double lt[QP_NLP], ev;
+  int slice;
+  point_loss_terms(pb, set, pt, npt, counts, x, y, f, D, active, lt, slice, ev, g, gD);
+  if (active && acc) {
+    if (set == 0) {
+      atomicAdd(&loss[lt[1] != 0.0 ? 1 : 0], lt[0] + lt[1]);
+      atomicAdd(&loss[2], lt[2]);
+      atomicAdd(&loss[3], lt[3]);
+      atomicAdd(&loss[4], lt[4]);
+      if (slice >= 0) atomicAdd(&loss[QP_NLP + slice], ev);
+    } else if (set == 1) {
+      atomicAdd(&loss[5], lt[5]);
+    } else {
+      atomicAdd(&loss[6], lt[6]);
     }
   }
 }
