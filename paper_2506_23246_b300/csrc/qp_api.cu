@@ -97,7 +97,7 @@ WsLayout ws_layout(const qp_plan* pl, int64_t P) {
   w.dpart = o; o = al256(o + (size_t)nch * dim * 2 * dim * 4);
   const bool dm = dg && pl->c.premap == QP_PREMAP_RFF_MLP;
   w.dWT = o; o = al256(o + (dm ? 2 * (2 * dim) * dim * 4 : 0));
-  w.dmu = o; o = al256(o + (dm ? (size_t)P * 4 * dim * 4 : 0));
+  w.dmu = o; o = al256(o + (dm && !fused_path(pl) ? (size_t)P * 4 * dim * 4 : 0));
   w.dW16 = o; o = al256(o + (dg && fused_path(pl) ? 2 * (2 * dim) * dim * 4 : 0));
   w.total = o;
   return w;
@@ -267,8 +267,10 @@ qp_status qp_plan_create(const qp_circuit* circuit, const qp_problem* problem, i
         cudaFuncSetAttribute((void*)qpd::dense_sweep_right_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (1 << n) * 16 * 8) != cudaSuccess ||
         (fused_path(pl) &&
-         cudaFuncSetAttribute((void*)qpd::dense_fused_fwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              qpd::fused_smem(n, pl->p.energy_nt).total) != cudaSuccess)) {
+         (cudaFuncSetAttribute((void*)qpd::dense_fused_fwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               qpd::fused_smem(n, pl->p.energy_nt).total) != cudaSuccess ||
+          cudaFuncSetAttribute((void*)qpd::dense_mu_embed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               qpd::mu_smem_bytes(n)) != cudaSuccess))) {
       cudaGetLastError();
       delete pl;
       return QP_ERR_CUDA;
@@ -528,32 +530,49 @@ static qp_status dense_loss_grad(qp_plan* pl, const float* d_params, const float
   }
   launches += 2;
   if (mlp) {
-    // back-projection mu = Re(U'^H lambda) per (point, vector) row, then the embedding
-    // gradients per point, then the premap backward shared with the SIMT path
-    base = 0;
-    for (int set = 0; set < 3; ++set) {
-      if (npts[set] > 0) {
-        qpd::GemmArgs ga;
-        ga.thetaJ = (const float*)(ws + w.thetaJ); ga.W = (const float*)(ws + w.dWT);
-        ga.phi = nullptr; ga.lam = (const float*)(ws + w.dphi); ga.mu = (float*)(ws + w.dmu);
-        ga.n = n; ga.nv = set == 0 ? 4 : 1;
-        ga.npts = npts[set]; ga.pt_base = base; ga.status = (int32_t*)(ws + w.status);
-        const int64_t ppt = qpd::TM / ga.nv;
-        const int64_t ntiles = (npts[set] + ppt - 1) / ppt;
-        const int gblocks = (int)(ntiles < pl->sm_count ? ntiles : pl->sm_count);
-        qpd::dense_row_gemm_kernel<1><<<gblocks, 128, qpd::gemm_smem_bytes(n, 1), s>>>(ga);
-        launches += 1;
+    if (fused) {
+      // mu rows on the tensor cores with the embedding gradients as the epilogue
+      qpd::MuArgs ma;
+      ma.thetaJ = (const float*)(ws + w.thetaJ); ma.WT = (const float*)(ws + w.dWT);
+      ma.lam = (const float*)(ws + w.dphi); ma.dthetaJ = (float*)(ws + w.dthetaJ); ma.n = n;
+      base = 0;
+      for (int i = 0; i < 3; ++i) { ma.npts[i] = npts[i]; ma.pt_base[i] = base; base += npts[i]; }
+      ma.tile_end[0] = (npts[0] + 31) / 32;
+      ma.tile_end[1] = ma.tile_end[0] + (npts[1] + qpd::TM - 1) / qpd::TM;
+      ma.tile_end[2] = ma.tile_end[1] + (npts[2] + qpd::TM - 1) / qpd::TM;
+      ma.status = (int32_t*)(ws + w.status);
+      const int64_t mt = ma.tile_end[2];
+      const int mblocks = (int)(mt < pl->sm_count ? (mt > 0 ? mt : 1) : pl->sm_count);
+      qpd::dense_mu_embed_kernel<<<mblocks, 128, qpd::mu_smem_bytes(n), s>>>(ma);
+      launches += 1;
+    } else {
+      // back-projection mu = Re(U'^H lambda) per (point, vector) row, then the embedding
+      // gradients per point, then the premap backward shared with the SIMT path
+      base = 0;
+      for (int set = 0; set < 3; ++set) {
+        if (npts[set] > 0) {
+          qpd::GemmArgs ga;
+          ga.thetaJ = (const float*)(ws + w.thetaJ); ga.W = (const float*)(ws + w.dWT);
+          ga.phi = nullptr; ga.lam = (const float*)(ws + w.dphi); ga.mu = (float*)(ws + w.dmu);
+          ga.n = n; ga.nv = set == 0 ? 4 : 1;
+          ga.npts = npts[set]; ga.pt_base = base; ga.status = (int32_t*)(ws + w.status);
+          const int64_t ppt = qpd::TM / ga.nv;
+          const int64_t ntiles = (npts[set] + ppt - 1) / ppt;
+          const int gblocks = (int)(ntiles < pl->sm_count ? ntiles : pl->sm_count);
+          qpd::dense_row_gemm_kernel<1><<<gblocks, 128, qpd::gemm_smem_bytes(n, 1), s>>>(ga);
+          launches += 1;
+        }
+        base += npts[set];
       }
-      base += npts[set];
+      qpd::EmbedArgs ea;
+      ea.thetaJ = (const float*)(ws + w.thetaJ); ea.mu = (const float*)(ws + w.dmu);
+      ea.dthetaJ = (float*)(ws + w.dthetaJ); ea.n = n;
+      base = 0;
+      for (int i = 0; i < 3; ++i) { ea.npts[i] = npts[i]; ea.pt_base[i] = base; base += npts[i]; }
+      const int64_t eb = (P + 7) / 8;
+      qpd::dense_embed_grad_kernel<<<(unsigned)(eb < 8192 ? eb : 8192), 256, 0, s>>>(ea);
+      launches += 1;
     }
-    qpd::EmbedArgs ea;
-    ea.thetaJ = (const float*)(ws + w.thetaJ); ea.mu = (const float*)(ws + w.dmu);
-    ea.dthetaJ = (float*)(ws + w.dthetaJ); ea.n = n;
-    base = 0;
-    for (int i = 0; i < 3; ++i) { ea.npts[i] = npts[i]; ea.pt_base[i] = base; base += npts[i]; }
-    const int64_t eb = (P + 7) / 8;
-    qpd::dense_embed_grad_kernel<<<(unsigned)(eb < 8192 ? eb : 8192), 256, 0, s>>>(ea);
-    launches += 1;
     st = launch_premap_bwd(pl, w, d_params, pts, npts, s);
     if (st != QP_OK) return st;
     launches += 2;
