@@ -306,7 +306,7 @@ def run_native(a):
         roof = {"bound": "tensor", "kernel": "dense_wgrad_gemm_kernel (3xTF32)",
                 "peak_basis": "measured bf16 %.0f TFLOP/s x 0.5 (nominal TF32/BF16 dense ratio) / 3 "
                               "(three TF32 products per 3xTF32 term)" % bf16,
-                "traffic": profiled_traffic("dense_wgrad_c3_8q6l.md", "qp_dense.cuh")}
+                "traffic": profiled_traffic("dense_wgrad_c3_8q6l.md", "qp_wgrad.cuh")}
     achieved = flops / (kms / 1000.0) / 1e12
 
     # end to end through the public call: pinned host inputs in, loss + gradient out

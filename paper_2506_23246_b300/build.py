@@ -12,7 +12,8 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 LIB = os.path.join(HERE, "libqpinn.so")
 SOURCES = ["qp_api.cu", "qp_sched.cpp", "qp_selftest.cpp"]
-HEADERS = ["qp_common.h", "qp_circuit.cuh", "qp_aux.cuh", "qp_tc.cuh", "qp_dense.cuh"]
+HEADERS = ["qp_common.h", "qp_circuit.cuh", "qp_aux.cuh", "qp_tc.cuh", "qp_dense.cuh", "qp_fused.cuh",
+           "qp_mu.cuh", "qp_wgrad.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -11,6 +11,9 @@
 #include "qp_circuit.cuh"
 #include "qp_common.h"
 #include "qp_dense.cuh"
+#include "qp_fused.cuh"
+#include "qp_mu.cuh"
+#include "qp_wgrad.cuh"
 
 extern "C" int qp_build_sched(int n, int L, int ansatz, QPSched* out);
 

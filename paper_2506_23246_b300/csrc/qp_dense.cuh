@@ -612,704 +612,6 @@ __global__ void dense_point_kernel(PointArgs a) {
   for (int i = threadIdx.x; i < 3 * m + 3; i += blockDim.x) bg[a.nE + i] = hacc[i];
 }
 
-// ------------------------------------------------------------------------- fused forward + costates
-// For n <= 8 a 128-row tile's whole output row (2^(n+1) <= 512 FP32 columns) stays in tensor
-// memory, so the pointwise stage runs as the epilogue of the forward contraction and the
-// states never reach HBM: readout z_i = <phi|Z_i|phi>, d z_i/dv_d = 2 Re<phi_d|Z_i|phi> (the
-// readout of the forward-mode tangents), the linear head, the loss terms and cotangents of
-// the point, and the costates
-//   lambda_0 = O phi_0 + sum_d O_d phi_d,  lambda_d = O_d phi_0,  O = sum_i zbar_i Z_i
-// (Z_i diagonal: O is a per-amplitude sign sum), written in place of the states.
-// Tile rows: collocation tiles hold 32 points x 4 vectors (row = vector * 32 + point, so warp
-// w and w + 4 own vector w % 4, the two halves of the columns); IC/BC tiles 128 points.
-constexpr int F_THREADS = 256;
-constexpr int F_MAXH = 5;       // embedding qubits above the 3 lowest index bits (n <= 8)
-
-
-struct FusedArgs {
-  const float* thetaJ;     // [P][n] float4 (theta, dtheta/dx, dtheta/dy, dtheta/dt)
-  const float* W16;        // [dim / FKC][nc][2 (hi, lo)][256 x FKC] operand blocks of W
-  float2* lam;             // [P][4][2^n] costates (output)
-  const float* head;       // W[3][m], b[3]
-  int32_t n, m;
-  const float* pts[3];
-  int64_t npts[3], pt_base[3];
-  int64_t tile_end[3];     // cumulative tiles: collocation tiles of 32 points, IC/BC of 128
-  QPProblemDev pb;
-  const int32_t* counts;
-  double* blk_loss;
-  float* blk_grad;
-  int32_t loss_stride, grad_stride, nE, nblk;
-  int32_t* status;
-};
-
-struct FusedSmem {
-  int a_bytes, w_bytes, stage, x0, tb, zp, zb, hw, sloss, hsum, bars, total;
-};
-__host__ __device__ inline FusedSmem fused_smem(int n, int nt) {
-  FusedSmem f;
-  const int nc = (2 << n) / 256;
-  f.a_bytes = TM * FKC * 4;
-  f.w_bytes = nc * 2 * 256 * FKC * 4;
-  f.stage = 2 * f.a_bytes + f.w_bytes;
-  int o = 2 * f.stage;
-  f.x0 = o; o += 2 * 32 * 32 * 4;                 // phi_0 chunk per column half
-  f.tb = o; o += 2 * 3 * 32 * 32 * 4;             // O_d phi_d chunks per column half
-  f.zp = o; o += 2 * TM * QP_MAXQ * 4;            // readout partials [half][row][i]
-  f.zb = o; o += TM * QP_MAXQ * 4;                // sign-sum coefficients [row][i]
-  f.hw = o; o += (3 * QP_MAXQ + 3) * 4 + 4;       // head weights
-  o = (o + 15) / 16 * 16;
-  f.sloss = o; o += (QP_NLP + nt) * 8;
-  o = (o + 15) / 16 * 16;
-  f.hsum = o; o += (3 * QP_MAXQ + 3) * 4 + 4;
-  o = (o + 15) / 16 * 16;
-  f.bars = o; o += 64;                            // w_full[2], mma_done[2], tensor-memory slot
-  f.total = o;
-  return f;
-}
-
-__device__ __forceinline__ void named_bar(int id) {
-  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(128) : "memory");
-}
-__device__ __forceinline__ double warp_sum_d(double v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
-__device__ __forceinline__ float warp_sum_f(float v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
-
-__global__ void __launch_bounds__(F_THREADS, 1) dense_fused_fwd_kernel(FusedArgs a) {
-  extern __shared__ __align__(1024) unsigned char sm[];
-  const int n = a.n, dim = 1 << n, m = a.m, nt = a.pb.energy_nt;
-  const int nc = (2 << n) / 256;
-  const FusedSmem L = fused_smem(n, nt);
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int ws = warp & 3, hh = warp >> 2;        // tensor-memory lane group, column half
-  uint64_t* bars = reinterpret_cast<uint64_t*>(sm + L.bars);  // w_full[2], mma_done[2]
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + L.bars + 32);
-  float4* X0 = reinterpret_cast<float4*>(sm + L.x0) + hh * 256;
-  float4* TB = reinterpret_cast<float4*>(sm + L.tb) + hh * 768;
-  float* zp = reinterpret_cast<float*>(sm + L.zp);
-  float* zbs = reinterpret_cast<float*>(sm + L.zb);
-  float* hw = reinterpret_cast<float*>(sm + L.hw);
-  double* sloss = reinterpret_cast<double*>(sm + L.sloss);
-  float* hsum = reinterpret_cast<float*>(sm + L.hsum);
-  const uint32_t tcols = 2u << n;
-  if (warp == 0) qptc::tmem_alloc(tslot, tcols);
-  if (tid == 0) {
-    for (int i = 0; i < 4; ++i) qptc::mbar_init(&bars[i], 1);
-  }
-  for (int i = tid; i < 3 * m + 3; i += blockDim.x) { hw[i] = a.head[i]; hsum[i] = 0.f; }
-  for (int i = tid; i < QP_NLP + nt; i += blockDim.x) sloss[i] = 0.0;
-  qptc::fence_before();
-  __syncthreads();
-  qptc::fence_after();
-  const uint32_t tmem = *tslot;
-  const uint32_t id = qptc::idesc(2, TM, 256);
-  const int nkc = dim / FKC;
-  const int arow = tid & (TM - 1), khalf = tid >> 7;
-  const int r = ws * 32 + lane;                   // tile row read from tensor memory
-  const int half_cols = dim;                      // 2 dim columns split between two halves
-  // per-thread running sums over all tiles (point threads only)
-  double lacc[QP_NLP];
-#pragma unroll
-  for (int i = 0; i < QP_NLP; ++i) lacc[i] = 0.0;
-  float hg[3][QP_MAXQ], hb[3];
-#pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    hb[c] = 0.f;
-#pragma unroll
-    for (int i = 0; i < QP_MAXQ; ++i) hg[c][i] = 0.f;
-  }
-  bool ok = true;
-  uint32_t it = 0;
-  int64_t last_copy = -1, last_commit = -1;
-  const int64_t T2 = a.tile_end[2];
-  for (int64_t tile = blockIdx.x; tile < T2 && ok; tile += gridDim.x) {
-    int set;
-    int64_t p0;
-    if (tile < a.tile_end[0]) { set = 0; p0 = tile * 32; }
-    else if (tile < a.tile_end[1]) { set = 1; p0 = (tile - a.tile_end[0]) * TM; }
-    else { set = 2; p0 = (tile - a.tile_end[1]) * TM; }
-    const bool nv4 = set == 0;
-    const int64_t np = a.npts[set], base = a.pt_base[set];
-    // ---- embedding tables of the A row generated by this thread
-    const int s_a = nv4 ? arow >> 5 : 0;
-    const int64_t pa = p0 + (nv4 ? (arow & 31) : arow);
-    const int64_t pac = pa < np ? pa : np - 1;
-    const float4* tj = reinterpret_cast<const float4*>(a.thetaJ) + (base + pac) * n;
-    float Lo[8], Lod[8];
-#pragma unroll
-    for (int t = 0; t < 8; ++t) { Lo[t] = 1.f; Lod[t] = 0.f; }
-#pragma unroll
-    for (int b = 0; b < 3; ++b) {
-      const float4 tq = __ldg(tj + (n - 1 - b));
-      float sn, cs;
-      sincosf(0.5f * tq.x, &sn, &cs);
-      const float J = s_a == 0 ? 0.f : (s_a == 1 ? tq.y : (s_a == 2 ? tq.z : tq.w));
-#pragma unroll
-      for (int t = 0; t < 8; ++t) {
-        const bool bit = (t >> b) & 1;
-        const float f = bit ? sn : cs, d = bit ? 0.5f * cs : -0.5f * sn;
-        Lod[t] = Lod[t] * f + Lo[t] * d * J;
-        Lo[t] *= f;
-      }
-    }
-    float hc[F_MAXH], hs[F_MAXH], hj[F_MAXH];
-#pragma unroll
-    for (int q = 0; q < F_MAXH; ++q) {
-      hc[q] = 1.f; hs[q] = 0.f; hj[q] = 0.f;
-      if (q < n - 3) {
-        const float4 tq = __ldg(tj + q);
-        sincosf(0.5f * tq.x, &hs[q], &hc[q]);
-        hj[q] = s_a == 0 ? 0.f : (s_a == 1 ? tq.y : (s_a == 2 ? tq.z : tq.w));
-      }
-    }
-    // ---- forward contraction: TMEM[row][2j + re/im] = sum_k R[row][k] W[2j + re/im][k]
-    for (int kc = 0; kc < nkc && ok; ++kc, ++it) {
-      const uint32_t st = it & 1;
-      unsigned char* sA = sm + st * L.stage;
-      unsigned char* sW = sA + 2 * L.a_bytes;
-      bool w_ok = true;
-      if (it >= 2) w_ok = qptc::mbar_wait(&bars[2 + st], ((it - 2) >> 1) & 1);
-      ok = __syncthreads_and(w_ok);
-      if (!ok) break;
-      if (tid == 0) {
-        qptc::mbar_arrive_expect_tx(&bars[st], L.w_bytes);
-        qptc::bulk_g2s(sW, a.W16 + (int64_t)kc * (L.w_bytes / 4), L.w_bytes, &bars[st]);
-        last_copy = it;
-      }
-      // basis indices k = kc * 16 + khalf * 8 + t: bits 0-2 from the tables, the rest from H
-      const int hbits = kc * 2 + khalf;
-      float H = 1.f, Hd = 0.f;
-#pragma unroll
-      for (int q = 0; q < F_MAXH; ++q) {
-        if (q < n - 3) {
-          const bool bit = (hbits >> (n - 4 - q)) & 1;
-          const float f = bit ? hs[q] : hc[q], d = bit ? 0.5f * hc[q] : -0.5f * hs[q];
-          Hd = Hd * f + H * d * hj[q];
-          H *= f;
-        }
-      }
-      float* Ahi = reinterpret_cast<float*>(sA);
-      float* Alo = reinterpret_cast<float*>(sA + L.a_bytes);
-#pragma unroll
-      for (int g4 = 0; g4 < 2; ++g4) {
-        float4 h4, l4;
-        float* hv = &h4.x;
-        float* lv = &l4.x;
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          const int t = g4 * 4 + e;
-          const float v = s_a == 0 ? H * Lo[t] : Hd * Lo[t] + H * Lod[t];
-          qptc::split_tf32(v, hv[e], lv[e]);
-        }
-        const uint32_t off = core_off16(arow, khalf * 8 + g4 * 4) / 4;
-        *reinterpret_cast<float4*>(Ahi + off) = h4;
-        *reinterpret_cast<float4*>(Alo + off) = l4;
-      }
-      qptc::fence_proxy_async();
-      __syncthreads();
-      bool m_ok = true;
-      if (tid == 0) {
-        m_ok = qptc::mbar_wait(&bars[st], (it >> 1) & 1);
-        if (m_ok) {
-          qptc::fence_after();
-          const uint32_t sa = qptc::smem_u32(sA), sw = qptc::smem_u32(sW);
-          const uint32_t wblk = 256 * FKC * 4;
-#pragma unroll
-          for (int ks = 0; ks < FKC / 8; ++ks) {
-            const uint64_t ah = qptc::desc_kmajor(sa + ks * 256, 128, (FKC / 4) * 128);
-            const uint64_t al = qptc::desc_kmajor(sa + L.a_bytes + ks * 256, 128, (FKC / 4) * 128);
-            for (int c = 0; c < nc; ++c) {
-              const uint64_t wh = qptc::desc_kmajor(sw + c * 2 * wblk + ks * 256, 128, (FKC / 4) * 128);
-              const uint64_t wl = qptc::desc_kmajor(sw + c * 2 * wblk + wblk + ks * 256, 128, (FKC / 4) * 128);
-              const uint32_t dt = tmem + c * 256;
-              qptc::mma_tf32(dt, ah, wh, id, (kc > 0 || ks > 0) ? 1u : 0u);
-              qptc::mma_tf32(dt, ah, wl, id, 1u);
-              qptc::mma_tf32(dt, al, wh, id, 1u);
-            }
-          }
-          qptc::commit(&bars[2 + st]);
-          last_commit = it;
-        }
-      }
-      ok = __syncthreads_and(m_ok);
-    }
-    if (!ok) break;
-    ok = __syncthreads_and(qptc::mbar_wait(&bars[2 + ((it - 1) & 1)], ((it - 1) >> 1) & 1));
-    if (!ok) break;
-    qptc::fence_after();
-    // ---- pass 1: readout partial sums over this thread's half of the columns
-    float acc[QP_MAXQ];
-#pragma unroll
-    for (int i = 0; i < QP_MAXQ; ++i) acc[i] = 0.f;
-    for (int cc = 0; cc < half_cols; cc += 32) {
-      const int col = hh * half_cols + cc;
-      float v[32];
-      qptc::tmem_ld32(tmem + ((uint32_t)(ws * 32) << 16) + col, v);
-      float y[16];
-      if (nv4) {
-        if (ws == 0) {
-#pragma unroll
-          for (int e = 0; e < 8; ++e)
-            X0[lane * 8 + (e ^ (lane & 7))] = make_float4(v[4 * e], v[4 * e + 1], v[4 * e + 2], v[4 * e + 3]);
-#pragma unroll
-          for (int e = 0; e < 16; ++e) y[e] = v[2 * e] * v[2 * e] + v[2 * e + 1] * v[2 * e + 1];
-        }
-        named_bar(1 + hh);
-        if (ws != 0) {
-#pragma unroll
-          for (int e = 0; e < 8; ++e) {
-            const float4 x = X0[lane * 8 + (e ^ (lane & 7))];
-            y[2 * e] = 2.f * (v[4 * e] * x.x + v[4 * e + 1] * x.y);
-            y[2 * e + 1] = 2.f * (v[4 * e + 2] * x.z + v[4 * e + 3] * x.w);
-          }
-        }
-        named_bar(1 + hh);
-      } else {
-#pragma unroll
-        for (int e = 0; e < 16; ++e) y[e] = v[2 * e] * v[2 * e] + v[2 * e + 1] * v[2 * e + 1];
-      }
-      // total and the four single-bit sign sums over the 16 amplitudes of the chunk
-      float T = 0.f, S[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-      for (int e = 0; e < 16; ++e) {
-        T += y[e];
-#pragma unroll
-        for (int b = 0; b < 4; ++b) S[b] += ((e >> b) & 1) ? -y[e] : y[e];
-      }
-      const int j0 = col >> 1;
-#pragma unroll
-      for (int i = 0; i < QP_MAXQ; ++i) {
-        if (i < m) {
-          const int pbit = n - 1 - i;
-          const float sv = pbit == 0 ? S[0] : pbit == 1 ? S[1] : pbit == 2 ? S[2] : pbit == 3 ? S[3]
-                         : (((j0 >> pbit) & 1) ? -T : T);
-          acc[i] += sv;
-        }
-      }
-    }
-#pragma unroll
-    for (int i = 0; i < QP_MAXQ; ++i)
-      if (i < m) zp[(hh * TM + r) * QP_MAXQ + i] = acc[i];
-    __syncthreads();
-    // ---- point stage: head, loss terms, cotangents, sign-sum coefficients
-    if (nv4 ? warp == 0 : warp < 4) {
-      const int r0 = nv4 ? lane : r;
-      const int64_t pp = p0 + r0;
-      const bool active = pp < np;
-      const int64_t ppc = active ? pp : np - 1;
-      float z[QP_MAXQ], dz[3][QP_MAXQ];
-#pragma unroll
-      for (int i = 0; i < QP_MAXQ; ++i) {
-        z[i] = 0.f; dz[0][i] = dz[1][i] = dz[2][i] = 0.f;
-        if (i < m) {
-          z[i] = zp[r0 * QP_MAXQ + i] + zp[(TM + r0) * QP_MAXQ + i];
-          if (nv4) {
-#pragma unroll
-            for (int d = 0; d < 3; ++d)
-              dz[d][i] = zp[((d + 1) * 32 + lane) * QP_MAXQ + i] + zp[(TM + (d + 1) * 32 + lane) * QP_MAXQ + i];
-          }
-        }
-      }
-      float f[3], D[3][3];
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        float accf = hw[3 * m + c], ad[3] = {0.f, 0.f, 0.f};
-#pragma unroll
-        for (int i = 0; i < QP_MAXQ; ++i)
-          if (i < m) {
-            const float w = hw[c * m + i];
-            accf += w * z[i];
-#pragma unroll
-            for (int d = 0; d < 3; ++d) ad[d] += w * dz[d][i];
-          }
-        f[c] = accf;
-#pragma unroll
-        for (int d = 0; d < 3; ++d) D[c][d] = ad[d];
-      }
-      const float* xp = a.pts[set] + ppc * 3;
-      float g[3], gD[3][3];
-      double lt[QP_NLP], ev;
-      int slice;
-      qpk::point_loss_terms(a.pb, set, ppc, np, a.counts, __ldg(xp), __ldg(xp + 1), f, D, active, lt, slice, ev, g, gD);
-#pragma unroll
-      for (int i = 0; i < QP_NLP; ++i) lacc[i] += lt[i];
-      // energy slices: one FP64 shared add per warp when the warp's points share a slice
-      const int s0 = __shfl_sync(0xffffffffu, slice, 0);
-      if (__all_sync(0xffffffffu, slice == s0)) {
-        const double evs = warp_sum_d(ev);
-        if (lane == 0 && s0 >= 0) atomicAdd(&sloss[QP_NLP + s0], evs);
-      } else if (slice >= 0) {
-        atomicAdd(&sloss[QP_NLP + slice], ev);
-      }
-#pragma unroll
-      for (int i = 0; i < QP_MAXQ; ++i) {
-        if (i < m) {
-          float zb = 0.f, zbd[3] = {0.f, 0.f, 0.f};
-#pragma unroll
-          for (int c = 0; c < 3; ++c) {
-            const float w = hw[c * m + i];
-            zb += w * g[c];
-#pragma unroll
-            for (int d = 0; d < 3; ++d) zbd[d] += w * gD[c][d];
-            hg[c][i] += g[c] * z[i] + gD[c][0] * dz[0][i] + gD[c][1] * dz[1][i] + gD[c][2] * dz[2][i];
-          }
-          zbs[r0 * QP_MAXQ + i] = zb;
-          if (nv4) {
-#pragma unroll
-            for (int d = 0; d < 3; ++d) zbs[((d + 1) * 32 + lane) * QP_MAXQ + i] = zbd[d];
-          }
-        }
-      }
-#pragma unroll
-      for (int c = 0; c < 3; ++c) hb[c] += g[c];
-    }
-    __syncthreads();
-    // ---- pass 2: costates of this thread's row, written over the state rows
-    {
-      float coef[QP_MAXQ], cb[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-      for (int i = 0; i < QP_MAXQ; ++i) {
-        coef[i] = i < m ? zbs[r * QP_MAXQ + i] : 0.f;
-        const int pbit = n - 1 - i;
-        if (i < m && pbit < 4) {
-          if (pbit == 0) cb[0] = coef[i];
-          else if (pbit == 1) cb[1] = coef[i];
-          else if (pbit == 2) cb[2] = coef[i];
-          else cb[3] = coef[i];
-        }
-      }
-      const float t01[4] = {cb[0] + cb[1], -cb[0] + cb[1], cb[0] - cb[1], -cb[0] - cb[1]};
-      const float t23[4] = {cb[2] + cb[3], -cb[2] + cb[3], cb[2] - cb[3], -cb[2] - cb[3]};
-      const int s_r = nv4 ? ws : 0;
-      const int64_t pr = p0 + (nv4 ? lane : r);
-      const bool act = pr < np;
-      float2* dst = a.lam + ((base + (act ? pr : 0)) * 4 + s_r) * (int64_t)dim;
-      for (int cc = 0; cc < half_cols; cc += 32) {
-        const int col = hh * half_cols + cc;
-        const int j0 = col >> 1;
-        float Bs = 0.f;
-#pragma unroll
-        for (int i = 0; i < QP_MAXQ; ++i) {
-          const int pbit = n - 1 - i;
-          if (i < m && pbit >= 4) Bs += ((j0 >> pbit) & 1) ? -coef[i] : coef[i];
-        }
-        float O[16];
-#pragma unroll
-        for (int e = 0; e < 16; ++e) O[e] = Bs + t01[e & 3] + t23[e >> 2];
-        float v[32];
-        qptc::tmem_ld32(tmem + ((uint32_t)(ws * 32) << 16) + col, v);
-        float4 outv[8];
-        if (nv4) {
-          if (ws == 0) {
-#pragma unroll
-            for (int e = 0; e < 8; ++e)
-              X0[lane * 8 + (e ^ (lane & 7))] = make_float4(v[4 * e], v[4 * e + 1], v[4 * e + 2], v[4 * e + 3]);
-          } else {
-#pragma unroll
-            for (int e = 0; e < 8; ++e)
-              TB[(ws - 1) * 256 + lane * 8 + (e ^ (lane & 7))] =
-                  make_float4(O[2 * e] * v[4 * e], O[2 * e] * v[4 * e + 1], O[2 * e + 1] * v[4 * e + 2],
-                              O[2 * e + 1] * v[4 * e + 3]);
-          }
-          named_bar(1 + hh);
-          if (ws == 0) {
-#pragma unroll
-            for (int e = 0; e < 8; ++e) {
-              const int sw = lane * 8 + (e ^ (lane & 7));
-              const float4 t1 = TB[sw], t2 = TB[256 + sw], t3 = TB[512 + sw];
-              outv[e] = make_float4(O[2 * e] * v[4 * e] + t1.x + t2.x + t3.x,
-                                    O[2 * e] * v[4 * e + 1] + t1.y + t2.y + t3.y,
-                                    O[2 * e + 1] * v[4 * e + 2] + t1.z + t2.z + t3.z,
-                                    O[2 * e + 1] * v[4 * e + 3] + t1.w + t2.w + t3.w);
-            }
-          } else {
-#pragma unroll
-            for (int e = 0; e < 8; ++e) {
-              const float4 x = X0[lane * 8 + (e ^ (lane & 7))];
-              outv[e] = make_float4(O[2 * e] * x.x, O[2 * e] * x.y, O[2 * e + 1] * x.z, O[2 * e + 1] * x.w);
-            }
-          }
-          named_bar(1 + hh);
-        } else {
-#pragma unroll
-          for (int e = 0; e < 8; ++e)
-            outv[e] = make_float4(O[2 * e] * v[4 * e], O[2 * e] * v[4 * e + 1], O[2 * e + 1] * v[4 * e + 2],
-                                  O[2 * e + 1] * v[4 * e + 3]);
-        }
-        if (act) {
-          float4* d4 = reinterpret_cast<float4*>(dst + j0);
-#pragma unroll
-          for (int e = 0; e < 8; ++e) d4[e] = outv[e];
-        }
-      }
-    }
-    qptc::fence_before();
-    __syncthreads();
-  }
-  if (!ok) {
-    if (tid == 0) {
-      atomicExch(a.status, 6);
-      // let the last bulk copy and tensor-core operations of this CTA land before exiting
-      if (last_copy >= 0) qptc::mbar_wait(&bars[last_copy & 1], ((uint32_t)last_copy >> 1) & 1);
-      if (last_commit >= 0) qptc::mbar_wait(&bars[2 + (last_commit & 1)], ((uint32_t)last_commit >> 1) & 1);
-    }
-  }
-  // ---- block partials: loss sums (FP64) and head gradients
-#pragma unroll
-  for (int i = 0; i < QP_NLP; ++i) {
-    const double v = warp_sum_d(lacc[i]);
-    if (lane == 0 && warp < 4 && v != 0.0) atomicAdd(&sloss[i], v);
-  }
-#pragma unroll
-  for (int c = 0; c < 3; ++c) {
-#pragma unroll
-    for (int i = 0; i < QP_MAXQ; ++i) {
-      if (i < m) {
-        const float v = warp_sum_f(hg[c][i]);
-        if (lane == 0 && warp < 4) atomicAdd(&hsum[c * m + i], v);
-      }
-    }
-    const float v = warp_sum_f(hb[c]);
-    if (lane == 0 && warp < 4) atomicAdd(&hsum[3 * m + c], v);
-  }
-  qptc::fence_before();
-  __syncthreads();
-  if (warp == 0) qptc::tmem_dealloc(tmem, tcols);
-  for (int b = blockIdx.x; b < a.nblk; b += gridDim.x) {
-    const bool mine = b == (int)blockIdx.x;
-    double* bl = a.blk_loss + (int64_t)b * a.loss_stride;
-    for (int i = tid; i < QP_NLP + nt; i += blockDim.x) bl[i] = mine ? sloss[i] : 0.0;
-    float* bg = a.blk_grad + (int64_t)b * a.grad_stride;
-    for (int i = tid; i < a.nE; i += blockDim.x) bg[i] = 0.f;
-    for (int i = tid; i < 3 * m + 3; i += blockDim.x) bg[a.nE + i] = mine ? hsum[i] : 0.f;
-  }
-}
-
-// ------------------------------------------------------------------------- weight-gradient GEMM
-// G_part[chunk][k][o] = sum over the chunk's (point, vector) rows of R_s[k] * Lambda_s[o]:
-// M = 128 basis indices k, N = 256 costate components o = (amp, re|im), K = (point, vector)
-// rows, 32 per K-chunk. K-chunks never straddle point sets: a collocation chunk holds 8 points
-// x 4 vectors (rows consecutive in the costate buffer), an IC/BC chunk 32 points x 1 vector.
-// R is regenerated from the angles, one product-rule pass per point giving all four vectors.
-struct WgArgs {
-  const float* thetaJ;
-  const float2* lam;          // [P][4][dim]
-  float* part;                // [nchunks][dim][2 dim]
-  int32_t n;
-  int64_t npts[3], pt_base[3];
-  int64_t kc_end[3];          // cumulative K-chunk counts per set
-  int32_t nchunks;            // point-range chunks (grid.y)
-  int32_t* status;
-};
-
-__host__ __device__ inline int wg_smem_bytes() { return 2 * (2 * TM * KC * 4 + 2 * 256 * KC * 4) + 128 + 32 * QP_MAXQ * 32; }
-
-// Global loads of one K-chunk, issued one iteration ahead (software pipeline): the costate
-// values this thread stages (component o = nt * 256 + tid of the chunk's 32 rows) and the raw
-// angle entries (theta, J) of up to 2 (point, qubit) pairs of the chunk.
-constexpr int WG_THREADS = 256;
-struct WgPrefetch {
-  float lam[KC];
-  float4 tj[2];
-};
-
-__device__ __forceinline__ void wg_chunk_geom(const WgArgs& a, int64_t kc, int& set, int64_t& p0, int& ppc) {
-  set = kc < a.kc_end[0] ? 0 : (kc < a.kc_end[1] ? 1 : 2);
-  const int64_t ck = kc - (set == 0 ? 0 : a.kc_end[set - 1]);
-  ppc = set == 0 ? 8 : 32;
-  p0 = ck * ppc;
-}
-
-__device__ __forceinline__ void wg_prefetch(const WgArgs& a, int64_t kc, int tid, int o, WgPrefetch& f) {
-  const int n = a.n, dim = 1 << n;
-  int set, ppc;
-  int64_t p0;
-  wg_chunk_geom(a, kc, set, p0, ppc);
-  const int64_t np = a.npts[set];
-  const float* lamf = reinterpret_cast<const float*>(a.lam);
-  const int64_t row0 = (a.pt_base[set] + p0) * 4;
-  const int rstep = set == 0 ? 1 : 4;
-  const int nvalid = set == 0 ? (int)((np - p0) * 4 < KC ? (np - p0) * 4 : KC) : (int)(np - p0 < KC ? np - p0 : KC);
-#pragma unroll
-  for (int t = 0; t < KC; ++t)
-    f.lam[t] = t < nvalid ? __ldg(lamf + (row0 + (int64_t)t * rstep) * (2 * dim) + o) : 0.f;
-#pragma unroll
-  for (int j = 0; j < 2; ++j) {
-    const int e = tid + j * WG_THREADS;
-    const int pl = e / n, q = e % n;
-    f.tj[j] = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (e < ppc * n && p0 + pl < np)
-      f.tj[j] = __ldg(reinterpret_cast<const float4*>(a.thetaJ) + (a.pt_base[set] + p0 + pl) * n + q);
-  }
-}
-
-__global__ void __launch_bounds__(WG_THREADS, 1) dense_wgrad_gemm_kernel(WgArgs a) {
-  extern __shared__ __align__(1024) unsigned char sm[];
-  const int n = a.n, dim = 1 << n;
-  const int tid = threadIdx.x, warp = tid >> 5;
-  const int mt = blockIdx.x % (dim / TM), nt = blockIdx.x / (dim / TM);
-  const int nch = 256;
-  const int abytes = TM * KC * 4, bbytes = nch * KC * 4;
-  const int stage_bytes = 2 * abytes + 2 * bbytes;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(sm + 2 * stage_bytes);  // mma_done[2]
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + 2 * stage_bytes + 64);
-  float4* fac = reinterpret_cast<float4*>(sm + 2 * stage_bytes + 128);  // [32 pts][n][2]
-  if (warp == 0) qptc::tmem_alloc(tslot, 256);
-  if (tid == 0) { qptc::mbar_init(&bars[0], 1); qptc::mbar_init(&bars[1], 1); }
-  qptc::fence_before();
-  __syncthreads();
-  qptc::fence_after();
-  const uint32_t tmem = *tslot;
-  const uint32_t id = qptc::idesc(2, TM, nch);
-  const int64_t nkc_total = a.kc_end[2];
-  const int64_t per = (nkc_total + a.nchunks - 1) / a.nchunks;
-  const int64_t kc0 = blockIdx.y * per;
-  const int64_t kc1 = kc0 + per < nkc_total ? kc0 + per : nkc_total;
-  const int arow = tid & (TM - 1), ahalf = tid >> 7;  // A row (basis index) and half of the chunk
-  const int krow = mt * TM + arow;
-  const int o = nt * nch + tid;                      // costate component staged by this thread
-  bool ok = true;
-  uint32_t it = 0;
-  WgPrefetch pf;
-  if (kc0 < kc1) wg_prefetch(a, kc0, tid, o, pf);
-  for (int64_t kc = kc0; kc < kc1 && ok; ++kc, ++it) {
-    const uint32_t st = it & 1;
-    unsigned char* sA = sm + st * stage_bytes;
-    unsigned char* sB = sA + 2 * abytes;
-    int set, ppc;
-    int64_t p0;
-    wg_chunk_geom(a, kc, set, p0, ppc);
-    bool w_ok = true;
-    if (it >= 2) w_ok = qptc::mbar_wait(&bars[st], ((it - 2) >> 1) & 1);
-    ok = __syncthreads_and(w_ok);  // also orders the previous chunk's reads of `fac`
-    if (!ok) break;
-    // per-point factors from the prefetched angles: (cos, sin of theta_q / 2, Jx, Jy), (Jt, .)
-#pragma unroll
-    for (int j = 0; j < 2; ++j) {
-      const int e = tid + j * WG_THREADS;
-      if (e < ppc * n) {
-        const float4 tq = pf.tj[j];
-        float sn, cs;
-        sincosf(0.5f * tq.x, &sn, &cs);
-        const int pl = e / n, q = e % n;
-        const bool valid = p0 + pl < a.npts[set];  // rows past the end of the set contribute zero
-        fac[(pl * n + q) * 2] = valid ? make_float4(cs, sn, tq.y, tq.z) : make_float4(0.f, 0.f, 0.f, 0.f);
-        fac[(pl * n + q) * 2 + 1] = valid ? make_float4(tq.w, 1.f, 0.f, 0.f) : make_float4(0.f, 0.f, 0.f, 0.f);
-      }
-    }
-    // B: costate rows of the chunk (prefetched) -> (o, row) core layout, TF32 hi/lo
-    {
-      float* Bhi = reinterpret_cast<float*>(sB);
-      float* Blo = reinterpret_cast<float*>(sB + bbytes);
-#pragma unroll
-      for (int g4 = 0; g4 < KC / 4; ++g4) {
-        float4 h4, l4;
-        qptc::split_tf32(pf.lam[4 * g4], h4.x, l4.x);
-        qptc::split_tf32(pf.lam[4 * g4 + 1], h4.y, l4.y);
-        qptc::split_tf32(pf.lam[4 * g4 + 2], h4.z, l4.z);
-        qptc::split_tf32(pf.lam[4 * g4 + 3], h4.w, l4.w);
-        const uint32_t off = core_off(tid, g4 * 4) / 4;
-        *reinterpret_cast<float4*>(Bhi + off) = h4;
-        *reinterpret_cast<float4*>(Blo + off) = l4;
-      }
-    }
-    __syncthreads();  // fac visible
-    // next chunk's global loads are in flight while this chunk is generated and multiplied
-    if (kc + 1 < kc1) wg_prefetch(a, kc + 1, tid, o, pf);
-    float* Ahi = reinterpret_cast<float*>(sA);
-    float* Alo = reinterpret_cast<float*>(sA + abytes);
-    float av[KC / 2];  // this thread's half of the row: K indices 16 * ahalf .. + 15
-    if (set == 0) {
-#pragma unroll
-      for (int pi = 0; pi < 4; ++pi) {
-        const int pl = ahalf * 4 + pi;
-        float P = 1.f, D0 = 0.f, D1 = 0.f, D2 = 0.f;
-        for (int q = 0; q < n; ++q) {
-          const float4 f0 = fac[(pl * n + q) * 2], f1 = fac[(pl * n + q) * 2 + 1];
-          const bool bit = (krow >> (n - 1 - q)) & 1;
-          const float f = bit ? f0.y : f0.x, d = bit ? 0.5f * f0.x : -0.5f * f0.y;
-          D0 = D0 * f + P * d * f0.z;
-          D1 = D1 * f + P * d * f0.w;
-          D2 = D2 * f + P * d * f1.x;
-          P *= f;
-        }
-        av[4 * pi] = P; av[4 * pi + 1] = D0; av[4 * pi + 2] = D1; av[4 * pi + 3] = D2;
-      }
-    } else {
-#pragma unroll
-      for (int pi = 0; pi < 16; ++pi) {
-        const int pl = ahalf * 16 + pi;
-        float P = 1.f;
-        for (int q = 0; q < n; ++q) {
-          const float4 f0 = fac[(pl * n + q) * 2];
-          P *= ((krow >> (n - 1 - q)) & 1) ? f0.y : f0.x;
-        }
-        av[pi] = P;
-      }
-    }
-#pragma unroll
-    for (int g4 = 0; g4 < KC / 8; ++g4) {
-      float4 h4, l4;
-      qptc::split_tf32(av[4 * g4], h4.x, l4.x);
-      qptc::split_tf32(av[4 * g4 + 1], h4.y, l4.y);
-      qptc::split_tf32(av[4 * g4 + 2], h4.z, l4.z);
-      qptc::split_tf32(av[4 * g4 + 3], h4.w, l4.w);
-      const uint32_t off = core_off(arow, ahalf * (KC / 2) + g4 * 4) / 4;
-      *reinterpret_cast<float4*>(Ahi + off) = h4;
-      *reinterpret_cast<float4*>(Alo + off) = l4;
-    }
-    qptc::fence_proxy_async();
-    __syncthreads();
-    if (tid == 0) {
-      qptc::fence_after();
-      const uint32_t sa = qptc::smem_u32(sA), sb = qptc::smem_u32(sB);
-#pragma unroll
-      for (int ks = 0; ks < KC / 8; ++ks) {
-        const uint64_t ah = qptc::desc_kmajor(sa + ks * 256, 128, (KC / 4) * 128);
-        const uint64_t al = qptc::desc_kmajor(sa + abytes + ks * 256, 128, (KC / 4) * 128);
-        const uint64_t bh = qptc::desc_kmajor(sb + ks * 256, 128, (KC / 4) * 128);
-        const uint64_t bl = qptc::desc_kmajor(sb + bbytes + ks * 256, 128, (KC / 4) * 128);
-        qptc::mma_tf32(tmem, ah, bh, id, (kc > kc0 || ks > 0) ? 1u : 0u);
-        qptc::mma_tf32(tmem, ah, bl, id, 1u);
-        qptc::mma_tf32(tmem, al, bh, id, 1u);
-      }
-      qptc::commit(&bars[st]);
-    }
-  }
-  // epilogue: 128 x 256 partial tile; warps w and w + 4 read the same lanes, column halves
-  const int lrow = (warp & 3) * 32 + (tid & 31), chalf = warp >> 2;
-  float* outp = a.part + ((int64_t)blockIdx.y * dim + mt * TM + lrow) * (2 * dim) + nt * nch + chalf * 128;
-  if (ok && it > 0) {
-    ok = __syncthreads_and(qptc::mbar_wait(&bars[(it - 1) & 1], ((it - 1) >> 1) & 1));
-    if (ok) {
-      qptc::fence_after();
-      float v[32];
-      for (int c0 = 0; c0 < 128; c0 += 32) {
-        qptc::tmem_ld32(tmem + ((uint32_t)((warp & 3) * 32) << 16) + chalf * 128 + c0, v);
-#pragma unroll
-        for (int e = 0; e < 8; ++e)
-          reinterpret_cast<float4*>(outp + c0)[e] = make_float4(v[4 * e], v[4 * e + 1], v[4 * e + 2], v[4 * e + 3]);
-      }
-    }
-  } else if (ok) {
-    for (int c0 = 0; c0 < 128; c0 += 4) *reinterpret_cast<float4*>(outp + c0) = make_float4(0.f, 0.f, 0.f, 0.f);
-  }
-  if (!ok) {
-    if (tid == 0) atomicExch(a.status, 6);
-    if (it >= 1) qptc::mbar_wait(&bars[(it - 1) & 1], ((it - 1) >> 1) & 1);
-  }
-  qptc::fence_before();
-  __syncthreads();
-  if (warp == 0) qptc::tmem_dealloc(tmem, 256);
-}
-
 // ------------------------------------------------------------------------- B-independent sweep
 // G[k][j] = sum_chunks (part[.][k][2j] - i part[.][k][2j+1]) (FP64 over chunks);
 // Y = U' G with U' the fused unitary including the embedding phase: Y = sum phi lambda^dag at
@@ -1606,315 +908,6 @@ __global__ void dense_embed_grad_kernel(EmbedArgs a) {
       }
     }
   }
-}
-
-// ------------------------------------------------------------------------- mu + embedding gradients
-// n <= 8: mu_s = Re(U'^H lambda_s) row by row on the tensor cores (A = costate rows, B = the
-// transposed operand blocks), and the embedding gradients taken from tensor memory in the
-// epilogue. With the flipped-factor identity d r / d theta_q [k] ~ sign_q(k) r[k ^ e_q]
-// (the derivative of cos/sin(theta/2) is the other one, halved and signed), a row (p, s)
-// contributes
-//   C_q = sum_k sign_q(k) r_s[k ^ e_q] mu_s[k]   (to dL/dtheta_q, summed over s)
-//   D_q = sum_k sign_q(k) r_0[k ^ e_q] mu_s[k]   (s >= 1: dL/dJ_{q, s-1})
-// with sign_q(k) = +1 where qubit q is 1. r_s is a product over qubits: the five lowest index
-// bits come from 32-entry tables, the higher ones from a per-chunk factor, so every sum splits
-// into 32-column correlations. The drain of a tile runs one 32-column chunk per K-step of the
-// next tile, under its tensor-core work.
-struct MuArgs {
-  const float* thetaJ;     // [P][n] float4
-  const float* WT;         // transposed operand blocks (rows a = basis index, K = 2 dim)
-  const float* lam;        // [P][4][2 dim] costate rows
-  float* dthetaJ;          // [P][n] float4 (dL/dtheta, dL/dJ_x, dL/dJ_y, dL/dJ_t)
-  int32_t n;
-  int64_t npts[3], pt_base[3], tile_end[3];
-  int32_t* status;
-};
-
-__host__ __device__ inline int mu_smem_bytes(int n) { return gemm_smem_bytes(n, 1) + 2 * 4 * 32 * 8 * 4; }
-
-// Per-row state of a tile being drained.
-struct MuRow {
-  float Lo[32], Lod[32];          // low five qubits: value and tangent-s product tables
-  float hc[3], hs[3], hj[3];      // high qubits (n - 5 <= 3): cos, sin of theta/2, J along s
-  float C[8], D[8];
-};
-
-__device__ __forceinline__ void mu_row_setup(const MuArgs& a, int n, int set, int64_t p, int s, MuRow& R) {
-  const float4* tj = reinterpret_cast<const float4*>(a.thetaJ) + (a.pt_base[set] + p) * n;
-#pragma unroll
-  for (int t = 0; t < 32; ++t) { R.Lo[t] = 1.f; R.Lod[t] = 0.f; }
-#pragma unroll
-  for (int b = 0; b < 5; ++b) {
-    const float4 tq = __ldg(tj + (n - 1 - b));
-    float sn, cs;
-    sincosf(0.5f * tq.x, &sn, &cs);
-    const float J = s == 0 ? 0.f : (s == 1 ? tq.y : (s == 2 ? tq.z : tq.w));
-#pragma unroll
-    for (int t = 0; t < 32; ++t) {
-      const bool bit = (t >> b) & 1;
-      const float f = bit ? sn : cs, d = bit ? 0.5f * cs : -0.5f * sn;
-      R.Lod[t] = R.Lod[t] * f + R.Lo[t] * d * J;
-      R.Lo[t] *= f;
-    }
-  }
-#pragma unroll
-  for (int q = 0; q < 3; ++q) {
-    R.hc[q] = 1.f; R.hs[q] = 0.f; R.hj[q] = 0.f;
-    if (q < n - 5) {
-      const float4 tq = __ldg(tj + q);
-      sincosf(0.5f * tq.x, &R.hs[q], &R.hc[q]);
-      R.hj[q] = s == 0 ? 0.f : (s == 1 ? tq.y : (s == 2 ? tq.z : tq.w));
-    }
-  }
-#pragma unroll
-  for (int q = 0; q < 8; ++q) { R.C[q] = 0.f; R.D[q] = 0.f; }
-}
-
-// High-qubit factor of chunk index c (bits of k above the low five) and its tangent.
-__device__ __forceinline__ void mu_high(const MuRow& R, int n, int c, float& H, float& Hd) {
-  H = 1.f;
-  Hd = 0.f;
-#pragma unroll
-  for (int q = 0; q < 3; ++q) {
-    if (q < n - 5) {
-      const bool bit = (c >> (n - 6 - q)) & 1;
-      const float f = bit ? R.hs[q] : R.hc[q], d = bit ? 0.5f * R.hc[q] : -0.5f * R.hs[q];
-      Hd = Hd * f + H * d * R.hj[q];
-      H *= f;
-    }
-  }
-}
-
-// One 32-column chunk c of the row's mu (tensor memory) into C and D.
-__device__ __forceinline__ void mu_chunk(MuRow& R, int n, int s, int c, uint32_t taddr) {
-  float v[32];
-  qptc::tmem_ld32(taddr, v);
-  float X = 0.f, Y = 0.f, A[5], B[5];
-#pragma unroll
-  for (int b = 0; b < 5; ++b) { A[b] = 0.f; B[b] = 0.f; }
-#pragma unroll
-  for (int l = 0; l < 32; ++l) {
-    X += v[l] * R.Lo[l];
-#pragma unroll
-    for (int b = 0; b < 5; ++b) {
-      const float sv = ((l >> b) & 1) ? v[l] : -v[l];
-      A[b] += sv * R.Lo[l ^ (1 << b)];
-    }
-  }
-  if (s != 0) {
-#pragma unroll
-    for (int l = 0; l < 32; ++l) {
-      Y += v[l] * R.Lod[l];
-#pragma unroll
-      for (int b = 0; b < 5; ++b) {
-        const float sv = ((l >> b) & 1) ? v[l] : -v[l];
-        B[b] += sv * R.Lod[l ^ (1 << b)];
-      }
-    }
-  }
-  float H, Hd;
-  mu_high(R, n, c, H, Hd);
-  // low qubits q = n - 1 - b: the flip stays inside the chunk
-#pragma unroll
-  for (int b = 0; b < 5; ++b) {
-    const int q = n - 1 - b;
-#pragma unroll
-    for (int qq = 0; qq < 8; ++qq) {
-      if (qq == q) {
-        R.C[qq] += s == 0 ? H * A[b] : Hd * A[b] + H * B[b];
-        R.D[qq] += H * A[b];
-      }
-    }
-  }
-  // high qubits: the flip moves to chunk c ^ e
-#pragma unroll
-  for (int q = 0; q < 3; ++q) {
-    if (q < n - 5) {
-      const int e = 1 << (n - 6 - q);
-      float Hf, Hdf;
-      mu_high(R, n, c ^ e, Hf, Hdf);
-      const float sg = (c & e) ? 1.f : -1.f;
-      R.C[q] += sg * (s == 0 ? Hf * X : Hdf * X + Hf * Y);
-      R.D[q] += sg * Hf * X;
-    }
-  }
-}
-
-__global__ void __launch_bounds__(128, 1) dense_mu_embed_kernel(MuArgs a) {
-  extern __shared__ __align__(1024) unsigned char sm[];
-  const int n = a.n, dim = 1 << n;
-  const int ktot = 2 * dim, nch = dim, nkc = ktot / KC;   // dim <= 256: one column chunk
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int abytes = TM * KC * 4, wbytes = nch * KC * 4;
-  const int stage_bytes = 2 * abytes + 2 * wbytes;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(sm + 2 * stage_bytes);  // w_full[2], mma_done[2]
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + 2 * stage_bytes + 64);
-  float* ex = reinterpret_cast<float*>(sm + 2 * stage_bytes + 128);    // [2 (C, D)][4][32][8]
-  const uint32_t tcols = 2 * nch <= 256 ? (2 * nch <= 128 ? 128 : 256) : 512;
-  if (warp == 0) qptc::tmem_alloc(tslot, tcols);
-  if (tid == 0) {
-    for (int i = 0; i < 4; ++i) qptc::mbar_init(&bars[i], 1);
-  }
-  qptc::fence_before();
-  __syncthreads();
-  qptc::fence_after();
-  const uint32_t tmem = *tslot;
-  const uint32_t id = qptc::idesc(2, TM, nch);
-  const int nchunk32 = dim / 32;
-  bool ok = true;
-  uint32_t it = 0, cbuf = 0;
-  int64_t last_copy = -1, last_commit = -1;
-  // pending tile (being drained)
-  bool pend = false, pend_nv4 = false, pend_act = false;
-  int pend_set = 0;
-  int64_t pend_p = 0;
-  uint32_t pend_buf = 0, pend_it = 0;
-  MuRow R;
-  auto finalize = [&]() {
-    qptc::fence_before();
-    // rows of one point sit in four warps (same lane): combine through shared memory
-    const int s = pend_nv4 ? warp : 0;
-    if (pend_nv4) {
-#pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        ex[(s * 32 + lane) * 8 + q] = R.C[q];
-        ex[1024 + (s * 32 + lane) * 8 + q] = R.D[q];
-      }
-    }
-    __syncthreads();
-    if (pend_act && (!pend_nv4 || warp == 0)) {
-      float4* dst = reinterpret_cast<float4*>(a.dthetaJ) + (a.pt_base[pend_set] + pend_p) * n;
-      for (int q = 0; q < n; ++q) {
-        if (pend_nv4) {
-          const float c = ex[lane * 8 + q] + ex[(32 + lane) * 8 + q] + ex[(64 + lane) * 8 + q] + ex[(96 + lane) * 8 + q];
-          dst[q] = make_float4(c, ex[1024 + (32 + lane) * 8 + q], ex[1024 + (64 + lane) * 8 + q],
-                               ex[1024 + (96 + lane) * 8 + q]);
-        } else {
-          float c = 0.f;
-#pragma unroll
-          for (int qq = 0; qq < 8; ++qq) if (qq == q) c = R.C[qq];
-          dst[q] = make_float4(c, 0.f, 0.f, 0.f);
-        }
-      }
-    }
-    __syncthreads();
-    pend = false;
-  };
-  auto begin_drain = [&]() -> bool {
-    const bool w = __syncthreads_and(qptc::mbar_wait(&bars[2 + (pend_it & 1)], (pend_it >> 1) & 1));
-    if (w) {
-      qptc::fence_after();
-      const int s = pend_nv4 ? warp : 0;
-      const int64_t np = a.npts[pend_set];
-      mu_row_setup(a, n, pend_set, pend_p < np ? pend_p : np - 1, s, R);
-    }
-    return w;
-  };
-  const int64_t T2 = a.tile_end[2];
-  for (int64_t tile = blockIdx.x; tile < T2 && ok; tile += gridDim.x) {
-    int set;
-    int64_t p0;
-    if (tile < a.tile_end[0]) { set = 0; p0 = tile * 32; }
-    else if (tile < a.tile_end[1]) { set = 1; p0 = (tile - a.tile_end[0]) * TM; }
-    else { set = 2; p0 = (tile - a.tile_end[1]) * TM; }
-    const bool nv4 = set == 0;
-    const int64_t np = a.npts[set];
-    const int s = nv4 ? warp : 0;
-    const int64_t p = p0 + (nv4 ? lane : tid);
-    const int64_t pc = p < np ? p : np - 1;
-    const float4* src = reinterpret_cast<const float4*>(a.lam + ((a.pt_base[set] + pc) * 4 + s) * (int64_t)ktot);
-    for (int kc = 0; kc < nkc && ok; ++kc, ++it) {
-      const uint32_t st = it & 1;
-      unsigned char* sA = sm + st * stage_bytes;
-      unsigned char* sW = sA + 2 * abytes;
-      bool w_ok = true;
-      if (it >= 2) w_ok = qptc::mbar_wait(&bars[2 + st], ((it - 2) >> 1) & 1);
-      ok = __syncthreads_and(w_ok);
-      if (!ok) break;
-      if (tid == 0) {
-        qptc::mbar_arrive_expect_tx(&bars[st], 2 * wbytes);
-        qptc::bulk_g2s(sW, a.WT + (int64_t)kc * 2 * (nch * KC), 2 * wbytes, &bars[st]);
-        last_copy = it;
-      }
-      {
-        float* Ahi = reinterpret_cast<float*>(sA);
-        float* Alo = reinterpret_cast<float*>(sA + abytes);
-#pragma unroll
-        for (int g4 = 0; g4 < KC / 4; ++g4) {
-          const float4 v4 = __ldg(src + kc * (KC / 4) + g4);
-          float4 h4, l4;
-          qptc::split_tf32(v4.x, h4.x, l4.x);
-          qptc::split_tf32(v4.y, h4.y, l4.y);
-          qptc::split_tf32(v4.z, h4.z, l4.z);
-          qptc::split_tf32(v4.w, h4.w, l4.w);
-          const uint32_t off = core_off(tid, g4 * 4) / 4;
-          *reinterpret_cast<float4*>(Ahi + off) = h4;
-          *reinterpret_cast<float4*>(Alo + off) = l4;
-        }
-      }
-      qptc::fence_proxy_async();
-      __syncthreads();
-      bool m_ok = true;
-      if (tid == 0) {
-        m_ok = qptc::mbar_wait(&bars[st], (it >> 1) & 1);
-        if (m_ok) {
-          qptc::fence_after();
-          const uint32_t sa = qptc::smem_u32(sA), sw = qptc::smem_u32(sW);
-          const uint32_t dt = tmem + cbuf * (tcols / 2);
-#pragma unroll
-          for (int ks = 0; ks < KC / 8; ++ks) {
-            const uint64_t ah = qptc::desc_kmajor(sa + ks * 256, 128, (KC / 4) * 128);
-            const uint64_t al = qptc::desc_kmajor(sa + abytes + ks * 256, 128, (KC / 4) * 128);
-            const uint64_t wh = qptc::desc_kmajor(sw + ks * 256, 128, (KC / 4) * 128);
-            const uint64_t wl = qptc::desc_kmajor(sw + wbytes + ks * 256, 128, (KC / 4) * 128);
-            qptc::mma_tf32(dt, ah, wh, id, (kc > 0 || ks > 0) ? 1u : 0u);
-            qptc::mma_tf32(dt, ah, wl, id, 1u);
-            qptc::mma_tf32(dt, al, wh, id, 1u);
-          }
-          qptc::commit(&bars[2 + st]);
-          last_commit = it;
-        }
-      }
-      ok = __syncthreads_and(m_ok);
-      if (!ok) break;
-      // drain the previous tile one 32-column chunk per K-step, under this tile's MMAs
-      if (pend) {
-        if (kc == 0) ok = begin_drain();
-        if (!ok) break;
-        if (kc < nchunk32)
-          mu_chunk(R, n, pend_nv4 ? warp : 0, kc,
-                   tmem + ((uint32_t)(warp * 32) << 16) + pend_buf * (tcols / 2) + kc * 32);
-        if (kc == nchunk32 - 1) finalize();
-      }
-    }
-    if (!ok) break;
-    pend = true;
-    pend_nv4 = nv4;
-    pend_set = set;
-    pend_p = p;
-    pend_act = p < np;
-    pend_buf = cbuf;
-    pend_it = it - 1;
-    cbuf ^= 1;
-  }
-  if (ok && pend) {
-    ok = begin_drain();
-    if (ok) {
-      for (int c = 0; c < nchunk32; ++c)
-        mu_chunk(R, n, pend_nv4 ? warp : 0, c, tmem + ((uint32_t)(warp * 32) << 16) + pend_buf * (tcols / 2) + c * 32);
-      finalize();
-    }
-  }
-  if (!ok) {
-    if (tid == 0) {
-      atomicExch(a.status, 6);
-      if (last_copy >= 0) qptc::mbar_wait(&bars[last_copy & 1], ((uint32_t)last_copy >> 1) & 1);
-      if (last_commit >= 0) qptc::mbar_wait(&bars[2 + (last_commit & 1)], ((uint32_t)last_commit >> 1) & 1);
-    }
-  }
-  qptc::fence_before();
-  __syncthreads();
-  if (warp == 0) qptc::tmem_dealloc(tmem, tcols);
 }
 
 }  // namespace qpd

@@ -1,0 +1,317 @@
+// qp_mu.cuh -- back-projection mu = Re(U'^H lambda) on the tensor cores with the embedding
+// gradients as its epilogue, n = 7, 8.
+#pragma once
+#include "qp_dense.cuh"
+
+namespace qpd {
+
+// ------------------------------------------------------------------------- mu + embedding gradients
+// n <= 8: mu_s = Re(U'^H lambda_s) row by row on the tensor cores (A = costate rows, B = the
+// transposed operand blocks), and the embedding gradients taken from tensor memory in the
+// epilogue. With the flipped-factor identity d r / d theta_q [k] ~ sign_q(k) r[k ^ e_q]
+// (the derivative of cos/sin(theta/2) is the other one, halved and signed), a row (p, s)
+// contributes
+//   C_q = sum_k sign_q(k) r_s[k ^ e_q] mu_s[k]   (to dL/dtheta_q, summed over s)
+//   D_q = sum_k sign_q(k) r_0[k ^ e_q] mu_s[k]   (s >= 1: dL/dJ_{q, s-1})
+// with sign_q(k) = +1 where qubit q is 1. r_s is a product over qubits: the five lowest index
+// bits come from 32-entry tables, the higher ones from a per-chunk factor, so every sum splits
+// into 32-column correlations. The drain of a tile runs one 32-column chunk per K-step of the
+// next tile, under its tensor-core work.
+struct MuArgs {
+  const float* thetaJ;     // [P][n] float4
+  const float* WT;         // transposed operand blocks (rows a = basis index, K = 2 dim)
+  const float* lam;        // [P][4][2 dim] costate rows
+  float* dthetaJ;          // [P][n] float4 (dL/dtheta, dL/dJ_x, dL/dJ_y, dL/dJ_t)
+  int32_t n;
+  int64_t npts[3], pt_base[3], tile_end[3];
+  int32_t* status;
+};
+
+__host__ __device__ inline int mu_smem_bytes(int n) { return gemm_smem_bytes(n, 1) + 2 * 4 * 32 * 8 * 4; }
+
+// Per-row state of a tile being drained.
+struct MuRow {
+  float Lo[32], Lod[32];          // low five qubits: value and tangent-s product tables
+  float hc[3], hs[3], hj[3];      // high qubits (n - 5 <= 3): cos, sin of theta/2, J along s
+  float C[8], D[8];
+};
+
+__device__ __forceinline__ void mu_row_setup(const MuArgs& a, int n, int set, int64_t p, int s, MuRow& R) {
+  const float4* tj = reinterpret_cast<const float4*>(a.thetaJ) + (a.pt_base[set] + p) * n;
+#pragma unroll
+  for (int t = 0; t < 32; ++t) { R.Lo[t] = 1.f; R.Lod[t] = 0.f; }
+#pragma unroll
+  for (int b = 0; b < 5; ++b) {
+    const float4 tq = __ldg(tj + (n - 1 - b));
+    float sn, cs;
+    sincosf(0.5f * tq.x, &sn, &cs);
+    const float J = s == 0 ? 0.f : (s == 1 ? tq.y : (s == 2 ? tq.z : tq.w));
+#pragma unroll
+    for (int t = 0; t < 32; ++t) {
+      const bool bit = (t >> b) & 1;
+      const float f = bit ? sn : cs, d = bit ? 0.5f * cs : -0.5f * sn;
+      R.Lod[t] = R.Lod[t] * f + R.Lo[t] * d * J;
+      R.Lo[t] *= f;
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    R.hc[q] = 1.f; R.hs[q] = 0.f; R.hj[q] = 0.f;
+    if (q < n - 5) {
+      const float4 tq = __ldg(tj + q);
+      sincosf(0.5f * tq.x, &R.hs[q], &R.hc[q]);
+      R.hj[q] = s == 0 ? 0.f : (s == 1 ? tq.y : (s == 2 ? tq.z : tq.w));
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < 8; ++q) { R.C[q] = 0.f; R.D[q] = 0.f; }
+}
+
+// High-qubit factor of chunk index c (bits of k above the low five) and its tangent.
+__device__ __forceinline__ void mu_high(const MuRow& R, int n, int c, float& H, float& Hd) {
+  H = 1.f;
+  Hd = 0.f;
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    if (q < n - 5) {
+      const bool bit = (c >> (n - 6 - q)) & 1;
+      const float f = bit ? R.hs[q] : R.hc[q], d = bit ? 0.5f * R.hc[q] : -0.5f * R.hs[q];
+      Hd = Hd * f + H * d * R.hj[q];
+      H *= f;
+    }
+  }
+}
+
+// One 32-column chunk c of the row's mu (tensor memory) into C and D.
+__device__ __forceinline__ void mu_chunk(MuRow& R, int n, int s, int c, uint32_t taddr) {
+  float v[32];
+  qptc::tmem_ld32(taddr, v);
+  float X = 0.f, Y = 0.f, A[5], B[5];
+#pragma unroll
+  for (int b = 0; b < 5; ++b) { A[b] = 0.f; B[b] = 0.f; }
+#pragma unroll
+  for (int l = 0; l < 32; ++l) {
+    X += v[l] * R.Lo[l];
+#pragma unroll
+    for (int b = 0; b < 5; ++b) {
+      const float sv = ((l >> b) & 1) ? v[l] : -v[l];
+      A[b] += sv * R.Lo[l ^ (1 << b)];
+    }
+  }
+  if (s != 0) {
+#pragma unroll
+    for (int l = 0; l < 32; ++l) {
+      Y += v[l] * R.Lod[l];
+#pragma unroll
+      for (int b = 0; b < 5; ++b) {
+        const float sv = ((l >> b) & 1) ? v[l] : -v[l];
+        B[b] += sv * R.Lod[l ^ (1 << b)];
+      }
+    }
+  }
+  float H, Hd;
+  mu_high(R, n, c, H, Hd);
+  // low qubits q = n - 1 - b: the flip stays inside the chunk
+#pragma unroll
+  for (int b = 0; b < 5; ++b) {
+    const int q = n - 1 - b;
+#pragma unroll
+    for (int qq = 0; qq < 8; ++qq) {
+      if (qq == q) {
+        R.C[qq] += s == 0 ? H * A[b] : Hd * A[b] + H * B[b];
+        R.D[qq] += H * A[b];
+      }
+    }
+  }
+  // high qubits: the flip moves to chunk c ^ e
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    if (q < n - 5) {
+      const int e = 1 << (n - 6 - q);
+      float Hf, Hdf;
+      mu_high(R, n, c ^ e, Hf, Hdf);
+      const float sg = (c & e) ? 1.f : -1.f;
+      R.C[q] += sg * (s == 0 ? Hf * X : Hdf * X + Hf * Y);
+      R.D[q] += sg * Hf * X;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(128, 1) dense_mu_embed_kernel(MuArgs a) {
+  extern __shared__ __align__(1024) unsigned char sm[];
+  const int n = a.n, dim = 1 << n;
+  const int ktot = 2 * dim, nch = dim, nkc = ktot / KC;   // dim <= 256: one column chunk
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int abytes = TM * KC * 4, wbytes = nch * KC * 4;
+  const int stage_bytes = 2 * abytes + 2 * wbytes;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sm + 2 * stage_bytes);  // w_full[2], mma_done[2]
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + 2 * stage_bytes + 64);
+  float* ex = reinterpret_cast<float*>(sm + 2 * stage_bytes + 128);    // [2 (C, D)][4][32][8]
+  const uint32_t tcols = 2 * nch <= 256 ? (2 * nch <= 128 ? 128 : 256) : 512;
+  if (warp == 0) qptc::tmem_alloc(tslot, tcols);
+  if (tid == 0) {
+    for (int i = 0; i < 4; ++i) qptc::mbar_init(&bars[i], 1);
+  }
+  qptc::fence_before();
+  __syncthreads();
+  qptc::fence_after();
+  const uint32_t tmem = *tslot;
+  const uint32_t id = qptc::idesc(2, TM, nch);
+  const int nchunk32 = dim / 32;
+  bool ok = true;
+  uint32_t it = 0, cbuf = 0;
+  int64_t last_copy = -1, last_commit = -1;
+  // pending tile (being drained)
+  bool pend = false, pend_nv4 = false, pend_act = false;
+  int pend_set = 0;
+  int64_t pend_p = 0;
+  uint32_t pend_buf = 0, pend_it = 0;
+  MuRow R;
+  auto finalize = [&]() {
+    qptc::fence_before();
+    // rows of one point sit in four warps (same lane): combine through shared memory
+    const int s = pend_nv4 ? warp : 0;
+    if (pend_nv4) {
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        ex[(s * 32 + lane) * 8 + q] = R.C[q];
+        ex[1024 + (s * 32 + lane) * 8 + q] = R.D[q];
+      }
+    }
+    __syncthreads();
+    if (pend_act && (!pend_nv4 || warp == 0)) {
+      float4* dst = reinterpret_cast<float4*>(a.dthetaJ) + (a.pt_base[pend_set] + pend_p) * n;
+      for (int q = 0; q < n; ++q) {
+        if (pend_nv4) {
+          const float c = ex[lane * 8 + q] + ex[(32 + lane) * 8 + q] + ex[(64 + lane) * 8 + q] + ex[(96 + lane) * 8 + q];
+          dst[q] = make_float4(c, ex[1024 + (32 + lane) * 8 + q], ex[1024 + (64 + lane) * 8 + q],
+                               ex[1024 + (96 + lane) * 8 + q]);
+        } else {
+          float c = 0.f;
+#pragma unroll
+          for (int qq = 0; qq < 8; ++qq) if (qq == q) c = R.C[qq];
+          dst[q] = make_float4(c, 0.f, 0.f, 0.f);
+        }
+      }
+    }
+    __syncthreads();
+    pend = false;
+  };
+  auto begin_drain = [&]() -> bool {
+    const bool w = __syncthreads_and(qptc::mbar_wait(&bars[2 + (pend_it & 1)], (pend_it >> 1) & 1));
+    if (w) {
+      qptc::fence_after();
+      const int s = pend_nv4 ? warp : 0;
+      const int64_t np = a.npts[pend_set];
+      mu_row_setup(a, n, pend_set, pend_p < np ? pend_p : np - 1, s, R);
+    }
+    return w;
+  };
+  const int64_t T2 = a.tile_end[2];
+  for (int64_t tile = blockIdx.x; tile < T2 && ok; tile += gridDim.x) {
+    int set;
+    int64_t p0;
+    if (tile < a.tile_end[0]) { set = 0; p0 = tile * 32; }
+    else if (tile < a.tile_end[1]) { set = 1; p0 = (tile - a.tile_end[0]) * TM; }
+    else { set = 2; p0 = (tile - a.tile_end[1]) * TM; }
+    const bool nv4 = set == 0;
+    const int64_t np = a.npts[set];
+    const int s = nv4 ? warp : 0;
+    const int64_t p = p0 + (nv4 ? lane : tid);
+    const int64_t pc = p < np ? p : np - 1;
+    const float4* src = reinterpret_cast<const float4*>(a.lam + ((a.pt_base[set] + pc) * 4 + s) * (int64_t)ktot);
+    for (int kc = 0; kc < nkc && ok; ++kc, ++it) {
+      const uint32_t st = it & 1;
+      unsigned char* sA = sm + st * stage_bytes;
+      unsigned char* sW = sA + 2 * abytes;
+      bool w_ok = true;
+      if (it >= 2) w_ok = qptc::mbar_wait(&bars[2 + st], ((it - 2) >> 1) & 1);
+      ok = __syncthreads_and(w_ok);
+      if (!ok) break;
+      if (tid == 0) {
+        qptc::mbar_arrive_expect_tx(&bars[st], 2 * wbytes);
+        qptc::bulk_g2s(sW, a.WT + (int64_t)kc * 2 * (nch * KC), 2 * wbytes, &bars[st]);
+        last_copy = it;
+      }
+      {
+        float* Ahi = reinterpret_cast<float*>(sA);
+        float* Alo = reinterpret_cast<float*>(sA + abytes);
+#pragma unroll
+        for (int g4 = 0; g4 < KC / 4; ++g4) {
+          const float4 v4 = __ldg(src + kc * (KC / 4) + g4);
+          float4 h4, l4;
+          qptc::split_tf32(v4.x, h4.x, l4.x);
+          qptc::split_tf32(v4.y, h4.y, l4.y);
+          qptc::split_tf32(v4.z, h4.z, l4.z);
+          qptc::split_tf32(v4.w, h4.w, l4.w);
+          const uint32_t off = core_off(tid, g4 * 4) / 4;
+          *reinterpret_cast<float4*>(Ahi + off) = h4;
+          *reinterpret_cast<float4*>(Alo + off) = l4;
+        }
+      }
+      qptc::fence_proxy_async();
+      __syncthreads();
+      bool m_ok = true;
+      if (tid == 0) {
+        m_ok = qptc::mbar_wait(&bars[st], (it >> 1) & 1);
+        if (m_ok) {
+          qptc::fence_after();
+          const uint32_t sa = qptc::smem_u32(sA), sw = qptc::smem_u32(sW);
+          const uint32_t dt = tmem + cbuf * (tcols / 2);
+#pragma unroll
+          for (int ks = 0; ks < KC / 8; ++ks) {
+            const uint64_t ah = qptc::desc_kmajor(sa + ks * 256, 128, (KC / 4) * 128);
+            const uint64_t al = qptc::desc_kmajor(sa + abytes + ks * 256, 128, (KC / 4) * 128);
+            const uint64_t wh = qptc::desc_kmajor(sw + ks * 256, 128, (KC / 4) * 128);
+            const uint64_t wl = qptc::desc_kmajor(sw + wbytes + ks * 256, 128, (KC / 4) * 128);
+            qptc::mma_tf32(dt, ah, wh, id, (kc > 0 || ks > 0) ? 1u : 0u);
+            qptc::mma_tf32(dt, ah, wl, id, 1u);
+            qptc::mma_tf32(dt, al, wh, id, 1u);
+          }
+          qptc::commit(&bars[2 + st]);
+          last_commit = it;
+        }
+      }
+      ok = __syncthreads_and(m_ok);
+      if (!ok) break;
+      // drain the previous tile one 32-column chunk per K-step, under this tile's MMAs
+      if (pend) {
+        if (kc == 0) ok = begin_drain();
+        if (!ok) break;
+        if (kc < nchunk32)
+          mu_chunk(R, n, pend_nv4 ? warp : 0, kc,
+                   tmem + ((uint32_t)(warp * 32) << 16) + pend_buf * (tcols / 2) + kc * 32);
+        if (kc == nchunk32 - 1) finalize();
+      }
+    }
+    if (!ok) break;
+    pend = true;
+    pend_nv4 = nv4;
+    pend_set = set;
+    pend_p = p;
+    pend_act = p < np;
+    pend_buf = cbuf;
+    pend_it = it - 1;
+    cbuf ^= 1;
+  }
+  if (ok && pend) {
+    ok = begin_drain();
+    if (ok) {
+      for (int c = 0; c < nchunk32; ++c)
+        mu_chunk(R, n, pend_nv4 ? warp : 0, c, tmem + ((uint32_t)(warp * 32) << 16) + pend_buf * (tcols / 2) + c * 32);
+      finalize();
+    }
+  }
+  if (!ok) {
+    if (tid == 0) {
+      atomicExch(a.status, 6);
+      if (last_copy >= 0) qptc::mbar_wait(&bars[last_copy & 1], ((uint32_t)last_copy >> 1) & 1);
+      if (last_commit >= 0) qptc::mbar_wait(&bars[2 + (last_commit & 1)], ((uint32_t)last_commit >> 1) & 1);
+    }
+  }
+  qptc::fence_before();
+  __syncthreads();
+  if (warp == 0) qptc::tmem_dealloc(tmem, tcols);
+}
+
+}  // namespace qpd
