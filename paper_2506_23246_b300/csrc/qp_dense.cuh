@@ -627,30 +627,44 @@ struct SweepArgs {
   float* eout;          // blk_grad block 0: E[(l n + q) * 3 + P]
 };
 
+// Compensated FP32 accumulation (Neumaier): s + c carries the sum to about twice FP32
+// precision without the FP64 pipe (conversions and FP64 adds are slow on this part).
+struct CSum {
+  float s = 0.f, c = 0.f;
+  __device__ __forceinline__ void add(float x) {
+    const float t = s + x;
+    c += fabsf(s) >= fabsf(x) ? (s - t) + x : (x - t) + s;
+    s = t;
+  }
+  __device__ __forceinline__ void add(const CSum& o) { add(o.s); c += o.c; }
+  __device__ __forceinline__ float value() const { return s + c; }
+};
+
 __global__ void dense_gsum_kernel(SweepArgs a) {
   const int dim = 1 << a.n;
   const int64_t tot = (int64_t)dim * dim;
   const int64_t cstride = (int64_t)dim * 2 * dim;  // floats between consecutive chunk partials
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
     const int64_t k = e / dim, j = e % dim;
-    const float2* r = reinterpret_cast<const float2*>(a.part + k * (2 * dim)) + j;
-    double re[4] = {0.0, 0.0, 0.0, 0.0}, im[4] = {0.0, 0.0, 0.0, 0.0};
+    const float* r = a.part + k * (2 * dim) + 2 * j;
+    CSum re[2], im[2];
     int c = 0;
-    // eight independent loads in flight per thread; FP64 sums in four interleaved lanes
+    // eight independent loads in flight per thread
     for (; c + 8 <= a.nchunks; c += 8) {
       float2 v[8];
 #pragma unroll
-      for (int u = 0; u < 8; ++u) v[u] = __ldg(reinterpret_cast<const float2*>(
-          reinterpret_cast<const float*>(r) + (int64_t)(c + u) * cstride));
+      for (int u = 0; u < 8; ++u) v[u] = __ldg(reinterpret_cast<const float2*>(r + (int64_t)(c + u) * cstride));
 #pragma unroll
-      for (int u = 0; u < 8; ++u) { re[u & 3] += v[u].x; im[u & 3] -= v[u].y; }
+      for (int u = 0; u < 8; ++u) { re[u & 1].add(v[u].x); im[u & 1].add(-v[u].y); }
     }
     for (; c < a.nchunks; ++c) {
-      const float2 v = __ldg(reinterpret_cast<const float2*>(reinterpret_cast<const float*>(r) + (int64_t)c * cstride));
-      re[0] += v.x;
-      im[0] -= v.y;
+      const float2 v = __ldg(reinterpret_cast<const float2*>(r + (int64_t)c * cstride));
+      re[0].add(v.x);
+      im[0].add(-v.y);
     }
-    a.G[e] = make_float2((float)((re[0] + re[1]) + (re[2] + re[3])), (float)((im[0] + im[1]) + (im[2] + im[3])));
+    re[0].add(re[1]);
+    im[0].add(im[1]);
+    a.G[e] = make_float2(re[0].value(), im[0].value());
   }
 }
 

@@ -208,18 +208,37 @@ __global__ void __launch_bounds__(128, 1) dense_mu_embed_kernel(MuArgs a) {
     return w;
   };
   const int64_t T2 = a.tile_end[2];
-  for (int64_t tile = blockIdx.x; tile < T2 && ok; tile += gridDim.x) {
-    int set;
-    int64_t p0;
+  // costate row of this thread in a tile (A operand source)
+  auto tile_row = [&](int64_t tile, int& set, int64_t& p0, int64_t& p) -> const float4* {
     if (tile < a.tile_end[0]) { set = 0; p0 = tile * 32; }
     else if (tile < a.tile_end[1]) { set = 1; p0 = (tile - a.tile_end[0]) * TM; }
     else { set = 2; p0 = (tile - a.tile_end[1]) * TM; }
+    const int64_t np = a.npts[set];
+    p = p0 + (set == 0 ? lane : tid);
+    const int64_t pc = p < np ? p : np - 1;
+    return reinterpret_cast<const float4*>(a.lam + ((a.pt_base[set] + pc) * 4 + (set == 0 ? warp : 0)) * (int64_t)ktot);
+  };
+  // the next K-step's eight float4 of the row are loaded one step ahead (software pipeline)
+  float4 nxt[KC / 4];
+  if ((int64_t)blockIdx.x < T2) {
+    int st0;
+    int64_t q0, q1;
+    const float4* s0 = tile_row(blockIdx.x, st0, q0, q1);
+#pragma unroll
+    for (int g4 = 0; g4 < KC / 4; ++g4) nxt[g4] = __ldg(s0 + g4);
+  }
+  for (int64_t tile = blockIdx.x; tile < T2 && ok; tile += gridDim.x) {
+    int set;
+    int64_t p0, p;
+    const float4* src = tile_row(tile, set, p0, p);
     const bool nv4 = set == 0;
     const int64_t np = a.npts[set];
-    const int s = nv4 ? warp : 0;
-    const int64_t p = p0 + (nv4 ? lane : tid);
-    const int64_t pc = p < np ? p : np - 1;
-    const float4* src = reinterpret_cast<const float4*>(a.lam + ((a.pt_base[set] + pc) * 4 + s) * (int64_t)ktot);
+    const float4* src_next = nullptr;
+    if (tile + gridDim.x < T2) {
+      int st1;
+      int64_t q0, q1;
+      src_next = tile_row(tile + gridDim.x, st1, q0, q1);
+    }
     for (int kc = 0; kc < nkc && ok; ++kc, ++it) {
       const uint32_t st = it & 1;
       unsigned char* sA = sm + st * stage_bytes;
@@ -236,9 +255,17 @@ __global__ void __launch_bounds__(128, 1) dense_mu_embed_kernel(MuArgs a) {
       {
         float* Ahi = reinterpret_cast<float*>(sA);
         float* Alo = reinterpret_cast<float*>(sA + abytes);
+        float4 cur[KC / 4];
+#pragma unroll
+        for (int g4 = 0; g4 < KC / 4; ++g4) cur[g4] = nxt[g4];
+        const float4* ns = kc + 1 < nkc ? src + (kc + 1) * (KC / 4) : src_next;
+        if (ns) {
+#pragma unroll
+          for (int g4 = 0; g4 < KC / 4; ++g4) nxt[g4] = __ldg(ns + g4);
+        }
 #pragma unroll
         for (int g4 = 0; g4 < KC / 4; ++g4) {
-          const float4 v4 = __ldg(src + kc * (KC / 4) + g4);
+          const float4 v4 = cur[g4];
           float4 h4, l4;
           qptc::split_tf32(v4.x, h4.x, l4.x);
           qptc::split_tf32(v4.y, h4.y, l4.y);
