@@ -59,6 +59,28 @@ struct WsLayout {
 // accumulation length; chunks are summed in FP64).
 int64_t wg_rows_per_chunk(int n) { return n <= 8 ? 512 : 4096; }
 
+// Weight-gradient launch geometry for `nkc` 16-row steps: tiles of 128 basis indices x
+// min(512, 2^(n+1)) components, CTA groups per tile (persistent CTAs, balanced step ranges),
+// partial slots per CTA and steps per slot (at most wg_rows_per_chunk rows each).
+struct WgGeom {
+  int tiles, ngroups, spc, fl;
+  int64_t nslots;
+};
+WgGeom wg_geom(const qp_plan* pl, int64_t nkc) {
+  WgGeom g;
+  const int n = pl->c.n_qubits, dim = 1 << n;
+  const int nt = 2 * dim < 512 ? 2 * dim : 512;
+  g.tiles = (dim / qpd::TM) * (2 * dim / nt);
+  g.ngroups = pl->sm_count / g.tiles > 0 ? pl->sm_count / g.tiles : 1;
+  const int64_t per = nkc > 0 ? (nkc + g.ngroups - 1) / g.ngroups : 1;
+  const int64_t flmax = wg_rows_per_chunk(n) / qpd::WKC;
+  const int64_t nfl = (per + flmax - 1) / flmax;
+  g.fl = (int)((per + nfl - 1) / nfl);
+  g.spc = (int)nfl;
+  g.nslots = (int64_t)g.ngroups * g.spc;
+  return g;
+}
+
 bool dense_path(const qp_plan* pl) { return pl->path == QP_PATH_GEMM_3XTF32; }
 
 // The fused forward kernel keeps a tile's whole output row (2^(n+1) FP32 columns) in tensor
@@ -95,8 +117,9 @@ WsLayout ws_layout(const qp_plan* pl, int64_t P) {
   w.dU = o; o = al256(o + (dg ? dim * dim * 16 : 0));
   w.dG = o; o = al256(o + (dg ? dim * dim * 8 : 0));
   w.dY = o; o = al256(o + (dg ? dim * dim * 8 : 0));
-  const int64_t rows = 4 * P;
-  const int64_t nch = dg ? (rows + wg_rows_per_chunk(n) - 1) / wg_rows_per_chunk(n) : 0;
+  // upper bound of the weight-gradient partial slots: 16-row steps of 4 P rows, plus one per
+  // set boundary
+  const int64_t nch = dg ? wg_geom(pl, (4 * P + qpd::WKC - 1) / qpd::WKC + 2).nslots : 0;
   w.dpart = o; o = al256(o + (size_t)nch * dim * 2 * dim * 4);
   const bool dm = dg && pl->c.premap == QP_PREMAP_RFF_MLP;
   w.dWT = o; o = al256(o + (dm ? 2 * (2 * dim) * dim * 4 : 0));
@@ -264,7 +287,7 @@ qp_status qp_plan_create(const qp_circuit* circuit, const qp_problem* problem, i
         cudaFuncSetAttribute((void*)qpd::dense_row_gemm_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              qpd::gemm_smem_bytes(n, 1)) != cudaSuccess ||
         cudaFuncSetAttribute((void*)qpd::dense_wgrad_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             qpd::wg_smem_bytes()) != cudaSuccess ||
+                             qpd::wg_smem_bytes(n)) != cudaSuccess ||
         cudaFuncSetAttribute((void*)qpd::dense_sweep_left_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (1 << n) * 16 * 8) != cudaSuccess ||
         cudaFuncSetAttribute((void*)qpd::dense_sweep_right_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -496,20 +519,19 @@ static qp_status dense_loss_grad(qp_plan* pl, const float* d_params, const float
   wa.part = (float*)(ws + w.dpart); wa.n = n;
   base = 0;
   for (int i = 0; i < 3; ++i) { wa.npts[i] = npts[i]; wa.pt_base[i] = base; base += npts[i]; }
-  wa.kc_end[0] = (4 * npts[0] + qpd::KC - 1) / qpd::KC;
-  wa.kc_end[1] = wa.kc_end[0] + (npts[1] + qpd::KC - 1) / qpd::KC;
-  wa.kc_end[2] = wa.kc_end[1] + (npts[2] + qpd::KC - 1) / qpd::KC;
-  const int64_t rpc = wg_rows_per_chunk(n);
-  wa.nchunks = (int32_t)((wa.kc_end[2] * qpd::KC + rpc - 1) / rpc);
-  if (wa.nchunks < 1) wa.nchunks = 1;
+  wa.kc_end[0] = (4 * npts[0] + qpd::WKC - 1) / qpd::WKC;
+  wa.kc_end[1] = wa.kc_end[0] + (npts[1] + qpd::WKC - 1) / qpd::WKC;
+  wa.kc_end[2] = wa.kc_end[1] + (npts[2] + qpd::WKC - 1) / qpd::WKC;
+  const WgGeom wgm = wg_geom(pl, wa.kc_end[2]);
+  if (wgm.nslots > wg_geom(pl, (4 * P + qpd::WKC - 1) / qpd::WKC + 2).nslots) return QP_ERR_INTERNAL;
+  wa.tiles = wgm.tiles; wa.ngroups = wgm.ngroups; wa.spc = wgm.spc; wa.fl = wgm.fl;
   wa.status = (int32_t*)(ws + w.status);
-  const int tiles = (dim / qpd::TM) * (2 * dim / 256);
   if (pl->prof_start) cudaEventRecord(pl->prof_start, s);
-  qpd::dense_wgrad_gemm_kernel<<<dim3(tiles, wa.nchunks), qpd::WG_THREADS, qpd::wg_smem_bytes(), s>>>(wa);
+  qpd::dense_wgrad_gemm_kernel<<<wgm.tiles * wgm.ngroups, qpd::WG_THREADS, qpd::wg_smem_bytes(n), s>>>(wa);
   if (pl->prof_stop) cudaEventRecord(pl->prof_stop, s);
   launches += 1;
   qpd::SweepArgs sa;
-  sa.part = wa.part; sa.nchunks = wa.nchunks; sa.n = n; sa.L = L; sa.ansatz = pl->c.ansatz;
+  sa.part = wa.part; sa.nchunks = (int32_t)wgm.nslots; sa.n = n; sa.L = L; sa.ansatz = pl->c.ansatz;
   sa.U = (const double2*)(ws + w.dU); sa.G = (float2*)(ws + w.dG); sa.Y = (float2*)(ws + w.dY);
   sa.params = d_params; sa.circ_off = pl->circ_off; sa.eout = (float*)(ws + w.blk_grad);
   qpd::dense_gsum_kernel<<<(dim * dim + 255) / 256, 256, 0, s>>>(sa);

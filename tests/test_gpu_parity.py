@@ -183,7 +183,8 @@ def test_loss_grad_other_sizes(torch_cuda, oracle, n, L):
 
 @pytest.mark.parametrize("n,L,ans,enc,medium", [(7, 3, "strong_rot", "rx", "vacuum"),
                                                  (8, 4, "basic_ryrz", "ry", "dielectric"),
-                                                 (8, 6, "strong_rot", "rx", "dielectric")])
+                                                 (8, 6, "strong_rot", "rx", "dielectric"),
+                                                 (10, 2, "strong_rot", "rx", "vacuum")])
 def test_dense_tensorcore_loss_grad_parity(torch_cuda, oracle, n, L, ans, enc, medium):
     """Fused-unitary loss and gradient (tcgen05 forward and weight-gradient contractions,
     B-independent sweep): every loss term and every parameter against the oracle."""
