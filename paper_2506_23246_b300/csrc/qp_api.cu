@@ -59,8 +59,8 @@ struct WsLayout {
 // accumulation length; chunks are summed in FP64).
 int64_t wg_rows_per_chunk(int n) { return n <= 8 ? 512 : 4096; }
 
-// Weight-gradient launch geometry for `nkc` 16-row steps: tiles of 128 basis indices x
-// min(512, 2^(n+1)) components, CTA groups per tile (persistent CTAs, balanced step ranges),
+// Weight-gradient launch geometry for `nkc` 16-row steps: tiles of min(256, 2^n) basis
+// indices x 256 components, CTA groups per tile (persistent CTAs, balanced step ranges),
 // partial slots per CTA and steps per slot (at most wg_rows_per_chunk rows each).
 struct WgGeom {
   int tiles, ngroups, spc, fl;
@@ -69,8 +69,7 @@ struct WgGeom {
 WgGeom wg_geom(const qp_plan* pl, int64_t nkc) {
   WgGeom g;
   const int n = pl->c.n_qubits, dim = 1 << n;
-  const int nt = 2 * dim < 512 ? 2 * dim : 512;
-  g.tiles = (dim / qpd::TM) * (2 * dim / nt);
+  g.tiles = (dim / qpd::wg_mtc(n)) * (2 * dim / 256);
   g.ngroups = pl->sm_count / g.tiles > 0 ? pl->sm_count / g.tiles : 1;
   const int64_t per = nkc > 0 ? (nkc + g.ngroups - 1) / g.ngroups : 1;
   const int64_t flmax = wg_rows_per_chunk(n) / qpd::WKC;
@@ -467,7 +466,8 @@ static qp_status dense_loss_grad(qp_plan* pl, const float* d_params, const float
     // forward contraction with the pointwise stage as its epilogue (states stay on chip)
     qpd::FusedArgs fa;
     fa.thetaJ = (const float*)(ws + w.thetaJ); fa.W16 = (const float*)(ws + w.dW16);
-    fa.lam = (float2*)(ws + w.dphi); fa.head = d_params + pl->head_off;
+    fa.lam = (float*)(ws + w.dphi); fa.rtot = 4 * npts[0] + npts[1] + npts[2];
+    fa.head = d_params + pl->head_off;
     fa.n = n; fa.m = pl->c.n_readout;
     for (int i = 0; i < 3; ++i) { fa.pts[i] = pts[i]; fa.npts[i] = npts[i]; fa.pt_base[i] = base; base += npts[i]; }
     fa.tile_end[0] = (npts[0] + 31) / 32;
@@ -515,7 +515,8 @@ static qp_status dense_loss_grad(qp_plan* pl, const float* d_params, const float
     launches += 1;
   }
   qpd::WgArgs wa;
-  wa.thetaJ = (const float*)(ws + w.thetaJ); wa.lam = (const float2*)(ws + w.dphi);
+  wa.thetaJ = (const float*)(ws + w.thetaJ); wa.lam = (const float*)(ws + w.dphi);
+  wa.rtot = fused ? 4 * npts[0] + npts[1] + npts[2] : 0;
   wa.part = (float*)(ws + w.dpart); wa.n = n;
   base = 0;
   for (int i = 0; i < 3; ++i) { wa.npts[i] = npts[i]; wa.pt_base[i] = base; base += npts[i]; }
@@ -559,7 +560,8 @@ static qp_status dense_loss_grad(qp_plan* pl, const float* d_params, const float
       // mu rows on the tensor cores with the embedding gradients as the epilogue
       qpd::MuArgs ma;
       ma.thetaJ = (const float*)(ws + w.thetaJ); ma.WT = (const float*)(ws + w.dWT);
-      ma.lam = (const float*)(ws + w.dphi); ma.dthetaJ = (float*)(ws + w.dthetaJ); ma.n = n;
+      ma.lam = (const float*)(ws + w.dphi); ma.rtot = 4 * npts[0] + npts[1] + npts[2];
+      ma.dthetaJ = (float*)(ws + w.dthetaJ); ma.n = n;
       base = 0;
       for (int i = 0; i < 3; ++i) { ma.npts[i] = npts[i]; ma.pt_base[i] = base; base += npts[i]; }
       ma.tile_end[0] = (npts[0] + 31) / 32;

@@ -37,6 +37,14 @@ __host__ __device__ inline uint32_t core_off16(int r, int t) {
   return (uint32_t)((r >> 3) * (FKC / 4) * 128 + (t >> 2) * 128 + (r & 7) * 16 + (t & 3) * 4);
 }
 
+// Blocked costate layout of the fused path (n = 7, 8): [2^(n+1) / 256][rows][256] floats, rows
+// = 4 per collocation point (vector-major inside the point), then the IC and BC points with
+// one row each. A 16-row step of the weight-gradient contraction is one contiguous 16 KiB run
+// per 256-column block.
+__host__ __device__ inline int64_t lam_row(int set, int64_t p, int s, int64_t n0, int64_t base) {
+  return set == 0 ? p * 4 + s : 3 * n0 + base + p;
+}
+
 // ------------------------------------------------------------------------- unitary build
 struct BuildArgs {
   const float* params;

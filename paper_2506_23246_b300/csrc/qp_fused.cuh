@@ -22,7 +22,8 @@ constexpr int F_MAXH = 5;       // embedding qubits above the 3 lowest index bit
 struct FusedArgs {
   const float* thetaJ;     // [P][n] float4 (theta, dtheta/dx, dtheta/dy, dtheta/dt)
   const float* W16;        // [dim / FKC][nc][2 (hi, lo)][256 x FKC] operand blocks of W
-  float2* lam;             // [P][4][2^n] costates (output)
+  float* lam;              // costates (output), blocked layout [2^(n+1) / 256][rtot][256]
+  int64_t rtot;
   const float* head;       // W[3][m], b[3]
   int32_t n, m;
   const float* pts[3];
@@ -383,7 +384,7 @@ __global__ void __launch_bounds__(F_THREADS, 1) dense_fused_fwd_kernel(FusedArgs
       const int s_r = nv4 ? ws : 0;
       const int64_t pr = p0 + (nv4 ? lane : r);
       const bool act = pr < np;
-      float2* dst = a.lam + ((base + (act ? pr : 0)) * 4 + s_r) * (int64_t)dim;
+      const int64_t lrow = lam_row(set, act ? pr : 0, s_r, a.npts[0], base);
       for (int cc = 0; cc < half_cols; cc += 32) {
         const int col = hh * half_cols + cc;
         const int j0 = col >> 1;
@@ -437,7 +438,7 @@ __global__ void __launch_bounds__(F_THREADS, 1) dense_fused_fwd_kernel(FusedArgs
                                   O[2 * e + 1] * v[4 * e + 3]);
         }
         if (act) {
-          float4* d4 = reinterpret_cast<float4*>(dst + j0);
+          float4* d4 = reinterpret_cast<float4*>(a.lam + (int64_t)(col >> 8) * a.rtot * 256 + lrow * 256 + (col & 255));
 #pragma unroll
           for (int e = 0; e < 8; ++e) d4[e] = outv[e];
         }

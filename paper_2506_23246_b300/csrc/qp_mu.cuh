@@ -20,12 +20,18 @@ namespace qpd {
 struct MuArgs {
   const float* thetaJ;     // [P][n] float4
   const float* WT;         // transposed operand blocks (rows a = basis index, K = 2 dim)
-  const float* lam;        // [P][4][2 dim] costate rows
+  const float* lam;        // costate rows, blocked layout [2 dim / 256][rtot][256]
+  int64_t rtot;
   float* dthetaJ;          // [P][n] float4 (dL/dtheta, dL/dJ_x, dL/dJ_y, dL/dJ_t)
   int32_t n;
   int64_t npts[3], pt_base[3], tile_end[3];
   int32_t* status;
 };
+
+// float4 offset of K-chunk kc (KC costate components) from the start of a row's first block.
+__device__ __forceinline__ int64_t mu_koff(const MuArgs& a, int kc) {
+  return ((int64_t)(kc / (256 / KC)) * a.rtot * 256 + (kc % (256 / KC)) * KC) / 4;
+}
 
 __host__ __device__ inline int mu_smem_bytes(int n) { return gemm_smem_bytes(n, 1) + 2 * 4 * 32 * 8 * 4; }
 
@@ -216,7 +222,7 @@ __global__ void __launch_bounds__(128, 1) dense_mu_embed_kernel(MuArgs a) {
     const int64_t np = a.npts[set];
     p = p0 + (set == 0 ? lane : tid);
     const int64_t pc = p < np ? p : np - 1;
-    return reinterpret_cast<const float4*>(a.lam + ((a.pt_base[set] + pc) * 4 + (set == 0 ? warp : 0)) * (int64_t)ktot);
+    return reinterpret_cast<const float4*>(a.lam + lam_row(set, pc, set == 0 ? warp : 0, a.npts[0], a.pt_base[set]) * 256);
   };
   // the next K-step's eight float4 of the row are loaded one step ahead (software pipeline)
   float4 nxt[KC / 4];
@@ -258,7 +264,7 @@ __global__ void __launch_bounds__(128, 1) dense_mu_embed_kernel(MuArgs a) {
         float4 cur[KC / 4];
 #pragma unroll
         for (int g4 = 0; g4 < KC / 4; ++g4) cur[g4] = nxt[g4];
-        const float4* ns = kc + 1 < nkc ? src + (kc + 1) * (KC / 4) : src_next;
+        const float4* ns = kc + 1 < nkc ? src + mu_koff(a, kc + 1) : src_next;
         if (ns) {
 #pragma unroll
           for (int g4 = 0; g4 < KC / 4; ++g4) nxt[g4] = __ldg(ns + g4);

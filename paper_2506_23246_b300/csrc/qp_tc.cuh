@@ -123,4 +123,14 @@ __device__ __forceinline__ void split_tf32(float x, float& hi, float& lo) {
   lo = __uint_as_float(l);
 }
 
+// TF32 split for an operand whose remainder goes to the tensor core as is: hi rounded to
+// TF32, lo = x - hi exact in FP32; the MMA reads lo's top 19 bits, an error of at most
+// 2^-22 |x| (|lo| <= 2^-11 |x|).
+__device__ __forceinline__ void split_tf32_fast(float x, float& hi, float& lo) {
+  uint32_t h;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h) : "f"(x));
+  hi = __uint_as_float(h);
+  lo = x - hi;
+}
+
 }  // namespace qptc

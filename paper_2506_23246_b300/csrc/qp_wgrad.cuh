@@ -6,26 +6,35 @@
 namespace qpd {
 
 // ------------------------------------------------------------------------- weight-gradient GEMM
-// G_part[slot][k][o] = sum over the slot's (point, vector) rows of R_s[k] * Lambda_s[o]:
-// M = 128 basis indices k, N = min(512, 2^(n+1)) costate components o = (amp, re|im) as one or
-// two N = 256 MMAs (all of the row's components in one CTA: R is generated once), K = 16
-// (point, vector) rows per step. Steps never straddle point sets: a collocation step holds
-// 4 points x 4 vectors (rows consecutive in the costate buffer), an IC/BC step 16 points x 1.
+// G_part[slot][k][o] = sum over the slot's (point, vector) rows of R_s[k] * Lambda_s[o]. A CTA
+// tile covers MTC = min(256, 2^n) basis indices k (one or two M = 128 MMAs) x 256 costate
+// components o = (amp, re|im) (N = 256), so tensor memory holds the whole tile (<= 512
+// columns) and every costate element is read by one CTA only. K = 16 (point, vector) rows per
+// step; steps never straddle point sets: a collocation step holds 4 points x 4 vectors (rows
+// consecutive in the costate buffer), an IC/BC step 16 points x 1 vector.
 //
-// R comes from per-point tables: k = (high bits, 5 low bits); the low five qubits give a
-// 32-entry table Lo, the others (bits 5, 6 vary inside a 128-row tile) a 4-entry table H,
-// both as a value and its three tangents (forward-mode duals), so each element of R is one
-// dual product H[k >> 5] x Lo[k & 31].
+// R comes from per-point tables: k = (high bits, 5 low bits); the five low qubits give a
+// 32-entry table Lo, the others an 8-entry table H over the bits 5-7 of k inside the tile
+// (higher bits fixed by the tile), both as a value and its three tangents (forward-mode
+// duals), so each element of R is one dual product H[k >> 5] x Lo[k & 31].
 //
-// Persistent CTAs: CTA b owns tile b % tiles and a balanced range of K-steps; every `fl`
-// steps (<= 512 rows, the FP32 accumulation length) the tensor-memory accumulator is flushed
-// to its own partial slot, summed later in compensated FP32.
+// Persistent CTAs: CTA b owns tile b % tiles and a balanced range of steps; every `fl` steps
+// (<= 512 rows, the FP32 accumulation length) the accumulator is flushed to its own partial
+// slot, summed later in compensated FP32.
+//
+// Pipeline of one step (3 block barriers): the costate rows arrive in a 4-slot shared-memory
+// ring by bulk copies issued three steps ahead; the step's R tables were built during the
+// previous step and their angle factors the step before. A step writes its A operand from the
+// tables, builds the next tables and factors, reads its costate columns, starts the copy three
+// steps ahead, splits the columns into the TF32 B operand, and one thread issues the MMAs.
 constexpr int WKC = 16;
 constexpr int WG_THREADS = 256;
+constexpr int WG_RING = 4;
 
 struct WgArgs {
   const float* thetaJ;        // [P][n] float4
-  const float2* lam;          // [P][4][dim]
+  const float* lam;           // costate rows: blocked [2 dim / 256][rtot][256] or rows [P][4][2 dim]
+  int64_t rtot;               // rows of the blocked layout (0: row layout)
   float* part;                // [nslots][dim][2 dim]
   int32_t n;
   int64_t npts[3], pt_base[3];
@@ -35,61 +44,48 @@ struct WgArgs {
 };
 
 struct WgSmem {
-  int a_bytes, b_bytes, stage, fac, lo, hi, bars, total;
+  int a_bytes, b_bytes, stage, raw, fac, tab, bars, total;
 };
+constexpr int WG_TAB4 = 16 * 32 + 16 * 8;                 // Lo [16 pts][32], H [16 pts][8] float4
+constexpr int WG_FAC4 = 16 * QP_MAXQ * 2;                 // [16 pts][q][2] float4
+__host__ __device__ inline int wg_mtc(int n) { return (1 << n) < 256 ? (1 << n) : 256; }
 __host__ __device__ inline WgSmem wg_smem(int n) {
   WgSmem w;
-  const int nt = (2 << n) < 512 ? (2 << n) : 512;
-  w.a_bytes = TM * WKC * 4;
-  w.b_bytes = nt * WKC * 4;
-  w.stage = 2 * w.a_bytes + 2 * w.b_bytes;
+  w.a_bytes = (wg_mtc(n) / TM) * 2 * TM * WKC * 4;   // hi, lo per M sub-tile
+  w.b_bytes = 2 * 256 * WKC * 4;                     // hi, lo
+  w.stage = w.a_bytes + w.b_bytes;
   int o = 2 * w.stage;
-  w.fac = o; o += 2 * 16 * QP_MAXQ * 2 * 16;   // [2][16 pts][q][2] float4
-  w.lo = o; o += 16 * 32 * 16;                 // [16 pts][32] float4
-  w.hi = o; o += 16 * 4 * 16;                  // [16 pts][4] float4
-  w.bars = o; o += 64;
+  w.raw = o; o += WG_RING * WKC * 256 * 4;           // costate columns of a step [16][256]
+  w.fac = o; o += 2 * WG_FAC4 * 16;
+  w.tab = o; o += 2 * WG_TAB4 * 16;
+  w.bars = o; o += 64;                               // mma_done[2], raw_full[4], tmem slot
   w.total = o;
   return w;
 }
 __host__ inline int wg_smem_bytes(int n) { return wg_smem(n).total; }
 
-__device__ __forceinline__ void wg_step_geom(const WgArgs& a, int64_t kc, int& set, int64_t& p0, int& ppc) {
+__device__ __forceinline__ void wg_step_geom(const WgArgs& a, int64_t kc, int& set, int64_t& p0, int& ppc,
+                                             int& nvalid) {
   set = kc < a.kc_end[0] ? 0 : (kc < a.kc_end[1] ? 1 : 2);
   const int64_t ck = kc - (set == 0 ? 0 : a.kc_end[set - 1]);
   ppc = set == 0 ? 4 : 16;
   p0 = ck * ppc;
+  const int64_t left = (a.npts[set] - p0) * (set == 0 ? 4 : 1);
+  nvalid = (int)(left < WKC ? left : WKC);
 }
 
-// Costate values of one step for this thread's components o (one per N half) and the raw
-// angle entry (theta, J) of the (point, qubit) pair this thread stages.
-struct WgLoads {
-  float lam[2][WKC];
-  float4 tj;
-};
-__device__ __forceinline__ void wg_load(const WgArgs& a, int64_t kc, int tid, int o0, int nhalf, WgLoads& f) {
-  const int n = a.n, dim = 1 << n;
-  int set, ppc;
+// Raw angle entry (theta, J) of the (point, qubit) pair `tid` of step kc.
+__device__ __forceinline__ float4 wg_load_tj(const WgArgs& a, int64_t kc, int tid) {
+  int set, ppc, nv;
   int64_t p0;
-  wg_step_geom(a, kc, set, p0, ppc);
-  const int64_t np = a.npts[set];
-  const float* lamf = reinterpret_cast<const float*>(a.lam);
-  const int64_t row0 = (a.pt_base[set] + p0) * 4;
-  const int rstep = set == 0 ? 1 : 4;
-  const int nvalid = set == 0 ? (int)((np - p0) * 4 < WKC ? (np - p0) * 4 : WKC)
-                              : (int)(np - p0 < WKC ? np - p0 : WKC);
-#pragma unroll
-  for (int h = 0; h < 2; ++h) {
-#pragma unroll
-    for (int t = 0; t < WKC; ++t)
-      f.lam[h][t] = (h < nhalf && t < nvalid) ? __ldg(lamf + (row0 + (int64_t)t * rstep) * (2 * dim) + o0 + h * 256) : 0.f;
-  }
-  const int pl = tid / n, q = tid % n;
-  f.tj = make_float4(0.f, 0.f, 0.f, 0.f);
-  if (tid < ppc * n && p0 + pl < np)
-    f.tj = __ldg(reinterpret_cast<const float4*>(a.thetaJ) + (a.pt_base[set] + p0 + pl) * n + q);
+  wg_step_geom(a, kc, set, p0, ppc, nv);
+  const int n = a.n, pl = tid / n, q = tid % n;
+  if (tid < ppc * n && p0 + pl < a.npts[set])
+    return __ldg(reinterpret_cast<const float4*>(a.thetaJ) + (a.pt_base[set] + p0 + pl) * n + q);
+  return make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
-// Per (point, qubit) factors: (cos, sin of theta/2, J_x, J_y), (J_t, valid, ., .).
+// Per (point, qubit) factors: (cos, sin of theta/2, J_x, J_y), (J_t, ., ., .).
 __device__ __forceinline__ void wg_fac(float4* fac, int tid, int n, int ppc, const float4& tq) {
   if (tid < ppc * n) {
     float sn, cs;
@@ -105,22 +101,76 @@ __device__ __forceinline__ float4 wg_dmul(const float4& p, const float4& f0, con
   return make_float4(p.x * f, p.y * f + p.x * d * f0.z, p.z * f + p.x * d * f0.w, p.w * f + p.x * d * f1.x);
 }
 
+// Tables of one step: Lo over the five low qubits, H over the others for k = kbase + 32 j.
+__device__ __forceinline__ void wg_tables(const float4* fac, float4* tab, int tid, int n, int ppc, int kbase,
+                                          int nj) {
+  float4* tlo = tab;
+  float4* thi = tab + 16 * 32;
+  for (int idx = tid; idx < ppc * 32; idx += WG_THREADS) {
+    const int pl = idx >> 5, e = idx & 31;
+    float4 p = make_float4(1.f, 0.f, 0.f, 0.f);
+#pragma unroll
+    for (int b = 4; b >= 0; --b) {
+      const int q = n - 1 - b;
+      p = wg_dmul(p, fac[(pl * n + q) * 2], fac[(pl * n + q) * 2 + 1], (e >> b) & 1);
+    }
+    tlo[idx] = p;
+  }
+  for (int idx = tid; idx < ppc * 8; idx += WG_THREADS) {
+    const int pl = idx >> 3, j = idx & 7;
+    if (j < nj) {
+      const int kb = kbase + j * 32;
+      float4 p = make_float4(1.f, 0.f, 0.f, 0.f);
+      for (int q = 0; q < n - 5; ++q)
+        p = wg_dmul(p, fac[(pl * n + q) * 2], fac[(pl * n + q) * 2 + 1], (kb >> (n - 1 - q)) & 1);
+      thi[idx] = p;
+    }
+  }
+}
+
+// Bulk copies of the valid costate rows of step kc (this tile's 256 columns) into `raw`.
+__device__ __forceinline__ void wg_copy_rows(const WgArgs& a, int64_t kc, int ntile, float* raw, uint64_t* bar) {
+  const int dim = 1 << a.n;
+  int set, ppc, nv;
+  int64_t p0;
+  wg_step_geom(a, kc, set, p0, ppc, nv);
+  const uint32_t rowb = 256 * 4;
+  qptc::mbar_arrive_expect_tx(bar, nv * rowb);
+  const float* lamf = a.lam;
+  const int64_t row0 = (a.pt_base[set] + p0) * 4;
+  if (a.rtot > 0) {
+    // blocked layout: the step's rows are consecutive in every 256-column block
+    const int64_t r0 = lam_row(set, p0, 0, a.npts[0], a.pt_base[set]);
+    qptc::bulk_g2s(raw, lamf + ((int64_t)ntile * a.rtot + r0) * 256, nv * rowb, bar);
+  } else if (set == 0 && 2 * dim == 256) {
+    qptc::bulk_g2s(raw, lamf + row0 * (2 * dim), nv * rowb, bar);
+  } else {
+    const int rstep = set == 0 ? 1 : 4;
+    for (int t = 0; t < nv; ++t)
+      qptc::bulk_g2s(raw + t * 256, lamf + (row0 + (int64_t)t * rstep) * (2 * dim) + ntile * 256, rowb, bar);
+  }
+}
+
 __global__ void __launch_bounds__(WG_THREADS, 1) dense_wgrad_gemm_kernel(WgArgs a) {
   extern __shared__ __align__(1024) unsigned char sm[];
   const int n = a.n, dim = 1 << n;
   const WgSmem L = wg_smem(n);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int NT = (2 << n) < 512 ? (2 << n) : 512, nhalf = NT / 256;
+  const int MTC = wg_mtc(n), msub = MTC / TM, nj = MTC / 32;
   const int tile = blockIdx.x % a.tiles, lb = blockIdx.x / a.tiles;
-  const int nmt = dim / TM;
-  const int mt = tile % nmt, nt = tile / nmt;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(sm + L.bars);  // mma_done[2]
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + L.bars + 32);
+  const int nmt = dim / MTC;
+  const int mtile = tile % nmt, ntile = tile / nmt;
+  const int kbase = mtile * MTC;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sm + L.bars);  // mma_done[2], raw_full[4]
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + L.bars + 48);
+  float* raw = reinterpret_cast<float*>(sm + L.raw);
   float4* facb = reinterpret_cast<float4*>(sm + L.fac);
-  float4* tlo = reinterpret_cast<float4*>(sm + L.lo);
-  float4* thi = reinterpret_cast<float4*>(sm + L.hi);
-  if (warp == 0) qptc::tmem_alloc(tslot, NT);
-  if (tid == 0) { qptc::mbar_init(&bars[0], 1); qptc::mbar_init(&bars[1], 1); }
+  float4* tabb = reinterpret_cast<float4*>(sm + L.tab);
+  const uint32_t tcols = msub * 256;
+  if (warp == 0) qptc::tmem_alloc(tslot, tcols);
+  if (tid == 0) {
+    for (int i = 0; i < 2 + WG_RING; ++i) qptc::mbar_init(&bars[i], 1);
+  }
   qptc::fence_before();
   __syncthreads();
   qptc::fence_after();
@@ -128,33 +178,47 @@ __global__ void __launch_bounds__(WG_THREADS, 1) dense_wgrad_gemm_kernel(WgArgs 
   const uint32_t id = qptc::idesc(2, TM, 256);
   const int64_t nkc = a.kc_end[2];
   const int64_t c0 = (int64_t)lb * nkc / a.ngroups, c1 = (int64_t)(lb + 1) * nkc / a.ngroups;
-  const int o0 = nt * NT + tid;          // costate components staged by this thread (+256)
   const int kk = tid & (TM - 1), khalf = tid >> 7;
   bool ok = true;
   uint32_t it = 0;
-  int64_t last_commit = -1;
+  int64_t last_commit = -1, last_copy = -1;
   int slot = 0;
   bool fresh = true;                     // next MMA starts a new partial
-  WgLoads cur, nxt;
+  float4 tjn = make_float4(0.f, 0.f, 0.f, 0.f);  // angles of step c0 + it + 2
   if (c0 < c1) {
-    int set, ppc;
+    int set, ppc, nv;
     int64_t p0;
-    wg_step_geom(a, c0, set, p0, ppc);
-    wg_load(a, c0, tid, o0, nhalf, cur);
-    wg_fac(facb + (c0 & 1) * (16 * QP_MAXQ * 2), tid, n, ppc, cur.tj);
-    if (c0 + 1 < c1) wg_load(a, c0 + 1, tid, o0, nhalf, nxt);
+    wg_step_geom(a, c0, set, p0, ppc, nv);
+    wg_fac(facb, tid, n, ppc, wg_load_tj(a, c0, tid));
+    if (c0 + 1 < c1) {
+      int set1, ppc1, nv1;
+      int64_t p01;
+      wg_step_geom(a, c0 + 1, set1, p01, ppc1, nv1);
+      wg_fac(facb + WG_FAC4, tid, n, ppc1, wg_load_tj(a, c0 + 1, tid));
+    }
+    if (c0 + 2 < c1) tjn = wg_load_tj(a, c0 + 2, tid);
+    if (tid == 0) {
+      for (int j = 0; j < WG_RING - 1 && c0 + j < c1; ++j) {
+        wg_copy_rows(a, c0 + j, ntile, raw + j * (WKC * 256), &bars[2 + j]);
+        last_copy = j;
+      }
+    }
+    __syncthreads();
+    wg_tables(facb, tabb, tid, n, ppc, kbase, nj);
   }
   __syncthreads();
-  // epilogue of one partial: 128 x NT accumulator -> part[slot]; warps w, w + 4 share lanes
+  // epilogue of one partial: the MTC x 256 accumulator -> part[slot]
   auto flush = [&](int sl, bool zero) {
-    const int lrow = (warp & 3) * 32 + lane, chalf = warp >> 2;
-    const int ncols = NT / 2;
-    float* outp = a.part + (((int64_t)(lb * a.spc + sl) * dim) + mt * TM + lrow) * (2 * dim) + nt * NT + chalf * ncols;
+    const int g = warp & 3, hw = warp >> 2;
+    const int u = msub == 2 ? hw : 0;                 // M sub-tile read by this warp
+    const int cbeg = msub == 2 ? 0 : hw * 128, ncols = msub == 2 ? 256 : 128;
+    const int64_t krow = kbase + u * TM + g * 32 + lane;
+    float* outp = a.part + (((int64_t)(lb * a.spc + sl) * dim) + krow) * (2 * dim) + ntile * 256 + cbeg;
     if (!zero) {
       qptc::fence_after();
       float v[32];
       for (int c = 0; c < ncols; c += 32) {
-        qptc::tmem_ld32(tmem + ((uint32_t)((warp & 3) * 32) << 16) + chalf * ncols + c, v);
+        qptc::tmem_ld32(tmem + ((uint32_t)(g * 32) << 16) + u * 256 + cbeg + c, v);
 #pragma unroll
         for (int e = 0; e < 8; ++e)
           reinterpret_cast<float4*>(outp + c)[e] = make_float4(v[4 * e], v[4 * e + 1], v[4 * e + 2], v[4 * e + 3]);
@@ -167,95 +231,101 @@ __global__ void __launch_bounds__(WG_THREADS, 1) dense_wgrad_gemm_kernel(WgArgs 
   for (int64_t kc = c0; kc < c1 && ok; ++kc, ++it) {
     const uint32_t st = it & 1;
     unsigned char* sA = sm + st * L.stage;
-    unsigned char* sB = sA + 2 * L.a_bytes;
-    int set, ppc;
+    unsigned char* sB = sA + L.a_bytes;
+    int set, ppc, nvalid;
     int64_t p0;
-    wg_step_geom(a, kc, set, p0, ppc);
+    wg_step_geom(a, kc, set, p0, ppc, nvalid);
     bool w_ok = true;
     if (it >= 2) w_ok = qptc::mbar_wait(&bars[st], ((it - 2) >> 1) & 1);
-    ok = __syncthreads_and(w_ok);   // also orders the previous step's reads of the tables
+    ok = __syncthreads_and(w_ok);
     if (!ok) break;
-    const float4* fac = facb + (kc & 1) * (16 * QP_MAXQ * 2);
-    // tables of this step: Lo over the five low qubits, H over the others for k >> 5 in tile
-    for (int idx = tid; idx < ppc * 32; idx += WG_THREADS) {
-      const int pl = idx >> 5, e = idx & 31;
-      float4 p = make_float4(1.f, 0.f, 0.f, 0.f);
-#pragma unroll
-      for (int b = 4; b >= 0; --b) {
-        const int q = n - 1 - b;
-        p = wg_dmul(p, fac[(pl * n + q) * 2], fac[(pl * n + q) * 2 + 1], (e >> b) & 1);
-      }
-      tlo[idx] = p;
-    }
-    for (int idx = tid; idx < ppc * 4; idx += WG_THREADS) {
-      const int pl = idx >> 2, j = idx & 3;
-      const int kb = mt * TM + j * 32;
-      float4 p = make_float4(1.f, 0.f, 0.f, 0.f);
-      for (int q = 0; q < n - 5; ++q)
-        p = wg_dmul(p, fac[(pl * n + q) * 2], fac[(pl * n + q) * 2 + 1], (kb >> (n - 1 - q)) & 1);
-      thi[idx] = p;
-    }
-    // factors of the next step (other buffer) and B staging of this step
-    if (kc + 1 < c1) {
-      int set1, ppc1;
-      int64_t p01;
-      wg_step_geom(a, kc + 1, set1, p01, ppc1);
-      wg_fac(facb + ((kc + 1) & 1) * (16 * QP_MAXQ * 2), tid, n, ppc1, nxt.tj);
-    }
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      if (h < nhalf) {
-        float* Bhi = reinterpret_cast<float*>(sB + h * 2 * (256 * WKC * 4));
-        float* Blo = Bhi + 256 * WKC;
-#pragma unroll
-        for (int g4 = 0; g4 < WKC / 4; ++g4) {
-          float4 h4, l4;
-          qptc::split_tf32(cur.lam[h][4 * g4], h4.x, l4.x);
-          qptc::split_tf32(cur.lam[h][4 * g4 + 1], h4.y, l4.y);
-          qptc::split_tf32(cur.lam[h][4 * g4 + 2], h4.z, l4.z);
-          qptc::split_tf32(cur.lam[h][4 * g4 + 3], h4.w, l4.w);
-          const uint32_t off = core_off16(tid, g4 * 4) / 4;
-          *reinterpret_cast<float4*>(Bhi + off) = h4;
-          *reinterpret_cast<float4*>(Blo + off) = l4;
-        }
-      }
-    }
-    // global loads two steps ahead are in flight while this step is generated and multiplied
-    cur = nxt;
-    if (kc + 2 < c1) wg_load(a, kc + 2, tid, o0, nhalf, nxt);
-    __syncthreads();  // tables visible
+    // A operand of this step from its tables
     {
-      float av[8];
-      const int j = kk >> 5, e = kk & 31;
-      if (set == 0) {
+      const float4* tlo = tabb + (it & 1) * WG_TAB4;
+      const float4* thi = tlo + 16 * 32;
+      const int e = kk & 31;
 #pragma unroll
-        for (int pi = 0; pi < 2; ++pi) {
-          const int pl = khalf * 2 + pi;
-          const float4 h = thi[pl * 4 + j], l = tlo[pl * 32 + e];
-          av[4 * pi] = h.x * l.x;
-          av[4 * pi + 1] = h.y * l.x + h.x * l.y;
-          av[4 * pi + 2] = h.z * l.x + h.x * l.z;
-          av[4 * pi + 3] = h.w * l.x + h.x * l.w;
-        }
-      } else {
+      for (int u = 0; u < 2; ++u) {
+        if (u < msub) {
+          const int j = (u * TM + kk) >> 5;
+          float av[8];
+          if (set == 0) {
 #pragma unroll
-        for (int pi = 0; pi < 8; ++pi) {
-          const int pl = khalf * 8 + pi;
-          av[pi] = thi[pl * 4 + j].x * tlo[pl * 32 + e].x;
+            for (int pi = 0; pi < 2; ++pi) {
+              const int pl = khalf * 2 + pi;
+              const float4 h = thi[pl * 8 + j], l = tlo[pl * 32 + e];
+              av[4 * pi] = h.x * l.x;
+              av[4 * pi + 1] = h.y * l.x + h.x * l.y;
+              av[4 * pi + 2] = h.z * l.x + h.x * l.z;
+              av[4 * pi + 3] = h.w * l.x + h.x * l.w;
+            }
+          } else {
+#pragma unroll
+            for (int pi = 0; pi < 8; ++pi) {
+              const int pl = khalf * 8 + pi;
+              av[pi] = thi[pl * 8 + j].x * tlo[pl * 32 + e].x;
+            }
+          }
+          float* Ahi = reinterpret_cast<float*>(sA + u * 2 * (TM * WKC * 4));
+          float* Alo = Ahi + TM * WKC;
+#pragma unroll
+          for (int g4 = 0; g4 < 2; ++g4) {
+            float4 h4, l4;
+            qptc::split_tf32_fast(av[4 * g4], h4.x, l4.x);
+            qptc::split_tf32_fast(av[4 * g4 + 1], h4.y, l4.y);
+            qptc::split_tf32_fast(av[4 * g4 + 2], h4.z, l4.z);
+            qptc::split_tf32_fast(av[4 * g4 + 3], h4.w, l4.w);
+            const uint32_t off = core_off16(kk, khalf * 8 + g4 * 4) / 4;
+            *reinterpret_cast<float4*>(Ahi + off) = h4;
+            *reinterpret_cast<float4*>(Alo + off) = l4;
+          }
         }
       }
-      float* Ahi = reinterpret_cast<float*>(sA);
-      float* Alo = reinterpret_cast<float*>(sA + L.a_bytes);
+    }
+    // tables of the next step, factors of the step after
+    if (kc + 1 < c1) {
+      int set1, ppc1, nv1;
+      int64_t p01;
+      wg_step_geom(a, kc + 1, set1, p01, ppc1, nv1);
+      wg_tables(facb + ((it + 1) & 1) * WG_FAC4, tabb + ((it + 1) & 1) * WG_TAB4, tid, n, ppc1, kbase, nj);
+    }
+    if (kc + 2 < c1) {
+      int set2, ppc2, nv2;
+      int64_t p02;
+      wg_step_geom(a, kc + 2, set2, p02, ppc2, nv2);
+      wg_fac(facb + (it & 1) * WG_FAC4, tid, n, ppc2, tjn);
+      if (kc + 3 < c1) tjn = wg_load_tj(a, kc + 3, tid);
+    }
+    // this step's costate columns (bulk-copied three steps ago)
+    float lv[WKC];
+    {
+      const uint32_t rs = it % WG_RING;
+      if (!qptc::mbar_wait(&bars[2 + rs], (it / WG_RING) & 1)) ok = false;
+      const float* rr = raw + rs * (WKC * 256);
 #pragma unroll
-      for (int g4 = 0; g4 < 2; ++g4) {
+      for (int t = 0; t < WKC; ++t) lv[t] = t < nvalid ? rr[t * 256 + tid] : 0.f;
+    }
+    ok = __syncthreads_and(ok);   // the ring slot is consumed; tables and factors written
+    if (!ok) break;
+    if (tid == 0 && kc + WG_RING - 1 < c1) {
+      const uint32_t rs = (it + WG_RING - 1) % WG_RING;
+      qptc::fence_proxy_async();
+      wg_copy_rows(a, kc + WG_RING - 1, ntile, raw + rs * (WKC * 256), &bars[2 + rs]);
+      last_copy = it + WG_RING - 1;
+    }
+    {
+      float* Bhi = reinterpret_cast<float*>(sB);
+      float* Blo = Bhi + 256 * WKC;
+#pragma unroll
+      for (int g4 = 0; g4 < WKC / 4; ++g4) {
         float4 h4, l4;
-        qptc::split_tf32(av[4 * g4], h4.x, l4.x);
-        qptc::split_tf32(av[4 * g4 + 1], h4.y, l4.y);
-        qptc::split_tf32(av[4 * g4 + 2], h4.z, l4.z);
-        qptc::split_tf32(av[4 * g4 + 3], h4.w, l4.w);
-        const uint32_t off = core_off16(kk, khalf * 8 + g4 * 4) / 4;
-        *reinterpret_cast<float4*>(Ahi + off) = h4;
-        *reinterpret_cast<float4*>(Alo + off) = l4;
+        qptc::split_tf32_fast(lv[4 * g4], h4.x, l4.x);
+        qptc::split_tf32_fast(lv[4 * g4 + 1], h4.y, l4.y);
+        qptc::split_tf32_fast(lv[4 * g4 + 2], h4.z, l4.z);
+        qptc::split_tf32_fast(lv[4 * g4 + 3], h4.w, l4.w);
+        const uint32_t off = core_off16(tid, g4 * 4) / 4;
+        *reinterpret_cast<float4*>(Bhi + off) = h4;
+        *reinterpret_cast<float4*>(Blo + off) = l4;
       }
     }
     qptc::fence_proxy_async();
@@ -263,15 +333,15 @@ __global__ void __launch_bounds__(WG_THREADS, 1) dense_wgrad_gemm_kernel(WgArgs 
     if (tid == 0) {
       qptc::fence_after();
       const uint32_t sa = qptc::smem_u32(sA), sb = qptc::smem_u32(sB);
-      const uint32_t bblk = 256 * WKC * 4;
+      const uint32_t ablk = TM * WKC * 4, bblk = 256 * WKC * 4;
 #pragma unroll
       for (int ks = 0; ks < WKC / 8; ++ks) {
-        const uint64_t ah = qptc::desc_kmajor(sa + ks * 256, 128, (WKC / 4) * 128);
-        const uint64_t al = qptc::desc_kmajor(sa + L.a_bytes + ks * 256, 128, (WKC / 4) * 128);
-        for (int h = 0; h < nhalf; ++h) {
-          const uint64_t bh = qptc::desc_kmajor(sb + h * 2 * bblk + ks * 256, 128, (WKC / 4) * 128);
-          const uint64_t bl = qptc::desc_kmajor(sb + h * 2 * bblk + bblk + ks * 256, 128, (WKC / 4) * 128);
-          const uint32_t dt = tmem + h * 256;
+        const uint64_t bh = qptc::desc_kmajor(sb + ks * 256, 128, (WKC / 4) * 128);
+        const uint64_t bl = qptc::desc_kmajor(sb + bblk + ks * 256, 128, (WKC / 4) * 128);
+        for (int u = 0; u < msub; ++u) {
+          const uint64_t ah = qptc::desc_kmajor(sa + u * 2 * ablk + ks * 256, 128, (WKC / 4) * 128);
+          const uint64_t al = qptc::desc_kmajor(sa + u * 2 * ablk + ablk + ks * 256, 128, (WKC / 4) * 128);
+          const uint32_t dt = tmem + u * 256;
           qptc::mma_tf32(dt, ah, bh, id, (fresh && ks == 0) ? 0u : 1u);
           qptc::mma_tf32(dt, ah, bl, id, 1u);
           qptc::mma_tf32(dt, al, bh, id, 1u);
@@ -295,12 +365,15 @@ __global__ void __launch_bounds__(WG_THREADS, 1) dense_wgrad_gemm_kernel(WgArgs 
   } else {
     if (tid == 0) {
       atomicExch(a.status, 6);
+      // let every bulk copy and tensor-core operation of this CTA land before exiting
+      for (int64_t j = last_copy - (WG_RING - 1) < 0 ? 0 : last_copy - (WG_RING - 1); j <= last_copy; ++j)
+        qptc::mbar_wait(&bars[2 + (j % WG_RING)], (uint32_t)(j / WG_RING) & 1);
       if (last_commit >= 0) qptc::mbar_wait(&bars[last_commit & 1], ((uint32_t)last_commit >> 1) & 1);
     }
   }
   qptc::fence_before();
   __syncthreads();
-  if (warp == 0) qptc::tmem_dealloc(tmem, NT);
+  if (warp == 0) qptc::tmem_dealloc(tmem, tcols);
 }
 
 }  // namespace qpd
