@@ -28,7 +28,7 @@ namespace qpd {
 // tables, builds the next tables and factors, reads its costate columns, starts the copy three
 // steps ahead, splits the columns into the TF32 B operand, and one thread issues the MMAs.
 constexpr int WKC = 16;
-constexpr int WG_THREADS = 256;
+constexpr int WG_THREADS = 512;
 constexpr int WG_RING = 4;
 
 struct WgArgs {
@@ -178,7 +178,7 @@ __global__ void __launch_bounds__(WG_THREADS, 1) dense_wgrad_gemm_kernel(WgArgs 
   const uint32_t id = qptc::idesc(2, TM, 256);
   const int64_t nkc = a.kc_end[2];
   const int64_t c0 = (int64_t)lb * nkc / a.ngroups, c1 = (int64_t)(lb + 1) * nkc / a.ngroups;
-  const int kk = tid & (TM - 1), khalf = tid >> 7;
+  const int kk = tid & (TM - 1), khalf = tid >> 8;
   bool ok = true;
   uint32_t it = 0;
   int64_t last_commit = -1, last_copy = -1;
@@ -209,9 +209,9 @@ __global__ void __launch_bounds__(WG_THREADS, 1) dense_wgrad_gemm_kernel(WgArgs 
   __syncthreads();
   // epilogue of one partial: the MTC x 256 accumulator -> part[slot]
   auto flush = [&](int sl, bool zero) {
-    const int g = warp & 3, hw = warp >> 2;
-    const int u = msub == 2 ? hw : 0;                 // M sub-tile read by this warp
-    const int cbeg = msub == 2 ? 0 : hw * 128, ncols = msub == 2 ? 256 : 128;
+    const int g = warp & 3, qw = warp >> 2;          // lane group, quarter of the columns
+    const int u = msub == 2 ? qw >> 1 : 0;            // M sub-tile read by this warp
+    const int cbeg = msub == 2 ? (qw & 1) * 128 : qw * 64, ncols = msub == 2 ? 128 : 64;
     const int64_t krow = kbase + u * TM + g * 32 + lane;
     float* outp = a.part + (((int64_t)(lb * a.spc + sl) * dim) + krow) * (2 * dim) + ntile * 256 + cbeg;
     if (!zero) {
@@ -239,13 +239,13 @@ __global__ void __launch_bounds__(WG_THREADS, 1) dense_wgrad_gemm_kernel(WgArgs 
     if (it >= 2) w_ok = qptc::mbar_wait(&bars[st], ((it - 2) >> 1) & 1);
     ok = __syncthreads_and(w_ok);
     if (!ok) break;
-    // A operand of this step from its tables
+    // A operand of this step from its tables: thread -> (k, M sub-tile, half of the rows)
     {
       const float4* tlo = tabb + (it & 1) * WG_TAB4;
       const float4* thi = tlo + 16 * 32;
       const int e = kk & 31;
-#pragma unroll
-      for (int u = 0; u < 2; ++u) {
+      {
+        const int u = (tid >> 7) & 1;
         if (u < msub) {
           const int j = (u * TM + kk) >> 5;
           float av[8];
@@ -297,13 +297,17 @@ __global__ void __launch_bounds__(WG_THREADS, 1) dense_wgrad_gemm_kernel(WgArgs 
       if (kc + 3 < c1) tjn = wg_load_tj(a, kc + 3, tid);
     }
     // this step's costate columns (bulk-copied three steps ago)
-    float lv[WKC];
+    float lv[WKC / 2];
+    const int bo = tid & 255, bh = tid >> 8;   // component and half of the rows staged here
     {
       const uint32_t rs = it % WG_RING;
       if (!qptc::mbar_wait(&bars[2 + rs], (it / WG_RING) & 1)) ok = false;
       const float* rr = raw + rs * (WKC * 256);
 #pragma unroll
-      for (int t = 0; t < WKC; ++t) lv[t] = t < nvalid ? rr[t * 256 + tid] : 0.f;
+      for (int t = 0; t < WKC / 2; ++t) {
+        const int row = bh * (WKC / 2) + t;
+        lv[t] = row < nvalid ? rr[row * 256 + bo] : 0.f;
+      }
     }
     ok = __syncthreads_and(ok);   // the ring slot is consumed; tables and factors written
     if (!ok) break;
@@ -317,13 +321,13 @@ __global__ void __launch_bounds__(WG_THREADS, 1) dense_wgrad_gemm_kernel(WgArgs 
       float* Bhi = reinterpret_cast<float*>(sB);
       float* Blo = Bhi + 256 * WKC;
 #pragma unroll
-      for (int g4 = 0; g4 < WKC / 4; ++g4) {
+      for (int g4 = 0; g4 < WKC / 8; ++g4) {
         float4 h4, l4;
         qptc::split_tf32_fast(lv[4 * g4], h4.x, l4.x);
         qptc::split_tf32_fast(lv[4 * g4 + 1], h4.y, l4.y);
         qptc::split_tf32_fast(lv[4 * g4 + 2], h4.z, l4.z);
         qptc::split_tf32_fast(lv[4 * g4 + 3], h4.w, l4.w);
-        const uint32_t off = core_off16(tid, g4 * 4) / 4;
+        const uint32_t off = core_off16(bo, bh * (WKC / 2) + g4 * 4) / 4;
         *reinterpret_cast<float4*>(Bhi + off) = h4;
         *reinterpret_cast<float4*>(Blo + off) = l4;
       }
