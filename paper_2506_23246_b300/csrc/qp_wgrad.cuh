@@ -28,7 +28,8 @@ namespace qpd {
 // tables, builds the next tables and factors, reads its costate columns, starts the copy three
 // steps ahead, splits the columns into the TF32 B operand, and one thread issues the MMAs.
 constexpr int WKC = 16;
-constexpr int WG_THREADS = 512;
+constexpr int WG_STAGERS = 512;                 // operand-staging threads (16 warps)
+constexpr int WG_THREADS = WG_STAGERS + 32;       // + one control warp (copies, MMAs)
 constexpr int WG_RING = 4;
 
 struct WgArgs {
@@ -58,7 +59,7 @@ __host__ __device__ inline WgSmem wg_smem(int n) {
   w.raw = o; o += WG_RING * WKC * 256 * 4;           // costate columns of a step [16][256]
   w.fac = o; o += 2 * WG_FAC4 * 16;
   w.tab = o; o += 2 * WG_TAB4 * 16;
-  w.bars = o; o += 64;                               // mma_done[2], raw_full[4], tmem slot
+  w.bars = o; o += 128;  // mma_done[2], raw_full[4], stage_full[2], raw_free[4], acc_free, tmem slot
   w.total = o;
   return w;
 }
@@ -106,7 +107,7 @@ __device__ __forceinline__ void wg_tables(const float4* fac, float4* tab, int ti
                                           int nj) {
   float4* tlo = tab;
   float4* thi = tab + 16 * 32;
-  for (int idx = tid; idx < ppc * 32; idx += WG_THREADS) {
+  for (int idx = tid; idx < ppc * 32; idx += WG_STAGERS) {
     const int pl = idx >> 5, e = idx & 31;
     float4 p = make_float4(1.f, 0.f, 0.f, 0.f);
 #pragma unroll
@@ -116,7 +117,7 @@ __device__ __forceinline__ void wg_tables(const float4* fac, float4* tab, int ti
     }
     tlo[idx] = p;
   }
-  for (int idx = tid; idx < ppc * 8; idx += WG_THREADS) {
+  for (int idx = tid; idx < ppc * 8; idx += WG_STAGERS) {
     const int pl = idx >> 3, j = idx & 7;
     if (j < nj) {
       const int kb = kbase + j * 32;
@@ -156,95 +157,158 @@ __global__ void __launch_bounds__(WG_THREADS, 1) dense_wgrad_gemm_kernel(WgArgs 
   const int n = a.n, dim = 1 << n;
   const WgSmem L = wg_smem(n);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const bool ctrl = warp == WG_STAGERS / 32;
   const int MTC = wg_mtc(n), msub = MTC / TM, nj = MTC / 32;
   const int tile = blockIdx.x % a.tiles, lb = blockIdx.x / a.tiles;
   const int nmt = dim / MTC;
   const int mtile = tile % nmt, ntile = tile / nmt;
   const int kbase = mtile * MTC;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(sm + L.bars);  // mma_done[2], raw_full[4]
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + L.bars + 48);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sm + L.bars);
+  uint64_t* mma_done = bars;          // [2]  tensor-core work of a stage finished (commit)
+  uint64_t* raw_full = bars + 2;      // [4]  costate rows of a ring slot landed
+  uint64_t* stage_full = bars + 6;    // [2]  A and B operands of a stage written (16 warps)
+  uint64_t* raw_free = bars + 8;      // [4]  ring slot read by the staging warps (16 warps)
+  uint64_t* acc_free = bars + 12;     // accumulator flushed (16 warps)
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + L.bars + 104);
   float* raw = reinterpret_cast<float*>(sm + L.raw);
   float4* facb = reinterpret_cast<float4*>(sm + L.fac);
   float4* tabb = reinterpret_cast<float4*>(sm + L.tab);
   const uint32_t tcols = msub * 256;
+  constexpr int NSW = WG_STAGERS / 32;
   if (warp == 0) qptc::tmem_alloc(tslot, tcols);
   if (tid == 0) {
-    for (int i = 0; i < 2 + WG_RING; ++i) qptc::mbar_init(&bars[i], 1);
+    for (int i = 0; i < 6; ++i) qptc::mbar_init(&bars[i], 1);
+    for (int i = 6; i < 13; ++i) qptc::mbar_init(&bars[i], NSW);
   }
   qptc::fence_before();
   __syncthreads();
   qptc::fence_after();
   const uint32_t tmem = *tslot;
-  const uint32_t id = qptc::idesc(2, TM, 256);
   const int64_t nkc = a.kc_end[2];
   const int64_t c0 = (int64_t)lb * nkc / a.ngroups, c1 = (int64_t)(lb + 1) * nkc / a.ngroups;
-  const int kk = tid & (TM - 1), khalf = tid >> 8;
-  bool ok = true;
-  uint32_t it = 0;
+  const int kk = tid & (TM - 1), khalf = (tid >> 8) & 1;
   int64_t last_commit = -1, last_copy = -1;
-  int slot = 0;
-  bool fresh = true;                     // next MMA starts a new partial
-  float4 tjn = make_float4(0.f, 0.f, 0.f, 0.f);  // angles of step c0 + it + 2
+  float4 tjn = make_float4(0.f, 0.f, 0.f, 0.f);  // stagers: angles of step c0 + it + 2
   if (c0 < c1) {
-    int set, ppc, nv;
-    int64_t p0;
-    wg_step_geom(a, c0, set, p0, ppc, nv);
-    wg_fac(facb, tid, n, ppc, wg_load_tj(a, c0, tid));
-    if (c0 + 1 < c1) {
-      int set1, ppc1, nv1;
-      int64_t p01;
-      wg_step_geom(a, c0 + 1, set1, p01, ppc1, nv1);
-      wg_fac(facb + WG_FAC4, tid, n, ppc1, wg_load_tj(a, c0 + 1, tid));
-    }
-    if (c0 + 2 < c1) tjn = wg_load_tj(a, c0 + 2, tid);
-    if (tid == 0) {
+    if (!ctrl) {
+      int set, ppc, nv;
+      int64_t p0;
+      wg_step_geom(a, c0, set, p0, ppc, nv);
+      wg_fac(facb, tid, n, ppc, wg_load_tj(a, c0, tid));
+      if (c0 + 1 < c1) {
+        int set1, ppc1, nv1;
+        int64_t p01;
+        wg_step_geom(a, c0 + 1, set1, p01, ppc1, nv1);
+        wg_fac(facb + WG_FAC4, tid, n, ppc1, wg_load_tj(a, c0 + 1, tid));
+      }
+      if (c0 + 2 < c1) tjn = wg_load_tj(a, c0 + 2, tid);
+    } else if (lane == 0) {
       for (int j = 0; j < WG_RING - 1 && c0 + j < c1; ++j) {
-        wg_copy_rows(a, c0 + j, ntile, raw + j * (WKC * 256), &bars[2 + j]);
+        wg_copy_rows(a, c0 + j, ntile, raw + j * (WKC * 256), &raw_full[j]);
         last_copy = j;
       }
     }
-    __syncthreads();
+  }
+  __syncthreads();
+  if (c0 < c1 && !ctrl) {
+    int set, ppc, nv;
+    int64_t p0;
+    wg_step_geom(a, c0, set, p0, ppc, nv);
     wg_tables(facb, tabb, tid, n, ppc, kbase, nj);
   }
   __syncthreads();
-  // epilogue of one partial: the MTC x 256 accumulator -> part[slot]
-  auto flush = [&](int sl, bool zero) {
-    const int g = warp & 3, qw = warp >> 2;          // lane group, quarter of the columns
-    const int u = msub == 2 ? qw >> 1 : 0;            // M sub-tile read by this warp
-    const int cbeg = msub == 2 ? (qw & 1) * 128 : qw * 64, ncols = msub == 2 ? 128 : 64;
-    const int64_t krow = kbase + u * TM + g * 32 + lane;
-    float* outp = a.part + (((int64_t)(lb * a.spc + sl) * dim) + krow) * (2 * dim) + ntile * 256 + cbeg;
-    if (!zero) {
-      qptc::fence_after();
-      float v[32];
-      for (int c = 0; c < ncols; c += 32) {
-        qptc::tmem_ld32(tmem + ((uint32_t)(g * 32) << 16) + u * 256 + cbeg + c, v);
+  bool ok = true;
+  if (ctrl) {
+    // ---- control thread: bulk copies three steps ahead, MMAs when a stage is full
+    if (lane == 0) {
+      const uint32_t id = qptc::idesc(2, TM, 256);
+      int slot = 0;
+      bool fresh = true;
+      uint32_t it = 0;
+      for (int64_t kc = c0; kc < c1 && ok; ++kc, ++it) {
+        const uint32_t st = it & 1;
+        const int64_t j = it + WG_RING - 1;
+        if (kc + WG_RING - 1 < c1) {
+          if (j >= WG_RING) ok = qptc::mbar_wait(&raw_free[j % WG_RING], (uint32_t)((j - WG_RING) / WG_RING) & 1);
+          if (!ok) break;
+          qptc::fence_proxy_async();
+          wg_copy_rows(a, kc + WG_RING - 1, ntile, raw + (j % WG_RING) * (WKC * 256), &raw_full[j % WG_RING]);
+          last_copy = j;
+        }
+        if (fresh && slot > 0) ok = qptc::mbar_wait(acc_free, (uint32_t)(slot - 1) & 1);
+        if (!ok) break;
+        ok = qptc::mbar_wait(&stage_full[st], (it >> 1) & 1);
+        if (!ok) break;
+        qptc::fence_after();
+        unsigned char* sA = sm + st * L.stage;
+        const uint32_t sa = qptc::smem_u32(sA), sb = qptc::smem_u32(sA + L.a_bytes);
+        const uint32_t ablk = TM * WKC * 4, bblk = 256 * WKC * 4;
 #pragma unroll
-        for (int e = 0; e < 8; ++e)
-          reinterpret_cast<float4*>(outp + c)[e] = make_float4(v[4 * e], v[4 * e + 1], v[4 * e + 2], v[4 * e + 3]);
+        for (int ks = 0; ks < WKC / 8; ++ks) {
+          const uint64_t bh = qptc::desc_kmajor(sb + ks * 256, 128, (WKC / 4) * 128);
+          const uint64_t bl = qptc::desc_kmajor(sb + bblk + ks * 256, 128, (WKC / 4) * 128);
+          for (int u = 0; u < msub; ++u) {
+            const uint64_t ah = qptc::desc_kmajor(sa + u * 2 * ablk + ks * 256, 128, (WKC / 4) * 128);
+            const uint64_t al = qptc::desc_kmajor(sa + u * 2 * ablk + ablk + ks * 256, 128, (WKC / 4) * 128);
+            const uint32_t dt = tmem + u * 256;
+            qptc::mma_tf32(dt, ah, bh, id, (fresh && ks == 0) ? 0u : 1u);
+            qptc::mma_tf32(dt, ah, bl, id, 1u);
+            qptc::mma_tf32(dt, al, bh, id, 1u);
+          }
+        }
+        qptc::commit(&mma_done[st]);
+        last_commit = it;
+        fresh = false;
+        if ((kc - c0 + 1) % a.fl == 0 || kc + 1 == c1) {
+          fresh = true;
+          ++slot;
+        }
       }
-    } else {
-      for (int c = 0; c < ncols; c += 4) *reinterpret_cast<float4*>(outp + c) = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (!ok) {
+        atomicExch(a.status, 6);
+        // let every bulk copy and tensor-core operation of this CTA land before exiting
+        for (int64_t j = last_copy - (WG_RING - 1) < 0 ? 0 : last_copy - (WG_RING - 1); j <= last_copy; ++j)
+          qptc::mbar_wait(&raw_full[j % WG_RING], (uint32_t)(j / WG_RING) & 1);
+        if (last_commit >= 0) qptc::mbar_wait(&mma_done[last_commit & 1], ((uint32_t)last_commit >> 1) & 1);
+      }
     }
-    qptc::fence_before();
-  };
-  for (int64_t kc = c0; kc < c1 && ok; ++kc, ++it) {
-    const uint32_t st = it & 1;
-    unsigned char* sA = sm + st * L.stage;
-    unsigned char* sB = sA + L.a_bytes;
-    int set, ppc, nvalid;
-    int64_t p0;
-    wg_step_geom(a, kc, set, p0, ppc, nvalid);
-    bool w_ok = true;
-    if (it >= 2) w_ok = qptc::mbar_wait(&bars[st], ((it - 2) >> 1) & 1);
-    ok = __syncthreads_and(w_ok);
-    if (!ok) break;
-    // A operand of this step from its tables: thread -> (k, M sub-tile, half of the rows)
-    {
-      const float4* tlo = tabb + (it & 1) * WG_TAB4;
-      const float4* thi = tlo + 16 * 32;
-      const int e = kk & 31;
-      {
+  } else {
+    // ---- staging warps
+    // epilogue of one partial: the MTC x 256 accumulator -> part[slot]
+    auto flush = [&](int sl, bool zero) {
+      const int g = warp & 3, qw = warp >> 2;          // lane group, quarter of the columns
+      const int u = msub == 2 ? qw >> 1 : 0;            // M sub-tile read by this warp
+      const int cbeg = msub == 2 ? (qw & 1) * 128 : qw * 64, ncols = msub == 2 ? 128 : 64;
+      const int64_t krow = kbase + u * TM + g * 32 + lane;
+      float* outp = a.part + (((int64_t)(lb * a.spc + sl) * dim) + krow) * (2 * dim) + ntile * 256 + cbeg;
+      if (!zero) {
+        float v[32];
+        for (int c = 0; c < ncols; c += 32) {
+          qptc::tmem_ld32(tmem + ((uint32_t)(g * 32) << 16) + u * 256 + cbeg + c, v);
+#pragma unroll
+          for (int e = 0; e < 8; ++e)
+            reinterpret_cast<float4*>(outp + c)[e] = make_float4(v[4 * e], v[4 * e + 1], v[4 * e + 2], v[4 * e + 3]);
+        }
+      } else {
+        for (int c = 0; c < ncols; c += 4) *reinterpret_cast<float4*>(outp + c) = make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+    };
+    int slot = 0;
+    uint32_t it = 0;
+    for (int64_t kc = c0; kc < c1 && ok; ++kc, ++it) {
+      const uint32_t st = it & 1;
+      unsigned char* sA = sm + st * L.stage;
+      unsigned char* sB = sA + L.a_bytes;
+      int set, ppc, nvalid;
+      int64_t p0;
+      wg_step_geom(a, kc, set, p0, ppc, nvalid);
+      bool good = true;
+      if (it >= 2) good = qptc::mbar_wait(&mma_done[st], ((it - 2) >> 1) & 1);
+      if (good) {
+        // A operand of this step from its tables: thread -> (k, M sub-tile, half of the rows)
+        const float4* tlo = tabb + (it & 1) * WG_TAB4;
+        const float4* thi = tlo + 16 * 32;
+        const int e = kk & 31;
         const int u = (tid >> 7) & 1;
         if (u < msub) {
           const int j = (u * TM + kk) >> 5;
@@ -280,99 +344,70 @@ __global__ void __launch_bounds__(WG_THREADS, 1) dense_wgrad_gemm_kernel(WgArgs 
             *reinterpret_cast<float4*>(Alo + off) = l4;
           }
         }
+        // tables of the next step, factors of the step after
+        if (kc + 1 < c1) {
+          int set1, ppc1, nv1;
+          int64_t p01;
+          wg_step_geom(a, kc + 1, set1, p01, ppc1, nv1);
+          wg_tables(facb + ((it + 1) & 1) * WG_FAC4, tabb + ((it + 1) & 1) * WG_TAB4, tid, n, ppc1, kbase, nj);
+        }
+        if (kc + 2 < c1) {
+          int set2, ppc2, nv2;
+          int64_t p02;
+          wg_step_geom(a, kc + 2, set2, p02, ppc2, nv2);
+          wg_fac(facb + (it & 1) * WG_FAC4, tid, n, ppc2, tjn);
+          if (kc + 3 < c1) tjn = wg_load_tj(a, kc + 3, tid);
+        }
       }
-    }
-    // tables of the next step, factors of the step after
-    if (kc + 1 < c1) {
-      int set1, ppc1, nv1;
-      int64_t p01;
-      wg_step_geom(a, kc + 1, set1, p01, ppc1, nv1);
-      wg_tables(facb + ((it + 1) & 1) * WG_FAC4, tabb + ((it + 1) & 1) * WG_TAB4, tid, n, ppc1, kbase, nj);
-    }
-    if (kc + 2 < c1) {
-      int set2, ppc2, nv2;
-      int64_t p02;
-      wg_step_geom(a, kc + 2, set2, p02, ppc2, nv2);
-      wg_fac(facb + (it & 1) * WG_FAC4, tid, n, ppc2, tjn);
-      if (kc + 3 < c1) tjn = wg_load_tj(a, kc + 3, tid);
-    }
-    // this step's costate columns (bulk-copied three steps ago)
-    float lv[WKC / 2];
-    const int bo = tid & 255, bh = tid >> 8;   // component and half of the rows staged here
-    {
+      // this step's costate columns (bulk-copied three steps ahead)
       const uint32_t rs = it % WG_RING;
-      if (!qptc::mbar_wait(&bars[2 + rs], (it / WG_RING) & 1)) ok = false;
+      if (good) good = qptc::mbar_wait(&raw_full[rs], (it / WG_RING) & 1);
+      float lv[WKC / 2];
+      const int bo = tid & 255, bh = tid >> 8;   // component and half of the rows staged here
       const float* rr = raw + rs * (WKC * 256);
 #pragma unroll
       for (int t = 0; t < WKC / 2; ++t) {
         const int row = bh * (WKC / 2) + t;
-        lv[t] = row < nvalid ? rr[row * 256 + bo] : 0.f;
+        lv[t] = (good && row < nvalid) ? rr[row * 256 + bo] : 0.f;
       }
-    }
-    ok = __syncthreads_and(ok);   // the ring slot is consumed; tables and factors written
-    if (!ok) break;
-    if (tid == 0 && kc + WG_RING - 1 < c1) {
-      const uint32_t rs = (it + WG_RING - 1) % WG_RING;
-      qptc::fence_proxy_async();
-      wg_copy_rows(a, kc + WG_RING - 1, ntile, raw + rs * (WKC * 256), &bars[2 + rs]);
-      last_copy = it + WG_RING - 1;
-    }
-    {
-      float* Bhi = reinterpret_cast<float*>(sB);
-      float* Blo = Bhi + 256 * WKC;
+      __syncwarp();
+      if (lane == 0) qptc::mbar_arrive(&raw_free[rs]);
+      {
+        float* Bhi = reinterpret_cast<float*>(sB);
+        float* Blo = Bhi + 256 * WKC;
 #pragma unroll
-      for (int g4 = 0; g4 < WKC / 8; ++g4) {
-        float4 h4, l4;
-        qptc::split_tf32_fast(lv[4 * g4], h4.x, l4.x);
-        qptc::split_tf32_fast(lv[4 * g4 + 1], h4.y, l4.y);
-        qptc::split_tf32_fast(lv[4 * g4 + 2], h4.z, l4.z);
-        qptc::split_tf32_fast(lv[4 * g4 + 3], h4.w, l4.w);
-        const uint32_t off = core_off16(bo, bh * (WKC / 2) + g4 * 4) / 4;
-        *reinterpret_cast<float4*>(Bhi + off) = h4;
-        *reinterpret_cast<float4*>(Blo + off) = l4;
-      }
-    }
-    qptc::fence_proxy_async();
-    __syncthreads();
-    if (tid == 0) {
-      qptc::fence_after();
-      const uint32_t sa = qptc::smem_u32(sA), sb = qptc::smem_u32(sB);
-      const uint32_t ablk = TM * WKC * 4, bblk = 256 * WKC * 4;
-#pragma unroll
-      for (int ks = 0; ks < WKC / 8; ++ks) {
-        const uint64_t bh = qptc::desc_kmajor(sb + ks * 256, 128, (WKC / 4) * 128);
-        const uint64_t bl = qptc::desc_kmajor(sb + bblk + ks * 256, 128, (WKC / 4) * 128);
-        for (int u = 0; u < msub; ++u) {
-          const uint64_t ah = qptc::desc_kmajor(sa + u * 2 * ablk + ks * 256, 128, (WKC / 4) * 128);
-          const uint64_t al = qptc::desc_kmajor(sa + u * 2 * ablk + ablk + ks * 256, 128, (WKC / 4) * 128);
-          const uint32_t dt = tmem + u * 256;
-          qptc::mma_tf32(dt, ah, bh, id, (fresh && ks == 0) ? 0u : 1u);
-          qptc::mma_tf32(dt, ah, bl, id, 1u);
-          qptc::mma_tf32(dt, al, bh, id, 1u);
+        for (int g4 = 0; g4 < WKC / 8; ++g4) {
+          float4 h4, l4;
+          qptc::split_tf32_fast(lv[4 * g4], h4.x, l4.x);
+          qptc::split_tf32_fast(lv[4 * g4 + 1], h4.y, l4.y);
+          qptc::split_tf32_fast(lv[4 * g4 + 2], h4.z, l4.z);
+          qptc::split_tf32_fast(lv[4 * g4 + 3], h4.w, l4.w);
+          const uint32_t off = core_off16(bo, bh * (WKC / 2) + g4 * 4) / 4;
+          *reinterpret_cast<float4*>(Bhi + off) = h4;
+          *reinterpret_cast<float4*>(Blo + off) = l4;
         }
       }
-      qptc::commit(&bars[st]);
-      last_commit = it;
+      qptc::fence_proxy_async();
+      __syncwarp();
+      if (lane == 0) qptc::mbar_arrive(&stage_full[st]);
+      if ((kc - c0 + 1) % a.fl == 0 || kc + 1 == c1) {
+        if (good) good = qptc::mbar_wait(&mma_done[st], (it >> 1) & 1);
+        if (good) {
+          qptc::fence_after();
+          flush(slot, false);
+        }
+        qptc::fence_before();
+        __syncwarp();
+        if (lane == 0) qptc::mbar_arrive(acc_free);
+        ++slot;
+      }
+      // one barrier per step over the staging warps: tables and factors of the next steps
+      ok = qptc::bar_and(1, WG_STAGERS, good);
     }
-    fresh = false;
-    if ((kc - c0 + 1) % a.fl == 0 || kc + 1 == c1) {
-      ok = __syncthreads_and(qptc::mbar_wait(&bars[st], (it >> 1) & 1));
-      if (!ok) break;
-      flush(slot, false);
-      ++slot;
-      fresh = true;
-      __syncthreads();
-    }
-  }
-  if (ok) {
-    for (int sl = slot; sl < a.spc; ++sl) flush(sl, true);
-  } else {
-    if (tid == 0) {
+    if (ok) {
+      for (int sl = slot; sl < a.spc; ++sl) flush(sl, true);
+    } else if (tid == 0) {
       atomicExch(a.status, 6);
-      // let every bulk copy and tensor-core operation of this CTA land before exiting
-      for (int64_t j = last_copy - (WG_RING - 1) < 0 ? 0 : last_copy - (WG_RING - 1); j <= last_copy; ++j)
-        qptc::mbar_wait(&bars[2 + (j % WG_RING)], (uint32_t)(j / WG_RING) & 1);
-      if (last_commit >= 0) qptc::mbar_wait(&bars[last_commit & 1], ((uint32_t)last_commit >> 1) & 1);
     }
   }
   qptc::fence_before();
