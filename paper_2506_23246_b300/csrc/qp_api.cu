@@ -52,7 +52,7 @@ int geo_ppw(int n) { return 32 >> (n - geo_lb(n)); }
 
 struct WsLayout {
   size_t status, gates, cmat, cenc, thetaJ, dthetaJ, d1, d2, u1, blk_loss, blk_grad, wpart;
-  size_t dW, dphi, dU, dG, dY, dpart, dWT, dmu, dW16, total;
+  size_t dW, dphi, dU, dG, dY, dpart, dWT, dmu, dW16, dcs, total;
 };
 
 // Rows of (point, vector) accumulated per weight-gradient chunk (bounds the FP32 tensor-core
@@ -124,6 +124,7 @@ WsLayout ws_layout(const qp_plan* pl, int64_t P) {
   w.dWT = o; o = al256(o + (dm ? 2 * (2 * dim) * dim * 4 : 0));
   w.dmu = o; o = al256(o + (dm && !fused_path(pl) ? (size_t)P * 4 * dim * 4 : 0));
   w.dW16 = o; o = al256(o + (dg && fused_path(pl) ? 2 * (2 * dim) * dim * 4 : 0));
+  w.dcs = o; o = al256(o + (dg ? (size_t)P * n * 8 : 0));
   w.total = o;
   return w;
 }
@@ -458,6 +459,12 @@ static qp_status dense_loss_grad(qp_plan* pl, const float* d_params, const float
   ba.WT = mlp ? (float*)(ws + w.dWT) : nullptr;
   const bool fused = fused_path(pl);
   ba.W16 = fused ? (float*)(ws + w.dW16) : nullptr;
+  if (P > 0) {
+    const int64_t tot = P * n;
+    const int hb = (int)((tot + 255) / 256 < pl->sm_count * 4 ? (tot + 255) / 256 : pl->sm_count * 4);
+    qpd::dense_halfangle_kernel<<<hb, 256, 0, s>>>((const float4*)(ws + w.thetaJ), (float2*)(ws + w.dcs), tot);
+    launches += 1;
+  }
   if (fused) ba.W = nullptr;
   qpd::dense_build_kernel<<<dim, 256, dim * 16, s>>>(ba);
   launches += 1;
@@ -515,7 +522,8 @@ static qp_status dense_loss_grad(qp_plan* pl, const float* d_params, const float
     launches += 1;
   }
   qpd::WgArgs wa;
-  wa.thetaJ = (const float*)(ws + w.thetaJ); wa.lam = (const float*)(ws + w.dphi);
+  wa.thetaJ = (const float*)(ws + w.thetaJ); wa.cs = (const float2*)(ws + w.dcs);
+  wa.lam = (const float*)(ws + w.dphi);
   wa.rtot = fused ? 4 * npts[0] + npts[1] + npts[2] : 0;
   wa.part = (float*)(ws + w.dpart); wa.n = n;
   base = 0;

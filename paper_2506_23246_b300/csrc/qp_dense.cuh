@@ -45,6 +45,16 @@ __host__ __device__ inline int64_t lam_row(int set, int64_t p, int s, int64_t n0
   return set == 0 ? p * 4 + s : 3 * n0 + base + p;
 }
 
+// cos and sin of theta / 2 for every (point, qubit) angle, once per call (the encoding factors
+// of the product states, shared by the contractions that regenerate them).
+__global__ void dense_halfangle_kernel(const float4* thetaJ, float2* cs, int64_t total) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    float sn, c;
+    sincosf(0.5f * thetaJ[i].x, &sn, &c);
+    cs[i] = make_float2(c, sn);
+  }
+}
+
 // ------------------------------------------------------------------------- unitary build
 struct BuildArgs {
   const float* params;

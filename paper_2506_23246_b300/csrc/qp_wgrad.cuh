@@ -33,7 +33,8 @@ constexpr int WG_THREADS = WG_STAGERS + 32;       // + one control warp (copies,
 constexpr int WG_RING = 4;
 
 struct WgArgs {
-  const float* thetaJ;        // [P][n] float4
+  const float* thetaJ;        // [P][n] float4 (theta, J_x, J_y, J_t)
+  const float2* cs;           // [P][n] (cos, sin) of theta / 2
   const float* lam;           // costate rows: blocked [2 dim / 256][rtot][256] or rows [P][4][2 dim]
   int64_t rtot;               // rows of the blocked layout (0: row layout)
   float* part;                // [nslots][dim][2 dim]
@@ -75,24 +76,34 @@ __device__ __forceinline__ void wg_step_geom(const WgArgs& a, int64_t kc, int& s
   nvalid = (int)(left < WKC ? left : WKC);
 }
 
-// Raw angle entry (theta, J) of the (point, qubit) pair `tid` of step kc.
-__device__ __forceinline__ float4 wg_load_tj(const WgArgs& a, int64_t kc, int tid) {
+// Angle entry of the (point, qubit) pair `tid` of step kc: (cos, sin of theta/2, J_x, J_y), J_t.
+struct WgAng {
+  float4 f0;
+  float jt;
+};
+__device__ __forceinline__ WgAng wg_load_ang(const WgArgs& a, int64_t kc, int tid) {
   int set, ppc, nv;
   int64_t p0;
   wg_step_geom(a, kc, set, p0, ppc, nv);
   const int n = a.n, pl = tid / n, q = tid % n;
-  if (tid < ppc * n && p0 + pl < a.npts[set])
-    return __ldg(reinterpret_cast<const float4*>(a.thetaJ) + (a.pt_base[set] + p0 + pl) * n + q);
-  return make_float4(0.f, 0.f, 0.f, 0.f);
+  WgAng r;
+  r.f0 = make_float4(0.f, 0.f, 0.f, 0.f);
+  r.jt = 0.f;
+  if (tid < ppc * n && p0 + pl < a.npts[set]) {
+    const int64_t i = (a.pt_base[set] + p0 + pl) * n + q;
+    const float4 tq = __ldg(reinterpret_cast<const float4*>(a.thetaJ) + i);
+    const float2 c = __ldg(a.cs + i);
+    r.f0 = make_float4(c.x, c.y, tq.y, tq.z);
+    r.jt = tq.w;
+  }
+  return r;
 }
 
 // Per (point, qubit) factors: (cos, sin of theta/2, J_x, J_y), (J_t, ., ., .).
-__device__ __forceinline__ void wg_fac(float4* fac, int tid, int n, int ppc, const float4& tq) {
+__device__ __forceinline__ void wg_fac(float4* fac, int tid, int n, int ppc, const WgAng& g) {
   if (tid < ppc * n) {
-    float sn, cs;
-    sincosf(0.5f * tq.x, &sn, &cs);
-    fac[tid * 2] = make_float4(cs, sn, tq.y, tq.z);
-    fac[tid * 2 + 1] = make_float4(tq.w, 0.f, 0.f, 0.f);
+    fac[tid * 2] = g.f0;
+    fac[tid * 2 + 1] = make_float4(g.jt, 0.f, 0.f, 0.f);
   }
 }
 
@@ -107,7 +118,7 @@ __device__ __forceinline__ void wg_tables(const float4* fac, float4* tab, int ti
                                           int nj) {
   float4* tlo = tab;
   float4* thi = tab + 16 * 32;
-  for (int idx = tid; idx < ppc * 32; idx += WG_STAGERS) {
+  for (int idx = tid; idx < ppc * 32; idx += WG_STAGERS / 2) {
     const int pl = idx >> 5, e = idx & 31;
     float4 p = make_float4(1.f, 0.f, 0.f, 0.f);
 #pragma unroll
@@ -117,7 +128,7 @@ __device__ __forceinline__ void wg_tables(const float4* fac, float4* tab, int ti
     }
     tlo[idx] = p;
   }
-  for (int idx = tid; idx < ppc * 8; idx += WG_STAGERS) {
+  for (int idx = tid; idx < ppc * 8; idx += WG_STAGERS / 2) {
     const int pl = idx >> 3, j = idx & 7;
     if (j < nj) {
       const int kb = kbase + j * 32;
@@ -167,7 +178,7 @@ __global__ void __launch_bounds__(WG_THREADS, 1) dense_wgrad_gemm_kernel(WgArgs 
   uint64_t* mma_done = bars;          // [2]  tensor-core work of a stage finished (commit)
   uint64_t* raw_full = bars + 2;      // [4]  costate rows of a ring slot landed
   uint64_t* stage_full = bars + 6;    // [2]  A and B operands of a stage written (16 warps)
-  uint64_t* raw_free = bars + 8;      // [4]  ring slot read by the staging warps (16 warps)
+  uint64_t* raw_free = bars + 8;      // [4]  ring slot read by the B-group (8 warps)
   uint64_t* acc_free = bars + 12;     // accumulator flushed (16 warps)
   uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + L.bars + 104);
   float* raw = reinterpret_cast<float*>(sm + L.raw);
@@ -178,7 +189,9 @@ __global__ void __launch_bounds__(WG_THREADS, 1) dense_wgrad_gemm_kernel(WgArgs 
   if (warp == 0) qptc::tmem_alloc(tslot, tcols);
   if (tid == 0) {
     for (int i = 0; i < 6; ++i) qptc::mbar_init(&bars[i], 1);
-    for (int i = 6; i < 13; ++i) qptc::mbar_init(&bars[i], NSW);
+    for (int i = 6; i < 8; ++i) qptc::mbar_init(&bars[i], NSW);        // stage_full: all staging warps
+    for (int i = 8; i < 12; ++i) qptc::mbar_init(&bars[i], NSW / 2);   // raw_free: B-group warps
+    qptc::mbar_init(&bars[12], NSW);                                   // acc_free: all staging warps
   }
   qptc::fence_before();
   __syncthreads();
@@ -186,22 +199,25 @@ __global__ void __launch_bounds__(WG_THREADS, 1) dense_wgrad_gemm_kernel(WgArgs 
   const uint32_t tmem = *tslot;
   const int64_t nkc = a.kc_end[2];
   const int64_t c0 = (int64_t)lb * nkc / a.ngroups, c1 = (int64_t)(lb + 1) * nkc / a.ngroups;
-  const int kk = tid & (TM - 1), khalf = (tid >> 8) & 1;
+  const bool agrp = tid < WG_STAGERS / 2;   // A-group: R tables and A operand; B-group: costates
+  const int kk = tid & (TM - 1), khalf = (tid >> 7) & 1;
   int64_t last_commit = -1, last_copy = -1;
-  float4 tjn = make_float4(0.f, 0.f, 0.f, 0.f);  // stagers: angles of step c0 + it + 2
+  WgAng tjn{};  // A-group: angles of step c0 + it + 2
   if (c0 < c1) {
     if (!ctrl) {
-      int set, ppc, nv;
-      int64_t p0;
-      wg_step_geom(a, c0, set, p0, ppc, nv);
-      wg_fac(facb, tid, n, ppc, wg_load_tj(a, c0, tid));
-      if (c0 + 1 < c1) {
-        int set1, ppc1, nv1;
-        int64_t p01;
-        wg_step_geom(a, c0 + 1, set1, p01, ppc1, nv1);
-        wg_fac(facb + WG_FAC4, tid, n, ppc1, wg_load_tj(a, c0 + 1, tid));
+      if (agrp) {
+        int set, ppc, nv;
+        int64_t p0;
+        wg_step_geom(a, c0, set, p0, ppc, nv);
+        wg_fac(facb, tid, n, ppc, wg_load_ang(a, c0, tid));
+        if (c0 + 1 < c1) {
+          int set1, ppc1, nv1;
+          int64_t p01;
+          wg_step_geom(a, c0 + 1, set1, p01, ppc1, nv1);
+          wg_fac(facb + WG_FAC4, tid, n, ppc1, wg_load_ang(a, c0 + 1, tid));
+        }
+        if (c0 + 2 < c1) tjn = wg_load_ang(a, c0 + 2, tid);
       }
-      if (c0 + 2 < c1) tjn = wg_load_tj(a, c0 + 2, tid);
     } else if (lane == 0) {
       for (int j = 0; j < WG_RING - 1 && c0 + j < c1; ++j) {
         wg_copy_rows(a, c0 + j, ntile, raw + j * (WKC * 256), &raw_full[j]);
@@ -210,7 +226,7 @@ __global__ void __launch_bounds__(WG_THREADS, 1) dense_wgrad_gemm_kernel(WgArgs 
     }
   }
   __syncthreads();
-  if (c0 < c1 && !ctrl) {
+  if (c0 < c1 && !ctrl && agrp) {
     int set, ppc, nv;
     int64_t p0;
     wg_step_geom(a, c0, set, p0, ppc, nv);
@@ -304,85 +320,85 @@ __global__ void __launch_bounds__(WG_THREADS, 1) dense_wgrad_gemm_kernel(WgArgs 
       wg_step_geom(a, kc, set, p0, ppc, nvalid);
       bool good = true;
       if (it >= 2) good = qptc::mbar_wait(&mma_done[st], ((it - 2) >> 1) & 1);
-      if (good) {
-        // A operand of this step from its tables: thread -> (k, M sub-tile, half of the rows)
-        const float4* tlo = tabb + (it & 1) * WG_TAB4;
-        const float4* thi = tlo + 16 * 32;
-        const int e = kk & 31;
-        const int u = (tid >> 7) & 1;
-        if (u < msub) {
-          const int j = (u * TM + kk) >> 5;
-          float av[8];
-          if (set == 0) {
+      if (agrp) {
+        if (good) {
+          // A operand of this step from its tables: thread -> (k, half of the rows), both M sub-tiles
+          const float4* tlo = tabb + (it & 1) * WG_TAB4;
+          const float4* thi = tlo + 16 * 32;
+          const int e = kk & 31;
 #pragma unroll
-            for (int pi = 0; pi < 2; ++pi) {
-              const int pl = khalf * 2 + pi;
-              const float4 h = thi[pl * 8 + j], l = tlo[pl * 32 + e];
-              av[4 * pi] = h.x * l.x;
-              av[4 * pi + 1] = h.y * l.x + h.x * l.y;
-              av[4 * pi + 2] = h.z * l.x + h.x * l.z;
-              av[4 * pi + 3] = h.w * l.x + h.x * l.w;
-            }
-          } else {
+          for (int u = 0; u < 2; ++u) {
+            if (u < msub) {
+              const int j = (u * TM + kk) >> 5;
+              float av[8];
+              if (set == 0) {
 #pragma unroll
-            for (int pi = 0; pi < 8; ++pi) {
-              const int pl = khalf * 8 + pi;
-              av[pi] = thi[pl * 8 + j].x * tlo[pl * 32 + e].x;
+                for (int pi = 0; pi < 2; ++pi) {
+                  const int pl = khalf * 2 + pi;
+                  const float4 h = thi[pl * 8 + j], l = tlo[pl * 32 + e];
+                  av[4 * pi] = h.x * l.x;
+                  av[4 * pi + 1] = h.y * l.x + h.x * l.y;
+                  av[4 * pi + 2] = h.z * l.x + h.x * l.z;
+                  av[4 * pi + 3] = h.w * l.x + h.x * l.w;
+                }
+              } else {
+#pragma unroll
+                for (int pi = 0; pi < 8; ++pi) {
+                  const int pl = khalf * 8 + pi;
+                  av[pi] = thi[pl * 8 + j].x * tlo[pl * 32 + e].x;
+                }
+              }
+              float* Ahi = reinterpret_cast<float*>(sA + u * 2 * (TM * WKC * 4));
+              float* Alo = Ahi + TM * WKC;
+#pragma unroll
+              for (int g4 = 0; g4 < 2; ++g4) {
+                float4 h4, l4;
+                qptc::split_tf32_fast(av[4 * g4], h4.x, l4.x);
+                qptc::split_tf32_fast(av[4 * g4 + 1], h4.y, l4.y);
+                qptc::split_tf32_fast(av[4 * g4 + 2], h4.z, l4.z);
+                qptc::split_tf32_fast(av[4 * g4 + 3], h4.w, l4.w);
+                const uint32_t off = core_off16(kk, khalf * 8 + g4 * 4) / 4;
+                *reinterpret_cast<float4*>(Ahi + off) = h4;
+                *reinterpret_cast<float4*>(Alo + off) = l4;
+              }
             }
           }
-          float* Ahi = reinterpret_cast<float*>(sA + u * 2 * (TM * WKC * 4));
-          float* Alo = Ahi + TM * WKC;
-#pragma unroll
-          for (int g4 = 0; g4 < 2; ++g4) {
-            float4 h4, l4;
-            qptc::split_tf32_fast(av[4 * g4], h4.x, l4.x);
-            qptc::split_tf32_fast(av[4 * g4 + 1], h4.y, l4.y);
-            qptc::split_tf32_fast(av[4 * g4 + 2], h4.z, l4.z);
-            qptc::split_tf32_fast(av[4 * g4 + 3], h4.w, l4.w);
-            const uint32_t off = core_off16(kk, khalf * 8 + g4 * 4) / 4;
-            *reinterpret_cast<float4*>(Ahi + off) = h4;
-            *reinterpret_cast<float4*>(Alo + off) = l4;
+          // tables of the next step, factors of the step after
+          if (kc + 1 < c1) {
+            int set1, ppc1, nv1;
+            int64_t p01;
+            wg_step_geom(a, kc + 1, set1, p01, ppc1, nv1);
+            wg_tables(facb + ((it + 1) & 1) * WG_FAC4, tabb + ((it + 1) & 1) * WG_TAB4, tid, n, ppc1, kbase, nj);
+          }
+          if (kc + 2 < c1) {
+            int set2, ppc2, nv2;
+            int64_t p02;
+            wg_step_geom(a, kc + 2, set2, p02, ppc2, nv2);
+            wg_fac(facb + (it & 1) * WG_FAC4, tid, n, ppc2, tjn);
+            if (kc + 3 < c1) tjn = wg_load_ang(a, kc + 3, tid);
           }
         }
-        // tables of the next step, factors of the step after
-        if (kc + 1 < c1) {
-          int set1, ppc1, nv1;
-          int64_t p01;
-          wg_step_geom(a, kc + 1, set1, p01, ppc1, nv1);
-          wg_tables(facb + ((it + 1) & 1) * WG_FAC4, tabb + ((it + 1) & 1) * WG_TAB4, tid, n, ppc1, kbase, nj);
-        }
-        if (kc + 2 < c1) {
-          int set2, ppc2, nv2;
-          int64_t p02;
-          wg_step_geom(a, kc + 2, set2, p02, ppc2, nv2);
-          wg_fac(facb + (it & 1) * WG_FAC4, tid, n, ppc2, tjn);
-          if (kc + 3 < c1) tjn = wg_load_tj(a, kc + 3, tid);
-        }
-      }
-      // this step's costate columns (bulk-copied three steps ahead)
-      const uint32_t rs = it % WG_RING;
-      if (good) good = qptc::mbar_wait(&raw_full[rs], (it / WG_RING) & 1);
-      float lv[WKC / 2];
-      const int bo = tid & 255, bh = tid >> 8;   // component and half of the rows staged here
-      const float* rr = raw + rs * (WKC * 256);
+      } else {
+        // this step's costate columns (bulk-copied three steps ahead): component bo, 16 rows
+        const uint32_t rs = it % WG_RING;
+        if (good) good = qptc::mbar_wait(&raw_full[rs], (it / WG_RING) & 1);
+        float lv[WKC];
+        const int bo = tid - WG_STAGERS / 2;
+        const float* rr = raw + rs * (WKC * 256);
 #pragma unroll
-      for (int t = 0; t < WKC / 2; ++t) {
-        const int row = bh * (WKC / 2) + t;
-        lv[t] = (good && row < nvalid) ? rr[row * 256 + bo] : 0.f;
-      }
-      __syncwarp();
-      if (lane == 0) qptc::mbar_arrive(&raw_free[rs]);
-      {
+        for (int t = 0; t < WKC; ++t) lv[t] = (good && t < nvalid) ? rr[t * 256 + bo] : 0.f;
+        __syncwarp();
+        if (lane == 0) qptc::mbar_arrive(&raw_free[rs]);
         float* Bhi = reinterpret_cast<float*>(sB);
         float* Blo = Bhi + 256 * WKC;
 #pragma unroll
-        for (int g4 = 0; g4 < WKC / 8; ++g4) {
+        for (int g4 = 0; g4 < WKC / 4; ++g4) {
           float4 h4, l4;
           qptc::split_tf32_fast(lv[4 * g4], h4.x, l4.x);
           qptc::split_tf32_fast(lv[4 * g4 + 1], h4.y, l4.y);
           qptc::split_tf32_fast(lv[4 * g4 + 2], h4.z, l4.z);
           qptc::split_tf32_fast(lv[4 * g4 + 3], h4.w, l4.w);
-          const uint32_t off = core_off16(bo, bh * (WKC / 2) + g4 * 4) / 4;
+          const uint32_t off = core_off16(bo, g4 * 4) / 4;
           *reinterpret_cast<float4*>(Bhi + off) = h4;
           *reinterpret_cast<float4*>(Blo + off) = l4;
         }
@@ -401,8 +417,9 @@ __global__ void __launch_bounds__(WG_THREADS, 1) dense_wgrad_gemm_kernel(WgArgs 
         if (lane == 0) qptc::mbar_arrive(acc_free);
         ++slot;
       }
-      // one barrier per step over the staging warps: tables and factors of the next steps
-      ok = qptc::bar_and(1, WG_STAGERS, good);
+      // the A-group shares tables and factors across steps: one barrier per step over it
+      if (agrp) ok = qptc::bar_and(1, WG_STAGERS / 2, good);
+      else ok = __all_sync(0xffffffffu, good);
     }
     if (ok) {
       for (int sl = slot; sl < a.spc; ++sl) flush(sl, true);
