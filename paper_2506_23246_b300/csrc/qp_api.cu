@@ -281,7 +281,7 @@ qp_status qp_plan_create(const qp_circuit* circuit, const qp_problem* problem, i
   }
   if (dense_path(pl)) {
     if (cudaFuncSetAttribute((void*)qpd::dense_build_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (1 << n) * 16) != cudaSuccess ||
+                             2 * (1 << n) * 16) != cudaSuccess ||
         cudaFuncSetAttribute((void*)qpd::dense_row_gemm_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              qpd::gemm_smem_bytes(n, 0)) != cudaSuccess ||
         cudaFuncSetAttribute((void*)qpd::dense_row_gemm_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -466,7 +466,7 @@ static qp_status dense_loss_grad(qp_plan* pl, const float* d_params, const float
     launches += 1;
   }
   if (fused) ba.W = nullptr;
-  qpd::dense_build_kernel<<<dim, 256, dim * 16, s>>>(ba);
+  qpd::dense_build_kernel<<<dim, 256, 2 * dim * 16, s>>>(ba);
   launches += 1;
   int64_t base = 0;
   if (fused) {
@@ -637,7 +637,7 @@ qp_status qp_forward(qp_plan* pl, const float* d_params, const float* d_pts, int
     ba.params = d_params; ba.circ_off = pl->circ_off; ba.n = n; ba.L = pl->c.n_layers;
     ba.ansatz = pl->c.ansatz; ba.enc = pl->c.enc; ba.W = (float*)(ws + w.dW); ba.U = nullptr;
     ba.W16 = nullptr;
-    qpd::dense_build_kernel<<<dim, 256, dim * 16, s>>>(ba);
+    qpd::dense_build_kernel<<<dim, 256, 2 * dim * 16, s>>>(ba);
     qpd::GemmArgs ga;
     ga.thetaJ = (const float*)(ws + w.thetaJ); ga.W = (const float*)(ws + w.dW);
     ga.phi = (float2*)(ws + w.dphi); ga.n = n; ga.nv = d_dfields ? 4 : 1;

@@ -70,44 +70,56 @@ __device__ inline double2 zmul(double2 a, double2 b) {
   return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
 
-// One block per basis column k: |k> through all layers (gates and CNOT rings) in FP64.
+// Gate of (layer l, qubit q) in double precision (same formulas as the build).
+__device__ inline void gate_fp64(const float* params, int64_t circ_off, int ansatz, int n, int l, int q,
+                                 double2* g) {
+  const int kp = ansatz == 0 ? 2 : 3;
+  const float* p = params + circ_off + ((int64_t)l * n + q) * kp;
+  if (ansatz == 0) {
+    double ca, sa, cb, sb;
+    sincos(0.5 * (double)p[0], &sa, &ca);
+    sincos(0.5 * (double)p[1], &sb, &cb);
+    g[0] = make_double2(cb * ca, -sb * ca); g[1] = make_double2(-cb * sa, sb * sa);
+    g[2] = make_double2(cb * sa, sb * sa); g[3] = make_double2(cb * ca, sb * ca);
+  } else {
+    double cb, sb;
+    sincos(0.5 * (double)p[1], &sb, &cb);
+    const double ap = 0.5 * ((double)p[0] + (double)p[2]), am = 0.5 * ((double)p[0] - (double)p[2]);
+    double cp, sp, cm, smm;
+    sincos(ap, &sp, &cp);
+    sincos(am, &smm, &cm);
+    g[0] = make_double2(cp * cb, -sp * cb); g[1] = make_double2(-cm * sb, -smm * sb);
+    g[2] = make_double2(cm * sb, -smm * sb); g[3] = make_double2(cp * cb, sp * cb);
+  }
+}
+
+// Index map of the CNOT ring of layer l (basis state |k> -> |c(k)>).
+__device__ __forceinline__ int ring_map(int n, int ansatz, int l, int k) {
+  if (ansatz == 3 || n < 2) return k;
+  const int r = ansatz == 2 ? 1 + (l % (n - 1)) : 1;
+  for (int i = 0; i < n; ++i) {
+    const int bc = 1 << (n - 1 - i), bt = 1 << (n - 1 - (i + r) % n);
+    if (k & bc) k ^= bt;
+  }
+  return k;
+}
+
+// One block per basis column k: |k> through all layers (gates and CNOT rings) in FP64. The
+// gate matrices of every (layer, qubit) are formed in parallel first; a gate is one pass over
+// the amplitude pairs, a CNOT ring one permutation pass.
 __global__ void dense_build_kernel(BuildArgs a) {
-  extern __shared__ __align__(16) double2 col[];
-  __shared__ double2 g[4];
+  extern __shared__ __align__(16) double2 colbuf[];  // two [2^n] column buffers
+  __shared__ double2 gm[QP_MAXL * QP_MAXQ * 4];
   const int n = a.n, dim = 1 << n, k = blockIdx.x;
+  for (int i = threadIdx.x; i < a.L * n; i += blockDim.x)
+    gate_fp64(a.params, a.circ_off, a.ansatz, n, i / n, i % n, &gm[i * 4]);
+  double2* col = colbuf;
+  double2* nxt = colbuf + dim;
   for (int j = threadIdx.x; j < dim; j += blockDim.x) col[j] = make_double2(j == k ? 1.0 : 0.0, 0.0);
   __syncthreads();
-  const int kp = a.ansatz == 0 ? 2 : 3;
   for (int l = 0; l < a.L; ++l) {
     for (int q = 0; q < n; ++q) {
-      if (threadIdx.x == 0) {
-        const float* p = a.params + a.circ_off + ((int64_t)l * n + q) * kp;
-        double c0, s0;
-        double2 u00, u01, u10, u11;
-        if (a.ansatz == 0) {  // RZ(b) RY(a)
-          double ca, sa, cb, sb;
-          sincos(0.5 * (double)p[0], &sa, &ca);
-          sincos(0.5 * (double)p[1], &sb, &cb);
-          u00 = make_double2(cb * ca, -sb * ca);
-          u01 = make_double2(-cb * sa, sb * sa);
-          u10 = make_double2(cb * sa, sb * sa);
-          u11 = make_double2(cb * ca, sb * ca);
-        } else {              // RZ(g) RY(b) RZ(a)
-          double cb, sb;
-          sincos(0.5 * (double)p[1], &sb, &cb);
-          const double ap = 0.5 * ((double)p[0] + (double)p[2]), am = 0.5 * ((double)p[0] - (double)p[2]);
-          double cp, sp, cm, sm;
-          sincos(ap, &sp, &cp);
-          sincos(am, &sm, &cm);
-          u00 = make_double2(cp * cb, -sp * cb);
-          u01 = make_double2(-cm * sb, -sm * sb);
-          u10 = make_double2(cm * sb, -sm * sb);
-          u11 = make_double2(cp * cb, sp * cb);
-        }
-        (void)c0; (void)s0;
-        g[0] = u00; g[1] = u01; g[2] = u10; g[3] = u11;
-      }
-      __syncthreads();
+      const double2* g = &gm[(l * n + q) * 4];
       const int bit = 1 << (n - 1 - q);
       for (int i = threadIdx.x; i < dim / 2; i += blockDim.x) {
         const int k0 = ((i & ~(bit - 1)) << 1) | (i & (bit - 1));
@@ -120,18 +132,11 @@ __global__ void dense_build_kernel(BuildArgs a) {
       __syncthreads();
     }
     if (a.ansatz != 3 && n > 1) {
-      const int r = a.ansatz == 2 ? 1 + (l % (n - 1)) : 1;
-      for (int i = 0; i < n; ++i) {
-        const int bc = 1 << (n - 1 - i), bt = 1 << (n - 1 - (i + r) % n);
-        for (int j = threadIdx.x; j < dim; j += blockDim.x) {
-          if ((j & bc) && !(j & bt)) {
-            const double2 t = col[j];
-            col[j] = col[j | bt];
-            col[j | bt] = t;
-          }
-        }
-        __syncthreads();
-      }
+      for (int j = threadIdx.x; j < dim; j += blockDim.x) nxt[ring_map(n, a.ansatz, l, j)] = col[j];
+      __syncthreads();
+      double2* t = col;
+      col = nxt;
+      nxt = t;
     }
   }
   // fold the embedding phase (-i)^{popcount k} (RX) into column k
@@ -707,40 +712,6 @@ __global__ void dense_y_kernel(SweepArgs a) {
     __syncthreads();
   }
   if (j < dim && jj < dim) a.Y[(int64_t)j * dim + jj] = acc;
-}
-
-// Gate of (layer l, qubit q) in double precision (same formulas as the build).
-__device__ inline void gate_fp64(const float* params, int64_t circ_off, int ansatz, int n, int l, int q,
-                                 double2* g) {
-  const int kp = ansatz == 0 ? 2 : 3;
-  const float* p = params + circ_off + ((int64_t)l * n + q) * kp;
-  if (ansatz == 0) {
-    double ca, sa, cb, sb;
-    sincos(0.5 * (double)p[0], &sa, &ca);
-    sincos(0.5 * (double)p[1], &sb, &cb);
-    g[0] = make_double2(cb * ca, -sb * ca); g[1] = make_double2(-cb * sa, sb * sa);
-    g[2] = make_double2(cb * sa, sb * sa); g[3] = make_double2(cb * ca, sb * ca);
-  } else {
-    double cb, sb;
-    sincos(0.5 * (double)p[1], &sb, &cb);
-    const double ap = 0.5 * ((double)p[0] + (double)p[2]), am = 0.5 * ((double)p[0] - (double)p[2]);
-    double cp, sp, cm, smm;
-    sincos(ap, &sp, &cp);
-    sincos(am, &smm, &cm);
-    g[0] = make_double2(cp * cb, -sp * cb); g[1] = make_double2(-cm * sb, -smm * sb);
-    g[2] = make_double2(cm * sb, -smm * sb); g[3] = make_double2(cp * cb, sp * cb);
-  }
-}
-
-// Index map of the CNOT ring of layer l (basis state |k> -> |c(k)>).
-__device__ __forceinline__ int ring_map(int n, int ansatz, int l, int k) {
-  if (ansatz == 3 || n < 2) return k;
-  const int r = ansatz == 2 ? 1 + (l % (n - 1)) : 1;
-  for (int i = 0; i < n; ++i) {
-    const int bc = 1 << (n - 1 - i), bt = 1 << (n - 1 - (i + r) % n);
-    if (k & bc) k ^= bt;
-  }
-  return k;
 }
 
 // Undo ring l (Y2[a][b] = Y[c(a)][c(b)], i.e. C^dag Y C) and accumulate, at that point,
