@@ -111,7 +111,17 @@ typedef struct {
 
 /* Point sets of one loss evaluation (device pointers, float32 [n][3]). colloc points
  * carry the residual and energy terms; ic points the initial-condition misfit (Eq. 17);
- * bc points the PEC boundary term Ez = 0. Any set may be empty (NULL, 0). */
+ * bc points the PEC boundary term Ez = 0. Any set may be empty (NULL, 0).
+ *
+ * Sharding (data parallelism over ranks): the loss terms are means over whole point sets
+ * (Eqs. 11-17, 23). When one loss is split over several calls, give each call the whole-loss
+ * counts in norm_colloc / norm_ic / norm_bc (each >= this call's count), the whole collocation
+ * set's number of points inside the dielectric disk in norm_diel (0 <= norm_diel <=
+ * norm_colloc; see qp_count_dielectric; read when norm_colloc > 0) and the global index of
+ * this call's first collocation point in colloc_offset (energy slices of Eq. 31; requires
+ * colloc_offset + n_colloc <= norm_colloc). The loss terms and gradients of the calls then sum
+ * to those of the whole loss. All zero: the call's own sets are the whole loss. Invalid
+ * combinations fail with QP_ERR_INVALID_ARG before any launch. */
 typedef struct {
   const float* colloc;
   int64_t n_colloc;
@@ -119,6 +129,7 @@ typedef struct {
   int64_t n_ic;
   const float* bc;
   int64_t n_bc;
+  int64_t norm_colloc, norm_ic, norm_bc, norm_diel, colloc_offset;
 } qp_batch;
 
 /* Layout of d_loss written by qp_loss_grad (float64):
@@ -163,6 +174,34 @@ qp_status qp_forward(qp_plan* plan, const float* d_params, const float* d_pts, i
  * total loss w.r.t. every parameter (float32 [n_params]; Omega entries get 0). */
 qp_status qp_loss_grad(qp_plan* plan, const float* d_params, const qp_batch* batch,
                        double* d_loss, float* d_grad, void* stream);
+
+/* Number of points of d_pts [n][3] strictly inside the problem's dielectric disk (the test the
+ * loss uses), written to the device int64 *d_count (overwritten). For sharded losses: the
+ * ranks all-reduce their counts into qp_batch.norm_diel. QP_ERR_INVALID_ARG for bad pointers
+ * or n < 0; a vacuum problem writes 0. */
+qp_status qp_count_dielectric(qp_plan* plan, const float* d_pts, int64_t n, int64_t* d_count,
+                              void* stream);
+
+/* One loss evaluation of a batched step (qp_batch_step): parameters, point sets and
+ * outputs of one instance, with the meaning they have in qp_loss_grad. */
+typedef struct {
+  const float* d_params;
+  qp_batch batch;
+  double* d_loss;
+  float* d_grad;
+} qp_step_args;
+
+/* Loss and gradient of `count` independent instances (the paper's experiments train many
+ * configurations; each instance is its own circuit, problem and point sets) in one call:
+ * instance i is qp_loss_grad(plans[i], args[i]...). The instances run concurrently on
+ * library-owned streams forked from `stream` (longest first, each on the least loaded
+ * stream) and joined back into it, so work issued on `stream` after the call sees every
+ * result; the call is capturable into a CUDA graph on `stream`. Every plan must have its
+ * own workspace (the same plan may not appear twice). All arguments are checked before any
+ * launch (QP_ERR_INVALID_ARG, QP_ERR_BUFFER_TOO_SMALL, QP_ERR_UNSUPPORTED as qp_loss_grad);
+ * the first instance that fails to launch stops the call with its status, after the
+ * streams are joined. */
+qp_status qp_batch_step(qp_plan* const* plans, int32_t count, const qp_step_args* args, void* stream);
 
 /* Synchronise the stream of the last call on this plan and return the device status word
  * (QP_OK, QP_ERR_NONFINITE or QP_ERR_TIMEOUT) or QP_ERR_CUDA for a sticky CUDA error. */

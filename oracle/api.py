@@ -38,6 +38,8 @@ def lib():
         L.qpo_loss.argtypes = [_P, _P, _P, _P, _P, _I64, _P, _I64, _P, _I64, _P]
         L.qpo_grad.argtypes = [_P, _P, _P, _P, _P, _I64, _P, _I64, _P, _I64, _P, _I64, _P,
                                ctypes.c_int]
+        L.qpo_count_diel.restype = _I64
+        L.qpo_count_diel.argtypes = [_P, _P, _P, _I64]
         L.qpo_loss_from_fields.argtypes = [_P, _P, _P, _I64, _P, _P, _P, _I64, _P, _P, _I64, _P, _P]
         _lib = L
     return _lib
@@ -54,9 +56,15 @@ def circ_array(circ):
                      circ.get("mlp_depth", 0)], dtype=np.int32)
 
 
-def prob_arrays(prob):
+def prob_arrays(prob, norm=None):
+    """norm: optional sharding of one loss over several calls, dict with the whole-loss counts
+    n_colloc, n_ic, n_bc, the whole set's n_diel (points inside the disk) and colloc_offset
+    (global index of this call's first collocation point)."""
+    nm = norm or {}
     pi = np.array([1 if prob["medium"] == "dielectric" else 0, prob.get("energy_slice", 0),
-                   prob.get("energy_nt", 0)], dtype=np.int32)
+                   prob.get("energy_nt", 0), nm.get("n_colloc", 0), nm.get("n_ic", 0),
+                   nm.get("n_bc", 0), nm.get("n_diel", 0), nm.get("colloc_offset", 0)],
+                  dtype=np.int32)
     pd = np.array([prob["eps_r"], prob["disk_r"], prob["disk_x0"], prob["disk_y0"],
                    prob["sigmoid_w"], prob["ic_sigma"], prob["ic_x0"], prob["ic_y0"], prob["w_ic"],
                    prob["w_bc"], prob["w_energy"]], dtype=np.float64)
@@ -135,9 +143,9 @@ def _sets(sets):
     return out
 
 
-def loss(circ, prob, params, sets):
+def loss(circ, prob, params, sets, norm=None):
     ci = circ_array(circ)
-    pi, pd = prob_arrays(prob)
+    pi, pd = prob_arrays(prob, norm)
     p = _f64(params)
     c, i, b = _sets(sets)
     out = np.zeros(NLOSS + max(prob.get("energy_nt", 0), 0))
@@ -147,9 +155,9 @@ def loss(circ, prob, params, sets):
     return out
 
 
-def grad(circ, prob, params, sets, idx=None, nthreads=None):
+def grad(circ, prob, params, sets, idx=None, nthreads=None, norm=None):
     ci = circ_array(circ)
-    pi, pd = prob_arrays(prob)
+    pi, pd = prob_arrays(prob, norm)
     p = _f64(params)
     c, i, b = _sets(sets)
     if idx is None:
@@ -178,3 +186,10 @@ def loss_from_fields(prob, colloc, fc, dfc, ic=None, fi=None, bc=None, fb=None):
                                _ptr(ic), ic.shape[0], _ptr(fi), _ptr(bc), bc.shape[0], _ptr(fb),
                                _ptr(out))
     return out
+
+
+def count_dielectric(prob, pts):
+    """Points of pts [n,3] inside the dielectric disk (the loss's own test)."""
+    pi, pd = prob_arrays(prob)
+    p = _f64(pts).reshape(-1, 3)
+    return int(lib().qpo_count_diel(_ptr(pi), _ptr(pd), _ptr(p), p.shape[0]))

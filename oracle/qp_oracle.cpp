@@ -39,6 +39,9 @@
 //     premap: 0 direct (theta_j = scale(v_j), j < n_direct; 0 otherwise)
 //             1 RFF + tanh MLP (a = tanh(h_out), theta = scale(a))
 //   pi[0..2]  = medium (0 vacuum, 1 dielectric), energy_slice_size, energy_nt
+//   pi[3..7]  = sharding: whole-loss counts of the collocation, IC and BC sets (0 = this
+//               call's), whole-set points inside the disk, global index of the first
+//               collocation point (see Prob)
 //   pd[0..10] = eps_r, disk_r, disk_x0, disk_y0, sigmoid_w, ic_sigma, ic_x0, ic_y0,
 //               w_ic, w_bc, w_energy
 // Parameter layout (flat):
@@ -167,11 +170,18 @@ bool circ_ok(const Circ& c) {
 
 struct Prob {
   int medium, slice, nt;
+  // Sharding of one loss over several calls: the means of Eqs. 11-17 and 23 run over the
+  // whole point sets, so a call holding part of them divides its sums by the whole counts
+  // (norm_*; 0 = this call's own sets), uses the whole set's number of points inside the
+  // disk (norm_diel, read when norm_c > 0) and places its collocation points in the energy
+  // slices of Eq. 31 from global index colloc_off on.
+  int64_t norm_c, norm_i, norm_b, norm_diel, colloc_off;
   double eps_r, disk_r, x0, y0, sw, ic_sigma, ic_x0, ic_y0, w_ic, w_bc, w_energy;
 };
 Prob read_prob(const int* pi, const double* pd) {
   Prob p;
   p.medium = pi[0]; p.slice = pi[1]; p.nt = pi[2];
+  p.norm_c = pi[3]; p.norm_i = pi[4]; p.norm_b = pi[5]; p.norm_diel = pi[6]; p.colloc_off = pi[7];
   p.eps_r = pd[0]; p.disk_r = pd[1]; p.x0 = pd[2]; p.y0 = pd[3]; p.sw = pd[4];
   p.ic_sigma = pd[5]; p.ic_x0 = pd[6]; p.ic_y0 = pd[7];
   p.w_ic = pd[8]; p.w_bc = pd[9]; p.w_energy = pd[10];
@@ -385,7 +395,10 @@ void loss_terms(const Prob& pb, const double* pc, int64_t Bc, const std::vector<
   D s1v{0, 0}, s1d{0, 0}, s2{0, 0}, s3{0, 0}, se{0, 0};
   int64_t nd = 0;
   for (int64_t b = 0; b < Bc; ++b) nd += in_diel(pb, pc[3 * b], pc[3 * b + 1]) ? 1 : 0;
-  const int64_t nv = Bc - nd;
+  const int64_t Nc = pb.norm_c > 0 ? pb.norm_c : Bc;   // collocation mean denominator
+  if (pb.norm_c > 0) nd = pb.norm_diel;
+  const int64_t nv = Nc - nd;
+  const int64_t Ni = pb.norm_i > 0 ? pb.norm_i : Bi, Nb = pb.norm_b > 0 ? pb.norm_b : Bb;
   std::vector<double> U(pb.nt > 0 ? pb.nt : 0, 0.0);
   for (int64_t b = 0; b < Bc; ++b) {
     const double x = pc[3 * b], y = pc[3 * b + 1];
@@ -407,7 +420,7 @@ void loss_terms(const Prob& pb, const double* pc, int64_t Bc, const std::vector<
           (dd(0, 0) * f[2] + f[0] * dd(2, 0)) + (dd(0, 1) * f[1] + f[0] * dd(1, 1));
     se = se + e * e;
     if (pb.nt > 0 && pb.slice > 0) {
-      int64_t k = b / pb.slice;
+      int64_t k = (pb.colloc_off + b) / pb.slice;
       if (k < pb.nt) U[k] += 0.5 * (eps * f[0].v * f[0].v + f[1].v * f[1].v + f[2].v * f[2].v);
     }
   }
@@ -415,13 +428,13 @@ void loss_terms(const Prob& pb, const double* pc, int64_t Bc, const std::vector<
   if (pb.medium == 1) {
     if (nv > 0) mse1v = (1.0 / nv) * s1v;
     if (nd > 0) mse1d = (1.0 / nd) * s1d;
-  } else if (Bc > 0) {
-    mse1v = (1.0 / Bc) * s1v;
+  } else if (Nc > 0) {
+    mse1v = (1.0 / Nc) * s1v;
   }
-  D mse2 = Bc > 0 ? (1.0 / Bc) * s2 : D{0, 0};
-  D mse3 = Bc > 0 ? (1.0 / Bc) * s3 : D{0, 0};
+  D mse2 = Nc > 0 ? (1.0 / Nc) * s2 : D{0, 0};
+  D mse3 = Nc > 0 ? (1.0 / Nc) * s3 : D{0, 0};
   D phys = mse1v + mse1d + mse2 + mse3;
-  D energy = Bc > 0 ? (pb.w_energy / Bc) * se : D{0, 0};
+  D energy = Nc > 0 ? (pb.w_energy / Nc) * se : D{0, 0};
   // Eq. 17 with a Gaussian pulse centred at (ic_x0, ic_y0): exp(-r^2 / (2 sigma^2)).
   D sic{0, 0};
   for (int64_t b = 0; b < Bi; ++b) {
@@ -430,11 +443,11 @@ void loss_terms(const Prob& pb, const double* pc, int64_t Bc, const std::vector<
     D m0 = Fi[3 * b] - D{e0, 0};
     sic = sic + m0 * m0 + Fi[3 * b + 1] * Fi[3 * b + 1] + Fi[3 * b + 2] * Fi[3 * b + 2];
   }
-  D ic = Bi > 0 ? (pb.w_ic / Bi) * sic : D{0, 0};
+  D ic = Ni > 0 ? (pb.w_ic / Ni) * sic : D{0, 0};
   // PEC boundary: tangential E vanishes, Ez = 0 on the edges.
   D sbc{0, 0};
   for (int64_t b = 0; b < Bb; ++b) sbc = sbc + Fb[3 * b] * Fb[3 * b];
-  D bc = Bb > 0 ? (pb.w_bc / Bb) * sbc : D{0, 0};
+  D bc = Nb > 0 ? (pb.w_bc / Nb) * sbc : D{0, 0};
   D tot = phys + ic + bc + energy;
   D terms[9] = {tot, phys, ic, bc, energy, mse1v, mse1d, mse2, mse3};
   for (int i = 0; i < 9; ++i) {
@@ -605,6 +618,15 @@ int qpo_grad(const int* ci, const int* pi, const double* pd, const double* param
 
 // Loss terms from externally given fields (no circuit): f_c[Bc][3], df_c[Bc][3][3],
 // f_i[Bi][3], f_b[Bb][3]. Used to pin the residual and energy formulas.
+// Number of points of pts[n][3] inside the dielectric disk (the in_diel test of the loss).
+int64_t qpo_count_diel(const int* pi, const double* pd, const double* pts, int64_t n) {
+  Prob pb = read_prob(pi, pd);
+  int64_t c = 0;
+  if (pb.medium != 1) return 0;
+  for (int64_t b = 0; b < n; ++b) c += in_diel(pb, pts[3 * b], pts[3 * b + 1]) ? 1 : 0;
+  return c;
+}
+
 int qpo_loss_from_fields(const int* pi, const double* pd, const double* pc, int64_t Bc,
                          const double* fc, const double* dfc, const double* pi_, int64_t Bi,
                          const double* fi, const double* pbnd, int64_t Bb, const double* fb,

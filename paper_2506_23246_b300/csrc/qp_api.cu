@@ -3,7 +3,10 @@
 #include <cuda_runtime.h>
 
 #include <cstdio>
+#include <algorithm>
 #include <cstring>
+#include <mutex>
+#include <vector>
 #include <new>
 
 #include "../../include/qpinn.h"
@@ -23,6 +26,8 @@ struct qp_plan {
   int32_t path;
   QPSched sched;
   int device = 0, sm_count = 0;
+  // sharding of the current loss call (qp_batch norm_* fields; zeros: unsharded)
+  int64_t cur_norm[3] = {0, 0, 0}, cur_norm_diel = 0, cur_colloc_off = 0;
   int warps_grad = 0, blocks_grad = 0, warps_fwd = 0, blocks_fwd = 0;
   int smem_grad = 0, smem_fwd = 0, sstride_grad = 0, sstride_fwd = 0;
   int nwblk = 0, wtile = 0, smem_wgrad = 0, smem_premap = 0;
@@ -49,6 +54,19 @@ int64_t premap_count(const qp_circuit& c) {
 
 int geo_lb(int n) { return n <= 3 ? n : (n <= 8 ? 3 : n - 5); }
 int geo_ppw(int n) { return 32 >> (n - geo_lb(n)); }
+
+// Dynamic shared-memory allowance of a kernel. The attribute belongs to the function, not to a
+// plan, so plans only ever raise it: a plan created later with a smaller need must not shrink
+// the allowance an earlier plan's launches rely on.
+static std::mutex g_attr_mu;
+static cudaError_t raise_smem_limit(const void* fn, cudaFuncAttribute attr, int bytes) {
+  std::lock_guard<std::mutex> lk(g_attr_mu);
+  cudaFuncAttributes fa;
+  cudaError_t e = cudaFuncGetAttributes(&fa, fn);
+  if (e != cudaSuccess) return e;
+  if (fa.maxDynamicSharedSizeBytes >= bytes) return cudaSuccess;
+  return cudaFuncSetAttribute(fn, attr, bytes);
+}
 
 struct WsLayout {
   size_t status, gates, cmat, cenc, thetaJ, dthetaJ, d1, d2, u1, blk_loss, blk_grad, wpart;
@@ -263,7 +281,7 @@ qp_status qp_plan_create(const qp_circuit* circuit, const qp_problem* problem, i
     }
     if (warps < 1) { delete pl; return QP_ERR_UNSUPPORTED; }
     void* fn = circuit_kernel_ptr(n, grad);
-    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, lay.total) != cudaSuccess) {
+    if (raise_smem_limit(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, lay.total) != cudaSuccess) {
       cudaGetLastError();
       delete pl;
       return QP_ERR_CUDA;
@@ -280,22 +298,22 @@ qp_status qp_plan_create(const qp_circuit* circuit, const qp_problem* problem, i
     }
   }
   if (dense_path(pl)) {
-    if (cudaFuncSetAttribute((void*)qpd::dense_build_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    if (raise_smem_limit((void*)qpd::dense_build_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              2 * (1 << n) * 16) != cudaSuccess ||
-        cudaFuncSetAttribute((void*)qpd::dense_row_gemm_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        raise_smem_limit((void*)qpd::dense_row_gemm_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              qpd::gemm_smem_bytes(n, 0)) != cudaSuccess ||
-        cudaFuncSetAttribute((void*)qpd::dense_row_gemm_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        raise_smem_limit((void*)qpd::dense_row_gemm_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              qpd::gemm_smem_bytes(n, 1)) != cudaSuccess ||
-        cudaFuncSetAttribute((void*)qpd::dense_wgrad_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        raise_smem_limit((void*)qpd::dense_wgrad_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              qpd::wg_smem_bytes(n)) != cudaSuccess ||
-        cudaFuncSetAttribute((void*)qpd::dense_sweep_left_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        raise_smem_limit((void*)qpd::dense_sweep_left_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (1 << n) * 16 * 8) != cudaSuccess ||
-        cudaFuncSetAttribute((void*)qpd::dense_sweep_right_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        raise_smem_limit((void*)qpd::dense_sweep_right_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (1 << n) * 16 * 8) != cudaSuccess ||
         (fused_path(pl) &&
-         (cudaFuncSetAttribute((void*)qpd::dense_fused_fwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+         (raise_smem_limit((void*)qpd::dense_fused_fwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                qpd::fused_smem(n, pl->p.energy_nt).total) != cudaSuccess ||
-          cudaFuncSetAttribute((void*)qpd::dense_mu_embed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+          raise_smem_limit((void*)qpd::dense_mu_embed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                qpd::mu_smem_bytes(n)) != cudaSuccess))) {
       cudaGetLastError();
       delete pl;
@@ -310,9 +328,9 @@ qp_status qp_plan_create(const qp_circuit* circuit, const qp_problem* problem, i
     while (tile > 1 && (tile * (2 * F + 2 * H + n) * 16 + 3 * F * 4) > 96 * 1024) tile >>= 1;
     pl->wtile = tile;
     pl->smem_wgrad = tile * (2 * F + 2 * H + n) * 16 + 3 * F * 4;
-    if (cudaFuncSetAttribute(premap_fwd_ptr(H), cudaFuncAttributeMaxDynamicSharedMemorySize, pl->smem_premap) != cudaSuccess ||
-        cudaFuncSetAttribute(premap_bwd_ptr(H), cudaFuncAttributeMaxDynamicSharedMemorySize, pl->smem_premap) != cudaSuccess ||
-        cudaFuncSetAttribute((void*)qpk::premap_wgrad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, pl->smem_wgrad) != cudaSuccess) {
+    if (raise_smem_limit(premap_fwd_ptr(H), cudaFuncAttributeMaxDynamicSharedMemorySize, pl->smem_premap) != cudaSuccess ||
+        raise_smem_limit(premap_bwd_ptr(H), cudaFuncAttributeMaxDynamicSharedMemorySize, pl->smem_premap) != cudaSuccess ||
+        raise_smem_limit((void*)qpk::premap_wgrad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, pl->smem_wgrad) != cudaSuccess) {
       cudaGetLastError();
       delete pl;
       return QP_ERR_CUDA;
@@ -367,6 +385,9 @@ static void fill_problem(const qp_plan* pl, QPProblemDev& d) {
   d.disk_y0 = p.disk_y0; d.sigmoid_w = p.sigmoid_w; d.ic_sigma = p.ic_sigma; d.ic_x0 = p.ic_x0;
   d.ic_y0 = p.ic_y0; d.w_ic = p.w_ic; d.w_bc = p.w_bc; d.w_energy = p.w_energy;
   d.energy_slice = p.energy_slice; d.energy_nt = p.energy_nt;
+  for (int i = 0; i < 3; ++i) d.norm[i] = pl->cur_norm[i];
+  d.norm_diel = pl->cur_norm_diel;
+  d.colloc_off = pl->cur_colloc_off;
 }
 
 // Shared prologue: gate preparation and premap forward for all point sets.
@@ -620,6 +641,8 @@ static qp_status dense_loss_grad(qp_plan* pl, const float* d_params, const float
 qp_status qp_forward(qp_plan* pl, const float* d_params, const float* d_pts, int64_t B,
                      float* d_fields, float* d_dfields, void* stream) {
   if (!pl || !d_params || B < 0 || (B > 0 && (!d_pts || !d_fields))) return QP_ERR_INVALID_ARG;
+  pl->cur_norm[0] = pl->cur_norm[1] = pl->cur_norm[2] = 0;
+  pl->cur_norm_diel = pl->cur_colloc_off = 0;
   pl->last_launches = 0;
   if (B == 0) return QP_OK;
   const WsLayout w = ws_layout(pl, B);
@@ -674,12 +697,38 @@ qp_status qp_forward(qp_plan* pl, const float* d_params, const float* d_pts, int
   return cuda_status(cudaGetLastError());
 }
 
-qp_status qp_loss_grad(qp_plan* pl, const float* d_params, const qp_batch* batch, double* d_loss,
-                       float* d_grad, void* stream) {
+// Argument checks of a loss call (nothing launched, no plan state changed).
+static qp_status check_loss_args(const qp_plan* pl, const float* d_params, const qp_batch* batch,
+                                 const double* d_loss, const float* d_grad) {
   if (!pl || !d_params || !batch || !d_loss || !d_grad) return QP_ERR_INVALID_ARG;
   if (batch->n_colloc < 0 || batch->n_ic < 0 || batch->n_bc < 0) return QP_ERR_INVALID_ARG;
   if ((batch->n_colloc && !batch->colloc) || (batch->n_ic && !batch->ic) || (batch->n_bc && !batch->bc))
     return QP_ERR_INVALID_ARG;
+  // sharding fields: whole-loss counts cover this call's sets, the offset places its
+  // collocation points inside the whole set
+  const int64_t nloc[3] = {batch->n_colloc, batch->n_ic, batch->n_bc};
+  const int64_t nrm[3] = {batch->norm_colloc, batch->norm_ic, batch->norm_bc};
+  for (int i = 0; i < 3; ++i)
+    if (nrm[i] < 0 || (nrm[i] > 0 && nrm[i] < nloc[i])) return QP_ERR_INVALID_ARG;
+  if (batch->colloc_offset < 0) return QP_ERR_INVALID_ARG;
+  if (nrm[0] > 0 && (batch->norm_diel < 0 || batch->norm_diel > nrm[0] ||
+                     batch->colloc_offset + batch->n_colloc > nrm[0]))
+    return QP_ERR_INVALID_ARG;
+  if (nrm[0] == 0 && batch->colloc_offset != 0) return QP_ERR_INVALID_ARG;
+  if (dense_path(pl) && pl->c.n_qubits < 7) return QP_ERR_UNSUPPORTED;
+  const int64_t P = nloc[0] + nloc[1] + nloc[2];
+  if (!pl->ws || pl->ws_bytes < ws_layout(pl, P).total) return QP_ERR_BUFFER_TOO_SMALL;
+  return QP_OK;
+}
+
+qp_status qp_loss_grad(qp_plan* pl, const float* d_params, const qp_batch* batch, double* d_loss,
+                       float* d_grad, void* stream) {
+  const qp_status chk = check_loss_args(pl, d_params, batch, d_loss, d_grad);
+  if (chk != QP_OK) return chk;
+  const int64_t nrm[3] = {batch->norm_colloc, batch->norm_ic, batch->norm_bc};
+  for (int i = 0; i < 3; ++i) pl->cur_norm[i] = nrm[i];
+  pl->cur_norm_diel = nrm[0] > 0 ? batch->norm_diel : 0;
+  pl->cur_colloc_off = batch->colloc_offset;
   pl->last_launches = 0;
   const float* pts[3] = {batch->colloc, batch->ic, batch->bc};
   if (dense_path(pl)) {
@@ -789,7 +838,10 @@ static qp_status launch_reduce(qp_plan* pl, const WsLayout& w, const float* d_pa
   ra.n = pl->c.n_qubits; ra.L = pl->c.n_layers; ra.m = pl->c.n_readout;
   ra.k = pl->c.ansatz == QP_ANSATZ_BASIC_RYRZ ? 2 : 3;
   ra.nt = pl->p.energy_nt; ra.medium = pl->p.medium;
-  ra.nc = npts[0]; ra.ni = npts[1]; ra.nb = npts[2];
+  ra.nc = pl->cur_norm[0] > 0 ? pl->cur_norm[0] : npts[0];
+  ra.ni = pl->cur_norm[1] > 0 ? pl->cur_norm[1] : npts[1];
+  ra.nb = pl->cur_norm[2] > 0 ? pl->cur_norm[2] : npts[2];
+  ra.norm_diel = pl->cur_norm[0] > 0 ? pl->cur_norm_diel : -1;
   ra.w_ic = pl->p.w_ic; ra.w_bc = pl->p.w_bc; ra.w_energy = pl->p.w_energy;
   const int64_t nred = pl->n_params > QP_MAXNT ? pl->n_params : QP_MAXNT;
   qpk::reduce_kernel<<<(unsigned)((nred + 255) / 256), 256, 0, s>>>(ra);
@@ -845,6 +897,93 @@ qp_status noalloc_scratch_address(void** out) {
   return QP_OK;
 }
 }  // namespace
+
+qp_status qp_count_dielectric(qp_plan* pl, const float* d_pts, int64_t n, int64_t* d_count, void* stream) {
+  if (!pl || !d_count || n < 0 || (n > 0 && !d_pts)) return QP_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (cudaMemsetAsync(d_count, 0, sizeof(int64_t), s) != cudaSuccess) return QP_ERR_CUDA;
+  pl->last_launches = 0;
+  if (n > 0 && pl->p.medium == QP_MEDIUM_DIELECTRIC) {
+    const int64_t nb = (n + 255) / 256;
+    qpk::count_dielectric_kernel<<<(unsigned)(nb < pl->sm_count * 4 ? nb : pl->sm_count * 4), 256, 0, s>>>(
+        d_pts, n, pl->p.disk_x0, pl->p.disk_y0, pl->p.disk_r, reinterpret_cast<unsigned long long*>(d_count));
+    if (cudaGetLastError() != cudaSuccess) return QP_ERR_CUDA;
+    pl->last_launches = 1;
+  }
+  return QP_OK;
+}
+
+namespace {
+// Library-owned worker streams of qp_batch_step, created once per device.
+constexpr int QP_BATCH_STREAMS = 8;
+struct BatchStreams {
+  cudaStream_t st[QP_BATCH_STREAMS];
+  cudaEvent_t fork, join[QP_BATCH_STREAMS];
+  bool ok = false;
+};
+std::mutex g_batch_mu;
+BatchStreams g_batch[64];
+
+BatchStreams* batch_streams() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+  std::lock_guard<std::mutex> lk(g_batch_mu);
+  BatchStreams& b = g_batch[dev];
+  if (!b.ok) {
+    for (int i = 0; i < QP_BATCH_STREAMS; ++i) {
+      if (cudaStreamCreateWithFlags(&b.st[i], cudaStreamNonBlocking) != cudaSuccess) return nullptr;
+      if (cudaEventCreateWithFlags(&b.join[i], cudaEventDisableTiming) != cudaSuccess) return nullptr;
+    }
+    if (cudaEventCreateWithFlags(&b.fork, cudaEventDisableTiming) != cudaSuccess) return nullptr;
+    b.ok = true;
+  }
+  return &b;
+}
+}  // namespace
+
+qp_status qp_batch_step(qp_plan* const* plans, int32_t count, const qp_step_args* args, void* stream) {
+  if (count < 0 || (count > 0 && (!plans || !args))) return QP_ERR_INVALID_ARG;
+  for (int32_t i = 0; i < count; ++i) {
+    for (int32_t j = 0; j < i; ++j)
+      if (plans[j] == plans[i]) return QP_ERR_INVALID_ARG;
+    const qp_status c = check_loss_args(plans[i], args[i].d_params, &args[i].batch, args[i].d_loss, args[i].d_grad);
+    if (c != QP_OK) return c;
+  }
+  if (count == 0) return QP_OK;
+  BatchStreams* bs = batch_streams();
+  if (!bs) return QP_ERR_CUDA;
+  cudaStream_t s = (cudaStream_t)stream;
+  // longest first, each onto the least loaded stream (work ~ rows x layers x qubits x 2^n)
+  std::vector<int32_t> order(count);
+  std::vector<double> cost(count);
+  for (int32_t i = 0; i < count; ++i) {
+    const qp_batch& b = args[i].batch;
+    const qp_circuit& c = plans[i]->c;
+    cost[i] = (double)(4 * b.n_colloc + b.n_ic + b.n_bc + 1) * c.n_layers * c.n_qubits * (double)(1 << c.n_qubits);
+    order[i] = i;
+  }
+  std::sort(order.begin(), order.end(), [&](int32_t x, int32_t y) { return cost[x] > cost[y]; });
+  const int nst = count < QP_BATCH_STREAMS ? count : QP_BATCH_STREAMS;
+  double load[QP_BATCH_STREAMS] = {0};
+  if (cudaEventRecord(bs->fork, s) != cudaSuccess) return QP_ERR_CUDA;
+  for (int k = 0; k < nst; ++k)
+    if (cudaStreamWaitEvent(bs->st[k], bs->fork, 0) != cudaSuccess) return QP_ERR_CUDA;
+  qp_status st = QP_OK;
+  for (int32_t oi = 0; oi < count && st == QP_OK; ++oi) {
+    const int32_t i = order[oi];
+    int k = 0;
+    for (int q = 1; q < nst; ++q)
+      if (load[q] < load[k]) k = q;
+    load[k] += cost[i];
+    st = qp_loss_grad(plans[i], args[i].d_params, &args[i].batch, args[i].d_loss, args[i].d_grad, bs->st[k]);
+  }
+  for (int k = 0; k < nst; ++k) {
+    if (cudaEventRecord(bs->join[k], bs->st[k]) != cudaSuccess) return QP_ERR_CUDA;
+    if (cudaStreamWaitEvent(s, bs->join[k], 0) != cudaSuccess) return QP_ERR_CUDA;
+  }
+  return st;
+}
+
 
 extern "C" qp_status qp_forward_noalloc(qp_plan* pl, const float* d_params, const float* d_pts,
                                         int64_t B, float* d_fields, float* d_dfields, void* stream) {

@@ -413,6 +413,19 @@ __global__ void premap_wgrad_kernel(WgradArgs w) {
   }
 }
 
+// Number of points strictly inside the dielectric disk (the same float32 test as the loss).
+__global__ void count_dielectric_kernel(const float* pts, int64_t n, float x0, float y0, float r,
+                                        unsigned long long* out) {
+  unsigned long long c = 0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const float dx = pts[3 * i] - x0, dy = pts[3 * i + 1] - y0;
+    c += __fmaf_rn(dx, dx, dy * dy) < r * r ? 1ull : 0ull;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+  if ((threadIdx.x & 31) == 0 && c) atomicAdd(out, c);
+}
+
 // --------------------------------------------------------------------------- final reduce
 
 struct ReduceArgs {
@@ -428,7 +441,8 @@ struct ReduceArgs {
   float* grad;
   int64_t nparams, circ_off, head_off, mlp_off, mlp_count;
   int32_t n, L, m, k, nt, medium;
-  int64_t nc, ni, nb;
+  int64_t nc, ni, nb;          // mean denominators of the three sets
+  int64_t norm_diel;           // whole-set points inside the disk, or -1: the counted ones
   float w_ic, w_bc, w_energy;
 };
 
@@ -465,7 +479,7 @@ __global__ void reduce_kernel(ReduceArgs a) {
     for (int b = 0; b < a.nblk; ++b)
       for (int k = 0; k < QP_NLP; ++k) s[k] += a.blk_loss[(int64_t)b * a.loss_stride + k];
     const double N = (double)a.nc;
-    const double nd = a.medium == 1 ? (double)a.counts[0] : 0.0;
+    const double nd = a.medium == 1 ? (a.norm_diel >= 0 ? (double)a.norm_diel : (double)a.counts[0]) : 0.0;
     const double nv = N - nd;
     double m1v = 0, m1d = 0;
     if (a.medium == 1) {

@@ -148,10 +148,10 @@ __device__ __forceinline__ void point_loss_terms(const QPProblemDev& pb, int set
     const float res3 = D[2][2] - D[0][0];
     const float e = eps * f[0] * D[0][2] + f[1] * D[1][2] + f[2] * D[2][2] -
                     (D[0][0] * f[2] + f[0] * D[2][0]) + (D[0][1] * f[1] + f[0] * D[1][1]);
-    const float N = (float)npt;
+    const float N = (float)(pb.norm[0] > 0 ? pb.norm[0] : npt);
     float N1 = N;
     if (pb.medium == 1) {
-      const float nd = (float)counts[0];
+      const float nd = (float)(pb.norm[0] > 0 ? pb.norm_diel : counts[0]);
       N1 = diel ? nd : N - nd;
     }
     const float k1 = 2.f * res1 / N1, k2 = 2.f * res2 / N, k3 = 2.f * res3 / N;
@@ -173,7 +173,7 @@ __device__ __forceinline__ void point_loss_terms(const QPProblemDev& pb, int set
     lt[3] = (double)res3 * (double)res3;
     lt[4] = (double)e * (double)e;
     if (pb.energy_nt > 0 && pb.energy_slice > 0) {
-      const int64_t k = pt / pb.energy_slice;
+      const int64_t k = (pt + pb.colloc_off) / pb.energy_slice;
       if (k < pb.energy_nt) {
         slice = (int)k;
         ev = 0.5 * ((double)eps * f[0] * f[0] + (double)f[1] * f[1] + (double)f[2] * f[2]);
@@ -182,13 +182,13 @@ __device__ __forceinline__ void point_loss_terms(const QPProblemDev& pb, int set
   } else if (set == 1) {
     const float dx = x - pb.ic_x0, dy = y - pb.ic_y0;
     const float e0 = expf(-(dx * dx + dy * dy) / (2.f * pb.ic_sigma * pb.ic_sigma));
-    const float k = 2.f * pb.w_ic / (float)npt;
+    const float k = 2.f * pb.w_ic / (float)(pb.norm[1] > 0 ? pb.norm[1] : npt);
     g[0] = k * (f[0] - e0);
     g[1] = k * f[1];
     g[2] = k * f[2];
     lt[5] = (double)(f[0] - e0) * (f[0] - e0) + (double)f[1] * f[1] + (double)f[2] * f[2];
   } else {
-    g[0] = 2.f * pb.w_bc * f[0] / (float)npt;
+    g[0] = 2.f * pb.w_bc * f[0] / (float)(pb.norm[2] > 0 ? pb.norm[2] : npt);
     lt[6] = (double)f[0] * f[0];
   }
 }

@@ -45,6 +45,10 @@ struct QPProblemDev {
   float eps_r, disk_r, disk_x0, disk_y0, sigmoid_w;
   float ic_sigma, ic_x0, ic_y0, w_ic, w_bc, w_energy;
   int32_t energy_slice, energy_nt;
+  // sharding of one loss over several calls: whole-loss counts of the collocation, IC and BC
+  // sets (0: this call's), whole-set points inside the disk (read when norm[0] > 0), global
+  // index of this call's first collocation point (energy slices)
+  int64_t norm[3], norm_diel, colloc_off;
 };
 
 // Arguments of the circuit kernel (passed by value; the schedule is copied to shared memory).

@@ -45,7 +45,15 @@ class QPProblem(ctypes.Structure):
 class QPBatch(ctypes.Structure):
     _fields_ = [("colloc", ctypes.c_void_p), ("n_colloc", ctypes.c_int64),
                 ("ic", ctypes.c_void_p), ("n_ic", ctypes.c_int64),
-                ("bc", ctypes.c_void_p), ("n_bc", ctypes.c_int64)]
+                ("bc", ctypes.c_void_p), ("n_bc", ctypes.c_int64),
+                ("norm_colloc", ctypes.c_int64), ("norm_ic", ctypes.c_int64),
+                ("norm_bc", ctypes.c_int64), ("norm_diel", ctypes.c_int64),
+                ("colloc_offset", ctypes.c_int64)]
+
+
+class QPStepArgs(ctypes.Structure):
+    _fields_ = [("d_params", ctypes.c_void_p), ("batch", QPBatch), ("d_loss", ctypes.c_void_p),
+                ("d_grad", ctypes.c_void_p)]
 
 
 _lib = None
@@ -70,6 +78,8 @@ def lib():
         L.qp_set_workspace.argtypes = [P, P, ctypes.c_size_t]
         L.qp_forward.argtypes = [P, P, P, I64, P, P, P]
         L.qp_loss_grad.argtypes = [P, P, ctypes.POINTER(QPBatch), P, P, P]
+        L.qp_count_dielectric.argtypes = [P, P, I64, P, P]
+        L.qp_batch_step.argtypes = [ctypes.POINTER(P), I32, ctypes.POINTER(QPStepArgs), P]
         L.qp_last_device_error.argtypes = [P]
         L.qp_status_str.argtypes = [I32]
         L.qp_status_str.restype = ctypes.c_char_p
@@ -183,8 +193,7 @@ class Plan:
                                 self._stream(stream)), "qp_forward")
         return f, df
 
-    def loss_grad(self, params, sets, out=None, stream=None):
-        """Loss terms (float64 [9 + energy_nt]) and d total / d params (float32 [n_params])."""
+    def _batch(self, params, sets, norm):
         _dev_f32(params, None, "params")
         if params.numel() != self.n_params:
             raise ValueError("params has %d entries, plan expects %d" % (params.numel(), self.n_params))
@@ -195,19 +204,41 @@ class Plan:
                 ts[k] = _dev_f32(t, None, k)
         total = sum(t.shape[0] for t in ts.values())
         self.reserve(total, params.device)
+        nm = norm or {}
         batch = QPBatch(
             _ptr(ts.get("colloc")), ts["colloc"].shape[0] if "colloc" in ts else 0,
             _ptr(ts.get("ic")), ts["ic"].shape[0] if "ic" in ts else 0,
-            _ptr(ts.get("bc")), ts["bc"].shape[0] if "bc" in ts else 0)
-        if out is None:
-            nl = NLOSS + self.problem.get("energy_nt", 0)
-            loss = torch.empty(nl, dtype=torch.float64, device=params.device)
-            grad = torch.empty(self.n_params, dtype=torch.float32, device=params.device)
-        else:
-            loss, grad = out
+            _ptr(ts.get("bc")), ts["bc"].shape[0] if "bc" in ts else 0,
+            int(nm.get("n_colloc", 0)), int(nm.get("n_ic", 0)), int(nm.get("n_bc", 0)),
+            int(nm.get("n_diel", 0)), int(nm.get("colloc_offset", 0)))
+        return batch, ts
+
+    def _outputs(self, params, out):
+        if out is not None:
+            return out
+        nl = NLOSS + self.problem.get("energy_nt", 0)
+        return (torch.empty(nl, dtype=torch.float64, device=params.device),
+                torch.empty(self.n_params, dtype=torch.float32, device=params.device))
+
+    def loss_grad(self, params, sets, out=None, stream=None, norm=None):
+        """Loss terms (float64 [9 + energy_nt]) and d total / d params (float32 [n_params]).
+        norm: sharding of one loss over several calls (dict: whole-loss counts n_colloc, n_ic,
+        n_bc, whole-set n_diel, colloc_offset); see qp_batch in qpinn.h."""
+        batch, _ = self._batch(params, sets, norm)
+        loss, grad = self._outputs(params, out)
         _check(lib().qp_loss_grad(self._h, _ptr(params), ctypes.byref(batch), _ptr(loss), _ptr(grad),
                                   self._stream(stream)), "qp_loss_grad")
         return loss, grad
+
+    def count_dielectric(self, pts, out=None, stream=None):
+        """Number of points of pts [n,3] inside the dielectric disk, as a device int64 [1]."""
+        n = pts.shape[0]
+        if n > 0:
+            _dev_f32(pts, None, "pts")
+        c = out if out is not None else torch.empty(1, dtype=torch.int64, device=pts.device)
+        _check(lib().qp_count_dielectric(self._h, _ptr(pts) if n > 0 else None, n, _ptr(c),
+                                         self._stream(stream)), "qp_count_dielectric")
+        return c
 
     def last_device_error(self):
         return lib().qp_last_device_error(self._h)
@@ -225,6 +256,27 @@ class Plan:
         s = ctypes.c_void_p(start.cuda_event) if start is not None else ctypes.c_void_p(0)
         e = ctypes.c_void_p(stop.cuda_event) if stop is not None else ctypes.c_void_p(0)
         _check(lib().qp_set_profile_events(self._h, s, e), "qp_set_profile_events")
+
+
+def batch_step(plans, params, sets, outs=None, norms=None, stream=None):
+    """Loss and gradient of independent instances in one qp_batch_step call: plans[i] with
+    params[i] on sets[i]; returns [(loss, grad)] in the order given."""
+    k = len(plans)
+    outs = outs or [None] * k
+    norms = norms or [None] * k
+    arr = (QPStepArgs * max(k, 1))()
+    handles = (ctypes.c_void_p * max(k, 1))()
+    keep, res = [], []
+    for i in range(k):
+        batch, ts = plans[i]._batch(params[i], sets[i], norms[i])
+        loss, grad = plans[i]._outputs(params[i], outs[i])
+        keep.append(ts)
+        arr[i] = QPStepArgs(_ptr(params[i]), batch, _ptr(loss), _ptr(grad))
+        handles[i] = plans[i]._h
+        res.append((loss, grad))
+    s = stream if stream is not None else torch.cuda.current_stream()
+    _check(lib().qp_batch_step(handles, k, arr, ctypes.c_void_p(s.cuda_stream)), "qp_batch_step")
+    return res
 
 
 class QPINNLoss(torch.autograd.Function):
