@@ -306,17 +306,18 @@ def run_native(a):
                               "peaks)" % (sms, sm_max),
                 "traffic": profiled_traffic()}
     else:
-        # weight-gradient contraction G = sum R Lambda^H on the tensor cores: algorithmic
-        # 2 M N K with M = 2^n, N = 2^(n+1), K = (point, vector) rows; 3xTF32 runs three TF32
-        # products per term, so its ceiling is the TF32 peak / 3
+        # fused forward contraction Phi = R W^T on the tensor cores (the step's largest kernel),
+        # readout, losses and costates in its epilogue: algorithmic 2 M N K with M = (point,
+        # vector) rows, N = 2^(n+1), K = 2^n; 3xTF32 runs three TF32 products per term, so its
+        # ceiling is the TF32 peak / 3
         dim = 1 << 8
-        flops = 2.0 * dim * (2 * dim) * (4 * ncol + nic)
+        flops = 2.0 * (4 * ncol + nic) * (2 * dim) * dim
         bf16 = peaks.get("bf16_tflops", 1800.0)
         peak = bf16 * 0.5 / 3.0
-        roof = {"bound": "tensor", "kernel": "dense_wgrad_gemm_kernel (3xTF32)",
+        roof = {"bound": "tensor", "kernel": "dense_fused_fwd_kernel (3xTF32)",
                 "peak_basis": "measured bf16 %.0f TFLOP/s x 0.5 (nominal TF32/BF16 dense ratio) / 3 "
                               "(three TF32 products per 3xTF32 term)" % bf16,
-                "traffic": profiled_traffic("dense_wgrad_c3_8q6l.md", "qp_wgrad.cuh")}
+                "traffic": profiled_traffic("dense_fused_fwd_c3_8q6l.md", "qp_fused.cuh")}
     achieved = flops / (kms / 1000.0) / 1e12
 
     # end to end through the public call: pinned host inputs in, loss + gradient out

@@ -217,8 +217,9 @@ int32_t qp_plan_path(const qp_plan* plan);
 
 /* Optional profiling: two cudaEvent_t (passed as void*, created by the caller) that the
  * following compute calls record on their stream immediately before and after the dominant
- * kernel -- the statevector kernel on the SIMT path, the weight-gradient tensor-core
- * contraction on the GEMM path of qp_loss_grad, the forward contraction of qp_forward -- so
+ * kernel -- the statevector kernel on the SIMT path; on the GEMM path of qp_loss_grad the
+ * fused forward contraction (n = 7, 8) or the weight-gradient contraction (n >= 9); the
+ * forward contraction of qp_forward -- so
  * its device time can be read with cudaEventElapsedTime. Pass NULL, NULL to stop. The plan
  * does not own the events. */
 qp_status qp_set_profile_events(qp_plan* plan, void* ev_start, void* ev_stop);

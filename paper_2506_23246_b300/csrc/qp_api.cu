@@ -511,7 +511,9 @@ static qp_status dense_loss_grad(qp_plan* pl, const float* d_params, const float
     fa.status = (int32_t*)(ws + w.status);
     const int64_t ftiles = fa.tile_end[2];
     const int fblocks = (int)(ftiles < pl->sm_count ? (ftiles > 0 ? ftiles : 1) : pl->sm_count);
+    if (pl->prof_start) cudaEventRecord(pl->prof_start, s);
     qpd::dense_fused_fwd_kernel<<<fblocks, qpd::F_THREADS, qpd::fused_smem(n, pl->p.energy_nt).total, s>>>(fa);
+    if (pl->prof_stop) cudaEventRecord(pl->prof_stop, s);
     launches += 1;
   } else {
     for (int set = 0; set < 3; ++set) {
@@ -556,9 +558,9 @@ static qp_status dense_loss_grad(qp_plan* pl, const float* d_params, const float
   if (wgm.nslots > wg_geom(pl, (4 * P + qpd::WKC - 1) / qpd::WKC + 2).nslots) return QP_ERR_INTERNAL;
   wa.tiles = wgm.tiles; wa.ngroups = wgm.ngroups; wa.spc = wgm.spc; wa.fl = wgm.fl;
   wa.status = (int32_t*)(ws + w.status);
-  if (pl->prof_start) cudaEventRecord(pl->prof_start, s);
+  if (pl->prof_start && !fused) cudaEventRecord(pl->prof_start, s);
   qpd::dense_wgrad_gemm_kernel<<<wgm.tiles * wgm.ngroups, qpd::WG_THREADS, qpd::wg_smem_bytes(n), s>>>(wa);
-  if (pl->prof_stop) cudaEventRecord(pl->prof_stop, s);
+  if (pl->prof_stop && !fused) cudaEventRecord(pl->prof_stop, s);
   launches += 1;
   qpd::SweepArgs sa;
   sa.part = wa.part; sa.nchunks = (int32_t)wgm.nslots; sa.n = n; sa.L = L; sa.ansatz = pl->c.ansatz;
