@@ -382,9 +382,8 @@ __global__ void __launch_bounds__(F_THREADS, 1) dense_fused_fwd_kernel(FusedArgs
       const float t01[4] = {cb[0] + cb[1], -cb[0] + cb[1], cb[0] - cb[1], -cb[0] - cb[1]};
       const float t23[4] = {cb[2] + cb[3], -cb[2] + cb[3], cb[2] - cb[3], -cb[2] - cb[3]};
       const int s_r = nv4 ? ws : 0;
-      const int64_t pr = p0 + (nv4 ? lane : r);
-      const bool act = pr < np;
-      const int64_t lrow = lam_row(set, act ? pr : 0, s_r, a.npts[0], base);
+      (void)s_r;
+      const int64_t grow0 = lam_row(set, p0, 0, a.npts[0], base);   // first costate row of the tile
       for (int cc = 0; cc < half_cols; cc += 32) {
         const int col = hh * half_cols + cc;
         const int j0 = col >> 1;
@@ -437,10 +436,26 @@ __global__ void __launch_bounds__(F_THREADS, 1) dense_fused_fwd_kernel(FusedArgs
             outv[e] = make_float4(O[2 * e] * v[4 * e], O[2 * e] * v[4 * e + 1], O[2 * e + 1] * v[4 * e + 2],
                                   O[2 * e + 1] * v[4 * e + 3]);
         }
-        if (act) {
-          float4* d4 = reinterpret_cast<float4*>(a.lam + (int64_t)(col >> 8) * a.rtot * 256 + lrow * 256 + (col & 255));
+        // the column group's 128 rows are consecutive costate rows: stage the chunk in that
+        // order (operand stage 0 is idle during the epilogue) and store 128-byte row segments,
+        // four rows per warp instruction instead of one 16-byte piece of 32 rows
+        {
+          float4* stg = reinterpret_cast<float4*>(sm) + hh * 1024;   // [128 rows][8] float4
+          const int srow = nv4 ? lane * 4 + ws : r;
+          const int ssw = nv4 ? (lane & 7) : (lane & 7);
+          if (!nv4) named_bar(1 + hh);   // the previous chunk's stores have read the staging
 #pragma unroll
-          for (int e = 0; e < 8; ++e) d4[e] = outv[e];
+          for (int e = 0; e < 8; ++e) stg[srow * 8 + (e ^ ssw)] = outv[e];
+          named_bar(1 + hh);
+          const int gt = ws * 32 + lane;
+          const int nrows = (int)(nv4 ? (np - p0 < 32 ? (np - p0) * 4 : 128) : (np - p0 < TM ? np - p0 : TM));
+          float* gbase = a.lam + (int64_t)(col >> 8) * a.rtot * 256 + grow0 * 256 + (col & 255);
+#pragma unroll
+          for (int i = 0; i < 8; ++i) {
+            const int idx = i * 128 + gt, row = idx >> 3, c4 = idx & 7;
+            const int rsw = nv4 ? ((row >> 2) & 7) : (row & 7);
+            if (row < nrows) *reinterpret_cast<float4*>(gbase + (int64_t)row * 256 + c4 * 4) = stg[row * 8 + (c4 ^ rsw)];
+          }
         }
       }
     }
