@@ -70,7 +70,7 @@ static cudaError_t raise_smem_limit(const void* fn, cudaFuncAttribute attr, int 
 
 struct WsLayout {
   size_t status, gates, cmat, cenc, thetaJ, dthetaJ, d1, d2, u1, blk_loss, blk_grad, wpart;
-  size_t dW, dphi, dU, dG, dY, dpart, dWT, dmu, dW16, dcs, total;
+  size_t dW, dphi, dU, dG, dY, dpart, dWT, dmu, dW16, dcs, dgs, total;
 };
 
 // Rows of (point, vector) accumulated per weight-gradient chunk (bounds the FP32 tensor-core
@@ -108,6 +108,13 @@ bool fused_path(const qp_plan* pl) {
 
 size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
 
+// Slot groups of the weight-gradient partial sum: enough blocks to cover the GPU.
+int gsum_groups(const qp_plan* pl) {
+  const int64_t dd = (int64_t)1 << (2 * pl->c.n_qubits);
+  const int64_t g = ((int64_t)pl->sm_count * 8 * 256 + dd - 1) / dd;
+  return (int)(g < 1 ? 1 : (g > 8 ? 8 : g));
+}
+
 WsLayout ws_layout(const qp_plan* pl, int64_t P) {
   WsLayout w;
   const int n = pl->c.n_qubits, H = pl->c.premap == QP_PREMAP_RFF_MLP ? pl->c.mlp_width : 0;
@@ -143,6 +150,7 @@ WsLayout ws_layout(const qp_plan* pl, int64_t P) {
   w.dmu = o; o = al256(o + (dm && !fused_path(pl) ? (size_t)P * 4 * dim * 4 : 0));
   w.dW16 = o; o = al256(o + (dg && fused_path(pl) ? 2 * (2 * dim) * dim * 4 : 0));
   w.dcs = o; o = al256(o + (dg ? (size_t)P * n * 8 : 0));
+  w.dgs = o; o = al256(o + (dg ? (size_t)gsum_groups(pl) * dim * dim * 16 : 0));
   w.total = o;
   return w;
 }
@@ -566,7 +574,14 @@ static qp_status dense_loss_grad(qp_plan* pl, const float* d_params, const float
   sa.part = wa.part; sa.nchunks = (int32_t)wgm.nslots; sa.n = n; sa.L = L; sa.ansatz = pl->c.ansatz;
   sa.U = (const double2*)(ws + w.dU); sa.G = (float2*)(ws + w.dG); sa.Y = (float2*)(ws + w.dY);
   sa.params = d_params; sa.circ_off = pl->circ_off; sa.eout = (float*)(ws + w.blk_grad);
-  qpd::dense_gsum_kernel<<<(dim * dim + 255) / 256, 256, 0, s>>>(sa);
+  {
+    const int gg = gsum_groups(pl);
+    qpd::dense_gsum_kernel<<<dim3((dim * dim + 255) / 256, gg), 256, 0, s>>>(sa, gg, (float4*)(ws + w.dgs));
+    const int64_t fb = ((int64_t)dim * dim + 255) / 256;
+    qpd::dense_gsum_fin_kernel<<<(unsigned)(fb < pl->sm_count * 8 ? fb : pl->sm_count * 8), 256, 0, s>>>(
+        sa, gg, (const float4*)(ws + w.dgs));
+    launches += 1;
+  }
   qpd::dense_y_kernel<<<dim3(dim / 16, dim / 16), 256, 0, s>>>(sa);
   {
     float2* Ya = sa.Y;

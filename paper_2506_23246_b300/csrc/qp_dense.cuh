@@ -663,31 +663,51 @@ struct CSum {
   __device__ __forceinline__ float value() const { return s + c; }
 };
 
-__global__ void dense_gsum_kernel(SweepArgs a) {
+// G[k][j] = conj(sum over partial slots of part[slot][k][2j + re|im]), in two passes: slot
+// groups (grid.y) each give a compensated partial (re sum, re carry, im sum, im carry), then
+// the groups are combined. Eight independent loads in flight per thread.
+__global__ void dense_gsum_kernel(SweepArgs a, int32_t groups, float4* gpart) {
   const int dim = 1 << a.n;
   const int64_t tot = (int64_t)dim * dim;
-  const int64_t cstride = (int64_t)dim * 2 * dim;  // floats between consecutive chunk partials
+  const int64_t cstride = (int64_t)dim * 2 * dim;  // floats between consecutive slots
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= tot) return;
+  const int g = blockIdx.y;
+  const int c0 = (int)((int64_t)g * a.nchunks / groups), c1 = (int)((int64_t)(g + 1) * a.nchunks / groups);
+  const int64_t k = e / dim, j = e % dim;
+  const float* r = a.part + k * (2 * dim) + 2 * j;
+  CSum re[2], im[2];
+  int c = c0;
+  for (; c + 8 <= c1; c += 8) {
+    float2 v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) v[u] = __ldg(reinterpret_cast<const float2*>(r + (int64_t)(c + u) * cstride));
+#pragma unroll
+    for (int u = 0; u < 8; ++u) { re[u & 1].add(v[u].x); im[u & 1].add(-v[u].y); }
+  }
+  for (; c < c1; ++c) {
+    const float2 v = __ldg(reinterpret_cast<const float2*>(r + (int64_t)c * cstride));
+    re[0].add(v.x);
+    im[0].add(-v.y);
+  }
+  re[0].add(re[1]);
+  im[0].add(im[1]);
+  gpart[(int64_t)g * tot + e] = make_float4(re[0].s, re[0].c, im[0].s, im[0].c);
+}
+
+__global__ void dense_gsum_fin_kernel(SweepArgs a, int32_t groups, const float4* gpart) {
+  const int dim = 1 << a.n;
+  const int64_t tot = (int64_t)dim * dim;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t k = e / dim, j = e % dim;
-    const float* r = a.part + k * (2 * dim) + 2 * j;
-    CSum re[2], im[2];
-    int c = 0;
-    // eight independent loads in flight per thread
-    for (; c + 8 <= a.nchunks; c += 8) {
-      float2 v[8];
-#pragma unroll
-      for (int u = 0; u < 8; ++u) v[u] = __ldg(reinterpret_cast<const float2*>(r + (int64_t)(c + u) * cstride));
-#pragma unroll
-      for (int u = 0; u < 8; ++u) { re[u & 1].add(v[u].x); im[u & 1].add(-v[u].y); }
+    CSum re, im;
+    for (int g = 0; g < groups; ++g) {
+      const float4 p = gpart[(int64_t)g * tot + e];
+      CSum pr, pi;
+      pr.s = p.x; pr.c = p.y; pi.s = p.z; pi.c = p.w;
+      re.add(pr);
+      im.add(pi);
     }
-    for (; c < a.nchunks; ++c) {
-      const float2 v = __ldg(reinterpret_cast<const float2*>(r + (int64_t)c * cstride));
-      re[0].add(v.x);
-      im[0].add(-v.y);
-    }
-    re[0].add(re[1]);
-    im[0].add(im[1]);
-    a.G[e] = make_float2(re[0].value(), im[0].value());
+    a.G[e] = make_float2(re.value(), im.value());
   }
 }
 
