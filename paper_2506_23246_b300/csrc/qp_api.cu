@@ -30,7 +30,7 @@ struct qp_plan {
   int64_t cur_norm[3] = {0, 0, 0}, cur_norm_diel = 0, cur_colloc_off = 0;
   int warps_grad = 0, blocks_grad = 0, warps_fwd = 0, blocks_fwd = 0;
   int smem_grad = 0, smem_fwd = 0, sstride_grad = 0, sstride_fwd = 0;
-  int nwblk = 0, wtile = 0, smem_wgrad = 0, smem_premap = 0;
+  int nwblk = 0, wtile = 0, smem_wgrad = 0, smem_premap = 0, smem_premap4 = 0;
   int64_t n_params = 0, circ_off = 0, head_off = 0, mlp_off = 0, mlp_count = 0, nfixed = 0;
   void* ws = nullptr;
   size_t ws_bytes = 0;
@@ -175,6 +175,26 @@ void* premap_fwd_ptr(int H) {
     case 16: return (void*)qpk::premap_fwd_kernel<16>;
     case 32: return (void*)qpk::premap_fwd_kernel<32>;
     case 64: return (void*)qpk::premap_fwd_kernel<64>;
+  }
+  return nullptr;
+}
+void* premap_fwd4_ptr(int H) {
+  switch (H) {
+    case 4: return (void*)qpk::premap_fwd4_kernel<4>;
+    case 8: return (void*)qpk::premap_fwd4_kernel<8>;
+    case 16: return (void*)qpk::premap_fwd4_kernel<16>;
+    case 32: return (void*)qpk::premap_fwd4_kernel<32>;
+    case 64: return (void*)qpk::premap_fwd4_kernel<64>;
+  }
+  return nullptr;
+}
+void* premap_bwd4_ptr(int H) {
+  switch (H) {
+    case 4: return (void*)qpk::premap_bwd4_kernel<4>;
+    case 8: return (void*)qpk::premap_bwd4_kernel<8>;
+    case 16: return (void*)qpk::premap_bwd4_kernel<16>;
+    case 32: return (void*)qpk::premap_bwd4_kernel<32>;
+    case 64: return (void*)qpk::premap_bwd4_kernel<64>;
   }
   return nullptr;
 }
@@ -336,7 +356,10 @@ qp_status qp_plan_create(const qp_circuit* circuit, const qp_problem* problem, i
     while (tile > 1 && (tile * (2 * F + 2 * H + n) * 16 + 3 * F * 4) > 96 * 1024) tile >>= 1;
     pl->wtile = tile;
     pl->smem_wgrad = tile * (2 * F + 2 * H + n) * 16 + 3 * F * 4;
+    pl->smem_premap4 = qpk::premap4_smem(F, H, n);
     if (raise_smem_limit(premap_fwd_ptr(H), cudaFuncAttributeMaxDynamicSharedMemorySize, pl->smem_premap) != cudaSuccess ||
+        raise_smem_limit(premap_fwd4_ptr(H), cudaFuncAttributeMaxDynamicSharedMemorySize, pl->smem_premap4) != cudaSuccess ||
+        raise_smem_limit(premap_bwd4_ptr(H), cudaFuncAttributeMaxDynamicSharedMemorySize, pl->smem_premap4) != cudaSuccess ||
         raise_smem_limit(premap_bwd_ptr(H), cudaFuncAttributeMaxDynamicSharedMemorySize, pl->smem_premap) != cudaSuccess ||
         raise_smem_limit((void*)qpk::premap_wgrad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, pl->smem_wgrad) != cudaSuccess) {
       cudaGetLastError();
@@ -420,9 +443,12 @@ static qp_status launch_front(qp_plan* pl, const float* d_params, const float* c
   ma.disk_r = pl->p.disk_r; ma.disk_x0 = pl->p.disk_x0; ma.disk_y0 = pl->p.disk_y0;
   const int pblocks = (int)((ma.ptot + 127) / 128 < pl->sm_count * 8 ? (ma.ptot + 127) / 128 : pl->sm_count * 8);
   if (pl->c.premap == QP_PREMAP_RFF_MLP) {
-    void* fn = premap_fwd_ptr(pl->c.mlp_width);
+    // four threads per point, 32 points per block
+    const int64_t qb = (ma.ptot + 31) / 32;
+    const int qblocks = (int)(qb < pl->sm_count * 8 ? (qb > 0 ? qb : 1) : pl->sm_count * 8);
+    void* fn = premap_fwd4_ptr(pl->c.mlp_width);
     void* args[] = {&ma};
-    if (cudaLaunchKernel(fn, dim3(pblocks > 0 ? pblocks : 1), dim3(128), args, pl->smem_premap, s) != cudaSuccess)
+    if (cudaLaunchKernel(fn, dim3(qblocks), dim3(128), args, pl->smem_premap4, s) != cudaSuccess)
       return QP_ERR_CUDA;
   } else {
     qpk::premap_fwd_kernel<4><<<pblocks > 0 ? pblocks : 1, 128, 0, s>>>(ma);
@@ -816,10 +842,11 @@ static qp_status launch_premap_bwd(qp_plan* pl, const WsLayout& w, const float* 
   ma.dthetaJ = (const float*)(ws + w.dthetaJ);
   ma.d1 = (float*)(ws + w.d1); ma.d2 = (float*)(ws + w.d2); ma.u1 = (float*)(ws + w.u1);
   if (P > 0) {
-    const int pblocks = (int)((P + 127) / 128 < pl->sm_count * 8 ? (P + 127) / 128 : pl->sm_count * 8);
+    const int64_t qb = (P + 31) / 32;
+    const int pblocks = (int)(qb < pl->sm_count * 8 ? qb : pl->sm_count * 8);
     void* bargs[] = {&ma};
-    if (cudaLaunchKernel(premap_bwd_ptr(pl->c.mlp_width), dim3(pblocks), dim3(128), bargs,
-                         pl->smem_premap, s) != cudaSuccess)
+    if (cudaLaunchKernel(premap_bwd4_ptr(pl->c.mlp_width), dim3(pblocks), dim3(128), bargs,
+                         pl->smem_premap4, s) != cudaSuccess)
       return QP_ERR_CUDA;
   }
   qpk::WgradArgs wa;

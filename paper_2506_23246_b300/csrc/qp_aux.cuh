@@ -225,6 +225,213 @@ __global__ void premap_fwd_kernel(PremapArgs a) {
   }
 }
 
+// ---- RFF + MLP premap, four threads per point (each owns H/4 hidden units)
+// The block's 32 points get their [cos, sin](Omega v) table once in shared memory; the first
+// layer's weights are kept transposed ([2F][H]) so a thread reads its H/4 units contiguously;
+// the output layer is summed over the four lanes of a point with two butterfly shuffles.
+__host__ __device__ inline int premap4_smem(int F, int H, int n) {
+  const int wfl = 2 * F * H + H + n * H + n + 3 * F;
+  return ((wfl + 3) & ~3) * 4 + 32 * (F + 1) * 8;
+}
+
+struct Premap4Smem {
+  float *w1t, *b1, *w2, *b2, *om;
+  float2* sc;
+};
+__device__ __forceinline__ Premap4Smem premap4_load(const PremapArgs& a, float* psm) {
+  const int F = a.F, n = a.n, H = a.H;
+  Premap4Smem m;
+  m.w1t = psm;
+  m.b1 = m.w1t + 2 * F * H;
+  m.w2 = m.b1 + H;
+  m.b2 = m.w2 + n * H;
+  m.om = m.b2 + n;
+  m.sc = reinterpret_cast<float2*>(psm + ((2 * F * H + H + n * H + n + 3 * F + 3) & ~3));
+  const float* om = a.params;
+  const float* W1 = om + 3 * F;
+  for (int i = threadIdx.x; i < 3 * F; i += blockDim.x) m.om[i] = om[i];
+  for (int i = threadIdx.x; i < H * 2 * F; i += blockDim.x) {
+    const int o = i / (2 * F), k = i % (2 * F);
+    m.w1t[k * H + o] = W1[i];
+  }
+  for (int i = threadIdx.x; i < H; i += blockDim.x) m.b1[i] = W1[H * 2 * F + i];
+  for (int i = threadIdx.x; i < n * H; i += blockDim.x) m.w2[i] = W1[H * 2 * F + H + i];
+  for (int i = threadIdx.x; i < n; i += blockDim.x) m.b2[i] = W1[H * 2 * F + H + n * H + i];
+  return m;
+}
+
+// [cos, sin](Omega v) of the block's 32 points starting at p0 (rows of F + 1 entries).
+__device__ __forceinline__ void premap4_table(const PremapArgs& a, const Premap4Smem& m, int64_t p0) {
+  const int F = a.F;
+  for (int e = threadIdx.x; e < 32 * F; e += blockDim.x) {
+    const int pi = e / F, f = e % F;
+    const int64_t gp = p0 + pi;
+    float2 v = make_float2(1.f, 0.f);
+    if (gp < a.ptot) {
+      int set;
+      int64_t li;
+      const float* x = point_ptr(a, gp, set, li);
+      float sn, cs;
+      sincosf(m.om[3 * f] * x[0] + m.om[3 * f + 1] * x[1] + m.om[3 * f + 2] * x[2], &sn, &cs);
+      v = make_float2(cs, sn);
+    }
+    m.sc[pi * (F + 1) + f] = v;
+  }
+}
+
+// Hidden layer of this thread's units (pre-activation and x, y, t tangents).
+template <int QH>
+__device__ __forceinline__ void premap4_hidden(const PremapArgs& a, const Premap4Smem& m, int pl, int ob,
+                                               float (&h)[QH][4]) {
+  const int F = a.F, H = a.H;
+#pragma unroll
+  for (int k = 0; k < QH; ++k) { h[k][0] = m.b1[ob + k]; h[k][1] = h[k][2] = h[k][3] = 0.f; }
+  for (int f = 0; f < F; ++f) {
+    const float2 c = m.sc[pl * (F + 1) + f];
+    const float ox = m.om[3 * f], oy = m.om[3 * f + 1], ot = m.om[3 * f + 2];
+    const float* wc = m.w1t + f * H + ob;
+    const float* wsn = m.w1t + (F + f) * H + ob;
+#pragma unroll
+    for (int k = 0; k < QH; ++k) {
+      h[k][0] += wc[k] * c.x + wsn[k] * c.y;
+      const float q = c.x * wsn[k] - c.y * wc[k];  // d/du of (wc cos u + ws sin u)
+      h[k][1] += q * ox;
+      h[k][2] += q * oy;
+      h[k][3] += q * ot;
+    }
+  }
+}
+
+// Sum of a value over the four lanes of a point.
+__device__ __forceinline__ float quad_sum(float v) {
+  v += __shfl_xor_sync(0xffffffffu, v, 1);
+  return v + __shfl_xor_sync(0xffffffffu, v, 2);
+}
+
+template <int H>
+__global__ void __launch_bounds__(128) premap_fwd4_kernel(PremapArgs a) {
+  constexpr int QH = H / 4;
+  extern __shared__ __align__(16) float psm[];
+  const Premap4Smem m = premap4_load(a, psm);
+  const int n = a.n;
+  const int pl = threadIdx.x >> 2, oq = threadIdx.x & 3, ob = oq * QH;
+  for (int64_t p0 = blockIdx.x * 32LL; p0 < a.ptot; p0 += gridDim.x * 32LL) {
+    __syncthreads();  // weights loaded / the previous points' table consumed
+    premap4_table(a, m, p0);
+    __syncthreads();
+    const int64_t gp = p0 + pl;
+    const bool act = gp < a.ptot;
+    float h[QH][4];
+    premap4_hidden<QH>(a, m, pl, ob, h);
+#pragma unroll
+    for (int k = 0; k < QH; ++k) {
+      const float u = tanhf(h[k][0]);
+      const float du = 1.f - u * u;
+      h[k][0] = u;
+      h[k][1] *= du; h[k][2] *= du; h[k][3] *= du;
+    }
+    float4* out = reinterpret_cast<float4*>(a.thetaJ) + gp * n;
+    for (int j = 0; j < n; ++j) {
+      float z0 = 0.f, z1 = 0.f, z2 = 0.f, z3 = 0.f;
+#pragma unroll
+      for (int k = 0; k < QH; ++k) {
+        const float w = m.w2[j * H + ob + k];
+        z0 += w * h[k][0]; z1 += w * h[k][1]; z2 += w * h[k][2]; z3 += w * h[k][3];
+      }
+      z0 = quad_sum(z0) + m.b2[j];
+      z1 = quad_sum(z1); z2 = quad_sum(z2); z3 = quad_sum(z3);
+      if (act && oq == (j & 3)) {
+        float g0, g1, g2;
+        scale_tanh(a.scale, z0, g0, g1, g2);
+        out[j] = make_float4(g0, g1 * z1, g1 * z2, g1 * z3);
+      }
+    }
+    if (act && oq == 0 && a.medium == 1) {
+      int set;
+      int64_t li;
+      const float* v = point_ptr(a, gp, set, li);
+      if (set == 0) {
+        const float dx = v[0] - a.disk_x0, dy = v[1] - a.disk_y0;
+        if (__fmaf_rn(dx, dx, dy * dy) < a.disk_r * a.disk_r) atomicAdd(&a.counts[0], 1);
+      }
+    }
+  }
+}
+
+// Backward of the premap with four threads per point (see premap_bwd_kernel for the algebra).
+template <int H>
+__global__ void __launch_bounds__(128) premap_bwd4_kernel(PremapArgs a) {
+  constexpr int QH = H / 4;
+  extern __shared__ __align__(16) float psm[];
+  const Premap4Smem m = premap4_load(a, psm);
+  const int n = a.n;
+  const int pl = threadIdx.x >> 2, oq = threadIdx.x & 3, ob = oq * QH;
+  for (int64_t p0 = blockIdx.x * 32LL; p0 < a.ptot; p0 += gridDim.x * 32LL) {
+    __syncthreads();
+    premap4_table(a, m, p0);
+    __syncthreads();
+    const int64_t gp = p0 + pl;
+    const bool act = gp < a.ptot;
+    const int64_t gpc = act ? gp : 0;
+    float h[QH][4], hd[QH][4];
+    premap4_hidden<QH>(a, m, pl, ob, h);
+#pragma unroll
+    for (int k = 0; k < QH; ++k) {
+      const float u = tanhf(h[k][0]);
+      const float du = 1.f - u * u;
+      hd[k][0] = u;
+      hd[k][1] = h[k][1]; hd[k][2] = h[k][2]; hd[k][3] = h[k][3];
+      h[k][0] = u;
+      h[k][1] *= du; h[k][2] *= du; h[k][3] *= du;
+    }
+    if (act) {
+      float4* u1o = reinterpret_cast<float4*>(a.u1) + gp * H + ob;
+#pragma unroll
+      for (int k = 0; k < QH; ++k) u1o[k] = make_float4(h[k][0], h[k][1], h[k][2], h[k][3]);
+    }
+    float gu[QH][4];
+#pragma unroll
+    for (int k = 0; k < QH; ++k) gu[k][0] = gu[k][1] = gu[k][2] = gu[k][3] = 0.f;
+    const float4* dtj = reinterpret_cast<const float4*>(a.dthetaJ) + gpc * n;
+    float4* d2o = reinterpret_cast<float4*>(a.d2) + gpc * n;
+    for (int j = 0; j < n; ++j) {
+      float z0 = 0.f, z1 = 0.f, z2 = 0.f, z3 = 0.f;
+#pragma unroll
+      for (int k = 0; k < QH; ++k) {
+        const float w = m.w2[j * H + ob + k];
+        z0 += w * h[k][0]; z1 += w * h[k][1]; z2 += w * h[k][2]; z3 += w * h[k][3];
+      }
+      z0 = quad_sum(z0) + m.b2[j];
+      z1 = quad_sum(z1); z2 = quad_sum(z2); z3 = quad_sum(z3);
+      float g0, g1, g2;
+      scale_tanh(a.scale, z0, g0, g1, g2);
+      const float4 dt = dtj[j];
+      // theta = g(z0), J_d = g'(z0) z_d
+      const float dz1 = dt.y * g1, dz2 = dt.z * g1, dz3 = dt.w * g1;
+      const float dz0 = dt.x * g1 + g2 * (dt.y * z1 + dt.z * z2 + dt.w * z3);
+      if (act && oq == (j & 3)) d2o[j] = make_float4(dz0, dz1, dz2, dz3);
+#pragma unroll
+      for (int k = 0; k < QH; ++k) {
+        const float w = m.w2[j * H + ob + k];
+        gu[k][0] += w * dz0; gu[k][1] += w * dz1; gu[k][2] += w * dz2; gu[k][3] += w * dz3;
+      }
+    }
+    if (act) {
+      float4* d1o = reinterpret_cast<float4*>(a.d1) + gp * H + ob;
+#pragma unroll
+      for (int k = 0; k < QH; ++k) {
+        const float u = hd[k][0];
+        const float du = 1.f - u * u;
+        // u1_d = du * h1_d; d du / d h1 = -2 u du
+        const float g1x = gu[k][1] * du, g1y = gu[k][2] * du, g1t = gu[k][3] * du;
+        const float g10 = gu[k][0] * du -
+                          2.f * u * du * (gu[k][1] * hd[k][1] + gu[k][2] * hd[k][2] + gu[k][3] * hd[k][3]);
+        d1o[k] = make_float4(g10, g1x, g1y, g1t);
+      }
+    }
+  }
+}
+
 // Per-point backward through scale, output layer and tanh hidden layer, given
 // dL/dtheta_j and dL/dJ_jd from the circuit's adjoint sweep.
 template <int H>
