@@ -642,7 +642,7 @@ static qp_status dense_loss_grad(qp_plan* pl, const float* d_params, const float
       ma.status = (int32_t*)(ws + w.status);
       const int64_t mt = ma.tile_end[2];
       const int mblocks = (int)(mt < pl->sm_count ? (mt > 0 ? mt : 1) : pl->sm_count);
-      qpd::dense_mu_embed_kernel<<<mblocks, 128, qpd::mu_smem_bytes(n), s>>>(ma);
+      qpd::dense_mu_embed_kernel<<<mblocks, qpd::MU_THREADS, qpd::mu_smem_bytes(n), s>>>(ma);
       launches += 1;
     } else {
       // back-projection mu = Re(U'^H lambda) per (point, vector) row, then the embedding

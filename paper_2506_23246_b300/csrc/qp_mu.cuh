@@ -143,154 +143,62 @@ __device__ __forceinline__ void mu_chunk(MuRow& R, int n, int s, int c, uint32_t
   }
 }
 
-__global__ void __launch_bounds__(128, 1) dense_mu_embed_kernel(MuArgs a) {
+constexpr int MU_STAGERS = 128;   // operand staging + embedding epilogue (4 warps)
+constexpr int MU_THREADS = MU_STAGERS + 32;
+
+__global__ void __launch_bounds__(MU_THREADS, 1) dense_mu_embed_kernel(MuArgs a) {
   extern __shared__ __align__(1024) unsigned char sm[];
   const int n = a.n, dim = 1 << n;
   const int ktot = 2 * dim, nch = dim, nkc = ktot / KC;   // dim <= 256: one column chunk
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const bool ctrl = warp == MU_STAGERS / 32;
   const int abytes = TM * KC * 4, wbytes = nch * KC * 4;
   const int stage_bytes = 2 * abytes + 2 * wbytes;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(sm + 2 * stage_bytes);  // w_full[2], mma_done[2]
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sm + 2 * stage_bytes);
+  uint64_t* w_full = bars;         // [2] W operand of a stage landed
+  uint64_t* mma_done = bars + 2;   // [2] tensor-core work of a stage finished
+  uint64_t* a_full = bars + 4;     // [2] A operand of a stage written (4 staging warps)
+  uint64_t* acc_free = bars + 6;   // [2] a tensor-memory buffer drained (4 staging warps)
   uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + 2 * stage_bytes + 64);
   float* ex = reinterpret_cast<float*>(sm + 2 * stage_bytes + 128);    // [2 (C, D)][4][32][8]
   const uint32_t tcols = 2 * nch <= 256 ? (2 * nch <= 128 ? 128 : 256) : 512;
   if (warp == 0) qptc::tmem_alloc(tslot, tcols);
   if (tid == 0) {
     for (int i = 0; i < 4; ++i) qptc::mbar_init(&bars[i], 1);
+    for (int i = 4; i < 8; ++i) qptc::mbar_init(&bars[i], MU_STAGERS / 32);
   }
   qptc::fence_before();
   __syncthreads();
   qptc::fence_after();
   const uint32_t tmem = *tslot;
-  const uint32_t id = qptc::idesc(2, TM, nch);
   const int nchunk32 = dim / 32;
-  bool ok = true;
-  uint32_t it = 0, cbuf = 0;
-  int64_t last_copy = -1, last_commit = -1;
-  // pending tile (being drained)
-  bool pend = false, pend_nv4 = false, pend_act = false;
-  int pend_set = 0;
-  int64_t pend_p = 0;
-  uint32_t pend_buf = 0, pend_it = 0;
-  MuRow R;
-  auto finalize = [&]() {
-    qptc::fence_before();
-    // rows of one point sit in four warps (same lane): combine through shared memory
-    const int s = pend_nv4 ? warp : 0;
-    if (pend_nv4) {
-#pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        ex[(s * 32 + lane) * 8 + q] = R.C[q];
-        ex[1024 + (s * 32 + lane) * 8 + q] = R.D[q];
-      }
-    }
-    __syncthreads();
-    if (pend_act && (!pend_nv4 || warp == 0)) {
-      float4* dst = reinterpret_cast<float4*>(a.dthetaJ) + (a.pt_base[pend_set] + pend_p) * n;
-      for (int q = 0; q < n; ++q) {
-        if (pend_nv4) {
-          const float c = ex[lane * 8 + q] + ex[(32 + lane) * 8 + q] + ex[(64 + lane) * 8 + q] + ex[(96 + lane) * 8 + q];
-          dst[q] = make_float4(c, ex[1024 + (32 + lane) * 8 + q], ex[1024 + (64 + lane) * 8 + q],
-                               ex[1024 + (96 + lane) * 8 + q]);
-        } else {
-          float c = 0.f;
-#pragma unroll
-          for (int qq = 0; qq < 8; ++qq) if (qq == q) c = R.C[qq];
-          dst[q] = make_float4(c, 0.f, 0.f, 0.f);
-        }
-      }
-    }
-    __syncthreads();
-    pend = false;
-  };
-  auto begin_drain = [&]() -> bool {
-    const bool w = __syncthreads_and(qptc::mbar_wait(&bars[2 + (pend_it & 1)], (pend_it >> 1) & 1));
-    if (w) {
-      qptc::fence_after();
-      const int s = pend_nv4 ? warp : 0;
-      const int64_t np = a.npts[pend_set];
-      mu_row_setup(a, n, pend_set, pend_p < np ? pend_p : np - 1, s, R);
-    }
-    return w;
-  };
   const int64_t T2 = a.tile_end[2];
-  // costate row of this thread in a tile (A operand source)
-  auto tile_row = [&](int64_t tile, int& set, int64_t& p0, int64_t& p) -> const float4* {
-    if (tile < a.tile_end[0]) { set = 0; p0 = tile * 32; }
-    else if (tile < a.tile_end[1]) { set = 1; p0 = (tile - a.tile_end[0]) * TM; }
-    else { set = 2; p0 = (tile - a.tile_end[1]) * TM; }
-    const int64_t np = a.npts[set];
-    p = p0 + (set == 0 ? lane : tid);
-    const int64_t pc = p < np ? p : np - 1;
-    return reinterpret_cast<const float4*>(a.lam + lam_row(set, pc, set == 0 ? warp : 0, a.npts[0], a.pt_base[set]) * 256);
-  };
-  // the next K-step's eight float4 of the row are loaded one step ahead (software pipeline)
-  float4 nxt[KC / 4];
-  if ((int64_t)blockIdx.x < T2) {
-    int st0;
-    int64_t q0, q1;
-    const float4* s0 = tile_row(blockIdx.x, st0, q0, q1);
-#pragma unroll
-    for (int g4 = 0; g4 < KC / 4; ++g4) nxt[g4] = __ldg(s0 + g4);
-  }
-  for (int64_t tile = blockIdx.x; tile < T2 && ok; tile += gridDim.x) {
-    int set;
-    int64_t p0, p;
-    const float4* src = tile_row(tile, set, p0, p);
-    const bool nv4 = set == 0;
-    const int64_t np = a.npts[set];
-    const float4* src_next = nullptr;
-    if (tile + gridDim.x < T2) {
-      int st1;
-      int64_t q0, q1;
-      src_next = tile_row(tile + gridDim.x, st1, q0, q1);
-    }
-    for (int kc = 0; kc < nkc && ok; ++kc, ++it) {
-      const uint32_t st = it & 1;
-      unsigned char* sA = sm + st * stage_bytes;
-      unsigned char* sW = sA + 2 * abytes;
-      bool w_ok = true;
-      if (it >= 2) w_ok = qptc::mbar_wait(&bars[2 + st], ((it - 2) >> 1) & 1);
-      ok = __syncthreads_and(w_ok);
-      if (!ok) break;
-      if (tid == 0) {
-        qptc::mbar_arrive_expect_tx(&bars[st], 2 * wbytes);
-        qptc::bulk_g2s(sW, a.WT + (int64_t)kc * 2 * (nch * KC), 2 * wbytes, &bars[st]);
-        last_copy = it;
+  bool ok = true;
+  if (ctrl) {
+    // ---- control thread: W copies one step ahead, MMAs as soon as a stage's A is written
+    if (lane == 0) {
+      const uint32_t id = qptc::idesc(2, TM, nch);
+      const int64_t ntl = (int64_t)blockIdx.x < T2 ? (T2 - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+      const int64_t total = ntl * nkc;
+      int64_t last_copy = -1, last_commit = -1;
+      uint32_t it = 0;
+      if (total > 0) {
+        qptc::mbar_arrive_expect_tx(&w_full[0], 2 * wbytes);
+        qptc::bulk_g2s(sm + 2 * abytes, a.WT, 2 * wbytes, &w_full[0]);
+        last_copy = 0;
       }
-      {
-        float* Ahi = reinterpret_cast<float*>(sA);
-        float* Alo = reinterpret_cast<float*>(sA + abytes);
-        float4 cur[KC / 4];
-#pragma unroll
-        for (int g4 = 0; g4 < KC / 4; ++g4) cur[g4] = nxt[g4];
-        const float4* ns = kc + 1 < nkc ? src + mu_koff(a, kc + 1) : src_next;
-        if (ns) {
-#pragma unroll
-          for (int g4 = 0; g4 < KC / 4; ++g4) nxt[g4] = __ldg(ns + g4);
-        }
-#pragma unroll
-        for (int g4 = 0; g4 < KC / 4; ++g4) {
-          const float4 v4 = cur[g4];
-          float4 h4, l4;
-          qptc::split_tf32(v4.x, h4.x, l4.x);
-          qptc::split_tf32(v4.y, h4.y, l4.y);
-          qptc::split_tf32(v4.z, h4.z, l4.z);
-          qptc::split_tf32(v4.w, h4.w, l4.w);
-          const uint32_t off = core_off(tid, g4 * 4) / 4;
-          *reinterpret_cast<float4*>(Ahi + off) = h4;
-          *reinterpret_cast<float4*>(Alo + off) = l4;
-        }
-      }
-      qptc::fence_proxy_async();
-      __syncthreads();
-      bool m_ok = true;
-      if (tid == 0) {
-        m_ok = qptc::mbar_wait(&bars[st], (it >> 1) & 1);
-        if (m_ok) {
+      for (int64_t t = 0; t < ntl && ok; ++t) {
+        const uint32_t buf = t & 1;
+        // the buffer's previous tile (t - 2) must be drained before it is overwritten
+        if (t >= 2) ok = qptc::mbar_wait(&acc_free[buf], (uint32_t)((t - 2) >> 1) & 1);
+        for (int kc = 0; kc < nkc && ok; ++kc, ++it) {
+          const uint32_t st = it & 1;
+          ok = qptc::mbar_wait(&w_full[st], (it >> 1) & 1);
+          if (ok) ok = qptc::mbar_wait(&a_full[st], (it >> 1) & 1);
+          if (!ok) break;
           qptc::fence_after();
-          const uint32_t sa = qptc::smem_u32(sA), sw = qptc::smem_u32(sW);
-          const uint32_t dt = tmem + cbuf * (tcols / 2);
+          const uint32_t sa = qptc::smem_u32(sm + st * stage_bytes), sw = sa + 2 * abytes;
+          const uint32_t dt = tmem + buf * (tcols / 2);
 #pragma unroll
           for (int ks = 0; ks < KC / 8; ++ks) {
             const uint64_t ah = qptc::desc_kmajor(sa + ks * 256, 128, (KC / 4) * 128);
@@ -301,46 +209,169 @@ __global__ void __launch_bounds__(128, 1) dense_mu_embed_kernel(MuArgs a) {
             qptc::mma_tf32(dt, ah, wl, id, 1u);
             qptc::mma_tf32(dt, al, wh, id, 1u);
           }
-          qptc::commit(&bars[2 + st]);
+          qptc::commit(&mma_done[st]);
           last_commit = it;
+          if ((int64_t)it + 1 < total) {
+            const uint32_t s2 = (it + 1) & 1;
+            if (it >= 1) ok = qptc::mbar_wait(&mma_done[s2], ((it - 1) >> 1) & 1);
+            if (!ok) break;
+            qptc::mbar_arrive_expect_tx(&w_full[s2], 2 * wbytes);
+            qptc::bulk_g2s(sm + s2 * stage_bytes + 2 * abytes, a.WT + (int64_t)((kc + 1) % nkc) * 2 * (nch * KC),
+                           2 * wbytes, &w_full[s2]);
+            last_copy = it + 1;
+          }
         }
       }
-      ok = __syncthreads_and(m_ok);
-      if (!ok) break;
-      // drain the previous tile one 32-column chunk per K-step, under this tile's MMAs
-      if (pend) {
-        if (kc == 0) ok = begin_drain();
-        if (!ok) break;
-        if (kc < nchunk32)
-          mu_chunk(R, n, pend_nv4 ? warp : 0, kc,
-                   tmem + ((uint32_t)(warp * 32) << 16) + pend_buf * (tcols / 2) + kc * 32);
-        if (kc == nchunk32 - 1) finalize();
+      if (!ok) {
+        atomicExch(a.status, 6);
+        if (last_copy >= 0) qptc::mbar_wait(&w_full[last_copy & 1], ((uint32_t)last_copy >> 1) & 1);
+        if (last_commit >= 0) qptc::mbar_wait(&mma_done[last_commit & 1], ((uint32_t)last_commit >> 1) & 1);
       }
     }
-    if (!ok) break;
-    pend = true;
-    pend_nv4 = nv4;
-    pend_set = set;
-    pend_p = p;
-    pend_act = p < np;
-    pend_buf = cbuf;
-    pend_it = it - 1;
-    cbuf ^= 1;
-  }
-  if (ok && pend) {
-    ok = begin_drain();
-    if (ok) {
-      for (int c = 0; c < nchunk32; ++c)
-        mu_chunk(R, n, pend_nv4 ? warp : 0, c, tmem + ((uint32_t)(warp * 32) << 16) + pend_buf * (tcols / 2) + c * 32);
-      finalize();
+  } else {
+    // ---- staging warps: costate rows -> TF32 A operand; drain of the previous tile
+    uint32_t it = 0, cbuf = 0;
+    bool pend = false, pend_nv4 = false, pend_act = false;
+    int pend_set = 0;
+    int64_t pend_p = 0;
+    uint32_t pend_buf = 0, pend_it = 0;
+    MuRow R;
+    auto bar = [&]() { asm volatile("bar.sync 1, %0;" ::"r"(MU_STAGERS) : "memory"); };
+    auto finalize = [&]() {
+      qptc::fence_before();
+      // rows of one point sit in four warps (same lane): combine through shared memory
+      const int s = pend_nv4 ? warp : 0;
+      if (pend_nv4) {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          ex[(s * 32 + lane) * 8 + q] = R.C[q];
+          ex[1024 + (s * 32 + lane) * 8 + q] = R.D[q];
+        }
+      }
+      bar();
+      if (pend_act && (!pend_nv4 || warp == 0)) {
+        float4* dst = reinterpret_cast<float4*>(a.dthetaJ) + (a.pt_base[pend_set] + pend_p) * n;
+        for (int q = 0; q < n; ++q) {
+          if (pend_nv4) {
+            const float c = ex[lane * 8 + q] + ex[(32 + lane) * 8 + q] + ex[(64 + lane) * 8 + q] + ex[(96 + lane) * 8 + q];
+            dst[q] = make_float4(c, ex[1024 + (32 + lane) * 8 + q], ex[1024 + (64 + lane) * 8 + q],
+                                 ex[1024 + (96 + lane) * 8 + q]);
+          } else {
+            float c = 0.f;
+#pragma unroll
+            for (int qq = 0; qq < 8; ++qq) if (qq == q) c = R.C[qq];
+            dst[q] = make_float4(c, 0.f, 0.f, 0.f);
+          }
+        }
+      }
+      bar();
+      // the buffer is fully read: the control thread may overwrite it
+      if (lane == 0) qptc::mbar_arrive(&acc_free[pend_buf]);
+      pend = false;
+    };
+    auto begin_drain = [&]() -> bool {
+      const bool w = qptc::bar_and(1, MU_STAGERS, ok && qptc::mbar_wait(&mma_done[pend_it & 1], (pend_it >> 1) & 1));
+      if (w) {
+        qptc::fence_after();
+        const int s = pend_nv4 ? warp : 0;
+        const int64_t np = a.npts[pend_set];
+        mu_row_setup(a, n, pend_set, pend_p < np ? pend_p : np - 1, s, R);
+      }
+      return w;
+    };
+    // costate row of this thread in a tile (A operand source)
+    auto tile_row = [&](int64_t tile, int& set, int64_t& p0, int64_t& p) -> const float4* {
+      if (tile < a.tile_end[0]) { set = 0; p0 = tile * 32; }
+      else if (tile < a.tile_end[1]) { set = 1; p0 = (tile - a.tile_end[0]) * TM; }
+      else { set = 2; p0 = (tile - a.tile_end[1]) * TM; }
+      const int64_t np = a.npts[set];
+      p = p0 + (set == 0 ? lane : tid);
+      const int64_t pc = p < np ? p : np - 1;
+      return reinterpret_cast<const float4*>(a.lam + lam_row(set, pc, set == 0 ? warp : 0, a.npts[0], a.pt_base[set]) * 256);
+    };
+    // the next K-step's eight float4 of the row are loaded one step ahead (software pipeline)
+    float4 nxt[KC / 4];
+    if ((int64_t)blockIdx.x < T2) {
+      int st0;
+      int64_t q0, q1;
+      const float4* s0 = tile_row(blockIdx.x, st0, q0, q1);
+#pragma unroll
+      for (int g4 = 0; g4 < KC / 4; ++g4) nxt[g4] = __ldg(s0 + g4);
     }
-  }
-  if (!ok) {
-    if (tid == 0) {
-      atomicExch(a.status, 6);
-      if (last_copy >= 0) qptc::mbar_wait(&bars[last_copy & 1], ((uint32_t)last_copy >> 1) & 1);
-      if (last_commit >= 0) qptc::mbar_wait(&bars[2 + (last_commit & 1)], ((uint32_t)last_commit >> 1) & 1);
+    for (int64_t tile = blockIdx.x; tile < T2 && ok; tile += gridDim.x) {
+      int set;
+      int64_t p0, p;
+      const float4* src = tile_row(tile, set, p0, p);
+      const bool nv4 = set == 0;
+      const int64_t np = a.npts[set];
+      const float4* src_next = nullptr;
+      if (tile + gridDim.x < T2) {
+        int st1;
+        int64_t q0, q1;
+        src_next = tile_row(tile + gridDim.x, st1, q0, q1);
+      }
+      for (int kc = 0; kc < nkc; ++kc, ++it) {
+        const uint32_t st = it & 1;
+        unsigned char* sA = sm + st * stage_bytes;
+        if (it >= 2 && ok) ok = qptc::mbar_wait(&mma_done[st], ((it - 2) >> 1) & 1);
+        {
+          float* Ahi = reinterpret_cast<float*>(sA);
+          float* Alo = reinterpret_cast<float*>(sA + abytes);
+          float4 cur[KC / 4];
+#pragma unroll
+          for (int g4 = 0; g4 < KC / 4; ++g4) cur[g4] = nxt[g4];
+          const float4* ns = kc + 1 < nkc ? src + mu_koff(a, kc + 1) : src_next;
+          if (ns) {
+#pragma unroll
+            for (int g4 = 0; g4 < KC / 4; ++g4) nxt[g4] = __ldg(ns + g4);
+          }
+          if (ok) {
+#pragma unroll
+            for (int g4 = 0; g4 < KC / 4; ++g4) {
+              const float4 v4 = cur[g4];
+              float4 h4, l4;
+              qptc::split_tf32(v4.x, h4.x, l4.x);
+              qptc::split_tf32(v4.y, h4.y, l4.y);
+              qptc::split_tf32(v4.z, h4.z, l4.z);
+              qptc::split_tf32(v4.w, h4.w, l4.w);
+              const uint32_t off = core_off(tid, g4 * 4) / 4;
+              *reinterpret_cast<float4*>(Ahi + off) = h4;
+              *reinterpret_cast<float4*>(Alo + off) = l4;
+            }
+          }
+        }
+        qptc::fence_proxy_async();
+        __syncwarp();
+        if (lane == 0) qptc::mbar_arrive(&a_full[st]);
+        // drain the previous tile one 32-column chunk per K-step, under this tile's MMAs
+        if (pend) {
+          if (kc == 0) ok = begin_drain();
+          if (ok && kc < nchunk32)
+            mu_chunk(R, n, pend_nv4 ? warp : 0, kc,
+                     tmem + ((uint32_t)(warp * 32) << 16) + pend_buf * (tcols / 2) + kc * 32);
+          if (kc == nchunk32 - 1) finalize();
+        }
+      }
+      ok = qptc::bar_and(1, MU_STAGERS, ok);
+      if (!ok) break;
+      pend = true;
+      pend_nv4 = nv4;
+      pend_set = set;
+      pend_p = p;
+      pend_act = p < np;
+      pend_buf = cbuf;
+      pend_it = it - 1;
+      cbuf ^= 1;
     }
+    if (ok && pend) {
+      ok = begin_drain();
+      if (ok) {
+        for (int c = 0; c < nchunk32; ++c)
+          mu_chunk(R, n, pend_nv4 ? warp : 0, c, tmem + ((uint32_t)(warp * 32) << 16) + pend_buf * (tcols / 2) + c * 32);
+        finalize();
+      }
+    }
+    if (!ok && tid == 0) atomicExch(a.status, 6);
   }
   qptc::fence_before();
   __syncthreads();
