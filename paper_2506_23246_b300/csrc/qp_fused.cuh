@@ -37,27 +37,38 @@ struct FusedArgs {
   int32_t* status;
 };
 
+// Shared memory: two A stages (TF32 hi, lo), a three-slot ring of W blocks (copies run two
+// K-steps ahead, across tile boundaries), and the persistent head/loss/barrier block. The
+// epilogue's exchange and readout buffers live in the W slot of the tile's last K-step (idle
+// until that slot's next copy, issued after the epilogue) when it is large enough, else in a
+// region of their own; the costate store staging lives in the A stages.
 struct FusedSmem {
-  int a_bytes, w_bytes, stage, x0, tb, zp, zb, hw, sloss, hsum, bars, total;
+  int a_bytes, w_bytes, wbase, epi, x0, tb, zp, zb, hw, sloss, hsum, bars, total;
+  bool epi_in_w;
 };
+constexpr int F_EPI_BYTES = 2 * 32 * 32 * 4 + 2 * 3 * 32 * 32 * 4 + 2 * TM * QP_MAXQ * 4 + TM * QP_MAXQ * 4;
 __host__ __device__ inline FusedSmem fused_smem(int n, int nt) {
   FusedSmem f;
   const int nc = (2 << n) / 256;
   f.a_bytes = TM * FKC * 4;
   f.w_bytes = nc * 2 * 256 * FKC * 4;
-  f.stage = 2 * f.a_bytes + f.w_bytes;
-  int o = 2 * f.stage;
-  f.x0 = o; o += 2 * 32 * 32 * 4;                 // phi_0 chunk per column half
-  f.tb = o; o += 2 * 3 * 32 * 32 * 4;             // O_d phi_d chunks per column half
-  f.zp = o; o += 2 * TM * QP_MAXQ * 4;            // readout partials [half][row][i]
-  f.zb = o; o += TM * QP_MAXQ * 4;                // sign-sum coefficients [row][i]
+  f.wbase = 2 * 2 * f.a_bytes;
+  int o = f.wbase + 3 * f.w_bytes;
   f.hw = o; o += (3 * QP_MAXQ + 3) * 4 + 4;       // head weights
   o = (o + 15) / 16 * 16;
   f.sloss = o; o += (QP_NLP + nt) * 8;
   o = (o + 15) / 16 * 16;
   f.hsum = o; o += (3 * QP_MAXQ + 3) * 4 + 4;
   o = (o + 15) / 16 * 16;
-  f.bars = o; o += 64;                            // w_full[2], mma_done[2], tensor-memory slot
+  f.bars = o; o += 128;                           // w_full[3], mma_done[2], tensor-memory slot
+  f.epi_in_w = f.w_bytes >= F_EPI_BYTES;
+  if (!f.epi_in_w) { f.epi = o; o += F_EPI_BYTES; }
+  else f.epi = -1;
+  // offsets inside the epilogue block
+  f.x0 = 0;                                       // phi_0 chunk per column half
+  f.tb = f.x0 + 2 * 32 * 32 * 4;                  // O_d phi_d chunks per column half
+  f.zp = f.tb + 2 * 3 * 32 * 32 * 4;              // readout partials [half][row][i]
+  f.zb = f.zp + 2 * TM * QP_MAXQ * 4;             // sign-sum coefficients [row][i]
   f.total = o;
   return f;
 }
@@ -83,19 +94,17 @@ __global__ void __launch_bounds__(F_THREADS, 1) dense_fused_fwd_kernel(FusedArgs
   const FusedSmem L = fused_smem(n, nt);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int ws = warp & 3, hh = warp >> 2;        // tensor-memory lane group, column half
-  uint64_t* bars = reinterpret_cast<uint64_t*>(sm + L.bars);  // w_full[2], mma_done[2]
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + L.bars + 32);
-  float4* X0 = reinterpret_cast<float4*>(sm + L.x0) + hh * 256;
-  float4* TB = reinterpret_cast<float4*>(sm + L.tb) + hh * 768;
-  float* zp = reinterpret_cast<float*>(sm + L.zp);
-  float* zbs = reinterpret_cast<float*>(sm + L.zb);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sm + L.bars);
+  uint64_t* w_full = bars;          // [3] W ring slot landed
+  uint64_t* mma_done = bars + 3;    // [2] tensor-core work of an A stage finished (commit)
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + L.bars + 64);
   float* hw = reinterpret_cast<float*>(sm + L.hw);
   double* sloss = reinterpret_cast<double*>(sm + L.sloss);
   float* hsum = reinterpret_cast<float*>(sm + L.hsum);
   const uint32_t tcols = 2u << n;
   if (warp == 0) qptc::tmem_alloc(tslot, tcols);
   if (tid == 0) {
-    for (int i = 0; i < 4; ++i) qptc::mbar_init(&bars[i], 1);
+    for (int i = 0; i < 5; ++i) qptc::mbar_init(&bars[i], 1);
   }
   for (int i = tid; i < 3 * m + 3; i += blockDim.x) { hw[i] = a.head[i]; hsum[i] = 0.f; }
   for (int i = tid; i < QP_NLP + nt; i += blockDim.x) sloss[i] = 0.0;
@@ -123,6 +132,17 @@ __global__ void __launch_bounds__(F_THREADS, 1) dense_fused_fwd_kernel(FusedArgs
   uint32_t it = 0;
   int64_t last_copy = -1, last_commit = -1;
   const int64_t T2 = a.tile_end[2];
+  const int64_t ntl = (int64_t)blockIdx.x < T2 ? (T2 - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+  const int64_t total = ntl * nkc;
+  if (tid == 0) {
+    // W of the first two K-steps
+    for (int j = 0; j < 2 && j < total; ++j) {
+      qptc::mbar_arrive_expect_tx(&w_full[j], L.w_bytes);
+      qptc::bulk_g2s(sm + L.wbase + j * L.w_bytes, a.W16 + (int64_t)(j % nkc) * (L.w_bytes / 4), L.w_bytes,
+                     &w_full[j]);
+      last_copy = j;
+    }
+  }
   for (int64_t tile = blockIdx.x; tile < T2 && ok; tile += gridDim.x) {
     int set;
     int64_t p0;
@@ -165,18 +185,13 @@ __global__ void __launch_bounds__(F_THREADS, 1) dense_fused_fwd_kernel(FusedArgs
     }
     // ---- forward contraction: TMEM[row][2j + re/im] = sum_k R[row][k] W[2j + re/im][k]
     for (int kc = 0; kc < nkc && ok; ++kc, ++it) {
-      const uint32_t st = it & 1;
-      unsigned char* sA = sm + st * L.stage;
-      unsigned char* sW = sA + 2 * L.a_bytes;
+      const uint32_t st = it & 1, wsl = it % 3;
+      unsigned char* sA = sm + st * 2 * L.a_bytes;
+      unsigned char* sW = sm + L.wbase + wsl * L.w_bytes;
       bool w_ok = true;
-      if (it >= 2) w_ok = qptc::mbar_wait(&bars[2 + st], ((it - 2) >> 1) & 1);
+      if (it >= 2) w_ok = qptc::mbar_wait(&mma_done[st], ((it - 2) >> 1) & 1);
       ok = __syncthreads_and(w_ok);
       if (!ok) break;
-      if (tid == 0) {
-        qptc::mbar_arrive_expect_tx(&bars[st], L.w_bytes);
-        qptc::bulk_g2s(sW, a.W16 + (int64_t)kc * (L.w_bytes / 4), L.w_bytes, &bars[st]);
-        last_copy = it;
-      }
       // basis indices k = kc * 16 + khalf * 8 + t: bits 0-2 from the tables, the rest from H
       const int hbits = kc * 2 + khalf;
       float H = 1.f, Hd = 0.f;
@@ -210,7 +225,7 @@ __global__ void __launch_bounds__(F_THREADS, 1) dense_fused_fwd_kernel(FusedArgs
       __syncthreads();
       bool m_ok = true;
       if (tid == 0) {
-        m_ok = qptc::mbar_wait(&bars[st], (it >> 1) & 1);
+        m_ok = qptc::mbar_wait(&w_full[wsl], (it / 3) & 1);
         if (m_ok) {
           qptc::fence_after();
           const uint32_t sa = qptc::smem_u32(sA), sw = qptc::smem_u32(sW);
@@ -228,16 +243,33 @@ __global__ void __launch_bounds__(F_THREADS, 1) dense_fused_fwd_kernel(FusedArgs
               qptc::mma_tf32(dt, al, wh, id, 1u);
             }
           }
-          qptc::commit(&bars[2 + st]);
+          qptc::commit(&mma_done[st]);
           last_commit = it;
+          // W two steps ahead goes into the slot whose last reader was step it - 1
+          if ((int64_t)it + 2 < total) {
+            const uint32_t j = it + 2, js = j % 3;
+            if (it >= 1) m_ok = qptc::mbar_wait(&mma_done[(it - 1) & 1], ((it - 1) >> 1) & 1);
+            if (m_ok) {
+              qptc::mbar_arrive_expect_tx(&w_full[js], L.w_bytes);
+              qptc::bulk_g2s(sm + L.wbase + js * L.w_bytes, a.W16 + (int64_t)((kc + 2) % nkc) * (L.w_bytes / 4),
+                             L.w_bytes, &w_full[js]);
+              last_copy = j;
+            }
+          }
         }
       }
       ok = __syncthreads_and(m_ok);
     }
     if (!ok) break;
-    ok = __syncthreads_and(qptc::mbar_wait(&bars[2 + ((it - 1) & 1)], ((it - 1) >> 1) & 1));
+    ok = __syncthreads_and(qptc::mbar_wait(&mma_done[(it - 1) & 1], ((it - 1) >> 1) & 1));
     if (!ok) break;
     qptc::fence_after();
+    // epilogue buffers: the W slot of the tile's last step (or their own region)
+    unsigned char* epi = L.epi_in_w ? sm + L.wbase + ((it - 1) % 3) * L.w_bytes : sm + L.epi;
+    float4* X0 = reinterpret_cast<float4*>(epi + L.x0) + hh * 256;
+    float4* TB = reinterpret_cast<float4*>(epi + L.tb) + hh * 768;
+    float* zp = reinterpret_cast<float*>(epi + L.zp);
+    float* zbs = reinterpret_cast<float*>(epi + L.zb);
     // ---- pass 1: readout partial sums over this thread's half of the columns
     float acc[QP_MAXQ];
 #pragma unroll
@@ -466,8 +498,10 @@ __global__ void __launch_bounds__(F_THREADS, 1) dense_fused_fwd_kernel(FusedArgs
     if (tid == 0) {
       atomicExch(a.status, 6);
       // let the last bulk copy and tensor-core operations of this CTA land before exiting
-      if (last_copy >= 0) qptc::mbar_wait(&bars[last_copy & 1], ((uint32_t)last_copy >> 1) & 1);
-      if (last_commit >= 0) qptc::mbar_wait(&bars[2 + (last_commit & 1)], ((uint32_t)last_commit >> 1) & 1);
+      // copies up to two steps ahead may be in flight: wait for every issued one not consumed
+      for (int64_t j = last_copy - 2 < 0 ? 0 : last_copy - 2; j <= last_copy; ++j)
+        qptc::mbar_wait(&w_full[j % 3], (uint32_t)(j / 3) & 1);
+      if (last_commit >= 0) qptc::mbar_wait(&mma_done[last_commit & 1], ((uint32_t)last_commit >> 1) & 1);
     }
   }
   // ---- block partials: loss sums (FP64) and head gradients
