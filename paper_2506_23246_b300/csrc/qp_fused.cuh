@@ -15,7 +15,8 @@ namespace qpd {
 // (Z_i diagonal: O is a per-amplitude sign sum), written in place of the states.
 // Tile rows: collocation tiles hold 32 points x 4 vectors (row = vector * 32 + point, so warp
 // w and w + 4 own vector w % 4, the two halves of the columns); IC/BC tiles 128 points.
-constexpr int F_THREADS = 256;
+constexpr int F_STAGERS = 256;                 // operand generation + epilogue (8 warps)
+constexpr int F_THREADS = F_STAGERS + 32;      // + one control warp (bulk copies, MMAs)
 constexpr int F_MAXH = 5;       // embedding qubits above the 3 lowest index bits (n <= 8)
 
 
@@ -76,6 +77,10 @@ __host__ __device__ inline FusedSmem fused_smem(int n, int nt) {
 __device__ __forceinline__ void named_bar(int id) {
   asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(128) : "memory");
 }
+// Barrier over the staging warps only (the control warp never joins it).
+__device__ __forceinline__ void stagers_bar() {
+  asm volatile("bar.sync %0, %1;" ::"r"(3), "r"(F_STAGERS) : "memory");
+}
 __device__ __forceinline__ double warp_sum_d(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -97,7 +102,10 @@ __global__ void __launch_bounds__(F_THREADS, 1) dense_fused_fwd_kernel(FusedArgs
   uint64_t* bars = reinterpret_cast<uint64_t*>(sm + L.bars);
   uint64_t* w_full = bars;          // [3] W ring slot landed
   uint64_t* mma_done = bars + 3;    // [2] tensor-core work of an A stage finished (commit)
+  uint64_t* a_full = bars + 5;      // [2] A operand of a stage written (8 staging warps)
+  uint64_t* acc_free = bars + 7;    // tile epilogue done with tensor memory (8 staging warps)
   uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + L.bars + 64);
+  const bool ctrl = warp == F_STAGERS / 32;
   float* hw = reinterpret_cast<float*>(sm + L.hw);
   double* sloss = reinterpret_cast<double*>(sm + L.sloss);
   float* hsum = reinterpret_cast<float*>(sm + L.hsum);
@@ -105,6 +113,7 @@ __global__ void __launch_bounds__(F_THREADS, 1) dense_fused_fwd_kernel(FusedArgs
   if (warp == 0) qptc::tmem_alloc(tslot, tcols);
   if (tid == 0) {
     for (int i = 0; i < 5; ++i) qptc::mbar_init(&bars[i], 1);
+    for (int i = 5; i < 8; ++i) qptc::mbar_init(&bars[i], F_STAGERS / 32);
   }
   for (int i = tid; i < 3 * m + 3; i += blockDim.x) { hw[i] = a.head[i]; hsum[i] = 0.f; }
   for (int i = tid; i < QP_NLP + nt; i += blockDim.x) sloss[i] = 0.0;
@@ -134,15 +143,63 @@ __global__ void __launch_bounds__(F_THREADS, 1) dense_fused_fwd_kernel(FusedArgs
   const int64_t T2 = a.tile_end[2];
   const int64_t ntl = (int64_t)blockIdx.x < T2 ? (T2 - 1 - blockIdx.x) / gridDim.x + 1 : 0;
   const int64_t total = ntl * nkc;
-  if (tid == 0) {
-    // W of the first two K-steps
-    for (int j = 0; j < 2 && j < total; ++j) {
-      qptc::mbar_arrive_expect_tx(&w_full[j], L.w_bytes);
-      qptc::bulk_g2s(sm + L.wbase + j * L.w_bytes, a.W16 + (int64_t)(j % nkc) * (L.w_bytes / 4), L.w_bytes,
-                     &w_full[j]);
-      last_copy = j;
+  if (ctrl) {
+    // ---- control thread: W two K-steps ahead, MMAs as soon as a stage's A is written
+    if (lane == 0) {
+      const uint32_t wblk = 256 * FKC * 4;
+      for (int j = 0; j < 2 && j < total; ++j) {
+        qptc::mbar_arrive_expect_tx(&w_full[j], L.w_bytes);
+        qptc::bulk_g2s(sm + L.wbase + j * L.w_bytes, a.W16 + (int64_t)(j % nkc) * (L.w_bytes / 4), L.w_bytes,
+                       &w_full[j]);
+        last_copy = j;
+      }
+      for (int64_t t = 0; t < ntl && ok; ++t) {
+        for (int kc = 0; kc < nkc && ok; ++kc, ++it) {
+          const uint32_t st = it & 1, wsl = it % 3;
+          // the previous tile's epilogue must be done with tensor memory (and with W slot it - 1)
+          if (kc == 0 && t > 0) ok = qptc::mbar_wait(acc_free, (uint32_t)(t - 1) & 1);
+          if (ok) ok = qptc::mbar_wait(&w_full[wsl], (it / 3) & 1);
+          if (ok) ok = qptc::mbar_wait(&a_full[st], (it >> 1) & 1);
+          if (!ok) break;
+          qptc::fence_after();
+          const uint32_t sa = qptc::smem_u32(sm + st * 2 * L.a_bytes), sw = qptc::smem_u32(sm + L.wbase + wsl * L.w_bytes);
+#pragma unroll
+          for (int ks = 0; ks < FKC / 8; ++ks) {
+            const uint64_t ah = qptc::desc_kmajor(sa + ks * 256, 128, (FKC / 4) * 128);
+            const uint64_t al = qptc::desc_kmajor(sa + L.a_bytes + ks * 256, 128, (FKC / 4) * 128);
+            for (int c = 0; c < nc; ++c) {
+              const uint64_t wh = qptc::desc_kmajor(sw + c * 2 * wblk + ks * 256, 128, (FKC / 4) * 128);
+              const uint64_t wl = qptc::desc_kmajor(sw + c * 2 * wblk + wblk + ks * 256, 128, (FKC / 4) * 128);
+              const uint32_t dt = tmem + c * 256;
+              qptc::mma_tf32(dt, ah, wh, id, (kc > 0 || ks > 0) ? 1u : 0u);
+              qptc::mma_tf32(dt, ah, wl, id, 1u);
+              qptc::mma_tf32(dt, al, wh, id, 1u);
+            }
+          }
+          qptc::commit(&mma_done[st]);
+          last_commit = it;
+          if ((int64_t)it + 2 < total) {
+            const uint32_t j = it + 2, js = j % 3;
+            if (it >= 1) ok = qptc::mbar_wait(&mma_done[(it - 1) & 1], ((it - 1) >> 1) & 1);
+            if (!ok) break;
+            // W slot js last held step it - 1 and, at a tile end, that tile's epilogue buffers:
+            // copies into it are issued only after acc_free (above) for the first step of a tile
+            qptc::fence_proxy_async();
+            qptc::mbar_arrive_expect_tx(&w_full[js], L.w_bytes);
+            qptc::bulk_g2s(sm + L.wbase + js * L.w_bytes, a.W16 + (int64_t)((kc + 2) % nkc) * (L.w_bytes / 4),
+                           L.w_bytes, &w_full[js]);
+            last_copy = j;
+          }
+        }
+      }
+      if (!ok) {
+        atomicExch(a.status, 6);
+        for (int64_t j = last_copy - 2 < 0 ? 0 : last_copy - 2; j <= last_copy; ++j)
+          qptc::mbar_wait(&w_full[j % 3], (uint32_t)(j / 3) & 1);
+        if (last_commit >= 0) qptc::mbar_wait(&mma_done[last_commit & 1], ((uint32_t)last_commit >> 1) & 1);
+      }
     }
-  }
+  } else
   for (int64_t tile = blockIdx.x; tile < T2 && ok; tile += gridDim.x) {
     int set;
     int64_t p0;
@@ -184,84 +241,46 @@ __global__ void __launch_bounds__(F_THREADS, 1) dense_fused_fwd_kernel(FusedArgs
       }
     }
     // ---- forward contraction: TMEM[row][2j + re/im] = sum_k R[row][k] W[2j + re/im][k]
-    for (int kc = 0; kc < nkc && ok; ++kc, ++it) {
-      const uint32_t st = it & 1, wsl = it % 3;
+    for (int kc = 0; kc < nkc; ++kc, ++it) {
+      const uint32_t st = it & 1;
       unsigned char* sA = sm + st * 2 * L.a_bytes;
-      unsigned char* sW = sm + L.wbase + wsl * L.w_bytes;
-      bool w_ok = true;
-      if (it >= 2) w_ok = qptc::mbar_wait(&mma_done[st], ((it - 2) >> 1) & 1);
-      ok = __syncthreads_and(w_ok);
-      if (!ok) break;
-      // basis indices k = kc * 16 + khalf * 8 + t: bits 0-2 from the tables, the rest from H
-      const int hbits = kc * 2 + khalf;
-      float H = 1.f, Hd = 0.f;
+      if (it >= 2 && ok) ok = qptc::mbar_wait(&mma_done[st], ((it - 2) >> 1) & 1);
+      if (ok) {
+        // basis indices k = kc * 16 + khalf * 8 + t: bits 0-2 from the tables, the rest from H
+        const int hbits = kc * 2 + khalf;
+        float H = 1.f, Hd = 0.f;
 #pragma unroll
-      for (int q = 0; q < F_MAXH; ++q) {
-        if (q < n - 3) {
-          const bool bit = (hbits >> (n - 4 - q)) & 1;
-          const float f = bit ? hs[q] : hc[q], d = bit ? 0.5f * hc[q] : -0.5f * hs[q];
-          Hd = Hd * f + H * d * hj[q];
-          H *= f;
+        for (int q = 0; q < F_MAXH; ++q) {
+          if (q < n - 3) {
+            const bool bit = (hbits >> (n - 4 - q)) & 1;
+            const float f = bit ? hs[q] : hc[q], d = bit ? 0.5f * hc[q] : -0.5f * hs[q];
+            Hd = Hd * f + H * d * hj[q];
+            H *= f;
+          }
         }
-      }
-      float* Ahi = reinterpret_cast<float*>(sA);
-      float* Alo = reinterpret_cast<float*>(sA + L.a_bytes);
+        float* Ahi = reinterpret_cast<float*>(sA);
+        float* Alo = reinterpret_cast<float*>(sA + L.a_bytes);
 #pragma unroll
-      for (int g4 = 0; g4 < 2; ++g4) {
-        float4 h4, l4;
-        float* hv = &h4.x;
-        float* lv = &l4.x;
+        for (int g4 = 0; g4 < 2; ++g4) {
+          float4 h4, l4;
+          float* hv = &h4.x;
+          float* lv = &l4.x;
 #pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          const int t = g4 * 4 + e;
-          const float v = s_a == 0 ? H * Lo[t] : Hd * Lo[t] + H * Lod[t];
-          qptc::split_tf32(v, hv[e], lv[e]);
+          for (int e = 0; e < 4; ++e) {
+            const int t = g4 * 4 + e;
+            const float v = s_a == 0 ? H * Lo[t] : Hd * Lo[t] + H * Lod[t];
+            qptc::split_tf32(v, hv[e], lv[e]);
+          }
+          const uint32_t off = core_off16(arow, khalf * 8 + g4 * 4) / 4;
+          *reinterpret_cast<float4*>(Ahi + off) = h4;
+          *reinterpret_cast<float4*>(Alo + off) = l4;
         }
-        const uint32_t off = core_off16(arow, khalf * 8 + g4 * 4) / 4;
-        *reinterpret_cast<float4*>(Ahi + off) = h4;
-        *reinterpret_cast<float4*>(Alo + off) = l4;
       }
       qptc::fence_proxy_async();
-      __syncthreads();
-      bool m_ok = true;
-      if (tid == 0) {
-        m_ok = qptc::mbar_wait(&w_full[wsl], (it / 3) & 1);
-        if (m_ok) {
-          qptc::fence_after();
-          const uint32_t sa = qptc::smem_u32(sA), sw = qptc::smem_u32(sW);
-          const uint32_t wblk = 256 * FKC * 4;
-#pragma unroll
-          for (int ks = 0; ks < FKC / 8; ++ks) {
-            const uint64_t ah = qptc::desc_kmajor(sa + ks * 256, 128, (FKC / 4) * 128);
-            const uint64_t al = qptc::desc_kmajor(sa + L.a_bytes + ks * 256, 128, (FKC / 4) * 128);
-            for (int c = 0; c < nc; ++c) {
-              const uint64_t wh = qptc::desc_kmajor(sw + c * 2 * wblk + ks * 256, 128, (FKC / 4) * 128);
-              const uint64_t wl = qptc::desc_kmajor(sw + c * 2 * wblk + wblk + ks * 256, 128, (FKC / 4) * 128);
-              const uint32_t dt = tmem + c * 256;
-              qptc::mma_tf32(dt, ah, wh, id, (kc > 0 || ks > 0) ? 1u : 0u);
-              qptc::mma_tf32(dt, ah, wl, id, 1u);
-              qptc::mma_tf32(dt, al, wh, id, 1u);
-            }
-          }
-          qptc::commit(&mma_done[st]);
-          last_commit = it;
-          // W two steps ahead goes into the slot whose last reader was step it - 1
-          if ((int64_t)it + 2 < total) {
-            const uint32_t j = it + 2, js = j % 3;
-            if (it >= 1) m_ok = qptc::mbar_wait(&mma_done[(it - 1) & 1], ((it - 1) >> 1) & 1);
-            if (m_ok) {
-              qptc::mbar_arrive_expect_tx(&w_full[js], L.w_bytes);
-              qptc::bulk_g2s(sm + L.wbase + js * L.w_bytes, a.W16 + (int64_t)((kc + 2) % nkc) * (L.w_bytes / 4),
-                             L.w_bytes, &w_full[js]);
-              last_copy = j;
-            }
-          }
-        }
-      }
-      ok = __syncthreads_and(m_ok);
+      __syncwarp();
+      if (lane == 0) qptc::mbar_arrive(&a_full[st]);
     }
-    if (!ok) break;
-    ok = __syncthreads_and(qptc::mbar_wait(&mma_done[(it - 1) & 1], ((it - 1) >> 1) & 1));
+    ok = qptc::bar_and(3, F_STAGERS, ok && qptc::mbar_wait(&mma_done[(it - 1) & 1], ((it - 1) >> 1) & 1));
     if (!ok) break;
     qptc::fence_after();
     // epilogue buffers: the W slot of the tile's last step (or their own region)
@@ -323,7 +342,7 @@ __global__ void __launch_bounds__(F_THREADS, 1) dense_fused_fwd_kernel(FusedArgs
 #pragma unroll
     for (int i = 0; i < QP_MAXQ; ++i)
       if (i < m) zp[(hh * TM + r) * QP_MAXQ + i] = acc[i];
-    __syncthreads();
+    stagers_bar();
     // ---- point stage: head, loss terms, cotangents, sign-sum coefficients
     if (nv4 ? warp == 0 : warp < 4) {
       const int r0 = nv4 ? lane : r;
@@ -396,7 +415,7 @@ __global__ void __launch_bounds__(F_THREADS, 1) dense_fused_fwd_kernel(FusedArgs
 #pragma unroll
       for (int c = 0; c < 3; ++c) hb[c] += g[c];
     }
-    __syncthreads();
+    stagers_bar();
     // ---- pass 2: costates of this thread's row, written over the state rows
     {
       float coef[QP_MAXQ], cb[4] = {0.f, 0.f, 0.f, 0.f};
@@ -491,19 +510,12 @@ __global__ void __launch_bounds__(F_THREADS, 1) dense_fused_fwd_kernel(FusedArgs
         }
       }
     }
+    // tensor memory and the W slot of this tile's last step are free again
     qptc::fence_before();
-    __syncthreads();
+    stagers_bar();
+    if (lane == 0) qptc::mbar_arrive(acc_free);
   }
-  if (!ok) {
-    if (tid == 0) {
-      atomicExch(a.status, 6);
-      // let the last bulk copy and tensor-core operations of this CTA land before exiting
-      // copies up to two steps ahead may be in flight: wait for every issued one not consumed
-      for (int64_t j = last_copy - 2 < 0 ? 0 : last_copy - 2; j <= last_copy; ++j)
-        qptc::mbar_wait(&w_full[j % 3], (uint32_t)(j / 3) & 1);
-      if (last_commit >= 0) qptc::mbar_wait(&mma_done[last_commit & 1], ((uint32_t)last_commit >> 1) & 1);
-    }
-  }
+  if (!ok && !ctrl && tid == 0) atomicExch(a.status, 6);
   // ---- block partials: loss sums (FP64) and head gradients
 #pragma unroll
   for (int i = 0; i < QP_NLP; ++i) {
