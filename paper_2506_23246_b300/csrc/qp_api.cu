@@ -31,6 +31,7 @@ struct qp_plan {
   int warps_grad = 0, blocks_grad = 0, warps_fwd = 0, blocks_fwd = 0;
   int smem_grad = 0, smem_fwd = 0, sstride_grad = 0, sstride_fwd = 0;
   int nwblk = 0, wtile = 0, smem_wgrad = 0, smem_premap = 0, smem_premap4 = 0;
+  bool swc_big = false;   // the one-launch sweep runs as a 16-CTA cluster
   int64_t n_params = 0, circ_off = 0, head_off = 0, mlp_off = 0, mlp_count = 0, nfixed = 0;
   void* ws = nullptr;
   size_t ws_bytes = 0;
@@ -70,7 +71,7 @@ static cudaError_t raise_smem_limit(const void* fn, cudaFuncAttribute attr, int 
 
 struct WsLayout {
   size_t status, gates, cmat, cenc, thetaJ, dthetaJ, d1, d2, u1, blk_loss, blk_grad, wpart;
-  size_t dW, dphi, dU, dG, dY, dpart, dWT, dmu, dW16, dcs, dgs, total;
+  size_t dW, dphi, dU, dG, dY, dpart, dWT, dmu, dW16, dcs, dgs, dgates, total;
 };
 
 // Rows of (point, vector) accumulated per weight-gradient chunk (bounds the FP32 tensor-core
@@ -79,7 +80,8 @@ int64_t wg_rows_per_chunk(int n) { return n <= 8 ? 512 : 4096; }
 
 // Weight-gradient launch geometry for `nkc` 16-row steps: tiles of min(256, 2^n) basis
 // indices x 256 components, CTA groups per tile (persistent CTAs, balanced step ranges),
-// partial slots per CTA and steps per slot (at most wg_rows_per_chunk rows each).
+// flushes per CTA and steps per flush (at most wg_rows_per_chunk rows each); one partial slot
+// per CTA of a tile.
 struct WgGeom {
   int tiles, ngroups, spc, fl;
   int64_t nslots;
@@ -94,7 +96,7 @@ WgGeom wg_geom(const qp_plan* pl, int64_t nkc) {
   const int64_t nfl = (per + flmax - 1) / flmax;
   g.fl = (int)((per + nfl - 1) / nfl);
   g.spc = (int)nfl;
-  g.nslots = (int64_t)g.ngroups * g.spc;
+  g.nslots = g.ngroups;
   return g;
 }
 
@@ -151,6 +153,7 @@ WsLayout ws_layout(const qp_plan* pl, int64_t P) {
   w.dW16 = o; o = al256(o + (dg && fused_path(pl) ? 2 * (2 * dim) * dim * 4 : 0));
   w.dcs = o; o = al256(o + (dg ? (size_t)P * n * 8 : 0));
   w.dgs = o; o = al256(o + (dg ? (size_t)gsum_groups(pl) * dim * dim * 16 : 0));
+  w.dgates = o; o = al256(o + (dg ? (size_t)pl->c.n_layers * n * 4 * 16 : 0));
   w.total = o;
   return w;
 }
@@ -338,6 +341,8 @@ qp_status qp_plan_create(const qp_circuit* circuit, const qp_problem* problem, i
                              (1 << n) * 16 * 8) != cudaSuccess ||
         raise_smem_limit((void*)qpd::dense_sweep_right_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (1 << n) * 16 * 8) != cudaSuccess ||
+        (n <= 8 && raise_smem_limit((void*)qpd::dense_sweep_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    qpd::swc_smem(n, pl->c.n_layers, qpd::swc_size(n, false))) != cudaSuccess) ||
         (fused_path(pl) &&
          (raise_smem_limit((void*)qpd::dense_fused_fwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                qpd::fused_smem(n, pl->p.energy_nt).total) != cudaSuccess ||
@@ -346,6 +351,27 @@ qp_status qp_plan_create(const qp_circuit* circuit, const qp_problem* problem, i
       cudaGetLastError();
       delete pl;
       return QP_ERR_CUDA;
+    }
+    if (n >= 4 && n <= 8) {
+      // a 16-CTA cluster (non-portable size) halves every CTA's share of the sweep
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3(16);
+      cfg.blockDim = dim3(qpd::SWC_THREADS);
+      cfg.dynamicSmemBytes = qpd::swc_smem(n, pl->c.n_layers, 16);
+      cudaLaunchAttribute attr[1];
+      attr[0].id = cudaLaunchAttributeClusterDimension;
+      attr[0].val.clusterDim.x = 16;
+      attr[0].val.clusterDim.y = 1;
+      attr[0].val.clusterDim.z = 1;
+      cfg.attrs = attr;
+      cfg.numAttrs = 1;
+      int nclusters = 0;
+      pl->swc_big = cudaFuncSetAttribute((const void*)qpd::dense_sweep_cluster_kernel,
+                                         cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess &&
+                    cudaOccupancyMaxActiveClusters(&nclusters, (const void*)qpd::dense_sweep_cluster_kernel, &cfg) ==
+                        cudaSuccess &&
+                    nclusters >= 1;
+      cudaGetLastError();
     }
   }
   if (circuit->premap == QP_PREMAP_RFF_MLP) {
@@ -507,8 +533,9 @@ static qp_status dense_loss_grad(qp_plan* pl, const float* d_params, const float
   qp_status st = launch_front(pl, d_params, pts, npts, w, s);
   if (st != QP_OK) return st;
   launches += 2;
-  qpd::BuildArgs ba;
+  qpd::BuildArgs ba = {};
   ba.params = d_params; ba.circ_off = pl->circ_off; ba.n = n; ba.L = L;
+  ba.gates = (double2*)(ws + w.dgates);
   ba.ansatz = pl->c.ansatz; ba.enc = pl->c.enc; ba.W = (float*)(ws + w.dW); ba.U = (double2*)(ws + w.dU);
   const bool mlp = pl->c.premap == QP_PREMAP_RFF_MLP;
   ba.WT = mlp ? (float*)(ws + w.dWT) : nullptr;
@@ -600,6 +627,7 @@ static qp_status dense_loss_grad(qp_plan* pl, const float* d_params, const float
   sa.part = wa.part; sa.nchunks = (int32_t)wgm.nslots; sa.n = n; sa.L = L; sa.ansatz = pl->c.ansatz;
   sa.U = (const double2*)(ws + w.dU); sa.G = (float2*)(ws + w.dG); sa.Y = (float2*)(ws + w.dY);
   sa.params = d_params; sa.circ_off = pl->circ_off; sa.eout = (float*)(ws + w.blk_grad);
+  sa.gates = (const double2*)(ws + w.dgates);
   {
     const int gg = gsum_groups(pl);
     qpd::dense_gsum_kernel<<<dim3((dim * dim + 255) / 256, gg), 256, 0, s>>>(sa, gg, (float4*)(ws + w.dgs));
@@ -609,7 +637,24 @@ static qp_status dense_loss_grad(qp_plan* pl, const float* d_params, const float
     launches += 1;
   }
   qpd::dense_y_kernel<<<dim3(dim / 16, dim / 16), 256, 0, s>>>(sa);
-  {
+  if (n <= 8) {
+    // the whole sweep in one cluster launch (Y lives in the cluster's shared memory)
+    const int S = qpd::swc_size(n, pl->swc_big);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(S);
+    cfg.blockDim = dim3(qpd::SWC_THREADS);
+    cfg.dynamicSmemBytes = qpd::swc_smem(n, L, S);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = S;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    if (cudaLaunchKernelEx(&cfg, qpd::dense_sweep_cluster_kernel, sa) != cudaSuccess) return QP_ERR_CUDA;
+    launches += 1;
+  } else {
     float2* Ya = sa.Y;
     float2* Yb = sa.G;  // the G scratch is free once Y = U' G is formed
     const int tcol = 16, trow = 16;
@@ -699,7 +744,7 @@ qp_status qp_forward(qp_plan* pl, const float* d_params, const float* d_pts, int
   if (dense_path(pl)) {
     char* ws = (char*)pl->ws;
     const int n = pl->c.n_qubits, dim = 1 << n;
-    qpd::BuildArgs ba;
+    qpd::BuildArgs ba = {};
     ba.params = d_params; ba.circ_off = pl->circ_off; ba.n = n; ba.L = pl->c.n_layers;
     ba.ansatz = pl->c.ansatz; ba.enc = pl->c.enc; ba.W = (float*)(ws + w.dW); ba.U = nullptr;
     ba.W16 = nullptr;

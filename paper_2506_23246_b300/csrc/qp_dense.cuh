@@ -64,6 +64,7 @@ struct BuildArgs {
   double2* U;      // [2^n][2^n] fused unitary U' (row j, column k), FP64, or null
   float* WT;       // transpose operand (rows a = basis index, K = o), same tiling, or null
   float* W16;      // [dim / 16][2 dim / 256][2 (hi, lo)][256 x 16] blocks for the fused kernel, or null
+  double2* gates;  // [L][n][4] rotation gate matrices (written by block 0), or null
 };
 
 __device__ inline double2 zmul(double2 a, double2 b) {
@@ -113,6 +114,10 @@ __global__ void dense_build_kernel(BuildArgs a) {
   const int n = a.n, dim = 1 << n, k = blockIdx.x;
   for (int i = threadIdx.x; i < a.L * n; i += blockDim.x)
     gate_fp64(a.params, a.circ_off, a.ansatz, n, i / n, i % n, &gm[i * 4]);
+  if (a.gates && k == 0) {
+    __syncthreads();
+    for (int i = threadIdx.x; i < a.L * n * 4; i += blockDim.x) a.gates[i] = gm[i];
+  }
   double2* col = colbuf;
   double2* nxt = colbuf + dim;
   for (int j = threadIdx.x; j < dim; j += blockDim.x) col[j] = make_double2(j == k ? 1.0 : 0.0, 0.0);
@@ -648,6 +653,7 @@ struct SweepArgs {
   const float* params;
   int64_t circ_off;
   float* eout;          // blk_grad block 0: E[(l n + q) * 3 + P]
+  const double2* gates; // [L][n][4] rotation gates from the build (cluster sweep)
 };
 
 // Compensated FP32 accumulation (Neumaier): s + c carries the sum to about twice FP32
@@ -817,6 +823,199 @@ __global__ void dense_sweep_right_kernel(SweepArgs a, int l, float2* Y) {
   for (int e = threadIdx.x; e < dim * TROW; e += blockDim.x) Y[(int64_t)r0b * dim + e] = tile[e];
 }
 
+
+// ---- whole sweep in one thread-block cluster (n <= 8: Y fits the cluster's shared memory)
+// The S CTAs of the cluster hold Y (2^n x 2^n) in two layouts, w = 2^n / S indices each:
+//   C (columns): CTA c holds Y[row][c w + j] for every row, at bufC[row][j],
+//   R (rows):    CTA c holds Y[c w + i][col] for every column, at bufR[col][i],
+// both stored [full index x][local index j] with j swizzled by x (j ^ (x mod w)), so that
+// the row-wise gate passes, the column-wise gate passes and the transposing gathers between
+// the layouts all read and write shared memory without bank conflicts. Per layer l (last to
+// first): the CNOT ring is undone by gathering C from R across the cluster, E(l) is read off
+// C, the rotations are undone on the rows in C (R^dag Y) and, after a gather back to R, on
+// the columns (Y R). Two cluster barriers per layer; one launch for the whole sweep.
+constexpr int SWC_THREADS = 512;
+constexpr int SWC_UNROLL = 8;     // cluster loads in flight per thread
+// cluster size: 2^n CTAs up to 8, or 16 where the GPU can co-schedule a 16-CTA cluster
+__host__ __device__ inline int swc_size(int n, bool big) {
+  const int cap = big ? 16 : 8;
+  return (1 << n) < cap ? (1 << n) : cap;
+}
+__host__ __device__ inline int swc_smem(int n, int L, int S) {
+  const int dim = 1 << n, w = dim / S;
+  return 2 * dim * w * 8 + L * n * 4 * 8 + 2 * dim * 4 + L * n * 3 * 4;
+}
+__device__ __forceinline__ int swz(int x, int j, int w) { return x * w + (j ^ (x & (w - 1))); }
+
+// One pass of the gates of qubits q0 .. q0 + g - 1 (g <= 4) over the full index x of a
+// [2^n][w] buffer: each thread carries the 2^g elements of one (x outside the group, j) in
+// registers. y0 = u00 x0 + u10 x1, y1 = u01 x0 + u11 x1 with u conjugated when `dag`.
+__device__ __forceinline__ void swc_gates(float2* buf, int n, int w, int q0, int g, const float2* gl, bool dag) {
+  const int dim = 1 << n, plo = n - q0 - g, ng = 1 << g;
+  const int ngrp = (dim >> g) * w;
+  for (int t = threadIdx.x; t < ngrp; t += blockDim.x) {
+    const int j = t % w, rest = t / w;
+    const int xb = ((rest >> plo) << (plo + g)) | (rest & ((1 << plo) - 1));
+    float2 v[16];
+#pragma unroll
+    for (int m = 0; m < 16; ++m)
+      if (m < ng) v[m] = buf[swz(xb | (m << plo), j, w)];
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      if (b < g) {
+        // qubit q0 + g - 1 - b owns bit b of m
+        const float2* u = gl + (q0 + g - 1 - b) * 4;
+        const float sy = dag ? -1.f : 1.f;
+        const float2 u00 = make_float2(u[0].x, sy * u[0].y), u01 = make_float2(u[1].x, sy * u[1].y);
+        const float2 u10 = make_float2(u[2].x, sy * u[2].y), u11 = make_float2(u[3].x, sy * u[3].y);
+#pragma unroll
+        for (int m = 0; m < 16; ++m) {
+          if (m < ng && !((m >> b) & 1)) {
+            const float2 x0 = v[m], x1 = v[m | (1 << b)];
+            v[m] = make_float2(u00.x * x0.x - u00.y * x0.y + u10.x * x1.x - u10.y * x1.y,
+                               u00.x * x0.y + u00.y * x0.x + u10.x * x1.y + u10.y * x1.x);
+            v[m | (1 << b)] = make_float2(u01.x * x0.x - u01.y * x0.y + u11.x * x1.x - u11.y * x1.y,
+                                          u01.x * x0.y + u01.y * x0.x + u11.x * x1.y + u11.y * x1.x);
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int m = 0; m < 16; ++m)
+      if (m < ng) buf[swz(xb | (m << plo), j, w)] = v[m];
+  }
+}
+
+__global__ void __launch_bounds__(SWC_THREADS) dense_sweep_cluster_kernel(SweepArgs a) {
+  extern __shared__ __align__(16) float2 swsm[];
+  const int n = a.n, dim = 1 << n, L = a.L;
+  const int S = (int)qptc::cluster_size(), w = dim / S, lw = n - (31 - __clz(S));
+  const int c = (int)qptc::cluster_rank();
+  const int wi = threadIdx.x >> 5, ln = threadIdx.x & 31;
+  float2* bufR = swsm;                          // [dim][w]
+  float2* bufC = bufR + dim * w;                // [dim][w]
+  float2* gm = bufC + dim * w;                  // [L][n][4] rotation gates (FP32)
+  int* cmap = reinterpret_cast<int*>(gm + L * n * 4);   // ring map of the current layer
+  int* cinv = cmap + dim;                                // and its inverse
+  float* es = reinterpret_cast<float*>(cinv + dim);      // [L][n][3] E partials
+  for (int i = threadIdx.x; i < L * n * 4; i += blockDim.x) {
+    const double2 g = a.gates[i];
+    gm[i] = make_float2((float)g.x, (float)g.y);
+  }
+  for (int i = threadIdx.x; i < L * n * 3; i += blockDim.x) es[i] = 0.f;
+  // this CTA's rows of Y (row-major in global memory) into layout R
+  for (int e0 = threadIdx.x; e0 < w * dim; e0 += SWC_UNROLL * blockDim.x) {
+    float2 v[SWC_UNROLL];
+#pragma unroll
+    for (int u = 0; u < SWC_UNROLL; ++u) {
+      const int e = e0 + u * blockDim.x;
+      if (e < w * dim) v[u] = a.Y[(int64_t)(c * w + e / dim) * dim + e % dim];
+    }
+#pragma unroll
+    for (int u = 0; u < SWC_UNROLL; ++u) {
+      const int e = e0 + u * blockDim.x;
+      if (e < w * dim) bufR[swz(e % dim, e / dim, w)] = v[u];
+    }
+  }
+  qptc::cluster_sync();
+  for (int l = L - 1; l >= 0; --l) {
+    for (int k = threadIdx.x; k < dim; k += blockDim.x) {
+      const int ck = ring_map(n, a.ansatz, l, k);
+      cmap[k] = ck;
+      cinv[ck] = k;
+    }
+    __syncthreads();
+    // (1) Y2[ra][cb] = Y[c(ra)][c(cb)] for this CTA's columns cb = c w + j, into layout C. The
+    // lanes walk the source rows c(ra) = owner w + i of one source column c(cb): one
+    // contiguous row of the owner's layout R per warp access.
+    for (int e0 = threadIdx.x; e0 < dim * w; e0 += SWC_UNROLL * blockDim.x) {
+      float2 v[SWC_UNROLL];
+#pragma unroll
+      for (int u = 0; u < SWC_UNROLL; ++u) {
+        const int e = e0 + u * blockDim.x;
+        if (e < dim * w) {
+          const int i = e & (w - 1), j = (e >> lw) & (w - 1), owner = e >> (2 * lw);
+          v[u] = qptc::cluster_ld_f2(qptc::cluster_map(&bufR[swz(cmap[c * w + j], i, w)], (uint32_t)owner));
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < SWC_UNROLL; ++u) {
+        const int e = e0 + u * blockDim.x;
+        if (e < dim * w) {
+          const int i = e & (w - 1), j = (e >> lw) & (w - 1), owner = e >> (2 * lw);
+          bufC[swz(cinv[owner * w + i], j, w)] = v[u];
+        }
+      }
+    }
+    __syncthreads();
+    // E_P(l, q) = Im Tr(P_q Y2): warp b <= n takes the off-diagonal elements Y2[cb ^ 2^b][cb]
+    // (X and Y terms of qubit n - 1 - b) or, b = n, the diagonal (Z terms), lanes = columns
+    if (wi <= n) {
+      const bool act = ln < w;
+      const int cb = c * w + (act ? ln : 0);
+      float* el = es + l * n * 3;
+      if (wi == n) {
+        const float vy = act ? bufC[swz(cb, ln, w)].y : 0.f;
+        for (int q = 0; q < n; ++q) {
+          float t = ((cb >> (n - 1 - q)) & 1) ? -vy : vy;
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+          if (ln == 0) el[q * 3 + 2] += t;
+        }
+      } else {
+        const int q = n - 1 - wi;
+        const float2 v = act ? bufC[swz(cb ^ (1 << wi), ln, w)] : make_float2(0.f, 0.f);
+        float tx = v.y, ty = ((cb >> wi) & 1) ? v.x : -v.x;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          tx += __shfl_xor_sync(0xffffffffu, tx, o);
+          ty += __shfl_xor_sync(0xffffffffu, ty, o);
+        }
+        if (ln == 0) { el[q * 3 + 0] += tx; el[q * 3 + 1] += ty; }
+      }
+    }
+    if (l == 0) break;
+    __syncthreads();
+    // (2) rows: Y <- R_l^dag Y
+    const float2* gl = gm + l * n * 4;
+    for (int q0 = 0; q0 < n; q0 += 4) {
+      swc_gates(bufC, n, w, q0, n - q0 < 4 ? n - q0 : 4, gl, true);
+      __syncthreads();
+    }
+    qptc::cluster_sync();
+    // (3) back to layout R: Y[c w + i][col] sits in CTA col / w at bufC[c w + i][col mod w];
+    // the lanes walk col mod w (one contiguous row of the owner's layout C per warp access)
+    for (int e0 = threadIdx.x; e0 < dim * w; e0 += SWC_UNROLL * blockDim.x) {
+      float2 v[SWC_UNROLL];
+#pragma unroll
+      for (int u = 0; u < SWC_UNROLL; ++u) {
+        const int e = e0 + u * blockDim.x;
+        if (e < dim * w) {
+          const int j = e & (w - 1), i = (e >> lw) & (w - 1), owner = e >> (2 * lw);
+          v[u] = qptc::cluster_ld_f2(qptc::cluster_map(&bufC[swz(c * w + i, j, w)], (uint32_t)owner));
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < SWC_UNROLL; ++u) {
+        const int e = e0 + u * blockDim.x;
+        if (e < dim * w) {
+          const int j = e & (w - 1), i = (e >> lw) & (w - 1), owner = e >> (2 * lw);
+          bufR[swz(owner * w + j, i, w)] = v[u];
+        }
+      }
+    }
+    __syncthreads();
+    // (4) columns: Y <- Y R_l
+    for (int q0 = 0; q0 < n; q0 += 4) {
+      swc_gates(bufR, n, w, q0, n - q0 < 4 ? n - q0 : 4, gl, false);
+      __syncthreads();
+    }
+    qptc::cluster_sync();
+  }
+  // every peer is done reading this CTA's layout R before it exits
+  qptc::cluster_sync();
+  for (int i = threadIdx.x; i < L * n * 3; i += blockDim.x) atomicAdd(&a.eout[i], es[i]);
+}
 }  // namespace qpd
 
 namespace qpd {

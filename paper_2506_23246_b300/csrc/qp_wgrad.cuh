@@ -19,8 +19,9 @@ namespace qpd {
 // duals), so each element of R is one dual product H[k >> 5] x Lo[k & 31].
 //
 // Persistent CTAs: CTA b owns tile b % tiles and a balanced range of steps; every `fl` steps
-// (<= 512 rows, the FP32 accumulation length) the accumulator is flushed to its own partial
-// slot, summed later in compensated FP32.
+// (<= 512 rows, the FP32 accumulation length in tensor memory) the accumulator is added into
+// the CTA's partial slot (a few FP32 adds per element, the slot stays in L2); the slots of
+// all CTAs of a tile are summed later in compensated FP32.
 //
 // Pipeline of one step (3 block barriers): the costate rows arrive in a 4-slot shared-memory
 // ring by bulk copies issued three steps ahead; the step's R tables were built during the
@@ -28,6 +29,12 @@ namespace qpd {
 // tables, builds the next tables and factors, reads its costate columns, starts the copy three
 // steps ahead, splits the columns into the TF32 B operand, and one thread issues the MMAs.
 constexpr int WKC = 16;
+
+// Fire-and-forget vector add into global memory (performed at L2).
+__device__ __forceinline__ void red_add_f4(float4* p, float4 v) {
+  asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w)
+               : "memory");
+}
 constexpr int WG_STAGERS = 512;                 // operand-staging threads (16 warps)
 constexpr int WG_THREADS = WG_STAGERS + 32;       // + one control warp (copies, MMAs)
 constexpr int WG_RING = 4;
@@ -37,11 +44,11 @@ struct WgArgs {
   const float2* cs;           // [P][n] (cos, sin) of theta / 2
   const float* lam;           // costate rows: blocked [2 dim / 256][rtot][256] or rows [P][4][2 dim]
   int64_t rtot;               // rows of the blocked layout (0: row layout)
-  float* part;                // [nslots][dim][2 dim]
+  float* part;                // [ngroups][dim][2 dim], one slot per CTA of a tile
   int32_t n;
   int64_t npts[3], pt_base[3];
   int64_t kc_end[3];          // cumulative 16-row step counts per set
-  int32_t tiles, ngroups, spc, fl;  // tiles, CTAs per tile, partial slots per CTA, steps per slot
+  int32_t tiles, ngroups, spc, fl;  // tiles, CTAs per tile, flushes per CTA, steps per flush
   int32_t* status;
 };
 
@@ -290,20 +297,25 @@ __global__ void __launch_bounds__(WG_THREADS, 1) dense_wgrad_gemm_kernel(WgArgs 
     }
   } else {
     // ---- staging warps
-    // epilogue of one partial: the MTC x 256 accumulator -> part[slot]
-    auto flush = [&](int sl, bool zero) {
+    // epilogue of one partial: part[CTA slot] (+)= the MTC x 256 accumulator; every element
+    // is read and written by the same thread at every flush
+    auto flush = [&](bool add, bool zero) {
       const int g = warp & 3, qw = warp >> 2;          // lane group, quarter of the columns
       const int u = msub == 2 ? qw >> 1 : 0;            // M sub-tile read by this warp
       const int cbeg = msub == 2 ? (qw & 1) * 128 : qw * 64, ncols = msub == 2 ? 128 : 64;
       const int64_t krow = kbase + u * TM + g * 32 + lane;
-      float* outp = a.part + (((int64_t)(lb * a.spc + sl) * dim) + krow) * (2 * dim) + ntile * 256 + cbeg;
+      float* outp = a.part + (((int64_t)lb * dim) + krow) * (2 * dim) + ntile * 256 + cbeg;
       if (!zero) {
         float v[32];
         for (int c = 0; c < ncols; c += 32) {
           qptc::tmem_ld32(tmem + ((uint32_t)(g * 32) << 16) + u * 256 + cbeg + c, v);
+          float4* o4 = reinterpret_cast<float4*>(outp + c);
 #pragma unroll
-          for (int e = 0; e < 8; ++e)
-            reinterpret_cast<float4*>(outp + c)[e] = make_float4(v[4 * e], v[4 * e + 1], v[4 * e + 2], v[4 * e + 3]);
+          for (int e = 0; e < 8; ++e) {
+            const float4 r = make_float4(v[4 * e], v[4 * e + 1], v[4 * e + 2], v[4 * e + 3]);
+            if (add) red_add_f4(o4 + e, r);   // no return value: the flush does not wait on L2
+            else o4[e] = r;
+          }
         }
       } else {
         for (int c = 0; c < ncols; c += 4) *reinterpret_cast<float4*>(outp + c) = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -410,7 +422,7 @@ __global__ void __launch_bounds__(WG_THREADS, 1) dense_wgrad_gemm_kernel(WgArgs 
         if (good) good = qptc::mbar_wait(&mma_done[st], (it >> 1) & 1);
         if (good) {
           qptc::fence_after();
-          flush(slot, false);
+          flush(slot > 0, false);
         }
         qptc::fence_before();
         __syncwarp();
@@ -422,7 +434,7 @@ __global__ void __launch_bounds__(WG_THREADS, 1) dense_wgrad_gemm_kernel(WgArgs 
       else ok = __all_sync(0xffffffffu, good);
     }
     if (ok) {
-      for (int sl = slot; sl < a.spc; ++sl) flush(sl, true);
+      if (slot == 0) flush(false, true);   // no rows: the slot still joins the sum
     } else if (tid == 0) {
       atomicExch(a.status, 6);
     }
