@@ -32,6 +32,7 @@ struct qp_plan {
   int smem_grad = 0, smem_fwd = 0, sstride_grad = 0, sstride_fwd = 0;
   int nwblk = 0, wtile = 0, smem_wgrad = 0, smem_premap = 0, smem_premap4 = 0;
   bool swc_big = false;   // the one-launch sweep runs as a 16-CTA cluster
+  bool pg_ok = false;     // RFF + MLP premap with F = 64, H = 32: the GEMM-formulated kernels
   int64_t n_params = 0, circ_off = 0, head_off = 0, mlp_off = 0, mlp_count = 0, nfixed = 0;
   void* ws = nullptr;
   size_t ws_bytes = 0;
@@ -383,6 +384,16 @@ qp_status qp_plan_create(const qp_circuit* circuit, const qp_problem* problem, i
     pl->wtile = tile;
     pl->smem_wgrad = tile * (2 * F + 2 * H + n) * 16 + 3 * F * 4;
     pl->smem_premap4 = qpk::premap4_smem(F, H, n);
+    pl->pg_ok = F == qpk::PG_F && H == qpk::PG_H && n <= 16;
+    if (pl->pg_ok &&
+        (raise_smem_limit((void*)qpk::premap_fwd_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                          qpk::pg_fwd_smem(n)) != cudaSuccess ||
+         raise_smem_limit((void*)qpk::premap_bwd_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                          qpk::pg_bwd_smem(n)) != cudaSuccess)) {
+      cudaGetLastError();
+      delete pl;
+      return QP_ERR_CUDA;
+    }
     if (raise_smem_limit(premap_fwd_ptr(H), cudaFuncAttributeMaxDynamicSharedMemorySize, pl->smem_premap) != cudaSuccess ||
         raise_smem_limit(premap_fwd4_ptr(H), cudaFuncAttributeMaxDynamicSharedMemorySize, pl->smem_premap4) != cudaSuccess ||
         raise_smem_limit(premap_bwd4_ptr(H), cudaFuncAttributeMaxDynamicSharedMemorySize, pl->smem_premap4) != cudaSuccess ||
@@ -449,7 +460,7 @@ static void fill_problem(const qp_plan* pl, QPProblemDev& d) {
 
 // Shared prologue: gate preparation and premap forward for all point sets.
 static qp_status launch_front(qp_plan* pl, const float* d_params, const float* const pts[3],
-                              const int64_t npts[3], const WsLayout& w, cudaStream_t s) {
+                              const int64_t npts[3], const WsLayout& w, cudaStream_t s, bool grad) {
   char* ws = (char*)pl->ws;
   const int n = pl->c.n_qubits, L = pl->c.n_layers;
   qpk::PrepArgs pa;
@@ -468,7 +479,13 @@ static qp_status launch_front(qp_plan* pl, const float* d_params, const float* c
   ma.counts = pa.counts; ma.medium = pl->p.medium;
   ma.disk_r = pl->p.disk_r; ma.disk_x0 = pl->p.disk_x0; ma.disk_y0 = pl->p.disk_y0;
   const int pblocks = (int)((ma.ptot + 127) / 128 < pl->sm_count * 8 ? (ma.ptot + 127) / 128 : pl->sm_count * 8);
-  if (pl->c.premap == QP_PREMAP_RFF_MLP) {
+  if (pl->c.premap == QP_PREMAP_RFF_MLP && pl->pg_ok) {
+    // GEMM formulation over 64-point tiles; the unit table is kept for the backward
+    ma.u1 = grad ? (float*)(ws + w.u1) : nullptr;
+    const int64_t nt = (ma.ptot + qpk::PG_TP - 1) / qpk::PG_TP;
+    const int gb = (int)(nt < pl->sm_count * 2 ? (nt > 0 ? nt : 1) : pl->sm_count * 2);
+    qpk::premap_fwd_gemm_kernel<<<gb, qpk::PG_THREADS, qpk::pg_fwd_smem(n), s>>>(ma);
+  } else if (pl->c.premap == QP_PREMAP_RFF_MLP) {
     // four threads per point, 32 points per block
     const int64_t qb = (ma.ptot + 31) / 32;
     const int qblocks = (int)(qb < pl->sm_count * 8 ? (qb > 0 ? qb : 1) : pl->sm_count * 8);
@@ -530,7 +547,7 @@ static qp_status dense_loss_grad(qp_plan* pl, const float* d_params, const float
   char* ws = (char*)pl->ws;
   const int n = pl->c.n_qubits, dim = 1 << n, L = pl->c.n_layers;
   int launches = 0;
-  qp_status st = launch_front(pl, d_params, pts, npts, w, s);
+  qp_status st = launch_front(pl, d_params, pts, npts, w, s, true);
   if (st != QP_OK) return st;
   launches += 2;
   qpd::BuildArgs ba = {};
@@ -719,7 +736,7 @@ static qp_status dense_loss_grad(qp_plan* pl, const float* d_params, const float
     }
     st = launch_premap_bwd(pl, w, d_params, pts, npts, s);
     if (st != QP_OK) return st;
-    launches += 2;
+    launches += pl->pg_ok ? 1 : 2;
   }
   st = launch_reduce(pl, w, d_params, npts, d_loss, d_grad, mlp, s);
   pl->last_launches = launches + 1;
@@ -739,7 +756,7 @@ qp_status qp_forward(qp_plan* pl, const float* d_params, const float* d_pts, int
   pl->last_stream = s;
   const float* pts[3] = {d_pts, nullptr, nullptr};
   const int64_t npts[3] = {B, 0, 0};
-  qp_status st = launch_front(pl, d_params, pts, npts, w, s);
+  qp_status st = launch_front(pl, d_params, pts, npts, w, s, false);
   if (st != QP_OK) return st;
   if (dense_path(pl)) {
     char* ws = (char*)pl->ws;
@@ -833,7 +850,7 @@ qp_status qp_loss_grad(qp_plan* pl, const float* d_params, const qp_batch* batch
   char* ws = (char*)pl->ws;
   int launches = 0;
   if (P > 0) {
-    qp_status st = launch_front(pl, d_params, pts, npts, w, s);
+    qp_status st = launch_front(pl, d_params, pts, npts, w, s, true);
     if (st != QP_OK) return st;
     launches += 2;
   } else {
@@ -864,7 +881,7 @@ qp_status qp_loss_grad(qp_plan* pl, const float* d_params, const qp_batch* batch
   if (mlp) {
     qp_status stb = launch_premap_bwd(pl, w, d_params, pts, npts, s);
     if (stb != QP_OK) return stb;
-    launches += 2;
+    launches += pl->pg_ok ? 1 : 2;
   }
   qp_status st_red;
   st_red = launch_reduce(pl, w, d_params, npts, d_loss, d_grad, mlp, s);
@@ -886,6 +903,12 @@ static qp_status launch_premap_bwd(qp_plan* pl, const WsLayout& w, const float* 
   ma.thetaJ = (float*)(ws + w.thetaJ);
   ma.dthetaJ = (const float*)(ws + w.dthetaJ);
   ma.d1 = (float*)(ws + w.d1); ma.d2 = (float*)(ws + w.d2); ma.u1 = (float*)(ws + w.u1);
+  if (pl->pg_ok) {
+    // backward and weight-gradient partials in one pass (one partial slot per block)
+    qpk::premap_bwd_gemm_kernel<<<pl->nwblk, qpk::PG_THREADS, qpk::pg_bwd_smem(pl->c.n_qubits), s>>>(
+        ma, (float*)(ws + w.wpart), (int32_t)(pl->mlp_count - pl->nfixed));
+    return cuda_status(cudaGetLastError());
+  }
   if (P > 0) {
     const int64_t qb = (P + 31) / 32;
     const int pblocks = (int)(qb < pl->sm_count * 8 ? qb : pl->sm_count * 8);
@@ -932,8 +955,8 @@ static qp_status launch_reduce(qp_plan* pl, const WsLayout& w, const float* d_pa
   ra.nb = pl->cur_norm[2] > 0 ? pl->cur_norm[2] : npts[2];
   ra.norm_diel = pl->cur_norm[0] > 0 ? pl->cur_norm_diel : -1;
   ra.w_ic = pl->p.w_ic; ra.w_bc = pl->p.w_bc; ra.w_energy = pl->p.w_energy;
-  const int64_t nred = pl->n_params > QP_MAXNT ? pl->n_params : QP_MAXNT;
-  qpk::reduce_kernel<<<(unsigned)((nred + 255) / 256), 256, 0, s>>>(ra);
+  const int64_t nwarps = pl->n_params + 1 + ra.nt;   // one warp per output
+  qpk::reduce_kernel<<<(unsigned)((nwarps + 7) / 8), 256, 0, s>>>(ra);
   return cuda_status(cudaGetLastError());
 }
 

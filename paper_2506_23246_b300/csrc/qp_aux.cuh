@@ -513,6 +513,313 @@ __global__ void premap_bwd_kernel(PremapArgs a) {
   }
 }
 
+// ---- RFF + MLP premap as register-blocked FP32 GEMMs over 64-point tiles (F = 64, H = 32).
+// With r = [cos(Omega v), sin(Omega v)] (K = 2F = 128 features), unit o's pre-activation and
+// its x, y, t tangents are h_c[o] = sum_i B[(o, c)][i] r[i] with
+//   B[(o, 0)][i] = W1[o][i],  B[(o, c)][f] = W1[o][F + f] Omega[f][c],  B[(o, c)][F + f] = -W1[o][f] Omega[f][c]
+// (d/dv_c turns cos into -sin Omega and sin into cos Omega: the halves swap), so the forward is
+// one GEMM [points] x [K] x [N = 4H = 128 columns (o, c)] and needs no tangent rows. The weight
+// gradient is the transposed contraction over points, D[(o, c)][i] = sum_p d1_p[(o, c)] r_p[i],
+// folded back by the same rule:
+//   dW1[o][f] = D[(o,0)][f] - sum_c Omega[f][c] D[(o,c)][F+f],  dW1[o][F+f] = D[(o,0)][F+f] + sum_c Omega[f][c] D[(o,c)][f].
+// The forward keeps u = tanh(h_0) and its tangents u_c = (1 - u^2) h_c per point for the
+// backward (the backward needs no h_c: (1 - u^2) h_c = u_c).
+constexpr int PG_F = 64, PG_H = 32, PG_K = 2 * PG_F, PG_N = 4 * PG_H, PG_TP = 64, PG_THREADS = 256;
+constexpr int PG_US = PG_H + 1;   // padded row of the per-point unit table (float4)
+__host__ __device__ inline int pg_fwd_smem(int n) {
+  const int areg = PG_K * PG_TP > PG_TP * PG_US * 4 ? PG_K * PG_TP : PG_TP * PG_US * 4;
+  return (PG_K * PG_N + areg + 3 * PG_F + PG_H + n * PG_H + n + PG_TP * 3) * 4;
+}
+__host__ __device__ inline int pg_bwd_smem(int n) {
+  return (PG_TP * PG_US * 4 + PG_TP * PG_N + PG_TP * PG_K + PG_TP * n * 4 + 3 * PG_F + n * PG_H + n +
+          PG_TP * 3 + 8 * PG_H) * 4;
+}
+
+// the tile's point coordinates
+__device__ __forceinline__ void pg_load_points(const PremapArgs& a, int64_t p0, float* Ps) {
+  for (int e = threadIdx.x; e < PG_TP * 3; e += blockDim.x) {
+    const int64_t gp = p0 + e / 3;
+    float v = 0.f;
+    if (gp < a.ptot) {
+      int set;
+      int64_t li;
+      v = point_ptr(a, gp, set, li)[e % 3];
+    }
+    Ps[e] = v;
+  }
+}
+
+__global__ void __launch_bounds__(PG_THREADS, 2) premap_fwd_gemm_kernel(PremapArgs a) {
+  extern __shared__ __align__(16) float pg[];
+  const int n = a.n, tid = threadIdx.x;
+  const int areg = PG_K * PG_TP > PG_TP * PG_US * 4 ? PG_K * PG_TP : PG_TP * PG_US * 4;
+  float* Bs = pg;                                 // [K][N], column (o, c) = 4 o + c
+  float* As = Bs + PG_K * PG_N;                   // [K][TP] feature table of the tile
+  float4* Us = reinterpret_cast<float4*>(As);     // after the GEMM: [TP][PG_US] (u, u_x, u_y, u_t)
+  float* om = As + areg;                          // [F][3]
+  float* b1 = om + 3 * PG_F;
+  float* W2 = b1 + PG_H;                          // [n][H]
+  float* b2 = W2 + n * PG_H;
+  float* Ps = b2 + n;                             // [TP][3]
+  const float* W1 = a.params + 3 * PG_F;
+  for (int i = tid; i < 3 * PG_F; i += blockDim.x) om[i] = a.params[i];
+  for (int i = tid; i < PG_H; i += blockDim.x) b1[i] = W1[PG_H * PG_K + i];
+  for (int i = tid; i < n * PG_H; i += blockDim.x) W2[i] = W1[PG_H * PG_K + PG_H + i];
+  for (int i = tid; i < n; i += blockDim.x) b2[i] = W1[PG_H * PG_K + PG_H + n * PG_H + i];
+  __syncthreads();
+  for (int e = tid; e < PG_K * PG_N; e += blockDim.x) {
+    const int k = e / PG_N, col = e % PG_N, o = col >> 2, c = col & 3;
+    float v;
+    if (c == 0) v = W1[o * PG_K + k];
+    else if (k < PG_F) v = W1[o * PG_K + PG_F + k] * om[3 * k + c - 1];
+    else v = -W1[o * PG_K + (k - PG_F)] * om[3 * (k - PG_F) + c - 1];
+    Bs[e] = v;
+  }
+  const int ty = tid >> 4, tx = tid & 15;
+  const int64_t ntiles = (a.ptot + PG_TP - 1) / PG_TP;
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int64_t p0 = tile * PG_TP;
+    __syncthreads();   // the previous tile's unit table is consumed
+    pg_load_points(a, p0, Ps);
+    __syncthreads();
+    for (int e = tid; e < PG_F * PG_TP; e += blockDim.x) {
+      const int f = e / PG_TP, p = e % PG_TP;
+      float sn, cs;
+      sincosf(om[3 * f] * Ps[3 * p] + om[3 * f + 1] * Ps[3 * p + 1] + om[3 * f + 2] * Ps[3 * p + 2], &sn, &cs);
+      As[f * PG_TP + p] = cs;
+      As[(PG_F + f) * PG_TP + p] = sn;
+    }
+    __syncthreads();
+    // H[p][(o, c)] for points 4 ty + r, columns 4 tx + (0..3) and 64 + 4 tx + (0..3)
+    float acc[4][8];
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+      for (int q = 0; q < 8; ++q) acc[r][q] = 0.f;
+#pragma unroll 4
+    for (int k = 0; k < PG_K; ++k) {
+      const float4 av = *reinterpret_cast<const float4*>(&As[k * PG_TP + ty * 4]);
+      const float4 bv0 = *reinterpret_cast<const float4*>(&Bs[k * PG_N + tx * 4]);
+      const float4 bv1 = *reinterpret_cast<const float4*>(&Bs[k * PG_N + 64 + tx * 4]);
+      const float ar[4] = {av.x, av.y, av.z, av.w};
+      const float br[8] = {bv0.x, bv0.y, bv0.z, bv0.w, bv1.x, bv1.y, bv1.z, bv1.w};
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int q = 0; q < 8; ++q) acc[r][q] = fmaf(ar[r], br[q], acc[r][q]);
+    }
+    __syncthreads();   // the feature table is consumed: the unit table takes its place
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const int p = ty * 4 + r;
+      const int64_t gp = p0 + p;
+#pragma unroll
+      for (int uu = 0; uu < 2; ++uu) {
+        const int o = tx + 16 * uu;
+        const float u = tanhf(acc[r][4 * uu] + b1[o]);
+        const float du = 1.f - u * u;
+        const float4 u4 = make_float4(u, du * acc[r][4 * uu + 1], du * acc[r][4 * uu + 2], du * acc[r][4 * uu + 3]);
+        Us[p * PG_US + o] = u4;
+        if (a.u1 && gp < a.ptot) reinterpret_cast<float4*>(a.u1)[gp * PG_H + o] = u4;
+      }
+    }
+    __syncthreads();
+    // outputs: point tid / 4, outputs j = tid % 4 + 4 jj
+    {
+      const int p = tid >> 2, j0 = tid & 3;
+      const int64_t gp = p0 + p;
+      float4 z[3];
+#pragma unroll
+      for (int jj = 0; jj < 3; ++jj) z[jj] = make_float4(j0 + 4 * jj < n ? b2[j0 + 4 * jj] : 0.f, 0.f, 0.f, 0.f);
+      for (int o = 0; o < PG_H; ++o) {
+        const float4 u4 = Us[p * PG_US + o];
+#pragma unroll
+        for (int jj = 0; jj < 3; ++jj) {
+          const int j = j0 + 4 * jj;
+          if (j < n) {
+            const float w = W2[j * PG_H + o];
+            z[jj].x += w * u4.x; z[jj].y += w * u4.y; z[jj].z += w * u4.z; z[jj].w += w * u4.w;
+          }
+        }
+      }
+      if (gp < a.ptot) {
+        float4* out = reinterpret_cast<float4*>(a.thetaJ) + gp * n;
+#pragma unroll
+        for (int jj = 0; jj < 3; ++jj) {
+          const int j = j0 + 4 * jj;
+          if (j < n) {
+            float g0, g1, g2;
+            scale_tanh(a.scale, z[jj].x, g0, g1, g2);
+            out[j] = make_float4(g0, g1 * z[jj].y, g1 * z[jj].z, g1 * z[jj].w);
+          }
+        }
+      }
+      // collocation points inside the dielectric disk, counted once per point
+      bool inside = false;
+      if (a.medium == 1 && j0 == 0 && gp < a.npts[0]) {
+        const float dx = Ps[3 * p] - a.disk_x0, dy = Ps[3 * p + 1] - a.disk_y0;
+        inside = __fmaf_rn(dx, dx, dy * dy) < a.disk_r * a.disk_r;
+      }
+      const unsigned bal = __ballot_sync(0xffffffffu, inside);
+      if ((tid & 31) == 0 && bal) atomicAdd(&a.counts[0], __popc(bal));
+    }
+  }
+}
+
+// Backward of the premap from dL/dtheta and dL/dJ with its weight-gradient partials, one
+// slot per block in the parameter order [dW1 (H x 2F)][db1 (H)][dW2 (n x H)][db2 (n)].
+__global__ void __launch_bounds__(PG_THREADS, 2) premap_bwd_gemm_kernel(PremapArgs a, float* part, int32_t nW) {
+  extern __shared__ __align__(16) float pg[];
+  const int n = a.n, tid = threadIdx.x;
+  float4* Us = reinterpret_cast<float4*>(pg);                 // [TP][PG_US] (u, u_x, u_y, u_t)
+  float4* D1 = Us + PG_TP * PG_US;                            // [TP][H] dL/dh (c = 0..3)
+  float* As = reinterpret_cast<float*>(D1 + PG_TP * PG_H);    // [TP][K] feature table
+  float4* Dz = reinterpret_cast<float4*>(As + PG_TP * PG_K);  // [TP][n] dL/dz (c = 0..3)
+  float* om = reinterpret_cast<float*>(Dz + PG_TP * n);       // [F][3]
+  float* W2 = om + 3 * PG_F;                                  // [n][H]
+  float* b2 = W2 + n * PG_H;
+  float* Ps = b2 + n;                                         // [TP][3]
+  float* red = Ps + PG_TP * 3;                                // [8][H] db1 partials
+  const float* W1 = a.params + 3 * PG_F;
+  for (int i = tid; i < 3 * PG_F; i += blockDim.x) om[i] = a.params[i];
+  for (int i = tid; i < n * PG_H; i += blockDim.x) W2[i] = W1[PG_H * PG_K + PG_H + i];
+  for (int i = tid; i < n; i += blockDim.x) b2[i] = W1[PG_H * PG_K + PG_H + n * PG_H + i];
+  __syncthreads();   // the fold at the end reads Omega also in blocks without a tile
+  const int ty = tid >> 4, tx = tid & 15;
+  const int ow = tid & 31, pw = tid >> 5;       // (unit, point row) of the d1 and dW2 phases
+  float dacc[8][8];
+#pragma unroll
+  for (int r = 0; r < 8; ++r)
+#pragma unroll
+    for (int q = 0; q < 8; ++q) dacc[r][q] = 0.f;
+  float w2acc[2] = {0.f, 0.f}, b2acc[2] = {0.f, 0.f}, b1acc = 0.f;   // outputs pw, pw + 8
+  const int64_t ntiles = (a.ptot + PG_TP - 1) / PG_TP;
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int64_t p0 = tile * PG_TP;
+    __syncthreads();   // every table of the previous tile is consumed
+    pg_load_points(a, p0, Ps);
+    for (int e = tid; e < PG_TP * PG_H; e += blockDim.x) {
+      const int p = e / PG_H, o = e % PG_H;
+      const int64_t gp = p0 + p;
+      Us[p * PG_US + o] = gp < a.ptot ? reinterpret_cast<const float4*>(a.u1)[gp * PG_H + o]
+                                      : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    __syncthreads();
+    // dL/dz of point tid / 4, outputs j = tid % 4 + 4 jj: theta = g(z_0), J_c = g'(z_0) z_c
+    {
+      const int p = tid >> 2, j0 = tid & 3;
+      const int64_t gp = p0 + p;
+      float4 z[3];
+#pragma unroll
+      for (int jj = 0; jj < 3; ++jj) z[jj] = make_float4(j0 + 4 * jj < n ? b2[j0 + 4 * jj] : 0.f, 0.f, 0.f, 0.f);
+      for (int o = 0; o < PG_H; ++o) {
+        const float4 u4 = Us[p * PG_US + o];
+#pragma unroll
+        for (int jj = 0; jj < 3; ++jj) {
+          const int j = j0 + 4 * jj;
+          if (j < n) {
+            const float w = W2[j * PG_H + o];
+            z[jj].x += w * u4.x; z[jj].y += w * u4.y; z[jj].z += w * u4.z; z[jj].w += w * u4.w;
+          }
+        }
+      }
+#pragma unroll
+      for (int jj = 0; jj < 3; ++jj) {
+        const int j = j0 + 4 * jj;
+        if (j < n) {
+          float g0, g1, g2;
+          scale_tanh(a.scale, z[jj].x, g0, g1, g2);
+          const float4 dt = gp < a.ptot ? reinterpret_cast<const float4*>(a.dthetaJ)[gp * n + j]
+                                        : make_float4(0.f, 0.f, 0.f, 0.f);
+          const float dz0 = dt.x * g1 + g2 * (dt.y * z[jj].y + dt.z * z[jj].z + dt.w * z[jj].w);
+          Dz[p * n + j] = make_float4(dz0, dt.y * g1, dt.z * g1, dt.w * g1);
+        }
+      }
+    }
+    // feature table [p][i]
+    for (int e = tid; e < PG_TP * PG_F; e += blockDim.x) {
+      const int p = e / PG_F, f = e % PG_F;
+      float sn, cs;
+      sincosf(om[3 * f] * Ps[3 * p] + om[3 * f + 1] * Ps[3 * p + 1] + om[3 * f + 2] * Ps[3 * p + 2], &sn, &cs);
+      As[p * PG_K + f] = cs;
+      As[p * PG_K + PG_F + f] = sn;
+    }
+    __syncthreads();
+    // dW2[j][o] += sum_p dz_j . u_o (c = 0..3), db2[j] += sum_p dz_j0: warp j (and j - 8), lane o
+#pragma unroll
+    for (int jj = 0; jj < 2; ++jj) {
+      const int j = pw + 8 * jj;
+      if (j < n) {
+        for (int p = 0; p < PG_TP; ++p) {
+          const float4 d = Dz[p * n + j], u4 = Us[p * PG_US + ow];
+          w2acc[jj] += d.x * u4.x + d.y * u4.y + d.z * u4.z + d.w * u4.w;
+          b2acc[jj] += d.x;
+        }
+      }
+    }
+    // dL/du_o = sum_j W2[j][o] dz_j, then through tanh: d1 = dL/dh
+    for (int p = pw; p < PG_TP; p += PG_THREADS / 32) {
+      float4 gu = make_float4(0.f, 0.f, 0.f, 0.f);
+      for (int j = 0; j < n; ++j) {
+        const float w = W2[j * PG_H + ow];
+        const float4 d = Dz[p * n + j];
+        gu.x += w * d.x; gu.y += w * d.y; gu.z += w * d.z; gu.w += w * d.w;
+      }
+      const float4 u4 = Us[p * PG_US + ow];
+      const float du = 1.f - u4.x * u4.x;
+      const float g0 = gu.x * du - 2.f * u4.x * (gu.y * u4.y + gu.z * u4.z + gu.w * u4.w);
+      D1[p * PG_H + ow] = make_float4(g0, gu.y * du, gu.z * du, gu.w * du);
+      b1acc += g0;
+    }
+    __syncthreads();
+    // D[(o, c)][i] += sum_p d1_p[(o, c)] r_p[i]: units ty and ty + 16, features 4 tx + (0..3), 64 + 4 tx + (0..3)
+#pragma unroll 2
+    for (int p = 0; p < PG_TP; ++p) {
+      const float4 a0 = D1[p * PG_H + ty], a1 = D1[p * PG_H + ty + 16];
+      const float4 bv0 = *reinterpret_cast<const float4*>(&As[p * PG_K + tx * 4]);
+      const float4 bv1 = *reinterpret_cast<const float4*>(&As[p * PG_K + 64 + tx * 4]);
+      const float ar[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+      const float br[8] = {bv0.x, bv0.y, bv0.z, bv0.w, bv1.x, bv1.y, bv1.z, bv1.w};
+#pragma unroll
+      for (int r = 0; r < 8; ++r)
+#pragma unroll
+        for (int q = 0; q < 8; ++q) dacc[r][q] = fmaf(ar[r], br[q], dacc[r][q]);
+    }
+  }
+  // fold D back into dW1 (thread: units ty, ty + 16; frequencies f = 4 tx + ii)
+  float* out = part + (int64_t)blockIdx.x * nW;
+#pragma unroll
+  for (int uu = 0; uu < 2; ++uu) {
+    const int o = ty + 16 * uu;
+#pragma unroll
+    for (int ii = 0; ii < 4; ++ii) {
+      const int f = tx * 4 + ii;
+      const float ox = om[3 * f], oy = om[3 * f + 1], ot = om[3 * f + 2];
+      // dacc[4 uu + c][q]: q = ii the cos feature f, q = 4 + ii the sin feature F + f
+      const float cosp = dacc[4 * uu][ii], sinp = dacc[4 * uu][4 + ii];
+      const float dwc = cosp - (ox * dacc[4 * uu + 1][4 + ii] + oy * dacc[4 * uu + 2][4 + ii] + ot * dacc[4 * uu + 3][4 + ii]);
+      const float dws = sinp + (ox * dacc[4 * uu + 1][ii] + oy * dacc[4 * uu + 2][ii] + ot * dacc[4 * uu + 3][ii]);
+      out[o * PG_K + f] = dwc;
+      out[o * PG_K + PG_F + f] = dws;
+    }
+  }
+  red[pw * PG_H + ow] = b1acc;
+  __syncthreads();
+  if (tid < PG_H) {
+    float t = 0.f;
+    for (int r = 0; r < PG_THREADS / 32; ++r) t += red[r * PG_H + tid];
+    out[PG_H * PG_K + tid] = t;
+  }
+#pragma unroll
+  for (int jj = 0; jj < 2; ++jj) {
+    const int j = pw + 8 * jj;
+    if (j < n) {
+      out[PG_H * PG_K + PG_H + j * PG_H + ow] = w2acc[jj];
+      if (ow == 0) out[PG_H * PG_K + PG_H + n * PG_H + j] = b2acc[jj];
+    }
+  }
+}
+
 // Weight gradients of the premap as block partials over contiguous point chunks.
 //   dW1[o][i] = sum_p d1[o].(r_i, r_{i,x}, r_{i,y}, r_{i,t}),  db1[o] = sum_p d1[o].x
 //   dW2[j][o] = sum_p d2[j].(u1[o] with tangents),             db2[j] = sum_p d2[j].x
@@ -653,9 +960,18 @@ struct ReduceArgs {
   float w_ic, w_bc, w_energy;
 };
 
+// One warp per output: parameter gradients (the lanes split the block partials), then the
+// loss terms and the energy slices. FP64 sums.
+__device__ __forceinline__ double warp_sum_dbl(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
 __global__ void reduce_kernel(ReduceArgs a) {
-  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i < a.nparams) {
+  const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (gw < a.nparams) {
+    const int64_t i = gw;
     float val = 0.f;
     if (i >= a.circ_off && i < a.head_off) {
       const int64_t r = i - a.circ_off;
@@ -663,52 +979,60 @@ __global__ void reduce_kernel(ReduceArgs a) {
       const int kk = (int)(r % a.k);
       const float* c = a.cmat + (lq * 3 + kk) * 4;
       double e0 = 0, e1 = 0, e2 = 0;
-      for (int b = 0; b < a.nblk; ++b) {
+      for (int b = lane; b < a.nblk; b += 32) {
         const float* g = a.blk_grad + (int64_t)b * a.grad_stride + lq * 3;
         e0 += g[0]; e1 += g[1]; e2 += g[2];
       }
+      e0 = warp_sum_dbl(e0); e1 = warp_sum_dbl(e1); e2 = warp_sum_dbl(e2);
       val = (float)(c[0] * e0 + c[1] * e1 + c[2] * e2);
     } else if (i >= a.head_off) {
       const int64_t hi = 3LL * a.n * a.L + (i - a.head_off);
-      double s = 0;
-      for (int b = 0; b < a.nblk; ++b) s += a.blk_grad[(int64_t)b * a.grad_stride + hi];
-      val = (float)s;
+      double t = 0;
+      for (int b = lane; b < a.nblk; b += 32) t += a.blk_grad[(int64_t)b * a.grad_stride + hi];
+      val = (float)warp_sum_dbl(t);
     } else if (i >= a.mlp_off && a.mlp_count > 0) {
       const int64_t wi = i - a.mlp_off;
-      double s = 0;
-      for (int b = 0; b < a.nwblk; ++b) s += a.wpart[(int64_t)b * a.nW + wi];
-      val = (float)s;
+      double t = 0;
+      for (int b = lane; b < a.nwblk; b += 32) t += a.wpart[(int64_t)b * a.nW + wi];
+      val = (float)warp_sum_dbl(t);
     }
-    a.grad[i] = val;
-  }
-  if (i == 0) {
-    double s[QP_NLP] = {0, 0, 0, 0, 0, 0, 0};
-    for (int b = 0; b < a.nblk; ++b)
+    if (lane == 0) a.grad[i] = val;
+  } else if (gw == a.nparams) {
+    double s[QP_NLP];
+#pragma unroll
+    for (int k = 0; k < QP_NLP; ++k) s[k] = 0.0;
+    for (int b = lane; b < a.nblk; b += 32)
+#pragma unroll
       for (int k = 0; k < QP_NLP; ++k) s[k] += a.blk_loss[(int64_t)b * a.loss_stride + k];
-    const double N = (double)a.nc;
-    const double nd = a.medium == 1 ? (a.norm_diel >= 0 ? (double)a.norm_diel : (double)a.counts[0]) : 0.0;
-    const double nv = N - nd;
-    double m1v = 0, m1d = 0;
-    if (a.medium == 1) {
-      if (nv > 0) m1v = s[0] / nv;
-      if (nd > 0) m1d = s[1] / nd;
-    } else if (N > 0) {
-      m1v = s[0] / N;
+#pragma unroll
+    for (int k = 0; k < QP_NLP; ++k) s[k] = warp_sum_dbl(s[k]);
+    if (lane == 0) {
+      const double N = (double)a.nc;
+      const double nd = a.medium == 1 ? (a.norm_diel >= 0 ? (double)a.norm_diel : (double)a.counts[0]) : 0.0;
+      const double nv = N - nd;
+      double m1v = 0, m1d = 0;
+      if (a.medium == 1) {
+        if (nv > 0) m1v = s[0] / nv;
+        if (nd > 0) m1d = s[1] / nd;
+      } else if (N > 0) {
+        m1v = s[0] / N;
+      }
+      const double m2 = N > 0 ? s[2] / N : 0, m3 = N > 0 ? s[3] / N : 0;
+      const double phys = m1v + m1d + m2 + m3;
+      const double en = N > 0 ? a.w_energy * s[4] / N : 0;
+      const double ic = a.ni > 0 ? a.w_ic * s[5] / (double)a.ni : 0;
+      const double bc = a.nb > 0 ? a.w_bc * s[6] / (double)a.nb : 0;
+      const double tot = phys + ic + bc + en;
+      a.loss[0] = tot; a.loss[1] = phys; a.loss[2] = ic; a.loss[3] = bc; a.loss[4] = en;
+      a.loss[5] = m1v; a.loss[6] = m1d; a.loss[7] = m2; a.loss[8] = m3;
+      if (!isfinite(tot)) atomicExch(a.status, (int)5);
     }
-    const double m2 = N > 0 ? s[2] / N : 0, m3 = N > 0 ? s[3] / N : 0;
-    const double phys = m1v + m1d + m2 + m3;
-    const double en = N > 0 ? a.w_energy * s[4] / N : 0;
-    const double ic = a.ni > 0 ? a.w_ic * s[5] / (double)a.ni : 0;
-    const double bc = a.nb > 0 ? a.w_bc * s[6] / (double)a.nb : 0;
-    const double tot = phys + ic + bc + en;
-    a.loss[0] = tot; a.loss[1] = phys; a.loss[2] = ic; a.loss[3] = bc; a.loss[4] = en;
-    a.loss[5] = m1v; a.loss[6] = m1d; a.loss[7] = m2; a.loss[8] = m3;
-    if (!isfinite(tot)) atomicExch(a.status, (int)5);
-  }
-  if (i < a.nt) {
+  } else if (gw <= a.nparams + a.nt) {
+    const int64_t i = gw - a.nparams - 1;
     double u = 0;
-    for (int b = 0; b < a.nblk; ++b) u += a.blk_loss[(int64_t)b * a.loss_stride + QP_NLP + i];
-    a.loss[QP_NLOSS_OUT + i] = u;
+    for (int b = lane; b < a.nblk; b += 32) u += a.blk_loss[(int64_t)b * a.loss_stride + QP_NLP + i];
+    u = warp_sum_dbl(u);
+    if (lane == 0) a.loss[QP_NLOSS_OUT + i] = u;
   }
 }
 
