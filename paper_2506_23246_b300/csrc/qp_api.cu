@@ -557,7 +557,7 @@ static qp_status dense_loss_grad(qp_plan* pl, const float* d_params, const float
   const bool mlp = pl->c.premap == QP_PREMAP_RFF_MLP;
   ba.WT = mlp ? (float*)(ws + w.dWT) : nullptr;
   const bool fused = fused_path(pl);
-  ba.W16 = fused ? (float*)(ws + w.dW16) : nullptr;
+  ba.W16 = fused ? (__half*)(ws + w.dW16) : nullptr;
   if (P > 0) {
     const int64_t tot = P * n;
     const int hb = (int)((tot + 255) / 256 < pl->sm_count * 4 ? (tot + 255) / 256 : pl->sm_count * 4);
@@ -571,7 +571,7 @@ static qp_status dense_loss_grad(qp_plan* pl, const float* d_params, const float
   if (fused) {
     // forward contraction with the pointwise stage as its epilogue (states stay on chip)
     qpd::FusedArgs fa;
-    fa.thetaJ = (const float*)(ws + w.thetaJ); fa.W16 = (const float*)(ws + w.dW16);
+    fa.thetaJ = (const float*)(ws + w.thetaJ); fa.W16 = (const __half*)(ws + w.dW16);
     fa.lam = (float*)(ws + w.dphi); fa.rtot = 4 * npts[0] + npts[1] + npts[2];
     fa.head = d_params + pl->head_off;
     fa.n = n; fa.m = pl->c.n_readout;

@@ -12,6 +12,7 @@
 // streamed by bulk copies; the product runs in 3xTF32 (hi*hi + hi*lo + lo*hi, FP32
 // accumulation in tensor memory).
 #pragma once
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include "qp_circuit.cuh"
@@ -31,10 +32,18 @@ __host__ __device__ inline uint32_t core_off(int r, int t) {
   return (uint32_t)((r >> 3) * (KC / 4) * 128 + (t >> 2) * 128 + (r & 7) * 16 + (t & 3) * 4);
 }
 
-constexpr int FKC = 16;       // K per pipeline stage of the fused forward kernel
+constexpr int FKC = 16;       // K per pipeline stage of the weight-gradient kernel (TF32)
+constexpr int HKC = 32;       // K per pipeline stage of the fused forward kernel (FP16 pairs)
+// Fixed power-of-two scale of the fused unitary's FP16 operand pair (|U'| <= 1).
+constexpr float W16_SCALE = 16384.f;
 // The same layout with 16-element K chunks (operand blocks of the fused forward kernel).
 __host__ __device__ inline uint32_t core_off16(int r, int t) {
   return (uint32_t)((r >> 3) * (FKC / 4) * 128 + (t >> 2) * 128 + (r & 7) * 16 + (t & 3) * 4);
+}
+// Byte offset of 16-bit element (row r, K index k) in a K-major HKC-wide block: core matrices
+// of 8 rows x 8 elements, K-adjacent ones 128 bytes apart, 8-row groups (HKC / 8) * 128 apart.
+__host__ __device__ inline uint32_t core_off_h(int r, int k) {
+  return (uint32_t)((r >> 3) * (HKC / 8) * 128 + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2);
 }
 
 // Blocked costate layout of the fused path (n = 7, 8): [2^(n+1) / 256][rows][256] floats, rows
@@ -63,7 +72,7 @@ struct BuildArgs {
   float* W;        // [ncc][nkc][2 (hi, lo)][nch x KC] tiled operand blocks
   double2* U;      // [2^n][2^n] fused unitary U' (row j, column k), FP64, or null
   float* WT;       // transpose operand (rows a = basis index, K = o), same tiling, or null
-  float* W16;      // [dim / 16][2 dim / 256][2 (hi, lo)][256 x 16] blocks for the fused kernel, or null
+  __half* W16;     // [dim / HKC][2 dim / 256][2 (hi, lo)][256 x HKC] FP16 pairs of W * W16_SCALE, or null
   double2* gates;  // [L][n][4] rotation gate matrices (written by block 0), or null
 };
 
@@ -175,10 +184,14 @@ __global__ void dense_build_kernel(BuildArgs a) {
         blk[nch * KC + core_off(r, t) / 4] = lo;
       }
       if (a.W16) {
+        // FP16 pair of the scaled element: x = hi + lo to about 2^-24 relative
         const int nc16 = (2 * dim) / 256, c = o / 256, r = o % 256;
-        float* blk = a.W16 + ((int64_t)((k / 16) * nc16 + c) * 2) * (256 * 16);
-        blk[core_off16(r, k % 16) / 4] = hi;
-        blk[256 * 16 + core_off16(r, k % 16) / 4] = lo;
+        const double xs = (c2 == 0 ? v.x : v.y) * (double)W16_SCALE;
+        const __half hh = __double2half(xs);
+        const __half hl = __double2half(xs - (double)__half2float(hh));
+        __half* blk = a.W16 + ((int64_t)((k / HKC) * nc16 + c) * 2) * (256 * HKC);
+        blk[core_off_h(r, k % HKC) / 2] = hh;
+        blk[256 * HKC + core_off_h(r, k % HKC) / 2] = hl;
       }
       if (a.WT) {
         // transpose: row a = k (N = dim, chunks of nch2), K = o (2 dim, chunks of KC)

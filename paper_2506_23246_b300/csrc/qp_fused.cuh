@@ -22,7 +22,7 @@ constexpr int F_MAXH = 5;       // embedding qubits above the 3 lowest index bit
 
 struct FusedArgs {
   const float* thetaJ;     // [P][n] float4 (theta, dtheta/dx, dtheta/dy, dtheta/dt)
-  const float* W16;        // [dim / FKC][nc][2 (hi, lo)][256 x FKC] operand blocks of W
+  const __half* W16;       // [dim / HKC][nc][2 (hi, lo)][256 x HKC] FP16 operand pairs of W * W16_SCALE
   float* lam;              // costates (output), blocked layout [2^(n+1) / 256][rtot][256]
   int64_t rtot;
   const float* head;       // W[3][m], b[3]
@@ -44,15 +44,15 @@ struct FusedArgs {
 // until that slot's next copy, issued after the epilogue) when it is large enough, else in a
 // region of their own; the costate store staging lives in the A stages.
 struct FusedSmem {
-  int a_bytes, w_bytes, wbase, epi, x0, tb, zp, zb, hw, sloss, hsum, bars, total;
+  int a_bytes, w_bytes, wbase, epi, x0, tb, zp, zb, hw, sloss, hsum, rsc, bars, total;
   bool epi_in_w;
 };
 constexpr int F_EPI_BYTES = 2 * 32 * 32 * 4 + 2 * 3 * 32 * 32 * 4 + 2 * TM * QP_MAXQ * 4 + TM * QP_MAXQ * 4;
 __host__ __device__ inline FusedSmem fused_smem(int n, int nt) {
   FusedSmem f;
   const int nc = (2 << n) / 256;
-  f.a_bytes = TM * FKC * 4;
-  f.w_bytes = nc * 2 * 256 * FKC * 4;
+  f.a_bytes = TM * HKC * 2;
+  f.w_bytes = nc * 2 * 256 * HKC * 2;
   f.wbase = 2 * 2 * f.a_bytes;
   int o = f.wbase + 3 * f.w_bytes;
   f.hw = o; o += (3 * QP_MAXQ + 3) * 4 + 4;       // head weights
@@ -61,6 +61,7 @@ __host__ __device__ inline FusedSmem fused_smem(int n, int nt) {
   o = (o + 15) / 16 * 16;
   f.hsum = o; o += (3 * QP_MAXQ + 3) * 4 + 4;
   o = (o + 15) / 16 * 16;
+  f.rsc = o; o += TM * 4;                         // per-row unscale factors of the tile
   f.bars = o; o += 128;                           // w_full[3], mma_done[2], tensor-memory slot
   f.epi_in_w = f.w_bytes >= F_EPI_BYTES;
   if (!f.epi_in_w) { f.epi = o; o += F_EPI_BYTES; }
@@ -121,8 +122,9 @@ __global__ void __launch_bounds__(F_THREADS, 1) dense_fused_fwd_kernel(FusedArgs
   __syncthreads();
   qptc::fence_after();
   const uint32_t tmem = *tslot;
-  const uint32_t id = qptc::idesc(2, TM, 256);
-  const int nkc = dim / FKC;
+  const uint32_t id = qptc::idesc(0, TM, 256);   // FP16 x FP16 -> FP32
+  const int nkc = dim / HKC;
+  float* rsc = reinterpret_cast<float*>(sm + L.rsc);
   const int arow = tid & (TM - 1), khalf = tid >> 7;
   const int r = ws * 32 + lane;                   // tile row read from tensor memory
   const int half_cols = dim;                      // 2 dim columns split between two halves
@@ -146,10 +148,10 @@ __global__ void __launch_bounds__(F_THREADS, 1) dense_fused_fwd_kernel(FusedArgs
   if (ctrl) {
     // ---- control thread: W two K-steps ahead, MMAs as soon as a stage's A is written
     if (lane == 0) {
-      const uint32_t wblk = 256 * FKC * 4;
+      const uint32_t wblk = 256 * HKC * 2;
       for (int j = 0; j < 2 && j < total; ++j) {
         qptc::mbar_arrive_expect_tx(&w_full[j], L.w_bytes);
-        qptc::bulk_g2s(sm + L.wbase + j * L.w_bytes, a.W16 + (int64_t)(j % nkc) * (L.w_bytes / 4), L.w_bytes,
+        qptc::bulk_g2s(sm + L.wbase + j * L.w_bytes, a.W16 + (int64_t)(j % nkc) * (L.w_bytes / 2), L.w_bytes,
                        &w_full[j]);
         last_copy = j;
       }
@@ -164,16 +166,16 @@ __global__ void __launch_bounds__(F_THREADS, 1) dense_fused_fwd_kernel(FusedArgs
           qptc::fence_after();
           const uint32_t sa = qptc::smem_u32(sm + st * 2 * L.a_bytes), sw = qptc::smem_u32(sm + L.wbase + wsl * L.w_bytes);
 #pragma unroll
-          for (int ks = 0; ks < FKC / 8; ++ks) {
-            const uint64_t ah = qptc::desc_kmajor(sa + ks * 256, 128, (FKC / 4) * 128);
-            const uint64_t al = qptc::desc_kmajor(sa + L.a_bytes + ks * 256, 128, (FKC / 4) * 128);
+          for (int ks = 0; ks < HKC / 16; ++ks) {
+            const uint64_t ah = qptc::desc_kmajor(sa + ks * 256, 128, (HKC / 8) * 128);
+            const uint64_t al = qptc::desc_kmajor(sa + L.a_bytes + ks * 256, 128, (HKC / 8) * 128);
             for (int c = 0; c < nc; ++c) {
-              const uint64_t wh = qptc::desc_kmajor(sw + c * 2 * wblk + ks * 256, 128, (FKC / 4) * 128);
-              const uint64_t wl = qptc::desc_kmajor(sw + c * 2 * wblk + wblk + ks * 256, 128, (FKC / 4) * 128);
+              const uint64_t wh = qptc::desc_kmajor(sw + c * 2 * wblk + ks * 256, 128, (HKC / 8) * 128);
+              const uint64_t wl = qptc::desc_kmajor(sw + c * 2 * wblk + wblk + ks * 256, 128, (HKC / 8) * 128);
               const uint32_t dt = tmem + c * 256;
-              qptc::mma_tf32(dt, ah, wh, id, (kc > 0 || ks > 0) ? 1u : 0u);
-              qptc::mma_tf32(dt, ah, wl, id, 1u);
-              qptc::mma_tf32(dt, al, wh, id, 1u);
+              qptc::mma_f16(dt, ah, wh, id, (kc > 0 || ks > 0) ? 1u : 0u);
+              qptc::mma_f16(dt, ah, wl, id, 1u);
+              qptc::mma_f16(dt, al, wh, id, 1u);
             }
           }
           qptc::commit(&mma_done[st]);
@@ -186,7 +188,7 @@ __global__ void __launch_bounds__(F_THREADS, 1) dense_fused_fwd_kernel(FusedArgs
             // copies into it are issued only after acc_free (above) for the first step of a tile
             qptc::fence_proxy_async();
             qptc::mbar_arrive_expect_tx(&w_full[js], L.w_bytes);
-            qptc::bulk_g2s(sm + L.wbase + js * L.w_bytes, a.W16 + (int64_t)((kc + 2) % nkc) * (L.w_bytes / 4),
+            qptc::bulk_g2s(sm + L.wbase + js * L.w_bytes, a.W16 + (int64_t)((kc + 2) % nkc) * (L.w_bytes / 2),
                            L.w_bytes, &w_full[js]);
             last_copy = j;
           }
@@ -214,6 +216,7 @@ __global__ void __launch_bounds__(F_THREADS, 1) dense_fused_fwd_kernel(FusedArgs
     const int64_t pac = pa < np ? pa : np - 1;
     const float4* tj = reinterpret_cast<const float4*>(a.thetaJ) + (base + pac) * n;
     float Lo[8], Lod[8];
+    float jsum = 0.f;   // sum over qubits of |J| along this row's direction
 #pragma unroll
     for (int t = 0; t < 8; ++t) { Lo[t] = 1.f; Lod[t] = 0.f; }
 #pragma unroll
@@ -222,6 +225,7 @@ __global__ void __launch_bounds__(F_THREADS, 1) dense_fused_fwd_kernel(FusedArgs
       float sn, cs;
       sincosf(0.5f * tq.x, &sn, &cs);
       const float J = s_a == 0 ? 0.f : (s_a == 1 ? tq.y : (s_a == 2 ? tq.z : tq.w));
+      jsum += fabsf(J);
 #pragma unroll
       for (int t = 0; t < 8; ++t) {
         const bool bit = (t >> b) & 1;
@@ -238,7 +242,20 @@ __global__ void __launch_bounds__(F_THREADS, 1) dense_fused_fwd_kernel(FusedArgs
         const float4 tq = __ldg(tj + q);
         sincosf(0.5f * tq.x, &hs[q], &hc[q]);
         hj[q] = s_a == 0 ? 0.f : (s_a == 1 ? tq.y : (s_a == 2 ? tq.z : tq.w));
+        jsum += fabsf(hj[q]);
       }
+    }
+    // FP16 operand scale of this row (a power of two): |R_0| <= 1 and |R_d| <= sum_q |J_q| / 2
+    // (each product-rule term carries one derivative factor of size at most |J| / 2), so the
+    // scaled row stays below 2^13; the epilogue takes the scales back out of the accumulators.
+    float rs;
+    {
+      const float bnd = s_a == 0 ? 1.f : 0.5f * jsum;
+      int eb = 0;
+      if (bnd > 0.f) frexpf(bnd, &eb);
+      const int e = bnd > 0.f ? max(-100, min(100, 13 - eb)) : 0;
+      rs = ldexpf(1.f, e);
+      if (khalf == 0) rsc[arow] = ldexpf(1.f, -e) * (1.f / W16_SCALE);
     }
     // ---- forward contraction: TMEM[row][2j + re/im] = sum_k R[row][k] W[2j + re/im][k]
     for (int kc = 0; kc < nkc; ++kc, ++it) {
@@ -246,34 +263,40 @@ __global__ void __launch_bounds__(F_THREADS, 1) dense_fused_fwd_kernel(FusedArgs
       unsigned char* sA = sm + st * 2 * L.a_bytes;
       if (it >= 2 && ok) ok = qptc::mbar_wait(&mma_done[st], ((it - 2) >> 1) & 1);
       if (ok) {
-        // basis indices k = kc * 16 + khalf * 8 + t: bits 0-2 from the tables, the rest from H
-        const int hbits = kc * 2 + khalf;
-        float H = 1.f, Hd = 0.f;
 #pragma unroll
-        for (int q = 0; q < F_MAXH; ++q) {
-          if (q < n - 3) {
-            const bool bit = (hbits >> (n - 4 - q)) & 1;
-            const float f = bit ? hs[q] : hc[q], d = bit ? 0.5f * hc[q] : -0.5f * hs[q];
-            Hd = Hd * f + H * d * hj[q];
-            H *= f;
+        for (int g = 0; g < 2; ++g) {
+          // basis indices k = kc * 32 + khalf * 16 + g * 8 + t: bits 0-2 from the tables, the
+          // rest from H
+          const int hbits = kc * 4 + khalf * 2 + g;
+          float H = 1.f, Hd = 0.f;
+#pragma unroll
+          for (int q = 0; q < F_MAXH; ++q) {
+            if (q < n - 3) {
+              const bool bit = (hbits >> (n - 4 - q)) & 1;
+              const float f = bit ? hs[q] : hc[q], d = bit ? 0.5f * hc[q] : -0.5f * hs[q];
+              Hd = Hd * f + H * d * hj[q];
+              H *= f;
+            }
           }
-        }
-        float* Ahi = reinterpret_cast<float*>(sA);
-        float* Alo = reinterpret_cast<float*>(sA + L.a_bytes);
-#pragma unroll
-        for (int g4 = 0; g4 < 2; ++g4) {
-          float4 h4, l4;
-          float* hv = &h4.x;
-          float* lv = &l4.x;
+          // FP16 pair of the scaled value: x = hi + lo (lo = the rounding remainder of hi)
+          uint32_t hw[4], lw[4];
 #pragma unroll
           for (int e = 0; e < 4; ++e) {
-            const int t = g4 * 4 + e;
-            const float v = s_a == 0 ? H * Lo[t] : Hd * Lo[t] + H * Lod[t];
-            qptc::split_tf32(v, hv[e], lv[e]);
+            float x[2];
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+              const int t = 2 * e + u;
+              x[u] = rs * (s_a == 0 ? H * Lo[t] : Hd * Lo[t] + H * Lod[t]);
+            }
+            const __half2 h2 = __floats2half2_rn(x[0], x[1]);
+            const float2 hf = __half22float2(h2);
+            const __half2 l2 = __floats2half2_rn(x[0] - hf.x, x[1] - hf.y);
+            hw[e] = *reinterpret_cast<const uint32_t*>(&h2);
+            lw[e] = *reinterpret_cast<const uint32_t*>(&l2);
           }
-          const uint32_t off = core_off16(arow, khalf * 8 + g4 * 4) / 4;
-          *reinterpret_cast<float4*>(Ahi + off) = h4;
-          *reinterpret_cast<float4*>(Alo + off) = l4;
+          const uint32_t off = core_off_h(arow, khalf * 16 + g * 8);
+          *reinterpret_cast<uint4*>(sA + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+          *reinterpret_cast<uint4*>(sA + L.a_bytes + off) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
         }
       }
       qptc::fence_proxy_async();
@@ -283,6 +306,7 @@ __global__ void __launch_bounds__(F_THREADS, 1) dense_fused_fwd_kernel(FusedArgs
     ok = qptc::bar_and(3, F_STAGERS, ok && qptc::mbar_wait(&mma_done[(it - 1) & 1], ((it - 1) >> 1) & 1));
     if (!ok) break;
     qptc::fence_after();
+    const float us = rsc[r];   // this thread's tensor-memory row: back to unscaled amplitudes
     // epilogue buffers: the W slot of the tile's last step (or their own region)
     unsigned char* epi = L.epi_in_w ? sm + L.wbase + ((it - 1) % 3) * L.w_bytes : sm + L.epi;
     float4* X0 = reinterpret_cast<float4*>(epi + L.x0) + hh * 256;
@@ -297,6 +321,8 @@ __global__ void __launch_bounds__(F_THREADS, 1) dense_fused_fwd_kernel(FusedArgs
       const int col = hh * half_cols + cc;
       float v[32];
       qptc::tmem_ld32(tmem + ((uint32_t)(ws * 32) << 16) + col, v);
+      #pragma unroll
+      for (int e = 0; e < 32; ++e) v[e] *= us;
       float y[16];
       if (nv4) {
         if (ws == 0) {
@@ -449,6 +475,8 @@ __global__ void __launch_bounds__(F_THREADS, 1) dense_fused_fwd_kernel(FusedArgs
         for (int e = 0; e < 16; ++e) O[e] = Bs + t01[e & 3] + t23[e >> 2];
         float v[32];
         qptc::tmem_ld32(tmem + ((uint32_t)(ws * 32) << 16) + col, v);
+        #pragma unroll
+        for (int e = 0; e < 32; ++e) v[e] *= us;
         float4 outv[8];
         if (nv4) {
           if (ws == 0) {

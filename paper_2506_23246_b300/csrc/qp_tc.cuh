@@ -52,7 +52,7 @@ __device__ __forceinline__ uint64_t desc_kmajor(uint32_t saddr, uint32_t kstride
 }
 
 // Instruction descriptor: FP32 accumulate, both operands K-major, shape M x N.
-// fmt = 2 for TF32 operands (kind::tf32), 1 for BF16 operands (kind::f16).
+// fmt = 2 for TF32 operands (kind::tf32); 0 for FP16, 1 for BF16 operands (kind::f16).
 __host__ __device__ constexpr uint32_t idesc(int fmt, int M, int N) {
   return (1u << 4) | ((uint32_t)fmt << 7) | ((uint32_t)fmt << 10) | ((uint32_t)(N >> 3) << 17) |
          ((uint32_t)(M >> 4) << 24);
@@ -65,8 +65,9 @@ __device__ __forceinline__ void mma_tf32(uint32_t tmem_d, uint64_t da, uint64_t 
       "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
       "l"(da), "l"(db), "r"(id), "r"(accumulate));
 }
-__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t da, uint64_t db, uint32_t id,
-                                         uint32_t accumulate) {
+// kind::f16: FP16 or BF16 operands (both the same type, set in the instruction descriptor).
+__device__ __forceinline__ void mma_f16(uint32_t tmem_d, uint64_t da, uint64_t db, uint32_t id,
+                                        uint32_t accumulate) {
   asm volatile(
       "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
       "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
