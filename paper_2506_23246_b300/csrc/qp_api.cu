@@ -336,8 +336,10 @@ qp_status qp_plan_create(const qp_circuit* circuit, const qp_problem* problem, i
                              qpd::gemm_smem_bytes(n, 0)) != cudaSuccess ||
         raise_smem_limit((void*)qpd::dense_row_gemm_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              qpd::gemm_smem_bytes(n, 1)) != cudaSuccess ||
-        raise_smem_limit((void*)qpd::dense_wgrad_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        raise_smem_limit((void*)qpd::dense_wgrad_gemm_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              qpd::wg_smem_bytes(n)) != cudaSuccess ||
+        raise_smem_limit((void*)qpd::dense_wgrad_gemm_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             qpd::wg_smem_bytes(n, true)) != cudaSuccess ||
         raise_smem_limit((void*)qpd::dense_sweep_left_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (1 << n) * 16 * 8) != cudaSuccess ||
         raise_smem_limit((void*)qpd::dense_sweep_right_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -587,6 +589,7 @@ static qp_status dense_loss_grad(qp_plan* pl, const float* d_params, const float
     fa.nE = 3 * n * L;
     fa.nblk = pl->blocks_grad;
     fa.status = (int32_t*)(ws + w.status);
+    fa.scal = (int32_t*)(ws + w.status) + 16;
     const int64_t ftiles = fa.tile_end[2];
     const int fblocks = (int)(ftiles < pl->sm_count ? (ftiles > 0 ? ftiles : 1) : pl->sm_count);
     if (pl->prof_start) cudaEventRecord(pl->prof_start, s);
@@ -637,7 +640,11 @@ static qp_status dense_loss_grad(qp_plan* pl, const float* d_params, const float
   wa.tiles = wgm.tiles; wa.ngroups = wgm.ngroups; wa.spc = wgm.spc; wa.fl = wgm.fl;
   wa.status = (int32_t*)(ws + w.status);
   if (pl->prof_start && !fused) cudaEventRecord(pl->prof_start, s);
-  qpd::dense_wgrad_gemm_kernel<<<wgm.tiles * wgm.ngroups, qpd::WG_THREADS, qpd::wg_smem_bytes(n), s>>>(wa);
+  wa.scal = (const int32_t*)(ws + w.status) + 16;
+  if (fused)   // the fused forward recorded both operand ranges: FP16 pairs
+    qpd::dense_wgrad_gemm_kernel<true><<<wgm.tiles * wgm.ngroups, qpd::WG_THREADS, qpd::wg_smem_bytes(n, true), s>>>(wa);
+  else
+    qpd::dense_wgrad_gemm_kernel<false><<<wgm.tiles * wgm.ngroups, qpd::WG_THREADS, qpd::wg_smem_bytes(n), s>>>(wa);
   if (pl->prof_stop && !fused) cudaEventRecord(pl->prof_stop, s);
   launches += 1;
   qpd::SweepArgs sa;

@@ -55,7 +55,8 @@ __device__ inline void pauli_coords(const M2& V, int G, float* out) {
 // One thread per (layer, qubit): forward gate matrix and gradient coordinates.
 __global__ void prep_kernel(PrepArgs a) {
   const int t = threadIdx.x + blockIdx.x * blockDim.x;
-  if (t == 0) { a.counts[0] = 0; a.status[0] = 0; }
+  // status word, dielectric count and the two operand-range maxima of the FP16 contractions
+  if (t == 0) { a.counts[0] = 0; a.status[0] = 0; a.status[16] = 0; a.status[17] = 0; }
   if (t >= a.L * a.n) return;
   const int l = t / a.n, q = t % a.n;
   const int k = a.ansatz == 0 ? 2 : 3;

@@ -36,6 +36,7 @@ struct FusedArgs {
   float* blk_grad;
   int32_t loss_stride, grad_stride, nE, nblk;
   int32_t* status;
+  int32_t* scal;           // [2] float bits (atomic max): row bound of the product states, max |lambda|
 };
 
 // Shared memory: two A stages (TF32 hi, lo), a three-slot ring of W blocks (copies run two
@@ -85,6 +86,11 @@ __device__ __forceinline__ void stagers_bar() {
 __device__ __forceinline__ double warp_sum_d(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ float warp_max_f(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
   return v;
 }
 __device__ __forceinline__ float warp_sum_f(float v) {
@@ -256,6 +262,9 @@ __global__ void __launch_bounds__(F_THREADS, 1) dense_fused_fwd_kernel(FusedArgs
       const int e = bnd > 0.f ? max(-100, min(100, 13 - eb)) : 0;
       rs = ldexpf(1.f, e);
       if (khalf == 0) rsc[arow] = ldexpf(1.f, -e) * (1.f / W16_SCALE);
+      // the weight-gradient contraction scales all product-state rows by one bound
+      const float wb = warp_max_f(bnd);
+      if (lane == 0) atomicMax(a.scal, __float_as_int(wb));
     }
     // ---- forward contraction: TMEM[row][2j + re/im] = sum_k R[row][k] W[2j + re/im][k]
     for (int kc = 0; kc < nkc; ++kc, ++it) {
@@ -461,6 +470,7 @@ __global__ void __launch_bounds__(F_THREADS, 1) dense_fused_fwd_kernel(FusedArgs
       const int s_r = nv4 ? ws : 0;
       (void)s_r;
       const int64_t grow0 = lam_row(set, p0, 0, a.npts[0], base);   // first costate row of the tile
+      float lmax = 0.f;   // largest costate magnitude of this thread (FP16 scale of the next contractions)
       for (int cc = 0; cc < half_cols; cc += 32) {
         const int col = hh * half_cols + cc;
         const int j0 = col >> 1;
@@ -515,6 +525,9 @@ __global__ void __launch_bounds__(F_THREADS, 1) dense_fused_fwd_kernel(FusedArgs
             outv[e] = make_float4(O[2 * e] * v[4 * e], O[2 * e] * v[4 * e + 1], O[2 * e + 1] * v[4 * e + 2],
                                   O[2 * e + 1] * v[4 * e + 3]);
         }
+#pragma unroll
+        for (int e = 0; e < 8; ++e)
+          lmax = fmaxf(lmax, fmaxf(fmaxf(fabsf(outv[e].x), fabsf(outv[e].y)), fmaxf(fabsf(outv[e].z), fabsf(outv[e].w))));
         // the column group's 128 rows are consecutive costate rows: stage the chunk in that
         // order (operand stage 0 is idle during the epilogue) and store 128-byte row segments,
         // four rows per warp instruction instead of one 16-byte piece of 32 rows
@@ -537,6 +550,8 @@ __global__ void __launch_bounds__(F_THREADS, 1) dense_fused_fwd_kernel(FusedArgs
           }
         }
       }
+      const float wl = warp_max_f(lmax);
+      if (lane == 0) atomicMax(a.scal + 1, __float_as_int(wl));
     }
     // tensor memory and the W slot of this tile's last step are free again
     qptc::fence_before();

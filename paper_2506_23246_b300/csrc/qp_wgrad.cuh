@@ -50,7 +50,36 @@ struct WgArgs {
   int64_t kc_end[3];          // cumulative 16-row step counts per set
   int32_t tiles, ngroups, spc, fl;  // tiles, CTAs per tile, flushes per CTA, steps per flush
   int32_t* status;
+  const int32_t* scal;        // FP16 operands: [2] float bits, bound of |R|, max |lambda|
 };
+
+// Byte offset of 16-bit element (row r, K index k) in a K-major WKC-wide block (core matrices
+// of 8 rows x 8 elements, K-adjacent ones 128 bytes apart, 8-row groups 256 bytes apart).
+__host__ __device__ inline uint32_t core_off_w16(int r, int k) {
+  return (uint32_t)((r >> 3) * (WKC / 8) * 128 + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2);
+}
+// Power-of-two scale that puts magnitudes up to `mx` below 2^13 (1 when mx is not positive).
+__device__ __forceinline__ float pow2_scale(float mx) {
+  if (!(mx > 0.f)) return 1.f;
+  int e = 0;
+  frexpf(mx, &e);
+  return ldexpf(1.f, max(-100, min(100, 13 - e)));
+}
+// Eight scaled values as FP16 pairs (hi, lo = rounding remainder), packed for one 16-byte store.
+__device__ __forceinline__ void pack_h8(const float* v, float sc, uint4& hi, uint4& lo) {
+  uint32_t h[4], l[4];
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    const float x0 = sc * v[2 * e], x1 = sc * v[2 * e + 1];
+    const __half2 h2 = __floats2half2_rn(x0, x1);
+    const float2 hf = __half22float2(h2);
+    const __half2 l2 = __floats2half2_rn(x0 - hf.x, x1 - hf.y);
+    h[e] = *reinterpret_cast<const uint32_t*>(&h2);
+    l[e] = *reinterpret_cast<const uint32_t*>(&l2);
+  }
+  hi = make_uint4(h[0], h[1], h[2], h[3]);
+  lo = make_uint4(l[0], l[1], l[2], l[3]);
+}
 
 struct WgSmem {
   int a_bytes, b_bytes, stage, raw, fac, tab, bars, total;
@@ -58,10 +87,11 @@ struct WgSmem {
 constexpr int WG_TAB4 = 16 * 32 + 16 * 8;                 // Lo [16 pts][32], H [16 pts][8] float4
 constexpr int WG_FAC4 = 16 * QP_MAXQ * 2;                 // [16 pts][q][2] float4
 __host__ __device__ inline int wg_mtc(int n) { return (1 << n) < 256 ? (1 << n) : 256; }
-__host__ __device__ inline WgSmem wg_smem(int n) {
+// esz: operand element size, 4 (TF32 pairs) or 2 (FP16 pairs)
+__host__ __device__ inline WgSmem wg_smem(int n, int esz = 4) {
   WgSmem w;
-  w.a_bytes = (wg_mtc(n) / TM) * 2 * TM * WKC * 4;   // hi, lo per M sub-tile
-  w.b_bytes = 2 * 256 * WKC * 4;                     // hi, lo
+  w.a_bytes = (wg_mtc(n) / TM) * 2 * TM * WKC * esz;   // hi, lo per M sub-tile
+  w.b_bytes = 2 * 256 * WKC * esz;                     // hi, lo
   w.stage = w.a_bytes + w.b_bytes;
   int o = 2 * w.stage;
   w.raw = o; o += WG_RING * WKC * 256 * 4;           // costate columns of a step [16][256]
@@ -71,7 +101,7 @@ __host__ __device__ inline WgSmem wg_smem(int n) {
   w.total = o;
   return w;
 }
-__host__ inline int wg_smem_bytes(int n) { return wg_smem(n).total; }
+__host__ inline int wg_smem_bytes(int n, bool h16 = false) { return wg_smem(n, h16 ? 2 : 4).total; }
 
 __device__ __forceinline__ void wg_step_geom(const WgArgs& a, int64_t kc, int& set, int64_t& p0, int& ppc,
                                              int& nvalid) {
@@ -170,10 +200,19 @@ __device__ __forceinline__ void wg_copy_rows(const WgArgs& a, int64_t kc, int nt
   }
 }
 
+// H16: FP16 operand pairs (kind::f16, one K = 16 MMA per term) with one power-of-two scale
+// per operand from the recorded ranges; else TF32 pairs (two K = 8 MMAs per term).
+template <bool H16>
 __global__ void __launch_bounds__(WG_THREADS, 1) dense_wgrad_gemm_kernel(WgArgs a) {
   extern __shared__ __align__(1024) unsigned char sm[];
   const int n = a.n, dim = 1 << n;
-  const WgSmem L = wg_smem(n);
+  const WgSmem L = wg_smem(n, H16 ? 2 : 4);
+  float sR = 1.f, sL = 1.f;
+  if (H16) {
+    sR = pow2_scale(__int_as_float(__ldg(a.scal)));
+    sL = pow2_scale(__int_as_float(__ldg(a.scal + 1)));
+  }
+  const float unsc = 1.f / (sR * sL);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const bool ctrl = warp == WG_STAGERS / 32;
   const int MTC = wg_mtc(n), msub = MTC / TM, nj = MTC / 32;
@@ -244,7 +283,7 @@ __global__ void __launch_bounds__(WG_THREADS, 1) dense_wgrad_gemm_kernel(WgArgs 
   if (ctrl) {
     // ---- control thread: bulk copies three steps ahead, MMAs when a stage is full
     if (lane == 0) {
-      const uint32_t id = qptc::idesc(2, TM, 256);
+      const uint32_t id = qptc::idesc(H16 ? 0 : 2, TM, 256);
       int slot = 0;
       bool fresh = true;
       uint32_t it = 0;
@@ -265,9 +304,22 @@ __global__ void __launch_bounds__(WG_THREADS, 1) dense_wgrad_gemm_kernel(WgArgs 
         qptc::fence_after();
         unsigned char* sA = sm + st * L.stage;
         const uint32_t sa = qptc::smem_u32(sA), sb = qptc::smem_u32(sA + L.a_bytes);
+        if (H16) {
+          const uint32_t ablk = TM * WKC * 2, bblk = 256 * WKC * 2;
+          const uint64_t bh = qptc::desc_kmajor(sb, 128, (WKC / 8) * 128);
+          const uint64_t bl = qptc::desc_kmajor(sb + bblk, 128, (WKC / 8) * 128);
+          for (int u = 0; u < msub; ++u) {
+            const uint64_t ah = qptc::desc_kmajor(sa + u * 2 * ablk, 128, (WKC / 8) * 128);
+            const uint64_t al = qptc::desc_kmajor(sa + u * 2 * ablk + ablk, 128, (WKC / 8) * 128);
+            const uint32_t dt = tmem + u * 256;
+            qptc::mma_f16(dt, ah, bh, id, fresh ? 0u : 1u);
+            qptc::mma_f16(dt, ah, bl, id, 1u);
+            qptc::mma_f16(dt, al, bh, id, 1u);
+          }
+        }
         const uint32_t ablk = TM * WKC * 4, bblk = 256 * WKC * 4;
 #pragma unroll
-        for (int ks = 0; ks < WKC / 8; ++ks) {
+        for (int ks = 0; ks < (H16 ? 0 : WKC / 8); ++ks) {
           const uint64_t bh = qptc::desc_kmajor(sb + ks * 256, 128, (WKC / 4) * 128);
           const uint64_t bl = qptc::desc_kmajor(sb + bblk + ks * 256, 128, (WKC / 4) * 128);
           for (int u = 0; u < msub; ++u) {
@@ -312,7 +364,7 @@ __global__ void __launch_bounds__(WG_THREADS, 1) dense_wgrad_gemm_kernel(WgArgs 
           float4* o4 = reinterpret_cast<float4*>(outp + c);
 #pragma unroll
           for (int e = 0; e < 8; ++e) {
-            const float4 r = make_float4(v[4 * e], v[4 * e + 1], v[4 * e + 2], v[4 * e + 3]);
+            const float4 r = make_float4(unsc * v[4 * e], unsc * v[4 * e + 1], unsc * v[4 * e + 2], unsc * v[4 * e + 3]);
             if (add) red_add_f4(o4 + e, r);   // no return value: the flush does not wait on L2
             else o4[e] = r;
           }
@@ -360,10 +412,18 @@ __global__ void __launch_bounds__(WG_THREADS, 1) dense_wgrad_gemm_kernel(WgArgs 
                   av[pi] = thi[pl * 8 + j].x * tlo[pl * 32 + e].x;
                 }
               }
+              if (H16) {
+                uint4 h8, l8;
+                pack_h8(av, sR, h8, l8);
+                unsigned char* Ab = sA + u * 2 * (TM * WKC * 2);
+                const uint32_t off = core_off_w16(kk, khalf * 8);
+                *reinterpret_cast<uint4*>(Ab + off) = h8;
+                *reinterpret_cast<uint4*>(Ab + TM * WKC * 2 + off) = l8;
+              }
               float* Ahi = reinterpret_cast<float*>(sA + u * 2 * (TM * WKC * 4));
               float* Alo = Ahi + TM * WKC;
 #pragma unroll
-              for (int g4 = 0; g4 < 2; ++g4) {
+              for (int g4 = 0; g4 < (H16 ? 0 : 2); ++g4) {
                 float4 h4, l4;
                 qptc::split_tf32_fast(av[4 * g4], h4.x, l4.x);
                 qptc::split_tf32_fast(av[4 * g4 + 1], h4.y, l4.y);
@@ -401,10 +461,20 @@ __global__ void __launch_bounds__(WG_THREADS, 1) dense_wgrad_gemm_kernel(WgArgs 
         for (int t = 0; t < WKC; ++t) lv[t] = (good && t < nvalid) ? rr[t * 256 + bo] : 0.f;
         __syncwarp();
         if (lane == 0) qptc::mbar_arrive(&raw_free[rs]);
+        if (H16) {
+#pragma unroll
+          for (int g8 = 0; g8 < WKC / 8; ++g8) {
+            uint4 h8, l8;
+            pack_h8(lv + 8 * g8, sL, h8, l8);
+            const uint32_t off = core_off_w16(bo, g8 * 8);
+            *reinterpret_cast<uint4*>(sB + off) = h8;
+            *reinterpret_cast<uint4*>(sB + 256 * WKC * 2 + off) = l8;
+          }
+        }
         float* Bhi = reinterpret_cast<float*>(sB);
         float* Blo = Bhi + 256 * WKC;
 #pragma unroll
-        for (int g4 = 0; g4 < WKC / 4; ++g4) {
+        for (int g4 = 0; g4 < (H16 ? 0 : WKC / 4); ++g4) {
           float4 h4, l4;
           qptc::split_tf32_fast(lv[4 * g4], h4.x, l4.x);
           qptc::split_tf32_fast(lv[4 * g4 + 1], h4.y, l4.y);
