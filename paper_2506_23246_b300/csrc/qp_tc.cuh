@@ -134,7 +134,10 @@ __device__ __forceinline__ bool bar_and(int id, int count, bool v) {
   return r != 0;
 }
 // Bounded wait for completion of the phase with parity `parity`; false if the limit ran out.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint32_t limit = 1u << 22) {
+#ifndef QP_MBAR_LIMIT
+#define QP_MBAR_LIMIT (1u << 22)   // polls before a wait gives up and reports a status error
+#endif
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint32_t limit = QP_MBAR_LIMIT) {
   uint32_t done = 0;
   for (uint32_t it = 0; it < limit; ++it) {
     asm volatile(
