@@ -308,15 +308,15 @@ def run_native(a):
     else:
         # fused forward contraction Phi = R W^T on the tensor cores (the step's largest kernel),
         # readout, losses and costates in its epilogue: algorithmic 2 M N K with M = (point,
-        # vector) rows, N = 2^(n+1), K = 2^n; 3xTF32 runs three TF32 products per term, so its
-        # ceiling is the TF32 peak / 3
+        # vector) rows, N = 2^(n+1), K = 2^n. The operands are FP16 pairs (hi + lo) with three
+        # FP16 products per term, so its ceiling is the dense FP16 (= BF16) peak / 3
         dim = 1 << 8
         flops = 2.0 * (4 * ncol + nic) * (2 * dim) * dim
         bf16 = peaks.get("bf16_tflops", 1800.0)
-        peak = bf16 * 0.5 / 3.0
-        roof = {"bound": "tensor", "kernel": "dense_fused_fwd_kernel (3xTF32)",
-                "peak_basis": "measured bf16 %.0f TFLOP/s x 0.5 (nominal TF32/BF16 dense ratio) / 3 "
-                              "(three TF32 products per 3xTF32 term)" % bf16,
+        peak = bf16 / 3.0
+        roof = {"bound": "tensor", "kernel": "dense_fused_fwd_kernel (FP16 pairs)",
+                "peak_basis": "measured bf16 %.0f TFLOP/s (dense FP16 runs at the BF16 rate) / 3 "
+                              "(three FP16 products per FP16-pair term)" % bf16,
                 "traffic": profiled_traffic("dense_fused_fwd_c3_8q6l.md", "qp_fused.cuh")}
     achieved = flops / (kms / 1000.0) / 1e12
 
