@@ -558,6 +558,10 @@ static qp_status dense_loss_grad(qp_plan* pl, const float* d_params, const float
   ba.ansatz = pl->c.ansatz; ba.enc = pl->c.enc; ba.W = (float*)(ws + w.dW); ba.U = (double2*)(ws + w.dU);
   const bool mlp = pl->c.premap == QP_PREMAP_RFF_MLP;
   ba.WT = mlp ? (float*)(ws + w.dWT) : nullptr;
+  if (mlp && fused_path(pl)) {
+    ba.WT16 = (__half*)(ws + w.dWT);   // the mu kernel takes FP16 pairs
+    ba.WT = nullptr;
+  }
   const bool fused = fused_path(pl);
   ba.W16 = fused ? (__half*)(ws + w.dW16) : nullptr;
   if (P > 0) {
@@ -700,7 +704,8 @@ static qp_status dense_loss_grad(qp_plan* pl, const float* d_params, const float
     if (fused) {
       // mu rows on the tensor cores with the embedding gradients as the epilogue
       qpd::MuArgs ma;
-      ma.thetaJ = (const float*)(ws + w.thetaJ); ma.WT = (const float*)(ws + w.dWT);
+      ma.thetaJ = (const float*)(ws + w.thetaJ); ma.WT16 = (const __half*)(ws + w.dWT);
+      ma.scal = (const int32_t*)(ws + w.status) + 16;
       ma.lam = (const float*)(ws + w.dphi); ma.rtot = 4 * npts[0] + npts[1] + npts[2];
       ma.dthetaJ = (float*)(ws + w.dthetaJ); ma.n = n;
       base = 0;

@@ -46,6 +46,29 @@ __host__ __device__ inline uint32_t core_off_h(int r, int k) {
   return (uint32_t)((r >> 3) * (HKC / 8) * 128 + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2);
 }
 
+// Power-of-two scale that puts magnitudes up to `mx` below 2^13 (1 when mx is not positive).
+__device__ __forceinline__ float pow2_scale(float mx) {
+  if (!(mx > 0.f)) return 1.f;
+  int e = 0;
+  frexpf(mx, &e);
+  return ldexpf(1.f, max(-100, min(100, 13 - e)));
+}
+// Eight scaled values as FP16 pairs (hi, lo = rounding remainder), packed for one 16-byte store.
+__device__ __forceinline__ void pack_h8(const float* v, float sc, uint4& hi, uint4& lo) {
+  uint32_t h[4], l[4];
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    const float x0 = sc * v[2 * e], x1 = sc * v[2 * e + 1];
+    const __half2 h2 = __floats2half2_rn(x0, x1);
+    const float2 hf = __half22float2(h2);
+    const __half2 l2 = __floats2half2_rn(x0 - hf.x, x1 - hf.y);
+    h[e] = *reinterpret_cast<const uint32_t*>(&h2);
+    l[e] = *reinterpret_cast<const uint32_t*>(&l2);
+  }
+  hi = make_uint4(h[0], h[1], h[2], h[3]);
+  lo = make_uint4(l[0], l[1], l[2], l[3]);
+}
+
 // Blocked costate layout of the fused path (n = 7, 8): [2^(n+1) / 256][rows][256] floats, rows
 // = 4 per collocation point (vector-major inside the point), then the IC and BC points with
 // one row each. A 16-row step of the weight-gradient contraction is one contiguous 16 KiB run
@@ -74,6 +97,7 @@ struct BuildArgs {
   float* WT;       // transpose operand (rows a = basis index, K = o), same tiling, or null
   __half* W16;     // [dim / HKC][2 dim / 256][2 (hi, lo)][256 x HKC] FP16 pairs of W * W16_SCALE, or null
   double2* gates;  // [L][n][4] rotation gate matrices (written by block 0), or null
+  __half* WT16;    // [2 dim / HKC][hi, lo][dim x HKC] FP16 pairs of 2^14 U' transposed (mu kernel), or null
 };
 
 __device__ inline double2 zmul(double2 a, double2 b) {
@@ -192,6 +216,15 @@ __global__ void dense_build_kernel(BuildArgs a) {
         __half* blk = a.W16 + ((int64_t)((k / HKC) * nc16 + c) * 2) * (256 * HKC);
         blk[core_off_h(r, k % HKC) / 2] = hh;
         blk[256 * HKC + core_off_h(r, k % HKC) / 2] = hl;
+      }
+      if (a.WT16) {
+        // transposed FP16 pairs: row a = k (N = dim <= 256), K = o in HKC-wide steps
+        const double xs = (c2 == 0 ? v.x : v.y) * (double)W16_SCALE;
+        const __half hh = __double2half(xs);
+        const __half hl = __double2half(xs - (double)__half2float(hh));
+        __half* blk = a.WT16 + (int64_t)(o / HKC) * 2 * (dim * HKC);
+        blk[core_off_h(k, o % HKC) / 2] = hh;
+        blk[dim * HKC + core_off_h(k, o % HKC) / 2] = hl;
       }
       if (a.WT) {
         // transpose: row a = k (N = dim, chunks of nch2), K = o (2 dim, chunks of KC)

@@ -19,13 +19,14 @@ namespace qpd {
 // next tile, under its tensor-core work.
 struct MuArgs {
   const float* thetaJ;     // [P][n] float4
-  const float* WT;         // transposed operand blocks (rows a = basis index, K = 2 dim)
+  const __half* WT16;      // FP16 pairs of 2^14 U' transposed, [2 dim / HKC][hi, lo][dim x HKC]
   const float* lam;        // costate rows, blocked layout [2 dim / 256][rtot][256]
   int64_t rtot;
   float* dthetaJ;          // [P][n] float4 (dL/dtheta, dL/dJ_x, dL/dJ_y, dL/dJ_t)
   int32_t n;
   int64_t npts[3], pt_base[3], tile_end[3];
   int32_t* status;
+  const int32_t* scal;     // [2] float bits; [1] = max |lambda| (scale of the costate operand)
 };
 
 // float4 offset of K-chunk kc (KC costate components) from the start of a row's first block.
@@ -33,7 +34,11 @@ __device__ __forceinline__ int64_t mu_koff(const MuArgs& a, int kc) {
   return ((int64_t)(kc / (256 / KC)) * a.rtot * 256 + (kc % (256 / KC)) * KC) / 4;
 }
 
-__host__ __device__ inline int mu_smem_bytes(int n) { return gemm_smem_bytes(n, 1) + 2 * 4 * 32 * 8 * 4; }
+// Two stages of (A: costate rows, W: transposed operand), FP16 pairs, HKC-wide K steps, then
+// the epilogue's exchange buffer.
+__host__ __device__ inline int mu_smem_bytes(int n) {
+  return 2 * (2 * TM * HKC * 2 + 2 * (1 << n) * HKC * 2) + 256 + 2 * 4 * 32 * 8 * 4;
+}
 
 // Per-row state of a tile being drained.
 struct MuRow {
@@ -89,9 +94,11 @@ __device__ __forceinline__ void mu_high(const MuRow& R, int n, int c, float& H, 
 }
 
 // One 32-column chunk c of the row's mu (tensor memory) into C and D.
-__device__ __forceinline__ void mu_chunk(MuRow& R, int n, int s, int c, uint32_t taddr) {
+__device__ __forceinline__ void mu_chunk(MuRow& R, int n, int s, int c, uint32_t taddr, float us) {
   float v[32];
   qptc::tmem_ld32(taddr, v);
+#pragma unroll
+  for (int l = 0; l < 32; ++l) v[l] *= us;
   float X = 0.f, Y = 0.f, A[5], B[5];
 #pragma unroll
   for (int b = 0; b < 5; ++b) { A[b] = 0.f; B[b] = 0.f; }
@@ -149,10 +156,14 @@ constexpr int MU_THREADS = MU_STAGERS + 32;
 __global__ void __launch_bounds__(MU_THREADS, 1) dense_mu_embed_kernel(MuArgs a) {
   extern __shared__ __align__(1024) unsigned char sm[];
   const int n = a.n, dim = 1 << n;
-  const int ktot = 2 * dim, nch = dim, nkc = ktot / KC;   // dim <= 256: one column chunk
+  const int ktot = 2 * dim, nch = dim, nkc = ktot / HKC;   // dim <= 256: one column chunk
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const bool ctrl = warp == MU_STAGERS / 32;
-  const int abytes = TM * KC * 4, wbytes = nch * KC * 4;
+  const int abytes = TM * HKC * 2, wbytes = nch * HKC * 2;
+  // FP16 pairs: the costates scaled by one power of two from the recorded maximum, the
+  // operand blocks by 2^14; both come back out in the drain
+  const float sL = pow2_scale(__int_as_float(__ldg(a.scal + 1)));
+  const float us = 1.f / (sL * W16_SCALE);
   const int stage_bytes = 2 * abytes + 2 * wbytes;
   uint64_t* bars = reinterpret_cast<uint64_t*>(sm + 2 * stage_bytes);
   uint64_t* w_full = bars;         // [2] W operand of a stage landed
@@ -177,14 +188,14 @@ __global__ void __launch_bounds__(MU_THREADS, 1) dense_mu_embed_kernel(MuArgs a)
   if (ctrl) {
     // ---- control thread: W copies one step ahead, MMAs as soon as a stage's A is written
     if (lane == 0) {
-      const uint32_t id = qptc::idesc(2, TM, nch);
+      const uint32_t id = qptc::idesc(0, TM, nch);
       const int64_t ntl = (int64_t)blockIdx.x < T2 ? (T2 - 1 - blockIdx.x) / gridDim.x + 1 : 0;
       const int64_t total = ntl * nkc;
       int64_t last_copy = -1, last_commit = -1;
       uint32_t it = 0;
       if (total > 0) {
         qptc::mbar_arrive_expect_tx(&w_full[0], 2 * wbytes);
-        qptc::bulk_g2s(sm + 2 * abytes, a.WT, 2 * wbytes, &w_full[0]);
+        qptc::bulk_g2s(sm + 2 * abytes, a.WT16, 2 * wbytes, &w_full[0]);
         last_copy = 0;
       }
       for (int64_t t = 0; t < ntl && ok; ++t) {
@@ -200,14 +211,14 @@ __global__ void __launch_bounds__(MU_THREADS, 1) dense_mu_embed_kernel(MuArgs a)
           const uint32_t sa = qptc::smem_u32(sm + st * stage_bytes), sw = sa + 2 * abytes;
           const uint32_t dt = tmem + buf * (tcols / 2);
 #pragma unroll
-          for (int ks = 0; ks < KC / 8; ++ks) {
-            const uint64_t ah = qptc::desc_kmajor(sa + ks * 256, 128, (KC / 4) * 128);
-            const uint64_t al = qptc::desc_kmajor(sa + abytes + ks * 256, 128, (KC / 4) * 128);
-            const uint64_t wh = qptc::desc_kmajor(sw + ks * 256, 128, (KC / 4) * 128);
-            const uint64_t wl = qptc::desc_kmajor(sw + wbytes + ks * 256, 128, (KC / 4) * 128);
-            qptc::mma_tf32(dt, ah, wh, id, (kc > 0 || ks > 0) ? 1u : 0u);
-            qptc::mma_tf32(dt, ah, wl, id, 1u);
-            qptc::mma_tf32(dt, al, wh, id, 1u);
+          for (int ks = 0; ks < HKC / 16; ++ks) {
+            const uint64_t ah = qptc::desc_kmajor(sa + ks * 256, 128, (HKC / 8) * 128);
+            const uint64_t al = qptc::desc_kmajor(sa + abytes + ks * 256, 128, (HKC / 8) * 128);
+            const uint64_t wh = qptc::desc_kmajor(sw + ks * 256, 128, (HKC / 8) * 128);
+            const uint64_t wl = qptc::desc_kmajor(sw + wbytes + ks * 256, 128, (HKC / 8) * 128);
+            qptc::mma_f16(dt, ah, wh, id, (kc > 0 || ks > 0) ? 1u : 0u);
+            qptc::mma_f16(dt, ah, wl, id, 1u);
+            qptc::mma_f16(dt, al, wh, id, 1u);
           }
           qptc::commit(&mma_done[st]);
           last_commit = it;
@@ -216,7 +227,7 @@ __global__ void __launch_bounds__(MU_THREADS, 1) dense_mu_embed_kernel(MuArgs a)
             if (it >= 1) ok = qptc::mbar_wait(&mma_done[s2], ((it - 1) >> 1) & 1);
             if (!ok) break;
             qptc::mbar_arrive_expect_tx(&w_full[s2], 2 * wbytes);
-            qptc::bulk_g2s(sm + s2 * stage_bytes + 2 * abytes, a.WT + (int64_t)((kc + 1) % nkc) * 2 * (nch * KC),
+            qptc::bulk_g2s(sm + s2 * stage_bytes + 2 * abytes, a.WT16 + (int64_t)((kc + 1) % nkc) * 2 * (nch * HKC),
                            2 * wbytes, &w_full[s2]);
             last_copy = it + 1;
           }
@@ -327,16 +338,14 @@ __global__ void __launch_bounds__(MU_THREADS, 1) dense_mu_embed_kernel(MuArgs a)
           }
           if (ok) {
 #pragma unroll
-            for (int g4 = 0; g4 < KC / 4; ++g4) {
-              const float4 v4 = cur[g4];
-              float4 h4, l4;
-              qptc::split_tf32(v4.x, h4.x, l4.x);
-              qptc::split_tf32(v4.y, h4.y, l4.y);
-              qptc::split_tf32(v4.z, h4.z, l4.z);
-              qptc::split_tf32(v4.w, h4.w, l4.w);
-              const uint32_t off = core_off(tid, g4 * 4) / 4;
-              *reinterpret_cast<float4*>(Ahi + off) = h4;
-              *reinterpret_cast<float4*>(Alo + off) = l4;
+            for (int g8 = 0; g8 < HKC / 8; ++g8) {
+              const float v8[8] = {cur[2 * g8].x, cur[2 * g8].y, cur[2 * g8].z, cur[2 * g8].w,
+                                   cur[2 * g8 + 1].x, cur[2 * g8 + 1].y, cur[2 * g8 + 1].z, cur[2 * g8 + 1].w};
+              uint4 h8, l8;
+              pack_h8(v8, sL, h8, l8);
+              const uint32_t off = core_off_h(tid, g8 * 8);
+              *reinterpret_cast<uint4*>(reinterpret_cast<unsigned char*>(Ahi) + off) = h8;
+              *reinterpret_cast<uint4*>(reinterpret_cast<unsigned char*>(Alo) + off) = l8;
             }
           }
         }
@@ -348,7 +357,7 @@ __global__ void __launch_bounds__(MU_THREADS, 1) dense_mu_embed_kernel(MuArgs a)
           if (kc == 0) ok = begin_drain();
           if (ok && kc < nchunk32)
             mu_chunk(R, n, pend_nv4 ? warp : 0, kc,
-                     tmem + ((uint32_t)(warp * 32) << 16) + pend_buf * (tcols / 2) + kc * 32);
+                     tmem + ((uint32_t)(warp * 32) << 16) + pend_buf * (tcols / 2) + kc * 32, us);
           if (kc == nchunk32 - 1) finalize();
         }
       }
@@ -367,7 +376,7 @@ __global__ void __launch_bounds__(MU_THREADS, 1) dense_mu_embed_kernel(MuArgs a)
       ok = begin_drain();
       if (ok) {
         for (int c = 0; c < nchunk32; ++c)
-          mu_chunk(R, n, pend_nv4 ? warp : 0, c, tmem + ((uint32_t)(warp * 32) << 16) + pend_buf * (tcols / 2) + c * 32);
+          mu_chunk(R, n, pend_nv4 ? warp : 0, c, tmem + ((uint32_t)(warp * 32) << 16) + pend_buf * (tcols / 2) + c * 32, us);
         finalize();
       }
     }

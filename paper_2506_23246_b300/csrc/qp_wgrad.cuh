@@ -58,28 +58,7 @@ struct WgArgs {
 __host__ __device__ inline uint32_t core_off_w16(int r, int k) {
   return (uint32_t)((r >> 3) * (WKC / 8) * 128 + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2);
 }
-// Power-of-two scale that puts magnitudes up to `mx` below 2^13 (1 when mx is not positive).
-__device__ __forceinline__ float pow2_scale(float mx) {
-  if (!(mx > 0.f)) return 1.f;
-  int e = 0;
-  frexpf(mx, &e);
-  return ldexpf(1.f, max(-100, min(100, 13 - e)));
-}
-// Eight scaled values as FP16 pairs (hi, lo = rounding remainder), packed for one 16-byte store.
-__device__ __forceinline__ void pack_h8(const float* v, float sc, uint4& hi, uint4& lo) {
-  uint32_t h[4], l[4];
-#pragma unroll
-  for (int e = 0; e < 4; ++e) {
-    const float x0 = sc * v[2 * e], x1 = sc * v[2 * e + 1];
-    const __half2 h2 = __floats2half2_rn(x0, x1);
-    const float2 hf = __half22float2(h2);
-    const __half2 l2 = __floats2half2_rn(x0 - hf.x, x1 - hf.y);
-    h[e] = *reinterpret_cast<const uint32_t*>(&h2);
-    l[e] = *reinterpret_cast<const uint32_t*>(&l2);
-  }
-  hi = make_uint4(h[0], h[1], h[2], h[3]);
-  lo = make_uint4(l[0], l[1], l[2], l[3]);
-}
+
 
 struct WgSmem {
   int a_bytes, b_bytes, stage, raw, fac, tab, bars, total;
