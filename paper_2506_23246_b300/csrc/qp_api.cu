@@ -1,5 +1,7 @@
 // qp_api.cu -- the C-ABI of libqpinn.so (declared in include/qpinn.h): plan creation and
 // validation, workspace carving and the launch sequence of one forward or loss+gradient call.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <cstdio>
@@ -110,6 +112,51 @@ bool fused_path(const qp_plan* pl) {
 }
 
 size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// The driver's tensor-map encoder, through the runtime's entry-point query (no libcuda link).
+PFN_cuTensorMapEncodeTiled_v12000 tmap_encoder() {
+  static std::once_flag once;
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    cudaGetLastError();
+  });
+  return fn;
+}
+
+// Tensor maps of the blocked costate buffer [nblk][rtot][256] for the fused forward's bulk
+// stores: the collocation rows (4 per point, point-major) as (column, point, vector, block) so
+// that a tile's vector-major rows land in place; the IC and BC rows as (column, point, block).
+// Each map's point extent is its set's size, so the last, partial tile of a set is clipped.
+bool lam_maps(float* lam, int64_t rtot, const int64_t npts[3], int nblk, CUtensorMap m[3]) {
+  const PFN_cuTensorMapEncodeTiled_v12000 enc = tmap_encoder();
+  if (!enc) return false;
+  const cuuint32_t es[4] = {1, 1, 1, 1};
+  {
+    const cuuint64_t dims[4] = {256, (cuuint64_t)(npts[0] > 0 ? npts[0] : 1), 4, (cuuint64_t)nblk};
+    const cuuint64_t str[3] = {4096, 1024, (cuuint64_t)rtot * 1024};
+    const cuuint32_t box[4] = {32, 32, 4, 1};
+    if (enc(&m[0], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, lam, dims, str, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) !=
+        CUDA_SUCCESS)
+      return false;
+  }
+  for (int set = 1; set < 3; ++set) {
+    const int64_t row0 = 4 * npts[0] + (set == 2 ? npts[1] : 0);
+    const cuuint64_t dims[3] = {256, (cuuint64_t)(npts[set] > 0 ? npts[set] : 1), (cuuint64_t)nblk};
+    const cuuint64_t str[2] = {1024, (cuuint64_t)rtot * 1024};
+    const cuuint32_t box[3] = {32, 128, 1};
+    if (enc(&m[set], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, lam + row0 * 256, dims, str, box, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return false;
+  }
+  return true;
+}
 
 // Slot groups of the weight-gradient partial sum: enough blocks to cover the GPU.
 int gsum_groups(const qp_plan* pl) {
@@ -597,7 +644,11 @@ static qp_status dense_loss_grad(qp_plan* pl, const float* d_params, const float
     const int64_t ftiles = fa.tile_end[2];
     const int fblocks = (int)(ftiles < pl->sm_count ? (ftiles > 0 ? ftiles : 1) : pl->sm_count);
     if (pl->prof_start) cudaEventRecord(pl->prof_start, s);
-    qpd::dense_fused_fwd_kernel<<<fblocks, qpd::F_THREADS, qpd::fused_smem(n, pl->p.energy_nt).total, s>>>(fa);
+    alignas(64) CUtensorMap tmaps[3];
+    std::memset(tmaps, 0, sizeof(tmaps));
+    fa.use_tma = lam_maps(fa.lam, fa.rtot, npts, (2 * dim) / 256, tmaps) ? 1 : 0;
+    qpd::dense_fused_fwd_kernel<<<fblocks, qpd::F_THREADS, qpd::fused_smem(n, pl->p.energy_nt).total, s>>>(
+        fa, tmaps[0], tmaps[1], tmaps[2]);
     if (pl->prof_stop) cudaEventRecord(pl->prof_stop, s);
     launches += 1;
   } else {

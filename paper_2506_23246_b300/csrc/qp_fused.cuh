@@ -1,6 +1,7 @@
 // qp_fused.cuh -- forward contraction of the fused-unitary path with the pointwise stage
 // (readout, head, loss terms, cotangents, costates) as its tensor-memory epilogue, n = 7, 8.
 #pragma once
+#include <cuda.h>   // CUtensorMap (the maps are encoded on the host)
 #include "qp_dense.cuh"
 
 namespace qpd {
@@ -37,7 +38,23 @@ struct FusedArgs {
   int32_t loss_stride, grad_stride, nE, nblk;
   int32_t* status;
   int32_t* scal;           // [2] float bits (atomic max): row bound of the product states, max |lambda|
+  int32_t use_tma;         // 1: costates leave through tensor-map bulk stores (maps valid), 0: plain stores
 };
+
+// Tensor-map bulk store of one staged 128-row x 32-column chunk (bulk group of this thread).
+__device__ __forceinline__ void tma_store_4d(const CUtensorMap* m, const void* src, int x, int y, int z, int w) {
+  asm volatile("cp.async.bulk.tensor.4d.global.shared::cta.bulk_group [%0, {%1, %2, %3, %4}], [%5];" ::"l"(m),
+               "r"(x), "r"(y), "r"(z), "r"(w), "r"(qptc::smem_u32(src))
+               : "memory");
+}
+__device__ __forceinline__ void tma_store_3d(const CUtensorMap* m, const void* src, int x, int y, int z) {
+  asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%1, %2, %3}], [%4];" ::"l"(m), "r"(x),
+               "r"(y), "r"(z), "r"(qptc::smem_u32(src))
+               : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+// The bulk stores issued by this thread have finished reading shared memory.
+__device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
 
 // Shared memory: two A stages (TF32 hi, lo), a three-slot ring of W blocks (copies run two
 // K-steps ahead, across tile boundaries), and the persistent head/loss/barrier block. The
@@ -99,7 +116,12 @@ __device__ __forceinline__ float warp_sum_f(float v) {
   return v;
 }
 
-__global__ void __launch_bounds__(F_THREADS, 1) dense_fused_fwd_kernel(FusedArgs a) {
+// tm_c: costates of the collocation rows as (column, point, vector, 256-column block), i.e. the
+// point-major rows addressed in the tile's vector-major row order; tm_i / tm_b: IC / BC rows as
+// (column, point, block). Tiles that run past a set's points are clipped by the maps.
+__global__ void __launch_bounds__(F_THREADS, 1) dense_fused_fwd_kernel(FusedArgs a, const __grid_constant__ CUtensorMap tm_c,
+                                                                       const __grid_constant__ CUtensorMap tm_i,
+                                                                       const __grid_constant__ CUtensorMap tm_b) {
   extern __shared__ __align__(1024) unsigned char sm[];
   const int n = a.n, dim = 1 << n, m = a.m, nt = a.pb.energy_nt;
   const int nc = (2 << n) / 256;
@@ -528,6 +550,25 @@ __global__ void __launch_bounds__(F_THREADS, 1) dense_fused_fwd_kernel(FusedArgs
 #pragma unroll
         for (int e = 0; e < 8; ++e)
           lmax = fmaxf(lmax, fmaxf(fmaxf(fabsf(outv[e].x), fabsf(outv[e].y)), fmaxf(fabsf(outv[e].z), fabsf(outv[e].w))));
+        if (a.use_tma) {
+          // stage the chunk in tensor-memory row order with the 128-byte swizzle (16-byte
+          // piece e of row r at e ^ (r mod 8): conflict-free for 32 consecutive rows) and let
+          // one thread of the half hand it to a tensor-map bulk store (operand stage 0 is idle
+          // during the epilogue)
+          float4* stg = reinterpret_cast<float4*>(sm) + hh * 1024;   // [128 rows][8] float4
+          const bool issuer = ws == 0 && lane == 0;
+          if (issuer) bulk_wait_read();      // the previous chunk's store has read the staging
+          named_bar(1 + hh);
+#pragma unroll
+          for (int e = 0; e < 8; ++e) stg[r * 8 + (e ^ (r & 7))] = outv[e];
+          qptc::fence_proxy_async();
+          named_bar(1 + hh);
+          if (issuer) {
+            if (set == 0) tma_store_4d(&tm_c, stg, col & 255, (int)p0, 0, col >> 8);
+            else tma_store_3d(set == 1 ? &tm_i : &tm_b, stg, col & 255, (int)p0, col >> 8);
+            bulk_commit();
+          }
+        } else
         // the column group's 128 rows are consecutive costate rows: stage the chunk in that
         // order (operand stage 0 is idle during the epilogue) and store 128-byte row segments,
         // four rows per warp instruction instead of one 16-byte piece of 32 rows
@@ -552,6 +593,8 @@ __global__ void __launch_bounds__(F_THREADS, 1) dense_fused_fwd_kernel(FusedArgs
       }
       const float wl = warp_max_f(lmax);
       if (lane == 0) atomicMax(a.scal + 1, __float_as_int(wl));
+      // the next tile's operands overwrite the staging: its last store must have read it
+      if (a.use_tma && ws == 0 && lane == 0) bulk_wait_read();
     }
     // tensor memory and the W slot of this tile's last step are free again
     qptc::fence_before();
