@@ -129,25 +129,16 @@ PFN_cuTensorMapEncodeTiled_v12000 tmap_encoder() {
 }
 
 // Tensor maps of the blocked costate buffer [nblk][rtot][256] for the fused forward's bulk
-// stores: the collocation rows (4 per point, point-major) as (column, point, vector, block) so
-// that a tile's vector-major rows land in place; the IC and BC rows as (column, point, block).
-// Each map's point extent is its set's size, so the last, partial tile of a set is clipped.
+// stores: per point set, its rows (4 per collocation point, 1 per IC/BC point) as (column,
+// row, block). Each map's row extent is its set's, so the last, partial tile is clipped.
 bool lam_maps(float* lam, int64_t rtot, const int64_t npts[3], int nblk, CUtensorMap m[3]) {
   const PFN_cuTensorMapEncodeTiled_v12000 enc = tmap_encoder();
   if (!enc) return false;
-  const cuuint32_t es[4] = {1, 1, 1, 1};
-  {
-    const cuuint64_t dims[4] = {256, (cuuint64_t)(npts[0] > 0 ? npts[0] : 1), 4, (cuuint64_t)nblk};
-    const cuuint64_t str[3] = {4096, 1024, (cuuint64_t)rtot * 1024};
-    const cuuint32_t box[4] = {32, 32, 4, 1};
-    if (enc(&m[0], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, lam, dims, str, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
-            CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) !=
-        CUDA_SUCCESS)
-      return false;
-  }
-  for (int set = 1; set < 3; ++set) {
-    const int64_t row0 = 4 * npts[0] + (set == 2 ? npts[1] : 0);
-    const cuuint64_t dims[3] = {256, (cuuint64_t)(npts[set] > 0 ? npts[set] : 1), (cuuint64_t)nblk};
+  const cuuint32_t es[3] = {1, 1, 1};
+  for (int set = 0; set < 3; ++set) {
+    const int64_t row0 = set == 0 ? 0 : 4 * npts[0] + (set == 2 ? npts[1] : 0);
+    const int64_t rows = set == 0 ? 4 * npts[0] : npts[set];
+    const cuuint64_t dims[3] = {256, (cuuint64_t)(rows > 0 ? rows : 1), (cuuint64_t)nblk};
     const cuuint64_t str[2] = {1024, (cuuint64_t)rtot * 1024};
     const cuuint32_t box[3] = {32, 128, 1};
     if (enc(&m[set], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, lam + row0 * 256, dims, str, box, es,

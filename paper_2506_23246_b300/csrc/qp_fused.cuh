@@ -14,8 +14,10 @@ namespace qpd {
 // the point, and the costates
 //   lambda_0 = O phi_0 + sum_d O_d phi_d,  lambda_d = O_d phi_0,  O = sum_i zbar_i Z_i
 // (Z_i diagonal: O is a per-amplitude sign sum), written in place of the states.
-// Tile rows: collocation tiles hold 32 points x 4 vectors (row = vector * 32 + point, so warp
-// w and w + 4 own vector w % 4, the two halves of the columns); IC/BC tiles 128 points.
+// Tile rows: collocation tiles hold 32 points x 4 vectors (row = 4 point + vector, the order of
+// the costate rows in HBM), so a point's four rows sit in one lane quad of a warp and every
+// exchange between them is a shuffle; IC/BC tiles hold 128 points. Warps w and w + 4 read the
+// same 32 rows, the two halves of the columns.
 constexpr int F_STAGERS = 256;                 // operand generation + epilogue (8 warps)
 constexpr int F_THREADS = F_STAGERS + 32;      // + one control warp (bulk copies, MMAs)
 constexpr int F_MAXH = 5;       // embedding qubits above the 3 lowest index bits (n <= 8)
@@ -42,11 +44,6 @@ struct FusedArgs {
 };
 
 // Tensor-map bulk store of one staged 128-row x 32-column chunk (bulk group of this thread).
-__device__ __forceinline__ void tma_store_4d(const CUtensorMap* m, const void* src, int x, int y, int z, int w) {
-  asm volatile("cp.async.bulk.tensor.4d.global.shared::cta.bulk_group [%0, {%1, %2, %3, %4}], [%5];" ::"l"(m),
-               "r"(x), "r"(y), "r"(z), "r"(w), "r"(qptc::smem_u32(src))
-               : "memory");
-}
 __device__ __forceinline__ void tma_store_3d(const CUtensorMap* m, const void* src, int x, int y, int z) {
   asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%1, %2, %3}], [%4];" ::"l"(m), "r"(x),
                "r"(y), "r"(z), "r"(qptc::smem_u32(src))
@@ -116,9 +113,8 @@ __device__ __forceinline__ float warp_sum_f(float v) {
   return v;
 }
 
-// tm_c: costates of the collocation rows as (column, point, vector, 256-column block), i.e. the
-// point-major rows addressed in the tile's vector-major row order; tm_i / tm_b: IC / BC rows as
-// (column, point, block). Tiles that run past a set's points are clipped by the maps.
+// tm_c, tm_i, tm_b: the costate rows of the collocation, IC and BC sets as (column, row,
+// 256-column block); tiles that run past a set's rows are clipped by the maps.
 __global__ void __launch_bounds__(F_THREADS, 1) dense_fused_fwd_kernel(FusedArgs a, const __grid_constant__ CUtensorMap tm_c,
                                                                        const __grid_constant__ CUtensorMap tm_i,
                                                                        const __grid_constant__ CUtensorMap tm_b) {
@@ -239,8 +235,8 @@ __global__ void __launch_bounds__(F_THREADS, 1) dense_fused_fwd_kernel(FusedArgs
     const bool nv4 = set == 0;
     const int64_t np = a.npts[set], base = a.pt_base[set];
     // ---- embedding tables of the A row generated by this thread
-    const int s_a = nv4 ? arow >> 5 : 0;
-    const int64_t pa = p0 + (nv4 ? (arow & 31) : arow);
+    const int s_a = nv4 ? (arow & 3) : 0;                 // row = 4 point + vector
+    const int64_t pa = p0 + (nv4 ? (arow >> 2) : arow);
     const int64_t pac = pa < np ? pa : np - 1;
     const float4* tj = reinterpret_cast<const float4*>(a.thetaJ) + (base + pac) * n;
     float Lo[8], Lod[8];
@@ -340,9 +336,9 @@ __global__ void __launch_bounds__(F_THREADS, 1) dense_fused_fwd_kernel(FusedArgs
     const float us = rsc[r];   // this thread's tensor-memory row: back to unscaled amplitudes
     // epilogue buffers: the W slot of the tile's last step (or their own region)
     unsigned char* epi = L.epi_in_w ? sm + L.wbase + ((it - 1) % 3) * L.w_bytes : sm + L.epi;
-    float4* X0 = reinterpret_cast<float4*>(epi + L.x0) + hh * 256;
-    float4* TB = reinterpret_cast<float4*>(epi + L.tb) + hh * 768;
     float* zp = reinterpret_cast<float*>(epi + L.zp);
+    const int s_r = nv4 ? (lane & 3) : 0;     // vector of this thread's row r = 4 point + vector
+    const int q0 = lane & ~3;                 // the lane of the row's point with vector 0
     float* zbs = reinterpret_cast<float*>(epi + L.zb);
     // ---- pass 1: readout partial sums over this thread's half of the columns
     float acc[QP_MAXQ];
@@ -356,23 +352,12 @@ __global__ void __launch_bounds__(F_THREADS, 1) dense_fused_fwd_kernel(FusedArgs
       for (int e = 0; e < 32; ++e) v[e] *= us;
       float y[16];
       if (nv4) {
-        if (ws == 0) {
+        // the point's four rows sit in one lane quad: phi_0 comes from the quad's first lane
 #pragma unroll
-          for (int e = 0; e < 8; ++e)
-            X0[lane * 8 + (e ^ (lane & 7))] = make_float4(v[4 * e], v[4 * e + 1], v[4 * e + 2], v[4 * e + 3]);
-#pragma unroll
-          for (int e = 0; e < 16; ++e) y[e] = v[2 * e] * v[2 * e] + v[2 * e + 1] * v[2 * e + 1];
+        for (int e = 0; e < 16; ++e) {
+          const float xa = __shfl_sync(0xffffffffu, v[2 * e], q0), xb = __shfl_sync(0xffffffffu, v[2 * e + 1], q0);
+          y[e] = s_r == 0 ? v[2 * e] * v[2 * e] + v[2 * e + 1] * v[2 * e + 1] : 2.f * (v[2 * e] * xa + v[2 * e + 1] * xb);
         }
-        named_bar(1 + hh);
-        if (ws != 0) {
-#pragma unroll
-          for (int e = 0; e < 8; ++e) {
-            const float4 x = X0[lane * 8 + (e ^ (lane & 7))];
-            y[2 * e] = 2.f * (v[4 * e] * x.x + v[4 * e + 1] * x.y);
-            y[2 * e + 1] = 2.f * (v[4 * e + 2] * x.z + v[4 * e + 3] * x.w);
-          }
-        }
-        named_bar(1 + hh);
       } else {
 #pragma unroll
         for (int e = 0; e < 16; ++e) y[e] = v[2 * e] * v[2 * e] + v[2 * e + 1] * v[2 * e + 1];
@@ -400,10 +385,13 @@ __global__ void __launch_bounds__(F_THREADS, 1) dense_fused_fwd_kernel(FusedArgs
     for (int i = 0; i < QP_MAXQ; ++i)
       if (i < m) zp[(hh * TM + r) * QP_MAXQ + i] = acc[i];
     stagers_bar();
-    // ---- point stage: head, loss terms, cotangents, sign-sum coefficients
-    if (nv4 ? warp == 0 : warp < 4) {
-      const int r0 = nv4 ? lane : r;
-      const int64_t pp = p0 + r0;
+    // ---- point stage: head, loss terms, cotangents, sign-sum coefficients. Collocation
+    // tiles: the four lanes of a point (rows 4 point + vector) share the point's loss terms and
+    // each forms the cotangent of its own row; IC/BC tiles: one point per lane.
+    if (warp < 4) {
+      const int pl = nv4 ? (r >> 2) : r;
+      const int row0 = nv4 ? pl * 4 : pl;
+      const int64_t pp = p0 + pl;
       const bool active = pp < np;
       const int64_t ppc = active ? pp : np - 1;
       float z[QP_MAXQ], dz[3][QP_MAXQ];
@@ -411,11 +399,11 @@ __global__ void __launch_bounds__(F_THREADS, 1) dense_fused_fwd_kernel(FusedArgs
       for (int i = 0; i < QP_MAXQ; ++i) {
         z[i] = 0.f; dz[0][i] = dz[1][i] = dz[2][i] = 0.f;
         if (i < m) {
-          z[i] = zp[r0 * QP_MAXQ + i] + zp[(TM + r0) * QP_MAXQ + i];
+          z[i] = zp[row0 * QP_MAXQ + i] + zp[(TM + row0) * QP_MAXQ + i];
           if (nv4) {
 #pragma unroll
             for (int d = 0; d < 3; ++d)
-              dz[d][i] = zp[((d + 1) * 32 + lane) * QP_MAXQ + i] + zp[(TM + (d + 1) * 32 + lane) * QP_MAXQ + i];
+              dz[d][i] = zp[(row0 + d + 1) * QP_MAXQ + i] + zp[(TM + row0 + d + 1) * QP_MAXQ + i];
           }
         }
       }
@@ -440,37 +428,40 @@ __global__ void __launch_bounds__(F_THREADS, 1) dense_fused_fwd_kernel(FusedArgs
       double lt[QP_NLP], ev;
       int slice;
       qpk::point_loss_terms(a.pb, set, ppc, np, a.counts, __ldg(xp), __ldg(xp + 1), f, D, active, lt, slice, ev, g, gD);
+      if (s_r != 0) ev = 0.0;   // each point once
+      if (s_r == 0) {
 #pragma unroll
-      for (int i = 0; i < QP_NLP; ++i) lacc[i] += lt[i];
+        for (int i = 0; i < QP_NLP; ++i) lacc[i] += lt[i];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) hb[c] += g[c];
+      }
       // energy slices: one FP64 shared add per warp when the warp's points share a slice
       const int s0 = __shfl_sync(0xffffffffu, slice, 0);
       if (__all_sync(0xffffffffu, slice == s0)) {
         const double evs = warp_sum_d(ev);
         if (lane == 0 && s0 >= 0) atomicAdd(&sloss[QP_NLP + s0], evs);
-      } else if (slice >= 0) {
+      } else if (slice >= 0 && s_r == 0) {
         atomicAdd(&sloss[QP_NLP + slice], ev);
       }
+      // this row's cotangent weights: zbar (vector 0) or zbar_d (vector d), and its share of the
+      // head gradient
+      float gs[3];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) gs[c] = s_r == 0 ? g[c] : (s_r == 1 ? gD[c][0] : (s_r == 2 ? gD[c][1] : gD[c][2]));
 #pragma unroll
       for (int i = 0; i < QP_MAXQ; ++i) {
         if (i < m) {
-          float zb = 0.f, zbd[3] = {0.f, 0.f, 0.f};
+          const float zs = s_r == 0 ? z[i] : (s_r == 1 ? dz[0][i] : (s_r == 2 ? dz[1][i] : dz[2][i]));
+          float zb = 0.f;
 #pragma unroll
           for (int c = 0; c < 3; ++c) {
             const float w = hw[c * m + i];
-            zb += w * g[c];
-#pragma unroll
-            for (int d = 0; d < 3; ++d) zbd[d] += w * gD[c][d];
-            hg[c][i] += g[c] * z[i] + gD[c][0] * dz[0][i] + gD[c][1] * dz[1][i] + gD[c][2] * dz[2][i];
+            zb += w * gs[c];
+            hg[c][i] += gs[c] * zs;
           }
-          zbs[r0 * QP_MAXQ + i] = zb;
-          if (nv4) {
-#pragma unroll
-            for (int d = 0; d < 3; ++d) zbs[((d + 1) * 32 + lane) * QP_MAXQ + i] = zbd[d];
-          }
+          zbs[r * QP_MAXQ + i] = zb;
         }
       }
-#pragma unroll
-      for (int c = 0; c < 3; ++c) hb[c] += g[c];
     }
     stagers_bar();
     // ---- pass 2: costates of this thread's row, written over the state rows
@@ -489,8 +480,6 @@ __global__ void __launch_bounds__(F_THREADS, 1) dense_fused_fwd_kernel(FusedArgs
       }
       const float t01[4] = {cb[0] + cb[1], -cb[0] + cb[1], cb[0] - cb[1], -cb[0] - cb[1]};
       const float t23[4] = {cb[2] + cb[3], -cb[2] + cb[3], cb[2] - cb[3], -cb[2] - cb[3]};
-      const int s_r = nv4 ? ws : 0;
-      (void)s_r;
       const int64_t grow0 = lam_row(set, p0, 0, a.npts[0], base);   // first costate row of the tile
       float lmax = 0.f;   // largest costate magnitude of this thread (FP16 scale of the next contractions)
       for (int cc = 0; cc < half_cols; cc += 32) {
@@ -509,76 +498,68 @@ __global__ void __launch_bounds__(F_THREADS, 1) dense_fused_fwd_kernel(FusedArgs
         qptc::tmem_ld32(tmem + ((uint32_t)(ws * 32) << 16) + col, v);
         #pragma unroll
         for (int e = 0; e < 32; ++e) v[e] *= us;
-        float4 outv[8];
+        float4* stg = reinterpret_cast<float4*>(sm) + hh * 1024;   // [128 rows][8] float4 staging
+        const bool issuer = ws == 0 && lane == 0;
+        // the previous chunk's costates have left the staging (operand stage 0 is idle during
+        // the epilogue); 16-byte piece e of row r is staged at e ^ (r mod 8)
+        if (a.use_tma && issuer) bulk_wait_read();
+        named_bar(1 + hh);
         if (nv4) {
-          if (ws == 0) {
+          // lambda_s = O_s phi_0 for s >= 1 (phi_0 from the quad's first lane), then
+          // lambda_0 = sum_s O_s phi_s over the quad, reduced so that lane s keeps columns
+          // 8s .. 8s + 7 of it
 #pragma unroll
-            for (int e = 0; e < 8; ++e)
-              X0[lane * 8 + (e ^ (lane & 7))] = make_float4(v[4 * e], v[4 * e + 1], v[4 * e + 2], v[4 * e + 3]);
-          } else {
+          for (int e = 0; e < 8; ++e) {
+            float x[4];
 #pragma unroll
-            for (int e = 0; e < 8; ++e)
-              TB[(ws - 1) * 256 + lane * 8 + (e ^ (lane & 7))] =
-                  make_float4(O[2 * e] * v[4 * e], O[2 * e] * v[4 * e + 1], O[2 * e + 1] * v[4 * e + 2],
-                              O[2 * e + 1] * v[4 * e + 3]);
-          }
-          named_bar(1 + hh);
-          if (ws == 0) {
-#pragma unroll
-            for (int e = 0; e < 8; ++e) {
-              const int sw = lane * 8 + (e ^ (lane & 7));
-              const float4 t1 = TB[sw], t2 = TB[256 + sw], t3 = TB[512 + sw];
-              outv[e] = make_float4(O[2 * e] * v[4 * e] + t1.x + t2.x + t3.x,
-                                    O[2 * e] * v[4 * e + 1] + t1.y + t2.y + t3.y,
-                                    O[2 * e + 1] * v[4 * e + 2] + t1.z + t2.z + t3.z,
-                                    O[2 * e + 1] * v[4 * e + 3] + t1.w + t2.w + t3.w);
-            }
-          } else {
-#pragma unroll
-            for (int e = 0; e < 8; ++e) {
-              const float4 x = X0[lane * 8 + (e ^ (lane & 7))];
-              outv[e] = make_float4(O[2 * e] * x.x, O[2 * e] * x.y, O[2 * e + 1] * x.z, O[2 * e + 1] * x.w);
+            for (int u = 0; u < 4; ++u) x[u] = __shfl_sync(0xffffffffu, v[4 * e + u], q0);
+            const float4 o4 = make_float4(O[2 * e] * x[0], O[2 * e] * x[1], O[2 * e + 1] * x[2], O[2 * e + 1] * x[3]);
+            if (s_r != 0) {
+              stg[r * 8 + (e ^ (r & 7))] = o4;
+              lmax = fmaxf(lmax, fmaxf(fmaxf(fabsf(o4.x), fabsf(o4.y)), fmaxf(fabsf(o4.z), fabsf(o4.w))));
             }
           }
-          named_bar(1 + hh);
+#pragma unroll
+          for (int k = 0; k < 32; ++k) v[k] *= O[k >> 1];
+          const bool up = (s_r & 2) != 0, lo = (s_r & 1) != 0;
+          float kept[16];
+#pragma unroll
+          for (int k = 0; k < 16; ++k) {
+            const float keep = up ? v[16 + k] : v[k], send = up ? v[k] : v[16 + k];
+            kept[k] = keep + __shfl_xor_sync(0xffffffffu, send, 2);
+          }
+          float l0[8];
+#pragma unroll
+          for (int k = 0; k < 8; ++k) {
+            const float keep = lo ? kept[8 + k] : kept[k], send = lo ? kept[k] : kept[8 + k];
+            l0[k] = keep + __shfl_xor_sync(0xffffffffu, send, 1);
+          }
+          const int rq = r & ~3;
+#pragma unroll
+          for (int j2 = 0; j2 < 2; ++j2) {
+            const float4 o4 = make_float4(l0[4 * j2], l0[4 * j2 + 1], l0[4 * j2 + 2], l0[4 * j2 + 3]);
+            stg[rq * 8 + ((2 * s_r + j2) ^ (rq & 7))] = o4;
+            lmax = fmaxf(lmax, fmaxf(fmaxf(fabsf(o4.x), fabsf(o4.y)), fmaxf(fabsf(o4.z), fabsf(o4.w))));
+          }
         } else {
 #pragma unroll
-          for (int e = 0; e < 8; ++e)
-            outv[e] = make_float4(O[2 * e] * v[4 * e], O[2 * e] * v[4 * e + 1], O[2 * e + 1] * v[4 * e + 2],
-                                  O[2 * e + 1] * v[4 * e + 3]);
+          for (int e = 0; e < 8; ++e) {
+            const float4 o4 = make_float4(O[2 * e] * v[4 * e], O[2 * e] * v[4 * e + 1], O[2 * e + 1] * v[4 * e + 2],
+                                          O[2 * e + 1] * v[4 * e + 3]);
+            stg[r * 8 + (e ^ (r & 7))] = o4;
+            lmax = fmaxf(lmax, fmaxf(fmaxf(fabsf(o4.x), fabsf(o4.y)), fmaxf(fabsf(o4.z), fabsf(o4.w))));
+          }
         }
-#pragma unroll
-        for (int e = 0; e < 8; ++e)
-          lmax = fmaxf(lmax, fmaxf(fmaxf(fabsf(outv[e].x), fabsf(outv[e].y)), fmaxf(fabsf(outv[e].z), fabsf(outv[e].w))));
         if (a.use_tma) {
-          // stage the chunk in tensor-memory row order with the 128-byte swizzle (16-byte
-          // piece e of row r at e ^ (r mod 8): conflict-free for 32 consecutive rows) and let
-          // one thread of the half hand it to a tensor-map bulk store (operand stage 0 is idle
-          // during the epilogue)
-          float4* stg = reinterpret_cast<float4*>(sm) + hh * 1024;   // [128 rows][8] float4
-          const bool issuer = ws == 0 && lane == 0;
-          if (issuer) bulk_wait_read();      // the previous chunk's store has read the staging
-          named_bar(1 + hh);
-#pragma unroll
-          for (int e = 0; e < 8; ++e) stg[r * 8 + (e ^ (r & 7))] = outv[e];
+          // one thread of the half hands the chunk to a tensor-map bulk store
           qptc::fence_proxy_async();
           named_bar(1 + hh);
           if (issuer) {
-            if (set == 0) tma_store_4d(&tm_c, stg, col & 255, (int)p0, 0, col >> 8);
-            else tma_store_3d(set == 1 ? &tm_i : &tm_b, stg, col & 255, (int)p0, col >> 8);
+            tma_store_3d(set == 0 ? &tm_c : (set == 1 ? &tm_i : &tm_b), stg, col & 255, (int)(nv4 ? p0 * 4 : p0), col >> 8);
             bulk_commit();
           }
-        } else
-        // the column group's 128 rows are consecutive costate rows: stage the chunk in that
-        // order (operand stage 0 is idle during the epilogue) and store 128-byte row segments,
-        // four rows per warp instruction instead of one 16-byte piece of 32 rows
-        {
-          float4* stg = reinterpret_cast<float4*>(sm) + hh * 1024;   // [128 rows][8] float4
-          const int srow = nv4 ? lane * 4 + ws : r;
-          const int ssw = nv4 ? (lane & 7) : (lane & 7);
-          if (!nv4) named_bar(1 + hh);   // the previous chunk's stores have read the staging
-#pragma unroll
-          for (int e = 0; e < 8; ++e) stg[srow * 8 + (e ^ ssw)] = outv[e];
+        } else {
+          // plain stores of 128-byte row segments, four rows per warp instruction
           named_bar(1 + hh);
           const int gt = ws * 32 + lane;
           const int nrows = (int)(nv4 ? (np - p0 < 32 ? (np - p0) * 4 : 128) : (np - p0 < TM ? np - p0 : TM));
@@ -586,8 +567,7 @@ __global__ void __launch_bounds__(F_THREADS, 1) dense_fused_fwd_kernel(FusedArgs
 #pragma unroll
           for (int i = 0; i < 8; ++i) {
             const int idx = i * 128 + gt, row = idx >> 3, c4 = idx & 7;
-            const int rsw = nv4 ? ((row >> 2) & 7) : (row & 7);
-            if (row < nrows) *reinterpret_cast<float4*>(gbase + (int64_t)row * 256 + c4 * 4) = stg[row * 8 + (c4 ^ rsw)];
+            if (row < nrows) *reinterpret_cast<float4*>(gbase + (int64_t)row * 256 + c4 * 4) = stg[row * 8 + (c4 ^ (row & 7))];
           }
         }
       }
