@@ -192,7 +192,7 @@ WsLayout ws_layout(const qp_plan* pl, int64_t P) {
   w.dW16 = o; o = al256(o + (dg && fused_path(pl) ? 2 * (2 * dim) * dim * 4 : 0));
   w.dcs = o; o = al256(o + (dg ? (size_t)P * n * 8 : 0));
   w.dgs = o; o = al256(o + (dg ? (size_t)gsum_groups(pl) * dim * dim * 16 : 0));
-  w.dgates = o; o = al256(o + (dg ? (size_t)pl->c.n_layers * n * 4 * 16 : 0));
+  w.dgates = o; o = al256(o + (dn ? (size_t)pl->c.n_layers * n * 4 * 16 : 0));
   w.total = o;
   return w;
 }
@@ -609,8 +609,9 @@ static qp_status dense_loss_grad(qp_plan* pl, const float* d_params, const float
     launches += 1;
   }
   if (fused) ba.W = nullptr;
-  qpd::dense_build_kernel<<<dim, 256, 2 * dim * 16, s>>>(ba);
-  launches += 1;
+  qpd::dense_gates_kernel<<<1, L * n, 0, s>>>(ba);
+  qpd::dense_build_kernel<<<dim, 128, 2 * dim * 16, s>>>(ba);
+  launches += 2;
   int64_t base = 0;
   if (fused) {
     // forward contraction with the pointwise stage as its epilogue (states stay on chip)
@@ -819,7 +820,9 @@ qp_status qp_forward(qp_plan* pl, const float* d_params, const float* d_pts, int
     ba.params = d_params; ba.circ_off = pl->circ_off; ba.n = n; ba.L = pl->c.n_layers;
     ba.ansatz = pl->c.ansatz; ba.enc = pl->c.enc; ba.W = (float*)(ws + w.dW); ba.U = nullptr;
     ba.W16 = nullptr;
-    qpd::dense_build_kernel<<<dim, 256, 2 * dim * 16, s>>>(ba);
+    ba.gates = (double2*)(ws + w.dgates);
+    qpd::dense_gates_kernel<<<1, pl->c.n_layers * n, 0, s>>>(ba);
+    qpd::dense_build_kernel<<<dim, 128, 2 * dim * 16, s>>>(ba);
     qpd::GemmArgs ga;
     ga.thetaJ = (const float*)(ws + w.thetaJ); ga.W = (const float*)(ws + w.dW);
     ga.phi = (float2*)(ws + w.dphi); ga.n = n; ga.nv = d_dfields ? 4 : 1;

@@ -138,41 +138,80 @@ __device__ __forceinline__ int ring_map(int n, int ansatz, int l, int k) {
   return k;
 }
 
-// One block per basis column k: |k> through all layers (gates and CNOT rings) in FP64. The
-// gate matrices of every (layer, qubit) are formed in parallel first; a gate is one pass over
-// the amplitude pairs, a CNOT ring one permutation pass.
+// Gate matrices of every (layer, qubit) in FP64, once per call (one thread each).
+__global__ void dense_gates_kernel(BuildArgs a) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < a.L * a.n) gate_fp64(a.params, a.circ_off, a.ansatz, a.n, i / a.n, i % a.n, &a.gates[i * 4]);
+}
+
+// Double-float arithmetic (an unevaluated sum h + l of two floats, ~48-bit significand): the
+// build runs on the FP32 pipes, which on this part are 64x the FP64 rate. Products by the
+// exact FMA residual, sums by the two-sum of Knuth with the low parts added.
+struct DFl {
+  float h, l;
+};
+__device__ __forceinline__ DFl df_mul(float ah, float al, float bh, float bl) {
+  const float p = ah * bh;
+  float e = fmaf(ah, bh, -p);
+  e = fmaf(ah, bl, e);
+  e = fmaf(al, bh, e);
+  return {p, e};
+}
+__device__ __forceinline__ DFl df_add(DFl a, DFl b) {
+  const float s = a.h + b.h, bb = s - a.h;
+  const float e = (a.h - (s - bb)) + (b.h - bb) + a.l + b.l;
+  const float h = s + e;
+  return {h, e - (h - s)};
+}
+// (g x) for a double-float complex g = (re h, re l, im h, im l) and amplitude x, same layout:
+// the real and imaginary parts as 2-term dot products.
+__device__ __forceinline__ void df_cmac(const float4& g, const float4& x, DFl& re, DFl& im) {
+  re = df_add(df_mul(g.x, g.y, x.x, x.y), df_mul(-g.z, -g.w, x.z, x.w));
+  im = df_add(df_mul(g.x, g.y, x.z, x.w), df_mul(g.z, g.w, x.x, x.y));
+}
+__device__ __forceinline__ float4 df_split(double v0, double v1) {
+  const float h0 = (float)v0, h1 = (float)v1;
+  return make_float4(h0, (float)(v0 - (double)h0), h1, (float)(v1 - (double)h1));
+}
+
+// One block per basis column k: |k> through all layers (gates and CNOT rings) in double-float
+// arithmetic from the FP64 gate matrices. A gate is one pass over the amplitude pairs, a CNOT
+// ring one permutation pass.
 __global__ void dense_build_kernel(BuildArgs a) {
-  extern __shared__ __align__(16) double2 colbuf[];  // two [2^n] column buffers
-  __shared__ double2 gm[QP_MAXL * QP_MAXQ * 4];
+  extern __shared__ __align__(16) float4 colbuf[];  // two [2^n] column buffers (double-float complex)
+  __shared__ float4 gm[QP_MAXL * QP_MAXQ * 4];
   const int n = a.n, dim = 1 << n, k = blockIdx.x;
-  for (int i = threadIdx.x; i < a.L * n; i += blockDim.x)
-    gate_fp64(a.params, a.circ_off, a.ansatz, n, i / n, i % n, &gm[i * 4]);
-  if (a.gates && k == 0) {
-    __syncthreads();
-    for (int i = threadIdx.x; i < a.L * n * 4; i += blockDim.x) a.gates[i] = gm[i];
+  for (int i = threadIdx.x; i < a.L * n * 4; i += blockDim.x) {
+    const double2 g = a.gates[i];
+    gm[i] = df_split(g.x, g.y);
   }
-  double2* col = colbuf;
-  double2* nxt = colbuf + dim;
-  for (int j = threadIdx.x; j < dim; j += blockDim.x) col[j] = make_double2(j == k ? 1.0 : 0.0, 0.0);
+  float4* col = colbuf;
+  float4* nxt = colbuf + dim;
+  for (int j = threadIdx.x; j < dim; j += blockDim.x) col[j] = make_float4(j == k ? 1.f : 0.f, 0.f, 0.f, 0.f);
   __syncthreads();
   for (int l = 0; l < a.L; ++l) {
     for (int q = 0; q < n; ++q) {
-      const double2* g = &gm[(l * n + q) * 4];
+      const float4* g = &gm[(l * n + q) * 4];
       const int bit = 1 << (n - 1 - q);
       for (int i = threadIdx.x; i < dim / 2; i += blockDim.x) {
         const int k0 = ((i & ~(bit - 1)) << 1) | (i & (bit - 1));
         const int k1 = k0 | bit;
-        const double2 x = col[k0], y = col[k1];
-        const double2 a0 = zmul(g[0], x), a1 = zmul(g[1], y), b0 = zmul(g[2], x), b1 = zmul(g[3], y);
-        col[k0] = make_double2(a0.x + a1.x, a0.y + a1.y);
-        col[k1] = make_double2(b0.x + b1.x, b0.y + b1.y);
+        const float4 x = col[k0], y = col[k1];
+        DFl r0, i0, r1, i1, r2, i2, r3, i3;
+        df_cmac(g[0], x, r0, i0);
+        df_cmac(g[1], y, r1, i1);
+        df_cmac(g[2], x, r2, i2);
+        df_cmac(g[3], y, r3, i3);
+        const DFl ar = df_add(r0, r1), ai = df_add(i0, i1), br = df_add(r2, r3), bi = df_add(i2, i3);
+        col[k0] = make_float4(ar.h, ar.l, ai.h, ai.l);
+        col[k1] = make_float4(br.h, br.l, bi.h, bi.l);
       }
       __syncthreads();
     }
     if (a.ansatz != 3 && n > 1) {
       for (int j = threadIdx.x; j < dim; j += blockDim.x) nxt[ring_map(n, a.ansatz, l, j)] = col[j];
       __syncthreads();
-      double2* t = col;
+      float4* t = col;
       col = nxt;
       nxt = t;
     }
@@ -186,7 +225,8 @@ __global__ void dense_build_kernel(BuildArgs a) {
   const int nch = n_cols_chunk(n), nkc = dim / KC;
   const int kc = k / KC, t = k % KC;
   for (int j = threadIdx.x; j < dim; j += blockDim.x) {
-    const double2 v = zmul(col[j], ph);
+    const float4 cj = col[j];
+    const double2 v = zmul(make_double2((double)cj.x + (double)cj.y, (double)cj.z + (double)cj.w), ph);
     if (a.U) a.U[(int64_t)j * dim + k] = v;
 #pragma unroll
     for (int c2 = 0; c2 < 2; ++c2) {
