@@ -90,11 +90,14 @@ __host__ __device__ inline FusedSmem fused_smem(int n, int nt) {
   return f;
 }
 
+// bar.sync is the aligned form: the warp is reconverged before it.
 __device__ __forceinline__ void named_bar(int id) {
+  __syncwarp();
   asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(128) : "memory");
 }
 // Barrier over the staging warps only (the control warp never joins it).
 __device__ __forceinline__ void stagers_bar() {
+  __syncwarp();
   asm volatile("bar.sync %0, %1;" ::"r"(3), "r"(F_STAGERS) : "memory");
 }
 __device__ __forceinline__ double warp_sum_d(double v) {

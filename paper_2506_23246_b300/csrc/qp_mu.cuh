@@ -247,7 +247,10 @@ __global__ void __launch_bounds__(MU_THREADS, 1) dense_mu_embed_kernel(MuArgs a)
     int64_t pend_p = 0;
     uint32_t pend_buf = 0, pend_it = 0;
     MuRow R;
-    auto bar = [&]() { asm volatile("bar.sync 1, %0;" ::"r"(MU_STAGERS) : "memory"); };
+    auto bar = [&]() {
+      __syncwarp();   // bar.sync is the aligned form
+      asm volatile("bar.sync 1, %0;" ::"r"(MU_STAGERS) : "memory");
+    };
     auto finalize = [&]() {
       qptc::fence_before();
       // rows of one point sit in four warps (same lane): combine through shared memory

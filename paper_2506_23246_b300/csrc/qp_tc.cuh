@@ -123,8 +123,11 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 // Named barrier over `count` threads with an AND reduction of `v` (count a multiple of 32).
+// bar.red is the aligned form: every lane of a warp must execute the same instance, so the
+// warp is reconverged first.
 __device__ __forceinline__ bool bar_and(int id, int count, bool v) {
   uint32_t r;
+  __syncwarp();
   asm volatile(
       "{\n.reg .pred p, q;\nsetp.ne.u32 q, %1, 0;\nbar.red.and.pred p, %2, %3, q;\n"
       "selp.u32 %0, 1, 0, p;\n}\n"
