@@ -349,10 +349,8 @@ __global__ void __launch_bounds__(F_THREADS, 1) dense_fused_fwd_kernel(FusedArgs
     for (int i = 0; i < QP_MAXQ; ++i) acc[i] = 0.f;
     for (int cc = 0; cc < half_cols; cc += 32) {
       const int col = hh * half_cols + cc;
-      float v[32];
+      float v[32];   // scaled amplitudes: the row scale comes out of the partial sums below
       qptc::tmem_ld32(tmem + ((uint32_t)(ws * 32) << 16) + col, v);
-      #pragma unroll
-      for (int e = 0; e < 32; ++e) v[e] *= us;
       float y[16];
       if (nv4) {
         // the point's four rows sit in one lane quad: phi_0 comes from the quad's first lane
@@ -384,9 +382,15 @@ __global__ void __launch_bounds__(F_THREADS, 1) dense_fused_fwd_kernel(FusedArgs
         }
       }
     }
+    {
+      // y is a product of this row's amplitudes with its own (vector 0) or its point's vector-0
+      // row's amplitudes: one factor of each row scale
+      const float us0 = __shfl_sync(0xffffffffu, us, q0);
+      const float yf = us * (nv4 && s_r != 0 ? us0 : us);
 #pragma unroll
-    for (int i = 0; i < QP_MAXQ; ++i)
-      if (i < m) zp[(hh * TM + r) * QP_MAXQ + i] = acc[i];
+      for (int i = 0; i < QP_MAXQ; ++i)
+        if (i < m) zp[(hh * TM + r) * QP_MAXQ + i] = acc[i] * yf;
+    }
     stagers_bar();
     // ---- point stage: head, loss terms, cotangents, sign-sum coefficients. Collocation
     // tiles: the four lanes of a point (rows 4 point + vector) share the point's loss terms and
@@ -497,10 +501,8 @@ __global__ void __launch_bounds__(F_THREADS, 1) dense_fused_fwd_kernel(FusedArgs
         float O[16];
 #pragma unroll
         for (int e = 0; e < 16; ++e) O[e] = Bs + t01[e & 3] + t23[e >> 2];
-        float v[32];
+        float v[32];   // scaled amplitudes: the row scales are folded into O below
         qptc::tmem_ld32(tmem + ((uint32_t)(ws * 32) << 16) + col, v);
-        #pragma unroll
-        for (int e = 0; e < 32; ++e) v[e] *= us;
         float4* stg = reinterpret_cast<float4*>(sm) + hh * 1024;   // [128 rows][8] float4 staging
         const bool issuer = ws == 0 && lane == 0;
         // the previous chunk's costates have left the staging (operand stage 0 is idle during
@@ -511,17 +513,21 @@ __global__ void __launch_bounds__(F_THREADS, 1) dense_fused_fwd_kernel(FusedArgs
           // lambda_s = O_s phi_0 for s >= 1 (phi_0 from the quad's first lane), then
           // lambda_0 = sum_s O_s phi_s over the quad, reduced so that lane s keeps columns
           // 8s .. 8s + 7 of it
+          const float us0 = __shfl_sync(0xffffffffu, us, q0);
 #pragma unroll
           for (int e = 0; e < 8; ++e) {
             float x[4];
 #pragma unroll
             for (int u = 0; u < 4; ++u) x[u] = __shfl_sync(0xffffffffu, v[4 * e + u], q0);
-            const float4 o4 = make_float4(O[2 * e] * x[0], O[2 * e] * x[1], O[2 * e + 1] * x[2], O[2 * e + 1] * x[3]);
+            const float oa = O[2 * e] * us0, ob = O[2 * e + 1] * us0;
+            const float4 o4 = make_float4(oa * x[0], oa * x[1], ob * x[2], ob * x[3]);
             if (s_r != 0) {
               stg[r * 8 + (e ^ (r & 7))] = o4;
               lmax = fmaxf(lmax, fmaxf(fmaxf(fabsf(o4.x), fabsf(o4.y)), fmaxf(fabsf(o4.z), fabsf(o4.w))));
             }
           }
+#pragma unroll
+          for (int e = 0; e < 16; ++e) O[e] *= us;
 #pragma unroll
           for (int k = 0; k < 32; ++k) v[k] *= O[k >> 1];
           const bool up = (s_r & 2) != 0, lo = (s_r & 1) != 0;
@@ -545,6 +551,8 @@ __global__ void __launch_bounds__(F_THREADS, 1) dense_fused_fwd_kernel(FusedArgs
             lmax = fmaxf(lmax, fmaxf(fmaxf(fabsf(o4.x), fabsf(o4.y)), fmaxf(fabsf(o4.z), fabsf(o4.w))));
           }
         } else {
+#pragma unroll
+          for (int e = 0; e < 16; ++e) O[e] *= us;
 #pragma unroll
           for (int e = 0; e < 8; ++e) {
             const float4 o4 = make_float4(O[2 * e] * v[4 * e], O[2 * e] * v[4 * e + 1], O[2 * e + 1] * v[4 * e + 2],
