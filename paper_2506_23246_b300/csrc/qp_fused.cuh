@@ -363,14 +363,23 @@ __global__ void __launch_bounds__(F_THREADS, 1) dense_fused_fwd_kernel(FusedArgs
 #pragma unroll
         for (int e = 0; e < 16; ++e) y[e] = v[2 * e] * v[2 * e] + v[2 * e + 1] * v[2 * e + 1];
       }
-      // total and the four single-bit sign sums over the 16 amplitudes of the chunk
-      float T = 0.f, S[4] = {0.f, 0.f, 0.f, 0.f};
+      // total and the four single-bit sign sums over the 16 amplitudes of the chunk, by
+      // pairwise sums and differences (bit b: S_b = sum over bit b clear - sum over bit b set)
+      float S[4];
+      float s8[8], s4[4];
+      {
+        float d = 0.f;
 #pragma unroll
-      for (int e = 0; e < 16; ++e) {
-        T += y[e];
+        for (int k = 0; k < 8; ++k) { s8[k] = y[2 * k] + y[2 * k + 1]; d += y[2 * k] - y[2 * k + 1]; }
+        S[0] = d;
+        d = 0.f;
 #pragma unroll
-        for (int b = 0; b < 4; ++b) S[b] += ((e >> b) & 1) ? -y[e] : y[e];
+        for (int k = 0; k < 4; ++k) { s4[k] = s8[2 * k] + s8[2 * k + 1]; d += s8[2 * k] - s8[2 * k + 1]; }
+        S[1] = d;
+        S[2] = (s4[0] - s4[1]) + (s4[2] - s4[3]);
+        S[3] = (s4[0] + s4[1]) - (s4[2] + s4[3]);
       }
+      const float T = (s4[0] + s4[1]) + (s4[2] + s4[3]);
       const int j0 = col >> 1;
 #pragma unroll
       for (int i = 0; i < QP_MAXQ; ++i) {
@@ -498,9 +507,11 @@ __global__ void __launch_bounds__(F_THREADS, 1) dense_fused_fwd_kernel(FusedArgs
           const int pbit = n - 1 - i;
           if (i < m && pbit >= 4) Bs += ((j0 >> pbit) & 1) ? -coef[i] : coef[i];
         }
-        float O[16];
+        float O[16], u01[4];
 #pragma unroll
-        for (int e = 0; e < 16; ++e) O[e] = Bs + t01[e & 3] + t23[e >> 2];
+        for (int e = 0; e < 4; ++e) u01[e] = Bs + t01[e];
+#pragma unroll
+        for (int e = 0; e < 16; ++e) O[e] = u01[e & 3] + t23[e >> 2];
         float v[32];   // scaled amplitudes: the row scales are folded into O below
         qptc::tmem_ld32(tmem + ((uint32_t)(ws * 32) << 16) + col, v);
         float4* stg = reinterpret_cast<float4*>(sm) + hh * 1024;   // [128 rows][8] float4 staging
