@@ -95,10 +95,8 @@ __device__ __forceinline__ void mu_high(const MuRow& R, int n, int c, float& H, 
 
 // One 32-column chunk c of the row's mu (tensor memory) into C and D.
 __device__ __forceinline__ void mu_chunk(MuRow& R, int n, int s, int c, uint32_t taddr, float us) {
-  float v[32];
+  float v[32];   // scaled mu: the scale comes out of the correlations below
   qptc::tmem_ld32(taddr, v);
-#pragma unroll
-  for (int l = 0; l < 32; ++l) v[l] *= us;
   float X = 0.f, Y = 0.f, A[5], B[5];
 #pragma unroll
   for (int b = 0; b < 5; ++b) { A[b] = 0.f; B[b] = 0.f; }
@@ -122,6 +120,10 @@ __device__ __forceinline__ void mu_chunk(MuRow& R, int n, int s, int c, uint32_t
       }
     }
   }
+  X *= us;
+  Y *= us;
+#pragma unroll
+  for (int b = 0; b < 5; ++b) { A[b] *= us; B[b] *= us; }
   float H, Hd;
   mu_high(R, n, c, H, Hd);
   // low qubits q = n - 1 - b: the flip stays inside the chunk
