@@ -72,7 +72,9 @@ typedef enum { QP_PREMAP_DIRECT = 0, QP_PREMAP_RFF_MLP = 1 } qp_premap;
 
 /* SIMT_FP32: gate-by-gate statevectors in registers and shared memory, FP32 (any n).
  * GEMM_3XTF32: the ansatz layers fused into one 2^n x 2^n unitary applied to all points as
- * tensor-core contractions (tcgen05, TF32 hi/lo split, FP32 accumulation); forward for
+ * tensor-core contractions (tcgen05) on split operands hi + lo with three products per
+ * term and FP32 accumulation: TF32 pairs, and for n = 7, 8 FP16 pairs scaled by powers of
+ * two (forward, weight gradient, back-projection), both about 22-bit operands; forward for
  * n >= 5, loss + gradient for n >= 7. AUTO picks GEMM_3XTF32 for 8-9 qubits, SIMT otherwise.
  * GEMM_BF16X3 is reserved (QP_ERR_UNSUPPORTED). */
 typedef enum {
