@@ -365,3 +365,26 @@ def test_invalid_arguments_rejected_on_host(torch_cuda):
         plan.loss_grad(torch.zeros(3, device="cuda"), {})
     rc = qp.lib().qp_forward(plan._h, None, None, 4, None, None, None)
     assert rc == 1
+
+
+@pytest.mark.parametrize("omega_scale,head_scale", [(30.0, 20.0), (1e-4, 1.0), (1.0, 1e-3)])
+def test_dense_fp16_pair_operand_ranges(torch_cuda, oracle, omega_scale, head_scale):
+    """The FP16-pair operands of the n = 8 tensor-core path take their power-of-two scales
+    from the data: large input Jacobians (RFF frequencies x30: tangent rows of size ~|J|),
+    vanishing ones (x1e-4: tangent rows ~1e-4, scaled up) and small costates (head x1e-3).
+    Every loss term and a sample of every gradient block stay within 1e-5 of the oracle."""
+    circ = W.circuit(8, 2, 8, ansatz="strong_rot", enc="rx", scale="acos", premap="rff_mlp",
+                     rff_freqs=8, mlp_width=8, mlp_depth=1)
+    prob = W.problem("dielectric", disk_x0=0.2, disk_r=0.6, w_energy=10.0, energy_slice=8,
+                     energy_nt=2)
+    sets = {"colloc": W.uniform_points(24, 31, 1.0), "ic": W.ic_points_uniform(4, 32),
+            "bc": W.bc_points(4, 33)}
+    params = W.init_params(circ, 13).astype(np.float64)
+    lay = oracle.param_layout(circ)
+    params[:lay["fixed"]] *= omega_scale                  # Omega (fixed RFF frequencies)
+    params[lay["head"]:lay["total"]] *= head_scale        # readout head W, b
+    params = params.astype(np.float32)
+    rng = np.random.default_rng(1)
+    mlp = rng.choice(np.arange(lay["fixed"], lay["circuit"]), 16, replace=False)
+    idx = np.concatenate([np.sort(mlp), np.arange(lay["circuit"], lay["total"])])
+    _loss_grad_check(torch_cuda, oracle, circ, prob, params, sets, idx, path="gemm_3xtf32")
