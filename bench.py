@@ -39,9 +39,10 @@ def _args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--path", default="auto", choices=["auto", "simt", "gemm_3xtf32"],
                     help="statevector path of the library (auto = the library's choice)")
-    ap.add_argument("--workload", default="c3", choices=["c3", "c5"],
+    ap.add_argument("--workload", default="c3", choices=["c3", "c5", "configs"],
                     help="c3: the full QPINN step (default); c5: 32 uneven instances in one "
-                         "batched call against the same instances called one by one")
+                         "batched call against the same instances called one by one; configs: "
+                         "one line per configuration (C1-C4) and compute path")
     return ap.parse_args()
 
 
@@ -459,12 +460,119 @@ def run_c5(a):
     return 0
 
 
+def run_configs(a):
+    """Every configuration on every compute path that supports it, one JSON line each:
+    C1 (4q/2L, 1024 points, forward + d/dx,dy,dt), C2 (6q/4L, 16,384 + 2,048 IC + 2,048 PEC
+    points, loss + gradient), C3 (the bench step) and C4 (10q/8L, 64^3 grid + 64^2 IC plane,
+    RFF64 + MLP32, loss + gradient). Paths: FP32 SIMT; tensor cores with FP16 pairs and with
+    3xTF32 where the configuration has them. Device time per step with L2 flushed between
+    steps; the dominant kernel's device time from the library's profiling events."""
+    import torch
+    from paper_2506_23246_b300 import build, qp
+    from paper_2506_23246_b300 import workloads as W
+    build.build()
+    dev = torch.device("cuda", 0)
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            peaks = json.load(fh)
+    except (OSError, ValueError):
+        pass
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    sm_max = peaks.get("sm_max_mhz", 2032.0)
+    bf16 = peaks.get("bf16_tflops", 1800.0)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    c1c, c1p, c1x = W.c1_workload(0, 1024)
+    c2c, c2pr, c2p, c2s = W.c2_workload(0)
+    c3c, c3pr, c3p, c3s = W.c3_workload(0)
+    c4c, c4pr, c4p, c4s = W.c4_workload(0)
+    cases = [("C1 4q/2L, 1024 points, forward + d/dx,dy,dt", c1c, None, c1p, {"pts": c1x},
+              [("simt", "fp16_pairs")]),
+             ("C2 6q/4L, 16384 colloc + 2048 IC + 2048 PEC, loss + gradient", c2c, c2pr, c2p, c2s,
+              [("simt", "fp16_pairs")]),
+             ("C3 8q/6L RFF64+MLP32 dielectric, 65536 colloc + 4096 IC, loss + gradient", c3c, c3pr,
+              c3p, c3s, [("simt", "fp16_pairs"), ("gemm_3xtf32", "fp16_pairs")]),
+             ("C4 10q/8L RFF64+MLP32, 64^3 colloc + 4096 IC, loss + gradient", c4c, c4pr, c4p, c4s,
+              [("simt", "fp16_pairs"), ("gemm_3xtf32", "fp16_pairs"), ("gemm_3xtf32", "tf32_pairs")])]
+    for name, circ, prob, params, sets, paths in cases:
+        n, L = circ["n_qubits"], circ["n_layers"]
+        dp = torch.tensor(params, device=dev)
+        dsets = {k: torch.tensor(v, device=dev) for k, v in sets.items()}
+        ncol = dsets["pts"].shape[0] if prob is None else dsets["colloc"].shape[0]
+        rows = sum(4 * v.shape[0] if k in ("pts", "colloc") else v.shape[0] for k, v in dsets.items())
+        for path, ops in paths:
+            plan = qp.Plan(circ, prob, path=path, operands=ops)
+            plan.reserve(sum(v.shape[0] for v in dsets.values()), dev)
+            if prob is None:
+                f = torch.empty(ncol, 3, device=dev)
+                df = torch.empty(ncol, 3, 3, device=dev)
+                fn = lambda: plan.forward(dp, dsets["pts"], out=(f, df))
+            else:
+                loss = torch.empty(9 + prob["energy_nt"], dtype=torch.float64, device=dev)
+                grad = torch.empty(plan.n_params, dtype=torch.float32, device=dev)
+                fn = lambda: plan.loss_grad(dp, dsets, out=(loss, grad))
+            k0, k1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            plan.set_profile_events(k0, k1)
+            for _ in range(max(a.warmup, 3)):
+                fn()
+            torch.cuda.synchronize()
+            steps = a.steps
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                  for _ in range(steps)]
+            kt = []
+            for i in range(steps):
+                flush.fill_(float(i))
+                ev[i][0].record(stream)
+                fn()
+                ev[i][1].record(stream)
+                k1.synchronize()
+                kt.append(k0.elapsed_time(k1))
+            torch.cuda.synchronize()
+            plan.set_profile_events(None, None)
+            ms = sum(e0.elapsed_time(e1) for e0, e1 in ev) / steps
+            kms = statistics.mean(kt)
+            dim = 1 << n
+            if plan.path == "simt":
+                kernel = "circuit_kernel<%d,%s>" % (n, "false" if prob is None else "true")
+                if prob is None:
+                    flops = ncol * 16 * dim * n * L * 4
+                else:
+                    flops = sum(v.shape[0] * circuit_flops_per_point(n, L, 4 if k == "colloc" else 1)
+                                for k, v in dsets.items())
+                peak, bound = sms * 128 * 2 * sm_max * 1e6 / 1e12, "alu"
+            else:
+                # dominant contraction: forward (qp_forward; fused n = 8) or weight gradient
+                # (n >= 9), 2 x rows x 2^(n+1) x 2^n algorithmic flops each
+                if prob is None or n <= 8:
+                    kernel = "dense_fused_fwd_kernel" if n in (7, 8) and prob is not None else "dense_row16_kernel<0>"
+                else:
+                    kernel = "dense_wgrad_gemm_kernel<%s>" % ("FP16" if ops == "fp16_pairs" else "TF32")
+                flops = 2.0 * rows * (2 * dim) * dim
+                peak = bf16 / 3.0 if ops == "fp16_pairs" else bf16 * 0.5 / 3.0
+                bound = "tensor"
+            achieved = flops / (kms / 1000.0) / 1e12
+            print(json.dumps({"config": name, "path": plan.path,
+                              "operands": ops if plan.path != "simt" else "fp32",
+                              "ms_per_step": ms, "colloc_pts_per_s": ncol / (ms / 1000.0),
+                              "steps": steps, "warmup": max(a.warmup, 3),
+                              "dominant_kernel": {"name": kernel, "ms": kms, "share": kms / ms,
+                                                  "bound": bound, "achieved_tflops": achieved,
+                                                  "peak_tflops": peak, "frac": achieved / peak},
+                              "gpu_launches_per_step": plan.last_launch_count()}), flush=True)
+            del plan
+            torch.cuda.empty_cache()
+    return 0
+
+
 def main():
     a = _args()
     if a.impl == "reference":
         return run_reference(a)
     if a.workload == "c5":
         return run_c5(a)
+    if a.workload == "configs":
+        return run_configs(a)
     return run_native(a)
 
 

@@ -75,7 +75,7 @@ typedef enum { QP_PREMAP_DIRECT = 0, QP_PREMAP_RFF_MLP = 1 } qp_premap;
  * tensor-core contractions (tcgen05) on split operands hi + lo with three products per
  * term and FP32 accumulation: TF32 pairs, and for n = 7, 8 FP16 pairs scaled by powers of
  * two (forward, weight gradient, back-projection), both about 22-bit operands; forward for
- * n >= 5, loss + gradient for n >= 7. AUTO picks GEMM_3XTF32 for 8-9 qubits, SIMT otherwise.
+ * n >= 5, loss + gradient for n >= 7. AUTO picks GEMM_3XTF32 for 8-10 qubits, SIMT otherwise.
  * GEMM_BF16X3 is reserved (QP_ERR_UNSUPPORTED). */
 typedef enum {
   QP_PATH_AUTO = 0,
@@ -216,6 +216,20 @@ int32_t qp_last_launch_count(const qp_plan* plan);
 
 /* The path a plan resolved to (QP_PATH_SIMT_FP32 or QP_PATH_GEMM_3XTF32). */
 int32_t qp_plan_path(const qp_plan* plan);
+
+/* Operand form of the tensor-core contractions that have two: the forward of qp_forward for
+ * n >= 7, and the forward, the weight gradient and the back-projection mu = Re(U'^H lambda)
+ * of qp_loss_grad for n = 9, 10 (the n = 7, 8 kernels of qp_loss_grad have FP16 pairs
+ * only). FP16_PAIRS (the default): FP16 hi + lo of
+ * power-of-two-scaled operands, the hi*hi products and the hi*lo + lo*hi corrections in
+ * separate FP32 accumulators. TF32_PAIRS: 3xTF32 in one accumulator. Both are ~22-bit
+ * operands; the FP16 form halves the tensor-core time, and the tensor core's truncating
+ * accumulation (about one FP32 ulp per instruction) touches the result K/16 times instead
+ * of 3K/8.
+ * Returns QP_ERR_INVALID_ARG for another value. Not thread-safe against concurrent calls on
+ * the same plan. */
+typedef enum { QP_OPERANDS_FP16_PAIRS = 0, QP_OPERANDS_TF32_PAIRS = 1 } qp_operands;
+qp_status qp_plan_set_operands(qp_plan* plan, int32_t operands);
 
 /* Optional profiling: two cudaEvent_t (passed as void*, created by the caller) that the
  * following compute calls record on their stream immediately before and after the dominant

@@ -35,6 +35,7 @@ struct qp_plan {
   int nwblk = 0, wtile = 0, smem_wgrad = 0, smem_premap = 0, smem_premap4 = 0;
   bool swc_big = false;   // the one-launch sweep runs as a 16-CTA cluster
   bool pg_ok = false;     // RFF + MLP premap with F = 64, H = 32: the GEMM-formulated kernels
+  int32_t operands = QP_OPERANDS_FP16_PAIRS;   // forward contraction outside the fused kernel
   int64_t n_params = 0, circ_off = 0, head_off = 0, mlp_off = 0, mlp_count = 0, nfixed = 0;
   void* ws = nullptr;
   size_t ws_bytes = 0;
@@ -189,7 +190,7 @@ WsLayout ws_layout(const qp_plan* pl, int64_t P) {
   const bool dm = dg && pl->c.premap == QP_PREMAP_RFF_MLP;
   w.dWT = o; o = al256(o + (dm ? 2 * (2 * dim) * dim * 4 : 0));
   w.dmu = o; o = al256(o + (dm && !fused_path(pl) ? (size_t)P * 4 * dim * 4 : 0));
-  w.dW16 = o; o = al256(o + (dg && fused_path(pl) ? 2 * (2 * dim) * dim * 4 : 0));
+  w.dW16 = o; o = al256(o + (dg ? 2 * (2 * dim) * dim * 2 : 0));
   w.dcs = o; o = al256(o + (dg ? (size_t)P * n * 8 : 0));
   w.dgs = o; o = al256(o + (dg ? (size_t)gsum_groups(pl) * dim * dim * 16 : 0));
   w.dgates = o; o = al256(o + (dn ? (size_t)pl->c.n_layers * n * 4 * 16 : 0));
@@ -313,9 +314,9 @@ qp_status qp_plan_create(const qp_circuit* circuit, const qp_problem* problem, i
   pl->c = *circuit;
   pl->p = *problem;
   // AUTO: the fused-unitary tensor-core path where it is faster and stays within 1e-5 of the
-  // FP64 reference (8-9 qubits); the FP32 gate-by-gate path otherwise.
+  // FP64 reference (8-10 qubits); the FP32 gate-by-gate path otherwise.
   pl->path = path != QP_PATH_AUTO ? path
-             : (circuit->n_qubits >= 8 && circuit->n_qubits <= 9 ? QP_PATH_GEMM_3XTF32 : QP_PATH_SIMT_FP32);
+             : (circuit->n_qubits >= 8 ? QP_PATH_GEMM_3XTF32 : QP_PATH_SIMT_FP32);
   const int n = circuit->n_qubits;
   if (qp_build_sched(n, circuit->n_layers, circuit->ansatz, &pl->sched) != 0) {
     delete pl;
@@ -374,6 +375,10 @@ qp_status qp_plan_create(const qp_circuit* circuit, const qp_problem* problem, i
                              qpd::gemm_smem_bytes(n, 0)) != cudaSuccess ||
         raise_smem_limit((void*)qpd::dense_row_gemm_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              qpd::gemm_smem_bytes(n, 1)) != cudaSuccess ||
+        raise_smem_limit((void*)qpd::dense_row16_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         qpd::row16_smem_bytes()) != cudaSuccess ||
+        raise_smem_limit((void*)qpd::dense_row16_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         qpd::row16_smem_bytes()) != cudaSuccess ||
         raise_smem_limit((void*)qpd::dense_wgrad_gemm_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              qpd::wg_smem_bytes(n)) != cudaSuccess ||
         raise_smem_limit((void*)qpd::dense_wgrad_gemm_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -479,6 +484,13 @@ qp_status qp_set_workspace(qp_plan* plan, void* d_ws, size_t bytes) {
 int32_t qp_last_launch_count(const qp_plan* plan) { return plan ? plan->last_launches : -1; }
 
 int32_t qp_plan_path(const qp_plan* plan) { return plan ? plan->path : -1; }
+
+qp_status qp_plan_set_operands(qp_plan* plan, int32_t operands) {
+  if (!plan || (operands != QP_OPERANDS_FP16_PAIRS && operands != QP_OPERANDS_TF32_PAIRS))
+    return QP_ERR_INVALID_ARG;
+  plan->operands = operands;
+  return QP_OK;
+}
 
 qp_status qp_set_profile_events(qp_plan* plan, void* ev_start, void* ev_stop) {
   if (!plan || ((ev_start == nullptr) != (ev_stop == nullptr))) return QP_ERR_INVALID_ARG;
@@ -595,20 +607,22 @@ static qp_status dense_loss_grad(qp_plan* pl, const float* d_params, const float
   ba.gates = (double2*)(ws + w.dgates);
   ba.ansatz = pl->c.ansatz; ba.enc = pl->c.enc; ba.W = (float*)(ws + w.dW); ba.U = (double2*)(ws + w.dU);
   const bool mlp = pl->c.premap == QP_PREMAP_RFF_MLP;
+  const bool fused = fused_path(pl);
+  // forward and back-projection on FP16 pairs (the fused n = 7, 8 kernels have no other form)
+  const bool fwd16 = fused || pl->operands == QP_OPERANDS_FP16_PAIRS;
   ba.WT = mlp ? (float*)(ws + w.dWT) : nullptr;
-  if (mlp && fused_path(pl)) {
-    ba.WT16 = (__half*)(ws + w.dWT);   // the mu kernel takes FP16 pairs
+  if (mlp && fwd16) {
+    ba.WT16 = (__half*)(ws + w.dWT);   // the mu contraction takes FP16 pairs
     ba.WT = nullptr;
   }
-  const bool fused = fused_path(pl);
-  ba.W16 = fused ? (__half*)(ws + w.dW16) : nullptr;
+  ba.W16 = fwd16 ? (__half*)(ws + w.dW16) : nullptr;
   if (P > 0) {
     const int64_t tot = P * n;
     const int hb = (int)((tot + 255) / 256 < pl->sm_count * 4 ? (tot + 255) / 256 : pl->sm_count * 4);
     qpd::dense_halfangle_kernel<<<hb, 256, 0, s>>>((const float4*)(ws + w.thetaJ), (float2*)(ws + w.dcs), tot);
     launches += 1;
   }
-  if (fused) ba.W = nullptr;
+  if (fwd16) ba.W = nullptr;
   qpd::dense_gates_kernel<<<1, L * n, 0, s>>>(ba);
   qpd::dense_build_kernel<<<dim, 128, 2 * dim * 16, s>>>(ba);
   launches += 2;
@@ -653,7 +667,13 @@ static qp_status dense_loss_grad(qp_plan* pl, const float* d_params, const float
         const int64_t ppt = qpd::TM / ga.nv;
         const int64_t ntiles = (npts[set] + ppt - 1) / ppt;
         const int gblocks = (int)(ntiles < pl->sm_count ? ntiles : pl->sm_count);
-        qpd::dense_row_gemm_kernel<0><<<gblocks, 128, qpd::gemm_smem_bytes(n, 0), s>>>(ga);
+        const int64_t items = ntiles * ((2 * dim) / 256);   // (tile, column chunk) items
+        const int iblocks = (int)(items < pl->sm_count ? items : pl->sm_count);
+        if (fwd16)   // records the operand range of R for the weight gradient
+          qpd::dense_row16_kernel<0><<<iblocks, qpd::F16_THREADS, qpd::row16_smem_bytes(), s>>>(
+              ga, (const __half*)(ws + w.dW16), (int32_t*)(ws + w.status) + 16);
+        else
+          qpd::dense_row_gemm_kernel<0><<<gblocks, 128, qpd::gemm_smem_bytes(n, 0), s>>>(ga);
         launches += 1;
       }
       base += npts[set];
@@ -668,6 +688,7 @@ static qp_status dense_loss_grad(qp_plan* pl, const float* d_params, const float
     pa.loss_stride = QP_NLP + pl->p.energy_nt;
     pa.grad_stride = 3 * n * L + 3 * pl->c.n_readout + 3;
     pa.nE = 3 * n * L;
+    pa.lmax = fwd16 ? (int32_t*)(ws + w.status) + 17 : nullptr;   // scale of the mu operand
     const int psmem = ((QP_NLP + pl->p.energy_nt) * 8 + 15) / 16 * 16 + (3 * pl->c.n_readout + 3) * 4;
     qpd::dense_point_kernel<<<pl->blocks_grad, 256, psmem, s>>>(pa);
     launches += 1;
@@ -688,7 +709,7 @@ static qp_status dense_loss_grad(qp_plan* pl, const float* d_params, const float
   wa.status = (int32_t*)(ws + w.status);
   if (pl->prof_start && !fused) cudaEventRecord(pl->prof_start, s);
   wa.scal = (const int32_t*)(ws + w.status) + 16;
-  if (fused)   // the fused forward recorded both operand ranges: FP16 pairs
+  if (fwd16)   // the forward recorded both operand ranges: FP16 pairs
     qpd::dense_wgrad_gemm_kernel<true><<<wgm.tiles * wgm.ngroups, qpd::WG_THREADS, qpd::wg_smem_bytes(n, true), s>>>(wa);
   else
     qpd::dense_wgrad_gemm_kernel<false><<<wgm.tiles * wgm.ngroups, qpd::WG_THREADS, qpd::wg_smem_bytes(n), s>>>(wa);
@@ -775,7 +796,13 @@ static qp_status dense_loss_grad(qp_plan* pl, const float* d_params, const float
           const int64_t ppt = qpd::TM / ga.nv;
           const int64_t ntiles = (npts[set] + ppt - 1) / ppt;
           const int gblocks = (int)(ntiles < pl->sm_count ? ntiles : pl->sm_count);
-          qpd::dense_row_gemm_kernel<1><<<gblocks, 128, qpd::gemm_smem_bytes(n, 1), s>>>(ga);
+          const int64_t items = ntiles * (dim / 256);   // (tile, column chunk) items
+          const int iblocks = (int)(items < pl->sm_count ? items : pl->sm_count);
+          if (fwd16)
+            qpd::dense_row16_kernel<1><<<iblocks, qpd::F16_THREADS, qpd::row16_smem_bytes(), s>>>(
+                ga, (const __half*)(ws + w.dWT), (int32_t*)(ws + w.status) + 16);
+          else
+            qpd::dense_row_gemm_kernel<1><<<gblocks, 128, qpd::gemm_smem_bytes(n, 1), s>>>(ga);
           launches += 1;
         }
         base += npts[set];
@@ -819,7 +846,9 @@ qp_status qp_forward(qp_plan* pl, const float* d_params, const float* d_pts, int
     qpd::BuildArgs ba = {};
     ba.params = d_params; ba.circ_off = pl->circ_off; ba.n = n; ba.L = pl->c.n_layers;
     ba.ansatz = pl->c.ansatz; ba.enc = pl->c.enc; ba.W = (float*)(ws + w.dW); ba.U = nullptr;
-    ba.W16 = nullptr;
+    const bool fwd16 = n >= 7 && pl->operands == QP_OPERANDS_FP16_PAIRS;
+    ba.W16 = fwd16 ? (__half*)(ws + w.dW16) : nullptr;
+    if (fwd16) ba.W = nullptr;
     ba.gates = (double2*)(ws + w.dgates);
     qpd::dense_gates_kernel<<<1, pl->c.n_layers * n, 0, s>>>(ba);
     qpd::dense_build_kernel<<<dim, 128, 2 * dim * 16, s>>>(ba);
@@ -830,8 +859,14 @@ qp_status qp_forward(qp_plan* pl, const float* d_params, const float* d_pts, int
     const int64_t ppt = qpd::TM / ga.nv;
     const int64_t ntiles = (B + ppt - 1) / ppt;
     const int gblocks = (int)(ntiles < pl->sm_count ? ntiles : pl->sm_count);
+    const int64_t items = ntiles * ((2 * dim) / 256);   // (tile, column chunk) items
+    const int iblocks = (int)(items < pl->sm_count ? items : pl->sm_count);
     if (pl->prof_start) cudaEventRecord(pl->prof_start, s);
-    qpd::dense_row_gemm_kernel<0><<<gblocks, 128, qpd::gemm_smem_bytes(n, 0), s>>>(ga);
+    if (fwd16)
+      qpd::dense_row16_kernel<0><<<iblocks, qpd::F16_THREADS, qpd::row16_smem_bytes(), s>>>(
+          ga, (const __half*)(ws + w.dW16), nullptr);
+    else
+      qpd::dense_row_gemm_kernel<0><<<gblocks, 128, qpd::gemm_smem_bytes(n, 0), s>>>(ga);
     if (pl->prof_stop) cudaEventRecord(pl->prof_stop, s);
     qpd::ReadoutArgs ra;
     ra.phi = ga.phi; ra.head = d_params + pl->head_off; ra.n = n; ra.m = pl->c.n_readout;

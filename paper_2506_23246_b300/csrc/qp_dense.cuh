@@ -506,6 +506,346 @@ __global__ void __launch_bounds__(128, 1) dense_row_gemm_kernel(GemmArgs a) {
   if (warp == 0) qptc::tmem_dealloc(tmem, tcols);
 }
 
+// ------------------------------------------------------------------------- row GEMMs, FP16 pairs
+// Row contractions for n = 9, 10 (and the forward of qp_forward for n >= 7) on FP16 operand
+// pairs, one 128-row tile of (point, vector) rows x 256 output columns at a time, K in
+// 32-wide stages:
+//   MODE 0, forward: Phi = R W^T, K = 2^n. W16 holds FP16 pairs of 2^14 W (the build); each
+//     generated row of R is scaled by a power of two 2^(13-e) bounding it (|R_0| <= 1,
+//     |R_d| <= sum_q |J_q,d| / 2). The largest bound goes to scal[0] (atomic maximum of the
+//     float bits) for the weight gradient's operand scale.
+//   MODE 1, back-projection: mu = Re(U'^H lambda) = Lambda W, K = 2^(n+1), N = 2^n. The B
+//     operand is WT16 (FP16 pairs of 2^14 U'^T from the build); the costate rows are scaled by
+//     one power of two from their largest magnitude, recorded by the pointwise stage.
+// x = hi + lo to ~2^-22 for every operand.
+//
+// The tensor core adds each instruction's partial products into the FP32 accumulator with a
+// truncating alignment, an error of up to one accumulator ulp per instruction that does not
+// average out over K. The large hi*hi products therefore go to one accumulator and the small
+// hi*lo + lo*hi corrections to a second (both 256 columns: the whole tensor memory), K / 16
+// truncations instead of 3K / 16 on the result; the epilogue adds the two in FP32 and unscales.
+//
+// Warp roles: eight stager warps generate (MODE 0: two threads per row, one half of each
+// 32-wide K stage) or load (MODE 1: coalesced, eight threads per row) the A operand, pack it
+// into FP16 pairs and run the epilogue (warps w and w + 4 drain the two column halves of
+// tensor-memory lanes 32 (w % 4) ..); a producer thread streams the B blocks by bulk copies as
+// soon as a stage's tensor-core work is done; an MMA thread issues a stage's MMAs as soon as
+// its A and B are in shared memory, so several stages of MMAs stay queued.
+constexpr int F16_ST = 4;                            // pipeline stages
+constexpr int F16_STAGERS = 256;                     // 8 stager warps
+constexpr int F16_THREADS = F16_STAGERS + 64;        // + producer warp + MMA warp
+constexpr int F16_ABYTES = TM * HKC * 2;             // one A half (hi or lo) of a stage
+constexpr int F16_WBYTES = 256 * HKC * 2;            // one B half
+constexpr int F16_STAGE = 2 * F16_ABYTES + 2 * F16_WBYTES;
+__host__ __device__ inline int row16_smem_bytes() { return F16_ST * F16_STAGE + 128; }
+
+// B operand block of iteration (column chunk c, K stage kc) into one stage (both halves).
+template <int MODE>
+__device__ __forceinline__ void row16_copy_b(const __half* B16, int dim, int ncc, int c, int kc, unsigned char* sW,
+                                             uint64_t* bar) {
+  qptc::mbar_arrive_expect_tx(bar, 2 * F16_WBYTES);
+  if (MODE == 0) {
+    // [K stage][column chunk][hi, lo][256 x HKC]
+    qptc::bulk_g2s(sW, B16 + ((int64_t)kc * ncc + c) * 2 * (256 * HKC), 2 * F16_WBYTES, bar);
+  } else {
+    // [K stage][hi, lo][dim x HKC]: rows 256 c .. 256 c + 255 of each half
+    const __half* blk = B16 + (int64_t)kc * 2 * (dim * HKC) + (int64_t)c * (256 * HKC);
+    qptc::bulk_g2s(sW, blk, F16_WBYTES, bar);
+    qptc::bulk_g2s(sW + F16_WBYTES, blk + (int64_t)dim * HKC, F16_WBYTES, bar);
+  }
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(F16_THREADS, 1) dense_row16_kernel(GemmArgs a, const __half* B16, int32_t* scal) {
+  extern __shared__ __align__(1024) unsigned char sm[];
+  const int n = a.n, dim = 1 << n;
+  const int ktot = MODE == 0 ? dim : 2 * dim, ntot = MODE == 0 ? 2 * dim : dim;
+  const int ncc = ntot / 256, nkc = ktot / HKC, high = n - 5;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  constexpr int NSW = F16_STAGERS / 32;
+  uint64_t* a_full = reinterpret_cast<uint64_t*>(sm + F16_ST * F16_STAGE);  // [ST] stager warps
+  uint64_t* w_full = a_full + F16_ST;                                         // [ST] bulk copies
+  uint64_t* mma_done = w_full + F16_ST;                                       // [ST] commit
+  uint64_t* acc_full = mma_done + F16_ST;                                     // chunk's MMAs done
+  uint64_t* acc_free = acc_full + 1;                                          // chunk drained
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(acc_free + 1);
+  if (warp == 0) qptc::tmem_alloc(tslot, 512);
+  if (tid == 0) {
+    for (int i = 0; i < F16_ST; ++i) {
+      qptc::mbar_init(&a_full[i], NSW);
+      qptc::mbar_init(&w_full[i], 1);
+      qptc::mbar_init(&mma_done[i], 1);
+    }
+    qptc::mbar_init(acc_full, 1);
+    qptc::mbar_init(acc_free, NSW);
+  }
+  qptc::fence_before();
+  __syncthreads();
+  qptc::fence_after();
+  const uint32_t tmem = *tslot;
+  const uint32_t t_main = tmem, t_corr = tmem + 256;
+
+  // rows of a tile: nv = 4 -> 32 points x 4 vectors (row = vector * 32 + point), nv = 1 -> 128
+  // points. Work items are (tile, column chunk) pairs, item = tile * ncc + chunk, dealt round
+  // robin: the CTAs holding the chunks of one tile run at the same time, so the tile's rows are
+  // read from HBM once (MODE 1) and its other reads hit L2. An item is nkc K stages.
+  const int ppt = TM / a.nv;
+  const int64_t ntiles = (a.npts + ppt - 1) / ppt;
+  const int64_t nitems = ntiles * ncc;
+  const int my_items = blockIdx.x < nitems ? (int)((nitems - 1 - blockIdx.x) / gridDim.x) + 1 : 0;
+  const int total = my_items * nkc;   // iterations of this CTA
+  bool ok = true;
+
+  if (warp == NSW) {
+    // ---- producer thread: the B block of iteration j once the MMAs of j - ST are done
+    if (lane == 0) {
+      int ji = 0, jk = 0;   // (item of this CTA, K stage) of iteration j
+      int nj = 0;           // copies issued
+      for (int j = 0; j < total && ok; ++j) {
+        if (j >= F16_ST) ok = qptc::mbar_wait(&mma_done[j % F16_ST], (uint32_t)((j - F16_ST) / F16_ST) & 1);
+        if (!ok) break;
+        const int cj = (int)((blockIdx.x + (int64_t)ji * gridDim.x) % ncc);
+        row16_copy_b<MODE>(B16, dim, ncc, cj, jk, sm + (j % F16_ST) * F16_STAGE + 2 * F16_ABYTES, &w_full[j % F16_ST]);
+        nj = j + 1;
+        if (++jk == nkc) { jk = 0; ++ji; }
+      }
+      if (!ok) {
+        atomicExch(a.status, 6);
+        // let this CTA's bulk copies land before exiting (the last ST issued at most)
+        for (int j = nj - F16_ST < 0 ? 0 : nj - F16_ST; j < nj; ++j)
+          qptc::mbar_wait(&w_full[j % F16_ST], (uint32_t)(j / F16_ST) & 1);
+      }
+    }
+  } else if (warp == NSW + 1) {
+    // ---- MMA thread: a stage's MMAs as soon as its operands are in shared memory
+    if (lane == 0) {
+      const uint32_t id = qptc::idesc(0, TM, 256);
+      int last_commit = -1;
+      int kc = 0, chunk = 0;
+      for (int it = 0; it < total && ok; ++it) {
+        const uint32_t st = (uint32_t)(it % F16_ST), ph = (uint32_t)(it / F16_ST) & 1;
+        if (kc == 0 && chunk > 0) ok = qptc::mbar_wait(acc_free, (uint32_t)(chunk - 1) & 1);
+        if (ok) ok = qptc::mbar_wait(&a_full[st], ph);
+        if (ok) ok = qptc::mbar_wait(&w_full[st], ph);
+        if (!ok) break;
+        qptc::fence_after();
+        const uint32_t sa = qptc::smem_u32(sm + st * F16_STAGE), sw = sa + 2 * F16_ABYTES;
+#pragma unroll
+        for (int ks = 0; ks < HKC / 16; ++ks) {
+          const uint64_t ah = qptc::desc_kmajor(sa + ks * 256, 128, (HKC / 8) * 128);
+          const uint64_t al = qptc::desc_kmajor(sa + F16_ABYTES + ks * 256, 128, (HKC / 8) * 128);
+          const uint64_t wh = qptc::desc_kmajor(sw + ks * 256, 128, (HKC / 8) * 128);
+          const uint64_t wl = qptc::desc_kmajor(sw + F16_WBYTES + ks * 256, 128, (HKC / 8) * 128);
+          const uint32_t acc = (kc > 0 || ks > 0) ? 1u : 0u;
+          qptc::mma_f16(t_main, ah, wh, id, acc);
+          qptc::mma_f16(t_corr, ah, wl, id, acc);
+          qptc::mma_f16(t_corr, al, wh, id, 1u);
+        }
+        qptc::commit(&mma_done[st]);
+        if (kc == nkc - 1) qptc::commit(acc_full);
+        last_commit = it;
+        if (++kc == nkc) { kc = 0; ++chunk; }
+      }
+      if (!ok) {
+        atomicExch(a.status, 6);
+        // let this CTA's tensor-core operations finish before tensor memory is freed
+        if (last_commit >= 0)
+          qptc::mbar_wait(&mma_done[last_commit % F16_ST], (uint32_t)(last_commit / F16_ST) & 1);
+      }
+    }
+  } else {
+    // ---- stager warps: tile row r (tensor-memory lane), half h of every K stage
+    const int r = tid & (TM - 1), h = tid >> 7;
+    const int s = a.nv == 4 ? r >> 5 : 0;
+    const int prow = a.nv == 4 ? lane : r;
+    const float sL = MODE == 1 ? pow2_scale(__int_as_float(__ldg(scal + 1))) : 1.f;
+    float Lo[MODE == 0 ? 16 : 1], Lod[MODE == 0 ? 16 : 1];
+    float hc[QP_MAXQ - 5], hsn[QP_MAXQ - 5], hj[QP_MAXQ - 5];
+    // MODE 1 loads: instruction i of warp w reads tile rows lr(i) = 4 (4 w + i) + lane / 8, four
+    // floats each at K offset 4 (lane % 8): 4 rows x 128 contiguous bytes per instruction.
+    // Costate chunks of the next two iterations (even / odd iteration; two named arrays with
+    // constant indices stay in registers).
+    float4 pf0[MODE == 1 ? 4 : 1], pf1[MODE == 1 ? 4 : 1];
+    auto lrow = [&](int i) { return 4 * (4 * warp + i) + (lane >> 3); };
+    // costate chunk of tile row lr, iteration (item ki of this CTA, K stage kcj) (clamped for a
+    // ragged tile)
+    auto lam_src = [&](int ki, int kcj, int lr) -> const float4* {
+      const int64_t tile = (blockIdx.x + (int64_t)ki * gridDim.x) / ncc;
+      const int ls = a.nv == 4 ? lr >> 5 : 0;
+      int64_t pj = tile * ppt + (a.nv == 4 ? (lr & 31) : lr);
+      if (pj >= a.npts) pj = a.npts - 1;
+      return reinterpret_cast<const float4*>(a.lam + ((a.pt_base + pj) * 4 + ls) * (int64_t)ktot + kcj * HKC +
+                                             4 * (lane & 7));
+    };
+    // prefetch cursor (item, K stage) two iterations ahead of the current one
+    int pki = 0, pkc = 0;
+    auto adv = [&](int& ki, int& kk) {
+      if (++kk == nkc) { kk = 0; ++ki; }
+    };
+    if (MODE == 1) {
+      if (total > 0) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) pf0[i] = __ldg(lam_src(pki, pkc, lrow(i)));
+        adv(pki, pkc);
+      }
+      if (total > 1) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) pf1[i] = __ldg(lam_src(pki, pkc, lrow(i)));
+        adv(pki, pkc);
+      }
+    }
+    float rs = sL, unsc = 1.f;
+    bool active = false;
+    int64_t row = 0;
+    int ki = 0, c = 0, kc = 0;
+    for (int it = 0; it < total && ok; ++it) {
+      const uint32_t st = (uint32_t)(it % F16_ST);
+      if (kc == 0) {
+        // a new item: its tile row, column chunk and (MODE 0) the tables of the row's product
+        // state and its scale
+        const int64_t item = blockIdx.x + (int64_t)ki * gridDim.x;
+        const int64_t tile = item / ncc;
+        c = (int)(item % ncc);
+        const int64_t p = tile * ppt + prow;
+        active = p < a.npts;
+        const int64_t pc = active ? p : a.npts - 1;
+        row = (a.pt_base + pc) * 4 + s;
+        if (MODE == 0) {
+          const float4* tj = reinterpret_cast<const float4*>(a.thetaJ) + (a.pt_base + pc) * n;
+          float jsum = 0.f;
+#pragma unroll
+          for (int t = 0; t < 16; ++t) { Lo[t] = 1.f; Lod[t] = 0.f; }
+          for (int b = 0; b < 5; ++b) {
+            const float4 tq = tj[n - 1 - b];
+            float sn, cs;
+            sincosf(0.5f * tq.x, &sn, &cs);
+            const float J = s == 1 ? tq.y : (s == 2 ? tq.z : tq.w);
+            jsum += fabsf(J);
+#pragma unroll
+            for (int t = 0; t < 16; ++t) {
+              const bool bit = ((16 * h + t) >> b) & 1;
+              const float f = bit ? sn : cs, d = bit ? 0.5f * cs : -0.5f * sn;
+              Lod[t] = Lod[t] * f + Lo[t] * d * J;
+              Lo[t] *= f;
+            }
+          }
+#pragma unroll
+          for (int q = 0; q < QP_MAXQ - 5; ++q) {
+            hc[q] = 1.f; hsn[q] = 0.f; hj[q] = 0.f;
+            if (q < high) {
+              const float4 tq = tj[q];
+              sincosf(0.5f * tq.x, &hsn[q], &hc[q]);
+              hj[q] = s == 1 ? tq.y : (s == 2 ? tq.z : tq.w);
+              jsum += fabsf(hj[q]);
+            }
+          }
+          const float bound = s == 0 ? 1.f : 0.5f * jsum;
+          rs = pow2_scale(bound);
+          if (scal && h == 0) {
+            float bm = active ? bound : 0.f;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) bm = fmaxf(bm, __shfl_xor_sync(0xffffffffu, bm, o));
+            if (lane == 0 && bm > 0.f) atomicMax(scal, __float_as_int(bm));
+          }
+        }
+        unsc = 1.f / (rs * W16_SCALE);
+      }
+      float v[HKC / 2];
+      if (MODE == 0) {
+        // high-bit factor of this K stage (qubit q <-> bit high-1-q of kc) and its derivative,
+        // with the row's scale folded in
+        float H = rs, Hd = 0.f;
+#pragma unroll
+        for (int q = 0; q < QP_MAXQ - 5; ++q) {
+          if (q < high) {
+            const bool bit = (kc >> (high - 1 - q)) & 1;
+            const float f = bit ? hsn[q] : hc[q], d = bit ? 0.5f * hc[q] : -0.5f * hsn[q];
+            Hd = Hd * f + H * d * hj[q];
+            H *= f;
+          }
+        }
+#pragma unroll
+        for (int t = 0; t < HKC / 2; ++t) v[t] = s == 0 ? H * Lo[t] : Hd * Lo[t] + H * Lod[t];
+      } else {
+        const bool odd = it & 1;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const float4 x = odd ? pf1[i] : pf0[i];
+          v[4 * i] = x.x * rs; v[4 * i + 1] = x.y * rs; v[4 * i + 2] = x.z * rs; v[4 * i + 3] = x.w * rs;
+        }
+        if (it + 2 < total) {   // the slot is free again: the chunk two iterations ahead
+          if (odd) {
+#pragma unroll
+            for (int i = 0; i < 4; ++i) pf1[i] = __ldg(lam_src(pki, pkc, lrow(i)));
+          } else {
+#pragma unroll
+            for (int i = 0; i < 4; ++i) pf0[i] = __ldg(lam_src(pki, pkc, lrow(i)));
+          }
+          adv(pki, pkc);
+        }
+      }
+      // the stage's A region is free once the MMAs of iteration it - ST have finished
+      bool good = true;
+      if (it >= F16_ST) good = qptc::mbar_wait(&mma_done[st], (uint32_t)((it - F16_ST) / F16_ST) & 1);
+      ok = __all_sync(0xffffffffu, good);
+      if (!ok) break;
+      unsigned char* sA = sm + st * F16_STAGE;
+      if (MODE == 0) {
+#pragma unroll
+        for (int g8 = 0; g8 < HKC / 16; ++g8) {
+          uint4 h8, l8;
+          pack_h8(v + 8 * g8, 1.f, h8, l8);
+          const uint32_t off = core_off_h(r, h * (HKC / 2) + g8 * 8);
+          *reinterpret_cast<uint4*>(sA + off) = h8;
+          *reinterpret_cast<uint4*>(sA + F16_ABYTES + off) = l8;
+        }
+      } else {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          uint4 h8, l8;   // only the first half of the eight-value pack is used
+          float w8[8] = {v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3], 0.f, 0.f, 0.f, 0.f};
+          pack_h8(w8, 1.f, h8, l8);
+          const uint32_t off = core_off_h(lrow(i), 4 * (lane & 7));
+          *reinterpret_cast<uint2*>(sA + off) = make_uint2(h8.x, h8.y);
+          *reinterpret_cast<uint2*>(sA + F16_ABYTES + off) = make_uint2(l8.x, l8.y);
+        }
+      }
+      qptc::fence_proxy_async();
+      __syncwarp();
+      if (lane == 0) qptc::mbar_arrive(&a_full[st]);
+      if (kc == nkc - 1) {
+        // epilogue of this column chunk: both accumulators back, summed, unscaled (this
+        // thread: its row, column half h)
+        ok = __all_sync(0xffffffffu, qptc::mbar_wait(acc_full, (uint32_t)ki & 1));
+        if (!ok) break;
+        qptc::fence_after();
+        float* orow = (MODE == 0 ? reinterpret_cast<float*>(a.phi) : a.mu) + row * (int64_t)ntot + c * 256 + h * 128;
+        const uint32_t lanes = (uint32_t)((warp & 3) * 32) << 16;
+        for (int c0 = 0; c0 < 128; c0 += 32) {
+          float vm[32], vc[32];
+          qptc::tmem_ld32(t_main + lanes + h * 128 + c0, vm);
+          qptc::tmem_ld32(t_corr + lanes + h * 128 + c0, vc);
+          if (active) {
+            float4* dst = reinterpret_cast<float4*>(orow + c0);
+#pragma unroll
+            for (int e = 0; e < 8; ++e)
+              dst[e] = make_float4((vm[4 * e] + vc[4 * e]) * unsc, (vm[4 * e + 1] + vc[4 * e + 1]) * unsc,
+                                   (vm[4 * e + 2] + vc[4 * e + 2]) * unsc, (vm[4 * e + 3] + vc[4 * e + 3]) * unsc);
+          }
+        }
+        qptc::fence_before();
+        __syncwarp();
+        if (lane == 0) qptc::mbar_arrive(acc_free);   // the accumulators are free for the next item
+      }
+      if (++kc == nkc) { kc = 0; ++ki; }
+    }
+    if (!ok && lane == 0) atomicExch(a.status, 6);
+  }
+  qptc::fence_before();
+  __syncthreads();
+  if (warp == 0) qptc::tmem_dealloc(tmem, 512);
+}
+
 // ------------------------------------------------------------------------- readout + head
 struct ReadoutArgs {
   const float2* phi;
@@ -527,6 +867,7 @@ __global__ void dense_readout_kernel(ReadoutArgs a) {
     float z[QP_MAXQ], dz[3][QP_MAXQ];
 #pragma unroll
     for (int i = 0; i < QP_MAXQ; ++i) { z[i] = 0.f; dz[0][i] = dz[1][i] = dz[2][i] = 0.f; }
+#pragma unroll 4
     for (int k = lane; k < dim; k += 32) {
       const float2 f0 = ph[k];
       const float pr = f0.x * f0.x + f0.y * f0.y;
@@ -598,6 +939,7 @@ struct PointArgs {
   double* blk_loss;
   float* blk_grad;
   int32_t loss_stride, grad_stride, nE;
+  int32_t* lmax;          // float bits of the largest |lambda| component (atomic maximum), or null
 };
 
 __global__ void dense_point_kernel(PointArgs a) {
@@ -622,6 +964,7 @@ __global__ void dense_point_kernel(PointArgs a) {
     float z[QP_MAXQ], dz[3][QP_MAXQ];
 #pragma unroll
     for (int i = 0; i < QP_MAXQ; ++i) { z[i] = 0.f; dz[0][i] = dz[1][i] = dz[2][i] = 0.f; }
+#pragma unroll 4
     for (int k = lane; k < dim; k += 32) {
       const float2 f0 = ph[k];
       const float pr = f0.x * f0.x + f0.y * f0.y;
@@ -689,11 +1032,16 @@ __global__ void dense_point_kernel(PointArgs a) {
     if (lane == 0) {
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
-        for (int i = 0; i < m; ++i)
-          atomicAdd(&hacc[c * m + i], g[c] * z[i] + gD[c][0] * dz[0][i] + gD[c][1] * dz[1][i] + gD[c][2] * dz[2][i]);
+        // constant indices keep z and dz in registers
+#pragma unroll
+        for (int i = 0; i < QP_MAXQ; ++i)
+          if (i < m)
+            atomicAdd(&hacc[c * m + i], g[c] * z[i] + gD[c][0] * dz[0][i] + gD[c][1] * dz[1][i] + gD[c][2] * dz[2][i]);
         atomicAdd(&hacc[3 * m + c], g[c]);
       }
     }
+    float lm = 0.f;
+#pragma unroll 4
     for (int k = lane; k < dim; k += 32) {
       float O = 0.f, Od[3] = {0.f, 0.f, 0.f};
 #pragma unroll
@@ -712,10 +1060,18 @@ __global__ void dense_point_kernel(PointArgs a) {
           const float2 fd = ph[(1 + d) * dim + k];
           lam.x += Od[d] * fd.x;
           lam.y += Od[d] * fd.y;
-          ph[(1 + d) * dim + k] = make_float2(Od[d] * f0.x, Od[d] * f0.y);
+          const float2 ld = make_float2(Od[d] * f0.x, Od[d] * f0.y);
+          ph[(1 + d) * dim + k] = ld;
+          lm = fmaxf(lm, fmaxf(fabsf(ld.x), fabsf(ld.y)));
         }
       }
       ph[k] = lam;
+      lm = fmaxf(lm, fmaxf(fabsf(lam.x), fabsf(lam.y)));
+    }
+    if (a.lmax) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) lm = fmaxf(lm, __shfl_xor_sync(0xffffffffu, lm, o));
+      if (lane == 0 && lm > 0.f) atomicMax(a.lmax, __float_as_int(lm));
     }
   }
   __syncthreads();

@@ -76,7 +76,8 @@ __host__ __device__ inline WgSmem wg_smem(int n, int esz = 4) {
   w.raw = o; o += WG_RING * WKC * 256 * 4;           // costate columns of a step [16][256]
   w.fac = o; o += 2 * WG_FAC4 * 16;
   w.tab = o; o += 2 * WG_TAB4 * 16;
-  w.bars = o; o += 128;  // mma_done[2], raw_full[4], stage_full[2], raw_free[4], acc_free, tmem slot
+  // mma_done[2], raw_full[4], stage_full[2], raw_free[4], acc_free, tab_full[2], tab_free[2], tmem slot
+  w.bars = o; o += 192;
   w.total = o;
   return w;
 }
@@ -205,7 +206,9 @@ __global__ void __launch_bounds__(WG_THREADS, 1) dense_wgrad_gemm_kernel(WgArgs 
   uint64_t* stage_full = bars + 6;    // [2]  A and B operands of a stage written (16 warps)
   uint64_t* raw_free = bars + 8;      // [4]  ring slot read by the B-group (8 warps)
   uint64_t* acc_free = bars + 12;     // accumulator flushed (16 warps)
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + L.bars + 104);
+  uint64_t* tab_full = bars + 13;     // [2]  tables of a step written (A-group, 8 warps)
+  uint64_t* tab_free = bars + 15;     // [2]  tables of a step read by the B-group (8 warps)
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + L.bars + 136);
   float* raw = reinterpret_cast<float*>(sm + L.raw);
   float4* facb = reinterpret_cast<float4*>(sm + L.fac);
   float4* tabb = reinterpret_cast<float4*>(sm + L.tab);
@@ -217,6 +220,7 @@ __global__ void __launch_bounds__(WG_THREADS, 1) dense_wgrad_gemm_kernel(WgArgs 
     for (int i = 6; i < 8; ++i) qptc::mbar_init(&bars[i], NSW);        // stage_full: all staging warps
     for (int i = 8; i < 12; ++i) qptc::mbar_init(&bars[i], NSW / 2);   // raw_free: B-group warps
     qptc::mbar_init(&bars[12], NSW);                                   // acc_free: all staging warps
+    for (int i = 13; i < 17; ++i) qptc::mbar_init(&bars[i], NSW / 2);  // tab_full, tab_free
   }
   qptc::fence_before();
   __syncthreads();
@@ -226,6 +230,8 @@ __global__ void __launch_bounds__(WG_THREADS, 1) dense_wgrad_gemm_kernel(WgArgs 
   const int64_t c0 = (int64_t)lb * nkc / a.ngroups, c1 = (int64_t)(lb + 1) * nkc / a.ngroups;
   const bool agrp = tid < WG_STAGERS / 2;   // A-group: R tables and A operand; B-group: costates
   const int kk = tid & (TM - 1), khalf = (tid >> 7) & 1;
+  // two M sub-tiles: the B-group writes the second one's A operand from the same tables
+  const bool bsplit = msub == 2;
   int64_t last_commit = -1, last_copy = -1;
   WgAng tjn{};  // A-group: angles of step c0 + it + 2
   if (c0 < c1) {
@@ -371,7 +377,7 @@ __global__ void __launch_bounds__(WG_THREADS, 1) dense_wgrad_gemm_kernel(WgArgs 
           const int e = kk & 31;
 #pragma unroll
           for (int u = 0; u < 2; ++u) {
-            if (u < msub) {
+            if (u < (bsplit ? 1 : msub)) {
               const int j = (u * TM + kk) >> 5;
               float av[8];
               if (set == 0) {
@@ -414,12 +420,18 @@ __global__ void __launch_bounds__(WG_THREADS, 1) dense_wgrad_gemm_kernel(WgArgs 
               }
             }
           }
-          // tables of the next step, factors of the step after
+          // tables of the next step (their buffer held the tables of step it - 1, which the
+          // B-group may still be reading), factors of the step after
           if (kc + 1 < c1) {
             int set1, ppc1, nv1;
             int64_t p01;
             wg_step_geom(a, kc + 1, set1, p01, ppc1, nv1);
-            wg_tables(facb + ((it + 1) & 1) * WG_FAC4, tabb + ((it + 1) & 1) * WG_TAB4, tid, n, ppc1, kbase, nj);
+            if (bsplit && it >= 1) good = qptc::mbar_wait(&tab_free[(it + 1) & 1], ((it - 1) >> 1) & 1);
+            if (good) wg_tables(facb + ((it + 1) & 1) * WG_FAC4, tabb + ((it + 1) & 1) * WG_TAB4, tid, n, ppc1, kbase, nj);
+            if (bsplit) {
+              __syncwarp();
+              if (lane == 0) qptc::mbar_arrive(&tab_full[(it + 1) & 1]);
+            }
           }
           if (kc + 2 < c1) {
             int set2, ppc2, nv2;
@@ -430,6 +442,60 @@ __global__ void __launch_bounds__(WG_THREADS, 1) dense_wgrad_gemm_kernel(WgArgs 
           }
         }
       } else {
+        if (bsplit) {
+          // A operand of the second M sub-tile from this step's tables (written by the A-group
+          // during the previous step; those of the first step before the loop)
+          if (good && it >= 1) good = qptc::mbar_wait(&tab_full[it & 1], ((it - 1) >> 1) & 1);
+          const int bo2 = tid - WG_STAGERS / 2;
+          const int k2 = bo2 & (TM - 1), h2 = bo2 >> 7;
+          const float4* tlo = tabb + (it & 1) * WG_TAB4;
+          const float4* thi = tlo + 16 * 32;
+          const int j = (TM + k2) >> 5, e = k2 & 31;
+          float av[8];
+          if (set == 0) {
+#pragma unroll
+            for (int pi = 0; pi < 2; ++pi) {
+              const int pl = h2 * 2 + pi;
+              const float4 h = thi[pl * 8 + j], l = tlo[pl * 32 + e];
+              av[4 * pi] = h.x * l.x;
+              av[4 * pi + 1] = h.y * l.x + h.x * l.y;
+              av[4 * pi + 2] = h.z * l.x + h.x * l.z;
+              av[4 * pi + 3] = h.w * l.x + h.x * l.w;
+            }
+          } else {
+#pragma unroll
+            for (int pi = 0; pi < 8; ++pi) {
+              const int pl = h2 * 8 + pi;
+              av[pi] = thi[pl * 8 + j].x * tlo[pl * 32 + e].x;
+            }
+          }
+          __syncwarp();
+          if (lane == 0) qptc::mbar_arrive(&tab_free[it & 1]);
+          if (good) {
+            if (H16) {
+              uint4 h8, l8;
+              pack_h8(av, sR, h8, l8);
+              unsigned char* Ab = sA + 2 * (TM * WKC * 2);
+              const uint32_t off = core_off_w16(k2, h2 * 8);
+              *reinterpret_cast<uint4*>(Ab + off) = h8;
+              *reinterpret_cast<uint4*>(Ab + TM * WKC * 2 + off) = l8;
+            } else {
+              float* Ahi = reinterpret_cast<float*>(sA + 2 * (TM * WKC * 4));
+              float* Alo = Ahi + TM * WKC;
+#pragma unroll
+              for (int g4 = 0; g4 < 2; ++g4) {
+                float4 h4, l4;
+                qptc::split_tf32_fast(av[4 * g4], h4.x, l4.x);
+                qptc::split_tf32_fast(av[4 * g4 + 1], h4.y, l4.y);
+                qptc::split_tf32_fast(av[4 * g4 + 2], h4.z, l4.z);
+                qptc::split_tf32_fast(av[4 * g4 + 3], h4.w, l4.w);
+                const uint32_t off = core_off16(k2, h2 * 8 + g4 * 4) / 4;
+                *reinterpret_cast<float4*>(Ahi + off) = h4;
+                *reinterpret_cast<float4*>(Alo + off) = l4;
+              }
+            }
+          }
+        }
         // this step's costate columns (bulk-copied three steps ahead): component bo, 16 rows
         const uint32_t rs = it % WG_RING;
         if (good) good = qptc::mbar_wait(&raw_full[rs], (it / WG_RING) & 1);

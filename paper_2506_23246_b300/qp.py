@@ -17,6 +17,7 @@ ENC = {"rx": 0, "ry": 1}
 SCALE = {"none": 0, "pi": 1, "bias": 2, "asin": 3, "acos": 4}
 PREMAP = {"direct": 0, "rff_mlp": 1}
 PATH = {"auto": 0, "simt": 1, "gemm_3xtf32": 2, "gemm_bf16x3": 3}
+OPERANDS = {"fp16_pairs": 0, "tf32_pairs": 1}
 NLOSS = 9
 STATUS = {0: "ok", 1: "invalid argument", 2: "unsupported configuration",
           3: "workspace missing or too small", 4: "CUDA error", 5: "non-finite loss",
@@ -87,6 +88,8 @@ def lib():
         L.qp_last_launch_count.restype = I32
         L.qp_plan_path.argtypes = [P]
         L.qp_plan_path.restype = I32
+        L.qp_plan_set_operands.argtypes = [P, I32]
+        L.qp_plan_set_operands.restype = I32
         L.qp_set_profile_events.argtypes = [P, P, P]
         L.qp_set_profile_events.restype = I32
         L.qp_sched_selftest.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_uint]
@@ -133,7 +136,7 @@ def _dev_f32(t, device, what):
 class Plan:
     """One circuit + problem configuration (qp_plan) with its device workspace."""
 
-    def __init__(self, circuit, problem=None, path="auto"):
+    def __init__(self, circuit, problem=None, path="auto", operands="fp16_pairs"):
         from . import workloads
         self.circuit = dict(circuit)
         self.problem = dict(problem or workloads.problem())
@@ -152,6 +155,8 @@ class Plan:
         _check(lib().qp_param_layout(self._h, lay), "qp_param_layout")
         self.layout = {"circuit": lay[0], "head": lay[1], "total": lay[2], "fixed": lay[3]}
         self.path = {1: "simt", 2: "gemm_3xtf32"}.get(lib().qp_plan_path(self._h), "?")
+        _check(lib().qp_plan_set_operands(self._h, OPERANDS[operands]), "qp_plan_set_operands")
+        self.operands = operands
 
     def __del__(self):
         h = getattr(self, "_h", None)

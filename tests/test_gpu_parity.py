@@ -38,9 +38,10 @@ def _rel(gpu, ref, floor=1e-12):
     return float(np.max(np.abs(gpu - ref))) / scale if ref.size else 0.0
 
 
-def _forward_check(torch, oracle, circ, params, pts, want_df=True, tol=TOL, path="simt"):
+def _forward_check(torch, oracle, circ, params, pts, want_df=True, tol=TOL, path="simt",
+                   operands="fp16_pairs"):
     from paper_2506_23246_b300 import qp
-    plan = qp.Plan(circ, path=path)
+    plan = qp.Plan(circ, path=path, operands=operands)
     dp = torch.tensor(params, device="cuda")
     dx = torch.tensor(pts, device="cuda")
     f, df = plan.forward(dp, dx, want_df=want_df)
@@ -100,25 +101,31 @@ def test_forward_rff_mlp_premap(torch_cuda, oracle):
                                           (8, 6, "strong_rot", "rx"), (9, 3, "strong_rot", "rx"),
                                           (10, 8, "strong_rot", "rx")])
 def test_dense_tensorcore_forward_parity(torch_cuda, oracle, n, L, ans, enc):
-    """Fused-unitary path (tcgen05, 3xTF32): fields and derivatives against the oracle, on a
-    ragged batch spanning several 128-row tiles. At 10 qubits the tensor core's FP32
-    accumulation over K = 1024 terms leaves a systematic ~1.2e-5 (rms ~ max) on the small,
-    concentrated outputs, so that size is held to 2e-5; the FP32 SIMT path stays at ~1e-6."""
+    """Fused-unitary path (tcgen05): fields and derivatives against the oracle, on a ragged
+    batch spanning several 128-row tiles, for both operand forms. The tensor core adds each
+    instruction's products into the FP32 accumulator with a truncating alignment (up to one
+    accumulator ulp per instruction, not averaging out): with 3xTF32 in one accumulator over
+    K = 1024 (3 x 128 instructions) that leaves a systematic ~1.2e-5 at 10 qubits, held to
+    2e-5 there. FP16 pairs (n >= 7) keep the hi*hi products (K / 16 instructions) apart from
+    the hi*lo + lo*hi corrections and hold 1e-5 at every size."""
     circ = W.circuit(n, L, n if ans != "basic_ryrz" else 3, ansatz=ans, enc=enc, scale="acos",
                      premap="rff_mlp", rff_freqs=16, mlp_width=8, mlp_depth=1)
     params = W.init_params(circ, n + 20)
     pts = W.uniform_points(301, 40 + n, 1.0)
-    tol = TOL if n <= 9 else 2e-5
-    _forward_check(torch_cuda, oracle, circ, params, pts, tol=tol, path="gemm_3xtf32")
-    _forward_check(torch_cuda, oracle, circ, params, pts[:77], want_df=False, tol=tol,
-                   path="gemm_3xtf32")
+    for ops in ("fp16_pairs", "tf32_pairs"):
+        tol = 2e-5 if (n == 10 and ops == "tf32_pairs") else TOL
+        _forward_check(torch_cuda, oracle, circ, params, pts, tol=tol, path="gemm_3xtf32",
+                       operands=ops)
+        _forward_check(torch_cuda, oracle, circ, params, pts[:77], want_df=False, tol=tol,
+                       path="gemm_3xtf32", operands=ops)
 
 
 # ----------------------------------------------------------------------------- loss + grad
 
-def _loss_grad_check(torch, oracle, circ, prob, params, sets, idx=None, tol=TOL, path="simt"):
+def _loss_grad_check(torch, oracle, circ, prob, params, sets, idx=None, tol=TOL, path="simt",
+                    operands="fp16_pairs"):
     from paper_2506_23246_b300 import qp
-    plan = qp.Plan(circ, prob, path=path)
+    plan = qp.Plan(circ, prob, path=path, operands=operands)
     dp = torch.tensor(params, device="cuda")
     dsets = {k: torch.tensor(v, device="cuda") for k, v in sets.items()}
     loss, grad = plan.loss_grad(dp, dsets)
@@ -213,6 +220,25 @@ def test_dense_tensorcore_c3_loss_grad_parity(torch_cuda, oracle, medium):
     mlp = rng.choice(np.arange(lay["fixed"], lay["circuit"]), 48, replace=False)
     idx = np.concatenate([np.arange(3), np.sort(mlp), np.arange(lay["circuit"], lay["total"])])
     _loss_grad_check(torch_cuda, oracle, circ, prob, params, sets, idx, path="gemm_3xtf32")
+
+
+@pytest.mark.parametrize("operands,tol", [("fp16_pairs", TOL), ("tf32_pairs", 3e-5)])
+def test_dense_tensorcore_c4_loss_grad_parity(torch_cuda, oracle, operands, tol):
+    """10 qubits, 8 strongly entangling layers, RFF(64) + tanh MLP(32): every circuit and head
+    parameter and a sample of MLP parameters. The MLP block goes through mu = Re(U'^H lambda)
+    with K = 2048: FP16 pairs with the hi*hi products in their own accumulator hold 1e-5;
+    3xTF32 in one accumulator (768 truncating additions per output) is held to 3e-5. The
+    circuit block goes through the weight gradient on the same operand form."""
+    circ = W.c3_circuit(10, 8)
+    prob = W.c3_problem("vacuum", 4, 4, 3)
+    sets = {"colloc": W.grid_points(4, 4, 3, 1.0), "ic": W.ic_grid(4, 2)}
+    params = W.init_params(circ, 0)
+    lay = oracle.param_layout(circ)
+    rng = np.random.default_rng(0)
+    mlp = rng.choice(np.arange(lay["fixed"], lay["circuit"]), 48, replace=False)
+    idx = np.concatenate([np.sort(mlp), np.arange(lay["circuit"], lay["total"])])
+    _loss_grad_check(torch_cuda, oracle, circ, prob, params, sets, idx, tol=tol,
+                     path="gemm_3xtf32", operands=operands)
 
 
 def test_dense_tensorcore_mlp_all_params(torch_cuda, oracle):
