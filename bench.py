@@ -38,7 +38,14 @@ def _args():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--path", default="auto", choices=["auto", "simt", "gemm_3xtf32"],
-                    help="statevector path of the library (auto = the library's choice)")
+                    help="statevector path of the library (auto = the library's choice; with "
+                         "--workload configs: every path the configuration has)")
+    ap.add_argument("--operands", default=None, choices=["fp16_pairs", "tf32_pairs"],
+                    help="--workload configs: only this tensor-core operand form")
+    ap.add_argument("--config", default=None, choices=["C1", "C2", "C3", "C4"],
+                    help="--workload configs: only this configuration")
+    ap.add_argument("--grid", type=int, default=64,
+                    help="--workload configs: C4 grid points per axis (64: the 64^3 grid)")
     ap.add_argument("--workload", default="c3", choices=["c3", "c5", "configs"],
                     help="c3: the full QPINN step (default); c5: 32 uneven instances in one "
                          "batched call against the same instances called one by one; configs: "
@@ -486,16 +493,21 @@ def run_configs(a):
     c1c, c1p, c1x = W.c1_workload(0, 1024)
     c2c, c2pr, c2p, c2s = W.c2_workload(0)
     c3c, c3pr, c3p, c3s = W.c3_workload(0)
-    c4c, c4pr, c4p, c4s = W.c4_workload(0)
+    c4c, c4pr, c4p, c4s = W.c4_workload(0, n=a.grid)
     cases = [("C1 4q/2L, 1024 points, forward + d/dx,dy,dt", c1c, None, c1p, {"pts": c1x},
               [("simt", "fp16_pairs")]),
              ("C2 6q/4L, 16384 colloc + 2048 IC + 2048 PEC, loss + gradient", c2c, c2pr, c2p, c2s,
               [("simt", "fp16_pairs")]),
              ("C3 8q/6L RFF64+MLP32 dielectric, 65536 colloc + 4096 IC, loss + gradient", c3c, c3pr,
               c3p, c3s, [("simt", "fp16_pairs"), ("gemm_3xtf32", "fp16_pairs")]),
-             ("C4 10q/8L RFF64+MLP32, 64^3 colloc + 4096 IC, loss + gradient", c4c, c4pr, c4p, c4s,
+             ("C4 10q/8L RFF64+MLP32, %d^3 colloc + %d IC, loss + gradient" % (a.grid, a.grid * a.grid),
+              c4c, c4pr, c4p, c4s,
               [("simt", "fp16_pairs"), ("gemm_3xtf32", "fp16_pairs"), ("gemm_3xtf32", "tf32_pairs")])]
     for name, circ, prob, params, sets, paths in cases:
+        if a.config and not name.startswith(a.config + " "):
+            continue
+        paths = [(p, o) for p, o in paths if (a.path == "auto" or p == a.path) and
+                 (a.operands is None or p == "simt" or o == a.operands)]
         n, L = circ["n_qubits"], circ["n_layers"]
         dp = torch.tensor(params, device=dev)
         dsets = {k: torch.tensor(v, device=dev) for k, v in sets.items()}

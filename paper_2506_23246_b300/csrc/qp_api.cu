@@ -660,10 +660,11 @@ static qp_status dense_loss_grad(qp_plan* pl, const float* d_params, const float
   } else {
     for (int set = 0; set < 3; ++set) {
       if (npts[set] > 0) {
-        qpd::GemmArgs ga;
+        qpd::GemmArgs ga = {};
         ga.thetaJ = (const float*)(ws + w.thetaJ); ga.W = (const float*)(ws + w.dW);
         ga.phi = (float2*)(ws + w.dphi); ga.n = n; ga.nv = set == 0 ? 4 : 1;
         ga.npts = npts[set]; ga.pt_base = base; ga.status = (int32_t*)(ws + w.status);
+        ga.cs = (const float2*)(ws + w.dcs);   // half-angle factors of the call
         const int64_t ppt = qpd::TM / ga.nv;
         const int64_t ntiles = (npts[set] + ppt - 1) / ppt;
         const int gblocks = (int)(ntiles < pl->sm_count ? ntiles : pl->sm_count);
@@ -788,7 +789,7 @@ static qp_status dense_loss_grad(qp_plan* pl, const float* d_params, const float
       base = 0;
       for (int set = 0; set < 3; ++set) {
         if (npts[set] > 0) {
-          qpd::GemmArgs ga;
+          qpd::GemmArgs ga = {};
           ga.thetaJ = (const float*)(ws + w.thetaJ); ga.W = (const float*)(ws + w.dWT);
           ga.phi = nullptr; ga.lam = (const float*)(ws + w.dphi); ga.mu = (float*)(ws + w.dmu);
           ga.n = n; ga.nv = set == 0 ? 4 : 1;
@@ -852,7 +853,7 @@ qp_status qp_forward(qp_plan* pl, const float* d_params, const float* d_pts, int
     ba.gates = (double2*)(ws + w.dgates);
     qpd::dense_gates_kernel<<<1, pl->c.n_layers * n, 0, s>>>(ba);
     qpd::dense_build_kernel<<<dim, 128, 2 * dim * 16, s>>>(ba);
-    qpd::GemmArgs ga;
+    qpd::GemmArgs ga = {};
     ga.thetaJ = (const float*)(ws + w.thetaJ); ga.W = (const float*)(ws + w.dW);
     ga.phi = (float2*)(ws + w.dphi); ga.n = n; ga.nv = d_dfields ? 4 : 1;
     ga.npts = B; ga.pt_base = 0; ga.status = (int32_t*)(ws + w.status);

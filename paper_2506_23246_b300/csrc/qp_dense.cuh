@@ -288,6 +288,7 @@ struct GemmArgs {
   int32_t* status;
   const float* lam;         // MODE 1: costate rows [P][4][2 dim] (A operand)
   float* mu;                // MODE 1: output rows [P][4][dim]
+  const float2* cs;         // [P][n] (cos, sin) of theta / 2, or null (computed from thetaJ)
 };
 
 // Output columns per chunk for the two modes: MODE 0 (forward) has 2 dim outputs over K = dim;
@@ -586,14 +587,26 @@ __global__ void __launch_bounds__(F16_THREADS, 1) dense_row16_kernel(GemmArgs a,
   const uint32_t t_main = tmem, t_corr = tmem + 256;
 
   // rows of a tile: nv = 4 -> 32 points x 4 vectors (row = vector * 32 + point), nv = 1 -> 128
-  // points. Work items are (tile, column chunk) pairs, item = tile * ncc + chunk, dealt round
-  // robin: the CTAs holding the chunks of one tile run at the same time, so the tile's rows are
-  // read from HBM once (MODE 1) and its other reads hit L2. An item is nkc K stages.
+  // points. Work items are (tile, column chunk) pairs; an item is nkc K stages.
+  //  - MODE 1 (and small MODE 0 grids): items tile * ncc + chunk dealt round robin, so the CTAs
+  //    holding the chunks of one tile run at the same time: the tile's costate rows are read
+  //    from HBM once and its other reads hit L2.
+  //  - MODE 0 with at least one tile per CTA: tiles dealt round robin, each CTA runs all
+  //    chunks of its tile in turn (the row's tables are built once per tile).
   const int ppt = TM / a.nv;
   const int64_t ntiles = (a.npts + ppt - 1) / ppt;
+  const bool tmaj = MODE == 0 && ntiles >= gridDim.x;
   const int64_t nitems = ntiles * ncc;
-  const int my_items = blockIdx.x < nitems ? (int)((nitems - 1 - blockIdx.x) / gridDim.x) + 1 : 0;
+  const int my_items = tmaj ? (blockIdx.x < ntiles ? (int)((ntiles - 1 - blockIdx.x) / gridDim.x) + 1 : 0) * ncc
+                            : (blockIdx.x < nitems ? (int)((nitems - 1 - blockIdx.x) / gridDim.x) + 1 : 0);
   const int total = my_items * nkc;   // iterations of this CTA
+  // (tile, column chunk) of item ki of this CTA
+  auto item_tile = [&](int ki) -> int64_t {
+    return tmaj ? blockIdx.x + (int64_t)(ki / ncc) * gridDim.x : (blockIdx.x + (int64_t)ki * gridDim.x) / ncc;
+  };
+  auto item_chunk = [&](int ki) -> int {
+    return tmaj ? ki % ncc : (int)((blockIdx.x + (int64_t)ki * gridDim.x) % ncc);
+  };
   bool ok = true;
 
   if (warp == NSW) {
@@ -604,7 +617,7 @@ __global__ void __launch_bounds__(F16_THREADS, 1) dense_row16_kernel(GemmArgs a,
       for (int j = 0; j < total && ok; ++j) {
         if (j >= F16_ST) ok = qptc::mbar_wait(&mma_done[j % F16_ST], (uint32_t)((j - F16_ST) / F16_ST) & 1);
         if (!ok) break;
-        const int cj = (int)((blockIdx.x + (int64_t)ji * gridDim.x) % ncc);
+        const int cj = item_chunk(ji);
         row16_copy_b<MODE>(B16, dim, ncc, cj, jk, sm + (j % F16_ST) * F16_STAGE + 2 * F16_ABYTES, &w_full[j % F16_ST]);
         nj = j + 1;
         if (++jk == nkc) { jk = 0; ++ji; }
@@ -670,7 +683,7 @@ __global__ void __launch_bounds__(F16_THREADS, 1) dense_row16_kernel(GemmArgs a,
     // costate chunk of tile row lr, iteration (item ki of this CTA, K stage kcj) (clamped for a
     // ragged tile)
     auto lam_src = [&](int ki, int kcj, int lr) -> const float4* {
-      const int64_t tile = (blockIdx.x + (int64_t)ki * gridDim.x) / ncc;
+      const int64_t tile = item_tile(ki);
       const int ls = a.nv == 4 ? lr >> 5 : 0;
       int64_t pj = tile * ppt + (a.nv == 4 ? (lr & 31) : lr);
       if (pj >= a.npts) pj = a.npts - 1;
@@ -698,19 +711,21 @@ __global__ void __launch_bounds__(F16_THREADS, 1) dense_row16_kernel(GemmArgs a,
     bool active = false;
     int64_t row = 0;
     int ki = 0, c = 0, kc = 0;
+    int64_t cur_tile = -1;
     for (int it = 0; it < total && ok; ++it) {
       const uint32_t st = (uint32_t)(it % F16_ST);
       if (kc == 0) {
-        // a new item: its tile row, column chunk and (MODE 0) the tables of the row's product
-        // state and its scale
-        const int64_t item = blockIdx.x + (int64_t)ki * gridDim.x;
-        const int64_t tile = item / ncc;
-        c = (int)(item % ncc);
+        // a new item: its column chunk; on a new tile its row and (MODE 0) the tables of the
+        // row's product state and its scale
+        const int64_t tile = item_tile(ki);
+        c = item_chunk(ki);
         const int64_t p = tile * ppt + prow;
         active = p < a.npts;
         const int64_t pc = active ? p : a.npts - 1;
         row = (a.pt_base + pc) * 4 + s;
-        if (MODE == 0) {
+        if (MODE == 0 && tile != cur_tile) {
+          cur_tile = tile;
+          const float2* csp = a.cs ? a.cs + (a.pt_base + pc) * n : nullptr;
           const float4* tj = reinterpret_cast<const float4*>(a.thetaJ) + (a.pt_base + pc) * n;
           float jsum = 0.f;
 #pragma unroll
@@ -718,7 +733,12 @@ __global__ void __launch_bounds__(F16_THREADS, 1) dense_row16_kernel(GemmArgs a,
           for (int b = 0; b < 5; ++b) {
             const float4 tq = tj[n - 1 - b];
             float sn, cs;
-            sincosf(0.5f * tq.x, &sn, &cs);
+            if (csp) {
+              const float2 q2 = csp[n - 1 - b];
+              cs = q2.x; sn = q2.y;
+            } else {
+              sincosf(0.5f * tq.x, &sn, &cs);
+            }
             const float J = s == 1 ? tq.y : (s == 2 ? tq.z : tq.w);
             jsum += fabsf(J);
 #pragma unroll
@@ -734,7 +754,12 @@ __global__ void __launch_bounds__(F16_THREADS, 1) dense_row16_kernel(GemmArgs a,
             hc[q] = 1.f; hsn[q] = 0.f; hj[q] = 0.f;
             if (q < high) {
               const float4 tq = tj[q];
-              sincosf(0.5f * tq.x, &hsn[q], &hc[q]);
+              if (csp) {
+                const float2 q2 = csp[q];
+                hc[q] = q2.x; hsn[q] = q2.y;
+              } else {
+                sincosf(0.5f * tq.x, &hsn[q], &hc[q]);
+              }
               hj[q] = s == 1 ? tq.y : (s == 2 ? tq.z : tq.w);
               jsum += fabsf(hj[q]);
             }
