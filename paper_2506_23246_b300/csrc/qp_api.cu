@@ -80,7 +80,12 @@ struct WsLayout {
 
 // Rows of (point, vector) accumulated per weight-gradient chunk (bounds the FP32 tensor-core
 // accumulation length; chunks are summed in FP64).
-int64_t wg_rows_per_chunk(int n) { return n <= 8 ? 512 : 4096; }
+// Rows accumulated in tensor memory before a flush. The tensor core adds each instruction's
+// products into the FP32 accumulator with a truncating alignment (about one accumulator ulp
+// per instruction, not averaging out), and the three FP16-pair products of a 16-row step go to
+// the same accumulator: 512 rows (96 instructions) keep the full-size weight gradient within
+// ~4e-6 of the FP32 SIMT path; 4096 rows reached 2e-5.
+int64_t wg_rows_per_chunk(int) { return 512; }
 
 // Weight-gradient launch geometry for `nkc` 16-row steps: tiles of min(256, 2^n) basis
 // indices x 256 components, CTA groups per tile (persistent CTAs, balanced step ranges),

@@ -145,7 +145,9 @@ __device__ __forceinline__ void wg_tables(const float4* fac, float4* tab, int ti
     }
     tlo[idx] = p;
   }
-  for (int idx = tid; idx < ppc * 8; idx += WG_STAGERS / 2) {
+  // the H entries start at the fifth warp of the group: the first four hold the Lo entries of
+  // a collocation step, so no warp builds both
+  for (int idx = (tid + WG_STAGERS / 4) & (WG_STAGERS / 2 - 1); idx < ppc * 8; idx += WG_STAGERS / 2) {
     const int pl = idx >> 3, j = idx & 7;
     if (j < nj) {
       const int kb = kbase + j * 32;
@@ -230,6 +232,9 @@ __global__ void __launch_bounds__(WG_THREADS, 1) dense_wgrad_gemm_kernel(WgArgs 
   const int64_t c0 = (int64_t)lb * nkc / a.ngroups, c1 = (int64_t)(lb + 1) * nkc / a.ngroups;
   const bool agrp = tid < WG_STAGERS / 2;   // A-group: R tables and A operand; B-group: costates
   const int kk = tid & (TM - 1), khalf = (tid >> 7) & 1;
+  // (point, qubit) slot of this thread for the angle loads and factors: the group's last warp
+  // first (a collocation step has 4 x n <= 32 of them), away from the warps building tables
+  const int fid = (tid + 32) & (WG_STAGERS / 2 - 1);
   // two M sub-tiles: the B-group writes the second one's A operand from the same tables
   const bool bsplit = msub == 2;
   int64_t last_commit = -1, last_copy = -1;
@@ -240,14 +245,14 @@ __global__ void __launch_bounds__(WG_THREADS, 1) dense_wgrad_gemm_kernel(WgArgs 
         int set, ppc, nv;
         int64_t p0;
         wg_step_geom(a, c0, set, p0, ppc, nv);
-        wg_fac(facb, tid, n, ppc, wg_load_ang(a, c0, tid));
+        wg_fac(facb, fid, n, ppc, wg_load_ang(a, c0, fid));
         if (c0 + 1 < c1) {
           int set1, ppc1, nv1;
           int64_t p01;
           wg_step_geom(a, c0 + 1, set1, p01, ppc1, nv1);
-          wg_fac(facb + WG_FAC4, tid, n, ppc1, wg_load_ang(a, c0 + 1, tid));
+          wg_fac(facb + WG_FAC4, fid, n, ppc1, wg_load_ang(a, c0 + 1, fid));
         }
-        if (c0 + 2 < c1) tjn = wg_load_ang(a, c0 + 2, tid);
+        if (c0 + 2 < c1) tjn = wg_load_ang(a, c0 + 2, fid);
       }
     } else if (lane == 0) {
       for (int j = 0; j < WG_RING - 1 && c0 + j < c1; ++j) {
@@ -437,8 +442,8 @@ __global__ void __launch_bounds__(WG_THREADS, 1) dense_wgrad_gemm_kernel(WgArgs 
             int set2, ppc2, nv2;
             int64_t p02;
             wg_step_geom(a, kc + 2, set2, p02, ppc2, nv2);
-            wg_fac(facb + (it & 1) * WG_FAC4, tid, n, ppc2, tjn);
-            if (kc + 3 < c1) tjn = wg_load_ang(a, kc + 3, tid);
+            wg_fac(facb + (it & 1) * WG_FAC4, fid, n, ppc2, tjn);
+            if (kc + 3 < c1) tjn = wg_load_ang(a, kc + 3, fid);
           }
         }
       } else {

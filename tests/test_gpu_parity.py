@@ -251,12 +251,16 @@ def test_dense_tensorcore_mlp_all_params(torch_cuda, oracle):
     _loss_grad_check(torch_cuda, oracle, circ, prob, params, sets, path="gemm_3xtf32")
 
 
-def test_dense_matches_simt_full_size(torch_cuda):
-    """Full 64x64x16 grid + IC plane in the bench's configuration: the tensor-core path and the
-    FP32 SIMT path agree on every loss term and on the gradient."""
+@pytest.mark.parametrize("workload", ["c3", "c4"])
+def test_dense_matches_simt_full_size(torch_cuda, workload):
+    """Full-size workloads (C3: the bench's 64x64x16 grid + IC plane; C4: 10 qubits, 8 layers,
+    64^3 grid + IC plane, 1,052,672 rows): the tensor-core path and the FP32 SIMT path agree on
+    every loss term and gradient block within 1e-5. At this size each weight-gradient CTA
+    accumulates thousands of rows, so the test covers the accumulator flushes (the oracle
+    cannot run these sizes; the SIMT path is within ~1e-6 of it at every tested size)."""
     from paper_2506_23246_b300 import qp
     torch = torch_cuda
-    circ, prob, params, sets = W.c3_workload(0)
+    circ, prob, params, sets = (W.c3_workload(0) if workload == "c3" else W.c4_workload(0))
     dp = torch.tensor(params, device="cuda")
     dsets = {k: torch.tensor(v, device="cuda") for k, v in sets.items()}
     out = {}
@@ -268,11 +272,11 @@ def test_dense_matches_simt_full_size(torch_cuda):
         out[path] = (l.clone(), g.clone())
     ls, gs = out["simt"]
     ld, gd = out["gemm_3xtf32"]
-    assert float(((ls - ld).abs() / ls.abs().clamp_min(1e-12)).max()) < 2e-5
+    assert float(((ls - ld).abs() / ls.abs().clamp_min(1e-12)).max()) < TOL
     lay = qp.Plan(circ, prob).layout
     for lo, hi in ((lay["fixed"], lay["circuit"]), (lay["circuit"], lay["head"]),
                    (lay["head"], lay["total"])):
-        assert float((gs[lo:hi] - gd[lo:hi]).abs().max()) <= 2e-5 * float(gs[lo:hi].abs().max())
+        assert float((gs[lo:hi] - gd[lo:hi]).abs().max()) <= TOL * float(gs[lo:hi].abs().max()), (lo, hi)
 
 
 def test_auto_path_c3_matches_oracle(torch_cuda, oracle):
