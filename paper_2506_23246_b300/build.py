@@ -13,7 +13,7 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 LIB = os.path.join(HERE, "libqpinn.so")
 SOURCES = ["qp_api.cu", "qp_sched.cpp", "qp_selftest.cpp"]
 HEADERS = ["qp_common.h", "qp_circuit.cuh", "qp_aux.cuh", "qp_tc.cuh", "qp_dense.cuh", "qp_fused.cuh",
-           "qp_mu.cuh", "qp_wgrad.cuh"]
+           "qp_mu.cuh", "qp_wgrad.cuh", "qp_premap_tc.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -13,6 +13,7 @@
 
 #include "../../include/qpinn.h"
 #include "qp_aux.cuh"
+#include "qp_premap_tc.cuh"
 #include "qp_circuit.cuh"
 #include "qp_common.h"
 #include "qp_dense.cuh"
@@ -436,8 +437,8 @@ qp_status qp_plan_create(const qp_circuit* circuit, const qp_problem* problem, i
     pl->smem_premap4 = qpk::premap4_smem(F, H, n);
     pl->pg_ok = F == qpk::PG_F && H == qpk::PG_H && n <= 16;
     if (pl->pg_ok &&
-        (raise_smem_limit((void*)qpk::premap_fwd_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                          qpk::pg_fwd_smem(n)) != cudaSuccess ||
+        (raise_smem_limit((void*)qpk::premap_fwd_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                          qpk::pt_smem(n).total) != cudaSuccess ||
          raise_smem_limit((void*)qpk::premap_bwd_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                           qpk::pg_bwd_smem(n)) != cudaSuccess)) {
       cudaGetLastError();
@@ -533,15 +534,15 @@ static qp_status launch_front(qp_plan* pl, const float* d_params, const float* c
   ma.params = d_params; ma.n = n; ma.premap = pl->c.premap; ma.scale = pl->c.scale;
   ma.n_direct = pl->c.n_direct; ma.F = pl->c.rff_freqs; ma.H = pl->c.mlp_width;
   ma.thetaJ = (float*)(ws + w.thetaJ);
-  ma.counts = pa.counts; ma.medium = pl->p.medium;
+  ma.counts = pa.counts; ma.medium = pl->p.medium; ma.status = pa.status;
   ma.disk_r = pl->p.disk_r; ma.disk_x0 = pl->p.disk_x0; ma.disk_y0 = pl->p.disk_y0;
   const int pblocks = (int)((ma.ptot + 127) / 128 < pl->sm_count * 8 ? (ma.ptot + 127) / 128 : pl->sm_count * 8);
   if (pl->c.premap == QP_PREMAP_RFF_MLP && pl->pg_ok) {
-    // GEMM formulation over 64-point tiles; the unit table is kept for the backward
+    // one tensor-core contraction per 128-point tile; the unit table is kept for the backward
     ma.u1 = grad ? (float*)(ws + w.u1) : nullptr;
-    const int64_t nt = (ma.ptot + qpk::PG_TP - 1) / qpk::PG_TP;
-    const int gb = (int)(nt < pl->sm_count * 2 ? (nt > 0 ? nt : 1) : pl->sm_count * 2);
-    qpk::premap_fwd_gemm_kernel<<<gb, qpk::PG_THREADS, qpk::pg_fwd_smem(n), s>>>(ma);
+    const int64_t nt = (ma.ptot + qpk::PT_M - 1) / qpk::PT_M;   // two CTAs per SM
+    const int gb = (int)(nt < 2 * pl->sm_count ? (nt > 0 ? nt : 1) : 2 * pl->sm_count);
+    qpk::premap_fwd_tc_kernel<<<gb, qpk::PT_THREADS, qpk::pt_smem(n).total, s>>>(ma);
   } else if (pl->c.premap == QP_PREMAP_RFF_MLP) {
     // four threads per point, 32 points per block
     const int64_t qb = (ma.ptot + 31) / 32;

@@ -102,6 +102,7 @@ struct PremapArgs {
   int32_t* counts;
   int32_t medium;
   float disk_r, disk_x0, disk_y0;
+  int32_t* status;        // device status word (tensor-core premap: an expired wait), or null
 };
 
 // theta = g(h) with a = tanh(h) and one of Eq. 27's scalings; g', g'' in terms of h.

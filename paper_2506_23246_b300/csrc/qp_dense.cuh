@@ -708,6 +708,7 @@ __global__ void __launch_bounds__(F16_THREADS, 1) dense_row16_kernel(GemmArgs a,
       }
     }
     float rs = sL, unsc = 1.f;
+    float bmax = 0.f;   // MODE 0: largest row bound of this thread's active rows
     bool active = false;
     int64_t row = 0;
     int ki = 0, c = 0, kc = 0;
@@ -766,12 +767,7 @@ __global__ void __launch_bounds__(F16_THREADS, 1) dense_row16_kernel(GemmArgs a,
           }
           const float bound = s == 0 ? 1.f : 0.5f * jsum;
           rs = pow2_scale(bound);
-          if (scal && h == 0) {
-            float bm = active ? bound : 0.f;
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) bm = fmaxf(bm, __shfl_xor_sync(0xffffffffu, bm, o));
-            if (lane == 0 && bm > 0.f) atomicMax(scal, __float_as_int(bm));
-          }
+          if (active) bmax = fmaxf(bmax, bound);
         }
         unsc = 1.f / (rs * W16_SCALE);
       }
@@ -863,6 +859,11 @@ __global__ void __launch_bounds__(F16_THREADS, 1) dense_row16_kernel(GemmArgs a,
         if (lane == 0) qptc::mbar_arrive(acc_free);   // the accumulators are free for the next item
       }
       if (++kc == nkc) { kc = 0; ++ki; }
+    }
+    if (MODE == 0 && scal && h == 0) {   // one atomic per warp (same-address atomics serialise in L2)
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) bmax = fmaxf(bmax, __shfl_xor_sync(0xffffffffu, bmax, o));
+      if (lane == 0 && bmax > 0.f) atomicMax(scal, __float_as_int(bmax));
     }
     if (!ok && lane == 0) atomicExch(a.status, 6);
   }
@@ -980,6 +981,7 @@ __global__ void dense_point_kernel(PointArgs a) {
   const int64_t wg = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const int64_t total = a.npts[0] + a.npts[1] + a.npts[2];
+  float lm = 0.f;   // largest |lambda| component this lane wrote
   for (int64_t gq = wg; gq < total; gq += nw) {
     int set = 0;
     int64_t li = gq;
@@ -1065,7 +1067,6 @@ __global__ void dense_point_kernel(PointArgs a) {
         atomicAdd(&hacc[3 * m + c], g[c]);
       }
     }
-    float lm = 0.f;
 #pragma unroll 4
     for (int k = lane; k < dim; k += 32) {
       float O = 0.f, Od[3] = {0.f, 0.f, 0.f};
@@ -1093,11 +1094,11 @@ __global__ void dense_point_kernel(PointArgs a) {
       ph[k] = lam;
       lm = fmaxf(lm, fmaxf(fabsf(lam.x), fabsf(lam.y)));
     }
-    if (a.lmax) {
+  }
+  if (a.lmax) {   // one atomic per warp (same-address atomics serialise in L2)
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) lm = fmaxf(lm, __shfl_xor_sync(0xffffffffu, lm, o));
-      if (lane == 0 && lm > 0.f) atomicMax(a.lmax, __float_as_int(lm));
-    }
+    for (int o = 16; o > 0; o >>= 1) lm = fmaxf(lm, __shfl_xor_sync(0xffffffffu, lm, o));
+    if (lane == 0 && lm > 0.f) atomicMax(a.lmax, __float_as_int(lm));
   }
   __syncthreads();
   double* bl = a.blk_loss + (int64_t)blockIdx.x * a.loss_stride;
