@@ -515,7 +515,8 @@ __global__ void premap_bwd_kernel(PremapArgs a) {
   }
 }
 
-// ---- RFF + MLP premap as register-blocked FP32 GEMMs over 64-point tiles (F = 64, H = 32).
+// ---- RFF + MLP premap backward as a register-blocked FP32 GEMM over 64-point tiles (F = 64,
+// H = 32; the forward runs on the tensor cores, qp_premap_tc.cuh).
 // With r = [cos(Omega v), sin(Omega v)] (K = 2F = 128 features), unit o's pre-activation and
 // its x, y, t tangents are h_c[o] = sum_i B[(o, c)][i] r[i] with
 //   B[(o, 0)][i] = W1[o][i],  B[(o, c)][f] = W1[o][F + f] Omega[f][c],  B[(o, c)][F + f] = -W1[o][f] Omega[f][c]
@@ -528,10 +529,6 @@ __global__ void premap_bwd_kernel(PremapArgs a) {
 // backward (the backward needs no h_c: (1 - u^2) h_c = u_c).
 constexpr int PG_F = 64, PG_H = 32, PG_K = 2 * PG_F, PG_N = 4 * PG_H, PG_TP = 64, PG_THREADS = 256;
 constexpr int PG_US = PG_H + 1;   // padded row of the per-point unit table (float4)
-__host__ __device__ inline int pg_fwd_smem(int n) {
-  const int areg = PG_K * PG_TP > PG_TP * PG_US * 4 ? PG_K * PG_TP : PG_TP * PG_US * 4;
-  return (PG_K * PG_N + areg + 3 * PG_F + PG_H + n * PG_H + n + PG_TP * 3) * 4;
-}
 __host__ __device__ inline int pg_bwd_smem(int n) {
   return (PG_TP * PG_US * 4 + PG_TP * PG_N + PG_TP * PG_K + PG_TP * n * 4 + 3 * PG_F + n * PG_H + n +
           PG_TP * 3 + 8 * PG_H) * 4;
@@ -548,123 +545,6 @@ __device__ __forceinline__ void pg_load_points(const PremapArgs& a, int64_t p0, 
       v = point_ptr(a, gp, set, li)[e % 3];
     }
     Ps[e] = v;
-  }
-}
-
-__global__ void __launch_bounds__(PG_THREADS, 2) premap_fwd_gemm_kernel(PremapArgs a) {
-  extern __shared__ __align__(16) float pg[];
-  const int n = a.n, tid = threadIdx.x;
-  const int areg = PG_K * PG_TP > PG_TP * PG_US * 4 ? PG_K * PG_TP : PG_TP * PG_US * 4;
-  float* Bs = pg;                                 // [K][N], column (o, c) = 4 o + c
-  float* As = Bs + PG_K * PG_N;                   // [K][TP] feature table of the tile
-  float4* Us = reinterpret_cast<float4*>(As);     // after the GEMM: [TP][PG_US] (u, u_x, u_y, u_t)
-  float* om = As + areg;                          // [F][3]
-  float* b1 = om + 3 * PG_F;
-  float* W2 = b1 + PG_H;                          // [n][H]
-  float* b2 = W2 + n * PG_H;
-  float* Ps = b2 + n;                             // [TP][3]
-  const float* W1 = a.params + 3 * PG_F;
-  for (int i = tid; i < 3 * PG_F; i += blockDim.x) om[i] = a.params[i];
-  for (int i = tid; i < PG_H; i += blockDim.x) b1[i] = W1[PG_H * PG_K + i];
-  for (int i = tid; i < n * PG_H; i += blockDim.x) W2[i] = W1[PG_H * PG_K + PG_H + i];
-  for (int i = tid; i < n; i += blockDim.x) b2[i] = W1[PG_H * PG_K + PG_H + n * PG_H + i];
-  __syncthreads();
-  for (int e = tid; e < PG_K * PG_N; e += blockDim.x) {
-    const int k = e / PG_N, col = e % PG_N, o = col >> 2, c = col & 3;
-    float v;
-    if (c == 0) v = W1[o * PG_K + k];
-    else if (k < PG_F) v = W1[o * PG_K + PG_F + k] * om[3 * k + c - 1];
-    else v = -W1[o * PG_K + (k - PG_F)] * om[3 * (k - PG_F) + c - 1];
-    Bs[e] = v;
-  }
-  const int ty = tid >> 4, tx = tid & 15;
-  const int64_t ntiles = (a.ptot + PG_TP - 1) / PG_TP;
-  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const int64_t p0 = tile * PG_TP;
-    __syncthreads();   // the previous tile's unit table is consumed
-    pg_load_points(a, p0, Ps);
-    __syncthreads();
-    for (int e = tid; e < PG_F * PG_TP; e += blockDim.x) {
-      const int f = e / PG_TP, p = e % PG_TP;
-      float sn, cs;
-      sincosf(om[3 * f] * Ps[3 * p] + om[3 * f + 1] * Ps[3 * p + 1] + om[3 * f + 2] * Ps[3 * p + 2], &sn, &cs);
-      As[f * PG_TP + p] = cs;
-      As[(PG_F + f) * PG_TP + p] = sn;
-    }
-    __syncthreads();
-    // H[p][(o, c)] for points 4 ty + r, columns 4 tx + (0..3) and 64 + 4 tx + (0..3)
-    float acc[4][8];
-#pragma unroll
-    for (int r = 0; r < 4; ++r)
-#pragma unroll
-      for (int q = 0; q < 8; ++q) acc[r][q] = 0.f;
-#pragma unroll 4
-    for (int k = 0; k < PG_K; ++k) {
-      const float4 av = *reinterpret_cast<const float4*>(&As[k * PG_TP + ty * 4]);
-      const float4 bv0 = *reinterpret_cast<const float4*>(&Bs[k * PG_N + tx * 4]);
-      const float4 bv1 = *reinterpret_cast<const float4*>(&Bs[k * PG_N + 64 + tx * 4]);
-      const float ar[4] = {av.x, av.y, av.z, av.w};
-      const float br[8] = {bv0.x, bv0.y, bv0.z, bv0.w, bv1.x, bv1.y, bv1.z, bv1.w};
-#pragma unroll
-      for (int r = 0; r < 4; ++r)
-#pragma unroll
-        for (int q = 0; q < 8; ++q) acc[r][q] = fmaf(ar[r], br[q], acc[r][q]);
-    }
-    __syncthreads();   // the feature table is consumed: the unit table takes its place
-#pragma unroll
-    for (int r = 0; r < 4; ++r) {
-      const int p = ty * 4 + r;
-      const int64_t gp = p0 + p;
-#pragma unroll
-      for (int uu = 0; uu < 2; ++uu) {
-        const int o = tx + 16 * uu;
-        const float u = tanhf(acc[r][4 * uu] + b1[o]);
-        const float du = 1.f - u * u;
-        const float4 u4 = make_float4(u, du * acc[r][4 * uu + 1], du * acc[r][4 * uu + 2], du * acc[r][4 * uu + 3]);
-        Us[p * PG_US + o] = u4;
-        if (a.u1 && gp < a.ptot) reinterpret_cast<float4*>(a.u1)[gp * PG_H + o] = u4;
-      }
-    }
-    __syncthreads();
-    // outputs: point tid / 4, outputs j = tid % 4 + 4 jj
-    {
-      const int p = tid >> 2, j0 = tid & 3;
-      const int64_t gp = p0 + p;
-      float4 z[3];
-#pragma unroll
-      for (int jj = 0; jj < 3; ++jj) z[jj] = make_float4(j0 + 4 * jj < n ? b2[j0 + 4 * jj] : 0.f, 0.f, 0.f, 0.f);
-      for (int o = 0; o < PG_H; ++o) {
-        const float4 u4 = Us[p * PG_US + o];
-#pragma unroll
-        for (int jj = 0; jj < 3; ++jj) {
-          const int j = j0 + 4 * jj;
-          if (j < n) {
-            const float w = W2[j * PG_H + o];
-            z[jj].x += w * u4.x; z[jj].y += w * u4.y; z[jj].z += w * u4.z; z[jj].w += w * u4.w;
-          }
-        }
-      }
-      if (gp < a.ptot) {
-        float4* out = reinterpret_cast<float4*>(a.thetaJ) + gp * n;
-#pragma unroll
-        for (int jj = 0; jj < 3; ++jj) {
-          const int j = j0 + 4 * jj;
-          if (j < n) {
-            float g0, g1, g2;
-            scale_tanh(a.scale, z[jj].x, g0, g1, g2);
-            out[j] = make_float4(g0, g1 * z[jj].y, g1 * z[jj].z, g1 * z[jj].w);
-          }
-        }
-      }
-      // collocation points inside the dielectric disk, counted once per point
-      bool inside = false;
-      if (a.medium == 1 && j0 == 0 && gp < a.npts[0]) {
-        const float dx = Ps[3 * p] - a.disk_x0, dy = Ps[3 * p + 1] - a.disk_y0;
-        inside = __fmaf_rn(dx, dx, dy * dy) < a.disk_r * a.disk_r;
-      }
-      const unsigned bal = __ballot_sync(0xffffffffu, inside);
-      if ((tid & 31) == 0 && bal) atomicAdd(&a.counts[0], __popc(bal));
-    }
   }
 }
 
