@@ -439,8 +439,8 @@ qp_status qp_plan_create(const qp_circuit* circuit, const qp_problem* problem, i
     if (pl->pg_ok &&
         (raise_smem_limit((void*)qpk::premap_fwd_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                           qpk::pt_smem(n).total) != cudaSuccess ||
-         raise_smem_limit((void*)qpk::premap_bwd_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                          qpk::pg_bwd_smem(n)) != cudaSuccess)) {
+         raise_smem_limit((void*)qpk::premap_bwd_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                          qpk::pb_smem(n)) != cudaSuccess)) {
       cudaGetLastError();
       delete pl;
       return QP_ERR_CUDA;
@@ -1004,7 +1004,8 @@ static qp_status launch_premap_bwd(qp_plan* pl, const WsLayout& w, const float* 
   ma.d1 = (float*)(ws + w.d1); ma.d2 = (float*)(ws + w.d2); ma.u1 = (float*)(ws + w.u1);
   if (pl->pg_ok) {
     // backward and weight-gradient partials in one pass (one partial slot per block)
-    qpk::premap_bwd_gemm_kernel<<<pl->nwblk, qpk::PG_THREADS, qpk::pg_bwd_smem(pl->c.n_qubits), s>>>(
+    ma.status = (int32_t*)(ws + w.status);
+    qpk::premap_bwd_tc_kernel<<<pl->nwblk, qpk::PG_THREADS, qpk::pb_smem(pl->c.n_qubits), s>>>(
         ma, (float*)(ws + w.wpart), (int32_t)(pl->mlp_count - pl->nfixed));
     return cuda_status(cudaGetLastError());
   }

@@ -515,8 +515,8 @@ __global__ void premap_bwd_kernel(PremapArgs a) {
   }
 }
 
-// ---- RFF + MLP premap backward as a register-blocked FP32 GEMM over 64-point tiles (F = 64,
-// H = 32; the forward runs on the tensor cores, qp_premap_tc.cuh).
+// ---- RFF + MLP premap with F = 64, H = 32: shared constants and the tile loader of the
+// tensor-core kernels (qp_premap_tc.cuh).
 // With r = [cos(Omega v), sin(Omega v)] (K = 2F = 128 features), unit o's pre-activation and
 // its x, y, t tangents are h_c[o] = sum_i B[(o, c)][i] r[i] with
 //   B[(o, 0)][i] = W1[o][i],  B[(o, c)][f] = W1[o][F + f] Omega[f][c],  B[(o, c)][F + f] = -W1[o][f] Omega[f][c]
@@ -529,11 +529,6 @@ __global__ void premap_bwd_kernel(PremapArgs a) {
 // backward (the backward needs no h_c: (1 - u^2) h_c = u_c).
 constexpr int PG_F = 64, PG_H = 32, PG_K = 2 * PG_F, PG_N = 4 * PG_H, PG_TP = 64, PG_THREADS = 256;
 constexpr int PG_US = PG_H + 1;   // padded row of the per-point unit table (float4)
-__host__ __device__ inline int pg_bwd_smem(int n) {
-  return (PG_TP * PG_US * 4 + PG_TP * PG_N + PG_TP * PG_K + PG_TP * n * 4 + 3 * PG_F + n * PG_H + n +
-          PG_TP * 3 + 8 * PG_H) * 4;
-}
-
 // the tile's point coordinates
 __device__ __forceinline__ void pg_load_points(const PremapArgs& a, int64_t p0, float* Ps) {
   for (int e = threadIdx.x; e < PG_TP * 3; e += blockDim.x) {
@@ -548,159 +543,6 @@ __device__ __forceinline__ void pg_load_points(const PremapArgs& a, int64_t p0, 
   }
 }
 
-// Backward of the premap from dL/dtheta and dL/dJ with its weight-gradient partials, one
-// slot per block in the parameter order [dW1 (H x 2F)][db1 (H)][dW2 (n x H)][db2 (n)].
-__global__ void __launch_bounds__(PG_THREADS, 2) premap_bwd_gemm_kernel(PremapArgs a, float* part, int32_t nW) {
-  extern __shared__ __align__(16) float pg[];
-  const int n = a.n, tid = threadIdx.x;
-  float4* Us = reinterpret_cast<float4*>(pg);                 // [TP][PG_US] (u, u_x, u_y, u_t)
-  float4* D1 = Us + PG_TP * PG_US;                            // [TP][H] dL/dh (c = 0..3)
-  float* As = reinterpret_cast<float*>(D1 + PG_TP * PG_H);    // [TP][K] feature table
-  float4* Dz = reinterpret_cast<float4*>(As + PG_TP * PG_K);  // [TP][n] dL/dz (c = 0..3)
-  float* om = reinterpret_cast<float*>(Dz + PG_TP * n);       // [F][3]
-  float* W2 = om + 3 * PG_F;                                  // [n][H]
-  float* b2 = W2 + n * PG_H;
-  float* Ps = b2 + n;                                         // [TP][3]
-  float* red = Ps + PG_TP * 3;                                // [8][H] db1 partials
-  const float* W1 = a.params + 3 * PG_F;
-  for (int i = tid; i < 3 * PG_F; i += blockDim.x) om[i] = a.params[i];
-  for (int i = tid; i < n * PG_H; i += blockDim.x) W2[i] = W1[PG_H * PG_K + PG_H + i];
-  for (int i = tid; i < n; i += blockDim.x) b2[i] = W1[PG_H * PG_K + PG_H + n * PG_H + i];
-  __syncthreads();   // the fold at the end reads Omega also in blocks without a tile
-  const int ty = tid >> 4, tx = tid & 15;
-  const int ow = tid & 31, pw = tid >> 5;       // (unit, point row) of the d1 and dW2 phases
-  float dacc[8][8];
-#pragma unroll
-  for (int r = 0; r < 8; ++r)
-#pragma unroll
-    for (int q = 0; q < 8; ++q) dacc[r][q] = 0.f;
-  float w2acc[2] = {0.f, 0.f}, b2acc[2] = {0.f, 0.f}, b1acc = 0.f;   // outputs pw, pw + 8
-  const int64_t ntiles = (a.ptot + PG_TP - 1) / PG_TP;
-  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const int64_t p0 = tile * PG_TP;
-    __syncthreads();   // every table of the previous tile is consumed
-    pg_load_points(a, p0, Ps);
-    for (int e = tid; e < PG_TP * PG_H; e += blockDim.x) {
-      const int p = e / PG_H, o = e % PG_H;
-      const int64_t gp = p0 + p;
-      Us[p * PG_US + o] = gp < a.ptot ? reinterpret_cast<const float4*>(a.u1)[gp * PG_H + o]
-                                      : make_float4(0.f, 0.f, 0.f, 0.f);
-    }
-    __syncthreads();
-    // dL/dz of point tid / 4, outputs j = tid % 4 + 4 jj: theta = g(z_0), J_c = g'(z_0) z_c
-    {
-      const int p = tid >> 2, j0 = tid & 3;
-      const int64_t gp = p0 + p;
-      float4 z[3];
-#pragma unroll
-      for (int jj = 0; jj < 3; ++jj) z[jj] = make_float4(j0 + 4 * jj < n ? b2[j0 + 4 * jj] : 0.f, 0.f, 0.f, 0.f);
-      for (int o = 0; o < PG_H; ++o) {
-        const float4 u4 = Us[p * PG_US + o];
-#pragma unroll
-        for (int jj = 0; jj < 3; ++jj) {
-          const int j = j0 + 4 * jj;
-          if (j < n) {
-            const float w = W2[j * PG_H + o];
-            z[jj].x += w * u4.x; z[jj].y += w * u4.y; z[jj].z += w * u4.z; z[jj].w += w * u4.w;
-          }
-        }
-      }
-#pragma unroll
-      for (int jj = 0; jj < 3; ++jj) {
-        const int j = j0 + 4 * jj;
-        if (j < n) {
-          float g0, g1, g2;
-          scale_tanh(a.scale, z[jj].x, g0, g1, g2);
-          const float4 dt = gp < a.ptot ? reinterpret_cast<const float4*>(a.dthetaJ)[gp * n + j]
-                                        : make_float4(0.f, 0.f, 0.f, 0.f);
-          const float dz0 = dt.x * g1 + g2 * (dt.y * z[jj].y + dt.z * z[jj].z + dt.w * z[jj].w);
-          Dz[p * n + j] = make_float4(dz0, dt.y * g1, dt.z * g1, dt.w * g1);
-        }
-      }
-    }
-    // feature table [p][i]
-    for (int e = tid; e < PG_TP * PG_F; e += blockDim.x) {
-      const int p = e / PG_F, f = e % PG_F;
-      float sn, cs;
-      sincosf(om[3 * f] * Ps[3 * p] + om[3 * f + 1] * Ps[3 * p + 1] + om[3 * f + 2] * Ps[3 * p + 2], &sn, &cs);
-      As[p * PG_K + f] = cs;
-      As[p * PG_K + PG_F + f] = sn;
-    }
-    __syncthreads();
-    // dW2[j][o] += sum_p dz_j . u_o (c = 0..3), db2[j] += sum_p dz_j0: warp j (and j - 8), lane o
-#pragma unroll
-    for (int jj = 0; jj < 2; ++jj) {
-      const int j = pw + 8 * jj;
-      if (j < n) {
-        for (int p = 0; p < PG_TP; ++p) {
-          const float4 d = Dz[p * n + j], u4 = Us[p * PG_US + ow];
-          w2acc[jj] += d.x * u4.x + d.y * u4.y + d.z * u4.z + d.w * u4.w;
-          b2acc[jj] += d.x;
-        }
-      }
-    }
-    // dL/du_o = sum_j W2[j][o] dz_j, then through tanh: d1 = dL/dh
-    for (int p = pw; p < PG_TP; p += PG_THREADS / 32) {
-      float4 gu = make_float4(0.f, 0.f, 0.f, 0.f);
-      for (int j = 0; j < n; ++j) {
-        const float w = W2[j * PG_H + ow];
-        const float4 d = Dz[p * n + j];
-        gu.x += w * d.x; gu.y += w * d.y; gu.z += w * d.z; gu.w += w * d.w;
-      }
-      const float4 u4 = Us[p * PG_US + ow];
-      const float du = 1.f - u4.x * u4.x;
-      const float g0 = gu.x * du - 2.f * u4.x * (gu.y * u4.y + gu.z * u4.z + gu.w * u4.w);
-      D1[p * PG_H + ow] = make_float4(g0, gu.y * du, gu.z * du, gu.w * du);
-      b1acc += g0;
-    }
-    __syncthreads();
-    // D[(o, c)][i] += sum_p d1_p[(o, c)] r_p[i]: units ty and ty + 16, features 4 tx + (0..3), 64 + 4 tx + (0..3)
-#pragma unroll 2
-    for (int p = 0; p < PG_TP; ++p) {
-      const float4 a0 = D1[p * PG_H + ty], a1 = D1[p * PG_H + ty + 16];
-      const float4 bv0 = *reinterpret_cast<const float4*>(&As[p * PG_K + tx * 4]);
-      const float4 bv1 = *reinterpret_cast<const float4*>(&As[p * PG_K + 64 + tx * 4]);
-      const float ar[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
-      const float br[8] = {bv0.x, bv0.y, bv0.z, bv0.w, bv1.x, bv1.y, bv1.z, bv1.w};
-#pragma unroll
-      for (int r = 0; r < 8; ++r)
-#pragma unroll
-        for (int q = 0; q < 8; ++q) dacc[r][q] = fmaf(ar[r], br[q], dacc[r][q]);
-    }
-  }
-  // fold D back into dW1 (thread: units ty, ty + 16; frequencies f = 4 tx + ii)
-  float* out = part + (int64_t)blockIdx.x * nW;
-#pragma unroll
-  for (int uu = 0; uu < 2; ++uu) {
-    const int o = ty + 16 * uu;
-#pragma unroll
-    for (int ii = 0; ii < 4; ++ii) {
-      const int f = tx * 4 + ii;
-      const float ox = om[3 * f], oy = om[3 * f + 1], ot = om[3 * f + 2];
-      // dacc[4 uu + c][q]: q = ii the cos feature f, q = 4 + ii the sin feature F + f
-      const float cosp = dacc[4 * uu][ii], sinp = dacc[4 * uu][4 + ii];
-      const float dwc = cosp - (ox * dacc[4 * uu + 1][4 + ii] + oy * dacc[4 * uu + 2][4 + ii] + ot * dacc[4 * uu + 3][4 + ii]);
-      const float dws = sinp + (ox * dacc[4 * uu + 1][ii] + oy * dacc[4 * uu + 2][ii] + ot * dacc[4 * uu + 3][ii]);
-      out[o * PG_K + f] = dwc;
-      out[o * PG_K + PG_F + f] = dws;
-    }
-  }
-  red[pw * PG_H + ow] = b1acc;
-  __syncthreads();
-  if (tid < PG_H) {
-    float t = 0.f;
-    for (int r = 0; r < PG_THREADS / 32; ++r) t += red[r * PG_H + tid];
-    out[PG_H * PG_K + tid] = t;
-  }
-#pragma unroll
-  for (int jj = 0; jj < 2; ++jj) {
-    const int j = pw + 8 * jj;
-    if (j < n) {
-      out[PG_H * PG_K + PG_H + j * PG_H + ow] = w2acc[jj];
-      if (ow == 0) out[PG_H * PG_K + PG_H + n * PG_H + j] = b2acc[jj];
-    }
-  }
-}
 
 // Weight gradients of the premap as block partials over contiguous point chunks.
 //   dW1[o][i] = sum_p d1[o].(r_i, r_{i,x}, r_{i,y}, r_{i,t}),  db1[o] = sum_p d1[o].x

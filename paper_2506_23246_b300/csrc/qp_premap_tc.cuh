@@ -253,4 +253,251 @@ __global__ void __launch_bounds__(PT_THREADS, 2) premap_fwd_tc_kernel(PremapArgs
   if (warp == 0) qptc::tmem_dealloc(tmem, 256);
 }
 
+// ---- premap backward: per 64-point tile the SIMT phases of the FP32 kernel (dL/dz through the
+// output layer and the scaling, dL/dh through tanh, the output-layer weight gradient), and the
+// first-layer weight gradient D[(o, c)][i] = sum_p d1_p[(o, c)] r_p[i] as one [128 (o, c)] x
+// [128 features] x [K = 64 points] tensor-core contraction on FP16 pairs (d1 scaled by one
+// power of two per tile, the features by 2^12). Each tile's product comes back from tensor
+// memory into FP32 registers, so the sum over tiles is the FP32 sum of the SIMT kernel; the
+// Omega fold-back at the end is unchanged.
+constexpr int PB_OPB = 128 * PG_TP * 2;   // one FP16 half of a 128-row, K = 64 operand
+__host__ __device__ inline int pb_smem(int n) {
+  // [A hi, A lo, B hi, B lo] (then the 128 x 129 float result, reaching into Us), Us, Dz,
+  // Omega, W2, b2, points, db1 partials, per-warp maxima, mbarrier + tensor-memory slot
+  return 4 * PB_OPB + PG_TP * PG_US * 16 + PG_TP * n * 16 + 3 * PG_F * 4 + n * PG_H * 4 + ((n + 3) & ~3) * 4 +
+         PG_TP * 3 * 4 + 8 * PG_H * 4 + 8 * 4 + 16;
+}
+__device__ __forceinline__ uint32_t pb_off(int r, int k) {
+  return (uint32_t)((k >> 5) * (128 * qpd::HKC * 2)) + qpd::core_off_h(r, k & 31);
+}
+
+__global__ void __launch_bounds__(PG_THREADS, 2) premap_bwd_tc_kernel(PremapArgs a, float* part, int32_t nW) {
+  extern __shared__ __align__(1024) unsigned char pb_[];
+  const int n = a.n, tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  unsigned char* Ah = pb_;
+  unsigned char* Al = pb_ + PB_OPB;
+  unsigned char* Bh = pb_ + 2 * PB_OPB;
+  unsigned char* Bl = pb_ + 3 * PB_OPB;
+  float4* Us = reinterpret_cast<float4*>(pb_ + 4 * PB_OPB);   // [TP][PG_US] (u, u_x, u_y, u_t)
+  float4* Dz = Us + PG_TP * PG_US;                             // [TP][n] dL/dz (c = 0..3)
+  float* om = reinterpret_cast<float*>(Dz + PG_TP * n);        // [F][3]
+  float* W2 = om + 3 * PG_F;                                   // [n][H]
+  float* b2 = W2 + n * PG_H;
+  float* Ps = b2 + ((n + 3) & ~3);                             // [TP][3]
+  float* red = Ps + PG_TP * 3;                                 // [8][H] db1 partials
+  float* wmax = red + 8 * PG_H;                                // [8] per-warp max |d1|
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(wmax + 8);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 1);
+  float* Dm = reinterpret_cast<float*>(pb_);                   // at the end: [128][129] result
+  const float* W1 = a.params + 3 * PG_F;
+  if (warp == 0) qptc::tmem_alloc(tslot, 128);
+  if (tid == 0) qptc::mbar_init(mbar, 1);
+  for (int i = tid; i < 3 * PG_F; i += blockDim.x) om[i] = a.params[i];
+  for (int i = tid; i < n * PG_H; i += blockDim.x) W2[i] = W1[PG_H * PG_K + PG_H + i];
+  for (int i = tid; i < n; i += blockDim.x) b2[i] = W1[PG_H * PG_K + PG_H + n * PG_H + i];
+  qptc::fence_before();
+  __syncthreads();   // the fold at the end reads Omega also in blocks without a tile
+  qptc::fence_after();
+  const uint32_t tmem = *tslot;
+  const uint32_t id = qptc::idesc(0, 128, PG_K);
+  const float sB = qpd::pow2_scale(1.f);
+  const int ow = tid & 31, pw = tid >> 5;       // (unit, point row) of the dW2 phase
+  float acc[64];                                // this thread's row m, 64 columns of D
+#pragma unroll
+  for (int q = 0; q < 64; ++q) acc[q] = 0.f;
+  const int m = 32 * (warp & 3) + lane, chalf = warp >> 2;
+  float w2acc[2] = {0.f, 0.f}, b2acc[2] = {0.f, 0.f}, b1acc = 0.f;   // outputs pw, pw + 8
+  bool ok = true;
+  uint32_t phase = 0;
+  const int64_t ntiles = (a.ptot + PG_TP - 1) / PG_TP;
+  for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, phase ^= 1) {
+    const int64_t p0 = tile * PG_TP;
+    __syncthreads();   // every table of the previous tile is consumed
+    pg_load_points(a, p0, Ps);
+    for (int e = tid; e < PG_TP * PG_H; e += blockDim.x) {
+      const int p = e / PG_H, o = e % PG_H;
+      const int64_t gp = p0 + p;
+      Us[p * PG_US + o] = gp < a.ptot ? reinterpret_cast<const float4*>(a.u1)[gp * PG_H + o]
+                                      : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    __syncthreads();
+    // dL/dz of point tid / 4, outputs j = tid % 4 + 4 jj: theta = g(z_0), J_c = g'(z_0) z_c
+    {
+      const int p = tid >> 2, j0 = tid & 3;
+      const int64_t gp = p0 + p;
+      float4 z[3];
+#pragma unroll
+      for (int jj = 0; jj < 3; ++jj) z[jj] = make_float4(j0 + 4 * jj < n ? b2[j0 + 4 * jj] : 0.f, 0.f, 0.f, 0.f);
+      for (int o = 0; o < PG_H; ++o) {
+        const float4 u4 = Us[p * PG_US + o];
+#pragma unroll
+        for (int jj = 0; jj < 3; ++jj) {
+          const int j = j0 + 4 * jj;
+          if (j < n) {
+            const float w = W2[j * PG_H + o];
+            z[jj].x += w * u4.x; z[jj].y += w * u4.y; z[jj].z += w * u4.z; z[jj].w += w * u4.w;
+          }
+        }
+      }
+#pragma unroll
+      for (int jj = 0; jj < 3; ++jj) {
+        const int j = j0 + 4 * jj;
+        if (j < n) {
+          float g0, g1, g2;
+          scale_tanh(a.scale, z[jj].x, g0, g1, g2);
+          const float4 dt = gp < a.ptot ? reinterpret_cast<const float4*>(a.dthetaJ)[gp * n + j]
+                                        : make_float4(0.f, 0.f, 0.f, 0.f);
+          const float dz0 = dt.x * g1 + g2 * (dt.y * z[jj].y + dt.z * z[jj].z + dt.w * z[jj].w);
+          Dz[p * n + j] = make_float4(dz0, dt.y * g1, dt.z * g1, dt.w * g1);
+        }
+      }
+    }
+    // feature operand B[i][p] (K = points): thread -> (frequency, 8 consecutive points)
+    for (int e = tid; e < PG_F * (PG_TP / 8); e += blockDim.x) {
+      const int f = e & (PG_F - 1), pg8 = (e >> 6) * 8;
+      float cv[8], sv[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int p = pg8 + q;
+        sincosf(om[3 * f] * Ps[3 * p] + om[3 * f + 1] * Ps[3 * p + 1] + om[3 * f + 2] * Ps[3 * p + 2], &sv[q], &cv[q]);
+      }
+      uint4 h8, l8;
+      qpd::pack_h8(cv, sB, h8, l8);
+      *reinterpret_cast<uint4*>(Bh + pb_off(f, pg8)) = h8;
+      *reinterpret_cast<uint4*>(Bl + pb_off(f, pg8)) = l8;
+      qpd::pack_h8(sv, sB, h8, l8);
+      *reinterpret_cast<uint4*>(Bh + pb_off(PG_F + f, pg8)) = h8;
+      *reinterpret_cast<uint4*>(Bl + pb_off(PG_F + f, pg8)) = l8;
+    }
+    __syncthreads();
+    // dW2[j][o] += sum_p dz_j . u_o (c = 0..3), db2[j] += sum_p dz_j0: warp j (and j - 8), lane o
+#pragma unroll
+    for (int jj = 0; jj < 2; ++jj) {
+      const int j = pw + 8 * jj;
+      if (j < n) {
+        for (int p = 0; p < PG_TP; ++p) {
+          const float4 d = Dz[p * n + j], u4 = Us[p * PG_US + ow];
+          w2acc[jj] += d.x * u4.x + d.y * u4.y + d.z * u4.z + d.w * u4.w;
+          b2acc[jj] += d.x;
+        }
+      }
+    }
+    // dL/du_o = sum_j W2[j][o] dz_j, then through tanh: d1 = dL/dh; thread -> (unit ow, 8
+    // consecutive points from 8 pw)
+    float d1v[4][8];
+    float dm = 0.f;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int p = 8 * pw + q;
+      float4 gu = make_float4(0.f, 0.f, 0.f, 0.f);
+      for (int j = 0; j < n; ++j) {
+        const float w = W2[j * PG_H + ow];
+        const float4 d = Dz[p * n + j];
+        gu.x += w * d.x; gu.y += w * d.y; gu.z += w * d.z; gu.w += w * d.w;
+      }
+      const float4 u4 = Us[p * PG_US + ow];
+      const float du = 1.f - u4.x * u4.x;
+      const float g0 = gu.x * du - 2.f * u4.x * (gu.y * u4.y + gu.z * u4.z + gu.w * u4.w);
+      d1v[0][q] = g0; d1v[1][q] = gu.y * du; d1v[2][q] = gu.z * du; d1v[3][q] = gu.w * du;
+      b1acc += g0;
+#pragma unroll
+      for (int c = 0; c < 4; ++c) dm = fmaxf(dm, fabsf(d1v[c][q]));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) dm = fmaxf(dm, __shfl_xor_sync(0xffffffffu, dm, o));
+    if (lane == 0) wmax[warp] = dm;
+    __syncthreads();
+    dm = 0.f;
+#pragma unroll
+    for (int w = 0; w < PG_THREADS / 32; ++w) dm = fmaxf(dm, wmax[w]);
+    const float sD = qpd::pow2_scale(dm);
+    // d1 operand A[(o, c)][p] (K = points)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      uint4 h8, l8;
+      qpd::pack_h8(d1v[c], sD, h8, l8);
+      *reinterpret_cast<uint4*>(Ah + pb_off(4 * ow + c, 8 * pw)) = h8;
+      *reinterpret_cast<uint4*>(Al + pb_off(4 * ow + c, 8 * pw)) = l8;
+    }
+    qptc::fence_proxy_async();
+    __syncthreads();
+    if (tid == 0) {
+      qptc::fence_after();
+      const uint32_t ah0 = qptc::smem_u32(Ah), al0 = qptc::smem_u32(Al);
+      const uint32_t bh0 = qptc::smem_u32(Bh), bl0 = qptc::smem_u32(Bl);
+#pragma unroll
+      for (int ks = 0; ks < PG_TP / 16; ++ks) {
+        const uint32_t off = (ks >> 1) * (128 * qpd::HKC * 2) + (ks & 1) * 256;
+        const uint64_t ah = qptc::desc_kmajor(ah0 + off, 128, (qpd::HKC / 8) * 128);
+        const uint64_t al = qptc::desc_kmajor(al0 + off, 128, (qpd::HKC / 8) * 128);
+        const uint64_t bh = qptc::desc_kmajor(bh0 + off, 128, (qpd::HKC / 8) * 128);
+        const uint64_t bl = qptc::desc_kmajor(bl0 + off, 128, (qpd::HKC / 8) * 128);
+        qptc::mma_f16(tmem, ah, bh, id, ks > 0 ? 1u : 0u);
+        qptc::mma_f16(tmem, ah, bl, id, 1u);
+        qptc::mma_f16(tmem, al, bh, id, 1u);
+      }
+      qptc::commit(mbar);
+    }
+    ok = __syncthreads_and(qptc::mbar_wait(mbar, phase));
+    if (!ok) break;
+    qptc::fence_after();
+    {
+      const float us = 1.f / (sD * sB);
+      const uint32_t lanes = (uint32_t)(32 * (warp & 3)) << 16;
+      float v[32];
+#pragma unroll
+      for (int hh = 0; hh < 2; ++hh) {
+        qptc::tmem_ld32(tmem + lanes + 64 * chalf + 32 * hh, v);
+#pragma unroll
+        for (int q = 0; q < 32; ++q) acc[32 * hh + q] = fmaf(v[q], us, acc[32 * hh + q]);
+      }
+    }
+    qptc::fence_before();
+  }
+  if (!ok && tid == 0) {
+    if (a.status) atomicExch(a.status, 6);
+    qptc::mbar_wait(mbar, phase);   // the tile's MMAs must finish before tensor memory is freed
+  }
+  __syncthreads();   // the operand buffers are free: the result table takes their place
+#pragma unroll
+  for (int q = 0; q < 64; ++q) Dm[m * 129 + 64 * chalf + q] = acc[q];
+  __syncthreads();
+  // fold D back into dW1 (thread: units ty, ty + 16; frequencies f = 4 tx + ii)
+  const int ty = tid >> 4, tx = tid & 15;
+  float* out = part + (int64_t)blockIdx.x * nW;
+#pragma unroll
+  for (int uu = 0; uu < 2; ++uu) {
+    const int o = ty + 16 * uu;
+#pragma unroll
+    for (int ii = 0; ii < 4; ++ii) {
+      const int f = tx * 4 + ii;
+      const float ox = om[3 * f], oy = om[3 * f + 1], ot = om[3 * f + 2];
+      const float* r0 = Dm + (4 * o) * 129;
+      const float cosp = r0[f], sinp = r0[PG_F + f];
+      const float dwc = cosp - (ox * r0[129 + PG_F + f] + oy * r0[2 * 129 + PG_F + f] + ot * r0[3 * 129 + PG_F + f]);
+      const float dws = sinp + (ox * r0[129 + f] + oy * r0[2 * 129 + f] + ot * r0[3 * 129 + f]);
+      out[o * PG_K + f] = dwc;
+      out[o * PG_K + PG_F + f] = dws;
+    }
+  }
+  red[pw * PG_H + ow] = b1acc;
+  __syncthreads();
+  if (tid < PG_H) {
+    float t = 0.f;
+    for (int r = 0; r < PG_THREADS / 32; ++r) t += red[r * PG_H + tid];
+    out[PG_H * PG_K + tid] = t;
+  }
+#pragma unroll
+  for (int jj = 0; jj < 2; ++jj) {
+    const int j = pw + 8 * jj;
+    if (j < n) {
+      out[PG_H * PG_K + PG_H + j * PG_H + ow] = w2acc[jj];
+      if (ow == 0) out[PG_H * PG_K + PG_H + n * PG_H + j] = b2acc[jj];
+    }
+  }
+  qptc::fence_before();
+  __syncthreads();
+  if (warp == 0) qptc::tmem_dealloc(tmem, 128);
+}
+
 }  // namespace qpk
