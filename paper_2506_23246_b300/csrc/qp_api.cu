@@ -697,7 +697,7 @@ static qp_status dense_loss_grad(qp_plan* pl, const float* d_params, const float
     pa.nE = 3 * n * L;
     pa.lmax = fwd16 ? (int32_t*)(ws + w.status) + 17 : nullptr;   // scale of the mu operand
     const int psmem = ((QP_NLP + pl->p.energy_nt) * 8 + 15) / 16 * 16 + (3 * pl->c.n_readout + 3) * 4;
-    qpd::dense_point_kernel<<<pl->blocks_grad, 256, psmem, s>>>(pa);
+    qpd::dense_point_kernel<<<pl->blocks_grad, qpd::PT_POINT_THREADS, psmem, s>>>(pa);
     launches += 1;
   }
   qpd::WgArgs wa;
@@ -816,7 +816,7 @@ static qp_status dense_loss_grad(qp_plan* pl, const float* d_params, const float
       }
       qpd::EmbedArgs ea;
       ea.thetaJ = (const float*)(ws + w.thetaJ); ea.mu = (const float*)(ws + w.dmu);
-      ea.dthetaJ = (float*)(ws + w.dthetaJ); ea.n = n;
+      ea.dthetaJ = (float*)(ws + w.dthetaJ); ea.n = n; ea.cs = (const float2*)(ws + w.dcs);
       base = 0;
       for (int i = 0; i < 3; ++i) { ea.npts[i] = npts[i]; ea.pt_base[i] = base; base += npts[i]; }
       const int64_t eb = (P + 7) / 8;

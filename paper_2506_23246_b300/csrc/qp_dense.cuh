@@ -968,7 +968,10 @@ struct PointArgs {
   int32_t* lmax;          // float bits of the largest |lambda| component (atomic maximum), or null
 };
 
-__global__ void dense_point_kernel(PointArgs a) {
+// 8 warps per SM: a point's states (32 KiB at n = 10) are read twice, and the second read
+// should hit L2; twice as many warps in flight measured 40% slower
+constexpr int PT_POINT_THREADS = 256;
+__global__ void __launch_bounds__(PT_POINT_THREADS, 1) dense_point_kernel(PointArgs a) {
   extern __shared__ __align__(16) unsigned char psh[];
   const int n = a.n, dim = 1 << n, m = a.m;
   const int nt = a.pb.energy_nt;
@@ -991,7 +994,7 @@ __global__ void dense_point_kernel(PointArgs a) {
     float z[QP_MAXQ], dz[3][QP_MAXQ];
 #pragma unroll
     for (int i = 0; i < QP_MAXQ; ++i) { z[i] = 0.f; dz[0][i] = dz[1][i] = dz[2][i] = 0.f; }
-#pragma unroll 4
+#pragma unroll 8
     for (int k = lane; k < dim; k += 32) {
       const float2 f0 = ph[k];
       const float pr = f0.x * f0.x + f0.y * f0.y;
@@ -1067,7 +1070,7 @@ __global__ void dense_point_kernel(PointArgs a) {
         atomicAdd(&hacc[3 * m + c], g[c]);
       }
     }
-#pragma unroll 4
+#pragma unroll 8
     for (int k = lane; k < dim; k += 32) {
       float O = 0.f, Od[3] = {0.f, 0.f, 0.f};
 #pragma unroll
@@ -1501,6 +1504,7 @@ struct EmbedArgs {
   float* dthetaJ;           // [P][n] float4
   int32_t n;
   int64_t npts[3], pt_base[3];
+  const float2* cs;         // [P][n] (cos, sin) of theta / 2
 };
 
 struct Dual4 {
@@ -1510,9 +1514,24 @@ __device__ __forceinline__ Dual4 dmul4(const Dual4& a, const Dual4& b) {
   return {a.v * b.v, a.d0 * b.v + a.v * b.d0, a.d1 * b.v + a.v * b.d1, a.d2 * b.v + a.v * b.d2};
 }
 
-__global__ void dense_embed_grad_kernel(EmbedArgs a) {
-  const int n = a.n, dim = 1 << n;
-  const int lane = threadIdx.x & 31;
+// Embedding gradients from mu (n >= 5), warp per point. With the flipped-factor identity (the
+// derivative of a qubit's cos/sin(theta/2) factor is the other one, halved and signed),
+//   dL/dtheta_q = sum_k sign_q(k) [F_q(k).v mu_0[k] + sum_d F_q(k).d_d mu_d[k]],
+//   dL/dJ_{q,d} = sum_k sign_q(k) F_q(k).v mu_d[k],
+// with F_q(k) the product state's dual (value; x, y, t tangents) with qubit q's factor flipped
+// and sign_q(k) = +1 where qubit q is 1. Split k = (hi, lo), lo the five lowest index bits:
+// the product state is Hi(hi) x Lo(lo) and a flip stays inside one factor, so every sum is a
+// 2^(n-5) x 32 table contraction; lane = lo, one pass over the rows hi of mu:
+//   low q:  sum_lo sign [LF_q.v (A0 + sum_d B_d) + sum_d LF_q.d_d A_d],  A_d[lo] = sum_hi Hi.v mu_d,
+//           A0 = sum_hi Hi.v mu_0, B_d = sum_hi Hi.d_d mu_d;
+//   high q: sum_hi sign [HF_q.v (sum_lo Lo.v mu_0 + Lo.d_d mu_d) + sum_d HF_q.d_d sum_lo Lo.v mu_d].
+constexpr int EG_WARPS = 8;
+__global__ void __launch_bounds__(EG_WARPS * 32) dense_embed_grad_kernel(EmbedArgs a) {
+  constexpr int NHQ = QP_MAXQ - 5;                       // high qubits at most
+  __shared__ float4 tabs[EG_WARPS][NHQ + 1][32];         // per warp: Hi, then HF_q, over hi
+  const int n = a.n, dim = 1 << n, nh = n - 5, nhi = dim >> 5;
+  const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+  float4 (*tb)[32] = tabs[wl];
   const int64_t wg = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const int64_t total = a.npts[0] + a.npts[1] + a.npts[2];
@@ -1520,66 +1539,118 @@ __global__ void dense_embed_grad_kernel(EmbedArgs a) {
     int set = 0;
     int64_t li = gq;
     if (li >= a.npts[0]) { li -= a.npts[0]; set = 1; if (li >= a.npts[1]) { li -= a.npts[1]; set = 2; } }
-    const int nv = set == 0 ? 4 : 1;
+    const bool nv4 = set == 0;
     const int64_t gp = a.pt_base[set] + li;
-    const float4* tj = reinterpret_cast<const float4*>(a.thetaJ) + gp * n;
-    float cs[QP_MAXQ], sn[QP_MAXQ], Jx[QP_MAXQ], Jy[QP_MAXQ], Jt[QP_MAXQ];
+    // lane q < n holds qubit q's (cos, sin) of theta/2 and its J
+    float cq = 1.f, sq = 0.f;
+    float4 jq = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (lane < n) {
+      const float2 c2 = __ldg(a.cs + gp * n + lane);
+      cq = c2.x; sq = c2.y;
+      jq = __ldg(reinterpret_cast<const float4*>(a.thetaJ) + gp * n + lane);
+    }
+    // factor and flipped factor of qubit q at bit value `bit`, as duals (all lanes shuffle)
+    auto factors = [&](int q, bool bit, Dual4& F, Dual4& G) {
+      const float c = __shfl_sync(0xffffffffu, cq, q), sn = __shfl_sync(0xffffffffu, sq, q);
+      const float jx = __shfl_sync(0xffffffffu, jq.y, q), jy = __shfl_sync(0xffffffffu, jq.z, q),
+                  jt = __shfl_sync(0xffffffffu, jq.w, q);
+      const float f = bit ? sn : c, d = bit ? 0.5f * c : -0.5f * sn;
+      const float g = bit ? c : sn, e = bit ? -0.5f * sn : 0.5f * c;
+      F = {f, d * jx, d * jy, d * jt};
+      G = {g, e * jx, e * jy, e * jt};
+    };
+    // low factors of this lane's lo (qubit n - 1 - b <-> bit b), prefix / suffix products
+    Dual4 LF[5], Lo;
+    {
+      Dual4 F[5], G[5], pre[6], suf[6];
 #pragma unroll
-    for (int q = 0; q < QP_MAXQ; ++q) {
-      if (q < n) {
-        const float4 t = tj[q];
-        sincosf(0.5f * t.x, &sn[q], &cs[q]);
-        Jx[q] = t.y; Jy[q] = t.z; Jt[q] = t.w;
-      } else {
-        cs[q] = 1.f; sn[q] = 0.f; Jx[q] = Jy[q] = Jt[q] = 0.f;
+      for (int b = 0; b < 5; ++b) factors(n - 1 - b, (lane >> b) & 1, F[b], G[b]);
+      pre[0] = {1.f, 0.f, 0.f, 0.f};
+      suf[5] = {1.f, 0.f, 0.f, 0.f};
+#pragma unroll
+      for (int b = 0; b < 5; ++b) pre[b + 1] = dmul4(pre[b], F[b]);
+#pragma unroll
+      for (int b = 4; b >= 0; --b) suf[b] = dmul4(F[b], suf[b + 1]);
+      Lo = pre[5];
+#pragma unroll
+      for (int b = 0; b < 5; ++b) LF[b] = dmul4(dmul4(pre[b], G[b]), suf[b + 1]);
+    }
+    // high tables for hi = lane (qubit q < nh <-> bit nh - 1 - q of hi)
+    {
+      Dual4 F[NHQ], G[NHQ], pre[NHQ + 1], suf[NHQ + 1];
+#pragma unroll
+      for (int q = 0; q < NHQ; ++q) {
+        F[q] = {1.f, 0.f, 0.f, 0.f};
+        G[q] = {1.f, 0.f, 0.f, 0.f};
+        if (q < nh) factors(q, (lane >> (nh - 1 - q)) & 1, F[q], G[q]);
+      }
+      pre[0] = {1.f, 0.f, 0.f, 0.f};
+      suf[NHQ] = {1.f, 0.f, 0.f, 0.f};
+#pragma unroll
+      for (int q = 0; q < NHQ; ++q) pre[q + 1] = dmul4(pre[q], F[q]);
+#pragma unroll
+      for (int q = NHQ - 1; q >= 0; --q) suf[q] = dmul4(F[q], suf[q + 1]);
+      __syncwarp();   // the previous point's tables are read
+      if (lane < nhi) {
+        tb[0][lane] = make_float4(pre[NHQ].v, pre[NHQ].d0, pre[NHQ].d1, pre[NHQ].d2);
+#pragma unroll
+        for (int q = 0; q < NHQ; ++q)
+          if (q < nh) {
+            const Dual4 h = dmul4(dmul4(pre[q], G[q]), suf[q + 1]);
+            tb[1 + q][lane] = make_float4(h.v, h.d0, h.d1, h.d2);
+          }
+      }
+      __syncwarp();
+    }
+    // one pass over the rows of mu
+    const float* mu = a.mu + gp * 4 * dim;
+    float A0 = 0.f, Ad[3] = {0.f, 0.f, 0.f}, Bd[3] = {0.f, 0.f, 0.f};
+    float gh[NHQ], gJh[3][NHQ];
+#pragma unroll
+    for (int q = 0; q < NHQ; ++q) { gh[q] = 0.f; gJh[0][q] = gJh[1][q] = gJh[2][q] = 0.f; }
+    for (int hi = 0; hi < nhi; ++hi) {
+      const int k = hi * 32 + lane;
+      const float m0 = mu[k];
+      float md[3] = {0.f, 0.f, 0.f};
+      if (nv4) { md[0] = mu[dim + k]; md[1] = mu[2 * dim + k]; md[2] = mu[3 * dim + k]; }
+      const float4 H = tb[0][hi];
+      A0 += H.x * m0;
+      Ad[0] += H.x * md[0]; Ad[1] += H.x * md[1]; Ad[2] += H.x * md[2];
+      Bd[0] += H.y * md[0]; Bd[1] += H.z * md[1]; Bd[2] += H.w * md[2];
+      const float t0 = Lo.v * m0 + Lo.d0 * md[0] + Lo.d1 * md[1] + Lo.d2 * md[2];
+      const float td0 = Lo.v * md[0], td1 = Lo.v * md[1], td2 = Lo.v * md[2];
+#pragma unroll
+      for (int q = 0; q < NHQ; ++q) {
+        if (q < nh) {
+          const float4 HF = tb[1 + q][hi];
+          const float sg = ((hi >> (nh - 1 - q)) & 1) ? 1.f : -1.f;
+          gh[q] += sg * (HF.x * t0 + HF.y * td0 + HF.z * td1 + HF.w * td2);
+          gJh[0][q] += sg * HF.x * td0;
+          gJh[1][q] += sg * HF.x * td1;
+          gJh[2][q] += sg * HF.x * td2;
+        }
       }
     }
+    // this lane's contributions: low qubits from its lo, high qubits from its pass
     float gth[QP_MAXQ], gJ[3][QP_MAXQ];
 #pragma unroll
-    for (int q = 0; q < QP_MAXQ; ++q) gth[q] = gJ[0][q] = gJ[1][q] = gJ[2][q] = 0.f;
-    const float* mu = a.mu + gp * 4 * dim;
-    for (int k = lane; k < dim; k += 32) {
-      float m0 = mu[k], md[3] = {0.f, 0.f, 0.f};
-      if (nv == 4) { md[0] = mu[dim + k]; md[1] = mu[2 * dim + k]; md[2] = mu[3 * dim + k]; }
-      Dual4 pre[QP_MAXQ + 1], suf[QP_MAXQ + 1];
-      pre[0] = {1.f, 0.f, 0.f, 0.f};
+    for (int q = 0; q < QP_MAXQ; ++q) { gth[q] = 0.f; gJ[0][q] = gJ[1][q] = gJ[2][q] = 0.f; }
+#pragma unroll
+    for (int q = 0; q < NHQ; ++q) {
+      if (q < nh) { gth[q] = gh[q]; gJ[0][q] = gJh[0][q]; gJ[1][q] = gJh[1][q]; gJ[2][q] = gJh[2][q]; }
+    }
+    const float AB = A0 + Bd[0] + Bd[1] + Bd[2];
+#pragma unroll
+    for (int b = 0; b < 5; ++b) {
+      const float sg = ((lane >> b) & 1) ? 1.f : -1.f;
+      const float gl = sg * (LF[b].v * AB + LF[b].d0 * Ad[0] + LF[b].d1 * Ad[1] + LF[b].d2 * Ad[2]);
 #pragma unroll
       for (int q = 0; q < QP_MAXQ; ++q) {
-        Dual4 fq = {1.f, 0.f, 0.f, 0.f};
-        if (q < n) {
-          const bool bit = (k >> (n - 1 - q)) & 1;
-          const float f = bit ? sn[q] : cs[q], d = bit ? 0.5f * cs[q] : -0.5f * sn[q];
-          fq = {f, d * Jx[q], d * Jy[q], d * Jt[q]};
-        }
-        pre[q + 1] = dmul4(pre[q], fq);
-      }
-      suf[QP_MAXQ] = {1.f, 0.f, 0.f, 0.f};
-#pragma unroll
-      for (int q = QP_MAXQ - 1; q >= 0; --q) {
-        Dual4 fq = {1.f, 0.f, 0.f, 0.f};
-        if (q < n) {
-          const bool bit = (k >> (n - 1 - q)) & 1;
-          const float f = bit ? sn[q] : cs[q], d = bit ? 0.5f * cs[q] : -0.5f * sn[q];
-          fq = {f, d * Jx[q], d * Jy[q], d * Jt[q]};
-        }
-        suf[q] = dmul4(fq, suf[q + 1]);
-      }
-#pragma unroll
-      for (int q = 0; q < QP_MAXQ; ++q) {
-        if (q < n) {
-          const bool bit = (k >> (n - 1 - q)) & 1;
-          // factor of qubit q at the flipped bit
-          const float f = bit ? cs[q] : sn[q], d = bit ? -0.5f * sn[q] : 0.5f * cs[q];
-          const Dual4 fl = dmul4(dmul4(pre[q], {f, d * Jx[q], d * Jy[q], d * Jt[q]}), suf[q + 1]);
-          const float sg = bit ? 1.f : -1.f;
-          float acc = fl.v * m0;
-          if (nv == 4) {
-            acc += fl.d0 * md[0] + fl.d1 * md[1] + fl.d2 * md[2];
-            gJ[0][q] += sg * fl.v * md[0];
-            gJ[1][q] += sg * fl.v * md[1];
-            gJ[2][q] += sg * fl.v * md[2];
-          }
-          gth[q] += sg * acc;
+        if (q == n - 1 - b) {
+          gth[q] = gl;
+          gJ[0][q] = sg * LF[b].v * Ad[0];
+          gJ[1][q] = sg * LF[b].v * Ad[1];
+          gJ[2][q] = sg * LF[b].v * Ad[2];
         }
       }
     }

@@ -395,6 +395,9 @@ def test_invalid_arguments_rejected_on_host(torch_cuda):
         plan.loss_grad(torch.zeros(3, device="cuda"), {})
     rc = qp.lib().qp_forward(plan._h, None, None, 4, None, None, None)
     assert rc == 1
+    assert qp.lib().qp_plan_set_operands(plan._h, 2) == 1      # not an operand form
+    assert qp.lib().qp_plan_set_operands(None, 0) == 1
+    assert qp.lib().qp_plan_set_operands(plan._h, 1) == 0
 
 
 @pytest.mark.parametrize("omega_scale,head_scale", [(30.0, 20.0), (1e-4, 1.0), (1.0, 1e-3)])
