@@ -184,6 +184,17 @@ qp_status qp_loss_grad(qp_plan* plan, const float* d_params, const qp_batch* bat
 qp_status qp_count_dielectric(qp_plan* plan, const float* d_pts, int64_t n, int64_t* d_count,
                               void* stream);
 
+/* Black-hole collapse indicator (Sec. 5, "Black hole" loss landscape) from the energy slices
+ * U(t_k) that qp_loss_grad writes into its loss terms ([QP_NLOSS .. QP_NLOSS + energy_nt),
+ * float64), on the uniform slice times t_k = t_max k / (energy_nt - 1): the normalised
+ * energies U~(t_k) = U(t_k) / U(0) and I_BH = 1 - min over t_k >= delta of U~(t_k) (close to 1:
+ * the fields collapsed to the trivial solution after t = 0). d_out: float64 [energy_nt + 1],
+ * U~(t_0 .. t_{nt-1}) then I_BH. Device pointers, stream-ordered, no allocation. Not finite
+ * when U(0) is not positive. QP_ERR_INVALID_ARG for null pointers, energy_nt < 2 or above
+ * the energy-slice limit, t_max <= 0 or delta outside [0, t_max]. */
+qp_status qp_bh_indicator(const double* d_loss_terms, int32_t energy_nt, double t_max, double delta,
+                          double* d_out, void* stream);
+
 /* One loss evaluation of a batched step (qp_batch_step): parameters, point sets and
  * outputs of one instance, with the meaning they have in qp_loss_grad. */
 typedef struct {

@@ -193,3 +193,17 @@ def count_dielectric(prob, pts):
     pi, pd = prob_arrays(prob)
     p = _f64(pts).reshape(-1, 3)
     return int(lib().qpo_count_diel(_ptr(pi), _ptr(pd), _ptr(p), p.shape[0]))
+
+
+def bh_indicator(energy, t_max, delta):
+    """Black-hole collapse indicator of Sec. 5 ("Black hole" loss landscape) from the energy
+    slices U(t_k) (Eq. 31) of a loss evaluation on the uniform time grid t_k = t_max k/(nt-1):
+    the normalised energy U~(t_k) = U(t_k) / U(0) and I_BH = 1 - min over t_k >= delta of
+    U~(t_k). Returns (U~ [nt], I_BH). Plain definition, FP64."""
+    u = np.asarray(energy, dtype=np.float64)
+    nt = u.shape[0]
+    if nt < 2 or not t_max > 0 or not 0 <= delta <= t_max:
+        raise ValueError("need nt >= 2 and 0 <= delta <= t_max")
+    t = t_max * np.arange(nt) / (nt - 1)
+    ut = u / u[0]
+    return ut, float(1.0 - np.min(ut[t >= delta - 1e-12 * t_max]))

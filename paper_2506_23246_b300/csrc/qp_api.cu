@@ -4,6 +4,7 @@
 #include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
+#include <cmath>
 #include <cstdio>
 #include <algorithm>
 #include <cstring>
@@ -490,6 +491,18 @@ qp_status qp_set_workspace(qp_plan* plan, void* d_ws, size_t bytes) {
 int32_t qp_last_launch_count(const qp_plan* plan) { return plan ? plan->last_launches : -1; }
 
 int32_t qp_plan_path(const qp_plan* plan) { return plan ? plan->path : -1; }
+
+qp_status qp_bh_indicator(const double* d_loss_terms, int32_t energy_nt, double t_max, double delta,
+                          double* d_out, void* stream) {
+  if (!d_loss_terms || !d_out || energy_nt < 2 || energy_nt > QP_MAXNT || !(t_max > 0.0) ||
+      !(delta >= 0.0 && delta <= t_max))
+    return QP_ERR_INVALID_ARG;
+  // first slice with t_k >= delta (the same relative slack as the FP64 reference)
+  const double kf = std::ceil((delta / t_max - 1e-12) * (energy_nt - 1));
+  const int k0 = kf < 0.0 ? 0 : (kf > energy_nt - 1 ? energy_nt - 1 : (int)kf);
+  qpk::bh_indicator_kernel<<<1, 32, 0, (cudaStream_t)stream>>>(d_loss_terms + QP_NLOSS, energy_nt, k0, d_out);
+  return cuda_status(cudaGetLastError());
+}
 
 qp_status qp_plan_set_operands(qp_plan* plan, int32_t operands) {
   if (!plan || (operands != QP_OPERANDS_FP16_PAIRS && operands != QP_OPERANDS_TF32_PAIRS))

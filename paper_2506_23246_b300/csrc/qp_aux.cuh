@@ -86,6 +86,23 @@ __global__ void prep_kernel(PrepArgs a) {
   if (l == 0) pauli_coords(U, a.enc == 0 ? 0 : 1, a.cenc + q * 4);
 }
 
+// --------------------------------------------------------------------------- BH indicator
+// Sec. 5: U~(t_k) = U(t_k) / U(0) for the energy slices u[0 .. nt), and I_BH = 1 - min over
+// the slices k >= k0 (t_k >= delta) of U~(t_k). One warp.
+__global__ void bh_indicator_kernel(const double* u, int nt, int k0, double* out) {
+  const int lane = threadIdx.x;
+  const double u0 = u[0];
+  double mn = 1.0 / 0.0;
+  for (int k = lane; k < nt; k += 32) {
+    const double r = u[k] / u0;
+    out[k] = r;
+    if (k >= k0) mn = fmin(mn, r);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mn = fmin(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+  if (lane == 0) out[nt] = 1.0 - mn;
+}
+
 // --------------------------------------------------------------------------- premap
 
 struct PremapArgs {

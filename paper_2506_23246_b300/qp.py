@@ -90,6 +90,8 @@ def lib():
         L.qp_plan_path.restype = I32
         L.qp_plan_set_operands.argtypes = [P, I32]
         L.qp_plan_set_operands.restype = I32
+        L.qp_bh_indicator.argtypes = [P, I32, ctypes.c_double, ctypes.c_double, P, P]
+        L.qp_bh_indicator.restype = I32
         L.qp_set_profile_events.argtypes = [P, P, P]
         L.qp_set_profile_events.restype = I32
         L.qp_sched_selftest.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_uint]
@@ -261,6 +263,22 @@ class Plan:
         s = ctypes.c_void_p(start.cuda_event) if start is not None else ctypes.c_void_p(0)
         e = ctypes.c_void_p(stop.cuda_event) if stop is not None else ctypes.c_void_p(0)
         _check(lib().qp_set_profile_events(self._h, s, e), "qp_set_profile_events")
+
+
+def bh_indicator(loss_terms, energy_nt, t_max, delta, out=None, stream=None):
+    """Black-hole collapse indicator (Sec. 5) from the loss terms of loss_grad: a float64
+    device tensor [energy_nt + 1], the normalised energies U(t_k) / U(0) then I_BH."""
+    if not isinstance(loss_terms, torch.Tensor) or loss_terms.device.type != "cuda" or \
+            loss_terms.dtype != torch.float64 or not loss_terms.is_contiguous():
+        raise ValueError("loss_terms must be a contiguous float64 CUDA tensor")
+    if loss_terms.numel() < NLOSS + energy_nt:
+        raise ValueError("loss_terms holds fewer than 9 + energy_nt values")
+    if out is None:
+        out = torch.empty(energy_nt + 1, dtype=torch.float64, device=loss_terms.device)
+    s = stream if stream is not None else torch.cuda.current_stream(loss_terms.device)
+    _check(lib().qp_bh_indicator(_ptr(loss_terms), int(energy_nt), float(t_max), float(delta), _ptr(out),
+                                 ctypes.c_void_p(s.cuda_stream)), "qp_bh_indicator")
+    return out
 
 
 def batch_step(plans, params, sets, outs=None, norms=None, stream=None):

@@ -423,3 +423,30 @@ def test_dense_fp16_pair_operand_ranges(torch_cuda, oracle, omega_scale, head_sc
     mlp = rng.choice(np.arange(lay["fixed"], lay["circuit"]), 16, replace=False)
     idx = np.concatenate([np.sort(mlp), np.arange(lay["circuit"], lay["total"])])
     _loss_grad_check(torch_cuda, oracle, circ, prob, params, sets, idx, path="gemm_3xtf32")
+
+
+@pytest.mark.parametrize("path", ["simt", "gemm_3xtf32"])
+def test_bh_indicator_parity(torch_cuda, oracle, path):
+    """Black-hole indicator (Sec. 5) from the energy slices of one loss evaluation: the
+    normalised energies and I_BH against the oracle's, with delta between slices; host-side
+    argument checks."""
+    from paper_2506_23246_b300 import qp
+    torch = torch_cuda
+    circ = W.c3_circuit(8, 6)
+    prob = W.c3_problem("vacuum", 4, 4, 5)
+    tmax = W.c3_tmax("vacuum")
+    sets = {"colloc": W.grid_points(4, 4, 5, tmax), "ic": W.ic_grid(4, 2)}
+    params = W.init_params(circ, 4)
+    plan = qp.Plan(circ, prob, path=path)
+    dp = torch.tensor(params, device="cuda")
+    dsets = {k: torch.tensor(v, device="cuda") for k, v in sets.items()}
+    loss, _ = plan.loss_grad(dp, dsets)
+    lo = oracle.loss(circ, prob, params, sets)
+    for delta in (0.0, 0.3 * tmax, tmax):
+        out = qp.bh_indicator(loss, 5, tmax, delta).cpu().numpy()
+        ut, ibh = oracle.bh_indicator(lo[9:14], tmax, delta)
+        assert np.max(np.abs(out[:5] - ut)) < TOL * np.max(np.abs(ut)), (delta, out, ut)
+        assert abs(out[5] - ibh) < TOL * max(1.0, abs(ibh)), (delta, out[5], ibh)
+    bad = torch.zeros(6, dtype=torch.float64, device="cuda")
+    assert qp.lib().qp_bh_indicator(qp._ptr(loss), 1, tmax, 0.0, qp._ptr(bad), None) == 1
+    assert qp.lib().qp_bh_indicator(qp._ptr(loss), 5, tmax, 2 * tmax, qp._ptr(bad), None) == 1

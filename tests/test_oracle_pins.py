@@ -492,3 +492,54 @@ def test_dielectric_eps_limits(oracle):
         df[0, 0, 2] = 1.0
         out = oracle.loss_from_fields(prob, pts, f, df)
         assert abs(out[4] - (eps * 0.4) ** 2) < 1e-4
+
+
+# ----------------------------------------------------------------------------- BH indicator
+
+def _bh_fields(amp, nx=16, ny=16, nt=6, tmax=1.5):
+    """Energy slices of Ez = Hy = amp(t) cos(2 pi x) on a full-period grid: U(t) =
+    amp(t)^2 * (nx ny / 2) exactly (sum of cos^2 over whole periods)."""
+    pts = W.grid_points(nx, ny, nt, tmax).astype(np.float64)
+    prob = W.problem("vacuum", w_energy=0.0, energy_slice=nx * ny, energy_nt=nt)
+    a = amp(pts[:, 2])
+    ph = 2 * math.pi * pts[:, 0]
+    f = np.stack([a * np.cos(ph), np.zeros_like(ph), a * np.cos(ph)], axis=1)
+    out = oracle_api().loss_from_fields(prob, pts, f, np.zeros((pts.shape[0], 9)))
+    return out[9:9 + nt], tmax, nt
+
+
+def oracle_api():
+    from oracle import api
+    return api
+
+
+def test_bh_indicator_constant_energy(oracle):
+    """A lossless field keeps U(t) = U(0): U~ = 1 at every slice and I_BH = 0."""
+    u, tmax, nt = _bh_fields(lambda t: np.ones_like(t))
+    ut, ibh = oracle.bh_indicator(u, tmax, 0.2)
+    assert np.max(np.abs(ut - 1.0)) < 1e-12 and abs(ibh) < 1e-12
+
+
+def test_bh_indicator_exponential_decay(oracle):
+    """Amplitude exp(-lam t): U~(t) = exp(-2 lam t) in closed form, I_BH = 1 - exp(-2 lam T);
+    delta = T leaves only the last slice."""
+    lam = 0.8
+    u, tmax, nt = _bh_fields(lambda t: np.exp(-lam * t))
+    ut, ibh = oracle.bh_indicator(u, tmax, 0.1)
+    t = tmax * np.arange(nt) / (nt - 1)
+    assert np.max(np.abs(ut - np.exp(-2 * lam * t))) < 1e-6   # float32 grid times
+    assert abs(ibh - (1 - math.exp(-2 * lam * tmax))) < 1e-6
+    _, ibh_last = oracle.bh_indicator(u, tmax, tmax)
+    assert abs(ibh_last - ibh) < 1e-12
+
+
+def test_bh_indicator_collapse_and_window(oracle):
+    """Collapse to the trivial solution (fields vanish after t = 0): I_BH = 1; a growing
+    amplitude gives a negative I_BH; delta excludes earlier slices from the minimum."""
+    u, tmax, nt = _bh_fields(lambda t: np.where(t > 0, 0.0, 1.0))
+    assert abs(oracle.bh_indicator(u, tmax, 0.1)[1] - 1.0) < 1e-12
+    u, tmax, nt = _bh_fields(lambda t: 1.0 + t)
+    assert oracle.bh_indicator(u, tmax, 0.0)[1] == 0.0      # the minimum is U~(0) = 1
+    assert oracle.bh_indicator(u, tmax, 0.5)[1] < 0.0       # every slice after 0.5 has grown
+    with pytest.raises(ValueError):
+        oracle.bh_indicator(u, tmax, tmax * 1.5)
