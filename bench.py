@@ -557,7 +557,7 @@ def run_configs(a):
                 # dominant contraction: forward (qp_forward; fused n = 8) or weight gradient
                 # (n >= 9), 2 x rows x 2^(n+1) x 2^n algorithmic flops each
                 if prob is None or n <= 8:
-                    kernel = "dense_fused_fwd_kernel" if n in (7, 8) and prob is not None else "dense_row16_kernel<0>"
+                    kernel = ("dense_fused_fwd_kernel<%d>" % n) if n in (7, 8) and prob is not None else "dense_row16_kernel<0>"
                 else:
                     kernel = "dense_wgrad_gemm_kernel<%s>" % ("FP16" if ops == "fp16_pairs" else "TF32")
                 flops = 2.0 * rows * (2 * dim) * dim

@@ -397,8 +397,9 @@ qp_status qp_plan_create(const qp_circuit* circuit, const qp_problem* problem, i
         (n <= 8 && raise_smem_limit((void*)qpd::dense_sweep_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     qpd::swc_smem(n, pl->c.n_layers, qpd::swc_size(n, false))) != cudaSuccess) ||
         (fused_path(pl) &&
-         (raise_smem_limit((void*)qpd::dense_fused_fwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               qpd::fused_smem(n, pl->p.energy_nt).total) != cudaSuccess ||
+         (raise_smem_limit(n == 7 ? (void*)qpd::dense_fused_fwd_kernel<7> : (void*)qpd::dense_fused_fwd_kernel<8>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           qpd::fused_smem(n, pl->p.energy_nt).total) != cudaSuccess ||
           raise_smem_limit((void*)qpd::dense_mu_embed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                qpd::mu_smem_bytes(n)) != cudaSuccess))) {
       cudaGetLastError();
@@ -672,8 +673,11 @@ static qp_status dense_loss_grad(qp_plan* pl, const float* d_params, const float
     alignas(64) CUtensorMap tmaps[3];
     std::memset(tmaps, 0, sizeof(tmaps));
     fa.use_tma = lam_maps(fa.lam, fa.rtot, npts, (2 * dim) / 256, tmaps) ? 1 : 0;
-    qpd::dense_fused_fwd_kernel<<<fblocks, qpd::F_THREADS, qpd::fused_smem(n, pl->p.energy_nt).total, s>>>(
-        fa, tmaps[0], tmaps[1], tmaps[2]);
+    const int fsmem = qpd::fused_smem(n, pl->p.energy_nt).total;
+    if (n == 7)
+      qpd::dense_fused_fwd_kernel<7><<<fblocks, qpd::F_THREADS, fsmem, s>>>(fa, tmaps[0], tmaps[1], tmaps[2]);
+    else
+      qpd::dense_fused_fwd_kernel<8><<<fblocks, qpd::F_THREADS, fsmem, s>>>(fa, tmaps[0], tmaps[1], tmaps[2]);
     if (pl->prof_stop) cudaEventRecord(pl->prof_stop, s);
     launches += 1;
   } else {

@@ -115,12 +115,15 @@ __device__ __forceinline__ float slot_sum(float v) {
 // collocation points carry the residuals of Eqs. 8-10 (1/eps pointwise in the dielectric case,
 // Eq. 13 splits res1 by set) and the squared Poynting residual of Eq. 23; IC points the misfit
 // of Eq. 17 against the Gaussian pulse of Eq. 14; BC points Ez^2 (PEC). The point's
-// contributions to the QP_NLP FP64 partial sums go to `lt` (zero where the point adds
-// nothing), its energy-slice term of Eq. 31 to `ev` with slice index `slice` (-1: none).
+// contributions to the QP_NLP partial sums go to `lt` (zero where the point adds nothing),
+// its energy-slice term of Eq. 31 to `ev` with slice index `slice` (-1: none). The terms are
+// FP32 squares of FP32 residuals (one rounding each); callers sum them in FP64 or with
+// compensated FP32 sums, so the sums keep the terms' precision (FP64 arithmetic runs at a
+// small fraction of the FP32 rate on this part).
 __device__ __forceinline__ void point_loss_terms(const QPProblemDev& pb, int set, int64_t pt, int64_t npt,
                                                  const int32_t* counts, float x, float y,
                                                  const float (&f)[3], const float (&D)[3][3], bool active,
-                                                 double (&lt)[QP_NLP], int& slice, double& ev,
+                                                 float (&lt)[QP_NLP], int& slice, float& ev,
                                                  float (&g)[3], float (&gD)[3][3]) {
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
@@ -128,9 +131,9 @@ __device__ __forceinline__ void point_loss_terms(const QPProblemDev& pb, int set
     gD[c][0] = gD[c][1] = gD[c][2] = 0.f;
   }
 #pragma unroll
-  for (int i = 0; i < QP_NLP; ++i) lt[i] = 0.0;
+  for (int i = 0; i < QP_NLP; ++i) lt[i] = 0.f;
   slice = -1;
-  ev = 0.0;
+  ev = 0.f;
   if (!active) return;
   if (set == 0) {
     float eps = 1.f;
@@ -166,17 +169,17 @@ __device__ __forceinline__ void point_loss_terms(const QPProblemDev& pb, int set
     gD[1][2] = k2 + kE * f[1];
     gD[2][0] = -k1 * ie - kE * f[0];
     gD[2][2] = k3 + kE * f[2];
-    const double r1sq = (double)res1 * (double)res1;
-    lt[0] = diel ? 0.0 : r1sq;
-    lt[1] = diel ? r1sq : 0.0;
-    lt[2] = (double)res2 * (double)res2;
-    lt[3] = (double)res3 * (double)res3;
-    lt[4] = (double)e * (double)e;
+    const float r1sq = res1 * res1;
+    lt[0] = diel ? 0.f : r1sq;
+    lt[1] = diel ? r1sq : 0.f;
+    lt[2] = res2 * res2;
+    lt[3] = res3 * res3;
+    lt[4] = e * e;
     if (pb.energy_nt > 0 && pb.energy_slice > 0) {
       const int64_t k = (pt + pb.colloc_off) / pb.energy_slice;
       if (k < pb.energy_nt) {
         slice = (int)k;
-        ev = 0.5 * ((double)eps * f[0] * f[0] + (double)f[1] * f[1] + (double)f[2] * f[2]);
+        ev = 0.5f * (eps * f[0] * f[0] + f[1] * f[1] + f[2] * f[2]);
       }
     }
   } else if (set == 1) {
@@ -186,10 +189,11 @@ __device__ __forceinline__ void point_loss_terms(const QPProblemDev& pb, int set
     g[0] = k * (f[0] - e0);
     g[1] = k * f[1];
     g[2] = k * f[2];
-    lt[5] = (double)(f[0] - e0) * (f[0] - e0) + (double)f[1] * f[1] + (double)f[2] * f[2];
+    const float d0 = f[0] - e0;
+    lt[5] = d0 * d0 + f[1] * f[1] + f[2] * f[2];
   } else {
     g[0] = 2.f * pb.w_bc * f[0] / (float)(pb.norm[2] > 0 ? pb.norm[2] : npt);
-    lt[6] = (double)f[0] * f[0];
+    lt[6] = f[0] * f[0];
   }
 }
 
@@ -198,20 +202,20 @@ __device__ __forceinline__ void point_loss(const QPProblemDev& pb, int set, int6
                                            const int32_t* counts, float x, float y,
                                            const float (&f)[3], const float (&D)[3][3], bool active,
                                            bool acc, double* loss, float (&g)[3], float (&gD)[3][3]) {
-  double lt[QP_NLP], ev;
+  float lt[QP_NLP], ev;
   int slice;
   point_loss_terms(pb, set, pt, npt, counts, x, y, f, D, active, lt, slice, ev, g, gD);
   if (active && acc) {
     if (set == 0) {
-      atomicAdd(&loss[lt[1] != 0.0 ? 1 : 0], lt[0] + lt[1]);
-      atomicAdd(&loss[2], lt[2]);
-      atomicAdd(&loss[3], lt[3]);
-      atomicAdd(&loss[4], lt[4]);
-      if (slice >= 0) atomicAdd(&loss[QP_NLP + slice], ev);
+      atomicAdd(&loss[lt[1] != 0.f ? 1 : 0], (double)(lt[0] + lt[1]));
+      atomicAdd(&loss[2], (double)lt[2]);
+      atomicAdd(&loss[3], (double)lt[3]);
+      atomicAdd(&loss[4], (double)lt[4]);
+      if (slice >= 0) atomicAdd(&loss[QP_NLP + slice], (double)ev);
     } else if (set == 1) {
-      atomicAdd(&loss[5], lt[5]);
+      atomicAdd(&loss[5], (double)lt[5]);
     } else {
-      atomicAdd(&loss[6], lt[6]);
+      atomicAdd(&loss[6], (double)lt[6]);
     }
   }
 }

@@ -52,17 +52,20 @@ __device__ __forceinline__ void tma_store_3d(const CUtensorMap* m, const void* s
 __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
 // The bulk stores issued by this thread have finished reading shared memory.
 __device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+// All but the most recent bulk group of this thread have finished reading shared memory.
+__device__ __forceinline__ void bulk_wait_read_but1() { asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory"); }
 
-// Shared memory: two A stages (TF32 hi, lo), a three-slot ring of W blocks (copies run two
+// Shared memory: two A stages (FP16 hi, lo), a three-slot ring of W blocks (copies run two
 // K-steps ahead, across tile boundaries), and the persistent head/loss/barrier block. The
-// epilogue's exchange and readout buffers live in the W slot of the tile's last K-step (idle
-// until that slot's next copy, issued after the epilogue) when it is large enough, else in a
-// region of their own; the costate store staging lives in the A stages.
+// epilogue's readout buffers and the second costate staging buffer live in the W slot of the
+// tile's last K-step (idle until that slot's next copy, issued after the epilogue) when it is
+// large enough, else in a region of their own; the first staging buffer is the A stages.
 struct FusedSmem {
-  int a_bytes, w_bytes, wbase, epi, x0, tb, zp, zb, hw, sloss, hsum, rsc, bars, total;
+  int a_bytes, w_bytes, wbase, epi, zp, zb, st2, hw, sloss, hsum, rsc, bars, total;
   bool epi_in_w;
 };
-constexpr int F_EPI_BYTES = 2 * 32 * 32 * 4 + 2 * 3 * 32 * 32 * 4 + 2 * TM * QP_MAXQ * 4 + TM * QP_MAXQ * 4;
+constexpr int F_STG_BYTES = 2 * TM * 32 * 4;   // one 128-row x 32-column chunk per column half
+constexpr int F_EPI_BYTES = 16384 + F_STG_BYTES;
 __host__ __device__ inline FusedSmem fused_smem(int n, int nt) {
   FusedSmem f;
   const int nc = (2 << n) / 256;
@@ -79,13 +82,12 @@ __host__ __device__ inline FusedSmem fused_smem(int n, int nt) {
   f.rsc = o; o += TM * 4;                         // per-row unscale factors of the tile
   f.bars = o; o += 128;                           // w_full[3], mma_done[2], tensor-memory slot
   f.epi_in_w = f.w_bytes >= F_EPI_BYTES;
-  if (!f.epi_in_w) { f.epi = o; o += F_EPI_BYTES; }
+  if (!f.epi_in_w) { o = (o + 1023) / 1024 * 1024; f.epi = o; o += F_EPI_BYTES; }
   else f.epi = -1;
-  // offsets inside the epilogue block
-  f.x0 = 0;                                       // phi_0 chunk per column half
-  f.tb = f.x0 + 2 * 32 * 32 * 4;                  // O_d phi_d chunks per column half
-  f.zp = f.tb + 2 * 3 * 32 * 32 * 4;              // readout partials [half][row][i]
+  // offsets inside the epilogue block (1024-byte aligned, as the swizzled staging needs)
+  f.zp = 0;                                       // readout partials [half][row][i]
   f.zb = f.zp + 2 * TM * QP_MAXQ * 4;             // sign-sum coefficients [row][i]
+  f.st2 = 16384;                                  // second costate staging buffer
   f.total = o;
   return f;
 }
@@ -94,6 +96,13 @@ __host__ __device__ inline FusedSmem fused_smem(int n, int nt) {
 __device__ __forceinline__ void named_bar(int id) {
   __syncwarp();
   asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(128) : "memory");
+}
+// Compensated accumulation (Knuth's TwoSum): s + c holds the running sum of the added FP32
+// terms to about twice FP32 precision, with FP32 adds only.
+__device__ __forceinline__ void two_sum_add(float& s, float& c, float x) {
+  const float t = s + x, bp = t - s;
+  c += (s - (t - bp)) + (x - bp);
+  s = t;
 }
 // Barrier over the staging warps only (the control warp never joins it).
 __device__ __forceinline__ void stagers_bar() {
@@ -118,12 +127,17 @@ __device__ __forceinline__ float warp_sum_f(float v) {
 
 // tm_c, tm_i, tm_b: the costate rows of the collocation, IC and BC sets as (column, row,
 // 256-column block); tiles that run past a set's rows are clipped by the maps.
+// NQ = n (7 or 8, equal to a.n): the qubit count fixes the bit positions of the embedding
+// tables, the readout sign sums and the costate sign sums at compile time.
+template <int NQ>
 __global__ void __launch_bounds__(F_THREADS, 1) dense_fused_fwd_kernel(FusedArgs a, const __grid_constant__ CUtensorMap tm_c,
                                                                        const __grid_constant__ CUtensorMap tm_i,
                                                                        const __grid_constant__ CUtensorMap tm_b) {
+  static_assert(NQ == 7 || NQ == 8, "the fused kernel holds a tile's 2^(n+1) columns in tensor memory");
   extern __shared__ __align__(1024) unsigned char sm[];
-  const int n = a.n, dim = 1 << n, m = a.m, nt = a.pb.energy_nt;
-  const int nc = (2 << n) / 256;
+  constexpr int n = NQ, dim = 1 << n;
+  const int m = a.m, nt = a.pb.energy_nt;
+  constexpr int nc = (2 << n) / 256;
   const FusedSmem L = fused_smem(n, nt);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int ws = warp & 3, hh = warp >> 2;        // tensor-memory lane group, column half
@@ -155,10 +169,10 @@ __global__ void __launch_bounds__(F_THREADS, 1) dense_fused_fwd_kernel(FusedArgs
   const int arow = tid & (TM - 1), khalf = tid >> 7;
   const int r = ws * 32 + lane;                   // tile row read from tensor memory
   const int half_cols = dim;                      // 2 dim columns split between two halves
-  // per-thread running sums over all tiles (point threads only)
-  double lacc[QP_NLP];
+  // per-thread running sums over all tiles (point threads only), compensated FP32
+  float lacc[QP_NLP], lcmp[QP_NLP];
 #pragma unroll
-  for (int i = 0; i < QP_NLP; ++i) lacc[i] = 0.0;
+  for (int i = 0; i < QP_NLP; ++i) lacc[i] = lcmp[i] = 0.f;
   float hg[3][QP_MAXQ], hb[3];
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
@@ -441,23 +455,23 @@ __global__ void __launch_bounds__(F_THREADS, 1) dense_fused_fwd_kernel(FusedArgs
       }
       const float* xp = a.pts[set] + ppc * 3;
       float g[3], gD[3][3];
-      double lt[QP_NLP], ev;
+      float lt[QP_NLP], ev;
       int slice;
       qpk::point_loss_terms(a.pb, set, ppc, np, a.counts, __ldg(xp), __ldg(xp + 1), f, D, active, lt, slice, ev, g, gD);
-      if (s_r != 0) ev = 0.0;   // each point once
+      if (s_r != 0) ev = 0.f;   // each point once
       if (s_r == 0) {
 #pragma unroll
-        for (int i = 0; i < QP_NLP; ++i) lacc[i] += lt[i];
+        for (int i = 0; i < QP_NLP; ++i) two_sum_add(lacc[i], lcmp[i], lt[i]);
 #pragma unroll
         for (int c = 0; c < 3; ++c) hb[c] += g[c];
       }
       // energy slices: one FP64 shared add per warp when the warp's points share a slice
       const int s0 = __shfl_sync(0xffffffffu, slice, 0);
       if (__all_sync(0xffffffffu, slice == s0)) {
-        const double evs = warp_sum_d(ev);
-        if (lane == 0 && s0 >= 0) atomicAdd(&sloss[QP_NLP + s0], evs);
+        const float evs = warp_sum_f(ev);
+        if (lane == 0 && s0 >= 0) atomicAdd(&sloss[QP_NLP + s0], (double)evs);
       } else if (slice >= 0 && s_r == 0) {
-        atomicAdd(&sloss[QP_NLP + slice], ev);
+        atomicAdd(&sloss[QP_NLP + slice], (double)ev);
       }
       // this row's cotangent weights: zbar (vector 0) or zbar_d (vector d), and its share of the
       // head gradient
@@ -514,11 +528,13 @@ __global__ void __launch_bounds__(F_THREADS, 1) dense_fused_fwd_kernel(FusedArgs
         for (int e = 0; e < 16; ++e) O[e] = u01[e & 3] + t23[e >> 2];
         float v[32];   // scaled amplitudes: the row scales are folded into O below
         qptc::tmem_ld32(tmem + ((uint32_t)(ws * 32) << 16) + col, v);
-        float4* stg = reinterpret_cast<float4*>(sm) + hh * 1024;   // [128 rows][8] float4 staging
+        // [128 rows][8] float4 staging, two buffers in turn: the A stages (idle during the
+        // epilogue) and a buffer beside the readout partials
+        float4* stg = reinterpret_cast<float4*>(((cc >> 5) & 1) ? epi + L.st2 : sm) + hh * 1024;
         const bool issuer = ws == 0 && lane == 0;
-        // the previous chunk's costates have left the staging (operand stage 0 is idle during
-        // the epilogue); 16-byte piece e of row r is staged at e ^ (r mod 8)
-        if (a.use_tma && issuer) bulk_wait_read();
+        // the store of the chunk before last (same buffer) has read the staging; 16-byte piece
+        // e of row r is staged at e ^ (r mod 8)
+        if (a.use_tma && issuer) bulk_wait_read_but1();
         named_bar(1 + hh);
         if (nv4) {
           // lambda_s = O_s phi_0 for s >= 1 (phi_0 from the quad's first lane), then
@@ -607,7 +623,7 @@ __global__ void __launch_bounds__(F_THREADS, 1) dense_fused_fwd_kernel(FusedArgs
   // ---- block partials: loss sums (FP64) and head gradients
 #pragma unroll
   for (int i = 0; i < QP_NLP; ++i) {
-    const double v = warp_sum_d(lacc[i]);
+    const double v = warp_sum_d((double)lacc[i] + (double)lcmp[i]);
     if (lane == 0 && warp < 4 && v != 0.0) atomicAdd(&sloss[i], v);
   }
 #pragma unroll
