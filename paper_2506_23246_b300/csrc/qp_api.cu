@@ -66,6 +66,18 @@ int geo_ppw(int n) { return 32 >> (n - geo_lb(n)); }
 // plan, so plans only ever raise it: a plan created later with a smaller need must not shrink
 // the allowance an earlier plan's launches rely on.
 static std::mutex g_attr_mu;
+// The weight-gradient kernel compiled for n qubits (7 .. 10; plans of fewer qubits never launch
+// it and take the 7-qubit form for their shared-memory limit).
+template <bool H16>
+static const void* wgrad_kernel(int n) {
+  switch (n) {
+    case 10: return (const void*)qpd::dense_wgrad_gemm_kernel<H16, 10>;
+    case 9: return (const void*)qpd::dense_wgrad_gemm_kernel<H16, 9>;
+    case 8: return (const void*)qpd::dense_wgrad_gemm_kernel<H16, 8>;
+    default: return (const void*)qpd::dense_wgrad_gemm_kernel<H16, 7>;
+  }
+}
+
 static cudaError_t raise_smem_limit(const void* fn, cudaFuncAttribute attr, int bytes) {
   std::lock_guard<std::mutex> lk(g_attr_mu);
   cudaFuncAttributes fa;
@@ -386,9 +398,9 @@ qp_status qp_plan_create(const qp_circuit* circuit, const qp_problem* problem, i
                          qpd::row16_smem_bytes()) != cudaSuccess ||
         raise_smem_limit((void*)qpd::dense_row16_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          qpd::row16_smem_bytes()) != cudaSuccess ||
-        raise_smem_limit((void*)qpd::dense_wgrad_gemm_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        raise_smem_limit(wgrad_kernel<false>(n), cudaFuncAttributeMaxDynamicSharedMemorySize,
                              qpd::wg_smem_bytes(n)) != cudaSuccess ||
-        raise_smem_limit((void*)qpd::dense_wgrad_gemm_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        raise_smem_limit(wgrad_kernel<true>(n), cudaFuncAttributeMaxDynamicSharedMemorySize,
                              qpd::wg_smem_bytes(n, true)) != cudaSuccess ||
         raise_smem_limit((void*)qpd::dense_sweep_left_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (1 << n) * 16 * 8) != cudaSuccess ||
@@ -400,8 +412,8 @@ qp_status qp_plan_create(const qp_circuit* circuit, const qp_problem* problem, i
          (raise_smem_limit(n == 7 ? (void*)qpd::dense_fused_fwd_kernel<7> : (void*)qpd::dense_fused_fwd_kernel<8>,
                            cudaFuncAttributeMaxDynamicSharedMemorySize,
                            qpd::fused_smem(n, pl->p.energy_nt).total) != cudaSuccess ||
-          raise_smem_limit((void*)qpd::dense_mu_embed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               qpd::mu_smem_bytes(n)) != cudaSuccess))) {
+          raise_smem_limit(n == 7 ? (void*)qpd::dense_mu_embed_kernel<7> : (void*)qpd::dense_mu_embed_kernel<8>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, qpd::mu_smem_bytes(n)) != cudaSuccess))) {
       cudaGetLastError();
       delete pl;
       return QP_ERR_CUDA;
@@ -733,10 +745,14 @@ static qp_status dense_loss_grad(qp_plan* pl, const float* d_params, const float
   wa.status = (int32_t*)(ws + w.status);
   if (pl->prof_start && !fused) cudaEventRecord(pl->prof_start, s);
   wa.scal = (const int32_t*)(ws + w.status) + 16;
-  if (fwd16)   // the forward recorded both operand ranges: FP16 pairs
-    qpd::dense_wgrad_gemm_kernel<true><<<wgm.tiles * wgm.ngroups, qpd::WG_THREADS, qpd::wg_smem_bytes(n, true), s>>>(wa);
-  else
-    qpd::dense_wgrad_gemm_kernel<false><<<wgm.tiles * wgm.ngroups, qpd::WG_THREADS, qpd::wg_smem_bytes(n), s>>>(wa);
+  {
+    // FP16 pairs when the forward recorded both operand ranges
+    void* wargs[] = {&wa};
+    const cudaError_t le = cudaLaunchKernel(fwd16 ? wgrad_kernel<true>(n) : wgrad_kernel<false>(n),
+                                            dim3((unsigned)(wgm.tiles * wgm.ngroups)), dim3(qpd::WG_THREADS), wargs,
+                                            qpd::wg_smem_bytes(n, fwd16), s);
+    if (le != cudaSuccess) return QP_ERR_CUDA;
+  }
   if (pl->prof_stop && !fused) cudaEventRecord(pl->prof_stop, s);
   launches += 1;
   qpd::SweepArgs sa;
@@ -804,7 +820,10 @@ static qp_status dense_loss_grad(qp_plan* pl, const float* d_params, const float
       ma.status = (int32_t*)(ws + w.status);
       const int64_t mt = ma.tile_end[2];
       const int mblocks = (int)(mt < pl->sm_count ? (mt > 0 ? mt : 1) : pl->sm_count);
-      qpd::dense_mu_embed_kernel<<<mblocks, qpd::MU_THREADS, qpd::mu_smem_bytes(n), s>>>(ma);
+      if (n == 7)
+        qpd::dense_mu_embed_kernel<7><<<mblocks, qpd::MU_THREADS, qpd::mu_smem_bytes(n), s>>>(ma);
+      else
+        qpd::dense_mu_embed_kernel<8><<<mblocks, qpd::MU_THREADS, qpd::mu_smem_bytes(n), s>>>(ma);
       launches += 1;
     } else {
       // back-projection mu = Re(U'^H lambda) per (point, vector) row, then the embedding

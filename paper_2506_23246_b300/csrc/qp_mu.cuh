@@ -155,10 +155,14 @@ __device__ __forceinline__ void mu_chunk(MuRow& R, int n, int s, int c, uint32_t
 constexpr int MU_STAGERS = 128;   // operand staging + embedding epilogue (4 warps)
 constexpr int MU_THREADS = MU_STAGERS + 32;
 
+// NQ = n (7 or 8, equal to a.n): the qubit count fixes the table bit positions and the qubit
+// index of every correlation at compile time.
+template <int NQ>
 __global__ void __launch_bounds__(MU_THREADS, 1) dense_mu_embed_kernel(MuArgs a) {
+  static_assert(NQ == 7 || NQ == 8, "one 256-column chunk of mu per row");
   extern __shared__ __align__(1024) unsigned char sm[];
-  const int n = a.n, dim = 1 << n;
-  const int ktot = 2 * dim, nch = dim, nkc = ktot / HKC;   // dim <= 256: one column chunk
+  constexpr int n = NQ, dim = 1 << n;
+  constexpr int ktot = 2 * dim, nch = dim, nkc = ktot / HKC;   // dim <= 256: one column chunk
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const bool ctrl = warp == MU_STAGERS / 32;
   const int abytes = TM * HKC * 2, wbytes = nch * HKC * 2;

@@ -98,11 +98,11 @@ struct WgAng {
   float4 f0;
   float jt;
 };
-__device__ __forceinline__ WgAng wg_load_ang(const WgArgs& a, int64_t kc, int tid) {
+__device__ __forceinline__ WgAng wg_load_ang(const WgArgs& a, int64_t kc, int tid, int n) {
   int set, ppc, nv;
   int64_t p0;
   wg_step_geom(a, kc, set, p0, ppc, nv);
-  const int n = a.n, pl = tid / n, q = tid % n;
+  const int pl = tid / n, q = tid % n;
   WgAng r;
   r.f0 = make_float4(0.f, 0.f, 0.f, 0.f);
   r.jt = 0.f;
@@ -184,10 +184,13 @@ __device__ __forceinline__ void wg_copy_rows(const WgArgs& a, int64_t kc, int nt
 
 // H16: FP16 operand pairs (kind::f16, one K = 16 MMA per term) with one power-of-two scale
 // per operand from the recorded ranges; else TF32 pairs (two K = 8 MMAs per term).
-template <bool H16>
+// NQ = n (7 .. 10, equal to a.n): the qubit count fixes the (point, qubit) slot arithmetic and
+// the table loops at compile time.
+template <bool H16, int NQ>
 __global__ void __launch_bounds__(WG_THREADS, 1) dense_wgrad_gemm_kernel(WgArgs a) {
+  static_assert(NQ >= 7 && NQ <= 10, "weight-gradient contraction: 7 to 10 qubits");
   extern __shared__ __align__(1024) unsigned char sm[];
-  const int n = a.n, dim = 1 << n;
+  constexpr int n = NQ, dim = 1 << n;
   const WgSmem L = wg_smem(n, H16 ? 2 : 4);
   float sR = 1.f, sL = 1.f;
   if (H16) {
@@ -245,14 +248,14 @@ __global__ void __launch_bounds__(WG_THREADS, 1) dense_wgrad_gemm_kernel(WgArgs 
         int set, ppc, nv;
         int64_t p0;
         wg_step_geom(a, c0, set, p0, ppc, nv);
-        wg_fac(facb, fid, n, ppc, wg_load_ang(a, c0, fid));
+        wg_fac(facb, fid, n, ppc, wg_load_ang(a, c0, fid, n));
         if (c0 + 1 < c1) {
           int set1, ppc1, nv1;
           int64_t p01;
           wg_step_geom(a, c0 + 1, set1, p01, ppc1, nv1);
-          wg_fac(facb + WG_FAC4, fid, n, ppc1, wg_load_ang(a, c0 + 1, fid));
+          wg_fac(facb + WG_FAC4, fid, n, ppc1, wg_load_ang(a, c0 + 1, fid, n));
         }
-        if (c0 + 2 < c1) tjn = wg_load_ang(a, c0 + 2, fid);
+        if (c0 + 2 < c1) tjn = wg_load_ang(a, c0 + 2, fid, n);
       }
     } else if (lane == 0) {
       for (int j = 0; j < WG_RING - 1 && c0 + j < c1; ++j) {
@@ -443,7 +446,7 @@ __global__ void __launch_bounds__(WG_THREADS, 1) dense_wgrad_gemm_kernel(WgArgs 
             int64_t p02;
             wg_step_geom(a, kc + 2, set2, p02, ppc2, nv2);
             wg_fac(facb + (it & 1) * WG_FAC4, fid, n, ppc2, tjn);
-            if (kc + 3 < c1) tjn = wg_load_ang(a, kc + 3, fid);
+            if (kc + 3 < c1) tjn = wg_load_ang(a, kc + 3, fid, n);
           }
         }
       } else {
