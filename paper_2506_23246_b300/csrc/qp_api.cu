@@ -726,7 +726,10 @@ static qp_status dense_loss_grad(qp_plan* pl, const float* d_params, const float
     pa.nE = 3 * n * L;
     pa.lmax = fwd16 ? (int32_t*)(ws + w.status) + 17 : nullptr;   // scale of the mu operand
     const int psmem = ((QP_NLP + pl->p.energy_nt) * 8 + 15) / 16 * 16 + (3 * pl->c.n_readout + 3) * 4;
-    qpd::dense_point_kernel<<<pl->blocks_grad, qpd::PT_POINT_THREADS, psmem, s>>>(pa);
+    if (n == 9)
+      qpd::dense_point_kernel<9><<<pl->blocks_grad, qpd::PT_POINT_THREADS, psmem, s>>>(pa);
+    else
+      qpd::dense_point_kernel<10><<<pl->blocks_grad, qpd::PT_POINT_THREADS, psmem, s>>>(pa);
     launches += 1;
   }
   qpd::WgArgs wa;

@@ -971,9 +971,18 @@ struct PointArgs {
 // 8 warps per SM: a point's states (32 KiB at n = 10) are read twice, and the second read
 // should hit L2; twice as many warps in flight measured 40% slower
 constexpr int PT_POINT_THREADS = 256;
+// NQ = n (9 or 10; the fused kernel covers 7 and 8). Lane l holds amplitudes k = l + 32 j: the
+// sign of qubit i < n - 5 is bit n - 6 - i of j (a compile-time constant in the unrolled
+// loops), that of qubit i >= n - 5 bit n - 1 - i of the lane. Both passes load PT_JB
+// amplitudes of each vector before using them, so the loads of a batch are in flight together
+// (the costate stores of pass 2 would otherwise order every load behind the previous store).
+constexpr int PT_JB = 8;
+template <int NQ>
 __global__ void __launch_bounds__(PT_POINT_THREADS, 1) dense_point_kernel(PointArgs a) {
+  static_assert(NQ >= 9 && NQ <= QP_MAXQ, "point kernel of the 9- and 10-qubit path");
   extern __shared__ __align__(16) unsigned char psh[];
-  const int n = a.n, dim = 1 << n, m = a.m;
+  constexpr int n = NQ, dim = 1 << n, NJ = dim / 32, NH = n - 5;
+  const int m = a.m;
   const int nt = a.pb.energy_nt;
   double* sloss = reinterpret_cast<double*>(psh);
   float* hacc = reinterpret_cast<float*>(psh + ((QP_NLP + nt) * 8 + 15) / 16 * 16);
@@ -989,31 +998,59 @@ __global__ void __launch_bounds__(PT_POINT_THREADS, 1) dense_point_kernel(PointA
     int set = 0;
     int64_t li = gq;
     if (li >= a.npts[0]) { li -= a.npts[0]; set = 1; if (li >= a.npts[1]) { li -= a.npts[1]; set = 2; } }
-    const int nv = set == 0 ? 4 : 1;
+    const bool v4 = set == 0;
     float2* ph = a.phi + (a.pt_base[set] + li) * 4 * dim;
-    float z[QP_MAXQ], dz[3][QP_MAXQ];
+    // ---- pass 1: |phi_0|^2 and 2 Re(phi_d^* phi_0) summed over this lane's amplitudes, with
+    // the signs of the high qubits applied per j and those of the low qubits after the loop
+    float tp = 0.f, tq[3] = {0.f, 0.f, 0.f}, hp[NH], hq[3][NH];
 #pragma unroll
-    for (int i = 0; i < QP_MAXQ; ++i) { z[i] = 0.f; dz[0][i] = dz[1][i] = dz[2][i] = 0.f; }
-#pragma unroll 8
-    for (int k = lane; k < dim; k += 32) {
-      const float2 f0 = ph[k];
-      const float pr = f0.x * f0.x + f0.y * f0.y;
-      float q[3] = {0.f, 0.f, 0.f};
-      if (nv == 4) {
+    for (int i = 0; i < NH; ++i) { hp[i] = 0.f; hq[0][i] = hq[1][i] = hq[2][i] = 0.f; }
 #pragma unroll
-        for (int d = 0; d < 3; ++d) {
-          const float2 fd = ph[(1 + d) * dim + k];
-          q[d] = 2.f * (fd.x * f0.x + fd.y * f0.y);
-        }
+    for (int j0 = 0; j0 < NJ; j0 += PT_JB) {
+      float2 f0[PT_JB], fd[3][PT_JB];
+#pragma unroll
+      for (int u = 0; u < PT_JB; ++u) {
+        const int k = lane + 32 * (j0 + u);
+        f0[u] = ph[k];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) fd[d][u] = v4 ? ph[(1 + d) * dim + k] : make_float2(0.f, 0.f);
       }
 #pragma unroll
-      for (int i = 0; i < QP_MAXQ; ++i)
-        if (i < m) {
-          const float sg = ((k >> (n - 1 - i)) & 1) ? -1.f : 1.f;
-          z[i] += sg * pr;
+      for (int u = 0; u < PT_JB; ++u) {
+        const int j = j0 + u;
+        const float pr = f0[u].x * f0[u].x + f0[u].y * f0[u].y;
+        float q[3];
 #pragma unroll
-          for (int d = 0; d < 3; ++d) dz[d][i] += sg * q[d];
+        for (int d = 0; d < 3; ++d) q[d] = 2.f * (fd[d][u].x * f0[u].x + fd[d][u].y * f0[u].y);
+        tp += pr;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) tq[d] += q[d];
+#pragma unroll
+        for (int i = 0; i < NH; ++i) {
+          const bool neg = (j >> (NH - 1 - i)) & 1;
+          hp[i] += neg ? -pr : pr;
+#pragma unroll
+          for (int d = 0; d < 3; ++d) hq[d][i] += neg ? -q[d] : q[d];
         }
+      }
+    }
+    float z[QP_MAXQ], dz[3][QP_MAXQ];
+#pragma unroll
+    for (int i = 0; i < QP_MAXQ; ++i) {
+      float sv = 0.f, sd[3] = {0.f, 0.f, 0.f};
+      if (i < NH) {
+        sv = hp[i];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) sd[d] = hq[d][i];
+      } else if (i < n) {
+        const bool neg = (lane >> (n - 1 - i)) & 1;
+        sv = neg ? -tp : tp;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) sd[d] = neg ? -tq[d] : tq[d];
+      }
+      z[i] = i < m ? sv : 0.f;
+#pragma unroll
+      for (int d = 0; d < 3; ++d) dz[d][i] = i < m ? sd[d] : 0.f;
     }
 #pragma unroll
     for (int i = 0; i < QP_MAXQ; ++i)
@@ -1070,32 +1107,51 @@ __global__ void __launch_bounds__(PT_POINT_THREADS, 1) dense_point_kernel(PointA
         atomicAdd(&hacc[3 * m + c], g[c]);
       }
     }
-#pragma unroll 8
-    for (int k = lane; k < dim; k += 32) {
-      float O = 0.f, Od[3] = {0.f, 0.f, 0.f};
+    // ---- pass 2: costates; O(k) = (low-qubit part of this lane) + (high-qubit part of j)
+    // (zb and zbd are zero for the qubits that are not read out)
+    float Ol = 0.f, Odl[3] = {0.f, 0.f, 0.f};
 #pragma unroll
-      for (int i = 0; i < QP_MAXQ; ++i)
-        if (i < m) {
-          const float sg = ((k >> (n - 1 - i)) & 1) ? -1.f : 1.f;
-          O += sg * zb[i];
+    for (int i = NH; i < n; ++i) {
+      const bool neg = (lane >> (n - 1 - i)) & 1;
+      Ol += neg ? -zb[i] : zb[i];
 #pragma unroll
-          for (int d = 0; d < 3; ++d) Od[d] += sg * zbd[d][i];
-        }
-      const float2 f0 = ph[k];
-      float2 lam = make_float2(O * f0.x, O * f0.y);
-      if (nv == 4) {
+      for (int d = 0; d < 3; ++d) Odl[d] += neg ? -zbd[d][i] : zbd[d][i];
+    }
 #pragma unroll
-        for (int d = 0; d < 3; ++d) {
-          const float2 fd = ph[(1 + d) * dim + k];
-          lam.x += Od[d] * fd.x;
-          lam.y += Od[d] * fd.y;
-          const float2 ld = make_float2(Od[d] * f0.x, Od[d] * f0.y);
-          ph[(1 + d) * dim + k] = ld;
-          lm = fmaxf(lm, fmaxf(fabsf(ld.x), fabsf(ld.y)));
-        }
+    for (int j0 = 0; j0 < NJ; j0 += PT_JB) {
+      float2 f0[PT_JB], fd[3][PT_JB];
+#pragma unroll
+      for (int u = 0; u < PT_JB; ++u) {
+        const int k = lane + 32 * (j0 + u);
+        f0[u] = ph[k];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) fd[d][u] = v4 ? ph[(1 + d) * dim + k] : make_float2(0.f, 0.f);
       }
-      ph[k] = lam;
-      lm = fmaxf(lm, fmaxf(fabsf(lam.x), fabsf(lam.y)));
+#pragma unroll
+      for (int u = 0; u < PT_JB; ++u) {
+        const int j = j0 + u, k = lane + 32 * j;
+        float O = Ol, Od[3] = {Odl[0], Odl[1], Odl[2]};
+#pragma unroll
+        for (int i = 0; i < NH; ++i) {
+          const bool neg = (j >> (NH - 1 - i)) & 1;
+          O += neg ? -zb[i] : zb[i];
+#pragma unroll
+          for (int d = 0; d < 3; ++d) Od[d] += neg ? -zbd[d][i] : zbd[d][i];
+        }
+        float2 lam = make_float2(O * f0[u].x, O * f0[u].y);
+        if (v4) {
+#pragma unroll
+          for (int d = 0; d < 3; ++d) {
+            lam.x += Od[d] * fd[d][u].x;
+            lam.y += Od[d] * fd[d][u].y;
+            const float2 ld = make_float2(Od[d] * f0[u].x, Od[d] * f0[u].y);
+            ph[(1 + d) * dim + k] = ld;
+            lm = fmaxf(lm, fmaxf(fabsf(ld.x), fabsf(ld.y)));
+          }
+        }
+        ph[k] = lam;
+        lm = fmaxf(lm, fmaxf(fabsf(lam.x), fabsf(lam.y)));
+      }
     }
   }
   if (a.lmax) {   // one atomic per warp (same-address atomics serialise in L2)
