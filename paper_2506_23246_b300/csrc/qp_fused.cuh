@@ -97,13 +97,6 @@ __device__ __forceinline__ void named_bar(int id) {
   __syncwarp();
   asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(128) : "memory");
 }
-// Compensated accumulation (Knuth's TwoSum): s + c holds the running sum of the added FP32
-// terms to about twice FP32 precision, with FP32 adds only.
-__device__ __forceinline__ void two_sum_add(float& s, float& c, float x) {
-  const float t = s + x, bp = t - s;
-  c += (s - (t - bp)) + (x - bp);
-  s = t;
-}
 // Barrier over the staging warps only (the control warp never joins it).
 __device__ __forceinline__ void stagers_bar() {
   __syncwarp();
@@ -170,9 +163,7 @@ __global__ void __launch_bounds__(F_THREADS, 1) dense_fused_fwd_kernel(FusedArgs
   const int r = ws * 32 + lane;                   // tile row read from tensor memory
   const int half_cols = dim;                      // 2 dim columns split between two halves
   // per-thread running sums over all tiles (point threads only), compensated FP32
-  float lacc[QP_NLP], lcmp[QP_NLP];
-#pragma unroll
-  for (int i = 0; i < QP_NLP; ++i) lacc[i] = lcmp[i] = 0.f;
+  CSum lacc[QP_NLP];
   float hg[3][QP_MAXQ], hb[3];
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
@@ -461,7 +452,7 @@ __global__ void __launch_bounds__(F_THREADS, 1) dense_fused_fwd_kernel(FusedArgs
       if (s_r != 0) ev = 0.f;   // each point once
       if (s_r == 0) {
 #pragma unroll
-        for (int i = 0; i < QP_NLP; ++i) two_sum_add(lacc[i], lcmp[i], lt[i]);
+        for (int i = 0; i < QP_NLP; ++i) lacc[i].add(lt[i]);
 #pragma unroll
         for (int c = 0; c < 3; ++c) hb[c] += g[c];
       }
@@ -623,7 +614,7 @@ __global__ void __launch_bounds__(F_THREADS, 1) dense_fused_fwd_kernel(FusedArgs
   // ---- block partials: loss sums (FP64) and head gradients
 #pragma unroll
   for (int i = 0; i < QP_NLP; ++i) {
-    const double v = warp_sum_d((double)lacc[i] + (double)lcmp[i]);
+    const double v = warp_sum_d((double)lacc[i].s + (double)lacc[i].c);
     if (lane == 0 && warp < 4 && v != 0.0) atomicAdd(&sloss[i], v);
   }
 #pragma unroll
