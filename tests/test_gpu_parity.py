@@ -223,14 +223,15 @@ def test_dense_tensorcore_c3_loss_grad_parity(torch_cuda, oracle, medium):
 
 
 @pytest.mark.parametrize("n,L,operands,tol", [(10, 8, "fp16_pairs", TOL), (10, 8, "tf32_pairs", 3e-5),
-                                               (9, 3, "fp16_pairs", TOL)])
+                                               (9, 3, "fp16_pairs", TOL), (9, 3, "tf32_pairs", 3e-5)])
 def test_dense_tensorcore_c4_loss_grad_parity(torch_cuda, oracle, n, L, operands, tol):
     """10 qubits, 8 strongly entangling layers, RFF(64) + tanh MLP(32): every circuit and head
     parameter and a sample of MLP parameters. The MLP block goes through mu = Re(U'^H lambda)
     with K = 2048: FP16 pairs with the hi*hi products in their own accumulator hold 1e-5;
     3xTF32 in one accumulator (768 truncating additions per output) is held to 3e-5. The
     circuit block goes through the weight gradient on the same operand form. 9 qubits run the
-    same kernels with 16 rows of the (hi, lo) tables."""
+    same kernels with 16 rows of the (hi, lo) tables; the kernels are compiled per qubit count,
+    so each (n, operand form) pair here is its own weight-gradient and point-kernel build."""
     circ = W.c3_circuit(n, L)
     prob = W.c3_problem("vacuum", 4, 4, 3)
     sets = {"colloc": W.grid_points(4, 4, 3, 1.0), "ic": W.ic_grid(4, 2)}
