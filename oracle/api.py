@@ -35,7 +35,7 @@ def lib():
         L.qpo_forward.argtypes = [_P, _P, _P, _I64, _P, _P, ctypes.c_int]
         L.qpo_state.argtypes = [_P, _P, _P, _P, _P]
         L.qpo_layer_unitary.argtypes = [_P, _P, ctypes.c_int, _P, _P]
-        L.qpo_loss.argtypes = [_P, _P, _P, _P, _P, _I64, _P, _I64, _P, _I64, _P]
+        L.qpo_loss.argtypes = [_P, _P, _P, _P, _P, _I64, _P, _I64, _P, _I64, _P, ctypes.c_int]
         L.qpo_grad.argtypes = [_P, _P, _P, _P, _P, _I64, _P, _I64, _P, _I64, _P, _I64, _P,
                                ctypes.c_int]
         L.qpo_count_diel.restype = _I64
@@ -143,14 +143,17 @@ def _sets(sets):
     return out
 
 
-def loss(circ, prob, params, sets, norm=None):
+def loss(circ, prob, params, sets, norm=None, nthreads=None):
+    """Loss terms [9 + energy_nt]. The point evaluations run on nthreads threads (default: all
+    cores); the sums run in point order, so the result does not depend on the thread count."""
     ci = circ_array(circ)
     pi, pd = prob_arrays(prob, norm)
     p = _f64(params)
     c, i, b = _sets(sets)
     out = np.zeros(NLOSS + max(prob.get("energy_nt", 0), 0))
+    nt = nthreads or os.cpu_count() or 1
     if lib().qpo_loss(_ptr(ci), _ptr(pi), _ptr(pd), _ptr(p), _ptr(c), c.shape[0], _ptr(i),
-                      i.shape[0], _ptr(b), b.shape[0], _ptr(out)) != 0:
+                      i.shape[0], _ptr(b), b.shape[0], _ptr(out), nt) != 0:
         raise ValueError("bad circuit")
     return out
 

@@ -457,6 +457,15 @@ void loss_terms(const Prob& pb, const double* pc, int64_t Bc, const std::vector<
   for (int k = 0; k < pb.nt; ++k) out[9 + k] = U[k];
 }
 
+template <class F>
+void parallel_for(int64_t n, int nthreads, F fn) {
+  if (nthreads <= 1 || n <= 1) { for (int64_t i = 0; i < n; ++i) fn(i); return; }
+  std::vector<std::thread> th;
+  for (int t = 0; t < nthreads; ++t)
+    th.emplace_back([&, t] { for (int64_t i = t; i < n; i += nthreads) fn(i); });
+  for (auto& x : th) x.join();
+}
+
 void to_duals(const R f[3], D* F, D* DF) {
   for (int c = 0; c < 3; ++c) {
     F[c] = {f[c].c[0], f[c].c[4]};
@@ -472,25 +481,30 @@ std::vector<R> make_params(const Circ& c, const double* params, int64_t sel) {
   return P;
 }
 
+// The point evaluations are independent, so they may run on several threads (each writes
+// only its own point's entries); the loss sums of loss_terms then run in point order on one
+// thread, so the result does not depend on the thread count.
 void eval_loss(const Circ& c, const Prob& pb, const double* params, int64_t sel, const double* pc,
                int64_t Bc, const double* pi_, int64_t Bi, const double* pbnd, int64_t Bb, double* out,
-               double* outp) {
+               double* outp, int nthreads) {
   std::vector<R> P = make_params(c, params, sel);
   std::vector<D> Fc(3 * Bc), DFc(9 * Bc), Fi(3 * Bi), Fb(3 * Bb);
-  R f[3];
-  for (int64_t b = 0; b < Bc; ++b) { eval_point(c, P.data(), pc + 3 * b, f); to_duals(f, &Fc[3 * b], &DFc[9 * b]); }
-  for (int64_t b = 0; b < Bi; ++b) { eval_point(c, P.data(), pi_ + 3 * b, f); to_duals(f, &Fi[3 * b], nullptr); }
-  for (int64_t b = 0; b < Bb; ++b) { eval_point(c, P.data(), pbnd + 3 * b, f); to_duals(f, &Fb[3 * b], nullptr); }
+  parallel_for(Bc + Bi + Bb, nthreads, [&](int64_t q) {
+    R f[3];
+    if (q < Bc) {
+      eval_point(c, P.data(), pc + 3 * q, f);
+      to_duals(f, &Fc[3 * q], &DFc[9 * q]);
+    } else if (q < Bc + Bi) {
+      const int64_t b = q - Bc;
+      eval_point(c, P.data(), pi_ + 3 * b, f);
+      to_duals(f, &Fi[3 * b], nullptr);
+    } else {
+      const int64_t b = q - Bc - Bi;
+      eval_point(c, P.data(), pbnd + 3 * b, f);
+      to_duals(f, &Fb[3 * b], nullptr);
+    }
+  });
   loss_terms(pb, pc, Bc, Fc, DFc, pi_, Bi, Fi, pbnd, Bb, Fb, out, outp);
-}
-
-template <class F>
-void parallel_for(int64_t n, int nthreads, F fn) {
-  if (nthreads <= 1 || n <= 1) { for (int64_t i = 0; i < n; ++i) fn(i); return; }
-  std::vector<std::thread> th;
-  for (int t = 0; t < nthreads; ++t)
-    th.emplace_back([&, t] { for (int64_t i = t; i < n; i += nthreads) fn(i); });
-  for (auto& x : th) x.join();
 }
 
 }  // namespace
@@ -589,11 +603,12 @@ int qpo_layer_unitary(const int* ci, const double* params, int layer, double* re
 // L_BC, [4] weighted L_energy, [5] MSE res1 (vacuum set), [6] MSE res1 (dielectric
 // set), [7] MSE res2, [8] MSE res3, [9 .. 9+nt) energy slice sums U(t_k).
 int qpo_loss(const int* ci, const int* pi, const double* pd, const double* params, const double* pc,
-             int64_t Bc, const double* pi_, int64_t Bi, const double* pbnd, int64_t Bb, double* out) {
+             int64_t Bc, const double* pi_, int64_t Bi, const double* pbnd, int64_t Bb, double* out,
+             int nthreads) {
   Circ c = read_circ(ci);
   if (!circ_ok(c)) return 1;
   Prob pb = read_prob(pi, pd);
-  eval_loss(c, pb, params, -1, pc, Bc, pi_, Bi, pbnd, Bb, out, nullptr);
+  eval_loss(c, pb, params, -1, pc, Bc, pi_, Bi, pbnd, Bb, out, nullptr, nthreads);
   return 0;
 }
 
@@ -607,10 +622,14 @@ int qpo_grad(const int* ci, const int* pi, const double* pd, const double* param
   const int64_t nfixed = c.premap == 1 ? 3LL * c.F : 0;
   for (int64_t i = 0; i < nidx; ++i)
     if (idx[i] < 0 || idx[i] >= c.total()) return 2;
-  parallel_for(nidx, nthreads, [&](int64_t i) {
+  // threads over the listed parameters, or over the points of each evaluation when there are
+  // fewer parameters than threads (same arithmetic either way)
+  const bool outer = nidx >= nthreads;
+  parallel_for(nidx, outer ? nthreads : 1, [&](int64_t i) {
     if (idx[i] < nfixed) { grad[i] = 0.0; return; }
     std::vector<double> out(9 + (pb.nt > 0 ? pb.nt : 0)), outp(9);
-    eval_loss(c, pb, params, idx[i], pc, Bc, pi_, Bi, pbnd, Bb, out.data(), outp.data());
+    eval_loss(c, pb, params, idx[i], pc, Bc, pi_, Bi, pbnd, Bb, out.data(), outp.data(),
+              outer ? 1 : nthreads);
     grad[i] = outp[0];
   });
   return 0;

@@ -543,3 +543,125 @@ def test_bh_indicator_collapse_and_window(oracle):
     assert oracle.bh_indicator(u, tmax, 0.5)[1] < 0.0       # every slice after 0.5 has grown
     with pytest.raises(ValueError):
         oracle.bh_indicator(u, tmax, tmax * 1.5)
+
+
+# ----------------------------------------------------------------------------- RFF + MLP premap
+
+def _premap_pin_params(circ, omega, layers, w_out, b_out, head_w, head_b):
+    """Flat parameter vector in the documented layout: Omega[F][3], per hidden layer W and b,
+    W_out, b_out, (no circuit parameters at L = 0), head W[3][1] and b[3]."""
+    parts = [np.asarray(omega, dtype=np.float64).ravel()]
+    for Wl, bl in layers:
+        parts += [np.asarray(Wl, dtype=np.float64).ravel(), np.asarray(bl, dtype=np.float64).ravel()]
+    parts += [np.asarray(w_out, dtype=np.float64).ravel(), np.asarray(b_out, dtype=np.float64).ravel(),
+              np.asarray(head_w, dtype=np.float64).ravel(), np.asarray(head_b, dtype=np.float64).ravel()]
+    p = np.concatenate(parts)
+    assert p.shape[0] == W.param_offsets(circ)["total"][0]
+    return p
+
+
+# <Z> after RX(theta)|0> is cos(theta) (Fig. 3 caption); with the scalings of Eq. 27a-e applied
+# to a = tanh(h) this is, as a function of h, and its derivative d<Z>/dh:
+_Z_OF_H = {
+    "acos": (lambda h: np.tanh(h), lambda h: 1 - np.tanh(h) ** 2),            # <Z> = a
+    "asin": (lambda h: -np.tanh(h), lambda h: -(1 - np.tanh(h) ** 2)),        # <Z> = -a
+    "pi": (lambda h: np.cos(np.pi * np.tanh(h)),
+           lambda h: -np.pi * np.sin(np.pi * np.tanh(h)) * (1 - np.tanh(h) ** 2)),
+    "bias": (lambda h: -np.sin(0.5 * np.pi * np.tanh(h)),                      # cos((a+1) pi/2)
+             lambda h: -0.5 * np.pi * np.cos(0.5 * np.pi * np.tanh(h)) * (1 - np.tanh(h) ** 2)),
+    "none": (lambda h: np.cos(np.tanh(h)), lambda h: -np.sin(np.tanh(h)) * (1 - np.tanh(h) ** 2)),
+}
+
+
+@pytest.mark.parametrize("scale", ["acos", "asin", "pi", "bias", "none"])
+@pytest.mark.parametrize("enc", ["rx", "ry"])
+def test_rff_premap_depth0_closed_form(oracle, scale, enc):
+    """One qubit, no ansatz layer, one frequency per input axis: the RFF features of Sec. 2.2
+    are (cos(omega v_d), sin(omega v_d)) and with no hidden layer the encoding angle is
+    scale(tanh(w_c cos(omega v_d) + w_s sin(omega v_d) + b)). The head (W, b) maps <Z> to the
+    three fields. Values and all three input derivatives against that closed form."""
+    zf, dzf = _Z_OF_H[scale]
+    head_w, head_b = np.array([1.0, -0.75, 2.5]), np.array([0.125, -0.5, 0.25])
+    for d in range(3):
+        omega = np.zeros((1, 3))
+        omega[0, d] = 1.7
+        wc, ws, b = 0.8, -0.45, 0.3
+        circ = W.circuit(1, 0, 1, ansatz="basic_rot", enc=enc, scale=scale, premap="rff_mlp",
+                         rff_freqs=1, mlp_width=4, mlp_depth=0)
+        params = _premap_pin_params(circ, omega, [], [[wc, ws]], [b], head_w, head_b)
+        pts = np.array([[0.3, -0.7, 0.55], [-0.9, 0.2, 0.05], [0.0, 0.6, 0.95]])
+        f, df = oracle.forward(circ, params, pts)
+        for i, v in enumerate(pts):
+            s = 1.7 * v[d]
+            h = wc * math.cos(s) + ws * math.sin(s) + b
+            dh = 1.7 * (-wc * math.sin(s) + ws * math.cos(s))
+            z, dz = zf(h), dzf(h) * dh
+            assert np.max(np.abs(f[i] - (head_w * z + head_b))) < 1e-13
+            for dd in range(3):
+                want = head_w * dz if dd == d else np.zeros(3)
+                assert np.max(np.abs(df[i, :, dd] - want)) < 1e-12, (scale, d, dd)
+
+
+@pytest.mark.parametrize("scale", ["acos", "asin", "pi"])
+def test_rff_premap_hidden_layers_closed_form(oracle, scale):
+    """One qubit, no ansatz layer, two frequencies over all three axes and one or two tanh
+    hidden layers: <Z> = z(h) with h = W_out tanh(... tanh(W_1 r + b_1) ...) + b_out and
+    r = [cos(Omega v), sin(Omega v)] (all cosines first, Sec. 2.2). Input derivatives by the
+    chain rule written out per layer."""
+    zf, dzf = _Z_OF_H[scale]
+    rng = np.random.default_rng(3)
+    F, H = 2, 3
+    omega = rng.normal(size=(F, 3))
+    for depth in (1, 2):
+        layers = []
+        fan = 2 * F
+        for _ in range(depth):
+            layers.append((rng.uniform(-0.8, 0.8, size=(H, fan)), rng.uniform(-0.3, 0.3, size=H)))
+            fan = H
+        w_out, b_out = rng.uniform(-0.8, 0.8, size=(1, fan)), rng.uniform(-0.3, 0.3, size=1)
+        circ = W.circuit(1, 0, 1, ansatz="noent_rot", enc="rx", scale=scale, premap="rff_mlp",
+                         rff_freqs=F, mlp_width=H, mlp_depth=depth)
+        head_w, head_b = np.array([1.0, 0.5, -2.0]), np.zeros(3)
+        params = _premap_pin_params(circ, omega, layers, w_out, b_out, head_w, head_b)
+        pts = W.uniform_points(4, 11).astype(np.float64)
+        f, df = oracle.forward(circ, params, pts)
+        for i, v in enumerate(pts):
+            arg = omega @ v
+            u = np.concatenate([np.cos(arg), np.sin(arg)])
+            du = np.concatenate([-np.sin(arg)[:, None] * omega, np.cos(arg)[:, None] * omega])
+            for Wl, bl in layers:
+                y = np.tanh(Wl @ u + bl)
+                du = (1 - y ** 2)[:, None] * (Wl @ du)
+                u = y
+            h = float((w_out @ u + b_out)[0])
+            dh = (w_out @ du).ravel()
+            z = zf(h)
+            assert np.max(np.abs(f[i] - (head_w * z + head_b))) < 1e-13, (scale, depth)
+            for d in range(3):
+                assert np.max(np.abs(df[i, :, d] - head_w * dzf(h) * dh[d])) < 1e-12, (scale, depth, d)
+
+
+def test_rff_premap_theta_and_jacobian(oracle):
+    """The encoding angles themselves (qpo_premap) for every scaling of Eq. 27a-e at a = tanh(h)
+    with h from one RFF frequency and no hidden layer, and their input Jacobian."""
+    omega = np.array([[0.9, -1.3, 0.4]])
+    wc, ws, b = -0.6, 1.1, 0.2
+    pts = W.uniform_points(5, 12).astype(np.float64)
+    theta_of_a = {"none": lambda a: a, "pi": lambda a: np.pi * a,
+                  "bias": lambda a: (a + 1) * np.pi / 2,
+                  "asin": lambda a: np.arcsin(a) + np.pi / 2, "acos": lambda a: np.arccos(a)}
+    dtheta_da = {"none": lambda a: 1.0, "pi": lambda a: np.pi, "bias": lambda a: np.pi / 2,
+                 "asin": lambda a: 1 / np.sqrt(1 - a * a), "acos": lambda a: -1 / np.sqrt(1 - a * a)}
+    for scale in theta_of_a:
+        circ = W.circuit(1, 0, 1, ansatz="noent_rot", enc="rx", scale=scale, premap="rff_mlp",
+                         rff_freqs=1, mlp_width=2, mlp_depth=0)
+        params = _premap_pin_params(circ, omega, [], [[wc, ws]], [b], np.ones(3), np.zeros(3))
+        th, J = oracle.premap(circ, params, pts)
+        for i, v in enumerate(pts):
+            s = float(omega[0] @ v)
+            h = wc * math.cos(s) + ws * math.sin(s) + b
+            a = math.tanh(h)
+            assert abs(th[i, 0] - theta_of_a[scale](a)) < 1e-13, scale
+            dh = (-wc * math.sin(s) + ws * math.cos(s)) * omega[0]
+            want = dtheta_da[scale](a) * (1 - a * a) * dh
+            assert np.max(np.abs(J[i, 0] - want)) < 1e-12, scale
