@@ -37,7 +37,7 @@ def _args():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--path", default="auto", choices=["auto", "simt", "gemm_3xtf32"],
+    ap.add_argument("--path", default="auto", choices=["auto", "simt", "gemm_split"],
                     help="statevector path of the library (auto = the library's choice; with "
                          "--workload configs: every path the configuration has)")
     ap.add_argument("--operands", default=None, choices=["fp16_pairs", "tf32_pairs"],
@@ -71,27 +71,34 @@ def _config(world):
 # ----------------------------------------------------------------------------- oracle arm
 
 def _oracle_sample(steps_budget_s=10.0, nthreads=None):
-    """Time the FP64 oracle (loss + gradient of every parameter) on a few collocation points
-    of the same workload; returns (points per second, threads, sample description)."""
+    """Time the FP64 oracle on a bounded sample of the same workload: k collocation points of
+    the grid and one initial-condition point per 16 of them (the step's ratio), with the energy
+    term and slices on, loss + the gradient of every parameter. Returns (collocation points per
+    second, threads, sample description)."""
     from oracle import api as oracle
     from paper_2506_23246_b300 import workloads as W
     circ, prob, params, sets = W.c3_workload(0)
     nt = nthreads or os.cpu_count() or 1
-    pts = sets["colloc"]
-    k = 1
+    pts, ic = sets["colloc"], sets["ic"]
+    stride_c = pts.shape[0] // 64
+    stride_i = ic.shape[0] // 4
     done = 0
+    nic = 0
     t0 = time.perf_counter()
     while True:
-        sub = {"colloc": pts[done:done + k]}
-        prob_s = dict(prob, energy_nt=0)
-        oracle.loss(circ, prob_s, params, sub)
-        oracle.grad(circ, prob_s, params, sub, nthreads=nt)
-        done += k
+        sub = {"colloc": pts[done * stride_c:done * stride_c + 1]}
+        if done % 16 == 0:
+            sub["ic"] = ic[(nic % 4) * stride_i:(nic % 4) * stride_i + 1]
+            nic += 1
+        oracle.loss(circ, prob, params, sub, nthreads=nt)
+        oracle.grad(circ, prob, params, sub, nthreads=nt)
+        done += 1
         el = time.perf_counter() - t0
         if el > steps_budget_s or done >= 64:
             break
-    return done / el, nt, "%d collocation points of the 64x64x16 grid, loss + all %d parameter " \
-        "gradients, %d threads" % (done, params.shape[0], nt)
+    return done / el, nt, "%d collocation points spread over the 64x64x16 grid and %d initial-" \
+        "condition points (the step's 16:1 ratio), energy term on: loss + all %d parameter " \
+        "gradients, %d threads" % (done, nic, params.shape[0], nt)
 
 
 def run_reference(a):
@@ -246,8 +253,12 @@ def run_native(a):
     grad = torch.empty(plan.n_params, dtype=torch.float32, device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
-    k0, k1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    plan.set_profile_events(k0, k1)
+    # device time of the measured kernels: the statevector kernel (SIMT path), or the three
+    # tensor-core contractions (forward, weight gradient, back-projection mu)
+    kinds = ["main"] if plan.path == "simt" else ["main", "wgrad", "mu"]
+    kev = {k: (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for k in kinds}
+    for k in kinds:
+        plan.set_profile_events(*kev[k], kernel=k)
 
     # data parallelism: the union of the ranks' slabs is one loss; whole-loss normalisers are
     # gathered once (the points do not move), and each step sums loss terms and gradients
@@ -269,7 +280,7 @@ def run_native(a):
 
     ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(a.steps)]
     ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(a.steps)]
-    kt = []
+    kt = {k: [] for k in kinds}
     clk = ClockSampler(local)
     clk.start()
     time.sleep(0.3)
@@ -281,8 +292,9 @@ def run_native(a):
         ev0[i].record(stream)
         step()
         ev1[i].record(stream)
-        k1.synchronize()
-        kt.append(k0.elapsed_time(k1))
+        for k in kinds:
+            kev[k][1].synchronize()
+            kt[k].append(kev[k][0].elapsed_time(kev[k][1]))
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
@@ -295,7 +307,6 @@ def run_native(a):
         ms = float(t.item())
     value = world * ncol / (ms / 1000.0)
 
-    kms = statistics.mean(kt)
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     peaks = {}
     try:
@@ -307,26 +318,48 @@ def run_native(a):
     nic = dsets["ic"].shape[0]
     if plan.path == "simt":
         # statevector kernel, FP32 SIMT
+        kms = statistics.mean(kt["main"])
         flops = ncol * circuit_flops_per_point(8, 6, 4) + nic * circuit_flops_per_point(8, 6, 1)
         peak = sms * 128 * 2 * sm_max * 1e6 / 1e12
-        roof = {"bound": "alu", "kernel": "circuit_kernel<8,true>",
+        achieved = flops / (kms / 1000.0) / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": profiled_traffic(),
+                "kernel": "circuit_kernel<8,true>", "kernel_ms": kms,
                 "peak_basis": "%d SMs x 128 FP32 FMA/clk x 2 x %.0f MHz (max SM clock of measured "
-                              "peaks)" % (sms, sm_max),
-                "traffic": profiled_traffic()}
+                              "peaks)" % (sms, sm_max)}
+        contractions = None
+        dtype = "f32"
     else:
-        # fused forward contraction Phi = R W^T on the tensor cores (the step's largest kernel),
-        # readout, losses and costates in its epilogue: algorithmic 2 M N K with M = (point,
-        # vector) rows, N = 2^(n+1), K = 2^n. The operands are FP16 pairs (hi + lo) with three
-        # FP16 products per term, so its ceiling is the dense FP16 (= BF16) peak / 3
+        # the three contractions of the step on the tensor cores, each algorithmically
+        # 2 x rows x 2^(n+1) x 2^n flops with rows = 4 per collocation point + 1 per IC point
+        # (forward Phi = R W^T, weight gradient G = sum R Lambda^H, back-projection
+        # mu = Re(U'^H Lambda)). Operands are FP16 pairs (hi + lo) with three FP16 products per
+        # term, so each one's ceiling is the dense FP16 (= BF16) peak / 3. The reported
+        # roofline is the one that takes the longest (all three do the same work).
         dim = 1 << 8
         flops = 2.0 * (4 * ncol + nic) * (2 * dim) * dim
         bf16 = peaks.get("bf16_tflops", 1800.0)
         peak = bf16 / 3.0
-        roof = {"bound": "tensor", "kernel": "dense_fused_fwd_kernel (FP16 pairs)",
-                "peak_basis": "measured bf16 %.0f TFLOP/s (dense FP16 runs at the BF16 rate) / 3 "
-                              "(three FP16 products per FP16-pair term)" % bf16,
-                "traffic": profiled_traffic("dense_fused_fwd_c3_8q6l.md", "qp_fused.cuh")}
-    achieved = flops / (kms / 1000.0) / 1e12
+        basis = ("measured bf16 %.0f TFLOP/s (dense FP16 runs at the BF16 rate) / 3 (three FP16 "
+                 "products per FP16-pair term)" % bf16)
+        names = {"main": ("dense_fused_fwd_kernel<8> (forward + readout + losses + costates)",
+                          "dense_fused_fwd_c3_8q6l.md", "qp_fused.cuh"),
+                 "wgrad": ("dense_wgrad_gemm_kernel<FP16, 8> (weight gradient)",
+                           "dense_wgrad_c3_8q6l.md", "qp_wgrad.cuh"),
+                 "mu": ("dense_mu_embed_kernel<8> (back-projection + embedding gradients)",
+                        "dense_mu_embed_c3_8q6l.md", "qp_mu.cuh")}
+        contractions = {}
+        for k in kinds:
+            kms_k = statistics.mean(kt[k])
+            ach = flops / (kms_k / 1000.0) / 1e12
+            contractions[k] = {"kernel": names[k][0], "kernel_ms": kms_k, "achieved": ach,
+                               "frac": ach / peak, "traffic": profiled_traffic(names[k][1], names[k][2])}
+        top = max(kinds, key=lambda k: contractions[k]["kernel_ms"])
+        c = contractions[top]
+        roof = {"bound": "tensor", "achieved": c["achieved"], "peak": peak, "unit": "TFLOP/s",
+                "frac": c["frac"], "traffic": c["traffic"], "kernel": c["kernel"],
+                "kernel_ms": c["kernel_ms"], "peak_basis": basis}
+        dtype = "fp16x2-split, fp32 accum"
 
     # end to end through the public call: pinned host inputs in, loss + gradient out
     hp = torch.tensor(params).pin_memory()
@@ -360,19 +393,19 @@ def run_native(a):
         t = torch.tensor([ems], device=dev)
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         ems = float(t.item())
-    plan.set_profile_events(None, None)
+    for k in kinds:
+        plan.set_profile_events(None, None, kernel=k)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
                 "warmup": max(a.warmup, 3), "ms_per_step": ms, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "scaling": "weak", "vs_baseline": None, "dtype": dtype, "data": "synthetic",
                 "config": _config(world),
                 "e2e": {"value": world * ncol / (ems / 1000.0), "unit": UNIT,
                         "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
                 "gpu_launches": launches * a.steps,
-                "roofline": {"bound": roof["bound"], "achieved": achieved, "peak": peak,
-                             "unit": "TFLOP/s", "frac": achieved / peak, "traffic": roof["traffic"],
-                             "kernel": roof["kernel"], "kernel_ms": kms, "peak_basis": roof["peak_basis"]},
+                "roofline": roof,
+                "contractions": contractions,
                 "path": plan.path,
                 "clocks": clocks}
         if not a.no_cpu_baseline and world == 1:
@@ -499,10 +532,10 @@ def run_configs(a):
              ("C2 6q/4L, 16384 colloc + 2048 IC + 2048 PEC, loss + gradient", c2c, c2pr, c2p, c2s,
               [("simt", "fp16_pairs")]),
              ("C3 8q/6L RFF64+MLP32 dielectric, 65536 colloc + 4096 IC, loss + gradient", c3c, c3pr,
-              c3p, c3s, [("simt", "fp16_pairs"), ("gemm_3xtf32", "fp16_pairs")]),
+              c3p, c3s, [("simt", "fp16_pairs"), ("gemm_split", "fp16_pairs")]),
              ("C4 10q/8L RFF64+MLP32, %d^3 colloc + %d IC, loss + gradient" % (a.grid, a.grid * a.grid),
               c4c, c4pr, c4p, c4s,
-              [("simt", "fp16_pairs"), ("gemm_3xtf32", "fp16_pairs"), ("gemm_3xtf32", "tf32_pairs")])]
+              [("simt", "fp16_pairs"), ("gemm_split", "fp16_pairs"), ("gemm_split", "tf32_pairs")])]
     for name, circ, prob, params, sets, paths in cases:
         if a.config and not name.startswith(a.config + " "):
             continue
@@ -524,26 +557,34 @@ def run_configs(a):
                 loss = torch.empty(9 + prob["energy_nt"], dtype=torch.float64, device=dev)
                 grad = torch.empty(plan.n_params, dtype=torch.float32, device=dev)
                 fn = lambda: plan.loss_grad(dp, dsets, out=(loss, grad))
-            k0, k1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            plan.set_profile_events(k0, k1)
+            # measured kernels: the statevector kernel (SIMT), the forward contraction
+            # (qp_forward), or all three contractions of a loss call (tensor cores)
+            kinds = ["main"] if (plan.path == "simt" or prob is None) else ["main", "wgrad", "mu"]
+            kev = {k: (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                   for k in kinds}
+            for k in kinds:
+                plan.set_profile_events(*kev[k], kernel=k)
             for _ in range(max(a.warmup, 3)):
                 fn()
             torch.cuda.synchronize()
             steps = a.steps
             ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
                   for _ in range(steps)]
-            kt = []
+            kt = {k: [] for k in kinds}
             for i in range(steps):
                 flush.fill_(float(i))
                 ev[i][0].record(stream)
                 fn()
                 ev[i][1].record(stream)
-                k1.synchronize()
-                kt.append(k0.elapsed_time(k1))
+                for k in kinds:
+                    kev[k][1].synchronize()
+                    kt[k].append(kev[k][0].elapsed_time(kev[k][1]))
             torch.cuda.synchronize()
-            plan.set_profile_events(None, None)
+            for k in kinds:
+                plan.set_profile_events(None, None, kernel=k)
             ms = sum(e0.elapsed_time(e1) for e0, e1 in ev) / steps
-            kms = statistics.mean(kt)
+            top = max(kinds, key=lambda k: statistics.mean(kt[k]))
+            kms = statistics.mean(kt[top])
             dim = 1 << n
             if plan.path == "simt":
                 kernel = "circuit_kernel<%d,%s>" % (n, "false" if prob is None else "true")
@@ -554,12 +595,13 @@ def run_configs(a):
                                 for k, v in dsets.items())
                 peak, bound = sms * 128 * 2 * sm_max * 1e6 / 1e12, "alu"
             else:
-                # dominant contraction: forward (qp_forward; fused n = 8) or weight gradient
-                # (n >= 9), 2 x rows x 2^(n+1) x 2^n algorithmic flops each
-                if prob is None or n <= 8:
-                    kernel = ("dense_fused_fwd_kernel<%d>" % n) if n in (7, 8) and prob is not None else "dense_row16_kernel<0>"
-                else:
-                    kernel = "dense_wgrad_gemm_kernel<%s>" % ("FP16" if ops == "fp16_pairs" else "TF32")
+                # the longest of the contractions, 2 x rows x 2^(n+1) x 2^n algorithmic flops each
+                form = "FP16" if ops == "fp16_pairs" else "TF32"
+                kernel = {"main": ("dense_fused_fwd_kernel<%d>" % n) if n in (7, 8) and prob is not None
+                          else "dense_row16_kernel<0>" if ops == "fp16_pairs" else "dense_row_gemm_kernel<0>",
+                          "wgrad": "dense_wgrad_gemm_kernel<%s, %d>" % (form, n),
+                          "mu": ("dense_mu_embed_kernel<%d>" % n) if n in (7, 8)
+                          else "dense_row16_kernel<1>" if ops == "fp16_pairs" else "dense_row_gemm_kernel<1>"}[top]
                 flops = 2.0 * rows * (2 * dim) * dim
                 peak = bf16 / 3.0 if ops == "fp16_pairs" else bf16 * 0.5 / 3.0
                 bound = "tensor"

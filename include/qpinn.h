@@ -71,16 +71,18 @@ typedef enum {
 typedef enum { QP_PREMAP_DIRECT = 0, QP_PREMAP_RFF_MLP = 1 } qp_premap;
 
 /* SIMT_FP32: gate-by-gate statevectors in registers and shared memory, FP32 (any n).
- * GEMM_3XTF32: the ansatz layers fused into one 2^n x 2^n unitary applied to all points as
- * tensor-core contractions (tcgen05) on split operands hi + lo with three products per
- * term and FP32 accumulation: TF32 pairs, and for n = 7, 8 FP16 pairs scaled by powers of
- * two (forward, weight gradient, back-projection), both about 22-bit operands; forward for
- * n >= 5, loss + gradient for n >= 7. AUTO picks GEMM_3XTF32 for 8-10 qubits, SIMT otherwise.
- * GEMM_BF16X3 is reserved (QP_ERR_UNSUPPORTED). */
+ * GEMM_SPLIT: the ansatz layers fused into one 2^n x 2^n unitary applied to all points as
+ * tensor-core contractions (tcgen05) on split operands hi + lo with FP32 accumulation, about
+ * 22-bit operands: FP16 pairs scaled by powers of two (three FP16 products per term, the hi*hi
+ * products and the hi*lo + lo*hi corrections in separate accumulators; the default and the
+ * only form of the n = 7, 8 loss kernels) or 3xTF32 (qp_plan_set_operands). Forward for
+ * n >= 5, loss + gradient for n >= 7. AUTO picks GEMM_SPLIT for 8-10 qubits, SIMT otherwise.
+ * GEMM_BF16X3 is reserved (QP_ERR_UNSUPPORTED): FP16 pairs with power-of-two scaling give
+ * the same operand precision with three products instead of six. */
 typedef enum {
   QP_PATH_AUTO = 0,
   QP_PATH_SIMT_FP32 = 1,
-  QP_PATH_GEMM_3XTF32 = 2,
+  QP_PATH_GEMM_SPLIT = 2,
   QP_PATH_GEMM_BF16X3 = 3
 } qp_path;
 
@@ -216,8 +218,10 @@ typedef struct {
  * streams are joined. */
 qp_status qp_batch_step(qp_plan* const* plans, int32_t count, const qp_step_args* args, void* stream);
 
-/* Synchronise the stream of the last call on this plan and return the device status word
- * (QP_OK, QP_ERR_NONFINITE or QP_ERR_TIMEOUT) or QP_ERR_CUDA for a sticky CUDA error. */
+/* Synchronise the stream of the last compute call on this plan and return that call's device
+ * status word (QP_OK, QP_ERR_NONFINITE or QP_ERR_TIMEOUT; QP_OK before the first call) or
+ * QP_ERR_CUDA for a sticky CUDA error. After qp_forward_noalloc the word is the one in the
+ * library's fixed array, which the next qp_forward_noalloc call on any plan overwrites. */
 qp_status qp_last_device_error(qp_plan* plan);
 
 const char* qp_status_str(qp_status s);
@@ -225,7 +229,7 @@ const char* qp_status_str(qp_status s);
 /* Kernel launches issued by the last compute call on this plan (for accounting). */
 int32_t qp_last_launch_count(const qp_plan* plan);
 
-/* The path a plan resolved to (QP_PATH_SIMT_FP32 or QP_PATH_GEMM_3XTF32). */
+/* The path a plan resolved to (QP_PATH_SIMT_FP32 or QP_PATH_GEMM_SPLIT). */
 int32_t qp_plan_path(const qp_plan* plan);
 
 /* Operand form of the tensor-core contractions that have two: the forward of qp_forward for
@@ -243,26 +247,38 @@ typedef enum { QP_OPERANDS_FP16_PAIRS = 0, QP_OPERANDS_TF32_PAIRS = 1 } qp_opera
 qp_status qp_plan_set_operands(qp_plan* plan, int32_t operands);
 
 /* Optional profiling: two cudaEvent_t (passed as void*, created by the caller) that the
- * following compute calls record on their stream immediately before and after the dominant
- * kernel -- the statevector kernel on the SIMT path; on the GEMM path of qp_loss_grad the
- * fused forward contraction (n = 7, 8) or the weight-gradient contraction (n >= 9); the
- * forward contraction of qp_forward -- so
- * its device time can be read with cudaEventElapsedTime. Pass NULL, NULL to stop. The plan
- * does not own the events. */
-qp_status qp_set_profile_events(qp_plan* plan, void* ev_start, void* ev_stop);
+ * following compute calls record on their stream immediately before and after one measured
+ * kernel, so its device time can be read with cudaEventElapsedTime. kernel selects it:
+ *   QP_PROF_MAIN (0): the statevector kernel on the SIMT path; on the tensor-core path the
+ *     forward contraction (the fused forward kernel of qp_loss_grad for n = 7, 8; the forward
+ *     launches of every point set otherwise, and of qp_forward);
+ *   QP_PROF_WGRAD (1): the weight-gradient contraction of qp_loss_grad (tensor-core path);
+ *   QP_PROF_MU (2): the back-projection mu = Re(U'^H lambda) of qp_loss_grad (tensor-core
+ *     path with the RFF + MLP premap; with its embedding-gradient epilogue for n = 7, 8).
+ * Pass NULL, NULL to stop. The plan does not own the events. QP_ERR_INVALID_ARG for another
+ * kernel value or only one null event. */
+typedef enum { QP_PROF_MAIN = 0, QP_PROF_WGRAD = 1, QP_PROF_MU = 2 } qp_prof_kernel;
+qp_status qp_set_profile_events(qp_plan* plan, int32_t kernel, void* ev_start, void* ev_stop);
 
-/* Same result as qp_forward, for callers that cannot allocate device memory (a memory pool
- * that refuses new allocations, a plugin given a fixed device budget, a host that forbids
- * cudaMalloc after start-up). The paper has no counterpart: this is a library convenience.
- * Instead of the plan's workspace, the call uses one fixed 16 MiB array of device memory owned
- * by the library; every GPU that loads the library keeps that array until the process exits.
- * Nothing is allocated or freed by this call. Limit: B * n_qubits * 16 bytes plus about 13 KiB
- * of tables must fit in 16 MiB (B <= 104,000 points at 10 qubits, 130,000 at 8); a larger B is
- * rejected with QP_ERR_BUFFER_TOO_SMALL before anything is launched. The first call on a device
- * (with that device current) looks up the array's device address once, so make that first call
- * before any stream capture. All calls share the one array and each call overwrites it, so
- * calls that overlap on the GPU (other streams, other plans, other threads) race; serialise
- * them. Arguments, layouts and the other errors are those of qp_forward. */
+/* Fields and input derivatives like qp_forward, for callers that cannot allocate device memory:
+ * code running inside a memory pool that refuses new allocations, a plugin handed a fixed
+ * device budget, a host that forbids cudaMalloc after start-up. The paper has no counterpart:
+ * this is a library convenience. Instead of the plan's workspace, the call uses one fixed
+ * 16 MiB array of device memory owned by the library; every GPU that loads the library keeps
+ * that array until the process exits. Nothing is allocated or freed by this call.
+ * It always runs the FP32 SIMT path (premap kernel without tensor cores, gate-by-gate circuit
+ * kernel), whatever path and operand form the plan names: on a plan with the direct premap and
+ * the SIMT path its results equal qp_forward's bit for bit; otherwise both agree with the FP64
+ * oracle within the library's 1e-5 relative bar.
+ * Limit: B * n_qubits * 16 bytes plus about 13 KiB of tables must fit in 16 MiB (B <= 104,000
+ * points at 10 qubits, 130,000 at 8); a larger B is rejected with QP_ERR_BUFFER_TOO_SMALL
+ * before anything is launched. The array's device address is looked up with the device current
+ * on every call made outside stream capture; a call made while its stream is capturing reuses
+ * the address of the last call outside capture on that device, so make one call before any
+ * capture (otherwise QP_ERR_CUDA). All calls share the one array and each call overwrites it,
+ * so calls that overlap on the GPU (other streams, other plans, other threads) race; serialise
+ * them. qp_last_device_error then reads the status word in that array. Arguments, layouts and
+ * the other errors are those of qp_forward. */
 qp_status qp_forward_noalloc(qp_plan* plan, const float* d_params, const float* d_pts, int64_t B,
                              float* d_fields, float* d_dfields, void* stream);
 

@@ -43,7 +43,12 @@ struct qp_plan {
   size_t ws_bytes = 0;
   int32_t last_launches = 0;
   cudaStream_t last_stream = nullptr;
-  cudaEvent_t prof_start = nullptr, prof_stop = nullptr;
+  // device status word of the last compute call: the workspace's, or the fixed array's after
+  // qp_forward_noalloc (null before the first call)
+  const int32_t* last_status = nullptr;
+  // profiling events per measured kernel (qp_set_profile_events): [0] statevector kernel or
+  // forward contraction, [1] weight-gradient contraction, [2] back-projection mu
+  cudaEvent_t prof_start[3] = {nullptr, nullptr, nullptr}, prof_stop[3] = {nullptr, nullptr, nullptr};
 };
 
 namespace {
@@ -99,7 +104,13 @@ struct WsLayout {
 // per instruction, not averaging out), and the three FP16-pair products of a 16-row step go to
 // the same accumulator: 512 rows (96 instructions) keep the full-size weight gradient within
 // ~4e-6 of the FP32 SIMT path; 4096 rows reached 2e-5.
-int64_t wg_rows_per_chunk(int) { return 512; }
+// 3xTF32 operands take two instructions per product of a 16-row step (K = 8 each) where FP16
+// pairs take one, so their accumulator is flushed every 256 rows: the same number of
+// truncating instructions per flush.
+int64_t wg_rows_per_chunk(const qp_plan* pl) {
+  const bool h16 = (pl->c.n_qubits <= 8) || pl->operands == QP_OPERANDS_FP16_PAIRS;
+  return h16 ? 512 : 256;
+}
 
 // Weight-gradient launch geometry for `nkc` 16-row steps: tiles of min(256, 2^n) basis
 // indices x 256 components, CTA groups per tile (persistent CTAs, balanced step ranges),
@@ -115,7 +126,7 @@ WgGeom wg_geom(const qp_plan* pl, int64_t nkc) {
   g.tiles = (dim / qpd::wg_mtc(n)) * (2 * dim / 256);
   g.ngroups = pl->sm_count / g.tiles > 0 ? pl->sm_count / g.tiles : 1;
   const int64_t per = nkc > 0 ? (nkc + g.ngroups - 1) / g.ngroups : 1;
-  const int64_t flmax = wg_rows_per_chunk(n) / qpd::WKC;
+  const int64_t flmax = wg_rows_per_chunk(pl) / qpd::WKC;
   const int64_t nfl = (per + flmax - 1) / flmax;
   g.fl = (int)((per + nfl - 1) / nfl);
   g.spc = (int)nfl;
@@ -123,7 +134,7 @@ WgGeom wg_geom(const qp_plan* pl, int64_t nkc) {
   return g;
 }
 
-bool dense_path(const qp_plan* pl) { return pl->path == QP_PATH_GEMM_3XTF32; }
+bool dense_path(const qp_plan* pl) { return pl->path == QP_PATH_GEMM_SPLIT; }
 
 // The fused forward kernel keeps a tile's whole output row (2^(n+1) FP32 columns) in tensor
 // memory, which holds 512 columns: n = 7 and 8.
@@ -294,7 +305,7 @@ qp_status validate(const qp_circuit* c, const qp_problem* p, int32_t path) {
   if (p->energy_nt < 0 || p->energy_nt > QP_MAXNT || p->energy_slice < 0) return QP_ERR_INVALID_ARG;
   if (p->medium == QP_MEDIUM_DIELECTRIC && !(p->sigmoid_w > 0.f)) return QP_ERR_INVALID_ARG;
   if (!(p->ic_sigma > 0.f)) return QP_ERR_INVALID_ARG;
-  if (path == QP_PATH_GEMM_3XTF32) {
+  if (path == QP_PATH_GEMM_SPLIT) {
     if (c->n_qubits < 5) return QP_ERR_UNSUPPORTED;  // K = 2^n must hold one 32-wide chunk
   } else if (path != QP_PATH_AUTO && path != QP_PATH_SIMT_FP32) {
     return QP_ERR_UNSUPPORTED;
@@ -335,7 +346,7 @@ qp_status qp_plan_create(const qp_circuit* circuit, const qp_problem* problem, i
   // AUTO: the fused-unitary tensor-core path where it is faster and stays within 1e-5 of the
   // FP64 reference (8-10 qubits); the FP32 gate-by-gate path otherwise.
   pl->path = path != QP_PATH_AUTO ? path
-             : (circuit->n_qubits >= 8 ? QP_PATH_GEMM_3XTF32 : QP_PATH_SIMT_FP32);
+             : (circuit->n_qubits >= 8 ? QP_PATH_GEMM_SPLIT : QP_PATH_SIMT_FP32);
   const int n = circuit->n_qubits;
   if (qp_build_sched(n, circuit->n_layers, circuit->ansatz, &pl->sched) != 0) {
     delete pl;
@@ -496,6 +507,8 @@ qp_status qp_workspace_size(const qp_plan* plan, int64_t max_points, size_t* byt
 qp_status qp_set_workspace(qp_plan* plan, void* d_ws, size_t bytes) {
   if (!plan || (bytes && !d_ws)) return QP_ERR_INVALID_ARG;
   if (((uintptr_t)d_ws & 255) != 0) return QP_ERR_INVALID_ARG;
+  // the status word lives at the start of the workspace: follow it to the new one
+  if (plan->ws && plan->last_status == (const int32_t*)plan->ws) plan->last_status = (const int32_t*)d_ws;
   plan->ws = d_ws;
   plan->ws_bytes = bytes;
   return QP_OK;
@@ -524,11 +537,18 @@ qp_status qp_plan_set_operands(qp_plan* plan, int32_t operands) {
   return QP_OK;
 }
 
-qp_status qp_set_profile_events(qp_plan* plan, void* ev_start, void* ev_stop) {
-  if (!plan || ((ev_start == nullptr) != (ev_stop == nullptr))) return QP_ERR_INVALID_ARG;
-  plan->prof_start = (cudaEvent_t)ev_start;
-  plan->prof_stop = (cudaEvent_t)ev_stop;
+qp_status qp_set_profile_events(qp_plan* plan, int32_t kernel, void* ev_start, void* ev_stop) {
+  if (!plan || kernel < 0 || kernel > 2 || ((ev_start == nullptr) != (ev_stop == nullptr)))
+    return QP_ERR_INVALID_ARG;
+  plan->prof_start[kernel] = (cudaEvent_t)ev_start;
+  plan->prof_stop[kernel] = (cudaEvent_t)ev_stop;
   return QP_OK;
+}
+
+// Record the plan's profiling event of `kernel` (start or stop), if it has one.
+static void prof_mark(const qp_plan* pl, int kernel, bool start, cudaStream_t s) {
+  const cudaEvent_t e = start ? pl->prof_start[kernel] : pl->prof_stop[kernel];
+  if (e) cudaEventRecord(e, s);
 }
 
 static void fill_problem(const qp_plan* pl, QPProblemDev& d) {
@@ -628,6 +648,7 @@ static qp_status dense_loss_grad(qp_plan* pl, const float* d_params, const float
   const WsLayout w = ws_layout(pl, P);
   if (!pl->ws || pl->ws_bytes < w.total) return QP_ERR_BUFFER_TOO_SMALL;
   pl->last_stream = s;
+  pl->last_status = (const int32_t*)((char*)pl->ws + w.status);
   char* ws = (char*)pl->ws;
   const int n = pl->c.n_qubits, dim = 1 << n, L = pl->c.n_layers;
   int launches = 0;
@@ -681,7 +702,7 @@ static qp_status dense_loss_grad(qp_plan* pl, const float* d_params, const float
     fa.scal = (int32_t*)(ws + w.status) + 16;
     const int64_t ftiles = fa.tile_end[2];
     const int fblocks = (int)(ftiles < pl->sm_count ? (ftiles > 0 ? ftiles : 1) : pl->sm_count);
-    if (pl->prof_start) cudaEventRecord(pl->prof_start, s);
+    prof_mark(pl, 0, true, s);
     alignas(64) CUtensorMap tmaps[3];
     std::memset(tmaps, 0, sizeof(tmaps));
     fa.use_tma = lam_maps(fa.lam, fa.rtot, npts, (2 * dim) / 256, tmaps) ? 1 : 0;
@@ -690,9 +711,10 @@ static qp_status dense_loss_grad(qp_plan* pl, const float* d_params, const float
       qpd::dense_fused_fwd_kernel<7><<<fblocks, qpd::F_THREADS, fsmem, s>>>(fa, tmaps[0], tmaps[1], tmaps[2]);
     else
       qpd::dense_fused_fwd_kernel<8><<<fblocks, qpd::F_THREADS, fsmem, s>>>(fa, tmaps[0], tmaps[1], tmaps[2]);
-    if (pl->prof_stop) cudaEventRecord(pl->prof_stop, s);
+    prof_mark(pl, 0, false, s);
     launches += 1;
   } else {
+    prof_mark(pl, 0, true, s);
     for (int set = 0; set < 3; ++set) {
       if (npts[set] > 0) {
         qpd::GemmArgs ga = {};
@@ -714,6 +736,7 @@ static qp_status dense_loss_grad(qp_plan* pl, const float* d_params, const float
       }
       base += npts[set];
     }
+    prof_mark(pl, 0, false, s);
     qpd::PointArgs pa;
     pa.phi = (float2*)(ws + w.dphi); pa.head = d_params + pl->head_off; pa.n = n; pa.m = pl->c.n_readout;
     base = 0;
@@ -746,7 +769,7 @@ static qp_status dense_loss_grad(qp_plan* pl, const float* d_params, const float
   if (wgm.nslots > wg_geom(pl, (4 * P + qpd::WKC - 1) / qpd::WKC + 2).nslots) return QP_ERR_INTERNAL;
   wa.tiles = wgm.tiles; wa.ngroups = wgm.ngroups; wa.spc = wgm.spc; wa.fl = wgm.fl;
   wa.status = (int32_t*)(ws + w.status);
-  if (pl->prof_start && !fused) cudaEventRecord(pl->prof_start, s);
+  prof_mark(pl, 1, true, s);
   wa.scal = (const int32_t*)(ws + w.status) + 16;
   {
     // FP16 pairs when the forward recorded both operand ranges
@@ -756,7 +779,7 @@ static qp_status dense_loss_grad(qp_plan* pl, const float* d_params, const float
                                             qpd::wg_smem_bytes(n, fwd16), s);
     if (le != cudaSuccess) return QP_ERR_CUDA;
   }
-  if (pl->prof_stop && !fused) cudaEventRecord(pl->prof_stop, s);
+  prof_mark(pl, 1, false, s);
   launches += 1;
   qpd::SweepArgs sa;
   sa.part = wa.part; sa.nchunks = (int32_t)wgm.nslots; sa.n = n; sa.L = L; sa.ansatz = pl->c.ansatz;
@@ -823,15 +846,18 @@ static qp_status dense_loss_grad(qp_plan* pl, const float* d_params, const float
       ma.status = (int32_t*)(ws + w.status);
       const int64_t mt = ma.tile_end[2];
       const int mblocks = (int)(mt < pl->sm_count ? (mt > 0 ? mt : 1) : pl->sm_count);
+      prof_mark(pl, 2, true, s);
       if (n == 7)
         qpd::dense_mu_embed_kernel<7><<<mblocks, qpd::MU_THREADS, qpd::mu_smem_bytes(n), s>>>(ma);
       else
         qpd::dense_mu_embed_kernel<8><<<mblocks, qpd::MU_THREADS, qpd::mu_smem_bytes(n), s>>>(ma);
+      prof_mark(pl, 2, false, s);
       launches += 1;
     } else {
       // back-projection mu = Re(U'^H lambda) per (point, vector) row, then the embedding
       // gradients per point, then the premap backward shared with the SIMT path
       base = 0;
+      prof_mark(pl, 2, true, s);
       for (int set = 0; set < 3; ++set) {
         if (npts[set] > 0) {
           qpd::GemmArgs ga = {};
@@ -853,6 +879,7 @@ static qp_status dense_loss_grad(qp_plan* pl, const float* d_params, const float
         }
         base += npts[set];
       }
+      prof_mark(pl, 2, false, s);
       qpd::EmbedArgs ea;
       ea.thetaJ = (const float*)(ws + w.thetaJ); ea.mu = (const float*)(ws + w.dmu);
       ea.dthetaJ = (float*)(ws + w.dthetaJ); ea.n = n; ea.cs = (const float2*)(ws + w.dcs);
@@ -882,6 +909,7 @@ qp_status qp_forward(qp_plan* pl, const float* d_params, const float* d_pts, int
   if (!pl->ws || pl->ws_bytes < w.total) return QP_ERR_BUFFER_TOO_SMALL;
   cudaStream_t s = (cudaStream_t)stream;
   pl->last_stream = s;
+  pl->last_status = (const int32_t*)((char*)pl->ws + w.status);
   const float* pts[3] = {d_pts, nullptr, nullptr};
   const int64_t npts[3] = {B, 0, 0};
   qp_status st = launch_front(pl, d_params, pts, npts, w, s, false);
@@ -907,13 +935,13 @@ qp_status qp_forward(qp_plan* pl, const float* d_params, const float* d_pts, int
     const int gblocks = (int)(ntiles < pl->sm_count ? ntiles : pl->sm_count);
     const int64_t items = ntiles * ((2 * dim) / 256);   // (tile, column chunk) items
     const int iblocks = (int)(items < pl->sm_count ? items : pl->sm_count);
-    if (pl->prof_start) cudaEventRecord(pl->prof_start, s);
+    prof_mark(pl, 0, true, s);
     if (fwd16)
       qpd::dense_row16_kernel<0><<<iblocks, qpd::F16_THREADS, qpd::row16_smem_bytes(), s>>>(
           ga, (const __half*)(ws + w.dW16), nullptr);
     else
       qpd::dense_row_gemm_kernel<0><<<gblocks, 128, qpd::gemm_smem_bytes(n, 0), s>>>(ga);
-    if (pl->prof_stop) cudaEventRecord(pl->prof_stop, s);
+    prof_mark(pl, 0, false, s);
     qpd::ReadoutArgs ra;
     ra.phi = ga.phi; ra.head = d_params + pl->head_off; ra.n = n; ra.m = pl->c.n_readout;
     ra.nv = ga.nv; ra.npts = B; ra.pt_base = 0; ra.out_f = d_fields; ra.out_df = d_dfields;
@@ -931,11 +959,11 @@ qp_status qp_forward(qp_plan* pl, const float* d_params, const float* d_pts, int
   int64_t blocks = (tasks + pl->warps_fwd - 1) / pl->warps_fwd;
   if (blocks > pl->blocks_fwd) blocks = pl->blocks_fwd;
   void* args[] = {&a};
-  if (pl->prof_start) cudaEventRecord(pl->prof_start, s);
+  prof_mark(pl, 0, true, s);
   if (cudaLaunchKernel(circuit_kernel_ptr(pl->c.n_qubits, false), dim3((unsigned)blocks),
                        dim3(pl->warps_fwd * 32), args, pl->smem_fwd, s) != cudaSuccess)
     return QP_ERR_CUDA;
-  if (pl->prof_stop) cudaEventRecord(pl->prof_stop, s);
+  prof_mark(pl, 0, false, s);
   pl->last_launches = 3;
   return cuda_status(cudaGetLastError());
 }
@@ -985,6 +1013,7 @@ qp_status qp_loss_grad(qp_plan* pl, const float* d_params, const qp_batch* batch
   if (!pl->ws || pl->ws_bytes < w.total) return QP_ERR_BUFFER_TOO_SMALL;
   cudaStream_t s = (cudaStream_t)stream;
   pl->last_stream = s;
+  pl->last_status = (const int32_t*)((char*)pl->ws + w.status);
   char* ws = (char*)pl->ws;
   int launches = 0;
   if (P > 0) {
@@ -1009,11 +1038,11 @@ qp_status qp_loss_grad(qp_plan* pl, const float* d_params, const qp_batch* batch
   const int64_t tasks = a.task_end[2];
   // every block writes its partials, so the grid is fixed to the plan's block count
   void* args[] = {&a};
-  if (pl->prof_start) cudaEventRecord(pl->prof_start, s);
+  prof_mark(pl, 0, true, s);
   if (cudaLaunchKernel(circuit_kernel_ptr(pl->c.n_qubits, true), dim3(pl->blocks_grad),
                        dim3(pl->warps_grad * 32), args, pl->smem_grad, s) != cudaSuccess)
     return QP_ERR_CUDA;
-  if (pl->prof_stop) cudaEventRecord(pl->prof_stop, s);
+  prof_mark(pl, 0, false, s);
   (void)tasks;
   launches += 1;
   if (mlp) {
@@ -1102,9 +1131,9 @@ static qp_status launch_reduce(qp_plan* pl, const WsLayout& w, const float* d_pa
 qp_status qp_last_device_error(qp_plan* pl) {
   if (!pl) return QP_ERR_INVALID_ARG;
   if (cudaStreamSynchronize(pl->last_stream) != cudaSuccess) return QP_ERR_CUDA;
-  if (!pl->ws) return QP_OK;
+  if (!pl->last_status) return QP_OK;
   int32_t st = 0;
-  if (cudaMemcpy(&st, pl->ws, sizeof(st), cudaMemcpyDeviceToHost) != cudaSuccess) return QP_ERR_CUDA;
+  if (cudaMemcpy(&st, pl->last_status, sizeof(st), cudaMemcpyDeviceToHost) != cudaSuccess) return QP_ERR_CUDA;
   return (qp_status)st;
 }
 
@@ -1129,20 +1158,26 @@ std::mutex g_noalloc_mutex;
 void* g_noalloc_addr[kNoAllocMaxDevices] = {};
 
 // Device address of the fixed scratch on the current device. In host code the array's name is
-// only a stand-in, so the real address is looked up once per device (with that device
-// current) and cached.
-qp_status noalloc_scratch_address(void** out) {
+// only a stand-in, so the real address comes from cudaGetSymbolAddress with the device current.
+// It is looked up again on every call made outside stream capture, so it follows the module
+// when the device's context is re-created; a call made while `s` is capturing uses the address
+// of the last call outside capture on this device (and fails if there was none).
+qp_status noalloc_scratch_address(cudaStream_t s, void** out) {
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); return QP_ERR_CUDA; }
   if (dev < 0 || dev >= kNoAllocMaxDevices) return QP_ERR_UNSUPPORTED;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cs) != cudaSuccess) { cudaGetLastError(); return QP_ERR_CUDA; }
   std::lock_guard<std::mutex> lock(g_noalloc_mutex);
-  if (!g_noalloc_addr[dev]) {
+  if (cs == cudaStreamCaptureStatusNone) {
     void* p = nullptr;
     if (cudaGetSymbolAddress(&p, qp_noalloc_scratch) != cudaSuccess || !p) {
       cudaGetLastError();
       return QP_ERR_CUDA;
     }
     g_noalloc_addr[dev] = p;
+  } else if (!g_noalloc_addr[dev]) {
+    return QP_ERR_CUDA;
   }
   *out = g_noalloc_addr[dev];
   return QP_OK;
@@ -1249,12 +1284,13 @@ extern "C" qp_status qp_forward_noalloc(qp_plan* pl, const float* d_params, cons
   const size_t off_cenc = al256(off_cmat + (size_t)QP_MAXL * QP_MAXQ * 3 * 4 * 4);
   const size_t off_theta = al256(off_cenc + (size_t)QP_MAXQ * 4 * 4);
   if ((uint64_t)B > (kNoAllocScratchBytes - off_theta) / ((size_t)n * 16)) return QP_ERR_BUFFER_TOO_SMALL;
+  cudaStream_t s = (cudaStream_t)stream;
   void* base = nullptr;
-  qp_status st = noalloc_scratch_address(&base);
+  qp_status st = noalloc_scratch_address(s, &base);
   if (st != QP_OK) return st;
   char* ws = (char*)base;
-  cudaStream_t s = (cudaStream_t)stream;
   pl->last_stream = s;
+  pl->last_status = (const int32_t*)(ws + off_status);
 
   qpk::PrepArgs pa;
   pa.params = d_params; pa.circ_off = pl->circ_off; pa.n = n; pa.L = L;
@@ -1271,7 +1307,7 @@ extern "C" qp_status qp_forward_noalloc(qp_plan* pl, const float* d_params, cons
   ma.params = d_params; ma.n = n; ma.premap = pl->c.premap; ma.scale = pl->c.scale;
   ma.n_direct = pl->c.n_direct; ma.F = pl->c.rff_freqs; ma.H = pl->c.mlp_width;
   ma.thetaJ = (float*)(ws + off_theta);
-  ma.counts = pa.counts; ma.medium = pl->p.medium;
+  ma.counts = pa.counts; ma.medium = pl->p.medium; ma.status = pa.status;
   ma.disk_r = pl->p.disk_r; ma.disk_x0 = pl->p.disk_x0; ma.disk_y0 = pl->p.disk_y0;
   const int64_t pb = (B + 127) / 128;
   const int pblocks = (int)(pb < pl->sm_count * 8 ? pb : pl->sm_count * 8);

@@ -24,7 +24,9 @@ namespace qpd {
 constexpr int KC = 32;        // K (basis index) elements per chunk
 constexpr int TM = 128;       // rows per tile (tensor-memory lanes)
 
-__host__ __device__ inline int n_cols_chunk(int n) { return (2 << n) < 256 ? (2 << n) : 256; }
+// Output columns per chunk of the 3xTF32 row contractions (at most 128: two accumulators of
+// a chunk, double-buffered, fill the 512 tensor-memory columns).
+__host__ __device__ inline int n_cols_chunk(int n) { return (2 << n) < 128 ? (2 << n) : 128; }
 
 // Byte offset of element (row r, k-in-chunk t) in a K-major, no-swizzle operand block whose
 // 8-row groups hold KC/4 core matrices of 8 x 16 bytes.
@@ -268,7 +270,7 @@ __global__ void dense_build_kernel(BuildArgs a) {
       }
       if (a.WT) {
         // transpose: row a = k (N = dim, chunks of nch2), K = o (2 dim, chunks of KC)
-        const int nch2 = dim < 256 ? dim : 256, nkc2 = 2 * dim / KC;
+        const int nch2 = dim < 128 ? dim : 128, nkc2 = 2 * dim / KC;
         const int c2b = k / nch2, r2 = k % nch2, kc2 = o / KC, t2 = o % KC;
         float* blk2 = a.WT + ((int64_t)(c2b * nkc2 + kc2) * 2) * (nch2 * KC);
         blk2[core_off(r2, t2) / 4] = hi;
@@ -295,7 +297,7 @@ struct GemmArgs {
 // MODE 1 (back-projection mu = Re(U'^H lambda)) has dim outputs over K = 2 dim.
 __host__ __device__ inline int row_nch(int n, int mode) {
   const int ntot = mode == 0 ? (2 << n) : (1 << n);
-  return ntot < 256 ? ntot : 256;
+  return ntot < 128 ? ntot : 128;
 }
 // Smem: 2 stages x (A hi, A lo: 128 x KC fp32; W hi, W lo: nch x KC fp32) + barriers.
 __host__ __device__ inline int gemm_smem_bytes(int n, int mode = 0) {
@@ -303,8 +305,13 @@ __host__ __device__ inline int gemm_smem_bytes(int n, int mode = 0) {
   return 2 * (2 * TM * KC * 4 + 2 * nch * KC * 4) + 128;
 }
 
-// Row GEMM over (point, vector) rows. MODE 0: Phi = R W^T with R generated from the angles.
-// MODE 1: mu = Lambda W (rows of Lambda loaded, B operand the transposed blocks).
+// Row GEMM over (point, vector) rows on 3xTF32 operands. MODE 0: Phi = R W^T with R generated
+// from the angles. MODE 1: mu = Lambda W (rows of Lambda loaded, B operand the transposed
+// blocks). The tensor core adds each instruction's products into the FP32 accumulator with a
+// truncating alignment (about one accumulator ulp per instruction, not averaging out over K),
+// so the hi*hi products go to one accumulator and the hi*lo + lo*hi corrections, 2^-11
+// smaller, to a second: K / 8 truncations on the result instead of 3K / 8. Each column chunk
+// (at most 128 columns) therefore takes 2 x nch columns, double-buffered across chunks.
 template <int MODE>
 __global__ void __launch_bounds__(128, 1) dense_row_gemm_kernel(GemmArgs a) {
   extern __shared__ __align__(1024) unsigned char sm[];
@@ -316,7 +323,8 @@ __global__ void __launch_bounds__(128, 1) dense_row_gemm_kernel(GemmArgs a) {
   const int stage_bytes = 2 * abytes + 2 * wbytes;
   uint64_t* bars = reinterpret_cast<uint64_t*>(sm + 2 * stage_bytes);  // w_full[2], mma_done[2]
   uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + 2 * stage_bytes + 64);
-  const uint32_t tcols = nch * 2 <= 32 ? 32 : (nch * 2 <= 64 ? 64 : (nch * 2 <= 128 ? 128 : (nch * 2 <= 256 ? 256 : 512)));
+  // two buffers x (hi*hi accumulator, correction accumulator) of nch columns each
+  const uint32_t tcols = nch * 4 <= 32 ? 32 : (nch * 4 <= 64 ? 64 : (nch * 4 <= 128 ? 128 : (nch * 4 <= 256 ? 256 : 512)));
   if (warp == 0) qptc::tmem_alloc(tslot, tcols);
   if (tid == 0) {
     for (int i = 0; i < 4; ++i) qptc::mbar_init(&bars[i], 1);
@@ -431,16 +439,18 @@ __global__ void __launch_bounds__(128, 1) dense_row_gemm_kernel(GemmArgs a) {
           if (ok) {
             qptc::fence_after();
             const uint32_t sa = qptc::smem_u32(sA), sw = qptc::smem_u32(sW);
-            const uint32_t dt = tmem + cbuf * (tcols / 2);
+            const uint32_t dt = tmem + cbuf * (tcols / 2);   // hi*hi accumulator
+            const uint32_t dc = dt + nch;                      // correction accumulator
 #pragma unroll
             for (int ks = 0; ks < KC / 8; ++ks) {
               const uint64_t ah = qptc::desc_kmajor(sa + ks * 256, 128, (KC / 4) * 128);
               const uint64_t al = qptc::desc_kmajor(sa + abytes + ks * 256, 128, (KC / 4) * 128);
               const uint64_t wh = qptc::desc_kmajor(sw + ks * 256, 128, (KC / 4) * 128);
               const uint64_t wl = qptc::desc_kmajor(sw + wbytes + ks * 256, 128, (KC / 4) * 128);
-              qptc::mma_tf32(dt, ah, wh, id, (kc > 0 || ks > 0) ? 1u : 0u);
-              qptc::mma_tf32(dt, ah, wl, id, 1u);
-              qptc::mma_tf32(dt, al, wh, id, 1u);
+              const uint32_t acc = (kc > 0 || ks > 0) ? 1u : 0u;
+              qptc::mma_tf32(dt, ah, wh, id, acc);
+              qptc::mma_tf32(dc, ah, wl, id, acc);
+              qptc::mma_tf32(dc, al, wh, id, 1u);
             }
             qptc::commit(&bars[2 + st]);
           }
@@ -453,9 +463,13 @@ __global__ void __launch_bounds__(128, 1) dense_row_gemm_kernel(GemmArgs a) {
           if (ok) {
             qptc::fence_after();
             const int64_t pp = pend_tile * ppt + prow;
-            float v[32];
+            float v[32], vc[32];
             for (int c0 = 0; c0 < nch; c0 += 32) {
-              qptc::tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + pend_buf * (tcols / 2) + c0, v);
+              const uint32_t ta = tmem + ((uint32_t)(warp * 32) << 16) + pend_buf * (tcols / 2) + c0;
+              qptc::tmem_ld32(ta, v);
+              qptc::tmem_ld32(ta + nch, vc);
+#pragma unroll
+              for (int e = 0; e < 32; ++e) v[e] += vc[e];
               if (pp < a.npts) {
                 float* orow = MODE == 0 ? reinterpret_cast<float*>(a.phi) : a.mu;
                 float4* dst = reinterpret_cast<float4*>(orow + ((a.pt_base + pp) * 4 + s) * (int64_t)ntot +
@@ -484,9 +498,13 @@ __global__ void __launch_bounds__(128, 1) dense_row_gemm_kernel(GemmArgs a) {
     if (ok) {
       qptc::fence_after();
       const int64_t pp = pend_tile * ppt + prow;
-      float v[32];
+      float v[32], vc[32];
       for (int c0 = 0; c0 < nch; c0 += 32) {
-        qptc::tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + pend_buf * (tcols / 2) + c0, v);
+        const uint32_t ta = tmem + ((uint32_t)(warp * 32) << 16) + pend_buf * (tcols / 2) + c0;
+        qptc::tmem_ld32(ta, v);
+        qptc::tmem_ld32(ta + nch, vc);
+#pragma unroll
+        for (int e = 0; e < 32; ++e) v[e] += vc[e];
         if (pp < a.npts) {
           float* orow = MODE == 0 ? reinterpret_cast<float*>(a.phi) : a.mu;
           float4* dst = reinterpret_cast<float4*>(orow + ((a.pt_base + pp) * 4 + s) * (int64_t)ntot +

@@ -16,7 +16,7 @@ ANSATZ = {"basic_ryrz": 0, "basic_rot": 1, "strong_rot": 2, "noent_rot": 3}
 ENC = {"rx": 0, "ry": 1}
 SCALE = {"none": 0, "pi": 1, "bias": 2, "asin": 3, "acos": 4}
 PREMAP = {"direct": 0, "rff_mlp": 1}
-PATH = {"auto": 0, "simt": 1, "gemm_3xtf32": 2, "gemm_bf16x3": 3}
+PATH = {"auto": 0, "simt": 1, "gemm_split": 2, "gemm_bf16x3": 3}
 OPERANDS = {"fp16_pairs": 0, "tf32_pairs": 1}
 NLOSS = 9
 STATUS = {0: "ok", 1: "invalid argument", 2: "unsupported configuration",
@@ -92,7 +92,7 @@ def lib():
         L.qp_plan_set_operands.restype = I32
         L.qp_bh_indicator.argtypes = [P, I32, ctypes.c_double, ctypes.c_double, P, P]
         L.qp_bh_indicator.restype = I32
-        L.qp_set_profile_events.argtypes = [P, P, P]
+        L.qp_set_profile_events.argtypes = [P, I32, P, P]
         L.qp_set_profile_events.restype = I32
         L.qp_sched_selftest.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_uint]
         L.qp_sched_selftest.restype = ctypes.c_double
@@ -156,7 +156,7 @@ class Plan:
         lay = (ctypes.c_int64 * 4)()
         _check(lib().qp_param_layout(self._h, lay), "qp_param_layout")
         self.layout = {"circuit": lay[0], "head": lay[1], "total": lay[2], "fixed": lay[3]}
-        self.path = {1: "simt", 2: "gemm_3xtf32"}.get(lib().qp_plan_path(self._h), "?")
+        self.path = {1: "simt", 2: "gemm_split"}.get(lib().qp_plan_path(self._h), "?")
         _check(lib().qp_plan_set_operands(self._h, OPERANDS[operands]), "qp_plan_set_operands")
         self.operands = operands
 
@@ -253,8 +253,12 @@ class Plan:
     def last_launch_count(self):
         return lib().qp_last_launch_count(self._h)
 
-    def set_profile_events(self, start=None, stop=None):
-        """Record two torch.cuda.Event objects around the circuit kernel of later calls."""
+    PROF = {"main": 0, "wgrad": 1, "mu": 2}
+
+    def set_profile_events(self, start=None, stop=None, kernel="main"):
+        """Record two torch.cuda.Event objects around one measured kernel of later calls:
+        "main" (the statevector kernel, or the forward contraction on the tensor-core path),
+        "wgrad" (weight-gradient contraction) or "mu" (back-projection)."""
         if start is not None:
             # torch creates the CUDA event on first record; make sure both handles exist
             start.record()
@@ -262,7 +266,7 @@ class Plan:
             torch.cuda.synchronize()
         s = ctypes.c_void_p(start.cuda_event) if start is not None else ctypes.c_void_p(0)
         e = ctypes.c_void_p(stop.cuda_event) if stop is not None else ctypes.c_void_p(0)
-        _check(lib().qp_set_profile_events(self._h, s, e), "qp_set_profile_events")
+        _check(lib().qp_set_profile_events(self._h, self.PROF[kernel], s, e), "qp_set_profile_events")
 
 
 def bh_indicator(loss_terms, energy_nt, t_max, delta, out=None, stream=None):

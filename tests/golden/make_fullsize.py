@@ -14,6 +14,7 @@ gradient of the total loss at a fixed spread of parameter indices (first-layer w
 biases, output layer, every circuit layer, head), and fields + input derivatives at 256
 collocation points drawn with a fixed seed.
 """
+import argparse
 import hashlib
 import json
 import os
@@ -69,11 +70,11 @@ def grad_indices(circ, n_mlp, n_circ, n_head):
 
 
 def main(argv):
-    names = [a for a in argv if not a.startswith("--")] or ["c3", "c4"]
-    nt = os.cpu_count() or 1
-    for i, a in enumerate(argv):
-        if a == "--threads":
-            nt = int(argv[i + 1])
+    ap = argparse.ArgumentParser()
+    ap.add_argument("names", nargs="*", default=["c3", "c4"])
+    ap.add_argument("--threads", type=int, default=os.cpu_count() or 1)
+    args = ap.parse_args(argv)
+    names, nt = args.names, args.threads
     for name in names:
         circ, prob, params, sets = workload(name)
         sizes = (8, 10, 6) if name == "c3" else (6, 6, 4)

@@ -20,8 +20,8 @@ import numpy as np
 sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
 
 PATHS = (("simt", "fp16_pairs", "FP32 SIMT"),
-         ("gemm_3xtf32", "fp16_pairs", "tensor cores, FP16 pairs"),
-         ("gemm_3xtf32", "tf32_pairs", "tensor cores, 3xTF32"))
+         ("gemm_split", "fp16_pairs", "tensor cores, FP16 pairs"),
+         ("gemm_split", "tf32_pairs", "tensor cores, 3xTF32"))
 
 
 def _err(gpu, ref):

@@ -40,7 +40,7 @@ def test_count_dielectric_matches_oracle(torch_cuda, oracle):
     assert int(vac.count_dielectric(torch.tensor(W.uniform_points(100, 5, 1.0), device="cuda")).item()) == 0
 
 
-@pytest.mark.parametrize("n,L,path", [(6, 3, "simt"), (8, 4, "gemm_3xtf32"), (9, 2, "gemm_3xtf32")])
+@pytest.mark.parametrize("n,L,path", [(6, 3, "simt"), (8, 4, "gemm_split"), (9, 2, "gemm_split")])
 def test_sharded_calls_sum_to_whole(torch_cuda, n, L, path):
     """Three uneven shards of a dielectric loss with energy slices (one shard without IC
     points): with the whole-loss normalisers (counts, dielectric count, collocation offsets)

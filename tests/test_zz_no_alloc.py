@@ -54,3 +54,54 @@ def test_forward_noalloc_matches_forward_on_consecutive_calls():
     # a batch beyond the fixed array is refused before anything runs
     rc = fn(plan._h, dp.data_ptr(), dx.data_ptr(), 10 ** 7, f.data_ptr(), df.data_ptr(), stream)
     assert rc == 3
+
+
+def _fn():
+    from paper_2506_23246_b300 import qp
+    fn = qp.lib().qp_forward_noalloc
+    fn.argtypes = [ctypes.c_void_p] * 3 + [ctypes.c_int64] + [ctypes.c_void_p] * 3
+    fn.restype = ctypes.c_int32
+    return fn
+
+
+def test_forward_noalloc_equals_simt_forward_and_oracle(oracle):
+    """The call always runs the FP32 SIMT kernels. On a SIMT plan with the direct premap it
+    runs exactly the kernels qp_forward runs, so the outputs are identical; on a plan whose
+    qp_forward takes the tensor cores (8 qubits, RFF + MLP premap) both are held to the FP64
+    oracle. After the call, qp_last_device_error reads the call's own status word."""
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2506_23246_b300 import build, qp
+    build.build()
+    fn = _fn()
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+    circ = W.circuit(6, 4, 3, ansatz="basic_ryrz", enc="ry", scale="pi", premap="direct")
+    plan = qp.Plan(circ, path="simt")
+    dp = torch.tensor(W.init_params(circ, 3), device="cuda")
+    for seed in (4, 5):
+        dx = torch.tensor(W.uniform_points(777, seed), device="cuda")
+        f_ref, df_ref = plan.forward(dp, dx)
+        f = torch.full_like(f_ref, float("nan"))
+        df = torch.full_like(df_ref, float("nan"))
+        assert fn(plan._h, dp.data_ptr(), dx.data_ptr(), dx.shape[0], f.data_ptr(), df.data_ptr(),
+                  stream) == 0
+        torch.cuda.synchronize()
+        assert plan.last_device_error() == 0
+        assert torch.equal(f, f_ref) and torch.equal(df, df_ref)
+
+    circ = W.c3_circuit(8, 6)
+    params = W.init_params(circ, 1)
+    pts = W.uniform_points(300, 6, 0.7)
+    plan = qp.Plan(circ, W.c3_problem("dielectric"))
+    dp = torch.tensor(params, device="cuda")
+    dx = torch.tensor(pts, device="cuda")
+    f = torch.empty(300, 3, device="cuda")
+    df = torch.empty(300, 3, 3, device="cuda")
+    assert fn(plan._h, dp.data_ptr(), dx.data_ptr(), 300, f.data_ptr(), df.data_ptr(), stream) == 0
+    torch.cuda.synchronize()
+    assert plan.last_device_error() == 0
+    fo, dfo = oracle.forward(circ, params, pts)
+    assert _rel(f.cpu().numpy(), fo) < TOL
+    assert _rel(df.cpu().numpy(), dfo) < TOL
