@@ -35,6 +35,10 @@
 //   ci[ 0..10] = n_qubits, n_layers, n_readout, ansatz, enc, scale, premap,
 //                n_direct, rff_freqs, mlp_width, mlp_depth
 //     ansatz: 0 Basic RY,RZ   1 Basic Rot   2 Strongly Rot   3 No-entanglement Rot
+//             4 Cross-Mesh (RX per qubit, CRZ(i,j) for every ordered pair i != j)
+//             5 Cross-Mesh-2-Rotations (RX then RZ per qubit, the same CRZ mesh)
+//             6 Cross-Mesh-CNOT (Rot per qubit, CNOT(i,j) for every ordered pair i != j)
+//     (Sec. 2.3 items 3-5, Eq. 29; the mesh gates run i = 0..n-1 outer, j = 0..n-1 inner)
 //     enc:    0 RX  1 RY;  scale: 0 none 1 pi 2 bias 3 asin 4 acos (Eq. 27a-e)
 //     premap: 0 direct (theta_j = scale(v_j), j < n_direct; 0 otherwise)
 //             1 RFF + tanh MLP (a = tanh(h_out), theta = scale(a))
@@ -47,7 +51,9 @@
 // Parameter layout (flat):
 //   premap RFF+MLP: Omega[F][3] (fixed, zero gradient), then per hidden layer
 //     W[H][in] (in = 2F first, H after), b[H]; then W_out[n][H], b_out[n]
-//   circuit: [L][n][k], k = 2 (RY angle, RZ angle) for ansatz 0, else 3 (Rot a,b,g)
+//   circuit: per layer [n][k] single-qubit angles, k = 2 (RY, RZ) for ansatz 0, 1 (RX) for
+//     ansatz 4, 2 (RX, RZ) for ansatz 5, else 3 (Rot a,b,g); then, for ansatz 4 and 5, the
+//     n (n-1) CRZ angles [i][j != i] (control i, targets j in increasing order)
 //   head: W[3][m], b[3]
 #include <cmath>
 #include <complex>
@@ -140,7 +146,9 @@ R hexp(const R& a) { double e = std::exp(a.c[0]); return fun(a, e, e, e); }
 // ---------------------------------------------------------------- configs
 struct Circ {
   int n, L, m, ansatz, enc, scale, premap, n_direct, F, H, depth;
-  int k() const { return ansatz == 0 ? 2 : 3; }
+  int k() const { return ansatz == 0 || ansatz == 5 ? 2 : (ansatz == 4 ? 1 : 3); }
+  bool crz() const { return ansatz == 4 || ansatz == 5; }
+  int64_t layer_count() const { return (int64_t)n * k() + (crz() ? (int64_t)n * (n - 1) : 0); }
   int64_t premap_count() const {
     if (premap == 0) return 0;
     int64_t c = 3LL * F;
@@ -150,7 +158,7 @@ struct Circ {
     return c;
   }
   int64_t circuit_offset() const { return premap_count(); }
-  int64_t circuit_count() const { return (int64_t)L * n * k(); }
+  int64_t circuit_count() const { return (int64_t)L * layer_count(); }
   int64_t head_offset() const { return circuit_offset() + circuit_count(); }
   int64_t total() const { return head_offset() + 3LL * m + 3; }
 };
@@ -162,7 +170,7 @@ Circ read_circ(const int* ci) {
 }
 bool circ_ok(const Circ& c) {
   if (c.n < 1 || c.n > 12 || c.L < 0 || c.m < 1 || c.m > c.n) return false;
-  if (c.ansatz < 0 || c.ansatz > 3 || c.enc < 0 || c.enc > 1 || c.scale < 0 || c.scale > 4) return false;
+  if (c.ansatz < 0 || c.ansatz > 6 || c.enc < 0 || c.enc > 1 || c.scale < 0 || c.scale > 4) return false;
   if (c.premap == 0) return c.n_direct >= 0 && c.n_direct <= 3 && c.n_direct <= c.n;
   if (c.premap == 1) return c.F >= 1 && c.H >= 1 && c.depth >= 0;
   return false;
@@ -263,15 +271,44 @@ int ring_stride(const Circ& c, int l) {
   if (c.ansatz == 2) return c.n > 1 ? 1 + (l % (c.n - 1)) : 1;
   return 1;
 }
-// One ansatz layer l: single-qubit rotations on every qubit, then the CNOT ring.
+// Controlled RZ (Sec. 2.3 item 3): RZ(t) on the target where the control qubit is 1.
+void apply_crz(std::vector<C>& s, int n, int ctl, int tgt, const R& t) {
+  const int64_t bc = 1LL << bitpos(n, ctl), bt = 1LL << bitpos(n, tgt);
+  const G2 g = g_rz(t);
+  const int64_t dim = 1LL << n;
+  for (int64_t k = 0; k < dim; ++k)
+    if (k & bc) s[k] = ((k & bt) ? g.d : g.a) * s[k];
+}
+// One ansatz layer l: single-qubit rotations on every qubit, then the entangling part (CNOT
+// ring, CRZ mesh or CNOT mesh).
 void apply_layer(std::vector<C>& s, const Circ& c, const R* cp, int l) {
   const int k = c.k();
+  const R* lp = cp + (int64_t)l * c.layer_count();
   for (int q = 0; q < c.n; ++q) {
-    const R* p = cp + ((int64_t)l * c.n + q) * k;
-    G2 g = (c.ansatz == 0) ? mul(g_rz(p[1]), g_ry(p[0])) : g_rot(p[0], p[1], p[2]);
+    const R* p = lp + (int64_t)q * k;
+    G2 g;
+    switch (c.ansatz) {
+      case 0: g = mul(g_rz(p[1]), g_ry(p[0])); break;   // RY(a) then RZ(b)
+      case 4: g = g_rx(p[0]); break;                     // RX(a)
+      case 5: g = mul(g_rz(p[1]), g_rx(p[0])); break;   // RX(a) then RZ(b)
+      default: g = g_rot(p[0], p[1], p[2]); break;
+    }
     apply1(s, c.n, q, g);
   }
   if (c.ansatz == 3 || c.n < 2) return;
+  if (c.crz()) {
+    const R* t = lp + (int64_t)c.n * k;
+    for (int i = 0; i < c.n; ++i)
+      for (int j = 0; j < c.n; ++j)
+        if (j != i) apply_crz(s, c.n, i, j, t[i * (c.n - 1) + (j < i ? j : j - 1)]);
+    return;
+  }
+  if (c.ansatz == 6) {
+    for (int i = 0; i < c.n; ++i)
+      for (int j = 0; j < c.n; ++j)
+        if (j != i) apply_cnot(s, c.n, i, j);
+    return;
+  }
   const int r = ring_stride(c, l);
   for (int i = 0; i < c.n; ++i) apply_cnot(s, c.n, i, (i + r) % c.n);
 }

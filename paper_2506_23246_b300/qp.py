@@ -12,7 +12,8 @@ import torch
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libqpinn.so")
 
-ANSATZ = {"basic_ryrz": 0, "basic_rot": 1, "strong_rot": 2, "noent_rot": 3}
+ANSATZ = {"basic_ryrz": 0, "basic_rot": 1, "strong_rot": 2, "noent_rot": 3, "cross_mesh": 4,
+          "cross_mesh_2rot": 5, "cross_mesh_cnot": 6}
 ENC = {"rx": 0, "ry": 1}
 SCALE = {"none": 0, "pi": 1, "bias": 2, "asin": 3, "acos": 4}
 PREMAP = {"direct": 0, "rff_mlp": 1}

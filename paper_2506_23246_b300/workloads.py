@@ -111,10 +111,19 @@ def bc_points(n, seed, tmax=1.0):
 
 # ----------------------------------------------------------------------------- params
 
+CRZ_ANSATZE = ("cross_mesh", "cross_mesh_2rot")
+
+
+def single_qubit_params(ansatz):
+    """Angles of the single-qubit gate per qubit and layer: RY, RZ (basic_ryrz); RX
+    (cross_mesh); RX, RZ (cross_mesh_2rot); Rot(a, b, g) otherwise (Sec. 2.3, Eq. 28)."""
+    return {"basic_ryrz": 2, "cross_mesh": 1, "cross_mesh_2rot": 2}.get(ansatz, 3)
+
+
 def param_blocks(circ):
     """Sizes of the parameter blocks in the flat layout, in order."""
     n, L, m = circ["n_qubits"], circ["n_layers"], circ["n_readout"]
-    k = 2 if circ["ansatz"] == "basic_ryrz" else 3
+    k = single_qubit_params(circ["ansatz"])
     blocks = []
     if circ["premap"] == "rff_mlp":
         F, H, depth = circ["rff_freqs"], circ["mlp_width"], circ["mlp_depth"]
@@ -126,7 +135,11 @@ def param_blocks(circ):
             fan = H
         blocks.append(("W_out", (n, fan)))
         blocks.append(("b_out", (n,)))
-    blocks.append(("circuit", (L, n, k)))
+    if circ["ansatz"] in CRZ_ANSATZE:
+        # per layer: n x k single-qubit angles, then the n (n - 1) CRZ angles [i][j != i]
+        blocks.append(("circuit", (L, n * k + n * (n - 1))))
+    else:
+        blocks.append(("circuit", (L, n, k)))
     blocks.append(("head_W", (3, m)))
     blocks.append(("head_b", (3,)))
     return blocks

@@ -91,7 +91,8 @@ def test_table1_param_counts(oracle):
             if line and not line.startswith("#"):
                 parts = line.split()
                 rows[tuple(parts[:-1])] = int(parts[-1])
-    for ans in ("basic_rot", "strong_rot", "noent_rot"):
+    for ans in ("basic_rot", "strong_rot", "noent_rot", "cross_mesh", "cross_mesh_2rot",
+                "cross_mesh_cnot"):
         circ = W.circuit(7, 4, 7, ansatz=ans, enc="rx", scale="acos", premap="direct")
         lay = oracle.param_layout(circ)
         assert lay["head"] - lay["circuit"] == rows[("quantum", ans)]
@@ -182,7 +183,8 @@ def test_clifford_z_propagation(oracle, n, L, ansatz):
 
 
 @pytest.mark.parametrize("n,ansatz", [(1, "basic_rot"), (3, "basic_ryrz"), (6, "strong_rot"),
-                                      (8, "strong_rot")])
+                                      (8, "strong_rot"), (5, "cross_mesh"), (6, "cross_mesh_2rot"),
+                                      (5, "cross_mesh_cnot")])
 def test_norm_and_layer_unitarity(oracle, n, ansatz):
     L = 3
     circ = W.circuit(n, L, 1, ansatz=ansatz, enc="rx", scale="pi", premap="direct",
@@ -223,18 +225,35 @@ def _kron_cnot(n, c, t):
     return ka + kb
 
 
+def _kron_crz(n, c, t, theta):
+    """Controlled RZ as the exponential of its generator |1><1|_c (x) Z_t (Kronecker)."""
+    P1 = np.array([[0, 0], [0, 1]], dtype=complex)
+    mats = [np.eye(2, dtype=complex)] * n
+    mats = list(mats)
+    mats[c] = P1
+    mats[t] = Z
+    gen = mats[0]
+    for m in mats[1:]:
+        gen = np.kron(gen, m)
+    return expm(-0.5j * theta * gen)
+
+
 @pytest.mark.parametrize("n,ansatz,enc", [(2, "basic_rot", "rx"), (3, "basic_ryrz", "ry"),
-                                          (4, "strong_rot", "rx"), (4, "noent_rot", "ry")])
+                                          (4, "strong_rot", "rx"), (4, "noent_rot", "ry"),
+                                          (3, "cross_mesh", "rx"), (4, "cross_mesh_2rot", "ry"),
+                                          (4, "cross_mesh_cnot", "rx")])
 def test_bruteforce_dense_kronecker(oracle, n, ansatz, enc):
     """n <= 4: the dense product of Kronecker-expanded matrix exponentials equals the
-    oracle's pair-loop state."""
+    oracle's pair-loop state. The CRZ mesh (Eq. 29) is multiplied here in the reverse of the
+    oracle's order: its gates are diagonal and commute."""
     L = 3
     circ = W.circuit(n, L, 1, ansatz=ansatz, enc=enc, scale="pi", premap="direct",
                      n_direct=min(3, n))
     params = W.init_params(circ, 2).astype(np.float64)
     off = W.param_offsets(circ)
     o, shape = off["circuit"]
-    cp = params[o:o + int(np.prod(shape))].reshape(shape)
+    k = W.single_qubit_params(ansatz)
+    cl = params[o:o + int(np.prod(shape))].reshape(L, -1)
     rng = np.random.default_rng(9)
     theta = rng.uniform(-3, 3, n)
     psi = np.zeros(1 << n, dtype=complex)
@@ -243,13 +262,28 @@ def test_bruteforce_dense_kronecker(oracle, n, ansatz, enc):
         psi = _kron_gate(n, j, _rot_exp(X if enc == "rx" else Y, theta[j])) @ psi
     for l in range(L):
         for q in range(n):
+            p = cl[l, q * k:(q + 1) * k]
             if ansatz == "basic_ryrz":
-                g = _rot_exp(Z, cp[l, q, 1]) @ _rot_exp(Y, cp[l, q, 0])
+                g = _rot_exp(Z, p[1]) @ _rot_exp(Y, p[0])
+            elif ansatz == "cross_mesh":
+                g = _rot_exp(X, p[0])
+            elif ansatz == "cross_mesh_2rot":
+                g = _rot_exp(Z, p[1]) @ _rot_exp(X, p[0])
             else:
-                a, b, gm = cp[l, q]
+                a, b, gm = p
                 g = _rot_exp(Z, gm) @ _rot_exp(Y, b) @ _rot_exp(Z, a)
             psi = _kron_gate(n, q, g) @ psi
-        if ansatz != "noent_rot" and n > 1:
+        if ansatz in ("cross_mesh", "cross_mesh_2rot"):
+            ang = cl[l, n * k:].reshape(n, n - 1)
+            pairs = [(i, j) for i in range(n) for j in range(n) if j != i]
+            for i, j in reversed(pairs):
+                psi = _kron_crz(n, i, j, ang[i, j if j < i else j - 1]) @ psi
+        elif ansatz == "cross_mesh_cnot":
+            for i in range(n):
+                for j in range(n):
+                    if j != i:
+                        psi = _kron_cnot(n, i, j) @ psi
+        elif ansatz != "noent_rot" and n > 1:
             r = 1 + (l % (n - 1)) if ansatz == "strong_rot" else 1
             for i in range(n):
                 psi = _kron_cnot(n, i, (i + r) % n) @ psi
@@ -665,3 +699,57 @@ def test_rff_premap_theta_and_jacobian(oracle):
             dh = (-wc * math.sin(s) + ws * math.cos(s)) * omega[0]
             want = dtheta_da[scale](a) * (1 - a * a) * dh
             assert np.max(np.abs(J[i, 0] - want)) < 1e-12, scale
+
+
+# ----------------------------------------------------------------------------- Cross-Mesh
+
+@pytest.mark.parametrize("ansatz", ["cross_mesh", "cross_mesh_2rot"])
+def test_cross_mesh_single_layer_readout(oracle, ansatz):
+    """One Cross-Mesh layer: the CRZ mesh is diagonal, so it leaves every <Z_i> unchanged.
+    RX(theta_i) then RX(a_i) (and RZ, which also commutes with Z) gives <Z_i> = cos(theta_i +
+    a_i) whatever the CRZ angles, and the gradient of any loss w.r.t. a CRZ angle is 0."""
+    n = 4
+    circ = W.circuit(n, 1, n, ansatz=ansatz, enc="rx", scale="pi", premap="direct", n_direct=3)
+    params = W.init_params(circ, 3).astype(np.float64)
+    off = W.param_offsets(circ)
+    o, _ = off["circuit"]
+    k = W.single_qubit_params(ansatz)
+    pts = W.uniform_points(5, 4).astype(np.float64)
+    for rows in ([0, 1, 2], [3, 0, 1]):
+        p = _set_head(circ, params, rows)
+        f, _ = oracle.forward(circ, p, pts)
+        for b, v in enumerate(pts):
+            theta = [math.pi * v[0], math.pi * v[1], math.pi * v[2], 0.0]
+            for c, i in enumerate(rows):
+                assert abs(f[b, c] - math.cos(theta[i] + p[o + i * k])) < 1e-13
+    prob = W.problem("vacuum", w_energy=10.0)
+    sets = {"colloc": pts, "ic": W.ic_points_uniform(3, 5)}
+    crz = np.arange(o + n * k, o + n * k + n * (n - 1))
+    g = oracle.grad(circ, prob, params, sets, crz)
+    assert np.max(np.abs(g)) < 1e-13
+
+
+def test_crz_gradient_exact_shift_rule(oracle):
+    """A CRZ angle theta enters through exp(-i theta P / 2) with P = |1><1|_c (x) Z_t, whose
+    eigenvalues are 0 and +-1: the states carry frequencies 0 and 1/2 in theta, the fields
+    and input derivatives are trig polynomials of degree 2 in u = theta / 2, the squared
+    residuals degree 4 and the squared Poynting residual degree 8. The R = 8 shift rule in u
+    is then exact: dL/dtheta = (1/2) dL/du."""
+    circ = W.circuit(4, 2, 4, ansatz="cross_mesh_2rot", enc="rx", scale="acos", premap="rff_mlp",
+                     **SMALL_MLP)
+    prob = W.problem("dielectric", disk_x0=0.2, disk_r=0.5, w_energy=10.0, energy_slice=4,
+                     energy_nt=2)
+    sets = {"colloc": W.uniform_points(6, 40), "ic": W.ic_points_uniform(3, 41),
+            "bc": W.bc_points(2, 42)}
+    params = W.init_params(circ, 8).astype(np.float64)
+    lay = oracle.param_layout(circ)
+    per = (lay["head"] - lay["circuit"]) // 2
+    idx = [lay["circuit"] + 8 + j for j in (0, 5, 11)] + [lay["circuit"] + per + 8 + 7, lay["circuit"] + 3]
+    g = oracle.grad(circ, prob, params, sets, idx)
+    for j, i in enumerate(idx):
+        def fn(u, i=i):
+            pp = params.copy()
+            pp[i] = 2.0 * u
+            return oracle.loss(circ, prob, pp, sets)[0]
+        want = 0.5 * _shift_rule(fn, params[i] / 2.0, 8)
+        assert abs(want - g[j]) < 1e-10 * max(1.0, abs(g[j])), (i, want, g[j])
