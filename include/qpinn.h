@@ -45,13 +45,25 @@ typedef enum {
   QP_ERR_INTERNAL = 7
 } qp_status;
 
-/* Ansatz layers (Sec. 2.3). BASIC_RYRZ is the RY(a) then RZ(b) per-qubit variant
- * with the nearest-neighbour CNOT ring; the others use Rot gates (Eq. 28). */
+/* Ansatz layers (Sec. 2.3). Each layer applies one single-qubit gate per qubit, then its
+ * entangling part:
+ *   BASIC_RYRZ       RY(a) then RZ(b); CNOT ring of stride 1
+ *   BASIC_ROT        Rot(a, b, g) (Eq. 28); CNOT ring of stride 1
+ *   STRONG_ROT       Rot; CNOT ring of stride 1 + (l mod (n-1))
+ *   NOENT_ROT        Rot; no two-qubit gate
+ *   CROSS_MESH       RX(a); CRZ(i, j) for every ordered pair i != j, each with its own angle
+ *                    (Eq. 29; control i, target j, CRZ(t) = RZ(t) on j where qubit i is 1)
+ *   CROSS_MESH_2ROT  RX(a) then RZ(b); the same CRZ mesh
+ *   CROSS_MESH_CNOT  Rot; CNOT(i, j) for every ordered pair i != j
+ * The mesh gates run i = 0..n-1 (outer) and j = 0..n-1, j != i (inner), in that order. */
 typedef enum {
   QP_ANSATZ_BASIC_RYRZ = 0,
   QP_ANSATZ_BASIC_ROT = 1,
   QP_ANSATZ_STRONG_ROT = 2,
-  QP_ANSATZ_NOENT_ROT = 3
+  QP_ANSATZ_NOENT_ROT = 3,
+  QP_ANSATZ_CROSS_MESH = 4,
+  QP_ANSATZ_CROSS_MESH_2ROT = 5,
+  QP_ANSATZ_CROSS_MESH_CNOT = 6
 } qp_ansatz;
 
 typedef enum { QP_ENC_RX = 0, QP_ENC_RY = 1 } qp_enc_gate;
@@ -156,7 +168,9 @@ void qp_plan_destroy(qp_plan* plan);
 /* Number of float32 entries of the flat parameter vector. Layout (Sec. 2.2-2.3):
  *   RFF_MLP premap: Omega[F][3] (fixed, gradient 0), then per hidden layer W[H][in]
  *   (in = 2F first, H after) and b[H], then W_out[n][H], b_out[n];
- *   circuit: [L][n][k] with k = 2 (RY angle, RZ angle) for BASIC_RYRZ, else 3 (Rot a,b,g);
+ *   circuit, per layer: [n][k] single-qubit angles with k = 2 (RY, RZ) for BASIC_RYRZ, 1 (RX)
+ *   for CROSS_MESH, 2 (RX, RZ) for CROSS_MESH_2ROT, else 3 (Rot a, b, g); then, for CROSS_MESH
+ *   and CROSS_MESH_2ROT, the n (n-1) CRZ angles [i][j != i] (targets j in increasing order);
  *   head: W[3][m], b[3]. */
 qp_status qp_param_count(const qp_plan* plan, int64_t* n_params);
 /* offsets[0] circuit block, [1] head block, [2] total, [3] number of fixed (Omega) entries. */
@@ -270,8 +284,9 @@ qp_status qp_set_profile_events(qp_plan* plan, int32_t kernel, void* ev_start, v
  * kernel), whatever path and operand form the plan names: on a plan with the direct premap and
  * the SIMT path its results equal qp_forward's bit for bit; otherwise both agree with the FP64
  * oracle within the library's 1e-5 relative bar.
- * Limit: B * n_qubits * 16 bytes plus about 13 KiB of tables must fit in 16 MiB (B <= 104,000
- * points at 10 qubits, 130,000 at 8); a larger B is rejected with QP_ERR_BUFFER_TOO_SMALL
+ * Limit: B * n_qubits * 16 bytes plus about 13 KiB of tables (and L * 2^n * 8 bytes of the CRZ
+ * mesh diagonal for the Cross-Mesh ansatze) must fit in 16 MiB (B <= 104,000 points at 10
+ * qubits, 130,000 at 8); a larger B is rejected with QP_ERR_BUFFER_TOO_SMALL
  * before anything is launched. The array's device address is looked up with the device current
  * on every call made outside stream capture; a call made while its stream is capturing reuses
  * the address of the last call outside capture on that device, so make one call before any

@@ -39,6 +39,7 @@ struct qp_plan {
   bool pg_ok = false;     // RFF + MLP premap with F = 64, H = 32: the GEMM-formulated kernels
   int32_t operands = QP_OPERANDS_FP16_PAIRS;   // forward contraction outside the fused kernel
   int64_t n_params = 0, circ_off = 0, head_off = 0, mlp_off = 0, mlp_count = 0, nfixed = 0;
+  int32_t nE = 0;   // gate-gradient partial sums per block: 3 n L Pauli sums + L CRZ sums
   void* ws = nullptr;
   size_t ws_bytes = 0;
   int32_t last_launches = 0;
@@ -93,7 +94,7 @@ static cudaError_t raise_smem_limit(const void* fn, cudaFuncAttribute attr, int 
 }
 
 struct WsLayout {
-  size_t status, gates, cmat, cenc, thetaJ, dthetaJ, d1, d2, u1, blk_loss, blk_grad, wpart;
+  size_t status, gates, cmat, cenc, crz, crz64, thetaJ, dthetaJ, d1, d2, u1, blk_loss, blk_grad, wpart;
   size_t dW, dphi, dU, dG, dY, dpart, dWT, dmu, dW16, dcs, dgs, dgates, total;
 };
 
@@ -135,6 +136,9 @@ WgGeom wg_geom(const qp_plan* pl, int64_t nkc) {
 }
 
 bool dense_path(const qp_plan* pl) { return pl->path == QP_PATH_GEMM_SPLIT; }
+
+// Kernels launched by launch_front: gate preparation, the CRZ mesh diagonal (CRZ ansatze), premap.
+int front_launches(const qp_plan* pl) { return qp_has_crz(pl->c.ansatz) ? 3 : 2; }
 
 // The fused forward kernel keeps a tile's whole output row (2^(n+1) FP32 columns) in tensor
 // memory, which holds 512 columns: n = 7 and 8.
@@ -195,6 +199,9 @@ WsLayout ws_layout(const qp_plan* pl, int64_t P) {
   w.gates = o; o = al256(o + (size_t)QP_MAXL * QP_MAXQ * 8 * 4);
   w.cmat = o; o = al256(o + (size_t)QP_MAXL * QP_MAXQ * 3 * 4 * 4);
   w.cenc = o; o = al256(o + (size_t)QP_MAXQ * 4 * 4);
+  const bool crz = qp_has_crz(pl->c.ansatz);
+  w.crz = o; o = al256(o + (crz ? (size_t)pl->c.n_layers * ((size_t)1 << n) * 8 : 0));
+  w.crz64 = o; o = al256(o + (crz && dense_path(pl) ? (size_t)pl->c.n_layers * ((size_t)1 << n) * 16 : 0));
   w.thetaJ = o; o = al256(o + (size_t)P * n * 16);
   w.dthetaJ = o; o = al256(o + (size_t)P * n * 16);
   w.d1 = o; o = al256(o + (size_t)P * H * 16);
@@ -202,7 +209,7 @@ WsLayout ws_layout(const qp_plan* pl, int64_t P) {
   w.u1 = o; o = al256(o + (size_t)P * H * 16);
   const int nt = pl->p.energy_nt;
   w.blk_loss = o; o = al256(o + (size_t)pl->blocks_grad * (QP_NLP + nt) * 8);
-  w.blk_grad = o; o = al256(o + (size_t)pl->blocks_grad * (3 * n * pl->c.n_layers + 3 * pl->c.n_readout + 3) * 4);
+  w.blk_grad = o; o = al256(o + (size_t)pl->blocks_grad * (pl->nE + 3 * pl->c.n_readout + 3) * 4);
   const int64_t nW = H ? (int64_t)H * 2 * pl->c.rff_freqs + H + (int64_t)n * H + n : 0;
   w.wpart = o; o = al256(o + (size_t)pl->nwblk * nW * 4);
   const size_t dim = (size_t)1 << n;
@@ -287,7 +294,7 @@ qp_status validate(const qp_circuit* c, const qp_problem* p, int32_t path) {
   if (c->n_qubits < 1 || c->n_qubits > QP_MAXQ) return QP_ERR_INVALID_ARG;
   if (c->n_layers < 1 || c->n_layers > QP_MAXL) return QP_ERR_INVALID_ARG;
   if (c->n_readout < 1 || c->n_readout > c->n_qubits) return QP_ERR_INVALID_ARG;
-  if (c->ansatz < 0 || c->ansatz > 3 || c->enc < 0 || c->enc > 1) return QP_ERR_INVALID_ARG;
+  if (c->ansatz < 0 || c->ansatz > 6 || c->enc < 0 || c->enc > 1) return QP_ERR_INVALID_ARG;
   if (c->scale < 0 || c->scale > 4) return QP_ERR_INVALID_ARG;
   if (c->premap == QP_PREMAP_DIRECT) {
     if (c->n_direct < 0 || c->n_direct > 3 || c->n_direct > c->n_qubits) return QP_ERR_INVALID_ARG;
@@ -352,12 +359,12 @@ qp_status qp_plan_create(const qp_circuit* circuit, const qp_problem* problem, i
     delete pl;
     return QP_ERR_UNSUPPORTED;
   }
-  const int k = circuit->ansatz == QP_ANSATZ_BASIC_RYRZ ? 2 : 3;
   pl->mlp_count = premap_count(*circuit);
   pl->nfixed = circuit->premap == QP_PREMAP_RFF_MLP ? 3LL * circuit->rff_freqs : 0;
   pl->mlp_off = pl->nfixed;
   pl->circ_off = pl->mlp_count;
-  pl->head_off = pl->circ_off + (int64_t)circuit->n_layers * n * k;
+  pl->head_off = pl->circ_off + (int64_t)circuit->n_layers * qp_layer_params(circuit->ansatz, n);
+  pl->nE = 3 * n * circuit->n_layers + circuit->n_layers * qp_crz_sums(circuit->ansatz, n);
   pl->n_params = pl->head_off + 3LL * circuit->n_readout + 3;
 
   if (cudaGetDevice(&pl->device) != cudaSuccess ||
@@ -377,7 +384,7 @@ qp_status qp_plan_create(const qp_circuit* circuit, const qp_problem* problem, i
     int warps = kMaxWarps;
     qpk::SmemLayout lay;
     for (; warps >= 1; --warps) {
-      lay = qpk::smem_layout(n, circuit->n_layers, circuit->n_readout, grad ? nt : 0, warps, sstride, ppw);
+      lay = qpk::smem_layout(n, circuit->n_layers, circuit->n_readout, grad ? nt : 0, warps, sstride, ppw, pl->nE);
       if (lay.total <= smem_optin) break;
     }
     if (warps < 1) { delete pl; return QP_ERR_UNSUPPORTED; }
@@ -418,7 +425,7 @@ qp_status qp_plan_create(const qp_circuit* circuit, const qp_problem* problem, i
         raise_smem_limit((void*)qpd::dense_sweep_right_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (1 << n) * 16 * 8) != cudaSuccess ||
         (n <= 8 && raise_smem_limit((void*)qpd::dense_sweep_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    qpd::swc_smem(n, pl->c.n_layers, qpd::swc_size(n, false))) != cudaSuccess) ||
+                                    qpd::swc_smem(n, pl->c.n_layers, qpd::swc_size(n, false), qp_crz_sums(pl->c.ansatz, n))) != cudaSuccess) ||
         (fused_path(pl) &&
          (raise_smem_limit(n == 7 ? (void*)qpd::dense_fused_fwd_kernel<7> : (void*)qpd::dense_fused_fwd_kernel<8>,
                            cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -434,7 +441,7 @@ qp_status qp_plan_create(const qp_circuit* circuit, const qp_problem* problem, i
       cudaLaunchConfig_t cfg = {};
       cfg.gridDim = dim3(16);
       cfg.blockDim = dim3(qpd::SWC_THREADS);
-      cfg.dynamicSmemBytes = qpd::swc_smem(n, pl->c.n_layers, 16);
+      cfg.dynamicSmemBytes = qpd::swc_smem(n, pl->c.n_layers, 16, qp_crz_sums(pl->c.ansatz, n));
       cudaLaunchAttribute attr[1];
       attr[0].id = cudaLaunchAttributeClusterDimension;
       attr[0].val.clusterDim.x = 16;
@@ -573,6 +580,13 @@ static qp_status launch_front(qp_plan* pl, const float* d_params, const float* c
   pa.gates = (float*)(ws + w.gates); pa.cmat = (float*)(ws + w.cmat); pa.cenc = (float*)(ws + w.cenc);
   pa.counts = (int32_t*)(ws + w.status) + 1; pa.status = (int32_t*)(ws + w.status);
   qpk::prep_kernel<<<(L * n + 63) / 64, 64, 0, s>>>(pa);
+  if (qp_has_crz(pl->c.ansatz)) {
+    // diagonal of every layer's CRZ mesh (FP64 as well for the unitary build)
+    const int64_t tot = (int64_t)L << n;
+    qpk::crz_phase_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(
+        d_params, pl->circ_off, n, L, pl->c.ansatz, (float2*)(ws + w.crz),
+        dense_path(pl) ? (double2*)(ws + w.crz64) : nullptr);
+  }
   qpk::PremapArgs ma;
   std::memset(&ma, 0, sizeof(ma));
   for (int i = 0; i < 3; ++i) { ma.pts[i] = pts[i]; ma.npts[i] = npts[i]; }
@@ -630,7 +644,10 @@ static void fill_circ(qp_plan* pl, QPCircArgs& a, const WsLayout& w, const float
   a.blk_loss = (double*)(ws + w.blk_loss);
   a.blk_grad = (float*)(ws + w.blk_grad);
   a.loss_stride = QP_NLP + pl->p.energy_nt;
-  a.grad_stride = 3 * n * pl->c.n_layers + 3 * pl->c.n_readout + 3;
+  a.grad_stride = pl->nE + 3 * pl->c.n_readout + 3;
+  a.nE = pl->nE;
+  a.ansatz = pl->c.ansatz;
+  a.crz = qp_has_crz(pl->c.ansatz) ? (const float2*)(ws + w.crz) : nullptr;
 }
 
 static qp_status launch_reduce(qp_plan* pl, const WsLayout& w, const float* d_params, const int64_t npts[3],
@@ -654,11 +671,12 @@ static qp_status dense_loss_grad(qp_plan* pl, const float* d_params, const float
   int launches = 0;
   qp_status st = launch_front(pl, d_params, pts, npts, w, s, true);
   if (st != QP_OK) return st;
-  launches += 2;
+  launches += front_launches(pl);
   qpd::BuildArgs ba = {};
   ba.params = d_params; ba.circ_off = pl->circ_off; ba.n = n; ba.L = L;
   ba.gates = (double2*)(ws + w.dgates);
   ba.ansatz = pl->c.ansatz; ba.enc = pl->c.enc; ba.W = (float*)(ws + w.dW); ba.U = (double2*)(ws + w.dU);
+  ba.crz64 = qp_has_crz(pl->c.ansatz) ? (const double2*)(ws + w.crz64) : nullptr;
   const bool mlp = pl->c.premap == QP_PREMAP_RFF_MLP;
   const bool fused = fused_path(pl);
   // forward and back-projection on FP16 pairs (the fused n = 7, 8 kernels have no other form)
@@ -695,8 +713,8 @@ static qp_status dense_loss_grad(qp_plan* pl, const float* d_params, const float
     fa.counts = (const int32_t*)(ws + w.status) + 1;
     fa.blk_loss = (double*)(ws + w.blk_loss); fa.blk_grad = (float*)(ws + w.blk_grad);
     fa.loss_stride = QP_NLP + pl->p.energy_nt;
-    fa.grad_stride = 3 * n * L + 3 * pl->c.n_readout + 3;
-    fa.nE = 3 * n * L;
+    fa.grad_stride = pl->nE + 3 * pl->c.n_readout + 3;
+    fa.nE = pl->nE;
     fa.nblk = pl->blocks_grad;
     fa.status = (int32_t*)(ws + w.status);
     fa.scal = (int32_t*)(ws + w.status) + 16;
@@ -745,8 +763,8 @@ static qp_status dense_loss_grad(qp_plan* pl, const float* d_params, const float
     pa.counts = (const int32_t*)(ws + w.status) + 1;
     pa.blk_loss = (double*)(ws + w.blk_loss); pa.blk_grad = (float*)(ws + w.blk_grad);
     pa.loss_stride = QP_NLP + pl->p.energy_nt;
-    pa.grad_stride = 3 * n * L + 3 * pl->c.n_readout + 3;
-    pa.nE = 3 * n * L;
+    pa.grad_stride = pl->nE + 3 * pl->c.n_readout + 3;
+    pa.nE = pl->nE;
     pa.lmax = fwd16 ? (int32_t*)(ws + w.status) + 17 : nullptr;   // scale of the mu operand
     const int psmem = ((QP_NLP + pl->p.energy_nt) * 8 + 15) / 16 * 16 + (3 * pl->c.n_readout + 3) * 4;
     if (n == 9)
@@ -786,6 +804,7 @@ static qp_status dense_loss_grad(qp_plan* pl, const float* d_params, const float
   sa.U = (const double2*)(ws + w.dU); sa.G = (float2*)(ws + w.dG); sa.Y = (float2*)(ws + w.dY);
   sa.params = d_params; sa.circ_off = pl->circ_off; sa.eout = (float*)(ws + w.blk_grad);
   sa.gates = (const double2*)(ws + w.dgates);
+  sa.crz = qp_has_crz(pl->c.ansatz) ? (const float2*)(ws + w.crz) : nullptr;
   {
     const int gg = gsum_groups(pl);
     qpd::dense_gsum_kernel<<<dim3((dim * dim + 255) / 256, gg), 256, 0, s>>>(sa, gg, (float4*)(ws + w.dgs));
@@ -801,7 +820,7 @@ static qp_status dense_loss_grad(qp_plan* pl, const float* d_params, const float
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(S);
     cfg.blockDim = dim3(qpd::SWC_THREADS);
-    cfg.dynamicSmemBytes = qpd::swc_smem(n, L, S);
+    cfg.dynamicSmemBytes = qpd::swc_smem(n, L, S, qp_crz_sums(pl->c.ansatz, n));
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -920,6 +939,7 @@ qp_status qp_forward(qp_plan* pl, const float* d_params, const float* d_pts, int
     qpd::BuildArgs ba = {};
     ba.params = d_params; ba.circ_off = pl->circ_off; ba.n = n; ba.L = pl->c.n_layers;
     ba.ansatz = pl->c.ansatz; ba.enc = pl->c.enc; ba.W = (float*)(ws + w.dW); ba.U = nullptr;
+    ba.crz64 = qp_has_crz(pl->c.ansatz) ? (const double2*)(ws + w.crz64) : nullptr;
     const bool fwd16 = n >= 7 && pl->operands == QP_OPERANDS_FP16_PAIRS;
     ba.W16 = fwd16 ? (__half*)(ws + w.dW16) : nullptr;
     if (fwd16) ba.W = nullptr;
@@ -947,7 +967,7 @@ qp_status qp_forward(qp_plan* pl, const float* d_params, const float* d_pts, int
     ra.nv = ga.nv; ra.npts = B; ra.pt_base = 0; ra.out_f = d_fields; ra.out_df = d_dfields;
     const int64_t rb = (B + 7) / 8;
     qpd::dense_readout_kernel<<<(unsigned)(rb < 4096 ? rb : 4096), 256, 0, s>>>(ra);
-    pl->last_launches = 5;
+    pl->last_launches = front_launches(pl) + 3;
     return cuda_status(cudaGetLastError());
   }
   QPCircArgs a;
@@ -964,7 +984,7 @@ qp_status qp_forward(qp_plan* pl, const float* d_params, const float* d_pts, int
                        dim3(pl->warps_fwd * 32), args, pl->smem_fwd, s) != cudaSuccess)
     return QP_ERR_CUDA;
   prof_mark(pl, 0, false, s);
-  pl->last_launches = 3;
+  pl->last_launches = front_launches(pl) + 1;
   return cuda_status(cudaGetLastError());
 }
 
@@ -1019,7 +1039,7 @@ qp_status qp_loss_grad(qp_plan* pl, const float* d_params, const qp_batch* batch
   if (P > 0) {
     qp_status st = launch_front(pl, d_params, pts, npts, w, s, true);
     if (st != QP_OK) return st;
-    launches += 2;
+    launches += front_launches(pl);
   } else {
     // nothing to evaluate: still clear the status/counters through the prep kernel
     qpk::PrepArgs pa;
@@ -1105,7 +1125,9 @@ static qp_status launch_reduce(qp_plan* pl, const WsLayout& w, const float* d_pa
   ra.blk_grad = (const float*)(ws + w.blk_grad);
   ra.nblk = pl->blocks_grad;
   ra.loss_stride = QP_NLP + pl->p.energy_nt;
-  ra.grad_stride = 3 * pl->c.n_qubits * pl->c.n_layers + 3 * pl->c.n_readout + 3;
+  ra.grad_stride = pl->nE + 3 * pl->c.n_readout + 3;
+  ra.nE = pl->nE;
+  ra.ansatz = pl->c.ansatz;
   ra.wpart = (const float*)(ws + w.wpart);
   ra.nwblk = mlp ? pl->nwblk : 0;
   ra.nW = (int32_t)(pl->mlp_count - pl->nfixed);
@@ -1116,7 +1138,7 @@ static qp_status launch_reduce(qp_plan* pl, const WsLayout& w, const float* d_pa
   ra.nparams = pl->n_params; ra.circ_off = pl->circ_off; ra.head_off = pl->head_off;
   ra.mlp_off = pl->nfixed; ra.mlp_count = pl->mlp_count - pl->nfixed;
   ra.n = pl->c.n_qubits; ra.L = pl->c.n_layers; ra.m = pl->c.n_readout;
-  ra.k = pl->c.ansatz == QP_ANSATZ_BASIC_RYRZ ? 2 : 3;
+  ra.k = qp_ansatz_k(pl->c.ansatz);
   ra.nt = pl->p.energy_nt; ra.medium = pl->p.medium;
   ra.nc = pl->cur_norm[0] > 0 ? pl->cur_norm[0] : npts[0];
   ra.ni = pl->cur_norm[1] > 0 ? pl->cur_norm[1] : npts[1];
@@ -1282,7 +1304,9 @@ extern "C" qp_status qp_forward_noalloc(qp_plan* pl, const float* d_params, cons
   const size_t off_gates = al256(off_status + 256);
   const size_t off_cmat = al256(off_gates + (size_t)QP_MAXL * QP_MAXQ * 8 * 4);
   const size_t off_cenc = al256(off_cmat + (size_t)QP_MAXL * QP_MAXQ * 3 * 4 * 4);
-  const size_t off_theta = al256(off_cenc + (size_t)QP_MAXQ * 4 * 4);
+  const size_t off_crz = al256(off_cenc + (size_t)QP_MAXQ * 4 * 4);
+  const bool crz = qp_has_crz(pl->c.ansatz);
+  const size_t off_theta = al256(off_crz + (crz ? (size_t)L * ((size_t)1 << n) * 8 : 0));
   if ((uint64_t)B > (kNoAllocScratchBytes - off_theta) / ((size_t)n * 16)) return QP_ERR_BUFFER_TOO_SMALL;
   cudaStream_t s = (cudaStream_t)stream;
   void* base = nullptr;
@@ -1300,6 +1324,11 @@ extern "C" qp_status qp_forward_noalloc(qp_plan* pl, const float* d_params, cons
   pa.counts = (int32_t*)(ws + off_status) + 1;  // zeroed by prep_kernel on every call
   pa.status = (int32_t*)(ws + off_status);
   qpk::prep_kernel<<<(L * n + 63) / 64, 64, 0, s>>>(pa);
+  if (crz) {
+    const int64_t tot = (int64_t)L << n;
+    qpk::crz_phase_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(
+        d_params, pl->circ_off, n, L, pl->c.ansatz, (float2*)(ws + off_crz), nullptr);
+  }
 
   qpk::PremapArgs ma;
   std::memset(&ma, 0, sizeof(ma));
@@ -1331,6 +1360,9 @@ extern "C" qp_status qp_forward_noalloc(qp_plan* pl, const float* d_params, cons
   a.task_end[0] = a.task_end[1] = a.task_end[2] = tasks;
   a.thetaJ = (const float*)(ws + off_theta);
   a.gates = (const float*)(ws + off_gates);
+  a.crz = crz ? (const float2*)(ws + off_crz) : nullptr;
+  a.ansatz = pl->c.ansatz;
+  a.nE = pl->nE;
   a.cenc = (const float*)(ws + off_cenc);
   a.head = d_params + pl->head_off;
   a.counts = pa.counts;
@@ -1343,6 +1375,6 @@ extern "C" qp_status qp_forward_noalloc(qp_plan* pl, const float* d_params, cons
   if (cudaLaunchKernel(circuit_kernel_ptr(n, false), dim3((unsigned)blocks), dim3(pl->warps_fwd * 32),
                        args, pl->smem_fwd, s) != cudaSuccess)
     return QP_ERR_CUDA;
-  pl->last_launches = 3;
+  pl->last_launches = crz ? 4 : 3;
   return cuda_status(cudaGetLastError());
 }

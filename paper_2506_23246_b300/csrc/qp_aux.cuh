@@ -38,6 +38,11 @@ __device__ inline M2 m_ry(double t) {
   sincos(0.5 * t, &s, &c);
   return {{c, 0}, {-s, 0}, {s, 0}, {c, 0}};
 }
+__device__ inline M2 m_rx(double t) {
+  double s, c;
+  sincos(0.5 * t, &s, &c);
+  return {{c, 0}, {0, -s}, {0, -s}, {c, 0}};
+}
 __device__ inline M2 m_pauli(int k) {
   if (k == 0) return {{0, 0}, {1, 0}, {1, 0}, {0, 0}};
   if (k == 1) return {{0, 0}, {0, -1}, {0, 1}, {0, 0}};
@@ -59,15 +64,24 @@ __global__ void prep_kernel(PrepArgs a) {
   if (t == 0) { a.counts[0] = 0; a.status[0] = 0; a.status[16] = 0; a.status[17] = 0; }
   if (t >= a.L * a.n) return;
   const int l = t / a.n, q = t % a.n;
-  const int k = a.ansatz == 0 ? 2 : 3;
-  const float* p = a.params + a.circ_off + (int64_t)t * k;
+  const int k = qp_ansatz_k(a.ansatz);
+  const float* p = a.params + a.circ_off + (int64_t)l * qp_layer_params(a.ansatz, a.n) + (int64_t)q * k;
   M2 U, Vk[3];
   int Gk[3];
+  const M2 I2 = {{1, 0}, {0, 0}, {0, 0}, {1, 0}};
   if (a.ansatz == 0) {  // RY(a) then RZ(b): U = RZ(b) RY(a)
     const M2 rz = m_rz(p[1]), ry = m_ry(p[0]);
     U = mmul(rz, ry);
     Vk[0] = rz; Gk[0] = 1;
-    Vk[1] = {{1, 0}, {0, 0}, {0, 0}, {1, 0}}; Gk[1] = 2;
+    Vk[1] = I2; Gk[1] = 2;
+  } else if (a.ansatz == 4) {  // RX(a) (Cross-Mesh)
+    U = m_rx(p[0]);
+    Vk[0] = I2; Gk[0] = 0;
+  } else if (a.ansatz == 5) {  // RX(a) then RZ(b): U = RZ(b) RX(a) (Cross-Mesh-2-Rotations)
+    const M2 rz = m_rz(p[1]);
+    U = mmul(rz, m_rx(p[0]));
+    Vk[0] = rz; Gk[0] = 0;
+    Vk[1] = I2; Gk[1] = 2;
   } else {              // Rot(a,b,g) = RZ(g) RY(b) RZ(a), Eq. 28
     const M2 za = m_rz(p[0]), yb = m_ry(p[1]), zg = m_rz(p[2]);
     U = mmul(zg, mmul(yb, za));
@@ -84,6 +98,33 @@ __global__ void prep_kernel(PrepArgs a) {
     else c[0] = c[1] = c[2] = c[3] = 0.f;
   }
   if (l == 0) pauli_coords(U, a.enc == 0 ? 0 : 1, a.cenc + q * 4);
+}
+
+// Diagonal of the CRZ mesh of every layer (Eq. 29): CRZ(c, t)(theta) multiplies |k> by
+// exp(i theta (b_t(k) - 1/2)) where b_c(k) = 1, so the whole mesh multiplies |k> by
+// exp(i phi_l(k)), phi_l(k) = sum over ordered pairs c != t of theta_ct b_c(k) (b_t(k) - 1/2)
+// (b_q(k) = bit n-1-q of k). One thread per (layer, k), FP64; writes (cos, sin) in FP32
+// and, if d64 is given, in FP64.
+__global__ void crz_phase_kernel(const float* params, int64_t circ_off, int n, int L, int ansatz,
+                                 float2* out, double2* d64) {
+  const int dim = 1 << n;
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= (int64_t)L * dim) return;
+  const int l = (int)(i / dim), k = (int)(i % dim);
+  const float* th = params + circ_off + (int64_t)l * qp_layer_params(ansatz, n) + n * qp_ansatz_k(ansatz);
+  double ph = 0.0;
+  for (int c = 0; c < n; ++c) {
+    if (!((k >> (n - 1 - c)) & 1)) continue;
+    for (int t = 0; t < n; ++t) {
+      if (t == c) continue;
+      const double bt = ((k >> (n - 1 - t)) & 1) ? 0.5 : -0.5;
+      ph += (double)th[c * (n - 1) + (t < c ? t : t - 1)] * bt;
+    }
+  }
+  double sn, cs;
+  sincos(ph, &sn, &cs);
+  out[i] = make_float2((float)cs, (float)sn);
+  if (d64) d64[i] = make_double2(cs, sn);
 }
 
 // --------------------------------------------------------------------------- BH indicator
@@ -695,7 +736,8 @@ struct ReduceArgs {
   double* loss;
   float* grad;
   int64_t nparams, circ_off, head_off, mlp_off, mlp_count;
-  int32_t n, L, m, k, nt, medium;
+  int32_t n, L, m, k, nt, medium, ansatz;
+  int32_t nE;                  // gate-gradient partial sums per block (head partials follow)
   int64_t nc, ni, nb;          // mean denominators of the three sets
   int64_t norm_diel;           // whole-set points inside the disk, or -1: the counted ones
   float w_ic, w_bc, w_energy;
@@ -716,18 +758,38 @@ __global__ void reduce_kernel(ReduceArgs a) {
     float val = 0.f;
     if (i >= a.circ_off && i < a.head_off) {
       const int64_t r = i - a.circ_off;
-      const int64_t lq = r / a.k;
-      const int kk = (int)(r % a.k);
-      const float* c = a.cmat + (lq * 3 + kk) * 4;
-      double e0 = 0, e1 = 0, e2 = 0;
-      for (int b = lane; b < a.nblk; b += 32) {
-        const float* g = a.blk_grad + (int64_t)b * a.grad_stride + lq * 3;
-        e0 += g[0]; e1 += g[1]; e2 += g[2];
+      const int per = qp_layer_params(a.ansatz, a.n);
+      const int l = (int)(r / per), w = (int)(r % per);
+      if (w < a.n * a.k) {
+        // single-qubit angle: Pauli contractions of its gate combined by the coordinates
+        const int64_t lq = (int64_t)l * a.n + w / a.k;
+        const int kk = w % a.k;
+        const float* c = a.cmat + (lq * 3 + kk) * 4;
+        double e0 = 0, e1 = 0, e2 = 0;
+        for (int b = lane; b < a.nblk; b += 32) {
+          const float* g = a.blk_grad + (int64_t)b * a.grad_stride + lq * 3;
+          e0 += g[0]; e1 += g[1]; e2 += g[2];
+        }
+        e0 = warp_sum_dbl(e0); e1 = warp_sum_dbl(e1); e2 = warp_sum_dbl(e2);
+        val = (float)(c[0] * e0 + c[1] * e1 + c[2] * e2);
+      } else {
+        // CRZ(c, t) angle: generator |1><1|_c (x) Z_t = (Z_t - Z_c Z_t) / 2, so the gradient
+        // is (Z_t - Z_ct) / 2 from the layer's Z-correlation sums
+        const int pi = w - a.n * a.k, c = pi / (a.n - 1), tj = pi % (a.n - 1);
+        const int t = tj < c ? tj : tj + 1;
+        const int64_t base = 3LL * a.n * a.L + (int64_t)l * qp_crz_sums(a.ansatz, a.n);
+        const int64_t ot = base + t;
+        const int64_t oct = base + a.n + qp_pair_index(a.n, c < t ? c : t, c < t ? t : c);
+        double zt = 0, zct = 0;
+        for (int b = lane; b < a.nblk; b += 32) {
+          zt += a.blk_grad[(int64_t)b * a.grad_stride + ot];
+          zct += a.blk_grad[(int64_t)b * a.grad_stride + oct];
+        }
+        zt = warp_sum_dbl(zt); zct = warp_sum_dbl(zct);
+        val = (float)(0.5 * (zt - zct));
       }
-      e0 = warp_sum_dbl(e0); e1 = warp_sum_dbl(e1); e2 = warp_sum_dbl(e2);
-      val = (float)(c[0] * e0 + c[1] * e1 + c[2] * e2);
     } else if (i >= a.head_off) {
-      const int64_t hi = 3LL * a.n * a.L + (i - a.head_off);
+      const int64_t hi = a.nE + (i - a.head_off);
       double t = 0;
       for (int b = lane; b < a.nblk; b += 32) t += a.blk_grad[(int64_t)b * a.grad_stride + hi];
       val = (float)warp_sum_dbl(t);

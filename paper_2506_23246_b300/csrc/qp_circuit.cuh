@@ -26,13 +26,13 @@ __host__ __device__ inline int align16(int x) { return (x + 15) & ~15; }
 
 // Shared-memory layout of the circuit kernel (identical on host and device).
 __host__ __device__ inline SmemLayout smem_layout(int n, int L, int m, int nt, int warps,
-                                                  int sstride, int ppw) {
+                                                  int sstride, int ppw, int nE) {
   SmemLayout s;
   int o = align16((int)sizeof(QPSched));
   s.off_gates = o; o = align16(o + L * n * 8 * 4);
   s.off_cenc = o; o = align16(o + n * 4 * 4);
   s.off_head = o; o = align16(o + (3 * m + 3) * 4);
-  s.off_eacc = o; o = align16(o + 3 * n * L * 4);
+  s.off_eacc = o; o = align16(o + nE * 4);
   s.off_hacc = o; o = align16(o + (3 * m + 3) * 4);
   s.off_loss = o; o = align16(o + (QP_NLP + nt) * 8);
   s.off_state = o; o = align16(o + warps * ppw * sstride * 8);
@@ -296,6 +296,15 @@ __device__ __forceinline__ void run_task(const QPCircArgs& a, const Shared& sh, 
       const int ng = S.ngate[P];
       float U[LB][8];
       load_gates<LB>(sh, S, l, n, P, ng, U);
+      // CRZ mesh (Eq. 29) after the last rotation pass of the layer: one phase per amplitude,
+      // looked up by its logical basis index (the frame is the identity: no CNOTs)
+      const bool crz_here = qp_has_crz(a.ansatz) && p == npl - 1;
+      float2 dph[AMPS];
+      if (crz_here) {
+        const int kb = S.klog[l][lane];
+#pragma unroll
+        for (int j = 0; j < AMPS; ++j) dph[j] = __ldg(&a.crz[l * DIM + (kb ^ S.jlog[l][j])]);
+      }
       EmbedLocal el[LB];
       uint32_t localmask = 0;
       if (P == 0) {
@@ -357,6 +366,10 @@ __device__ __forceinline__ void run_task(const QPCircArgs& a, const Shared& sh, 
 #pragma unroll
             for (int j0 = 0; j0 < AMPS; ++j0)
               if (!(j0 & (1 << b))) gate2(r[j0], r[j0 | (1 << b)], U[b]);
+        if (crz_here) {
+#pragma unroll
+          for (int j = 0; j < AMPS; ++j) r[j] = cmul(r[j], dph[j]);
+        }
 #pragma unroll
         for (int j = 0; j < AMPS; ++j) sv[ad[j]] = r[j];
       }
@@ -516,6 +529,21 @@ __device__ __forceinline__ void run_task(const QPCircArgs& a, const Shared& sh, 
       float E[LB][3];
 #pragma unroll
       for (int b = 0; b < LB; ++b) E[b][0] = E[b][1] = E[b][2] = 0.f;
+      // CRZ mesh of this layer (its last pass): the gradient sums w(k) = sum_s Im(lambda_s(k)^*
+      // phi_s(k)) are taken after the mesh, then the mesh is undone on states and costates
+      const bool crz_here = qp_has_crz(a.ansatz) && p == npl - 1;
+      float2 dph[AMPS];
+      float wk[AMPS];
+#pragma unroll
+      for (int j = 0; j < AMPS; ++j) wk[j] = 0.f;
+      if (crz_here) {
+        const int kb = S.klog[l][lane];
+#pragma unroll
+        for (int j = 0; j < AMPS; ++j) {
+          const float2 d = __ldg(&a.crz[l * DIM + (kb ^ S.jlog[l][j])]);
+          dph[j] = make_float2(d.x, -d.y);
+        }
+      }
       // (state, costate) pairs: vector s and vector nv + s
 #pragma unroll 1
       for (int s = 0; s < nv; ++s) {
@@ -526,6 +554,14 @@ __device__ __forceinline__ void run_task(const QPCircArgs& a, const Shared& sh, 
         for (int j = 0; j < AMPS; ++j) {
           xs[j] = sx[ad[j]];
           ys[j] = sy[ad[j]];
+        }
+        if (crz_here) {
+#pragma unroll
+          for (int j = 0; j < AMPS; ++j) {
+            wk[j] += ys[j].x * xs[j].y - ys[j].y * xs[j].x;
+            xs[j] = cmul(xs[j], dph[j]);
+            ys[j] = cmul(ys[j], dph[j]);
+          }
         }
 #pragma unroll
         for (int b = 0; b < LB; ++b)
@@ -540,12 +576,45 @@ __device__ __forceinline__ void run_task(const QPCircArgs& a, const Shared& sh, 
                   gate2_inv(xs[j0], xs[j0 | (1 << b)], U[b]);
                   gate2_inv(ys[j0], ys[j0 | (1 << b)], U[b]);
                 }
+        }
+        if (l > 0 || crz_here) {
 #pragma unroll
           for (int j = 0; j < AMPS; ++j) {
             sx[ad[j]] = xs[j];
             sy[ad[j]] = ys[j];
           }
         }
+      }
+      if (crz_here) {
+        // Z-correlation sums of the layer: Z_t = sum_k w(k) z_t(k) and Z_ct = sum_k w(k) z_c(k)
+        // z_t(k), z_q(k) = 1 - 2 b_q(k); lanes of a point hold disjoint k = K | sv_j
+        const int kb = S.klog[l][lane];
+        float* zacc = sh.eacc + 3 * NQ * L + l * qp_crz_sums(a.ansatz, NQ);
+#pragma unroll
+        for (int t = 0; t < NQ; ++t) {
+          float zt = 0.f;
+#pragma unroll
+          for (int j = 0; j < AMPS; ++j) {
+            const int kj = kb ^ S.jlog[l][j];
+            zt += ((kj >> (NQ - 1 - t)) & 1) ? -wk[j] : wk[j];
+          }
+          zt = slot_sum<GL>(group_sum<GL>(zt));
+          if (lane == 0) atomicAdd(&zacc[t], zt);
+        }
+#pragma unroll
+        for (int c = 0; c < NQ; ++c)
+#pragma unroll
+          for (int t = c + 1; t < NQ; ++t) {
+            float zct = 0.f;
+#pragma unroll
+            for (int j = 0; j < AMPS; ++j) {
+              const int kj = kb ^ S.jlog[l][j];
+              const int par = ((kj >> (NQ - 1 - t)) ^ (kj >> (NQ - 1 - c))) & 1;
+              zct += par ? -wk[j] : wk[j];
+            }
+            zct = slot_sum<GL>(group_sum<GL>(zct));
+            if (lane == 0) atomicAdd(&zacc[NQ + qp_pair_index(NQ, c, t)], zct);
+          }
       }
       float E2[LB][3][3];  // layer 0: Im<lambda_d|P phi> for the input-Jacobian gradient
 #pragma unroll
@@ -617,7 +686,7 @@ __global__ void __launch_bounds__(384) circuit_kernel(const __grid_constant__ QP
   const int warps = blockDim.x >> 5;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nt = GRAD ? a.pb.energy_nt : 0;
-  const SmemLayout lay = smem_layout(a.n, a.L, a.m, nt, warps, a.sstride, Gm::PPW);
+  const SmemLayout lay = smem_layout(a.n, a.L, a.m, nt, warps, a.sstride, Gm::PPW, a.nE);
   {
     const uint32_t* src = reinterpret_cast<const uint32_t*>(&a.s);
     uint32_t* dst = reinterpret_cast<uint32_t*>(smem);
@@ -629,7 +698,7 @@ __global__ void __launch_bounds__(384) circuit_kernel(const __grid_constant__ QP
     float* h = reinterpret_cast<float*>(smem + lay.off_head);
     for (int i = threadIdx.x; i < 3 * a.m + 3; i += blockDim.x) h[i] = a.head[i];
     float* e = reinterpret_cast<float*>(smem + lay.off_eacc);
-    for (int i = threadIdx.x; i < 3 * a.n * a.L; i += blockDim.x) e[i] = 0.f;
+    for (int i = threadIdx.x; i < a.nE; i += blockDim.x) e[i] = 0.f;
     float* ha = reinterpret_cast<float*>(smem + lay.off_hacc);
     for (int i = threadIdx.x; i < 3 * a.m + 3; i += blockDim.x) ha[i] = 0.f;
     double* lo = reinterpret_cast<double*>(smem + lay.off_loss);
@@ -662,8 +731,8 @@ __global__ void __launch_bounds__(384) circuit_kernel(const __grid_constant__ QP
   double* bl = a.blk_loss + (int64_t)blockIdx.x * a.loss_stride;
   for (int i = threadIdx.x; i < QP_NLP + nt; i += blockDim.x) bl[i] = sh.loss[i];
   float* bg = a.blk_grad + (int64_t)blockIdx.x * a.grad_stride;
-  for (int i = threadIdx.x; i < 3 * a.n * a.L; i += blockDim.x) bg[i] = sh.eacc[i];
-  for (int i = threadIdx.x; i < 3 * a.m + 3; i += blockDim.x) bg[3 * a.n * a.L + i] = sh.hacc[i];
+  for (int i = threadIdx.x; i < a.nE; i += blockDim.x) bg[i] = sh.eacc[i];
+  for (int i = threadIdx.x; i < 3 * a.m + 3; i += blockDim.x) bg[a.nE + i] = sh.hacc[i];
 }
 
 }  // namespace qpk

@@ -1,6 +1,7 @@
 // qp_common.h -- definitions shared by the host planner, the C-ABI and the kernels.
 #pragma once
 #include <stdint.h>
+#include <cuda_runtime.h>
 
 #define QP_MAXQ 10      // qubits
 #define QP_MAXL 16      // ansatz layers
@@ -38,7 +39,57 @@ struct QPSched {
   uint16_t ro_mask[32];  // readout: bit i set -> lane's sign for Z_i flips
   uint8_t ro_sel[16];    // readout: Walsh index (over local bits) of Z_i in the last pass
   int32_t conflict_max;  // planner's worst predicted bank-conflict factor
+  // last pass of each layer (CRZ mesh ansatze: no CNOT, so the frame stays the identity):
+  // logical basis index of each lane's register 0, and of register j relative to it
+  uint16_t klog[QP_MAXL][32];
+  uint16_t jlog[QP_MAXL][32];
 };
+
+// Ansatz properties shared by the host and the kernels (qp_ansatz of qpinn.h).
+__host__ __device__ inline bool qp_has_crz(int ansatz) { return ansatz == 4 || ansatz == 5; }
+// single-qubit angles per qubit and layer: RY, RZ (0); RX (4); RX, RZ (5); Rot (1, 2, 3, 6)
+__host__ __device__ inline int qp_ansatz_k(int ansatz) {
+  return ansatz == 0 || ansatz == 5 ? 2 : (ansatz == 4 ? 1 : 3);
+}
+// circuit parameters per layer: single-qubit angles, then n (n-1) CRZ angles [i][j != i]
+__host__ __device__ inline int qp_layer_params(int ansatz, int n) {
+  return n * qp_ansatz_k(ansatz) + (qp_has_crz(ansatz) ? n * (n - 1) : 0);
+}
+// CRZ gradient sums per layer: Z_t for every qubit t, then Z_ct for every pair c < t
+__host__ __device__ inline int qp_crz_sums(int ansatz, int n) {
+  return qp_has_crz(ansatz) ? n + n * (n - 1) / 2 : 0;
+}
+// index of the pair (c, t), c < t, among the pairs of n qubits
+__host__ __device__ inline int qp_pair_index(int n, int c, int t) { return c * (2 * n - c - 1) / 2 + (t - c - 1); }
+// Entangling permutation of layer l on basis index k (CNOT ring or CNOT mesh; identity for
+// the no-entanglement and CRZ ansatze, whose mesh is diagonal). Qubit q is bit n-1-q.
+__host__ __device__ inline uint32_t qp_ent_map(int n, int ansatz, int l, uint32_t k) {
+  if (n < 2 || ansatz == 3 || ansatz == 4 || ansatz == 5) return k;
+  if (ansatz == 6) {
+    for (int i = 0; i < n; ++i)
+      for (int j = 0; j < n; ++j)
+        if (j != i && ((k >> (n - 1 - i)) & 1u)) k ^= 1u << (n - 1 - j);
+    return k;
+  }
+  const int r = ansatz == 2 ? 1 + (l % (n - 1)) : 1;
+  for (int i = 0; i < n; ++i)
+    if ((k >> (n - 1 - i)) & 1u) k ^= 1u << (n - 1 - (i + r) % n);
+  return k;
+}
+// Its inverse (the gates in reverse order).
+__host__ __device__ inline uint32_t qp_ent_unmap(int n, int ansatz, int l, uint32_t k) {
+  if (n < 2 || ansatz == 3 || ansatz == 4 || ansatz == 5) return k;
+  if (ansatz == 6) {
+    for (int i = n - 1; i >= 0; --i)
+      for (int j = n - 1; j >= 0; --j)
+        if (j != i && ((k >> (n - 1 - i)) & 1u)) k ^= 1u << (n - 1 - j);
+    return k;
+  }
+  const int r = ansatz == 2 ? 1 + (l % (n - 1)) : 1;
+  for (int i = n - 1; i >= 0; --i)
+    if ((k >> (n - 1 - i)) & 1u) k ^= 1u << (n - 1 - (i + r) % n);
+  return k;
+}
 
 struct QPProblemDev {
   int32_t medium;
@@ -66,6 +117,9 @@ struct QPCircArgs {
   const float* thetaJ;        // [P][n][4] (theta, dtheta/dx, dtheta/dy, dtheta/dt)
   float* dthetaJ;             // [P][n][4] (dL/dtheta, dL/dJ_x, dL/dJ_y, dL/dJ_t)
   const float* gates;         // [L][n][8] forward 2x2 complex gate per qubit and layer
+  const float2* crz;          // CRZ mesh ansatze: [L][2^n] phase (cos, sin) by logical index
+  int32_t ansatz;
+  int32_t nE;                 // gate-gradient partial sums per block (3 n L + L crz sums)
   const float* cenc;          // [n][4] Pauli coefficients of the embedding generator
   const float* head;          // W[3][m], b[3]
   const int32_t* counts;      // [0] dielectric-set size

@@ -99,6 +99,7 @@ struct BuildArgs {
   float* WT;       // transpose operand (rows a = basis index, K = o), same tiling, or null
   __half* W16;     // [dim / HKC][2 dim / 256][2 (hi, lo)][256 x HKC] FP16 pairs of W * W16_SCALE, or null
   double2* gates;  // [L][n][4] rotation gate matrices (written by block 0), or null
+  const double2* crz64;  // CRZ mesh ansatze: [L][2^n] diagonal (cos, sin) of each layer's mesh
   __half* WT16;    // [2 dim / HKC][hi, lo][dim x HKC] FP16 pairs of 2^14 U' transposed (mu kernel), or null
 };
 
@@ -106,12 +107,20 @@ __device__ inline double2 zmul(double2 a, double2 b) {
   return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
 
-// Gate of (layer l, qubit q) in double precision (same formulas as the build).
+// Single-qubit gate of (layer l, qubit q) in double precision (same formulas as the build).
 __device__ inline void gate_fp64(const float* params, int64_t circ_off, int ansatz, int n, int l, int q,
                                  double2* g) {
-  const int kp = ansatz == 0 ? 2 : 3;
-  const float* p = params + circ_off + ((int64_t)l * n + q) * kp;
-  if (ansatz == 0) {
+  const int kp = qp_ansatz_k(ansatz);
+  const float* p = params + circ_off + (int64_t)l * qp_layer_params(ansatz, n) + (int64_t)q * kp;
+  if (ansatz == 4 || ansatz == 5) {
+    // RX(a), then RZ(b) for the two-rotation Cross-Mesh: RZ multiplies row 0 by e^{-ib/2} and
+    // row 1 by e^{ib/2}
+    double c, sn, cb = 1.0, sb = 0.0;
+    sincos(0.5 * (double)p[0], &sn, &c);
+    if (ansatz == 5) sincos(0.5 * (double)p[1], &sb, &cb);
+    g[0] = make_double2(cb * c, -sb * c); g[1] = make_double2(-sn * sb, -sn * cb);
+    g[2] = make_double2(sn * sb, -sn * cb); g[3] = make_double2(cb * c, sb * c);
+  } else if (ansatz == 0) {
     double ca, sa, cb, sb;
     sincos(0.5 * (double)p[0], &sa, &ca);
     sincos(0.5 * (double)p[1], &sb, &cb);
@@ -129,15 +138,9 @@ __device__ inline void gate_fp64(const float* params, int64_t circ_off, int ansa
   }
 }
 
-// Index map of the CNOT ring of layer l (basis state |k> -> |c(k)>).
+// Index map of the CNOTs of layer l (ring or mesh; basis state |k> -> |c(k)>).
 __device__ __forceinline__ int ring_map(int n, int ansatz, int l, int k) {
-  if (ansatz == 3 || n < 2) return k;
-  const int r = ansatz == 2 ? 1 + (l % (n - 1)) : 1;
-  for (int i = 0; i < n; ++i) {
-    const int bc = 1 << (n - 1 - i), bt = 1 << (n - 1 - (i + r) % n);
-    if (k & bc) k ^= bt;
-  }
-  return k;
+  return (int)qp_ent_map(n, ansatz, l, (uint32_t)k);
 }
 
 // Gate matrices of every (layer, qubit) in FP64, once per call (one thread each).
@@ -210,7 +213,17 @@ __global__ void dense_build_kernel(BuildArgs a) {
       }
       __syncthreads();
     }
-    if (a.ansatz != 3 && n > 1) {
+    if (qp_has_crz(a.ansatz)) {
+      // CRZ mesh: one phase per basis index
+      for (int j = threadIdx.x; j < dim; j += blockDim.x) {
+        const double2 d = a.crz64[(int64_t)l * dim + j];
+        const float4 x = col[j];
+        DFl re, im;
+        df_cmac(df_split(d.x, d.y), x, re, im);
+        col[j] = make_float4(re.h, re.l, im.h, im.l);
+      }
+      __syncthreads();
+    } else if (a.ansatz != 3 && n > 1) {
       for (int j = threadIdx.x; j < dim; j += blockDim.x) nxt[ring_map(n, a.ansatz, l, j)] = col[j];
       __syncthreads();
       float4* t = col;
@@ -1197,9 +1210,22 @@ struct SweepArgs {
   float2* Y;            // [dim][dim]
   const float* params;
   int64_t circ_off;
-  float* eout;          // blk_grad block 0: E[(l n + q) * 3 + P]
+  float* eout;          // blk_grad block 0: E[(l n + q) * 3 + P], then the CRZ sums [L][ncz]
   const double2* gates; // [L][n][4] rotation gates from the build (cluster sweep)
+  const float2* crz;    // CRZ mesh ansatze: [L][2^n] diagonal (cos, sin) of each layer's mesh
 };
+
+// CRZ mesh gradient sums of one diagonal element w = Im Y[k][k] (basis index k): Z_t += z_t(k) w
+// for every qubit t and Z_ct += z_c(k) z_t(k) w for every pair c < t (z_q(k) = 1 - 2 b_q(k)),
+// into zs[ncz] by shared-memory atomics.
+__device__ __forceinline__ void crz_sums_add(float* zs, int n, int k, float w) {
+  for (int t = 0; t < n; ++t) {
+    const float zt = ((k >> (n - 1 - t)) & 1) ? -w : w;
+    atomicAdd(&zs[t], zt);
+    for (int c = 0; c < t; ++c)
+      atomicAdd(&zs[n + qp_pair_index(n, c, t)], ((k >> (n - 1 - c)) & 1) ? -zt : zt);
+  }
+}
 
 // Compensated FP32 accumulation (Neumaier): s + c carries the sum to about twice FP32
 // precision without the FP64 pipe (conversions and FP64 adds are slow on this part).
@@ -1288,15 +1314,29 @@ __global__ void dense_y_kernel(SweepArgs a) {
 // Undo ring l (Y2[a][b] = Y[c(a)][c(b)], i.e. C^dag Y C) and accumulate, at that point,
 // E_P(l, q) = Im Tr(P_q Y2) for all q: Tr(X_q Y) = sum_a Y[a^q][a],
 // Tr(Y_q Y) = sum_a (bit_q(a) ? i : -i) Y[a^q][a], Tr(Z_q Y) = sum_a (bit_q(a) ? -1 : 1) Y[a][a].
+// For the CRZ mesh ansatze the layer ends with a diagonal D instead: Y2 = D^dag Y D, i.e.
+// Y2[a][b] = conj(d_a) Y[a][b] d_b, and the mesh's gradient sums come from the diagonal.
 __global__ void dense_sweep_ring_kernel(SweepArgs a, int l, const float2* Yin, float2* Yout) {
   const int n = a.n, dim = 1 << n;
   const int64_t tot = (int64_t)dim * dim;
-  __shared__ float es[QP_MAXQ * 3];
-  for (int i = threadIdx.x; i < n * 3; i += blockDim.x) es[i] = 0.f;
+  const bool crz = qp_has_crz(a.ansatz);
+  const int ncz = qp_crz_sums(a.ansatz, n);
+  __shared__ float es[QP_MAXQ * 3 + QP_MAXQ + QP_MAXQ * (QP_MAXQ - 1) / 2];
+  float* zs = es + n * 3;
+  for (int i = threadIdx.x; i < n * 3 + ncz; i += blockDim.x) es[i] = 0.f;
   __syncthreads();
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
     const int ra = (int)(e / dim), cb = (int)(e % dim);
-    const float2 v = Yin[(int64_t)ring_map(n, a.ansatz, l, ra) * dim + ring_map(n, a.ansatz, l, cb)];
+    float2 v;
+    if (crz) {
+      const float2 y = Yin[e];
+      const float2 da = a.crz[(int64_t)l * dim + ra], db = a.crz[(int64_t)l * dim + cb];
+      const float2 t = make_float2(da.x * y.x + da.y * y.y, da.x * y.y - da.y * y.x);  // conj(da) y
+      v = make_float2(t.x * db.x - t.y * db.y, t.x * db.y + t.y * db.x);
+      if (ra == cb) crz_sums_add(zs, n, cb, y.y);
+    } else {
+      v = Yin[(int64_t)ring_map(n, a.ansatz, l, ra) * dim + ring_map(n, a.ansatz, l, cb)];
+    }
     Yout[e] = v;
     const int x = ra ^ cb;
     if (x == 0) {
@@ -1310,6 +1350,7 @@ __global__ void dense_sweep_ring_kernel(SweepArgs a, int l, const float2* Yin, f
   }
   __syncthreads();
   for (int i = threadIdx.x; i < n * 3; i += blockDim.x) atomicAdd(&a.eout[l * n * 3 + i], es[i]);
+  for (int i = threadIdx.x; i < ncz; i += blockDim.x) atomicAdd(&a.eout[3 * n * a.L + l * ncz + i], zs[i]);
 }
 
 // Y <- R^dag Y (rows, TCOL-column tiles per block) for the rotations of layer l.
@@ -1386,9 +1427,9 @@ __host__ __device__ inline int swc_size(int n, bool big) {
   const int cap = big ? 16 : 8;
   return (1 << n) < cap ? (1 << n) : cap;
 }
-__host__ __device__ inline int swc_smem(int n, int L, int S) {
+__host__ __device__ inline int swc_smem(int n, int L, int S, int ncz) {
   const int dim = 1 << n, w = dim / S;
-  return 2 * dim * w * 8 + L * n * 4 * 8 + 2 * dim * 4 + L * n * 3 * 4;
+  return 2 * dim * w * 8 + L * n * 4 * 8 + 2 * dim * 4 + L * n * 3 * 4 + L * ncz * 4;
 }
 __device__ __forceinline__ int swz(int x, int j, int w) { return x * w + (j ^ (x & (w - 1))); }
 
@@ -1442,12 +1483,14 @@ __global__ void __launch_bounds__(SWC_THREADS) dense_sweep_cluster_kernel(SweepA
   float2* gm = bufC + dim * w;                  // [L][n][4] rotation gates (FP32)
   int* cmap = reinterpret_cast<int*>(gm + L * n * 4);   // ring map of the current layer
   int* cinv = cmap + dim;                                // and its inverse
-  float* es = reinterpret_cast<float*>(cinv + dim);      // [L][n][3] E partials
+  float* es = reinterpret_cast<float*>(cinv + dim);      // [L][n][3] E partials, [L][ncz] CRZ sums
+  const bool crz = qp_has_crz(a.ansatz);
+  const int ncz = qp_crz_sums(a.ansatz, n);
   for (int i = threadIdx.x; i < L * n * 4; i += blockDim.x) {
     const double2 g = a.gates[i];
     gm[i] = make_float2((float)g.x, (float)g.y);
   }
-  for (int i = threadIdx.x; i < L * n * 3; i += blockDim.x) es[i] = 0.f;
+  for (int i = threadIdx.x; i < L * n * 3 + L * ncz; i += blockDim.x) es[i] = 0.f;
   // this CTA's rows of Y (row-major in global memory) into layout R
   for (int e0 = threadIdx.x; e0 < w * dim; e0 += SWC_UNROLL * blockDim.x) {
     float2 v[SWC_UNROLL];
@@ -1488,7 +1531,14 @@ __global__ void __launch_bounds__(SWC_THREADS) dense_sweep_cluster_kernel(SweepA
         const int e = e0 + u * blockDim.x;
         if (e < dim * w) {
           const int i = e & (w - 1), j = (e >> lw) & (w - 1), owner = e >> (2 * lw);
-          bufC[swz(cinv[owner * w + i], j, w)] = v[u];
+          float2 y = v[u];
+          if (crz) {
+            // CRZ mesh: Y2[ra][cb] = conj(d_ra) Y[ra][cb] d_cb (the maps are the identity)
+            const float2 da = __ldg(&a.crz[l * dim + owner * w + i]), db = __ldg(&a.crz[l * dim + c * w + j]);
+            const float2 t = make_float2(da.x * y.x + da.y * y.y, da.x * y.y - da.y * y.x);
+            y = make_float2(t.x * db.x - t.y * db.y, t.x * db.y + t.y * db.x);
+          }
+          bufC[swz(cinv[owner * w + i], j, w)] = y;
         }
       }
     }
@@ -1506,6 +1556,23 @@ __global__ void __launch_bounds__(SWC_THREADS) dense_sweep_cluster_kernel(SweepA
 #pragma unroll
           for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
           if (ln == 0) el[q * 3 + 2] += t;
+        }
+        if (crz) {
+          // CRZ mesh sums from the same diagonal: Z_t and Z_ct for c < t
+          float* zl = es + L * n * 3 + l * ncz;
+          for (int t = 0; t < n; ++t) {
+            const float zt = ((cb >> (n - 1 - t)) & 1) ? -vy : vy;
+            float r = zt;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
+            if (ln == 0) zl[t] += r;
+            for (int c2 = 0; c2 < t; ++c2) {
+              float r2 = ((cb >> (n - 1 - c2)) & 1) ? -zt : zt;
+#pragma unroll
+              for (int o = 16; o > 0; o >>= 1) r2 += __shfl_xor_sync(0xffffffffu, r2, o);
+              if (ln == 0) zl[n + qp_pair_index(n, c2, t)] += r2;
+            }
+          }
         }
       } else {
         const int q = n - 1 - wi;
@@ -1559,7 +1626,7 @@ __global__ void __launch_bounds__(SWC_THREADS) dense_sweep_cluster_kernel(SweepA
   }
   // every peer is done reading this CTA's layout R before it exits
   qptc::cluster_sync();
-  for (int i = threadIdx.x; i < L * n * 3; i += blockDim.x) atomicAdd(&a.eout[i], es[i]);
+  for (int i = threadIdx.x; i < L * n * 3 + L * ncz; i += blockDim.x) atomicAdd(&a.eout[i], es[i]);
 }
 }  // namespace qpd
 

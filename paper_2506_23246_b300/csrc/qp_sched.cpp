@@ -4,10 +4,12 @@
 // 2^LB amplitudes of one coset of the LB local qubits into registers, applies the
 // single-qubit gates of those qubits (Sec. 2.3, Eq. 28) and stores them back.
 //
-// The CNOT ring that ends each ansatz layer is a permutation k -> C k of basis
-// indices that is linear over GF(2). It is never executed: the planner tracks a
-// frame T (logical index -> storage index) and replaces T by T C^-1, so the next
-// passes simply address the permuted amplitudes where they already are.
+// The CNOTs that end each ansatz layer (a ring, or the all-pairs mesh) are a permutation
+// k -> C k of basis indices that is linear over GF(2). It is never executed: the planner
+// tracks a frame T (logical index -> storage index) and replaces T by T C^-1, so the next
+// passes simply address the permuted amplitudes where they already are. The diagonal CRZ
+// mesh is applied by the kernel from the logical indices the planner records for the last
+// pass of each layer (klog, jlog).
 //
 // Storage index s is further swizzled (its low 4 bits replaced by an invertible linear
 // mix of all its bits) and every point slot XORs a constant into the low bits, so that the
@@ -42,19 +44,10 @@ Lin identity(int n) {
   return m;
 }
 
-int ring_stride(int n, int ansatz, int l) { return ansatz == 2 ? 1 + (l % (n - 1)) : 1; }
-bool has_ring(int n, int ansatz) { return ansatz != 3 && n > 1; }
-
-// Basis-index map of the CNOT ring of layer l: CNOT(i, i+r) flips target if control is set.
+// Basis-index map of the entangling part of layer l (CNOT ring or mesh; the identity where the
+// layer has no CNOT), or its inverse.
 uint32_t ring_apply(int n, int ansatz, int l, uint32_t k, bool inverse) {
-  if (!has_ring(n, ansatz)) return k;
-  const int r = ring_stride(n, ansatz, l);
-  for (int s = 0; s < n; ++s) {
-    const int i = inverse ? n - 1 - s : s;
-    const int c = i, t = (i + r) % n;
-    if ((k >> pos(n, c)) & 1u) k ^= 1u << pos(n, t);
-  }
-  return k;
+  return inverse ? qp_ent_unmap(n, ansatz, l, k) : qp_ent_map(n, ansatz, l, k);
 }
 
 // Storage -> physical swizzle: phys = s with its low 4 bits replaced by A s_lo ^ B s_hi
@@ -195,6 +188,7 @@ int plan_with(int n, int L, int ansatz, const Swz& swz, QPSched* out) {
         if (g < 4 && n >= 4) a ^= (uint32_t)((slot % (16 / GL)) << g);
         out->lane_addr[P][lane] = (uint16_t)a;
         if (P == 0) out->enc_k[lane] = (uint16_t)K;
+        if (p == npl - 1) out->klog[l][lane] = (uint16_t)K;
         if (l == L - 1 && p == npl - 1) {
           uint32_t Ck = ring_apply(n, ansatz, l, K, false);
           uint16_t msk = 0;
@@ -208,6 +202,7 @@ int plan_with(int n, int L, int ansatz, const Swz& swz, QPSched* out) {
         for (int b = 0; b < lb; ++b)
           if ((j >> b) & 1) sv |= 1u << pos(n, best.ql[b]);
         out->joff[P][j] = (uint16_t)swz(T.apply(sv));
+        if (p == npl - 1) out->jlog[l][j] = (uint16_t)sv;
       }
       if (l == L - 1 && p == npl - 1) {
         for (int i = 0; i < n; ++i) {

@@ -1,9 +1,11 @@
 // qp_selftest.cpp -- host-only check of the pass schedule.
 //
 // Emulates, lane by lane, what the circuit kernel does with the planner's tables: the fused
-// embedding in pass 0, load / gate / store through lane_addr ^ joff, CNOT rings folded into
-// the frame, and the readout through ro_mask / ro_sel with the Walsh transform. The result is
-// compared with a direct gate-by-gate simulation that applies every CNOT explicitly.
+// embedding in pass 0, load / gate / store through lane_addr ^ joff, CNOTs (ring or mesh)
+// folded into the frame, a diagonal phase per layer (the CRZ mesh ansatze) applied in the
+// layer's last pass by the logical indices klog ^ jlog, and the readout through ro_mask /
+// ro_sel with the Walsh transform. The result is compared with a direct gate-by-gate
+// simulation that applies every CNOT and every phase explicitly.
 // Also checks that every pass touches each amplitude of a point exactly once.
 #include <cmath>
 #include <complex>
@@ -45,6 +47,11 @@ extern "C" double qp_sched_selftest(int n, int L, int ansatz, unsigned seed) {
     double co = std::cos(0.5 * b), si = std::sin(0.5 * b);
     g = {ea * co, -std::conj(eb) * si, eb * si, std::conj(ea) * co};
   }
+  // diagonal phase of each layer (stands in for the CRZ mesh: any diagonal exercises the
+  // logical-index tables)
+  std::vector<double> dph((size_t)L * DIM);
+  for (auto& x : dph) x = U(rng);
+  const bool diag = qp_has_crz(ansatz);
   std::vector<std::vector<double>> theta(PPW, std::vector<double>(n));
   for (auto& t : theta)
     for (auto& x : t) x = U(rng);
@@ -97,6 +104,13 @@ extern "C" double qp_sched_selftest(int n, int L, int ansatz, unsigned seed) {
             r[j1] = u.c * x + u.d * y;
           }
         }
+        if (diag && p == S.npl - 1) {
+          for (int j = 0; j < AMPS; ++j) {
+            const int k = S.klog[l][lane] ^ S.jlog[l][j];
+            if (k < 0 || k >= DIM) return -2.0;
+            r[j] *= std::polar(1.0, dph[(size_t)l * DIM + k]);
+          }
+        }
         if (P == L * S.npl - 1) {
           std::vector<double> w(AMPS);
           for (int j = 0; j < AMPS; ++j) w[j] = std::norm(r[j]);
@@ -121,7 +135,17 @@ extern "C" double qp_sched_selftest(int n, int L, int ansatz, unsigned seed) {
     }
     for (int l = 0; l < L; ++l) {
       for (int q = 0; q < n; ++q) apply_direct(s, n, q, gates[l * n + q]);
-      if (ansatz != 3 && n > 1) {
+      if (diag) {
+        for (int k = 0; k < DIM; ++k) s[k] *= std::polar(1.0, dph[(size_t)l * DIM + k]);
+      } else if (ansatz == 6 && n > 1) {
+        for (int i = 0; i < n; ++i)
+          for (int j = 0; j < n; ++j) {
+            if (j == i) continue;
+            const int bc = 1 << (n - 1 - i), bt = 1 << (n - 1 - j);
+            for (int k = 0; k < DIM; ++k)
+              if ((k & bc) && !(k & bt)) std::swap(s[k], s[k | bt]);
+          }
+      } else if (ansatz != 3 && n > 1) {
         const int r = ansatz == 2 ? 1 + (l % (n - 1)) : 1;
         for (int i = 0; i < n; ++i) {
           const int bc = 1 << (n - 1 - i), bt = 1 << (n - 1 - (i + r) % n);

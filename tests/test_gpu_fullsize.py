@@ -9,7 +9,8 @@ never reach. The oracle's values come from tests/golden/make_fullsize.py (the or
 minutes to hours of CPU time); the inputs are regenerated here from their seeds and checked
 against the digests stored with those values.
 
-Bars (fp32 arithmetic against FP64): every loss term and energy slice within 1e-5 relative;
+Bars (fp32 arithmetic against FP64): every loss term within 1e-5 of the larger of itself and
+the total loss and within 1e-4 of itself, every energy slice within 1e-5 of itself;
 every gradient entry within 1e-5 of its block's largest oracle entry plus 1e-4 of its own
 value; fields and input derivatives at 256 sampled points within 1e-5 of their group's largest
 value, each channel within 1e-4 of its own.
@@ -69,7 +70,11 @@ def test_fullsize_loss_grad_fields_vs_oracle(name):
     assert loss.shape == lo.shape
     for i in range(lo.shape[0]):
         err = abs(loss[i] - lo[i])
-        assert err <= TOL * abs(lo[i]) or err < 1e-10, ("loss term", i, loss[i], lo[i])
+        if err < 1e-10:
+            continue
+        scale = max(abs(lo[i]), abs(lo[0])) if i < 9 else abs(lo[i])
+        assert err <= TOL * scale, ("loss term", i, loss[i], lo[i])
+        assert err <= CHAN_TOL * abs(lo[i]), ("loss term (own value)", i, loss[i], lo[i])
 
     idx = np.asarray(g["grad_idx"])
     go = np.asarray(g["grad"])

@@ -1,6 +1,7 @@
 """CPU-side checks of libqpinn.so: it loads, exports every function include/qpinn.h
 declares, and its host planner's pass schedule reproduces a direct statevector simulation
-when emulated lane by lane (addressing, CNOT frames, readout masks)."""
+when emulated lane by lane (addressing, CNOT frames of the ring and the all-pairs mesh, the
+per-layer diagonal of the CRZ mesh by logical index, readout masks)."""
 import os
 import re
 
@@ -35,7 +36,7 @@ def test_status_strings(qlib):
 
 
 @pytest.mark.parametrize("n", list(range(1, 11)))
-@pytest.mark.parametrize("ansatz", [0, 2, 3])
+@pytest.mark.parametrize("ansatz", [0, 2, 3, 4, 6])
 def test_schedule_emulation_matches_direct(qlib, n, ansatz):
     for L in (1, 3, 6):
         err = qlib.qp_sched_selftest(n, L, ansatz, 7 + n)
