@@ -260,6 +260,14 @@ int32_t qp_plan_path(const qp_plan* plan);
 typedef enum { QP_OPERANDS_FP16_PAIRS = 0, QP_OPERANDS_TF32_PAIRS = 1 } qp_operands;
 qp_status qp_plan_set_operands(qp_plan* plan, int32_t operands);
 
+/* Failure detection, for tests: every wait of the fused forward kernel's pipeline (the
+ * tensor-core loss path at n = 7, 8) gives up after `polls` polls of its mbarrier instead of
+ * the built-in bound (0 restores it). A wait that runs out stops the kernel cleanly: the waits
+ * that let its in-flight copies and MMAs finish keep the built-in bound, tensor memory is freed,
+ * and the call's status word reads QP_ERR_TIMEOUT (qp_last_device_error). The plan stays
+ * usable; the call's outputs are not meaningful. QP_ERR_INVALID_ARG for a null plan. */
+qp_status qp_set_wait_limit(qp_plan* plan, uint32_t polls);
+
 /* Optional profiling: two cudaEvent_t (passed as void*, created by the caller) that the
  * following compute calls record on their stream immediately before and after one measured
  * kernel, so its device time can be read with cudaEventElapsedTime. kernel selects it:

@@ -40,6 +40,7 @@ struct qp_plan {
   int32_t operands = QP_OPERANDS_FP16_PAIRS;   // forward contraction outside the fused kernel
   int64_t n_params = 0, circ_off = 0, head_off = 0, mlp_off = 0, mlp_count = 0, nfixed = 0;
   int32_t nE = 0;   // gate-gradient partial sums per block: 3 n L Pauli sums + L CRZ sums
+  uint32_t wait_limit = 0;   // pipeline-wait polls of the fused forward (0: the kernel's default)
   void* ws = nullptr;
   size_t ws_bytes = 0;
   int32_t last_launches = 0;
@@ -544,6 +545,12 @@ qp_status qp_plan_set_operands(qp_plan* plan, int32_t operands) {
   return QP_OK;
 }
 
+qp_status qp_set_wait_limit(qp_plan* plan, uint32_t polls) {
+  if (!plan) return QP_ERR_INVALID_ARG;
+  plan->wait_limit = polls;
+  return QP_OK;
+}
+
 qp_status qp_set_profile_events(qp_plan* plan, int32_t kernel, void* ev_start, void* ev_stop) {
   if (!plan || kernel < 0 || kernel > 2 || ((ev_start == nullptr) != (ev_stop == nullptr)))
     return QP_ERR_INVALID_ARG;
@@ -718,6 +725,7 @@ static qp_status dense_loss_grad(qp_plan* pl, const float* d_params, const float
     fa.nblk = pl->blocks_grad;
     fa.status = (int32_t*)(ws + w.status);
     fa.scal = (int32_t*)(ws + w.status) + 16;
+    fa.wait_limit = pl->wait_limit;
     const int64_t ftiles = fa.tile_end[2];
     const int fblocks = (int)(ftiles < pl->sm_count ? (ftiles > 0 ? ftiles : 1) : pl->sm_count);
     prof_mark(pl, 0, true, s);

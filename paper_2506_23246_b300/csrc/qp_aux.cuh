@@ -828,7 +828,7 @@ __global__ void reduce_kernel(ReduceArgs a) {
       const double tot = phys + ic + bc + en;
       a.loss[0] = tot; a.loss[1] = phys; a.loss[2] = ic; a.loss[3] = bc; a.loss[4] = en;
       a.loss[5] = m1v; a.loss[6] = m1d; a.loss[7] = m2; a.loss[8] = m3;
-      if (!isfinite(tot)) atomicExch(a.status, (int)5);
+      if (!isfinite(tot)) atomicCAS(a.status, 0, (int)5);   // an earlier error code stands
     }
   } else if (gw <= a.nparams + a.nt) {
     const int64_t i = gw - a.nparams - 1;

@@ -41,6 +41,8 @@ struct FusedArgs {
   int32_t* status;
   int32_t* scal;           // [2] float bits (atomic max): row bound of the product states, max |lambda|
   int32_t use_tma;         // 1: costates leave through tensor-map bulk stores (maps valid), 0: plain stores
+  uint32_t wait_limit;     // polls of the pipeline waits (0: QP_MBAR_LIMIT); the drain waits that
+                           // let in-flight copies and MMAs finish always keep QP_MBAR_LIMIT
 };
 
 // Tensor-map bulk store of one staged 128-row x 32-column chunk (bulk group of this thread).
@@ -174,6 +176,7 @@ __global__ void __launch_bounds__(F_THREADS, 1) dense_fused_fwd_kernel(FusedArgs
   bool ok = true;
   uint32_t it = 0;
   int64_t last_copy = -1, last_commit = -1;
+  const uint32_t lim = a.wait_limit ? a.wait_limit : QP_MBAR_LIMIT;
   const int64_t T2 = a.tile_end[2];
   const int64_t ntl = (int64_t)blockIdx.x < T2 ? (T2 - 1 - blockIdx.x) / gridDim.x + 1 : 0;
   const int64_t total = ntl * nkc;
@@ -191,9 +194,9 @@ __global__ void __launch_bounds__(F_THREADS, 1) dense_fused_fwd_kernel(FusedArgs
         for (int kc = 0; kc < nkc && ok; ++kc, ++it) {
           const uint32_t st = it & 1, wsl = it % 3;
           // the previous tile's epilogue must be done with tensor memory (and with W slot it - 1)
-          if (kc == 0 && t > 0) ok = qptc::mbar_wait(acc_free, (uint32_t)(t - 1) & 1);
-          if (ok) ok = qptc::mbar_wait(&w_full[wsl], (it / 3) & 1);
-          if (ok) ok = qptc::mbar_wait(&a_full[st], (it >> 1) & 1);
+          if (kc == 0 && t > 0) ok = qptc::mbar_wait(acc_free, (uint32_t)(t - 1) & 1, lim);
+          if (ok) ok = qptc::mbar_wait(&w_full[wsl], (it / 3) & 1, lim);
+          if (ok) ok = qptc::mbar_wait(&a_full[st], (it >> 1) & 1, lim);
           if (!ok) break;
           qptc::fence_after();
           const uint32_t sa = qptc::smem_u32(sm + st * 2 * L.a_bytes), sw = qptc::smem_u32(sm + L.wbase + wsl * L.w_bytes);
@@ -214,7 +217,7 @@ __global__ void __launch_bounds__(F_THREADS, 1) dense_fused_fwd_kernel(FusedArgs
           last_commit = it;
           if ((int64_t)it + 2 < total) {
             const uint32_t j = it + 2, js = j % 3;
-            if (it >= 1) ok = qptc::mbar_wait(&mma_done[(it - 1) & 1], ((it - 1) >> 1) & 1);
+            if (it >= 1) ok = qptc::mbar_wait(&mma_done[(it - 1) & 1], ((it - 1) >> 1) & 1, lim);
             if (!ok) break;
             // W slot js last held step it - 1 and, at a tile end, that tile's epilogue buffers:
             // copies into it are issued only after acc_free (above) for the first step of a tile
@@ -296,7 +299,7 @@ __global__ void __launch_bounds__(F_THREADS, 1) dense_fused_fwd_kernel(FusedArgs
     for (int kc = 0; kc < nkc; ++kc, ++it) {
       const uint32_t st = it & 1;
       unsigned char* sA = sm + st * 2 * L.a_bytes;
-      if (it >= 2 && ok) ok = qptc::mbar_wait(&mma_done[st], ((it - 2) >> 1) & 1);
+      if (it >= 2 && ok) ok = qptc::mbar_wait(&mma_done[st], ((it - 2) >> 1) & 1, lim);
       if (ok) {
 #pragma unroll
         for (int g = 0; g < 2; ++g) {
@@ -338,7 +341,7 @@ __global__ void __launch_bounds__(F_THREADS, 1) dense_fused_fwd_kernel(FusedArgs
       __syncwarp();
       if (lane == 0) qptc::mbar_arrive(&a_full[st]);
     }
-    ok = qptc::bar_and(3, F_STAGERS, ok && qptc::mbar_wait(&mma_done[(it - 1) & 1], ((it - 1) >> 1) & 1));
+    ok = qptc::bar_and(3, F_STAGERS, ok && qptc::mbar_wait(&mma_done[(it - 1) & 1], ((it - 1) >> 1) & 1, lim));
     if (!ok) break;
     qptc::fence_after();
     const float us = rsc[r];   // this thread's tensor-memory row: back to unscaled amplitudes

@@ -93,6 +93,8 @@ def lib():
         L.qp_plan_set_operands.restype = I32
         L.qp_bh_indicator.argtypes = [P, I32, ctypes.c_double, ctypes.c_double, P, P]
         L.qp_bh_indicator.restype = I32
+        L.qp_set_wait_limit.argtypes = [P, ctypes.c_uint32]
+        L.qp_set_wait_limit.restype = I32
         L.qp_set_profile_events.argtypes = [P, I32, P, P]
         L.qp_set_profile_events.restype = I32
         L.qp_sched_selftest.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_uint]
@@ -250,6 +252,10 @@ class Plan:
 
     def last_device_error(self):
         return lib().qp_last_device_error(self._h)
+
+    def set_wait_limit(self, polls):
+        """Test hook: bound the fused forward's pipeline waits to `polls` polls (0: default)."""
+        _check(lib().qp_set_wait_limit(self._h, int(polls)), "qp_set_wait_limit")
 
     def last_launch_count(self):
         return lib().qp_last_launch_count(self._h)

@@ -519,3 +519,32 @@ def test_cross_mesh_loss_grad(torch_cuda, oracle, n, L, path, ansatz):
             "bc": W.bc_points(16, n + 62)}
     params = W.init_params(circ, n + 63)
     _loss_grad_check(torch_cuda, oracle, circ, prob, params, sets, path=path)
+
+
+def test_wait_timeout_reported_and_plan_recovers(torch_cuda, oracle):
+    """Failure detection without a fault: with the fused forward's pipeline waits bounded to one
+    poll, a wait runs out, the kernel stops cleanly (in-flight copies and MMAs drained, tensor
+    memory freed) and the call reports QP_ERR_TIMEOUT. The same plan, with the bound restored,
+    then matches the oracle."""
+    from paper_2506_23246_b300 import qp
+    torch = torch_cuda
+    circ = W.c3_circuit(8, 6)
+    prob = W.c3_problem("vacuum", 4, 4, 2)
+    sets = {"colloc": W.grid_points(4, 4, 2, 1.5), "ic": W.ic_grid(4, 2)}
+    params = W.init_params(circ, 2)
+    plan = qp.Plan(circ, prob)
+    assert plan.path == "gemm_split"
+    dp = torch.tensor(params, device="cuda")
+    dsets = {k: torch.tensor(v, device="cuda") for k, v in sets.items()}
+    plan.set_wait_limit(1)
+    plan.loss_grad(dp, dsets)
+    assert plan.last_device_error() == 6
+    plan.set_wait_limit(0)
+    loss, grad = plan.loss_grad(dp, dsets)
+    assert plan.last_device_error() == 0
+    lo = oracle.loss(circ, prob, params, sets)
+    _loss_terms_check(loss.cpu().numpy(), lo)
+    lay = oracle.param_layout(circ)
+    idx = np.arange(lay["circuit"], lay["total"])
+    go = oracle.grad(circ, prob, params, sets, idx)
+    assert _rel(grad.cpu().numpy()[idx], go) < TOL
