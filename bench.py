@@ -46,10 +46,12 @@ def _args():
                     help="--workload configs: only this configuration")
     ap.add_argument("--grid", type=int, default=64,
                     help="--workload configs: C4 grid points per axis (64: the 64^3 grid)")
-    ap.add_argument("--workload", default="c3", choices=["c3", "c5", "configs"],
+    ap.add_argument("--workload", default="c3", choices=["c3", "c5", "configs", "paper_net"],
                     help="c3: the full QPINN step (default); c5: 32 uneven instances in one "
                          "batched call against the same instances called one by one; configs: "
-                         "one line per configuration (C1-C4) and compute path")
+                         "one line per configuration (C1-C4) and compute path; paper_net: the "
+                         "paper's hybrid network (7 qubits, 4 layers, RFF 128 + three tanh "
+                         "layers of 128) on the 40^3 and 87^3 grids of its timing table")
     return ap.parse_args()
 
 
@@ -257,8 +259,6 @@ def run_native(a):
     # tensor-core contractions (forward, weight gradient, back-projection mu)
     kinds = ["main"] if plan.path == "simt" else ["main", "wgrad", "mu"]
     kev = {k: (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for k in kinds}
-    for k in kinds:
-        plan.set_profile_events(*kev[k], kernel=k)
 
     # data parallelism: the union of the ranks' slabs is one loss; whole-loss normalisers are
     # gathered once (the points do not move), and each step sums loss terms and gradients
@@ -292,13 +292,23 @@ def run_native(a):
         ev0[i].record(stream)
         step()
         ev1[i].record(stream)
-        for k in kinds:
-            kev[k][1].synchronize()
-            kt[k].append(kev[k][0].elapsed_time(kev[k][1]))
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
     clocks = clk.stop()
+    # a second pass of the same steps with the library's profiling events around the measured
+    # kernels (kept out of the timed steps above)
+    for k in kinds:
+        plan.set_profile_events(*kev[k], kernel=k)
+    for i in range(a.steps):
+        flush.fill_(float(i))
+        step()
+        for k in kinds:
+            kev[k][1].synchronize()
+            kt[k].append(kev[k][0].elapsed_time(kev[k][1]))
+    for k in kinds:
+        plan.set_profile_events(None, None, kernel=k)
+    torch.cuda.synchronize()
     step_ms = [ev0[i].elapsed_time(ev1[i]) for i in range(a.steps)]
     ms = sum(step_ms) / a.steps
     if world > 1:
@@ -393,8 +403,6 @@ def run_native(a):
         t = torch.tensor([ems], device=dev)
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         ems = float(t.item())
-    for k in kinds:
-        plan.set_profile_events(None, None, kernel=k)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
@@ -619,6 +627,60 @@ def run_configs(a):
     return 0
 
 
+def run_paper_net(a):
+    """The paper's hybrid network (Sec. 2.2-2.3, Table 1: RFF with 128 frequencies, three tanh
+    layers of width 128, 7 angles, 7 qubits x 4 strongly entangling layers, head of 3) on the
+    grid sizes of its timing table (40^3 and 87^3 collocation points on [-1,1]^2 x [0,1.5],
+    vacuum, IC plane of the grid, energy term over the grid's time slices): one step is
+    qp_loss_grad (fields, input derivatives, losses, adjoint gradient of all 67,315 parameters).
+    The paper's numbers (TorQ, one training epoch with second-order autograd and Adam, A100 or
+    L40s) are context, not the same measurement."""
+    import torch
+    from paper_2506_23246_b300 import build, qp
+    from paper_2506_23246_b300 import workloads as W
+    build.build()
+    dev = torch.device("cuda", 0)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    paper = {40: 0.145136, 87: 0.849967}
+    for g in (40, 87):
+        circ = W.circuit(7, 4, 7, ansatz="strong_rot", enc="rx", scale="acos", premap="rff_mlp",
+                         rff_freqs=128, mlp_width=128, mlp_depth=3)
+        prob = W.problem("vacuum", w_energy=10.0, energy_slice=g * g, energy_nt=g)
+        sets = {"colloc": W.grid_points(g, g, g, 1.5), "ic": W.ic_grid(g, g)}
+        params = W.init_params(circ, 0)
+        plan = qp.Plan(circ, prob)
+        dp = torch.tensor(params, device=dev)
+        dsets = {k: torch.tensor(v, device=dev) for k, v in sets.items()}
+        plan.reserve(sum(v.shape[0] for v in dsets.values()), dev)
+        loss = torch.empty(9 + prob["energy_nt"], dtype=torch.float64, device=dev)
+        grad = torch.empty(plan.n_params, dtype=torch.float32, device=dev)
+        for _ in range(max(a.warmup, 3)):
+            plan.loss_grad(dp, dsets, out=(loss, grad))
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(a.steps)]
+        for i in range(a.steps):
+            flush.fill_(float(i))
+            ev[i][0].record(stream)
+            plan.loss_grad(dp, dsets, out=(loss, grad))
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+        assert plan.last_device_error() == 0
+        ms = sum(e0.elapsed_time(e1) for e0, e1 in ev) / a.steps
+        ncol = sets["colloc"].shape[0]
+        print(json.dumps({"workload": "paper hybrid net, %d^3 grid" % g, "n_params": plan.n_params,
+                          "path": plan.path, "colloc_points": ncol, "ic_points": sets["ic"].shape[0],
+                          "ms_per_step": ms, "colloc_pts_per_s": ncol / (ms / 1000.0),
+                          "steps": a.steps, "warmup": max(a.warmup, 3),
+                          "gpu_launches_per_step": plan.last_launch_count(),
+                          "paper_context": {"system": "TorQ, one training epoch (backprop, Adam), A100 or L40s",
+                                            "s_per_epoch": paper[g], "pts_per_s": ncol / paper[g]}}),
+              flush=True)
+        del plan
+        torch.cuda.empty_cache()
+    return 0
+
+
 def main():
     a = _args()
     if a.impl == "reference":
@@ -627,6 +689,8 @@ def main():
         return run_c5(a)
     if a.workload == "configs":
         return run_configs(a)
+    if a.workload == "paper_net":
+        return run_paper_net(a)
     return run_native(a)
 
 

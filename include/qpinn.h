@@ -109,9 +109,9 @@ typedef struct {
   int32_t scale;     /* qp_scale */
   int32_t premap;    /* qp_premap */
   int32_t n_direct;  /* DIRECT premap: inputs mapped to qubits 0..n_direct-1 (<= 3) */
-  int32_t rff_freqs; /* RFF_MLP: number of frequencies F (Omega is [F][3]) */
-  int32_t mlp_width; /* RFF_MLP: hidden width H */
-  int32_t mlp_depth; /* RFF_MLP: number of hidden tanh layers */
+  int32_t rff_freqs; /* RFF_MLP: number of frequencies F (Omega is [F][3]), 1..256 */
+  int32_t mlp_width; /* RFF_MLP: hidden width H, 1..1024 */
+  int32_t mlp_depth; /* RFF_MLP: number of hidden tanh layers, 0..8 */
 } qp_circuit;
 
 typedef struct {
@@ -291,7 +291,9 @@ qp_status qp_set_profile_events(qp_plan* plan, int32_t kernel, void* ev_start, v
  * It always runs the FP32 SIMT path (premap kernel without tensor cores, gate-by-gate circuit
  * kernel), whatever path and operand form the plan names: on a plan with the direct premap and
  * the SIMT path its results equal qp_forward's bit for bit; otherwise both agree with the FP64
- * oracle within the library's 1e-5 relative bar.
+ * oracle within the library's 1e-5 relative bar. Plans whose RFF + MLP premap is not one hidden
+ * layer of width 4, 8, 16, 32 or 64 are refused with QP_ERR_UNSUPPORTED (their premap keeps
+ * every layer's rows for all points).
  * Limit: B * n_qubits * 16 bytes plus about 13 KiB of tables (and L * 2^n * 8 bytes of the CRZ
  * mesh diagonal for the Cross-Mesh ansatze) must fit in 16 MiB (B <= 104,000 points at 10
  * qubits, 130,000 at 8); a larger B is rejected with QP_ERR_BUFFER_TOO_SMALL

@@ -19,6 +19,7 @@
 #include "qp_common.h"
 #include "qp_dense.cuh"
 #include "qp_fused.cuh"
+#include "qp_mlp.cuh"
 #include "qp_mu.cuh"
 #include "qp_wgrad.cuh"
 
@@ -37,6 +38,7 @@ struct qp_plan {
   int nwblk = 0, wtile = 0, smem_wgrad = 0, smem_premap = 0, smem_premap4 = 0;
   bool swc_big = false;   // the one-launch sweep runs as a 16-CTA cluster
   bool pg_ok = false;     // RFF + MLP premap with F = 64, H = 32: the GEMM-formulated kernels
+  bool deep = false;      // RFF + MLP premap of another depth or width: the layer-by-layer kernels
   int32_t operands = QP_OPERANDS_FP16_PAIRS;   // forward contraction outside the fused kernel
   int64_t n_params = 0, circ_off = 0, head_off = 0, mlp_off = 0, mlp_count = 0, nfixed = 0;
   int32_t nE = 0;   // gate-gradient partial sums per block: 3 n L Pauli sums + L CRZ sums
@@ -96,6 +98,7 @@ static cudaError_t raise_smem_limit(const void* fn, cudaFuncAttribute attr, int 
 
 struct WsLayout {
   size_t status, gates, cmat, cenc, crz, crz64, thetaJ, dthetaJ, d1, d2, u1, blk_loss, blk_grad, wpart;
+  size_t mact, mcot;   // layer-by-layer premap: hidden activations, two cotangent buffers
   size_t dW, dphi, dU, dG, dY, dpart, dWT, dmu, dW16, dcs, dgs, dgates, total;
 };
 
@@ -138,8 +141,16 @@ WgGeom wg_geom(const qp_plan* pl, int64_t nkc) {
 
 bool dense_path(const qp_plan* pl) { return pl->path == QP_PATH_GEMM_SPLIT; }
 
-// Kernels launched by launch_front: gate preparation, the CRZ mesh diagonal (CRZ ansatze), premap.
-int front_launches(const qp_plan* pl) { return qp_has_crz(pl->c.ansatz) ? 3 : 2; }
+// Kernels launched by launch_front: gate preparation, the CRZ mesh diagonal (CRZ ansatze), the
+// premap (one kernel, or one per layer).
+int front_launches(const qp_plan* pl) {
+  return (qp_has_crz(pl->c.ansatz) ? 2 : 1) + (pl->deep ? pl->c.mlp_depth + 1 : 1);
+}
+// Kernels of the premap backward: the fused per-point kernels (1 or 2), or layer by layer the
+// output layer, a weight gradient per layer and an input cotangent per hidden layer.
+int premap_bwd_launches(const qp_plan* pl) {
+  return pl->deep ? 1 + (pl->c.mlp_depth + 1) + pl->c.mlp_depth : (pl->pg_ok ? 1 : 2);
+}
 
 // The fused forward kernel keeps a tile's whole output row (2^(n+1) FP32 columns) in tensor
 // memory, which holds 512 columns: n = 7 and 8.
@@ -211,8 +222,13 @@ WsLayout ws_layout(const qp_plan* pl, int64_t P) {
   const int nt = pl->p.energy_nt;
   w.blk_loss = o; o = al256(o + (size_t)pl->blocks_grad * (QP_NLP + nt) * 8);
   w.blk_grad = o; o = al256(o + (size_t)pl->blocks_grad * (pl->nE + 3 * pl->c.n_readout + 3) * 4);
-  const int64_t nW = H ? (int64_t)H * 2 * pl->c.rff_freqs + H + (int64_t)n * H + n : 0;
+  const int64_t nW = H ? pl->mlp_count - pl->nfixed : 0;
   w.wpart = o; o = al256(o + (size_t)pl->nwblk * nW * 4);
+  // layer-by-layer premap: (y0, z_x, z_y, z_t) of every hidden layer, and two cotangent
+  // buffers of the widest layer
+  const int64_t mw = pl->deep ? (H > n ? H : n) : 0;
+  w.mact = o; o = al256(o + (pl->deep ? (size_t)pl->c.mlp_depth * P * 4 * H * 4 : 0));
+  w.mcot = o; o = al256(o + (size_t)2 * P * 4 * mw * 4);
   const size_t dim = (size_t)1 << n;
   const bool dn = dense_path(pl);
   w.dW = o; o = al256(o + (dn ? 2 * (2 * dim) * dim * 4 : 0));
@@ -301,11 +317,8 @@ qp_status validate(const qp_circuit* c, const qp_problem* p, int32_t path) {
     if (c->n_direct < 0 || c->n_direct > 3 || c->n_direct > c->n_qubits) return QP_ERR_INVALID_ARG;
   } else if (c->premap == QP_PREMAP_RFF_MLP) {
     if (c->rff_freqs < 1 || c->mlp_width < 1 || c->mlp_depth < 0) return QP_ERR_INVALID_ARG;
-    if (c->mlp_depth != 1) return QP_ERR_UNSUPPORTED;
-    const int H = c->mlp_width;
-    if (H != 4 && H != 8 && H != 16 && H != 32 && H != 64) return QP_ERR_UNSUPPORTED;
-    if (c->rff_freqs > QP_MAXF || (c->rff_freqs % 2) != 0) return QP_ERR_UNSUPPORTED;
-    if ((int64_t)H * 2 * c->rff_freqs > 16 * 4 * 256 || c->n_qubits * H > 4 * 256) return QP_ERR_UNSUPPORTED;
+    // any depth and width up to these bounds (the layer-by-layer kernels)
+    if (c->rff_freqs > QP_MAXF || c->mlp_width > 1024 || c->mlp_depth > 8) return QP_ERR_UNSUPPORTED;
   } else {
     return QP_ERR_INVALID_ARG;
   }
@@ -468,7 +481,11 @@ qp_status qp_plan_create(const qp_circuit* circuit, const qp_problem* problem, i
     pl->wtile = tile;
     pl->smem_wgrad = tile * (2 * F + 2 * H + n) * 16 + 3 * F * 4;
     pl->smem_premap4 = qpk::premap4_smem(F, H, n);
-    pl->pg_ok = F == qpk::PG_F && H == qpk::PG_H && n <= 16;
+    // one hidden layer of a width the fused per-point kernels take; otherwise layer by layer
+    const bool one_layer = circuit->mlp_depth == 1 && (H == 4 || H == 8 || H == 16 || H == 32 || H == 64) &&
+                           (F % 2) == 0 && (int64_t)H * 2 * F <= 16 * 4 * 256 && n * H <= 4 * 256;
+    pl->deep = !one_layer;
+    pl->pg_ok = one_layer && F == qpk::PG_F && H == qpk::PG_H && n <= 16;
     if (pl->pg_ok &&
         (raise_smem_limit((void*)qpk::premap_fwd_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                           qpk::pt_smem(n).total) != cudaSuccess ||
@@ -478,11 +495,12 @@ qp_status qp_plan_create(const qp_circuit* circuit, const qp_problem* problem, i
       delete pl;
       return QP_ERR_CUDA;
     }
-    if (raise_smem_limit(premap_fwd_ptr(H), cudaFuncAttributeMaxDynamicSharedMemorySize, pl->smem_premap) != cudaSuccess ||
+    if (!pl->deep &&
+        (raise_smem_limit(premap_fwd_ptr(H), cudaFuncAttributeMaxDynamicSharedMemorySize, pl->smem_premap) != cudaSuccess ||
         raise_smem_limit(premap_fwd4_ptr(H), cudaFuncAttributeMaxDynamicSharedMemorySize, pl->smem_premap4) != cudaSuccess ||
         raise_smem_limit(premap_bwd4_ptr(H), cudaFuncAttributeMaxDynamicSharedMemorySize, pl->smem_premap4) != cudaSuccess ||
         raise_smem_limit(premap_bwd_ptr(H), cudaFuncAttributeMaxDynamicSharedMemorySize, pl->smem_premap) != cudaSuccess ||
-        raise_smem_limit((void*)qpk::premap_wgrad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, pl->smem_wgrad) != cudaSuccess) {
+        raise_smem_limit((void*)qpk::premap_wgrad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, pl->smem_wgrad) != cudaSuccess)) {
       cudaGetLastError();
       delete pl;
       return QP_ERR_CUDA;
@@ -576,6 +594,110 @@ static void fill_problem(const qp_plan* pl, QPProblemDev& d) {
   d.colloc_off = pl->cur_colloc_off;
 }
 
+// MLP layer l of the layer-by-layer premap (0 .. depth - 1 hidden, depth the output layer):
+// input and output widths, offsets of its W [out][in] and b [out] after the Omega entries.
+static void mlp_layer_geom(const qp_plan* pl, int l, int& in, int& out, int64_t& w_off, int64_t& b_off) {
+  const int F = pl->c.rff_freqs, H = pl->c.mlp_width, D = pl->c.mlp_depth;
+  int64_t o = 0;
+  int fan = 2 * F;
+  for (int i = 0; i < l; ++i) { o += (int64_t)H * fan + H; fan = H; }
+  in = fan;
+  out = l == D ? pl->c.n_qubits : H;
+  w_off = o;
+  b_off = o + (int64_t)out * in;
+}
+
+static qpm::MlpArgs mlp_layer_args(const qp_plan* pl, const float* d_params, const float* const pts[3],
+                                   const int64_t npts[3], const WsLayout& w, int l) {
+  char* ws = (char*)pl->ws;
+  qpm::MlpArgs m;
+  std::memset(&m, 0, sizeof(m));
+  for (int i = 0; i < 3; ++i) { m.pts[i] = pts[i]; m.npts[i] = npts[i]; }
+  m.ptot = npts[0] + npts[1] + npts[2];
+  m.omega = d_params;
+  m.F = pl->c.rff_freqs;
+  int64_t wo, bo;
+  mlp_layer_geom(pl, l, m.in, m.out, wo, bo);
+  m.W = d_params + pl->nfixed + wo;
+  m.b = d_params + pl->nfixed + bo;
+  m.in_rff = l == 0 ? 1 : 0;
+  const int64_t lstride = m.ptot * 4 * pl->c.mlp_width;
+  m.act_in = l > 0 ? (const float*)(ws + w.mact) + (int64_t)(l - 1) * lstride : nullptr;
+  m.final_layer = l == pl->c.mlp_depth ? 1 : 0;
+  m.act_out = m.final_layer ? nullptr : (float*)(ws + w.mact) + (int64_t)l * lstride;
+  m.scale = pl->c.scale;
+  m.thetaJ = (float*)(ws + w.thetaJ);
+  m.hout = (float*)(ws + w.d2);
+  m.counts = (int32_t*)(ws + w.status) + 1;
+  m.medium = pl->p.medium;
+  m.disk_r = pl->p.disk_r; m.disk_x0 = pl->p.disk_x0; m.disk_y0 = pl->p.disk_y0;
+  return m;
+}
+
+static int mlp_grid(const qp_plan* pl, int64_t tiles) {
+  const int64_t cap = (int64_t)pl->sm_count * 4;
+  return (int)(tiles < 1 ? 1 : (tiles < cap ? tiles : cap));
+}
+
+// Forward of the layer-by-layer premap: every layer in turn, the output layer writes the
+// angles and their Jacobian (and counts the dielectric set).
+static qp_status launch_mlp_fwd(qp_plan* pl, const float* d_params, const float* const pts[3],
+                                const int64_t npts[3], const WsLayout& w, cudaStream_t s) {
+  const int64_t P = npts[0] + npts[1] + npts[2];
+  for (int l = 0; l <= pl->c.mlp_depth; ++l) {
+    const qpm::MlpArgs m = mlp_layer_args(pl, d_params, pts, npts, w, l);
+    const int64_t tiles = ((P + qpm::MT_P - 1) / qpm::MT_P) * ((m.out + qpm::MT_N - 1) / qpm::MT_N);
+    qpm::mlp_fwd_kernel<<<mlp_grid(pl, tiles), qpm::MT_THREADS, 0, s>>>(m);
+  }
+  return cuda_status(cudaGetLastError());
+}
+
+// Backward of the layer-by-layer premap from dL/dtheta, dL/dJ: the output layer's cotangents,
+// then per layer (last to first) its weight-gradient partials (one slot per row chunk) and
+// the cotangents of the previous layer.
+static qp_status launch_mlp_bwd(qp_plan* pl, const float* d_params, const float* const pts[3],
+                                const int64_t npts[3], const WsLayout& w, cudaStream_t s) {
+  char* ws = (char*)pl->ws;
+  const int64_t P = npts[0] + npts[1] + npts[2];
+  const int n = pl->c.n_qubits, D = pl->c.mlp_depth, H = pl->c.mlp_width;
+  const int64_t mw = H > n ? H : n;
+  float* cot[2] = {(float*)(ws + w.mcot), (float*)(ws + w.mcot) + P * 4 * mw};
+  int cur = 0;
+  {
+    const int64_t tot = P * n;
+    const int gb = mlp_grid(pl, (tot + 255) / 256);
+    qpm::mlp_bwd_out_kernel<<<gb, 256, 0, s>>>((const float*)(ws + w.d2), (const float*)(ws + w.dthetaJ), P, n,
+                                               pl->c.scale, cot[cur]);
+  }
+  const int64_t lstride = P * 4 * H;
+  for (int l = D; l >= 0; --l) {
+    qpm::MlpDwArgs da;
+    da.x = mlp_layer_args(pl, d_params, pts, npts, w, l);
+    int in, out;
+    mlp_layer_geom(pl, l, in, out, da.w_off, da.b_off);
+    da.cot = cot[cur];
+    da.part = (float*)(ws + w.wpart);
+    da.nW = pl->mlp_count - pl->nfixed;
+    da.nchunks = pl->nwblk;
+    const int nto = (out + qpm::MT_N - 1) / qpm::MT_N, nti = (in + qpm::MT_N - 1) / qpm::MT_N;
+    qpm::mlp_dw_kernel<<<dim3((unsigned)(nto * nti), (unsigned)pl->nwblk), qpm::MT_THREADS, 0, s>>>(da);
+    if (l > 0) {
+      qpm::MlpBwdArgs ba;
+      ba.ptot = P;
+      ba.W = da.x.W;
+      ba.in = in;
+      ba.out = out;
+      ba.cot = cot[cur];
+      ba.act_prev = (const float*)(ws + w.mact) + (int64_t)(l - 1) * lstride;
+      ba.cot_prev = cot[cur ^ 1];
+      const int64_t tiles = ((P + qpm::MT_P - 1) / qpm::MT_P) * ((in + qpm::MT_N - 1) / qpm::MT_N);
+      qpm::mlp_bwd_dx_kernel<<<mlp_grid(pl, tiles), qpm::MT_THREADS, 0, s>>>(ba);
+      cur ^= 1;
+    }
+  }
+  return cuda_status(cudaGetLastError());
+}
+
 // Shared prologue: gate preparation and premap forward for all point sets.
 static qp_status launch_front(qp_plan* pl, const float* d_params, const float* const pts[3],
                               const int64_t npts[3], const WsLayout& w, cudaStream_t s, bool grad) {
@@ -604,7 +726,9 @@ static qp_status launch_front(qp_plan* pl, const float* d_params, const float* c
   ma.counts = pa.counts; ma.medium = pl->p.medium; ma.status = pa.status;
   ma.disk_r = pl->p.disk_r; ma.disk_x0 = pl->p.disk_x0; ma.disk_y0 = pl->p.disk_y0;
   const int pblocks = (int)((ma.ptot + 127) / 128 < pl->sm_count * 8 ? (ma.ptot + 127) / 128 : pl->sm_count * 8);
-  if (pl->c.premap == QP_PREMAP_RFF_MLP && pl->pg_ok) {
+  if (pl->c.premap == QP_PREMAP_RFF_MLP && pl->deep) {
+    return launch_mlp_fwd(pl, d_params, pts, npts, w, s);
+  } else if (pl->c.premap == QP_PREMAP_RFF_MLP && pl->pg_ok) {
     // one tensor-core contraction per 128-point tile; the unit table is kept for the backward
     ma.u1 = grad ? (float*)(ws + w.u1) : nullptr;
     const int64_t nt = (ma.ptot + qpk::PT_M - 1) / qpk::PT_M;   // two CTAs per SM
@@ -918,7 +1042,7 @@ static qp_status dense_loss_grad(qp_plan* pl, const float* d_params, const float
     }
     st = launch_premap_bwd(pl, w, d_params, pts, npts, s);
     if (st != QP_OK) return st;
-    launches += pl->pg_ok ? 1 : 2;
+    launches += premap_bwd_launches(pl);
   }
   st = launch_reduce(pl, w, d_params, npts, d_loss, d_grad, mlp, s);
   pl->last_launches = launches + 1;
@@ -1076,7 +1200,7 @@ qp_status qp_loss_grad(qp_plan* pl, const float* d_params, const qp_batch* batch
   if (mlp) {
     qp_status stb = launch_premap_bwd(pl, w, d_params, pts, npts, s);
     if (stb != QP_OK) return stb;
-    launches += pl->pg_ok ? 1 : 2;
+    launches += premap_bwd_launches(pl);
   }
   qp_status st_red;
   st_red = launch_reduce(pl, w, d_params, npts, d_loss, d_grad, mlp, s);
@@ -1098,6 +1222,7 @@ static qp_status launch_premap_bwd(qp_plan* pl, const WsLayout& w, const float* 
   ma.thetaJ = (float*)(ws + w.thetaJ);
   ma.dthetaJ = (const float*)(ws + w.dthetaJ);
   ma.d1 = (float*)(ws + w.d1); ma.d2 = (float*)(ws + w.d2); ma.u1 = (float*)(ws + w.u1);
+  if (pl->deep) return launch_mlp_bwd(pl, d_params, pts, npts, w, s);
   if (pl->pg_ok) {
     // backward and weight-gradient partials in one pass (one partial slot per block)
     ma.status = (int32_t*)(ws + w.status);
@@ -1316,6 +1441,7 @@ extern "C" qp_status qp_forward_noalloc(qp_plan* pl, const float* d_params, cons
   const bool crz = qp_has_crz(pl->c.ansatz);
   const size_t off_theta = al256(off_crz + (crz ? (size_t)L * ((size_t)1 << n) * 8 : 0));
   if ((uint64_t)B > (kNoAllocScratchBytes - off_theta) / ((size_t)n * 16)) return QP_ERR_BUFFER_TOO_SMALL;
+  if (pl->deep) return QP_ERR_UNSUPPORTED;   // the layer-by-layer premap keeps per-layer rows
   cudaStream_t s = (cudaStream_t)stream;
   void* base = nullptr;
   qp_status st = noalloc_scratch_address(s, &base);

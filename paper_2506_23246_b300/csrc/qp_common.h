@@ -10,7 +10,7 @@
 #define QP_NLP 7        // loss partial sums: res1 vac, res1 diel, res2, res3, energy, ic, bc
 #define QP_NLOSS_OUT 9  // loss terms written before the energy slices (QP_NLOSS of qpinn.h)
 #define QP_MAXF 256     // RFF frequencies
-#define QP_MAXH 64      // MLP width on the GPU path
+#define QP_MAXH 64      // MLP width of the fused one-hidden-layer premap kernels
 
 // Geometry of one statevector per point group (compile-time per qubit count).
 //   LB   : qubits held in registers per lane ("local" qubits of a pass)

@@ -548,3 +548,55 @@ def test_wait_timeout_reported_and_plan_recovers(torch_cuda, oracle):
     idx = np.arange(lay["circuit"], lay["total"])
     go = oracle.grad(circ, prob, params, sets, idx)
     assert _rel(grad.cpu().numpy()[idx], go) < TOL
+
+
+# ----------------------------------------------------------------------------- deeper premaps
+
+def _mlp_sample(oracle, circ, k, seed):
+    """Gradient entries spread over every MLP layer's W and b, plus every circuit and head
+    parameter."""
+    off = W.param_offsets(circ)
+    rng = np.random.default_rng(seed)
+    idx = []
+    for name, (o, shape) in off.items():
+        if name in ("omega", "total", "circuit", "head_W", "head_b"):
+            continue
+        size = int(np.prod(shape))
+        idx.extend(o + rng.choice(size, min(k, size), replace=False))
+    lay = oracle.param_layout(circ)
+    return np.concatenate([np.sort(np.asarray(idx, dtype=np.int64)),
+                           np.arange(lay["circuit"], lay["total"])])
+
+
+@pytest.mark.parametrize("n,L,F,H,depth,path", [(4, 2, 8, 4, 0, "simt"), (5, 2, 8, 12, 2, "simt"),
+                                                (7, 2, 24, 40, 3, "simt"), (8, 3, 32, 48, 2, "gemm_split"),
+                                                (9, 2, 16, 24, 3, "gemm_split")])
+def test_deep_premap_loss_grad(torch_cuda, oracle, n, L, F, H, depth, path):
+    """RFF + tanh MLP premaps of other depths and widths (the layer-by-layer kernels): depth 0
+    (RFF straight into the output layer), widths that are not multiples of the 64-wide output
+    tiles, both statevector paths; loss terms and gradients spread over every layer."""
+    circ = W.circuit(n, L, n, ansatz="strong_rot", enc="rx", scale="acos", premap="rff_mlp",
+                     rff_freqs=F, mlp_width=H, mlp_depth=depth)
+    prob = W.problem("dielectric", disk_x0=0.2, disk_r=0.6, w_energy=10.0, energy_slice=16,
+                     energy_nt=2)
+    sets = {"colloc": W.uniform_points(41, n + 70, 1.0), "ic": W.ic_points_uniform(16, n + 71),
+            "bc": W.bc_points(16, n + 72)}
+    params = W.init_params(circ, n + 73)
+    idx = _mlp_sample(oracle, circ, 6, n)
+    _loss_grad_check(torch_cuda, oracle, circ, prob, params, sets, idx, path=path)
+
+
+def test_paper_hybrid_net_forward_and_grad(torch_cuda, oracle):
+    """The paper's hybrid network (Sec. 2.2-2.3, Table 1): RFF with 128 frequencies (256
+    features), three tanh layers of width 128, a linear layer to 7 angles, 7 qubits, 4 strongly
+    entangling layers, head to (Ez, Hx, Hy). Fields and input derivatives on a ragged batch,
+    then loss terms and gradients spread over all layers."""
+    circ = W.circuit(7, 4, 7, ansatz="strong_rot", enc="rx", scale="acos", premap="rff_mlp",
+                     rff_freqs=128, mlp_width=128, mlp_depth=3)
+    params = W.init_params(circ, 11)
+    pts = W.uniform_points(150, 12, 1.5)
+    _forward_check(torch_cuda, oracle, circ, params, pts)
+    prob = W.problem("vacuum", w_energy=10.0, energy_slice=8, energy_nt=2)
+    sets = {"colloc": W.uniform_points(24, 13, 1.5), "ic": W.ic_points_uniform(8, 14)}
+    idx = _mlp_sample(oracle, circ, 5, 7)
+    _loss_grad_check(torch_cuda, oracle, circ, prob, params, sets, idx)
