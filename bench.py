@@ -46,6 +46,9 @@ def _args():
                     help="--workload configs: only this configuration")
     ap.add_argument("--grid", type=int, default=64,
                     help="--workload configs: C4 grid points per axis (64: the 64^3 grid)")
+    ap.add_argument("--c3-grid", type=int, default=64,
+                    help="default workload: x and y points of the collocation grid (64: the benchmark "
+                         "step; smaller only for profiling captures)")
     ap.add_argument("--workload", default="c3", choices=["c3", "c5", "configs", "paper_net"],
                     help="c3: the full QPINN step (default); c5: 32 uneven instances in one "
                          "batched call against the same instances called one by one; configs: "
@@ -239,7 +242,7 @@ def run_native(a):
         build.build()
     if world > 1:
         torch.distributed.barrier()
-    circ, prob, params, sets = W.c3_workload(0)
+    circ, prob, params, sets = W.c3_workload(0, nx=a.c3_grid, ny=a.c3_grid)
     # weak scaling: every rank owns its own 64x64x16 slab of the time axis (independent points)
     if world > 1:
         sets = dict(sets)
