@@ -123,6 +123,11 @@ typedef struct {
   float w_ic, w_bc, w_energy; /* loss weights (Eq. 24 uses 10) */
   int32_t energy_slice;       /* collocation point p belongs to energy slice p/energy_slice */
   int32_t energy_nt;          /* number of energy slices U(t_k) reported (0 = none) */
+  int32_t phys_loss;          /* dielectric physics loss: 0 Eq. 13 (separate MSEs of res1 over the
+                                 vacuum and dielectric sets, 1/eps(x,y) pointwise), 1 the intuitive
+                                 form of Eqs. 34-35 (one MSE over all collocation points, eps = 1 or
+                                 eps_r by set) */
+  float w_sym;                /* weight of the symmetry penalty L_sym (Eq. 18; Eq. 24 uses 10), 0 = off */
 } qp_problem;
 
 /* Point sets of one loss evaluation (device pointers, float32 [n][3]). colloc points

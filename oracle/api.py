@@ -19,6 +19,7 @@ ENC = {"rx": 0, "ry": 1}
 SCALE = {"none": 0, "pi": 1, "bias": 2, "asin": 3, "acos": 4}
 PREMAP = {"direct": 0, "rff_mlp": 1}
 NLOSS = 9
+PHYS_LOSS = {"split": 0, "intuitive": 1}
 
 _P = ctypes.c_void_p
 _I64 = ctypes.c_int64
@@ -42,6 +43,8 @@ def lib():
         L.qpo_count_diel.restype = _I64
         L.qpo_count_diel.argtypes = [_P, _P, _P, _I64]
         L.qpo_loss_from_fields.argtypes = [_P, _P, _P, _I64, _P, _P, _P, _I64, _P, _P, _I64, _P, _P]
+        L.qpo_sym_from_fields.argtypes = [_P, _P, _I64, _P, _P, _P]
+        L.qpo_sym_from_fields.restype = ctypes.c_double
         _lib = L
     return _lib
 
@@ -64,11 +67,11 @@ def prob_arrays(prob, norm=None):
     nm = norm or {}
     pi = np.array([1 if prob["medium"] == "dielectric" else 0, prob.get("energy_slice", 0),
                    prob.get("energy_nt", 0), nm.get("n_colloc", 0), nm.get("n_ic", 0),
-                   nm.get("n_bc", 0), nm.get("n_diel", 0), nm.get("colloc_offset", 0)],
-                  dtype=np.int32)
+                   nm.get("n_bc", 0), nm.get("n_diel", 0), nm.get("colloc_offset", 0),
+                   PHYS_LOSS[prob.get("phys_loss", "split")]], dtype=np.int32)
     pd = np.array([prob["eps_r"], prob["disk_r"], prob["disk_x0"], prob["disk_y0"],
                    prob["sigmoid_w"], prob["ic_sigma"], prob["ic_x0"], prob["ic_y0"], prob["w_ic"],
-                   prob["w_bc"], prob["w_energy"]], dtype=np.float64)
+                   prob["w_bc"], prob["w_energy"], prob.get("w_sym", 0.0)], dtype=np.float64)
     return pi, pd
 
 
@@ -151,7 +154,7 @@ def loss(circ, prob, params, sets, norm=None, nthreads=None):
     pi, pd = prob_arrays(prob, norm)
     p = _f64(params)
     c, i, b = _sets(sets)
-    out = np.zeros(NLOSS + max(prob.get("energy_nt", 0), 0))
+    out = np.zeros(n_loss(prob))
     nt = nthreads or os.cpu_count() or 1
     if lib().qpo_loss(_ptr(ci), _ptr(pi), _ptr(pd), _ptr(p), _ptr(c), c.shape[0], _ptr(i),
                       i.shape[0], _ptr(b), b.shape[0], _ptr(out), nt) != 0:
@@ -185,11 +188,24 @@ def loss_from_fields(prob, colloc, fc, dfc, ic=None, fi=None, bc=None, fb=None):
     fi = np.zeros((0, 3)) if fi is None else _f64(fi).reshape(-1, 3)
     bc = np.zeros((0, 3)) if bc is None else _f64(bc).reshape(-1, 3)
     fb = np.zeros((0, 3)) if fb is None else _f64(fb).reshape(-1, 3)
-    out = np.zeros(NLOSS + max(prob.get("energy_nt", 0), 0))
+    out = np.zeros(n_loss(prob))
     lib().qpo_loss_from_fields(_ptr(pi), _ptr(pd), _ptr(c), c.shape[0], _ptr(fc), _ptr(dfc),
                                _ptr(ic), ic.shape[0], _ptr(fi), _ptr(bc), bc.shape[0], _ptr(fb),
                                _ptr(out))
     return out
+
+
+def sym_from_fields(prob, fc, fmx, fmy):
+    """w_sym L_sym (Eq. 18) from fields at the points, at (-x, y, t) and at (x, -y, t)."""
+    pi, pd = prob_arrays(prob)
+    fc, fmx, fmy = (_f64(a).reshape(-1, 3) for a in (fc, fmx, fmy))
+    return float(lib().qpo_sym_from_fields(_ptr(pi), _ptr(pd), fc.shape[0], _ptr(fc), _ptr(fmx), _ptr(fmy)))
+
+
+def n_loss(prob):
+    """Length of the loss-term array: the 9 terms, the energy slices, then w_sym L_sym when the
+    symmetry penalty is on."""
+    return NLOSS + max(prob.get("energy_nt", 0), 0) + (1 if prob.get("w_sym", 0.0) > 0 else 0)
 
 
 def count_dielectric(prob, pts):

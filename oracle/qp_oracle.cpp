@@ -46,8 +46,11 @@
 //   pi[3..7]  = sharding: whole-loss counts of the collocation, IC and BC sets (0 = this
 //               call's), whole-set points inside the disk, global index of the first
 //               collocation point (see Prob)
-//   pd[0..10] = eps_r, disk_r, disk_x0, disk_y0, sigmoid_w, ic_sigma, ic_x0, ic_y0,
-//               w_ic, w_bc, w_energy
+//   pi[8]     = physics loss of the dielectric case: 0 Eq. 13 (separate MSEs of res1 over the
+//               vacuum and dielectric sets, 1/eps(x,y) pointwise), 1 Eqs. 34-35 (one MSE of
+//               res1 over all collocation points, eps = 1 or eps_r by set)
+//   pd[0..11] = eps_r, disk_r, disk_x0, disk_y0, sigmoid_w, ic_sigma, ic_x0, ic_y0,
+//               w_ic, w_bc, w_energy, w_sym (weight of L_sym, Eq. 18; 0 = off)
 // Parameter layout (flat):
 //   premap RFF+MLP: Omega[F][3] (fixed, zero gradient), then per hidden layer
 //     W[H][in] (in = 2F first, H after), b[H]; then W_out[n][H], b_out[n]
@@ -184,15 +187,17 @@ struct Prob {
   // disk (norm_diel, read when norm_c > 0) and places its collocation points in the energy
   // slices of Eq. 31 from global index colloc_off on.
   int64_t norm_c, norm_i, norm_b, norm_diel, colloc_off;
-  double eps_r, disk_r, x0, y0, sw, ic_sigma, ic_x0, ic_y0, w_ic, w_bc, w_energy;
+  int phys_loss;
+  double eps_r, disk_r, x0, y0, sw, ic_sigma, ic_x0, ic_y0, w_ic, w_bc, w_energy, w_sym;
 };
 Prob read_prob(const int* pi, const double* pd) {
   Prob p;
   p.medium = pi[0]; p.slice = pi[1]; p.nt = pi[2];
   p.norm_c = pi[3]; p.norm_i = pi[4]; p.norm_b = pi[5]; p.norm_diel = pi[6]; p.colloc_off = pi[7];
+  p.phys_loss = pi[8];
   p.eps_r = pd[0]; p.disk_r = pd[1]; p.x0 = pd[2]; p.y0 = pd[3]; p.sw = pd[4];
   p.ic_sigma = pd[5]; p.ic_x0 = pd[6]; p.ic_y0 = pd[7];
-  p.w_ic = pd[8]; p.w_bc = pd[9]; p.w_energy = pd[10];
+  p.w_ic = pd[8]; p.w_bc = pd[9]; p.w_energy = pd[10]; p.w_sym = pd[11];
   return p;
 }
 
@@ -426,9 +431,30 @@ bool in_diel(const Prob& pb, double x, double y) {
 // Loss terms from fields. Fc: per collocation point [3] values (Ez,Hx,Hy) and
 // DFc [3][3] (c, d) input derivatives, as duals in p. Layout of out (values) and
 // outp (d/dp): see header comment of qpo_loss.
+// Symmetry penalty of Eq. 18 summed over the collocation points (before the 1/N of the mean):
+// Fmx = f(-x, y, t), Fmy = f(x, -y, t) per point; in the dielectric case the terms mirrored
+// along x are left out (the disk breaks that symmetry).
+D sym_sum(const Prob& pb, int64_t Bc, const std::vector<D>& Fc, const std::vector<D>& Fmx,
+          const std::vector<D>& Fmy) {
+  D s{0, 0};
+  for (int64_t b = 0; b < Bc; ++b) {
+    const D* f = &Fc[3 * b];
+    if (pb.medium == 0) {
+      const D* m = &Fmx[3 * b];   // (i) Ez even, (ii) Hx even, (iii) Hy odd in x
+      const D a = f[0] - m[0], c = f[1] - m[1], e = f[2] + m[2];
+      s = s + a * a + c * c + e * e;
+    }
+    const D* m = &Fmy[3 * b];     // (i) Ez even, (ii) Hx odd, (iii) Hy even in y
+    const D a = f[0] - m[0], c = f[1] + m[1], e = f[2] - m[2];
+    s = s + a * a + c * c + e * e;
+  }
+  return s;
+}
+
 void loss_terms(const Prob& pb, const double* pc, int64_t Bc, const std::vector<D>& Fc,
                 const std::vector<D>& DFc, const double* pi_, int64_t Bi, const std::vector<D>& Fi,
-                const double* pbnd, int64_t Bb, const std::vector<D>& Fb, double* out, double* outp) {
+                const double* pbnd, int64_t Bb, const std::vector<D>& Fb, double* out, double* outp,
+                const std::vector<D>& Fmx, const std::vector<D>& Fmy) {
   D s1v{0, 0}, s1d{0, 0}, s2{0, 0}, s3{0, 0}, se{0, 0};
   int64_t nd = 0;
   for (int64_t b = 0; b < Bc; ++b) nd += in_diel(pb, pc[3 * b], pc[3 * b + 1]) ? 1 : 0;
@@ -443,12 +469,15 @@ void loss_terms(const Prob& pb, const double* pc, int64_t Bc, const std::vector<
     const D* f = &Fc[3 * b];
     const D* Df = &DFc[9 * b];  // Df[c*3+d]
     auto dd = [&](int cc, int d) { return Df[cc * 3 + d]; };
-    // Eq. 8 / 9 (1/eps pointwise in the dielectric case), Eq. 10a-b.
+    // Eq. 8 / 9 (1/eps pointwise in the dielectric case), Eq. 10a-b; the intuitive form
+    // (Eq. 34) takes eps = eps_r on the dielectric set and 1 elsewhere, in one MSE
     D curl = dd(2, 0) - dd(1, 1);
-    D r1 = dd(0, 2) - (1.0 / eps) * curl;
+    const bool intuitive = pb.medium == 1 && pb.phys_loss == 1;
+    const double e1 = intuitive ? (in_diel(pb, x, y) ? pb.eps_r : 1.0) : eps;
+    D r1 = dd(0, 2) - (1.0 / e1) * curl;
     D r2 = dd(1, 2) + dd(0, 1);
     D r3 = dd(2, 2) - dd(0, 0);
-    if (pb.medium == 1 && in_diel(pb, x, y)) s1d = s1d + r1 * r1;
+    if (pb.medium == 1 && !intuitive && in_diel(pb, x, y)) s1d = s1d + r1 * r1;
     else s1v = s1v + r1 * r1;
     s2 = s2 + r2 * r2;
     s3 = s3 + r3 * r3;
@@ -462,7 +491,9 @@ void loss_terms(const Prob& pb, const double* pc, int64_t Bc, const std::vector<
     }
   }
   D mse1v{0, 0}, mse1d{0, 0};
-  if (pb.medium == 1) {
+  if (pb.medium == 1 && pb.phys_loss == 1) {
+    if (Nc > 0) mse1v = (1.0 / Nc) * s1v;   // Eq. 35: all collocation points weigh the same
+  } else if (pb.medium == 1) {
     if (nv > 0) mse1v = (1.0 / nv) * s1v;
     if (nd > 0) mse1d = (1.0 / nd) * s1d;
   } else if (Nc > 0) {
@@ -485,13 +516,17 @@ void loss_terms(const Prob& pb, const double* pc, int64_t Bc, const std::vector<
   D sbc{0, 0};
   for (int64_t b = 0; b < Bb; ++b) sbc = sbc + Fb[3 * b] * Fb[3 * b];
   D bc = Nb > 0 ? (pb.w_bc / Nb) * sbc : D{0, 0};
-  D tot = phys + ic + bc + energy;
+  // Eq. 18 weighted as in Eq. 24, a mean over the collocation points
+  D sym{0, 0};
+  if (pb.w_sym > 0 && Nc > 0 && (int64_t)Fmy.size() == 3 * Bc) sym = (pb.w_sym / Nc) * sym_sum(pb, Bc, Fc, Fmx, Fmy);
+  D tot = phys + ic + bc + energy + sym;
   D terms[9] = {tot, phys, ic, bc, energy, mse1v, mse1d, mse2, mse3};
   for (int i = 0; i < 9; ++i) {
     out[i] = terms[i].v;
     if (outp) outp[i] = terms[i].p;
   }
   for (int k = 0; k < pb.nt; ++k) out[9 + k] = U[k];
+  if (pb.w_sym > 0) out[9 + (pb.nt > 0 ? pb.nt : 0)] = sym.v;
 }
 
 template <class F>
@@ -526,6 +561,19 @@ void eval_loss(const Circ& c, const Prob& pb, const double* params, int64_t sel,
                double* outp, int nthreads) {
   std::vector<R> P = make_params(c, params, sel);
   std::vector<D> Fc(3 * Bc), DFc(9 * Bc), Fi(3 * Bi), Fb(3 * Bb);
+  // L_sym (Eq. 18): the fields at the mirrored points (-x, y, t) and (x, -y, t)
+  const bool sym = pb.w_sym > 0;
+  std::vector<D> Fmx(sym ? 3 * Bc : 0), Fmy(sym ? 3 * Bc : 0);
+  if (sym) {
+    parallel_for(2 * Bc, nthreads, [&](int64_t q) {
+      const int64_t b = q % Bc;
+      const bool mx = q < Bc;
+      const double pt[3] = {mx ? -pc[3 * b] : pc[3 * b], mx ? pc[3 * b + 1] : -pc[3 * b + 1], pc[3 * b + 2]};
+      R f[3];
+      eval_point(c, P.data(), pt, f);
+      to_duals(f, mx ? &Fmx[3 * b] : &Fmy[3 * b], nullptr);
+    });
+  }
   parallel_for(Bc + Bi + Bb, nthreads, [&](int64_t q) {
     R f[3];
     if (q < Bc) {
@@ -541,7 +589,7 @@ void eval_loss(const Circ& c, const Prob& pb, const double* params, int64_t sel,
       to_duals(f, &Fb[3 * b], nullptr);
     }
   });
-  loss_terms(pb, pc, Bc, Fc, DFc, pi_, Bi, Fi, pbnd, Bb, Fb, out, outp);
+  loss_terms(pb, pc, Bc, Fc, DFc, pi_, Bi, Fi, pbnd, Bb, Fb, out, outp, Fmx, Fmy);
 }
 
 }  // namespace
@@ -664,7 +712,7 @@ int qpo_grad(const int* ci, const int* pi, const double* pd, const double* param
   const bool outer = nidx >= nthreads;
   parallel_for(nidx, outer ? nthreads : 1, [&](int64_t i) {
     if (idx[i] < nfixed) { grad[i] = 0.0; return; }
-    std::vector<double> out(9 + (pb.nt > 0 ? pb.nt : 0)), outp(9);
+    std::vector<double> out(10 + (pb.nt > 0 ? pb.nt : 0)), outp(9);
     eval_loss(c, pb, params, idx[i], pc, Bc, pi_, Bi, pbnd, Bb, out.data(), outp.data(),
               outer ? 1 : nthreads);
     grad[i] = outp[0];
@@ -693,8 +741,19 @@ int qpo_loss_from_fields(const int* pi, const double* pd, const double* pc, int6
   for (int64_t i = 0; i < 9 * Bc; ++i) DFc[i] = {dfc[i], 0};
   for (int64_t i = 0; i < 3 * Bi; ++i) Fi[i] = {fi[i], 0};
   for (int64_t i = 0; i < 3 * Bb; ++i) Fb[i] = {fb[i], 0};
-  loss_terms(pb, pc, Bc, Fc, DFc, pi_, Bi, Fi, pbnd, Bb, Fb, out, nullptr);
+  loss_terms(pb, pc, Bc, Fc, DFc, pi_, Bi, Fi, pbnd, Bb, Fb, out, nullptr, {}, {});
   return 0;
+}
+
+// w_sym L_sym (Eq. 18 as weighted in Eq. 24) from given fields: f_c, f(-x,y,t), f(x,-y,t), each
+// [Bc][3]; the mean runs over Bc points (or the sharding count).
+double qpo_sym_from_fields(const int* pi, const double* pd, int64_t Bc, const double* fc, const double* fmx,
+                           const double* fmy) {
+  Prob pb = read_prob(pi, pd);
+  std::vector<D> Fc(3 * Bc), Fmx(3 * Bc), Fmy(3 * Bc);
+  for (int64_t i = 0; i < 3 * Bc; ++i) { Fc[i] = {fc[i], 0}; Fmx[i] = {fmx[i], 0}; Fmy[i] = {fmy[i], 0}; }
+  const int64_t Nc = pb.norm_c > 0 ? pb.norm_c : Bc;
+  return Nc > 0 ? pb.w_sym / Nc * sym_sum(pb, Bc, Fc, Fmx, Fmy).v : 0.0;
 }
 
 }  // extern "C"

@@ -323,6 +323,7 @@ qp_status validate(const qp_circuit* c, const qp_problem* p, int32_t path) {
     return QP_ERR_INVALID_ARG;
   }
   if (p->medium != QP_MEDIUM_VACUUM && p->medium != QP_MEDIUM_DIELECTRIC) return QP_ERR_INVALID_ARG;
+  if (p->phys_loss < 0 || p->phys_loss > 1 || !(p->w_sym >= 0.f)) return QP_ERR_INVALID_ARG;
   if (p->energy_nt < 0 || p->energy_nt > QP_MAXNT || p->energy_slice < 0) return QP_ERR_INVALID_ARG;
   if (p->medium == QP_MEDIUM_DIELECTRIC && !(p->sigmoid_w > 0.f)) return QP_ERR_INVALID_ARG;
   if (!(p->ic_sigma > 0.f)) return QP_ERR_INVALID_ARG;
@@ -589,6 +590,7 @@ static void fill_problem(const qp_plan* pl, QPProblemDev& d) {
   d.disk_y0 = p.disk_y0; d.sigmoid_w = p.sigmoid_w; d.ic_sigma = p.ic_sigma; d.ic_x0 = p.ic_x0;
   d.ic_y0 = p.ic_y0; d.w_ic = p.w_ic; d.w_bc = p.w_bc; d.w_energy = p.w_energy;
   d.energy_slice = p.energy_slice; d.energy_nt = p.energy_nt;
+  d.phys_loss = p.phys_loss; d.w_sym = p.w_sym;
   for (int i = 0; i < 3; ++i) d.norm[i] = pl->cur_norm[i];
   d.norm_diel = pl->cur_norm_diel;
   d.colloc_off = pl->cur_colloc_off;
@@ -1272,7 +1274,7 @@ static qp_status launch_reduce(qp_plan* pl, const WsLayout& w, const float* d_pa
   ra.mlp_off = pl->nfixed; ra.mlp_count = pl->mlp_count - pl->nfixed;
   ra.n = pl->c.n_qubits; ra.L = pl->c.n_layers; ra.m = pl->c.n_readout;
   ra.k = qp_ansatz_k(pl->c.ansatz);
-  ra.nt = pl->p.energy_nt; ra.medium = pl->p.medium;
+  ra.nt = pl->p.energy_nt; ra.medium = pl->p.medium; ra.phys_loss = pl->p.phys_loss;
   ra.nc = pl->cur_norm[0] > 0 ? pl->cur_norm[0] : npts[0];
   ra.ni = pl->cur_norm[1] > 0 ? pl->cur_norm[1] : npts[1];
   ra.nb = pl->cur_norm[2] > 0 ? pl->cur_norm[2] : npts[2];

@@ -736,7 +736,7 @@ struct ReduceArgs {
   double* loss;
   float* grad;
   int64_t nparams, circ_off, head_off, mlp_off, mlp_count;
-  int32_t n, L, m, k, nt, medium, ansatz;
+  int32_t n, L, m, k, nt, medium, ansatz, phys_loss;
   int32_t nE;                  // gate-gradient partial sums per block (head partials follow)
   int64_t nc, ni, nb;          // mean denominators of the three sets
   int64_t norm_diel;           // whole-set points inside the disk, or -1: the counted ones
@@ -814,7 +814,9 @@ __global__ void reduce_kernel(ReduceArgs a) {
       const double nd = a.medium == 1 ? (a.norm_diel >= 0 ? (double)a.norm_diel : (double)a.counts[0]) : 0.0;
       const double nv = N - nd;
       double m1v = 0, m1d = 0;
-      if (a.medium == 1) {
+      if (a.medium == 1 && a.phys_loss == 1) {
+        if (N > 0) m1v = s[0] / N;   // Eq. 35: one MSE over all collocation points
+      } else if (a.medium == 1) {
         if (nv > 0) m1v = s[0] / nv;
         if (nd > 0) m1d = s[1] / nd;
       } else if (N > 0) {

@@ -145,7 +145,9 @@ __device__ __forceinline__ void point_loss_terms(const QPProblemDev& pb, int set
       const float rr = sqrtf(r2);
       eps = 1.f + (pb.eps_r - 1.f) / (1.f + expf(-(pb.disk_r - rr) / pb.sigmoid_w));
     }
-    const float ie = 1.f / eps;
+    // Eq. 34 (intuitive form): eps = eps_r on the dielectric set, 1 elsewhere, one MSE
+    const bool intuitive = pb.medium == 1 && pb.phys_loss == 1;
+    const float ie = intuitive ? (diel ? 1.f / pb.eps_r : 1.f) : 1.f / eps;
     const float res1 = D[0][2] - ie * (D[2][0] - D[1][1]);
     const float res2 = D[1][2] + D[0][1];
     const float res3 = D[2][2] - D[0][0];
@@ -153,7 +155,7 @@ __device__ __forceinline__ void point_loss_terms(const QPProblemDev& pb, int set
                     (D[0][0] * f[2] + f[0] * D[2][0]) + (D[0][1] * f[1] + f[0] * D[1][1]);
     const float N = (float)(pb.norm[0] > 0 ? pb.norm[0] : npt);
     float N1 = N;
-    if (pb.medium == 1) {
+    if (pb.medium == 1 && !intuitive) {
       const float nd = (float)(pb.norm[0] > 0 ? pb.norm_diel : counts[0]);
       N1 = diel ? nd : N - nd;
     }
@@ -170,8 +172,8 @@ __device__ __forceinline__ void point_loss_terms(const QPProblemDev& pb, int set
     gD[2][0] = -k1 * ie - kE * f[0];
     gD[2][2] = k3 + kE * f[2];
     const float r1sq = res1 * res1;
-    lt[0] = diel ? 0.f : r1sq;
-    lt[1] = diel ? r1sq : 0.f;
+    lt[0] = diel && !intuitive ? 0.f : r1sq;
+    lt[1] = diel && !intuitive ? r1sq : 0.f;
     lt[2] = res2 * res2;
     lt[3] = res3 * res3;
     lt[4] = e * e;

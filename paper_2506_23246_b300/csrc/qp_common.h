@@ -96,6 +96,8 @@ struct QPProblemDev {
   float eps_r, disk_r, disk_x0, disk_y0, sigmoid_w;
   float ic_sigma, ic_x0, ic_y0, w_ic, w_bc, w_energy;
   int32_t energy_slice, energy_nt;
+  int32_t phys_loss;   // 0: Eq. 13, 1: Eqs. 34-35 (dielectric case)
+  float w_sym;         // weight of L_sym (Eq. 18), 0 = off
   // sharding of one loss over several calls: whole-loss counts of the collocation, IC and BC
   // sets (0: this call's), whole-set points inside the disk (read when norm[0] > 0), global
   // index of this call's first collocation point (energy slices)

@@ -20,6 +20,7 @@ PREMAP = {"direct": 0, "rff_mlp": 1}
 PATH = {"auto": 0, "simt": 1, "gemm_split": 2, "gemm_bf16x3": 3}
 OPERANDS = {"fp16_pairs": 0, "tf32_pairs": 1}
 NLOSS = 9
+PHYS_LOSS = {"split": 0, "intuitive": 1}
 STATUS = {0: "ok", 1: "invalid argument", 2: "unsupported configuration",
           3: "workspace missing or too small", 4: "CUDA error", 5: "non-finite loss",
           6: "device wait timed out", 7: "internal error"}
@@ -41,7 +42,8 @@ class QPProblem(ctypes.Structure):
     _fields_ = [("medium", ctypes.c_int32)] + [(k, ctypes.c_float) for k in (
         "eps_r", "disk_r", "disk_x0", "disk_y0", "sigmoid_w", "ic_sigma", "ic_x0", "ic_y0",
         "w_ic", "w_bc", "w_energy")] + [("energy_slice", ctypes.c_int32),
-                                        ("energy_nt", ctypes.c_int32)]
+                                        ("energy_nt", ctypes.c_int32),
+                                        ("phys_loss", ctypes.c_int32), ("w_sym", ctypes.c_float)]
 
 
 class QPBatch(ctypes.Structure):
@@ -123,7 +125,8 @@ def make_problem(p):
     return QPProblem(1 if p["medium"] == "dielectric" else 0, p["eps_r"], p["disk_r"],
                      p["disk_x0"], p["disk_y0"], p["sigmoid_w"], p["ic_sigma"], p["ic_x0"],
                      p["ic_y0"], p["w_ic"], p["w_bc"], p["w_energy"], p.get("energy_slice", 0),
-                     p.get("energy_nt", 0))
+                     p.get("energy_nt", 0), PHYS_LOSS[p.get("phys_loss", "split")],
+                     float(p.get("w_sym", 0.0)))
 
 
 def _ptr(t):

@@ -27,11 +27,18 @@ def circuit(n_qubits, n_layers, n_readout=None, ansatz="strong_rot", enc="rx", s
 
 def problem(medium="vacuum", eps_r=4.0, disk_r=0.25, disk_x0=0.5, disk_y0=0.0, sigmoid_w=0.02,
             ic_sigma=math.sqrt(1.0 / 50.0), ic_x0=0.0, ic_y0=0.0, w_ic=10.0, w_bc=10.0,
-            w_energy=10.0, energy_slice=0, energy_nt=0):
-    return {"medium": medium, "eps_r": eps_r, "disk_r": disk_r, "disk_x0": disk_x0,
-            "disk_y0": disk_y0, "sigmoid_w": sigmoid_w, "ic_sigma": ic_sigma, "ic_x0": ic_x0,
-            "ic_y0": ic_y0, "w_ic": w_ic, "w_bc": w_bc, "w_energy": w_energy,
-            "energy_slice": energy_slice, "energy_nt": energy_nt}
+            w_energy=10.0, energy_slice=0, energy_nt=0, phys_loss="split", w_sym=0.0):
+    """phys_loss: "split" (Eq. 13: separate MSEs of res1 over the vacuum and dielectric sets) or
+    "intuitive" (Eqs. 34-35); w_sym: weight of the symmetry penalty L_sym (Eq. 18), 0 = off."""
+    p = {"medium": medium, "eps_r": eps_r, "disk_r": disk_r, "disk_x0": disk_x0,
+         "disk_y0": disk_y0, "sigmoid_w": sigmoid_w, "ic_sigma": ic_sigma, "ic_x0": ic_x0,
+         "ic_y0": ic_y0, "w_ic": w_ic, "w_bc": w_bc, "w_energy": w_energy,
+         "energy_slice": energy_slice, "energy_nt": energy_nt}
+    if phys_loss != "split":
+        p["phys_loss"] = phys_loss
+    if w_sym:
+        p["w_sym"] = w_sym
+    return p
 
 
 def c1_circuit():

@@ -600,3 +600,21 @@ def test_paper_hybrid_net_forward_and_grad(torch_cuda, oracle):
     sets = {"colloc": W.uniform_points(24, 13, 1.5), "ic": W.ic_points_uniform(8, 14)}
     idx = _mlp_sample(oracle, circ, 5, 7)
     _loss_grad_check(torch_cuda, oracle, circ, prob, params, sets, idx)
+
+
+# ----------------------------------------------------------------------------- paper loss variants
+
+@pytest.mark.parametrize("n,path", [(5, "simt"), (8, "gemm_split"), (10, "gemm_split")])
+def test_intuitive_dielectric_loss_grad(torch_cuda, oracle, n, path):
+    """The intuitive dielectric physics loss (Eqs. 34-35): one MSE of res1 over all collocation
+    points with eps = eps_r on the dielectric set; loss terms and every circuit and head
+    parameter against the oracle on both paths."""
+    circ = W.circuit(n, 2, n, ansatz="strong_rot", enc="rx", scale="acos", premap="rff_mlp",
+                     rff_freqs=8, mlp_width=8, mlp_depth=1)
+    prob = W.problem("dielectric", disk_x0=0.2, disk_r=0.6, w_energy=10.0, energy_slice=16,
+                     energy_nt=2, phys_loss="intuitive")
+    sets = {"colloc": W.uniform_points(48, n + 80, 1.0), "ic": W.ic_points_uniform(16, n + 81)}
+    params = W.init_params(circ, n + 82)
+    lay = oracle.param_layout(circ)
+    idx = np.concatenate([np.arange(lay["fixed"], lay["fixed"] + 24), np.arange(lay["circuit"], lay["total"])])
+    _loss_grad_check(torch_cuda, oracle, circ, prob, params, sets, idx, path=path)

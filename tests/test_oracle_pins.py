@@ -753,3 +753,106 @@ def test_crz_gradient_exact_shift_rule(oracle):
             return oracle.loss(circ, prob, pp, sets)[0]
         want = 0.5 * _shift_rule(fn, params[i] / 2.0, 8)
         assert abs(want - g[j]) < 1e-10 * max(1.0, abs(g[j])), (i, want, g[j])
+
+
+# ----------------------------------------------------------------------------- intuitive loss
+
+def _plane_wave_fields(pts, k, w):
+    """Ez = cos(kx - w t), Hx = 0, Hy = -(k/w) cos(kx - w t) with w given per point: it solves
+    the TM system (Eqs. 8-10) in a medium of permittivity k^2 / w^2."""
+    ph = k * pts[:, 0] - w * pts[:, 2]
+    a = -k / w
+    f = np.stack([np.cos(ph), np.zeros_like(ph), a * np.cos(ph)], axis=1)
+    df = np.zeros((pts.shape[0], 3, 3))
+    df[:, 0, 0] = -k * np.sin(ph)
+    df[:, 0, 2] = w * np.sin(ph)
+    df[:, 2, 0] = -a * k * np.sin(ph)
+    df[:, 2, 2] = a * w * np.sin(ph)
+    return f, df, ph
+
+
+def test_intuitive_dielectric_loss(oracle):
+    """Eqs. 34-35: res1 with eps = eps_r on the dielectric set and 1 elsewhere, one MSE over all
+    collocation points. A plane wave whose speed is 1/sqrt(eps) of each point's own region
+    makes it vanish (and res2, res3), while Eq. 13's smooth eps(x, y) does not; with the
+    vacuum speed everywhere, res1 = k (1 - 1/eps_r) sin(kx - wt) on the dielectric set only."""
+    prob = W.problem("dielectric", disk_x0=0.2, disk_r=0.5, w_energy=0.0, phys_loss="intuitive")
+    split = W.problem("dielectric", disk_x0=0.2, disk_r=0.5, w_energy=0.0)
+    pts = W.uniform_points(400, 21).astype(np.float64)
+    inside = ((pts[:, 0].astype(np.float32) - np.float32(0.2)) ** 2 +
+              pts[:, 1].astype(np.float32) ** 2) < np.float32(0.5) ** 2
+    assert 20 < inside.sum() < 380
+    k, er = 2.0, prob["eps_r"]
+    f, df, _ = _plane_wave_fields(pts, k, np.where(inside, k / math.sqrt(er), k))
+    out = oracle.loss_from_fields(prob, pts, f, df)
+    assert abs(out[5]) < 1e-13 and out[6] == 0.0 and abs(out[7]) < 1e-15 and abs(out[8]) < 1e-13
+    assert abs(out[1]) < 1e-12
+    assert oracle.loss_from_fields(split, pts, f, df)[1] > 1e-3
+    f, df, ph = _plane_wave_fields(pts, k, np.full(pts.shape[0], k))
+    out = oracle.loss_from_fields(prob, pts, f, df)
+    m = np.mean(np.where(inside, (k * (1 - 1 / er) * np.sin(ph)) ** 2, 0.0))
+    assert abs(out[5] - m) < 1e-13 and out[6] == 0.0 and abs(out[1] - m) < 1e-12
+
+
+# ----------------------------------------------------------------------------- symmetry penalty
+
+@pytest.mark.parametrize("medium", ["vacuum", "dielectric"])
+def test_sym_penalty_closed_form(oracle, medium):
+    """Eq. 18 on a circuit whose outputs have known parities: one qubit per input, RX(pi v_j),
+    no ansatz layer, so z_0 = cos(pi x), z_1 = cos(pi y), z_2 = cos(pi t) are all even in x and
+    y. Ez = z_0 + z_1 satisfies (i), so with Hx = Hy = 0 the penalty is 0. Hx = z_0 breaks the
+    odd-in-y parity of (ii): (Hx + Hx(x,-y))^2 = 4 cos^2(pi x). Hy = z_1 breaks the odd-in-x
+    parity of (iii): 4 cos^2(pi y), a term the dielectric case leaves out."""
+    circ = W.circuit(3, 0, 3, ansatz="noent_rot", enc="rx", scale="pi", premap="direct", n_direct=3)
+    prob = W.problem(medium, disk_x0=0.5, disk_r=0.25, w_ic=0.0, w_bc=0.0, w_energy=0.0, w_sym=10.0)
+    pts = W.uniform_points(40, 6).astype(np.float64)
+    off = W.param_offsets(circ)
+    o, _ = off["head_W"]
+    p = np.zeros(off["total"][0])
+    p[o + 0] = p[o + 1] = 1.0                      # Ez = z_0 + z_1
+    lo = oracle.loss(circ, prob, p, {"colloc": pts})
+    assert abs(lo[-1]) < 1e-14
+    p[o + 3] = 1.0                                  # Hx = z_0
+    p[o + 7] = 1.0                                  # Hy = z_1
+    lo = oracle.loss(circ, prob, p, {"colloc": pts})
+    want = 4 * np.cos(np.pi * pts[:, 0]) ** 2
+    if medium == "vacuum":
+        want = want + 4 * np.cos(np.pi * pts[:, 1]) ** 2
+    assert abs(lo[-1] - 10.0 * np.mean(want)) < 1e-12
+    assert abs(lo[0] - (lo[1] + lo[4] + lo[-1])) < 1e-12
+
+
+def test_sym_from_fields_parities(oracle):
+    """Fields built with the parities (i)-(iii) give L_sym = 0; flipping a sign of one mirrored
+    field gives 4 f^2 for that term."""
+    prob = W.problem("vacuum", w_sym=1.0)
+    rng = np.random.default_rng(2)
+    pts = rng.uniform(-1, 1, (30, 3))
+    x, y = pts[:, 0], pts[:, 1]
+    def fields(x, y):
+        return np.stack([np.cos(x) * np.cos(2 * y), np.cos(3 * x) * np.sin(y), np.sin(x) * np.cos(y)], axis=1)
+    fc, fmx, fmy = fields(x, y), fields(-x, y), fields(x, -y)
+    assert abs(oracle.sym_from_fields(prob, fc, fmx, fmy)) < 1e-15
+    fmy_bad = fmy.copy()
+    fmy_bad[:, 1] *= -1.0                           # Hx(x, -y) = +Hx(x, y): (ii) violated
+    got = oracle.sym_from_fields(prob, fc, fmx, fmy_bad)
+    assert abs(got - np.mean(4 * fc[:, 1] ** 2)) < 1e-14
+
+
+def test_sym_penalty_gradient_exact_shift_rule(oracle):
+    """With L_sym on, every loss term is still a trig polynomial of degree <= 4 in each circuit
+    angle (squares of sums of first-harmonic fields): the R = 4 shift rule gives the exact
+    gradient, also through the mirrored evaluations."""
+    circ = W.circuit(4, 2, 4, ansatz="strong_rot", enc="rx", scale="acos", premap="rff_mlp", **SMALL_MLP)
+    prob = W.problem("vacuum", w_energy=10.0, w_sym=10.0)
+    sets = {"colloc": W.uniform_points(6, 50), "ic": W.ic_points_uniform(3, 51)}
+    params = W.init_params(circ, 9).astype(np.float64)
+    lay = oracle.param_layout(circ)
+    idx = np.arange(lay["circuit"], lay["head"], 5)
+    g = oracle.grad(circ, prob, params, sets, idx)
+    for j, i in enumerate(idx):
+        def fn(x, i=i):
+            pp = params.copy()
+            pp[i] = x
+            return oracle.loss(circ, prob, pp, sets)[0]
+        assert abs(_shift_rule(fn, params[i], 4) - g[j]) < 1e-10 * max(1.0, abs(g[j])), i
