@@ -157,7 +157,11 @@ typedef struct {
  *  [0] total loss (Eq. 24 without L_sym), [1] L_phys (Eq. 11 or 13), [2] w_ic * L_IC,
  *  [3] w_bc * L_BC, [4] w_energy * mean(Eq. 23 residual^2), [5] MSE(res1) over the vacuum
  *  set (all points in vacuum), [6] MSE(res1) over the dielectric set, [7] MSE(res2),
- *  [8] MSE(res3), [9 .. 9+energy_nt) energy slice sums U(t_k) (Eq. 31). */
+ *  [8] MSE(res3), [9 .. 9+energy_nt) energy slice sums U(t_k) (Eq. 31), and when w_sym > 0
+ *  [9+energy_nt] w_sym * L_sym (Eq. 18: fields at (-x, y, t) and (x, -y, t) of every
+ *  collocation point, the x-mirror terms left out in the dielectric case), which the total
+ *  [0] includes. The symmetry penalty runs on the SIMT path (AUTO picks it; GEMM_SPLIT plans
+ *  with w_sym > 0 are refused with QP_ERR_UNSUPPORTED). */
 #define QP_NLOSS 9
 
 typedef struct qp_plan qp_plan;
@@ -193,7 +197,7 @@ qp_status qp_set_workspace(qp_plan* plan, void* d_workspace, size_t bytes);
 qp_status qp_forward(qp_plan* plan, const float* d_params, const float* d_pts, int64_t B,
                      float* d_fields, float* d_dfields, void* stream);
 
-/* Loss terms (layout above, float64 [QP_NLOSS + energy_nt]) and the gradient of the
+/* Loss terms (layout above, float64 [QP_NLOSS + energy_nt], one more with L_sym) and the gradient of the
  * total loss w.r.t. every parameter (float32 [n_params]; Omega entries get 0). */
 qp_status qp_loss_grad(qp_plan* plan, const float* d_params, const qp_batch* batch,
                        double* d_loss, float* d_grad, void* stream);

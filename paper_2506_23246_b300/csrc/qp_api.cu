@@ -99,6 +99,7 @@ static cudaError_t raise_smem_limit(const void* fn, cudaFuncAttribute attr, int 
 struct WsLayout {
   size_t status, gates, cmat, cenc, crz, crz64, thetaJ, dthetaJ, d1, d2, u1, blk_loss, blk_grad, wpart;
   size_t mact, mcot;   // layer-by-layer premap: hidden activations, two cotangent buffers
+  size_t sxb, sF, sgs, sge, spart;   // symmetry penalty: set-2 points, fields, cotangents, sums
   size_t dW, dphi, dU, dG, dY, dpart, dWT, dmu, dW16, dcs, dgs, dgates, total;
 };
 
@@ -203,8 +204,12 @@ int gsum_groups(const qp_plan* pl) {
   return (int)(g < 1 ? 1 : (g > 8 ? 8 : g));
 }
 
-WsLayout ws_layout(const qp_plan* pl, int64_t P) {
+WsLayout ws_layout(const qp_plan* pl, int64_t P0) {
   WsLayout w;
+  // with the symmetry penalty the main pass also evaluates up to two mirrored copies of every
+  // collocation point
+  const bool sym = pl->p.w_sym > 0.f;
+  const int64_t P = sym ? 3 * P0 : P0;
   const int n = pl->c.n_qubits, H = pl->c.premap == QP_PREMAP_RFF_MLP ? pl->c.mlp_width : 0;
   size_t o = 0;
   w.status = o; o = al256(o + 256);
@@ -229,6 +234,11 @@ WsLayout ws_layout(const qp_plan* pl, int64_t P) {
   const int64_t mw = pl->deep ? (H > n ? H : n) : 0;
   w.mact = o; o = al256(o + (pl->deep ? (size_t)pl->c.mlp_depth * P * 4 * H * 4 : 0));
   w.mcot = o; o = al256(o + (size_t)2 * P * 4 * mw * 4);
+  w.sxb = o; o = al256(o + (sym ? (size_t)P * 3 * 4 : 0));
+  w.sF = o; o = al256(o + (sym ? (size_t)P * 3 * 4 : 0));
+  w.sgs = o; o = al256(o + (sym ? (size_t)P0 * 3 * 4 : 0));
+  w.sge = o; o = al256(o + (sym ? (size_t)2 * P0 * 3 * 4 : 0));
+  w.spart = o; o = al256(o + (sym ? (size_t)pl->sm_count * 4 * 8 : 0));
   const size_t dim = (size_t)1 << n;
   const bool dn = dense_path(pl);
   w.dW = o; o = al256(o + (dn ? 2 * (2 * dim) * dim * 4 : 0));
@@ -324,6 +334,8 @@ qp_status validate(const qp_circuit* c, const qp_problem* p, int32_t path) {
   }
   if (p->medium != QP_MEDIUM_VACUUM && p->medium != QP_MEDIUM_DIELECTRIC) return QP_ERR_INVALID_ARG;
   if (p->phys_loss < 0 || p->phys_loss > 1 || !(p->w_sym >= 0.f)) return QP_ERR_INVALID_ARG;
+  // the symmetry penalty's mirrored evaluations run on the gate-by-gate path
+  if (p->w_sym > 0.f && path == QP_PATH_GEMM_SPLIT) return QP_ERR_UNSUPPORTED;
   if (p->energy_nt < 0 || p->energy_nt > QP_MAXNT || p->energy_slice < 0) return QP_ERR_INVALID_ARG;
   if (p->medium == QP_MEDIUM_DIELECTRIC && !(p->sigmoid_w > 0.f)) return QP_ERR_INVALID_ARG;
   if (!(p->ic_sigma > 0.f)) return QP_ERR_INVALID_ARG;
@@ -368,7 +380,7 @@ qp_status qp_plan_create(const qp_circuit* circuit, const qp_problem* problem, i
   // AUTO: the fused-unitary tensor-core path where it is faster and stays within 1e-5 of the
   // FP64 reference (8-10 qubits); the FP32 gate-by-gate path otherwise.
   pl->path = path != QP_PATH_AUTO ? path
-             : (circuit->n_qubits >= 8 ? QP_PATH_GEMM_SPLIT : QP_PATH_SIMT_FP32);
+             : (circuit->n_qubits >= 8 && !(problem->w_sym > 0.f) ? QP_PATH_GEMM_SPLIT : QP_PATH_SIMT_FP32);
   const int n = circuit->n_qubits;
   if (qp_build_sched(n, circuit->n_layers, circuit->ansatz, &pl->sched) != 0) {
     delete pl;
@@ -779,12 +791,13 @@ static void fill_circ(qp_plan* pl, QPCircArgs& a, const WsLayout& w, const float
   a.loss_stride = QP_NLP + pl->p.energy_nt;
   a.grad_stride = pl->nE + 3 * pl->c.n_readout + 3;
   a.nE = pl->nE;
+  a.nbc = npts[2];
   a.ansatz = pl->c.ansatz;
   a.crz = qp_has_crz(pl->c.ansatz) ? (const float2*)(ws + w.crz) : nullptr;
 }
 
 static qp_status launch_reduce(qp_plan* pl, const WsLayout& w, const float* d_params, const int64_t npts[3],
-                               double* d_loss, float* d_grad, bool mlp, cudaStream_t s);
+                               double* d_loss, float* d_grad, bool mlp, cudaStream_t s, int nsym = 0);
 static qp_status launch_premap_bwd(qp_plan* pl, const WsLayout& w, const float* d_params,
                                    const float* const pts[3], const int64_t npts[3], cudaStream_t s);
 
@@ -1170,8 +1183,44 @@ qp_status qp_loss_grad(qp_plan* pl, const float* d_params, const qp_batch* batch
   pl->last_status = (const int32_t*)((char*)pl->ws + w.status);
   char* ws = (char*)pl->ws;
   int launches = 0;
+  // symmetry penalty (Eq. 18): fields at the collocation points and their mirrors first, then
+  // the main pass with the mirrored points appended to set 2 as given-cotangent rows
+  const bool sym = pl->p.w_sym > 0.f && npts[0] > 0;
+  const int64_t nm = sym ? (pl->p.medium == QP_MEDIUM_VACUUM ? 2 * npts[0] : npts[0]) : 0;
+  int nsym = 0;
+  const float* mpts[3] = {pts[0], pts[1], pts[2]};
+  int64_t mnp[3] = {npts[0], npts[1], npts[2]};
+  if (sym) {
+    float* xb = (float*)(ws + w.sxb);
+    const int64_t tot = npts[2] + nm;
+    qpk::sym_points_kernel<<<(unsigned)((tot + 255) / 256 < pl->sm_count * 4 ? (tot + 255) / 256 : pl->sm_count * 4),
+                             256, 0, s>>>(pts[0], npts[0], pts[2], npts[2], pl->p.medium, xb);
+    const float* fp[3] = {pts[0], xb + 3 * npts[2], nullptr};
+    const int64_t fn[3] = {npts[0], nm, 0};
+    qp_status st = launch_front(pl, d_params, fp, fn, w, s, false);
+    if (st != QP_OK) return st;
+    QPCircArgs fa;
+    fill_circ(pl, fa, w, d_params, fp, fn, false);
+    fa.want_df = 0;
+    fa.out_f = (float*)(ws + w.sF);
+    const int64_t ftasks = fa.task_end[2];
+    int64_t fblocks = (ftasks + pl->warps_fwd - 1) / pl->warps_fwd;
+    if (fblocks > pl->blocks_fwd) fblocks = pl->blocks_fwd;
+    void* fargs[] = {&fa};
+    if (cudaLaunchKernel(circuit_kernel_ptr(pl->c.n_qubits, false), dim3((unsigned)fblocks),
+                         dim3(pl->warps_fwd * 32), fargs, pl->smem_fwd, s) != cudaSuccess)
+      return QP_ERR_CUDA;
+    const int64_t nb = (npts[0] + 255) / 256;
+    nsym = (int)(nb < pl->sm_count * 4 ? nb : pl->sm_count * 4);
+    const double N = (double)(pl->cur_norm[0] > 0 ? pl->cur_norm[0] : npts[0]);
+    qpk::sym_cot_kernel<<<nsym, 256, 0, s>>>((const float*)(ws + w.sF), npts[0], pl->p.medium, pl->p.w_sym, N,
+                                             (float*)(ws + w.sgs), (float*)(ws + w.sge), (double*)(ws + w.spart));
+    launches += 3 + front_launches(pl);
+    mpts[2] = xb;
+    mnp[2] = npts[2] + nm;
+  }
   if (P > 0) {
-    qp_status st = launch_front(pl, d_params, pts, npts, w, s, true);
+    qp_status st = launch_front(pl, d_params, mpts, mnp, w, s, true);
     if (st != QP_OK) return st;
     launches += front_launches(pl);
   } else {
@@ -1186,7 +1235,12 @@ qp_status qp_loss_grad(qp_plan* pl, const float* d_params, const qp_batch* batch
     launches += 1;
   }
   QPCircArgs a;
-  fill_circ(pl, a, w, d_params, pts, npts, true);
+  fill_circ(pl, a, w, d_params, mpts, mnp, true);
+  if (sym) {
+    a.gsym = (const float*)(ws + w.sgs);
+    a.gext = (const float*)(ws + w.sge);
+    a.nbc = npts[2];
+  }
   const bool mlp = pl->c.premap == QP_PREMAP_RFF_MLP;
   a.want_dtheta = mlp ? 1 : 0;
   const int64_t tasks = a.task_end[2];
@@ -1200,12 +1254,12 @@ qp_status qp_loss_grad(qp_plan* pl, const float* d_params, const qp_batch* batch
   (void)tasks;
   launches += 1;
   if (mlp) {
-    qp_status stb = launch_premap_bwd(pl, w, d_params, pts, npts, s);
+    qp_status stb = launch_premap_bwd(pl, w, d_params, mpts, mnp, s);
     if (stb != QP_OK) return stb;
     launches += premap_bwd_launches(pl);
   }
   qp_status st_red;
-  st_red = launch_reduce(pl, w, d_params, npts, d_loss, d_grad, mlp, s);
+  st_red = launch_reduce(pl, w, d_params, npts, d_loss, d_grad, mlp, s, nsym);
   pl->last_launches = launches + 1;
   return st_red;
 }
@@ -1253,9 +1307,12 @@ static qp_status launch_premap_bwd(qp_plan* pl, const WsLayout& w, const float* 
 }
 
 static qp_status launch_reduce(qp_plan* pl, const WsLayout& w, const float* d_params, const int64_t npts[3],
-                               double* d_loss, float* d_grad, bool mlp, cudaStream_t s) {
+                               double* d_loss, float* d_grad, bool mlp, cudaStream_t s, int nsym) {
   char* ws = (char*)pl->ws;
   qpk::ReduceArgs ra;
+  ra.sym_part = nsym > 0 ? (const double*)(ws + w.spart) : nullptr;
+  ra.nsym = nsym;
+  ra.w_sym = pl->p.w_sym;
   ra.blk_loss = (const double*)(ws + w.blk_loss);
   ra.blk_grad = (const float*)(ws + w.blk_grad);
   ra.nblk = pl->blocks_grad;

@@ -127,6 +127,69 @@ __global__ void crz_phase_kernel(const float* params, int64_t circ_off, int n, i
   if (d64) d64[i] = make_double2(cs, sn);
 }
 
+// --------------------------------------------------------------------------- symmetry penalty
+// Eq. 18 needs the fields at the mirrored points (-x, y, t) and (x, -y, t) of every collocation
+// point; in the dielectric case only (x, -y, t) (the terms mirrored along x are left out).
+// Points of set 2 of the main pass: the boundary points, then the mirrored points
+// (vacuum: all x-mirrors, then all y-mirrors; dielectric: the y-mirrors).
+__global__ void sym_points_kernel(const float* colloc, int64_t nc, const float* bc, int64_t nb, int medium,
+                                  float* out) {
+  const int64_t nm = medium == 0 ? 2 * nc : nc;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nb + nm; i += (int64_t)gridDim.x * blockDim.x) {
+    float x, y, t;
+    if (i < nb) {
+      x = bc[3 * i]; y = bc[3 * i + 1]; t = bc[3 * i + 2];
+    } else {
+      const int64_t j = i - nb, p = j % nc;
+      const bool mx = medium == 0 && j < nc;
+      x = mx ? -colloc[3 * p] : colloc[3 * p];
+      y = mx ? colloc[3 * p + 1] : -colloc[3 * p + 1];
+      t = colloc[3 * p + 2];
+    }
+    out[3 * i] = x; out[3 * i + 1] = y; out[3 * i + 2] = t;
+  }
+}
+
+// From the fields F (global rows: the nc collocation points, then the mirrored points in the
+// order above): the per-point sums of Eq. 18 (one FP64 partial per block), the cotangents of
+// w_sym L_sym = (w_sym / N) sum_p [...] for the collocation points' fields (gsym) and for the
+// mirrored points' fields (gext). 256 threads per block.
+__global__ void sym_cot_kernel(const float* F, int64_t nc, int medium, float w_sym, double N, float* gsym,
+                               float* gext, double* part) {
+  __shared__ double ws[8];
+  const float k = (float)(2.0 * w_sym / N);
+  double acc = 0.0;
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < nc; p += (int64_t)gridDim.x * blockDim.x) {
+    const float* f = F + 3 * p;
+    float gc[3] = {0.f, 0.f, 0.f};
+    if (medium == 0) {
+      const float* m = F + 3 * (nc + p);                 // f(-x, y, t): Ez, Hx even; Hy odd
+      const float a = f[0] - m[0], b = f[1] - m[1], c = f[2] + m[2];
+      acc += (double)(a * a + b * b + c * c);
+      gc[0] += k * a; gc[1] += k * b; gc[2] += k * c;
+      float* ge = gext + 3 * p;
+      ge[0] = -k * a; ge[1] = -k * b; ge[2] = k * c;
+    }
+    const int64_t oy = medium == 0 ? nc + p : p;         // row of f(x, -y, t) among the mirrors
+    const float* m = F + 3 * (nc + oy);                  // Ez even; Hx odd; Hy even in y
+    const float a = f[0] - m[0], b = f[1] + m[1], c = f[2] - m[2];
+    acc += (double)(a * a + b * b + c * c);
+    gc[0] += k * a; gc[1] += k * b; gc[2] += k * c;
+    float* ge = gext + 3 * oy;
+    ge[0] = -k * a; ge[1] = k * b; ge[2] = -k * c;
+    gsym[3 * p] = gc[0]; gsym[3 * p + 1] = gc[1]; gsym[3 * p + 2] = gc[2];
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += ws[i];
+    part[blockIdx.x] = t;
+  }
+}
+
 // --------------------------------------------------------------------------- BH indicator
 // Sec. 5: U~(t_k) = U(t_k) / U(0) for the energy slices u[0 .. nt), and I_BH = 1 - min over
 // the slices k >= k0 (t_k >= delta) of U~(t_k). One warp.
@@ -738,6 +801,9 @@ struct ReduceArgs {
   int64_t nparams, circ_off, head_off, mlp_off, mlp_count;
   int32_t n, L, m, k, nt, medium, ansatz, phys_loss;
   int32_t nE;                  // gate-gradient partial sums per block (head partials follow)
+  const double* sym_part;      // symmetry penalty: per-block sums of Eq. 18, or null
+  int32_t nsym;
+  float w_sym;
   int64_t nc, ni, nb;          // mean denominators of the three sets
   int64_t norm_diel;           // whole-set points inside the disk, or -1: the counted ones
   float w_ic, w_bc, w_energy;
@@ -827,7 +893,15 @@ __global__ void reduce_kernel(ReduceArgs a) {
       const double en = N > 0 ? a.w_energy * s[4] / N : 0;
       const double ic = a.ni > 0 ? a.w_ic * s[5] / (double)a.ni : 0;
       const double bc = a.nb > 0 ? a.w_bc * s[6] / (double)a.nb : 0;
-      const double tot = phys + ic + bc + en;
+      double sym = 0.0;
+      if (a.w_sym > 0.f) {
+        if (a.sym_part && N > 0) {
+          for (int b = 0; b < a.nsym; ++b) sym += a.sym_part[b];
+          sym *= (double)a.w_sym / N;
+        }
+        a.loss[QP_NLOSS_OUT + a.nt] = sym;   // w_sym L_sym after the energy slices
+      }
+      const double tot = phys + ic + bc + en + sym;
       a.loss[0] = tot; a.loss[1] = phys; a.loss[2] = ic; a.loss[3] = bc; a.loss[4] = en;
       a.loss[5] = m1v; a.loss[6] = m1d; a.loss[7] = m2; a.loss[8] = m3;
       if (!isfinite(tot)) atomicCAS(a.status, 0, (int)5);   // an earlier error code stands

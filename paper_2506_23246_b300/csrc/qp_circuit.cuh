@@ -436,13 +436,14 @@ __device__ __forceinline__ void run_task(const QPCircArgs& a, const Shared& sh, 
   }
   if (!GRAD) {
     if (active && lin == 0) {
+      const int64_t go = a.pt_base[set] + pt;   // global point index (set 0 alone: pt)
 #pragma unroll
-      for (int c = 0; c < 3; ++c) a.out_f[pt * 3 + c] = f[c];
+      for (int c = 0; c < 3; ++c) a.out_f[go * 3 + c] = f[c];
       if (nv == 4 && a.out_df) {
 #pragma unroll
         for (int c = 0; c < 3; ++c)
 #pragma unroll
-          for (int d = 0; d < 3; ++d) a.out_df[pt * 9 + c * 3 + d] = D[c][d];
+          for (int d = 0; d < 3; ++d) a.out_df[go * 9 + c * 3 + d] = D[c][d];
       }
     }
     return;
@@ -450,7 +451,18 @@ __device__ __forceinline__ void run_task(const QPCircArgs& a, const Shared& sh, 
   // ------------------------------------------------------------------ loss and cotangents
   const float* xp = a.pts[set] + ptc * 3;
   float g[3], gD[3][3];
-  point_loss(a.pb, set, pt, npt, a.counts, xp[0], xp[1], f, D, active, lin == 0, sh.loss, g, gD);
+  // rows of set 2 past the boundary points carry given cotangents (mirrored points of L_sym)
+  const bool given = set == 2 && pt >= a.nbc;
+  point_loss(a.pb, set, pt, set == 2 ? a.nbc : npt, a.counts, xp[0], xp[1], f, D, active && !given,
+             lin == 0, sh.loss, g, gD);
+  if (given && active) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) g[c] = a.gext[(pt - a.nbc) * 3 + c];
+  }
+  if (set == 0 && a.gsym && active) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) g[c] += a.gsym[pt * 3 + c];
+  }
   // back through the head: zbar = W^T g, zbar_d = W^T g_d; head gradients
   float zb[QP_MAXQ], zbd[3][QP_MAXQ];
 #pragma unroll

@@ -127,7 +127,12 @@ struct QPCircArgs {
   const int32_t* counts;      // [0] dielectric-set size
   double* blk_loss;           // [grid][QP_NLP + nt]
   float* blk_grad;            // [grid][3 n L + 3 m + 3]
-  float* out_f;               // forward mode [B][3]
+  float* out_f;               // forward mode [B][3] (all sets, by global point index)
   float* out_df;              // forward mode [B][3][3]
   int32_t loss_stride, grad_stride;
+  // symmetry penalty (Eq. 18): extra cotangents of the collocation points' fields, and the rows
+  // of set 2 from index nbc on (the mirrored points) whose cotangents are given, not a loss's
+  const float* gsym;          // [n colloc][3] or null
+  const float* gext;          // [npts[2] - nbc][3] or null
+  int64_t nbc;                // boundary points of set 2 (the rest are the given-cotangent rows)
 };

@@ -229,7 +229,7 @@ class Plan:
     def _outputs(self, params, out):
         if out is not None:
             return out
-        nl = NLOSS + self.problem.get("energy_nt", 0)
+        nl = NLOSS + self.problem.get("energy_nt", 0) + (1 if self.problem.get("w_sym", 0.0) > 0 else 0)
         return (torch.empty(nl, dtype=torch.float64, device=params.device),
                 torch.empty(self.n_params, dtype=torch.float32, device=params.device))
 
