@@ -57,7 +57,7 @@ def circ_array(circ):
     return np.array([circ["n_qubits"], circ["n_layers"], circ["n_readout"], ANSATZ[circ["ansatz"]],
                      ENC[circ["enc"]], SCALE[circ["scale"]], PREMAP[circ["premap"]],
                      circ.get("n_direct", 3), circ.get("rff_freqs", 0), circ.get("mlp_width", 0),
-                     circ.get("mlp_depth", 0)], dtype=np.int32)
+                     circ.get("mlp_depth", 0), 1 if circ.get("periodic") else 0], dtype=np.int32)
 
 
 def prob_arrays(prob, norm=None):

@@ -32,8 +32,12 @@
 //     r = 1 (Basic) or r = 1 + (l mod (n-1)) (Strongly entangling, Sec. 2.3 item 2).
 //
 // Config arrays (ctypes-friendly):
-//   ci[ 0..10] = n_qubits, n_layers, n_readout, ansatz, enc, scale, premap,
-//                n_direct, rff_freqs, mlp_width, mlp_depth
+//   ci[ 0..11] = n_qubits, n_layers, n_readout, ansatz, enc, scale, premap,
+//                n_direct, rff_freqs, mlp_width, mlp_depth, periodic
+//     periodic (RFF premap): 1 = the periodic input map of Eqs. 25-26 before the RFF layer:
+//       (x, y, t) -> (sin(2 pi x / 2), cos(2 pi x / 2), sin(2 pi y / 2), cos(2 pi y / 2),
+//       sin(2 pi t / T), cos(2 pi t / T)) with the domain lengths L_x = L_y = 2 of [-1, 1]^2 and
+//       a learned time period T
 //     ansatz: 0 Basic RY,RZ   1 Basic Rot   2 Strongly Rot   3 No-entanglement Rot
 //             4 Cross-Mesh (RX per qubit, CRZ(i,j) for every ordered pair i != j)
 //             5 Cross-Mesh-2-Rotations (RX then RZ per qubit, the same CRZ mesh)
@@ -52,8 +56,9 @@
 //   pd[0..11] = eps_r, disk_r, disk_x0, disk_y0, sigmoid_w, ic_sigma, ic_x0, ic_y0,
 //               w_ic, w_bc, w_energy, w_sym (weight of L_sym, Eq. 18; 0 = off)
 // Parameter layout (flat):
-//   premap RFF+MLP: Omega[F][3] (fixed, zero gradient), then per hidden layer
-//     W[H][in] (in = 2F first, H after), b[H]; then W_out[n][H], b_out[n]
+//   premap RFF+MLP: Omega[F][3] (Omega[F][6] with the periodic map; fixed, zero gradient), the
+//     learned period T (periodic map only), then per hidden layer W[H][in] (in = 2F first, H
+//     after), b[H]; then W_out[n][H], b_out[n]
 //   circuit: per layer [n][k] single-qubit angles, k = 2 (RY, RZ) for ansatz 0, 1 (RX) for
 //     ansatz 4, 2 (RX, RZ) for ansatz 5, else 3 (Rot a,b,g); then, for ansatz 4 and 5, the
 //     n (n-1) CRZ angles [i][j != i] (control i, targets j in increasing order)
@@ -148,13 +153,14 @@ R hexp(const R& a) { double e = std::exp(a.c[0]); return fun(a, e, e, e); }
 
 // ---------------------------------------------------------------- configs
 struct Circ {
-  int n, L, m, ansatz, enc, scale, premap, n_direct, F, H, depth;
+  int n, L, m, ansatz, enc, scale, premap, n_direct, F, H, depth, periodic;
+  int in_dim() const { return periodic ? 6 : 3; }   // RFF input width
   int k() const { return ansatz == 0 || ansatz == 5 ? 2 : (ansatz == 4 ? 1 : 3); }
   bool crz() const { return ansatz == 4 || ansatz == 5; }
   int64_t layer_count() const { return (int64_t)n * k() + (crz() ? (int64_t)n * (n - 1) : 0); }
   int64_t premap_count() const {
     if (premap == 0) return 0;
-    int64_t c = 3LL * F;
+    int64_t c = (int64_t)in_dim() * F + (periodic ? 1 : 0);
     int in = 2 * F;
     for (int l = 0; l < depth; ++l) { c += (int64_t)H * in + H; in = H; }
     c += (int64_t)n * in + n;
@@ -169,13 +175,14 @@ Circ read_circ(const int* ci) {
   Circ c;
   c.n = ci[0]; c.L = ci[1]; c.m = ci[2]; c.ansatz = ci[3]; c.enc = ci[4]; c.scale = ci[5];
   c.premap = ci[6]; c.n_direct = ci[7]; c.F = ci[8]; c.H = ci[9]; c.depth = ci[10];
+  c.periodic = ci[11];
   return c;
 }
 bool circ_ok(const Circ& c) {
   if (c.n < 1 || c.n > 12 || c.L < 0 || c.m < 1 || c.m > c.n) return false;
   if (c.ansatz < 0 || c.ansatz > 6 || c.enc < 0 || c.enc > 1 || c.scale < 0 || c.scale > 4) return false;
   if (c.premap == 0) return c.n_direct >= 0 && c.n_direct <= 3 && c.n_direct <= c.n;
-  if (c.premap == 1) return c.F >= 1 && c.H >= 1 && c.depth >= 0;
+  if (c.premap == 1) return c.F >= 1 && c.H >= 1 && c.depth >= 0 && (c.periodic == 0 || c.periodic == 1);
   return false;
 }
 
@@ -325,14 +332,27 @@ void premap(const Circ& c, const R* P, const R v[3], std::vector<R>& theta) {
     for (int j = 0; j < c.n_direct; ++j) theta[j] = scale_direct(c.scale, v[j]);
     return;
   }
-  const R* om = P;  // Omega[F][3]
+  const R* om = P;  // Omega[F][in_dim]
+  const int di = c.in_dim();
+  // periodic map (Eqs. 25-26): space over the domain lengths 2, time over the learned period
+  std::vector<R> u(di);
+  if (c.periodic) {
+    const R T = P[(int64_t)di * c.F];
+    const R ax = scal(v[0], M_PI), ay = scal(v[1], M_PI);
+    const R invT = fun(T, 1.0 / T.c[0], -1.0 / (T.c[0] * T.c[0]), 2.0 / (T.c[0] * T.c[0] * T.c[0]));
+    const R at = scal(v[2] * invT, 2.0 * M_PI);
+    u[0] = hsin(ax); u[1] = hcos(ax); u[2] = hsin(ay); u[3] = hcos(ay); u[4] = hsin(at); u[5] = hcos(at);
+  } else {
+    u[0] = v[0]; u[1] = v[1]; u[2] = v[2];
+  }
   std::vector<R> x(2 * c.F);
   for (int f = 0; f < c.F; ++f) {
-    R arg = om[3 * f] * v[0] + om[3 * f + 1] * v[1] + om[3 * f + 2] * v[2];
+    R arg = om[(int64_t)di * f] * u[0];
+    for (int j = 1; j < di; ++j) arg = arg + om[(int64_t)di * f + j] * u[j];
     x[f] = hcos(arg);
     x[c.F + f] = hsin(arg);
   }
-  const R* w = P + 3 * c.F;
+  const R* w = P + (int64_t)di * c.F + (c.periodic ? 1 : 0);
   int in = 2 * c.F;
   for (int l = 0; l < c.depth; ++l) {
     std::vector<R> y(c.H);
@@ -610,7 +630,7 @@ int qpo_param_layout(const int* ci, int64_t* out) {
   Circ c = read_circ(ci);
   if (!circ_ok(c)) return 1;
   out[0] = c.circuit_offset(); out[1] = c.head_offset(); out[2] = c.total();
-  out[3] = c.premap == 1 ? 3LL * c.F : 0;
+  out[3] = c.premap == 1 ? (int64_t)c.in_dim() * c.F : 0;
   return 0;
 }
 
@@ -704,7 +724,7 @@ int qpo_grad(const int* ci, const int* pi, const double* pd, const double* param
   Circ c = read_circ(ci);
   if (!circ_ok(c)) return 1;
   Prob pb = read_prob(pi, pd);
-  const int64_t nfixed = c.premap == 1 ? 3LL * c.F : 0;
+  const int64_t nfixed = c.premap == 1 ? (int64_t)c.in_dim() * c.F : 0;
   for (int64_t i = 0; i < nidx; ++i)
     if (idx[i] < 0 || idx[i] >= c.total()) return 2;
   // threads over the listed parameters, or over the points of each evaluation when there are

@@ -16,13 +16,24 @@ import numpy as np
 # ----------------------------------------------------------------------------- presets
 
 def circuit(n_qubits, n_layers, n_readout=None, ansatz="strong_rot", enc="rx", scale="acos",
-            premap="rff_mlp", n_direct=3, rff_freqs=64, mlp_width=32, mlp_depth=1):
-    return {"n_qubits": n_qubits, "n_layers": n_layers,
-            "n_readout": n_qubits if n_readout is None else n_readout, "ansatz": ansatz,
-            "enc": enc, "scale": scale, "premap": premap, "n_direct": n_direct,
-            "rff_freqs": rff_freqs if premap == "rff_mlp" else 0,
-            "mlp_width": mlp_width if premap == "rff_mlp" else 0,
-            "mlp_depth": mlp_depth if premap == "rff_mlp" else 0}
+            premap="rff_mlp", n_direct=3, rff_freqs=64, mlp_width=32, mlp_depth=1, periodic=False):
+    """periodic: the periodic input map of Eqs. 25-26 in front of the RFF layer (a learned time
+    period T becomes the first trainable premap parameter)."""
+    c = {"n_qubits": n_qubits, "n_layers": n_layers,
+         "n_readout": n_qubits if n_readout is None else n_readout, "ansatz": ansatz,
+         "enc": enc, "scale": scale, "premap": premap, "n_direct": n_direct,
+         "rff_freqs": rff_freqs if premap == "rff_mlp" else 0,
+         "mlp_width": mlp_width if premap == "rff_mlp" else 0,
+         "mlp_depth": mlp_depth if premap == "rff_mlp" else 0}
+    if periodic and premap == "rff_mlp":
+        c["periodic"] = True
+    return c
+
+
+# Initial value of the learned time period of the periodic map (Eqs. 25-26): longer than every
+# time range of the paper's problems (t <= 1.5), as the paper notes the simulated time does not
+# complete a period.
+PERIOD_INIT = 4.0
 
 
 def problem(medium="vacuum", eps_r=4.0, disk_r=0.25, disk_x0=0.5, disk_y0=0.0, sigmoid_w=0.02,
@@ -134,7 +145,9 @@ def param_blocks(circ):
     blocks = []
     if circ["premap"] == "rff_mlp":
         F, H, depth = circ["rff_freqs"], circ["mlp_width"], circ["mlp_depth"]
-        blocks.append(("omega", (F, 3)))
+        blocks.append(("omega", (F, 6 if circ.get("periodic") else 3)))
+        if circ.get("periodic"):
+            blocks.append(("period", (1,)))
         fan = 2 * F
         for li in range(depth):
             blocks.append(("W%d" % li, (H, fan)))
@@ -183,6 +196,8 @@ def init_params(circ, seed=0):
                 bname = "b" + name[1:]
                 vals[bname] = rng.uniform(-1 / math.sqrt(fan), 1 / math.sqrt(fan), blocks[bname])
         vals["omega"] = rng.standard_normal(blocks["omega"])
+        if circ.get("periodic"):
+            vals["period"] = np.full(1, PERIOD_INIT)
     flat = [np.asarray(vals[name], dtype=np.float64).ravel() for name, _ in param_blocks(circ)]
     return np.concatenate(flat).astype(np.float32)
 

@@ -103,6 +103,11 @@ def test_table1_param_counts(oracle):
     classical = lay["total"] - lay["fixed"] - quantum
     assert classical + rows[("learned_period",)] == rows[("classical_qpinn",)]
     assert lay["total"] == W.param_offsets(circ)["total"][0]
+    # with the periodic input map (Eqs. 25-26) the learned period is a parameter of the layout
+    circ = dict(circ, periodic=True)
+    lay = oracle.param_layout(circ)
+    assert lay["total"] - lay["fixed"] - (lay["head"] - lay["circuit"]) == rows[("classical_qpinn",)]
+    assert lay["total"] == W.param_offsets(circ)["total"][0]
 
 
 # ----------------------------------------------------------------------------- closed forms
@@ -856,3 +861,68 @@ def test_sym_penalty_gradient_exact_shift_rule(oracle):
             pp[i] = x
             return oracle.loss(circ, prob, pp, sets)[0]
         assert abs(_shift_rule(fn, params[i], 4) - g[j]) < 1e-10 * max(1.0, abs(g[j])), i
+
+
+# ----------------------------------------------------------------------------- periodic input map
+
+def _periodic_circ(**kw):
+    return W.circuit(4, 2, 4, ansatz="strong_rot", enc="rx", scale="acos", premap="rff_mlp",
+                     rff_freqs=5, mlp_width=6, mlp_depth=2, periodic=True, **kw)
+
+
+def test_periodic_map_periodicity(oracle):
+    """Eqs. 25-26 make the network periodic: f(x + 2, y, t) = f(x, y + 2, t) = f(x, y, t + T) =
+    f(x, y, t) for the domain lengths 2 and the learned period T, fields and input derivatives."""
+    circ = _periodic_circ()
+    params = W.init_params(circ, 3).astype(np.float64)
+    T = params[W.param_offsets(circ)["period"][0]]
+    pts = W.uniform_points(12, 4).astype(np.float64)
+    f, df = oracle.forward(circ, params, pts)
+    for shift in (np.array([2.0, 0, 0]), np.array([0, -2.0, 0]), np.array([0, 0, T])):
+        g, dg = oracle.forward(circ, params, pts + shift)
+        assert np.max(np.abs(g - f)) < 1e-11 and np.max(np.abs(dg - df)) < 1e-10
+
+
+def test_periodic_map_derivatives_vs_fd(oracle):
+    """Input derivatives through the periodic map, and the gradient w.r.t. the learned period,
+    against central differences."""
+    circ = _periodic_circ()
+    params = W.init_params(circ, 5).astype(np.float64)
+    pts = W.uniform_points(6, 8).astype(np.float64)
+    f, df = oracle.forward(circ, params, pts)
+    h = 1e-5
+    for d in range(3):
+        e = np.zeros(3)
+        e[d] = h
+        fd = (oracle.forward(circ, params, pts + e)[0] - oracle.forward(circ, params, pts - e)[0]) / (2 * h)
+        assert np.max(np.abs(fd - df[:, :, d])) < 1e-7
+    prob = W.problem("vacuum", w_energy=10.0)
+    sets = {"colloc": pts, "ic": W.ic_points_uniform(3, 9)}
+    it = W.param_offsets(circ)["period"][0]
+    g = oracle.grad(circ, prob, params, sets, [it])[0]
+    pp, pm = params.copy(), params.copy()
+    pp[it] += h
+    pm[it] -= h
+    fd = (oracle.loss(circ, prob, pp, sets)[0] - oracle.loss(circ, prob, pm, sets)[0]) / (2 * h)
+    assert abs(fd - g) < 1e-6 * max(1.0, abs(g))
+    assert abs(g) > 1e-6
+
+
+def test_periodic_map_closed_form(oracle):
+    """One qubit, no ansatz layer, one frequency selecting sin(2 pi x / 2) (Omega = e_1), no
+    hidden layer, acos scaling: <Z> = tanh(w_c cos(sin(pi x)) + w_s sin(sin(pi x)) + b) (Fig. 3,
+    Sec. 2.2 RFF and Eq. 25), and the time feature t / T enters only through the period."""
+    circ = W.circuit(1, 0, 1, ansatz="noent_rot", enc="rx", scale="acos", premap="rff_mlp",
+                     rff_freqs=1, mlp_width=2, mlp_depth=0, periodic=True)
+    wc, ws, b = 0.7, -0.4, 0.1
+    p = np.concatenate([[1.0, 0, 0, 0, 0, 0], [3.0], [wc, ws], [b], [1.0, 0, 0], [0, 0, 0]])
+    assert p.shape[0] == W.param_offsets(circ)["total"][0]
+    pts = W.uniform_points(7, 10).astype(np.float64)
+    f, df = oracle.forward(circ, p, pts)
+    for i, v in enumerate(pts):
+        u = math.sin(math.pi * v[0])
+        h = wc * math.cos(u) + ws * math.sin(u) + b
+        assert abs(f[i, 0] - math.tanh(h)) < 1e-13
+        dh = (-wc * math.sin(u) + ws * math.cos(u)) * math.pi * math.cos(math.pi * v[0])
+        assert abs(df[i, 0, 0] - (1 - math.tanh(h) ** 2) * dh) < 1e-12
+        assert abs(df[i, 0, 1]) < 1e-15 and abs(df[i, 0, 2]) < 1e-15
