@@ -631,11 +631,13 @@ def run_configs(a):
 
 
 def run_paper_net(a):
-    """The paper's hybrid network (Sec. 2.2-2.3, Table 1: RFF with 128 frequencies, three tanh
-    layers of width 128, 7 angles, 7 qubits x 4 strongly entangling layers, head of 3) on the
+    """The paper's hybrid network (Sec. 2.2-2.3, Table 1: periodic input map with a learned period,
+    RFF with 128 frequencies, three tanh layers of width 128, 7 angles, 7 qubits x 4 strongly
+    entangling layers, head of 3; 66,848 classical + 84 quantum parameters) on the
     grid sizes of its timing table (40^3 and 87^3 collocation points on [-1,1]^2 x [0,1.5],
     vacuum, IC plane of the grid, energy term over the grid's time slices): one step is
-    qp_loss_grad (fields, input derivatives, losses, adjoint gradient of all 67,315 parameters).
+    qp_loss_grad (fields, input derivatives, losses, adjoint gradient of all 66,932 trainable
+    parameters).
     The paper's numbers (TorQ, one training epoch with second-order autograd and Adam, A100 or
     L40s) are context, not the same measurement."""
     import torch
@@ -648,7 +650,7 @@ def run_paper_net(a):
     paper = {40: 0.145136, 87: 0.849967}
     for g in (40, 87):
         circ = W.circuit(7, 4, 7, ansatz="strong_rot", enc="rx", scale="acos", premap="rff_mlp",
-                         rff_freqs=128, mlp_width=128, mlp_depth=3)
+                         rff_freqs=128, mlp_width=128, mlp_depth=3, periodic=True)
         prob = W.problem("vacuum", w_energy=10.0, energy_slice=g * g, energy_nt=g)
         sets = {"colloc": W.grid_points(g, g, g, 1.5), "ic": W.ic_grid(g, g)}
         params = W.init_params(circ, 0)

@@ -112,6 +112,10 @@ typedef struct {
   int32_t rff_freqs; /* RFF_MLP: number of frequencies F (Omega is [F][3]), 1..256 */
   int32_t mlp_width; /* RFF_MLP: hidden width H, 1..1024 */
   int32_t mlp_depth; /* RFF_MLP: number of hidden tanh layers, 0..8 */
+  int32_t periodic;  /* RFF_MLP: 1 = the periodic input map of Eqs. 25-26 before the RFF layer,
+                        (x, y, t) -> (sin(pi x), cos(pi x), sin(pi y), cos(pi y), sin(2 pi t / T),
+                        cos(2 pi t / T)) for the domain lengths 2 of [-1, 1]^2 and a learned time
+                        period T; Omega is then [F][6] */
 } qp_circuit;
 
 typedef struct {
@@ -175,8 +179,9 @@ qp_status qp_plan_create(const qp_circuit* circuit, const qp_problem* problem, i
 void qp_plan_destroy(qp_plan* plan);
 
 /* Number of float32 entries of the flat parameter vector. Layout (Sec. 2.2-2.3):
- *   RFF_MLP premap: Omega[F][3] (fixed, gradient 0), then per hidden layer W[H][in]
- *   (in = 2F first, H after) and b[H], then W_out[n][H], b_out[n];
+ *   RFF_MLP premap: Omega[F][3] (Omega[F][6] with the periodic map; fixed, gradient 0), the
+ *   learned period T (periodic map only), then per hidden layer W[H][in] (in = 2F first, H
+ *   after) and b[H], then W_out[n][H], b_out[n];
  *   circuit, per layer: [n][k] single-qubit angles with k = 2 (RY, RZ) for BASIC_RYRZ, 1 (RX)
  *   for CROSS_MESH, 2 (RX, RZ) for CROSS_MESH_2ROT, else 3 (Rot a, b, g); then, for CROSS_MESH
  *   and CROSS_MESH_2ROT, the n (n-1) CRZ angles [i][j != i] (targets j in increasing order);

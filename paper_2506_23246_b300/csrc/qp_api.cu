@@ -59,9 +59,14 @@ namespace {
 
 constexpr int kMaxWarps = 12;
 
+// Fixed RFF frequencies: Omega [F][3], or [F][6] with the periodic input map.
+int64_t omega_count(const qp_circuit& c) {
+  return c.premap == QP_PREMAP_RFF_MLP ? (c.periodic ? 6LL : 3LL) * c.rff_freqs : 0;
+}
+
 int64_t premap_count(const qp_circuit& c) {
   if (c.premap != QP_PREMAP_RFF_MLP) return 0;
-  int64_t cnt = 3LL * c.rff_freqs;
+  int64_t cnt = omega_count(c) + (c.periodic ? 1 : 0);
   int64_t in = 2LL * c.rff_freqs;
   for (int l = 0; l < c.mlp_depth; ++l) { cnt += (int64_t)c.mlp_width * in + c.mlp_width; in = c.mlp_width; }
   cnt += (int64_t)c.n_qubits * in + c.n_qubits;
@@ -100,6 +105,7 @@ struct WsLayout {
   size_t status, gates, cmat, cenc, crz, crz64, thetaJ, dthetaJ, d1, d2, u1, blk_loss, blk_grad, wpart;
   size_t mact, mcot;   // layer-by-layer premap: hidden activations, two cotangent buffers
   size_t sxb, sF, sgs, sge, spart;   // symmetry penalty: set-2 points, fields, cotangents, sums
+  size_t mtg;                        // periodic map: FP64 sum of the learned period's gradient
   size_t dW, dphi, dU, dG, dY, dpart, dWT, dmu, dW16, dcs, dgs, dgates, total;
 };
 
@@ -150,7 +156,7 @@ int front_launches(const qp_plan* pl) {
 // Kernels of the premap backward: the fused per-point kernels (1 or 2), or layer by layer the
 // output layer, a weight gradient per layer and an input cotangent per hidden layer.
 int premap_bwd_launches(const qp_plan* pl) {
-  return pl->deep ? 1 + (pl->c.mlp_depth + 1) + pl->c.mlp_depth : (pl->pg_ok ? 1 : 2);
+  return pl->deep ? 1 + (pl->c.mlp_depth + 1) + pl->c.mlp_depth + (pl->c.periodic ? 2 : 0) : (pl->pg_ok ? 1 : 2);
 }
 
 // The fused forward kernel keeps a tile's whole output row (2^(n+1) FP32 columns) in tensor
@@ -239,6 +245,7 @@ WsLayout ws_layout(const qp_plan* pl, int64_t P0) {
   w.sgs = o; o = al256(o + (sym ? (size_t)P0 * 3 * 4 : 0));
   w.sge = o; o = al256(o + (sym ? (size_t)2 * P0 * 3 * 4 : 0));
   w.spart = o; o = al256(o + (sym ? (size_t)pl->sm_count * 4 * 8 : 0));
+  w.mtg = o; o = al256(o + (pl->c.periodic ? 8 : 0));
   const size_t dim = (size_t)1 << n;
   const bool dn = dense_path(pl);
   w.dW = o; o = al256(o + (dn ? 2 * (2 * dim) * dim * 4 : 0));
@@ -327,11 +334,13 @@ qp_status validate(const qp_circuit* c, const qp_problem* p, int32_t path) {
     if (c->n_direct < 0 || c->n_direct > 3 || c->n_direct > c->n_qubits) return QP_ERR_INVALID_ARG;
   } else if (c->premap == QP_PREMAP_RFF_MLP) {
     if (c->rff_freqs < 1 || c->mlp_width < 1 || c->mlp_depth < 0) return QP_ERR_INVALID_ARG;
+    if (c->periodic != 0 && c->periodic != 1) return QP_ERR_INVALID_ARG;
     // any depth and width up to these bounds (the layer-by-layer kernels)
     if (c->rff_freqs > QP_MAXF || c->mlp_width > 1024 || c->mlp_depth > 8) return QP_ERR_UNSUPPORTED;
   } else {
     return QP_ERR_INVALID_ARG;
   }
+  if (c->premap != QP_PREMAP_RFF_MLP && c->periodic != 0) return QP_ERR_INVALID_ARG;
   if (p->medium != QP_MEDIUM_VACUUM && p->medium != QP_MEDIUM_DIELECTRIC) return QP_ERR_INVALID_ARG;
   if (p->phys_loss < 0 || p->phys_loss > 1 || !(p->w_sym >= 0.f)) return QP_ERR_INVALID_ARG;
   // the symmetry penalty's mirrored evaluations run on the gate-by-gate path
@@ -387,7 +396,7 @@ qp_status qp_plan_create(const qp_circuit* circuit, const qp_problem* problem, i
     return QP_ERR_UNSUPPORTED;
   }
   pl->mlp_count = premap_count(*circuit);
-  pl->nfixed = circuit->premap == QP_PREMAP_RFF_MLP ? 3LL * circuit->rff_freqs : 0;
+  pl->nfixed = omega_count(*circuit);
   pl->mlp_off = pl->nfixed;
   pl->circ_off = pl->mlp_count;
   pl->head_off = pl->circ_off + (int64_t)circuit->n_layers * qp_layer_params(circuit->ansatz, n);
@@ -497,7 +506,7 @@ qp_status qp_plan_create(const qp_circuit* circuit, const qp_problem* problem, i
     // one hidden layer of a width the fused per-point kernels take; otherwise layer by layer
     const bool one_layer = circuit->mlp_depth == 1 && (H == 4 || H == 8 || H == 16 || H == 32 || H == 64) &&
                            (F % 2) == 0 && (int64_t)H * 2 * F <= 16 * 4 * 256 && n * H <= 4 * 256;
-    pl->deep = !one_layer;
+    pl->deep = !one_layer || circuit->periodic;
     pl->pg_ok = one_layer && F == qpk::PG_F && H == qpk::PG_H && n <= 16;
     if (pl->pg_ok &&
         (raise_smem_limit((void*)qpk::premap_fwd_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -612,7 +621,7 @@ static void fill_problem(const qp_plan* pl, QPProblemDev& d) {
 // input and output widths, offsets of its W [out][in] and b [out] after the Omega entries.
 static void mlp_layer_geom(const qp_plan* pl, int l, int& in, int& out, int64_t& w_off, int64_t& b_off) {
   const int F = pl->c.rff_freqs, H = pl->c.mlp_width, D = pl->c.mlp_depth;
-  int64_t o = 0;
+  int64_t o = pl->c.periodic ? 1 : 0;   // the learned period comes first
   int fan = 2 * F;
   for (int i = 0; i < l; ++i) { o += (int64_t)H * fan + H; fan = H; }
   in = fan;
@@ -630,6 +639,7 @@ static qpm::MlpArgs mlp_layer_args(const qp_plan* pl, const float* d_params, con
   m.ptot = npts[0] + npts[1] + npts[2];
   m.omega = d_params;
   m.F = pl->c.rff_freqs;
+  m.period = pl->c.periodic ? d_params + pl->nfixed : nullptr;
   int64_t wo, bo;
   mlp_layer_geom(pl, l, m.in, m.out, wo, bo);
   m.W = d_params + pl->nfixed + wo;
@@ -695,17 +705,24 @@ static qp_status launch_mlp_bwd(qp_plan* pl, const float* d_params, const float*
     da.nchunks = pl->nwblk;
     const int nto = (out + qpm::MT_N - 1) / qpm::MT_N, nti = (in + qpm::MT_N - 1) / qpm::MT_N;
     qpm::mlp_dw_kernel<<<dim3((unsigned)(nto * nti), (unsigned)pl->nwblk), qpm::MT_THREADS, 0, s>>>(da);
-    if (l > 0) {
+    if (l > 0 || pl->c.periodic) {
       qpm::MlpBwdArgs ba;
       ba.ptot = P;
       ba.W = da.x.W;
       ba.in = in;
       ba.out = out;
       ba.cot = cot[cur];
-      ba.act_prev = (const float*)(ws + w.mact) + (int64_t)(l - 1) * lstride;
-      ba.cot_prev = cot[cur ^ 1];
+      ba.act_prev = l > 0 ? (const float*)(ws + w.mact) + (int64_t)(l - 1) * lstride : nullptr;
+      ba.cot_prev = l > 0 ? cot[cur ^ 1] : nullptr;
+      ba.x = da.x;
+      // first layer with the periodic map: the input cotangents give the period's gradient
+      ba.tgrad = l == 0 ? (double*)(ws + w.mtg) : nullptr;
+      if (l == 0 && cudaMemsetAsync(ws + w.mtg, 0, sizeof(double), s) != cudaSuccess) return QP_ERR_CUDA;
       const int64_t tiles = ((P + qpm::MT_P - 1) / qpm::MT_P) * ((in + qpm::MT_N - 1) / qpm::MT_N);
       qpm::mlp_bwd_dx_kernel<<<mlp_grid(pl, tiles), qpm::MT_THREADS, 0, s>>>(ba);
+      if (l == 0)
+        qpm::mlp_period_fin_kernel<<<(pl->nwblk + 255) / 256, 256, 0, s>>>(
+            (const double*)(ws + w.mtg), (float*)(ws + w.wpart), da.nW, 0, pl->nwblk);
       cur ^= 1;
     }
   }

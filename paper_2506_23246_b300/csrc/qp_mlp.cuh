@@ -36,8 +36,9 @@ struct MlpArgs {
   const float* pts[3];
   int64_t npts[3];
   int64_t ptot;
-  const float* omega;       // [F][3] (fixed RFF frequencies)
+  const float* omega;       // [F][3], or [F][6] with the periodic map (fixed RFF frequencies)
   int32_t F;
+  const float* period;      // periodic input map (Eqs. 25-26): the learned time period T, or null
   // the layer: out x in weights (row-major [out][in]) and bias
   const float* W;
   const float* b;
@@ -63,6 +64,26 @@ __device__ __forceinline__ const float* mlp_point(const MlpArgs& a, int64_t gp, 
   return a.pts[set] + li * 3;
 }
 
+// RFF argument a = Omega_f . u(v) of point v and its x, y, t derivatives: u = v, or with the
+// periodic map (Eqs. 25-26) u = (sin pi x, cos pi x, sin pi y, cos pi y, sin(2 pi t/T),
+// cos(2 pi t/T)).
+__device__ __forceinline__ float4 rff_arg(const MlpArgs& a, const float* v, int f) {
+  if (!a.period) {
+    const float ox = __ldg(&a.omega[3 * f]), oy = __ldg(&a.omega[3 * f + 1]), ot = __ldg(&a.omega[3 * f + 2]);
+    return make_float4(ox * v[0] + oy * v[1] + ot * v[2], ox, oy, ot);
+  }
+  const float* o = a.omega + 6 * f;
+  const float T = __ldg(a.period), w = 6.28318530717959f / T;
+  float sx, cx, sy, cy, st, ct;
+  sincospif(v[0], &sx, &cx);
+  sincospif(v[1], &sy, &cy);
+  sincosf(w * v[2], &st, &ct);
+  const float pi = 3.14159265358979f;
+  const float o0 = __ldg(o), o1 = __ldg(o + 1), o2 = __ldg(o + 2), o3 = __ldg(o + 3), o4 = __ldg(o + 4), o5 = __ldg(o + 5);
+  return make_float4(o0 * sx + o1 * cx + o2 * sy + o3 * cy + o4 * st + o5 * ct, pi * (o0 * cx - o1 * sx),
+                     pi * (o2 * cy - o3 * sy), w * (o4 * ct - o5 * st));
+}
+
 // Input rows of point gp at input index k (< in), all four: RFF features and their tangents,
 // or the previous layer's (y0, s z_d).
 __device__ __forceinline__ float4 mlp_input(const MlpArgs& a, int64_t gp, int k) {
@@ -71,11 +92,11 @@ __device__ __forceinline__ float4 mlp_input(const MlpArgs& a, int64_t gp, int k)
     int set;
     const float* v = mlp_point(a, gp, set);
     const int f = k < a.F ? k : k - a.F;
-    const float ox = __ldg(&a.omega[3 * f]), oy = __ldg(&a.omega[3 * f + 1]), ot = __ldg(&a.omega[3 * f + 2]);
+    const float4 g = rff_arg(a, v, f);
     float sn, cs;
-    sincosf(ox * v[0] + oy * v[1] + ot * v[2], &sn, &cs);
+    sincosf(g.x, &sn, &cs);
     const float val = k < a.F ? cs : sn, d = k < a.F ? -sn : cs;
-    return make_float4(val, d * ox, d * oy, d * ot);
+    return make_float4(val, d * g.y, d * g.z, d * g.w);
   }
   const float* r = a.act_in + gp * 4 * (int64_t)a.in + k;
   const float y0 = r[0], sd = 1.f - y0 * y0;
@@ -189,7 +210,30 @@ struct MlpBwdArgs {
   const float* cot;         // [P][4][out] cotangents of the layer's pre-activations
   const float* act_prev;    // [P][4][in] (y0, z) of the previous hidden layer
   float* cot_prev;          // [P][4][in] cotangents of the previous layer's pre-activations
+  // first layer with the periodic map: the input cotangents are contracted with the features'
+  // derivative by the learned period and summed into *tgrad (FP64) instead of being stored
+  MlpArgs x;
+  double* tgrad;
 };
+
+// d/dT of the four rows of RFF feature k of point v (periodic map): T enters through
+// phi = 2 pi t / T in u4 = sin phi, u5 = cos phi and in their t-derivatives.
+__device__ __forceinline__ float4 rff_dfeature_dT(const MlpArgs& a, const float* v, int k) {
+  const int f = k < a.F ? k : k - a.F;
+  const float4 g = rff_arg(a, v, f);
+  const float T = __ldg(a.period), w = 6.28318530717959f / T, ph = w * v[2];
+  float st, ct;
+  sincosf(ph, &st, &ct);
+  const float o4 = __ldg(&a.omega[6 * f + 4]), o5 = __ldg(&a.omega[6 * f + 5]);
+  const float dphi = -ph / T;                                  // d phi / dT
+  const float daT = o4 * ct * dphi - o5 * st * dphi;           // d a / dT
+  const float ddtT = -w / T * (o4 * ct - o5 * st) + w * (-o4 * st - o5 * ct) * dphi;   // d (da/dt) / dT
+  float sn, cs;
+  sincosf(g.x, &sn, &cs);
+  if (k < a.F)   // rows: cos a, -sin a da_d
+    return make_float4(-sn * daT, -cs * daT * g.y, -cs * daT * g.z, -cs * daT * g.w - sn * ddtT);
+  return make_float4(cs * daT, -sn * daT * g.y, -sn * daT * g.z, -sn * daT * g.w + cs * ddtT);
+}
 
 // dU = cot W (the cotangents of the previous layer's outputs y0, y_d), then through that
 // layer's tanh: cot_prev = (s dU0 - 2 y0 s sum_d z_d dU_d, s dU_d).
@@ -235,6 +279,28 @@ __global__ void __launch_bounds__(MT_THREADS) mlp_bwd_dx_kernel(MlpBwdArgs a) {
 #pragma unroll
             for (int j = 0; j < 4; ++j) acc[i][s][j] = fmaf(cv[i][s], wv[j], acc[i][s][j]);
       }
+    }
+    if (a.tgrad) {
+      // periodic map: sum over the tile of dL/dr_s[k] dr_s[k]/dT
+      float tg = 0.f;
+#pragma unroll
+      for (int i = 0; i < 2; ++i) {
+        const int64_t gp = p0 + tp * 2 + i;
+        if (gp >= a.ptot) continue;
+        int set;
+        const float* v = mlp_point(a.x, gp, set);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int k = n0 + to * 4 + j;
+          if (k >= a.in) continue;
+          const float4 d = rff_dfeature_dT(a.x, v, k);
+          tg += acc[i][0][j] * d.x + acc[i][1][j] * d.y + acc[i][2][j] * d.z + acc[i][3][j] * d.w;
+        }
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) tg += __shfl_xor_sync(0xffffffffu, tg, o);
+      if ((tid & 31) == 0) atomicAdd(a.tgrad, (double)tg);
+      continue;
     }
 #pragma unroll
     for (int i = 0; i < 2; ++i) {
@@ -327,6 +393,13 @@ __global__ void __launch_bounds__(MT_THREADS) mlp_dw_kernel(MlpDwArgs a) {
     }
     if (i0 == 0 && tx == 0) slot[a.b_off + o] = db[u];
   }
+}
+
+// The learned period's gradient into the weight-gradient partial slots: chunk 0 takes the sum,
+// the others 0 (the reduction adds all chunks).
+__global__ void mlp_period_fin_kernel(const double* tgrad, float* part, int64_t nW, int64_t t_off, int nchunks) {
+  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nchunks; b += gridDim.x * blockDim.x)
+    part[(int64_t)b * nW + t_off] = b == 0 ? (float)*tgrad : 0.f;
 }
 
 }  // namespace qpm

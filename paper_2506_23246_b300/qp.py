@@ -35,7 +35,7 @@ class QPError(RuntimeError):
 class QPCircuit(ctypes.Structure):
     _fields_ = [(k, ctypes.c_int32) for k in (
         "n_qubits", "n_layers", "n_readout", "ansatz", "enc", "scale", "premap", "n_direct",
-        "rff_freqs", "mlp_width", "mlp_depth")]
+        "rff_freqs", "mlp_width", "mlp_depth", "periodic")]
 
 
 class QPProblem(ctypes.Structure):
@@ -118,7 +118,8 @@ def _check(code, what):
 def make_circuit(c):
     return QPCircuit(c["n_qubits"], c["n_layers"], c["n_readout"], ANSATZ[c["ansatz"]],
                      ENC[c["enc"]], SCALE[c["scale"]], PREMAP[c["premap"]], c.get("n_direct", 3),
-                     c.get("rff_freqs", 0), c.get("mlp_width", 0), c.get("mlp_depth", 0))
+                     c.get("rff_freqs", 0), c.get("mlp_width", 0), c.get("mlp_depth", 0),
+                     1 if c.get("periodic") else 0)
 
 
 def make_problem(p):

@@ -587,12 +587,15 @@ def test_deep_premap_loss_grad(torch_cuda, oracle, n, L, F, H, depth, path):
 
 
 def test_paper_hybrid_net_forward_and_grad(torch_cuda, oracle):
-    """The paper's hybrid network (Sec. 2.2-2.3, Table 1): RFF with 128 frequencies (256
-    features), three tanh layers of width 128, a linear layer to 7 angles, 7 qubits, 4 strongly
-    entangling layers, head to (Ez, Hx, Hy). Fields and input derivatives on a ragged batch,
-    then loss terms and gradients spread over all layers."""
+    """The paper's hybrid network (Sec. 2.2-2.3, Table 1): the periodic input map with a learned
+    period, RFF with 128 frequencies (256 features), three tanh layers of width 128, a linear
+    layer to 7 angles, 7 qubits, 4 strongly entangling layers, head to (Ez, Hx, Hy): 66,848
+    classical and 84 quantum parameters. Fields and input derivatives on a ragged batch, then
+    loss terms and gradients spread over all layers."""
     circ = W.circuit(7, 4, 7, ansatz="strong_rot", enc="rx", scale="acos", premap="rff_mlp",
-                     rff_freqs=128, mlp_width=128, mlp_depth=3)
+                     rff_freqs=128, mlp_width=128, mlp_depth=3, periodic=True)
+    lay = oracle.param_layout(circ)
+    assert lay["total"] - lay["fixed"] - 84 == 66848
     params = W.init_params(circ, 11)
     pts = W.uniform_points(150, 12, 1.5)
     _forward_check(torch_cuda, oracle, circ, params, pts)
@@ -638,3 +641,20 @@ def test_symmetry_penalty_loss_grad(torch_cuda, oracle, n, medium):
     assert plan.path == "simt" and loss.shape[0] == 9 + 3 + 1 and loss[-1] > 0
     with pytest.raises(qp.QPError):
         qp.Plan(circ, prob, path="gemm_split")
+
+
+@pytest.mark.parametrize("n,path,depth", [(5, "simt", 2), (8, "gemm_split", 1), (7, "simt", 3)])
+def test_periodic_map_loss_grad(torch_cuda, oracle, n, path, depth):
+    """The periodic input map (Eqs. 25-26: space over the domain lengths, time over a learned
+    period T) before the RFF layer: fields and input derivatives, loss terms, and gradients
+    including the learned period's, against the oracle on both paths."""
+    circ = W.circuit(n, 2, n, ansatz="strong_rot", enc="rx", scale="acos", premap="rff_mlp",
+                     rff_freqs=12, mlp_width=16, mlp_depth=depth, periodic=True)
+    params = W.init_params(circ, n + 100)
+    pts = W.uniform_points(90, n + 101, 1.5)
+    _forward_check(torch_cuda, oracle, circ, params, pts, path=path)
+    prob = W.problem("vacuum", w_energy=10.0, energy_slice=16, energy_nt=2)
+    sets = {"colloc": W.uniform_points(40, n + 102, 1.5), "ic": W.ic_points_uniform(16, n + 103)}
+    idx = _mlp_sample(oracle, circ, 6, n)
+    assert W.param_offsets(circ)["period"][0] in idx
+    _loss_grad_check(torch_cuda, oracle, circ, prob, params, sets, idx, path=path)
