@@ -431,8 +431,12 @@ def run_native(a):
 
 def run_c5(a):
     """32 uneven instances (n ~ U{4..10}, L ~ U{2..8}, B ~ 2^U(10, 16) collocation points plus
-    B/16 IC points, RFF64+MLP32 premap, strongly entangling) in one qp_batch_step per step,
-    against the same instances called one after the other on one stream."""
+    B/16 IC points, RFF64+MLP32 premap, strongly entangling) in one qp_batch_step per step:
+    the gate-by-gate instances (n <= 7) in the multi-instance launch with the shape the tuner
+    chose (tuned once before the timed region), the tensor-core instances as their own calls
+    on worker streams. Against the same call without the multi-instance launch (every
+    instance its own call on the worker streams) and against the instances called one after
+    the other on one stream."""
     import torch
     rank, world, local = _dist()
     if world > 1:
@@ -463,6 +467,9 @@ def run_c5(a):
     def batched():
         qp.batch_step(plans, params, sets, outs=outs)
 
+    def streams_only():
+        qp.batch_step(plans, params, sets, outs=outs, grouped=False)
+
     def sequential():
         for pl, p, st, o in zip(plans, params, sets, outs):
             pl.loss_grad(p, st, out=o)
@@ -485,13 +492,17 @@ def run_c5(a):
             ms = float(t.item())
         return ms
 
+    tune = qp.batch_tune(plans, params, sets, outs=outs)
+    torch.cuda.synchronize()
     clk = ClockSampler(local)
     clk.start()
     time.sleep(0.3)
     ms_b = timed(batched)
+    launches = sum(pl.last_launch_count() for pl in plans)
+    ms_u = timed(streams_only)
     ms_s = timed(sequential)
     clocks = clk.stop()
-    launches = sum(pl.last_launch_count() for pl in plans)
+    grouped = sum(1 for pl in plans if pl.path == "simt")
     if rank == 0:
         print(json.dumps({
             "metric": "collocation pts/s, 32 uneven QPINN instances per step (fwd+d/dx,dy,dt+adjoint grad)",
@@ -502,7 +513,11 @@ def run_c5(a):
                                    "colloc + B/16 IC, RFF64+MLP32, strongly entangling, vacuum",
                        "colloc_per_gpu": ncol, "instances": len(plans),
                        "paths": sorted(set(pl.path for pl in plans)),
+                       "grouped_instances": grouped,
+                       "multi_launch_shape": {"warps_per_cta": tune[0], "tasks_per_warp_and_item": tune[1]},
                        "l2": "flushed between timed steps (256 MiB write)"},
+            "streams_only": {"ms_per_step": ms_u, "value": world * ncol / (ms_u / 1000.0),
+                             "speedup_batched": ms_u / ms_b},
             "sequential": {"ms_per_step": ms_s, "value": world * ncol / (ms_s / 1000.0),
                            "speedup_batched": ms_s / ms_b},
             "gpu_launches": launches * a.steps, "roofline": None, "clocks": clocks}))

@@ -236,15 +236,45 @@ typedef struct {
 
 /* Loss and gradient of `count` independent instances (the paper's experiments train many
  * configurations; each instance is its own circuit, problem and point sets) in one call:
- * instance i is qp_loss_grad(plans[i], args[i]...). The instances run concurrently on
- * library-owned streams forked from `stream` (longest first, each on the least loaded
- * stream) and joined back into it, so work issued on `stream` after the call sees every
- * result; the call is capturable into a CUDA graph on `stream`. Every plan must have its
- * own workspace (the same plan may not appear twice). All arguments are checked before any
- * launch (QP_ERR_INVALID_ARG, QP_ERR_BUFFER_TOO_SMALL, QP_ERR_UNSUPPORTED as qp_loss_grad);
- * the first instance that fails to launch stops the call with its status, after the
- * streams are joined. */
+ * instance i is qp_loss_grad(plans[i], args[i]...). No counterpart in the paper, which trains
+ * one configuration per run; the uneven multi-configuration workload is a throughput target
+ * of this library.
+ *
+ * Instances on the gate-by-gate path (QP_PATH_SIMT_FP32, points to evaluate, no symmetry
+ * penalty) share one persistent statevector launch per qubit range (1-7 and 8-10 qubits, up
+ * to 64 instances each): every instance's premap and argument block first, then CTAs take
+ * items of consecutive warp-tasks (point groups) of any instance from one atomic counter, with
+ * the warps per CTA and the tasks per item that qp_batch_tune chose for this mix (12 warps and
+ * 4 tasks per warp until then), then every instance's premap backward and reduction. Each
+ * item writes its own partial slot, so an instance's loss and gradient are summed over its
+ * items (values equal to qp_loss_grad's up to FP32 summation order). The other instances
+ * (tensor-core path, symmetry penalty, empty) run as ordinary qp_loss_grad calls. The grouped
+ * work and those calls run concurrently on library-owned streams forked from `stream` (the
+ * longest call first, each on the least loaded stream) and joined back into it, so work
+ * issued on `stream` after the call sees every result; the call is capturable into a CUDA
+ * graph on `stream`. Every plan must have its own workspace (the same plan may not appear
+ * twice). All arguments are checked before any launch (QP_ERR_INVALID_ARG,
+ * QP_ERR_BUFFER_TOO_SMALL, QP_ERR_UNSUPPORTED as qp_loss_grad); the first launch that fails
+ * stops the call with its status, after the streams are joined. */
 qp_status qp_batch_step(qp_plan* const* plans, int32_t count, const qp_step_args* args, void* stream);
+
+/* qp_batch_step with flags: QP_BATCH_NO_GROUPING runs every instance as its own qp_loss_grad
+ * call on the worker streams (no multi-instance launch). Other bits: QP_ERR_INVALID_ARG. */
+typedef enum { QP_BATCH_NO_GROUPING = 1 } qp_batch_flags;
+qp_status qp_batch_step_flags(qp_plan* const* plans, int32_t count, const qp_step_args* args, void* stream,
+                              uint32_t flags);
+
+/* Tuner of the multi-instance launch: runs the grouped instances of this batch (as
+ * qp_batch_step would group them) once untimed and once timed with CUDA events on `stream` for
+ * every candidate shape (4, 8 or 12 warps per CTA x 1, 4 or 16 warp-tasks per warp and item),
+ * and stores the fastest in every grouped plan, keyed by the mix's signature (qubits, layers,
+ * readout, energy slices, ansatz and the power-of-two bucket of each instance's task count, in
+ * order); qp_batch_step uses it while the signature matches. The outputs in `args` are
+ * overwritten with this batch's results. Synchronises `stream`; QP_ERR_INVALID_ARG while the
+ * stream is capturing. chosen (may be NULL): [0] warps per CTA, [1] tasks per warp and item
+ * (0, 0 when no instance is grouped). */
+qp_status qp_batch_tune(qp_plan* const* plans, int32_t count, const qp_step_args* args, void* stream,
+                        int32_t* chosen);
 
 /* Synchronise the stream of the last compute call on this plan and return that call's device
  * status word (QP_OK, QP_ERR_NONFINITE or QP_ERR_TIMEOUT; QP_OK before the first call) or

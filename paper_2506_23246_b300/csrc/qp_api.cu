@@ -43,6 +43,10 @@ struct qp_plan {
   int64_t n_params = 0, circ_off = 0, head_off = 0, mlp_off = 0, mlp_count = 0, nfixed = 0;
   int32_t nE = 0;   // gate-gradient partial sums per block: 3 n L Pauli sums + L CRZ sums
   uint32_t wait_limit = 0;   // pipeline-wait polls of the fused forward (0: the kernel's default)
+  // multi-instance launch (qp_batch_step): the tuned shape of the last batch this plan was tuned
+  // in, keyed by that batch's signature (0: none)
+  uint64_t mt_sig = 0;
+  int32_t mt_warps = 0, mt_items = 0;
   void* ws = nullptr;
   size_t ws_bytes = 0;
   int32_t last_launches = 0;
@@ -106,6 +110,7 @@ struct WsLayout {
   size_t mact, mcot;   // layer-by-layer premap: hidden activations, two cotangent buffers
   size_t sxb, sF, sgs, sge, spart;   // symmetry penalty: set-2 points, fields, cotangents, sums
   size_t mtg;                        // periodic map: FP64 sum of the learned period's gradient
+  size_t desc;                       // multi-instance launch: the instance's argument block
   size_t dW, dphi, dU, dG, dY, dpart, dWT, dmu, dW16, dcs, dgs, dgates, total;
 };
 
@@ -246,6 +251,7 @@ WsLayout ws_layout(const qp_plan* pl, int64_t P0) {
   w.sge = o; o = al256(o + (sym ? (size_t)2 * P0 * 3 * 4 : 0));
   w.spart = o; o = al256(o + (sym ? (size_t)pl->sm_count * 4 * 8 : 0));
   w.mtg = o; o = al256(o + (pl->c.periodic ? 8 : 0));
+  w.desc = o; o = al256(o + (dense_path(pl) ? 0 : sizeof(QPCircArgs)));
   const size_t dim = (size_t)1 << n;
   const bool dn = dense_path(pl);
   w.dW = o; o = al256(o + (dn ? 2 * (2 * dim) * dim * 4 : 0));
@@ -813,8 +819,10 @@ static void fill_circ(qp_plan* pl, QPCircArgs& a, const WsLayout& w, const float
   a.crz = qp_has_crz(pl->c.ansatz) ? (const float2*)(ws + w.crz) : nullptr;
 }
 
+// nblk: block partial slots to sum (-1: the plan's statevector-kernel grid)
 static qp_status launch_reduce(qp_plan* pl, const WsLayout& w, const float* d_params, const int64_t npts[3],
-                               double* d_loss, float* d_grad, bool mlp, cudaStream_t s, int nsym = 0);
+                               double* d_loss, float* d_grad, bool mlp, cudaStream_t s, int nsym = 0,
+                               int64_t nblk = -1);
 static qp_status launch_premap_bwd(qp_plan* pl, const WsLayout& w, const float* d_params,
                                    const float* const pts[3], const int64_t npts[3], cudaStream_t s);
 
@@ -1324,7 +1332,8 @@ static qp_status launch_premap_bwd(qp_plan* pl, const WsLayout& w, const float* 
 }
 
 static qp_status launch_reduce(qp_plan* pl, const WsLayout& w, const float* d_params, const int64_t npts[3],
-                               double* d_loss, float* d_grad, bool mlp, cudaStream_t s, int nsym) {
+                               double* d_loss, float* d_grad, bool mlp, cudaStream_t s, int nsym,
+                               int64_t nblk) {
   char* ws = (char*)pl->ws;
   qpk::ReduceArgs ra;
   ra.sym_part = nsym > 0 ? (const double*)(ws + w.spart) : nullptr;
@@ -1332,7 +1341,7 @@ static qp_status launch_reduce(qp_plan* pl, const WsLayout& w, const float* d_pa
   ra.w_sym = pl->p.w_sym;
   ra.blk_loss = (const double*)(ws + w.blk_loss);
   ra.blk_grad = (const float*)(ws + w.blk_grad);
-  ra.nblk = pl->blocks_grad;
+  ra.nblk = nblk >= 0 ? (int32_t)nblk : pl->blocks_grad;
   ra.loss_stride = QP_NLP + pl->p.energy_nt;
   ra.grad_stride = pl->nE + 3 * pl->c.n_readout + 3;
   ra.nE = pl->nE;
@@ -1433,9 +1442,12 @@ qp_status qp_count_dielectric(qp_plan* pl, const float* d_pts, int64_t n, int64_
 namespace {
 // Library-owned worker streams of qp_batch_step, created once per device.
 constexpr int QP_BATCH_STREAMS = 8;
+constexpr int QP_GROUP_STREAMS = 4;   // streams of the multi-instance launches (one per qubit count in turn)
 struct BatchStreams {
   cudaStream_t st[QP_BATCH_STREAMS];
   cudaEvent_t fork, join[QP_BATCH_STREAMS];
+  cudaStream_t gst[QP_GROUP_STREAMS];
+  cudaEvent_t gfork, gjoin[QP_GROUP_STREAMS];
   bool ok = false;
 };
 std::mutex g_batch_mu;
@@ -1452,13 +1464,205 @@ BatchStreams* batch_streams() {
       if (cudaEventCreateWithFlags(&b.join[i], cudaEventDisableTiming) != cudaSuccess) return nullptr;
     }
     if (cudaEventCreateWithFlags(&b.fork, cudaEventDisableTiming) != cudaSuccess) return nullptr;
+    for (int i = 0; i < QP_GROUP_STREAMS; ++i) {
+      if (cudaStreamCreateWithFlags(&b.gst[i], cudaStreamNonBlocking) != cudaSuccess) return nullptr;
+      if (cudaEventCreateWithFlags(&b.gjoin[i], cudaEventDisableTiming) != cudaSuccess) return nullptr;
+    }
+    if (cudaEventCreateWithFlags(&b.gfork, cudaEventDisableTiming) != cudaSuccess) return nullptr;
     b.ok = true;
   }
   return &b;
 }
 }  // namespace
 
-qp_status qp_batch_step(qp_plan* const* plans, int32_t count, const qp_step_args* args, void* stream) {
+// ---------------------------------------------------------------- multi-instance launch
+namespace {
+constexpr int kMultiK[3] = {1, 4, 16};      // tuner candidates: tasks per item = warps x K
+constexpr int kMultiW[3] = {4, 8, 12};      // tuner candidates: warps per CTA
+constexpr int kMultiDefW = 12, kMultiDefK = 4;
+
+// Instances that join the multi-instance launch: gate-by-gate path, points to evaluate, no
+// symmetry penalty (its mirrored pre-pass stays with the single call).
+bool groupable(const qp_plan* pl, const qp_step_args& a) {
+  const int64_t P = a.batch.n_colloc + a.batch.n_ic + a.batch.n_bc;
+  return !dense_path(pl) && P > 0 && !(pl->p.w_sym > 0.f);
+}
+
+// Signature of a batch's grouped instances: qubits, layers, readout, energy slices and the
+// power-of-two bucket of the task count, in order.
+uint64_t group_signature(qp_plan* const* plans, const qp_step_args* args, const std::vector<int32_t>& idx) {
+  uint64_t h = 1469598103934665603ull;
+  auto mix = [&](uint64_t v) { h = (h ^ v) * 1099511628211ull; };
+  for (int32_t i : idx) {
+    const qp_plan* pl = plans[i];
+    const int ppw = geo_ppw(pl->c.n_qubits);
+    const qp_batch& b = args[i].batch;
+    const int64_t t = (b.n_colloc + ppw - 1) / ppw + (b.n_ic + ppw - 1) / ppw + (b.n_bc + ppw - 1) / ppw;
+    int lg = 0;
+    while ((1LL << lg) < t) ++lg;
+    mix((uint64_t)pl->c.n_qubits);
+    mix((uint64_t)pl->c.n_layers);
+    mix((uint64_t)pl->c.n_readout);
+    mix((uint64_t)pl->p.energy_nt);
+    mix((uint64_t)pl->c.ansatz);
+    mix((uint64_t)lg);
+  }
+  return h;
+}
+
+void* multi_kernel_ptr(int n) {
+  switch (n) {
+#define QP_CASE(N) case N: return (void*)qpk::circuit_multi_kernel<N>;
+    QP_CASE(1) QP_CASE(2) QP_CASE(3) QP_CASE(4) QP_CASE(5)
+    QP_CASE(6) QP_CASE(7) QP_CASE(8) QP_CASE(9) QP_CASE(10)
+#undef QP_CASE
+  }
+  return nullptr;
+}
+
+// The grouped instances' loss and gradient: every instance's front launches and argument
+// block on stream st[0], one persistent launch per qubit count and QP_MULTI_MAX instances (the
+// counts on the streams st[0 .. nst-1] in turn, after an event), then, back on st[0] after the
+// launches, every instance's premap backward and reduction over its items.
+qp_status launch_grouped(qp_plan* const* plans, const qp_step_args* args, const std::vector<int32_t>& idx,
+                         int W, int K, const cudaStream_t* st, int nst, cudaEvent_t fork, const cudaEvent_t* join,
+                         int* launches_out) {
+  const cudaStream_t s = st[0];
+  struct Inst {
+    int32_t i;
+    WsLayout w;
+    const float* pts[3];
+    int64_t npts[3];
+    QPCircArgs* dst;
+    int64_t tpi = 0, items = 0;
+  };
+  std::vector<Inst> v;
+  v.reserve(idx.size());
+  int launches = 0;
+  int optin = 0;
+  for (int32_t i : idx) {
+    qp_plan* pl = plans[i];
+    const qp_batch* b = &args[i].batch;
+    Inst in;
+    in.i = i;
+    in.pts[0] = b->colloc; in.pts[1] = b->ic; in.pts[2] = b->bc;
+    in.npts[0] = b->n_colloc; in.npts[1] = b->n_ic; in.npts[2] = b->n_bc;
+    in.w = ws_layout(pl, in.npts[0] + in.npts[1] + in.npts[2]);
+    pl->cur_norm[0] = b->norm_colloc; pl->cur_norm[1] = b->norm_ic; pl->cur_norm[2] = b->norm_bc;
+    pl->cur_norm_diel = b->norm_colloc > 0 ? b->norm_diel : 0;
+    pl->cur_colloc_off = b->colloc_offset;
+    pl->last_stream = s;
+    pl->last_status = (const int32_t*)((char*)pl->ws + in.w.status);
+    const qp_status st = launch_front(pl, args[i].d_params, in.pts, in.npts, in.w, s, true);
+    if (st != QP_OK) return st;
+    pl->last_launches = front_launches(pl);
+    in.dst = (QPCircArgs*)((char*)pl->ws + in.w.desc);
+    v.push_back(in);
+    if (optin == 0) cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, pl->device);
+  }
+  // argument blocks on st[0]; then one launch per (qubit count, chunk of QP_MULTI_MAX
+  // instances), the counts spread over the streams once st[0]'s work so far is done
+  struct Launch {
+    void* fn;
+    int64_t grid;
+    int warps, smem;
+    qpk::QPMultiArgs ma;
+    qp_plan* owner;
+  };
+  std::vector<Launch> ls;
+  for (int nq = 1; nq <= QP_MAXQ; ++nq) {
+    std::vector<int> mem;
+    for (int k = 0; k < (int)v.size(); ++k)
+      if (plans[v[k].i]->c.n_qubits == nq) mem.push_back(k);
+    for (size_t c0 = 0; c0 < mem.size(); c0 += QP_MULTI_MAX) {
+      const size_t c1 = std::min(mem.size(), c0 + QP_MULTI_MAX);
+      // warps per CTA: the largest up to W whose shared-memory layout fits every member
+      int Wc = W, smem = 0;
+      for (; Wc >= 1; --Wc) {
+        smem = 0;
+        for (size_t k = c0; k < c1; ++k) {
+          const qp_plan* pl = plans[v[mem[k]].i];
+          const qpk::SmemLayout lay = qpk::smem_layout(nq, pl->c.n_layers, pl->c.n_readout, pl->p.energy_nt, Wc,
+                                                       pl->sstride_grad, geo_ppw(nq), pl->nE, (int)sizeof(QPCircArgs));
+          smem = std::max(smem, lay.total);
+        }
+        if (smem <= optin - 1024) break;   // the kernel's static shared memory (item index)
+      }
+      if (Wc < 1) return QP_ERR_UNSUPPORTED;
+      Launch L;
+      std::memset(&L.ma, 0, sizeof(L.ma));
+      L.ma.count = (int32_t)(c1 - c0);
+      const Inst& f = v[mem[c0]];
+      L.owner = plans[f.i];
+      L.ma.queue = (unsigned long long*)((char*)plans[f.i]->ws + f.w.status + 192);
+      int64_t acc = 0;
+      for (size_t k = c0; k < c1; ++k) {
+        Inst& in = v[mem[k]];
+        qp_plan* pl = plans[in.i];
+        QPCircArgs a;
+        fill_circ(pl, a, in.w, args[in.i].d_params, in.pts, in.npts, true);
+        a.want_dtheta = pl->c.premap == QP_PREMAP_RFF_MLP ? 1 : 0;
+        const int64_t tasks = a.task_end[2];
+        // at most the plan's partial slots per instance
+        const int64_t minp = (tasks + pl->blocks_grad - 1) / pl->blocks_grad;
+        in.tpi = std::max<int64_t>((int64_t)Wc * K, minp);
+        in.items = (tasks + in.tpi - 1) / in.tpi;
+        qpk::store_desc_kernel<<<1, 256, 0, s>>>(a, in.dst, k == c0 ? L.ma.queue : nullptr);
+        if (cudaGetLastError() != cudaSuccess) return QP_ERR_CUDA;
+        pl->last_launches += 1;
+        L.ma.desc[k - c0] = in.dst;
+        L.ma.tasks_per_item[k - c0] = (int32_t)in.tpi;
+        acc += in.items;
+        L.ma.item_end[k - c0] = acc;
+      }
+      L.fn = multi_kernel_ptr(nq);
+      if (raise_smem_limit(L.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess) return QP_ERR_CUDA;
+      int per_sm = 0;
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, L.fn, Wc * 32, smem);
+      if (per_sm < 1) per_sm = 1;
+      const int64_t cap = (int64_t)plans[f.i]->sm_count * per_sm;
+      L.grid = acc < cap ? acc : cap;
+      L.warps = Wc;
+      L.smem = smem;
+      if (L.grid > 0) ls.push_back(L);
+    }
+  }
+  const int ns = std::min<int>(nst, (int)ls.size());
+  if (ns > 1) {
+    if (cudaEventRecord(fork, s) != cudaSuccess) return QP_ERR_CUDA;
+    for (int j = 1; j < ns; ++j)
+      if (cudaStreamWaitEvent(st[j], fork, 0) != cudaSuccess) return QP_ERR_CUDA;
+  }
+  for (size_t k = 0; k < ls.size(); ++k) {
+    Launch& L = ls[k];
+    void* kargs[] = {&L.ma};
+    if (cudaLaunchKernel(L.fn, dim3((unsigned)L.grid), dim3(L.warps * 32), kargs, L.smem, st[k % ns]) != cudaSuccess)
+      return QP_ERR_CUDA;
+    L.owner->last_launches += 1;
+    launches += 1;
+  }
+  for (int j = 1; j < ns; ++j) {
+    if (cudaEventRecord(join[j], st[j]) != cudaSuccess) return QP_ERR_CUDA;
+    if (cudaStreamWaitEvent(s, join[j], 0) != cudaSuccess) return QP_ERR_CUDA;
+  }
+  for (const Inst& in : v) {
+    qp_plan* pl = plans[in.i];
+    const bool mlp = pl->c.premap == QP_PREMAP_RFF_MLP;
+    if (mlp) {
+      const qp_status stb = launch_premap_bwd(pl, in.w, args[in.i].d_params, in.pts, in.npts, s);
+      if (stb != QP_OK) return stb;
+      pl->last_launches += premap_bwd_launches(pl);
+    }
+    const qp_status str = launch_reduce(pl, in.w, args[in.i].d_params, in.npts, args[in.i].d_loss,
+                                        args[in.i].d_grad, mlp, s, 0, in.items);
+    if (str != QP_OK) return str;
+    pl->last_launches += 1;
+  }
+  if (launches_out) *launches_out = launches;
+  return cuda_status(cudaGetLastError());
+}
+
+qp_status check_batch(qp_plan* const* plans, int32_t count, const qp_step_args* args) {
   if (count < 0 || (count > 0 && (!plans || !args))) return QP_ERR_INVALID_ARG;
   for (int32_t i = 0; i < count; ++i) {
     for (int32_t j = 0; j < i; ++j)
@@ -1466,32 +1670,57 @@ qp_status qp_batch_step(qp_plan* const* plans, int32_t count, const qp_step_args
     const qp_status c = check_loss_args(plans[i], args[i].d_params, &args[i].batch, args[i].d_loss, args[i].d_grad);
     if (c != QP_OK) return c;
   }
+  return QP_OK;
+}
+}  // namespace
+
+qp_status qp_batch_step_flags(qp_plan* const* plans, int32_t count, const qp_step_args* args, void* stream,
+                              uint32_t flags) {
+  if (flags & ~(uint32_t)QP_BATCH_NO_GROUPING) return QP_ERR_INVALID_ARG;
+  const qp_status chk = check_batch(plans, count, args);
+  if (chk != QP_OK) return chk;
   if (count == 0) return QP_OK;
   BatchStreams* bs = batch_streams();
   if (!bs) return QP_ERR_CUDA;
   cudaStream_t s = (cudaStream_t)stream;
-  // longest first, each onto the least loaded stream (work ~ rows x layers x qubits x 2^n)
-  std::vector<int32_t> order(count);
-  std::vector<double> cost(count);
+  std::vector<int32_t> grouped, rest;
   for (int32_t i = 0; i < count; ++i) {
+    if (!(flags & QP_BATCH_NO_GROUPING) && groupable(plans[i], args[i])) grouped.push_back(i);
+    else rest.push_back(i);
+  }
+  // longest first, each onto the least loaded stream (work ~ rows x layers x qubits x 2^n); the
+  // grouped instances count as one job on stream 0
+  auto cost_of = [&](int32_t i) {
     const qp_batch& b = args[i].batch;
     const qp_circuit& c = plans[i]->c;
-    cost[i] = (double)(4 * b.n_colloc + b.n_ic + b.n_bc + 1) * c.n_layers * c.n_qubits * (double)(1 << c.n_qubits);
-    order[i] = i;
-  }
-  std::sort(order.begin(), order.end(), [&](int32_t x, int32_t y) { return cost[x] > cost[y]; });
-  const int nst = count < QP_BATCH_STREAMS ? count : QP_BATCH_STREAMS;
+    return (double)(4 * b.n_colloc + b.n_ic + b.n_bc + 1) * c.n_layers * c.n_qubits * (double)(1 << c.n_qubits);
+  };
+  std::vector<int32_t> order(rest);
+  std::sort(order.begin(), order.end(), [&](int32_t x, int32_t y) { return cost_of(x) > cost_of(y); });
+  const int jobs = (int)rest.size() + (grouped.empty() ? 0 : 1);
+  const int nst = jobs < QP_BATCH_STREAMS ? jobs : QP_BATCH_STREAMS;
   double load[QP_BATCH_STREAMS] = {0};
   if (cudaEventRecord(bs->fork, s) != cudaSuccess) return QP_ERR_CUDA;
   for (int k = 0; k < nst; ++k)
     if (cudaStreamWaitEvent(bs->st[k], bs->fork, 0) != cudaSuccess) return QP_ERR_CUDA;
   qp_status st = QP_OK;
-  for (int32_t oi = 0; oi < count && st == QP_OK; ++oi) {
+  if (!grouped.empty()) {
+    double gc = 0.0;
+    for (int32_t i : grouped) gc += cost_of(i);
+    load[0] = gc;
+    const qp_plan* p0 = plans[grouped[0]];
+    const uint64_t sig = group_signature(plans, args, grouped);
+    const bool tuned = p0->mt_sig == sig && p0->mt_warps > 0;
+    cudaStream_t gs[QP_GROUP_STREAMS] = {bs->st[0], bs->gst[1], bs->gst[2], bs->gst[3]};
+    st = launch_grouped(plans, args, grouped, tuned ? p0->mt_warps : kMultiDefW, tuned ? p0->mt_items : kMultiDefK,
+                        gs, QP_GROUP_STREAMS, bs->gfork, bs->gjoin, nullptr);
+  }
+  for (size_t oi = 0; oi < order.size() && st == QP_OK; ++oi) {
     const int32_t i = order[oi];
     int k = 0;
     for (int q = 1; q < nst; ++q)
       if (load[q] < load[k]) k = q;
-    load[k] += cost[i];
+    load[k] += cost_of(i);
     st = qp_loss_grad(plans[i], args[i].d_params, &args[i].batch, args[i].d_loss, args[i].d_grad, bs->st[k]);
   }
   for (int k = 0; k < nst; ++k) {
@@ -1499,6 +1728,63 @@ qp_status qp_batch_step(qp_plan* const* plans, int32_t count, const qp_step_args
     if (cudaStreamWaitEvent(s, bs->join[k], 0) != cudaSuccess) return QP_ERR_CUDA;
   }
   return st;
+}
+
+qp_status qp_batch_step(qp_plan* const* plans, int32_t count, const qp_step_args* args, void* stream) {
+  return qp_batch_step_flags(plans, count, args, stream, 0u);
+}
+
+qp_status qp_batch_tune(qp_plan* const* plans, int32_t count, const qp_step_args* args, void* stream,
+                        int32_t* chosen) {
+  const qp_status chk = check_batch(plans, count, args);
+  if (chk != QP_OK) return chk;
+  std::vector<int32_t> grouped;
+  for (int32_t i = 0; i < count; ++i)
+    if (groupable(plans[i], args[i])) grouped.push_back(i);
+  if (grouped.empty()) {
+    if (chosen) { chosen[0] = 0; chosen[1] = 0; }
+    return QP_OK;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  BatchStreams* bs = batch_streams();
+  if (!bs) return QP_ERR_CUDA;
+  cudaStream_t gs[QP_GROUP_STREAMS] = {s, bs->gst[1], bs->gst[2], bs->gst[3]};
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cs) != cudaSuccess) return QP_ERR_CUDA;
+  if (cs != cudaStreamCaptureStatusNone) return QP_ERR_INVALID_ARG;   // times on the device: not capturable
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess) return QP_ERR_CUDA;
+  if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); return QP_ERR_CUDA; }
+  float best = -1.f;
+  int bw = kMultiDefW, bk = kMultiDefK;
+  qp_status st = QP_OK;
+  for (int wi = 0; wi < 3 && st == QP_OK; ++wi) {
+    for (int ki = 0; ki < 3 && st == QP_OK; ++ki) {
+      // one warm-up run, then the timed one
+      st = launch_grouped(plans, args, grouped, kMultiW[wi], kMultiK[ki], gs, QP_GROUP_STREAMS, bs->gfork,
+                          bs->gjoin, nullptr);
+      if (st != QP_OK) break;
+      if (cudaEventRecord(e0, s) != cudaSuccess) { st = QP_ERR_CUDA; break; }
+      st = launch_grouped(plans, args, grouped, kMultiW[wi], kMultiK[ki], gs, QP_GROUP_STREAMS, bs->gfork,
+                          bs->gjoin, nullptr);
+      if (st != QP_OK) break;
+      if (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) { st = QP_ERR_CUDA; break; }
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) { st = QP_ERR_CUDA; break; }
+      if (best < 0.f || ms < best) { best = ms; bw = kMultiW[wi]; bk = kMultiK[ki]; }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != QP_OK) return st;
+  const uint64_t sig = group_signature(plans, args, grouped);
+  for (int32_t i : grouped) {
+    plans[i]->mt_sig = sig;
+    plans[i]->mt_warps = bw;
+    plans[i]->mt_items = bk;
+  }
+  if (chosen) { chosen[0] = bw; chosen[1] = bk; }
+  return QP_OK;
 }
 
 

@@ -25,10 +25,13 @@ struct SmemLayout {
 __host__ __device__ inline int align16(int x) { return (x + 15) & ~15; }
 
 // Shared-memory layout of the circuit kernel (identical on host and device).
+// head: bytes before the gate table (the schedule; the whole argument block in the
+// multi-instance kernel, whose first member is the schedule).
 __host__ __device__ inline SmemLayout smem_layout(int n, int L, int m, int nt, int warps,
-                                                  int sstride, int ppw, int nE) {
+                                                  int sstride, int ppw, int nE,
+                                                  int head = (int)sizeof(QPSched)) {
   SmemLayout s;
-  int o = align16((int)sizeof(QPSched));
+  int o = align16(head);
   s.off_gates = o; o = align16(o + L * n * 8 * 4);
   s.off_cenc = o; o = align16(o + n * 4 * 4);
   s.off_head = o; o = align16(o + (3 * m + 3) * 4);
@@ -747,6 +750,109 @@ __global__ void __launch_bounds__(384) circuit_kernel(const __grid_constant__ QP
   float* bg = a.blk_grad + (int64_t)blockIdx.x * a.grad_stride;
   for (int i = threadIdx.x; i < a.nE; i += blockDim.x) bg[i] = sh.eacc[i];
   for (int i = threadIdx.x; i < 3 * a.m + 3; i += blockDim.x) bg[a.nE + i] = sh.hacc[i];
+}
+
+// ------------------------------------------------------------------------- multi-instance launch
+// Independent loss evaluations (instances: each its own circuit, problem, parameters and point
+// sets) of one qubit count in one persistent launch. Instance i's warp-tasks are cut into items of
+// tasks_per_item[i] consecutive tasks; a CTA takes the next item from one atomic counter,
+// loads the instance's argument block (schedule included), gate table and head into shared
+// memory when the instance changes, runs the item's tasks on its warps and writes the item's
+// loss and gradient partials to slot (item - first item of the instance) of the instance's
+// block partials, so the instance's reduction sums exactly its items. Items are handed out in
+// increasing order, so a CTA meets every instance in one run of consecutive items.
+#define QP_MULTI_MAX 64
+struct QPMultiArgs {
+  int32_t count;                              // instances of this launch (<= QP_MULTI_MAX)
+  unsigned long long* queue;                  // item counter, zero before the launch
+  const QPCircArgs* desc[QP_MULTI_MAX];       // argument block of each instance (device memory)
+  int64_t item_end[QP_MULTI_MAX];             // cumulative item counts
+  int32_t tasks_per_item[QP_MULTI_MAX];
+};
+
+// The argument block of one instance into device memory (and the item counter zeroed).
+__global__ void store_desc_kernel(const __grid_constant__ QPCircArgs a, QPCircArgs* dst,
+                                  unsigned long long* queue) {
+  const uint32_t* src = reinterpret_cast<const uint32_t*>(&a);
+  uint32_t* d = reinterpret_cast<uint32_t*>(dst);
+  for (int i = threadIdx.x; i < (int)(sizeof(QPCircArgs) / 4); i += blockDim.x) d[i] = src[i];
+  if (queue && threadIdx.x == 0) *queue = 0ull;
+}
+
+template <int NQ>
+__device__ __forceinline__ void multi_tasks(const QPCircArgs& a, const Shared& sh, unsigned char* state,
+                                            int64_t t0, int64_t t1, int warp, int warps, int lane) {
+  using Gm = QPGeo<NQ>;
+  float2* wstate = reinterpret_cast<float2*>(state) + warp * Gm::PPW * a.sstride;
+  for (int64_t t = t0 + warp; t < t1; t += warps) {
+    int set = 0;
+    int64_t base = 0;
+    if (t >= a.task_end[0]) { set = 1; base = a.task_end[0]; }
+    if (t >= a.task_end[1]) { set = 2; base = a.task_end[1]; }
+    run_task<NQ, true>(a, sh, wstate, set, (t - base) * Gm::PPW, lane, set == 0 ? 4 : 1);
+  }
+}
+
+// One qubit count per kernel: the register allocation of the single-instance kernel (a switch
+// over several counts in one kernel is allocated for all of them at once and spills).
+template <int NQ>
+__global__ void __launch_bounds__(384) circuit_multi_kernel(const __grid_constant__ QPMultiArgs m) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ long long s_item;
+  QPCircArgs& A = *reinterpret_cast<QPCircArgs*>(smem);
+  const int warps = blockDim.x >> 5;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t total = m.item_end[m.count - 1];
+  int cur = -1;
+  SmemLayout lay{};
+  Shared sh{};
+  for (;;) {
+    if (threadIdx.x == 0) s_item = (long long)atomicAdd(m.queue, 1ull);
+    __syncthreads();
+    const int64_t item = s_item;
+    if (item >= total) break;
+    int i = 0;
+    while (m.item_end[i] <= item) ++i;
+    const int64_t ib = i > 0 ? m.item_end[i - 1] : 0;
+    if (i != cur) {
+      const uint32_t* src = reinterpret_cast<const uint32_t*>(m.desc[i]);
+      uint32_t* dst = reinterpret_cast<uint32_t*>(smem);
+      for (int k = threadIdx.x; k < (int)(sizeof(QPCircArgs) / 4); k += blockDim.x) dst[k] = __ldg(src + k);
+      __syncthreads();
+      const int n = NQ;
+      lay = smem_layout(n, A.L, A.m, A.pb.energy_nt, warps, A.sstride, QPGeo<NQ>::PPW, A.nE, (int)sizeof(QPCircArgs));
+      float* g = reinterpret_cast<float*>(smem + lay.off_gates);
+      for (int k = threadIdx.x; k < A.L * n * 8; k += blockDim.x) g[k] = A.gates[k];
+      float* c = reinterpret_cast<float*>(smem + lay.off_cenc);
+      for (int k = threadIdx.x; k < n * 4; k += blockDim.x) c[k] = A.cenc ? A.cenc[k] : 0.f;
+      float* h = reinterpret_cast<float*>(smem + lay.off_head);
+      for (int k = threadIdx.x; k < 3 * A.m + 3; k += blockDim.x) h[k] = A.head[k];
+      sh.s = &A.s;
+      sh.gates = g;
+      sh.cenc = c;
+      sh.head = h;
+      sh.eacc = reinterpret_cast<float*>(smem + lay.off_eacc);
+      sh.hacc = reinterpret_cast<float*>(smem + lay.off_hacc);
+      sh.loss = reinterpret_cast<double*>(smem + lay.off_loss);
+      cur = i;
+    }
+    const int nt = A.pb.energy_nt;
+    for (int k = threadIdx.x; k < A.nE; k += blockDim.x) sh.eacc[k] = 0.f;
+    for (int k = threadIdx.x; k < 3 * A.m + 3; k += blockDim.x) sh.hacc[k] = 0.f;
+    for (int k = threadIdx.x; k < QP_NLP + nt; k += blockDim.x) sh.loss[k] = 0.0;
+    __syncthreads();
+    const int64_t ntask = A.task_end[2];
+    const int64_t t0 = (item - ib) * m.tasks_per_item[i];
+    const int64_t t1 = t0 + m.tasks_per_item[i] < ntask ? t0 + m.tasks_per_item[i] : ntask;
+    multi_tasks<NQ>(A, sh, smem + lay.off_state, t0, t1, warp, warps, lane);
+    __syncthreads();
+    const int64_t slot = item - ib;
+    double* bl = A.blk_loss + slot * A.loss_stride;
+    for (int k = threadIdx.x; k < QP_NLP + nt; k += blockDim.x) bl[k] = sh.loss[k];
+    float* bg = A.blk_grad + slot * A.grad_stride;
+    for (int k = threadIdx.x; k < A.nE; k += blockDim.x) bg[k] = sh.eacc[k];
+    for (int k = threadIdx.x; k < 3 * A.m + 3; k += blockDim.x) bg[A.nE + k] = sh.hacc[k];
+  }
 }
 
 }  // namespace qpk

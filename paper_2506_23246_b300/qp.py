@@ -84,6 +84,8 @@ def lib():
         L.qp_loss_grad.argtypes = [P, P, ctypes.POINTER(QPBatch), P, P, P]
         L.qp_count_dielectric.argtypes = [P, P, I64, P, P]
         L.qp_batch_step.argtypes = [ctypes.POINTER(P), I32, ctypes.POINTER(QPStepArgs), P]
+        L.qp_batch_step_flags.argtypes = [ctypes.POINTER(P), I32, ctypes.POINTER(QPStepArgs), P, ctypes.c_uint32]
+        L.qp_batch_tune.argtypes = [ctypes.POINTER(P), I32, ctypes.POINTER(QPStepArgs), P, ctypes.POINTER(I32)]
         L.qp_last_device_error.argtypes = [P]
         L.qp_status_str.argtypes = [I32]
         L.qp_status_str.restype = ctypes.c_char_p
@@ -296,9 +298,10 @@ def bh_indicator(loss_terms, energy_nt, t_max, delta, out=None, stream=None):
     return out
 
 
-def batch_step(plans, params, sets, outs=None, norms=None, stream=None):
-    """Loss and gradient of independent instances in one qp_batch_step call: plans[i] with
-    params[i] on sets[i]; returns [(loss, grad)] in the order given."""
+BATCH_NO_GROUPING = 1
+
+
+def _step_args(plans, params, sets, outs, norms):
     k = len(plans)
     outs = outs or [None] * k
     norms = norms or [None] * k
@@ -312,9 +315,29 @@ def batch_step(plans, params, sets, outs=None, norms=None, stream=None):
         arr[i] = QPStepArgs(_ptr(params[i]), batch, _ptr(loss), _ptr(grad))
         handles[i] = plans[i]._h
         res.append((loss, grad))
+    return handles, arr, keep, res
+
+
+def batch_step(plans, params, sets, outs=None, norms=None, stream=None, grouped=True):
+    """Loss and gradient of independent instances in one qp_batch_step call: plans[i] with
+    params[i] on sets[i]; returns [(loss, grad)] in the order given. grouped=False: every
+    instance as its own call on the worker streams (no multi-instance launch)."""
+    handles, arr, keep, res = _step_args(plans, params, sets, outs, norms)
     s = stream if stream is not None else torch.cuda.current_stream()
-    _check(lib().qp_batch_step(handles, k, arr, ctypes.c_void_p(s.cuda_stream)), "qp_batch_step")
+    flags = 0 if grouped else BATCH_NO_GROUPING
+    _check(lib().qp_batch_step_flags(handles, len(plans), arr, ctypes.c_void_p(s.cuda_stream), flags),
+           "qp_batch_step_flags")
     return res
+
+
+def batch_tune(plans, params, sets, outs=None, norms=None, stream=None):
+    """Time the multi-instance launch shapes on this mix and keep the fastest in its plans
+    (qp_batch_tune); returns (warps per CTA, tasks per warp and item)."""
+    handles, arr, keep, res = _step_args(plans, params, sets, outs, norms)
+    s = stream if stream is not None else torch.cuda.current_stream()
+    ch = (ctypes.c_int32 * 2)()
+    _check(lib().qp_batch_tune(handles, len(plans), arr, ctypes.c_void_p(s.cuda_stream), ch), "qp_batch_tune")
+    return int(ch[0]), int(ch[1])
 
 
 class QPINNLoss(torch.autograd.Function):

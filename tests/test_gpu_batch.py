@@ -120,3 +120,103 @@ def test_batch_step_matches_single_calls(torch_cuda):
     with pytest.raises(qp.QPError):
         qp.batch_step([plans[0], plans[0]], [params[0], params[0]], [sets[0], sets[0]])
     assert qp.batch_step([], [], []) == []
+
+
+TOL = 1e-5
+CHAN_TOL = 1e-4
+
+
+def _mix(torch, specs, seed0=0):
+    """Plans, device parameters and device point sets of a list of (n, L, B, medium) instances
+    (RFF64 + MLP32 premap, strongly entangling, energy term on the collocation points)."""
+    from paper_2506_23246_b300 import qp
+    plans, params, sets, host = [], [], [], []
+    for i, (n, L, B, medium) in enumerate(specs):
+        circ = W.c3_circuit(n, L)
+        prob = W.problem(medium, disk_x0=0.2, disk_r=0.6, w_energy=10.0, energy_slice=max(B // 4, 1),
+                         energy_nt=4)
+        p = W.init_params(circ, seed0 + i)
+        st = {"colloc": W.uniform_points(B, 300 + seed0 + i, 1.0),
+              "ic": W.ic_points_uniform(max(B // 8, 1), 400 + seed0 + i),
+              "bc": W.bc_points(max(B // 10, 1), 500 + seed0 + i)}
+        plans.append(qp.Plan(circ, prob))
+        params.append(torch.tensor(p, device="cuda"))
+        sets.append({k: torch.tensor(v, device="cuda") for k, v in st.items()})
+        host.append((circ, prob, p, st))
+    return plans, params, sets, host
+
+
+def test_grouped_batch_matches_oracle(torch_cuda, oracle):
+    """A six-instance mix (4 to 8 qubits, vacuum and dielectric, energy slices, ragged point
+    counts): five instances share the multi-instance launch, the 8-qubit one takes the
+    tensor-core path on a worker stream. Every instance's loss terms and gradient (all circuit
+    and head parameters, a sample of the MLP's) against the FP64 oracle at 1e-5."""
+    torch = torch_cuda
+    specs = [(4, 3, 61, "vacuum"), (5, 2, 90, "dielectric"), (6, 2, 37, "vacuum"), (7, 2, 29, "dielectric"),
+             (5, 4, 25, "vacuum"), (8, 2, 21, "vacuum")]
+    plans, params, sets, host = _mix(torch, specs)
+    assert [p.path for p in plans] == ["simt"] * 5 + ["gemm_split"]
+    out = qp_batch(plans, params, sets)
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(0)
+    for (loss, grad), pl, (circ, prob, p, st) in zip(out, plans, host):
+        assert pl.last_device_error() == 0
+        loss = loss.cpu().numpy().astype(np.float64)
+        grad = grad.cpu().numpy()
+        lo = np.asarray(oracle.loss(circ, prob, p, st), dtype=np.float64)
+        for i in range(lo.shape[0]):
+            err = abs(loss[i] - lo[i])
+            if err < 1e-10:
+                continue
+            scale = max(abs(lo[i]), abs(lo[0])) if i < 9 else abs(lo[i])
+            assert err <= TOL * scale and err <= CHAN_TOL * abs(lo[i]), (circ["n_qubits"], "loss", i)
+        lay = oracle.param_layout(circ)
+        mlp = rng.choice(np.arange(lay["fixed"], lay["circuit"]), 24, replace=False)
+        idx = np.concatenate([np.sort(mlp), np.arange(lay["circuit"], lay["total"])])
+        go = np.asarray(oracle.grad(circ, prob, p, st, idx), dtype=np.float64)
+        gg = grad[idx].astype(np.float64)
+        for lo_, hi_ in ((lay["fixed"], lay["circuit"]), (lay["circuit"], lay["head"]), (lay["head"], lay["total"])):
+            sel = (idx >= lo_) & (idx < hi_)
+            scale = float(np.max(np.abs(go[sel])))
+            err = np.abs(gg[sel] - go[sel])
+            assert np.all(err <= TOL * scale + CHAN_TOL * np.abs(go[sel])), (circ["n_qubits"], lo_, hi_)
+
+
+def qp_batch(plans, params, sets, grouped=True):
+    from paper_2506_23246_b300 import qp
+    return qp.batch_step(plans, params, sets, grouped=grouped)
+
+
+def test_grouped_equals_ungrouped_and_tuned(torch_cuda):
+    """The multi-instance launch (default shape, then the tuner's choice) against every instance
+    run as its own call: the same values up to FP32 summation order."""
+    from paper_2506_23246_b300 import qp
+    torch = torch_cuda
+    specs = [(4, 2, 700, "vacuum"), (5, 3, 1500, "dielectric"), (6, 2, 333, "vacuum"), (7, 3, 900, "vacuum"),
+             (7, 1, 50, "dielectric"), (3, 2, 128, "vacuum"), (9, 2, 100, "vacuum")]
+    plans, params, sets, _ = _mix(torch, specs, 10)
+    ref = [(l.clone(), g.clone()) for l, g in qp_batch(plans, params, sets, grouped=False)]
+    got = [(l.clone(), g.clone()) for l, g in qp_batch(plans, params, sets)]
+    w, k = qp.batch_tune(plans, params, sets)
+    assert w in (4, 8, 12) and k in (1, 4, 16)
+    tuned = qp_batch(plans, params, sets)
+    torch.cuda.synchronize()
+    for (lr, gr), (l1, g1), (l2, g2), pl in zip(ref, got, tuned, plans):
+        assert pl.last_device_error() == 0
+        for l, g in ((l1, g1), (l2, g2)):
+            assert _rel(l.cpu().numpy(), lr.cpu().numpy()) < 1e-6
+            assert _rel(g.cpu().numpy(), gr.cpu().numpy()) < 2e-6
+
+
+def test_grouped_more_instances_than_one_launch(torch_cuda):
+    """70 small instances of one qubit count: two launches of the multi-instance kernel (64
+    instances at most each), every instance equal to its own call."""
+    torch = torch_cuda
+    specs = [(4, 1 + i % 3, 17 + 5 * i, "vacuum") for i in range(70)]
+    plans, params, sets, _ = _mix(torch, specs, 20)
+    ref = [(l.clone(), g.clone()) for l, g in qp_batch(plans, params, sets, grouped=False)]
+    got = qp_batch(plans, params, sets)
+    torch.cuda.synchronize()
+    for (lr, gr), (l, g) in zip(ref, got):
+        assert _rel(l.cpu().numpy(), lr.cpu().numpy()) < 1e-6
+        assert _rel(g.cpu().numpy(), gr.cpu().numpy()) < 2e-6
