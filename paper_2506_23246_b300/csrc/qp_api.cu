@@ -459,9 +459,9 @@ qp_status qp_plan_create(const qp_circuit* circuit, const qp_problem* problem, i
         raise_smem_limit((void*)qpd::dense_row16_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          qpd::row16_smem_bytes()) != cudaSuccess ||
         raise_smem_limit(wgrad_kernel<false>(n), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             qpd::wg_smem_bytes(n)) != cudaSuccess ||
+                             qpd::wgc_smem(n, false).total) != cudaSuccess ||
         raise_smem_limit(wgrad_kernel<true>(n), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             qpd::wg_smem_bytes(n, true)) != cudaSuccess ||
+                             qpd::wgc_smem(n, true).total) != cudaSuccess ||
         raise_smem_limit((void*)qpd::dense_sweep_left_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (1 << n) * 16 * 8) != cudaSuccess ||
         raise_smem_limit((void*)qpd::dense_sweep_right_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -965,8 +965,8 @@ static qp_status dense_loss_grad(qp_plan* pl, const float* d_params, const float
     // FP16 pairs when the forward recorded both operand ranges
     void* wargs[] = {&wa};
     const cudaError_t le = cudaLaunchKernel(fwd16 ? wgrad_kernel<true>(n) : wgrad_kernel<false>(n),
-                                            dim3((unsigned)(wgm.tiles * wgm.ngroups)), dim3(qpd::WG_THREADS), wargs,
-                                            qpd::wg_smem_bytes(n, fwd16), s);
+                                            dim3((unsigned)(wgm.tiles * wgm.ngroups)), dim3(qpd::wgc_threads(fwd16)),
+                                            wargs, qpd::wgc_smem(n, fwd16).total, s);
     if (le != cudaSuccess) return QP_ERR_CUDA;
   }
   prof_mark(pl, 1, false, s);

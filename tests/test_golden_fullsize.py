@@ -13,7 +13,7 @@ from paper_2506_23246_b300 import workloads as W
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 
 
-@pytest.mark.parametrize("name", ["c3"])
+@pytest.mark.parametrize("name", ["c3", "c4"])
 def test_fullsize_golden_current(oracle, name):
     with open(os.path.join(GOLDEN, "%s_fullsize.json" % name)) as fh:
         g = json.load(fh)

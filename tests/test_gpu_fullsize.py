@@ -48,7 +48,7 @@ def _blocks(lay):
             ("head", lay["head"], lay["total"])]
 
 
-@pytest.mark.parametrize("name", ["c3"])
+@pytest.mark.parametrize("name", ["c3", "c4"])
 def test_fullsize_loss_grad_fields_vs_oracle(name):
     import torch
     if not torch.cuda.is_available():
