@@ -136,12 +136,14 @@ __device__ __forceinline__ void wg_copy_rows(const WgArgs& a, int64_t kc, int nt
 // factors, R tables, both M sub-tiles of the A operand and the B operand -- into its own
 // operand stage c, so NC steps are staged at once and the latency chain of one step (factor
 // and table barriers, the dependent dual products, the operand splits) overlaps the chains of
-// the other crews instead of setting the pace. The control warp streams the costate rows and
-// issues the MMAs in step order; the crew holding a chunk's last step drains the accumulator
-// into the CTA's partial slot while the other crews stage the next steps.
+// the other crews instead of setting the pace. A producer warp streams the costate rows into
+// the 4-slot ring as soon as a slot is read (up to four steps ahead, never held up by the MMA
+// issue); the control warp issues the MMAs in step order; the crew holding a chunk's last step
+// drains the accumulator into the CTA's partial slot while the other crews stage the next steps.
 constexpr int WGC_CREW = 256;   // threads of a crew
 __host__ __device__ constexpr int wgc_ncrew(bool h16) { return h16 ? 3 : 2; }
-__host__ __device__ constexpr int wgc_threads(bool h16) { return wgc_ncrew(h16) * WGC_CREW + 32; }
+// crews, then the control warp (MMAs) and the producer warp (costate copies)
+__host__ __device__ constexpr int wgc_threads(bool h16) { return wgc_ncrew(h16) * WGC_CREW + 64; }
 
 struct WgcSmem {
   int a_bytes, b_bytes, stage, raw, fac, tab, bars, total;
@@ -206,7 +208,7 @@ __global__ void __launch_bounds__(wgc_threads(H16), 1) dense_wgrad_gemm_kernel(W
   }
   const float unsc = 1.f / (sR * sL);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const bool ctrl = warp == NC * 8;
+  const bool ctrl = warp == NC * 8, prod = warp == NC * 8 + 1;
   const int MTC = wg_mtc(n), msub = MTC / TM, nj = MTC / 32;
   const int tile = blockIdx.x % a.tiles, lb = blockIdx.x / a.tiles;
   const int nmt = dim / MTC;
@@ -236,28 +238,35 @@ __global__ void __launch_bounds__(wgc_threads(H16), 1) dense_wgrad_gemm_kernel(W
   const int64_t nkc = a.kc_end[2];
   const int64_t c0 = (int64_t)lb * nkc / a.ngroups, c1 = (int64_t)(lb + 1) * nkc / a.ngroups;
   bool ok = true;
-  if (ctrl) {
-    // ---- control thread: bulk copies three steps ahead, MMAs in step order
+  if (prod) {
+    // ---- producer thread: the costate rows of every step into the ring, once the slot's
+    // previous step has been read
     if (lane == 0) {
-      int64_t last_commit = -1, last_copy = -1;
-      for (int j = 0; j < WG_RING - 1 && c0 + j < c1; ++j) {
-        wg_copy_rows(a, c0 + j, ntile, raw + j * (WKC * 256), &raw_full[j]);
+      int64_t last_copy = -1;
+      for (int64_t j = 0; c0 + j < c1 && ok; ++j) {
+        if (j >= WG_RING) ok = qptc::mbar_wait(&raw_free[j % WG_RING], (uint32_t)((j - WG_RING) / WG_RING) & 1);
+        if (!ok) break;
+        qptc::fence_proxy_async();
+        wg_copy_rows(a, c0 + j, ntile, raw + (j % WG_RING) * (WKC * 256), &raw_full[j % WG_RING]);
         last_copy = j;
       }
+      if (!ok) {
+        atomicExch(a.status, 6);
+        // let the copies in flight land before exiting
+        for (int64_t j = last_copy - (WG_RING - 1) < 0 ? 0 : last_copy - (WG_RING - 1); j <= last_copy; ++j)
+          qptc::mbar_wait(&raw_full[j % WG_RING], (uint32_t)(j / WG_RING) & 1);
+      }
+    }
+  } else if (ctrl) {
+    // ---- control thread: MMAs in step order
+    if (lane == 0) {
+      int64_t last_commit = -1;
       const uint32_t id = qptc::idesc(H16 ? 0 : 2, TM, 256);
       bool fresh = true;
       int chunk = 0;
       uint32_t it = 0;
       for (int64_t kc = c0; kc < c1 && ok; ++kc, ++it) {
         const uint32_t c = it % NC, lc = it / NC;
-        const int64_t j = it + WG_RING - 1;
-        if (kc + WG_RING - 1 < c1) {
-          if (j >= WG_RING) ok = qptc::mbar_wait(&raw_free[j % WG_RING], (uint32_t)((j - WG_RING) / WG_RING) & 1);
-          if (!ok) break;
-          qptc::fence_proxy_async();
-          wg_copy_rows(a, kc + WG_RING - 1, ntile, raw + (j % WG_RING) * (WKC * 256), &raw_full[j % WG_RING]);
-          last_copy = j;
-        }
         if (fresh && chunk > 0) ok = qptc::mbar_wait(acc_free, (uint32_t)(chunk - 1) & 1);
         if (!ok) break;
         ok = qptc::mbar_wait(&stage_full[c], lc & 1);
@@ -301,9 +310,7 @@ __global__ void __launch_bounds__(wgc_threads(H16), 1) dense_wgrad_gemm_kernel(W
       }
       if (!ok) {
         atomicExch(a.status, 6);
-        // let every bulk copy and tensor-core operation of this CTA land before exiting
-        for (int64_t j = last_copy - (WG_RING - 1) < 0 ? 0 : last_copy - (WG_RING - 1); j <= last_copy; ++j)
-          qptc::mbar_wait(&raw_full[j % WG_RING], (uint32_t)(j / WG_RING) & 1);
+        // let every tensor-core operation of this CTA land before exiting
         if (last_commit >= 0)
           qptc::mbar_wait(&mma_done[last_commit % NC], ((uint32_t)last_commit / NC) & 1);
       }
