@@ -237,6 +237,9 @@ __global__ void __launch_bounds__(wgc_threads(H16), 1) dense_wgrad_gemm_kernel(W
   const uint32_t tmem = *tslot;
   const int64_t nkc = a.kc_end[2];
   const int64_t c0 = (int64_t)lb * nkc / a.ngroups, c1 = (int64_t)(lb + 1) * nkc / a.ngroups;
+  // chunk boundaries staggered over the CTAs (the first chunk is shorter by 0 .. 7 eighths), so
+  // that the drains into L2 do not all fall at the same time
+  const int64_t choff = (int64_t)(blockIdx.x & 7) * a.fl / 8;
   bool ok = true;
   if (prod) {
     // ---- producer thread: the costate rows of every step into the ring, once the slot's
@@ -303,7 +306,7 @@ __global__ void __launch_bounds__(wgc_threads(H16), 1) dense_wgrad_gemm_kernel(W
         qptc::commit(&mma_done[c]);
         last_commit = it;
         fresh = false;
-        if ((kc - c0 + 1) % a.fl == 0 || kc + 1 == c1) {
+        if ((kc - c0 + 1 + choff) % a.fl == 0 || kc + 1 == c1) {
           fresh = true;
           ++chunk;
         }
@@ -454,15 +457,16 @@ __global__ void __launch_bounds__(wgc_threads(H16), 1) dense_wgrad_gemm_kernel(W
       qptc::fence_proxy_async();
       __syncwarp();
       if (lane == 0) qptc::mbar_arrive(&stage_full[crew]);
-      if ((kc - c0 + 1) % a.fl == 0 || kc + 1 == c1) {
+      if ((kc - c0 + 1 + choff) % a.fl == 0 || kc + 1 == c1) {
         // the chunk's last step: drain once its MMAs (and so all earlier ones) finished
         if (good) good = qptc::mbar_wait(&mma_done[crew], cnt & 1);
         if (good) {
           qptc::fence_after();
-          flush((kc - c0) / a.fl > 0, false);
+          flush((kc - c0 + choff) / a.fl > 0, false);
         }
-        // the next chunk's drain (another crew) adds to these elements: make them visible first
-        __threadfence();
+        // the first drain stores, later ones add (in any order): the next chunk's drain (another
+        // crew) must see the stores
+        if ((kc - c0 + choff) / a.fl == 0) __threadfence();
         qptc::fence_before();
         __syncwarp();
         if (lane == 0) qptc::mbar_arrive(acc_free);
