@@ -152,8 +152,9 @@ __device__ __forceinline__ void mu_chunk(MuRow& R, int n, int s, int c, uint32_t
   }
 }
 
-constexpr int MU_STAGERS = 128;   // operand staging + embedding epilogue (4 warps)
-constexpr int MU_THREADS = MU_STAGERS + 32;
+constexpr int MU_STAGERS = 128;   // operand staging (4 warps)
+constexpr int MU_DRAINERS = 128;  // embedding epilogue of the previous tile (4 warps, same rows)
+constexpr int MU_THREADS = MU_STAGERS + MU_DRAINERS + 32;
 
 // NQ = n (7 or 8, equal to a.n): the qubit count fixes the table bit positions and the qubit
 // index of every correlation at compile time.
@@ -164,7 +165,7 @@ __global__ void __launch_bounds__(MU_THREADS, 1) dense_mu_embed_kernel(MuArgs a)
   constexpr int n = NQ, dim = 1 << n;
   constexpr int ktot = 2 * dim, nch = dim, nkc = ktot / HKC;   // dim <= 256: one column chunk
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const bool ctrl = warp == MU_STAGERS / 32;
+  const bool ctrl = warp == (MU_STAGERS + MU_DRAINERS) / 32;
   const int abytes = TM * HKC * 2, wbytes = nch * HKC * 2;
   // FP16 pairs: the costates scaled by one power of two from the recorded maximum, the
   // operand blocks by 2^14; both come back out in the drain
@@ -175,14 +176,17 @@ __global__ void __launch_bounds__(MU_THREADS, 1) dense_mu_embed_kernel(MuArgs a)
   uint64_t* w_full = bars;         // [2] W operand of a stage landed
   uint64_t* mma_done = bars + 2;   // [2] tensor-core work of a stage finished
   uint64_t* a_full = bars + 4;     // [2] A operand of a stage written (4 staging warps)
-  uint64_t* acc_free = bars + 6;   // [2] a tensor-memory buffer drained (4 staging warps)
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + 2 * stage_bytes + 64);
+  uint64_t* acc_free = bars + 6;   // [2] a tensor-memory buffer drained (4 drain warps)
+  uint64_t* tile_done = bars + 8;  // [2] all MMAs of the tile in a tensor-memory buffer finished
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + 2 * stage_bytes + 96);
   float* ex = reinterpret_cast<float*>(sm + 2 * stage_bytes + 128);    // [2 (C, D)][4][32][8]
   const uint32_t tcols = 2 * nch <= 256 ? (2 * nch <= 128 ? 128 : 256) : 512;
   if (warp == 0) qptc::tmem_alloc(tslot, tcols);
   if (tid == 0) {
     for (int i = 0; i < 4; ++i) qptc::mbar_init(&bars[i], 1);
-    for (int i = 4; i < 8; ++i) qptc::mbar_init(&bars[i], MU_STAGERS / 32);
+    for (int i = 4; i < 6; ++i) qptc::mbar_init(&bars[i], MU_STAGERS / 32);
+    for (int i = 6; i < 8; ++i) qptc::mbar_init(&bars[i], MU_DRAINERS / 32);
+    for (int i = 8; i < 10; ++i) qptc::mbar_init(&bars[i], 1);
   }
   qptc::fence_before();
   __syncthreads();
@@ -227,6 +231,7 @@ __global__ void __launch_bounds__(MU_THREADS, 1) dense_mu_embed_kernel(MuArgs a)
             qptc::mma_f16(dt, al, wh, id, 1u);
           }
           qptc::commit(&mma_done[st]);
+          if (kc == nkc - 1) qptc::commit(&tile_done[buf]);   // the drain warps may read it
           last_commit = it;
           if ((int64_t)it + 1 < total) {
             const uint32_t s2 = (it + 1) & 1;
@@ -245,23 +250,93 @@ __global__ void __launch_bounds__(MU_THREADS, 1) dense_mu_embed_kernel(MuArgs a)
         if (last_commit >= 0) qptc::mbar_wait(&mma_done[last_commit & 1], ((uint32_t)last_commit >> 1) & 1);
       }
     }
+  } else if (warp < MU_STAGERS / 32) {
+    // ---- staging warps: costate rows -> FP16-pair A operand, one row per thread
+    uint32_t it = 0;
+    // costate row of this thread in a tile (A operand source)
+    auto tile_row = [&](int64_t tile) -> const float4* {
+      int set;
+      int64_t p0;
+      if (tile < a.tile_end[0]) { set = 0; p0 = tile * 32; }
+      else if (tile < a.tile_end[1]) { set = 1; p0 = (tile - a.tile_end[0]) * TM; }
+      else { set = 2; p0 = (tile - a.tile_end[1]) * TM; }
+      const int64_t np = a.npts[set];
+      const int64_t p = p0 + (set == 0 ? lane : tid);
+      const int64_t pc = p < np ? p : np - 1;
+      return reinterpret_cast<const float4*>(a.lam + lam_row(set, pc, set == 0 ? warp : 0, a.npts[0], a.pt_base[set]) * 256);
+    };
+    // the next K-step's eight float4 of the row are loaded one step ahead (software pipeline)
+    float4 nxt[KC / 4];
+    if ((int64_t)blockIdx.x < T2) {
+      const float4* s0 = tile_row(blockIdx.x);
+#pragma unroll
+      for (int g4 = 0; g4 < KC / 4; ++g4) nxt[g4] = __ldg(s0 + g4);
+    }
+    for (int64_t tile = blockIdx.x; tile < T2 && ok; tile += gridDim.x) {
+      const float4* src = tile_row(tile);
+      const float4* src_next = tile + gridDim.x < T2 ? tile_row(tile + gridDim.x) : nullptr;
+      for (int kc = 0; kc < nkc; ++kc, ++it) {
+        const uint32_t st = it & 1;
+        unsigned char* sA = sm + st * stage_bytes;
+        if (it >= 2 && ok) ok = qptc::mbar_wait(&mma_done[st], ((it - 2) >> 1) & 1);
+        float4 cur[KC / 4];
+#pragma unroll
+        for (int g4 = 0; g4 < KC / 4; ++g4) cur[g4] = nxt[g4];
+        const float4* ns = kc + 1 < nkc ? src + mu_koff(a, kc + 1) : src_next;
+        if (ns) {
+#pragma unroll
+          for (int g4 = 0; g4 < KC / 4; ++g4) nxt[g4] = __ldg(ns + g4);
+        }
+        if (ok) {
+#pragma unroll
+          for (int g8 = 0; g8 < HKC / 8; ++g8) {
+            const float v8[8] = {cur[2 * g8].x, cur[2 * g8].y, cur[2 * g8].z, cur[2 * g8].w,
+                                 cur[2 * g8 + 1].x, cur[2 * g8 + 1].y, cur[2 * g8 + 1].z, cur[2 * g8 + 1].w};
+            uint4 h8, l8;
+            pack_h8(v8, sL, h8, l8);
+            const uint32_t off = core_off_h(tid, g8 * 8);
+            *reinterpret_cast<uint4*>(sA + off) = h8;
+            *reinterpret_cast<uint4*>(sA + abytes + off) = l8;
+          }
+        }
+        qptc::fence_proxy_async();
+        __syncwarp();
+        if (lane == 0) qptc::mbar_arrive(&a_full[st]);
+      }
+      ok = qptc::bar_and(1, MU_STAGERS, ok);
+    }
+    if (!ok && lane == 0) atomicExch(a.status, 6);
   } else {
-    // ---- staging warps: costate rows -> TF32 A operand; drain of the previous tile
-    uint32_t it = 0, cbuf = 0;
-    bool pend = false, pend_nv4 = false, pend_act = false;
-    int pend_set = 0;
-    int64_t pend_p = 0;
-    uint32_t pend_buf = 0, pend_it = 0;
+    // ---- drain warps: the embedding correlations of each finished tile, read from tensor
+    // memory while the staging warps and the tensor core work on the next tile (warp 4 + w
+    // reads the tensor-memory lanes of staging warp w: the same rows)
+    const int dw = warp - MU_STAGERS / 32;
     MuRow R;
     auto bar = [&]() {
       __syncwarp();   // bar.sync is the aligned form
-      asm volatile("bar.sync 1, %0;" ::"r"(MU_STAGERS) : "memory");
+      asm volatile("bar.sync 2, %0;" ::"r"(MU_DRAINERS) : "memory");
     };
-    auto finalize = [&]() {
+    uint32_t t = 0;
+    for (int64_t tile = blockIdx.x; tile < T2 && ok; tile += gridDim.x, ++t) {
+      int set;
+      int64_t p0;
+      if (tile < a.tile_end[0]) { set = 0; p0 = tile * 32; }
+      else if (tile < a.tile_end[1]) { set = 1; p0 = (tile - a.tile_end[0]) * TM; }
+      else { set = 2; p0 = (tile - a.tile_end[1]) * TM; }
+      const bool nv4 = set == 0;
+      const int64_t np = a.npts[set];
+      const int64_t p = p0 + (nv4 ? lane : dw * 32 + lane);
+      const int s = nv4 ? dw : 0;
+      const uint32_t buf = t & 1;
+      ok = qptc::bar_and(2, MU_DRAINERS, ok && qptc::mbar_wait(&tile_done[buf], (t >> 1) & 1));
+      if (!ok) break;
+      qptc::fence_after();
+      mu_row_setup(a, n, set, p < np ? p : np - 1, s, R);
+      for (int c = 0; c < nchunk32; ++c)
+        mu_chunk(R, n, s, c, tmem + ((uint32_t)(dw * 32) << 16) + buf * (tcols / 2) + c * 32, us);
       qptc::fence_before();
       // rows of one point sit in four warps (same lane): combine through shared memory
-      const int s = pend_nv4 ? warp : 0;
-      if (pend_nv4) {
+      if (nv4) {
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
           ex[(s * 32 + lane) * 8 + q] = R.C[q];
@@ -269,10 +344,10 @@ __global__ void __launch_bounds__(MU_THREADS, 1) dense_mu_embed_kernel(MuArgs a)
         }
       }
       bar();
-      if (pend_act && (!pend_nv4 || warp == 0)) {
-        float4* dst = reinterpret_cast<float4*>(a.dthetaJ) + (a.pt_base[pend_set] + pend_p) * n;
+      if (p < np && (!nv4 || dw == 0)) {
+        float4* dst = reinterpret_cast<float4*>(a.dthetaJ) + (a.pt_base[set] + p) * n;
         for (int q = 0; q < n; ++q) {
-          if (pend_nv4) {
+          if (nv4) {
             const float c = ex[lane * 8 + q] + ex[(32 + lane) * 8 + q] + ex[(64 + lane) * 8 + q] + ex[(96 + lane) * 8 + q];
             dst[q] = make_float4(c, ex[1024 + (32 + lane) * 8 + q], ex[1024 + (64 + lane) * 8 + q],
                                  ex[1024 + (96 + lane) * 8 + q]);
@@ -286,110 +361,9 @@ __global__ void __launch_bounds__(MU_THREADS, 1) dense_mu_embed_kernel(MuArgs a)
       }
       bar();
       // the buffer is fully read: the control thread may overwrite it
-      if (lane == 0) qptc::mbar_arrive(&acc_free[pend_buf]);
-      pend = false;
-    };
-    auto begin_drain = [&]() -> bool {
-      const bool w = qptc::bar_and(1, MU_STAGERS, ok && qptc::mbar_wait(&mma_done[pend_it & 1], (pend_it >> 1) & 1));
-      if (w) {
-        qptc::fence_after();
-        const int s = pend_nv4 ? warp : 0;
-        const int64_t np = a.npts[pend_set];
-        mu_row_setup(a, n, pend_set, pend_p < np ? pend_p : np - 1, s, R);
-      }
-      return w;
-    };
-    // costate row of this thread in a tile (A operand source)
-    auto tile_row = [&](int64_t tile, int& set, int64_t& p0, int64_t& p) -> const float4* {
-      if (tile < a.tile_end[0]) { set = 0; p0 = tile * 32; }
-      else if (tile < a.tile_end[1]) { set = 1; p0 = (tile - a.tile_end[0]) * TM; }
-      else { set = 2; p0 = (tile - a.tile_end[1]) * TM; }
-      const int64_t np = a.npts[set];
-      p = p0 + (set == 0 ? lane : tid);
-      const int64_t pc = p < np ? p : np - 1;
-      return reinterpret_cast<const float4*>(a.lam + lam_row(set, pc, set == 0 ? warp : 0, a.npts[0], a.pt_base[set]) * 256);
-    };
-    // the next K-step's eight float4 of the row are loaded one step ahead (software pipeline)
-    float4 nxt[KC / 4];
-    if ((int64_t)blockIdx.x < T2) {
-      int st0;
-      int64_t q0, q1;
-      const float4* s0 = tile_row(blockIdx.x, st0, q0, q1);
-#pragma unroll
-      for (int g4 = 0; g4 < KC / 4; ++g4) nxt[g4] = __ldg(s0 + g4);
+      if (lane == 0) qptc::mbar_arrive(&acc_free[buf]);
     }
-    for (int64_t tile = blockIdx.x; tile < T2 && ok; tile += gridDim.x) {
-      int set;
-      int64_t p0, p;
-      const float4* src = tile_row(tile, set, p0, p);
-      const bool nv4 = set == 0;
-      const int64_t np = a.npts[set];
-      const float4* src_next = nullptr;
-      if (tile + gridDim.x < T2) {
-        int st1;
-        int64_t q0, q1;
-        src_next = tile_row(tile + gridDim.x, st1, q0, q1);
-      }
-      for (int kc = 0; kc < nkc; ++kc, ++it) {
-        const uint32_t st = it & 1;
-        unsigned char* sA = sm + st * stage_bytes;
-        if (it >= 2 && ok) ok = qptc::mbar_wait(&mma_done[st], ((it - 2) >> 1) & 1);
-        {
-          float* Ahi = reinterpret_cast<float*>(sA);
-          float* Alo = reinterpret_cast<float*>(sA + abytes);
-          float4 cur[KC / 4];
-#pragma unroll
-          for (int g4 = 0; g4 < KC / 4; ++g4) cur[g4] = nxt[g4];
-          const float4* ns = kc + 1 < nkc ? src + mu_koff(a, kc + 1) : src_next;
-          if (ns) {
-#pragma unroll
-            for (int g4 = 0; g4 < KC / 4; ++g4) nxt[g4] = __ldg(ns + g4);
-          }
-          if (ok) {
-#pragma unroll
-            for (int g8 = 0; g8 < HKC / 8; ++g8) {
-              const float v8[8] = {cur[2 * g8].x, cur[2 * g8].y, cur[2 * g8].z, cur[2 * g8].w,
-                                   cur[2 * g8 + 1].x, cur[2 * g8 + 1].y, cur[2 * g8 + 1].z, cur[2 * g8 + 1].w};
-              uint4 h8, l8;
-              pack_h8(v8, sL, h8, l8);
-              const uint32_t off = core_off_h(tid, g8 * 8);
-              *reinterpret_cast<uint4*>(reinterpret_cast<unsigned char*>(Ahi) + off) = h8;
-              *reinterpret_cast<uint4*>(reinterpret_cast<unsigned char*>(Alo) + off) = l8;
-            }
-          }
-        }
-        qptc::fence_proxy_async();
-        __syncwarp();
-        if (lane == 0) qptc::mbar_arrive(&a_full[st]);
-        // drain the previous tile one 32-column chunk per K-step, under this tile's MMAs
-        if (pend) {
-          if (kc == 0) ok = begin_drain();
-          if (ok && kc < nchunk32)
-            mu_chunk(R, n, pend_nv4 ? warp : 0, kc,
-                     tmem + ((uint32_t)(warp * 32) << 16) + pend_buf * (tcols / 2) + kc * 32, us);
-          if (kc == nchunk32 - 1) finalize();
-        }
-      }
-      ok = qptc::bar_and(1, MU_STAGERS, ok);
-      if (!ok) break;
-      pend = true;
-      pend_nv4 = nv4;
-      pend_set = set;
-      pend_p = p;
-      pend_act = p < np;
-      pend_buf = cbuf;
-      pend_it = it - 1;
-      cbuf ^= 1;
-    }
-    if (ok && pend) {
-      ok = begin_drain();
-      if (ok) {
-        for (int c = 0; c < nchunk32; ++c)
-          mu_chunk(R, n, pend_nv4 ? warp : 0, c, tmem + ((uint32_t)(warp * 32) << 16) + pend_buf * (tcols / 2) + c * 32, us);
-        finalize();
-      }
-    }
-    if (!ok && tid == 0) atomicExch(a.status, 6);
+    if (!ok && lane == 0) atomicExch(a.status, 6);
   }
   qptc::fence_before();
   __syncthreads();
