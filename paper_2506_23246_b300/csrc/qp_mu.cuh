@@ -152,7 +152,7 @@ __device__ __forceinline__ void mu_chunk(MuRow& R, int n, int s, int c, uint32_t
   }
 }
 
-constexpr int MU_STAGERS = 128;   // operand staging (4 warps)
+constexpr int MU_STAGERS = 256;   // operand staging (8 warps: two per row quarter, half a K step each)
 constexpr int MU_DRAINERS = 128;  // embedding epilogue of the previous tile (4 warps, same rows)
 constexpr int MU_THREADS = MU_STAGERS + MU_DRAINERS + 32;
 
@@ -251,7 +251,10 @@ __global__ void __launch_bounds__(MU_THREADS, 1) dense_mu_embed_kernel(MuArgs a)
       }
     }
   } else if (warp < MU_STAGERS / 32) {
-    // ---- staging warps: costate rows -> FP16-pair A operand, one row per thread
+    // ---- staging warps: costate rows -> FP16-pair A operand; warps w and w + 4 share the rows
+    // of quarter w, each splitting half of a K step's 32 components
+    const int rw = warp & 3, kh = warp >> 2;
+    const int row = rw * 32 + lane;
     uint32_t it = 0;
     // costate row of this thread in a tile (A operand source)
     auto tile_row = [&](int64_t tile) -> const float4* {
@@ -261,16 +264,17 @@ __global__ void __launch_bounds__(MU_THREADS, 1) dense_mu_embed_kernel(MuArgs a)
       else if (tile < a.tile_end[1]) { set = 1; p0 = (tile - a.tile_end[0]) * TM; }
       else { set = 2; p0 = (tile - a.tile_end[1]) * TM; }
       const int64_t np = a.npts[set];
-      const int64_t p = p0 + (set == 0 ? lane : tid);
+      const int64_t p = p0 + (set == 0 ? lane : row);
       const int64_t pc = p < np ? p : np - 1;
-      return reinterpret_cast<const float4*>(a.lam + lam_row(set, pc, set == 0 ? warp : 0, a.npts[0], a.pt_base[set]) * 256);
+      return reinterpret_cast<const float4*>(a.lam + lam_row(set, pc, set == 0 ? rw : 0, a.npts[0], a.pt_base[set]) * 256) +
+             kh * (KC / 8);
     };
-    // the next K-step's eight float4 of the row are loaded one step ahead (software pipeline)
-    float4 nxt[KC / 4];
+    // the next K-step's four float4 of this thread's half row are loaded one step ahead
+    float4 nxt[KC / 8];
     if ((int64_t)blockIdx.x < T2) {
       const float4* s0 = tile_row(blockIdx.x);
 #pragma unroll
-      for (int g4 = 0; g4 < KC / 4; ++g4) nxt[g4] = __ldg(s0 + g4);
+      for (int g4 = 0; g4 < KC / 8; ++g4) nxt[g4] = __ldg(s0 + g4);
     }
     for (int64_t tile = blockIdx.x; tile < T2 && ok; tile += gridDim.x) {
       const float4* src = tile_row(tile);
@@ -279,22 +283,22 @@ __global__ void __launch_bounds__(MU_THREADS, 1) dense_mu_embed_kernel(MuArgs a)
         const uint32_t st = it & 1;
         unsigned char* sA = sm + st * stage_bytes;
         if (it >= 2 && ok) ok = qptc::mbar_wait(&mma_done[st], ((it - 2) >> 1) & 1);
-        float4 cur[KC / 4];
+        float4 cur[KC / 8];
 #pragma unroll
-        for (int g4 = 0; g4 < KC / 4; ++g4) cur[g4] = nxt[g4];
+        for (int g4 = 0; g4 < KC / 8; ++g4) cur[g4] = nxt[g4];
         const float4* ns = kc + 1 < nkc ? src + mu_koff(a, kc + 1) : src_next;
         if (ns) {
 #pragma unroll
-          for (int g4 = 0; g4 < KC / 4; ++g4) nxt[g4] = __ldg(ns + g4);
+          for (int g4 = 0; g4 < KC / 8; ++g4) nxt[g4] = __ldg(ns + g4);
         }
         if (ok) {
 #pragma unroll
-          for (int g8 = 0; g8 < HKC / 8; ++g8) {
+          for (int g8 = 0; g8 < HKC / 16; ++g8) {
             const float v8[8] = {cur[2 * g8].x, cur[2 * g8].y, cur[2 * g8].z, cur[2 * g8].w,
                                  cur[2 * g8 + 1].x, cur[2 * g8 + 1].y, cur[2 * g8 + 1].z, cur[2 * g8 + 1].w};
             uint4 h8, l8;
             pack_h8(v8, sL, h8, l8);
-            const uint32_t off = core_off_h(tid, g8 * 8);
+            const uint32_t off = core_off_h(row, kh * (HKC / 2) + g8 * 8);
             *reinterpret_cast<uint4*>(sA + off) = h8;
             *reinterpret_cast<uint4*>(sA + abytes + off) = l8;
           }
