@@ -37,6 +37,8 @@ def _args():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-graph", action="store_true",
+                    help="launch the step's kernels one by one instead of replaying them as one CUDA graph")
     ap.add_argument("--path", default="auto", choices=["auto", "simt", "gemm_split"],
                     help="statevector path of the library (auto = the library's choice; with "
                          "--workload configs: every path the configuration has)")
@@ -65,11 +67,13 @@ def _dist():
     return rank, world, local
 
 
-def _config(world):
+def _config(world, graph=False):
     return {"workload": WORKLOAD, "n_qubits": 8, "n_layers": 6, "ansatz": "strongly entangling",
             "premap": "RFF 64 freq + tanh MLP width 32", "medium": "dielectric",
             "colloc_per_gpu": 65536, "ic_per_gpu": 4096, "global_batch": 65536 * world,
             "parallelism": "dp%d" % world if world > 1 else "single",
+            "launch": "one CUDA graph per step (the library's kernels captured once, replayed)" if graph
+                      else "kernels launched one by one",
             "l2": "flushed between timed steps (256 MiB write)"}
 
 
@@ -280,6 +284,18 @@ def run_native(a):
         step()
     torch.cuda.synchronize()
     launches = plan.last_launch_count()
+    # the step's launches captured once into a CUDA graph and replayed (same kernels, same
+    # buffers); the sharded form keeps plain launches around its collective
+    graph = None
+    if world == 1 and not a.no_graph:
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            step()
+        torch.cuda.synchronize()
+        for _ in range(3):
+            graph.replay()
+        torch.cuda.synchronize()
+    run = graph.replay if graph is not None else step
 
     ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(a.steps)]
     ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(a.steps)]
@@ -293,7 +309,7 @@ def run_native(a):
     for i in range(a.steps):
         flush.fill_(float(i))
         ev0[i].record(stream)
-        step()
+        run()
         ev1[i].record(stream)
     torch.cuda.synchronize()
     if world > 1:
@@ -386,7 +402,7 @@ def run_native(a):
         dp.copy_(hp, non_blocking=True)
         for k in hs:
             dsets[k].copy_(hs[k], non_blocking=True)
-        step()
+        run()
         hl.copy_(loss, non_blocking=True)
         hg.copy_(grad, non_blocking=True)
 
@@ -411,7 +427,7 @@ def run_native(a):
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
                 "warmup": max(a.warmup, 3), "ms_per_step": ms, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": dtype, "data": "synthetic",
-                "config": _config(world),
+                "config": _config(world, graph is not None),
                 "e2e": {"value": world * ncol / (ems / 1000.0), "unit": UNIT,
                         "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
                 "gpu_launches": launches * a.steps,
