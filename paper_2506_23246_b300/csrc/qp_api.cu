@@ -276,11 +276,15 @@ WsLayout ws_layout(const qp_plan* pl, int64_t P0) {
 }
 
 template <int NQ, bool GRAD>
-void* circuit_fn() { return (void*)qpk::circuit_kernel<NQ, GRAD>; }
+void* circuit_fn(bool crz) {
+  return crz ? (void*)qpk::circuit_kernel<NQ, GRAD, true> : (void*)qpk::circuit_kernel<NQ, GRAD, false>;
+}
 
-void* circuit_kernel_ptr(int n, bool grad) {
+// The statevector kernel of n qubits; crz: the CRZ-mesh form (the other ansatze use the one
+// compiled without it).
+void* circuit_kernel_ptr(int n, bool grad, bool crz) {
   switch (n) {
-#define QP_CASE(N) case N: return grad ? circuit_fn<N, true>() : circuit_fn<N, false>();
+#define QP_CASE(N) case N: return grad ? circuit_fn<N, true>(crz) : circuit_fn<N, false>(crz);
     QP_CASE(1) QP_CASE(2) QP_CASE(3) QP_CASE(4) QP_CASE(5)
     QP_CASE(6) QP_CASE(7) QP_CASE(8) QP_CASE(9) QP_CASE(10)
 #undef QP_CASE
@@ -430,7 +434,7 @@ qp_status qp_plan_create(const qp_circuit* circuit, const qp_problem* problem, i
       if (lay.total <= smem_optin) break;
     }
     if (warps < 1) { delete pl; return QP_ERR_UNSUPPORTED; }
-    void* fn = circuit_kernel_ptr(n, grad);
+    void* fn = circuit_kernel_ptr(n, grad, qp_has_crz(circuit->ansatz));
     if (raise_smem_limit(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, lay.total) != cudaSuccess) {
       cudaGetLastError();
       delete pl;
@@ -1152,7 +1156,7 @@ qp_status qp_forward(qp_plan* pl, const float* d_params, const float* d_pts, int
   if (blocks > pl->blocks_fwd) blocks = pl->blocks_fwd;
   void* args[] = {&a};
   prof_mark(pl, 0, true, s);
-  if (cudaLaunchKernel(circuit_kernel_ptr(pl->c.n_qubits, false), dim3((unsigned)blocks),
+  if (cudaLaunchKernel(circuit_kernel_ptr(pl->c.n_qubits, false, qp_has_crz(pl->c.ansatz)), dim3((unsigned)blocks),
                        dim3(pl->warps_fwd * 32), args, pl->smem_fwd, s) != cudaSuccess)
     return QP_ERR_CUDA;
   prof_mark(pl, 0, false, s);
@@ -1232,7 +1236,7 @@ qp_status qp_loss_grad(qp_plan* pl, const float* d_params, const qp_batch* batch
     int64_t fblocks = (ftasks + pl->warps_fwd - 1) / pl->warps_fwd;
     if (fblocks > pl->blocks_fwd) fblocks = pl->blocks_fwd;
     void* fargs[] = {&fa};
-    if (cudaLaunchKernel(circuit_kernel_ptr(pl->c.n_qubits, false), dim3((unsigned)fblocks),
+    if (cudaLaunchKernel(circuit_kernel_ptr(pl->c.n_qubits, false, qp_has_crz(pl->c.ansatz)), dim3((unsigned)fblocks),
                          dim3(pl->warps_fwd * 32), fargs, pl->smem_fwd, s) != cudaSuccess)
       return QP_ERR_CUDA;
     const int64_t nb = (npts[0] + 255) / 256;
@@ -1272,7 +1276,7 @@ qp_status qp_loss_grad(qp_plan* pl, const float* d_params, const qp_batch* batch
   // every block writes its partials, so the grid is fixed to the plan's block count
   void* args[] = {&a};
   prof_mark(pl, 0, true, s);
-  if (cudaLaunchKernel(circuit_kernel_ptr(pl->c.n_qubits, true), dim3(pl->blocks_grad),
+  if (cudaLaunchKernel(circuit_kernel_ptr(pl->c.n_qubits, true, qp_has_crz(pl->c.ansatz)), dim3(pl->blocks_grad),
                        dim3(pl->warps_grad * 32), args, pl->smem_grad, s) != cudaSuccess)
     return QP_ERR_CUDA;
   prof_mark(pl, 0, false, s);
@@ -1510,9 +1514,10 @@ uint64_t group_signature(qp_plan* const* plans, const qp_step_args* args, const 
   return h;
 }
 
-void* multi_kernel_ptr(int n) {
+void* multi_kernel_ptr(int n, bool crz) {
   switch (n) {
-#define QP_CASE(N) case N: return (void*)qpk::circuit_multi_kernel<N>;
+#define QP_CASE(N) \
+  case N: return crz ? (void*)qpk::circuit_multi_kernel<N, true> : (void*)qpk::circuit_multi_kernel<N, false>;
     QP_CASE(1) QP_CASE(2) QP_CASE(3) QP_CASE(4) QP_CASE(5)
     QP_CASE(6) QP_CASE(7) QP_CASE(8) QP_CASE(9) QP_CASE(10)
 #undef QP_CASE
@@ -1570,10 +1575,12 @@ qp_status launch_grouped(qp_plan* const* plans, const qp_step_args* args, const 
     qp_plan* owner;
   };
   std::vector<Launch> ls;
-  for (int nq = 1; nq <= QP_MAXQ; ++nq) {
+  for (int g = 0; g < 2 * QP_MAXQ; ++g) {
+    const int nq = 1 + g / 2;
+    const bool crz = (g & 1) != 0;   // the CRZ-mesh ansatze run in a kernel of their own
     std::vector<int> mem;
     for (int k = 0; k < (int)v.size(); ++k)
-      if (plans[v[k].i]->c.n_qubits == nq) mem.push_back(k);
+      if (plans[v[k].i]->c.n_qubits == nq && qp_has_crz(plans[v[k].i]->c.ansatz) == crz) mem.push_back(k);
     for (size_t c0 = 0; c0 < mem.size(); c0 += QP_MULTI_MAX) {
       const size_t c1 = std::min(mem.size(), c0 + QP_MULTI_MAX);
       // warps per CTA: the largest up to W whose shared-memory layout fits every member
@@ -1615,7 +1622,7 @@ qp_status launch_grouped(qp_plan* const* plans, const qp_step_args* args, const 
         acc += in.items;
         L.ma.item_end[k - c0] = acc;
       }
-      L.fn = multi_kernel_ptr(nq);
+      L.fn = multi_kernel_ptr(nq, crz);
       if (raise_smem_limit(L.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess) return QP_ERR_CUDA;
       int per_sm = 0;
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, L.fn, Wc * 32, smem);
@@ -1868,7 +1875,7 @@ extern "C" qp_status qp_forward_noalloc(qp_plan* pl, const float* d_params, cons
   int64_t blocks = (tasks + pl->warps_fwd - 1) / pl->warps_fwd;
   if (blocks > pl->blocks_fwd) blocks = pl->blocks_fwd;
   void* args[] = {&a};
-  if (cudaLaunchKernel(circuit_kernel_ptr(n, false), dim3((unsigned)blocks), dim3(pl->warps_fwd * 32),
+  if (cudaLaunchKernel(circuit_kernel_ptr(n, false, qp_has_crz(pl->c.ansatz)), dim3((unsigned)blocks), dim3(pl->warps_fwd * 32),
                        args, pl->smem_fwd, s) != cudaSuccess)
     return QP_ERR_CUDA;
   pl->last_launches = crz ? 4 : 3;

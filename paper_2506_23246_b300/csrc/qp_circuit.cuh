@@ -273,7 +273,7 @@ __device__ __forceinline__ float pick3(const float4& t, int d) {
 // phi_x, phi_y, phi_t) for collocation points, 1 where only the fields are needed. Every hot
 // loop body handles one vector (forward) or one (state, costate) pair (adjoint), so the code
 // that runs per gate pass stays small.
-template <int NQ, bool GRAD>
+template <int NQ, bool GRAD, bool CRZ>
 __device__ __forceinline__ void run_task(const QPCircArgs& a, const Shared& sh, float2* wstate,
                                          int set, int64_t first_pt, int lane, int nv) {
   using Gm = QPGeo<NQ>;
@@ -303,7 +303,7 @@ __device__ __forceinline__ void run_task(const QPCircArgs& a, const Shared& sh, 
       load_gates<LB>(sh, S, l, n, P, ng, U);
       // CRZ mesh (Eq. 29) after the last rotation pass of the layer: one phase per amplitude,
       // looked up by its logical basis index (the frame is the identity: no CNOTs)
-      const bool crz_here = qp_has_crz(a.ansatz) && p == npl - 1;
+      const bool crz_here = CRZ && p == npl - 1;
       float2 dph[AMPS];
       if (crz_here) {
         const int kb = S.klog[l][lane];
@@ -548,7 +548,7 @@ __device__ __forceinline__ void run_task(const QPCircArgs& a, const Shared& sh, 
       for (int b = 0; b < LB; ++b) E[b][0] = E[b][1] = E[b][2] = 0.f;
       // CRZ mesh of this layer (its last pass): the gradient sums w(k) = sum_s Im(lambda_s(k)^*
       // phi_s(k)) are taken after the mesh, then the mesh is undone on states and costates
-      const bool crz_here = qp_has_crz(a.ansatz) && p == npl - 1;
+      const bool crz_here = CRZ && p == npl - 1;
       float2 dph[AMPS];
       float wk[AMPS];
 #pragma unroll
@@ -695,8 +695,9 @@ __device__ __forceinline__ void run_task(const QPCircArgs& a, const Shared& sh, 
 }
 
 // Persistent kernel: every warp takes warp-tasks (PPW points of one set) in turn; block
-// partials of the loss sums and gradient sums are written at the end.
-template <int NQ, bool GRAD>
+// partials of the loss sums and gradient sums are written at the end. CRZ: the ansatz has a
+// CRZ mesh (compiled apart, so the other ansatze carry none of its registers).
+template <int NQ, bool GRAD, bool CRZ>
 __global__ void __launch_bounds__(384) circuit_kernel(const __grid_constant__ QPCircArgs a) {
   using Gm = QPGeo<NQ>;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -741,7 +742,7 @@ __global__ void __launch_bounds__(384) circuit_kernel(const __grid_constant__ QP
     if (t >= a.task_end[1]) { set = 2; base = a.task_end[1]; }
     const int64_t first = (t - base) * Gm::PPW;
     const int nv = (set == 0 && (GRAD || a.want_df)) ? 4 : 1;
-    run_task<NQ, GRAD>(a, sh, wstate, set, first, lane, nv);
+    run_task<NQ, GRAD, CRZ>(a, sh, wstate, set, first, lane, nv);
   }
   if (!GRAD) return;
   __syncthreads();
@@ -779,7 +780,7 @@ __global__ void store_desc_kernel(const __grid_constant__ QPCircArgs a, QPCircAr
   if (queue && threadIdx.x == 0) *queue = 0ull;
 }
 
-template <int NQ>
+template <int NQ, bool CRZ>
 __device__ __forceinline__ void multi_tasks(const QPCircArgs& a, const Shared& sh, unsigned char* state,
                                             int64_t t0, int64_t t1, int warp, int warps, int lane) {
   using Gm = QPGeo<NQ>;
@@ -789,13 +790,13 @@ __device__ __forceinline__ void multi_tasks(const QPCircArgs& a, const Shared& s
     int64_t base = 0;
     if (t >= a.task_end[0]) { set = 1; base = a.task_end[0]; }
     if (t >= a.task_end[1]) { set = 2; base = a.task_end[1]; }
-    run_task<NQ, true>(a, sh, wstate, set, (t - base) * Gm::PPW, lane, set == 0 ? 4 : 1);
+    run_task<NQ, true, CRZ>(a, sh, wstate, set, (t - base) * Gm::PPW, lane, set == 0 ? 4 : 1);
   }
 }
 
 // One qubit count per kernel: the register allocation of the single-instance kernel (a switch
 // over several counts in one kernel is allocated for all of them at once and spills).
-template <int NQ>
+template <int NQ, bool CRZ>
 __global__ void __launch_bounds__(384) circuit_multi_kernel(const __grid_constant__ QPMultiArgs m) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ long long s_item;
@@ -844,7 +845,7 @@ __global__ void __launch_bounds__(384) circuit_multi_kernel(const __grid_constan
     const int64_t ntask = A.task_end[2];
     const int64_t t0 = (item - ib) * m.tasks_per_item[i];
     const int64_t t1 = t0 + m.tasks_per_item[i] < ntask ? t0 + m.tasks_per_item[i] : ntask;
-    multi_tasks<NQ>(A, sh, smem + lay.off_state, t0, t1, warp, warps, lane);
+    multi_tasks<NQ, CRZ>(A, sh, smem + lay.off_state, t0, t1, warp, warps, lane);
     __syncthreads();
     const int64_t slot = item - ib;
     double* bl = A.blk_loss + slot * A.loss_stride;
