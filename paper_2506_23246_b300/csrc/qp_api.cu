@@ -57,6 +57,15 @@ struct qp_plan {
   // profiling events per measured kernel (qp_set_profile_events): [0] statevector kernel or
   // forward contraction, [1] weight-gradient contraction, [2] back-projection mu
   cudaEvent_t prof_start[3] = {nullptr, nullptr, nullptr}, prof_stop[3] = {nullptr, nullptr, nullptr};
+  // tensor-core path: a side stream for the unitary build, which runs beside the premap (forked
+  // from and joined back into the call's stream within the call)
+  cudaStream_t aux = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  ~qp_plan() {
+    if (ev_fork) cudaEventDestroy(ev_fork);
+    if (ev_join) cudaEventDestroy(ev_join);
+    if (aux) cudaStreamDestroy(aux);
+  }
 };
 
 namespace {
@@ -452,6 +461,13 @@ qp_status qp_plan_create(const qp_circuit* circuit, const qp_problem* problem, i
     }
   }
   if (dense_path(pl)) {
+    if (cudaStreamCreateWithFlags(&pl->aux, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&pl->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&pl->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+      cudaGetLastError();
+      delete pl;
+      return QP_ERR_CUDA;
+    }
     if (raise_smem_limit((void*)qpd::dense_build_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              2 * (1 << n) * 16) != cudaSuccess ||
         raise_smem_limit((void*)qpd::dense_row_gemm_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -844,9 +860,6 @@ static qp_status dense_loss_grad(qp_plan* pl, const float* d_params, const float
   char* ws = (char*)pl->ws;
   const int n = pl->c.n_qubits, dim = 1 << n, L = pl->c.n_layers;
   int launches = 0;
-  qp_status st = launch_front(pl, d_params, pts, npts, w, s, true);
-  if (st != QP_OK) return st;
-  launches += front_launches(pl);
   qpd::BuildArgs ba = {};
   ba.params = d_params; ba.circ_off = pl->circ_off; ba.n = n; ba.L = L;
   ba.gates = (double2*)(ws + w.dgates);
@@ -862,6 +875,21 @@ static qp_status dense_loss_grad(qp_plan* pl, const float* d_params, const float
     ba.WT = nullptr;
   }
   ba.W16 = fwd16 ? (__half*)(ws + w.dW16) : nullptr;
+  // the unitary build depends on the circuit parameters only (CRZ ansatze: also on the mesh
+  // diagonal of the front launches): it runs on the side stream beside the premap
+  const bool side = pl->aux && !qp_has_crz(pl->c.ansatz);
+  if (side) {
+    qpd::BuildArgs bs = ba;
+    if (fwd16) bs.W = nullptr;
+    if (cudaEventRecord(pl->ev_fork, s) != cudaSuccess || cudaStreamWaitEvent(pl->aux, pl->ev_fork, 0) != cudaSuccess)
+      return QP_ERR_CUDA;
+    qpd::dense_gates_kernel<<<1, L * n, 0, pl->aux>>>(bs);
+    qpd::dense_build_kernel<<<dim, 128, 2 * dim * 16, pl->aux>>>(bs);
+    if (cudaEventRecord(pl->ev_join, pl->aux) != cudaSuccess) return QP_ERR_CUDA;
+  }
+  qp_status st = launch_front(pl, d_params, pts, npts, w, s, true);
+  if (st != QP_OK) return st;
+  launches += front_launches(pl);
   if (P > 0) {
     const int64_t tot = P * n;
     const int hb = (int)((tot + 255) / 256 < pl->sm_count * 4 ? (tot + 255) / 256 : pl->sm_count * 4);
@@ -869,8 +897,12 @@ static qp_status dense_loss_grad(qp_plan* pl, const float* d_params, const float
     launches += 1;
   }
   if (fwd16) ba.W = nullptr;
-  qpd::dense_gates_kernel<<<1, L * n, 0, s>>>(ba);
-  qpd::dense_build_kernel<<<dim, 128, 2 * dim * 16, s>>>(ba);
+  if (side) {
+    if (cudaStreamWaitEvent(s, pl->ev_join, 0) != cudaSuccess) return QP_ERR_CUDA;
+  } else {
+    qpd::dense_gates_kernel<<<1, L * n, 0, s>>>(ba);
+    qpd::dense_build_kernel<<<dim, 128, 2 * dim * 16, s>>>(ba);
+  }
   launches += 2;
   int64_t base = 0;
   if (fused) {
