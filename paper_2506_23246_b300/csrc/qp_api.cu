@@ -1007,6 +1007,14 @@ static qp_status dense_loss_grad(qp_plan* pl, const float* d_params, const float
   }
   prof_mark(pl, 1, false, s);
   launches += 1;
+  // the gate-gradient chain (slot sum, Y = U'G, sweep) depends on G only: on the side stream,
+  // beside mu and the premap backward, joined back before the reduction
+  cudaStream_t ss = s;
+  if (side) {
+    if (cudaEventRecord(pl->ev_fork, s) != cudaSuccess || cudaStreamWaitEvent(pl->aux, pl->ev_fork, 0) != cudaSuccess)
+      return QP_ERR_CUDA;
+    ss = pl->aux;
+  }
   qpd::SweepArgs sa;
   sa.part = wa.part; sa.nchunks = (int32_t)wgm.nslots; sa.n = n; sa.L = L; sa.ansatz = pl->c.ansatz;
   sa.U = (const double2*)(ws + w.dU); sa.G = (float2*)(ws + w.dG); sa.Y = (float2*)(ws + w.dY);
@@ -1015,13 +1023,13 @@ static qp_status dense_loss_grad(qp_plan* pl, const float* d_params, const float
   sa.crz = qp_has_crz(pl->c.ansatz) ? (const float2*)(ws + w.crz) : nullptr;
   {
     const int gg = gsum_groups(pl);
-    qpd::dense_gsum_kernel<<<dim3((dim * dim + 255) / 256, gg), 256, 0, s>>>(sa, gg, (float4*)(ws + w.dgs));
+    qpd::dense_gsum_kernel<<<dim3((dim * dim + 255) / 256, gg), 256, 0, ss>>>(sa, gg, (float4*)(ws + w.dgs));
     const int64_t fb = ((int64_t)dim * dim + 255) / 256;
-    qpd::dense_gsum_fin_kernel<<<(unsigned)(fb < pl->sm_count * 8 ? fb : pl->sm_count * 8), 256, 0, s>>>(
+    qpd::dense_gsum_fin_kernel<<<(unsigned)(fb < pl->sm_count * 8 ? fb : pl->sm_count * 8), 256, 0, ss>>>(
         sa, gg, (const float4*)(ws + w.dgs));
     launches += 1;
   }
-  qpd::dense_y_kernel<<<dim3(dim / 16, dim / 16), 256, 0, s>>>(sa);
+  qpd::dense_y_kernel<<<dim3(dim / 16, dim / 16), 256, 0, ss>>>(sa);
   if (n <= 8) {
     // the whole sweep in one cluster launch (Y lives in the cluster's shared memory)
     const int S = qpd::swc_size(n, pl->swc_big);
@@ -1029,7 +1037,7 @@ static qp_status dense_loss_grad(qp_plan* pl, const float* d_params, const float
     cfg.gridDim = dim3(S);
     cfg.blockDim = dim3(qpd::SWC_THREADS);
     cfg.dynamicSmemBytes = qpd::swc_smem(n, L, S, qp_crz_sums(pl->c.ansatz, n));
-    cfg.stream = s;
+    cfg.stream = ss;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
     attr[0].val.clusterDim.x = S;
@@ -1046,10 +1054,10 @@ static qp_status dense_loss_grad(qp_plan* pl, const float* d_params, const float
     const int64_t tot = (int64_t)dim * dim;
     const int rblocks = (int)((tot + 255) / 256 < pl->sm_count * 8 ? (tot + 255) / 256 : pl->sm_count * 8);
     for (int l = L - 1; l >= 0; --l) {
-      qpd::dense_sweep_ring_kernel<<<rblocks, 256, 0, s>>>(sa, l, Ya, Yb);
+      qpd::dense_sweep_ring_kernel<<<rblocks, 256, 0, ss>>>(sa, l, Ya, Yb);
       if (l > 0) {
-        qpd::dense_sweep_left_kernel<16><<<dim / tcol, 256, dim * tcol * 8, s>>>(sa, l, Yb);
-        qpd::dense_sweep_right_kernel<16><<<dim / trow, 256, dim * trow * 8, s>>>(sa, l, Yb);
+        qpd::dense_sweep_left_kernel<16><<<dim / tcol, 256, dim * tcol * 8, ss>>>(sa, l, Yb);
+        qpd::dense_sweep_right_kernel<16><<<dim / trow, 256, dim * trow * 8, ss>>>(sa, l, Yb);
         launches += 2;
       }
       float2* t = Ya; Ya = Yb; Yb = t;
@@ -1057,6 +1065,7 @@ static qp_status dense_loss_grad(qp_plan* pl, const float* d_params, const float
     }
   }
   launches += 2;
+  if (side && cudaEventRecord(pl->ev_join, pl->aux) != cudaSuccess) return QP_ERR_CUDA;
   if (mlp) {
     if (fused) {
       // mu rows on the tensor cores with the embedding gradients as the epilogue
@@ -1120,6 +1129,7 @@ static qp_status dense_loss_grad(qp_plan* pl, const float* d_params, const float
     if (st != QP_OK) return st;
     launches += premap_bwd_launches(pl);
   }
+  if (side && cudaStreamWaitEvent(s, pl->ev_join, 0) != cudaSuccess) return QP_ERR_CUDA;
   st = launch_reduce(pl, w, d_params, npts, d_loss, d_grad, mlp, s);
   pl->last_launches = launches + 1;
   return st;
