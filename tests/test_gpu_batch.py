@@ -220,3 +220,20 @@ def test_grouped_more_instances_than_one_launch(torch_cuda):
     for (lr, gr), (l, g) in zip(ref, got):
         assert _rel(l.cpu().numpy(), lr.cpu().numpy()) < 1e-6
         assert _rel(g.cpu().numpy(), gr.cpu().numpy()) < 2e-6
+
+
+def test_batch_flags_and_tuner_arguments(torch_cuda):
+    """Unknown flag bits and a duplicated plan are refused before any launch; the tuner on a mix
+    without gate-by-gate instances reports no shape."""
+    from paper_2506_23246_b300 import qp
+    torch = torch_cuda
+    plans, params, sets, _ = _mix(torch, [(4, 2, 40, "vacuum"), (8, 2, 30, "vacuum")], 30)
+    handles, arr, keep, res = qp._step_args(plans, params, sets, None, None)
+    s = torch.cuda.current_stream()
+    import ctypes
+    rc = qp.lib().qp_batch_step_flags(handles, 2, arr, ctypes.c_void_p(s.cuda_stream), 2)
+    assert rc == 1
+    assert qp.batch_tune(plans[1:], params[1:], sets[1:]) == (0, 0)
+    w, k = qp.batch_tune(plans, params, sets)
+    assert w in (4, 8, 12) and k in (1, 4, 16)
+    torch.cuda.synchronize()
