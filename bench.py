@@ -67,13 +67,11 @@ def _dist():
     return rank, world, local
 
 
-def _config(world, graph=False):
+def _config(world):
     return {"workload": WORKLOAD, "n_qubits": 8, "n_layers": 6, "ansatz": "strongly entangling",
             "premap": "RFF 64 freq + tanh MLP width 32", "medium": "dielectric",
             "colloc_per_gpu": 65536, "ic_per_gpu": 4096, "global_batch": 65536 * world,
             "parallelism": "dp%d" % world if world > 1 else "single",
-            "launch": "one CUDA graph per step (the library's kernels captured once, replayed)" if graph
-                      else "kernels launched one by one",
             "l2": "flushed between timed steps (256 MiB write)"}
 
 
@@ -427,7 +425,9 @@ def run_native(a):
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
                 "warmup": max(a.warmup, 3), "ms_per_step": ms, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": dtype, "data": "synthetic",
-                "config": _config(world, graph is not None),
+                "config": _config(world),
+                "launch": ("one CUDA graph per step (the library's kernels captured once, replayed)"
+                           if graph is not None else "kernels launched one by one"),
                 "e2e": {"value": world * ncol / (ems / 1000.0), "unit": UNIT,
                         "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
                 "gpu_launches": launches * a.steps,
