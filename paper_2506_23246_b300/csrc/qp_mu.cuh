@@ -15,8 +15,9 @@ namespace qpd {
 //   D_q = sum_k sign_q(k) r_0[k ^ e_q] mu_s[k]   (s >= 1: dL/dJ_{q, s-1})
 // with sign_q(k) = +1 where qubit q is 1. r_s is a product over qubits: the five lowest index
 // bits come from 32-entry tables, the higher ones from a per-chunk factor, so every sum splits
-// into 32-column correlations. The drain of a tile runs one 32-column chunk per K-step of the
-// next tile, under its tensor-core work.
+// into 32-column correlations. Four drain warps take a finished tile's correlations out of
+// tensor memory while eight staging warps and the tensor core work on the next tile (the two
+// accumulator buffers alternate).
 struct MuArgs {
   const float* thetaJ;     // [P][n] float4
   const __half* WT16;      // FP16 pairs of 2^14 U' transposed, [2 dim / HKC][hi, lo][dim x HKC]
@@ -175,7 +176,7 @@ __global__ void __launch_bounds__(MU_THREADS, 1) dense_mu_embed_kernel(MuArgs a)
   uint64_t* bars = reinterpret_cast<uint64_t*>(sm + 2 * stage_bytes);
   uint64_t* w_full = bars;         // [2] W operand of a stage landed
   uint64_t* mma_done = bars + 2;   // [2] tensor-core work of a stage finished
-  uint64_t* a_full = bars + 4;     // [2] A operand of a stage written (4 staging warps)
+  uint64_t* a_full = bars + 4;     // [2] A operand of a stage written (8 staging warps)
   uint64_t* acc_free = bars + 6;   // [2] a tensor-memory buffer drained (4 drain warps)
   uint64_t* tile_done = bars + 8;  // [2] all MMAs of the tile in a tensor-memory buffer finished
   uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + 2 * stage_bytes + 96);
@@ -312,8 +313,8 @@ __global__ void __launch_bounds__(MU_THREADS, 1) dense_mu_embed_kernel(MuArgs a)
     if (!ok && lane == 0) atomicExch(a.status, 6);
   } else {
     // ---- drain warps: the embedding correlations of each finished tile, read from tensor
-    // memory while the staging warps and the tensor core work on the next tile (warp 4 + w
-    // reads the tensor-memory lanes of staging warp w: the same rows)
+    // memory while the staging warps and the tensor core work on the next tile (drain warp w
+    // reads tensor-memory lane quarter w, the rows that staging warps w and w + 4 wrote)
     const int dw = warp - MU_STAGERS / 32;
     MuRow R;
     auto bar = [&]() {
