@@ -685,7 +685,7 @@ def run_paper_net(a):
         prob = W.problem("vacuum", w_energy=10.0, energy_slice=g * g, energy_nt=g)
         sets = {"colloc": W.grid_points(g, g, g, 1.5), "ic": W.ic_grid(g, g)}
         params = W.init_params(circ, 0)
-        plan = qp.Plan(circ, prob)
+        plan = qp.Plan(circ, prob, path=a.path)
         dp = torch.tensor(params, device=dev)
         dsets = {k: torch.tensor(v, device=dev) for k, v in sets.items()}
         plan.reserve(sum(v.shape[0] for v in dsets.values()), dev)

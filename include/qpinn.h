@@ -88,7 +88,7 @@ typedef enum { QP_PREMAP_DIRECT = 0, QP_PREMAP_RFF_MLP = 1 } qp_premap;
  * 22-bit operands: FP16 pairs scaled by powers of two (three FP16 products per term, the hi*hi
  * products and the hi*lo + lo*hi corrections in separate accumulators; the default and the
  * only form of the n = 7, 8 loss kernels) or 3xTF32 (qp_plan_set_operands). Forward for
- * n >= 5, loss + gradient for n >= 7. AUTO picks GEMM_SPLIT for 8-10 qubits, SIMT otherwise.
+ * n >= 5, loss + gradient for n >= 7. AUTO picks GEMM_SPLIT for 7-10 qubits, SIMT otherwise.
  * GEMM_BF16X3 is reserved (QP_ERR_UNSUPPORTED): FP16 pairs with power-of-two scaling give
  * the same operand precision with three products instead of six. */
 typedef enum {
