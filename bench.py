@@ -51,6 +51,9 @@ def _args():
     ap.add_argument("--c3-grid", type=int, default=64,
                     help="default workload: x and y points of the collocation grid (64: the benchmark "
                          "step; smaller only for profiling captures)")
+    ap.add_argument("--paper-grid", type=int, default=0,
+                    help="--workload paper_net: only this grid (points per axis; 0: the 40^3 and 87^3 "
+                         "grids of the paper's timing table)")
     ap.add_argument("--workload", default="c3", choices=["c3", "c5", "configs", "paper_net"],
                     help="c3: the full QPINN step (default); c5: 32 uneven instances in one "
                          "batched call against the same instances called one by one; configs: "
@@ -679,7 +682,7 @@ def run_paper_net(a):
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
     paper = {40: 0.145136, 87: 0.849967}
-    for g in (40, 87):
+    for g in ((a.paper_grid,) if a.paper_grid > 0 else (40, 87)):
         circ = W.circuit(7, 4, 7, ansatz="strong_rot", enc="rx", scale="acos", premap="rff_mlp",
                          rff_freqs=128, mlp_width=128, mlp_depth=3, periodic=True)
         prob = W.problem("vacuum", w_energy=10.0, energy_slice=g * g, energy_nt=g)
@@ -710,7 +713,8 @@ def run_paper_net(a):
                           "steps": a.steps, "warmup": max(a.warmup, 3),
                           "gpu_launches_per_step": plan.last_launch_count(),
                           "paper_context": {"system": "TorQ, one training epoch (backprop, Adam), A100 or L40s",
-                                            "s_per_epoch": paper[g], "pts_per_s": ncol / paper[g]}}),
+                                            "s_per_epoch": paper[g], "pts_per_s": ncol / paper[g]}
+                                          if g in paper else None}),
               flush=True)
         del plan
         torch.cuda.empty_cache()

@@ -13,7 +13,7 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 LIB = os.path.join(HERE, "libqpinn.so")
 SOURCES = ["qp_api.cu", "qp_sched.cpp", "qp_selftest.cpp"]
 HEADERS = ["qp_common.h", "qp_circuit.cuh", "qp_aux.cuh", "qp_tc.cuh", "qp_dense.cuh", "qp_fused.cuh",
-           "qp_mu.cuh", "qp_wgrad.cuh", "qp_premap_tc.cuh"]
+           "qp_mu.cuh", "qp_wgrad.cuh", "qp_premap_tc.cuh", "qp_mlp.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -38,7 +38,7 @@ def build(force=False, verbose=False):
     tmp = LIB + ".tmp%d" % os.getpid()
     cmd = [_nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-shared",
            "-I", INCLUDE, "-Xptxas", "-v" if verbose else "-O3",
-           *[os.path.join(CSRC, f) for f in SOURCES], "-o", tmp]
+           *[os.path.join(CSRC, f) for f in SOURCES], "-lcublas", "-o", tmp]
     res = subprocess.run(cmd, capture_output=True, text=True)
     if res.returncode != 0:
         sys.stderr.write(res.stdout + res.stderr)

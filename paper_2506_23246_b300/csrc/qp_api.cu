@@ -3,6 +3,7 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_runtime.h>
+#include <cublas_v2.h>
 
 #include <cmath>
 #include <cstdio>
@@ -61,7 +62,12 @@ struct qp_plan {
   // from and joined back into the call's stream within the call)
   cudaStream_t aux = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  // layer-by-layer premap: the library GEMM handle of its contractions and the compute type
+  // that handle accepted (FP32 emulated on the tensor cores, else plain FP32)
+  cublasHandle_t blas = nullptr;
+  cublasComputeType_t blas_ct = CUBLAS_COMPUTE_32F_EMULATED_16BFX9;
   ~qp_plan() {
+    if (blas) cublasDestroy(blas);
     if (ev_fork) cudaEventDestroy(ev_fork);
     if (ev_join) cudaEventDestroy(ev_join);
     if (aux) cudaStreamDestroy(aux);
@@ -71,6 +77,7 @@ struct qp_plan {
 namespace {
 
 constexpr int kMaxWarps = 12;
+constexpr size_t kBlasWorkspace = size_t(32) << 20;   // library GEMM scratch of a deep-premap call
 
 // Fixed RFF frequencies: Omega [F][3], or [F][6] with the periodic input map.
 int64_t omega_count(const qp_circuit& c) {
@@ -120,6 +127,7 @@ struct WsLayout {
   size_t sxb, sF, sgs, sge, spart;   // symmetry penalty: set-2 points, fields, cotangents, sums
   size_t mtg;                        // periodic map: FP64 sum of the learned period's gradient
   size_t desc;                       // multi-instance launch: the instance's argument block
+  size_t mx0, blasws;                // layer-by-layer premap: RFF features [P][4][2F], GEMM scratch
   size_t dW, dphi, dU, dG, dY, dpart, dWT, dmu, dW16, dcs, dgs, dgates, total;
 };
 
@@ -163,14 +171,17 @@ WgGeom wg_geom(const qp_plan* pl, int64_t nkc) {
 bool dense_path(const qp_plan* pl) { return pl->path == QP_PATH_GEMM_SPLIT; }
 
 // Kernels launched by launch_front: gate preparation, the CRZ mesh diagonal (CRZ ansatze), the
-// premap (one kernel, or one per layer).
+// premap (one kernel, or layer by layer the features and one activation kernel per layer; the
+// layers' library GEMMs are not counted).
 int front_launches(const qp_plan* pl) {
-  return (qp_has_crz(pl->c.ansatz) ? 2 : 1) + (pl->deep ? pl->c.mlp_depth + 1 : 1);
+  return (qp_has_crz(pl->c.ansatz) ? 2 : 1) + (pl->deep ? pl->c.mlp_depth + 2 : 1);
 }
 // Kernels of the premap backward: the fused per-point kernels (1 or 2), or layer by layer the
-// output layer, a weight gradient per layer and an input cotangent per hidden layer.
+// output layer, the bias gradient and the unused slots' zeroing per layer, the tanh backward per
+// hidden layer and the period's two kernels with the periodic map.
 int premap_bwd_launches(const qp_plan* pl) {
-  return pl->deep ? 1 + (pl->c.mlp_depth + 1) + pl->c.mlp_depth + (pl->c.periodic ? 2 : 0) : (pl->pg_ok ? 1 : 2);
+  return pl->deep ? 1 + 2 * (pl->c.mlp_depth + 1) + pl->c.mlp_depth + (pl->c.periodic ? 2 : 0)
+                  : (pl->pg_ok ? 1 : 2);
 }
 
 // The fused forward kernel keeps a tile's whole output row (2^(n+1) FP32 columns) in tensor
@@ -261,6 +272,8 @@ WsLayout ws_layout(const qp_plan* pl, int64_t P0) {
   w.spart = o; o = al256(o + (sym ? (size_t)pl->sm_count * 4 * 8 : 0));
   w.mtg = o; o = al256(o + (pl->c.periodic ? 8 : 0));
   w.desc = o; o = al256(o + (dense_path(pl) ? 0 : sizeof(QPCircArgs)));
+  w.mx0 = o; o = al256(o + (pl->deep ? (size_t)P * 4 * 2 * pl->c.rff_freqs * 4 : 0));
+  w.blasws = o; o = al256(o + (pl->deep ? kBlasWorkspace : 0));
   const size_t dim = (size_t)1 << n;
   const bool dn = dense_path(pl);
   w.dW = o; o = al256(o + (dn ? 2 * (2 * dim) * dim * 4 : 0));
@@ -534,6 +547,11 @@ qp_status qp_plan_create(const qp_circuit* circuit, const qp_problem* problem, i
     const bool one_layer = circuit->mlp_depth == 1 && (H == 4 || H == 8 || H == 16 || H == 32 || H == 64) &&
                            (F % 2) == 0 && (int64_t)H * 2 * F <= 16 * 4 * 256 && n * H <= 4 * 256;
     pl->deep = !one_layer || circuit->periodic;
+    if (pl->deep && cublasCreate(&pl->blas) != CUBLAS_STATUS_SUCCESS) {
+      pl->blas = nullptr;
+      delete pl;
+      return QP_ERR_CUDA;
+    }
     pl->pg_ok = one_layer && F == qpk::PG_F && H == qpk::PG_H && n <= 16;
     if (pl->pg_ok &&
         (raise_smem_limit((void*)qpk::premap_fwd_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -690,67 +708,145 @@ static int mlp_grid(const qp_plan* pl, int64_t tiles) {
   return (int)(tiles < 1 ? 1 : (tiles < cap ? tiles : cap));
 }
 
-// Forward of the layer-by-layer premap: every layer in turn, the output layer writes the
-// angles and their Jacobian (and counts the dielectric set).
+// Library GEMM of the layer-by-layer premap on the plan's handle, column-major arguments
+// (C = op(A) op(B), alpha 1). The first call that the emulated FP32 compute type does not
+// accept switches the plan to plain FP32.
+static qp_status mlp_gemm(qp_plan* pl, cublasOperation_t ta, cublasOperation_t tb, int m, int n, int k,
+                          const float* A, int lda, const float* B, int ldb, float* C, int ldc,
+                          long long sa = 0, long long sb = 0, long long sc = 0, int batch = 0) {
+  const float one = 1.f, zero = 0.f;
+  for (;;) {
+    const cublasStatus_t st = batch > 0
+        ? cublasGemmStridedBatchedEx(pl->blas, ta, tb, m, n, k, &one, A, CUDA_R_32F, lda, sa, B, CUDA_R_32F, ldb,
+                                     sb, &zero, C, CUDA_R_32F, ldc, sc, batch, pl->blas_ct, CUBLAS_GEMM_DEFAULT)
+        : cublasGemmEx(pl->blas, ta, tb, m, n, k, &one, A, CUDA_R_32F, lda, B, CUDA_R_32F, ldb, &zero, C,
+                       CUDA_R_32F, ldc, pl->blas_ct, CUBLAS_GEMM_DEFAULT);
+    if (st == CUBLAS_STATUS_SUCCESS) return QP_OK;
+    if (pl->blas_ct == CUBLAS_COMPUTE_32F ||
+        (st != CUBLAS_STATUS_NOT_SUPPORTED && st != CUBLAS_STATUS_INVALID_VALUE))
+      return QP_ERR_CUDA;
+    pl->blas_ct = CUBLAS_COMPUTE_32F;
+  }
+}
+
+// Binds the plan's handle to the call's stream and workspace (no allocation, so the calls
+// can be captured into a graph).
+static qp_status mlp_blas_bind(qp_plan* pl, const WsLayout& w, cudaStream_t s) {
+  if (cublasSetStream(pl->blas, s) != CUBLAS_STATUS_SUCCESS ||
+      cublasSetWorkspace(pl->blas, (char*)pl->ws + w.blasws, kBlasWorkspace) != CUBLAS_STATUS_SUCCESS)
+    return QP_ERR_CUDA;
+  return QP_OK;
+}
+
+static int ew_grid(const qp_plan* pl, int64_t n) {
+  const int64_t b = (n + 255) / 256, cap = (int64_t)pl->sm_count * 8;
+  return (int)(b < 1 ? 1 : (b < cap ? b : cap));
+}
+
+// Forward of the layer-by-layer premap: the RFF features of every point, then per layer the
+// contraction of all (point, s) rows as one library GEMM and its activation; the output layer
+// writes the angles and their Jacobian (and counts the dielectric set).
 static qp_status launch_mlp_fwd(qp_plan* pl, const float* d_params, const float* const pts[3],
                                 const int64_t npts[3], const WsLayout& w, cudaStream_t s) {
+  char* ws = (char*)pl->ws;
   const int64_t P = npts[0] + npts[1] + npts[2];
-  for (int l = 0; l <= pl->c.mlp_depth; ++l) {
+  const int D = pl->c.mlp_depth;
+  if (4 * P > (int64_t)INT32_MAX) return QP_ERR_UNSUPPORTED;
+  const int R = (int)(4 * P);
+  qp_status st = mlp_blas_bind(pl, w, s);
+  if (st != QP_OK) return st;
+  float* X0 = (float*)(ws + w.mx0);
+  {
+    const qpm::MlpArgs m0 = mlp_layer_args(pl, d_params, pts, npts, w, 0);
+    qpm::mlp_features_kernel<<<ew_grid(pl, P * m0.F), 256, 0, s>>>(m0, X0);
+  }
+  for (int l = 0; l <= D; ++l) {
     const qpm::MlpArgs m = mlp_layer_args(pl, d_params, pts, npts, w, l);
-    const int64_t tiles = ((P + qpm::MT_P - 1) / qpm::MT_P) * ((m.out + qpm::MT_N - 1) / qpm::MT_N);
-    qpm::mlp_fwd_kernel<<<mlp_grid(pl, tiles), qpm::MT_THREADS, 0, s>>>(m);
+    const float* X = l == 0 ? X0 : m.act_in;
+    float* Hl = l == D ? (float*)(ws + w.mcot) : m.act_out;
+    // H[R][out] = X[R][in] W^T: column-major H^T = W X^T
+    if (R > 0) st = mlp_gemm(pl, CUBLAS_OP_T, CUBLAS_OP_N, m.out, R, m.in, m.W, m.in, X, m.in, Hl, m.out);
+    if (st != QP_OK) return st;
+    if (l < D)
+      qpm::mlp_act_kernel<<<ew_grid(pl, P * m.out), 256, 0, s>>>(Hl, m.b, P, m.out);
+    else
+      qpm::mlp_out_kernel<<<ew_grid(pl, P * m.out), 256, 0, s>>>(Hl, m);
   }
   return cuda_status(cudaGetLastError());
 }
 
+// Weight and bias gradients of layer l from its input rows X [R][in] and the cotangents of
+// its pre-activations cot [R][out], one partial slot per point chunk (the slots are summed in
+// FP64 with the others): dW = cot^T X per chunk as one strided batched GEMM, the last partial
+// chunk as one more GEMM, the unused slots zeroed.
+static qp_status mlp_layer_dw(qp_plan* pl, const float* X, const float* cot, int64_t P, int in, int out,
+                              int64_t w_off, int64_t b_off, const WsLayout& w, cudaStream_t s) {
+  float* part = (float*)((char*)pl->ws + w.wpart);
+  const int64_t nW = pl->mlp_count - pl->nfixed;
+  const int nc = pl->nwblk;
+  const int64_t chunk = P > nc ? (P + nc - 1) / nc : 1;   // points per slot
+  const int64_t nfull = P / chunk, rest = P - nfull * chunk;
+  const int used = (int)(nfull + (rest > 0 ? 1 : 0));
+  const int rc = (int)(4 * chunk);
+  qp_status st = QP_OK;
+  // column-major dW^T [in x out] = X_c^T (in x rc) . cot_c (rc x out)
+  if (nfull > 0)
+    st = mlp_gemm(pl, CUBLAS_OP_N, CUBLAS_OP_T, in, out, rc, X, in, cot, out, part + w_off, in,
+                  (long long)rc * in, (long long)rc * out, (long long)nW, (int)nfull);
+  if (st == QP_OK && rest > 0)
+    st = mlp_gemm(pl, CUBLAS_OP_N, CUBLAS_OP_T, in, out, (int)(4 * rest), X + nfull * rc * (int64_t)in, in,
+                  cot + nfull * rc * (int64_t)out, out, part + nfull * nW + w_off, in);
+  if (st != QP_OK) return st;
+  qpm::mlp_db_kernel<<<nc, out < 256 ? ((out + 31) / 32) * 32 : 256, 0, s>>>(cot, P, out, chunk, nc, part, nW, b_off);
+  qpm::mlp_zero_slots_kernel<<<ew_grid(pl, (int64_t)(nc - used) * out * in), 256, 0, s>>>(
+      part, nW, w_off, (int64_t)out * in, used, nc);
+  return QP_OK;
+}
+
 // Backward of the layer-by-layer premap from dL/dtheta, dL/dJ: the output layer's cotangents,
-// then per layer (last to first) its weight-gradient partials (one slot per row chunk) and
-// the cotangents of the previous layer.
+// then per layer (last to first) its weight-gradient partials and the cotangents of the
+// previous layer (dU = cot W as one library GEMM, then back through that layer's tanh). With
+// the periodic map the first layer's input cotangents give the learned period's gradient.
 static qp_status launch_mlp_bwd(qp_plan* pl, const float* d_params, const float* const pts[3],
                                 const int64_t npts[3], const WsLayout& w, cudaStream_t s) {
   char* ws = (char*)pl->ws;
   const int64_t P = npts[0] + npts[1] + npts[2];
   const int n = pl->c.n_qubits, D = pl->c.mlp_depth, H = pl->c.mlp_width;
   const int64_t mw = H > n ? H : n;
+  const int64_t nW = pl->mlp_count - pl->nfixed;
+  if (4 * P > (int64_t)INT32_MAX) return QP_ERR_UNSUPPORTED;
+  const int R = (int)(4 * P);
+  qp_status st = mlp_blas_bind(pl, w, s);
+  if (st != QP_OK) return st;
   float* cot[2] = {(float*)(ws + w.mcot), (float*)(ws + w.mcot) + P * 4 * mw};
   int cur = 0;
-  {
-    const int64_t tot = P * n;
-    const int gb = mlp_grid(pl, (tot + 255) / 256);
-    qpm::mlp_bwd_out_kernel<<<gb, 256, 0, s>>>((const float*)(ws + w.d2), (const float*)(ws + w.dthetaJ), P, n,
-                                               pl->c.scale, cot[cur]);
-  }
-  const int64_t lstride = P * 4 * H;
+  qpm::mlp_bwd_out_kernel<<<ew_grid(pl, P * n), 256, 0, s>>>((const float*)(ws + w.d2),
+                                                             (const float*)(ws + w.dthetaJ), P, n, pl->c.scale,
+                                                             cot[cur]);
+  float* X0 = (float*)(ws + w.mx0);
   for (int l = D; l >= 0; --l) {
-    qpm::MlpDwArgs da;
-    da.x = mlp_layer_args(pl, d_params, pts, npts, w, l);
+    const qpm::MlpArgs m = mlp_layer_args(pl, d_params, pts, npts, w, l);
     int in, out;
-    mlp_layer_geom(pl, l, in, out, da.w_off, da.b_off);
-    da.cot = cot[cur];
-    da.part = (float*)(ws + w.wpart);
-    da.nW = pl->mlp_count - pl->nfixed;
-    da.nchunks = pl->nwblk;
-    const int nto = (out + qpm::MT_N - 1) / qpm::MT_N, nti = (in + qpm::MT_N - 1) / qpm::MT_N;
-    qpm::mlp_dw_kernel<<<dim3((unsigned)(nto * nti), (unsigned)pl->nwblk), qpm::MT_THREADS, 0, s>>>(da);
-    if (l > 0 || pl->c.periodic) {
-      qpm::MlpBwdArgs ba;
-      ba.ptot = P;
-      ba.W = da.x.W;
-      ba.in = in;
-      ba.out = out;
-      ba.cot = cot[cur];
-      ba.act_prev = l > 0 ? (const float*)(ws + w.mact) + (int64_t)(l - 1) * lstride : nullptr;
-      ba.cot_prev = l > 0 ? cot[cur ^ 1] : nullptr;
-      ba.x = da.x;
-      // first layer with the periodic map: the input cotangents give the period's gradient
-      ba.tgrad = l == 0 ? (double*)(ws + w.mtg) : nullptr;
-      if (l == 0 && cudaMemsetAsync(ws + w.mtg, 0, sizeof(double), s) != cudaSuccess) return QP_ERR_CUDA;
-      const int64_t tiles = ((P + qpm::MT_P - 1) / qpm::MT_P) * ((in + qpm::MT_N - 1) / qpm::MT_N);
-      qpm::mlp_bwd_dx_kernel<<<mlp_grid(pl, tiles), qpm::MT_THREADS, 0, s>>>(ba);
-      if (l == 0)
-        qpm::mlp_period_fin_kernel<<<(pl->nwblk + 255) / 256, 256, 0, s>>>(
-            (const double*)(ws + w.mtg), (float*)(ws + w.wpart), da.nW, 0, pl->nwblk);
+    int64_t w_off, b_off;
+    mlp_layer_geom(pl, l, in, out, w_off, b_off);
+    const float* X = l == 0 ? X0 : m.act_in;
+    st = mlp_layer_dw(pl, X, cot[cur], P, in, out, w_off, b_off, w, s);
+    if (st != QP_OK) return st;
+    if (l > 0) {
+      // dU[R][in] = cot[R][out] W: column-major dU^T = W^T cot^T
+      float* dU = cot[cur ^ 1];
+      if (R > 0) st = mlp_gemm(pl, CUBLAS_OP_N, CUBLAS_OP_N, in, R, out, m.W, in, cot[cur], out, dU, in);
+      if (st != QP_OK) return st;
+      qpm::mlp_dact_kernel<<<ew_grid(pl, P * in), 256, 0, s>>>(dU, m.act_in, P, in);
       cur ^= 1;
+    } else if (pl->c.periodic) {
+      // the features are no longer needed: their cotangents go over them
+      if (R > 0) st = mlp_gemm(pl, CUBLAS_OP_N, CUBLAS_OP_N, in, R, out, m.W, in, cot[cur], out, X0, in);
+      if (st != QP_OK) return st;
+      if (cudaMemsetAsync(ws + w.mtg, 0, sizeof(double), s) != cudaSuccess) return QP_ERR_CUDA;
+      qpm::mlp_period_kernel<<<ew_grid(pl, P * in), 256, 0, s>>>(X0, m, (double*)(ws + w.mtg));
+      qpm::mlp_period_fin_kernel<<<(pl->nwblk + 255) / 256, 256, 0, s>>>(
+          (const double*)(ws + w.mtg), (float*)(ws + w.wpart), nW, 0, pl->nwblk);
     }
   }
   return cuda_status(cudaGetLastError());

@@ -402,4 +402,125 @@ __global__ void mlp_period_fin_kernel(const double* tgrad, float* part, int64_t 
     part[(int64_t)b * nW + t_off] = b == 0 ? (float)*tgrad : 0.f;
 }
 
+// ------------------------------------------------------------------------- library-GEMM form
+// The layers' contractions as plain GEMMs (library calls on the tensor cores, FP32 results),
+// with the point-coupled parts as elementwise kernels around them. Rows are (point, s) with
+// s = 0 the value and s = 1..3 the x, y, t tangents; a hidden layer's stored rows are its
+// outputs (y0, y_d = s z_d), which are the next layer's inputs as they stand.
+
+// RFF features of every point, [P][4][2F]: row s = 0 the features, s = 1..3 their tangents.
+__global__ void mlp_features_kernel(MlpArgs a, float* X) {
+  const int F = a.F;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < a.ptot * F;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t gp = e / F;
+    const int f = (int)(e % F);
+    int set;
+    const float* v = mlp_point(a, gp, set);
+    const float4 g = rff_arg(a, v, f);
+    float sn, cs;
+    sincosf(g.x, &sn, &cs);
+    float* r = X + gp * 4 * (int64_t)(2 * F);
+    r[f] = cs; r[F + f] = sn;
+    r[2 * F + f] = -sn * g.y; r[2 * F + F + f] = cs * g.y;
+    r[4 * F + f] = -sn * g.z; r[4 * F + F + f] = cs * g.z;
+    r[6 * F + f] = -sn * g.w; r[6 * F + F + f] = cs * g.w;
+  }
+}
+
+// Hidden layer after its contraction, in place on H = [P][4][out] (pre-activations h0 - b and
+// pre-tangents z_d): y0 = tanh(h0), y_d = (1 - y0^2) z_d.
+__global__ void mlp_act_kernel(float* H, const float* b, int64_t P, int out) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < P * out; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t p = e / out;
+    const int o = (int)(e % out);
+    float* r = H + p * 4 * (int64_t)out + o;
+    const float y0 = tanhf(r[0] + __ldg(&b[o])), sd = 1.f - y0 * y0;
+    r[0] = y0;
+    r[out] *= sd;
+    r[2 * out] *= sd;
+    r[3 * out] *= sd;
+  }
+}
+
+// Output layer after its contraction (H = [P][4][n]): theta = g(h), J_d = g'(h) h_d (Eq. 27),
+// the rows (h, h_d) kept for the backward, and the dielectric-set count of the loss.
+__global__ void mlp_out_kernel(const float* H, MlpArgs a) {
+  const int n = a.out;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < a.ptot * n; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t gp = e / n;
+    const int o = (int)(e % n);
+    const float* r = H + gp * 4 * (int64_t)n + o;
+    const float h = r[0] + __ldg(&a.b[o]);
+    float g0, g1, g2;
+    qpk::scale_tanh(a.scale, h, g0, g1, g2);
+    reinterpret_cast<float4*>(a.thetaJ)[e] = make_float4(g0, g1 * r[n], g1 * r[2 * n], g1 * r[3 * n]);
+    reinterpret_cast<float4*>(a.hout)[e] = make_float4(h, r[n], r[2 * n], r[3 * n]);
+    if (o == 0 && a.medium == 1) {
+      int set;
+      const float* v = mlp_point(a, gp, set);
+      if (set == 0) {
+        const float dx = v[0] - a.disk_x0, dy = v[1] - a.disk_y0;
+        if (__fmaf_rn(dx, dx, dy * dy) < a.disk_r * a.disk_r) atomicAdd(&a.counts[0], 1);
+      }
+    }
+  }
+}
+
+// Through a hidden layer's tanh, in place on dU = [P][4][in] (cotangents of its outputs y0, y_d)
+// with its stored outputs act = [P][4][in]: dH0 = s dU0 - 2 y0 sum_d y_d dU_d, dZ_d = s dU_d.
+__global__ void mlp_dact_kernel(float* dU, const float* act, int64_t P, int in) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < P * in; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t p = e / in;
+    const int k = (int)(e % in);
+    const int64_t off = p * 4 * (int64_t)in + k;
+    const float y0 = act[off], sd = 1.f - y0 * y0;
+    const float d1 = dU[off + in], d2 = dU[off + 2 * in], d3 = dU[off + 3 * in];
+    const float ys = act[off + in] * d1 + act[off + 2 * in] * d2 + act[off + 3 * in] * d3;
+    dU[off] = sd * dU[off] - 2.f * y0 * ys;
+    dU[off + in] = sd * d1;
+    dU[off + 2 * in] = sd * d2;
+    dU[off + 3 * in] = sd * d3;
+  }
+}
+
+// Bias gradient of one layer per point chunk: slot c gets sum over the chunk's points of the
+// value-row cotangent (0 for chunks past the points).
+__global__ void mlp_db_kernel(const float* cot, int64_t P, int out, int64_t chunk, int nchunks, float* part,
+                              int64_t nW, int64_t b_off) {
+  const int c = blockIdx.x;
+  for (int o = threadIdx.x; o < out; o += blockDim.x) {
+    float acc = 0.f;
+    const int64_t p1 = (int64_t)(c + 1) * chunk < P ? (int64_t)(c + 1) * chunk : P;
+    for (int64_t p = (int64_t)c * chunk; p < p1; ++p) acc += cot[p * 4 * (int64_t)out + o];
+    part[(int64_t)c * nW + b_off + o] = acc;
+  }
+}
+
+// Zero one parameter segment [off, off + len) of the partial slots c0 .. nchunks - 1.
+__global__ void mlp_zero_slots_kernel(float* part, int64_t nW, int64_t off, int64_t len, int c0, int nchunks) {
+  const int64_t tot = (int64_t)(nchunks - c0) * len;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x)
+    part[(int64_t)(c0 + e / len) * nW + off + e % len] = 0.f;
+}
+
+// Learned period's gradient from the first layer's input cotangents dX = [P][4][2F]:
+// sum over points and features of dX . d(features)/dT, added in FP64.
+__global__ void mlp_period_kernel(const float* dX, MlpArgs a, double* tgrad) {
+  const int in = 2 * a.F;
+  float tg = 0.f;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < a.ptot * in; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t gp = e / in;
+    const int k = (int)(e % in);
+    int set;
+    const float* v = mlp_point(a, gp, set);
+    const float4 d = rff_dfeature_dT(a, v, k);
+    const float* r = dX + gp * 4 * (int64_t)in + k;
+    tg += r[0] * d.x + r[in] * d.y + r[2 * in] * d.z + r[3 * in] * d.w;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) tg += __shfl_xor_sync(0xffffffffu, tg, o);
+  if ((threadIdx.x & 31) == 0) atomicAdd(tgrad, (double)tg);
+}
+
 }  // namespace qpm

@@ -97,3 +97,43 @@ def test_batch_step_graph_replay(torch_cuda):
         assert pl.last_device_error() == 0
         assert _rel(l.cpu().numpy(), lr.cpu().numpy()) < 1e-6
         assert _rel(gr.cpu().numpy(), grr.cpu().numpy()) < 2e-6
+
+
+@pytest.mark.parametrize("n,path", [(5, "simt"), (8, "gemm_split")])
+def test_deep_premap_graph_replay(torch_cuda, n, path):
+    """A layer-by-layer premap (periodic map, three tanh layers; its contractions are library
+    GEMMs bound to the call's stream and the plan's workspace) captured and replayed equals the
+    direct call, and a replay reads new parameters in place."""
+    from paper_2506_23246_b300 import qp
+    torch = torch_cuda
+    circ = W.circuit(n, 2, n, ansatz="strong_rot", enc="rx", scale="acos", premap="rff_mlp",
+                     rff_freqs=24, mlp_width=40, mlp_depth=3, periodic=True)
+    prob = W.problem("vacuum", w_energy=10.0, energy_slice=16, energy_nt=2)
+    plan = qp.Plan(circ, prob, path=path)
+    sets = {"colloc": torch.tensor(W.uniform_points(600, 5, 1.5), device="cuda"),
+            "ic": torch.tensor(W.ic_points_uniform(40, 6), device="cuda")}
+    p0 = W.init_params(circ, 7)
+    p1 = W.init_params(circ, 8)
+    dp = torch.tensor(p0, device="cuda")
+    loss = torch.empty(9 + 2, dtype=torch.float64, device="cuda")
+    grad = torch.empty(plan.n_params, dtype=torch.float32, device="cuda")
+    plan.reserve(640, torch.device("cuda"))
+    l_ref, g_ref = [x.clone() for x in plan.loss_grad(dp, sets)]
+    dp.copy_(torch.tensor(p1, device="cuda"))
+    l_ref1, g_ref1 = [x.clone() for x in plan.loss_grad(dp, sets)]
+    dp.copy_(torch.tensor(p0, device="cuda"))
+    plan.loss_grad(dp, sets, out=(loss, grad))
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        plan.loss_grad(dp, sets, out=(loss, grad))
+    g.replay()
+    torch.cuda.synchronize()
+    assert plan.last_device_error() == 0
+    assert _rel(loss.cpu().numpy(), l_ref.cpu().numpy()) < 1e-6
+    assert _rel(grad.cpu().numpy(), g_ref.cpu().numpy()) < 1e-6
+    dp.copy_(torch.tensor(p1, device="cuda"))
+    g.replay()
+    torch.cuda.synchronize()
+    assert _rel(loss.cpu().numpy(), l_ref1.cpu().numpy()) < 1e-6
+    assert _rel(grad.cpu().numpy(), g_ref1.cpu().numpy()) < 1e-6

@@ -658,3 +658,17 @@ def test_periodic_map_loss_grad(torch_cuda, oracle, n, path, depth):
     idx = _mlp_sample(oracle, circ, 6, n)
     assert W.param_offsets(circ)["period"][0] in idx
     _loss_grad_check(torch_cuda, oracle, circ, prob, params, sets, idx, path=path)
+
+
+def test_deep_premap_chunked_weight_gradients(torch_cuda, oracle):
+    """Layer-by-layer premap on more points than weight-gradient slots: the slots take chunks of
+    several points (a strided batch of full chunks plus a ragged last chunk, the unused slots
+    zeroed), periodic map with its learned period, widths off every tile size."""
+    circ = W.circuit(5, 2, 5, ansatz="strong_rot", enc="rx", scale="acos", premap="rff_mlp",
+                     rff_freqs=20, mlp_width=36, mlp_depth=2, periodic=True)
+    prob = W.problem("vacuum", w_energy=10.0, energy_slice=16, energy_nt=2)
+    sets = {"colloc": W.uniform_points(701, 130, 1.5), "ic": W.ic_points_uniform(45, 131),
+            "bc": W.bc_points(17, 132)}
+    params = W.init_params(circ, 133)
+    idx = _mlp_sample(oracle, circ, 6, 5)
+    _loss_grad_check(torch_cuda, oracle, circ, prob, params, sets, idx, path="simt")
