@@ -128,6 +128,7 @@ struct WsLayout {
   size_t mtg;                        // periodic map: FP64 sum of the learned period's gradient
   size_t desc;                       // multi-instance launch: the instance's argument block
   size_t mx0, blasws;                // layer-by-layer premap: RFF features [P][4][2F], GEMM scratch
+  size_t mwt, mdw;                   // ... aligned copies of the layers' weights, per-chunk dW
   size_t dW, dphi, dU, dG, dY, dpart, dWT, dmu, dW16, dcs, dgs, dgates, total;
 };
 
@@ -171,13 +172,13 @@ WgGeom wg_geom(const qp_plan* pl, int64_t nkc) {
 bool dense_path(const qp_plan* pl) { return pl->path == QP_PATH_GEMM_SPLIT; }
 
 // Kernels launched by launch_front: gate preparation, the CRZ mesh diagonal (CRZ ansatze), the
-// premap (one kernel, or layer by layer the features and one activation kernel per layer; the
-// layers' library GEMMs are not counted).
+// premap (one kernel, or layer by layer the weight copy, the features and one activation kernel
+// per layer; the layers' library GEMMs are not counted).
 int front_launches(const qp_plan* pl) {
-  return (qp_has_crz(pl->c.ansatz) ? 2 : 1) + (pl->deep ? pl->c.mlp_depth + 2 : 1);
+  return (qp_has_crz(pl->c.ansatz) ? 2 : 1) + (pl->deep ? pl->c.mlp_depth + 3 : 1);
 }
 // Kernels of the premap backward: the fused per-point kernels (1 or 2), or layer by layer the
-// output layer, the bias gradient and the unused slots' zeroing per layer, the tanh backward per
+// output layer, the bias gradient and the dW slot copy per layer, the tanh backward per
 // hidden layer and the period's two kernels with the periodic map.
 int premap_bwd_launches(const qp_plan* pl) {
   return pl->deep ? 1 + 2 * (pl->c.mlp_depth + 1) + pl->c.mlp_depth + (pl->c.periodic ? 2 : 0)
@@ -235,6 +236,34 @@ int gsum_groups(const qp_plan* pl) {
   return (int)(g < 1 ? 1 : (g > 8 ? 8 : g));
 }
 
+// Layer-by-layer premap: every row buffer has its width rounded up to four floats (al4), so
+// that its rows are 16-byte aligned. The layers' weight matrices are copied as
+// [al4(out)][al4(in)] to 256-byte aligned offsets (floats from the copy's start; l = depth + 1 gives the total),
+// and each weight-gradient chunk writes its dW into a scratch row of the largest layer's size.
+int al4(int x) { return (x + 3) & ~3; }
+int64_t mlp_wcopy_off(const qp_plan* pl, int l) {
+  const int F = pl->c.rff_freqs, H = pl->c.mlp_width, D = pl->c.mlp_depth;
+  int64_t o = 0;
+  int fan = 2 * F;
+  for (int i = 0; i < l; ++i) {
+    const int out = i == D ? pl->c.n_qubits : H;
+    o += ((int64_t)al4(out) * al4(fan) + 63) / 64 * 64;
+    fan = H;
+  }
+  return o;
+}
+int64_t mlp_dw_stride(const qp_plan* pl) {
+  const int F = pl->c.rff_freqs, H = pl->c.mlp_width, D = pl->c.mlp_depth;
+  int64_t m = 0;
+  int fan = 2 * F;
+  for (int i = 0; i <= D; ++i) {
+    const int out = i == D ? pl->c.n_qubits : H;
+    m = std::max(m, (int64_t)al4(out) * al4(fan));
+    fan = H;
+  }
+  return (m + 63) / 64 * 64;
+}
+
 WsLayout ws_layout(const qp_plan* pl, int64_t P0) {
   WsLayout w;
   // with the symmetry penalty the main pass also evaluates up to two mirrored copies of every
@@ -262,8 +291,8 @@ WsLayout ws_layout(const qp_plan* pl, int64_t P0) {
   w.wpart = o; o = al256(o + (size_t)pl->nwblk * nW * 4);
   // layer-by-layer premap: (y0, z_x, z_y, z_t) of every hidden layer, and two cotangent
   // buffers of the widest layer
-  const int64_t mw = pl->deep ? (H > n ? H : n) : 0;
-  w.mact = o; o = al256(o + (pl->deep ? (size_t)pl->c.mlp_depth * P * 4 * H * 4 : 0));
+  const int64_t mw = pl->deep ? std::max(al4(H), al4(n)) : 0;
+  w.mact = o; o = al256(o + (pl->deep ? (size_t)pl->c.mlp_depth * P * 4 * al4(H) * 4 : 0));
   w.mcot = o; o = al256(o + (size_t)2 * P * 4 * mw * 4);
   w.sxb = o; o = al256(o + (sym ? (size_t)P * 3 * 4 : 0));
   w.sF = o; o = al256(o + (sym ? (size_t)P * 3 * 4 : 0));
@@ -272,8 +301,10 @@ WsLayout ws_layout(const qp_plan* pl, int64_t P0) {
   w.spart = o; o = al256(o + (sym ? (size_t)pl->sm_count * 4 * 8 : 0));
   w.mtg = o; o = al256(o + (pl->c.periodic ? 8 : 0));
   w.desc = o; o = al256(o + (dense_path(pl) ? 0 : sizeof(QPCircArgs)));
-  w.mx0 = o; o = al256(o + (pl->deep ? (size_t)P * 4 * 2 * pl->c.rff_freqs * 4 : 0));
+  w.mx0 = o; o = al256(o + (pl->deep ? (size_t)P * 4 * al4(2 * pl->c.rff_freqs) * 4 : 0));
   w.blasws = o; o = al256(o + (pl->deep ? kBlasWorkspace : 0));
+  w.mwt = o; o = al256(o + (pl->deep ? (size_t)mlp_wcopy_off(pl, pl->c.mlp_depth + 1) * 4 : 0));
+  w.mdw = o; o = al256(o + (pl->deep ? (size_t)pl->nwblk * mlp_dw_stride(pl) * 4 : 0));
   const size_t dim = (size_t)1 << n;
   const bool dn = dense_path(pl);
   w.dW = o; o = al256(o + (dn ? 2 * (2 * dim) * dim * 4 : 0));
@@ -547,8 +578,13 @@ qp_status qp_plan_create(const qp_circuit* circuit, const qp_problem* problem, i
     const bool one_layer = circuit->mlp_depth == 1 && (H == 4 || H == 8 || H == 16 || H == 32 || H == 64) &&
                            (F % 2) == 0 && (int64_t)H * 2 * F <= 16 * 4 * 256 && n * H <= 4 * 256;
     pl->deep = !one_layer || circuit->periodic;
-    if (pl->deep && cublasCreate(&pl->blas) != CUBLAS_STATUS_SUCCESS) {
-      pl->blas = nullptr;
+    // FP32 GEMMs emulated on the tensor cores (BF16x9: FP32 accuracy) wherever the library has
+    // them, without the special-value scans (the weight copy flags non-finite weights)
+    static_assert(qpm::MLP_MAX_LAYERS >= 9, "depth 8 premaps have nine layers");
+    if (pl->deep && (cublasCreate(&pl->blas) != CUBLAS_STATUS_SUCCESS ||
+                     cublasSetEmulationStrategy(pl->blas, CUBLAS_EMULATION_STRATEGY_EAGER) != CUBLAS_STATUS_SUCCESS ||
+                     cublasSetEmulationSpecialValuesSupport(pl->blas, CUDA_EMULATION_SPECIAL_VALUES_SUPPORT_NONE) !=
+                         CUBLAS_STATUS_SUCCESS)) {
       delete pl;
       return QP_ERR_CUDA;
     }
@@ -689,11 +725,11 @@ static qpm::MlpArgs mlp_layer_args(const qp_plan* pl, const float* d_params, con
   mlp_layer_geom(pl, l, m.in, m.out, wo, bo);
   m.W = d_params + pl->nfixed + wo;
   m.b = d_params + pl->nfixed + bo;
-  m.in_rff = l == 0 ? 1 : 0;
-  const int64_t lstride = m.ptot * 4 * pl->c.mlp_width;
+  m.ldi = al4(m.in);
+  m.ldo = al4(m.out);
+  const int64_t lstride = m.ptot * 4 * al4(pl->c.mlp_width);
   m.act_in = l > 0 ? (const float*)(ws + w.mact) + (int64_t)(l - 1) * lstride : nullptr;
-  m.final_layer = l == pl->c.mlp_depth ? 1 : 0;
-  m.act_out = m.final_layer ? nullptr : (float*)(ws + w.mact) + (int64_t)l * lstride;
+  m.act_out = l == pl->c.mlp_depth ? nullptr : (float*)(ws + w.mact) + (int64_t)l * lstride;
   m.scale = pl->c.scale;
   m.thetaJ = (float*)(ws + w.thetaJ);
   m.hout = (float*)(ws + w.d2);
@@ -710,19 +746,23 @@ static int mlp_grid(const qp_plan* pl, int64_t tiles) {
 
 // Library GEMM of the layer-by-layer premap on the plan's handle, column-major arguments
 // (C = op(A) op(B), alpha 1). The first call that the emulated FP32 compute type does not
-// accept switches the plan to plain FP32.
+// accept switches the plan to plain FP32. A GEMM with a dimension below 32 besides the rows
+// (the output layer's few angles) runs in plain FP32: the emulated kernels' tiles would be
+// mostly padding.
 static qp_status mlp_gemm(qp_plan* pl, cublasOperation_t ta, cublasOperation_t tb, int m, int n, int k,
                           const float* A, int lda, const float* B, int ldb, float* C, int ldc,
                           long long sa = 0, long long sb = 0, long long sc = 0, int batch = 0) {
   const float one = 1.f, zero = 0.f;
+  const int narrow = std::min(std::min(m, n), k);   // the row count is the largest of the three
   for (;;) {
+    const cublasComputeType_t ct = narrow < 32 ? CUBLAS_COMPUTE_32F : pl->blas_ct;
     const cublasStatus_t st = batch > 0
         ? cublasGemmStridedBatchedEx(pl->blas, ta, tb, m, n, k, &one, A, CUDA_R_32F, lda, sa, B, CUDA_R_32F, ldb,
-                                     sb, &zero, C, CUDA_R_32F, ldc, sc, batch, pl->blas_ct, CUBLAS_GEMM_DEFAULT)
+                                     sb, &zero, C, CUDA_R_32F, ldc, sc, batch, ct, CUBLAS_GEMM_DEFAULT)
         : cublasGemmEx(pl->blas, ta, tb, m, n, k, &one, A, CUDA_R_32F, lda, B, CUDA_R_32F, ldb, &zero, C,
-                       CUDA_R_32F, ldc, pl->blas_ct, CUBLAS_GEMM_DEFAULT);
+                       CUDA_R_32F, ldc, ct, CUBLAS_GEMM_DEFAULT);
     if (st == CUBLAS_STATUS_SUCCESS) return QP_OK;
-    if (pl->blas_ct == CUBLAS_COMPUTE_32F ||
+    if (ct == CUBLAS_COMPUTE_32F ||
         (st != CUBLAS_STATUS_NOT_SUPPORTED && st != CUBLAS_STATUS_INVALID_VALUE))
       return QP_ERR_CUDA;
     pl->blas_ct = CUBLAS_COMPUTE_32F;
@@ -756,19 +796,41 @@ static qp_status launch_mlp_fwd(qp_plan* pl, const float* d_params, const float*
   qp_status st = mlp_blas_bind(pl, w, s);
   if (st != QP_OK) return st;
   float* X0 = (float*)(ws + w.mx0);
+  float* Wc = (float*)(ws + w.mwt);
+  {
+    // the layers' weights at aligned offsets (the library's vectorised kernels need them)
+    qpm::MlpCopyArgs ca;
+    std::memset(&ca, 0, sizeof(ca));
+    ca.src = d_params + pl->nfixed;
+    ca.dst = Wc;
+    ca.nl = D + 1;
+    ca.status = (int32_t*)(ws + w.status);
+    int64_t most = 0;
+    for (int l = 0; l <= D; ++l) {
+      int64_t bo;
+      mlp_layer_geom(pl, l, ca.in[l], ca.out[l], ca.src_off[l], bo);
+      ca.ld[l] = al4(ca.in[l]);
+      ca.outp[l] = al4(ca.out[l]);
+      ca.dst_off[l] = mlp_wcopy_off(pl, l);
+      most = std::max(most, (int64_t)ca.outp[l] * ca.ld[l]);
+    }
+    qpm::mlp_wcopy_kernel<<<ew_grid(pl, most), 256, 0, s>>>(ca);
+  }
   {
     const qpm::MlpArgs m0 = mlp_layer_args(pl, d_params, pts, npts, w, 0);
-    qpm::mlp_features_kernel<<<ew_grid(pl, P * m0.F), 256, 0, s>>>(m0, X0);
+    qpm::mlp_features_kernel<<<ew_grid(pl, P * m0.F), 256, 0, s>>>(m0, X0, m0.ldi);   // pads zeroed
   }
   for (int l = 0; l <= D; ++l) {
     const qpm::MlpArgs m = mlp_layer_args(pl, d_params, pts, npts, w, l);
     const float* X = l == 0 ? X0 : m.act_in;
     float* Hl = l == D ? (float*)(ws + w.mcot) : m.act_out;
-    // H[R][out] = X[R][in] W^T: column-major H^T = W X^T
-    if (R > 0) st = mlp_gemm(pl, CUBLAS_OP_T, CUBLAS_OP_N, m.out, R, m.in, m.W, m.in, X, m.in, Hl, m.out);
+    // H[R][out] = X[R][in] W^T: column-major H^T = W X^T (padded sizes: the pads are zero)
+    if (R > 0)
+      st = mlp_gemm(pl, CUBLAS_OP_T, CUBLAS_OP_N, m.ldo, R, m.ldi, Wc + mlp_wcopy_off(pl, l), m.ldi, X, m.ldi, Hl,
+                    m.ldo);
     if (st != QP_OK) return st;
     if (l < D)
-      qpm::mlp_act_kernel<<<ew_grid(pl, P * m.out), 256, 0, s>>>(Hl, m.b, P, m.out);
+      qpm::mlp_act_kernel<<<ew_grid(pl, P * (m.ldo / 4)), 256, 0, s>>>(Hl, m.b, P, m.out, m.ldo);
     else
       qpm::mlp_out_kernel<<<ew_grid(pl, P * m.out), 256, 0, s>>>(Hl, m);
   }
@@ -777,11 +839,14 @@ static qp_status launch_mlp_fwd(qp_plan* pl, const float* d_params, const float*
 
 // Weight and bias gradients of layer l from its input rows X [R][in] and the cotangents of
 // its pre-activations cot [R][out], one partial slot per point chunk (the slots are summed in
-// FP64 with the others): dW = cot^T X per chunk as one strided batched GEMM, the last partial
-// chunk as one more GEMM, the unused slots zeroed.
+// FP64 with the others): dW = cot^T X per chunk as one strided batched GEMM into aligned
+// scratch rows, the last partial chunk as one more GEMM, then copied into the slots (the unused
+// ones zeroed).
 static qp_status mlp_layer_dw(qp_plan* pl, const float* X, const float* cot, int64_t P, int in, int out,
-                              int64_t w_off, int64_t b_off, const WsLayout& w, cudaStream_t s) {
+                              int ldi, int ldo, int64_t w_off, int64_t b_off, const WsLayout& w, cudaStream_t s) {
   float* part = (float*)((char*)pl->ws + w.wpart);
+  float* dw = (float*)((char*)pl->ws + w.mdw);
+  const int64_t dws = mlp_dw_stride(pl);
   const int64_t nW = pl->mlp_count - pl->nfixed;
   const int nc = pl->nwblk;
   const int64_t chunk = P > nc ? (P + nc - 1) / nc : 1;   // points per slot
@@ -789,17 +854,17 @@ static qp_status mlp_layer_dw(qp_plan* pl, const float* X, const float* cot, int
   const int used = (int)(nfull + (rest > 0 ? 1 : 0));
   const int rc = (int)(4 * chunk);
   qp_status st = QP_OK;
-  // column-major dW^T [in x out] = X_c^T (in x rc) . cot_c (rc x out)
+  // column-major dW^T [in x out] = X_c^T (in x rc) . cot_c (rc x out), on the padded sizes
   if (nfull > 0)
-    st = mlp_gemm(pl, CUBLAS_OP_N, CUBLAS_OP_T, in, out, rc, X, in, cot, out, part + w_off, in,
-                  (long long)rc * in, (long long)rc * out, (long long)nW, (int)nfull);
+    st = mlp_gemm(pl, CUBLAS_OP_N, CUBLAS_OP_T, ldi, ldo, rc, X, ldi, cot, ldo, dw, ldi,
+                  (long long)rc * ldi, (long long)rc * ldo, (long long)dws, (int)nfull);
   if (st == QP_OK && rest > 0)
-    st = mlp_gemm(pl, CUBLAS_OP_N, CUBLAS_OP_T, in, out, (int)(4 * rest), X + nfull * rc * (int64_t)in, in,
-                  cot + nfull * rc * (int64_t)out, out, part + nfull * nW + w_off, in);
+    st = mlp_gemm(pl, CUBLAS_OP_N, CUBLAS_OP_T, ldi, ldo, (int)(4 * rest), X + nfull * rc * (int64_t)ldi, ldi,
+                  cot + nfull * rc * (int64_t)ldo, ldo, dw + nfull * dws, ldi);
   if (st != QP_OK) return st;
-  qpm::mlp_db_kernel<<<nc, out < 256 ? ((out + 31) / 32) * 32 : 256, 0, s>>>(cot, P, out, chunk, nc, part, nW, b_off);
-  qpm::mlp_zero_slots_kernel<<<ew_grid(pl, (int64_t)(nc - used) * out * in), 256, 0, s>>>(
-      part, nW, w_off, (int64_t)out * in, used, nc);
+  qpm::mlp_db_kernel<<<nc, qpm::DB_THREADS, 0, s>>>(cot, P, out, ldo, chunk, part, nW, b_off);
+  qpm::mlp_dw_slots_kernel<<<ew_grid(pl, (int64_t)nc * out * in), 256, 0, s>>>(dw, dws, ldi, part, nW, w_off, in,
+                                                                               out, used, nc);
   return QP_OK;
 }
 
@@ -812,7 +877,7 @@ static qp_status launch_mlp_bwd(qp_plan* pl, const float* d_params, const float*
   char* ws = (char*)pl->ws;
   const int64_t P = npts[0] + npts[1] + npts[2];
   const int n = pl->c.n_qubits, D = pl->c.mlp_depth, H = pl->c.mlp_width;
-  const int64_t mw = H > n ? H : n;
+  const int64_t mw = std::max(al4(H), al4(n));
   const int64_t nW = pl->mlp_count - pl->nfixed;
   if (4 * P > (int64_t)INT32_MAX) return QP_ERR_UNSUPPORTED;
   const int R = (int)(4 * P);
@@ -820,31 +885,34 @@ static qp_status launch_mlp_bwd(qp_plan* pl, const float* d_params, const float*
   if (st != QP_OK) return st;
   float* cot[2] = {(float*)(ws + w.mcot), (float*)(ws + w.mcot) + P * 4 * mw};
   int cur = 0;
-  qpm::mlp_bwd_out_kernel<<<ew_grid(pl, P * n), 256, 0, s>>>((const float*)(ws + w.d2),
-                                                             (const float*)(ws + w.dthetaJ), P, n, pl->c.scale,
-                                                             cot[cur]);
+  qpm::mlp_bwd_out_kernel<<<ew_grid(pl, P * al4(n)), 256, 0, s>>>((const float*)(ws + w.d2),
+                                                             (const float*)(ws + w.dthetaJ), P, n, al4(n),
+                                                             pl->c.scale, cot[cur]);
   float* X0 = (float*)(ws + w.mx0);
+  const float* Wc = (const float*)(ws + w.mwt);   // the forward's aligned weight copies
   for (int l = D; l >= 0; --l) {
     const qpm::MlpArgs m = mlp_layer_args(pl, d_params, pts, npts, w, l);
     int in, out;
     int64_t w_off, b_off;
     mlp_layer_geom(pl, l, in, out, w_off, b_off);
     const float* X = l == 0 ? X0 : m.act_in;
-    st = mlp_layer_dw(pl, X, cot[cur], P, in, out, w_off, b_off, w, s);
+    st = mlp_layer_dw(pl, X, cot[cur], P, in, out, m.ldi, m.ldo, w_off, b_off, w, s);
     if (st != QP_OK) return st;
-    if (l > 0) {
-      // dU[R][in] = cot[R][out] W: column-major dU^T = W^T cot^T
-      float* dU = cot[cur ^ 1];
-      if (R > 0) st = mlp_gemm(pl, CUBLAS_OP_N, CUBLAS_OP_N, in, R, out, m.W, in, cot[cur], out, dU, in);
+    if (l > 0 || pl->c.periodic) {
+      // dU[R][in] = cot[R][out] W: column-major dU^T = W^T cot^T; for the first layer (periodic
+      // map) the features' cotangents, over the features, which are no longer needed
+      float* dU = l > 0 ? cot[cur ^ 1] : X0;
+      if (R > 0)
+        st = mlp_gemm(pl, CUBLAS_OP_N, CUBLAS_OP_N, m.ldi, R, m.ldo, Wc + mlp_wcopy_off(pl, l), m.ldi, cot[cur],
+                      m.ldo, dU, m.ldi);
       if (st != QP_OK) return st;
-      qpm::mlp_dact_kernel<<<ew_grid(pl, P * in), 256, 0, s>>>(dU, m.act_in, P, in);
-      cur ^= 1;
-    } else if (pl->c.periodic) {
-      // the features are no longer needed: their cotangents go over them
-      if (R > 0) st = mlp_gemm(pl, CUBLAS_OP_N, CUBLAS_OP_N, in, R, out, m.W, in, cot[cur], out, X0, in);
-      if (st != QP_OK) return st;
+      if (l > 0) {
+        qpm::mlp_dact_kernel<<<ew_grid(pl, P * (m.ldi / 4)), 256, 0, s>>>(dU, m.act_in, P, m.ldi);
+        cur ^= 1;
+        continue;
+      }
       if (cudaMemsetAsync(ws + w.mtg, 0, sizeof(double), s) != cudaSuccess) return QP_ERR_CUDA;
-      qpm::mlp_period_kernel<<<ew_grid(pl, P * in), 256, 0, s>>>(X0, m, (double*)(ws + w.mtg));
+      qpm::mlp_period_kernel<<<ew_grid(pl, P * m.F), 256, 0, s>>>(X0, m, m.ldi, (double*)(ws + w.mtg));
       qpm::mlp_period_fin_kernel<<<(pl->nwblk + 255) / 256, 256, 0, s>>>(
           (const double*)(ws + w.mtg), (float*)(ws + w.wpart), nW, 0, pl->nwblk);
     }

@@ -404,6 +404,30 @@ def test_nonfinite_params_reported(torch_cuda):
     assert plan.last_device_error() == 5
 
 
+@pytest.mark.parametrize("layer", ["W0", "W_out"])
+def test_nonfinite_deep_premap_weight_reported(torch_cuda, layer):
+    """A NaN in one weight of a layer-by-layer premap (whose contractions run as emulated FP32
+    GEMMs without special-value handling) is reported as a non-finite call."""
+    from paper_2506_23246_b300 import qp
+    torch = torch_cuda
+    circ = W.circuit(5, 2, 5, ansatz="strong_rot", enc="rx", scale="acos", premap="rff_mlp",
+                     rff_freqs=12, mlp_width=16, mlp_depth=2, periodic=True)
+    prob = W.problem("vacuum", w_energy=10.0, energy_slice=16, energy_nt=2)
+    sets = {"colloc": W.uniform_points(40, 140, 1.5), "ic": W.ic_points_uniform(16, 141)}
+    params = W.init_params(circ, 142).copy()
+    off = W.param_offsets(circ)
+    params[off[layer][0] + 3] = float("nan")
+    plan = qp.Plan(circ, prob)
+    dsets = {k: torch.tensor(v, device="cuda") for k, v in sets.items()}
+    plan.loss_grad(torch.tensor(params, device="cuda"), dsets)
+    torch.cuda.synchronize()
+    assert plan.last_device_error() == 5
+    params = W.init_params(circ, 142)   # the same plan recovers on finite parameters
+    plan.loss_grad(torch.tensor(params, device="cuda"), dsets)
+    torch.cuda.synchronize()
+    assert plan.last_device_error() == 0
+
+
 def test_invalid_arguments_rejected_on_host(torch_cuda):
     from paper_2506_23246_b300 import qp
     torch = torch_cuda
@@ -570,11 +594,13 @@ def _mlp_sample(oracle, circ, k, seed):
 
 @pytest.mark.parametrize("n,L,F,H,depth,path", [(4, 2, 8, 4, 0, "simt"), (5, 2, 8, 12, 2, "simt"),
                                                 (7, 2, 24, 40, 3, "simt"), (8, 3, 32, 48, 2, "gemm_split"),
-                                                (9, 2, 16, 24, 3, "gemm_split")])
+                                                (9, 2, 16, 24, 3, "gemm_split"), (6, 2, 7, 13, 2, "simt"),
+                                                (8, 2, 9, 21, 1, "gemm_split")])
 def test_deep_premap_loss_grad(torch_cuda, oracle, n, L, F, H, depth, path):
     """RFF + tanh MLP premaps of other depths and widths (the layer-by-layer kernels): depth 0
-    (RFF straight into the output layer), widths that are not multiples of the 64-wide output
-    tiles, both statevector paths; loss terms and gradients spread over every layer."""
+    (RFF straight into the output layer), widths and feature counts that are not multiples of
+    four (padded row buffers), both statevector paths; loss terms and gradients spread over
+    every layer."""
     circ = W.circuit(n, L, n, ansatz="strong_rot", enc="rx", scale="acos", premap="rff_mlp",
                      rff_freqs=F, mlp_width=H, mlp_depth=depth)
     prob = W.problem("dielectric", disk_x0=0.2, disk_r=0.6, w_energy=10.0, energy_slice=16,
