@@ -171,18 +171,25 @@ WgGeom wg_geom(const qp_plan* pl, int64_t nkc) {
 
 bool dense_path(const qp_plan* pl) { return pl->path == QP_PATH_GEMM_SPLIT; }
 
+int al4(int x);
+bool mlp_fused_out(const qp_plan* pl);
+
 // Kernels launched by launch_front: gate preparation, the CRZ mesh diagonal (CRZ ansatze), the
 // premap (one kernel, or layer by layer the weight copy, the features and one activation kernel
-// per layer; the layers' library GEMMs are not counted).
+// per layer, the output layer's own or folded into the last hidden layer's; the layers'
+// library GEMMs are not counted).
 int front_launches(const qp_plan* pl) {
-  return (qp_has_crz(pl->c.ansatz) ? 2 : 1) + (pl->deep ? pl->c.mlp_depth + 3 : 1);
+  const int D = pl->c.mlp_depth;
+  return (qp_has_crz(pl->c.ansatz) ? 2 : 1) + (pl->deep ? (mlp_fused_out(pl) ? D + 2 : D + 3) : 1);
 }
 // Kernels of the premap backward: the fused per-point kernels (1 or 2), or layer by layer the
-// output layer, the bias gradient and the dW slot copy per layer, the tanh backward per
-// hidden layer and the period's two kernels with the periodic map.
+// output layer (with the last hidden layer's tanh backward and its own weight gradient when
+// folded), the bias gradient and the dW slot copy per layer, the tanh backward per hidden layer
+// and the period's two kernels with the periodic map.
 int premap_bwd_launches(const qp_plan* pl) {
-  return pl->deep ? 1 + 2 * (pl->c.mlp_depth + 1) + pl->c.mlp_depth + (pl->c.periodic ? 2 : 0)
-                  : (pl->pg_ok ? 1 : 2);
+  const int D = pl->c.mlp_depth, per = pl->c.periodic ? 2 : 0;
+  if (!pl->deep) return pl->pg_ok ? 1 : 2;
+  return mlp_fused_out(pl) ? 1 + 2 * D + (D - 1) + per : 1 + 2 * (D + 1) + D + per;
 }
 
 // The fused forward kernel keeps a tile's whole output row (2^(n+1) FP32 columns) in tensor
@@ -241,6 +248,11 @@ int gsum_groups(const qp_plan* pl) {
 // [al4(out)][al4(in)] to 256-byte aligned offsets (floats from the copy's start; l = depth + 1 gives the total),
 // and each weight-gradient chunk writes its dW into a scratch row of the largest layer's size.
 int al4(int x) { return (x + 3) & ~3; }
+// The output layer folded into the kernels that pass over the last hidden layer's rows (a
+// hidden layer exists, at most 128 hidden units, at most 16 angles).
+bool mlp_fused_out(const qp_plan* pl) {
+  return pl->deep && pl->c.mlp_depth >= 1 && al4(pl->c.mlp_width) <= 128 && pl->c.n_qubits <= 16;
+}
 int64_t mlp_wcopy_off(const qp_plan* pl, int l) {
   const int F = pl->c.rff_freqs, H = pl->c.mlp_width, D = pl->c.mlp_depth;
   int64_t o = 0;
@@ -818,9 +830,11 @@ static qp_status launch_mlp_fwd(qp_plan* pl, const float* d_params, const float*
   }
   {
     const qpm::MlpArgs m0 = mlp_layer_args(pl, d_params, pts, npts, w, 0);
-    qpm::mlp_features_kernel<<<ew_grid(pl, P * m0.F), 256, 0, s>>>(m0, X0, m0.ldi);   // pads zeroed
+    qpm::mlp_features_kernel<<<ew_grid(pl, P * 32), 256, (size_t)m0.F * (m0.period ? 6 : 3) * 4, s>>>(
+        m0, X0, m0.ldi);   // pads zeroed
   }
-  for (int l = 0; l <= D; ++l) {
+  const bool fo = mlp_fused_out(pl);
+  for (int l = 0; l <= (fo ? D - 1 : D); ++l) {
     const qpm::MlpArgs m = mlp_layer_args(pl, d_params, pts, npts, w, l);
     const float* X = l == 0 ? X0 : m.act_in;
     float* Hl = l == D ? (float*)(ws + w.mcot) : m.act_out;
@@ -829,10 +843,19 @@ static qp_status launch_mlp_fwd(qp_plan* pl, const float* d_params, const float*
       st = mlp_gemm(pl, CUBLAS_OP_T, CUBLAS_OP_N, m.ldo, R, m.ldi, Wc + mlp_wcopy_off(pl, l), m.ldi, X, m.ldi, Hl,
                     m.ldo);
     if (st != QP_OK) return st;
-    if (l < D)
+    if (fo && l == D - 1) {
+      // the last hidden layer's activation with the output layer, per point
+      const qpm::MlpArgs mo = mlp_layer_args(pl, d_params, pts, npts, w, D);
+      const size_t sm = (size_t)mo.out * mo.ldi * 4;
+      if (mo.out <= 8)
+        qpm::mlp_act_out_kernel<8><<<ew_grid(pl, P * 32), 256, sm, s>>>(mo, Hl, m.b);
+      else
+        qpm::mlp_act_out_kernel<16><<<ew_grid(pl, P * 32), 256, sm, s>>>(mo, Hl, m.b);
+    } else if (l < D) {
       qpm::mlp_act_kernel<<<ew_grid(pl, P * (m.ldo / 4)), 256, 0, s>>>(Hl, m.b, P, m.out, m.ldo);
-    else
+    } else {
       qpm::mlp_out_kernel<<<ew_grid(pl, P * m.out), 256, 0, s>>>(Hl, m);
+    }
   }
   return cuda_status(cudaGetLastError());
 }
@@ -885,12 +908,32 @@ static qp_status launch_mlp_bwd(qp_plan* pl, const float* d_params, const float*
   if (st != QP_OK) return st;
   float* cot[2] = {(float*)(ws + w.mcot), (float*)(ws + w.mcot) + P * 4 * mw};
   int cur = 0;
-  qpm::mlp_bwd_out_kernel<<<ew_grid(pl, P * al4(n)), 256, 0, s>>>((const float*)(ws + w.d2),
-                                                             (const float*)(ws + w.dthetaJ), P, n, al4(n),
-                                                             pl->c.scale, cot[cur]);
+  const bool fo = mlp_fused_out(pl);
+  if (fo) {
+    // output layer, its weight gradient and the last hidden layer's tanh backward, per point
+    const qpm::MlpArgs mo = mlp_layer_args(pl, d_params, pts, npts, w, D);
+    int in, out;
+    int64_t w_off, b_off;
+    mlp_layer_geom(pl, D, in, out, w_off, b_off);
+    const int nc = pl->nwblk;
+    const int64_t chunk = P > nc ? (P + nc - 1) / nc : 1;
+    const size_t sm = (size_t)(2 * mo.out * mo.ldi + mo.out) * 4;
+    if (mo.out <= 8)
+      qpm::mlp_out_bwd_kernel<8><<<nc, 256, sm, s>>>(mo, (const float*)(ws + w.d2), (const float*)(ws + w.dthetaJ),
+                                                     mo.act_in, cot[cur], chunk, (float*)(ws + w.wpart), nW, w_off,
+                                                     b_off);
+    else
+      qpm::mlp_out_bwd_kernel<16><<<nc, 256, sm, s>>>(mo, (const float*)(ws + w.d2), (const float*)(ws + w.dthetaJ),
+                                                      mo.act_in, cot[cur], chunk, (float*)(ws + w.wpart), nW, w_off,
+                                                      b_off);
+  } else {
+    qpm::mlp_bwd_out_kernel<<<ew_grid(pl, P * al4(n)), 256, 0, s>>>((const float*)(ws + w.d2),
+                                                               (const float*)(ws + w.dthetaJ), P, n, al4(n),
+                                                               pl->c.scale, cot[cur]);
+  }
   float* X0 = (float*)(ws + w.mx0);
   const float* Wc = (const float*)(ws + w.mwt);   // the forward's aligned weight copies
-  for (int l = D; l >= 0; --l) {
+  for (int l = fo ? D - 1 : D; l >= 0; --l) {
     const qpm::MlpArgs m = mlp_layer_args(pl, d_params, pts, npts, w, l);
     int in, out;
     int64_t w_off, b_off;
@@ -912,7 +955,8 @@ static qp_status launch_mlp_bwd(qp_plan* pl, const float* d_params, const float*
         continue;
       }
       if (cudaMemsetAsync(ws + w.mtg, 0, sizeof(double), s) != cudaSuccess) return QP_ERR_CUDA;
-      qpm::mlp_period_kernel<<<ew_grid(pl, P * m.F), 256, 0, s>>>(X0, m, m.ldi, (double*)(ws + w.mtg));
+      qpm::mlp_period_kernel<<<ew_grid(pl, P * 32), 256, (size_t)m.F * 6 * 4, s>>>(X0, m, m.ldi,
+                                                                                 (double*)(ws + w.mtg));
       qpm::mlp_period_fin_kernel<<<(pl->nwblk + 255) / 256, 256, 0, s>>>(
           (const double*)(ws + w.mtg), (float*)(ws + w.wpart), nW, 0, pl->nwblk);
     }

@@ -595,12 +595,13 @@ def _mlp_sample(oracle, circ, k, seed):
 @pytest.mark.parametrize("n,L,F,H,depth,path", [(4, 2, 8, 4, 0, "simt"), (5, 2, 8, 12, 2, "simt"),
                                                 (7, 2, 24, 40, 3, "simt"), (8, 3, 32, 48, 2, "gemm_split"),
                                                 (9, 2, 16, 24, 3, "gemm_split"), (6, 2, 7, 13, 2, "simt"),
-                                                (8, 2, 9, 21, 1, "gemm_split")])
+                                                (8, 2, 9, 21, 1, "gemm_split"), (5, 2, 8, 136, 1, "simt")])
 def test_deep_premap_loss_grad(torch_cuda, oracle, n, L, F, H, depth, path):
     """RFF + tanh MLP premaps of other depths and widths (the layer-by-layer kernels): depth 0
     (RFF straight into the output layer), widths and feature counts that are not multiples of
-    four (padded row buffers), both statevector paths; loss terms and gradients spread over
-    every layer."""
+    four (padded row buffers), a width above 128 (the output layer as its own GEMMs instead of
+    folded into the last hidden layer's kernels), both statevector paths; loss terms and
+    gradients spread over every layer."""
     circ = W.circuit(n, L, n, ansatz="strong_rot", enc="rx", scale="acos", premap="rff_mlp",
                      rff_freqs=F, mlp_width=H, mlp_depth=depth)
     prob = W.problem("dielectric", disk_x0=0.2, disk_r=0.6, w_energy=10.0, energy_slice=16,
