@@ -8,8 +8,9 @@ gradient of every parameter.
 
 Prints one JSON line. `value` is collocation points per second over all ranks (device
 time, CUDA events around each step, L2 flushed between steps). `e2e` is the same metric
-through the public call with the inputs copied from pinned host memory and the loss and
-gradient copied back inside the timed region. The reference arm times the FP64 CPU oracle
+through the public call with every step's inputs copied from pinned host memory and its loss
+and gradient copied back inside the timed region (two device buffer sets, the copies on their
+own streams beside the neighbouring steps' compute; the L2 flushes are inside it too). The reference arm times the FP64 CPU oracle
 (deliberately slow, plain definition) on a bounded sample of the same workload.
 """
 import argparse
@@ -276,27 +277,33 @@ def run_native(a):
         norm = qdist.shard_norm((ncol, dsets["ic"].shape[0], 0), plan.count_dielectric(dsets["colloc"]),
                                 device=dev)
 
-    def step():
-        plan.loss_grad(dp, dsets, out=(loss, grad), norm=norm)
-        if world > 1:
-            qdist.allreduce_loss_grad(loss, grad)
+    def make_step(dp_, ds_, loss_, grad_):
+        def f():
+            plan.loss_grad(dp_, ds_, out=(loss_, grad_), norm=norm)
+            if world > 1:
+                qdist.allreduce_loss_grad(loss_, grad_)
+        return f
 
+    def make_run(f):
+        # the step's launches captured once into a CUDA graph and replayed (same kernels, same
+        # buffers); the sharded form keeps plain launches around its collective
+        if world > 1 or a.no_graph:
+            return f, None
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            f()
+        torch.cuda.synchronize()
+        for _ in range(3):
+            g.replay()
+        torch.cuda.synchronize()
+        return g.replay, g
+
+    step = make_step(dp, dsets, loss, grad)
     for _ in range(max(a.warmup, 3)):
         step()
     torch.cuda.synchronize()
     launches = plan.last_launch_count()
-    # the step's launches captured once into a CUDA graph and replayed (same kernels, same
-    # buffers); the sharded form keeps plain launches around its collective
-    graph = None
-    if world == 1 and not a.no_graph:
-        graph = torch.cuda.CUDAGraph()
-        with torch.cuda.graph(graph):
-            step()
-        torch.cuda.synchronize()
-        for _ in range(3):
-            graph.replay()
-        torch.cuda.synchronize()
-    run = graph.replay if graph is not None else step
+    run, graph = make_run(step)
 
     ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(a.steps)]
     ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(a.steps)]
@@ -391,34 +398,64 @@ def run_native(a):
                 "kernel_ms": c["kernel_ms"], "peak_basis": basis}
         dtype = "fp16x2-split, fp32 accum"
 
-    # end to end through the public call: pinned host inputs in, loss + gradient out
+    # end to end through the public call: pinned host inputs in, loss + gradient out. Two sets
+    # of device buffers: step i's inputs are copied in (copy stream) while step i - 1 computes,
+    # and its loss and gradient are read back (second copy stream) while step i + 1 computes.
+    # The timed region runs from before the first input copy to after the last read-back, L2
+    # flushes between the steps included.
     hp = torch.tensor(params).pin_memory()
     hs = {k: torch.tensor(v).pin_memory() for k, v in sets.items()}
-    hl = torch.empty(loss.shape, dtype=torch.float64).pin_memory()
-    hg = torch.empty(grad.shape, dtype=torch.float32).pin_memory()
+    hl = [torch.empty(loss.shape, dtype=torch.float64).pin_memory() for _ in range(2)]
+    hg = [torch.empty(grad.shape, dtype=torch.float32).pin_memory() for _ in range(2)]
     h2d = hp.numel() * 4 + sum(v.numel() * 4 for v in hs.values())
-    d2h = hl.numel() * 8 + hg.numel() * 4
-
-    def e2e_step():
-        dp.copy_(hp, non_blocking=True)
-        for k in hs:
-            dsets[k].copy_(hs[k], non_blocking=True)
-        run()
-        hl.copy_(loss, non_blocking=True)
-        hg.copy_(grad, non_blocking=True)
-
-    for _ in range(3):
-        e2e_step()
+    d2h = hl[0].numel() * 8 + hg[0].numel() * 4
+    bufs = [(dp, dsets, loss, grad, run)]
+    dp2, ds2 = torch.empty_like(dp), {k: torch.empty_like(v) for k, v in dsets.items()}
+    dp2.copy_(dp)
+    for k in ds2:
+        ds2[k].copy_(dsets[k])
+    loss2, grad2 = torch.empty_like(loss), torch.empty_like(grad)
+    step2 = make_step(dp2, ds2, loss2, grad2)
+    step2()
     torch.cuda.synchronize()
-    e0 = [torch.cuda.Event(enable_timing=True) for _ in range(a.steps)]
-    e1 = [torch.cuda.Event(enable_timing=True) for _ in range(a.steps)]
-    for i in range(a.steps):
-        flush.fill_(float(i))
-        e0[i].record(stream)
-        e2e_step()
-        e1[i].record(stream)
+    run2, graph2 = make_run(step2)
+    bufs.append((dp2, ds2, loss2, grad2, run2))
+    up, down = torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev)
+    ev = {n: [torch.cuda.Event() for _ in range(2)] for n in ("in", "done", "out")}
+
+    def e2e_steps(k, i0=0):
+        for i in range(i0, i0 + k):
+            b = i % 2
+            d_p, d_s, d_l, d_g, r = bufs[b]
+            with torch.cuda.stream(up):
+                if i >= 2:
+                    up.wait_event(ev["done"][b])     # step i - 2 has read these inputs
+                d_p.copy_(hp, non_blocking=True)
+                for key in hs:
+                    d_s[key].copy_(hs[key], non_blocking=True)
+                ev["in"][b].record(up)
+            stream.wait_event(ev["in"][b])
+            if i >= 2:
+                stream.wait_event(ev["out"][b])      # step i - 2's results have been read back
+            flush.fill_(float(i))
+            r()
+            ev["done"][b].record(stream)
+            with torch.cuda.stream(down):
+                down.wait_event(ev["done"][b])
+                hl[b].copy_(d_l, non_blocking=True)
+                hg[b].copy_(d_g, non_blocking=True)
+                ev["out"][b].record(down)
+
+    e2e_steps(4)
     torch.cuda.synchronize()
-    ems = sum(e0[i].elapsed_time(e1[i]) for i in range(a.steps)) / a.steps
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    up.wait_event(t0)
+    e2e_steps(a.steps)
+    down.wait_event(ev["out"][(a.steps - 1) % 2])
+    t1.record(down)
+    torch.cuda.synchronize()
+    ems = t0.elapsed_time(t1) / a.steps
     if world > 1:
         t = torch.tensor([ems], device=dev)
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
@@ -432,7 +469,10 @@ def run_native(a):
                 "launch": ("one CUDA graph per step (the library's kernels captured once, replayed)"
                            if graph is not None else "kernels launched one by one"),
                 "e2e": {"value": world * ncol / (ems / 1000.0), "unit": UNIT,
-                        "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+                        "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": ems,
+                        "copies": "double-buffered: inputs of step i+1 in and results of step i-1 "
+                                  "out on two copy streams while step i computes; L2 flush per step "
+                                  "inside the timed region"},
                 "gpu_launches": launches * a.steps,
                 "roofline": roof,
                 "contractions": contractions,
