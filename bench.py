@@ -639,7 +639,7 @@ def run_configs(a):
                 df = torch.empty(ncol, 3, 3, device=dev)
                 fn = lambda: plan.forward(dp, dsets["pts"], out=(f, df))
             else:
-                loss = torch.empty(9 + prob["energy_nt"], dtype=torch.float64, device=dev)
+                loss = torch.empty(9 + prob["energy_nt"] + (1 if wsym > 0 else 0), dtype=torch.float64, device=dev)
                 grad = torch.empty(plan.n_params, dtype=torch.float32, device=dev)
                 fn = lambda: plan.loss_grad(dp, dsets, out=(loss, grad))
             # measured kernels: the statevector kernel (SIMT), the forward contraction
@@ -711,7 +711,9 @@ def run_paper_net(a):
     grid sizes of its timing table (40^3 and 87^3 collocation points on [-1,1]^2 x [0,1.5],
     vacuum, IC plane of the grid, energy term over the grid's time slices): one step is
     qp_loss_grad (fields, input derivatives, losses, adjoint gradient of all 66,932 trainable
-    parameters).
+    parameters). Each grid runs twice: without the symmetry penalty, and with the whole loss of
+    Eq. 24 (L_sym of Eq. 18 at weight 10: every collocation point also evaluated at its two
+    mirrors).
     The paper's numbers (TorQ, one training epoch with second-order autograd and Adam, A100 or
     L40s) are context, not the same measurement."""
     import torch
@@ -722,17 +724,17 @@ def run_paper_net(a):
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
     paper = {40: 0.145136, 87: 0.849967}
-    for g in ((a.paper_grid,) if a.paper_grid > 0 else (40, 87)):
+    for g, wsym in [(g, w) for g in ((a.paper_grid,) if a.paper_grid > 0 else (40, 87)) for w in (0.0, 10.0)]:
         circ = W.circuit(7, 4, 7, ansatz="strong_rot", enc="rx", scale="acos", premap="rff_mlp",
                          rff_freqs=128, mlp_width=128, mlp_depth=3, periodic=True)
-        prob = W.problem("vacuum", w_energy=10.0, energy_slice=g * g, energy_nt=g)
+        prob = W.problem("vacuum", w_energy=10.0, energy_slice=g * g, energy_nt=g, w_sym=wsym)
         sets = {"colloc": W.grid_points(g, g, g, 1.5), "ic": W.ic_grid(g, g)}
         params = W.init_params(circ, 0)
         plan = qp.Plan(circ, prob, path=a.path)
         dp = torch.tensor(params, device=dev)
         dsets = {k: torch.tensor(v, device=dev) for k, v in sets.items()}
         plan.reserve(sum(v.shape[0] for v in dsets.values()), dev)
-        loss = torch.empty(9 + prob["energy_nt"], dtype=torch.float64, device=dev)
+        loss = torch.empty(9 + prob["energy_nt"] + (1 if wsym > 0 else 0), dtype=torch.float64, device=dev)
         grad = torch.empty(plan.n_params, dtype=torch.float32, device=dev)
         for _ in range(max(a.warmup, 3)):
             plan.loss_grad(dp, dsets, out=(loss, grad))
@@ -747,7 +749,8 @@ def run_paper_net(a):
         assert plan.last_device_error() == 0
         ms = sum(e0.elapsed_time(e1) for e0, e1 in ev) / a.steps
         ncol = sets["colloc"].shape[0]
-        print(json.dumps({"workload": "paper hybrid net, %d^3 grid" % g, "n_params": plan.n_params,
+        print(json.dumps({"workload": "paper hybrid net, %d^3 grid%s" % (g, ", with L_sym (Eq. 24 in full)" if wsym > 0
+                                                                         else ""), "n_params": plan.n_params,
                           "path": plan.path, "colloc_points": ncol, "ic_points": sets["ic"].shape[0],
                           "ms_per_step": ms, "colloc_pts_per_s": ncol / (ms / 1000.0),
                           "steps": a.steps, "warmup": max(a.warmup, 3),

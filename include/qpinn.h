@@ -164,8 +164,9 @@ typedef struct {
  *  [8] MSE(res3), [9 .. 9+energy_nt) energy slice sums U(t_k) (Eq. 31), and when w_sym > 0
  *  [9+energy_nt] w_sym * L_sym (Eq. 18: fields at (-x, y, t) and (x, -y, t) of every
  *  collocation point, the x-mirror terms left out in the dielectric case), which the total
- *  [0] includes. The symmetry penalty runs on the SIMT path (AUTO picks it; GEMM_SPLIT plans
- *  with w_sym > 0 are refused with QP_ERR_UNSUPPORTED). */
+ *  [0] includes. Both paths evaluate it: a fields-only pass over the collocation points and
+ *  their mirrors gives each mirrored point's field cotangents, and the main pass carries the
+ *  mirrored points as extra rows with those cotangents. */
 #define QP_NLOSS 9
 
 typedef struct qp_plan qp_plan;

@@ -418,8 +418,6 @@ qp_status validate(const qp_circuit* c, const qp_problem* p, int32_t path) {
   if (c->premap != QP_PREMAP_RFF_MLP && c->periodic != 0) return QP_ERR_INVALID_ARG;
   if (p->medium != QP_MEDIUM_VACUUM && p->medium != QP_MEDIUM_DIELECTRIC) return QP_ERR_INVALID_ARG;
   if (p->phys_loss < 0 || p->phys_loss > 1 || !(p->w_sym >= 0.f)) return QP_ERR_INVALID_ARG;
-  // the symmetry penalty's mirrored evaluations run on the gate-by-gate path
-  if (p->w_sym > 0.f && path == QP_PATH_GEMM_SPLIT) return QP_ERR_UNSUPPORTED;
   if (p->energy_nt < 0 || p->energy_nt > QP_MAXNT || p->energy_slice < 0) return QP_ERR_INVALID_ARG;
   if (p->medium == QP_MEDIUM_DIELECTRIC && !(p->sigmoid_w > 0.f)) return QP_ERR_INVALID_ARG;
   if (!(p->ic_sigma > 0.f)) return QP_ERR_INVALID_ARG;
@@ -463,9 +461,9 @@ qp_status qp_plan_create(const qp_circuit* circuit, const qp_problem* problem, i
   pl->p = *problem;
   // AUTO: the fused-unitary tensor-core path where it is faster and stays within 1e-5 of the
   // FP64 reference (7-10 qubits: at 7 qubits 2x the gate-by-gate speed at 2 layers, 4.5x at 6);
-  // the FP32 gate-by-gate path otherwise (and for the symmetry penalty).
+  // the FP32 gate-by-gate path otherwise.
   pl->path = path != QP_PATH_AUTO ? path
-             : (circuit->n_qubits >= 7 && !(problem->w_sym > 0.f) ? QP_PATH_GEMM_SPLIT : QP_PATH_SIMT_FP32);
+             : (circuit->n_qubits >= 7 ? QP_PATH_GEMM_SPLIT : QP_PATH_SIMT_FP32);
   const int n = circuit->n_qubits;
   if (qp_build_sched(n, circuit->n_layers, circuit->ansatz, &pl->sched) != 0) {
     delete pl;
@@ -1058,17 +1056,26 @@ static qp_status launch_premap_bwd(qp_plan* pl, const WsLayout& w, const float* 
 // Fused-unitary loss and gradient: forward GEMM per point set, pointwise loss and costates,
 // weight-gradient GEMM over all (point, vector) rows, FP64 chunk sum, Y = U' G and the
 // B-independent sweep for the Pauli contractions of every gate, then the common reduction.
-static qp_status dense_loss_grad(qp_plan* pl, const float* d_params, const float* const pts[3],
-                                 const int64_t npts[3], double* d_loss, float* d_grad, cudaStream_t s) {
+// With the symmetry penalty (Eq. 18) a fields-only tensor-core pass over the collocation points
+// and their mirrors comes first; its per-point cotangents then enter the main pass, the
+// mirrored points as rows of set 2 after the boundary points whose cotangents are given.
+static qp_status dense_loss_grad(qp_plan* pl, const float* d_params, const float* const pts0[3],
+                                 const int64_t npts0[3], double* d_loss, float* d_grad, cudaStream_t s) {
   pl->last_launches = 0;
-  const int64_t P = npts[0] + npts[1] + npts[2];
-  const WsLayout w = ws_layout(pl, P);
+  const WsLayout w = ws_layout(pl, npts0[0] + npts0[1] + npts0[2]);
   if (!pl->ws || pl->ws_bytes < w.total) return QP_ERR_BUFFER_TOO_SMALL;
   pl->last_stream = s;
   pl->last_status = (const int32_t*)((char*)pl->ws + w.status);
   char* ws = (char*)pl->ws;
   const int n = pl->c.n_qubits, dim = 1 << n, L = pl->c.n_layers;
   int launches = 0;
+  const bool sym = pl->p.w_sym > 0.f && npts0[0] > 0;
+  const int64_t nm = sym ? (pl->p.medium == QP_MEDIUM_VACUUM ? 2 * npts0[0] : npts0[0]) : 0;
+  // the points of the main pass: set 2 extended by the mirrored points
+  const float* pts[3] = {pts0[0], pts0[1], sym ? (const float*)(ws + w.sxb) : pts0[2]};
+  const int64_t npts[3] = {npts0[0], npts0[1], npts0[2] + nm};
+  const int64_t P = npts[0] + npts[1] + npts[2];
+  int nsym = 0;
   qpd::BuildArgs ba = {};
   ba.params = d_params; ba.circ_off = pl->circ_off; ba.n = n; ba.L = L;
   ba.gates = (double2*)(ws + w.dgates);
@@ -1085,9 +1092,50 @@ static qp_status dense_loss_grad(qp_plan* pl, const float* d_params, const float
   }
   ba.W16 = fwd16 ? (__half*)(ws + w.dW16) : nullptr;
   // the unitary build depends on the circuit parameters only (CRZ ansatze: also on the mesh
-  // diagonal of the front launches): it runs on the side stream beside the premap
+  // diagonal of the front launches): it runs on the side stream beside the premap, except
+  // with the symmetry penalty, whose fields-only pre-pass needs it first
   const bool side = pl->aux && !qp_has_crz(pl->c.ansatz);
-  if (side) {
+  const bool side_build = side && !sym;
+  if (sym) {
+    float* xb = (float*)(ws + w.sxb);
+    const int64_t tot = npts0[2] + nm;
+    qpk::sym_points_kernel<<<(unsigned)((tot + 255) / 256 < pl->sm_count * 4 ? (tot + 255) / 256 : pl->sm_count * 4),
+                             256, 0, s>>>(pts0[0], npts0[0], pts0[2], npts0[2], pl->p.medium, xb);
+    // fields at the collocation points (set 0) and their mirrors (set 1), no derivatives
+    const float* fp[3] = {pts0[0], xb + 3 * npts0[2], nullptr};
+    const int64_t fn[3] = {npts0[0], nm, 0};
+    qp_status st = launch_front(pl, d_params, fp, fn, w, s, false);
+    if (st != QP_OK) return st;
+    qpd::BuildArgs bp = ba;
+    if (fwd16) bp.W = nullptr;
+    qpd::dense_gates_kernel<<<1, L * n, 0, s>>>(bp);
+    qpd::dense_build_kernel<<<dim, 128, 2 * dim * 16, s>>>(bp);
+    qpd::GemmArgs ga = {};
+    ga.thetaJ = (const float*)(ws + w.thetaJ); ga.W = (const float*)(ws + w.dW);
+    ga.phi = (float2*)(ws + w.dphi); ga.n = n; ga.nv = 1;
+    ga.npts = npts0[0] + nm; ga.pt_base = 0; ga.status = (int32_t*)(ws + w.status);
+    const int64_t ntiles = (ga.npts + qpd::TM - 1) / qpd::TM;
+    const int gblocks = (int)(ntiles < pl->sm_count ? ntiles : pl->sm_count);
+    const int64_t items = ntiles * ((2 * dim) / 256);
+    const int iblocks = (int)(items < pl->sm_count ? items : pl->sm_count);
+    if (fwd16)
+      qpd::dense_row16_kernel<0><<<iblocks, qpd::F16_THREADS, qpd::row16_smem_bytes(), s>>>(
+          ga, (const __half*)(ws + w.dW16), nullptr);
+    else
+      qpd::dense_row_gemm_kernel<0><<<gblocks, 128, qpd::gemm_smem_bytes(n, 0), s>>>(ga);
+    qpd::ReadoutArgs ra;
+    ra.phi = ga.phi; ra.head = d_params + pl->head_off; ra.n = n; ra.m = pl->c.n_readout;
+    ra.nv = 1; ra.npts = ga.npts; ra.pt_base = 0; ra.out_f = (float*)(ws + w.sF); ra.out_df = nullptr;
+    const int64_t rb = (ga.npts + 7) / 8;
+    qpd::dense_readout_kernel<<<(unsigned)(rb < 4096 ? rb : 4096), 256, 0, s>>>(ra);
+    const int64_t nb = (npts0[0] + 255) / 256;
+    nsym = (int)(nb < pl->sm_count * 4 ? nb : pl->sm_count * 4);
+    const double N = (double)(pl->cur_norm[0] > 0 ? pl->cur_norm[0] : npts0[0]);
+    qpk::sym_cot_kernel<<<nsym, 256, 0, s>>>((const float*)(ws + w.sF), npts0[0], pl->p.medium, pl->p.w_sym, N,
+                                             (float*)(ws + w.sgs), (float*)(ws + w.sge), (double*)(ws + w.spart));
+    launches += 7 + front_launches(pl);
+  }
+  if (side_build) {
     qpd::BuildArgs bs = ba;
     if (fwd16) bs.W = nullptr;
     if (cudaEventRecord(pl->ev_fork, s) != cudaSuccess || cudaStreamWaitEvent(pl->aux, pl->ev_fork, 0) != cudaSuccess)
@@ -1106,13 +1154,14 @@ static qp_status dense_loss_grad(qp_plan* pl, const float* d_params, const float
     launches += 1;
   }
   if (fwd16) ba.W = nullptr;
-  if (side) {
+  if (side_build) {
     if (cudaStreamWaitEvent(s, pl->ev_join, 0) != cudaSuccess) return QP_ERR_CUDA;
-  } else {
+    launches += 2;
+  } else if (!sym) {
     qpd::dense_gates_kernel<<<1, L * n, 0, s>>>(ba);
     qpd::dense_build_kernel<<<dim, 128, 2 * dim * 16, s>>>(ba);
+    launches += 2;
   }
-  launches += 2;
   int64_t base = 0;
   if (fused) {
     // forward contraction with the pointwise stage as its epilogue (states stay on chip)
@@ -1135,6 +1184,9 @@ static qp_status dense_loss_grad(qp_plan* pl, const float* d_params, const float
     fa.status = (int32_t*)(ws + w.status);
     fa.scal = (int32_t*)(ws + w.status) + 16;
     fa.wait_limit = pl->wait_limit;
+    fa.gsym = sym ? (const float*)(ws + w.sgs) : nullptr;
+    fa.gext = sym ? (const float*)(ws + w.sge) : nullptr;
+    fa.nbc = npts0[2];
     const int64_t ftiles = fa.tile_end[2];
     const int fblocks = (int)(ftiles < pl->sm_count ? (ftiles > 0 ? ftiles : 1) : pl->sm_count);
     prof_mark(pl, 0, true, s);
@@ -1183,6 +1235,9 @@ static qp_status dense_loss_grad(qp_plan* pl, const float* d_params, const float
     pa.grad_stride = pl->nE + 3 * pl->c.n_readout + 3;
     pa.nE = pl->nE;
     pa.lmax = fwd16 ? (int32_t*)(ws + w.status) + 17 : nullptr;   // scale of the mu operand
+    pa.gsym = sym ? (const float*)(ws + w.sgs) : nullptr;
+    pa.gext = sym ? (const float*)(ws + w.sge) : nullptr;
+    pa.nbc = npts0[2];
     const int psmem = ((QP_NLP + pl->p.energy_nt) * 8 + 15) / 16 * 16 + (3 * pl->c.n_readout + 3) * 4;
     if (n == 9)
       qpd::dense_point_kernel<9><<<pl->blocks_grad, qpd::PT_POINT_THREADS, psmem, s>>>(pa);
@@ -1339,7 +1394,7 @@ static qp_status dense_loss_grad(qp_plan* pl, const float* d_params, const float
     launches += premap_bwd_launches(pl);
   }
   if (side && cudaStreamWaitEvent(s, pl->ev_join, 0) != cudaSuccess) return QP_ERR_CUDA;
-  st = launch_reduce(pl, w, d_params, npts, d_loss, d_grad, mlp, s);
+  st = launch_reduce(pl, w, d_params, npts0, d_loss, d_grad, mlp, s, nsym);
   pl->last_launches = launches + 1;
   return st;
 }

@@ -997,6 +997,11 @@ struct PointArgs {
   float* blk_grad;
   int32_t loss_stride, grad_stride, nE;
   int32_t* lmax;          // float bits of the largest |lambda| component (atomic maximum), or null
+  // symmetry penalty (Eq. 18): cotangents added to the collocation points' fields (gsym) and
+  // given for the rows of set 2 from nbc on (gext, the mirrored points); null without it
+  const float* gsym;
+  const float* gext;
+  int64_t nbc;
 };
 
 // 8 warps per SM: a point's states (32 KiB at n = 10) are read twice, and the second read
@@ -1111,7 +1116,17 @@ __global__ void __launch_bounds__(PT_POINT_THREADS, 1) dense_point_kernel(PointA
     }
     const float* xp = a.pts[set] + li * 3;
     float g[3], gD[3][3];
-    qpk::point_loss(a.pb, set, li, a.npts[set], a.counts, xp[0], xp[1], f, D, true, lane == 0, sloss, g, gD);
+    const bool given = set == 2 && a.gext != nullptr && li >= a.nbc;
+    qpk::point_loss(a.pb, set, li, set == 2 && a.gext != nullptr ? a.nbc : a.npts[set], a.counts, xp[0], xp[1], f, D,
+                    !given, lane == 0, sloss, g, gD);
+    if (given) {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) g[c] = __ldg(a.gext + (li - a.nbc) * 3 + c);
+    }
+    if (set == 0 && a.gsym != nullptr) {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) g[c] += __ldg(a.gsym + li * 3 + c);
+    }
     float zb[QP_MAXQ], zbd[3][QP_MAXQ];
 #pragma unroll
     for (int i = 0; i < QP_MAXQ; ++i) {

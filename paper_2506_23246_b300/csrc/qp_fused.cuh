@@ -43,6 +43,12 @@ struct FusedArgs {
   int32_t use_tma;         // 1: costates leave through tensor-map bulk stores (maps valid), 0: plain stores
   uint32_t wait_limit;     // polls of the pipeline waits (0: QP_MBAR_LIMIT); the drain waits that
                            // let in-flight copies and MMAs finish always keep QP_MBAR_LIMIT
+  // symmetry penalty (Eq. 18): field cotangents added to the collocation points' (gsym,
+  // [npts[0]][3]) and given outright for the rows of set 2 from nbc on, the mirrored points
+  // (gext, [npts[2] - nbc][3]); both null without the penalty
+  const float* gsym;
+  const float* gext;
+  int64_t nbc;
 };
 
 // Tensor-map bulk store of one staged 128-row x 32-column chunk (bulk group of this thread).
@@ -451,7 +457,19 @@ __global__ void __launch_bounds__(F_THREADS, 1) dense_fused_fwd_kernel(FusedArgs
       float g[3], gD[3][3];
       float lt[QP_NLP], ev;
       int slice;
-      qpk::point_loss_terms(a.pb, set, ppc, np, a.counts, __ldg(xp), __ldg(xp + 1), f, D, active, lt, slice, ev, g, gD);
+      // rows of set 2 past the boundary points are mirrored points with given cotangents
+      const bool given = set == 2 && a.gext != nullptr && pp >= a.nbc;
+      const int64_t npl = set == 2 && a.gext != nullptr ? a.nbc : np;
+      qpk::point_loss_terms(a.pb, set, ppc, npl, a.counts, __ldg(xp), __ldg(xp + 1), f, D, active && !given, lt, slice,
+                            ev, g, gD);
+      if (given && active) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) g[c] = __ldg(a.gext + (pp - a.nbc) * 3 + c);
+      }
+      if (set == 0 && a.gsym != nullptr && active) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) g[c] += __ldg(a.gsym + pp * 3 + c);
+      }
       if (s_r != 0) ev = 0.f;   // each point once
       if (s_r == 0) {
 #pragma unroll

@@ -650,24 +650,26 @@ def test_intuitive_dielectric_loss_grad(torch_cuda, oracle, n, path):
     _loss_grad_check(torch_cuda, oracle, circ, prob, params, sets, idx, path=path)
 
 
-@pytest.mark.parametrize("n,medium", [(5, "vacuum"), (5, "dielectric"), (8, "vacuum")])
-def test_symmetry_penalty_loss_grad(torch_cuda, oracle, n, medium):
+@pytest.mark.parametrize("n,medium,path,depth", [(5, "vacuum", "auto", 1), (5, "dielectric", "auto", 1),
+                                                 (8, "vacuum", "simt", 1), (8, "vacuum", "auto", 1),
+                                                 (8, "dielectric", "gemm_split", 1), (7, "vacuum", "gemm_split", 2),
+                                                 (9, "vacuum", "gemm_split", 1), (9, "dielectric", "gemm_split", 1)])
+def test_symmetry_penalty_loss_grad(torch_cuda, oracle, n, medium, path, depth):
     """The symmetry penalty L_sym (Eq. 18, weight 10 as in Eq. 24; x-mirror terms left out in
     the dielectric case): fields at the mirrored points, the penalty appended to the loss terms
-    and in the total, and its gradient through the mirrored evaluations, against the oracle.
-    The penalty runs on the gate-by-gate path (AUTO picks it at 8 qubits as well)."""
-    from paper_2506_23246_b300 import qp
+    and in the total, and its gradient through the mirrored evaluations, against the oracle, on
+    the gate-by-gate path and on the tensor-core path (fused kernels at 7 and 8 qubits, row
+    kernels at 9), where a fields-only pre-pass gives the mirrored points' cotangents."""
     circ = W.circuit(n, 2, n, ansatz="strong_rot", enc="rx", scale="acos", premap="rff_mlp",
-                     rff_freqs=8, mlp_width=8, mlp_depth=1)
+                     rff_freqs=8, mlp_width=8, mlp_depth=depth)
     prob = W.problem(medium, disk_x0=0.5, disk_r=0.3, w_energy=10.0, energy_slice=16,
                      energy_nt=3, w_sym=10.0)
     sets = {"colloc": W.uniform_points(45, n + 90, 1.0), "ic": W.ic_points_uniform(16, n + 91),
             "bc": W.bc_points(16, n + 92)}
     params = W.init_params(circ, n + 93)
-    plan, loss, _ = _loss_grad_check(torch_cuda, oracle, circ, prob, params, sets, path="auto")
-    assert plan.path == "simt" and loss.shape[0] == 9 + 3 + 1 and loss[-1] > 0
-    with pytest.raises(qp.QPError):
-        qp.Plan(circ, prob, path="gemm_split")
+    plan, loss, _ = _loss_grad_check(torch_cuda, oracle, circ, prob, params, sets, path=path)
+    want = path if path != "auto" else ("gemm_split" if n >= 7 else "simt")
+    assert plan.path == want and loss.shape[0] == 9 + 3 + 1 and loss[-1] > 0
 
 
 @pytest.mark.parametrize("n,path,depth", [(5, "simt", 2), (8, "gemm_split", 1), (7, "simt", 3)])
