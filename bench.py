@@ -55,6 +55,10 @@ def _args():
     ap.add_argument("--paper-grid", type=int, default=0,
                     help="--workload paper_net: only this grid (points per axis; 0: the 40^3 and 87^3 "
                          "grids of the paper's timing table)")
+    ap.add_argument("--timeline", action="store_true",
+                    help="diagnosis only, no bench line: the kernels of one graph-replayed step of the "
+                         "benchmark workload with their start, duration and stream (CUPTI through "
+                         "torch.profiler), one line each")
     ap.add_argument("--workload", default="c3", choices=["c3", "c5", "configs", "paper_net"],
                     help="c3: the full QPINN step (default); c5: 32 uneven instances in one "
                          "batched call against the same instances called one by one; configs: "
@@ -764,8 +768,61 @@ def run_paper_net(a):
     return 0
 
 
+def run_timeline(a):
+    """Kernel timeline of the benchmark step (both streams of the call), replayed as one CUDA graph
+    after L2 flushes, traced by CUPTI through torch.profiler. The durations come from a traced
+    run: they explain the bench numbers, they are not bench numbers."""
+    import tempfile
+    import torch
+    from torch.profiler import ProfilerActivity, profile
+    from paper_2506_23246_b300 import build, qp
+    from paper_2506_23246_b300 import workloads as W
+    build.build()
+    dev = torch.device("cuda", 0)
+    circ, prob, params, sets = W.c3_workload(0, nx=a.c3_grid, ny=a.c3_grid)
+    plan = qp.Plan(circ, prob, path=a.path)
+    dp = torch.tensor(params, device=dev)
+    dsets = {k: torch.tensor(v, device=dev) for k, v in sets.items()}
+    plan.reserve(sum(t.shape[0] for t in dsets.values()), dev)
+    loss = torch.empty(9 + prob["energy_nt"], dtype=torch.float64, device=dev)
+    grad = torch.empty(plan.n_params, dtype=torch.float32, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    for _ in range(max(a.warmup, 3)):
+        plan.loss_grad(dp, dsets, out=(loss, grad))
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        plan.loss_grad(dp, dsets, out=(loss, grad))
+    for _ in range(3):
+        g.replay()
+    torch.cuda.synchronize()
+    nsteps = max(a.steps, 2)
+    with profile(activities=[ProfilerActivity.CUDA]) as prof:
+        for i in range(nsteps):
+            flush.fill_(float(i))
+            g.replay()
+        torch.cuda.synchronize()
+    with tempfile.TemporaryDirectory() as td:
+        fn = os.path.join(td, "trace.json")
+        prof.export_chrome_trace(fn)
+        with open(fn) as fh:
+            events = json.load(fh)["traceEvents"]
+    ks = sorted((e["ts"], e["dur"], e.get("args", {}).get("stream"), e["name"]) for e in events
+                if e.get("cat") == "kernel")
+    # steps begin at the flush kernels; print the last whole step
+    starts = [i for i, k in enumerate(ks) if "FillFunctor" in k[3]]
+    i0, i1 = starts[-1], len(ks)
+    t0 = ks[i0][0] + ks[i0][1]
+    print("# start_us dur_us end_us stream kernel (t = 0 at the end of the L2 flush)")
+    for ts, d, st, name in ks[i0 + 1:i1]:
+        print("%9.1f %8.1f %9.1f  %s  %s" % (ts - t0, d, ts - t0 + d, st, name.split("(")[0]))
+    return 0
+
+
 def main():
     a = _args()
+    if a.timeline:
+        return run_timeline(a)
     if a.impl == "reference":
         return run_reference(a)
     if a.workload == "c5":

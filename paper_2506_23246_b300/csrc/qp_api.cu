@@ -37,6 +37,7 @@ struct qp_plan {
   int warps_grad = 0, blocks_grad = 0, warps_fwd = 0, blocks_fwd = 0;
   int smem_grad = 0, smem_fwd = 0, sstride_grad = 0, sstride_fwd = 0;
   int nwblk = 0, wtile = 0, smem_wgrad = 0, smem_premap = 0, smem_premap4 = 0;
+  int wblk = 0;   // premap weight-gradient slots written by the last premap backward (<= nwblk)
   bool swc_big = false;   // the one-launch sweep runs as a 16-CTA cluster
   bool pg_ok = false;     // RFF + MLP premap with F = 64, H = 32: the GEMM-formulated kernels
   bool deep = false;      // RFF + MLP premap of another depth or width: the layer-by-layer kernels
@@ -1050,8 +1051,11 @@ static void fill_circ(qp_plan* pl, QPCircArgs& a, const WsLayout& w, const float
 static qp_status launch_reduce(qp_plan* pl, const WsLayout& w, const float* d_params, const int64_t npts[3],
                                double* d_loss, float* d_grad, bool mlp, cudaStream_t s, int nsym = 0,
                                int64_t nblk = -1);
+// grid_cap > 0: at most that many blocks of the one-pass tensor-core kernel; pdl: launched as the
+// programmatic dependent of the kernel before it in the stream
 static qp_status launch_premap_bwd(qp_plan* pl, const WsLayout& w, const float* d_params,
-                                   const float* const pts[3], const int64_t npts[3], cudaStream_t s);
+                                   const float* const pts[3], const int64_t npts[3], cudaStream_t s,
+                                   int grid_cap = 0, bool pdl = false);
 
 // Fused-unitary loss and gradient: forward GEMM per point set, pointwise loss and costates,
 // weight-gradient GEMM over all (point, vector) rows, FP64 chunk sum, Y = U' G and the
@@ -1272,7 +1276,13 @@ static qp_status dense_loss_grad(qp_plan* pl, const float* d_params, const float
   prof_mark(pl, 1, false, s);
   launches += 1;
   // the gate-gradient chain (slot sum, Y = U'G, sweep) depends on G only: on the side stream,
-  // beside mu and the premap backward, joined back before the reduction
+  // beside mu and the premap backward, joined back before the reduction. With the one-pass
+  // premap backward (n = 7, 8) the chain stops at Y on the side stream; the sweep cluster runs
+  // on the call's stream after mu, and the premap backward is launched as its programmatic
+  // dependent on the other SMs (a one-wave kernel started first would hold every SM, and the
+  // cluster would wait for it to drain).
+  const bool pdl_tail = side && fused && mlp && !pl->deep && pl->pg_ok;
+  const int sweep_S = qpd::swc_size(n, pl->swc_big);
   cudaStream_t ss = s;
   if (side) {
     if (cudaEventRecord(pl->ev_fork, s) != cudaSuccess || cudaStreamWaitEvent(pl->aux, pl->ev_fork, 0) != cudaSuccess)
@@ -1294,22 +1304,27 @@ static qp_status dense_loss_grad(qp_plan* pl, const float* d_params, const float
     launches += 1;
   }
   qpd::dense_y_kernel<<<dim3(dim / 16, dim / 16), 256, 0, ss>>>(sa);
-  if (n <= 8) {
-    // the whole sweep in one cluster launch (Y lives in the cluster's shared memory)
-    const int S = qpd::swc_size(n, pl->swc_big);
+  // the whole sweep in one cluster launch (Y lives in the cluster's shared memory), n <= 8
+  auto launch_sweep = [&](cudaStream_t st) -> qp_status {
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(S);
+    cfg.gridDim = dim3(sweep_S);
     cfg.blockDim = dim3(qpd::SWC_THREADS);
-    cfg.dynamicSmemBytes = qpd::swc_smem(n, L, S, qp_crz_sums(pl->c.ansatz, n));
-    cfg.stream = ss;
+    cfg.dynamicSmemBytes = qpd::swc_smem(n, L, sweep_S, qp_crz_sums(pl->c.ansatz, n));
+    cfg.stream = st;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = S;
+    attr[0].val.clusterDim.x = sweep_S;
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    if (cudaLaunchKernelEx(&cfg, qpd::dense_sweep_cluster_kernel, sa) != cudaSuccess) return QP_ERR_CUDA;
+    return cudaLaunchKernelEx(&cfg, qpd::dense_sweep_cluster_kernel, sa) != cudaSuccess ? QP_ERR_CUDA : QP_OK;
+  };
+  if (n <= 8) {
+    if (!pdl_tail) {
+      const qp_status sst = launch_sweep(ss);
+      if (sst != QP_OK) return sst;
+    }
     launches += 1;
   } else {
     float2* Ya = sa.Y;
@@ -1389,11 +1404,20 @@ static qp_status dense_loss_grad(qp_plan* pl, const float* d_params, const float
       qpd::dense_embed_grad_kernel<<<(unsigned)(eb < 8192 ? eb : 8192), 256, 0, s>>>(ea);
       launches += 1;
     }
-    st = launch_premap_bwd(pl, w, d_params, pts, npts, s);
+    if (pdl_tail) {
+      // Y is ready on the side stream: the sweep on this stream, then the premap backward on
+      // the SMs the sweep cluster leaves (two blocks per SM)
+      if (cudaStreamWaitEvent(s, pl->ev_join, 0) != cudaSuccess) return QP_ERR_CUDA;
+      st = launch_sweep(s);
+      if (st != QP_OK) return st;
+      st = launch_premap_bwd(pl, w, d_params, pts, npts, s, 2 * (pl->sm_count - sweep_S), true);
+    } else {
+      st = launch_premap_bwd(pl, w, d_params, pts, npts, s);
+    }
     if (st != QP_OK) return st;
     launches += premap_bwd_launches(pl);
   }
-  if (side && cudaStreamWaitEvent(s, pl->ev_join, 0) != cudaSuccess) return QP_ERR_CUDA;
+  if (side && !pdl_tail && cudaStreamWaitEvent(s, pl->ev_join, 0) != cudaSuccess) return QP_ERR_CUDA;
   st = launch_reduce(pl, w, d_params, npts0, d_loss, d_grad, mlp, s, nsym);
   pl->last_launches = launches + 1;
   return st;
@@ -1601,8 +1625,10 @@ qp_status qp_loss_grad(qp_plan* pl, const float* d_params, const qp_batch* batch
 
 // Premap backward (per point) and its weight-gradient partials, from dL/dtheta and dL/dJ.
 static qp_status launch_premap_bwd(qp_plan* pl, const WsLayout& w, const float* d_params,
-                                   const float* const pts[3], const int64_t npts[3], cudaStream_t s) {
+                                   const float* const pts[3], const int64_t npts[3], cudaStream_t s,
+                                   int grid_cap, bool pdl) {
   char* ws = (char*)pl->ws;
+  pl->wblk = pl->nwblk;
   const int64_t P = npts[0] + npts[1] + npts[2];
   qpk::PremapArgs ma;
   std::memset(&ma, 0, sizeof(ma));
@@ -1617,9 +1643,20 @@ static qp_status launch_premap_bwd(qp_plan* pl, const WsLayout& w, const float* 
   if (pl->pg_ok) {
     // backward and weight-gradient partials in one pass (one partial slot per block)
     ma.status = (int32_t*)(ws + w.status);
-    qpk::premap_bwd_tc_kernel<<<pl->nwblk, qpk::PG_THREADS, qpk::pb_smem(pl->c.n_qubits), s>>>(
-        ma, (float*)(ws + w.wpart), (int32_t)(pl->mlp_count - pl->nfixed));
-    return cuda_status(cudaGetLastError());
+    const int grid = grid_cap > 0 && grid_cap < pl->nwblk ? grid_cap : pl->nwblk;
+    pl->wblk = grid;   // the reduction sums exactly the slots written
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(qpk::PG_THREADS);
+    cfg.dynamicSmemBytes = qpk::pb_smem(pl->c.n_qubits);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl ? 1 : 0;
+    return cuda_status(cudaLaunchKernelEx(&cfg, qpk::premap_bwd_tc_kernel, ma, (float*)(ws + w.wpart),
+                                          (int32_t)(pl->mlp_count - pl->nfixed)));
   }
   if (P > 0) {
     const int64_t qb = (P + 31) / 32;
@@ -1657,7 +1694,7 @@ static qp_status launch_reduce(qp_plan* pl, const WsLayout& w, const float* d_pa
   ra.nE = pl->nE;
   ra.ansatz = pl->c.ansatz;
   ra.wpart = (const float*)(ws + w.wpart);
-  ra.nwblk = mlp ? pl->nwblk : 0;
+  ra.nwblk = mlp ? pl->wblk : 0;
   ra.nW = (int32_t)(pl->mlp_count - pl->nfixed);
   ra.cmat = (const float*)(ws + w.cmat);
   ra.counts = (const int32_t*)(ws + w.status) + 1;

@@ -1501,6 +1501,9 @@ __global__ void __launch_bounds__(SWC_THREADS) dense_sweep_cluster_kernel(SweepA
   float* es = reinterpret_cast<float*>(cinv + dim);      // [L][n][3] E partials, [L][ncz] CRZ sums
   const bool crz = qp_has_crz(a.ansatz);
   const int ncz = qp_crz_sums(a.ansatz, n);
+  // the whole cluster is resident: a kernel launched as this one's programmatic dependent (the
+  // premap backward of the loss call) may take the other SMs now
+  qptc::pdl_launch_dependents();
   for (int i = threadIdx.x; i < L * n * 4; i += blockDim.x) {
     const double2 g = a.gates[i];
     gm[i] = make_float2((float)g.x, (float)g.y);

@@ -498,6 +498,9 @@ __global__ void __launch_bounds__(PG_THREADS, 2) premap_bwd_tc_kernel(PremapArgs
   qptc::fence_before();
   __syncthreads();
   if (warp == 0) qptc::tmem_dealloc(tmem, 128);
+  // launched as the programmatic dependent of the gate sweep: finish only after the sweep has,
+  // so that the launches after this one see its results (no-op for an ordinary launch)
+  qptc::pdl_wait();
 }
 
 }  // namespace qpk

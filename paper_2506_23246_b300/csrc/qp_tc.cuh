@@ -24,6 +24,12 @@ __device__ __forceinline__ float2 cluster_ld_f2(uint32_t addr) {
   asm volatile("ld.shared::cluster.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(addr) : "memory");
   return v;
 }
+// Programmatic dependent launch. launch_dependents lets the next kernel of the stream, when it
+// was launched with the programmatic-serialization attribute, be scheduled once every CTA of
+// this grid has issued it; pdl_wait waits until the grid this one depends on that way has
+// completed and its memory operations are visible. Both are no-ops for ordinary launches.
+__device__ __forceinline__ void pdl_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void cluster_sync() {
   asm volatile("barrier.cluster.arrive.release.aligned;\nbarrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
