@@ -643,7 +643,7 @@ def run_configs(a):
                 df = torch.empty(ncol, 3, 3, device=dev)
                 fn = lambda: plan.forward(dp, dsets["pts"], out=(f, df))
             else:
-                loss = torch.empty(9 + prob["energy_nt"] + (1 if wsym > 0 else 0), dtype=torch.float64, device=dev)
+                loss = torch.empty(9 + prob["energy_nt"], dtype=torch.float64, device=dev)
                 grad = torch.empty(plan.n_params, dtype=torch.float32, device=dev)
                 fn = lambda: plan.loss_grad(dp, dsets, out=(loss, grad))
             # measured kernels: the statevector kernel (SIMT), the forward contraction
