@@ -149,25 +149,44 @@ int64_t wg_rows_per_chunk(const qp_plan* pl) {
 }
 
 // Weight-gradient launch geometry for `nkc` 16-row steps: tiles of min(256, 2^n) basis
-// indices x 256 components, CTA groups per tile (persistent CTAs, balanced step ranges),
-// flushes per CTA and steps per flush (at most wg_rows_per_chunk rows each); one partial slot
-// per CTA of a tile.
+// indices x 256 components; the tiles' steps as one tile-major sequence split into `grid`
+// balanced ranges (persistent CTAs, one per SM; a range meets at most two tiles); steps per
+// flush (at most wg_rows_per_chunk rows); partial slots per tile: the most CTAs any tile meets.
 struct WgGeom {
-  int tiles, ngroups, spc, fl;
+  int tiles, grid, fl;
   int64_t nslots;
 };
+static int wg_tiles(const qp_plan* pl) {
+  const int n = pl->c.n_qubits, dim = 1 << n;
+  return (dim / qpd::wg_mtc(n)) * (2 * dim / 256);
+}
 WgGeom wg_geom(const qp_plan* pl, int64_t nkc) {
   WgGeom g;
-  const int n = pl->c.n_qubits, dim = 1 << n;
-  g.tiles = (dim / qpd::wg_mtc(n)) * (2 * dim / 256);
-  g.ngroups = pl->sm_count / g.tiles > 0 ? pl->sm_count / g.tiles : 1;
-  const int64_t per = nkc > 0 ? (nkc + g.ngroups - 1) / g.ngroups : 1;
+  g.tiles = wg_tiles(pl);
+  const int64_t T = (int64_t)g.tiles * (nkc > 0 ? nkc : 0);
+  g.grid = (int)(T > 0 && T < pl->sm_count ? T : pl->sm_count);
+  if (g.grid < g.tiles && T >= g.tiles) g.grid = g.tiles;   // a range then meets at most two tiles
+  // n <= 8: a multiple of the tile count, so that every range lies inside one tile (the
+  // kernel's second segment is compiled out there); T itself is one
+  if (pl->c.n_qubits <= 8) g.grid = g.grid / g.tiles * g.tiles;
+  const int64_t per = T > 0 ? (T + g.grid - 1) / g.grid : 1;
   const int64_t flmax = wg_rows_per_chunk(pl) / qpd::WKC;
   const int64_t nfl = (per + flmax - 1) / flmax;
   g.fl = (int)((per + nfl - 1) / nfl);
-  g.spc = (int)nfl;
-  g.nslots = g.ngroups;
+  g.nslots = 1;
+  for (int t = 0; t < g.tiles && T > 0; ++t) {
+    const int64_t m = qpd::wg_cta_of((int64_t)(t + 1) * nkc - 1, T, g.grid) - qpd::wg_cta_of((int64_t)t * nkc, T, g.grid) + 1;
+    if (m > g.nslots) g.nslots = m;
+  }
   return g;
+}
+// Partial slots the workspace holds: SMs / tiles where the SMs divide evenly over the tiles
+// (every range then lies inside one tile), else at most 2 ceil(SMs / tiles) + 2 ranges meet a
+// tile.
+int64_t wg_slots_cap(const qp_plan* pl) {
+  const int t = wg_tiles(pl);
+  if (pl->sm_count % t == 0 || pl->c.n_qubits <= 8) return pl->sm_count / t;
+  return 2 * ((pl->sm_count + t - 1) / t) + 2;
 }
 
 bool dense_path(const qp_plan* pl) { return pl->path == QP_PATH_GEMM_SPLIT; }
@@ -328,7 +347,7 @@ WsLayout ws_layout(const qp_plan* pl, int64_t P0) {
   w.dY = o; o = al256(o + (dg ? dim * dim * 8 : 0));
   // upper bound of the weight-gradient partial slots: 16-row steps of 4 P rows, plus one per
   // set boundary
-  const int64_t nch = dg ? wg_geom(pl, (4 * P + qpd::WKC - 1) / qpd::WKC + 2).nslots : 0;
+  const int64_t nch = dg ? wg_slots_cap(pl) : 0;
   w.dpart = o; o = al256(o + (size_t)nch * dim * 2 * dim * 4);
   const bool dm = dg && pl->c.premap == QP_PREMAP_RFF_MLP;
   w.dWT = o; o = al256(o + (dm ? 2 * (2 * dim) * dim * 4 : 0));
@@ -1260,8 +1279,9 @@ static qp_status dense_loss_grad(qp_plan* pl, const float* d_params, const float
   wa.kc_end[1] = wa.kc_end[0] + (npts[1] + qpd::WKC - 1) / qpd::WKC;
   wa.kc_end[2] = wa.kc_end[1] + (npts[2] + qpd::WKC - 1) / qpd::WKC;
   const WgGeom wgm = wg_geom(pl, wa.kc_end[2]);
-  if (wgm.nslots > wg_geom(pl, (4 * P + qpd::WKC - 1) / qpd::WKC + 2).nslots) return QP_ERR_INTERNAL;
-  wa.tiles = wgm.tiles; wa.ngroups = wgm.ngroups; wa.spc = wgm.spc; wa.fl = wgm.fl;
+  if (wgm.nslots > wg_slots_cap(pl)) return QP_ERR_INTERNAL;
+  if ((int64_t)wgm.tiles * wa.kc_end[2] > (int64_t)INT32_MAX) return QP_ERR_UNSUPPORTED;   // 32-bit step counts
+  wa.tiles = wgm.tiles; wa.nslots = (int32_t)wgm.nslots; wa.fl = wgm.fl;
   wa.status = (int32_t*)(ws + w.status);
   prof_mark(pl, 1, true, s);
   wa.scal = (const int32_t*)(ws + w.status) + 16;
@@ -1269,7 +1289,7 @@ static qp_status dense_loss_grad(qp_plan* pl, const float* d_params, const float
     // FP16 pairs when the forward recorded both operand ranges
     void* wargs[] = {&wa};
     const cudaError_t le = cudaLaunchKernel(fwd16 ? wgrad_kernel<true>(n) : wgrad_kernel<false>(n),
-                                            dim3((unsigned)(wgm.tiles * wgm.ngroups)), dim3(qpd::wgc_threads(fwd16)),
+                                            dim3((unsigned)wgm.grid), dim3(qpd::wgc_threads(fwd16)),
                                             wargs, qpd::wgc_smem(n, fwd16).total, s);
     if (le != cudaSuccess) return QP_ERR_CUDA;
   }

@@ -18,10 +18,13 @@ namespace qpd {
 // (higher bits fixed by the tile), both as a value and its three tangents (forward-mode
 // duals), so each element of R is one dual product H[k >> 5] x Lo[k & 31].
 //
-// Persistent CTAs: CTA b owns tile b % tiles and a balanced range of steps; every `fl` steps
-// (<= 512 rows, the FP32 accumulation length in tensor memory) the accumulator is added into
-// the CTA's partial slot (a few FP32 adds per element, the slot stays in L2); the slots of
-// all CTAs of a tile are summed later in compensated FP32.
+// Persistent CTAs: the tiles' steps are laid out tile-major as one sequence (step x = tile *
+// nkc + kc) and split into gridDim.x balanced ranges, so every SM gets the same number of steps
+// whatever the tile count; a range meets at most two tiles (two segments). Every `fl` steps of
+// a segment (<= 512 rows, the FP32 accumulation length in tensor memory), and at its end, the
+// accumulator is added into the CTA's partial slot of that tile (a few FP32 adds per element,
+// the slot stays in L2); a tile's slot j belongs to the j-th CTA whose range meets the tile,
+// and the slots of a tile are summed later in compensated FP32.
 //
 // Pipeline: the costate rows arrive in a 4-slot shared-memory ring by bulk copies issued three
 // steps ahead by a control thread, which also issues the MMAs in step order. The staging is
@@ -35,16 +38,25 @@ __device__ __forceinline__ void red_add_f4(float4* p, float4 v) {
 }
 constexpr int WG_RING = 4;
 
+// The range of the tile-major step sequence (T steps, G ranges) that holds step x.
+__host__ __device__ inline int64_t wg_range_start(int64_t b, int64_t T, int64_t G) { return b * T / G; }
+__host__ __device__ inline int64_t wg_cta_of(int64_t x, int64_t T, int64_t G) {
+  int64_t b = x * G / T;
+  while (b + 1 < G && wg_range_start(b + 1, T, G) <= x) ++b;
+  while (b > 0 && wg_range_start(b, T, G) > x) --b;
+  return b;
+}
+
 struct WgArgs {
   const float* thetaJ;        // [P][n] float4 (theta, J_x, J_y, J_t)
   const float2* cs;           // [P][n] (cos, sin) of theta / 2
   const float* lam;           // costate rows: blocked [2 dim / 256][rtot][256] or rows [P][4][2 dim]
   int64_t rtot;               // rows of the blocked layout (0: row layout)
-  float* part;                // [ngroups][dim][2 dim], one slot per CTA of a tile
+  float* part;                // [nslots][dim][2 dim]: slot j of a tile is the j-th CTA meeting it
   int32_t n;
   int64_t npts[3], pt_base[3];
   int64_t kc_end[3];          // cumulative 16-row step counts per set
-  int32_t tiles, ngroups, spc, fl;  // tiles, CTAs per tile, flushes per CTA, steps per flush
+  int32_t tiles, nslots, fl;   // tiles, partial slots per tile, steps per flush
   int32_t* status;
   const int32_t* scal;        // FP16 operands: [2] float bits, bound of |R|, max |lambda|
 };
@@ -210,10 +222,33 @@ __global__ void __launch_bounds__(wgc_threads(H16), 1) dense_wgrad_gemm_kernel(W
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const bool ctrl = warp == NC * 8, prod = warp == NC * 8 + 1;
   const int MTC = wg_mtc(n), msub = MTC / TM, nj = MTC / 32;
-  const int tile = blockIdx.x % a.tiles, lb = blockIdx.x / a.tiles;
   const int nmt = dim / MTC;
-  const int mtile = tile % nmt, ntile = tile / nmt;
-  const int kbase = mtile * MTC;
+  // this CTA's range of the tile-major step sequence: steps v < vb in tile t0 (from its step
+  // kc00 on, slot slot0), the rest in tile t0 + 1 (from its first step: slot 0)
+  const int64_t nkc = a.kc_end[2];
+  const int64_t T = (int64_t)a.tiles * nkc, G = gridDim.x;
+  // range of this CTA: where the CTAs divide evenly over the tiles, neighbouring CTAs take
+  // different tiles (CTA b: tile b mod tiles)
+  const int64_t rb = G % a.tiles == 0 ? (int64_t)(blockIdx.x % a.tiles) * (G / a.tiles) + blockIdx.x / a.tiles
+                                      : (int64_t)blockIdx.x;
+  // (the host keeps tiles x steps below 2^31, so step counts are 32-bit)
+  const int64_t X0 = T > 0 ? wg_range_start(rb, T, G) : 0;
+  const int V = T > 0 ? (int)(wg_range_start(rb + 1, T, G) - X0) : 0;
+  const int t0 = V > 0 ? (int)(X0 / nkc) : 0;
+  const int kc00 = (int)(X0 - (int64_t)t0 * nkc);
+  const int vb = (int)nkc - kc00 < V ? (int)nkc - kc00 : V;
+  const int slot0 = V > 0 ? (int)(rb - wg_cta_of((int64_t)t0 * nkc, T, G)) : 0;
+  // step v: tile, step index in the tile, position and length of its segment, slot
+  // (for n <= 8 the host makes the grid a multiple of the tile count: every range then lies
+  // inside one tile, and the second segment is compiled out)
+  auto step_of = [&](int v, int& tile, int& kc, int& vs, int& slen, int& slot) {
+    const bool s1 = NQ >= 9 && v >= vb;
+    tile = t0 + (s1 ? 1 : 0);
+    kc = s1 ? v - vb : kc00 + v;
+    vs = s1 ? v - vb : v;
+    slen = s1 ? V - vb : vb;
+    slot = s1 ? 0 : slot0;
+  };
   uint64_t* bars = reinterpret_cast<uint64_t*>(sm + L.bars);
   uint64_t* mma_done = bars;          // [NC] MMAs of a crew's stage finished (commit)
   uint64_t* stage_full = bars + 3;    // [NC] a crew's operands written (its 8 warps)
@@ -235,28 +270,28 @@ __global__ void __launch_bounds__(wgc_threads(H16), 1) dense_wgrad_gemm_kernel(W
   __syncthreads();
   qptc::fence_after();
   const uint32_t tmem = *tslot;
-  const int64_t nkc = a.kc_end[2];
-  const int64_t c0 = (int64_t)lb * nkc / a.ngroups, c1 = (int64_t)(lb + 1) * nkc / a.ngroups;
-  // chunk boundaries staggered over the CTAs (the first chunk is shorter by 0 .. 7 eighths), so
-  // that the drains into L2 do not all fall at the same time
-  const int64_t choff = (int64_t)(blockIdx.x & 7) * a.fl / 8;
+  // chunk boundaries staggered over the CTAs (a segment's first chunk is shorter by 0 .. 7
+  // eighths), so that the drains into L2 do not all fall at the same time
+  const int choff = (int)(blockIdx.x & 7) * a.fl / 8;
   bool ok = true;
   if (prod) {
     // ---- producer thread: the costate rows of every step into the ring, once the slot's
     // previous step has been read
     if (lane == 0) {
-      int64_t last_copy = -1;
-      for (int64_t j = 0; c0 + j < c1 && ok; ++j) {
+      int last_copy = -1;
+      for (int j = 0; j < V && ok; ++j) {
         if (j >= WG_RING) ok = qptc::mbar_wait(&raw_free[j % WG_RING], (uint32_t)((j - WG_RING) / WG_RING) & 1);
         if (!ok) break;
+        int tile, slot, kc, vs, slen;
+        step_of(j, tile, kc, vs, slen, slot);
         qptc::fence_proxy_async();
-        wg_copy_rows(a, c0 + j, ntile, raw + (j % WG_RING) * (WKC * 256), &raw_full[j % WG_RING]);
+        wg_copy_rows(a, kc, tile / nmt, raw + (j % WG_RING) * (WKC * 256), &raw_full[j % WG_RING]);
         last_copy = j;
       }
       if (!ok) {
         atomicExch(a.status, 6);
         // let the copies in flight land before exiting
-        for (int64_t j = last_copy - (WG_RING - 1) < 0 ? 0 : last_copy - (WG_RING - 1); j <= last_copy; ++j)
+        for (int j = last_copy - (WG_RING - 1) < 0 ? 0 : last_copy - (WG_RING - 1); j <= last_copy; ++j)
           qptc::mbar_wait(&raw_full[j % WG_RING], (uint32_t)(j / WG_RING) & 1);
       }
     }
@@ -268,8 +303,10 @@ __global__ void __launch_bounds__(wgc_threads(H16), 1) dense_wgrad_gemm_kernel(W
       bool fresh = true;
       int chunk = 0;
       uint32_t it = 0;
-      for (int64_t kc = c0; kc < c1 && ok; ++kc, ++it) {
+      for (int v = 0; v < V && ok; ++v, ++it) {
         const uint32_t c = it % NC, lc = it / NC;
+        int tile, slot, kc, vs, slen;
+        step_of(v, tile, kc, vs, slen, slot);
         if (fresh && chunk > 0) ok = qptc::mbar_wait(acc_free, (uint32_t)(chunk - 1) & 1);
         if (!ok) break;
         ok = qptc::mbar_wait(&stage_full[c], lc & 1);
@@ -306,7 +343,7 @@ __global__ void __launch_bounds__(wgc_threads(H16), 1) dense_wgrad_gemm_kernel(W
         qptc::commit(&mma_done[c]);
         last_commit = it;
         fresh = false;
-        if ((kc - c0 + 1 + choff) % a.fl == 0 || kc + 1 == c1) {
+        if ((vs + 1 + choff) % a.fl == 0 || vs + 1 == slen) {
           fresh = true;
           ++chunk;
         }
@@ -327,12 +364,12 @@ __global__ void __launch_bounds__(wgc_threads(H16), 1) dense_wgrad_gemm_kernel(W
     unsigned char* sA = sm + crew * L.stage;
     unsigned char* sB = sA + L.a_bytes;
     // drain of the accumulator by this crew: lane quarter cw & 3, half cw >> 2 of the columns
-    auto flush = [&](bool add, bool zero) {
+    auto flush = [&](bool add, bool zero, int slot, int tile) {
       const int g = cw & 3, h = cw >> 2;
       const int u = msub == 2 ? h : 0;
       const int cbeg = msub == 2 ? 0 : h * 128, ncols = msub == 2 ? 256 : 128;
-      const int64_t krow = kbase + u * TM + g * 32 + lane;
-      float* outp = a.part + (((int64_t)lb * dim) + krow) * (2 * dim) + ntile * 256 + cbeg;
+      const int64_t krow = (int64_t)(tile % nmt) * MTC + u * TM + g * 32 + lane;
+      float* outp = a.part + (((int64_t)slot * dim) + krow) * (2 * dim) + (tile / nmt) * 256 + cbeg;
       if (!zero) {
         float v[32];
         for (int c = 0; c < ncols; c += 32) {
@@ -349,17 +386,38 @@ __global__ void __launch_bounds__(wgc_threads(H16), 1) dense_wgrad_gemm_kernel(W
         for (int c = 0; c < ncols; c += 4) *reinterpret_cast<float4*>(outp + c) = make_float4(0.f, 0.f, 0.f, 0.f);
       }
     };
+    // the slots no CTA writes of each tile whose first step this CTA holds: zero, so that the
+    // slot sum can take the same slot count for every tile
+    if (NQ >= 9 && crew == 0 && V > 0) {
+      for (int sg = 0; sg < 2; ++sg) {
+        if (sg == 1 && V <= vb) break;
+        if (sg == 0 && slot0 != 0) continue;
+        const int tz = t0 + sg;
+        const int64_t nmeet = wg_cta_of((int64_t)(tz + 1) * nkc - 1, T, G) - rb + 1;
+        for (int j = (int)nmeet; j < a.nslots; ++j) flush(false, true, j, tz);
+      }
+    }
     WgAng g{};
-    if (c0 + crew < c1) g = wg_load_ang(a, c0 + crew, ct, n);
+    int tile = 0, slot = 0, kc = 0, vs = 0, slen = 0;
+    if (crew < V) {
+      step_of(crew, tile, kc, vs, slen, slot);
+      g = wg_load_ang(a, kc, ct, n);
+    }
     uint32_t cnt = 0;
-    for (int64_t kc = c0 + crew; kc < c1; kc += NC, ++cnt) {
-      const uint32_t it = (uint32_t)(kc - c0);
+    for (int v = crew; v < V; v += NC, ++cnt) {
+      const uint32_t it = (uint32_t)v;
+      step_of(v, tile, kc, vs, slen, slot);
+      const int kbase = (tile % nmt) * MTC;
       int set, ppc, nvalid;
       int64_t p0;
       wg_step_geom(a, kc, set, p0, ppc, nvalid);
       // factors of this step, then the angles of the crew's next step
       wg_fac(fac, ct, n, ppc, g);
-      if (kc + NC < c1) g = wg_load_ang(a, kc + NC, ct, n);
+      if (v + NC < V) {
+        int tn, sn, kn, vn, ln;
+        step_of(v + NC, tn, kn, vn, ln, sn);
+        g = wg_load_ang(a, kn, ct, n);
+      }
       ok = qptc::bar_and(bar_id, WGC_CREW, ok);
       if (!ok) break;
       wgc_tables(fac, tab, ct, n, ppc, kbase, nj);
@@ -457,16 +515,16 @@ __global__ void __launch_bounds__(wgc_threads(H16), 1) dense_wgrad_gemm_kernel(W
       qptc::fence_proxy_async();
       __syncwarp();
       if (lane == 0) qptc::mbar_arrive(&stage_full[crew]);
-      if ((kc - c0 + 1 + choff) % a.fl == 0 || kc + 1 == c1) {
+      if ((vs + 1 + choff) % a.fl == 0 || vs + 1 == slen) {
         // the chunk's last step: drain once its MMAs (and so all earlier ones) finished
         if (good) good = qptc::mbar_wait(&mma_done[crew], cnt & 1);
         if (good) {
           qptc::fence_after();
-          flush((kc - c0 + choff) / a.fl > 0, false);
+          flush((vs + choff) / a.fl > 0, false, slot, tile);
         }
-        // the first drain stores, later ones add (in any order): the next chunk's drain (another
-        // crew) must see the stores
-        if ((kc - c0 + choff) / a.fl == 0) __threadfence();
+        // a segment's first drain stores, later ones add (in any order): the next chunk's drain
+        // (another crew) must see the stores
+        if ((vs + choff) / a.fl == 0) __threadfence();
         qptc::fence_before();
         __syncwarp();
         if (lane == 0) qptc::mbar_arrive(acc_free);
@@ -476,7 +534,6 @@ __global__ void __launch_bounds__(wgc_threads(H16), 1) dense_wgrad_gemm_kernel(W
     // a crew that stopped early tells its other warps through the barrier it left them in:
     // they time out on their own waits; the status records the failure
     if (!ok && lane == 0) atomicExch(a.status, 6);
-    if (ok && crew == 0 && c0 >= c1) flush(false, true);   // no rows: the slot still joins the sum
   }
   qptc::fence_before();
   __syncthreads();
