@@ -1186,6 +1186,7 @@ static qp_status dense_loss_grad(qp_plan* pl, const float* d_params, const float
     launches += 2;
   }
   int64_t base = 0;
+  int64_t red_nblk = -1;   // partial slots of the loss and head sums (-1: the plan's block count)
   if (fused) {
     // forward contraction with the pointwise stage as its epilogue (states stay on chip)
     qpd::FusedArgs fa;
@@ -1203,7 +1204,6 @@ static qp_status dense_loss_grad(qp_plan* pl, const float* d_params, const float
     fa.loss_stride = QP_NLP + pl->p.energy_nt;
     fa.grad_stride = pl->nE + 3 * pl->c.n_readout + 3;
     fa.nE = pl->nE;
-    fa.nblk = pl->blocks_grad;
     fa.status = (int32_t*)(ws + w.status);
     fa.scal = (int32_t*)(ws + w.status) + 16;
     fa.wait_limit = pl->wait_limit;
@@ -1212,6 +1212,8 @@ static qp_status dense_loss_grad(qp_plan* pl, const float* d_params, const float
     fa.nbc = npts0[2];
     const int64_t ftiles = fa.tile_end[2];
     const int fblocks = (int)(ftiles < pl->sm_count ? (ftiles > 0 ? ftiles : 1) : pl->sm_count);
+    fa.nblk = fblocks;   // one loss/head partial slot per CTA; the reduction sums these only
+    red_nblk = fblocks;
     prof_mark(pl, 0, true, s);
     alignas(64) CUtensorMap tmaps[3];
     std::memset(tmaps, 0, sizeof(tmaps));
@@ -1438,7 +1440,7 @@ static qp_status dense_loss_grad(qp_plan* pl, const float* d_params, const float
     launches += premap_bwd_launches(pl);
   }
   if (side && !pdl_tail && cudaStreamWaitEvent(s, pl->ev_join, 0) != cudaSuccess) return QP_ERR_CUDA;
-  st = launch_reduce(pl, w, d_params, npts0, d_loss, d_grad, mlp, s, nsym);
+  st = launch_reduce(pl, w, d_params, npts0, d_loss, d_grad, mlp, s, nsym, red_nblk);
   pl->last_launches = launches + 1;
   return st;
 }
@@ -1731,7 +1733,9 @@ static qp_status launch_reduce(qp_plan* pl, const WsLayout& w, const float* d_pa
   ra.norm_diel = pl->cur_norm[0] > 0 ? pl->cur_norm_diel : -1;
   ra.w_ic = pl->p.w_ic; ra.w_bc = pl->p.w_bc; ra.w_energy = pl->p.w_energy;
   const int64_t nwarps = pl->n_params + 1 + ra.nt;   // one warp per output
-  qpk::reduce_kernel<<<(unsigned)((nwarps + 7) / 8), 256, 0, s>>>(ra);
+  ra.nmain_blocks = (int32_t)((nwarps + 7) / 8);
+  ra.mlp_blocks = ra.mlp_count > 0 ? (int32_t)((ra.mlp_count + 31) / 32) : 0;
+  qpk::reduce_kernel<<<(unsigned)(ra.nmain_blocks + ra.mlp_blocks), 256, 0, s>>>(ra);
   return cuda_status(cudaGetLastError());
 }
 

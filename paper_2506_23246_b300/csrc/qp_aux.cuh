@@ -807,18 +807,56 @@ struct ReduceArgs {
   int64_t nc, ni, nb;          // mean denominators of the three sets
   int64_t norm_diel;           // whole-set points inside the disk, or -1: the counted ones
   float w_ic, w_bc, w_energy;
+  int32_t nmain_blocks;        // blocks of the one-warp-per-output part
+  int32_t mlp_blocks;          // blocks after them for the premap weights (0: warps per output)
+};
+
+// Compensated FP32 sum (Neumaier's variant of Kahan summation): s + c carries the sum of the
+// added values to about twice FP32 precision, on the FP32 pipes.
+struct CSum {
+  float s = 0.f, c = 0.f;
+  __device__ __forceinline__ void add(float x) {
+    const float t = s + x;
+    c += fabsf(s) >= fabsf(x) ? (s - t) + x : (x - t) + s;
+    s = t;
+  }
+  __device__ __forceinline__ void add(const CSum& o) { add(o.s); c += o.c; }
+  __device__ __forceinline__ float value() const { return s + c; }
+  __device__ __forceinline__ double dvalue() const { return (double)s + (double)c; }
 };
 
 // One warp per output: parameter gradients (the lanes split the block partials), then the
-// loss terms and the energy slices. FP64 sums.
+// loss terms and the energy slices; the premap weights in blocks of 32 consecutive outputs
+// after them (8 warps split the partial slots, each warp load one contiguous 128-byte row
+// piece). The FP32 gradient partials are summed per lane in compensated FP32 (B300's FP64
+// pipe is a small fraction of its FP32 rate), then across lanes in FP64; the FP64 loss and
+// energy partials in FP64.
 __device__ __forceinline__ double warp_sum_dbl(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
 }
 __global__ void reduce_kernel(ReduceArgs a) {
-  const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
+  if ((int)blockIdx.x >= a.nmain_blocks) {
+    // (the whole block takes this branch)
+    __shared__ double mpart[8][32];
+    const int w = threadIdx.x >> 5;
+    const int64_t wi = (int64_t)(blockIdx.x - a.nmain_blocks) * 32 + lane;
+    CSum t;
+    if (wi < a.mlp_count)
+      for (int b = w; b < a.nwblk; b += 8) t.add(a.wpart[(int64_t)b * a.nW + wi]);
+    mpart[w][lane] = t.dvalue();
+    __syncthreads();
+    if (w == 0 && wi < a.mlp_count) {
+      double sum = 0;
+#pragma unroll
+      for (int k = 0; k < 8; ++k) sum += mpart[k][lane];
+      a.grad[a.mlp_off + wi] = (float)sum;
+    }
+    return;
+  }
+  const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   if (gw < a.nparams) {
     const int64_t i = gw;
     float val = 0.f;
@@ -831,12 +869,12 @@ __global__ void reduce_kernel(ReduceArgs a) {
         const int64_t lq = (int64_t)l * a.n + w / a.k;
         const int kk = w % a.k;
         const float* c = a.cmat + (lq * 3 + kk) * 4;
-        double e0 = 0, e1 = 0, e2 = 0;
+        CSum s0, s1, s2;
         for (int b = lane; b < a.nblk; b += 32) {
           const float* g = a.blk_grad + (int64_t)b * a.grad_stride + lq * 3;
-          e0 += g[0]; e1 += g[1]; e2 += g[2];
+          s0.add(g[0]); s1.add(g[1]); s2.add(g[2]);
         }
-        e0 = warp_sum_dbl(e0); e1 = warp_sum_dbl(e1); e2 = warp_sum_dbl(e2);
+        const double e0 = warp_sum_dbl(s0.dvalue()), e1 = warp_sum_dbl(s1.dvalue()), e2 = warp_sum_dbl(s2.dvalue());
         val = (float)(c[0] * e0 + c[1] * e1 + c[2] * e2);
       } else {
         // CRZ(c, t) angle: generator |1><1|_c (x) Z_t = (Z_t - Z_c Z_t) / 2, so the gradient
@@ -846,24 +884,25 @@ __global__ void reduce_kernel(ReduceArgs a) {
         const int64_t base = 3LL * a.n * a.L + (int64_t)l * qp_crz_sums(a.ansatz, a.n);
         const int64_t ot = base + t;
         const int64_t oct = base + a.n + qp_pair_index(a.n, c < t ? c : t, c < t ? t : c);
-        double zt = 0, zct = 0;
+        CSum st, sct;
         for (int b = lane; b < a.nblk; b += 32) {
-          zt += a.blk_grad[(int64_t)b * a.grad_stride + ot];
-          zct += a.blk_grad[(int64_t)b * a.grad_stride + oct];
+          st.add(a.blk_grad[(int64_t)b * a.grad_stride + ot]);
+          sct.add(a.blk_grad[(int64_t)b * a.grad_stride + oct]);
         }
-        zt = warp_sum_dbl(zt); zct = warp_sum_dbl(zct);
+        const double zt = warp_sum_dbl(st.dvalue()), zct = warp_sum_dbl(sct.dvalue());
         val = (float)(0.5 * (zt - zct));
       }
     } else if (i >= a.head_off) {
       const int64_t hi = a.nE + (i - a.head_off);
-      double t = 0;
-      for (int b = lane; b < a.nblk; b += 32) t += a.blk_grad[(int64_t)b * a.grad_stride + hi];
-      val = (float)warp_sum_dbl(t);
+      CSum t;
+      for (int b = lane; b < a.nblk; b += 32) t.add(a.blk_grad[(int64_t)b * a.grad_stride + hi]);
+      val = (float)warp_sum_dbl(t.dvalue());
     } else if (i >= a.mlp_off && a.mlp_count > 0) {
+      if (a.mlp_blocks > 0) return;   // written by the premap-weight blocks
       const int64_t wi = i - a.mlp_off;
-      double t = 0;
-      for (int b = lane; b < a.nwblk; b += 32) t += a.wpart[(int64_t)b * a.nW + wi];
-      val = (float)warp_sum_dbl(t);
+      CSum t;
+      for (int b = lane; b < a.nwblk; b += 32) t.add(a.wpart[(int64_t)b * a.nW + wi]);
+      val = (float)warp_sum_dbl(t.dvalue());
     }
     if (lane == 0) a.grad[i] = val;
   } else if (gw == a.nparams) {

@@ -15,6 +15,7 @@
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
+#include "qp_aux.cuh"
 #include "qp_circuit.cuh"
 #include "qp_common.h"
 #include "qp_tc.cuh"
@@ -1244,16 +1245,7 @@ __device__ __forceinline__ void crz_sums_add(float* zs, int n, int k, float w) {
 
 // Compensated FP32 accumulation (Neumaier): s + c carries the sum to about twice FP32
 // precision without the FP64 pipe (conversions and FP64 adds are slow on this part).
-struct CSum {
-  float s = 0.f, c = 0.f;
-  __device__ __forceinline__ void add(float x) {
-    const float t = s + x;
-    c += fabsf(s) >= fabsf(x) ? (s - t) + x : (x - t) + s;
-    s = t;
-  }
-  __device__ __forceinline__ void add(const CSum& o) { add(o.s); c += o.c; }
-  __device__ __forceinline__ float value() const { return s + c; }
-};
+using qpk::CSum;   // compensated FP32 sum (qp_aux.cuh)
 
 // G[k][j] = conj(sum over partial slots of part[slot][k][2j + re|im]), in two passes: slot
 // groups (grid.y) each give a compensated partial (re sum, re carry, im sum, im carry), then
