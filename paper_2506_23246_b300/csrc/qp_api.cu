@@ -746,6 +746,7 @@ static qpm::MlpArgs mlp_layer_args(const qp_plan* pl, const float* d_params, con
   char* ws = (char*)pl->ws;
   qpm::MlpArgs m;
   std::memset(&m, 0, sizeof(m));
+  m.rpp = 4;
   for (int i = 0; i < 3; ++i) { m.pts[i] = pts[i]; m.npts[i] = npts[i]; }
   m.ptot = npts[0] + npts[1] + npts[2];
   m.omega = d_params;
@@ -816,13 +817,15 @@ static int ew_grid(const qp_plan* pl, int64_t n) {
 // Forward of the layer-by-layer premap: the RFF features of every point, then per layer the
 // contraction of all (point, s) rows as one library GEMM and its activation; the output layer
 // writes the angles and their Jacobian (and counts the dielectric set).
+// rpp: rows per point, 4 (values and input tangents) or 1 (values only: the caller reads no
+// input derivatives, so the layers' contractions run on a quarter of the rows)
 static qp_status launch_mlp_fwd(qp_plan* pl, const float* d_params, const float* const pts[3],
-                                const int64_t npts[3], const WsLayout& w, cudaStream_t s) {
+                                const int64_t npts[3], const WsLayout& w, cudaStream_t s, int rpp) {
   char* ws = (char*)pl->ws;
   const int64_t P = npts[0] + npts[1] + npts[2];
   const int D = pl->c.mlp_depth;
   if (4 * P > (int64_t)INT32_MAX) return QP_ERR_UNSUPPORTED;
-  const int R = (int)(4 * P);
+  const int R = (int)(rpp * P);
   qp_status st = mlp_blas_bind(pl, w, s);
   if (st != QP_OK) return st;
   float* X0 = (float*)(ws + w.mx0);
@@ -847,13 +850,15 @@ static qp_status launch_mlp_fwd(qp_plan* pl, const float* d_params, const float*
     qpm::mlp_wcopy_kernel<<<ew_grid(pl, most), 256, 0, s>>>(ca);
   }
   {
-    const qpm::MlpArgs m0 = mlp_layer_args(pl, d_params, pts, npts, w, 0);
+    qpm::MlpArgs m0 = mlp_layer_args(pl, d_params, pts, npts, w, 0);
+    m0.rpp = rpp;
     qpm::mlp_features_kernel<<<ew_grid(pl, P * 32), 256, (size_t)m0.F * (m0.period ? 6 : 3) * 4, s>>>(
         m0, X0, m0.ldi);   // pads zeroed
   }
   const bool fo = mlp_fused_out(pl);
   for (int l = 0; l <= (fo ? D - 1 : D); ++l) {
-    const qpm::MlpArgs m = mlp_layer_args(pl, d_params, pts, npts, w, l);
+    qpm::MlpArgs m = mlp_layer_args(pl, d_params, pts, npts, w, l);
+    m.rpp = rpp;
     const float* X = l == 0 ? X0 : m.act_in;
     float* Hl = l == D ? (float*)(ws + w.mcot) : m.act_out;
     // H[R][out] = X[R][in] W^T: column-major H^T = W X^T (padded sizes: the pads are zero)
@@ -863,14 +868,15 @@ static qp_status launch_mlp_fwd(qp_plan* pl, const float* d_params, const float*
     if (st != QP_OK) return st;
     if (fo && l == D - 1) {
       // the last hidden layer's activation with the output layer, per point
-      const qpm::MlpArgs mo = mlp_layer_args(pl, d_params, pts, npts, w, D);
+      qpm::MlpArgs mo = mlp_layer_args(pl, d_params, pts, npts, w, D);
+      mo.rpp = rpp;
       const size_t sm = (size_t)mo.out * mo.ldi * 4;
       if (mo.out <= 8)
         qpm::mlp_act_out_kernel<8><<<ew_grid(pl, P * 32), 256, sm, s>>>(mo, Hl, m.b);
       else
         qpm::mlp_act_out_kernel<16><<<ew_grid(pl, P * 32), 256, sm, s>>>(mo, Hl, m.b);
     } else if (l < D) {
-      qpm::mlp_act_kernel<<<ew_grid(pl, P * (m.ldo / 4)), 256, 0, s>>>(Hl, m.b, P, m.out, m.ldo);
+      qpm::mlp_act_kernel<<<ew_grid(pl, P * (m.ldo / 4)), 256, 0, s>>>(Hl, m.b, P, m.out, m.ldo, rpp);
     } else {
       qpm::mlp_out_kernel<<<ew_grid(pl, P * m.out), 256, 0, s>>>(Hl, m);
     }
@@ -983,8 +989,11 @@ static qp_status launch_mlp_bwd(qp_plan* pl, const float* d_params, const float*
 }
 
 // Shared prologue: gate preparation and premap forward for all point sets.
+// values_only: the caller reads no input derivatives (the layer-by-layer premap then carries one
+// row per point instead of four).
 static qp_status launch_front(qp_plan* pl, const float* d_params, const float* const pts[3],
-                              const int64_t npts[3], const WsLayout& w, cudaStream_t s, bool grad) {
+                              const int64_t npts[3], const WsLayout& w, cudaStream_t s, bool grad,
+                              bool values_only = false) {
   char* ws = (char*)pl->ws;
   const int n = pl->c.n_qubits, L = pl->c.n_layers;
   qpk::PrepArgs pa;
@@ -1011,7 +1020,7 @@ static qp_status launch_front(qp_plan* pl, const float* d_params, const float* c
   ma.disk_r = pl->p.disk_r; ma.disk_x0 = pl->p.disk_x0; ma.disk_y0 = pl->p.disk_y0;
   const int pblocks = (int)((ma.ptot + 127) / 128 < pl->sm_count * 8 ? (ma.ptot + 127) / 128 : pl->sm_count * 8);
   if (pl->c.premap == QP_PREMAP_RFF_MLP && pl->deep) {
-    return launch_mlp_fwd(pl, d_params, pts, npts, w, s);
+    return launch_mlp_fwd(pl, d_params, pts, npts, w, s, values_only && !grad ? 1 : 4);
   } else if (pl->c.premap == QP_PREMAP_RFF_MLP && pl->pg_ok) {
     // one tensor-core contraction per 128-point tile; the unit table is kept for the backward
     ma.u1 = grad ? (float*)(ws + w.u1) : nullptr;
@@ -1127,7 +1136,7 @@ static qp_status dense_loss_grad(qp_plan* pl, const float* d_params, const float
     // fields at the collocation points (set 0) and their mirrors (set 1), no derivatives
     const float* fp[3] = {pts0[0], xb + 3 * npts0[2], nullptr};
     const int64_t fn[3] = {npts0[0], nm, 0};
-    qp_status st = launch_front(pl, d_params, fp, fn, w, s, false);
+    qp_status st = launch_front(pl, d_params, fp, fn, w, s, false, true);
     if (st != QP_OK) return st;
     qpd::BuildArgs bp = ba;
     if (fwd16) bp.W = nullptr;
@@ -1459,7 +1468,7 @@ qp_status qp_forward(qp_plan* pl, const float* d_params, const float* d_pts, int
   pl->last_status = (const int32_t*)((char*)pl->ws + w.status);
   const float* pts[3] = {d_pts, nullptr, nullptr};
   const int64_t npts[3] = {B, 0, 0};
-  qp_status st = launch_front(pl, d_params, pts, npts, w, s, false);
+  qp_status st = launch_front(pl, d_params, pts, npts, w, s, false, d_dfields == nullptr);
   if (st != QP_OK) return st;
   if (dense_path(pl)) {
     char* ws = (char*)pl->ws;
@@ -1578,7 +1587,7 @@ qp_status qp_loss_grad(qp_plan* pl, const float* d_params, const qp_batch* batch
                              256, 0, s>>>(pts[0], npts[0], pts[2], npts[2], pl->p.medium, xb);
     const float* fp[3] = {pts[0], xb + 3 * npts[2], nullptr};
     const int64_t fn[3] = {npts[0], nm, 0};
-    qp_status st = launch_front(pl, d_params, fp, fn, w, s, false);
+    qp_status st = launch_front(pl, d_params, fp, fn, w, s, false, true);
     if (st != QP_OK) return st;
     QPCircArgs fa;
     fill_circ(pl, fa, w, d_params, fp, fn, false);

@@ -42,8 +42,10 @@ struct MlpArgs {
   const float* W;
   const float* b;
   int32_t in, out, ldi, ldo;
-  const float* act_in;      // previous layer's outputs [P][4][ldi] (null for the first layer)
-  float* act_out;           // hidden layer: its outputs [P][4][ldo]
+  const float* act_in;      // previous layer's outputs [P][rpp][ldi] (null for the first layer)
+  float* act_out;           // hidden layer: its outputs [P][rpp][ldo]
+  int32_t rpp;              // rows per point: 4 (value and x, y, t tangents) or 1 (values only,
+                            // a forward whose caller reads no input derivatives)
   // output layer
   int32_t scale;            // Eq. 27 scaling
   float* thetaJ;            // [P][out] float4 (theta, J_x, J_y, J_t)
@@ -163,8 +165,8 @@ __global__ void mlp_wcopy_kernel(MlpCopyArgs a) {
   if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicCAS(a.status, 0, 5);   // QP_ERR_NONFINITE
 }
 
-// RFF features of every point into X = [P][4][ld]: row s = 0 the features (cos of the first F
-// columns, sin of the next F), s = 1..3 their tangents; the pad columns 2F .. ld - 1 zeroed.
+// RFF features of every point into X = [P][rpp][ld]: row s = 0 the features (cos of the first F
+// columns, sin of the next F), s = 1..3 their tangents (rpp = 4); the pad columns zeroed.
 // One warp per point (the input map once per lane), lanes over the frequencies; Omega in
 // shared memory ([F][3] or [F][6] floats).
 __global__ void mlp_features_kernel(MlpArgs a, float* X, int ld) {
@@ -175,29 +177,32 @@ __global__ void mlp_features_kernel(MlpArgs a, float* X, int ld) {
   for (int64_t gp = warp_id_global(); gp < a.ptot; gp += warp_count_global()) {
     int set;
     const RffMap m = rff_map(a, mlp_point(a, gp, set));
-    float* r = X + gp * 4 * (int64_t)ld;
+    float* r = X + gp * a.rpp * (int64_t)ld;
     for (int f = lane; f < F; f += 32) {
       const float4 g = rff_arg(a, om, m, f);
       float sn, cs;
       sincosf(g.x, &sn, &cs);
       r[f] = cs; r[F + f] = sn;
-      r[ld + f] = -sn * g.y; r[ld + F + f] = cs * g.y;
-      r[2 * ld + f] = -sn * g.z; r[2 * ld + F + f] = cs * g.z;
-      r[3 * ld + f] = -sn * g.w; r[3 * ld + F + f] = cs * g.w;
+      if (a.rpp == 4) {
+        r[ld + f] = -sn * g.y; r[ld + F + f] = cs * g.y;
+        r[2 * ld + f] = -sn * g.z; r[2 * ld + F + f] = cs * g.z;
+        r[3 * ld + f] = -sn * g.w; r[3 * ld + F + f] = cs * g.w;
+      }
     }
-    for (int k = 2 * F + lane; k < ld; k += 32) r[k] = r[ld + k] = r[2 * ld + k] = r[3 * ld + k] = 0.f;
+    for (int k = 2 * F + lane; k < ld; k += 32)
+      for (int d = 0; d < a.rpp; ++d) r[d * ld + k] = 0.f;
   }
 }
 
-// Hidden layer after its contraction, in place on H = [P][4][ld] (pre-activations h0 - b and
+// Hidden layer after its contraction, in place on H = [P][rpp][ld] (pre-activations h0 - b and
 // pre-tangents z_d): y0 = tanh(h0), y_d = (1 - y0^2) z_d, four columns per thread.
-__global__ void mlp_act_kernel(float* H, const float* b, int64_t P, int out, int ld) {
+__global__ void mlp_act_kernel(float* H, const float* b, int64_t P, int out, int ld, int rpp) {
   const int ng = ld >> 2;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < P * ng; e += (int64_t)gridDim.x * blockDim.x) {
     int64_t p;
     int q;
     split_pq(e, ng, p, q);
-    float4* r = reinterpret_cast<float4*>(H + p * 4 * (int64_t)ld) + q;
+    float4* r = reinterpret_cast<float4*>(H + p * rpp * (int64_t)ld) + q;
     const int o = 4 * q;
     const float4 bb = make_float4(o < out ? __ldg(&b[o]) : 0.f, o + 1 < out ? __ldg(&b[o + 1]) : 0.f,
                                   o + 2 < out ? __ldg(&b[o + 2]) : 0.f, o + 3 < out ? __ldg(&b[o + 3]) : 0.f);
@@ -207,6 +212,7 @@ __global__ void mlp_act_kernel(float* H, const float* b, int64_t P, int out, int
     r[0] = h;
 #pragma unroll
     for (int d = 1; d < 4; ++d) {
+      if (d >= rpp) break;
       float4 z = r[d * ng];
       z.x *= sd.x; z.y *= sd.y; z.z *= sd.z; z.w *= sd.w;
       r[d * ng] = z;
@@ -221,12 +227,14 @@ __global__ void mlp_out_kernel(const float* H, MlpArgs a) {
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < a.ptot * n; e += (int64_t)gridDim.x * blockDim.x) {
     const int64_t gp = e / n;
     const int o = (int)(e - gp * n);
-    const float* r = H + gp * 4 * (int64_t)ld + o;
+    const float* r = H + gp * a.rpp * (int64_t)ld + o;
     const float h = r[0] + __ldg(&a.b[o]);
+    const bool tg = a.rpp == 4;
+    const float hx = tg ? r[ld] : 0.f, hy = tg ? r[2 * ld] : 0.f, ht = tg ? r[3 * ld] : 0.f;
     float g0, g1, g2;
     qpk::scale_tanh(a.scale, h, g0, g1, g2);
-    reinterpret_cast<float4*>(a.thetaJ)[e] = make_float4(g0, g1 * r[ld], g1 * r[2 * ld], g1 * r[3 * ld]);
-    reinterpret_cast<float4*>(a.hout)[e] = make_float4(h, r[ld], r[2 * ld], r[3 * ld]);
+    reinterpret_cast<float4*>(a.thetaJ)[e] = make_float4(g0, g1 * hx, g1 * hy, g1 * ht);
+    reinterpret_cast<float4*>(a.hout)[e] = make_float4(h, hx, hy, ht);
     if (o == 0 && a.medium == 1) {
       int set;
       const float* v = mlp_point(a, gp, set);
@@ -419,22 +427,23 @@ __global__ void __launch_bounds__(256) mlp_act_out_kernel(MlpArgs a, float* Hh, 
   const int64_t nw = warp_count_global();
   float4 yn[4];
   int64_t gp = warp_id_global();
+  const int rpp = a.rpp;
 #pragma unroll
   for (int d = 0; d < 4; ++d)
-    yn[d] = active && gp < a.ptot ? reinterpret_cast<const float4*>(Hh + gp * 4 * (int64_t)ld)[d * ng + q]
-                                  : make_float4(0.f, 0.f, 0.f, 0.f);
+    yn[d] = active && d < rpp && gp < a.ptot ? reinterpret_cast<const float4*>(Hh + gp * rpp * (int64_t)ld)[d * ng + q]
+                                             : make_float4(0.f, 0.f, 0.f, 0.f);
   for (; gp < a.ptot; gp += nw) {
     float acc[NMAX][4];
 #pragma unroll
     for (int j = 0; j < NMAX; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.f;
-    float4* r = reinterpret_cast<float4*>(Hh + gp * 4 * (int64_t)ld);
+    float4* r = reinterpret_cast<float4*>(Hh + gp * rpp * (int64_t)ld);
     float4 y[4];
 #pragma unroll
     for (int d = 0; d < 4; ++d) y[d] = yn[d];
     if (active && gp + nw < a.ptot) {
-      const float4* rn = reinterpret_cast<const float4*>(Hh + (gp + nw) * 4 * (int64_t)ld);
+      const float4* rn = reinterpret_cast<const float4*>(Hh + (gp + nw) * rpp * (int64_t)ld);
 #pragma unroll
-      for (int d = 0; d < 4; ++d) yn[d] = rn[d * ng + q];
+      for (int d = 0; d < 4; ++d) yn[d] = d < rpp ? rn[d * ng + q] : make_float4(0.f, 0.f, 0.f, 0.f);
     }
     if (active) {
       y[0].x = tanhf(y[0].x + bb.x); y[0].y = tanhf(y[0].y + bb.y);
@@ -444,7 +453,8 @@ __global__ void __launch_bounds__(256) mlp_act_out_kernel(MlpArgs a, float* Hh, 
 #pragma unroll
       for (int d = 1; d < 4; ++d) { y[d].x *= sd.x; y[d].y *= sd.y; y[d].z *= sd.z; y[d].w *= sd.w; }
 #pragma unroll
-      for (int d = 0; d < 4; ++d) r[d * ng + q] = y[d];
+      for (int d = 0; d < 4; ++d)
+        if (d < rpp) r[d * ng + q] = y[d];
 #pragma unroll
       for (int j = 0; j < NMAX; ++j) {
         if (j >= n) break;

@@ -651,6 +651,7 @@ def test_intuitive_dielectric_loss_grad(torch_cuda, oracle, n, path):
 
 
 @pytest.mark.parametrize("n,medium,path,depth", [(5, "vacuum", "auto", 1), (5, "dielectric", "auto", 1),
+                                                 (5, "dielectric", "simt", 2),
                                                  (8, "vacuum", "simt", 1), (8, "vacuum", "auto", 1),
                                                  (8, "dielectric", "gemm_split", 1), (7, "vacuum", "gemm_split", 2),
                                                  (9, "vacuum", "gemm_split", 1), (9, "dielectric", "gemm_split", 1)])
@@ -672,7 +673,7 @@ def test_symmetry_penalty_loss_grad(torch_cuda, oracle, n, medium, path, depth):
     assert plan.path == want and loss.shape[0] == 9 + 3 + 1 and loss[-1] > 0
 
 
-@pytest.mark.parametrize("n,path,depth", [(5, "simt", 2), (8, "gemm_split", 1), (7, "simt", 3)])
+@pytest.mark.parametrize("n,path,depth", [(5, "simt", 2), (8, "gemm_split", 1), (7, "simt", 3), (7, "gemm_split", 2)])
 def test_periodic_map_loss_grad(torch_cuda, oracle, n, path, depth):
     """The periodic input map (Eqs. 25-26: space over the domain lengths, time over a learned
     period T) before the RFF layer: fields and input derivatives, loss terms, and gradients
@@ -682,6 +683,8 @@ def test_periodic_map_loss_grad(torch_cuda, oracle, n, path, depth):
     params = W.init_params(circ, n + 100)
     pts = W.uniform_points(90, n + 101, 1.5)
     _forward_check(torch_cuda, oracle, circ, params, pts, path=path)
+    # fields only: a layer-by-layer premap then carries one row per point
+    _forward_check(torch_cuda, oracle, circ, params, pts, want_df=False, path=path)
     prob = W.problem("vacuum", w_energy=10.0, energy_slice=16, energy_nt=2)
     sets = {"colloc": W.uniform_points(40, n + 102, 1.5), "ic": W.ic_points_uniform(16, n + 103)}
     idx = _mlp_sample(oracle, circ, 6, n)
