@@ -37,7 +37,7 @@ extern "C" {
 typedef enum {
   QP_OK = 0,
   QP_ERR_INVALID_ARG = 1,      /* null pointer, bad enum value, inconsistent sizes */
-  QP_ERR_UNSUPPORTED = 2,      /* valid request outside what this build implements */
+  QP_ERR_UNSUPPORTED = 2,      /* valid request outside what this library implements */
   QP_ERR_BUFFER_TOO_SMALL = 3, /* workspace missing or smaller than qp_workspace_size */
   QP_ERR_CUDA = 4,             /* a CUDA runtime call failed (launch error, bad device) */
   QP_ERR_NONFINITE = 5,        /* the device saw a non-finite loss (reported via status) */
@@ -174,7 +174,7 @@ typedef struct qp_plan qp_plan;
 /* Create a plan for one circuit + problem. Host-only: validates the configuration and
  * builds the shared-memory schedule of the gate passes. *out receives the plan (owned
  * by the caller, free with qp_plan_destroy). Fails with QP_ERR_INVALID_ARG for bad
- * values and QP_ERR_UNSUPPORTED for valid ones this build does not implement. */
+ * values and QP_ERR_UNSUPPORTED for valid ones this library does not implement. */
 qp_status qp_plan_create(const qp_circuit* circuit, const qp_problem* problem, int32_t path,
                          qp_plan** out);
 void qp_plan_destroy(qp_plan* plan);

@@ -220,7 +220,7 @@ bool fused_path(const qp_plan* pl) {
 
 size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-// The driver's tensor-map encoder, through the runtime's entry-point query (no libcuda link).
+// The CUDA driver's tensor-map encoder, through the runtime's entry-point query (no libcuda link).
 PFN_cuTensorMapEncodeTiled_v12000 tmap_encoder() {
   static std::once_flag once;
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
