@@ -988,6 +988,12 @@ static qp_status launch_mlp_bwd(qp_plan* pl, const float* d_params, const float*
   return cuda_status(cudaGetLastError());
 }
 
+// The tensor-core premap forward also writes the half-angle factors (cos, sin) of theta / 2
+// that the tensor-core path's contractions read (otherwise a kernel of their own does).
+static bool front_writes_cs(const qp_plan* pl) {
+  return dense_path(pl) && pl->c.n_qubits >= 7 && pl->c.premap == QP_PREMAP_RFF_MLP && !pl->deep && pl->pg_ok;
+}
+
 // Shared prologue: gate preparation and premap forward for all point sets.
 // values_only: the caller reads no input derivatives (the layer-by-layer premap then carries one
 // row per point instead of four).
@@ -1024,6 +1030,7 @@ static qp_status launch_front(qp_plan* pl, const float* d_params, const float* c
   } else if (pl->c.premap == QP_PREMAP_RFF_MLP && pl->pg_ok) {
     // one tensor-core contraction per 128-point tile; the unit table is kept for the backward
     ma.u1 = grad ? (float*)(ws + w.u1) : nullptr;
+    if (front_writes_cs(pl)) ma.cs = (float2*)(ws + w.dcs);
     const int64_t nt = (ma.ptot + qpk::PT_M - 1) / qpk::PT_M;   // two CTAs per SM
     const int gb = (int)(nt < 2 * pl->sm_count ? (nt > 0 ? nt : 1) : 2 * pl->sm_count);
     qpk::premap_fwd_tc_kernel<<<gb, qpk::PT_THREADS, qpk::pt_smem(n).total, s>>>(ma);
@@ -1179,7 +1186,7 @@ static qp_status dense_loss_grad(qp_plan* pl, const float* d_params, const float
   qp_status st = launch_front(pl, d_params, pts, npts, w, s, true);
   if (st != QP_OK) return st;
   launches += front_launches(pl);
-  if (P > 0) {
+  if (P > 0 && !front_writes_cs(pl)) {
     const int64_t tot = P * n;
     const int hb = (int)((tot + 255) / 256 < pl->sm_count * 4 ? (tot + 255) / 256 : pl->sm_count * 4);
     qpd::dense_halfangle_kernel<<<hb, 256, 0, s>>>((const float4*)(ws + w.thetaJ), (float2*)(ws + w.dcs), tot);

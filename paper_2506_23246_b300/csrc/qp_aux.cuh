@@ -216,6 +216,7 @@ struct PremapArgs {
   const float* params;
   int32_t n, premap, scale, n_direct, F, H;
   float* thetaJ;          // [P][n][4]
+  float2* cs;             // [P][n] (cos, sin) of theta / 2 for the tensor-core path, or null
   const float* dthetaJ;   // [P][n][4] (backward)
   float* d1;              // [P][H][4] dL/dh1, dL/dh1_d
   float* d2;              // [P][n][4] dL/dh2, dL/dh2_d

@@ -232,6 +232,12 @@ __global__ void __launch_bounds__(PT_THREADS, 2) premap_fwd_tc_kernel(PremapArgs
             float g0, g1, g2;
             scale_tanh(a.scale, z0, g0, g1, g2);
             out[j] = make_float4(g0, g1 * (z[j].y + zo.y), g1 * (z[j].z + zo.z), g1 * (z[j].w + zo.w));
+            if (a.cs) {
+              // half-angle factors of the tensor-core path's product states
+              float sn, c;
+              sincosf(0.5f * g0, &sn, &c);
+              a.cs[gp * n + j] = make_float2(c, sn);
+            }
           }
       }
       // collocation points inside the dielectric disk, counted once per point
