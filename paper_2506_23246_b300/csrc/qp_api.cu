@@ -746,7 +746,7 @@ static qpm::MlpArgs mlp_layer_args(const qp_plan* pl, const float* d_params, con
   char* ws = (char*)pl->ws;
   qpm::MlpArgs m;
   std::memset(&m, 0, sizeof(m));
-  m.rpp = 4;
+  m.n4 = npts[0] + npts[1] + npts[2];   // four rows for every point unless a caller says otherwise
   for (int i = 0; i < 3; ++i) { m.pts[i] = pts[i]; m.npts[i] = npts[i]; }
   m.ptot = npts[0] + npts[1] + npts[2];
   m.omega = d_params;
@@ -817,15 +817,15 @@ static int ew_grid(const qp_plan* pl, int64_t n) {
 // Forward of the layer-by-layer premap: the RFF features of every point, then per layer the
 // contraction of all (point, s) rows as one library GEMM and its activation; the output layer
 // writes the angles and their Jacobian (and counts the dielectric set).
-// rpp: rows per point, 4 (values and input tangents) or 1 (values only: the caller reads no
-// input derivatives, so the layers' contractions run on a quarter of the rows)
+// n4: the first n4 points carry four rows (values and input tangents), the others one (no
+// later stage reads their input derivatives), so the layers' contractions run on 3 n4 + P rows
 static qp_status launch_mlp_fwd(qp_plan* pl, const float* d_params, const float* const pts[3],
-                                const int64_t npts[3], const WsLayout& w, cudaStream_t s, int rpp) {
+                                const int64_t npts[3], const WsLayout& w, cudaStream_t s, int64_t n4) {
   char* ws = (char*)pl->ws;
   const int64_t P = npts[0] + npts[1] + npts[2];
   const int D = pl->c.mlp_depth;
   if (4 * P > (int64_t)INT32_MAX) return QP_ERR_UNSUPPORTED;
-  const int R = (int)(rpp * P);
+  const int R = (int)(3 * n4 + P);
   qp_status st = mlp_blas_bind(pl, w, s);
   if (st != QP_OK) return st;
   float* X0 = (float*)(ws + w.mx0);
@@ -851,14 +851,14 @@ static qp_status launch_mlp_fwd(qp_plan* pl, const float* d_params, const float*
   }
   {
     qpm::MlpArgs m0 = mlp_layer_args(pl, d_params, pts, npts, w, 0);
-    m0.rpp = rpp;
+    m0.n4 = n4;
     qpm::mlp_features_kernel<<<ew_grid(pl, P * 32), 256, (size_t)m0.F * (m0.period ? 6 : 3) * 4, s>>>(
         m0, X0, m0.ldi);   // pads zeroed
   }
   const bool fo = mlp_fused_out(pl);
   for (int l = 0; l <= (fo ? D - 1 : D); ++l) {
     qpm::MlpArgs m = mlp_layer_args(pl, d_params, pts, npts, w, l);
-    m.rpp = rpp;
+    m.n4 = n4;
     const float* X = l == 0 ? X0 : m.act_in;
     float* Hl = l == D ? (float*)(ws + w.mcot) : m.act_out;
     // H[R][out] = X[R][in] W^T: column-major H^T = W X^T (padded sizes: the pads are zero)
@@ -869,14 +869,14 @@ static qp_status launch_mlp_fwd(qp_plan* pl, const float* d_params, const float*
     if (fo && l == D - 1) {
       // the last hidden layer's activation with the output layer, per point
       qpm::MlpArgs mo = mlp_layer_args(pl, d_params, pts, npts, w, D);
-      mo.rpp = rpp;
+      mo.n4 = n4;
       const size_t sm = (size_t)mo.out * mo.ldi * 4;
       if (mo.out <= 8)
         qpm::mlp_act_out_kernel<8><<<ew_grid(pl, P * 32), 256, sm, s>>>(mo, Hl, m.b);
       else
         qpm::mlp_act_out_kernel<16><<<ew_grid(pl, P * 32), 256, sm, s>>>(mo, Hl, m.b);
     } else if (l < D) {
-      qpm::mlp_act_kernel<<<ew_grid(pl, P * (m.ldo / 4)), 256, 0, s>>>(Hl, m.b, P, m.out, m.ldo, rpp);
+      qpm::mlp_act_kernel<<<ew_grid(pl, P * (m.ldo / 4)), 256, 0, s>>>(Hl, m.b, P, m.out, m.ldo, n4);
     } else {
       qpm::mlp_out_kernel<<<ew_grid(pl, P * m.out), 256, 0, s>>>(Hl, m);
     }
@@ -889,27 +889,29 @@ static qp_status launch_mlp_fwd(qp_plan* pl, const float* d_params, const float*
 // FP64 with the others): dW = cot^T X per chunk as one strided batched GEMM into aligned
 // scratch rows, the last partial chunk as one more GEMM, then copied into the slots (the unused
 // ones zeroed).
-static qp_status mlp_layer_dw(qp_plan* pl, const float* X, const float* cot, int64_t P, int in, int out,
+static qp_status mlp_layer_dw(qp_plan* pl, const float* X, const float* cot, int64_t P, int64_t n4, int in, int out,
                               int ldi, int ldo, int64_t w_off, int64_t b_off, const WsLayout& w, cudaStream_t s) {
   float* part = (float*)((char*)pl->ws + w.wpart);
   float* dw = (float*)((char*)pl->ws + w.mdw);
   const int64_t dws = mlp_dw_stride(pl);
   const int64_t nW = pl->mlp_count - pl->nfixed;
   const int nc = pl->nwblk;
-  const int64_t chunk = P > nc ? (P + nc - 1) / nc : 1;   // points per slot
-  const int64_t nfull = P / chunk, rest = P - nfull * chunk;
+  const int64_t chunk = P > nc ? (P + nc - 1) / nc : 1;   // points per slot (bias sums)
+  // dW sums over rows, whichever point they belong to: chunks of rc rows
+  const int64_t Rr = 3 * n4 + P;
+  const int rc = (int)(Rr > nc ? (Rr + nc - 1) / nc : 1);
+  const int64_t nfull = Rr / rc, rest = Rr - nfull * rc;
   const int used = (int)(nfull + (rest > 0 ? 1 : 0));
-  const int rc = (int)(4 * chunk);
   qp_status st = QP_OK;
   // column-major dW^T [in x out] = X_c^T (in x rc) . cot_c (rc x out), on the padded sizes
   if (nfull > 0)
     st = mlp_gemm(pl, CUBLAS_OP_N, CUBLAS_OP_T, ldi, ldo, rc, X, ldi, cot, ldo, dw, ldi,
                   (long long)rc * ldi, (long long)rc * ldo, (long long)dws, (int)nfull);
   if (st == QP_OK && rest > 0)
-    st = mlp_gemm(pl, CUBLAS_OP_N, CUBLAS_OP_T, ldi, ldo, (int)(4 * rest), X + nfull * rc * (int64_t)ldi, ldi,
+    st = mlp_gemm(pl, CUBLAS_OP_N, CUBLAS_OP_T, ldi, ldo, (int)rest, X + nfull * rc * (int64_t)ldi, ldi,
                   cot + nfull * rc * (int64_t)ldo, ldo, dw + nfull * dws, ldi);
   if (st != QP_OK) return st;
-  qpm::mlp_db_kernel<<<nc, qpm::DB_THREADS, 0, s>>>(cot, P, out, ldo, chunk, part, nW, b_off);
+  qpm::mlp_db_kernel<<<nc, qpm::DB_THREADS, 0, s>>>(cot, P, out, ldo, chunk, part, nW, b_off, n4);
   qpm::mlp_dw_slots_kernel<<<ew_grid(pl, (int64_t)nc * out * in), 256, 0, s>>>(dw, dws, ldi, part, nW, w_off, in,
                                                                                out, used, nc);
   return QP_OK;
@@ -927,7 +929,9 @@ static qp_status launch_mlp_bwd(qp_plan* pl, const float* d_params, const float*
   const int64_t mw = std::max(al4(H), al4(n));
   const int64_t nW = pl->mlp_count - pl->nfixed;
   if (4 * P > (int64_t)INT32_MAX) return QP_ERR_UNSUPPORTED;
-  const int R = (int)(4 * P);
+  // the forward's layout: four rows for the collocation points, one for the others
+  const int64_t n4 = npts[0];
+  const int R = (int)(3 * n4 + P);
   qp_status st = mlp_blas_bind(pl, w, s);
   if (st != QP_OK) return st;
   float* cot[2] = {(float*)(ws + w.mcot), (float*)(ws + w.mcot) + P * 4 * mw};
@@ -935,7 +939,8 @@ static qp_status launch_mlp_bwd(qp_plan* pl, const float* d_params, const float*
   const bool fo = mlp_fused_out(pl);
   if (fo) {
     // output layer, its weight gradient and the last hidden layer's tanh backward, per point
-    const qpm::MlpArgs mo = mlp_layer_args(pl, d_params, pts, npts, w, D);
+    qpm::MlpArgs mo = mlp_layer_args(pl, d_params, pts, npts, w, D);
+    mo.n4 = n4;
     int in, out;
     int64_t w_off, b_off;
     mlp_layer_geom(pl, D, in, out, w_off, b_off);
@@ -953,17 +958,18 @@ static qp_status launch_mlp_bwd(qp_plan* pl, const float* d_params, const float*
   } else {
     qpm::mlp_bwd_out_kernel<<<ew_grid(pl, P * al4(n)), 256, 0, s>>>((const float*)(ws + w.d2),
                                                                (const float*)(ws + w.dthetaJ), P, n, al4(n),
-                                                               pl->c.scale, cot[cur]);
+                                                               pl->c.scale, cot[cur], n4);
   }
   float* X0 = (float*)(ws + w.mx0);
   const float* Wc = (const float*)(ws + w.mwt);   // the forward's aligned weight copies
   for (int l = fo ? D - 1 : D; l >= 0; --l) {
-    const qpm::MlpArgs m = mlp_layer_args(pl, d_params, pts, npts, w, l);
+    qpm::MlpArgs m = mlp_layer_args(pl, d_params, pts, npts, w, l);
+    m.n4 = n4;
     int in, out;
     int64_t w_off, b_off;
     mlp_layer_geom(pl, l, in, out, w_off, b_off);
     const float* X = l == 0 ? X0 : m.act_in;
-    st = mlp_layer_dw(pl, X, cot[cur], P, in, out, m.ldi, m.ldo, w_off, b_off, w, s);
+    st = mlp_layer_dw(pl, X, cot[cur], P, n4, in, out, m.ldi, m.ldo, w_off, b_off, w, s);
     if (st != QP_OK) return st;
     if (l > 0 || pl->c.periodic) {
       // dU[R][in] = cot[R][out] W: column-major dU^T = W^T cot^T; for the first layer (periodic
@@ -974,7 +980,7 @@ static qp_status launch_mlp_bwd(qp_plan* pl, const float* d_params, const float*
                       m.ldo, dU, m.ldi);
       if (st != QP_OK) return st;
       if (l > 0) {
-        qpm::mlp_dact_kernel<<<ew_grid(pl, P * (m.ldi / 4)), 256, 0, s>>>(dU, m.act_in, P, m.ldi);
+        qpm::mlp_dact_kernel<<<ew_grid(pl, P * (m.ldi / 4)), 256, 0, s>>>(dU, m.act_in, P, m.ldi, n4);
         cur ^= 1;
         continue;
       }
@@ -1026,7 +1032,7 @@ static qp_status launch_front(qp_plan* pl, const float* d_params, const float* c
   ma.disk_r = pl->p.disk_r; ma.disk_x0 = pl->p.disk_x0; ma.disk_y0 = pl->p.disk_y0;
   const int pblocks = (int)((ma.ptot + 127) / 128 < pl->sm_count * 8 ? (ma.ptot + 127) / 128 : pl->sm_count * 8);
   if (pl->c.premap == QP_PREMAP_RFF_MLP && pl->deep) {
-    return launch_mlp_fwd(pl, d_params, pts, npts, w, s, values_only && !grad ? 1 : 4);
+    return launch_mlp_fwd(pl, d_params, pts, npts, w, s, values_only && !grad ? 0 : npts[0]);
   } else if (pl->c.premap == QP_PREMAP_RFF_MLP && pl->pg_ok) {
     // one tensor-core contraction per 128-point tile; the unit table is kept for the backward
     ma.u1 = grad ? (float*)(ws + w.u1) : nullptr;

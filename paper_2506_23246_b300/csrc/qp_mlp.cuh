@@ -42,10 +42,10 @@ struct MlpArgs {
   const float* W;
   const float* b;
   int32_t in, out, ldi, ldo;
-  const float* act_in;      // previous layer's outputs [P][rpp][ldi] (null for the first layer)
-  float* act_out;           // hidden layer: its outputs [P][rpp][ldo]
-  int32_t rpp;              // rows per point: 4 (value and x, y, t tangents) or 1 (values only,
-                            // a forward whose caller reads no input derivatives)
+  const float* act_in;      // previous layer's outputs, rows by mlp_row (null for the first layer)
+  float* act_out;           // hidden layer: its outputs, rows by mlp_row
+  int64_t n4;               // the first n4 points carry four rows (value and x, y, t tangents),
+                            // the others one (no later stage reads their input derivatives)
   // output layer
   int32_t scale;            // Eq. 27 scaling
   float* thetaJ;            // [P][out] float4 (theta, J_x, J_y, J_t)
@@ -55,6 +55,9 @@ struct MlpArgs {
   int32_t medium;
   float disk_r, disk_x0, disk_y0;
 };
+
+// First row of point gp in a row buffer: four rows for each of the first n4 points, then one.
+__host__ __device__ __forceinline__ int64_t mlp_row(int64_t gp, int64_t n4) { return gp < n4 ? 4 * gp : 3 * n4 + gp; }
 
 __device__ __forceinline__ const float* mlp_point(const MlpArgs& a, int64_t gp, int& set) {
   set = 0;
@@ -165,8 +168,8 @@ __global__ void mlp_wcopy_kernel(MlpCopyArgs a) {
   if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicCAS(a.status, 0, 5);   // QP_ERR_NONFINITE
 }
 
-// RFF features of every point into X = [P][rpp][ld]: row s = 0 the features (cos of the first F
-// columns, sin of the next F), s = 1..3 their tangents (rpp = 4); the pad columns zeroed.
+// RFF features of every point into X (rows by mlp_row): row s = 0 the features (cos of the
+// first F columns, sin of the next F), s = 1..3 their tangents (four-row points); pads zeroed.
 // One warp per point (the input map once per lane), lanes over the frequencies; Omega in
 // shared memory ([F][3] or [F][6] floats).
 __global__ void mlp_features_kernel(MlpArgs a, float* X, int ld) {
@@ -177,32 +180,33 @@ __global__ void mlp_features_kernel(MlpArgs a, float* X, int ld) {
   for (int64_t gp = warp_id_global(); gp < a.ptot; gp += warp_count_global()) {
     int set;
     const RffMap m = rff_map(a, mlp_point(a, gp, set));
-    float* r = X + gp * a.rpp * (int64_t)ld;
+    float* r = X + mlp_row(gp, a.n4) * (int64_t)ld;
+    const int nr = gp < a.n4 ? 4 : 1;
     for (int f = lane; f < F; f += 32) {
       const float4 g = rff_arg(a, om, m, f);
       float sn, cs;
       sincosf(g.x, &sn, &cs);
       r[f] = cs; r[F + f] = sn;
-      if (a.rpp == 4) {
+      if (nr == 4) {
         r[ld + f] = -sn * g.y; r[ld + F + f] = cs * g.y;
         r[2 * ld + f] = -sn * g.z; r[2 * ld + F + f] = cs * g.z;
         r[3 * ld + f] = -sn * g.w; r[3 * ld + F + f] = cs * g.w;
       }
     }
     for (int k = 2 * F + lane; k < ld; k += 32)
-      for (int d = 0; d < a.rpp; ++d) r[d * ld + k] = 0.f;
+      for (int d = 0; d < nr; ++d) r[d * ld + k] = 0.f;
   }
 }
 
-// Hidden layer after its contraction, in place on H = [P][rpp][ld] (pre-activations h0 - b and
-// pre-tangents z_d): y0 = tanh(h0), y_d = (1 - y0^2) z_d, four columns per thread.
-__global__ void mlp_act_kernel(float* H, const float* b, int64_t P, int out, int ld, int rpp) {
+// Hidden layer after its contraction, in place on H (rows by mlp_row; pre-activations h0 - b
+// and pre-tangents z_d): y0 = tanh(h0), y_d = (1 - y0^2) z_d, four columns per thread.
+__global__ void mlp_act_kernel(float* H, const float* b, int64_t P, int out, int ld, int64_t n4) {
   const int ng = ld >> 2;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < P * ng; e += (int64_t)gridDim.x * blockDim.x) {
     int64_t p;
     int q;
     split_pq(e, ng, p, q);
-    float4* r = reinterpret_cast<float4*>(H + p * rpp * (int64_t)ld) + q;
+    float4* r = reinterpret_cast<float4*>(H + mlp_row(p, n4) * (int64_t)ld) + q;
     const int o = 4 * q;
     const float4 bb = make_float4(o < out ? __ldg(&b[o]) : 0.f, o + 1 < out ? __ldg(&b[o + 1]) : 0.f,
                                   o + 2 < out ? __ldg(&b[o + 2]) : 0.f, o + 3 < out ? __ldg(&b[o + 3]) : 0.f);
@@ -212,7 +216,7 @@ __global__ void mlp_act_kernel(float* H, const float* b, int64_t P, int out, int
     r[0] = h;
 #pragma unroll
     for (int d = 1; d < 4; ++d) {
-      if (d >= rpp) break;
+      if (p >= n4) break;
       float4 z = r[d * ng];
       z.x *= sd.x; z.y *= sd.y; z.z *= sd.z; z.w *= sd.w;
       r[d * ng] = z;
@@ -227,9 +231,9 @@ __global__ void mlp_out_kernel(const float* H, MlpArgs a) {
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < a.ptot * n; e += (int64_t)gridDim.x * blockDim.x) {
     const int64_t gp = e / n;
     const int o = (int)(e - gp * n);
-    const float* r = H + gp * a.rpp * (int64_t)ld + o;
+    const float* r = H + mlp_row(gp, a.n4) * (int64_t)ld + o;
     const float h = r[0] + __ldg(&a.b[o]);
-    const bool tg = a.rpp == 4;
+    const bool tg = gp < a.n4;
     const float hx = tg ? r[ld] : 0.f, hy = tg ? r[2 * ld] : 0.f, ht = tg ? r[3 * ld] : 0.f;
     float g0, g1, g2;
     qpk::scale_tanh(a.scale, h, g0, g1, g2);
@@ -249,13 +253,15 @@ __global__ void mlp_out_kernel(const float* H, MlpArgs a) {
 // Output layer backward, per (point, qubit): cotangents of (h, h_x, h_y, h_t) from dL/dtheta,
 // dL/dJ_d, into cot = [P][4][ld] (pad columns zero).
 __global__ void mlp_bwd_out_kernel(const float* hout, const float* dthetaJ, int64_t ptot, int n, int ld, int scale,
-                                   float* cot) {
+                                   float* cot, int64_t n4) {
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < ptot * ld; e += (int64_t)gridDim.x * blockDim.x) {
     const int64_t p = e / ld;
     const int j = (int)(e - p * ld);
+    float* c = cot + mlp_row(p, n4) * (int64_t)ld + j;
+    const bool tg = p < n4;
     if (j >= n) {
-      float* c = cot + p * 4 * (int64_t)ld + j;
-      c[0] = c[ld] = c[2 * ld] = c[3 * ld] = 0.f;
+      c[0] = 0.f;
+      if (tg) c[ld] = c[2 * ld] = c[3 * ld] = 0.f;
       continue;
     }
     const int64_t en = p * n + j;
@@ -263,25 +269,33 @@ __global__ void mlp_bwd_out_kernel(const float* hout, const float* dthetaJ, int6
     const float4 d = reinterpret_cast<const float4*>(dthetaJ)[en];
     float g0, g1, g2;
     qpk::scale_tanh(scale, h.x, g0, g1, g2);
-    float* c = cot + p * 4 * (int64_t)ld + j;
     c[0] = g1 * d.x + g2 * (h.y * d.y + h.z * d.z + h.w * d.w);
-    c[ld] = g1 * d.y;
-    c[2 * ld] = g1 * d.z;
-    c[3 * ld] = g1 * d.w;
+    if (tg) {
+      c[ld] = g1 * d.y;
+      c[2 * ld] = g1 * d.z;
+      c[3 * ld] = g1 * d.w;
+    }
   }
 }
 
 // Through a hidden layer's tanh, in place on dU = [P][4][ld] (cotangents of its outputs y0,
 // y_d) with its stored outputs act = [P][4][ld]: dH0 = s dU0 - 2 y0 sum_d y_d dU_d,
 // dZ_d = s dU_d, four columns per thread.
-__global__ void mlp_dact_kernel(float* dU, const float* act, int64_t P, int ld) {
+__global__ void mlp_dact_kernel(float* dU, const float* act, int64_t P, int ld, int64_t n4) {
   const int ng = ld >> 2;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < P * ng; e += (int64_t)gridDim.x * blockDim.x) {
     int64_t p;
     int q;
     split_pq(e, ng, p, q);
-    float4* u = reinterpret_cast<float4*>(dU + p * 4 * (int64_t)ld) + q;
-    const float4* y = reinterpret_cast<const float4*>(act + p * 4 * (int64_t)ld) + q;
+    float4* u = reinterpret_cast<float4*>(dU + mlp_row(p, n4) * (int64_t)ld) + q;
+    const float4* y = reinterpret_cast<const float4*>(act + mlp_row(p, n4) * (int64_t)ld) + q;
+    if (p >= n4) {
+      // one-row point: dH0 = s dU0
+      const float4 y0 = y[0], u0 = u[0];
+      u[0] = make_float4((1.f - y0.x * y0.x) * u0.x, (1.f - y0.y * y0.y) * u0.y, (1.f - y0.z * y0.z) * u0.z,
+                         (1.f - y0.w * y0.w) * u0.w);
+      continue;
+    }
     const float4 y0 = y[0], y1 = y[ng], y2 = y[2 * ng], y3 = y[3 * ng];
     const float4 u0 = u[0];
     float4 u1 = u[ng], u2 = u[2 * ng], u3 = u[3 * ng];
@@ -306,7 +320,8 @@ __global__ void mlp_dact_kernel(float* dU, const float* act, int64_t P, int ld) 
 // columns x 8 point lanes, summed in shared memory.
 constexpr int DB_THREADS = 512;
 __global__ void __launch_bounds__(DB_THREADS) mlp_db_kernel(const float* cot, int64_t P, int out, int ld,
-                                                           int64_t chunk, float* part, int64_t nW, int64_t b_off) {
+                                                           int64_t chunk, float* part, int64_t nW, int64_t b_off,
+                                                           int64_t n4) {
   __shared__ float red[8][64];
   const int c = blockIdx.x, ol = threadIdx.x & 63, j = threadIdx.x >> 6;
   const int64_t p0 = (int64_t)c * chunk, p1 = p0 + chunk < P ? p0 + chunk : P;
@@ -314,7 +329,7 @@ __global__ void __launch_bounds__(DB_THREADS) mlp_db_kernel(const float* cot, in
     const int o = o0 + ol;
     float acc = 0.f;
     if (o < out)
-      for (int64_t p = p0 + j; p < p1; p += 8) acc += cot[p * 4 * (int64_t)ld + o];
+      for (int64_t p = p0 + j; p < p1; p += 8) acc += cot[mlp_row(p, n4) * (int64_t)ld + o];
     red[j][ol] = acc;
     __syncthreads();
     if (j == 0 && o < out) {
@@ -353,7 +368,8 @@ __global__ void mlp_period_kernel(const float* dX, MlpArgs a, int ld, double* tg
   for (int64_t gp = warp_id_global(); gp < a.ptot; gp += warp_count_global()) {
     int set;
     const RffMap m = rff_map(a, mlp_point(a, gp, set));
-    const float* r = dX + gp * 4 * (int64_t)ld;
+    const float* r = dX + mlp_row(gp, a.n4) * (int64_t)ld;
+    const int nr = gp < a.n4 ? 4 : 1;
     for (int f0 = 0; f0 < F; f0 += 128) {
       float x[4][8];
 #pragma unroll
@@ -361,8 +377,8 @@ __global__ void mlp_period_kernel(const float* dX, MlpArgs a, int ld, double* tg
         const int f = f0 + lane + 32 * i;
 #pragma unroll
         for (int d = 0; d < 4; ++d) {
-          x[i][d] = f < F ? r[d * ld + f] : 0.f;
-          x[i][4 + d] = f < F ? r[d * ld + F + f] : 0.f;
+          x[i][d] = f < F && d < nr ? r[d * ld + f] : 0.f;
+          x[i][4 + d] = f < F && d < nr ? r[d * ld + F + f] : 0.f;
         }
       }
 #pragma unroll
@@ -427,23 +443,28 @@ __global__ void __launch_bounds__(256) mlp_act_out_kernel(MlpArgs a, float* Hh, 
   const int64_t nw = warp_count_global();
   float4 yn[4];
   int64_t gp = warp_id_global();
-  const int rpp = a.rpp;
+  {
+    const int nr = gp < a.n4 ? 4 : 1;
 #pragma unroll
-  for (int d = 0; d < 4; ++d)
-    yn[d] = active && d < rpp && gp < a.ptot ? reinterpret_cast<const float4*>(Hh + gp * rpp * (int64_t)ld)[d * ng + q]
-                                             : make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int d = 0; d < 4; ++d)
+      yn[d] = active && d < nr && gp < a.ptot
+                  ? reinterpret_cast<const float4*>(Hh + mlp_row(gp, a.n4) * (int64_t)ld)[d * ng + q]
+                  : make_float4(0.f, 0.f, 0.f, 0.f);
+  }
   for (; gp < a.ptot; gp += nw) {
     float acc[NMAX][4];
 #pragma unroll
     for (int j = 0; j < NMAX; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.f;
-    float4* r = reinterpret_cast<float4*>(Hh + gp * rpp * (int64_t)ld);
+    float4* r = reinterpret_cast<float4*>(Hh + mlp_row(gp, a.n4) * (int64_t)ld);
+    const int rpp = gp < a.n4 ? 4 : 1;
     float4 y[4];
 #pragma unroll
     for (int d = 0; d < 4; ++d) y[d] = yn[d];
     if (active && gp + nw < a.ptot) {
-      const float4* rn = reinterpret_cast<const float4*>(Hh + (gp + nw) * rpp * (int64_t)ld);
+      const float4* rn = reinterpret_cast<const float4*>(Hh + mlp_row(gp + nw, a.n4) * (int64_t)ld);
+      const int nrn = gp + nw < a.n4 ? 4 : 1;
 #pragma unroll
-      for (int d = 0; d < 4; ++d) yn[d] = d < rpp ? rn[d * ng + q] : make_float4(0.f, 0.f, 0.f, 0.f);
+      for (int d = 0; d < 4; ++d) yn[d] = d < nrn ? rn[d * ng + q] : make_float4(0.f, 0.f, 0.f, 0.f);
     }
     if (active) {
       y[0].x = tanhf(y[0].x + bb.x); y[0].y = tanhf(y[0].y + bb.y);
@@ -528,9 +549,11 @@ __global__ void __launch_bounds__(256, 2) mlp_out_bwd_kernel(MlpArgs a, const fl
   float4 yn[4], hn = make_float4(0.f, 0.f, 0.f, 0.f), dn = hn;
   {
     const int64_t gp = p0 + warp;
-    const float4* y4 = reinterpret_cast<const float4*>(act + gp * 4 * (int64_t)ld);
+    const float4* y4 = reinterpret_cast<const float4*>(act + mlp_row(gp, a.n4) * (int64_t)ld);
+    const int nr = gp < a.n4 ? 4 : 1;
 #pragma unroll
-    for (int d = 0; d < 4; ++d) yn[d] = active && gp < p1 ? y4[d * ng + lane] : make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int d = 0; d < 4; ++d)
+      yn[d] = active && gp < p1 && d < nr ? y4[d * ng + lane] : make_float4(0.f, 0.f, 0.f, 0.f);
     if (lane < n && gp < p1) {
       hn = reinterpret_cast<const float4*>(hout)[gp * n + lane];
       dn = reinterpret_cast<const float4*>(dthetaJ)[gp * n + lane];
@@ -546,10 +569,11 @@ __global__ void __launch_bounds__(256, 2) mlp_out_bwd_kernel(MlpArgs a, const fl
     const float4 h = hn, d = dn;
     if (gp + nwarp < p1) {
       const int64_t g2 = gp + nwarp;
-      const float4* y4 = reinterpret_cast<const float4*>(act + g2 * 4 * (int64_t)ld);
+      const float4* y4 = reinterpret_cast<const float4*>(act + mlp_row(g2, a.n4) * (int64_t)ld);
+      const int nr2 = g2 < a.n4 ? 4 : 1;
       if (active) {
 #pragma unroll
-        for (int k = 0; k < 4; ++k) yn[k] = y4[k * ng + lane];
+        for (int k = 0; k < 4; ++k) yn[k] = k < nr2 ? y4[k * ng + lane] : make_float4(0.f, 0.f, 0.f, 0.f);
       }
       if (lane < n) {
         hn = reinterpret_cast<const float4*>(hout)[g2 * n + lane];
@@ -583,7 +607,7 @@ __global__ void __launch_bounds__(256, 2) mlp_out_bwd_kernel(MlpArgs a, const fl
     }
     if (active) {
       // tanh backward: dH0 = s dU0 - 2 y0 sum_d y_d dU_d, dZ_d = s dU_d
-      float4* c4 = reinterpret_cast<float4*>(cot + gp * 4 * (int64_t)ld);
+      float4* c4 = reinterpret_cast<float4*>(cot + mlp_row(gp, a.n4) * (int64_t)ld);
       const float4 sd = make_float4(1.f - y[0].x * y[0].x, 1.f - y[0].y * y[0].y, 1.f - y[0].z * y[0].z,
                                     1.f - y[0].w * y[0].w);
       float4 h0;
@@ -592,9 +616,11 @@ __global__ void __launch_bounds__(256, 2) mlp_out_bwd_kernel(MlpArgs a, const fl
       h0.z = sd.z * u[0].z - 2.f * y[0].z * (y[1].z * u[1].z + y[2].z * u[2].z + y[3].z * u[3].z);
       h0.w = sd.w * u[0].w - 2.f * y[0].w * (y[1].w * u[1].w + y[2].w * u[2].w + y[3].w * u[3].w);
       c4[lane] = h0;
+      if (gp < a.n4) {
 #pragma unroll
-      for (int d = 1; d < 4; ++d)
-        c4[d * ng + lane] = make_float4(sd.x * u[d].x, sd.y * u[d].y, sd.z * u[d].z, sd.w * u[d].w);
+        for (int d = 1; d < 4; ++d)
+          c4[d * ng + lane] = make_float4(sd.x * u[d].x, sd.y * u[d].y, sd.z * u[d].z, sd.w * u[d].w);
+      }
     }
   }
   // block sums of dW and db, then the slot
